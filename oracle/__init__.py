@@ -1,0 +1,289 @@
+"""FP64 CPU oracle for CPTR/CPR-preconditioned FGMRES (arXiv 1907.04229) -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+this package.  The CUDA library never calls it and shares no code with it.  ``oracle.c`` holds the
+arithmetic (every step cites the paper's passage); this module only compiles it and marshals
+numpy arrays.
+
+Parity status of each oracle function is pinned by ``tests/test_oracle_pins.py``; nothing here is
+"parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+CPTR_FULL, CPTR_UPPER, CPTR_LOWER, BD, CPR, NONE1 = range(6)
+ILU0, NONE2 = 0, 1
+SCHUR_GIVEN, SCHUR_ATT = 0, 1
+L1, JACOBI = 0, 1
+
+
+def build(force: bool = False) -> str:
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
+        tmp = _LIB_PATH + ".tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("stage1", ctypes.c_int32), ("stage2", ctypes.c_int32), ("schur", ctypes.c_int32),
+                ("smoother", ctypes.c_int32), ("omega", ctypes.c_double), ("theta", ctypes.c_double),
+                ("n_coarse", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("max_it", ctypes.c_int32), ("dense_max", ctypes.c_int32), ("seed", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("est_rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double),
+                ("bnorm", ctypes.c_double)]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        lib.or_create.restype = P
+        lib.or_create.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P, P, ctypes.c_int32, ctypes.c_int32,
+                                  P, P, P, P]
+        lib.or_status.restype = ctypes.c_int
+        lib.or_status.argtypes = [P]
+        lib.or_destroy.restype = None
+        lib.or_destroy.argtypes = [P]
+        lib.or_solve.restype = ctypes.c_int
+        lib.or_solve.argtypes = [P, P, P, ctypes.c_double, P]
+        for name in ("or_precond", "or_stage1", "or_ilu_apply", "or_spmv", "or_weight_rhs"):
+            getattr(lib, name).restype = None
+            getattr(lib, name).argtypes = [P, P, P]
+        lib.or_vcycle.restype = None
+        lib.or_vcycle.argtypes = [P, ctypes.c_int, P, P]
+        lib.or_nlevels.restype = ctypes.c_int
+        lib.or_nlevels.argtypes = [P, ctypes.c_int]
+        lib.or_hier_level_info.restype = None
+        lib.or_hier_level_info.argtypes = [P, ctypes.c_int, P]
+        lib.or_hier_level_get.restype = None
+        lib.or_hier_level_get.argtypes = [P, ctypes.c_int] + [P] * 8
+        lib.or_hierarchy.restype = P
+        lib.or_hierarchy.argtypes = [P, ctypes.c_int]
+        lib.or_amg_create.restype = P
+        lib.or_amg_create.argtypes = [ctypes.c_int32, P, P, P, P, P]
+        lib.or_amg_destroy.restype = None
+        lib.or_amg_destroy.argtypes = [P]
+        lib.or_amg_vcycle.restype = None
+        lib.or_amg_vcycle.argtypes = [P, P, P]
+        lib.or_amg_nlevels.restype = ctypes.c_int
+        lib.or_amg_nlevels.argtypes = [P]
+        lib.or_nnz.restype = ctypes.c_int32
+        lib.or_nnz.argtypes = [P]
+        lib.or_matrix.restype = None
+        lib.or_matrix.argtypes = [P, P, P, P]
+        lib.or_ilu_factors.restype = None
+        lib.or_ilu_factors.argtypes = [P, P]
+        lib.or_field.restype = None
+        lib.or_field.argtypes = [P, ctypes.c_int, P]
+        lib.or_splitmix64.restype = ctypes.c_uint64
+        lib.or_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts(stage1=CPTR_FULL, stage2=ILU0, schur=SCHUR_GIVEN, smoother=L1, omega=2.0 / 3.0, theta=0.25,
+             n_coarse=256, max_levels=25, restart=30, max_it=1000, dense_max=1024, seed=0)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Oracle:
+    """One CPTR/CPR-FGMRES setup on a BSR Jacobian (raw rows, weights applied inside)."""
+
+    def __init__(self, n, b, row_ptr, col_idx, vals, weights=None, ps=0, ts=1, st=None, st_pattern=None, **opts):
+        lib = _load()
+        self.n, self.b = int(n), int(b)
+        self._keep = []
+
+        def keep(a, dt):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=dt)
+            self._keep.append(a)
+            return a
+
+        rp, ci = keep(row_ptr, np.int32), keep(col_idx, np.int32)
+        v = keep(vals, np.float64)
+        W = keep(weights, np.float64)
+        st_v = keep(st, np.float64)
+        if st_pattern is not None:
+            st_rp, st_ci = keep(st_pattern[0], np.int32), keep(st_pattern[1], np.int32)
+        else:
+            st_rp, st_ci = rp, ci
+        self.opts = default_opts(**opts)
+        if st_v is None:
+            self.opts.schur = SCHUR_ATT
+        self._c = lib.or_create(self.n, self.b, _p(rp), _p(ci), _p(v), _p(W), ps, ts, _p(st_rp), _p(st_ci),
+                                _p(st_v), ctypes.byref(self.opts))
+        self.status = lib.or_status(self._c)
+        if self.status != 0:
+            raise RuntimeError(f"oracle setup failed with status {self.status}")
+
+    @classmethod
+    def from_system(cls, sys: dict, use_st: bool = True, **opts) -> "Oracle":
+        return cls(sys["n"], sys["b"], sys["row_ptr"], sys["col_idx"], sys["vals"], sys["weights"],
+                   st=sys["st"] if use_st else None, **opts)
+
+    def __del__(self):
+        if getattr(self, "_c", None):
+            _load().or_destroy(self._c)
+            self._c = None
+
+    @property
+    def nb(self):
+        return self.n * self.b
+
+    def solve(self, rhs, rtol=1e-8):
+        lib = _load()
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64).reshape(-1)
+        x = np.zeros(self.nb)
+        st = Stats()
+        rc = lib.or_solve(self._c, _p(rhs), _p(x), rtol, ctypes.byref(st))
+        return x, dict(rc=rc, iters=st.iters, restarts=st.restarts, converged=bool(st.converged),
+                       est_rel_res=st.est_rel_res, true_rel_res=st.true_rel_res, bnorm=st.bnorm)
+
+    def _vec_op(self, name, v, nout=None):
+        lib = _load()
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+        out = np.zeros(nout if nout is not None else self.nb)
+        getattr(lib, name)(self._c, _p(v), _p(out))
+        return out
+
+    def precond(self, v):
+        return self._vec_op("or_precond", v)
+
+    def stage1(self, v):
+        return self._vec_op("or_stage1", v)
+
+    def ilu_apply(self, r):
+        return self._vec_op("or_ilu_apply", r)
+
+    def spmv(self, x):
+        return self._vec_op("or_spmv", x)
+
+    def weight_rhs(self, rhs):
+        return self._vec_op("or_weight_rhs", rhs)
+
+    def vcycle(self, which, bvec):
+        lib = _load()
+        bvec = np.ascontiguousarray(bvec, dtype=np.float64)
+        x = np.zeros_like(bvec)
+        lib.or_vcycle(self._c, which, _p(bvec), _p(x))
+        return x
+
+    def matrix(self):
+        """Decoupled A' as scalar interleaved CSR (rp, ci, v)."""
+        lib = _load()
+        nnz = lib.or_nnz(self._c)
+        rp = np.zeros(self.nb + 1, np.int32)
+        ci = np.zeros(nnz, np.int32)
+        v = np.zeros(nnz)
+        lib.or_matrix(self._c, _p(rp), _p(ci), _p(v))
+        return rp, ci, v
+
+    def dense(self):
+        rp, ci, v = self.matrix()
+        A = np.zeros((self.nb, self.nb))
+        for i in range(self.nb):
+            A[i, ci[rp[i]:rp[i + 1]]] += v[rp[i]:rp[i + 1]]
+        return A
+
+    def ilu_factors(self):
+        lib = _load()
+        nnz = lib.or_nnz(self._c)
+        v = np.zeros(nnz)
+        lib.or_ilu_factors(self._c, _p(v))
+        return v
+
+    def field(self, f, nnz):
+        lib = _load()
+        v = np.zeros(nnz)
+        lib.or_field(self._c, f, _p(v))
+        return v
+
+    def levels(self, which):
+        """AMG hierarchy of A_pp (which=0) or S~_T (which=1): list of dicts per level."""
+        lib = _load()
+        return _levels(lib.or_hierarchy(self._c, which), lib.or_nlevels(self._c, which))
+
+
+def _levels(h, nlev):
+    lib = _load()
+    out = []
+    for l in range(nlev):
+        info = np.zeros(5, np.int32)
+        lib.or_hier_level_info(h, l, _p(info))
+        n, nnz, nnzP, nc, dense = (int(t) for t in info)
+        rp = np.zeros(n + 1, np.int32)
+        ci = np.zeros(max(nnz, 1), np.int32)
+        v = np.zeros(max(nnz, 1))
+        dinv = np.zeros(max(n, 1))
+        coarse = nc > 0
+        cf = np.zeros(n, np.int32) if coarse else None
+        Prp = np.zeros(n + 1, np.int32) if coarse else None
+        Pci = np.zeros(max(nnzP, 1), np.int32) if coarse else None
+        Pv = np.zeros(max(nnzP, 1)) if coarse else None
+        lib.or_hier_level_get(h, l, _p(rp), _p(ci), _p(v), _p(dinv), _p(cf), _p(Prp), _p(Pci), _p(Pv))
+        lev = dict(n=n, rp=rp, ci=ci[:nnz], v=v[:nnz], dinv=dinv[:n], dense=bool(dense))
+        if coarse:
+            lev.update(cf=cf, nc=nc, Prp=Prp, Pci=Pci[:nnzP], Pv=Pv[:nnzP])
+        out.append(lev)
+    return out
+
+
+class AMG:
+    """Standalone oracle AMG hierarchy on a scalar CSR matrix (strength, PMIS, direct
+    interpolation, Galerkin RAP, smoother diagonal, dense coarsest solve)."""
+
+    def __init__(self, rp, ci, v, **opts):
+        lib = _load()
+        self._keep = [np.ascontiguousarray(rp, np.int32), np.ascontiguousarray(ci, np.int32),
+                      np.ascontiguousarray(v, np.float64)]
+        self.n = len(rp) - 1
+        self.opts = default_opts(**opts)
+        st = ctypes.c_int(0)
+        self._h = lib.or_amg_create(self.n, *(_p(a) for a in self._keep), ctypes.byref(self.opts), ctypes.byref(st))
+        if st.value != 0:
+            raise RuntimeError(f"oracle AMG setup failed with status {st.value}")
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _load().or_amg_destroy(self._h)
+            self._h = None
+
+    def vcycle(self, bvec):
+        bvec = np.ascontiguousarray(bvec, dtype=np.float64)
+        x = np.zeros_like(bvec)
+        _load().or_amg_vcycle(self._h, _p(bvec), _p(x))
+        return x
+
+    def levels(self):
+        lib = _load()
+        return _levels(self._h, lib.or_amg_nlevels(self._h))
+
+
+def splitmix64(seed: int, i: int) -> int:
+    return int(_load().or_splitmix64(seed, i))

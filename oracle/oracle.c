@@ -1,0 +1,828 @@
+/*
+ * FP64 CPU oracle for the CPTR-preconditioned FGMRES solve (arXiv 1907.04229).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the plain, serial, obviously-correct restatement of the
+ * method against which the CUDA library is checked.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it; the product path never calls it.  It shares no
+ * code with the CUDA library.  Compile with -ffp-contract=off so that results do not depend on
+ * whether the target fuses multiply-adds.
+ *
+ * Data: scalar CSR (int32 indices, double values).  The BSR Jacobian handed to or_create is
+ * expanded to the interleaved (cell-major) scalar CSR: unknown u of cell i is row i*b + u.
+ *
+ * Steps, each with the passage it follows:
+ *   decoupling + scaling  A' = W A, b' = W b            Sec. 2.2.2 eq. (weighted), Sec. 3.5 eq. (scaling)
+ *   p-T restriction       A_00 = [A_pp A_pT; A_Tp A_TT]  Sec. 3.2 eq. (A00)
+ *   block preconditioner  5 steps for A_00^{-1}          Sec. 3.3 eq. (Aschur) and its step list
+ *   Schur approximation   S~_T given (eq. Se) or A_TT    Sec. 3.3.1
+ *   CPR first stage       A_pp^{-1} on b_p               Sec. 3.1
+ *   two-stage combination x1 = M1^-1 v, b1 = v - A x1,
+ *                         z = M2^-1 b1 + x1              Sec. 3 "Two-stage preconditioners"
+ *   second stage          ILU(0)                         Sec. 4 (ILU(0) default)
+ *   AMG V-cycle           strength, PMIS, direct interpolation, Galerkin RAP, l1-Jacobi or
+ *                         omega-Jacobi, one pre- and one post-sweep, dense LU on the coarsest
+ *                         level (replaces BoomerAMG's defaults, Sec. 4)
+ *   Krylov                right-preconditioned (flexible) GMRES, restart m, classical
+ *                         Gram-Schmidt with one full re-orthogonalisation, Givens rotations,
+ *                         stop when the residual estimate <= rtol * ||b'||      Sec. 3, Sec. 4
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------------------------ */
+/* options and stats (layout mirrored by oracle/__init__.py)                                   */
+enum { OR_CPTR_FULL = 0, OR_CPTR_UPPER = 1, OR_CPTR_LOWER = 2, OR_BD = 3, OR_CPR = 4, OR_NONE1 = 5 };
+enum { OR_ILU0 = 0, OR_NONE2 = 1 };
+enum { OR_SCHUR_GIVEN = 0, OR_SCHUR_ATT = 1 };
+enum { OR_L1 = 0, OR_JACOBI = 1 };
+
+typedef struct {
+    int32_t stage1, stage2, schur, smoother;
+    double omega, theta;
+    int32_t n_coarse, max_levels, restart, max_it;
+    int32_t dense_max, seed;
+} or_opts;
+
+typedef struct {
+    int32_t iters, restarts, converged, pad;
+    double est_rel_res, true_rel_res, bnorm;
+} or_stats;
+
+typedef struct {
+    int32_t n, nnz;
+    int32_t *rp, *ci;
+    double *v;
+} csr;
+
+static void csr_alloc(csr *a, int32_t n, int32_t nnz) {
+    a->n = n; a->nnz = nnz;
+    a->rp = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    a->ci = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    a->v = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+}
+static void csr_free(csr *a) { free(a->rp); free(a->ci); free(a->v); memset(a, 0, sizeof(*a)); }
+
+/* y = A x */
+static void spmv(const csr *A, const double *x, double *y) {
+    for (int32_t i = 0; i < A->n; ++i) {
+        double s = 0.0;
+        for (int32_t k = A->rp[i]; k < A->rp[i + 1]; ++k) s += A->v[k] * x[A->ci[k]];
+        y[i] = s;
+    }
+}
+static double dot(int64_t n, const double *x, const double *y) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
+    return s;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* AMG                                                                                          */
+typedef struct {
+    csr A;          /* level operator */
+    double *dinv;   /* smoother diagonal inverse */
+    csr P, PT;      /* interpolation n x nc and its transpose (empty on the coarsest level) */
+    int32_t *cf;    /* 1 = C, 2 = F (empty on the coarsest level) */
+    double *r, *x, *b; /* work */
+} amg_level;
+
+typedef struct {
+    int nlev;
+    amg_level L[32];
+    double *lu;     /* coarsest: dense LU with partial pivoting (row-major) or NULL */
+    int32_t *piv;
+    int dense;      /* 1: coarsest level solved by dense LU; 0: by two smoothing sweeps */
+} amg;
+
+static uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+    /* i-th (0-based) output of the SplitMix64 stream started at state seed */
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Classical strength: j != i is strong for i iff -a_ij >= theta * max_{k != i}(-a_ik) and the
+ * maximum is positive.  Returned as a CSR pattern S (row i lists the j that i depends on). */
+static void strength(const csr *A, double theta, int32_t **Srp, int32_t **Sci) {
+    int32_t n = A->n;
+    int32_t *rp = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    int32_t *ci = (int32_t *)malloc(sizeof(int32_t) * (size_t)(A->nnz > 0 ? A->nnz : 1));
+    int32_t cnt = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        double m = 0.0;
+        int have = 0;
+        for (int32_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+            if (A->ci[k] == i) continue;
+            double t = -A->v[k];
+            if (!have || t > m) { m = t; have = 1; }
+        }
+        if (have && m > 0.0) {
+            double thr = theta * m;
+            for (int32_t k = A->rp[i]; k < A->rp[i + 1]; ++k)
+                if (A->ci[k] != i && -A->v[k] >= thr) ci[cnt++] = A->ci[k];
+        }
+        rp[i + 1] = cnt;
+    }
+    *Srp = rp; *Sci = ci;
+}
+
+static void transpose_pattern(int32_t n, const int32_t *rp, const int32_t *ci, int32_t **Trp, int32_t **Tci) {
+    int32_t nnz = rp[n];
+    int32_t *trp = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    int32_t *tci = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    for (int32_t k = 0; k < nnz; ++k) trp[ci[k] + 1]++;
+    for (int32_t i = 0; i < n; ++i) trp[i + 1] += trp[i];
+    int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    memcpy(pos, trp, sizeof(int32_t) * ((size_t)n + 1));
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) tci[pos[ci[k]]++] = i; /* rows ascending */
+    free(pos);
+    *Trp = trp; *Tci = tci;
+}
+
+/* key order used by PMIS: (|S^T_i|, 32-bit hash) with the larger index winning exact ties */
+static int beats(uint64_t ki, int32_t i, uint64_t kj, int32_t j) { return ki > kj || (ki == kj && i > j); }
+
+/* PMIS C/F splitting (De Sterck, Yang, Heys 2006), round-synchronous.  cf: 1 = C, 2 = F. */
+static void pmis(int32_t n, const int32_t *Srp, const int32_t *Sci, uint64_t seed, int32_t *cf) {
+    int32_t *Trp, *Tci;
+    transpose_pattern(n, Srp, Sci, &Trp, &Tci);
+    uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    for (int32_t i = 0; i < n; ++i) {
+        uint64_t deg = (uint64_t)(Trp[i + 1] - Trp[i]);
+        key[i] = (deg << 32) | (splitmix64_at(seed, (uint64_t)i) >> 32);
+        int isolated = (Srp[i + 1] == Srp[i]) && (Trp[i + 1] == Trp[i]);
+        cf[i] = isolated ? 2 : 0;
+    }
+    uint8_t *newc = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    for (;;) {
+        int32_t undecided = 0;
+        for (int32_t i = 0; i < n; ++i) undecided += (cf[i] == 0);
+        if (!undecided) break;
+        /* 1. undecided local maxima over undecided strong neighbours (S_i and S^T_i) */
+        for (int32_t i = 0; i < n; ++i) {
+            newc[i] = 0;
+            if (cf[i] != 0) continue;
+            int ok = 1;
+            for (int32_t k = Srp[i]; k < Srp[i + 1] && ok; ++k) {
+                int32_t j = Sci[k];
+                if (cf[j] == 0 && !beats(key[i], i, key[j], j)) ok = 0;
+            }
+            for (int32_t k = Trp[i]; k < Trp[i + 1] && ok; ++k) {
+                int32_t j = Tci[k];
+                if (cf[j] == 0 && !beats(key[i], i, key[j], j)) ok = 0;
+            }
+            newc[i] = (uint8_t)ok;
+        }
+        for (int32_t i = 0; i < n; ++i)
+            if (newc[i]) cf[i] = 1;
+        /* 2. undecided points that strongly depend on a C point become F */
+        for (int32_t i = 0; i < n; ++i) {
+            if (cf[i] != 0) continue;
+            for (int32_t k = Srp[i]; k < Srp[i + 1]; ++k)
+                if (cf[Sci[k]] == 1) { cf[i] = 2; break; }
+        }
+    }
+    free(newc); free(key); free(Trp); free(Tci);
+}
+
+/* Direct interpolation (Stueben): for an F point i with strong C neighbours C_i,
+ *   w_ij = -alpha a_ij / (a_ii + sum_{k != i, a_ik > 0} a_ik),
+ *   alpha = (sum_{k != i, a_ik < 0} a_ik) / (sum_{k in C_i} a_ik).
+ * Strong neighbours are negative entries, so positive couplings are lumped into the diagonal. */
+static void direct_interp(const csr *A, const int32_t *Srp, const int32_t *Sci, const int32_t *cf, csr *P,
+                          int32_t *nc_out) {
+    int32_t n = A->n;
+    int32_t *cidx = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t nc = 0;
+    for (int32_t i = 0; i < n; ++i) cidx[i] = (cf[i] == 1) ? nc++ : -1;
+    /* count */
+    int32_t *cnt = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    for (int32_t i = 0; i < n; ++i) {
+        if (cf[i] == 1) { cnt[i + 1] = 1; continue; }
+        int32_t c = 0;
+        for (int32_t k = Srp[i]; k < Srp[i + 1]; ++k) c += (cf[Sci[k]] == 1);
+        cnt[i + 1] = c;
+    }
+    for (int32_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+    csr_alloc(P, n, cnt[n]);
+    memcpy(P->rp, cnt, sizeof(int32_t) * ((size_t)n + 1));
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t o = P->rp[i];
+        if (cf[i] == 1) { P->ci[o] = cidx[i]; P->v[o] = 1.0; continue; }
+        if (P->rp[i + 1] == o) continue;
+        double aii = 0.0, sneg = 0.0, spos = 0.0, sc = 0.0;
+        for (int32_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+            int32_t j = A->ci[k];
+            double a = A->v[k];
+            if (j == i) aii += a;
+            else if (a < 0.0) sneg += a;
+            else if (a > 0.0) spos += a;
+        }
+        /* strong C neighbours in ascending column order (S rows are in A's column order) */
+        for (int32_t k = Srp[i]; k < Srp[i + 1]; ++k) {
+            int32_t j = Sci[k];
+            if (cf[j] != 1) continue;
+            for (int32_t q = A->rp[i]; q < A->rp[i + 1]; ++q)
+                if (A->ci[q] == j) { sc += A->v[q]; break; }
+        }
+        double d = aii + spos;
+        double alpha = sneg / sc;
+        for (int32_t k = Srp[i]; k < Srp[i + 1]; ++k) {
+            int32_t j = Sci[k];
+            if (cf[j] != 1) continue;
+            double a = 0.0;
+            for (int32_t q = A->rp[i]; q < A->rp[i + 1]; ++q)
+                if (A->ci[q] == j) { a = A->v[q]; break; }
+            P->ci[o] = cidx[j];
+            P->v[o] = -alpha * a / d;
+            ++o;
+        }
+    }
+    free(cnt); free(cidx);
+    *nc_out = nc;
+}
+
+static void csr_transpose(const csr *A, int32_t ncols, csr *T) {
+    csr_alloc(T, ncols, A->nnz);
+    for (int32_t k = 0; k < A->nnz; ++k) T->rp[A->ci[k] + 1]++;
+    for (int32_t i = 0; i < ncols; ++i) T->rp[i + 1] += T->rp[i];
+    int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * ((size_t)ncols + 1));
+    memcpy(pos, T->rp, sizeof(int32_t) * ((size_t)ncols + 1));
+    for (int32_t i = 0; i < A->n; ++i)
+        for (int32_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+            int32_t p = pos[A->ci[k]]++;
+            T->ci[p] = i;
+            T->v[p] = A->v[k];
+        }
+    free(pos);
+}
+
+static int cmp_i32(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* C = A B (ncols of B = ncb).  Every output entry is accumulated in the order of the inner index
+ * (ascending column of A's row, then B's row order), starting from 0.0; output columns ascending. */
+static void spgemm(const csr *A, const csr *B, int32_t ncb, csr *C) {
+    int32_t n = A->n;
+    double *acc = (double *)calloc((size_t)(ncb > 0 ? ncb : 1), sizeof(double));
+    int32_t *mark = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ncb > 0 ? ncb : 1));
+    for (int32_t j = 0; j < ncb; ++j) mark[j] = -1;
+    int32_t *list = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ncb > 0 ? ncb : 1));
+    int32_t cap = A->nnz + 16, nnz = 0;
+    int32_t *ci = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    double *v = (double *)malloc(sizeof(double) * (size_t)cap);
+    int32_t *rp = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t len = 0;
+        for (int32_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+            int32_t l = A->ci[k];
+            double a = A->v[k];
+            for (int32_t q = B->rp[l]; q < B->rp[l + 1]; ++q) {
+                int32_t j = B->ci[q];
+                if (mark[j] != i) { mark[j] = i; acc[j] = 0.0; list[len++] = j; }
+                acc[j] = acc[j] + a * B->v[q];
+            }
+        }
+        qsort(list, (size_t)len, sizeof(int32_t), cmp_i32);
+        if (nnz + len > cap) {
+            while (nnz + len > cap) cap *= 2;
+            ci = (int32_t *)realloc(ci, sizeof(int32_t) * (size_t)cap);
+            v = (double *)realloc(v, sizeof(double) * (size_t)cap);
+        }
+        for (int32_t t = 0; t < len; ++t) { ci[nnz] = list[t]; v[nnz] = acc[list[t]]; ++nnz; }
+        rp[i + 1] = nnz;
+    }
+    free(acc); free(mark); free(list);
+    C->n = n; C->nnz = nnz; C->rp = rp; C->ci = ci; C->v = v;
+}
+
+static void smoother_diag(const csr *A, int smoother, double omega, double *dinv) {
+    for (int32_t i = 0; i < A->n; ++i) {
+        double d = 0.0;
+        if (smoother == OR_L1) {
+            for (int32_t k = A->rp[i]; k < A->rp[i + 1]; ++k) d += fabs(A->v[k]);
+            dinv[i] = 1.0 / d;
+        } else {
+            for (int32_t k = A->rp[i]; k < A->rp[i + 1]; ++k)
+                if (A->ci[k] == i) d += A->v[k];
+            dinv[i] = omega / d;
+        }
+    }
+}
+
+/* dense LU with partial pivoting, in place, row-major; returns 0 or -1 if singular */
+static int dense_lu(int32_t n, double *a, int32_t *piv) {
+    for (int32_t k = 0; k < n; ++k) {
+        int32_t p = k;
+        double m = fabs(a[(size_t)k * n + k]);
+        for (int32_t i = k + 1; i < n; ++i)
+            if (fabs(a[(size_t)i * n + k]) > m) { m = fabs(a[(size_t)i * n + k]); p = i; }
+        piv[k] = p;
+        if (m == 0.0) return -1;
+        if (p != k)
+            for (int32_t j = 0; j < n; ++j) {
+                double t = a[(size_t)k * n + j]; a[(size_t)k * n + j] = a[(size_t)p * n + j]; a[(size_t)p * n + j] = t;
+            }
+        for (int32_t i = k + 1; i < n; ++i) {
+            double l = a[(size_t)i * n + k] / a[(size_t)k * n + k];
+            a[(size_t)i * n + k] = l;
+            for (int32_t j = k + 1; j < n; ++j) a[(size_t)i * n + j] -= l * a[(size_t)k * n + j];
+        }
+    }
+    return 0;
+}
+static void dense_lu_solve(int32_t n, const double *lu, const int32_t *piv, const double *b, double *x) {
+    memcpy(x, b, sizeof(double) * (size_t)n);
+    for (int32_t k = 0; k < n; ++k) {
+        int32_t p = piv[k];
+        if (p != k) { double t = x[k]; x[k] = x[p]; x[p] = t; }
+    }
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t j = 0; j < i; ++j) x[i] -= lu[(size_t)i * n + j] * x[j];
+    for (int32_t i = n - 1; i >= 0; --i) {
+        for (int32_t j = i + 1; j < n; ++j) x[i] -= lu[(size_t)i * n + j] * x[j];
+        x[i] /= lu[(size_t)i * n + i];
+    }
+}
+
+static void csr_copy(const csr *A, csr *B) {
+    csr_alloc(B, A->n, A->nnz);
+    memcpy(B->rp, A->rp, sizeof(int32_t) * ((size_t)A->n + 1));
+    memcpy(B->ci, A->ci, sizeof(int32_t) * (size_t)A->nnz);
+    memcpy(B->v, A->v, sizeof(double) * (size_t)A->nnz);
+}
+
+static int amg_setup(amg *h, const csr *A0, const or_opts *o) {
+    memset(h, 0, sizeof(*h));
+    csr_copy(A0, &h->L[0].A);
+    int l = 0;
+    int maxl = o->max_levels < 1 ? 1 : (o->max_levels > 32 ? 32 : o->max_levels);
+    for (;;) {
+        amg_level *L = &h->L[l];
+        int32_t n = L->A.n;
+        L->dinv = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        smoother_diag(&L->A, o->smoother, o->omega, L->dinv);
+        L->r = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+        L->x = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+        L->b = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+        if (l + 1 >= maxl || n <= o->n_coarse) break;
+        int32_t *Srp, *Sci;
+        strength(&L->A, o->theta, &Srp, &Sci);
+        L->cf = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+        pmis(n, Srp, Sci, (uint64_t)o->seed + (uint64_t)l, L->cf);
+        int32_t nc;
+        direct_interp(&L->A, Srp, Sci, L->cf, &L->P, &nc);
+        free(Srp); free(Sci);
+        if (nc == 0 || nc >= n) { /* no coarsening possible: this level is the coarsest */
+            csr_free(&L->P); free(L->cf); L->cf = NULL;
+            break;
+        }
+        csr_transpose(&L->P, nc, &L->PT);
+        csr AP;
+        spgemm(&L->A, &L->P, nc, &AP);
+        spgemm(&L->PT, &AP, nc, &h->L[l + 1].A);
+        csr_free(&AP);
+        ++l;
+    }
+    h->nlev = l + 1;
+    amg_level *C = &h->L[l];
+    int32_t n = C->A.n;
+    if (n <= o->dense_max) {
+        h->dense = 1;
+        h->lu = (double *)calloc((size_t)n * n + 1, sizeof(double));
+        h->piv = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t k = C->A.rp[i]; k < C->A.rp[i + 1]; ++k) h->lu[(size_t)i * n + C->A.ci[k]] += C->A.v[k];
+        if (dense_lu(n, h->lu, h->piv) != 0) return -6;
+    }
+    return 0;
+}
+
+static void amg_free(amg *h) {
+    for (int l = 0; l < h->nlev; ++l) {
+        amg_level *L = &h->L[l];
+        csr_free(&L->A); csr_free(&L->P); csr_free(&L->PT);
+        free(L->dinv); free(L->cf); free(L->r); free(L->x); free(L->b);
+    }
+    free(h->lu); free(h->piv);
+    memset(h, 0, sizeof(*h));
+}
+
+/* One V(1,1)-cycle with zero initial guess: x ~= A_l^{-1} b. */
+static void vcycle(amg *h, int l, const double *b, double *x) {
+    amg_level *L = &h->L[l];
+    int32_t n = L->A.n;
+    if (l == h->nlev - 1) {
+        if (h->dense) { dense_lu_solve(n, h->lu, h->piv, b, x); return; }
+        for (int32_t i = 0; i < n; ++i) x[i] = L->dinv[i] * b[i];
+        spmv(&L->A, x, L->r);
+        for (int32_t i = 0; i < n; ++i) x[i] = x[i] + L->dinv[i] * (b[i] - L->r[i]);
+        return;
+    }
+    amg_level *Cl = &h->L[l + 1];
+    /* pre-smoothing from zero: x = D^{-1} b */
+    for (int32_t i = 0; i < n; ++i) x[i] = L->dinv[i] * b[i];
+    /* residual r = b - A x, restriction b_c = P^T r */
+    spmv(&L->A, x, L->r);
+    for (int32_t i = 0; i < n; ++i) L->r[i] = b[i] - L->r[i];
+    spmv(&L->PT, L->r, Cl->b);
+    vcycle(h, l + 1, Cl->b, Cl->x);
+    /* prolongation x += P x_c */
+    spmv(&L->P, Cl->x, L->r);
+    for (int32_t i = 0; i < n; ++i) x[i] += L->r[i];
+    /* post-smoothing x = x + D^{-1}(b - A x) */
+    spmv(&L->A, x, L->r);
+    for (int32_t i = 0; i < n; ++i) L->r[i] = x[i] + L->dinv[i] * (b[i] - L->r[i]);
+    memcpy(x, L->r, sizeof(double) * (size_t)n);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* ILU(0) on the interleaved scalar CSR (IKJ form, no pivoting)                                 */
+typedef struct {
+    csr LU;        /* L (unit, strictly lower) and U (upper incl. diagonal) in A's pattern */
+    int32_t *diag; /* position of the diagonal in each row */
+} ilu0;
+
+static int ilu0_factor(const csr *A, ilu0 *f) {
+    csr_copy(A, &f->LU);
+    int32_t n = A->n;
+    f->diag = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    for (int32_t j = 0; j < n; ++j) pos[j] = -1;
+    csr *M = &f->LU;
+    for (int32_t i = 0; i < n; ++i) {
+        f->diag[i] = -1;
+        for (int32_t k = M->rp[i]; k < M->rp[i + 1]; ++k)
+            if (M->ci[k] == i) f->diag[i] = k;
+        if (f->diag[i] < 0) { free(pos); return -1; }
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t k = M->rp[i]; k < M->rp[i + 1]; ++k) pos[M->ci[k]] = k;
+        for (int32_t k = M->rp[i]; k < M->rp[i + 1]; ++k) {
+            int32_t c = M->ci[k];
+            if (c >= i) break;
+            double piv = M->v[f->diag[c]];
+            if (piv == 0.0) { free(pos); return -6; }
+            M->v[k] = M->v[k] / piv;
+            double lik = M->v[k];
+            for (int32_t q = f->diag[c] + 1; q < M->rp[c + 1]; ++q) {
+                int32_t p = pos[M->ci[q]];
+                if (p >= 0) M->v[p] = M->v[p] - lik * M->v[q];
+            }
+        }
+        for (int32_t k = M->rp[i]; k < M->rp[i + 1]; ++k) pos[M->ci[k]] = -1;
+        if (M->v[f->diag[i]] == 0.0) { free(pos); return -6; }
+    }
+    free(pos);
+    return 0;
+}
+
+static void ilu0_solve(const ilu0 *f, const double *r, double *z) {
+    const csr *M = &f->LU;
+    int32_t n = M->n;
+    for (int32_t i = 0; i < n; ++i) {
+        double s = r[i];
+        for (int32_t k = M->rp[i]; k < f->diag[i]; ++k) s -= M->v[k] * z[M->ci[k]];
+        z[i] = s;
+    }
+    for (int32_t i = n - 1; i >= 0; --i) {
+        double s = z[i];
+        for (int32_t k = f->diag[i] + 1; k < M->rp[i + 1]; ++k) s -= M->v[k] * z[M->ci[k]];
+        z[i] = s / M->v[f->diag[i]];
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* the solver context                                                                           */
+typedef struct {
+    or_opts o;
+    int32_t n, b, ps, ts;
+    csr A;             /* decoupled A' (interleaved scalar CSR) */
+    double *W;         /* [n, b, b] row weights (identity if none was given) */
+    csr App, ApT, ATp, St;
+    amg hp, hT;
+    ilu0 ilu;
+    /* work */
+    double *bp, *bT, *xp, *dT, *dp, *t1, *x1, *b1;
+    int status;
+} or_ctx;
+
+/* Expand BSR (row-major b x b blocks) to the interleaved scalar CSR, applying W if given:
+ * block row i of A' is W_i times block row i of A (Sec. 2.2.2 eq. weighted, Sec. 3.5 eq. scaling). */
+static void bsr_to_csr_weighted(int32_t n, int32_t b, const int32_t *rp, const int32_t *ci, const double *vals,
+                                const double *W, csr *A) {
+    int64_t nnzb = rp[n];
+    csr_alloc(A, n * b, (int32_t)(nnzb * b * b));
+    int32_t o = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t r = 0; r < b; ++r) {
+            for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+                const double *blk = vals + (int64_t)k * b * b;
+                for (int32_t c = 0; c < b; ++c) {
+                    double s;
+                    if (W) {
+                        s = 0.0;
+                        for (int32_t t = 0; t < b; ++t) s += W[(int64_t)i * b * b + r * b + t] * blk[t * b + c];
+                    } else {
+                        s = blk[r * b + c];
+                    }
+                    A->ci[o] = ci[k] * b + c;
+                    A->v[o] = s;
+                    ++o;
+                }
+            }
+            A->rp[i * b + r + 1] = o;
+        }
+    }
+}
+
+/* Scalar block (u, w) of A': entries A'(i*b+u, j*b+w) on the cell pattern (Sec. 3.2 eq. A00). */
+static void extract_field(const or_ctx *c, const int32_t *rp, const int32_t *ci, int u, int w, csr *F) {
+    int32_t n = c->n, b = c->b;
+    csr_alloc(F, n, rp[n]);
+    memcpy(F->rp, rp, sizeof(int32_t) * ((size_t)n + 1));
+    memcpy(F->ci, ci, sizeof(int32_t) * (size_t)rp[n]);
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t row = i * b + u;
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+            /* in the interleaved CSR, block k of cell row i occupies b consecutive entries */
+            int32_t base = c->A.rp[row] + (k - rp[i]) * b;
+            F->v[k] = c->A.v[base + w];
+        }
+    }
+}
+
+or_ctx *or_create(int32_t n, int32_t b, const int32_t *rp, const int32_t *ci, const double *vals, const double *W,
+                  int32_t ps, int32_t ts, const int32_t *st_rp, const int32_t *st_ci, const double *st_v,
+                  const or_opts *o) {
+    or_ctx *c = (or_ctx *)calloc(1, sizeof(or_ctx));
+    c->o = *o;
+    c->n = n; c->b = b; c->ps = ps; c->ts = ts;
+    c->W = (double *)malloc(sizeof(double) * (size_t)n * b * b);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t r = 0; r < b; ++r)
+            for (int32_t t = 0; t < b; ++t)
+                c->W[(int64_t)i * b * b + r * b + t] = W ? W[(int64_t)i * b * b + r * b + t] : (r == t ? 1.0 : 0.0);
+    bsr_to_csr_weighted(n, b, rp, ci, vals, W, &c->A);
+    extract_field(c, rp, ci, ps, ps, &c->App);
+    extract_field(c, rp, ci, ps, ts, &c->ApT);
+    extract_field(c, rp, ci, ts, ps, &c->ATp);
+    if (st_v && o->schur == OR_SCHUR_GIVEN) {
+        csr_alloc(&c->St, n, st_rp[n]);
+        memcpy(c->St.rp, st_rp, sizeof(int32_t) * ((size_t)n + 1));
+        memcpy(c->St.ci, st_ci, sizeof(int32_t) * (size_t)st_rp[n]);
+        memcpy(c->St.v, st_v, sizeof(double) * (size_t)st_rp[n]);
+    } else {
+        extract_field(c, rp, ci, ts, ts, &c->St); /* S~_{A_TT} = A_TT (Sec. 3.3.1) */
+    }
+    int rc = 0;
+    if (o->stage1 != OR_NONE1) rc = amg_setup(&c->hp, &c->App, o);
+    if (!rc && o->stage1 != OR_NONE1 && o->stage1 != OR_CPR) rc = amg_setup(&c->hT, &c->St, o);
+    if (!rc && o->stage2 == OR_ILU0) rc = ilu0_factor(&c->A, &c->ilu);
+    c->status = rc;
+    size_t nb = (size_t)n * b;
+    c->bp = calloc(n, sizeof(double)); c->bT = calloc(n, sizeof(double));
+    c->xp = calloc(n, sizeof(double)); c->dT = calloc(n, sizeof(double));
+    c->dp = calloc(n, sizeof(double)); c->t1 = calloc(n, sizeof(double));
+    c->x1 = calloc(nb, sizeof(double)); c->b1 = calloc(nb, sizeof(double));
+    return c;
+}
+
+int or_status(const or_ctx *c) { return c->status; }
+
+void or_destroy(or_ctx *c) {
+    if (!c) return;
+    csr_free(&c->A); csr_free(&c->App); csr_free(&c->ApT); csr_free(&c->ATp); csr_free(&c->St);
+    amg_free(&c->hp); amg_free(&c->hT);
+    csr_free(&c->ilu.LU); free(c->ilu.diag);
+    free(c->W); free(c->bp); free(c->bT); free(c->xp); free(c->dT); free(c->dp); free(c->t1);
+    free(c->x1); free(c->b1);
+    free(c);
+}
+
+/* First stage: x1 = M1^{-1} v on the p-T unknowns (zero elsewhere). */
+static void stage1(or_ctx *c, const double *v, double *x1) {
+    int32_t n = c->n, b = c->b;
+    memset(x1, 0, sizeof(double) * (size_t)n * b);
+    if (c->o.stage1 == OR_NONE1) return;
+    for (int32_t i = 0; i < n; ++i) { c->bp[i] = v[i * b + c->ps]; c->bT[i] = v[i * b + c->ts]; }
+    switch (c->o.stage1) {
+    case OR_CPTR_FULL: /* Sec. 3.3: the five steps */
+        vcycle(&c->hp, 0, c->bp, c->xp);                                         /* 1. A_pp x_p = b_p */
+        spmv(&c->ATp, c->xp, c->t1);
+        for (int32_t i = 0; i < n; ++i) c->t1[i] = c->bT[i] - c->t1[i];          /* 2. b~_T = b_T - A_Tp x_p */
+        vcycle(&c->hT, 0, c->t1, c->dT);                                         /* 3. S~_T d_T = b~_T */
+        spmv(&c->ApT, c->dT, c->t1);
+        for (int32_t i = 0; i < n; ++i) c->t1[i] = c->bp[i] - c->t1[i];          /* 4. b~_p = b_p - A_pT d_T */
+        vcycle(&c->hp, 0, c->t1, c->dp);                                         /* 5. A_pp d_p = b~_p */
+        break;
+    case OR_CPTR_LOWER: /* right factor of eq. (Aschur) dropped */
+        vcycle(&c->hp, 0, c->bp, c->dp);
+        spmv(&c->ATp, c->dp, c->t1);
+        for (int32_t i = 0; i < n; ++i) c->t1[i] = c->bT[i] - c->t1[i];
+        vcycle(&c->hT, 0, c->t1, c->dT);
+        break;
+    case OR_CPTR_UPPER: /* left factor of eq. (Aschur) dropped */
+        vcycle(&c->hT, 0, c->bT, c->dT);
+        spmv(&c->ApT, c->dT, c->t1);
+        for (int32_t i = 0; i < n; ++i) c->t1[i] = c->bp[i] - c->t1[i];
+        vcycle(&c->hp, 0, c->t1, c->dp);
+        break;
+    case OR_BD: /* block diagonal first stage */
+        vcycle(&c->hp, 0, c->bp, c->dp);
+        vcycle(&c->hT, 0, c->bT, c->dT);
+        break;
+    case OR_CPR: /* Sec. 3.1: pressure only */
+        vcycle(&c->hp, 0, c->bp, c->dp);
+        memset(c->dT, 0, sizeof(double) * (size_t)n);
+        break;
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        x1[i * b + c->ps] = c->dp[i];
+        if (c->o.stage1 != OR_CPR) x1[i * b + c->ts] = c->dT[i];
+    }
+}
+
+/* Two-stage preconditioner z = M2^{-1}(v - A' x1) + x1, x1 = M1^{-1} v. */
+void or_precond(or_ctx *c, const double *v, double *z) {
+    int32_t nb = c->n * c->b;
+    stage1(c, v, c->x1);
+    spmv(&c->A, c->x1, c->b1);
+    for (int32_t i = 0; i < nb; ++i) c->b1[i] = v[i] - c->b1[i];
+    if (c->o.stage2 == OR_ILU0) ilu0_solve(&c->ilu, c->b1, z);
+    else memcpy(z, c->b1, sizeof(double) * (size_t)nb);
+    for (int32_t i = 0; i < nb; ++i) z[i] += c->x1[i];
+}
+
+/* b' = W b */
+void or_weight_rhs(const or_ctx *c, const double *rhs, double *bw) {
+    int32_t b = c->b;
+    for (int32_t i = 0; i < c->n; ++i)
+        for (int32_t r = 0; r < b; ++r) {
+            double s = 0.0;
+            for (int32_t t = 0; t < b; ++t) s += c->W[(int64_t)i * b * b + r * b + t] * rhs[(int64_t)i * b + t];
+            bw[(int64_t)i * b + r] = s;
+        }
+}
+
+/* Right-preconditioned flexible GMRES(m) from x = 0 on A' x = W rhs. Returns 0 if converged,
+ * 1 if not, -4 on a non-finite value. */
+int or_solve(or_ctx *c, const double *rhs, double *x, double rtol, or_stats *st) {
+    int32_t nb = c->n * c->b, m = c->o.restart;
+    double *bw = (double *)malloc(sizeof(double) * (size_t)nb);
+    double *V = (double *)malloc(sizeof(double) * (size_t)nb * (m + 1));
+    double *Z = (double *)malloc(sizeof(double) * (size_t)nb * m);
+    double *w = (double *)malloc(sizeof(double) * (size_t)nb);
+    double *H = (double *)calloc((size_t)(m + 1) * m, sizeof(double)); /* H[i*m + j] */
+    double *h = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+    double *h2 = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+    double *cs = (double *)malloc(sizeof(double) * (size_t)m), *sn = (double *)malloc(sizeof(double) * (size_t)m);
+    double *g = (double *)malloc(sizeof(double) * (size_t)(m + 1)), *y = (double *)malloc(sizeof(double) * (size_t)m);
+    or_weight_rhs(c, rhs, bw);
+    memset(x, 0, sizeof(double) * (size_t)nb);
+    double bnorm = sqrt(dot(nb, bw, bw));
+    int it = 0, restarts = 0, conv = 0, rc = 1;
+    double est = 0.0;
+    st->bnorm = bnorm;
+    if (bnorm == 0.0) { conv = 1; rc = 0; goto done; }
+    for (;;) {
+        /* r = b' - A' x */
+        spmv(&c->A, x, w);
+        for (int32_t i = 0; i < nb; ++i) w[i] = bw[i] - w[i];
+        double beta = sqrt(dot(nb, w, w));
+        est = beta / bnorm;
+        if (!isfinite(beta)) { rc = -4; goto done; }
+        if (beta <= rtol * bnorm) { conv = 1; rc = 0; goto done; }
+        for (int32_t i = 0; i < nb; ++i) V[i] = w[i] / beta;
+        memset(g, 0, sizeof(double) * (size_t)(m + 1));
+        g[0] = beta;
+        int j, k = 0;
+        for (j = 0; j < m && it < c->o.max_it; ++j) {
+            double *vj = V + (size_t)j * nb, *zj = Z + (size_t)j * nb;
+            or_precond(c, vj, zj);
+            spmv(&c->A, zj, w);
+            /* CGS2: two passes of classical Gram-Schmidt against v_0..v_j */
+            for (int32_t q = 0; q <= j; ++q) h[q] = dot(nb, V + (size_t)q * nb, w);
+            for (int32_t q = 0; q <= j; ++q) {
+                const double *vq = V + (size_t)q * nb;
+                for (int32_t i = 0; i < nb; ++i) w[i] -= h[q] * vq[i];
+            }
+            for (int32_t q = 0; q <= j; ++q) h2[q] = dot(nb, V + (size_t)q * nb, w);
+            for (int32_t q = 0; q <= j; ++q) {
+                const double *vq = V + (size_t)q * nb;
+                for (int32_t i = 0; i < nb; ++i) w[i] -= h2[q] * vq[i];
+            }
+            for (int32_t q = 0; q <= j; ++q) H[q * m + j] = h[q] + h2[q];
+            double hn = sqrt(dot(nb, w, w));
+            H[(j + 1) * m + j] = hn;
+            ++it;
+            if (!isfinite(hn)) { rc = -4; goto done; }
+            if (hn > 0.0)
+                for (int32_t i = 0; i < nb; ++i) V[(size_t)(j + 1) * nb + i] = w[i] / hn;
+            /* apply the previous rotations to column j, then form the new one */
+            for (int32_t q = 0; q < j; ++q) {
+                double a = H[q * m + j], bq = H[(q + 1) * m + j];
+                H[q * m + j] = cs[q] * a + sn[q] * bq;
+                H[(q + 1) * m + j] = -sn[q] * a + cs[q] * bq;
+            }
+            double a = H[j * m + j], bq = H[(j + 1) * m + j];
+            double den = sqrt(a * a + bq * bq);
+            cs[j] = a / den;
+            sn[j] = bq / den;
+            H[j * m + j] = den;
+            H[(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            est = fabs(g[j + 1]) / bnorm;
+            k = j + 1;
+            if (fabs(g[j + 1]) <= rtol * bnorm || hn == 0.0) { conv = 1; break; }
+        }
+        /* y = H^{-1} g (upper triangular k x k), x += Z y */
+        for (int32_t i = k - 1; i >= 0; --i) {
+            double s = g[i];
+            for (int32_t q = i + 1; q < k; ++q) s -= H[i * m + q] * y[q];
+            y[i] = s / H[i * m + i];
+        }
+        for (int32_t q = 0; q < k; ++q) {
+            const double *zq = Z + (size_t)q * nb;
+            for (int32_t i = 0; i < nb; ++i) x[i] += y[q] * zq[i];
+        }
+        if (conv) { rc = 0; break; }
+        if (it >= c->o.max_it) { rc = 1; break; }
+        ++restarts;
+    }
+done:
+    spmv(&c->A, x, w);
+    for (int32_t i = 0; i < nb; ++i) w[i] = bw[i] - w[i];
+    st->iters = it;
+    st->restarts = restarts;
+    st->converged = conv;
+    st->est_rel_res = est;
+    st->true_rel_res = bnorm > 0.0 ? sqrt(dot(nb, w, w)) / bnorm : 0.0;
+    free(bw); free(V); free(Z); free(w); free(H); free(h); free(h2); free(cs); free(sn); free(g); free(y);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* accessors for tests                                                                          */
+static amg *pick(or_ctx *c, int which) { return which == 0 ? &c->hp : &c->hT; }
+int or_nlevels(or_ctx *c, int which) { return pick(c, which)->nlev; }
+/* info = {n, nnz, nnzP, nc, dense} */
+void or_hier_level_info(amg *h, int l, int32_t *info) {
+    amg_level *L = &h->L[l];
+    info[0] = L->A.n; info[1] = L->A.nnz;
+    info[2] = L->P.rp ? L->P.nnz : 0;
+    info[3] = (l + 1 < h->nlev) ? h->L[l + 1].A.n : 0;
+    info[4] = h->dense;
+}
+void or_hier_level_get(amg *h, int l, int32_t *rp, int32_t *ci, double *v, double *dinv, int32_t *cf,
+                       int32_t *Prp, int32_t *Pci, double *Pv) {
+    amg_level *L = &h->L[l];
+    memcpy(rp, L->A.rp, sizeof(int32_t) * ((size_t)L->A.n + 1));
+    memcpy(ci, L->A.ci, sizeof(int32_t) * (size_t)L->A.nnz);
+    memcpy(v, L->A.v, sizeof(double) * (size_t)L->A.nnz);
+    memcpy(dinv, L->dinv, sizeof(double) * (size_t)L->A.n);
+    if (L->cf && cf) {
+        memcpy(cf, L->cf, sizeof(int32_t) * (size_t)L->A.n);
+        memcpy(Prp, L->P.rp, sizeof(int32_t) * ((size_t)L->A.n + 1));
+        memcpy(Pci, L->P.ci, sizeof(int32_t) * (size_t)L->P.nnz);
+        memcpy(Pv, L->P.v, sizeof(double) * (size_t)L->P.nnz);
+    }
+}
+amg *or_hierarchy(or_ctx *c, int which) { return pick(c, which); }
+void or_vcycle(or_ctx *c, int which, const double *b, double *x) { vcycle(pick(c, which), 0, b, x); }
+void or_stage1(or_ctx *c, const double *v, double *x1) { stage1(c, v, x1); }
+void or_ilu_apply(or_ctx *c, const double *r, double *z) { ilu0_solve(&c->ilu, r, z); }
+void or_spmv(or_ctx *c, const double *x, double *y) { spmv(&c->A, x, y); }
+int32_t or_nnz(or_ctx *c) { return c->A.nnz; }
+void or_matrix(or_ctx *c, int32_t *rp, int32_t *ci, double *v) {
+    memcpy(rp, c->A.rp, sizeof(int32_t) * ((size_t)c->A.n + 1));
+    memcpy(ci, c->A.ci, sizeof(int32_t) * (size_t)c->A.nnz);
+    memcpy(v, c->A.v, sizeof(double) * (size_t)c->A.nnz);
+}
+void or_ilu_factors(or_ctx *c, double *v) { memcpy(v, c->ilu.LU.v, sizeof(double) * (size_t)c->ilu.LU.nnz); }
+/* field: 0 A_pp, 1 A_pT, 2 A_Tp, 3 S~_T (values on their own patterns; S~_T may differ) */
+void or_field(or_ctx *c, int f, double *v) {
+    const csr *F = f == 0 ? &c->App : f == 1 ? &c->ApT : f == 2 ? &c->ATp : &c->St;
+    memcpy(v, F->v, sizeof(double) * (size_t)F->nnz);
+}
+uint64_t or_splitmix64(uint64_t seed, uint64_t i) { return splitmix64_at(seed, i); }
+
+/* Standalone AMG hierarchy on a scalar CSR matrix (for tests of the AMG pieces in isolation). */
+amg *or_amg_create(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, const or_opts *o, int *status) {
+    amg *h = (amg *)calloc(1, sizeof(amg));
+    csr A;
+    A.n = n; A.nnz = rp[n];
+    A.rp = (int32_t *)rp; A.ci = (int32_t *)ci; A.v = (double *)v;
+    *status = amg_setup(h, &A, o);
+    return h;
+}
+void or_amg_destroy(amg *h) { if (h) { amg_free(h); free(h); } }
+void or_amg_vcycle(amg *h, const double *b, double *x) { vcycle(h, 0, b, x); }
+int or_amg_nlevels(amg *h) { return h->nlev; }

@@ -1,0 +1,500 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks one oracle function against something other than itself: a dense factorisation,
+a closed form, an invariant, an exact special case, or the minimal-residual property of GMRES.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+# ------------------------------------------------------------------------------------------------
+# helpers
+def dense_csr(rp, ci, v, n, m=None):
+    A = np.zeros((n, n if m is None else m))
+    for i in range(n):
+        np.add.at(A[i], ci[rp[i]:rp[i + 1]], v[rp[i]:rp[i + 1]])
+    return A
+
+
+def poisson3d(nx, ny, nz, shift=None):
+    """7-point Laplacian; Dirichlet-like (diagonal 6) unless shift is given, in which case the
+    diagonal is the neighbour count (zero row sums) plus shift[i]."""
+    n = nx * ny * nz
+    rp, ci, v = [0], [], []
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                i = x + nx * (y + ny * z)
+                nb = []
+                if z > 0: nb.append(i - nx * ny)
+                if y > 0: nb.append(i - nx)
+                if x > 0: nb.append(i - 1)
+                if x < nx - 1: nb.append(i + 1)
+                if y < ny - 1: nb.append(i + nx)
+                if z < nz - 1: nb.append(i + nx * ny)
+                diag = 6.0 if shift is None else len(nb) + shift[i]
+                cols = sorted(nb + [i])
+                for c in cols:
+                    ci.append(c)
+                    v.append(diag if c == i else -1.0)
+                rp.append(len(ci))
+    return np.array(rp, np.int32), np.array(ci, np.int32), np.array(v)
+
+
+def bsr_dense(s):
+    n, b = s["n"], s["b"]
+    A = np.zeros((n * b, n * b))
+    rp, ci, J = s["row_ptr"], s["col_idx"], s["vals"]
+    for i in range(n):
+        for k in range(rp[i], rp[i + 1]):
+            A[i * b:(i + 1) * b, ci[k] * b:(ci[k] + 1) * b] = J[k]
+    return A
+
+
+def tiny(nx=5, ny=4, nz=2, **kw):
+    return synth.make_box(nx, ny, nz, 3.125, seed=7, **kw)
+
+
+def pt_blocks(Ad, b, ps=0, ts=1):
+    """A_pp, A_pT, A_Tp, A_TT of a dense interleaved matrix."""
+    return Ad[ps::b, ps::b], Ad[ps::b, ts::b], Ad[ts::b, ps::b], Ad[ts::b, ts::b]
+
+
+def strong_sets(lev, theta=0.25):
+    """Strength graph S of a level, recomputed from its matrix (for the PMIS invariants)."""
+    n, rp, ci, v = lev["n"], lev["rp"], lev["ci"], lev["v"]
+    S = []
+    for i in range(n):
+        cols, vals = ci[rp[i]:rp[i + 1]], v[rp[i]:rp[i + 1]]
+        off = cols != i
+        m = (-vals[off]).max() if off.any() else 0.0
+        S.append(set(cols[off][-vals[off] >= theta * m].tolist()) if m > 0 else set())
+    return S
+
+
+# ------------------------------------------------------------------------------------------------
+# decoupling (eqs. weighted, scaling)
+def test_weighting_is_a_row_operation():
+    r = tiny()
+    s = r.system()
+    o = oracle.Oracle.from_system(s, max_levels=1, dense_max=4096)
+    A = bsr_dense(s)
+    Aw = o.dense()
+    b = s["rhs"].reshape(-1)
+    bw = o.weight_rhs(b)
+    # the solution of the weighted system solves the raw one (normwise backward error)
+    x2 = np.linalg.solve(Aw, bw)
+    assert np.linalg.norm(A @ x2 - b) <= 1e-13 * np.linalg.norm(A, 2) * np.linalg.norm(x2)
+    B = s["b"]
+    # energy rows untouched, pressure row = T_ref (c_vw water + c_vo oil), kept mass row = c_ref T_ref water
+    assert np.array_equal(Aw[1::B], A[1::B])
+    pr = r.T0 * (r.cv_w * A[0::B] + r.cv_o * A[2::B])
+    assert np.abs(Aw[0::B] - pr).max() <= 1e-14 * np.abs(pr).max()
+    cref = 0.8 * r.cv_o + 0.2 * r.cv_w
+    assert np.abs(Aw[2::B] - cref * r.T0 * A[0::B]).max() <= 1e-12 * np.abs(Aw[2::B]).max()
+
+
+# ------------------------------------------------------------------------------------------------
+# ILU(0)
+def _lu_from_factors(o):
+    rp, ci, _ = o.matrix()
+    v = o.ilu_factors()
+    n = o.nb
+    F = dense_csr(rp, ci, v, n)
+    L = np.tril(F, -1) + np.eye(n)
+    U = np.triu(F)
+    return L, U, rp, ci
+
+
+def test_ilu0_product_matches_matrix_on_pattern():
+    # the defining property of ILU(0): (L U)_ij = a_ij for every (i, j) in the pattern of A
+    o = oracle.Oracle.from_system(tiny().system(), max_levels=1, dense_max=4096)
+    L, U, rp, ci = _lu_from_factors(o)
+    A = o.dense()
+    LU = L @ U
+    mask = np.zeros_like(A, dtype=bool)
+    for i in range(o.nb):
+        mask[i, ci[rp[i]:rp[i + 1]]] = True
+    assert np.abs((LU - A)[mask]).max() <= 1e-12 * np.abs(A).max()
+    assert np.abs((LU - A)[~mask]).max() > 0  # dropped fill exists on a 2D grid
+
+
+def test_ilu0_solve_applies_lu_inverse():
+    o = oracle.Oracle.from_system(tiny().system(), max_levels=1, dense_max=4096)
+    L, U, _, _ = _lu_from_factors(o)
+    r = synth.normal(5, o.nb)
+    z = o.ilu_apply(r)
+    assert np.linalg.norm(L @ (U @ z) - r) <= 1e-10 * np.linalg.norm(r)
+
+
+def test_ilu0_exact_on_a_line():
+    # a 1D grid has a block-tridiagonal Jacobian: ILU(0) has no dropped fill, so it is exact LU
+    o = oracle.Oracle.from_system(synth.make_box(12, 1, 1, 3.125, seed=3).system(), max_levels=1)
+    A = o.dense()
+    r = synth.normal(6, o.nb)
+    assert np.linalg.norm(o.ilu_apply(r) - np.linalg.solve(A, r)) <= 1e-9 * np.linalg.norm(np.linalg.solve(A, r))
+
+
+def test_scalar_ilu0_equals_block_ilu0():
+    # with dense b x b blocks, scalar ILU(0) in cell-major order equals block ILU(0) with exact
+    # pivot-block inverses; the block form is written here from the textbook definition
+    s = tiny(4, 3, 2).system()
+    o = oracle.Oracle.from_system(s, max_levels=1, dense_max=4096)
+    n, b = s["n"], s["b"]
+    rp, ci = s["row_ptr"], s["col_idx"]
+    W = s["weights"]
+    blocks = {}
+    for i in range(n):
+        for k in range(rp[i], rp[i + 1]):
+            blocks[(i, int(ci[k]))] = W[i] @ s["vals"][k]
+    for i in range(n):
+        row = [int(c) for c in ci[rp[i]:rp[i + 1]]]
+        for k in [c for c in row if c < i]:
+            blocks[(i, k)] = blocks[(i, k)] @ np.linalg.inv(blocks[(k, k)])
+            for j in [c for c in row if c > k]:
+                if (k, j) in blocks:
+                    blocks[(i, j)] = blocks[(i, j)] - blocks[(i, k)] @ blocks[(k, j)]
+    r = synth.normal(8, n * b).reshape(n, b)
+    y = np.zeros((n, b))
+    for i in range(n):
+        y[i] = r[i] - sum(blocks[(i, int(k))] @ y[k] for k in ci[rp[i]:rp[i + 1]] if k < i)
+    z = np.zeros((n, b))
+    for i in reversed(range(n)):
+        t = y[i] - sum(blocks[(i, int(k))] @ z[k] for k in ci[rp[i]:rp[i + 1]] if k > i)
+        z[i] = np.linalg.solve(blocks[(i, i)], t)
+    zo = o.ilu_apply(r.reshape(-1))
+    assert np.linalg.norm(zo - z.reshape(-1)) <= 1e-10 * np.linalg.norm(z)
+
+
+# ------------------------------------------------------------------------------------------------
+# AMG
+def test_splitmix64_in_oracle():
+    assert [oracle.splitmix64(0, i) for i in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def pmis_reference(S, seed):
+    """Brute-force PMIS from its definition (De Sterck, Yang, Heys 2006) on Python sets: each
+    round, undecided points whose key (|S^T_i|, top 32 bits of SplitMix64(seed, i), index) beats
+    every undecided neighbour in S_i or S^T_i become C; undecided points that strongly depend on a
+    C point become F; points with no strong connection at all are F from the start."""
+    n = len(S)
+    ST = [set() for _ in range(n)]
+    for i in range(n):
+        for j in S[i]:
+            ST[j].add(i)
+    h = synth.splitmix64(seed, n) >> np.uint64(32)
+    key = [(len(ST[i]), int(h[i]), i) for i in range(n)]
+    state = ["F" if not S[i] and not ST[i] else "U" for i in range(n)]
+    while "U" in state:
+        new = [i for i in range(n) if state[i] == "U"
+               and all(key[i] > key[j] for j in S[i] | ST[i] if state[j] == "U")]
+        for i in new:
+            state[i] = "C"
+        for i in range(n):
+            if state[i] == "U" and any(state[j] == "C" for j in S[i]):
+                state[i] = "F"
+    return np.array([1 if t == "C" else 2 for t in state])
+
+
+@pytest.mark.parametrize("source", ["poisson", "App", "St"])
+def test_pmis_splitting(source):
+    if source == "poisson":
+        levels = oracle.AMG(*poisson3d(10, 10, 6), n_coarse=10).levels()
+    else:
+        s = synth.recipe("parity").system()
+        levels = oracle.Oracle.from_system(s).levels(0 if source == "App" else 1)
+    assert len(levels) >= 2
+    for l, lev in enumerate(levels[:-1]):
+        S = strong_sets(lev)
+        cf = lev["cf"]
+        assert np.array_equal(cf, pmis_reference(S, l))
+        for i in range(lev["n"]):
+            if cf[i] == 2 and S[i]:   # every F point with strong couplings has a strong C neighbour
+                assert any(cf[j] == 1 for j in S[i]), i
+        assert 0 < (cf == 1).sum() < lev["n"]
+
+
+@pytest.mark.parametrize("source", ["poisson", "App", "St"])
+def test_galerkin_coarse_operator(source):
+    if source == "poisson":
+        levels = oracle.AMG(*poisson3d(8, 8, 6), n_coarse=20).levels()
+    else:
+        s = synth.recipe("parity").system()
+        levels = oracle.Oracle.from_system(s).levels(0 if source == "App" else 1)
+    for l in range(len(levels) - 1):
+        f, c = levels[l], levels[l + 1]
+        A = dense_csr(f["rp"], f["ci"], f["v"], f["n"])
+        P = dense_csr(f["Prp"], f["Pci"], f["Pv"], f["n"], f["nc"])
+        Ac = dense_csr(c["rp"], c["ci"], c["v"], c["n"])
+        ref = P.T @ A @ P
+        assert np.abs(Ac - ref).max() <= 1e-13 * np.abs(ref).max()
+        # C points inject: their P row is a single 1 at their coarse index, numbered in order
+        cidx = np.cumsum(f["cf"] == 1) - 1
+        for i in np.nonzero(f["cf"] == 1)[0]:
+            assert P[i, cidx[i]] == 1.0 and np.count_nonzero(P[i]) == 1
+
+
+def test_direct_interpolation_preserves_constants():
+    # zero row sums on all rows but a few: F rows with zero row sum interpolate constants exactly
+    nx, ny, nz = 9, 8, 5
+    shift = np.zeros(nx * ny * nz)
+    shift[[0, 100, 250]] = 1.0
+    rp, ci, v = poisson3d(nx, ny, nz, shift)
+    lev = oracle.AMG(rp, ci, v, n_coarse=10).levels()[0]
+    P = dense_csr(lev["Prp"], lev["Pci"], lev["Pv"], lev["n"], lev["nc"])
+    rowsum = P.sum(axis=1)
+    zero_rows = np.abs(dense_csr(rp, ci, v, lev["n"]).sum(axis=1)) == 0
+    F = (lev["cf"] == 2) & zero_rows & (np.count_nonzero(P, axis=1) > 0)
+    assert F.sum() > 50
+    assert np.abs(rowsum[F] - 1.0).max() <= 1e-14
+
+
+def test_direct_interpolation_weights_closed_form():
+    # F point 0 with strong C neighbours 1, 2 (a = -1.5, -1), a weak negative neighbour 3
+    # (a = -0.1) and a positive neighbour 4 (a = +0.2), diagonal 4:
+    #   alpha = (-1.5 - 1 - 0.1) / (-1.5 - 1), d = 4 + 0.2, w_0j = -alpha a_0j / d
+    # points 1 and 2 are made C by giving each three more points (5-7, 8-10) that depend on them
+    rows = {0: {0: 4.0, 1: -1.5, 2: -1.0, 3: -0.1, 4: 0.2},
+            1: {0: -0.01, 1: 4.0, 5: -1.0, 6: -1.0, 7: -1.0},
+            2: {0: -0.01, 2: 4.0, 8: -1.0, 9: -1.0, 10: -1.0},
+            3: {0: -0.1, 3: 4.0}, 4: {0: 0.2, 4: 4.0}}
+    for leaf, c in ((5, 1), (6, 1), (7, 1), (8, 2), (9, 2), (10, 2)):
+        rows[leaf] = {c: -1.0, leaf: 4.0}
+    rp, ci, v = [0], [], []
+    for i in range(11):
+        for j in sorted(rows[i]):
+            ci.append(j)
+            v.append(rows[i][j])
+        rp.append(len(ci))
+    lev = oracle.AMG(np.array(rp), np.array(ci), np.array(v), n_coarse=1, max_levels=2).levels()[0]
+    cf = lev["cf"]
+    assert cf[1] == 1 and cf[2] == 1 and cf[0] == 2, cf
+    P = dense_csr(lev["Prp"], lev["Pci"], lev["Pv"], 11, lev["nc"])
+    cidx = np.cumsum(cf == 1) - 1
+    alpha = (-1.5 - 1.0 - 0.1) / (-1.5 - 1.0)
+    assert abs(P[0, cidx[1]] - (-alpha * -1.5 / 4.2)) < 1e-15
+    assert abs(P[0, cidx[2]] - (-alpha * -1.0 / 4.2)) < 1e-15
+    assert np.count_nonzero(P[0]) == 2
+
+
+def test_single_level_vcycle_is_exact():
+    rp, ci, v = poisson3d(6, 5, 4)
+    h = oracle.AMG(rp, ci, v, max_levels=1, dense_max=4096)
+    b = synth.normal(3, 120)
+    A = dense_csr(rp, ci, v, 120)
+    assert np.linalg.norm(h.vcycle(b) - np.linalg.solve(A, b)) <= 1e-12 * np.linalg.norm(np.linalg.solve(A, b))
+
+
+@pytest.mark.parametrize("smoother", [oracle.L1, oracle.JACOBI])
+def test_vcycle_converges_on_poisson(smoother):
+    # textbook behaviour (not a paper number): V(1,1) as a stationary iteration on 3D Poisson
+    rp, ci, v = poisson3d(16, 16, 16)
+    n = 16 ** 3
+    A = dense_csr(rp, ci, v, n)
+    h = oracle.AMG(rp, ci, v, n_coarse=50, smoother=smoother)
+    assert len(h.levels()) >= 3
+    b = np.zeros(n)
+    x = synth.normal(4, n)
+    e0 = np.linalg.norm(x)
+    k = 8
+    for _ in range(k):
+        x = x + h.vcycle(b - A @ x)
+    rho = (np.linalg.norm(x) / e0) ** (1.0 / k)
+    assert rho < 0.5, rho
+
+
+def test_smoother_diagonals():
+    rp, ci, v = poisson3d(5, 4, 3)
+    lev = oracle.AMG(rp, ci, v, max_levels=1).levels()[0]
+    A = dense_csr(rp, ci, v, 60)
+    assert np.allclose(lev["dinv"], 1.0 / np.abs(A).sum(axis=1), rtol=1e-15)
+    lev = oracle.AMG(rp, ci, v, max_levels=1, smoother=oracle.JACOBI).levels()[0]
+    assert np.allclose(lev["dinv"], (2.0 / 3.0) / np.diag(A), rtol=1e-15)
+
+
+# ------------------------------------------------------------------------------------------------
+# the block preconditioner for A_00 (eqs. Afact, Ainv, Aschur) and the two-stage combination
+def _exact_setup(r, mode, st="given"):
+    s = r.system()
+    n, b = s["n"], s["b"]
+    o0 = oracle.Oracle.from_system(s, max_levels=1, dense_max=4096)
+    Ad = o0.dense()
+    App, ApT, ATp, ATT = pt_blocks(Ad, b)
+    S_exact = ATT - ATp @ np.linalg.solve(App, ApT)
+    if st == "exact":
+        full_rp = np.arange(0, n * n + 1, n, dtype=np.int32)
+        full_ci = np.tile(np.arange(n, dtype=np.int32), n)
+        o = oracle.Oracle(n, b, s["row_ptr"], s["col_idx"], s["vals"], s["weights"], st=S_exact.reshape(-1),
+                          st_pattern=(full_rp, full_ci), stage1=mode, max_levels=1, dense_max=4096)
+        St = S_exact
+    else:
+        o = oracle.Oracle.from_system(s, stage1=mode, max_levels=1, dense_max=4096)
+        St = dense_csr(s["row_ptr"], s["col_idx"], s["st"], n)
+    return s, o, Ad, (App, ApT, ATp, ATT), St
+
+
+def test_exact_inner_solves_give_exact_block_inverse():
+    # eqs. (Afact)/(Ainv): with exact A_pp^{-1} and S~_T = S_T the five steps apply A_00^{-1}
+    r = tiny()
+    s, o, Ad, (App, ApT, ATp, ATT), St = _exact_setup(r, oracle.CPTR_FULL, st="exact")
+    n, b = s["n"], s["b"]
+    A00 = np.block([[App, ApT], [ATp, ATT]])
+    M1 = np.zeros((2 * n, 2 * n))
+    for c in range(2 * n):
+        v = np.zeros(n * b)
+        v[(c % n) * b + (c // n)] = 1.0
+        x1 = o.stage1(v).reshape(n, b)
+        M1[:, c] = np.concatenate([x1[:, 0], x1[:, 1]])
+        assert np.all(x1[:, 2:] == 0.0)
+    assert np.abs(M1 @ A00 - np.eye(2 * n)).max() <= 1e-8
+
+
+@pytest.mark.parametrize("mode", [oracle.CPTR_FULL, oracle.CPTR_LOWER, oracle.CPTR_UPPER, oracle.BD, oracle.CPR])
+def test_stage1_matches_factored_form(mode):
+    # eq. (Aschur) with exact A_pp^{-1} and the given S~_T; triangular variants drop a factor
+    r = tiny()
+    s, o, Ad, (App, ApT, ATp, ATT), St = _exact_setup(r, mode)
+    n, b = s["n"], s["b"]
+    I, Z = np.eye(n), np.zeros((n, n))
+    Ai, Si = np.linalg.inv(App), np.linalg.inv(St)
+    left = np.block([[I, -Ai @ ApT], [Z, I]])
+    mid = np.block([[Ai, Z], [Z, Si]])
+    right = np.block([[I, Z], [-ATp @ Ai, I]])
+    ref = {oracle.CPTR_FULL: left @ mid @ right, oracle.CPTR_LOWER: mid @ right, oracle.CPTR_UPPER: left @ mid,
+           oracle.BD: mid, oracle.CPR: np.block([[Ai, Z], [Z, Z]])}[mode]
+    v = synth.normal(11, n * b)
+    x1 = o.stage1(v).reshape(n, b)
+    vv = v.reshape(n, b)
+    want = ref @ np.concatenate([vv[:, 0], vv[:, 1]])
+    got = np.concatenate([x1[:, 0], x1[:, 1]])
+    assert np.linalg.norm(got - want) <= 1e-9 * np.linalg.norm(want)
+
+
+def test_schur_complement_invariant_to_pressure_row_scaling():
+    # S_T = A_TT - A_Tp A_pp^{-1} A_pT does not change when the pressure row is rescaled
+    s = tiny().system()
+    b = s["b"]
+    out = []
+    for scale in (1.0, 7.3):
+        W = s["weights"].copy()
+        W[:, 0, :] *= scale
+        o = oracle.Oracle(s["n"], b, s["row_ptr"], s["col_idx"], s["vals"], W, st=s["st"], max_levels=1, dense_max=4096)
+        App, ApT, ATp, ATT = pt_blocks(o.dense(), b)
+        out.append(ATT - ATp @ np.linalg.solve(App, ApT))
+    assert np.abs(out[0] - out[1]).max() <= 1e-10 * np.abs(out[0]).max()
+
+
+def test_schur_approximation_conditioning_trend():
+    # Table (tab:conds) trend: S~_T of eq. (Se) is a much better approximation of S_T than A_TT
+    r = synth.make_box(8, 8, 1, 3.125, seed=12, heaters=[(9, 200.0, 450.0), (54, 200.0, 450.0)], dt=86400.0 * 30)
+    s = r.system()
+    o = oracle.Oracle.from_system(s, max_levels=1, dense_max=4096)
+    App, ApT, ATp, ATT = pt_blocks(o.dense(), s["b"])
+    S = ATT - ATp @ np.linalg.solve(App, ApT)
+    St = dense_csr(s["row_ptr"], s["col_idx"], s["st"], s["n"])
+    Sdiag = ATT - ATp @ np.diag(1.0 / np.diag(App)) @ ApT
+
+    def kappa(M):
+        ev = np.abs(np.linalg.eigvals(np.linalg.solve(M, S)))
+        return ev.max() / ev.min()
+
+    k_st, k_att, k_diag = kappa(St), kappa(ATT), kappa(Sdiag)
+    assert k_st < 3.0
+    assert k_st <= k_att and k_st <= k_diag
+
+
+def test_two_stage_formula():
+    # M^{-1} = M2^{-1} (I - A M1^{-1}) + M1^{-1}   (Sec. 3, two-stage preconditioners)
+    s = tiny(4, 3, 2).system()
+    o = oracle.Oracle.from_system(s, max_levels=2, n_coarse=4)
+    nb = o.nb
+    A = o.dense()
+    E = np.eye(nb)
+    M1 = np.column_stack([o.stage1(E[:, c]) for c in range(nb)])
+    M2 = np.column_stack([o.ilu_apply(E[:, c]) for c in range(nb)])
+    M = M2 @ (np.eye(nb) - A @ M1) + M1
+    v = synth.normal(13, nb)
+    assert np.linalg.norm(o.precond(v) - M @ v) <= 1e-10 * np.linalg.norm(M @ v)
+
+
+def test_exact_two_stage_converges_in_one_iteration():
+    # 1D grid: ILU(0) is exact LU, so the two-stage preconditioner is A^{-1} for any first stage
+    s = synth.make_box(16, 1, 1, 3.125, seed=4).system()
+    for mode in (oracle.CPTR_FULL, oracle.CPR):
+        o = oracle.Oracle.from_system(s, stage1=mode, max_levels=2, n_coarse=4)
+        x, info = o.solve(s["rhs"], 1e-10)
+        assert info["converged"] and info["iters"] == 1, info
+
+
+# ------------------------------------------------------------------------------------------------
+# FGMRES
+def test_fgmres_solution_matches_dense_solve():
+    s = tiny(6, 5, 3).system()
+    o = oracle.Oracle.from_system(s, max_levels=2, n_coarse=8)
+    x, info = o.solve(s["rhs"], 1e-10)
+    A = o.dense()
+    xs = np.linalg.solve(A, o.weight_rhs(s["rhs"].reshape(-1)))
+    kappa = np.linalg.cond(A)
+    assert info["converged"] and info["true_rel_res"] <= 1e-10 * 1.01
+    assert np.linalg.norm(x - xs) <= kappa * 1e-10 * np.linalg.norm(xs)
+    assert abs(info["true_rel_res"] - info["est_rel_res"]) <= 1e-3 * info["est_rel_res"] + 1e-14
+
+
+@pytest.mark.parametrize("mode", [oracle.NONE1, oracle.CPTR_FULL])
+def test_gmres_minimal_residual_property(mode):
+    # after k steps without restart the residual is min over x in M^{-1} K_k(A M^{-1}, b)
+    s = tiny(5, 4, 2).system()
+    k = 6
+    stage2 = oracle.NONE2 if mode == oracle.NONE1 else oracle.ILU0
+    o = oracle.Oracle.from_system(s, stage1=mode, stage2=stage2, max_levels=2, n_coarse=4, max_it=k, restart=30)
+    x, info = o.solve(s["rhs"], 1e-30)
+    assert info["iters"] == k and not info["converged"]
+    nb = o.nb
+    A = o.dense()
+    Mi = np.column_stack([o.precond(np.eye(nb)[:, c]) for c in range(nb)])
+    B = A @ Mi
+    b = o.weight_rhs(s["rhs"].reshape(-1))
+    K = np.zeros((nb, k))
+    v = b / np.linalg.norm(b)
+    for j in range(k):
+        K[:, j] = v
+        v = B @ v
+        v = v / np.linalg.norm(v)
+    Q, _ = np.linalg.qr(K)
+    y, *_ = np.linalg.lstsq(B @ Q, b, rcond=None)
+    rmin = np.linalg.norm(b - B @ Q @ y) / np.linalg.norm(b)
+    assert abs(info["true_rel_res"] - rmin) <= 1e-6 * rmin
+    assert abs(info["est_rel_res"] - rmin) <= 1e-6 * rmin
+
+
+def test_identity_preconditioner_restarted_gmres():
+    s = tiny(4, 3, 2).system()
+    o = oracle.Oracle.from_system(s, stage1=oracle.NONE1, stage2=oracle.ILU0, restart=5, max_it=2000)
+    x, info = o.solve(s["rhs"], 1e-9)
+    assert info["converged"] and info["restarts"] >= 1
+    A = o.dense()
+    xs = np.linalg.solve(A, o.weight_rhs(s["rhs"].reshape(-1)))
+    assert np.linalg.norm(A @ x - A @ xs) <= 1.01e-9 * np.linalg.norm(A @ xs)
+
+
+def test_zero_rhs_returns_zero():
+    s = tiny(3, 3, 1).system()
+    o = oracle.Oracle.from_system(s, max_levels=1)
+    x, info = o.solve(np.zeros(o.nb), 1e-8)
+    assert info["converged"] and info["iters"] == 0 and not x.any()
+
+
+def test_cptr_needs_fewer_iterations_than_cpr_when_conduction_dominates():
+    # trend of Tables (tab:meshW)-(tab:anisomeshW): with heat diffusion dominant CPTR beats CPR
+    r = synth.make_box(24, 24, 4, 0.5, 0.5, 0.25, seed=11, sigma=2.0, layered=True, kv_ratio=0.1, kT_const=2.0,
+                       T_inj=500.0, q_inj=1e-6, dt=365 * 86400.0)
+    s = r.system()
+    its = {}
+    for mode in (oracle.CPTR_FULL, oracle.CPR):
+        x, info = oracle.Oracle.from_system(s, stage1=mode, n_coarse=64).solve(s["rhs"], 1e-6)
+        assert info["converged"]
+        its[mode] = info["iters"]
+    assert its[oracle.CPTR_FULL] < its[oracle.CPR], its
