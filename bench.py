@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Benchmark of the CPTR-FGMRES hot path on one GB300 per rank.
+
+A step is one pass of the whole path on one Jacobian: cptr_setup (decoupling, p-T extraction,
+two AMG hierarchies built on the device, block ILU(0)) followed by cptr_solve (FGMRES(30) with
+the two-stage CPTR preconditioner to a 1e-6 relative residual), on the seeded synthetic
+100x100x20 workload (200k cells, 600k unknowns).  Inputs are resident in HBM when the timed
+region starts and L2 is flushed before every step.  Ranks (torchrun) run independent replicas:
+the method has no data-parallel split of one system, so there is no collective on the data path.
+
+--impl reference times the FP64 CPU oracle on the same workload (host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CPTR-FGMRES solve time & dofs/s to 1e-6 rel. residual; SpMV/V-cycle HBM GB/s"
+UNIT = "dofs/s"
+RTOL = 1e-6
+WORKLOAD = "cptr200k"
+L2_BYTES = 129 * 2 ** 20
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return PEAKS_FALLBACK["hbm_gbs"], "fallback"
+
+
+# ------------------------------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        if not shutil.which("nvidia-smi"):
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd.insert(1, f"--id={self.gpu_id}")
+        self.fh = open(self.path, "w")
+        self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[3:]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_identifier(torch, dev):
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    if uuid is not None:
+        u = str(uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    return None
+
+
+# ------------------------------------------------------------------------------------------------
+def oracle_step(s):
+    import oracle
+    t0 = time.perf_counter()
+    o = oracle.Oracle.from_system(s)
+    x, info = o.solve(s["rhs"], RTOL)
+    return time.perf_counter() - t0, info
+
+
+def algorithmic_spmv_bytes(n, nnzb, b):
+    """Bytes one BSR SpMV w = A' z must move once: blocks (b*b FP64 + int32 column), row
+    pointers, z read once, w written once."""
+    return nnzb * (8 * b * b + 4) + (n + 1) * 4 + 2 * n * b * 8
+
+
+def ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_1907_04229_gb300 as cp
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    r = synth.recipe(WORKLOAD)
+    s = r.system()
+    n, b, nnzb = s["n"], s["b"], int(s["row_ptr"][-1])
+    dofs = n * b
+    host = {"rp": s["row_ptr"], "ci": s["col_idx"], "vals": s["vals"].reshape(-1), "kind": s["unknown_kind"],
+            "W": s["weights"].reshape(-1), "st": s["st"], "rhs": s["rhs"].reshape(-1)}
+    d = {k: torch.as_tensor(np.ascontiguousarray(v), device=dev) for k, v in host.items()}
+    x = torch.empty(dofs, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    S = cp.Solver(stream=stream)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        S.setup(n, b, d["rp"], d["ci"], d["vals"], d["kind"], d["W"], d["st"])
+        return S.solve(d["rhs"], RTOL, x=x)[1]
+
+    for _ in range(args.warmup):
+        info = step()
+    assert info["status"] == "CPTR_OK", info
+    cp.cptr_set_profiling(S.ctx, 0b11111)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(gpu_identifier(torch, dev))
+    clocks.start()
+    launches0 = cp.cptr_launch_count()
+    events = []
+    prof_sum = {k: [0.0, 0] for k in cp.PROFILE_FAMILIES}
+    infos = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos.append(step())
+        e1.record(stream)
+        events.append((e0, e1))
+        for k, (ms, cnt) in cp.cptr_profile(S.ctx).items():
+            prof_sum[k][0] += ms
+            prof_sum[k][1] += cnt
+    torch.cuda.synchronize(dev)
+    launches = cp.cptr_launch_count() - launches0
+    barrier(world)
+    clk = clocks.stop()
+    cp.cptr_set_profiling(S.ctx, 0)
+    total_ms = sum(a.elapsed_time(bb) for a, bb in events)
+    total_ms = allreduce_max(total_ms, world, dev)
+    ms_per_step = total_ms / args.steps
+    value = world * dofs * args.steps / (total_ms / 1e3)
+    setup_ms = statistics.mean(i["setup_ms"] for i in infos)
+    solve_ms = statistics.mean(i["solve_ms"] for i in infos)
+    iters = infos[-1]["iters"]
+
+    # roofline of the outer BSR SpMV (one kernel per timed region)
+    peak, peak_kind = peaks()
+    spmv_ms, spmv_n = prof_sum["spmv"]
+    spmv_bytes = algorithmic_spmv_bytes(n, nnzb, b)
+    spmv_avg_ms = spmv_ms / max(spmv_n, 1)
+    achieved = spmv_bytes / (spmv_avg_ms / 1e3) / 1e9
+    roofline = {"kernel": "k_bsr_spmv<3,8,0> (outer w = A' z_j)", "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": peak, "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "algorithmic_bytes_per_launch": spmv_bytes, "avg_launch_us": round(spmv_avg_ms * 1e3, 2)}
+    families = {k: {"ms_per_step": round(v[0] / args.steps, 3), "regions_per_step": v[1] / args.steps}
+                for k, v in prof_sum.items()}
+
+    # end to end through the public API with pinned host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        hp = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
+        xh = torch.empty(dofs, dtype=torch.float64).pin_memory()
+        Sh = cp.Solver(stream=stream)
+
+        def step_host():
+            Sh.setup(n, b, hp["rp"].numpy(), hp["ci"].numpy(), hp["vals"].numpy(), hp["kind"].numpy(),
+                     hp["W"].numpy(), hp["st"].numpy())
+            return Sh.solve(hp["rhs"].numpy(), RTOL, x=xh.numpy())[1]
+
+        for _ in range(max(1, min(args.warmup, 2))):
+            step_host()
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        t_tot = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            ih = step_host()
+            t_tot += time.perf_counter() - t0
+        t_tot = allreduce_max(t_tot * 1e3, world, dev)
+        h2d = sum(v.numel() * v.element_size() for v in hp.values())
+        e2e = {"value": world * dofs * args.steps / (t_tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": dofs * 8, "ms_per_step": t_tot / args.steps, "iters": ih["iters"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs, oinfo = oracle_step(s)
+        cpu = {"value": dofs / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one full setup+solve of the {WORKLOAD} workload ({dofs} dofs) by the serial FP64 C oracle, "
+                         f"{secs:.2f} s, {oinfo['iters']} iterations"}
+    if rank == 0:
+        out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": "cptr200k: 100x100x20 cells, 3 unknowns/cell (600k dofs), layered lognormal "
+                                      "permeability sigma 2, kv/kh 0.1, k_T 2 W/m/K, 500 K injector; CPTR "
+                                      "(full block factorisation, S_e Schur approximation) + ILU(0), FGMRES(30), "
+                                      "rtol 1e-6, FP64",
+                          "step": "cptr_setup + cptr_solve", "parallelism": f"replicas x{world}",
+                          "l2": "flushed before every step (256 MB write); working set > 1 GB"},
+               "iters": iters, "setup_ms": round(setup_ms, 3), "solve_ms": round(solve_ms, 3),
+               "solve_dofs_per_s": round(dofs / (solve_ms / 1e3), 1),
+               "true_rel_res": infos[-1]["true_rel_res"], "levels": [infos[-1]["levels_p"], infos[-1]["levels_T"]],
+               "families": families, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(out), flush=True)
+
+
+def reference(args, rank, world):
+    if rank != 0:
+        return
+    import synth
+    s = synth.recipe(WORKLOAD).system()
+    dofs = s["n"] * s["b"]
+    for _ in range(args.warmup):
+        oracle_step(s)
+    total = 0.0
+    for _ in range(args.steps):
+        secs, info = oracle_step(s)
+        total += secs
+    value = dofs * args.steps / total
+    sample = f"one full setup+solve of the {WORKLOAD} workload per step, serial FP64 C oracle, {info['iters']} iterations"
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "cptr200k: 100x100x20 cells, 3 unknowns/cell (600k dofs), CPTR + ILU(0), "
+                                  "FGMRES(30), rtol 1e-6, FP64", "step": "setup + solve"},
+           "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(v, world, dev):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        print(f"warning: --gpus {args.gpus} but WORLD_SIZE {world}", file=sys.stderr)
+    if args.impl == "reference":
+        reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    import __graft_entry__
+    __graft_entry__.build()
+    ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * cptr.h -- C ABI of the GB300 (sm_103a) CPTR-FGMRES library.
+ *
+ * Solves one Newton linear system A dx = b of fully implicit non-isothermal multiphase porous-
+ * media flow with right-preconditioned flexible GMRES and the two-stage Constrained Pressure-
+ * Temperature Residual preconditioner of Roy, Jonsthovel, Lemon, Wathen (arXiv 1907.04229):
+ *   Sec. 3.2, eq. (AXR)     the block system in (p, T, saturations) unknowns;
+ *   Sec. 2.2.2, eqs. (weighted), (scaling)   equation weighting applied as A' = W A, b' = W b;
+ *   Sec. 3, "Two-stage preconditioners"     z = M2^{-1}(v - A' x1) + x1, x1 = M1^{-1} v;
+ *   Sec. 3.2 eq. (A00), Sec. 3.3 eq. (Aschur) and its five steps    stage 1 on the p-T block;
+ *   Sec. 3.3.1 eq. (Se)     the Schur-complement approximation S~_T (supplied by the caller);
+ *   Sec. 3.1                CPR (pressure-only first stage), the baseline;
+ *   Sec. 4                  ILU(0) second stage, AMG V-cycles for A_pp and S~_T, GMRES tol.
+ * Every step runs in this library's CUDA kernels on the current device.  All calls are
+ * synchronous with respect to the host unless stated otherwise.
+ *
+ * Conventions for every entry point:
+ *   - Return value: CPTR_OK (0), CPTR_NOT_CONVERGED (1) or a negative error code.  No C++
+ *     exception crosses the ABI.  After an error, cptr_last_error(ctx) describes it.
+ *   - Ownership: the caller owns every input and output buffer.  The library copies what it
+ *     keeps; nothing the caller passes is retained after a call returns.
+ *   - Pointers: "on_device" = 1 means every array argument of the call is device memory of the
+ *     current device (e.g. a torch CUDA tensor's data_ptr); 0 means host memory, copied inside.
+ *   - Indices are int32, values IEEE double, arrays contiguous.
+ */
+#ifndef CPTR_H
+#define CPTR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cptr_ctx cptr_ctx;
+
+typedef enum {
+    CPTR_OK = 0,
+    CPTR_NOT_CONVERGED = 1, /* max_it reached; x holds the last iterate, stats are filled */
+    CPTR_EINVAL = -1,       /* invalid argument or malformed matrix (message says which) */
+    CPTR_ENOMEM = -2,       /* device allocation failed */
+    CPTR_ECUDA = -3,        /* a CUDA runtime call failed */
+    CPTR_EBREAKDOWN = -4,   /* non-finite value in the Krylov iteration */
+    CPTR_ETIMEOUT = -5,     /* a bounded device-side wait gave up */
+    CPTR_ESINGULAR = -6,    /* zero pivot in ILU(0) or singular coarsest AMG matrix */
+    CPTR_ESTATE = -7        /* call out of order (e.g. solve before setup) */
+} cptr_status;
+
+/* first stage M1 (Sec. 3.1, 3.3): full block factorisation, its block-triangular variants
+ * (one factor of eq. (Aschur) dropped), block diagonal, CPR pressure-only, or none */
+enum { CPTR_STAGE1_FULL = 0, CPTR_STAGE1_UPPER = 1, CPTR_STAGE1_LOWER = 2, CPTR_STAGE1_BD = 3,
+       CPTR_STAGE1_CPR = 4, CPTR_STAGE1_NONE = 5 };
+/* second stage M2: ILU(0) on the full system (Sec. 4) or none */
+enum { CPTR_STAGE2_ILU0 = 0, CPTR_STAGE2_NONE = 1 };
+/* Schur approximation: the caller's S~_T (eq. Se) or A_TT (Sec. 3.3.1) */
+enum { CPTR_SCHUR_GIVEN = 0, CPTR_SCHUR_ATT = 1 };
+/* AMG smoother: l1-Jacobi (d_i = sum_j |a_ij|) or omega-Jacobi (d_i = a_ii / omega) */
+enum { CPTR_SMOOTH_L1 = 0, CPTR_SMOOTH_JACOBI = 1 };
+/* precision of the preconditioner: all FP64, or FP32 AMG/ILU with BF16 coarse AMG levels */
+enum { CPTR_PREC_FP64 = 0, CPTR_PREC_MIXED = 1 };
+/* unknown kinds, one per block slot */
+enum { CPTR_U_P = 0, CPTR_U_T = 1, CPTR_U_SAT = 2 };
+
+typedef struct {
+    int32_t stage1, stage2, schur, smoother;
+    double omega;        /* omega-Jacobi weight (default 2/3) */
+    double theta;        /* AMG strength threshold (default 0.25) */
+    int32_t n_coarse;    /* stop coarsening at n <= n_coarse (default 256) */
+    int32_t max_levels;  /* AMG levels including the coarsest (default 25) */
+    int32_t restart;     /* FGMRES restart length m (default 30, at most 32) */
+    int32_t max_it;      /* total Arnoldi steps (default 1000) */
+    int32_t dense_max;   /* coarsest level solved densely if n <= dense_max (default 1024) */
+    int32_t seed;        /* PMIS weights: SplitMix64 stream seed + level */
+    int32_t precision;   /* CPTR_PREC_* */
+    int32_t check_every; /* host reads the convergence flag every k Arnoldi steps (default 1) */
+    void *stream;        /* cudaStream_t for all work; NULL = the legacy default stream */
+} cptr_options;
+
+typedef struct {
+    int32_t iters;           /* Arnoldi steps taken (all restart cycles) */
+    int32_t restarts;
+    int32_t converged;
+    int32_t levels_p, levels_T;
+    int32_t pad;
+    double est_rel_res;      /* Givens estimate |g_{j+1}| / ||b'|| at exit */
+    double true_rel_res;     /* ||b' - A' x|| / ||b'|| recomputed at exit */
+    double bnorm;            /* ||b'|| = ||W rhs|| */
+    double setup_ms, solve_ms;
+    double op_complexity_p, op_complexity_T;
+} cptr_stats;
+
+/* Fill *opt with the defaults listed above. */
+cptr_status cptr_default_options(cptr_options *opt);
+
+/* Create a context on the current device.  *out receives it (NULL on failure). */
+cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt);
+
+/* Destroy a context and free its device memory (NULL is ignored). */
+void cptr_destroy(cptr_ctx *ctx);
+
+/* Message of the last error on ctx ("" if none).  Valid until the next call on ctx. */
+const char *cptr_last_error(const cptr_ctx *ctx);
+
+/*
+ * Set up the preconditioner for one Jacobian (Sec. 3.2 eq. AXR; Sec. 3.3; Sec. 4).
+ *   n_cells, b     number of cells and unknowns per cell (b = 3 or 4)
+ *   row_ptr        [n_cells+1] BSR block-row pointers
+ *   col_idx        [nnzb] block column indices, strictly ascending within each row, the
+ *                  diagonal block present in every row
+ *   vals           [nnzb*b*b] raw Jacobian blocks, row-major within a block:
+ *                  vals[(k*b + r)*b + c] = d(equation r)/d(unknown c) of block k
+ *   unknown_kind   [b] CPTR_U_* per slot; exactly one P and one T
+ *   row_weights    [n_cells*b*b] per-cell W_i (row-major), the decoupled block row is W_i times
+ *                  the raw block row (eqs. weighted, scaling); NULL = identity
+ *   st_vals        [nnzb] S~_T on the same cell pattern (eq. Se); NULL = A_TT
+ * Validates the pattern on the host and the values on the device (finite), then builds on the
+ * device: the decoupled A', the p-T blocks, two AMG hierarchies and the ILU(0) factors.
+ * Errors: CPTR_EINVAL (bad sizes or pattern, non-finite values), CPTR_ESINGULAR, CPTR_ENOMEM,
+ * CPTR_ECUDA.  A context may be set up again; the previous setup is released first.
+ */
+cptr_status cptr_setup(cptr_ctx *ctx, int32_t n_cells, int32_t b, const int32_t *row_ptr,
+                       const int32_t *col_idx, const double *vals, const int32_t *unknown_kind,
+                       const double *row_weights, const double *st_vals, int32_t on_device);
+
+/*
+ * Solve A' x = W rhs with FGMRES(m) from x = 0 until |g_{j+1}| <= rtol * ||W rhs|| (Sec. 4).
+ *   rhs  [n_cells*b] raw right-hand side (cell-major, slot order of the setup)
+ *   x    [n_cells*b] output solution
+ *   st   optional statistics (may be NULL)
+ * Returns CPTR_OK, CPTR_NOT_CONVERGED (x = last iterate), CPTR_EBREAKDOWN, CPTR_ETIMEOUT,
+ * CPTR_ESTATE (no setup) or CPTR_ECUDA.
+ */
+cptr_status cptr_solve(cptr_ctx *ctx, const double *rhs, double *x, double rtol, cptr_stats *st,
+                       int32_t on_device);
+
+/* ------------------------------------------------------------------------------------------
+ * Component entry points.  They apply one piece of the set-up operator, for parity tests and
+ * profiling.  All vectors are device memory of length n_cells*b (cell-major) unless stated.
+ * ------------------------------------------------------------------------------------------ */
+
+/* y = A' x with the decoupled Jacobian A' = W A (BSR SpMV). */
+cptr_status cptr_apply_matrix(cptr_ctx *ctx, const double *x, double *y);
+
+/* out = W rhs (per-cell b x b weights). */
+cptr_status cptr_apply_weights(cptr_ctx *ctx, const double *rhs, double *out);
+
+/* x1 = M1^{-1} v: stage 1 of the selected kind; slots other than p and T are set to 0. */
+cptr_status cptr_apply_stage1(cptr_ctx *ctx, const double *v, double *x1);
+
+/* z = (L U)^{-1} r with the block ILU(0) factors of A'. */
+cptr_status cptr_apply_ilu(cptr_ctx *ctx, const double *r, double *z);
+
+/* z = M^{-1} v, the full two-stage preconditioner. */
+cptr_status cptr_apply_precond(cptr_ctx *ctx, const double *v, double *z);
+
+/* x = one V(1,1)-cycle from zero on hierarchy `which` (0: A_pp, 1: S~_T); b, x of length n_cells. */
+cptr_status cptr_apply_vcycle(cptr_ctx *ctx, int32_t which, const double *b, double *x);
+
+/* Hierarchy shape: *nlev levels; for level l, info[l*4 + {0,1,2,3}] = {n, nnz, nnzP, dense}
+ * (nnzP = 0 on the coarsest level; dense = 1 if the coarsest level is solved densely).
+ * info must hold 4 * 32 int32 (host memory). */
+cptr_status cptr_hierarchy_info(cptr_ctx *ctx, int32_t which, int32_t *nlev, int32_t *info);
+
+/* Copy level l of hierarchy `which` to host buffers sized from cptr_hierarchy_info:
+ * rp[n+1], ci[nnz], v[nnz], dinv[n]; and if l is not the coarsest: cf[n] (1 = C, 2 = F),
+ * Prp[n+1], Pci[nnzP], Pv[nnzP].  Any pointer may be NULL to skip that array. */
+cptr_status cptr_hierarchy_level(cptr_ctx *ctx, int32_t which, int32_t l, int32_t *rp, int32_t *ci,
+                                 double *v, double *dinv, int32_t *cf, int32_t *Prp, int32_t *Pci,
+                                 double *Pv);
+
+/* Number of ILU level sets of the forward and backward sweeps (host ints). */
+cptr_status cptr_ilu_levels(cptr_ctx *ctx, int32_t *n_forward, int32_t *n_backward);
+
+/* Number of kernels this library has launched in this process (all contexts, since load). */
+int64_t cptr_launch_count(void);
+
+/* Time families of kernels with CUDA events on the context's stream during cptr_solve; bit f
+ * of mask enables family f: 0 the outer BSR SpMV w = A' z_j (one kernel per region),
+ * 1 stage 1, 2 the stage-1 residual v - A' x1 (one kernel), 3 the ILU(0) solve, 4 Arnoldi
+ * (three Gram-Schmidt passes, Givens, normalisation).  0 disables (the default). */
+cptr_status cptr_set_profiling(cptr_ctx *ctx, uint32_t mask);
+
+/* Event time (ms) and number of timed regions per family during the last cptr_solve (host
+ * arrays of 8 entries; either may be NULL). */
+cptr_status cptr_profile(cptr_ctx *ctx, double *ms, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPTR_H */

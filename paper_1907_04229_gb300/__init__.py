@@ -1,0 +1,284 @@
+"""Python binding of the GB300 CPTR-FGMRES library (C ABI in include/cptr.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels of libcptr.so.  The
+functions mirror the C entry points by name; :class:`Solver` bundles them for torch tensors.
+There is no CPU fallback: if libcptr.so is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+LIB_PATH = _build.LIB
+
+CPTR_OK, CPTR_NOT_CONVERGED = 0, 1
+STATUS = {0: "CPTR_OK", 1: "CPTR_NOT_CONVERGED", -1: "CPTR_EINVAL", -2: "CPTR_ENOMEM", -3: "CPTR_ECUDA",
+          -4: "CPTR_EBREAKDOWN", -5: "CPTR_ETIMEOUT", -6: "CPTR_ESINGULAR", -7: "CPTR_ESTATE"}
+STAGE1 = {"full": 0, "upper": 1, "lower": 2, "bd": 3, "cpr": 4, "none": 5}
+STAGE2 = {"ilu0": 0, "none": 1}
+SCHUR = {"given": 0, "att": 1}
+SMOOTHER = {"l1": 0, "jacobi": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
+U_P, U_T, U_SAT = 0, 1, 2
+
+
+class cptr_options(ctypes.Structure):
+    _fields_ = [("stage1", ctypes.c_int32), ("stage2", ctypes.c_int32), ("schur", ctypes.c_int32),
+                ("smoother", ctypes.c_int32), ("omega", ctypes.c_double), ("theta", ctypes.c_double),
+                ("n_coarse", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("max_it", ctypes.c_int32), ("dense_max", ctypes.c_int32), ("seed", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("check_every", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class cptr_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("levels_p", ctypes.c_int32), ("levels_T", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("est_rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double), ("bnorm", ctypes.c_double),
+                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("op_complexity_p", ctypes.c_double), ("op_complexity_T", ctypes.c_double)]
+
+
+class CptrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int32
+_SIGS = {
+    "cptr_default_options": (_I, [_P]),
+    "cptr_create": (_I, [_P, _P]),
+    "cptr_destroy": (None, [_P]),
+    "cptr_last_error": (ctypes.c_char_p, [_P]),
+    "cptr_setup": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _I]),
+    "cptr_solve": (_I, [_P, _P, _P, ctypes.c_double, _P, _I]),
+    "cptr_apply_matrix": (_I, [_P, _P, _P]),
+    "cptr_apply_weights": (_I, [_P, _P, _P]),
+    "cptr_apply_stage1": (_I, [_P, _P, _P]),
+    "cptr_apply_ilu": (_I, [_P, _P, _P]),
+    "cptr_apply_precond": (_I, [_P, _P, _P]),
+    "cptr_apply_vcycle": (_I, [_P, _I, _P, _P]),
+    "cptr_hierarchy_info": (_I, [_P, _I, _P, _P]),
+    "cptr_hierarchy_level": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "cptr_ilu_levels": (_I, [_P, _P, _P]),
+    "cptr_launch_count": (ctypes.c_int64, []),
+    "cptr_set_profiling": (_I, [_P, ctypes.c_uint32]),
+    "cptr_profile": (_I, [_P, _P, _P]),
+}
+PROFILE_FAMILIES = ("spmv", "stage1", "stage1_resid", "ilu", "arnoldi")
+
+
+def load():
+    """Load libcptr.so (built by ``build()``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libcptr.so not found at {LIB_PATH}: run __graft_entry__.build() (no CPU fallback)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def _ptr(t):
+    """Data pointer of a torch tensor or numpy array (None passes through)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _on_device(*ts):
+    devs = {bool(getattr(t, "is_cuda", False)) for t in ts if t is not None}
+    if len(devs) > 1:
+        raise ValueError("mix of host and device arrays in one call")
+    return int(devs.pop()) if devs else 0
+
+
+def _check(ctx, code, ok=(CPTR_OK,)):
+    if code not in ok:
+        msg = load().cptr_last_error(ctx)
+        raise CptrError(code, msg.decode() if msg else "")
+    return code
+
+
+# ------------------------------------------------------------------------------------------------
+# thin wrappers with the C names
+def cptr_default_options(**kw) -> cptr_options:
+    o = cptr_options()
+    load().cptr_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "stage1" and isinstance(v, str):
+            v = STAGE1[v]
+        elif k == "stage2" and isinstance(v, str):
+            v = STAGE2[v]
+        elif k == "schur" and isinstance(v, str):
+            v = SCHUR[v]
+        elif k == "smoother" and isinstance(v, str):
+            v = SMOOTHER[v]
+        elif k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        setattr(o, k, v)
+    return o
+
+
+def cptr_create(opts: cptr_options) -> int:
+    h = ctypes.c_void_p()
+    code = load().cptr_create(ctypes.byref(h), ctypes.byref(opts))
+    if code != CPTR_OK:
+        raise CptrError(code, "cptr_create failed")
+    return h.value
+
+
+def cptr_destroy(ctx) -> None:
+    load().cptr_destroy(ctx)
+
+
+def cptr_setup(ctx, n_cells, b, row_ptr, col_idx, vals, unknown_kind, row_weights=None, st_vals=None):
+    dev = _on_device(row_ptr, col_idx, vals, unknown_kind, row_weights, st_vals)
+    return _check(ctx, load().cptr_setup(ctx, n_cells, b, _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
+                                         _ptr(unknown_kind), _ptr(row_weights), _ptr(st_vals), dev))
+
+
+def cptr_solve(ctx, rhs, x, rtol):
+    st = cptr_stats()
+    dev = _on_device(rhs, x)
+    code = _check(ctx, load().cptr_solve(ctx, _ptr(rhs), _ptr(x), rtol, ctypes.byref(st), dev),
+                  ok=(CPTR_OK, CPTR_NOT_CONVERGED))
+    return code, st
+
+
+def _vec_call(name, ctx, *args):
+    return _check(ctx, getattr(load(), name)(ctx, *args))
+
+
+def cptr_apply_matrix(ctx, x, y):
+    return _vec_call("cptr_apply_matrix", ctx, _ptr(x), _ptr(y))
+
+
+def cptr_apply_weights(ctx, rhs, out):
+    return _vec_call("cptr_apply_weights", ctx, _ptr(rhs), _ptr(out))
+
+
+def cptr_apply_stage1(ctx, v, x1):
+    return _vec_call("cptr_apply_stage1", ctx, _ptr(v), _ptr(x1))
+
+
+def cptr_apply_ilu(ctx, r, z):
+    return _vec_call("cptr_apply_ilu", ctx, _ptr(r), _ptr(z))
+
+
+def cptr_apply_precond(ctx, v, z):
+    return _vec_call("cptr_apply_precond", ctx, _ptr(v), _ptr(z))
+
+
+def cptr_apply_vcycle(ctx, which, b, x):
+    return _vec_call("cptr_apply_vcycle", ctx, which, _ptr(b), _ptr(x))
+
+
+def cptr_hierarchy_info(ctx, which):
+    nlev = ctypes.c_int32()
+    info = np.zeros(4 * 32, np.int32)
+    _check(ctx, load().cptr_hierarchy_info(ctx, which, ctypes.byref(nlev), info.ctypes.data))
+    return [dict(n=int(info[4 * l]), nnz=int(info[4 * l + 1]), nnzP=int(info[4 * l + 2]), dense=bool(info[4 * l + 3]))
+            for l in range(nlev.value)]
+
+
+def cptr_hierarchy_level(ctx, which, l, n, nnz, nnzP, coarse):
+    rp = np.zeros(n + 1, np.int32)
+    ci = np.zeros(max(nnz, 1), np.int32)
+    v = np.zeros(max(nnz, 1))
+    dinv = np.zeros(max(n, 1))
+    cf = np.zeros(n, np.int32) if not coarse else None
+    Prp = np.zeros(n + 1, np.int32) if not coarse else None
+    Pci = np.zeros(max(nnzP, 1), np.int32) if not coarse else None
+    Pv = np.zeros(max(nnzP, 1)) if not coarse else None
+    _check(ctx, load().cptr_hierarchy_level(ctx, which, l, _ptr(rp), _ptr(ci), _ptr(v), _ptr(dinv), _ptr(cf),
+                                            _ptr(Prp), _ptr(Pci), _ptr(Pv)))
+    out = dict(n=n, rp=rp, ci=ci[:nnz], v=v[:nnz], dinv=dinv[:n])
+    if not coarse:
+        out.update(cf=cf, Prp=Prp, Pci=Pci[:nnzP], Pv=Pv[:nnzP])
+    return out
+
+
+def cptr_ilu_levels(ctx):
+    f, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(ctx, load().cptr_ilu_levels(ctx, ctypes.byref(f), ctypes.byref(b)))
+    return f.value, b.value
+
+
+def cptr_launch_count() -> int:
+    return int(load().cptr_launch_count())
+
+
+def cptr_set_profiling(ctx, mask: int):
+    return _check(ctx, load().cptr_set_profiling(ctx, mask))
+
+
+def cptr_profile(ctx):
+    ms = np.zeros(8)
+    cnt = np.zeros(8, np.int64)
+    _check(ctx, load().cptr_profile(ctx, ms.ctypes.data, cnt.ctypes.data))
+    return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(PROFILE_FAMILIES)}
+
+
+# ------------------------------------------------------------------------------------------------
+class Solver:
+    """One CPTR-FGMRES context on the current CUDA device.
+
+    ``Solver(stage1="full", restart=30, stream=torch.cuda.current_stream())`` then
+    ``setup(...)`` with the BSR Jacobian and ``solve(rhs, rtol)``.  Arrays may be torch CUDA
+    tensors (used in place) or host arrays (copied by the library).
+    """
+
+    def __init__(self, stream=None, **opts):
+        s = getattr(stream, "cuda_stream", stream)
+        self.opts = cptr_default_options(stream=s, **opts)
+        self.ctx = cptr_create(self.opts)
+        self.n = self.b = None
+        self._keep = ()
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            cptr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        self.close()
+
+    def setup(self, n_cells, b, row_ptr, col_idx, vals, unknown_kind, row_weights=None, st_vals=None):
+        self.n, self.b = int(n_cells), int(b)
+        cptr_setup(self.ctx, self.n, self.b, row_ptr, col_idx, vals, unknown_kind, row_weights, st_vals)
+        return self
+
+    def solve(self, rhs, rtol=1e-6, x=None):
+        import torch
+        if x is None:
+            x = torch.empty_like(rhs) if hasattr(rhs, "is_cuda") else np.zeros(self.n * self.b)
+        code, st = cptr_solve(self.ctx, rhs, x, rtol)
+        info = {f: getattr(st, f) for f, _ in cptr_stats._fields_ if f != "pad"}
+        info["status"] = STATUS[code]
+        return x, info
+
+    def hierarchy(self, which):
+        levels = cptr_hierarchy_info(self.ctx, which)
+        out = []
+        for l, L in enumerate(levels):
+            coarse = l == len(levels) - 1
+            out.append(cptr_hierarchy_level(self.ctx, which, l, L["n"], L["nnz"], L["nnzP"], coarse))
+            out[-1]["dense"] = L["dense"]
+        return out

@@ -1,0 +1,638 @@
+// Classical AMG built and applied on the device: strength of connection, PMIS C/F splitting,
+// direct interpolation, Galerkin coarse operators A_c = P^T (A P), l1- or omega-Jacobi smoothing
+// and a dense inverse on the coarsest level.  Used for A_pp and S~_T in stage 1 of CPTR
+// (Sec. 3.3: "Both A_pp^{-1} and S~_T^{-1} are approximated using an AMG V-cycle") and for A_pp
+// in CPR (Sec. 3.1).  The set-up arithmetic is ordered so that every value is produced by the
+// same sequence of IEEE operations in a fixed order (no fused multiply-add in sums of products):
+// the hierarchy is deterministic run to run.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace cptr {
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------------------------------------------
+// smoother diagonal
+__global__ void k_dinv(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, int smoother, double omega,
+                       double *dinv) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double d = 0.0;
+    if (smoother == CPTR_SMOOTH_L1) {
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) d = __dadd_rn(d, fabs(v[k]));
+        dinv[i] = 1.0 / d;
+    } else {
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+            if (ci[k] == i) d = __dadd_rn(d, v[k]);
+        dinv[i] = omega / d;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// strength: j != i strong iff -a_ij >= theta * max_{k != i}(-a_ik) > 0
+__device__ __forceinline__ bool row_threshold(const int32_t *rp, const int32_t *ci, const double *v, int32_t i,
+                                              double theta, double *thr) {
+    double m = 0.0;
+    bool have = false;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+        if (ci[k] == i) continue;
+        double t = -v[k];
+        if (!have || t > m) { m = t; have = true; }
+    }
+    *thr = theta * m;
+    return have && m > 0.0;
+}
+
+__global__ void k_strength_count(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, double theta,
+                                 int32_t *cnt) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double thr;
+    int32_t c = 0;
+    if (row_threshold(rp, ci, v, i, theta, &thr))
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) c += (ci[k] != i && -v[k] >= thr);
+    cnt[i] = c;
+}
+
+__global__ void k_strength_fill(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, double theta,
+                                const int32_t *Srp, int32_t *Sci, int32_t *Spos) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double thr;
+    int32_t o = Srp[i];
+    if (row_threshold(rp, ci, v, i, theta, &thr))
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+            if (ci[k] != i && -v[k] >= thr) { Sci[o] = ci[k]; Spos[o] = k; ++o; }
+}
+
+// pattern transpose helpers
+__global__ void k_count_cols(int32_t nnz, const int32_t *ci, int32_t *cnt) {
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nnz) atomicAdd(cnt + ci[k], 1);
+}
+__global__ void k_fill_transpose(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, const int32_t *Trp,
+                                 int32_t *cursor, int32_t *Tci, double *Tv) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+        int32_t j = ci[k];
+        int32_t p = Trp[j] + atomicAdd(cursor + j, 1);
+        Tci[p] = i;
+        if (Tv) Tv[p] = v[k];
+    }
+}
+// sort every row by column (insertion sort; rows are short), values follow
+__global__ void k_sort_rows(int32_t n, const int32_t *rp, int32_t *ci, double *v) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int32_t a = rp[i] + 1; a < rp[i + 1]; ++a) {
+        int32_t c = ci[a];
+        double x = v ? v[a] : 0.0;
+        int32_t b = a - 1;
+        while (b >= rp[i] && ci[b] > c) {
+            ci[b + 1] = ci[b];
+            if (v) v[b + 1] = v[b];
+            --b;
+        }
+        ci[b + 1] = c;
+        if (v) v[b + 1] = x;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// PMIS (De Sterck, Yang, Heys 2006), round-synchronous.  key = (|S^T_i| << 32) | hash32, larger
+// (key, index) wins; hash32 = top 32 bits of the i-th SplitMix64 output of stream `seed`.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ bool beats(uint64_t ki, int32_t i, uint64_t kj, int32_t j) {
+    return ki > kj || (ki == kj && i > j);
+}
+
+__global__ void k_pmis_init(int32_t n, const int32_t *Srp, const int32_t *Trp, uint64_t seed, uint64_t *key,
+                            int32_t *state) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t deg = (uint64_t)(Trp[i + 1] - Trp[i]);
+    key[i] = (deg << 32) | (splitmix64_at(seed, (uint64_t)i) >> 32);
+    bool isolated = (Srp[i + 1] == Srp[i]) && (Trp[i + 1] == Trp[i]);
+    state[i] = isolated ? 2 : 0;
+}
+
+__global__ void k_pmis_select(int32_t n, const int32_t *Srp, const int32_t *Sci, const int32_t *Trp,
+                              const int32_t *Tci, const uint64_t *key, const int32_t *state, uint8_t *newc) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint8_t ok = 0;
+    if (state[i] == 0) {
+        ok = 1;
+        uint64_t ki = key[i];
+        for (int32_t k = Srp[i]; k < Srp[i + 1] && ok; ++k) {
+            int32_t j = Sci[k];
+            if (state[j] == 0 && !beats(ki, i, key[j], j)) ok = 0;
+        }
+        for (int32_t k = Trp[i]; k < Trp[i + 1] && ok; ++k) {
+            int32_t j = Tci[k];
+            if (state[j] == 0 && !beats(ki, i, key[j], j)) ok = 0;
+        }
+    }
+    newc[i] = ok;
+}
+
+__global__ void k_pmis_update(int32_t n, const int32_t *Srp, const int32_t *Sci, int32_t *state, const uint8_t *newc,
+                              int32_t *undecided) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (newc[i]) { state[i] = 1; return; }
+    if (state[i] != 0) return;
+    for (int32_t k = Srp[i]; k < Srp[i + 1]; ++k) {
+        int32_t j = Sci[k];
+        if (newc[j] || state[j] == 1) { state[i] = 2; return; }
+    }
+    atomicAdd(undecided, 1);
+}
+
+__global__ void k_is_c(int32_t n, const int32_t *state, int32_t *isc) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) isc[i] = state[i] == 1;
+}
+
+// ------------------------------------------------------------------------------------------------
+// direct interpolation (Stueben): F point i with strong C neighbours C_i,
+//   w_ij = -alpha a_ij / (a_ii + sum_{k != i, a_ik > 0} a_ik),
+//   alpha = sum_{k != i, a_ik < 0} a_ik / sum_{k in C_i} a_ik
+__global__ void k_interp_count(int32_t n, const int32_t *Srp, const int32_t *Sci, const int32_t *state, int32_t *cnt) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (state[i] == 1) { cnt[i] = 1; return; }
+    int32_t c = 0;
+    for (int32_t k = Srp[i]; k < Srp[i + 1]; ++k) c += state[Sci[k]] == 1;
+    cnt[i] = c;
+}
+
+__global__ void k_interp_fill(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, const int32_t *Srp,
+                              const int32_t *Sci, const int32_t *Spos, const int32_t *state, const int32_t *cidx,
+                              const int32_t *Prp, int32_t *Pci, double *Pv) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t o = Prp[i];
+    if (state[i] == 1) { Pci[o] = cidx[i]; Pv[o] = 1.0; return; }
+    if (Prp[i + 1] == o) return;
+    double aii = 0.0, sneg = 0.0, spos = 0.0, sc = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+        int32_t j = ci[k];
+        double a = v[k];
+        if (j == i) aii = __dadd_rn(aii, a);
+        else if (a < 0.0) sneg = __dadd_rn(sneg, a);
+        else if (a > 0.0) spos = __dadd_rn(spos, a);
+    }
+    for (int32_t k = Srp[i]; k < Srp[i + 1]; ++k)
+        if (state[Sci[k]] == 1) sc = __dadd_rn(sc, v[Spos[k]]);
+    double d = __dadd_rn(aii, spos);
+    double alpha = __ddiv_rn(sneg, sc);
+    for (int32_t k = Srp[i]; k < Srp[i + 1]; ++k) {
+        int32_t j = Sci[k];
+        if (state[j] != 1) continue;
+        Pci[o] = cidx[j];
+        Pv[o] = __ddiv_rn(__dmul_rn(-alpha, v[Spos[k]]), d);
+        ++o;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// C = A B by a per-row merge of the B rows selected by A's row.  Every output entry is the sum,
+// in ascending position of A's row, of the products a_il * b_lj, accumulated from 0.0 with
+// separately rounded multiply and add; output columns ascending.  NUM = false counts entries.
+constexpr int kMergeMax = 256;
+constexpr int kMergeThreads = 32;
+
+template <bool NUM>
+__global__ void __launch_bounds__(kMergeThreads) k_spgemm_merge(int32_t n, const int32_t *Arp, const int32_t *Aci,
+                                                                const double *Av, const int32_t *Brp,
+                                                                const int32_t *Bci, const double *Bv,
+                                                                const int32_t *Crp, int32_t *Cci_or_cnt, double *Cv,
+                                                                int32_t *err) {
+    extern __shared__ int32_t sm[];
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t a0 = Arp[i], m = Arp[i + 1] - a0;
+    if (m > kMergeMax) { atomicExch(err, 1); return; }
+    int32_t *pos = sm, *end = sm + kMergeMax * kMergeThreads;
+    const int t = threadIdx.x, T = kMergeThreads;
+    for (int q = 0; q < m; ++q) {
+        int32_t l = Aci[a0 + q];
+        pos[q * T + t] = Brp[l];
+        end[q * T + t] = Brp[l + 1];
+    }
+    int32_t out = NUM ? Crp[i] : 0;
+    int32_t cnt = 0;
+    for (;;) {
+        int32_t jmin = INT32_MAX;
+        for (int q = 0; q < m; ++q) {
+            int32_t p = pos[q * T + t];
+            if (p < end[q * T + t]) jmin = min(jmin, Bci[p]);
+        }
+        if (jmin == INT32_MAX) break;
+        double acc = 0.0;
+        for (int q = 0; q < m; ++q) {
+            int32_t p = pos[q * T + t];
+            if (p < end[q * T + t] && Bci[p] == jmin) {
+                if (NUM) acc = __dadd_rn(acc, __dmul_rn(Av[a0 + q], Bv[p]));
+                pos[q * T + t] = p + 1;
+            }
+        }
+        if (NUM) { Cci_or_cnt[out] = jmin; Cv[out] = acc; ++out; }
+        ++cnt;
+    }
+    if (!NUM) Cci_or_cnt[i] = cnt;
+}
+
+// ------------------------------------------------------------------------------------------------
+// coarsest level: densify and invert by Gauss-Jordan with partial pivoting (one block)
+__global__ void k_densify(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, double *D) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) D[(int64_t)i * n + ci[k]] += v[k];
+}
+
+__global__ void __launch_bounds__(1024) k_gauss_jordan(int32_t n, double *a, double *inv, int32_t *singular) {
+    extern __shared__ double fac[];   // n factors of the pivot column
+    __shared__ double red_v[32];
+    __shared__ int32_t red_i[32];
+    __shared__ int32_t piv_s;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int64_t e = tid; e < (int64_t)n * n; e += nt) inv[e] = ((e / n) == (e % n)) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int32_t k = 0; k < n; ++k) {
+        // pivot: max |a_ik|, i >= k, lowest index on ties
+        double best = -1.0;
+        int32_t bi = k;
+        for (int32_t i = k + tid; i < n; i += nt) {
+            double t = fabs(a[(int64_t)i * n + k]);
+            if (t > best) { best = t; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double ob = __shfl_down_sync(0xffffffffu, best, o);
+            int32_t oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            double bb = -1.0;
+            int32_t ii = k;
+            for (int w = 0; w < (nt + 31) / 32; ++w)
+                if (red_v[w] > bb || (red_v[w] == bb && red_i[w] < ii)) { bb = red_v[w]; ii = red_i[w]; }
+            piv_s = (bb > 0.0) ? ii : -1;
+            if (bb <= 0.0) *singular = 1;
+        }
+        __syncthreads();
+        int32_t p = piv_s;
+        if (p < 0) return;
+        if (p != k)
+            for (int32_t j = tid; j < n; j += nt) {
+                double t = a[(int64_t)k * n + j]; a[(int64_t)k * n + j] = a[(int64_t)p * n + j]; a[(int64_t)p * n + j] = t;
+                t = inv[(int64_t)k * n + j]; inv[(int64_t)k * n + j] = inv[(int64_t)p * n + j]; inv[(int64_t)p * n + j] = t;
+            }
+        __syncthreads();
+        double dk = 1.0 / a[(int64_t)k * n + k];
+        __syncthreads();
+        for (int32_t j = tid; j < n; j += nt) {
+            a[(int64_t)k * n + j] *= dk;
+            inv[(int64_t)k * n + j] *= dk;
+        }
+        __syncthreads();
+        for (int32_t i = tid; i < n; i += nt) fac[i] = (i == k) ? 0.0 : a[(int64_t)i * n + k];
+        __syncthreads();
+        for (int64_t e = tid; e < (int64_t)n * n; e += nt) {
+            int32_t i = (int32_t)(e / n), j = (int32_t)(e % n);
+            double f = fac[i];
+            if (f != 0.0) {
+                a[e] -= f * a[(int64_t)k * n + j];
+                inv[e] -= f * inv[(int64_t)k * n + j];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// host: one hierarchy
+static cptr_status transpose(Ctx *c, const Csr &A, int32_t ncols, Csr &T) {
+    T.n = ncols;
+    T.nnz = A.nnz;
+    int32_t *cnt = nullptr;
+    CPTR_TRY(dalloc_t(c, &cnt, (size_t)ncols + 1));
+    CPTR_TRY(dalloc_t(c, &T.rp, (size_t)ncols + 1));
+    CPTR_TRY(dalloc_t(c, &T.ci, (size_t)A.nnz));
+    CPTR_TRY(dalloc_t(c, &T.v, (size_t)A.nnz));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)ncols + 1), c->stream));
+    (k_count_cols<<<nblk(A.nnz, 256), 256, 0, c->stream>>>(A.nnz, A.ci, cnt), note_launch());
+    CPTR_TRY(scan_exclusive(c, cnt, T.rp, ncols, nullptr));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)ncols + 1), c->stream));
+    (k_fill_transpose<<<nblk(A.n, 256), 256, 0, c->stream>>>(A.n, A.rp, A.ci, A.v, T.rp, cnt, T.ci, T.v), note_launch());
+    (k_sort_rows<<<nblk(ncols, 128), 128, 0, c->stream>>>(ncols, T.rp, T.ci, T.v), note_launch());
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    dfree(cnt);
+    return CPTR_OK;
+}
+
+static cptr_status spgemm(Ctx *c, const Csr &A, const Csr &B, int32_t ncb, Csr &C) {
+    C.n = A.n;
+    CPTR_TRY(dalloc_t(c, &C.rp, (size_t)A.n + 1));
+    int32_t *cnt = nullptr;
+    CPTR_TRY(dalloc_t(c, &cnt, (size_t)A.n + 1));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
+    size_t smem = sizeof(int32_t) * 2 * kMergeMax * kMergeThreads;
+    CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_spgemm_merge<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_spgemm_merge<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    (k_spgemm_merge<false><<<nblk(A.n, kMergeThreads), kMergeThreads, smem, c->stream>>>(
+        A.n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, nullptr, cnt, nullptr, c->flag), note_launch());
+    int32_t total = 0;
+    CPTR_TRY(scan_exclusive(c, cnt, C.rp, A.n, &total));
+    int32_t bad = 0;
+    CPTR_CUDA_TRY(c, cudaMemcpy(&bad, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (bad) return c->fail(CPTR_EINVAL, "AMG: a row of the Galerkin product merges more than 256 rows");
+    C.nnz = total;
+    CPTR_TRY(dalloc_t(c, &C.ci, (size_t)total));
+    CPTR_TRY(dalloc_t(c, &C.v, (size_t)total));
+    (k_spgemm_merge<true><<<nblk(A.n, kMergeThreads), kMergeThreads, smem, c->stream>>>(
+        A.n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp, C.ci, C.v, c->flag), note_launch());
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    dfree(cnt);
+    (void)ncb;
+    return CPTR_OK;
+}
+
+static cptr_status alloc_level_vectors(Ctx *c, Level &L) {
+    size_t n = (size_t)(L.A.n > 0 ? L.A.n : 1);
+    CPTR_TRY(dalloc_t(c, &L.dinv, n));
+    CPTR_TRY(dalloc_t(c, &L.b, n));
+    CPTR_TRY(dalloc_t(c, &L.x, n));
+    CPTR_TRY(dalloc_t(c, &L.t, n));
+    CPTR_TRY(dalloc_t(c, &L.r, n));
+    (k_dinv<<<nblk(L.A.n, 256), 256, 0, c->stream>>>(L.A.n, L.A.rp, L.A.ci, L.A.v, c->o.smoother, c->o.omega, L.dinv), note_launch());
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    return CPTR_OK;
+}
+
+// Coarsen level L into P (n x nc) with PMIS + direct interpolation.  *nc_out = 0 if no C points.
+static cptr_status coarsen(Ctx *c, Level &L, int lev, int32_t *nc_out) {
+    const Csr &A = L.A;
+    int32_t n = A.n;
+    cudaStream_t s = c->stream;
+    int32_t *cnt = nullptr, *Srp = nullptr, *Sci = nullptr, *Spos = nullptr, *Trp = nullptr, *Tci = nullptr;
+    int32_t *state = nullptr, *cidx = nullptr, *und = nullptr;
+    uint64_t *key = nullptr;
+    uint8_t *newc = nullptr;
+    CPTR_TRY(dalloc_t(c, &cnt, (size_t)n + 1));
+    CPTR_TRY(dalloc_t(c, &Srp, (size_t)n + 1));
+    (k_strength_count<<<nblk(n, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, c->o.theta, cnt), note_launch());
+    int32_t nnzS = 0;
+    CPTR_TRY(scan_exclusive(c, cnt, Srp, n, &nnzS));
+    CPTR_TRY(dalloc_t(c, &Sci, (size_t)nnzS));
+    CPTR_TRY(dalloc_t(c, &Spos, (size_t)nnzS));
+    (k_strength_fill<<<nblk(n, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, c->o.theta, Srp, Sci, Spos), note_launch());
+    // S^T pattern (neighbour sets; order irrelevant)
+    CPTR_TRY(dalloc_t(c, &Trp, (size_t)n + 1));
+    CPTR_TRY(dalloc_t(c, &Tci, (size_t)nnzS));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)n + 1), s));
+    (k_count_cols<<<nblk(nnzS, 256), 256, 0, s>>>(nnzS, Sci, cnt), note_launch());
+    CPTR_TRY(scan_exclusive(c, cnt, Trp, n, nullptr));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)n + 1), s));
+    (k_fill_transpose<<<nblk(n, 256), 256, 0, s>>>(n, Srp, Sci, nullptr, Trp, cnt, Tci, nullptr), note_launch());
+    // PMIS rounds
+    CPTR_TRY(dalloc_t(c, &key, (size_t)n));
+    CPTR_TRY(dalloc_t(c, &state, (size_t)n));
+    CPTR_TRY(dalloc_t(c, &newc, (size_t)n));
+    CPTR_TRY(dalloc_t(c, &und, 1));
+    (k_pmis_init<<<nblk(n, 256), 256, 0, s>>>(n, Srp, Trp, (uint64_t)(int64_t)c->o.seed + (uint64_t)lev, key, state), note_launch());
+    int rounds = 0;
+    for (;;) {
+        (k_pmis_select<<<nblk(n, 256), 256, 0, s>>>(n, Srp, Sci, Trp, Tci, key, state, newc), note_launch());
+        CPTR_CUDA_TRY(c, cudaMemsetAsync(und, 0, sizeof(int32_t), s));
+        (k_pmis_update<<<nblk(n, 256), 256, 0, s>>>(n, Srp, Sci, state, newc, und), note_launch());
+        int32_t h_und = 0;
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(&h_und, und, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CPTR_CUDA_TRY(c, cudaStreamSynchronize(s));
+        if (h_und == 0) break;
+        if (++rounds > 100000) return c->fail(CPTR_EINVAL, "AMG: PMIS did not terminate");
+    }
+    // coarse numbering
+    CPTR_TRY(dalloc_t(c, &cidx, (size_t)n + 1));
+    (k_is_c<<<nblk(n, 256), 256, 0, s>>>(n, state, cnt), note_launch());
+    int32_t nc = 0;
+    CPTR_TRY(scan_exclusive(c, cnt, cidx, n, &nc));
+    *nc_out = nc;
+    L.cf = state;
+    state = nullptr;
+    if (nc > 0 && nc < n) {
+        // interpolation
+        L.P.n = n;
+        CPTR_TRY(dalloc_t(c, &L.P.rp, (size_t)n + 1));
+        (k_interp_count<<<nblk(n, 256), 256, 0, s>>>(n, Srp, Sci, L.cf, cnt), note_launch());
+        int32_t nnzP = 0;
+        CPTR_TRY(scan_exclusive(c, cnt, L.P.rp, n, &nnzP));
+        L.P.nnz = nnzP;
+        CPTR_TRY(dalloc_t(c, &L.P.ci, (size_t)nnzP));
+        CPTR_TRY(dalloc_t(c, &L.P.v, (size_t)nnzP));
+        (k_interp_fill<<<nblk(n, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, Srp, Sci, Spos, L.cf, cidx, L.P.rp, L.P.ci,
+                                                   L.P.v), note_launch());
+        CPTR_CUDA_TRY(c, cudaGetLastError());
+    }
+    dfree(cnt); dfree(Srp); dfree(Sci); dfree(Spos); dfree(Trp); dfree(Tci);
+    dfree(key); dfree(newc); dfree(und); dfree(cidx);
+    return CPTR_OK;
+}
+
+cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, const double *v, int32_t n) {
+    amg_free(h);
+    int32_t nnz = 0;
+    CPTR_CUDA_TRY(c, cudaMemcpy(&nnz, rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    Csr &A0 = h.L[0].A;
+    A0.n = n;
+    A0.nnz = nnz;
+    CPTR_TRY(dalloc_t(c, &A0.rp, (size_t)n + 1));
+    CPTR_TRY(dalloc_t(c, &A0.ci, (size_t)nnz));
+    CPTR_TRY(dalloc_t(c, &A0.v, (size_t)nnz));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(A0.rp, rp, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, c->stream));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(A0.ci, ci, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToDevice, c->stream));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(A0.v, v, sizeof(double) * (size_t)nnz, cudaMemcpyDeviceToDevice, c->stream));
+    int maxl = c->o.max_levels < 1 ? 1 : (c->o.max_levels > kMaxLevels ? kMaxLevels : c->o.max_levels);
+    int l = 0;
+    double nnz_sum = 0.0;
+    for (;;) {
+        Level &L = h.L[l];
+        CPTR_TRY(alloc_level_vectors(c, L));
+        nnz_sum += L.A.nnz;
+        if (l + 1 >= maxl || L.A.n <= c->o.n_coarse) break;
+        int32_t nc = 0;
+        CPTR_TRY(coarsen(c, L, l, &nc));
+        if (nc == 0 || nc >= L.A.n) {   // no coarsening possible: this level is the coarsest
+            csr_free(L.P);
+            dfree(L.cf);
+            L.cf = nullptr;
+            break;
+        }
+        L.nc = nc;
+        CPTR_TRY(transpose(c, L.P, nc, L.PT));
+        Csr AP;
+        CPTR_TRY(spgemm(c, L.A, L.P, nc, AP));
+        CPTR_TRY(spgemm(c, L.PT, AP, nc, h.L[l + 1].A));
+        csr_free(AP);
+        ++l;
+    }
+    h.nlev = l + 1;
+    h.op_complexity = nnz_sum / (double)(nnz > 0 ? nnz : 1);
+    Level &C = h.L[l];
+    int32_t cn = C.A.n;
+    h.dense = 0;
+    if (cn <= c->o.dense_max) {
+        double *D = nullptr;
+        CPTR_TRY(dalloc_t(c, &D, (size_t)cn * cn));
+        CPTR_TRY(dalloc_t(c, &h.cinv, (size_t)cn * cn));
+        CPTR_CUDA_TRY(c, cudaMemsetAsync(D, 0, sizeof(double) * (size_t)cn * cn, c->stream));
+        (k_densify<<<nblk(cn, 128), 128, 0, c->stream>>>(cn, C.A.rp, C.A.ci, C.A.v, D), note_launch());
+        CPTR_CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
+        size_t smem = sizeof(double) * (size_t)(cn > 0 ? cn : 1);
+        if (smem > 48 * 1024)
+            CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        (k_gauss_jordan<<<1, 1024, smem, c->stream>>>(cn, D, h.cinv, c->flag), note_launch());
+        CPTR_CUDA_TRY(c, cudaGetLastError());
+        int32_t sing = 0;
+        CPTR_CUDA_TRY(c, cudaMemcpy(&sing, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        dfree(D);
+        if (sing) return c->fail(CPTR_ESINGULAR, "AMG: singular coarsest-level matrix");
+        h.dense = 1;
+    }
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return CPTR_OK;
+}
+
+void amg_free(Hier &h) {
+    for (int l = 0; l < kMaxLevels; ++l) {
+        Level &L = h.L[l];
+        csr_free(L.A); csr_free(L.P); csr_free(L.PT);
+        dfree(L.dinv); dfree(L.cf); dfree(L.b); dfree(L.x); dfree(L.t); dfree(L.r);
+        L = Level{};
+    }
+    dfree(h.cinv);
+    h.cinv = nullptr;
+    h.nlev = 0;
+    h.dense = 0;
+}
+
+// ------------------------------------------------------------------------------------------------
+// V(1,1)-cycle kernels
+// pre-smoothing from zero fused with the residual: t = D^{-1} b, r = b - A t
+template <int G>
+__global__ void __launch_bounds__(256) k_vc_down(int32_t n, const int32_t *__restrict__ rp,
+                                                  const int32_t *__restrict__ ci, const double *__restrict__ v,
+                                                  const double *__restrict__ dinv, const double *__restrict__ b,
+                                                  double *__restrict__ t, double *__restrict__ r) {
+    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t row = (int32_t)(gid / G);
+    int lane = threadIdx.x % G;
+    double acc = 0.0;
+    if (row < n) {
+        int32_t k1 = __ldg(rp + row + 1);
+        for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G) {
+            int32_t j = __ldg(ci + k);
+            acc = fma(__ldg(v + k), __ldg(dinv + j) * __ldg(b + j), acc);
+        }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
+    if (row < n && lane == 0) {
+        double bi = b[row];
+        t[row] = dinv[row] * bi;
+        r[row] = bi - acc;
+    }
+}
+// post-smoothing: x = t + D^{-1} (b - A t)
+template <int G>
+__global__ void __launch_bounds__(256) k_vc_post(int32_t n, const int32_t *__restrict__ rp,
+                                                  const int32_t *__restrict__ ci, const double *__restrict__ v,
+                                                  const double *__restrict__ dinv, const double *__restrict__ b,
+                                                  const double *__restrict__ t, double *__restrict__ x) {
+    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t row = (int32_t)(gid / G);
+    int lane = threadIdx.x % G;
+    double acc = 0.0;
+    if (row < n) {
+        int32_t k1 = __ldg(rp + row + 1);
+        for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G) acc = fma(__ldg(v + k), __ldg(t + __ldg(ci + k)), acc);
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
+    if (row < n && lane == 0) x[row] = t[row] + dinv[row] * (b[row] - acc);
+}
+// coarsest dense solve x = A_c^{-1} b: one warp per row
+__global__ void k_dense_mv(int32_t n, const double *__restrict__ M, const double *__restrict__ b, double *__restrict__ x) {
+    int32_t row = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    double acc = 0.0;
+    for (int32_t j = lane; j < n; j += 32) acc = fma(M[(int64_t)row * n + j], b[j], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) x[row] = acc;
+}
+__global__ void k_diag_scale(int32_t n, const double *d, const double *b, double *x) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = d[i] * b[i];
+}
+
+static void launch_down(cudaStream_t s, const Level &L, const double *b) {
+    int G = lanes_for(L.A.n, L.A.nnz);
+    unsigned grid = nblk((int64_t)L.A.n * G, 256);
+    const Csr &A = L.A;
+    switch (G) {
+    case 4: (k_vc_down<4><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, L.t, L.r), note_launch()); break;
+    case 8: (k_vc_down<8><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, L.t, L.r), note_launch()); break;
+    case 16: (k_vc_down<16><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, L.t, L.r), note_launch()); break;
+    default: (k_vc_down<32><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, L.t, L.r), note_launch()); break;
+    }
+}
+static void launch_post(cudaStream_t s, const Level &L, const double *b, const double *t, double *x) {
+    int G = lanes_for(L.A.n, L.A.nnz);
+    unsigned grid = nblk((int64_t)L.A.n * G, 256);
+    const Csr &A = L.A;
+    switch (G) {
+    case 4: (k_vc_post<4><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, t, x), note_launch()); break;
+    case 8: (k_vc_post<8><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, t, x), note_launch()); break;
+    case 16: (k_vc_post<16><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, t, x), note_launch()); break;
+    default: (k_vc_post<32><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, t, x), note_launch()); break;
+    }
+}
+
+static void vcycle_level(const Ctx *c, const Hier &h, int l, const double *b, double *x) {
+    cudaStream_t s = c->stream;
+    const Level &L = h.L[l];
+    int32_t n = L.A.n;
+    if (l == h.nlev - 1) {
+        if (h.dense) {
+            (k_dense_mv<<<nblk((int64_t)n * 32, 256), 256, 0, s>>>(n, h.cinv, b, x), note_launch());
+        } else {  // two smoothing sweeps from zero
+            (k_diag_scale<<<nblk(n, 256), 256, 0, s>>>(n, L.dinv, b, L.t), note_launch());
+            launch_post(s, L, b, L.t, x);
+        }
+        return;
+    }
+    const Level &C = h.L[l + 1];
+    launch_down(s, L, b);                                   // t = D^{-1} b, r = b - A t
+    launch_csr_spmv(s, L.PT, L.r, C.b, 1.0, nullptr);       // b_c = P^T r
+    vcycle_level(c, h, l + 1, C.b, C.x);
+    launch_csr_spmv(s, L.P, C.x, L.t, 2.0, nullptr);        // t += P x_c
+    launch_post(s, L, b, L.t, x);                           // x = t + D^{-1}(b - A t)
+}
+
+void amg_vcycle(const Ctx *c, const Hier &h, const double *b, double *x) { vcycle_level(c, h, 0, b, x); }
+
+}  // namespace cptr

@@ -1,0 +1,417 @@
+// C ABI of the CPTR library (declared in include/cptr.h): argument validation, set-up
+// orchestration (decoupling, p-T extraction, two AMG hierarchies, ILU(0)), and the solve.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <chrono>
+#include <new>
+
+#include "common.cuh"
+
+using namespace cptr;
+
+struct cptr_ctx {
+    Ctx c;
+};
+
+namespace {
+
+bool host_or_device_copy(Ctx *c, void *dst, const void *src, size_t bytes, int on_device, cudaMemcpyKind to) {
+    cudaError_t e;
+    if (on_device) e = cudaMemcpyAsync(dst, src, bytes, to == cudaMemcpyDeviceToHost ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream);
+    else e = cudaMemcpyAsync(dst, src, bytes, to == cudaMemcpyDeviceToHost ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice, c->stream);
+    return e == cudaSuccess;
+}
+
+void release_setup(Ctx *c) {
+    dfree(c->rp); dfree(c->ci); dfree(c->diag); dfree(c->A); dfree(c->W);
+    dfree(c->App); dfree(c->ApT); dfree(c->ATp); dfree(c->St);
+    c->rp = c->ci = c->diag = nullptr;
+    c->A = c->W = c->App = c->ApT = c->ATp = c->St = nullptr;
+    amg_free(c->hp);
+    amg_free(c->hT);
+    ilu_free(c);
+    double **vecs[] = {&c->bp, &c->bT, &c->xp, &c->dp, &c->dT, &c->t1, &c->b1, &c->V, &c->Z, &c->w, &c->bw, &c->xw};
+    for (double **p : vecs) { dfree(*p); *p = nullptr; }
+    c->ready = false;
+}
+
+cptr_status validate_pattern(Ctx *c, int32_t n) {
+    const std::vector<int32_t> &rp = c->h_rp, &ci = c->h_ci;
+    if (rp[0] != 0) return c->fail(CPTR_EINVAL, "row_ptr[0] must be 0");
+    for (int32_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) return c->fail(CPTR_EINVAL, "row_ptr must be non-decreasing (row " + std::to_string(i) + ")");
+    c->h_diag.assign(n, -1);
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+            int32_t j = ci[k];
+            if (j < 0 || j >= n) return c->fail(CPTR_EINVAL, "col_idx out of range in row " + std::to_string(i));
+            if (k > rp[i] && ci[k - 1] >= j)
+                return c->fail(CPTR_EINVAL, "col_idx not strictly ascending in row " + std::to_string(i));
+            if (j == i) c->h_diag[i] = k;
+        }
+        if (c->h_diag[i] < 0) return c->fail(CPTR_EINVAL, "missing diagonal block in row " + std::to_string(i));
+    }
+    return CPTR_OK;
+}
+
+cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const int32_t *col_idx, const double *vals,
+                     const int32_t *kind, const double *W, const double *st, int on_device) {
+    if (n <= 0) return c->fail(CPTR_EINVAL, "n_cells must be positive");
+    if (b != 3 && b != 4) return c->fail(CPTR_EINVAL, "b must be 3 or 4");
+    if (!row_ptr || !col_idx || !vals || !kind) return c->fail(CPTR_EINVAL, "row_ptr, col_idx, vals, unknown_kind are required");
+    int32_t hk[4];
+    if (on_device) CPTR_CUDA_TRY(c, cudaMemcpy(hk, kind, sizeof(int32_t) * b, cudaMemcpyDeviceToHost));
+    else memcpy(hk, kind, sizeof(int32_t) * b);
+    int ps = -1, ts = -1;
+    for (int q = 0; q < b; ++q) {
+        if (hk[q] == CPTR_U_P) { if (ps >= 0) return c->fail(CPTR_EINVAL, "more than one pressure slot"); ps = q; }
+        else if (hk[q] == CPTR_U_T) { if (ts >= 0) return c->fail(CPTR_EINVAL, "more than one temperature slot"); ts = q; }
+        else if (hk[q] != CPTR_U_SAT) return c->fail(CPTR_EINVAL, "unknown_kind entries must be P, T or SAT");
+    }
+    if (ps < 0 || ts < 0) return c->fail(CPTR_EINVAL, "unknown_kind needs one P and one T slot");
+    release_setup(c);
+    auto t0 = std::chrono::steady_clock::now();
+    // pattern to the host for validation and level scheduling
+    c->h_rp.assign((size_t)n + 1, 0);
+    if (on_device) CPTR_CUDA_TRY(c, cudaMemcpy(c->h_rp.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost));
+    else memcpy(c->h_rp.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1));
+    int32_t nnzb = c->h_rp[n];
+    if (nnzb <= 0 || c->h_rp[0] != 0) return c->fail(CPTR_EINVAL, "row_ptr must start at 0 and end at nnzb > 0");
+    c->h_ci.assign((size_t)nnzb, 0);
+    if (on_device) CPTR_CUDA_TRY(c, cudaMemcpy(c->h_ci.data(), col_idx, sizeof(int32_t) * nnzb, cudaMemcpyDeviceToHost));
+    else memcpy(c->h_ci.data(), col_idx, sizeof(int32_t) * nnzb);
+    CPTR_TRY(validate_pattern(c, n));
+    c->n = n; c->b = b; c->ps = ps; c->ts = ts; c->nnzb = nnzb;
+    const size_t bb = (size_t)b * b;
+    CPTR_TRY(dalloc_t(c, &c->rp, (size_t)n + 1));
+    CPTR_TRY(dalloc_t(c, &c->ci, (size_t)nnzb));
+    CPTR_TRY(dalloc_t(c, &c->diag, (size_t)n));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->rp, c->h_rp.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, c->stream));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ci, c->h_ci.data(), sizeof(int32_t) * nnzb, cudaMemcpyHostToDevice, c->stream));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->diag, c->h_diag.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
+    double *Araw = nullptr;
+    CPTR_TRY(dalloc_t(c, &Araw, nnzb * bb));
+    CPTR_TRY(dalloc_t(c, &c->A, nnzb * bb));
+    if (!host_or_device_copy(c, Araw, vals, sizeof(double) * nnzb * bb, on_device, cudaMemcpyHostToDevice))
+        return c->fail(CPTR_ECUDA, "copy of vals failed");
+    if (W) {
+        CPTR_TRY(dalloc_t(c, &c->W, (size_t)n * bb));
+        if (!host_or_device_copy(c, c->W, W, sizeof(double) * n * bb, on_device, cudaMemcpyHostToDevice))
+            return c->fail(CPTR_ECUDA, "copy of row_weights failed");
+    }
+    CPTR_TRY(dalloc_t(c, &c->St, (size_t)nnzb));
+    if (st && c->o.schur == CPTR_SCHUR_GIVEN) {
+        if (!host_or_device_copy(c, c->St, st, sizeof(double) * nnzb, on_device, cudaMemcpyHostToDevice))
+            return c->fail(CPTR_ECUDA, "copy of st_vals failed");
+    }
+    // finite values
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
+    launch_check_finite(c, Araw, (int64_t)nnzb * bb, c->flag);
+    if (c->W) launch_check_finite(c, c->W, (int64_t)n * bb, c->flag);
+    if (st && c->o.schur == CPTR_SCHUR_GIVEN) launch_check_finite(c, c->St, nnzb, c->flag);
+    int32_t bad = 0;
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(&bad, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (bad) { dfree(Araw); return c->fail(CPTR_EINVAL, "non-finite value in vals, row_weights or st_vals"); }
+    // A' = W A, then the scalar p-T blocks on the cell pattern
+    launch_decouple(c, Araw, c->W, c->A);
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    dfree(Araw);
+    CPTR_TRY(dalloc_t(c, &c->App, (size_t)nnzb));
+    CPTR_TRY(dalloc_t(c, &c->ApT, (size_t)nnzb));
+    CPTR_TRY(dalloc_t(c, &c->ATp, (size_t)nnzb));
+    launch_extract(c, ps, ps, c->App);
+    launch_extract(c, ps, ts, c->ApT);
+    launch_extract(c, ts, ps, c->ATp);
+    if (!(st && c->o.schur == CPTR_SCHUR_GIVEN)) launch_extract(c, ts, ts, c->St);
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    int s1 = c->o.stage1;
+    if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_setup(c, c->hp, c->rp, c->ci, c->App, n));
+    if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) CPTR_TRY(amg_setup(c, c->hT, c->rp, c->ci, c->St, n));
+    if (c->o.stage2 == CPTR_STAGE2_ILU0) CPTR_TRY(ilu_setup(c));
+    // work vectors
+    const size_t nb = (size_t)n * b;
+    const int m = c->o.restart;
+    for (double **p : {&c->bp, &c->bT, &c->xp, &c->dp, &c->dT, &c->t1}) CPTR_TRY(dalloc_t(c, p, (size_t)n));
+    for (double **p : {&c->b1, &c->w, &c->bw, &c->xw}) CPTR_TRY(dalloc_t(c, p, nb));
+    CPTR_TRY(dalloc_t(c, &c->V, nb * (m + 1)));
+    CPTR_TRY(dalloc_t(c, &c->Z, nb * m));
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    c->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    c->ready = true;
+    return CPTR_OK;
+}
+
+template <typename F>
+cptr_status guarded(cptr_ctx *ctx, F &&f) {
+    if (!ctx) return CPTR_EINVAL;
+    try {
+        ctx->c.err.clear();
+        return f(&ctx->c);
+    } catch (const std::bad_alloc &) {
+        return ctx->c.fail(CPTR_ENOMEM, "host allocation failed");
+    } catch (...) {
+        return ctx->c.fail(CPTR_EINVAL, "unexpected host exception");
+    }
+}
+
+cptr_status need_ready(Ctx *c) {
+    if (!c->ready) return c->fail(CPTR_ESTATE, "no successful cptr_setup on this context");
+    return CPTR_OK;
+}
+
+cptr_status sync(Ctx *c) {
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return CPTR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cptr_status cptr_default_options(cptr_options *o) {
+    if (!o) return CPTR_EINVAL;
+    memset(o, 0, sizeof(*o));
+    o->stage1 = CPTR_STAGE1_FULL;
+    o->stage2 = CPTR_STAGE2_ILU0;
+    o->schur = CPTR_SCHUR_GIVEN;
+    o->smoother = CPTR_SMOOTH_L1;
+    o->omega = 2.0 / 3.0;
+    o->theta = 0.25;
+    o->n_coarse = 256;
+    o->max_levels = 25;
+    o->restart = 30;
+    o->max_it = 1000;
+    o->dense_max = 1024;
+    o->seed = 0;
+    o->precision = CPTR_PREC_FP64;
+    o->check_every = 1;
+    o->stream = nullptr;
+    return CPTR_OK;
+}
+
+cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
+    if (!out) return CPTR_EINVAL;
+    *out = nullptr;
+    cptr_options o;
+    if (opt) o = *opt;
+    else cptr_default_options(&o);
+    if (o.restart < 1 || o.restart > kMaxRestart || o.max_it < 0 || o.max_levels < 1 || o.dense_max < 1 ||
+        o.stage1 < 0 || o.stage1 > CPTR_STAGE1_NONE || o.stage2 < 0 || o.stage2 > CPTR_STAGE2_NONE ||
+        o.smoother < 0 || o.smoother > CPTR_SMOOTH_JACOBI || o.precision != CPTR_PREC_FP64)
+        return CPTR_EINVAL;
+    cptr_ctx *ctx = new (std::nothrow) cptr_ctx();
+    if (!ctx) return CPTR_ENOMEM;
+    Ctx *c = &ctx->c;
+    c->o = o;
+    c->stream = (cudaStream_t)o.stream;
+    cptr_status s = CPTR_OK;
+    if ((s = dalloc_t(c, &c->ks, 1)) != CPTR_OK || (s = dalloc_t(c, &c->flag, 4)) != CPTR_OK ||
+        (s = dalloc_t(c, &c->partial, (size_t)kRedBlocks * (kMaxRestart + 2))) != CPTR_OK) {
+        cptr_destroy(ctx);
+        return s;
+    }
+    if (cudaMallocHost((void **)&c->ks_host, sizeof(KState)) != cudaSuccess) {
+        c->ks_host = nullptr;
+        cptr_destroy(ctx);
+        return CPTR_ENOMEM;
+    }
+    *out = ctx;
+    return CPTR_OK;
+}
+
+void cptr_destroy(cptr_ctx *ctx) {
+    if (!ctx) return;
+    Ctx *c = &ctx->c;
+    cudaStreamSynchronize(c->stream);
+    release_setup(c);
+    dfree(c->ks); dfree(c->flag); dfree(c->partial); dfree(c->scan_tmp);
+    if (c->ks_host) cudaFreeHost(c->ks_host);
+    for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
+    delete ctx;
+}
+
+const char *cptr_last_error(const cptr_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
+
+cptr_status cptr_setup(cptr_ctx *ctx, int32_t n_cells, int32_t b, const int32_t *row_ptr, const int32_t *col_idx,
+                       const double *vals, const int32_t *unknown_kind, const double *row_weights,
+                       const double *st_vals, int32_t on_device) {
+    return guarded(ctx, [&](Ctx *c) {
+        cptr_status s = do_setup(c, n_cells, b, row_ptr, col_idx, vals, unknown_kind, row_weights, st_vals, on_device);
+        if (s != CPTR_OK) {
+            std::string keep = c->err;
+            cudaStreamSynchronize(c->stream);
+            release_setup(c);
+            c->err = keep;
+        }
+        return s;
+    });
+}
+
+cptr_status cptr_solve(cptr_ctx *ctx, const double *rhs, double *x, double rtol, cptr_stats *st, int32_t on_device) {
+    return guarded(ctx, [&](Ctx *c) {
+        CPTR_TRY(need_ready(c));
+        if (!rhs || !x) return c->fail(CPTR_EINVAL, "rhs and x are required");
+        if (!(rtol >= 0.0)) return c->fail(CPTR_EINVAL, "rtol must be >= 0");
+        const size_t nb = (size_t)c->n * c->b;
+        cudaEvent_t e0, e1;
+        CPTR_CUDA_TRY(c, cudaEventCreate(&e0));
+        CPTR_CUDA_TRY(c, cudaEventCreate(&e1));
+        CPTR_CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+        const double *rhs_dev = rhs;
+        if (!on_device) {
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->xw, rhs, sizeof(double) * nb, cudaMemcpyHostToDevice, c->stream));
+            rhs_dev = c->xw;
+        }
+        launch_weight_vec(c, c->W, rhs_dev, c->bw);
+        double *xd = on_device ? x : c->xw;
+        prof_reset(c);
+        cptr_status s = fgmres_solve(c, c->bw, xd, rtol, st);
+        if (!on_device && (s == CPTR_OK || s == CPTR_NOT_CONVERGED))
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(x, c->xw, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->stream));
+        CPTR_CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+        CPTR_CUDA_TRY(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        CPTR_TRY(prof_collect(c));
+        if (st) {
+            st->solve_ms = ms;
+            st->setup_ms = c->setup_ms;
+            st->levels_p = c->hp.nlev;
+            st->levels_T = c->hT.nlev;
+            st->op_complexity_p = c->hp.op_complexity;
+            st->op_complexity_T = c->hT.op_complexity;
+        }
+        return s;
+    });
+}
+
+cptr_status cptr_apply_matrix(cptr_ctx *ctx, const double *x, double *y) {
+    return guarded(ctx, [&](Ctx *c) {
+        CPTR_TRY(need_ready(c));
+        launch_bsr_spmv(c, x, y);
+        return sync(c);
+    });
+}
+
+cptr_status cptr_apply_weights(cptr_ctx *ctx, const double *rhs, double *out) {
+    return guarded(ctx, [&](Ctx *c) {
+        CPTR_TRY(need_ready(c));
+        launch_weight_vec(c, c->W, rhs, out);
+        return sync(c);
+    });
+}
+
+cptr_status cptr_apply_stage1(cptr_ctx *ctx, const double *v, double *x1) {
+    return guarded(ctx, [&](Ctx *c) {
+        CPTR_TRY(need_ready(c));
+        const double *dp, *dT;
+        apply_stage1(c, v, &dp, &dT);
+        if (dp) launch_scatter_pt(c, dp, dT, x1);
+        else CPTR_CUDA_TRY(c, cudaMemsetAsync(x1, 0, sizeof(double) * c->n * c->b, c->stream));
+        return sync(c);
+    });
+}
+
+cptr_status cptr_apply_ilu(cptr_ctx *ctx, const double *r, double *z) {
+    return guarded(ctx, [&](Ctx *c) {
+        CPTR_TRY(need_ready(c));
+        if (c->o.stage2 != CPTR_STAGE2_ILU0) return c->fail(CPTR_ESTATE, "ILU(0) was not set up");
+        ilu_apply(c, r, z, nullptr, nullptr);
+        return sync(c);
+    });
+}
+
+cptr_status cptr_apply_precond(cptr_ctx *ctx, const double *v, double *z) {
+    return guarded(ctx, [&](Ctx *c) {
+        CPTR_TRY(need_ready(c));
+        apply_precond(c, v, z);
+        return sync(c);
+    });
+}
+
+cptr_status cptr_apply_vcycle(cptr_ctx *ctx, int32_t which, const double *b, double *x) {
+    return guarded(ctx, [&](Ctx *c) {
+        CPTR_TRY(need_ready(c));
+        const Hier &h = which == 0 ? c->hp : c->hT;
+        if (which < 0 || which > 1 || h.nlev == 0) return c->fail(CPTR_EINVAL, "no such AMG hierarchy");
+        amg_vcycle(c, h, b, x);
+        return sync(c);
+    });
+}
+
+cptr_status cptr_hierarchy_info(cptr_ctx *ctx, int32_t which, int32_t *nlev, int32_t *info) {
+    return guarded(ctx, [&](Ctx *c) {
+        CPTR_TRY(need_ready(c));
+        if (!nlev || !info || which < 0 || which > 1) return c->fail(CPTR_EINVAL, "bad arguments");
+        const Hier &h = which == 0 ? c->hp : c->hT;
+        *nlev = h.nlev;
+        for (int l = 0; l < h.nlev; ++l) {
+            info[4 * l + 0] = h.L[l].A.n;
+            info[4 * l + 1] = h.L[l].A.nnz;
+            info[4 * l + 2] = (l + 1 < h.nlev) ? h.L[l].P.nnz : 0;
+            info[4 * l + 3] = h.dense;
+        }
+        return CPTR_OK;
+    });
+}
+
+cptr_status cptr_hierarchy_level(cptr_ctx *ctx, int32_t which, int32_t l, int32_t *rp, int32_t *ci, double *v,
+                                 double *dinv, int32_t *cf, int32_t *Prp, int32_t *Pci, double *Pv) {
+    return guarded(ctx, [&](Ctx *c) {
+        CPTR_TRY(need_ready(c));
+        const Hier &h = which == 0 ? c->hp : c->hT;
+        if (which < 0 || which > 1 || l < 0 || l >= h.nlev) return c->fail(CPTR_EINVAL, "no such level");
+        const Level &L = h.L[l];
+        auto cp = [&](void *dst, const void *src, size_t bytes) -> cptr_status {
+            if (dst && src && bytes) CPTR_CUDA_TRY(c, cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+            return CPTR_OK;
+        };
+        CPTR_TRY(cp(rp, L.A.rp, sizeof(int32_t) * ((size_t)L.A.n + 1)));
+        CPTR_TRY(cp(ci, L.A.ci, sizeof(int32_t) * (size_t)L.A.nnz));
+        CPTR_TRY(cp(v, L.A.v, sizeof(double) * (size_t)L.A.nnz));
+        CPTR_TRY(cp(dinv, L.dinv, sizeof(double) * (size_t)L.A.n));
+        if (l + 1 < h.nlev) {
+            CPTR_TRY(cp(cf, L.cf, sizeof(int32_t) * (size_t)L.A.n));
+            CPTR_TRY(cp(Prp, L.P.rp, sizeof(int32_t) * ((size_t)L.A.n + 1)));
+            CPTR_TRY(cp(Pci, L.P.ci, sizeof(int32_t) * (size_t)L.P.nnz));
+            CPTR_TRY(cp(Pv, L.P.v, sizeof(double) * (size_t)L.P.nnz));
+        }
+        return CPTR_OK;
+    });
+}
+
+int64_t cptr_launch_count(void) { return launch_count(); }
+
+cptr_status cptr_set_profiling(cptr_ctx *ctx, uint32_t mask) {
+    return guarded(ctx, [&](Ctx *c) {
+        c->prof.mask = mask;
+        return CPTR_OK;
+    });
+}
+
+cptr_status cptr_profile(cptr_ctx *ctx, double *ms, int64_t *count) {
+    return guarded(ctx, [&](Ctx *c) {
+        for (int f = 0; f < PF_N; ++f) {
+            if (ms) ms[f] = c->prof.ms[f];
+            if (count) count[f] = c->prof.cnt[f];
+        }
+        return CPTR_OK;
+    });
+}
+
+cptr_status cptr_ilu_levels(cptr_ctx *ctx, int32_t *n_forward, int32_t *n_backward) {
+    return guarded(ctx, [&](Ctx *c) {
+        CPTR_TRY(need_ready(c));
+        if (n_forward) *n_forward = c->nlev_f;
+        if (n_backward) *n_backward = c->nlev_b;
+        return CPTR_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+// Shared declarations of the CPTR CUDA library (sm_103a).  Device data structures, error
+// plumbing and the host-side launchers that the translation units share.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cptr.h"
+
+namespace cptr {
+
+constexpr int kMaxLevels = 32;
+constexpr int kMaxRestart = 32;
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs: fixed grid of the Krylov reductions
+constexpr int kRedThreads = 256;
+
+struct Error {
+    cptr_status code;
+    std::string msg;
+};
+
+// throw-free error propagation inside the library: every helper returns cptr_status and leaves
+// its message in the context
+#define CPTR_CUDA_TRY(ctx, call)                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) return (ctx)->fail(CPTR_ECUDA, std::string(#call) + ": " +      \
+                                                  cudaGetErrorString(e_));                     \
+    } while (0)
+
+#define CPTR_TRY(call)                                                                         \
+    do {                                                                                       \
+        cptr_status s_ = (call);                                                               \
+        if (s_ != CPTR_OK) return s_;                                                          \
+    } while (0)
+
+// Device CSR matrix (int32 indices, FP64 values)
+struct Csr {
+    int32_t n = 0, nnz = 0;
+    int32_t *rp = nullptr, *ci = nullptr;
+    double *v = nullptr;
+};
+
+struct Level {
+    Csr A;                 // level operator
+    double *dinv = nullptr;// smoother D^{-1}
+    Csr P, PT;             // interpolation and restriction (empty on the coarsest level)
+    int32_t nc = 0;
+    int32_t *cf = nullptr; // 1 = C, 2 = F
+    double *b = nullptr, *x = nullptr, *t = nullptr, *r = nullptr;  // level work vectors
+};
+
+struct Hier {
+    int nlev = 0;
+    Level L[kMaxLevels];
+    double *cinv = nullptr;  // coarsest level: dense inverse (row-major), if dense
+    int dense = 0;
+    double op_complexity = 0.0;
+};
+
+// Arnoldi/Givens state kept on the device (one per context)
+struct KState {
+    int32_t k, done, breakdown, pad;  // columns completed in this cycle, flags
+    uint32_t ticket;                  // last-block ticket of the reductions
+    int32_t pad2;
+    double bnorm, beta, tol_abs, hnorm, est, true_res;
+    double h[kMaxRestart + 1];       // first-pass CGS coefficients
+    double h2[kMaxRestart + 1];      // second-pass CGS coefficients
+    double g[kMaxRestart + 1], cs[kMaxRestart], sn[kMaxRestart], y[kMaxRestart];
+    double H[(kMaxRestart + 1) * kMaxRestart];  // column-major, H[col * (m+1) + row]
+};
+
+struct Ctx;
+
+// ---- launch counting and event timing of kernel families -----------------------------------------
+void note_launch();          // every kernel launch of the library calls this once
+int64_t launch_count();
+enum { PF_SPMV = 0, PF_STAGE1 = 1, PF_RESID = 2, PF_ILU = 3, PF_ARNOLDI = 4, PF_N = 8 };
+struct Prof {
+    uint32_t mask = 0;
+    std::vector<cudaEvent_t> ev;   // pairs (begin, end)
+    std::vector<int> fam;
+    size_t used = 0;
+    double ms[PF_N] = {0};
+    int64_t cnt[PF_N] = {0};
+};
+int prof_begin(const Ctx *c, int fam);
+void prof_end(const Ctx *c, int slot);
+void prof_reset(Ctx *c);
+cptr_status prof_collect(Ctx *c);
+
+// ---- memory helpers ----------------------------------------------------------------------------
+cptr_status dalloc(Ctx *c, void **p, size_t bytes);
+template <typename T>
+inline cptr_status dalloc_t(Ctx *c, T **p, size_t count) {
+    return dalloc(c, reinterpret_cast<void **>(p), count * sizeof(T));
+}
+void dfree(void *p);
+void csr_free(Csr &a);
+
+// ---- sparse.cu ---------------------------------------------------------------------------------
+cptr_status scan_exclusive(Ctx *c, const int32_t *in, int32_t *out, int32_t n, int32_t *total_host);
+void launch_decouple(const Ctx *c, const double *Araw, const double *W, double *A);
+void launch_weight_vec(const Ctx *c, const double *W, const double *rhs, double *out);
+void launch_extract(const Ctx *c, int u, int w, double *out);
+void launch_check_finite(const Ctx *c, const double *v, int64_t n, int32_t *flag);
+void launch_bsr_spmv(const Ctx *c, const double *x, double *y);
+void launch_bsr_resid(const Ctx *c, const double *x, const double *v, double *y);
+void launch_bsr_resid_pt(const Ctx *c, const double *dp, const double *dT, const double *v, double *b1);
+void launch_csr_spmv(cudaStream_t s, const Csr &A, const double *x, double *y, double alpha, const double *c0);
+void launch_gather_pt(const Ctx *c, const double *v, double *bp, double *bT);
+void launch_scatter_pt(const Ctx *c, const double *dp, const double *dT, double *x1);
+void launch_sub(cudaStream_t s, int32_t n, const double *a, const double *b, double *out);
+
+// ---- amg.cu ------------------------------------------------------------------------------------
+cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, const double *v, int32_t n);
+void amg_free(Hier &h);
+void amg_vcycle(const Ctx *c, const Hier &h, const double *b, double *x);
+
+// ---- ilu.cu ------------------------------------------------------------------------------------
+cptr_status ilu_setup(Ctx *c);
+void ilu_free(Ctx *c);
+void ilu_apply(const Ctx *c, const double *r, double *z, const double *dp, const double *dT);
+
+// ---- krylov.cu ---------------------------------------------------------------------------------
+cptr_status fgmres_solve(Ctx *c, const double *bw, double *x, double rtol, cptr_stats *st);
+void apply_stage1(const Ctx *c, const double *v, const double **dp, const double **dT);
+void apply_precond(const Ctx *c, const double *v, double *z);
+
+// ---- the context -------------------------------------------------------------------------------
+struct Ctx {
+    cptr_options o{};
+    cudaStream_t stream = nullptr;
+    std::string err;
+    bool ready = false;
+    int32_t n = 0, b = 0, ps = 0, ts = 1, nnzb = 0;
+    // pattern (device) and its host copy
+    int32_t *rp = nullptr, *ci = nullptr, *diag = nullptr;
+    std::vector<int32_t> h_rp, h_ci, h_diag;
+    double *A = nullptr;     // decoupled A' (BSR, row-major blocks)
+    double *W = nullptr;     // per-cell weights (n * b * b)
+    double *App = nullptr, *ApT = nullptr, *ATp = nullptr, *St = nullptr;  // cell-pattern fields
+    Hier hp, hT;
+    // ILU(0): factors in A's pattern, diagonal slots hold inverted pivot blocks
+    double *LU = nullptr;
+    int32_t nlev_f = 0, nlev_b = 0;
+    int32_t *lvl_f = nullptr, *lvl_b = nullptr;       // rows sorted by level (device)
+    std::vector<int32_t> h_lptr_f, h_lptr_b;           // level pointers (host)
+    double *ybuf = nullptr, *zbuf = nullptr;           // ILU intermediate vectors
+    // preconditioner work
+    double *bp = nullptr, *bT = nullptr, *xp = nullptr, *dp = nullptr, *dT = nullptr, *t1 = nullptr;
+    double *b1 = nullptr;
+    // Krylov
+    double *V = nullptr, *Z = nullptr, *w = nullptr, *bw = nullptr, *xw = nullptr, *partial = nullptr;
+    KState *ks = nullptr;    // device
+    KState *ks_host = nullptr;  // pinned mirror
+    int32_t *flag = nullptr;    // device scratch flag
+    int32_t *scan_tmp = nullptr; int64_t scan_tmp_len = 0;
+    double setup_ms = 0.0;
+    mutable Prof prof;
+
+    cptr_status fail(cptr_status code, const std::string &m) {
+        err = m;
+        return code;
+    }
+};
+
+// lanes per row for a CSR kernel, from the average row length
+inline int lanes_for(int32_t n, int32_t nnz) {
+    double avg = n > 0 ? double(nnz) / n : 1.0;
+    if (avg <= 4.5) return 4;
+    if (avg <= 9.0) return 8;
+    if (avg <= 24.0) return 16;
+    return 32;
+}
+
+}  // namespace cptr

@@ -1,0 +1,339 @@
+// Right-preconditioned flexible GMRES(m) (Sec. 3 and Sec. 4: right-preconditioned GMRES,
+// relative residual tolerance) with classical Gram-Schmidt and one full re-orthogonalisation
+// (CGS2).  Each Gram-Schmidt pass is one streaming kernel that updates w and forms all partial
+// dot products of the pass with warp-shuffle and block reductions; the last block to finish
+// reduces the per-block partials in block order (deterministic) and, after the second pass,
+// applies the Givens rotations on the device.  The two-stage preconditioner is driven from here.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+namespace cptr {
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+enum { PASS_DOT = 0, PASS_UPD_DOT = 1, PASS_UPD_NORM = 2, PASS_NORM = 3 };
+enum { FIN_H = 0, FIN_H2 = 1, FIN_GIVENS = 2, FIN_BNORM = 3, FIN_RESTART = 4, FIN_TRUE = 5 };
+
+constexpr int kMaxC = kMaxRestart;   // columns per pass
+constexpr int kPStride = kMaxC + 1;  // partial row stride
+
+// One Gram-Schmidt pass over v_0..v_{nc-1} (columns of V, stride nb):
+//   PASS_DOT       partial[q] = v_q . w
+//   PASS_UPD_DOT   w -= sum_q coef_q v_q; partial[q] = v_q . w
+//   PASS_UPD_NORM  w -= sum_q coef_q v_q; partial = w . w
+//   PASS_NORM      partial = w . w
+template <int PASS>
+__global__ void __launch_bounds__(kRedThreads) k_cgs(int64_t nb, const double *__restrict__ V, int nc,
+                                                    double *__restrict__ w, const double *__restrict__ coef,
+                                                    double *__restrict__ partial, KState *ks, int fin, int j, int m,
+                                                    double rtol) {
+    __shared__ double scoef[kMaxC];
+    __shared__ double red[kRedThreads / 32][kMaxC];
+    __shared__ bool last;
+    if (ks->done && fin <= FIN_GIVENS) return;   // nothing after convergence in this cycle
+    constexpr bool UPD = PASS == PASS_UPD_DOT || PASS == PASS_UPD_NORM;
+    constexpr bool NORM = PASS == PASS_UPD_NORM || PASS == PASS_NORM;
+    constexpr int NA = NORM ? 1 : kMaxC;
+    if (UPD && threadIdx.x < kMaxC) scoef[threadIdx.x] = threadIdx.x < nc ? coef[threadIdx.x] : 0.0;
+    __syncthreads();
+    double acc[NA];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) acc[q] = 0.0;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride) {
+        double wi = w[i];
+        if (UPD) {
+#pragma unroll
+            for (int q = 0; q < kMaxC; ++q)
+                if (q < nc) wi = fma(-scoef[q], __ldg(V + (int64_t)q * nb + i), wi);
+            w[i] = wi;
+        }
+        if (NORM) {
+            acc[0] = fma(wi, wi, acc[0]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kMaxC; ++q)
+                if (q < nc) acc[q] = fma(__ldg(V + (int64_t)q * nb + i), wi, acc[q]);
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int na = NORM ? 1 : nc;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+        if (q >= na) break;
+        double v = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[wid][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < na) {
+        double s = 0.0;
+        for (int w8 = 0; w8 < kRedThreads / 32; ++w8) s += red[w8][threadIdx.x];
+        partial[(int64_t)blockIdx.x * kPStride + threadIdx.x] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&ks->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    // last block: reduce over blocks in block order
+    __threadfence();
+    __shared__ double res[kMaxC];
+    if (threadIdx.x < na) {
+        double s = 0.0;
+        for (unsigned bb = 0; bb < gridDim.x; ++bb) s += __ldcg(partial + (int64_t)bb * kPStride + threadIdx.x);
+        res[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    ks->ticket = 0;
+    if (fin == FIN_H) {
+        for (int q = 0; q < nc; ++q) ks->h[q] = res[q];
+    } else if (fin == FIN_H2) {
+        for (int q = 0; q < nc; ++q) ks->h2[q] = res[q];
+    } else if (fin == FIN_GIVENS) {
+        double hn = sqrt(res[0]);
+        double *col = ks->H + (int64_t)j * (m + 1);
+        for (int q = 0; q <= j; ++q) col[q] = ks->h[q] + ks->h2[q];
+        col[j + 1] = hn;
+        for (int q = 0; q < j; ++q) {
+            double a = col[q], b = col[q + 1];
+            col[q] = ks->cs[q] * a + ks->sn[q] * b;
+            col[q + 1] = -ks->sn[q] * a + ks->cs[q] * b;
+        }
+        double a = col[j], b = col[j + 1];
+        double den = sqrt(a * a + b * b);
+        ks->cs[j] = a / den;
+        ks->sn[j] = b / den;
+        col[j] = den;
+        col[j + 1] = 0.0;
+        ks->g[j + 1] = -ks->sn[j] * ks->g[j];
+        ks->g[j] = ks->cs[j] * ks->g[j];
+        ks->hnorm = hn;
+        ks->k = j + 1;
+        ks->est = fabs(ks->g[j + 1]) / ks->bnorm;
+        if (!isfinite(hn) || !isfinite(den) || !isfinite(ks->g[j])) { ks->breakdown = 1; ks->done = 1; }
+        else if (fabs(ks->g[j + 1]) <= ks->tol_abs || hn == 0.0) ks->done = 1;
+    } else if (fin == FIN_BNORM || fin == FIN_RESTART) {
+        double beta = sqrt(res[0]);
+        if (fin == FIN_BNORM) {
+            ks->bnorm = beta;
+            ks->tol_abs = rtol * beta;
+        }
+        ks->beta = beta;
+        for (int q = 0; q <= m; ++q) ks->g[q] = 0.0;
+        ks->g[0] = beta;
+        ks->k = 0;
+        ks->est = ks->bnorm > 0.0 ? beta / ks->bnorm : 0.0;
+        if (!isfinite(beta)) { ks->breakdown = 1; ks->done = 1; }
+        else ks->done = (beta <= ks->tol_abs) ? 1 : 0;
+    } else {  // FIN_TRUE
+        ks->true_res = sqrt(res[0]);
+    }
+}
+
+// dst = src / scale, scale = ks->hnorm (which = 0) or ks->beta (which = 1); skipped if 0 or done
+__global__ void k_scale(int64_t nb, const double *__restrict__ src, double *__restrict__ dst, const KState *ks,
+                        int which, int check_done) {
+    if (check_done && ks->done) return;
+    double s = which == 0 ? ks->hnorm : ks->beta;
+    if (!(s > 0.0)) return;
+    double inv = 1.0 / s;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride) dst[i] = src[i] * inv;
+}
+
+// y = H^{-1} g (upper triangular, k x k)
+__global__ void k_trisolve(KState *ks, int m) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int k = ks->k;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = ks->g[i];
+        for (int q = i + 1; q < k; ++q) s -= ks->H[(int64_t)q * (m + 1) + i] * ks->y[q];
+        ks->y[i] = s / ks->H[(int64_t)i * (m + 1) + i];
+    }
+}
+
+// x += sum_{q < k} y_q z_q
+__global__ void __launch_bounds__(256) k_update_x(int64_t nb, const double *__restrict__ Z, const KState *ks,
+                                                  double *__restrict__ x) {
+    __shared__ double sy[kMaxC];
+    int k = ks->k;
+    if (threadIdx.x < kMaxC) sy[threadIdx.x] = threadIdx.x < k ? ks->y[threadIdx.x] : 0.0;
+    __syncthreads();
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride) {
+        double s = x[i];
+#pragma unroll
+        for (int q = 0; q < kMaxC; ++q)
+            if (q < k) s = fma(sy[q], __ldg(Z + (int64_t)q * nb + i), s);
+        x[i] = s;
+    }
+}
+
+__global__ void k_add_x1(int32_t n, int b, int ps, int ts, const double *dp, const double *dT, const double *b1,
+                         double *z) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int q = 0; q < b; ++q) {
+        int64_t o = (int64_t)i * b + q;
+        double add = 0.0;
+        if (dp && q == ps) add = dp[i];
+        if (dT && q == ts) add = dT[i];
+        z[o] = b1[o] + add;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// stage 1 (Sec. 3.1 CPR; Sec. 3.3 the block preconditioner and its variants)
+void apply_stage1(const Ctx *c, const double *v, const double **pdp, const double **pdT) {
+    cudaStream_t s = c->stream;
+    Csr ATp{c->n, c->nnzb, c->rp, c->ci, c->ATp}, ApT{c->n, c->nnzb, c->rp, c->ci, c->ApT};
+    *pdp = nullptr;
+    *pdT = nullptr;
+    int mode = c->o.stage1;
+    if (mode == CPTR_STAGE1_NONE) return;
+    launch_gather_pt(c, v, c->bp, c->bT);
+    switch (mode) {
+    case CPTR_STAGE1_FULL:
+        amg_vcycle(c, c->hp, c->bp, c->xp);                     // 1. A_pp x_p = b_p
+        launch_csr_spmv(s, ATp, c->xp, c->t1, 1.0, c->bT);      // 2. b~_T = b_T - A_Tp x_p
+        amg_vcycle(c, c->hT, c->t1, c->dT);                     // 3. S~_T d_T = b~_T
+        launch_csr_spmv(s, ApT, c->dT, c->t1, 1.0, c->bp);      // 4. b~_p = b_p - A_pT d_T
+        amg_vcycle(c, c->hp, c->t1, c->dp);                     // 5. A_pp d_p = b~_p
+        break;
+    case CPTR_STAGE1_LOWER:
+        amg_vcycle(c, c->hp, c->bp, c->dp);
+        launch_csr_spmv(s, ATp, c->dp, c->t1, 1.0, c->bT);
+        amg_vcycle(c, c->hT, c->t1, c->dT);
+        break;
+    case CPTR_STAGE1_UPPER:
+        amg_vcycle(c, c->hT, c->bT, c->dT);
+        launch_csr_spmv(s, ApT, c->dT, c->t1, 1.0, c->bp);
+        amg_vcycle(c, c->hp, c->t1, c->dp);
+        break;
+    case CPTR_STAGE1_BD:
+        amg_vcycle(c, c->hp, c->bp, c->dp);
+        amg_vcycle(c, c->hT, c->bT, c->dT);
+        break;
+    case CPTR_STAGE1_CPR:
+        amg_vcycle(c, c->hp, c->bp, c->dp);
+        *pdp = c->dp;
+        return;
+    }
+    *pdp = c->dp;
+    *pdT = c->dT;
+}
+
+// z = M2^{-1}(v - A' x1) + x1, x1 = M1^{-1} v  (Sec. 3, two-stage preconditioners)
+void apply_precond(const Ctx *c, const double *v, double *z) {
+    const double *dp, *dT;
+    int pf = prof_begin(c, PF_STAGE1);
+    apply_stage1(c, v, &dp, &dT);
+    prof_end(c, pf);
+    const double *b1 = v;
+    if (dp) {
+        pf = prof_begin(c, PF_RESID);
+        launch_bsr_resid_pt(c, dp, dT, v, c->b1);
+        prof_end(c, pf);
+        b1 = c->b1;
+    }
+    if (c->o.stage2 == CPTR_STAGE2_ILU0) {
+        pf = prof_begin(c, PF_ILU);
+        ilu_apply(c, b1, z, dp, dT);
+        prof_end(c, pf);
+    } else {
+        (k_add_x1<<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->ps, c->ts, dp, dT, b1, z), note_launch());
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+template <int PASS>
+static void cgs(const Ctx *c, const double *V, int nc, double *w, const double *coef, int fin, int j,
+                double rtol = 0.0) {
+    int64_t nb = (int64_t)c->n * c->b;
+    (k_cgs<PASS><<<kRedBlocks, kRedThreads, 0, c->stream>>>(nb, V, nc, w, coef, c->partial, c->ks, fin, j,
+                                                          c->o.restart, rtol), note_launch());
+}
+
+// device address of a member of the device-resident Krylov state
+static const double *ks_field(const Ctx *c, size_t off) {
+    return reinterpret_cast<const double *>(reinterpret_cast<const char *>(c->ks) + off);
+}
+
+static cptr_status read_state(Ctx *c) {
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ks_host, c->ks, offsetof(KState, h), cudaMemcpyDeviceToHost, c->stream));
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return CPTR_OK;
+}
+
+cptr_status fgmres_solve(Ctx *c, const double *bw, double *x, double rtol, cptr_stats *st) {
+    const int m = c->o.restart;
+    const int64_t nb = (int64_t)c->n * c->b;
+    cudaStream_t s = c->stream;
+    const unsigned vgrid = 4 * 152;
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->ks, 0, sizeof(KState), s));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(x, 0, sizeof(double) * nb, s));
+    // ||b'||, beta = ||b'|| (x = 0), v_0 = b' / beta
+    cgs<PASS_NORM>(c, nullptr, 0, const_cast<double *>(bw), nullptr, FIN_BNORM, 0, rtol);
+    CPTR_TRY(read_state(c));
+    int it = 0, restarts = 0;
+    bool done = c->ks_host->done != 0;
+    if (!done) (k_scale<<<vgrid, 256, 0, s>>>(nb, bw, c->V, c->ks, 1, 0), note_launch());
+    while (!done) {
+        int every = c->o.check_every > 0 ? c->o.check_every : 1;
+        for (int j = 0; j < m && it < c->o.max_it; ++j) {
+            double *vj = c->V + (int64_t)j * nb, *zj = c->Z + (int64_t)j * nb;
+            apply_precond(c, vj, zj);
+            int pf = prof_begin(c, PF_SPMV);
+            launch_bsr_spmv(c, zj, c->w);
+            prof_end(c, pf);
+            pf = prof_begin(c, PF_ARNOLDI);
+            cgs<PASS_DOT>(c, c->V, j + 1, c->w, nullptr, FIN_H, j);
+            cgs<PASS_UPD_DOT>(c, c->V, j + 1, c->w, ks_field(c, offsetof(KState, h)), FIN_H2, j);
+            cgs<PASS_UPD_NORM>(c, c->V, j + 1, c->w, ks_field(c, offsetof(KState, h2)), FIN_GIVENS, j);
+            (k_scale<<<vgrid, 256, 0, s>>>(nb, c->w, c->V + (int64_t)(j + 1) * nb, c->ks, 0, 1), note_launch());
+            prof_end(c, pf);
+            ++it;
+            if (it % every == 0 || j == m - 1 || it >= c->o.max_it) {
+                CPTR_TRY(read_state(c));
+                if (c->ks_host->done) break;
+            }
+        }
+        CPTR_CUDA_TRY(c, cudaGetLastError());
+        CPTR_TRY(read_state(c));
+        if (c->ks_host->breakdown) break;
+        (k_trisolve<<<1, 32, 0, s>>>(c->ks, m), note_launch());
+        (k_update_x<<<vgrid, 256, 0, s>>>(nb, c->Z, c->ks, x), note_launch());
+        if (c->ks_host->done || it >= c->o.max_it) break;
+        // restart: r = b' - A' x, beta = ||r||, v_0 = r / beta
+        launch_bsr_resid(c, x, bw, c->w);
+        cgs<PASS_NORM>(c, nullptr, 0, c->w, nullptr, FIN_RESTART, 0);
+        CPTR_TRY(read_state(c));
+        if (c->ks_host->done) break;
+        (k_scale<<<vgrid, 256, 0, s>>>(nb, c->w, c->V, c->ks, 1, 0), note_launch());
+        ++restarts;
+    }
+    // true residual
+    launch_bsr_resid(c, x, bw, c->w);
+    cgs<PASS_NORM>(c, nullptr, 0, c->w, nullptr, FIN_TRUE, 0);
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    CPTR_TRY(read_state(c));
+    const KState &h = *c->ks_host;
+    if (st) {
+        st->iters = it;
+        st->restarts = restarts;
+        st->converged = h.done && !h.breakdown;
+        st->est_rel_res = h.est;
+        st->bnorm = h.bnorm;
+        st->true_rel_res = h.bnorm > 0.0 ? h.true_res / h.bnorm : 0.0;
+    }
+    if (h.breakdown) return c->fail(CPTR_EBREAKDOWN, "FGMRES: non-finite value in the Arnoldi process");
+    return (h.done) ? CPTR_OK : CPTR_NOT_CONVERGED;
+}
+
+}  // namespace cptr

@@ -1,0 +1,407 @@
+// Sparse building blocks of the CPTR solve: BSR SpMV with b x b register blocks, the decoupling
+// A' = W A (Sec. 2.2.2 eq. weighted, Sec. 3.5 eq. scaling), the extraction of the scalar p-T
+// blocks on the cell pattern (Sec. 3.2 eq. A00), the stage-1 residual v - A' R_0^T x_0
+// (Sec. 3 "Two-stage preconditioners", step 2), scalar CSR SpMV, and a device prefix scan.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <atomic>
+
+#include "common.cuh"
+
+namespace cptr {
+
+static std::atomic<int64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+int prof_begin(const Ctx *c, int fam) {
+    Prof &p = c->prof;
+    if (!(p.mask & (1u << fam))) return -1;
+    if (2 * (p.used + 1) > p.ev.size()) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            p.ev.push_back(e);
+        }
+        p.fam.resize(p.ev.size() / 2);
+    }
+    size_t s = p.used++;
+    p.fam[s] = fam;
+    cudaEventRecord(p.ev[2 * s], c->stream);
+    return (int)s;
+}
+void prof_end(const Ctx *c, int slot) {
+    if (slot >= 0) cudaEventRecord(c->prof.ev[2 * (size_t)slot + 1], c->stream);
+}
+void prof_reset(Ctx *c) {
+    c->prof.used = 0;
+    for (int f = 0; f < PF_N; ++f) { c->prof.ms[f] = 0.0; c->prof.cnt[f] = 0; }
+}
+cptr_status prof_collect(Ctx *c) {
+    Prof &p = c->prof;
+    for (size_t s = 0; s < p.used; ++s) {
+        float ms = 0.f;
+        CPTR_CUDA_TRY(c, cudaEventSynchronize(p.ev[2 * s + 1]));
+        CPTR_CUDA_TRY(c, cudaEventElapsedTime(&ms, p.ev[2 * s], p.ev[2 * s + 1]));
+        p.ms[p.fam[s]] += ms;
+        p.cnt[p.fam[s]] += 1;
+    }
+    p.used = 0;
+    return CPTR_OK;
+}
+
+cptr_status dalloc(Ctx *c, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return c->fail(CPTR_ENOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+    return CPTR_OK;
+}
+void dfree(void *p) {
+    if (p) cudaFree(p);
+}
+void csr_free(Csr &a) {
+    dfree(a.rp); dfree(a.ci); dfree(a.v);
+    a = Csr{};
+}
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------------------------------------------
+// exclusive prefix scan of int32: tiles of 2048 (256 threads x 8 items)
+constexpr int kScanT = 256, kScanI = 8, kScanTile = kScanT * kScanI;
+
+__device__ __forceinline__ int32_t block_scan_excl(int32_t v, int32_t *total) {
+    __shared__ int32_t warp_sum[kScanT / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t s = lane < kScanT / 32 ? warp_sum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kScanT / 32) warp_sum[lane] = s;
+    }
+    __syncthreads();
+    int32_t before = (wid > 0 ? warp_sum[wid - 1] : 0) + x - v;
+    *total = warp_sum[kScanT / 32 - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void k_tile_sum(const int32_t *in, int32_t n, int32_t *tsum) {
+    int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanI;
+    int32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanI; ++k)
+        if (base + k < n) s += in[base + k];
+    int32_t tot;
+    block_scan_excl(s, &tot);
+    if (threadIdx.x == 0) tsum[blockIdx.x] = tot;
+}
+
+__global__ void k_tile_scan(const int32_t *in, int32_t n, const int32_t *toff, int32_t *out) {
+    int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanI;
+    int32_t loc[kScanI];
+    int32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanI; ++k) {
+        loc[k] = (base + k < n) ? in[base + k] : 0;
+        s += loc[k];
+    }
+    int32_t tot;
+    int32_t run = block_scan_excl(s, &tot) + (toff ? toff[blockIdx.x] : 0);
+#pragma unroll
+    for (int k = 0; k < kScanI; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += loc[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanT - 1) out[n] = run;
+}
+
+// out[0..n] = exclusive scan of in[0..n-1], out[n] = total.  out may not alias in.
+static cptr_status scan_rec(Ctx *c, const int32_t *in, int32_t *out, int32_t n, int32_t *tmp) {
+    if (n <= 0) {
+        CPTR_CUDA_TRY(c, cudaMemsetAsync(out, 0, sizeof(int32_t), c->stream));
+        return CPTR_OK;
+    }
+    int32_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        (k_tile_scan<<<1, kScanT, 0, c->stream>>>(in, n, nullptr, out), note_launch());
+        return CPTR_OK;
+    }
+    int32_t *tsum = tmp, *toff = tmp + tiles;
+    (k_tile_sum<<<tiles, kScanT, 0, c->stream>>>(in, n, tsum), note_launch());
+    CPTR_TRY(scan_rec(c, tsum, toff, tiles, tmp + 2 * tiles + 1));
+    (k_tile_scan<<<tiles, kScanT, 0, c->stream>>>(in, n, toff, out), note_launch());
+    return CPTR_OK;
+}
+
+cptr_status scan_exclusive(Ctx *c, const int32_t *in, int32_t *out, int32_t n, int32_t *total_host) {
+    int64_t need = 4 * ((int64_t)n / kScanTile + 8) + 64;
+    if (need > c->scan_tmp_len) {
+        dfree(c->scan_tmp);
+        c->scan_tmp = nullptr;
+        CPTR_TRY(dalloc_t(c, &c->scan_tmp, (size_t)need));
+        c->scan_tmp_len = need;
+    }
+    CPTR_TRY(scan_rec(c, in, out, n, c->scan_tmp));
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    if (total_host) {
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(total_host, out + n, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    return CPTR_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// decoupling: block row i of A' = W_i * (block row i of A); each entry is the sum over the slot
+// index of separately rounded products, in slot order, so that A' is reproducible bit for bit
+template <int B>
+__global__ void k_decouple(int32_t n, const int32_t *rp, const double *Araw, const double *W, double *A) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double w[B * B];
+#pragma unroll
+    for (int t = 0; t < B * B; ++t) w[t] = W ? W[(int64_t)i * B * B + t] : ((t / B == t % B) ? 1.0 : 0.0);
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+        const double *a = Araw + (int64_t)k * B * B;
+        double in[B * B];
+#pragma unroll
+        for (int t = 0; t < B * B; ++t) in[t] = a[t];
+#pragma unroll
+        for (int r = 0; r < B; ++r)
+#pragma unroll
+            for (int cc = 0; cc < B; ++cc) {
+                double s = 0.0;
+#pragma unroll
+                for (int q = 0; q < B; ++q) s = __dadd_rn(s, __dmul_rn(w[r * B + q], in[q * B + cc]));
+                A[(int64_t)k * B * B + r * B + cc] = s;
+            }
+    }
+}
+
+void launch_decouple(const Ctx *c, const double *Araw, const double *W, double *A) {
+    if (c->b == 3) (k_decouple<3><<<nblk(c->n, 128), 128, 0, c->stream>>>(c->n, c->rp, Araw, W, A), note_launch());
+    else (k_decouple<4><<<nblk(c->n, 128), 128, 0, c->stream>>>(c->n, c->rp, Araw, W, A), note_launch());
+}
+
+template <int B>
+__global__ void k_weight_vec(int32_t n, const double *W, const double *rhs, double *out) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) v[q] = rhs[(int64_t)i * B + q];
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < B; ++q) s = __dadd_rn(s, __dmul_rn(W ? W[(int64_t)i * B * B + r * B + q] : (r == q ? 1.0 : 0.0), v[q]));
+        out[(int64_t)i * B + r] = s;
+    }
+}
+
+void launch_weight_vec(const Ctx *c, const double *W, const double *rhs, double *out) {
+    if (c->b == 3) (k_weight_vec<3><<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, W, rhs, out), note_launch());
+    else (k_weight_vec<4><<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, W, rhs, out), note_launch());
+}
+
+// scalar field (u, w) of every block: out[k] = A'[k](u, w)
+__global__ void k_extract(int32_t nnzb, int b, const double *A, int u, int w, double *out) {
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nnzb) out[k] = A[(int64_t)k * b * b + u * b + w];
+}
+void launch_extract(const Ctx *c, int u, int w, double *out) {
+    (k_extract<<<nblk(c->nnzb, 256), 256, 0, c->stream>>>(c->nnzb, c->b, c->A, u, w, out), note_launch());
+}
+
+__global__ void k_check_finite(const double *v, int64_t n, int32_t *flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int bad = 0;
+    for (; i < n; i += stride) bad |= !isfinite(v[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+void launch_check_finite(const Ctx *c, const double *v, int64_t n, int32_t *flag) {
+    (k_check_finite<<<4 * 152, 256, 0, c->stream>>>(v, n, flag), note_launch());
+}
+
+// ------------------------------------------------------------------------------------------------
+// BSR SpMV: G lanes per block row, each lane owns whole b x b blocks (vectorised block loads),
+// the G partial row sums are combined with shuffles.  MODE 0: y = A x;  MODE 1: y = v - A x.
+template <int B, int G, int MODE>
+__global__ void __launch_bounds__(256) k_bsr_spmv(int32_t n, const int32_t *__restrict__ rp,
+                                                   const int32_t *__restrict__ ci, const double *__restrict__ A,
+                                                   const double *__restrict__ x, const double *__restrict__ v,
+                                                   double *__restrict__ y) {
+    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t row = (int32_t)(gid / G);
+    int lane = threadIdx.x % G;
+    double acc[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) acc[r] = 0.0;
+    if (row < n) {
+        int32_t k1 = __ldg(rp + row + 1);
+        for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G) {
+            int32_t col = __ldg(ci + k);
+            const double *a = A + (int64_t)k * B * B;
+            double xv[B];
+#pragma unroll
+            for (int q = 0; q < B; ++q) xv[q] = __ldg(x + (int64_t)col * B + q);
+#pragma unroll
+            for (int r = 0; r < B; ++r)
+#pragma unroll
+                for (int q = 0; q < B; ++q) acc[r] = fma(__ldg(a + r * B + q), xv[q], acc[r]);
+        }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < B; ++r) acc[r] += __shfl_down_sync(0xffffffffu, acc[r], o, G);
+    if (row < n && lane == 0) {
+#pragma unroll
+        for (int r = 0; r < B; ++r) {
+            int64_t o = (int64_t)row * B + r;
+            y[o] = MODE == 1 ? v[o] - acc[r] : acc[r];
+        }
+    }
+}
+
+template <int MODE>
+static void bsr_spmv_dispatch(const Ctx *c, const double *x, const double *v, double *y) {
+    constexpr int G = 8;
+    unsigned grid = nblk((int64_t)c->n * G, 256);
+    if (c->b == 3) (k_bsr_spmv<3, G, MODE><<<grid, 256, 0, c->stream>>>(c->n, c->rp, c->ci, c->A, x, v, y), note_launch());
+    else (k_bsr_spmv<4, G, MODE><<<grid, 256, 0, c->stream>>>(c->n, c->rp, c->ci, c->A, x, v, y), note_launch());
+}
+void launch_bsr_spmv(const Ctx *c, const double *x, double *y) { bsr_spmv_dispatch<0>(c, x, nullptr, y); }
+void launch_bsr_resid(const Ctx *c, const double *x, const double *v, double *y) { bsr_spmv_dispatch<1>(c, x, v, y); }
+
+// stage-1 residual b1 = v - A' R_0^T [dp; dT]: only the p and T columns of each block are used
+template <int B, int G>
+__global__ void __launch_bounds__(256) k_bsr_resid_pt(int32_t n, const int32_t *__restrict__ rp,
+                                                       const int32_t *__restrict__ ci, const double *__restrict__ A,
+                                                       int ps, int ts, const double *__restrict__ dp,
+                                                       const double *__restrict__ dT, const double *__restrict__ v,
+                                                       double *__restrict__ b1) {
+    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t row = (int32_t)(gid / G);
+    int lane = threadIdx.x % G;
+    double acc[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) acc[r] = 0.0;
+    if (row < n) {
+        int32_t k1 = __ldg(rp + row + 1);
+        for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G) {
+            int32_t col = __ldg(ci + k);
+            const double *a = A + (int64_t)k * B * B;
+            double xp = __ldg(dp + col);
+            double xt = dT ? __ldg(dT + col) : 0.0;
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                acc[r] = fma(__ldg(a + r * B + ps), xp, acc[r]);
+                if (dT) acc[r] = fma(__ldg(a + r * B + ts), xt, acc[r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < B; ++r) acc[r] += __shfl_down_sync(0xffffffffu, acc[r], o, G);
+    if (row < n && lane == 0) {
+#pragma unroll
+        for (int r = 0; r < B; ++r) {
+            int64_t o = (int64_t)row * B + r;
+            b1[o] = v[o] - acc[r];
+        }
+    }
+}
+void launch_bsr_resid_pt(const Ctx *c, const double *dp, const double *dT, const double *v, double *b1) {
+    constexpr int G = 8;
+    unsigned grid = nblk((int64_t)c->n * G, 256);
+    if (c->b == 3)
+        (k_bsr_resid_pt<3, G><<<grid, 256, 0, c->stream>>>(c->n, c->rp, c->ci, c->A, c->ps, c->ts, dp, dT, v, b1), note_launch());
+    else
+        (k_bsr_resid_pt<4, G><<<grid, 256, 0, c->stream>>>(c->n, c->rp, c->ci, c->A, c->ps, c->ts, dp, dT, v, b1), note_launch());
+}
+
+// ------------------------------------------------------------------------------------------------
+// scalar CSR SpMV with G lanes per row: y = alpha * A x, or y = c0 - A x when c0 != nullptr
+// (alpha ignored), or y += A x when alpha == 2 (prolongation-add)
+template <int G>
+__global__ void __launch_bounds__(256) k_csr_spmv(int32_t n, const int32_t *__restrict__ rp,
+                                                   const int32_t *__restrict__ ci, const double *__restrict__ v,
+                                                   const double *__restrict__ x, double *__restrict__ y, int mode,
+                                                   const double *__restrict__ c0) {
+    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t row = (int32_t)(gid / G);
+    int lane = threadIdx.x % G;
+    double acc = 0.0;
+    if (row < n) {
+        int32_t k1 = __ldg(rp + row + 1);
+        for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G) acc = fma(__ldg(v + k), __ldg(x + __ldg(ci + k)), acc);
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
+    if (row < n && lane == 0) {
+        if (mode == 0) y[row] = acc;
+        else if (mode == 1) y[row] = c0[row] - acc;
+        else y[row] += acc;
+    }
+}
+
+void launch_csr_spmv(cudaStream_t s, const Csr &A, const double *x, double *y, double alpha, const double *c0) {
+    int mode = c0 ? 1 : (alpha == 2.0 ? 2 : 0);
+    int G = lanes_for(A.n, A.nnz);
+    unsigned grid = nblk((int64_t)A.n * G, 256);
+    switch (G) {
+    case 4: (k_csr_spmv<4><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, x, y, mode, c0), note_launch()); break;
+    case 8: (k_csr_spmv<8><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, x, y, mode, c0), note_launch()); break;
+    case 16: (k_csr_spmv<16><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, x, y, mode, c0), note_launch()); break;
+    default: (k_csr_spmv<32><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, x, y, mode, c0), note_launch()); break;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// restriction to / prolongation from the p-T unknowns (Sec. 3.2)
+__global__ void k_gather_pt(int32_t n, int b, int ps, int ts, const double *v, double *bp, double *bT) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        bp[i] = v[(int64_t)i * b + ps];
+        bT[i] = v[(int64_t)i * b + ts];
+    }
+}
+void launch_gather_pt(const Ctx *c, const double *v, double *bp, double *bT) {
+    (k_gather_pt<<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->ps, c->ts, v, bp, bT), note_launch());
+}
+__global__ void k_scatter_pt(int32_t n, int b, int ps, int ts, const double *dp, const double *dT, double *x1) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        for (int q = 0; q < b; ++q) x1[(int64_t)i * b + q] = q == ps ? dp[i] : (q == ts && dT ? dT[i] : 0.0);
+}
+void launch_scatter_pt(const Ctx *c, const double *dp, const double *dT, double *x1) {
+    (k_scatter_pt<<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->ps, c->ts, dp, dT, x1), note_launch());
+}
+__global__ void k_sub(int32_t n, const double *a, const double *b, double *out) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] - b[i];
+}
+void launch_sub(cudaStream_t s, int32_t n, const double *a, const double *b, double *out) {
+    (k_sub<<<nblk(n, 256), 256, 0, s>>>(n, a, b, out), note_launch());
+}
+
+}  // namespace cptr

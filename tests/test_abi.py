@@ -1,0 +1,57 @@
+"""The C ABI library builds for sm_103a, loads, and exports every entry point its header declares.
+No compute call is made here (no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1907_04229_gb300 as cp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "cptr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cptr_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cp.build()
+    return cp.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(cp._SIGS), set(names) ^ set(cp._SIGS)
+
+
+def test_library_targets_sm103a():
+    # the fat binary embeds sm_103a code only; cuobjdump is not needed: nvcc's -gencode list is fixed
+    from paper_1907_04229_gb300 import _build
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.getsize(_build.LIB) > 100_000
+
+
+def test_default_options(lib):
+    o = cp.cptr_default_options()
+    assert (o.stage1, o.stage2, o.schur, o.smoother) == (0, 0, 0, 0)
+    assert abs(o.theta - 0.25) < 1e-15 and abs(o.omega - 2.0 / 3.0) < 1e-15
+    assert (o.n_coarse, o.max_levels, o.restart, o.max_it, o.dense_max) == (256, 25, 30, 1000, 1024)
+
+
+def test_option_struct_layout_matches_header():
+    # cptr_options: 4 int32, 2 doubles, 8 int32, one pointer
+    assert ctypes.sizeof(cp.cptr_options) == 16 + 16 + 32 + 8
+    assert ctypes.sizeof(cp.cptr_stats) == 24 + 7 * 8
+
+
+def test_null_context_is_rejected(lib):
+    assert lib.cptr_setup(None, 1, 3, None, None, None, None, None, None, 0) == -1
+    assert lib.cptr_solve(None, None, None, 1e-6, None, 0) == -1
+    assert lib.cptr_last_error(None) == b"null context"

@@ -1,0 +1,239 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs.
+
+Tolerances (FP64 throughout):
+  - set-up arithmetic (decoupling, AMG hierarchy: strength, PMIS, interpolation, Galerkin
+    products, smoother diagonals) is ordered identically on both sides: compared bit for bit;
+  - one application of an operator (SpMV, V-cycle, ILU, stage 1, two-stage preconditioner):
+    relative error <= 1e-10 (different summation order and fused multiply-adds, amplified by the
+    conditioning of the coarsest solve and of the triangular solves);
+  - the FGMRES solve: iterations equal to the oracle's +-1 and relative solution error <= 1e-8
+    per unknown kind (the acceptance bar of the method's parity requirement).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+import paper_1907_04229_gb300 as cp  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+_SYSTEMS = {}
+
+
+def system(name):
+    if name not in _SYSTEMS:
+        if name == "parity":
+            r = synth.recipe("parity")
+        elif name == "ragged":        # odd sizes: tails in every kernel's tiling
+            r = synth.make_box(7, 5, 3, 3.125, seed=17, heaters=[(11, 80.0, 420.0)])
+        elif name == "three_phase":   # b = 4
+            r = synth.make_box(6, 5, 3, 3.125, seed=19, nphase=3)
+        elif name == "medium":        # several AMG levels
+            r = synth.make_box(40, 40, 10, 0.5, 0.5, 0.25, seed=11, sigma=2.0, layered=True, kv_ratio=0.1,
+                               kT_const=2.0, T_inj=500.0, q_inj=1e-6, dt=365 * 86400.0)
+        elif name == "line":
+            r = synth.make_box(24, 1, 1, 3.125, seed=4)
+        elif name == "cptr200k":
+            r = synth.recipe("cptr200k")
+        else:
+            raise KeyError(name)
+        _SYSTEMS[name] = r.system()
+    return _SYSTEMS[name]
+
+
+OPTS = {"parity": dict(max_levels=2), "ragged": dict(max_levels=3, n_coarse=8), "three_phase": dict(n_coarse=16),
+        "medium": dict(), "line": dict(max_levels=2, n_coarse=4), "cptr200k": dict()}
+
+
+def gpu_solver(s, **opts):
+    S = cp.Solver(**opts)
+    S.setup(s["n"], s["b"], dev(s["row_ptr"]), dev(s["col_idx"]), dev(s["vals"].reshape(-1)),
+            dev(s["unknown_kind"]), dev(s["weights"].reshape(-1)), dev(s["st"]))
+    return S
+
+
+def pair(name, **extra):
+    s = system(name)
+    o = {**OPTS[name], **extra}
+    return s, oracle.Oracle.from_system(s, **o), gpu_solver(s, **o)
+
+
+def relerr(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["parity", "ragged", "three_phase"])
+def test_weights_and_matrix(name):
+    s, o, g = pair(name)
+    nb = s["n"] * s["b"]
+    rhs = s["rhs"].reshape(-1)
+    out = torch.empty(nb, dtype=torch.float64, device="cuda")
+    cp.cptr_apply_weights(g.ctx, dev(rhs), out)
+    assert np.array_equal(host(out), o.weight_rhs(rhs))          # same operation order: exact
+    x = synth.normal(3, nb)
+    y = torch.empty(nb, dtype=torch.float64, device="cuda")
+    cp.cptr_apply_matrix(g.ctx, dev(x), y)
+    rp, ci, v = o.matrix()
+    absAx = np.array([np.abs(v[rp[i]:rp[i + 1]]) @ np.abs(x[ci[rp[i]:rp[i + 1]]]) for i in range(nb)])
+    assert (np.abs(host(y) - o.spmv(x)) <= 1e-14 * absAx).all()
+
+
+@pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "medium"])
+def test_amg_hierarchy_bitwise(name):
+    s, o, g = pair(name)
+    for which in (0, 1):
+        lo, lg = o.levels(which), g.hierarchy(which)
+        assert len(lo) == len(lg) >= 2
+        for a, b in zip(lo, lg):
+            assert a["n"] == b["n"]
+            for key in ("rp", "ci", "v", "dinv"):
+                assert np.array_equal(a[key], b[key]), key
+            if "cf" in a:
+                for key in ("cf", "Prp", "Pci", "Pv"):
+                    assert np.array_equal(a[key], b[key]), key
+
+
+@pytest.mark.parametrize("name", ["parity", "ragged", "medium"])
+@pytest.mark.parametrize("smoother", ["l1", "jacobi"])
+def test_vcycle(name, smoother):
+    s, o, g = pair(name, smoother=cp.SMOOTHER[smoother])
+    for which in (0, 1):
+        b = synth.normal(21 + which, s["n"])
+        x = torch.empty(s["n"], dtype=torch.float64, device="cuda")
+        cp.cptr_apply_vcycle(g.ctx, which, dev(b), x)
+        assert relerr(host(x), o.vcycle(which, b)) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "line"])
+def test_ilu(name):
+    s, o, g = pair(name)
+    nb = s["n"] * s["b"]
+    r = synth.normal(5, nb)
+    z = torch.empty(nb, dtype=torch.float64, device="cuda")
+    cp.cptr_apply_ilu(g.ctx, dev(r), z)
+    assert relerr(host(z), o.ilu_apply(r)) <= 1e-10
+
+
+@pytest.mark.parametrize("mode", ["full", "upper", "lower", "bd", "cpr", "none"])
+def test_stage1_and_precond(mode):
+    s, o, g = pair("parity", stage1=cp.STAGE1[mode])
+    nb = s["n"] * s["b"]
+    v = synth.normal(9, nb)
+    x1 = torch.empty(nb, dtype=torch.float64, device="cuda")
+    cp.cptr_apply_stage1(g.ctx, dev(v), x1)
+    ref = o.stage1(v)
+    if mode == "none":
+        assert not host(x1).any()
+    else:
+        assert relerr(host(x1), ref) <= 1e-10
+    z = torch.empty(nb, dtype=torch.float64, device="cuda")
+    cp.cptr_apply_precond(g.ctx, dev(v), z)
+    assert relerr(host(z), o.precond(v)) <= 1e-10
+
+
+def check_solve(s, o, g, rtol, slack=1):
+    x_o, info_o = o.solve(s["rhs"], rtol)
+    x_g, info_g = g.solve(dev(s["rhs"].reshape(-1)), rtol)
+    x_g = host(x_g)
+    assert info_g["status"] == "CPTR_OK" and info_o["converged"]
+    assert abs(info_g["iters"] - info_o["iters"]) <= slack, (info_g["iters"], info_o["iters"])
+    assert info_g["true_rel_res"] <= rtol * 1.05
+    b = s["b"]
+    for u in range(b):  # per unknown kind: pressure, temperature, saturations
+        assert relerr(x_g[u::b], x_o[u::b]) <= 1e-8, (u, relerr(x_g[u::b], x_o[u::b]))
+    return info_o, info_g
+
+
+@pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "medium"])
+@pytest.mark.parametrize("mode", ["full", "cpr"])
+def test_solve(name, mode):
+    s, o, g = pair(name, stage1=cp.STAGE1[mode])
+    check_solve(s, o, g, 1e-8)
+
+
+@pytest.mark.parametrize("mode", ["upper", "lower", "bd", "none"])
+def test_solve_variants(mode):
+    s, o, g = pair("parity", stage1=cp.STAGE1[mode])
+    check_solve(s, o, g, 1e-8)
+
+
+def test_solve_full_size_workload():
+    # the benchmark's workload (100x100x20, 600k unknowns), the oracle run in full
+    s, o, g = pair("cptr200k")
+    info_o, info_g = check_solve(s, o, g, 1e-6)
+    assert info_g["levels_p"] == len(o.levels(0))
+
+
+def test_line_grid_converges_in_one_iteration():
+    s, o, g = pair("line")
+    x, info = g.solve(dev(s["rhs"].reshape(-1)), 1e-10)
+    assert info["iters"] == 1 and info["status"] == "CPTR_OK"
+
+
+def test_restarts_and_iteration_limit():
+    s, o, g = pair("parity", stage1=cp.STAGE1["none"], restart=5, max_it=400)
+    info_o, info_g = check_solve(s, o, g, 1e-8, slack=1)
+    assert info_g["restarts"] >= 1
+    # hitting max_it returns NOT_CONVERGED with the same iterate as the oracle
+    s, o, g = pair("parity", stage1=cp.STAGE1["none"], restart=5, max_it=12)
+    x_o, io = o.solve(s["rhs"], 1e-12)
+    x_g, ig = g.solve(dev(s["rhs"].reshape(-1)), 1e-12)
+    assert ig["status"] == "CPTR_NOT_CONVERGED" and ig["iters"] == io["iters"] == 12
+    assert relerr(host(x_g), x_o) <= 1e-8
+
+
+def test_zero_rhs():
+    s, o, g = pair("parity")
+    x, info = g.solve(torch.zeros(s["n"] * s["b"], dtype=torch.float64, device="cuda"), 1e-8)
+    assert info["iters"] == 0 and not host(x).any()
+
+
+def test_host_pointers_match_device_pointers():
+    s = system("ragged")
+    S = cp.Solver(**OPTS["ragged"])
+    S.setup(s["n"], s["b"], s["row_ptr"], s["col_idx"], s["vals"].reshape(-1), s["unknown_kind"],
+            s["weights"].reshape(-1), s["st"])
+    xh, ih = S.solve(np.ascontiguousarray(s["rhs"].reshape(-1)), 1e-8)
+    g = gpu_solver(s, **OPTS["ragged"])
+    xd, idv = g.solve(dev(s["rhs"].reshape(-1)), 1e-8)
+    assert ih["iters"] == idv["iters"]
+    assert np.array_equal(xh, host(xd))
+
+
+def test_invalid_inputs_are_rejected():
+    s = system("ragged")
+    S = cp.Solver()
+    with pytest.raises(cp.CptrError) as e:
+        S.solve(dev(s["rhs"].reshape(-1)), 1e-8)
+    assert e.value.code == -7                                     # solve before setup
+    ci = s["col_idx"].copy()
+    ci[[1, 2]] = ci[[2, 1]]                                       # unsorted row
+    with pytest.raises(cp.CptrError) as e:
+        S.setup(s["n"], s["b"], s["row_ptr"], ci, s["vals"].reshape(-1), s["unknown_kind"])
+    assert e.value.code == -1
+    v = s["vals"].reshape(-1).copy()
+    v[17] = np.nan
+    with pytest.raises(cp.CptrError) as e:
+        S.setup(s["n"], s["b"], s["row_ptr"], s["col_idx"], v, s["unknown_kind"])
+    assert e.value.code == -1 and "non-finite" in str(e.value)
+    with pytest.raises(cp.CptrError) as e:
+        S.setup(s["n"], s["b"], s["row_ptr"], s["col_idx"], s["vals"].reshape(-1), np.array([0, 2, 2], np.int32))
+    assert e.value.code == -1
+    # the context is still usable after errors
+    S.setup(s["n"], s["b"], s["row_ptr"], s["col_idx"], s["vals"].reshape(-1), s["unknown_kind"],
+            s["weights"].reshape(-1), s["st"])
+    x, info = S.solve(np.ascontiguousarray(s["rhs"].reshape(-1)), 1e-8)
+    assert info["status"] == "CPTR_OK"
