@@ -63,6 +63,7 @@ _SIGS = {
     "cptr_apply_stage1": (_I, [_P, _P, _P]),
     "cptr_apply_ilu": (_I, [_P, _P, _P]),
     "cptr_apply_precond": (_I, [_P, _P, _P]),
+    "cptr_apply_ilu_static": (_I, [_P, _P, _P]),
     "cptr_apply_vcycle": (_I, [_P, _I, _P, _P]),
     "cptr_hierarchy_info": (_I, [_P, _I, _P, _P]),
     "cptr_hierarchy_level": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -180,6 +181,11 @@ def cptr_apply_stage1(ctx, v, x1):
 
 def cptr_apply_ilu(ctx, r, z):
     return _vec_call("cptr_apply_ilu", ctx, _ptr(r), _ptr(z))
+
+
+def cptr_apply_ilu_static(ctx, r, z):
+    """Allocation-free ILU(0) application (scratch in a static device array, at most 2^20 unknowns)."""
+    return _vec_call("cptr_apply_ilu_static", ctx, _ptr(r), _ptr(z))
 
 
 def cptr_apply_precond(ctx, v, z):

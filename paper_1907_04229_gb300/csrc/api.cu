@@ -10,10 +10,6 @@
 
 using namespace cptr;
 
-struct cptr_ctx {
-    Ctx c;
-};
-
 namespace {
 
 bool host_or_device_copy(Ctx *c, void *dst, const void *src, size_t bytes, int on_device, cudaMemcpyKind to) {

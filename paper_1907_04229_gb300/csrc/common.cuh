@@ -124,6 +124,7 @@ void amg_vcycle(const Ctx *c, const Hier &h, const double *b, double *x);
 cptr_status ilu_setup(Ctx *c);
 void ilu_free(Ctx *c);
 void ilu_apply(const Ctx *c, const double *r, double *z, const double *dp, const double *dT);
+void ilu_apply_into(const Ctx *c, const double *r, double *z, double *ybuf, double *zbuf);
 
 // ---- krylov.cu ---------------------------------------------------------------------------------
 cptr_status fgmres_solve(Ctx *c, const double *bw, double *x, double rtol, cptr_stats *st);
@@ -178,3 +179,8 @@ inline int lanes_for(int32_t n, int32_t nnz) {
 }
 
 }  // namespace cptr
+
+// the opaque handle of the C ABI
+struct cptr_ctx {
+    cptr::Ctx c;
+};

@@ -256,4 +256,24 @@ void ilu_apply(const Ctx *c, const double *r, double *z, const double *dp, const
     }
 }
 
+// z = (LU)^{-1} r with caller-supplied intermediate vectors ybuf, zbuf (n*b doubles each);
+// used by the allocation-free entry point
+void ilu_apply_into(const Ctx *c, const double *r, double *z, double *ybuf, double *zbuf) {
+    cudaStream_t s = c->stream;
+    for (int32_t l = 0; l < c->nlev_f; ++l) {
+        int32_t st = c->h_lptr_f[l], cnt = c->h_lptr_f[l + 1] - st;
+        if (c->b == 3) (k_ilu_fwd<3><<<nblk(cnt, 128), 128, 0, s>>>(c->lvl_f, st, cnt, c->rp, c->ci, c->diag, c->LU, r, ybuf), note_launch());
+        else (k_ilu_fwd<4><<<nblk(cnt, 128), 128, 0, s>>>(c->lvl_f, st, cnt, c->rp, c->ci, c->diag, c->LU, r, ybuf), note_launch());
+    }
+    for (int32_t l = 0; l < c->nlev_b; ++l) {
+        int32_t st = c->h_lptr_b[l], cnt = c->h_lptr_b[l + 1] - st;
+        if (c->b == 3)
+            (k_ilu_bwd<3><<<nblk(cnt, 128), 128, 0, s>>>(c->lvl_b, st, cnt, c->rp, c->ci, c->diag, c->LU, ybuf, zbuf, z,
+                                                         c->ps, c->ts, nullptr, nullptr), note_launch());
+        else
+            (k_ilu_bwd<4><<<nblk(cnt, 128), 128, 0, s>>>(c->lvl_b, st, cnt, c->rp, c->ci, c->diag, c->LU, ybuf, zbuf, z,
+                                                         c->ps, c->ts, nullptr, nullptr), note_launch());
+    }
+}
+
 }  // namespace cptr
