@@ -161,7 +161,7 @@ def ours(args, rank, world, local_rank):
     clocks.start()
     launches0 = cp.cptr_launch_count()
     events = []
-    prof_sum = {k: [0.0, 0] for k in cp.PROFILE_FAMILIES}
+    prof_sum = {}
     infos = []
     for _ in range(args.steps):
         flush.zero_()
@@ -171,8 +171,9 @@ def ours(args, rank, world, local_rank):
         e1.record(stream)
         events.append((e0, e1))
         for k, (ms, cnt) in cp.cptr_profile(S.ctx).items():
-            prof_sum[k][0] += ms
-            prof_sum[k][1] += cnt
+            acc = prof_sum.setdefault(k, [0.0, 0])
+            acc[0] += ms
+            acc[1] += cnt
     torch.cuda.synchronize(dev)
     launches = cp.cptr_launch_count() - launches0
     barrier(world)

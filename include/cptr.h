@@ -73,6 +73,8 @@ typedef struct {
     int32_t seed;        /* PMIS weights: SplitMix64 stream seed + level */
     int32_t precision;   /* CPTR_PREC_* */
     int32_t check_every; /* host reads the convergence flag every k Arnoldi steps (default 1) */
+    int32_t use_graph;   /* 1: replay each Arnoldi step as one captured CUDA graph (default 1) */
+    int32_t reserved;
     void *stream;        /* cudaStream_t for all work; NULL = the legacy default stream */
 } cptr_options;
 
@@ -188,6 +190,13 @@ cptr_status cptr_apply_ilu_static(cptr_ctx *ctx, const double *r, double *z);
 /* Number of ILU level sets of the forward and backward sweeps (host ints). */
 cptr_status cptr_ilu_levels(cptr_ctx *ctx, int32_t *n_forward, int32_t *n_backward);
 
+/* Failure injection for tests (no GPU fault involved): while on != 0, the first row of every
+ * forward ILU(0) sweep also waits for a value that no thread ever writes.  The bounded wait gives
+ * up after about 0.5 s, the sweep completes, and the call (cptr_solve, cptr_apply_ilu,
+ * cptr_apply_precond) returns CPTR_ETIMEOUT.  The context stays usable; switch it off to solve
+ * normally again.  The paper has no counterpart; it exercises the library's own wait limits. */
+cptr_status cptr_inject_wait_timeout(cptr_ctx *ctx, int32_t on);
+
 /* Number of kernels this library has launched in this process (all contexts, since load). */
 int64_t cptr_launch_count(void);
 
@@ -198,7 +207,9 @@ int64_t cptr_launch_count(void);
 cptr_status cptr_set_profiling(cptr_ctx *ctx, uint32_t mask);
 
 /* Event time (ms) and number of timed regions per family during the last cptr_solve (host
- * arrays of 8 entries; either may be NULL). */
+ * arrays of 8 entries; either may be NULL).  Entries 5, 6, 7 hold the host-clock time of the
+ * last cptr_setup's phases (inputs + decoupling + extraction, both AMG hierarchies, ILU(0)),
+ * with count 1. */
 cptr_status cptr_profile(cptr_ctx *ctx, double *ms, int64_t *count);
 
 #ifdef __cplusplus

@@ -31,7 +31,8 @@ class cptr_options(ctypes.Structure):
                 ("smoother", ctypes.c_int32), ("omega", ctypes.c_double), ("theta", ctypes.c_double),
                 ("n_coarse", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_it", ctypes.c_int32), ("dense_max", ctypes.c_int32), ("seed", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("check_every", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("precision", ctypes.c_int32), ("check_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class cptr_stats(ctypes.Structure):
@@ -69,10 +70,12 @@ _SIGS = {
     "cptr_hierarchy_level": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
     "cptr_ilu_levels": (_I, [_P, _P, _P]),
     "cptr_launch_count": (ctypes.c_int64, []),
+    "cptr_inject_wait_timeout": (_I, [_P, _I]),
     "cptr_set_profiling": (_I, [_P, ctypes.c_uint32]),
     "cptr_profile": (_I, [_P, _P, _P]),
 }
-PROFILE_FAMILIES = ("spmv", "stage1", "stage1_resid", "ilu", "arnoldi")
+PROFILE_FAMILIES = ("spmv", "stage1", "stage1_resid", "ilu", "arnoldi", "_5", "_6", "_7")
+SETUP_PHASES = {5: "setup_inputs", 6: "setup_amg", 7: "setup_ilu"}
 
 
 def load():
@@ -231,6 +234,10 @@ def cptr_launch_count() -> int:
     return int(load().cptr_launch_count())
 
 
+def cptr_inject_wait_timeout(ctx, on: bool):
+    return _check(ctx, load().cptr_inject_wait_timeout(ctx, int(bool(on))))
+
+
 def cptr_set_profiling(ctx, mask: int):
     return _check(ctx, load().cptr_set_profiling(ctx, mask))
 
@@ -239,7 +246,10 @@ def cptr_profile(ctx):
     ms = np.zeros(8)
     cnt = np.zeros(8, np.int64)
     _check(ctx, load().cptr_profile(ctx, ms.ctypes.data, cnt.ctypes.data))
-    return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(PROFILE_FAMILIES)}
+    out = {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(PROFILE_FAMILIES) if not name.startswith("_")}
+    for i, name in SETUP_PHASES.items():
+        out[name] = (float(ms[i]), int(cnt[i]))
+    return out
 
 
 # ------------------------------------------------------------------------------------------------

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <stddef.h>
+
 #include <chrono>
 #include <new>
 
@@ -21,14 +23,21 @@ bool host_or_device_copy(Ctx *c, void *dst, const void *src, size_t bytes, int o
 
 void release_setup(Ctx *c) {
     dfree(c->rp); dfree(c->ci); dfree(c->diag); dfree(c->A); dfree(c->W);
+    dfree(c->sell_off); dfree(c->sell_col); dfree(c->sell_val);
+    c->sell_off = nullptr; c->sell_col = nullptr; c->sell_val = nullptr;
     dfree(c->App); dfree(c->ApT); dfree(c->ATp); dfree(c->St);
     c->rp = c->ci = c->diag = nullptr;
     c->A = c->W = c->App = c->ApT = c->ATp = c->St = nullptr;
     amg_free(c->hp);
     amg_free(c->hT);
     ilu_free(c);
-    double **vecs[] = {&c->bp, &c->bT, &c->xp, &c->dp, &c->dT, &c->t1, &c->b1, &c->V, &c->Z, &c->w, &c->bw, &c->xw};
+    double **vecs[] = {&c->bp, &c->bT, &c->xp, &c->dp, &c->dT, &c->t1, &c->b1, &c->V, &c->Z, &c->w, &c->bw, &c->xw,
+                       &c->vcur, &c->zcur};
     for (double **p : vecs) { dfree(*p); *p = nullptr; }
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
     c->ready = false;
 }
 
@@ -122,15 +131,28 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     launch_extract(c, ts, ps, c->ATp);
     if (!(st && c->o.schur == CPTR_SCHUR_GIVEN)) launch_extract(c, ts, ts, c->St);
     CPTR_CUDA_TRY(c, cudaGetLastError());
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    auto ms_since = [](std::chrono::steady_clock::time_point a) {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+    };
+    c->prof.setup_ms[0] = ms_since(t0);
+    auto t1 = std::chrono::steady_clock::now();
     int s1 = c->o.stage1;
     if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_setup(c, c->hp, c->rp, c->ci, c->App, n));
     if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) CPTR_TRY(amg_setup(c, c->hT, c->rp, c->ci, c->St, n));
+    c->prof.setup_ms[1] = ms_since(t1);
+    auto t2 = std::chrono::steady_clock::now();
     if (c->o.stage2 == CPTR_STAGE2_ILU0) CPTR_TRY(ilu_setup(c));
+    // A' for the solve in the SELL-32 layout; the BSR copy is not needed after set-up
+    CPTR_TRY(sell_build(c));
+    dfree(c->A);
+    c->A = nullptr;
+    c->prof.setup_ms[2] = ms_since(t2);
     // work vectors
     const size_t nb = (size_t)n * b;
     const int m = c->o.restart;
     for (double **p : {&c->bp, &c->bT, &c->xp, &c->dp, &c->dT, &c->t1}) CPTR_TRY(dalloc_t(c, p, (size_t)n));
-    for (double **p : {&c->b1, &c->w, &c->bw, &c->xw}) CPTR_TRY(dalloc_t(c, p, nb));
+    for (double **p : {&c->b1, &c->w, &c->bw, &c->xw, &c->vcur, &c->zcur}) CPTR_TRY(dalloc_t(c, p, nb));
     CPTR_TRY(dalloc_t(c, &c->V, nb * (m + 1)));
     CPTR_TRY(dalloc_t(c, &c->Z, nb * m));
     CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -164,6 +186,20 @@ cptr_status sync(Ctx *c) {
     return CPTR_OK;
 }
 
+// component calls that run the ILU sweeps: clear the wait flag before, check it after
+cptr_status clear_wait_flag(Ctx *c) {
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(reinterpret_cast<char *>(c->ks) + offsetof(KState, wait_err), 0, sizeof(int32_t),
+                                     c->stream));
+    return CPTR_OK;
+}
+cptr_status check_wait_flag(Ctx *c) {
+    int32_t w = 0;
+    CPTR_CUDA_TRY(c, cudaMemcpy(&w, reinterpret_cast<char *>(c->ks) + offsetof(KState, wait_err), sizeof(int32_t),
+                                cudaMemcpyDeviceToHost));
+    if (w) return c->fail(CPTR_ETIMEOUT, "ILU(0) sweep: a bounded wait gave up");
+    return CPTR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -185,6 +221,7 @@ cptr_status cptr_default_options(cptr_options *o) {
     o->seed = 0;
     o->precision = CPTR_PREC_FP64;
     o->check_every = 1;
+    o->use_graph = 1;
     o->stream = nullptr;
     return CPTR_OK;
 }
@@ -206,6 +243,7 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
     c->stream = (cudaStream_t)o.stream;
     cptr_status s = CPTR_OK;
     if ((s = dalloc_t(c, &c->ks, 1)) != CPTR_OK || (s = dalloc_t(c, &c->flag, 4)) != CPTR_OK ||
+        (s = dalloc_t(c, &c->never, 1)) != CPTR_OK ||
         (s = dalloc_t(c, &c->partial, (size_t)kRedBlocks * (kMaxRestart + 2))) != CPTR_OK) {
         cptr_destroy(ctx);
         return s;
@@ -224,9 +262,10 @@ void cptr_destroy(cptr_ctx *ctx) {
     Ctx *c = &ctx->c;
     cudaStreamSynchronize(c->stream);
     release_setup(c);
-    dfree(c->ks); dfree(c->flag); dfree(c->partial); dfree(c->scan_tmp);
+    dfree(c->ks); dfree(c->flag); dfree(c->partial); dfree(c->scan_tmp); dfree(c->never);
     if (c->ks_host) cudaFreeHost(c->ks_host);
     for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete ctx;
 }
 
@@ -318,16 +357,20 @@ cptr_status cptr_apply_ilu(cptr_ctx *ctx, const double *r, double *z) {
     return guarded(ctx, [&](Ctx *c) {
         CPTR_TRY(need_ready(c));
         if (c->o.stage2 != CPTR_STAGE2_ILU0) return c->fail(CPTR_ESTATE, "ILU(0) was not set up");
+        CPTR_TRY(clear_wait_flag(c));
         ilu_apply(c, r, z, nullptr, nullptr);
-        return sync(c);
+        CPTR_TRY(sync(c));
+        return check_wait_flag(c);
     });
 }
 
 cptr_status cptr_apply_precond(cptr_ctx *ctx, const double *v, double *z) {
     return guarded(ctx, [&](Ctx *c) {
         CPTR_TRY(need_ready(c));
+        CPTR_TRY(clear_wait_flag(c));
         apply_precond(c, v, z);
-        return sync(c);
+        CPTR_TRY(sync(c));
+        return check_wait_flag(c);
     });
 }
 
@@ -384,6 +427,13 @@ cptr_status cptr_hierarchy_level(cptr_ctx *ctx, int32_t which, int32_t l, int32_
 
 int64_t cptr_launch_count(void) { return launch_count(); }
 
+cptr_status cptr_inject_wait_timeout(cptr_ctx *ctx, int32_t on) {
+    return guarded(ctx, [&](Ctx *c) {
+        c->inject_wait = on ? 1 : 0;
+        return CPTR_OK;
+    });
+}
+
 cptr_status cptr_set_profiling(cptr_ctx *ctx, uint32_t mask) {
     return guarded(ctx, [&](Ctx *c) {
         c->prof.mask = mask;
@@ -394,8 +444,8 @@ cptr_status cptr_set_profiling(cptr_ctx *ctx, uint32_t mask) {
 cptr_status cptr_profile(cptr_ctx *ctx, double *ms, int64_t *count) {
     return guarded(ctx, [&](Ctx *c) {
         for (int f = 0; f < PF_N; ++f) {
-            if (ms) ms[f] = c->prof.ms[f];
-            if (count) count[f] = c->prof.cnt[f];
+            if (ms) ms[f] = f >= 5 ? c->prof.setup_ms[f - 5] : c->prof.ms[f];
+            if (count) count[f] = f >= 5 ? 1 : c->prof.cnt[f];
         }
         return CPTR_OK;
     });

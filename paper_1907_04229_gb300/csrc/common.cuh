@@ -63,7 +63,8 @@ struct Hier {
 
 // Arnoldi/Givens state kept on the device (one per context)
 struct KState {
-    int32_t k, done, breakdown, pad;  // columns completed in this cycle, flags
+    int32_t k, done, breakdown, wait_err;  // columns completed in this cycle, flags; a bounded
+                                           // device-side wait gave up (ILU sweeps)
     uint32_t ticket;                  // last-block ticket of the reductions
     int32_t pad2;
     double bnorm, beta, tol_abs, hnorm, est, true_res;
@@ -77,20 +78,30 @@ struct Ctx;
 
 // ---- launch counting and event timing of kernel families -----------------------------------------
 void note_launch();          // every kernel launch of the library calls this once
+void note_launches(int64_t n);  // a graph replay of n kernel nodes
 int64_t launch_count();
+void begin_capture_count();  // launches noted on this thread while capturing are not counted...
+int64_t end_capture_count(); // ...but returned here (the graph's kernel node count)
 enum { PF_SPMV = 0, PF_STAGE1 = 1, PF_RESID = 2, PF_ILU = 3, PF_ARNOLDI = 4, PF_N = 8 };
 struct Prof {
     uint32_t mask = 0;
     std::vector<cudaEvent_t> ev;   // pairs (begin, end)
     std::vector<int> fam;
-    size_t used = 0;
+    size_t used = 0;               // slots recorded by direct launches since the last collect
+    bool capturing = false;
+    std::vector<size_t> gslots;    // slots recorded inside the captured iteration graph
     double ms[PF_N] = {0};
     int64_t cnt[PF_N] = {0};
+    double setup_ms[3] = {0};      // set-up phases: inputs+decoupling, AMG, ILU
 };
 int prof_begin(const Ctx *c, int fam);
 void prof_end(const Ctx *c, int slot);
 void prof_reset(Ctx *c);
 cptr_status prof_collect(Ctx *c);
+cptr_status prof_collect_graph(Ctx *c);
+void prof_begin_capture(Ctx *c);
+void prof_end_capture(Ctx *c);
+cptr_status build_iteration_graph(Ctx *c);
 
 // ---- memory helpers ----------------------------------------------------------------------------
 cptr_status dalloc(Ctx *c, void **p, size_t bytes);
@@ -107,6 +118,8 @@ void launch_decouple(const Ctx *c, const double *Araw, const double *W, double *
 void launch_weight_vec(const Ctx *c, const double *W, const double *rhs, double *out);
 void launch_extract(const Ctx *c, int u, int w, double *out);
 void launch_check_finite(const Ctx *c, const double *v, int64_t n, int32_t *flag);
+cptr_status sell_build(Ctx *c);
+void launch_bsr_to_sell(const Ctx *c);
 void launch_bsr_spmv(const Ctx *c, const double *x, double *y);
 void launch_bsr_resid(const Ctx *c, const double *x, const double *v, double *y);
 void launch_bsr_resid_pt(const Ctx *c, const double *dp, const double *dT, const double *v, double *b1);
@@ -141,7 +154,12 @@ struct Ctx {
     // pattern (device) and its host copy
     int32_t *rp = nullptr, *ci = nullptr, *diag = nullptr;
     std::vector<int32_t> h_rp, h_ci, h_diag;
-    double *A = nullptr;     // decoupled A' (BSR, row-major blocks)
+    double *A = nullptr;     // decoupled A' (BSR, row-major blocks; set-up only)
+    int32_t sell_nch = 0;    // A' for the solve: SELL-32 block layout (see sparse.cu)
+    int64_t *sell_off = nullptr;
+    int32_t *sell_col = nullptr;
+    double *sell_val = nullptr;
+    int64_t sell_bytes = 0;
     double *W = nullptr;     // per-cell weights (n * b * b)
     double *App = nullptr, *ApT = nullptr, *ATp = nullptr, *St = nullptr;  // cell-pattern fields
     Hier hp, hT;
@@ -151,11 +169,28 @@ struct Ctx {
     int32_t *lvl_f = nullptr, *lvl_b = nullptr;       // rows sorted by level (device)
     std::vector<int32_t> h_lptr_f, h_lptr_b;           // level pointers (host)
     double *ybuf = nullptr, *zbuf = nullptr;           // ILU intermediate vectors
+    // ILU(0) solves, one launch per sweep: rows in level order, factors in SELL-32 chunks
+    int32_t *sf_pos_f = nullptr, *sf_pos_b = nullptr;  // level-ordered position -> row
+    int32_t *sf_bmap = nullptr;                        // backward position -> forward position
+    int64_t *sf_off_f = nullptr, *sf_off_b = nullptr;  // chunk slot offsets
+    int32_t *sf_col_f = nullptr, *sf_col_b = nullptr;  // dependency positions (-1 = padding)
+    double *sf_val_f = nullptr, *sf_val_b = nullptr;   // L and U blocks
+    double *sf_dinv = nullptr;                         // inverted pivot blocks, backward order
+    unsigned *sf_ticket = nullptr;                     // block tickets of the two sweeps
+    double *sf_y = nullptr, *sf_z = nullptr;           // level-ordered y and z (sentinel-filled)
+    int32_t inject_wait = 0;                           // failure injection (see cptr_inject_wait_timeout)
+    double *never = nullptr;                           // a word no thread writes
     // preconditioner work
     double *bp = nullptr, *bT = nullptr, *xp = nullptr, *dp = nullptr, *dT = nullptr, *t1 = nullptr;
     double *b1 = nullptr;
     // Krylov
     double *V = nullptr, *Z = nullptr, *w = nullptr, *bw = nullptr, *xw = nullptr, *partial = nullptr;
+    double *vcur = nullptr, *zcur = nullptr;           // fixed in/out vectors of the captured step
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_launches = 0;
+    uint32_t graph_mask = 0;
+    int32_t graph_inject = 0;
     KState *ks = nullptr;    // device
     KState *ks_host = nullptr;  // pinned mirror
     int32_t *flag = nullptr;    // device scratch flag

@@ -7,6 +7,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -177,6 +178,232 @@ __global__ void k_ilu_bwd(const int32_t *__restrict__ rows, int32_t start, int32
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Triangular solves in one launch per sweep.  Positions t = 0..n-1 enumerate the rows level by
+// level; a ticket counter hands out chunks of kSfThreads consecutive positions to a persistent
+// grid, and a block finishes its chunk before it takes another.  Each thread solves one row.  The
+// values of an unsolved row hold a sentinel NaN payload; the producer overwrites them (the last
+// one with release semantics) and a dependent row polls that last value with acquire loads, so the
+// value doubles as its ready flag.  A row depends only on earlier positions, which belong to
+// chunks held by blocks that already run: no deadlock.  Every wait is bounded by kWaitNs of GPU
+// time; a wait that gives up sets ks->wait_err and the call reports CPTR_ETIMEOUT.
+constexpr unsigned long long kSentinel = 0x7FF4C0DEDEADBEEFULL;  // never produced by arithmetic
+constexpr unsigned long long kWaitNs = 500ULL * 1000ULL * 1000ULL;
+constexpr int kSfThreads = 128;
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// a load the compiler may neither hoist out of a loop nor merge with another load
+// (relaxed, GPU scope: it observes stores of other SMs through L2)
+__device__ __forceinline__ double load_relaxed(const double *p) {
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void store_relaxed(double *p, double v) {
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+// the last value of a row is stored with release semantics and polled with acquire semantics:
+// seeing it implies seeing the row's earlier values
+__device__ __forceinline__ void store_release(double *p, double v) {
+    asm volatile("st.release.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ double load_acquire(const double *p) {
+    double v;
+    asm volatile("ld.acquire.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// wait (bounded) until *p no longer holds the sentinel; returns its value
+__device__ __forceinline__ double wait_value(const double *p, KState *ks) {
+    double v = load_acquire(p);
+    if (__double_as_longlong(v) != (long long)kSentinel) return v;
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+        __nanosleep(40);
+        v = load_acquire(p);
+        if (__double_as_longlong(v) != (long long)kSentinel) return v;
+        if (gtimer() - t0 > kWaitNs) {
+            atomicExch(&ks->wait_err, 1);
+            return 0.0;
+        }
+    }
+}
+
+__device__ __forceinline__ bool is_sentinel(double v) {
+    return __double_as_longlong(v) == (long long)kSentinel;
+}
+
+// Rows depended on are read in groups of up to kDepGroup: all their values are loaded at once
+// (relaxed, independent loads), then only the entries still holding the sentinel are polled
+// again, with a short sleep between rounds, until the bounded wait gives up.  Every value is
+// checked on its own, so producers publish with plain relaxed stores and no fence.
+constexpr int kDepGroup = 4;
+
+template <int B>
+__device__ __forceinline__ void load_group(const double *base, const int32_t *c, double (*v)[B], KState *ks) {
+    bool pending = false;
+#pragma unroll
+    for (int g = 0; g < kDepGroup; ++g)
+        if (c[g] >= 0)
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                v[g][q] = load_relaxed(base + (int64_t)c[g] * B + q);
+                pending |= is_sentinel(v[g][q]);
+            }
+    if (!pending) return;
+    const unsigned long long t0 = gtimer();
+    while (pending) {
+        __nanosleep(20);
+        pending = false;
+#pragma unroll
+        for (int g = 0; g < kDepGroup; ++g)
+            if (c[g] >= 0)
+#pragma unroll
+                for (int q = 0; q < B; ++q)
+                    if (is_sentinel(v[g][q])) {
+                        v[g][q] = load_relaxed(base + (int64_t)c[g] * B + q);
+                        pending |= is_sentinel(v[g][q]);
+                    }
+        if (pending && gtimer() - t0 > kWaitNs) {
+            atomicExch(&ks->wait_err, 1);
+#pragma unroll
+            for (int g = 0; g < kDepGroup; ++g)
+#pragma unroll
+                for (int q = 0; q < B; ++q)
+                    if (is_sentinel(v[g][q])) v[g][q] = 0.0;
+            return;
+        }
+    }
+}
+
+// s -= sum over the dependency slots [o0, o1) of block(slot) * value(dep(slot))
+template <int B>
+__device__ __forceinline__ void subtract_deps(double *s, int64_t o0, int64_t o1, int lane,
+                                              const int32_t *__restrict__ col, const double *__restrict__ val,
+                                              const double *vec, KState *ks) {
+    for (int64_t sl0 = o0; sl0 < o1; sl0 += kDepGroup) {
+        int32_t c[kDepGroup];
+#pragma unroll
+        for (int g = 0; g < kDepGroup; ++g) c[g] = (sl0 + g < o1) ? __ldg(col + (sl0 + g) * 32 + lane) : -1;
+        double a[kDepGroup][B * B];
+#pragma unroll
+        for (int g = 0; g < kDepGroup; ++g)
+            if (c[g] >= 0)
+#pragma unroll
+                for (int e = 0; e < B * B; ++e) a[g][e] = __ldg(val + ((sl0 + g) * B * B + e) * 32 + lane);
+        double v[kDepGroup][B];
+        load_group<B>(vec, c, v, ks);
+#pragma unroll
+        for (int g = 0; g < kDepGroup; ++g)
+            if (c[g] >= 0)
+#pragma unroll
+                for (int rr = 0; rr < B; ++rr)
+#pragma unroll
+                    for (int q = 0; q < B; ++q) s[rr] = fma(-a[g][rr * B + q], v[g][q], s[rr]);
+    }
+}
+
+__global__ void k_sf_fill(int64_t nvals, double *y, double *z, unsigned *ticket) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const double sent = __longlong_as_double((long long)kSentinel);
+    for (; i < nvals; i += stride) {
+        y[i] = sent;
+        z[i] = sent;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 2) ticket[threadIdx.x] = 0u;
+}
+
+// y(t) = r(pos[t]) - sum_s L(t, s) y(dep(t, s)).  A persistent grid: each block takes chunks of
+// kSfThreads positions in ticket order until none is left.
+template <int B>
+__global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_sf(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
+                                                          const int64_t *__restrict__ off, const int32_t *__restrict__ col,
+                                                          const double *__restrict__ val, const double *__restrict__ r,
+                                                          double *y, KState *ks, const double *never) {
+    __shared__ unsigned blk;
+    const unsigned nchunks = (unsigned)((n + kSfThreads - 1) / kSfThreads);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) blk = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const unsigned b = blk;
+        if (b >= nchunks) return;
+        const int32_t t = (int32_t)(b * kSfThreads + threadIdx.x);
+        if (t >= n) continue;
+        if (never && t == 0) (void)wait_value(never, ks);  // failure injection: a value nobody writes
+        const int32_t ch = t >> 5, lane = t & 31;
+        const int32_t row = __ldg(pos + t);
+        double s[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) s[q] = __ldg(r + (int64_t)row * B + q);
+        subtract_deps<B>(s, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, y, ks);
+#pragma unroll
+        for (int q = 0; q < B; ++q) store_relaxed(y + (int64_t)t * B + q, s[q]);
+    }
+}
+
+// z(t) = D(t)^{-1} (y(bmap[t]) - sum_s U(t, s) z(dep(t, s))); out(pos[t]) = z(t) + x1(pos[t])
+template <int B>
+__global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_sf(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
+                                                          const int32_t *__restrict__ bmap,
+                                                          const int64_t *__restrict__ off, const int32_t *__restrict__ col,
+                                                          const double *__restrict__ val, const double *__restrict__ dinv,
+                                                          const double *__restrict__ y, double *z, double *__restrict__ out,
+                                                          int ps, int ts, const double *__restrict__ dp,
+                                                          const double *__restrict__ dT, KState *ks) {
+    __shared__ unsigned blk;
+    const unsigned nchunks = (unsigned)((n + kSfThreads - 1) / kSfThreads);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) blk = atomicAdd(ticket + 1, 1u);
+        __syncthreads();
+        const unsigned b = blk;
+        if (b >= nchunks) return;
+        const int32_t t = (int32_t)(b * kSfThreads + threadIdx.x);
+        if (t >= n) continue;
+        const int32_t ch = t >> 5, lane = t & 31;
+        const int32_t row = __ldg(pos + t);
+        const int32_t tf = __ldg(bmap + t);
+        double s[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) s[q] = __ldcg(y + (int64_t)tf * B + q);
+        subtract_deps<B>(s, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, z, ks);
+        double zi[B];
+#pragma unroll
+        for (int rr = 0; rr < B; ++rr) {
+            double a = 0.0;
+#pragma unroll
+            for (int q = 0; q < B; ++q) a = fma(__ldg(dinv + ((int64_t)ch * B * B + rr * B + q) * 32 + lane), s[q], a);
+            zi[rr] = a;
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q) store_relaxed(z + (int64_t)t * B + q, zi[q]);
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            double add = 0.0;
+            if (dp && q == ps) add = dp[row];
+            if (dT && q == ts) add = dT[row];
+            out[(int64_t)row * B + q] = zi[q] + add;
+        }
+    }
+}
+
+// pack factor blocks into the SELL-32 layout: slot u (slot * 32 + lane) takes block kidx[u]
+__global__ void k_sf_pack(int64_t nslots32, int BB, const int32_t *kidx, const double *LU, double *val) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nslots32) return;
+    int64_t sl = u >> 5;
+    int lane = (int)(u & 31);
+    int32_t k = kidx[u];
+    for (int e = 0; e < BB; ++e) val[(sl * BB + e) * 32 + lane] = k >= 0 ? LU[(int64_t)k * BB + e] : 0.0;
+}
+
 static void level_sets(int32_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci, bool forward,
                        std::vector<int32_t> &lptr, std::vector<int32_t> &rows) {
     std::vector<int32_t> lev(n, 0);
@@ -197,6 +424,78 @@ static void level_sets(int32_t n, const std::vector<int32_t> &rp, const std::vec
     std::vector<int32_t> cur(lptr.begin(), lptr.end() - 1);
     rows.assign(n, 0);
     for (int32_t i = 0; i < n; ++i) rows[cur[lev[i]]++] = i;  // ascending within a level
+}
+
+// Level-ordered SELL-32 copies of the factors for the one-launch sweeps (see k_ilu_fwd_sf).
+static cptr_status sf_build(Ctx *c, const std::vector<int32_t> &pos_f, const std::vector<int32_t> &pos_b) {
+    const int32_t n = c->n, BB = c->b * c->b, nch = (n + 31) / 32;
+    const std::vector<int32_t> &rp = c->h_rp, &ci = c->h_ci, &dg = c->h_diag;
+    std::vector<int32_t> inv_f(n), inv_b(n), bmap(n);
+    for (int32_t t = 0; t < n; ++t) { inv_f[pos_f[t]] = t; inv_b[pos_b[t]] = t; }
+    for (int32_t t = 0; t < n; ++t) bmap[t] = inv_f[pos_b[t]];
+    auto build = [&](const std::vector<int32_t> &pos, const std::vector<int32_t> &inv, bool lower,
+                     std::vector<int64_t> &off, std::vector<int32_t> &col, std::vector<int32_t> &kidx) {
+        off.assign(nch + 1, 0);
+        for (int32_t ch = 0; ch < nch; ++ch) {
+            int32_t w = 0;
+            for (int32_t t = ch * 32; t < std::min(n, ch * 32 + 32); ++t) {
+                int32_t row = pos[t];
+                w = std::max(w, lower ? dg[row] - rp[row] : rp[row + 1] - dg[row] - 1);
+            }
+            off[ch + 1] = off[ch] + w;
+        }
+        col.assign((size_t)off[nch] * 32, -1);
+        kidx.assign((size_t)off[nch] * 32, -1);
+        for (int32_t t = 0; t < n; ++t) {
+            int32_t row = pos[t], ch = t >> 5, lane = t & 31;
+            int32_t k0 = lower ? rp[row] : dg[row] + 1, k1 = lower ? dg[row] : rp[row + 1];
+            for (int32_t k = k0; k < k1; ++k) {
+                int64_t u = (off[ch] + (k - k0)) * 32 + lane;
+                col[u] = inv[ci[k]];
+                kidx[u] = k;
+            }
+        }
+    };
+    std::vector<int64_t> off_f, off_b;
+    std::vector<int32_t> col_f, col_b, kidx_f, kidx_b, kidx_d((size_t)nch * 32, -1);
+    build(pos_f, inv_f, true, off_f, col_f, kidx_f);
+    build(pos_b, inv_b, false, off_b, col_b, kidx_b);
+    for (int32_t t = 0; t < n; ++t) kidx_d[t] = dg[pos_b[t]];
+    auto up = [&](auto **dst, const auto &v) -> cptr_status {
+        using T = typename std::remove_reference<decltype(v)>::type::value_type;
+        CPTR_TRY(dalloc_t(c, reinterpret_cast<T **>(dst), v.size() > 0 ? v.size() : 1));
+        if (!v.empty())
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, c->stream));
+        return CPTR_OK;
+    };
+    CPTR_TRY(up(&c->sf_pos_f, pos_f));
+    CPTR_TRY(up(&c->sf_pos_b, pos_b));
+    CPTR_TRY(up(&c->sf_bmap, bmap));
+    CPTR_TRY(up(&c->sf_off_f, off_f));
+    CPTR_TRY(up(&c->sf_off_b, off_b));
+    CPTR_TRY(up(&c->sf_col_f, col_f));
+    CPTR_TRY(up(&c->sf_col_b, col_b));
+    int32_t *dk = nullptr;
+    auto pack = [&](const std::vector<int32_t> &kidx, double **dst) -> cptr_status {
+        int64_t ns = (int64_t)kidx.size();
+        CPTR_TRY(dalloc_t(c, dst, (size_t)(ns > 0 ? ns : 1) * BB));
+        if (ns == 0) return CPTR_OK;
+        CPTR_TRY(dalloc_t(c, &dk, (size_t)ns));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(dk, kidx.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, c->stream));
+        (k_sf_pack<<<nblk(ns, 256), 256, 0, c->stream>>>(ns, BB, dk, c->LU, *dst), note_launch());
+        CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        dfree(dk);
+        dk = nullptr;
+        return CPTR_OK;
+    };
+    CPTR_TRY(pack(kidx_f, &c->sf_val_f));
+    CPTR_TRY(pack(kidx_b, &c->sf_val_b));
+    CPTR_TRY(pack(kidx_d, &c->sf_dinv));
+    CPTR_TRY(dalloc_t(c, &c->sf_ticket, 4));
+    CPTR_TRY(dalloc_t(c, &c->sf_y, (size_t)n * c->b));
+    CPTR_TRY(dalloc_t(c, &c->sf_z, (size_t)n * c->b));
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    return CPTR_OK;
 }
 
 cptr_status ilu_setup(Ctx *c) {
@@ -228,31 +527,40 @@ cptr_status ilu_setup(Ctx *c) {
     CPTR_CUDA_TRY(c, cudaMemcpyAsync(&sing, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
     CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (sing) return c->fail(CPTR_ESINGULAR, "ILU(0): singular pivot block");
-    return CPTR_OK;
+    return sf_build(c, rows_f, rows_b);
 }
 
 void ilu_free(Ctx *c) {
     dfree(c->lvl_f); dfree(c->lvl_b); dfree(c->LU); dfree(c->ybuf); dfree(c->zbuf);
     c->lvl_f = c->lvl_b = nullptr;
     c->LU = c->ybuf = c->zbuf = nullptr;
+    void **sf[] = {(void **)&c->sf_pos_f, (void **)&c->sf_pos_b, (void **)&c->sf_bmap, (void **)&c->sf_off_f,
+                   (void **)&c->sf_off_b, (void **)&c->sf_col_f, (void **)&c->sf_col_b, (void **)&c->sf_val_f,
+                   (void **)&c->sf_val_b, (void **)&c->sf_dinv, (void **)&c->sf_ticket, (void **)&c->sf_y,
+                   (void **)&c->sf_z};
+    for (void **p : sf) { dfree(*p); *p = nullptr; }
 }
 
-// z = (LU)^{-1} r + x1, where x1 carries dp in slot ps and dT in slot ts (either may be null)
+// z = (LU)^{-1} r + x1, where x1 carries dp in slot ps and dT in slot ts (either may be null):
+// sentinel fill, forward sweep, backward sweep (three launches)
 void ilu_apply(const Ctx *c, const double *r, double *z, const double *dp, const double *dT) {
     cudaStream_t s = c->stream;
-    for (int32_t l = 0; l < c->nlev_f; ++l) {
-        int32_t st = c->h_lptr_f[l], cnt = c->h_lptr_f[l + 1] - st;
-        if (c->b == 3) (k_ilu_fwd<3><<<nblk(cnt, 128), 128, 0, s>>>(c->lvl_f, st, cnt, c->rp, c->ci, c->diag, c->LU, r, c->ybuf), note_launch());
-        else (k_ilu_fwd<4><<<nblk(cnt, 128), 128, 0, s>>>(c->lvl_f, st, cnt, c->rp, c->ci, c->diag, c->LU, r, c->ybuf), note_launch());
-    }
-    for (int32_t l = 0; l < c->nlev_b; ++l) {
-        int32_t st = c->h_lptr_b[l], cnt = c->h_lptr_b[l + 1] - st;
-        if (c->b == 3)
-            (k_ilu_bwd<3><<<nblk(cnt, 128), 128, 0, s>>>(c->lvl_b, st, cnt, c->rp, c->ci, c->diag, c->LU, c->ybuf,
-                                                         c->zbuf, z, c->ps, c->ts, dp, dT), note_launch());
-        else
-            (k_ilu_bwd<4><<<nblk(cnt, 128), 128, 0, s>>>(c->lvl_b, st, cnt, c->rp, c->ci, c->diag, c->LU, c->ybuf,
-                                                         c->zbuf, z, c->ps, c->ts, dp, dT), note_launch());
+    const int32_t n = c->n;
+    const unsigned grid = std::min<unsigned>(nblk(n, kSfThreads), 4 * 152);
+    (k_sf_fill<<<4 * 152, 256, 0, s>>>((int64_t)n * c->b, c->sf_y, c->sf_z, c->sf_ticket), note_launch());
+    if (c->inject_wait) (k_sf_fill<<<1, 32, 0, s>>>(1, c->never, c->never, c->sf_ticket + 2), note_launch());
+    if (c->b == 3) {
+        (k_ilu_fwd_sf<3><<<grid, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_f, c->sf_off_f, c->sf_col_f, c->sf_val_f,
+                                                      r, c->sf_y, c->ks, c->inject_wait ? c->never : nullptr), note_launch());
+        (k_ilu_bwd_sf<3><<<grid, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_b, c->sf_bmap, c->sf_off_b, c->sf_col_b,
+                                                      c->sf_val_b, c->sf_dinv, c->sf_y, c->sf_z, z, c->ps, c->ts, dp,
+                                                      dT, c->ks), note_launch());
+    } else {
+        (k_ilu_fwd_sf<4><<<grid, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_f, c->sf_off_f, c->sf_col_f, c->sf_val_f,
+                                                      r, c->sf_y, c->ks, c->inject_wait ? c->never : nullptr), note_launch());
+        (k_ilu_bwd_sf<4><<<grid, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_b, c->sf_bmap, c->sf_off_b, c->sf_col_b,
+                                                      c->sf_val_b, c->sf_dinv, c->sf_y, c->sf_z, z, c->ps, c->ts, dp,
+                                                      dT, c->ks), note_launch());
     }
 }
 

@@ -29,11 +29,15 @@ template <int PASS>
 __global__ void __launch_bounds__(kRedThreads) k_cgs(int64_t nb, const double *__restrict__ V, int nc,
                                                     double *__restrict__ w, const double *__restrict__ coef,
                                                     double *__restrict__ partial, KState *ks, int fin, int j, int m,
-                                                    double rtol) {
+                                                    double rtol, int jdev) {
     __shared__ double scoef[kMaxC];
     __shared__ double red[kRedThreads / 32][kMaxC];
     __shared__ bool last;
     if (ks->done && fin <= FIN_GIVENS) return;   // nothing after convergence in this cycle
+    if (jdev) {                                   // column index from the device state (graphs)
+        j = ks->k;
+        nc = j + 1;
+    }
     constexpr bool UPD = PASS == PASS_UPD_DOT || PASS == PASS_UPD_NORM;
     constexpr bool NORM = PASS == PASS_UPD_NORM || PASS == PASS_NORM;
     constexpr int NA = NORM ? 1 : kMaxC;
@@ -80,13 +84,16 @@ __global__ void __launch_bounds__(kRedThreads) k_cgs(int64_t nb, const double *_
     if (threadIdx.x == 0) last = atomicAdd(&ks->ticket, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last) return;
-    // last block: reduce over blocks in block order
+    // last block: one warp per column; lane l sums blocks l, l+32, ... and the lanes are combined
+    // by a fixed shuffle tree (the same order every run)
     __threadfence();
     __shared__ double res[kMaxC];
-    if (threadIdx.x < na) {
+    for (int q = wid; q < na; q += kRedThreads / 32) {
         double s = 0.0;
-        for (unsigned bb = 0; bb < gridDim.x; ++bb) s += __ldcg(partial + (int64_t)bb * kPStride + threadIdx.x);
-        res[threadIdx.x] = s;
+        for (unsigned bb = lane; bb < gridDim.x; bb += 32) s += __ldcg(partial + (int64_t)bb * kPStride + q);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) res[q] = s;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -136,15 +143,29 @@ __global__ void __launch_bounds__(kRedThreads) k_cgs(int64_t nb, const double *_
     }
 }
 
-// dst = src / scale, scale = ks->hnorm (which = 0) or ks->beta (which = 1); skipped if 0 or done
+// dst = src / scale, scale = ks->hnorm (which = 0) or ks->beta (which = 1); skipped if 0 or done.
+// jdev: dst is column ks->k of the block starting at dst (the column after the Givens update).
 __global__ void k_scale(int64_t nb, const double *__restrict__ src, double *__restrict__ dst, const KState *ks,
-                        int which, int check_done) {
+                        int which, int check_done, int jdev) {
     if (check_done && ks->done) return;
+    if (jdev) dst += (int64_t)ks->k * nb;
     double s = which == 0 ? ks->hnorm : ks->beta;
     if (!(s > 0.0)) return;
     double inv = 1.0 / s;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride) dst[i] = src[i] * inv;
+}
+
+// copy between a fixed vector and column ks->k of a column block: dir 0 vec = base[k],
+// dir 1 base[k] = vec
+__global__ void k_copy_col(int64_t nb, double *__restrict__ base, double *__restrict__ vec, const KState *ks,
+                           int dir) {
+    double *col = base + (int64_t)ks->k * nb;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride) {
+        if (dir == 0) vec[i] = col[i];
+        else col[i] = vec[i];
+    }
 }
 
 // y = H^{-1} g (upper triangular, k x k)
@@ -252,17 +273,69 @@ void apply_precond(const Ctx *c, const double *v, double *z) {
 }
 
 // ------------------------------------------------------------------------------------------------
-template <int PASS>
-static void cgs(const Ctx *c, const double *V, int nc, double *w, const double *coef, int fin, int j,
-                double rtol = 0.0) {
-    int64_t nb = (int64_t)c->n * c->b;
-    (k_cgs<PASS><<<kRedBlocks, kRedThreads, 0, c->stream>>>(nb, V, nc, w, coef, c->partial, c->ks, fin, j,
-                                                          c->o.restart, rtol), note_launch());
-}
-
 // device address of a member of the device-resident Krylov state
 static const double *ks_field(const Ctx *c, size_t off) {
     return reinterpret_cast<const double *>(reinterpret_cast<const char *>(c->ks) + off);
+}
+
+template <int PASS>
+static void cgs(const Ctx *c, const double *V, int nc, double *w, const double *coef, int fin, int j,
+                double rtol = 0.0, int jdev = 0) {
+    int64_t nb = (int64_t)c->n * c->b;
+    (k_cgs<PASS><<<kRedBlocks, kRedThreads, 0, c->stream>>>(nb, V, nc, w, coef, c->partial, c->ks, fin, j,
+                                                          c->o.restart, rtol, jdev), note_launch());
+}
+
+// One Arnoldi step with the column index taken from the device state (ks->k): the kernel
+// sequence that is captured once per set-up into a CUDA graph and replayed every iteration.
+static void arnoldi_step_device_indexed(const Ctx *c) {
+    const int64_t nb = (int64_t)c->n * c->b;
+    const unsigned vgrid = 4 * 152;
+    cudaStream_t s = c->stream;
+    (k_copy_col<<<vgrid, 256, 0, s>>>(nb, c->V, c->vcur, c->ks, 0), note_launch());
+    apply_precond(c, c->vcur, c->zcur);
+    (k_copy_col<<<vgrid, 256, 0, s>>>(nb, c->Z, c->zcur, c->ks, 1), note_launch());
+    int pf = prof_begin(c, PF_SPMV);
+    launch_bsr_spmv(c, c->zcur, c->w);
+    prof_end(c, pf);
+    pf = prof_begin(c, PF_ARNOLDI);
+    cgs<PASS_DOT>(c, c->V, 0, c->w, nullptr, FIN_H, 0, 0.0, 1);
+    cgs<PASS_UPD_DOT>(c, c->V, 0, c->w, ks_field(c, offsetof(KState, h)), FIN_H2, 0, 0.0, 1);
+    cgs<PASS_UPD_NORM>(c, c->V, 0, c->w, ks_field(c, offsetof(KState, h2)), FIN_GIVENS, 0, 0.0, 1);
+    (k_scale<<<vgrid, 256, 0, s>>>(nb, c->w, c->V, c->ks, 0, 1, 1), note_launch());
+    prof_end(c, pf);
+}
+
+cptr_status build_iteration_graph(Ctx *c) {
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    if (!c->cap_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t orig = c->stream;
+    c->stream = c->cap_stream;
+    begin_capture_count();
+    prof_begin_capture(c);
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        arnoldi_step_device_indexed(c);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(c->cap_stream, &g);
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+            cudaGraphDestroy(g);
+        }
+    }
+    prof_end_capture(c);
+    c->graph_launches = end_capture_count();
+    c->graph_mask = c->prof.mask;
+    c->graph_inject = c->inject_wait;
+    c->stream = orig;
+    if (e != cudaSuccess) {
+        c->graph_exec = nullptr;
+        return c->fail(CPTR_ECUDA, std::string("capture of the Arnoldi step: ") + cudaGetErrorString(e));
+    }
+    return CPTR_OK;
 }
 
 static cptr_status read_state(Ctx *c) {
@@ -276,6 +349,12 @@ cptr_status fgmres_solve(Ctx *c, const double *bw, double *x, double rtol, cptr_
     const int64_t nb = (int64_t)c->n * c->b;
     cudaStream_t s = c->stream;
     const unsigned vgrid = 4 * 152;
+    if (c->o.use_graph && (!c->graph_exec || c->graph_mask != c->prof.mask || c->graph_inject != c->inject_wait))
+        CPTR_TRY(build_iteration_graph(c));
+    if (!c->o.use_graph && c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
     CPTR_CUDA_TRY(c, cudaMemsetAsync(c->ks, 0, sizeof(KState), s));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(x, 0, sizeof(double) * nb, s));
     // ||b'||, beta = ||b'|| (x = 0), v_0 = b' / beta
@@ -283,10 +362,20 @@ cptr_status fgmres_solve(Ctx *c, const double *bw, double *x, double rtol, cptr_
     CPTR_TRY(read_state(c));
     int it = 0, restarts = 0;
     bool done = c->ks_host->done != 0;
-    if (!done) (k_scale<<<vgrid, 256, 0, s>>>(nb, bw, c->V, c->ks, 1, 0), note_launch());
+    if (!done) (k_scale<<<vgrid, 256, 0, s>>>(nb, bw, c->V, c->ks, 1, 0, 0), note_launch());
     while (!done) {
         int every = c->o.check_every > 0 ? c->o.check_every : 1;
         for (int j = 0; j < m && it < c->o.max_it; ++j) {
+            if (c->graph_exec) {
+                CPTR_CUDA_TRY(c, cudaGraphLaunch(c->graph_exec, s));
+                note_launches(c->graph_launches);
+                ++it;
+                CPTR_TRY(read_state(c));
+                CPTR_TRY(prof_collect_graph(c));
+                if (c->ks_host->wait_err) return c->fail(CPTR_ETIMEOUT, "ILU(0) sweep: a bounded wait gave up");
+                if (c->ks_host->done) break;
+                continue;
+            }
             double *vj = c->V + (int64_t)j * nb, *zj = c->Z + (int64_t)j * nb;
             apply_precond(c, vj, zj);
             int pf = prof_begin(c, PF_SPMV);
@@ -296,11 +385,12 @@ cptr_status fgmres_solve(Ctx *c, const double *bw, double *x, double rtol, cptr_
             cgs<PASS_DOT>(c, c->V, j + 1, c->w, nullptr, FIN_H, j);
             cgs<PASS_UPD_DOT>(c, c->V, j + 1, c->w, ks_field(c, offsetof(KState, h)), FIN_H2, j);
             cgs<PASS_UPD_NORM>(c, c->V, j + 1, c->w, ks_field(c, offsetof(KState, h2)), FIN_GIVENS, j);
-            (k_scale<<<vgrid, 256, 0, s>>>(nb, c->w, c->V + (int64_t)(j + 1) * nb, c->ks, 0, 1), note_launch());
+            (k_scale<<<vgrid, 256, 0, s>>>(nb, c->w, c->V + (int64_t)(j + 1) * nb, c->ks, 0, 1, 0), note_launch());
             prof_end(c, pf);
             ++it;
             if (it % every == 0 || j == m - 1 || it >= c->o.max_it) {
                 CPTR_TRY(read_state(c));
+                if (c->ks_host->wait_err) return c->fail(CPTR_ETIMEOUT, "ILU(0) sweep: a bounded wait gave up");
                 if (c->ks_host->done) break;
             }
         }
@@ -315,7 +405,7 @@ cptr_status fgmres_solve(Ctx *c, const double *bw, double *x, double rtol, cptr_
         cgs<PASS_NORM>(c, nullptr, 0, c->w, nullptr, FIN_RESTART, 0);
         CPTR_TRY(read_state(c));
         if (c->ks_host->done) break;
-        (k_scale<<<vgrid, 256, 0, s>>>(nb, c->w, c->V, c->ks, 1, 0), note_launch());
+        (k_scale<<<vgrid, 256, 0, s>>>(nb, c->w, c->V, c->ks, 1, 0, 0), note_launch());
         ++restarts;
     }
     // true residual
@@ -324,6 +414,7 @@ cptr_status fgmres_solve(Ctx *c, const double *bw, double *x, double rtol, cptr_
     CPTR_CUDA_TRY(c, cudaGetLastError());
     CPTR_TRY(read_state(c));
     const KState &h = *c->ks_host;
+    if (h.wait_err) return c->fail(CPTR_ETIMEOUT, "ILU(0) sweep: a bounded wait gave up");
     if (st) {
         st->iters = it;
         st->restarts = restarts;

@@ -5,15 +5,25 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
 #include <atomic>
+#include <vector>
 
 #include "common.cuh"
 
 namespace cptr {
 
 static std::atomic<int64_t> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local bool t_capturing = false;
+static thread_local int64_t t_captured = 0;
+void note_launch() {
+    if (t_capturing) ++t_captured;
+    else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void begin_capture_count() { t_capturing = true; t_captured = 0; }
+int64_t end_capture_count() { t_capturing = false; return t_captured; }
 
 int prof_begin(const Ctx *c, int fam) {
     Prof &p = c->prof;
@@ -28,26 +38,53 @@ int prof_begin(const Ctx *c, int fam) {
     }
     size_t s = p.used++;
     p.fam[s] = fam;
-    cudaEventRecord(p.ev[2 * s], c->stream);
+    if (p.capturing) {
+        // inside stream capture a plain record is only a capture dependency: ask for a graph node
+        p.gslots.push_back(s);
+        cudaEventRecordWithFlags(p.ev[2 * s], c->stream, cudaEventRecordExternal);
+    } else {
+        cudaEventRecord(p.ev[2 * s], c->stream);
+    }
     return (int)s;
 }
+void prof_begin_capture(Ctx *c) {
+    c->prof.capturing = true;
+    c->prof.gslots.clear();
+}
+void prof_end_capture(Ctx *c) {
+    // the captured slots stay reserved at the front of the pool; direct launches use the rest
+    c->prof.capturing = false;
+}
+cptr_status prof_collect_graph(Ctx *c) {
+    Prof &p = c->prof;
+    for (size_t s : p.gslots) {
+        float ms = 0.f;
+        CPTR_CUDA_TRY(c, cudaEventElapsedTime(&ms, p.ev[2 * s], p.ev[2 * s + 1]));
+        p.ms[p.fam[s]] += ms;
+        p.cnt[p.fam[s]] += 1;
+    }
+    return CPTR_OK;
+}
 void prof_end(const Ctx *c, int slot) {
-    if (slot >= 0) cudaEventRecord(c->prof.ev[2 * (size_t)slot + 1], c->stream);
+    if (slot < 0) return;
+    if (c->prof.capturing) cudaEventRecordWithFlags(c->prof.ev[2 * (size_t)slot + 1], c->stream, cudaEventRecordExternal);
+    else cudaEventRecord(c->prof.ev[2 * (size_t)slot + 1], c->stream);
 }
 void prof_reset(Ctx *c) {
-    c->prof.used = 0;
+    c->prof.used = c->prof.gslots.empty() ? 0 : c->prof.gslots.back() + 1;
     for (int f = 0; f < PF_N; ++f) { c->prof.ms[f] = 0.0; c->prof.cnt[f] = 0; }
 }
 cptr_status prof_collect(Ctx *c) {
     Prof &p = c->prof;
-    for (size_t s = 0; s < p.used; ++s) {
+    size_t first = p.gslots.empty() ? 0 : p.gslots.back() + 1;
+    for (size_t s = first; s < p.used; ++s) {
         float ms = 0.f;
         CPTR_CUDA_TRY(c, cudaEventSynchronize(p.ev[2 * s + 1]));
         CPTR_CUDA_TRY(c, cudaEventElapsedTime(&ms, p.ev[2 * s], p.ev[2 * s + 1]));
         p.ms[p.fam[s]] += ms;
         p.cnt[p.fam[s]] += 1;
     }
-    p.used = 0;
+    p.used = first;
     return CPTR_OK;
 }
 
@@ -241,102 +278,116 @@ void launch_check_finite(const Ctx *c, const double *v, int64_t n, int32_t *flag
 }
 
 // ------------------------------------------------------------------------------------------------
-// BSR SpMV: G lanes per block row, each lane owns whole b x b blocks (vectorised block loads),
-// the G partial row sums are combined with shuffles.  MODE 0: y = A x;  MODE 1: y = v - A x.
-template <int B, int G, int MODE>
-__global__ void __launch_bounds__(256) k_bsr_spmv(int32_t n, const int32_t *__restrict__ rp,
-                                                   const int32_t *__restrict__ ci, const double *__restrict__ A,
-                                                   const double *__restrict__ x, const double *__restrict__ v,
-                                                   double *__restrict__ y) {
-    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int32_t row = (int32_t)(gid / G);
-    int lane = threadIdx.x % G;
+// A' is kept for the solve in a sliced-ELL block layout (SELL-32): block rows are grouped in
+// chunks of 32; chunk c holds w_c block slots per row (its longest row; shorter rows are padded
+// with zero blocks pointing at column 0) stored slot-major and lane-minor, so that the 32 rows
+// of a chunk read each block entry with one fully coalesced 256-byte access:
+//   col[(off_c + s) * 32 + lane],  val[((off_c + s) * b*b + e) * 32 + lane]
+// One thread computes one block row.
+cptr_status sell_build(Ctx *c) {
+    const int32_t n = c->n, B = c->b, nch = (n + 31) / 32;
+    std::vector<int64_t> off(nch + 1, 0);
+    std::vector<int32_t> w(nch, 0);
+    for (int32_t ch = 0; ch < nch; ++ch) {
+        int32_t mx = 0;
+        for (int32_t r = ch * 32; r < std::min(n, ch * 32 + 32); ++r) mx = std::max(mx, c->h_rp[r + 1] - c->h_rp[r]);
+        w[ch] = mx;
+        off[ch + 1] = off[ch] + mx;
+    }
+    c->sell_nch = nch;
+    const int64_t slots = off[nch] * 32;
+    CPTR_TRY(dalloc_t(c, &c->sell_off, (size_t)nch + 1));
+    CPTR_TRY(dalloc_t(c, &c->sell_col, (size_t)slots));
+    CPTR_TRY(dalloc_t(c, &c->sell_val, (size_t)slots * B * B));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->sell_off, off.data(), sizeof(int64_t) * (nch + 1), cudaMemcpyHostToDevice, c->stream));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->sell_col, 0, sizeof(int32_t) * slots, c->stream));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->sell_val, 0, sizeof(double) * slots * B * B, c->stream));
+    launch_bsr_to_sell(c);
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->sell_bytes = slots * (4 + 8 * B * B) + (nch + 1) * 8;
+    return CPTR_OK;
+}
+
+__global__ void k_bsr_to_sell(int32_t n, int B, const int32_t *rp, const int32_t *ci, const double *A,
+                              const int64_t *off, int32_t *col, double *val) {
+    int32_t row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    int32_t ch = row >> 5, lane = row & 31;
+    int64_t o = off[ch];
+    for (int32_t k = rp[row]; k < rp[row + 1]; ++k) {
+        int64_t slot = o + (k - rp[row]);
+        col[slot * 32 + lane] = ci[k];
+        for (int e = 0; e < B * B; ++e) val[(slot * B * B + e) * 32 + lane] = A[(int64_t)k * B * B + e];
+    }
+}
+void launch_bsr_to_sell(const Ctx *c) {
+    (k_bsr_to_sell<<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->rp, c->ci, c->A, c->sell_off, c->sell_col,
+                                                            c->sell_val), note_launch());
+}
+
+// MODE 0: y = A' x;  MODE 1: y = v - A' x;  MODE 2: y = v - A' R_0^T [dp; dT] (only the p and T
+// columns of each block are read; dT may be null for CPR)
+template <int B, int MODE>
+__global__ void __launch_bounds__(256) k_sell_spmv(int32_t n, const int64_t *__restrict__ off,
+                                                    const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                    const double *__restrict__ x, const double *__restrict__ v,
+                                                    double *__restrict__ y, int ps, int ts,
+                                                    const double *__restrict__ dp, const double *__restrict__ dT) {
+    int32_t row = blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t ch = row >> 5, lane = row & 31;
+    if (row >= ((n + 31) & ~31)) return;
+    const int64_t o0 = __ldg(off + ch), o1 = __ldg(off + ch + 1);
     double acc[B];
 #pragma unroll
     for (int r = 0; r < B; ++r) acc[r] = 0.0;
-    if (row < n) {
-        int32_t k1 = __ldg(rp + row + 1);
-        for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G) {
-            int32_t col = __ldg(ci + k);
-            const double *a = A + (int64_t)k * B * B;
+    for (int64_t sl = o0; sl < o1; ++sl) {
+        const int32_t cidx = __ldg(col + sl * 32 + lane);
+        const double *a = val + sl * B * B * 32 + lane;
+        if (MODE == 2) {
+            const double xp = __ldg(dp + cidx);
+            const double xt = dT ? __ldg(dT + cidx) : 0.0;
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                acc[r] = fma(__ldg(a + (r * B + ps) * 32), xp, acc[r]);
+                if (dT) acc[r] = fma(__ldg(a + (r * B + ts) * 32), xt, acc[r]);
+            }
+        } else {
             double xv[B];
 #pragma unroll
-            for (int q = 0; q < B; ++q) xv[q] = __ldg(x + (int64_t)col * B + q);
+            for (int q = 0; q < B; ++q) xv[q] = __ldg(x + (int64_t)cidx * B + q);
 #pragma unroll
             for (int r = 0; r < B; ++r)
 #pragma unroll
-                for (int q = 0; q < B; ++q) acc[r] = fma(__ldg(a + r * B + q), xv[q], acc[r]);
+                for (int q = 0; q < B; ++q) acc[r] = fma(__ldg(a + (r * B + q) * 32), xv[q], acc[r]);
         }
     }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1)
-#pragma unroll
-        for (int r = 0; r < B; ++r) acc[r] += __shfl_down_sync(0xffffffffu, acc[r], o, G);
-    if (row < n && lane == 0) {
+    if (row < n) {
 #pragma unroll
         for (int r = 0; r < B; ++r) {
-            int64_t o = (int64_t)row * B + r;
-            y[o] = MODE == 1 ? v[o] - acc[r] : acc[r];
+            int64_t oo = (int64_t)row * B + r;
+            y[oo] = MODE == 0 ? acc[r] : v[oo] - acc[r];
         }
     }
 }
 
 template <int MODE>
-static void bsr_spmv_dispatch(const Ctx *c, const double *x, const double *v, double *y) {
-    constexpr int G = 8;
-    unsigned grid = nblk((int64_t)c->n * G, 256);
-    if (c->b == 3) (k_bsr_spmv<3, G, MODE><<<grid, 256, 0, c->stream>>>(c->n, c->rp, c->ci, c->A, x, v, y), note_launch());
-    else (k_bsr_spmv<4, G, MODE><<<grid, 256, 0, c->stream>>>(c->n, c->rp, c->ci, c->A, x, v, y), note_launch());
+static void sell_dispatch(const Ctx *c, const double *x, const double *v, double *y, const double *dp,
+                          const double *dT) {
+    unsigned grid = nblk((int64_t)c->sell_nch * 32, 256);
+    if (c->b == 3)
+        (k_sell_spmv<3, MODE><<<grid, 256, 0, c->stream>>>(c->n, c->sell_off, c->sell_col, c->sell_val, x, v, y, c->ps,
+                                                           c->ts, dp, dT), note_launch());
+    else
+        (k_sell_spmv<4, MODE><<<grid, 256, 0, c->stream>>>(c->n, c->sell_off, c->sell_col, c->sell_val, x, v, y, c->ps,
+                                                           c->ts, dp, dT), note_launch());
 }
-void launch_bsr_spmv(const Ctx *c, const double *x, double *y) { bsr_spmv_dispatch<0>(c, x, nullptr, y); }
-void launch_bsr_resid(const Ctx *c, const double *x, const double *v, double *y) { bsr_spmv_dispatch<1>(c, x, v, y); }
-
-// stage-1 residual b1 = v - A' R_0^T [dp; dT]: only the p and T columns of each block are used
-template <int B, int G>
-__global__ void __launch_bounds__(256) k_bsr_resid_pt(int32_t n, const int32_t *__restrict__ rp,
-                                                       const int32_t *__restrict__ ci, const double *__restrict__ A,
-                                                       int ps, int ts, const double *__restrict__ dp,
-                                                       const double *__restrict__ dT, const double *__restrict__ v,
-                                                       double *__restrict__ b1) {
-    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int32_t row = (int32_t)(gid / G);
-    int lane = threadIdx.x % G;
-    double acc[B];
-#pragma unroll
-    for (int r = 0; r < B; ++r) acc[r] = 0.0;
-    if (row < n) {
-        int32_t k1 = __ldg(rp + row + 1);
-        for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G) {
-            int32_t col = __ldg(ci + k);
-            const double *a = A + (int64_t)k * B * B;
-            double xp = __ldg(dp + col);
-            double xt = dT ? __ldg(dT + col) : 0.0;
-#pragma unroll
-            for (int r = 0; r < B; ++r) {
-                acc[r] = fma(__ldg(a + r * B + ps), xp, acc[r]);
-                if (dT) acc[r] = fma(__ldg(a + r * B + ts), xt, acc[r]);
-            }
-        }
-    }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1)
-#pragma unroll
-        for (int r = 0; r < B; ++r) acc[r] += __shfl_down_sync(0xffffffffu, acc[r], o, G);
-    if (row < n && lane == 0) {
-#pragma unroll
-        for (int r = 0; r < B; ++r) {
-            int64_t o = (int64_t)row * B + r;
-            b1[o] = v[o] - acc[r];
-        }
-    }
+void launch_bsr_spmv(const Ctx *c, const double *x, double *y) { sell_dispatch<0>(c, x, nullptr, y, nullptr, nullptr); }
+void launch_bsr_resid(const Ctx *c, const double *x, const double *v, double *y) {
+    sell_dispatch<1>(c, x, v, y, nullptr, nullptr);
 }
 void launch_bsr_resid_pt(const Ctx *c, const double *dp, const double *dT, const double *v, double *b1) {
-    constexpr int G = 8;
-    unsigned grid = nblk((int64_t)c->n * G, 256);
-    if (c->b == 3)
-        (k_bsr_resid_pt<3, G><<<grid, 256, 0, c->stream>>>(c->n, c->rp, c->ci, c->A, c->ps, c->ts, dp, dT, v, b1), note_launch());
-    else
-        (k_bsr_resid_pt<4, G><<<grid, 256, 0, c->stream>>>(c->n, c->rp, c->ci, c->A, c->ps, c->ts, dp, dT, v, b1), note_launch());
+    sell_dispatch<2>(c, nullptr, v, b1, dp, dT);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -43,11 +43,12 @@ def test_default_options(lib):
     assert (o.stage1, o.stage2, o.schur, o.smoother) == (0, 0, 0, 0)
     assert abs(o.theta - 0.25) < 1e-15 and abs(o.omega - 2.0 / 3.0) < 1e-15
     assert (o.n_coarse, o.max_levels, o.restart, o.max_it, o.dense_max) == (256, 25, 30, 1000, 1024)
+    assert (o.check_every, o.use_graph) == (1, 1)
 
 
 def test_option_struct_layout_matches_header():
-    # cptr_options: 4 int32, 2 doubles, 8 int32, one pointer
-    assert ctypes.sizeof(cp.cptr_options) == 16 + 16 + 32 + 8
+    # cptr_options: 4 int32, 2 doubles, 10 int32, one pointer
+    assert ctypes.sizeof(cp.cptr_options) == 16 + 16 + 40 + 8
     assert ctypes.sizeof(cp.cptr_stats) == 24 + 7 * 8
 
 

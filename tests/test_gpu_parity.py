@@ -237,3 +237,41 @@ def test_invalid_inputs_are_rejected():
             s["weights"].reshape(-1), s["st"])
     x, info = S.solve(np.ascontiguousarray(s["rhs"].reshape(-1)), 1e-8)
     assert info["status"] == "CPTR_OK"
+
+
+def test_bounded_wait_reports_timeout_and_context_recovers():
+    # failure injection without a GPU fault: a row of the ILU sweep waits on a value nobody writes;
+    # the wait gives up after ~0.5 s and the call reports CPTR_ETIMEOUT
+    s, o, g = pair("parity")
+    nb = s["n"] * s["b"]
+    cp.cptr_inject_wait_timeout(g.ctx, True)
+    r = dev(synth.normal(5, nb))
+    z = torch.empty(nb, dtype=torch.float64, device="cuda")
+    with pytest.raises(cp.CptrError) as e:
+        cp.cptr_apply_ilu(g.ctx, r, z)
+    assert e.value.code == -5
+    with pytest.raises(cp.CptrError) as e:
+        g.solve(dev(s["rhs"].reshape(-1)), 1e-8)
+    assert e.value.code == -5
+    cp.cptr_inject_wait_timeout(g.ctx, False)
+    check_solve(s, o, g, 1e-8)
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_graph_and_direct_launches_agree(use_graph):
+    s, o, g = pair("medium", use_graph=use_graph)
+    info_o, info_g = check_solve(s, o, g, 1e-8)
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_profiling_counts_match_iterations(use_graph):
+    s, o, g = pair("parity", use_graph=use_graph)
+    cp.cptr_set_profiling(g.ctx, 0b11111)
+    x, info = g.solve(dev(s["rhs"].reshape(-1)), 1e-8)
+    prof = cp.cptr_profile(g.ctx)
+    for fam in ("spmv", "stage1", "stage1_resid", "ilu", "arnoldi"):
+        ms, n = prof[fam]
+        assert n == info["iters"] and ms > 0.0, (fam, prof[fam])
+    l0 = cp.cptr_launch_count()
+    g.solve(dev(s["rhs"].reshape(-1)), 1e-8)
+    assert cp.cptr_launch_count() - l0 > 20 * info["iters"]
