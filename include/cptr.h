@@ -58,6 +58,10 @@ enum { CPTR_SCHUR_GIVEN = 0, CPTR_SCHUR_ATT = 1 };
 enum { CPTR_SMOOTH_L1 = 0, CPTR_SMOOTH_JACOBI = 1 };
 /* precision of the preconditioner: all FP64, or FP32 AMG/ILU with BF16 coarse AMG levels */
 enum { CPTR_PREC_FP64 = 0, CPTR_PREC_MIXED = 1 };
+/* cell order of the ILU(0) factorisation (the paper does not state one): the caller's order, or
+ * multicolour: greedy distance-1 colouring of the cell graph in the caller's order, cells sorted
+ * by (colour, index) -- red-black on a 7-point grid, two level sets per triangular sweep */
+enum { CPTR_ILU_NATURAL = 0, CPTR_ILU_MULTICOLOR = 1 };
 /* unknown kinds, one per block slot */
 enum { CPTR_U_P = 0, CPTR_U_T = 1, CPTR_U_SAT = 2 };
 
@@ -74,7 +78,7 @@ typedef struct {
     int32_t precision;   /* CPTR_PREC_* */
     int32_t check_every; /* host reads the convergence flag every k Arnoldi steps (default 1) */
     int32_t use_graph;   /* 1: replay each Arnoldi step as one captured CUDA graph (default 1) */
-    int32_t reserved;
+    int32_t ilu_order;   /* CPTR_ILU_NATURAL (default) or CPTR_ILU_MULTICOLOR */
     void *stream;        /* cudaStream_t for all work; NULL = the legacy default stream */
 } cptr_options;
 
@@ -179,7 +183,8 @@ cptr_status cptr_hierarchy_level(cptr_ctx *ctx, int32_t which, int32_t l, int32_
  * memory budget is fixed in advance).  The paper has no counterpart; it is an engineering
  * addition.
  *   r, z   device vectors of n_cells*b doubles; n_cells*b must not exceed 2^20, else
- *          CPTR_EINVAL with a message naming the limit.
+ *          CPTR_EINVAL with a message naming the limit.  Natural ILU ordering only (else
+ *          CPTR_EINVAL).
  * The array's device address is looked up on the first call on each device, with that device
  * current; make that first call before any stream capture.  All calls on a device share the
  * array: calls whose work overlaps on the GPU race on it.  No part of the array needs to start at
@@ -201,15 +206,16 @@ cptr_status cptr_inject_wait_timeout(cptr_ctx *ctx, int32_t on);
 int64_t cptr_launch_count(void);
 
 /* Time families of kernels with CUDA events on the context's stream during cptr_solve; bit f
- * of mask enables family f: 0 the outer BSR SpMV w = A' z_j (one kernel per region),
- * 1 stage 1, 2 the stage-1 residual v - A' x1 (one kernel), 3 the ILU(0) solve, 4 Arnoldi
- * (three Gram-Schmidt passes, Givens, normalisation).  0 disables (the default). */
+ * of mask enables family f: 0 the outer SpMV w = A' z_j (one kernel per region), 1 stage 1,
+ * 2 the stage-1 residual v - A' x1 (one kernel), 3 the ILU(0) solve (three kernels), 4 Arnoldi
+ * (three Gram-Schmidt passes, Givens, normalisation), 5 the forward ILU sweep (one kernel),
+ * 6 the backward ILU sweep (one kernel).  0 disables (the default). */
 cptr_status cptr_set_profiling(cptr_ctx *ctx, uint32_t mask);
 
 /* Event time (ms) and number of timed regions per family during the last cptr_solve (host
- * arrays of 8 entries; either may be NULL).  Entries 5, 6, 7 hold the host-clock time of the
- * last cptr_setup's phases (inputs + decoupling + extraction, both AMG hierarchies, ILU(0)),
- * with count 1. */
+ * arrays of 16 entries; either may be NULL): entries 0-7 the families above; entries 8, 9, 10
+ * the host-clock time of the last cptr_setup's phases (inputs + decoupling + extraction, both
+ * AMG hierarchies, ILU(0) + SELL layout), with count 1. */
 cptr_status cptr_profile(cptr_ctx *ctx, double *ms, int64_t *count);
 
 #ifdef __cplusplus

@@ -39,7 +39,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("stage1", ctypes.c_int32), ("stage2", ctypes.c_int32), ("schur", ctypes.c_int32),
                 ("smoother", ctypes.c_int32), ("omega", ctypes.c_double), ("theta", ctypes.c_double),
                 ("n_coarse", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("restart", ctypes.c_int32),
-                ("max_it", ctypes.c_int32), ("dense_max", ctypes.c_int32), ("seed", ctypes.c_int32)]
+                ("max_it", ctypes.c_int32), ("dense_max", ctypes.c_int32), ("seed", ctypes.c_int32),
+                ("ilu_order", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -88,10 +89,14 @@ def _load():
         lib.or_nnz.argtypes = [P]
         lib.or_matrix.restype = None
         lib.or_matrix.argtypes = [P, P, P, P]
+        lib.or_ilu_order.restype = None
+        lib.or_ilu_order.argtypes = [P, P]
         lib.or_ilu_factors.restype = None
         lib.or_ilu_factors.argtypes = [P, P]
         lib.or_field.restype = None
         lib.or_field.argtypes = [P, ctypes.c_int, P]
+        lib.or_round_bf16.restype = ctypes.c_double
+        lib.or_round_bf16.argtypes = [ctypes.c_double]
         lib.or_splitmix64.restype = ctypes.c_uint64
         lib.or_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
         _lib = lib
@@ -104,7 +109,7 @@ def _p(a):
 
 def default_opts(**kw) -> Opts:
     o = Opts(stage1=CPTR_FULL, stage2=ILU0, schur=SCHUR_GIVEN, smoother=L1, omega=2.0 / 3.0, theta=0.25,
-             n_coarse=256, max_levels=25, restart=30, max_it=1000, dense_max=1024, seed=0)
+             n_coarse=256, max_levels=25, restart=30, max_it=1000, dense_max=1024, seed=0, ilu_order=0, precision=0)
     for k, v in kw.items():
         setattr(o, k, v)
     return o
@@ -211,6 +216,12 @@ class Oracle:
             A[i, ci[rp[i]:rp[i + 1]]] += v[rp[i]:rp[i + 1]]
         return A
 
+    def ilu_order(self):
+        """Cell order of the ILU(0) factorisation: new index -> original cell."""
+        out = np.zeros(self.n, np.int32)
+        _load().or_ilu_order(self._c, _p(out))
+        return out
+
     def ilu_factors(self):
         lib = _load()
         nnz = lib.or_nnz(self._c)
@@ -283,6 +294,10 @@ class AMG:
     def levels(self):
         lib = _load()
         return _levels(self._h, lib.or_amg_nlevels(self._h))
+
+
+def round_bf16(x: float) -> float:
+    return float(_load().or_round_bf16(x))
 
 
 def splitmix64(seed: int, i: int) -> int:

@@ -43,6 +43,9 @@ typedef struct {
     double omega, theta;
     int32_t n_coarse, max_levels, restart, max_it;
     int32_t dense_max, seed;
+    int32_t ilu_order;       /* 0: natural cell order; 1: multicolour (greedy colouring) */
+    int32_t precision;       /* 0: FP64 everywhere; 1: stored preconditioner values rounded as the
+                                mixed-precision GPU form stores them (FP64 arithmetic) */
 } or_opts;
 
 typedef struct {
@@ -504,10 +507,14 @@ typedef struct {
     or_opts o;
     int32_t n, b, ps, ts;
     csr A;             /* decoupled A' (interleaved scalar CSR) */
+    csr Alow;          /* mixed precision: A' with FP32-rounded values for the stage-1 residual */
     double *W;         /* [n, b, b] row weights (identity if none was given) */
     csr App, ApT, ATp, St;
     amg hp, hT;
     ilu0 ilu;
+    int32_t *cperm;    /* multicolour ILU: new cell index -> original cell (NULL: natural) */
+    csr Aperm;         /* A' with cells permuted (multicolour ILU only) */
+    double *rp_tmp, *zp_tmp;
     /* work */
     double *bp, *bT, *xp, *dT, *dp, *t1, *x1, *b1;
     int status;
@@ -558,6 +565,108 @@ static void extract_field(const or_ctx *c, const int32_t *rp, const int32_t *ci,
     }
 }
 
+/* Rounding to the storage formats of the mixed-precision form.  FP32: IEEE round to nearest
+ * (the C conversion).  BF16: the FP32 value rounded to 8 significant bits, round to nearest, ties
+ * to even (keep the top 16 bits of the binary32 encoding). */
+static double round_fp32(double x) { return (double)(float)x; }
+static double round_bf16(double x) {
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return (double)f;   /* inf / nan unchanged */
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    u &= 0xFFFF0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+static void round_array(double *v, int64_t n, int bf16) {
+    for (int64_t i = 0; i < n; ++i) v[i] = bf16 ? round_bf16(v[i]) : round_fp32(v[i]);
+}
+/* levels 0 and 1 in FP32, levels >= 2 in BF16 (matrix and transfer values); the smoother
+ * diagonal in FP32; the coarsest dense factorisation stays FP64 */
+static void round_hierarchy(amg *h) {
+    for (int l = 0; l < h->nlev; ++l) {
+        amg_level *L = &h->L[l];
+        int bf = l >= 2;
+        round_array(L->A.v, L->A.nnz, bf);
+        if (L->P.rp) round_array(L->P.v, L->P.nnz, bf);
+        if (L->PT.rp) round_array(L->PT.v, L->PT.nnz, bf);
+        round_array(L->dinv, L->A.n, 0);
+    }
+}
+double or_round_bf16(double x) { return round_bf16(x); }
+
+/* Greedy distance-1 colouring of the cell graph in natural order (each cell takes the smallest
+ * colour not used by its lower-index neighbours), then cells sorted by (colour, index).  Returns
+ * the order: new index -> original cell.  On a 7-point Cartesian grid this is red-black. */
+static int32_t *multicolour_order(int32_t n, const int32_t *rp, const int32_t *ci) {
+    int32_t *color = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t ncol = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t c = 0;
+        for (;;) {
+            int used = 0;
+            for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+                if (ci[k] < i && color[ci[k]] == c) { used = 1; break; }
+            if (!used) break;
+            ++c;
+        }
+        color[i] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t o = 0;
+    for (int32_t c = 0; c < ncol; ++c)
+        for (int32_t i = 0; i < n; ++i)
+            if (color[i] == c) order[o++] = i;
+    free(color);
+    return order;
+}
+
+/* P A P^T for a cell permutation (order: new -> original) of the interleaved scalar CSR:
+ * unknown u of new cell I is row I*b + u; columns renumbered likewise and sorted. */
+static int cmp_pair(const void *a, const void *b) {
+    int32_t x = ((const int32_t *)a)[0], y = ((const int32_t *)b)[0];
+    return (x > y) - (x < y);
+}
+static void permute_cells(const csr *A, int32_t b, const int32_t *order, csr *P) {
+    int32_t n = A->n / b;
+    int32_t *inv = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    for (int32_t I = 0; I < n; ++I) inv[order[I]] = I;
+    csr_alloc(P, A->n, A->nnz);
+    int32_t o = 0;
+    int32_t *pairs = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(A->n > 0 ? A->n : 1));
+    for (int32_t I = 0; I < n; ++I)
+        for (int32_t u = 0; u < b; ++u) {
+            int32_t row = order[I] * b + u, len = A->rp[row + 1] - A->rp[row];
+            for (int32_t t = 0; t < len; ++t) {
+                int32_t c = A->ci[A->rp[row] + t];
+                pairs[2 * t] = inv[c / b] * b + c % b;
+                pairs[2 * t + 1] = A->rp[row] + t;
+            }
+            qsort(pairs, (size_t)len, 2 * sizeof(int32_t), cmp_pair);
+            for (int32_t t = 0; t < len; ++t) {
+                P->ci[o] = pairs[2 * t];
+                P->v[o] = A->v[pairs[2 * t + 1]];
+                ++o;
+            }
+            P->rp[I * b + u + 1] = o;
+        }
+    free(pairs);
+    free(inv);
+}
+
+/* z = (LU)^{-1} r for the factors of the (possibly cell-permuted) matrix */
+static void ilu_apply_ordered(or_ctx *c, const double *r, double *z) {
+    if (!c->cperm) { ilu0_solve(&c->ilu, r, z); return; }
+    int32_t b = c->b;
+    for (int32_t I = 0; I < c->n; ++I)
+        for (int32_t u = 0; u < b; ++u) c->rp_tmp[I * b + u] = r[c->cperm[I] * b + u];
+    ilu0_solve(&c->ilu, c->rp_tmp, c->zp_tmp);
+    for (int32_t I = 0; I < c->n; ++I)
+        for (int32_t u = 0; u < b; ++u) z[c->cperm[I] * b + u] = c->zp_tmp[I * b + u];
+}
+
 or_ctx *or_create(int32_t n, int32_t b, const int32_t *rp, const int32_t *ci, const double *vals, const double *W,
                   int32_t ps, int32_t ts, const int32_t *st_rp, const int32_t *st_ci, const double *st_v,
                   const or_opts *o) {
@@ -584,7 +693,25 @@ or_ctx *or_create(int32_t n, int32_t b, const int32_t *rp, const int32_t *ci, co
     int rc = 0;
     if (o->stage1 != OR_NONE1) rc = amg_setup(&c->hp, &c->App, o);
     if (!rc && o->stage1 != OR_NONE1 && o->stage1 != OR_CPR) rc = amg_setup(&c->hT, &c->St, o);
-    if (!rc && o->stage2 == OR_ILU0) rc = ilu0_factor(&c->A, &c->ilu);
+    if (!rc && o->stage2 == OR_ILU0) {
+        if (o->ilu_order == 1) {
+            c->cperm = multicolour_order(n, rp, ci);
+            permute_cells(&c->A, b, c->cperm, &c->Aperm);
+            c->rp_tmp = (double *)calloc((size_t)n * b, sizeof(double));
+            c->zp_tmp = (double *)calloc((size_t)n * b, sizeof(double));
+            rc = ilu0_factor(&c->Aperm, &c->ilu);
+        } else {
+            rc = ilu0_factor(&c->A, &c->ilu);
+        }
+    }
+    if (!rc && o->precision == 1) {
+        round_hierarchy(&c->hp);
+        round_hierarchy(&c->hT);
+        round_array(c->ApT.v, c->ApT.nnz, 0);
+        round_array(c->ATp.v, c->ATp.nnz, 0);
+        csr_copy(&c->A, &c->Alow);            /* A' for the stage-1 residual, FP32 values */
+        round_array(c->Alow.v, c->Alow.nnz, 0);
+    }
     c->status = rc;
     size_t nb = (size_t)n * b;
     c->bp = calloc(n, sizeof(double)); c->bT = calloc(n, sizeof(double));
@@ -601,6 +728,7 @@ void or_destroy(or_ctx *c) {
     csr_free(&c->A); csr_free(&c->App); csr_free(&c->ApT); csr_free(&c->ATp); csr_free(&c->St);
     amg_free(&c->hp); amg_free(&c->hT);
     csr_free(&c->ilu.LU); free(c->ilu.diag);
+    free(c->cperm); csr_free(&c->Aperm); free(c->rp_tmp); free(c->zp_tmp); csr_free(&c->Alow);
     free(c->W); free(c->bp); free(c->bT); free(c->xp); free(c->dT); free(c->dp); free(c->t1);
     free(c->x1); free(c->b1);
     free(c);
@@ -653,9 +781,9 @@ static void stage1(or_ctx *c, const double *v, double *x1) {
 void or_precond(or_ctx *c, const double *v, double *z) {
     int32_t nb = c->n * c->b;
     stage1(c, v, c->x1);
-    spmv(&c->A, c->x1, c->b1);
+    spmv(c->Alow.rp ? &c->Alow : &c->A, c->x1, c->b1);
     for (int32_t i = 0; i < nb; ++i) c->b1[i] = v[i] - c->b1[i];
-    if (c->o.stage2 == OR_ILU0) ilu0_solve(&c->ilu, c->b1, z);
+    if (c->o.stage2 == OR_ILU0) ilu_apply_ordered(c, c->b1, z);
     else memcpy(z, c->b1, sizeof(double) * (size_t)nb);
     for (int32_t i = 0; i < nb; ++i) z[i] += c->x1[i];
 }
@@ -798,7 +926,11 @@ void or_hier_level_get(amg *h, int l, int32_t *rp, int32_t *ci, double *v, doubl
 amg *or_hierarchy(or_ctx *c, int which) { return pick(c, which); }
 void or_vcycle(or_ctx *c, int which, const double *b, double *x) { vcycle(pick(c, which), 0, b, x); }
 void or_stage1(or_ctx *c, const double *v, double *x1) { stage1(c, v, x1); }
-void or_ilu_apply(or_ctx *c, const double *r, double *z) { ilu0_solve(&c->ilu, r, z); }
+void or_ilu_apply(or_ctx *c, const double *r, double *z) { ilu_apply_ordered(c, r, z); }
+/* the cell order of the ILU factorisation (new -> original), or identity */
+void or_ilu_order(or_ctx *c, int32_t *order) {
+    for (int32_t I = 0; I < c->n; ++I) order[I] = c->cperm ? c->cperm[I] : I;
+}
 void or_spmv(or_ctx *c, const double *x, double *y) { spmv(&c->A, x, y); }
 int32_t or_nnz(or_ctx *c) { return c->A.nnz; }
 void or_matrix(or_ctx *c, int32_t *rp, int32_t *ci, double *v) {

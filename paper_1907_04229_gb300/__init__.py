@@ -23,6 +23,7 @@ STAGE2 = {"ilu0": 0, "none": 1}
 SCHUR = {"given": 0, "att": 1}
 SMOOTHER = {"l1": 0, "jacobi": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
+ILU_ORDER = {"natural": 0, "multicolor": 1}
 U_P, U_T, U_SAT = 0, 1, 2
 
 
@@ -32,7 +33,7 @@ class cptr_options(ctypes.Structure):
                 ("n_coarse", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_it", ctypes.c_int32), ("dense_max", ctypes.c_int32), ("seed", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("check_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("ilu_order", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class cptr_stats(ctypes.Structure):
@@ -74,8 +75,8 @@ _SIGS = {
     "cptr_set_profiling": (_I, [_P, ctypes.c_uint32]),
     "cptr_profile": (_I, [_P, _P, _P]),
 }
-PROFILE_FAMILIES = ("spmv", "stage1", "stage1_resid", "ilu", "arnoldi", "_5", "_6", "_7")
-SETUP_PHASES = {5: "setup_inputs", 6: "setup_amg", 7: "setup_ilu"}
+PROFILE_FAMILIES = ("spmv", "stage1", "stage1_resid", "ilu", "arnoldi", "ilu_fwd", "ilu_bwd", "_7")
+SETUP_PHASES = {8: "setup_inputs", 9: "setup_amg", 10: "setup_ilu"}
 
 
 def load():
@@ -136,6 +137,8 @@ def cptr_default_options(**kw) -> cptr_options:
             v = SMOOTHER[v]
         elif k == "precision" and isinstance(v, str):
             v = PRECISION[v]
+        elif k == "ilu_order" and isinstance(v, str):
+            v = ILU_ORDER[v]
         setattr(o, k, v)
     return o
 
@@ -243,8 +246,8 @@ def cptr_set_profiling(ctx, mask: int):
 
 
 def cptr_profile(ctx):
-    ms = np.zeros(8)
-    cnt = np.zeros(8, np.int64)
+    ms = np.zeros(16)
+    cnt = np.zeros(16, np.int64)
     _check(ctx, load().cptr_profile(ctx, ms.ctypes.data, cnt.ctypes.data))
     out = {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(PROFILE_FAMILIES) if not name.startswith("_")}
     for i, name in SETUP_PHASES.items():

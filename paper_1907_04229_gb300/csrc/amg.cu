@@ -521,6 +521,8 @@ void amg_free(Hier &h) {
         Level &L = h.L[l];
         csr_free(L.A); csr_free(L.P); csr_free(L.PT);
         dfree(L.dinv); dfree(L.cf); dfree(L.b); dfree(L.x); dfree(L.t); dfree(L.r);
+        dfree(L.Av_lo); dfree(L.Pv_lo); dfree(L.PTv_lo);
+        dfree(L.dinv32); dfree(L.b32); dfree(L.x32); dfree(L.t32); dfree(L.r32);
         L = Level{};
     }
     dfree(h.cinv);
@@ -530,109 +532,189 @@ void amg_free(Hier &h) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// V(1,1)-cycle kernels
+// V(1,1)-cycle kernels, values VT (double, float or bf16), vectors and sums XT (double or float)
+__device__ __forceinline__ double vld(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float vld(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float vld(const bf16 *p) {
+    return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p))));
+}
+
 // pre-smoothing from zero fused with the residual: t = D^{-1} b, r = b - A t
-template <int G>
+template <int G, typename VT, typename XT>
 __global__ void __launch_bounds__(256) k_vc_down(int32_t n, const int32_t *__restrict__ rp,
-                                                  const int32_t *__restrict__ ci, const double *__restrict__ v,
-                                                  const double *__restrict__ dinv, const double *__restrict__ b,
-                                                  double *__restrict__ t, double *__restrict__ r) {
+                                                  const int32_t *__restrict__ ci, const VT *__restrict__ v,
+                                                  const XT *__restrict__ dinv, const XT *__restrict__ b,
+                                                  XT *__restrict__ t, XT *__restrict__ r) {
     int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int32_t row = (int32_t)(gid / G);
     int lane = threadIdx.x % G;
-    double acc = 0.0;
+    XT acc = 0;
     if (row < n) {
         int32_t k1 = __ldg(rp + row + 1);
         for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G) {
             int32_t j = __ldg(ci + k);
-            acc = fma(__ldg(v + k), __ldg(dinv + j) * __ldg(b + j), acc);
+            acc = fma((XT)vld(v + k), __ldg(dinv + j) * __ldg(b + j), acc);
         }
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
     if (row < n && lane == 0) {
-        double bi = b[row];
+        XT bi = b[row];
         t[row] = dinv[row] * bi;
         r[row] = bi - acc;
     }
 }
 // post-smoothing: x = t + D^{-1} (b - A t)
-template <int G>
+template <int G, typename VT, typename XT>
 __global__ void __launch_bounds__(256) k_vc_post(int32_t n, const int32_t *__restrict__ rp,
-                                                  const int32_t *__restrict__ ci, const double *__restrict__ v,
-                                                  const double *__restrict__ dinv, const double *__restrict__ b,
-                                                  const double *__restrict__ t, double *__restrict__ x) {
+                                                  const int32_t *__restrict__ ci, const VT *__restrict__ v,
+                                                  const XT *__restrict__ dinv, const XT *__restrict__ b,
+                                                  const XT *__restrict__ t, XT *__restrict__ x) {
     int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int32_t row = (int32_t)(gid / G);
     int lane = threadIdx.x % G;
-    double acc = 0.0;
+    XT acc = 0;
     if (row < n) {
         int32_t k1 = __ldg(rp + row + 1);
-        for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G) acc = fma(__ldg(v + k), __ldg(t + __ldg(ci + k)), acc);
+        for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G)
+            acc = fma((XT)vld(v + k), __ldg(t + __ldg(ci + k)), acc);
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
     if (row < n && lane == 0) x[row] = t[row] + dinv[row] * (b[row] - acc);
 }
-// coarsest dense solve x = A_c^{-1} b: one warp per row
-__global__ void k_dense_mv(int32_t n, const double *__restrict__ M, const double *__restrict__ b, double *__restrict__ x) {
+// coarsest dense solve x = A_c^{-1} b in FP64 (one warp per row), whatever the vector type
+template <typename XT>
+__global__ void k_dense_mv(int32_t n, const double *__restrict__ M, const XT *__restrict__ b, XT *__restrict__ x) {
     int32_t row = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (row >= n) return;
     double acc = 0.0;
-    for (int32_t j = lane; j < n; j += 32) acc = fma(M[(int64_t)row * n + j], b[j], acc);
+    for (int32_t j = lane; j < n; j += 32) acc = fma(M[(int64_t)row * n + j], (double)b[j], acc);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) x[row] = acc;
+    if (lane == 0) x[row] = (XT)acc;
 }
-__global__ void k_diag_scale(int32_t n, const double *d, const double *b, double *x) {
+template <typename XT>
+__global__ void k_diag_scale(int32_t n, const XT *d, const XT *b, XT *x) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = d[i] * b[i];
 }
 
-static void launch_down(cudaStream_t s, const Level &L, const double *b) {
+template <typename VT, typename XT>
+static void launch_down(cudaStream_t s, const Level &L, const VT *v, const XT *dinv, const XT *b, XT *t, XT *r) {
     int G = lanes_for(L.A.n, L.A.nnz);
     unsigned grid = nblk((int64_t)L.A.n * G, 256);
     const Csr &A = L.A;
     switch (G) {
-    case 4: (k_vc_down<4><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, L.t, L.r), note_launch()); break;
-    case 8: (k_vc_down<8><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, L.t, L.r), note_launch()); break;
-    case 16: (k_vc_down<16><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, L.t, L.r), note_launch()); break;
-    default: (k_vc_down<32><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, L.t, L.r), note_launch()); break;
+    case 4: (k_vc_down<4, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
+    case 8: (k_vc_down<8, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
+    case 16: (k_vc_down<16, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
+    default: (k_vc_down<32, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
     }
 }
-static void launch_post(cudaStream_t s, const Level &L, const double *b, const double *t, double *x) {
+template <typename VT, typename XT>
+static void launch_post(cudaStream_t s, const Level &L, const VT *v, const XT *dinv, const XT *b, const XT *t, XT *x) {
     int G = lanes_for(L.A.n, L.A.nnz);
     unsigned grid = nblk((int64_t)L.A.n * G, 256);
     const Csr &A = L.A;
     switch (G) {
-    case 4: (k_vc_post<4><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, t, x), note_launch()); break;
-    case 8: (k_vc_post<8><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, t, x), note_launch()); break;
-    case 16: (k_vc_post<16><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, t, x), note_launch()); break;
-    default: (k_vc_post<32><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, L.dinv, b, t, x), note_launch()); break;
+    case 4: (k_vc_post<4, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
+    case 8: (k_vc_post<8, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
+    case 16: (k_vc_post<16, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
+    default: (k_vc_post<32, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
     }
 }
 
-static void vcycle_level(const Ctx *c, const Hier &h, int l, const double *b, double *x) {
+// per-level views of the arrays used by the FP64 or by the mixed-precision cycle
+template <typename XT> struct LevelVecs;
+template <> struct LevelVecs<double> {
+    static const double *dinv(const Level &L) { return L.dinv; }
+    static double *b(const Level &L) { return L.b; }
+    static double *x(const Level &L) { return L.x; }
+    static double *t(const Level &L) { return L.t; }
+    static double *r(const Level &L) { return L.r; }
+};
+template <> struct LevelVecs<float> {
+    static const float *dinv(const Level &L) { return L.dinv32; }
+    static float *b(const Level &L) { return L.b32; }
+    static float *x(const Level &L) { return L.x32; }
+    static float *t(const Level &L) { return L.t32; }
+    static float *r(const Level &L) { return L.r32; }
+};
+
+// one smoothing/residual/transfer step of level L with its matrix values in storage VT
+template <typename VT, typename XT>
+static void level_down(cudaStream_t s, const Level &L, const Level &C, const VT *Av, const VT *PTv, const XT *b) {
+    using LV = LevelVecs<XT>;
+    launch_down<VT, XT>(s, L, Av, LV::dinv(L), b, LV::t(L), LV::r(L));             // t = D^-1 b, r = b - A t
+    launch_csr_spmv_t<VT, XT>(s, L.PT.n, L.PT.nnz, L.PT.rp, L.PT.ci, PTv, LV::r(L), LV::b(C), 0, nullptr);  // b_c = P^T r
+}
+template <typename VT, typename XT>
+static void level_up(cudaStream_t s, const Level &L, const Level &C, const VT *Av, const VT *Pv, const XT *b, XT *x) {
+    using LV = LevelVecs<XT>;
+    launch_csr_spmv_t<VT, XT>(s, L.P.n, L.P.nnz, L.P.rp, L.P.ci, Pv, LV::x(C), LV::t(L), 2, nullptr);  // t += P x_c
+    launch_post<VT, XT>(s, L, Av, LV::dinv(L), b, LV::t(L), x);                     // x = t + D^-1 (b - A t)
+}
+
+template <typename XT>
+static void vcycle_level(const Ctx *c, const Hier &h, int l, const XT *b, XT *x) {
+    using LV = LevelVecs<XT>;
     cudaStream_t s = c->stream;
     const Level &L = h.L[l];
     int32_t n = L.A.n;
+    const bool lo = sizeof(XT) == 4;
     if (l == h.nlev - 1) {
         if (h.dense) {
-            (k_dense_mv<<<nblk((int64_t)n * 32, 256), 256, 0, s>>>(n, h.cinv, b, x), note_launch());
+            (k_dense_mv<XT><<<nblk((int64_t)n * 32, 256), 256, 0, s>>>(n, h.cinv, b, x), note_launch());
         } else {  // two smoothing sweeps from zero
-            (k_diag_scale<<<nblk(n, 256), 256, 0, s>>>(n, L.dinv, b, L.t), note_launch());
-            launch_post(s, L, b, L.t, x);
+            (k_diag_scale<XT><<<nblk(n, 256), 256, 0, s>>>(n, LV::dinv(L), b, LV::t(L)), note_launch());
+            if (!lo) launch_post<double, double>(s, L, L.A.v, L.dinv, (const double *)b, L.t, (double *)x);
+            else if (L.st == ST_BF16) launch_post<bf16, float>(s, L, (const bf16 *)L.Av_lo, L.dinv32, (const float *)b, L.t32, (float *)x);
+            else launch_post<float, float>(s, L, (const float *)L.Av_lo, L.dinv32, (const float *)b, L.t32, (float *)x);
         }
         return;
     }
     const Level &C = h.L[l + 1];
-    launch_down(s, L, b);                                   // t = D^{-1} b, r = b - A t
-    launch_csr_spmv(s, L.PT, L.r, C.b, 1.0, nullptr);       // b_c = P^T r
-    vcycle_level(c, h, l + 1, C.b, C.x);
-    launch_csr_spmv(s, L.P, C.x, L.t, 2.0, nullptr);        // t += P x_c
-    launch_post(s, L, b, L.t, x);                           // x = t + D^{-1}(b - A t)
+    if (!lo) {
+        level_down<double, double>(s, L, C, L.A.v, L.PT.v, (const double *)b);
+        vcycle_level<XT>(c, h, l + 1, LV::b(C), LV::x(C));
+        level_up<double, double>(s, L, C, L.A.v, L.P.v, (const double *)b, (double *)x);
+    } else if (L.st == ST_BF16) {
+        level_down<bf16, float>(s, L, C, (const bf16 *)L.Av_lo, (const bf16 *)L.PTv_lo, (const float *)b);
+        vcycle_level<XT>(c, h, l + 1, LV::b(C), LV::x(C));
+        level_up<bf16, float>(s, L, C, (const bf16 *)L.Av_lo, (const bf16 *)L.Pv_lo, (const float *)b, (float *)x);
+    } else {
+        level_down<float, float>(s, L, C, (const float *)L.Av_lo, (const float *)L.PTv_lo, (const float *)b);
+        vcycle_level<XT>(c, h, l + 1, LV::b(C), LV::x(C));
+        level_up<float, float>(s, L, C, (const float *)L.Av_lo, (const float *)L.Pv_lo, (const float *)b, (float *)x);
+    }
 }
 
-void amg_vcycle(const Ctx *c, const Hier &h, const double *b, double *x) { vcycle_level(c, h, 0, b, x); }
+void amg_vcycle(const Ctx *c, const Hier &h, const double *b, double *x) { vcycle_level<double>(c, h, 0, b, x); }
+void amg_vcycle32(const Ctx *c, const Hier &h, const float *b, float *x) { vcycle_level<float>(c, h, 0, b, x); }
+
+// the mixed-precision copies of a hierarchy: levels 0 and 1 in FP32, levels >= 2 in BF16
+// (matrix and transfer values); D^{-1} and work vectors in FP32; the coarsest dense inverse and
+// the FP64 arrays are kept
+__global__ void k_d2f(const double *src, int64_t n, float *dst) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = __double2float_rn(src[i]);
+}
+cptr_status amg_lower_precision(Ctx *c, Hier &h) {
+    for (int l = 0; l < h.nlev; ++l) {
+        Level &L = h.L[l];
+        L.st = l >= 2 ? ST_BF16 : ST_F32;
+        CPTR_TRY(to_lower(c, L.A.v, L.A.nnz, L.st, &L.Av_lo));
+        if (l + 1 < h.nlev) {
+            CPTR_TRY(to_lower(c, L.P.v, L.P.nnz, L.st, &L.Pv_lo));
+            CPTR_TRY(to_lower(c, L.PT.v, L.PT.nnz, L.st, &L.PTv_lo));
+        }
+        size_t n = (size_t)(L.A.n > 0 ? L.A.n : 1);
+        for (float **p : {&L.dinv32, &L.b32, &L.x32, &L.t32, &L.r32}) CPTR_TRY(dalloc_t(c, p, n));
+        (k_d2f<<<nblk(L.A.n, 256), 256, 0, c->stream>>>(L.dinv, L.A.n, L.dinv32), note_launch());
+    }
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    return CPTR_OK;
+}
 
 }  // namespace cptr

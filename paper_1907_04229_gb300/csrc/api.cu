@@ -34,6 +34,9 @@ void release_setup(Ctx *c) {
     double **vecs[] = {&c->bp, &c->bT, &c->xp, &c->dp, &c->dT, &c->t1, &c->b1, &c->V, &c->Z, &c->w, &c->bw, &c->xw,
                        &c->vcur, &c->zcur};
     for (double **p : vecs) { dfree(*p); *p = nullptr; }
+    float **vecs32[] = {&c->ApT32, &c->ATp32, &c->sell_val32, &c->bp32, &c->bT32, &c->xp32, &c->dp32, &c->dT32,
+                        &c->t132, &c->b132};
+    for (float **p : vecs32) { dfree(*p); *p = nullptr; }
     if (c->graph_exec) {
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;
@@ -145,6 +148,16 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     if (c->o.stage2 == CPTR_STAGE2_ILU0) CPTR_TRY(ilu_setup(c));
     // A' for the solve in the SELL-32 layout; the BSR copy is not needed after set-up
     CPTR_TRY(sell_build(c));
+    if (c->o.precision == CPTR_PREC_MIXED) {
+        // FP32/BF16 copies of the preconditioner's operators (the FP64 set-up is rounded once)
+        if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_lower_precision(c, c->hp));
+        if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) CPTR_TRY(amg_lower_precision(c, c->hT));
+        CPTR_TRY(to_lower(c, c->ApT, nnzb, ST_F32, (void **)&c->ApT32));
+        CPTR_TRY(to_lower(c, c->ATp, nnzb, ST_F32, (void **)&c->ATp32));
+        CPTR_TRY(to_lower(c, c->sell_val, c->sell_nvals, ST_F32, (void **)&c->sell_val32));
+        for (float **p : {&c->bp32, &c->bT32, &c->xp32, &c->dp32, &c->dT32, &c->t132}) CPTR_TRY(dalloc_t(c, p, (size_t)n));
+        CPTR_TRY(dalloc_t(c, &c->b132, (size_t)n * b));
+    }
     dfree(c->A);
     c->A = nullptr;
     c->prof.setup_ms[2] = ms_since(t2);
@@ -234,7 +247,9 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
     else cptr_default_options(&o);
     if (o.restart < 1 || o.restart > kMaxRestart || o.max_it < 0 || o.max_levels < 1 || o.dense_max < 1 ||
         o.stage1 < 0 || o.stage1 > CPTR_STAGE1_NONE || o.stage2 < 0 || o.stage2 > CPTR_STAGE2_NONE ||
-        o.smoother < 0 || o.smoother > CPTR_SMOOTH_JACOBI || o.precision != CPTR_PREC_FP64)
+        o.smoother < 0 || o.smoother > CPTR_SMOOTH_JACOBI || o.precision < CPTR_PREC_FP64 ||
+        o.precision > CPTR_PREC_MIXED ||
+        o.ilu_order < CPTR_ILU_NATURAL || o.ilu_order > CPTR_ILU_MULTICOLOR)
         return CPTR_EINVAL;
     cptr_ctx *ctx = new (std::nothrow) cptr_ctx();
     if (!ctx) return CPTR_ENOMEM;
@@ -345,10 +360,17 @@ cptr_status cptr_apply_weights(cptr_ctx *ctx, const double *rhs, double *out) {
 cptr_status cptr_apply_stage1(cptr_ctx *ctx, const double *v, double *x1) {
     return guarded(ctx, [&](Ctx *c) {
         CPTR_TRY(need_ready(c));
-        const double *dp, *dT;
-        apply_stage1(c, v, &dp, &dT);
-        if (dp) launch_scatter_pt(c, dp, dT, x1);
-        else CPTR_CUDA_TRY(c, cudaMemsetAsync(x1, 0, sizeof(double) * c->n * c->b, c->stream));
+        if (c->o.precision == CPTR_PREC_MIXED) {
+            const float *dp, *dT;
+            apply_stage1_32(c, v, &dp, &dT);
+            if (dp) launch_scatter_pt<float>(c, dp, dT, x1);
+            else CPTR_CUDA_TRY(c, cudaMemsetAsync(x1, 0, sizeof(double) * c->n * c->b, c->stream));
+        } else {
+            const double *dp, *dT;
+            apply_stage1(c, v, &dp, &dT);
+            if (dp) launch_scatter_pt<double>(c, dp, dT, x1);
+            else CPTR_CUDA_TRY(c, cudaMemsetAsync(x1, 0, sizeof(double) * c->n * c->b, c->stream));
+        }
         return sync(c);
     });
 }
@@ -379,7 +401,13 @@ cptr_status cptr_apply_vcycle(cptr_ctx *ctx, int32_t which, const double *b, dou
         CPTR_TRY(need_ready(c));
         const Hier &h = which == 0 ? c->hp : c->hT;
         if (which < 0 || which > 1 || h.nlev == 0) return c->fail(CPTR_EINVAL, "no such AMG hierarchy");
-        amg_vcycle(c, h, b, x);
+        if (c->o.precision == CPTR_PREC_MIXED) {   // FP64 in and out, FP32 cycle
+            launch_d2f(c, b, c->bp32, c->n);
+            amg_vcycle32(c, h, c->bp32, c->dp32);
+            launch_f2d(c, c->dp32, x, c->n);
+        } else {
+            amg_vcycle(c, h, b, x);
+        }
         return sync(c);
     });
 }
@@ -443,9 +471,13 @@ cptr_status cptr_set_profiling(cptr_ctx *ctx, uint32_t mask) {
 
 cptr_status cptr_profile(cptr_ctx *ctx, double *ms, int64_t *count) {
     return guarded(ctx, [&](Ctx *c) {
-        for (int f = 0; f < PF_N; ++f) {
-            if (ms) ms[f] = f >= 5 ? c->prof.setup_ms[f - 5] : c->prof.ms[f];
-            if (count) count[f] = f >= 5 ? 1 : c->prof.cnt[f];
+        for (int f = 0; f < 16; ++f) {
+            double m = 0.0;
+            int64_t n = 0;
+            if (f < PF_N) { m = c->prof.ms[f]; n = c->prof.cnt[f]; }
+            else if (f < PF_N + 3) { m = c->prof.setup_ms[f - PF_N]; n = 1; }
+            if (ms) ms[f] = m;
+            if (count) count[f] = n;
         }
         return CPTR_OK;
     });

@@ -2,6 +2,7 @@
 // plumbing and the host-side launchers that the translation units share.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -44,6 +45,9 @@ struct Csr {
     double *v = nullptr;
 };
 
+typedef __nv_bfloat16 bf16;
+enum { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2 };   // storage of matrix values
+
 struct Level {
     Csr A;                 // level operator
     double *dinv = nullptr;// smoother D^{-1}
@@ -51,6 +55,12 @@ struct Level {
     int32_t nc = 0;
     int32_t *cf = nullptr; // 1 = C, 2 = F
     double *b = nullptr, *x = nullptr, *t = nullptr, *r = nullptr;  // level work vectors
+    // mixed-precision form: values of A, P, P^T stored in FP32 (levels 0, 1) or BF16 (levels
+    // >= 2), D^{-1} and the work vectors in FP32
+    int st = ST_F64;
+    void *Av_lo = nullptr, *Pv_lo = nullptr, *PTv_lo = nullptr;
+    float *dinv32 = nullptr;
+    float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr, *r32 = nullptr;
 };
 
 struct Hier {
@@ -82,7 +92,8 @@ void note_launches(int64_t n);  // a graph replay of n kernel nodes
 int64_t launch_count();
 void begin_capture_count();  // launches noted on this thread while capturing are not counted...
 int64_t end_capture_count(); // ...but returned here (the graph's kernel node count)
-enum { PF_SPMV = 0, PF_STAGE1 = 1, PF_RESID = 2, PF_ILU = 3, PF_ARNOLDI = 4, PF_N = 8 };
+enum { PF_SPMV = 0, PF_STAGE1 = 1, PF_RESID = 2, PF_ILU = 3, PF_ARNOLDI = 4, PF_ILU_FWD = 5, PF_ILU_BWD = 6,
+       PF_N = 8 };
 struct Prof {
     uint32_t mask = 0;
     std::vector<cudaEvent_t> ev;   // pairs (begin, end)
@@ -124,24 +135,36 @@ void launch_bsr_spmv(const Ctx *c, const double *x, double *y);
 void launch_bsr_resid(const Ctx *c, const double *x, const double *v, double *y);
 void launch_bsr_resid_pt(const Ctx *c, const double *dp, const double *dT, const double *v, double *b1);
 void launch_csr_spmv(cudaStream_t s, const Csr &A, const double *x, double *y, double alpha, const double *c0);
-void launch_gather_pt(const Ctx *c, const double *v, double *bp, double *bT);
-void launch_scatter_pt(const Ctx *c, const double *dp, const double *dT, double *x1);
+// y = A x (mode 0), y = c0 - A x (mode 1), y += A x (mode 2); values VT, vectors and sums XT
+template <typename VT, typename XT>
+void launch_csr_spmv_t(cudaStream_t s, int32_t n, int32_t nnz, const int32_t *rp, const int32_t *ci, const VT *v,
+                       const XT *x, XT *y, int mode, const XT *c0);
+cptr_status to_lower(Ctx *c, const double *src, int64_t n, int st, void **dst);
+void launch_d2f(const Ctx *c, const double *a, float *b, int64_t n);
+void launch_f2d(const Ctx *c, const float *a, double *b, int64_t n);
+template <typename XT> void launch_gather_pt(const Ctx *c, const double *v, XT *bp, XT *bT);
+template <typename XT> void launch_scatter_pt(const Ctx *c, const XT *dp, const XT *dT, double *x1);
+void launch_resid_pt32(const Ctx *c, const float *dp, const float *dT, const double *v, float *b1);
 void launch_sub(cudaStream_t s, int32_t n, const double *a, const double *b, double *out);
 
 // ---- amg.cu ------------------------------------------------------------------------------------
 cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, const double *v, int32_t n);
 void amg_free(Hier &h);
 void amg_vcycle(const Ctx *c, const Hier &h, const double *b, double *x);
+void amg_vcycle32(const Ctx *c, const Hier &h, const float *b, float *x);
+cptr_status amg_lower_precision(Ctx *c, Hier &h);
 
 // ---- ilu.cu ------------------------------------------------------------------------------------
 cptr_status ilu_setup(Ctx *c);
 void ilu_free(Ctx *c);
 void ilu_apply(const Ctx *c, const double *r, double *z, const double *dp, const double *dT);
 void ilu_apply_into(const Ctx *c, const double *r, double *z, double *ybuf, double *zbuf);
+void ilu_apply32(const Ctx *c, const float *r, double *z, const float *dp, const float *dT);
 
 // ---- krylov.cu ---------------------------------------------------------------------------------
 cptr_status fgmres_solve(Ctx *c, const double *bw, double *x, double rtol, cptr_stats *st);
 void apply_stage1(const Ctx *c, const double *v, const double **dp, const double **dT);
+void apply_stage1_32(const Ctx *c, const double *v, const float **dp, const float **dT);
 void apply_precond(const Ctx *c, const double *v, double *z);
 
 // ---- the context -------------------------------------------------------------------------------
@@ -159,12 +182,15 @@ struct Ctx {
     int64_t *sell_off = nullptr;
     int32_t *sell_col = nullptr;
     double *sell_val = nullptr;
-    int64_t sell_bytes = 0;
+    int64_t sell_bytes = 0, sell_nvals = 0;
     double *W = nullptr;     // per-cell weights (n * b * b)
     double *App = nullptr, *ApT = nullptr, *ATp = nullptr, *St = nullptr;  // cell-pattern fields
     Hier hp, hT;
-    // ILU(0): factors in A's pattern, diagonal slots hold inverted pivot blocks
+    // ILU(0): factors in the pattern of the factorised matrix (A' in the caller's cell order, or
+    // with cells permuted by colour), diagonal slots hold inverted pivot blocks
     double *LU = nullptr;
+    int32_t *ilu_rp = nullptr, *ilu_ci = nullptr, *ilu_diag = nullptr;
+    bool ilu_owns_pattern = false;   // false: the ILU pattern aliases rp/ci/diag
     int32_t nlev_f = 0, nlev_b = 0;
     int32_t *lvl_f = nullptr, *lvl_b = nullptr;       // rows sorted by level (device)
     std::vector<int32_t> h_lptr_f, h_lptr_b;           // level pointers (host)
@@ -174,15 +200,19 @@ struct Ctx {
     int32_t *sf_bmap = nullptr;                        // backward position -> forward position
     int64_t *sf_off_f = nullptr, *sf_off_b = nullptr;  // chunk slot offsets
     int32_t *sf_col_f = nullptr, *sf_col_b = nullptr;  // dependency positions (-1 = padding)
-    double *sf_val_f = nullptr, *sf_val_b = nullptr;   // L and U blocks
-    double *sf_dinv = nullptr;                         // inverted pivot blocks, backward order
+    void *sf_val_f = nullptr, *sf_val_b = nullptr;     // L and U blocks (FP64, or FP32 when mixed)
+    void *sf_dinv = nullptr;                           // inverted pivot blocks, backward order
     unsigned *sf_ticket = nullptr;                     // block tickets of the two sweeps
-    double *sf_y = nullptr, *sf_z = nullptr;           // level-ordered y and z (sentinel-filled)
+    void *sf_y = nullptr, *sf_z = nullptr;             // level-ordered y and z (sentinel-filled)
     int32_t inject_wait = 0;                           // failure injection (see cptr_inject_wait_timeout)
     double *never = nullptr;                           // a word no thread writes
     // preconditioner work
     double *bp = nullptr, *bT = nullptr, *xp = nullptr, *dp = nullptr, *dT = nullptr, *t1 = nullptr;
     double *b1 = nullptr;
+    // mixed-precision form: FP32 copies of the stage-1 operators and the stage-1 vectors
+    float *ApT32 = nullptr, *ATp32 = nullptr, *sell_val32 = nullptr;
+    float *bp32 = nullptr, *bT32 = nullptr, *xp32 = nullptr, *dp32 = nullptr, *dT32 = nullptr, *t132 = nullptr;
+    float *b132 = nullptr;
     // Krylov
     double *V = nullptr, *Z = nullptr, *w = nullptr, *bw = nullptr, *xw = nullptr, *partial = nullptr;
     double *vcur = nullptr, *zcur = nullptr;           // fixed in/out vectors of the captured step

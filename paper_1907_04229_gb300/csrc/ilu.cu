@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -188,6 +189,7 @@ __global__ void k_ilu_bwd(const int32_t *__restrict__ rows, int32_t start, int32
 // chunks held by blocks that already run: no deadlock.  Every wait is bounded by kWaitNs of GPU
 // time; a wait that gives up sets ks->wait_err and the call reports CPTR_ETIMEOUT.
 constexpr unsigned long long kSentinel = 0x7FF4C0DEDEADBEEFULL;  // never produced by arithmetic
+constexpr unsigned kSentinel32 = 0x7FA6C0DEu;                      // the same for FP32 vectors
 constexpr unsigned long long kWaitNs = 500ULL * 1000ULL * 1000ULL;
 constexpr int kSfThreads = 128;
 
@@ -197,45 +199,49 @@ __device__ __forceinline__ unsigned long long gtimer() {
     return t;
 }
 
-// a load the compiler may neither hoist out of a loop nor merge with another load
-// (relaxed, GPU scope: it observes stores of other SMs through L2)
+// loads and stores the compiler may neither hoist out of a loop nor merge (relaxed, GPU scope:
+// they observe / publish values through L2 for other SMs)
 __device__ __forceinline__ double load_relaxed(const double *p) {
     double v;
     asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ float load_relaxed(const float *p) {
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void store_relaxed(double *p, double v) {
     asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
-// the last value of a row is stored with release semantics and polled with acquire semantics:
-// seeing it implies seeing the row's earlier values
-__device__ __forceinline__ void store_release(double *p, double v) {
-    asm volatile("st.release.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+__device__ __forceinline__ void store_relaxed(float *p, float v) {
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 __device__ __forceinline__ double load_acquire(const double *p) {
     double v;
     asm volatile("ld.acquire.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ bool is_sentinel(double v) { return __double_as_longlong(v) == (long long)kSentinel; }
+__device__ __forceinline__ bool is_sentinel(float v) { return __float_as_uint(v) == kSentinel32; }
+template <typename T> __device__ __forceinline__ T sentinel_value();
+template <> __device__ __forceinline__ double sentinel_value<double>() { return __longlong_as_double((long long)kSentinel); }
+template <> __device__ __forceinline__ float sentinel_value<float>() { return __uint_as_float(kSentinel32); }
 
-// wait (bounded) until *p no longer holds the sentinel; returns its value
+// wait (bounded) until *p no longer holds the sentinel; returns its value (failure injection)
 __device__ __forceinline__ double wait_value(const double *p, KState *ks) {
     double v = load_acquire(p);
-    if (__double_as_longlong(v) != (long long)kSentinel) return v;
+    if (!is_sentinel(v)) return v;
     const unsigned long long t0 = gtimer();
     for (;;) {
         __nanosleep(40);
         v = load_acquire(p);
-        if (__double_as_longlong(v) != (long long)kSentinel) return v;
+        if (!is_sentinel(v)) return v;
         if (gtimer() - t0 > kWaitNs) {
             atomicExch(&ks->wait_err, 1);
             return 0.0;
         }
     }
-}
-
-__device__ __forceinline__ bool is_sentinel(double v) {
-    return __double_as_longlong(v) == (long long)kSentinel;
 }
 
 // Rows depended on are read in groups of up to kDepGroup: all their values are loaded at once
@@ -244,8 +250,8 @@ __device__ __forceinline__ bool is_sentinel(double v) {
 // checked on its own, so producers publish with plain relaxed stores and no fence.
 constexpr int kDepGroup = 4;
 
-template <int B>
-__device__ __forceinline__ void load_group(const double *base, const int32_t *c, double (*v)[B], KState *ks) {
+template <int B, typename T>
+__device__ __forceinline__ void load_group(const T *base, const int32_t *c, T (*v)[B], KState *ks) {
     bool pending = false;
 #pragma unroll
     for (int g = 0; g < kDepGroup; ++g)
@@ -275,29 +281,28 @@ __device__ __forceinline__ void load_group(const double *base, const int32_t *c,
             for (int g = 0; g < kDepGroup; ++g)
 #pragma unroll
                 for (int q = 0; q < B; ++q)
-                    if (is_sentinel(v[g][q])) v[g][q] = 0.0;
+                    if (is_sentinel(v[g][q])) v[g][q] = (T)0;
             return;
         }
     }
 }
 
 // s -= sum over the dependency slots [o0, o1) of block(slot) * value(dep(slot))
-template <int B>
-__device__ __forceinline__ void subtract_deps(double *s, int64_t o0, int64_t o1, int lane,
-                                              const int32_t *__restrict__ col, const double *__restrict__ val,
-                                              const double *vec, KState *ks) {
+template <int B, typename T>
+__device__ __forceinline__ void subtract_deps(T *s, int64_t o0, int64_t o1, int lane, const int32_t *__restrict__ col,
+                                              const T *__restrict__ val, const T *vec, KState *ks) {
     for (int64_t sl0 = o0; sl0 < o1; sl0 += kDepGroup) {
         int32_t c[kDepGroup];
 #pragma unroll
         for (int g = 0; g < kDepGroup; ++g) c[g] = (sl0 + g < o1) ? __ldg(col + (sl0 + g) * 32 + lane) : -1;
-        double a[kDepGroup][B * B];
+        T a[kDepGroup][B * B];
 #pragma unroll
         for (int g = 0; g < kDepGroup; ++g)
             if (c[g] >= 0)
 #pragma unroll
                 for (int e = 0; e < B * B; ++e) a[g][e] = __ldg(val + ((sl0 + g) * B * B + e) * 32 + lane);
-        double v[kDepGroup][B];
-        load_group<B>(vec, c, v, ks);
+        T v[kDepGroup][B];
+        load_group<B, T>(vec, c, v, ks);
 #pragma unroll
         for (int g = 0; g < kDepGroup; ++g)
             if (c[g] >= 0)
@@ -308,10 +313,11 @@ __device__ __forceinline__ void subtract_deps(double *s, int64_t o0, int64_t o1,
     }
 }
 
-__global__ void k_sf_fill(int64_t nvals, double *y, double *z, unsigned *ticket) {
+template <typename T>
+__global__ void k_sf_fill(int64_t nvals, T *y, T *z, unsigned *ticket) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const double sent = __longlong_as_double((long long)kSentinel);
+    const T sent = sentinel_value<T>();
     for (; i < nvals; i += stride) {
         y[i] = sent;
         z[i] = sent;
@@ -320,12 +326,12 @@ __global__ void k_sf_fill(int64_t nvals, double *y, double *z, unsigned *ticket)
 }
 
 // y(t) = r(pos[t]) - sum_s L(t, s) y(dep(t, s)).  A persistent grid: each block takes chunks of
-// kSfThreads positions in ticket order until none is left.
-template <int B>
+// kSfThreads positions in ticket order until none is left.  Factors and y in T, r in RT.
+template <int B, typename T, typename RT>
 __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_sf(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
                                                           const int64_t *__restrict__ off, const int32_t *__restrict__ col,
-                                                          const double *__restrict__ val, const double *__restrict__ r,
-                                                          double *y, KState *ks, const double *never) {
+                                                          const T *__restrict__ val, const RT *__restrict__ r, T *y,
+                                                          KState *ks, const double *never) {
     __shared__ unsigned blk;
     const unsigned nchunks = (unsigned)((n + kSfThreads - 1) / kSfThreads);
     for (;;) {
@@ -339,24 +345,25 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_sf(int32_t n, unsigned *
         if (never && t == 0) (void)wait_value(never, ks);  // failure injection: a value nobody writes
         const int32_t ch = t >> 5, lane = t & 31;
         const int32_t row = __ldg(pos + t);
-        double s[B];
+        T s[B];
 #pragma unroll
-        for (int q = 0; q < B; ++q) s[q] = __ldg(r + (int64_t)row * B + q);
-        subtract_deps<B>(s, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, y, ks);
+        for (int q = 0; q < B; ++q) s[q] = (T)__ldg(r + (int64_t)row * B + q);
+        subtract_deps<B, T>(s, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, y, ks);
 #pragma unroll
         for (int q = 0; q < B; ++q) store_relaxed(y + (int64_t)t * B + q, s[q]);
     }
 }
 
-// z(t) = D(t)^{-1} (y(bmap[t]) - sum_s U(t, s) z(dep(t, s))); out(pos[t]) = z(t) + x1(pos[t])
-template <int B>
+// z(t) = D(t)^{-1} (y(bmap[t]) - sum_s U(t, s) z(dep(t, s))); out(pos[t]) = z(t) + x1(pos[t]),
+// x1 carrying dp in slot ps and dT in slot ts (vectors of type XT); out is FP64
+template <int B, typename T, typename XT>
 __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_sf(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
                                                           const int32_t *__restrict__ bmap,
                                                           const int64_t *__restrict__ off, const int32_t *__restrict__ col,
-                                                          const double *__restrict__ val, const double *__restrict__ dinv,
-                                                          const double *__restrict__ y, double *z, double *__restrict__ out,
-                                                          int ps, int ts, const double *__restrict__ dp,
-                                                          const double *__restrict__ dT, KState *ks) {
+                                                          const T *__restrict__ val, const T *__restrict__ dinv,
+                                                          const T *__restrict__ y, T *z, double *__restrict__ out,
+                                                          int ps, int ts, const XT *__restrict__ dp,
+                                                          const XT *__restrict__ dT, KState *ks) {
     __shared__ unsigned blk;
     const unsigned nchunks = (unsigned)((n + kSfThreads - 1) / kSfThreads);
     for (;;) {
@@ -370,14 +377,14 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_sf(int32_t n, unsigned *
         const int32_t ch = t >> 5, lane = t & 31;
         const int32_t row = __ldg(pos + t);
         const int32_t tf = __ldg(bmap + t);
-        double s[B];
+        T s[B];
 #pragma unroll
         for (int q = 0; q < B; ++q) s[q] = __ldcg(y + (int64_t)tf * B + q);
-        subtract_deps<B>(s, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, z, ks);
-        double zi[B];
+        subtract_deps<B, T>(s, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, z, ks);
+        T zi[B];
 #pragma unroll
         for (int rr = 0; rr < B; ++rr) {
-            double a = 0.0;
+            T a = 0;
 #pragma unroll
             for (int q = 0; q < B; ++q) a = fma(__ldg(dinv + ((int64_t)ch * B * B + rr * B + q) * 32 + lane), s[q], a);
             zi[rr] = a;
@@ -387,21 +394,22 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_sf(int32_t n, unsigned *
 #pragma unroll
         for (int q = 0; q < B; ++q) {
             double add = 0.0;
-            if (dp && q == ps) add = dp[row];
-            if (dT && q == ts) add = dT[row];
-            out[(int64_t)row * B + q] = zi[q] + add;
+            if (dp && q == ps) add = (double)dp[row];
+            if (dT && q == ts) add = (double)dT[row];
+            out[(int64_t)row * B + q] = (double)zi[q] + add;
         }
     }
 }
 
 // pack factor blocks into the SELL-32 layout: slot u (slot * 32 + lane) takes block kidx[u]
-__global__ void k_sf_pack(int64_t nslots32, int BB, const int32_t *kidx, const double *LU, double *val) {
+template <typename T>
+__global__ void k_sf_pack(int64_t nslots32, int BB, const int32_t *kidx, const double *LU, T *val) {
     int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= nslots32) return;
     int64_t sl = u >> 5;
     int lane = (int)(u & 31);
     int32_t k = kidx[u];
-    for (int e = 0; e < BB; ++e) val[(sl * BB + e) * 32 + lane] = k >= 0 ? LU[(int64_t)k * BB + e] : 0.0;
+    for (int e = 0; e < BB; ++e) val[(sl * BB + e) * 32 + lane] = (T)(k >= 0 ? LU[(int64_t)k * BB + e] : 0.0);
 }
 
 static void level_sets(int32_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci, bool forward,
@@ -427,9 +435,12 @@ static void level_sets(int32_t n, const std::vector<int32_t> &rp, const std::vec
 }
 
 // Level-ordered SELL-32 copies of the factors for the one-launch sweeps (see k_ilu_fwd_sf).
-static cptr_status sf_build(Ctx *c, const std::vector<int32_t> &pos_f, const std::vector<int32_t> &pos_b) {
+// rp, ci, dg: the pattern of the factorised matrix (cells possibly permuted); rowmap: its row ->
+// original cell (the sweeps read r and write z in the caller's order).
+static cptr_status sf_build(Ctx *c, const std::vector<int32_t> &pos_f, const std::vector<int32_t> &pos_b,
+                            const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
+                            const std::vector<int32_t> &dg, const std::vector<int32_t> &rowmap) {
     const int32_t n = c->n, BB = c->b * c->b, nch = (n + 31) / 32;
-    const std::vector<int32_t> &rp = c->h_rp, &ci = c->h_ci, &dg = c->h_diag;
     std::vector<int32_t> inv_f(n), inv_b(n), bmap(n);
     for (int32_t t = 0; t < n; ++t) { inv_f[pos_f[t]] = t; inv_b[pos_b[t]] = t; }
     for (int32_t t = 0; t < n; ++t) bmap[t] = inv_f[pos_b[t]];
@@ -468,21 +479,25 @@ static cptr_status sf_build(Ctx *c, const std::vector<int32_t> &pos_f, const std
             CPTR_CUDA_TRY(c, cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, c->stream));
         return CPTR_OK;
     };
-    CPTR_TRY(up(&c->sf_pos_f, pos_f));
-    CPTR_TRY(up(&c->sf_pos_b, pos_b));
+    std::vector<int32_t> orig_f(n), orig_b(n);
+    for (int32_t t = 0; t < n; ++t) { orig_f[t] = rowmap[pos_f[t]]; orig_b[t] = rowmap[pos_b[t]]; }
+    CPTR_TRY(up(&c->sf_pos_f, orig_f));
+    CPTR_TRY(up(&c->sf_pos_b, orig_b));
     CPTR_TRY(up(&c->sf_bmap, bmap));
     CPTR_TRY(up(&c->sf_off_f, off_f));
     CPTR_TRY(up(&c->sf_off_b, off_b));
     CPTR_TRY(up(&c->sf_col_f, col_f));
     CPTR_TRY(up(&c->sf_col_b, col_b));
     int32_t *dk = nullptr;
-    auto pack = [&](const std::vector<int32_t> &kidx, double **dst) -> cptr_status {
+    const bool lo = c->o.precision == CPTR_PREC_MIXED;   // factors stored in FP32
+    auto pack = [&](const std::vector<int32_t> &kidx, void **dst) -> cptr_status {
         int64_t ns = (int64_t)kidx.size();
-        CPTR_TRY(dalloc_t(c, dst, (size_t)(ns > 0 ? ns : 1) * BB));
+        CPTR_TRY(dalloc(c, dst, (size_t)(ns > 0 ? ns : 1) * BB * (lo ? 4 : 8)));
         if (ns == 0) return CPTR_OK;
         CPTR_TRY(dalloc_t(c, &dk, (size_t)ns));
         CPTR_CUDA_TRY(c, cudaMemcpyAsync(dk, kidx.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, c->stream));
-        (k_sf_pack<<<nblk(ns, 256), 256, 0, c->stream>>>(ns, BB, dk, c->LU, *dst), note_launch());
+        if (lo) (k_sf_pack<float><<<nblk(ns, 256), 256, 0, c->stream>>>(ns, BB, dk, c->LU, (float *)*dst), note_launch());
+        else (k_sf_pack<double><<<nblk(ns, 256), 256, 0, c->stream>>>(ns, BB, dk, c->LU, (double *)*dst), note_launch());
         CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
         dfree(dk);
         dk = nullptr;
@@ -492,45 +507,129 @@ static cptr_status sf_build(Ctx *c, const std::vector<int32_t> &pos_f, const std
     CPTR_TRY(pack(kidx_b, &c->sf_val_b));
     CPTR_TRY(pack(kidx_d, &c->sf_dinv));
     CPTR_TRY(dalloc_t(c, &c->sf_ticket, 4));
-    CPTR_TRY(dalloc_t(c, &c->sf_y, (size_t)n * c->b));
-    CPTR_TRY(dalloc_t(c, &c->sf_z, (size_t)n * c->b));
+    CPTR_TRY(dalloc(c, &c->sf_y, (size_t)n * c->b * (lo ? 4 : 8)));
+    CPTR_TRY(dalloc(c, &c->sf_z, (size_t)n * c->b * (lo ? 4 : 8)));
     CPTR_CUDA_TRY(c, cudaGetLastError());
     return CPTR_OK;
 }
 
+// Greedy distance-1 colouring of the cell graph in natural order (smallest colour unused by the
+// lower-index neighbours), cells sorted by (colour, index): new index -> original cell.
+static std::vector<int32_t> multicolour_order(int32_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci) {
+    std::vector<int32_t> color(n, 0), order;
+    int32_t ncol = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t cc = 0;
+        for (;;) {
+            bool used = false;
+            for (int32_t k = rp[i]; k < rp[i + 1] && !used; ++k) used = ci[k] < i && color[ci[k]] == cc;
+            if (!used) break;
+            ++cc;
+        }
+        color[i] = cc;
+        ncol = std::max(ncol, cc + 1);
+    }
+    order.reserve(n);
+    for (int32_t cc = 0; cc < ncol; ++cc)
+        for (int32_t i = 0; i < n; ++i)
+            if (color[i] == cc) order.push_back(i);
+    return order;
+}
+
+__global__ void k_gather_blocks(int32_t nnzb, int BB, const int32_t *kmap, const double *src, double *dst) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= (int64_t)nnzb * BB) return;
+    int64_t k = u / BB;
+    int e = (int)(u % BB);
+    dst[u] = src[(int64_t)kmap[k] * BB + e];
+}
+
 cptr_status ilu_setup(Ctx *c) {
     ilu_free(c);
+    const int32_t n = c->n, BB = c->b * c->b;
+    CPTR_TRY(dalloc_t(c, &c->LU, (size_t)c->nnzb * BB));
+    // the pattern the factorisation works on: the caller's order, or cells permuted by colour
+    std::vector<int32_t> prp, pci, pdg, rowmap(n);
+    const bool mc = c->o.ilu_order == CPTR_ILU_MULTICOLOR;
+    if (mc) {
+        rowmap = multicolour_order(n, c->h_rp, c->h_ci);
+        std::vector<int32_t> inv(n), kmap(c->nnzb);
+        for (int32_t I = 0; I < n; ++I) inv[rowmap[I]] = I;
+        prp.assign(n + 1, 0);
+        pci.resize(c->nnzb);
+        pdg.assign(n, -1);
+        std::vector<std::pair<int32_t, int32_t>> row;
+        for (int32_t I = 0; I < n; ++I) {
+            int32_t i = rowmap[I];
+            row.clear();
+            for (int32_t k = c->h_rp[i]; k < c->h_rp[i + 1]; ++k) row.push_back({inv[c->h_ci[k]], k});
+            std::sort(row.begin(), row.end());
+            int32_t o = prp[I];
+            for (auto &pr : row) {
+                pci[o] = pr.first;
+                kmap[o] = pr.second;
+                if (pr.first == I) pdg[I] = o;
+                ++o;
+            }
+            prp[I + 1] = o;
+        }
+        c->ilu_owns_pattern = true;
+        CPTR_TRY(dalloc_t(c, &c->ilu_rp, (size_t)n + 1));
+        CPTR_TRY(dalloc_t(c, &c->ilu_ci, (size_t)c->nnzb));
+        CPTR_TRY(dalloc_t(c, &c->ilu_diag, (size_t)n));
+        int32_t *dk = nullptr;
+        CPTR_TRY(dalloc_t(c, &dk, (size_t)c->nnzb));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ilu_rp, prp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, c->stream));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ilu_ci, pci.data(), sizeof(int32_t) * c->nnzb, cudaMemcpyHostToDevice, c->stream));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ilu_diag, pdg.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(dk, kmap.data(), sizeof(int32_t) * c->nnzb, cudaMemcpyHostToDevice, c->stream));
+        (k_gather_blocks<<<nblk((int64_t)c->nnzb * BB, 256), 256, 0, c->stream>>>(c->nnzb, BB, dk, c->A, c->LU), note_launch());
+        CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        dfree(dk);
+    } else {
+        prp = c->h_rp;
+        pci = c->h_ci;
+        pdg = c->h_diag;
+        for (int32_t i = 0; i < n; ++i) rowmap[i] = i;
+        c->ilu_rp = c->rp;
+        c->ilu_ci = c->ci;
+        c->ilu_diag = c->diag;
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->LU, c->A, sizeof(double) * (size_t)c->nnzb * BB, cudaMemcpyDeviceToDevice,
+                                         c->stream));
+    }
     std::vector<int32_t> rows_f, rows_b;
-    level_sets(c->n, c->h_rp, c->h_ci, true, c->h_lptr_f, rows_f);
-    level_sets(c->n, c->h_rp, c->h_ci, false, c->h_lptr_b, rows_b);
+    level_sets(n, prp, pci, true, c->h_lptr_f, rows_f);
+    level_sets(n, prp, pci, false, c->h_lptr_b, rows_b);
     c->nlev_f = (int32_t)c->h_lptr_f.size() - 1;
     c->nlev_b = (int32_t)c->h_lptr_b.size() - 1;
-    CPTR_TRY(dalloc_t(c, &c->lvl_f, (size_t)c->n));
-    CPTR_TRY(dalloc_t(c, &c->lvl_b, (size_t)c->n));
-    CPTR_TRY(dalloc_t(c, &c->LU, (size_t)c->nnzb * c->b * c->b));
-    CPTR_TRY(dalloc_t(c, &c->ybuf, (size_t)c->n * c->b));
-    CPTR_TRY(dalloc_t(c, &c->zbuf, (size_t)c->n * c->b));
-    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->lvl_f, rows_f.data(), sizeof(int32_t) * c->n, cudaMemcpyHostToDevice, c->stream));
-    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->lvl_b, rows_b.data(), sizeof(int32_t) * c->n, cudaMemcpyHostToDevice, c->stream));
-    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->LU, c->A, sizeof(double) * (size_t)c->nnzb * c->b * c->b,
-                                     cudaMemcpyDeviceToDevice, c->stream));
+    CPTR_TRY(dalloc_t(c, &c->lvl_f, (size_t)n));
+    CPTR_TRY(dalloc_t(c, &c->lvl_b, (size_t)n));
+    CPTR_TRY(dalloc_t(c, &c->ybuf, (size_t)n * c->b));
+    CPTR_TRY(dalloc_t(c, &c->zbuf, (size_t)n * c->b));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->lvl_f, rows_f.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->lvl_b, rows_b.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
     for (int32_t l = 0; l < c->nlev_f; ++l) {
         int32_t s = c->h_lptr_f[l], cnt = c->h_lptr_f[l + 1] - s;
         if (c->b == 3)
-            (k_bilu_factor<3><<<nblk(cnt, 128), 128, 0, c->stream>>>(c->lvl_f, s, cnt, c->rp, c->ci, c->diag, c->LU, c->flag), note_launch());
+            (k_bilu_factor<3><<<nblk(cnt, 128), 128, 0, c->stream>>>(c->lvl_f, s, cnt, c->ilu_rp, c->ilu_ci, c->ilu_diag,
+                                                                      c->LU, c->flag), note_launch());
         else
-            (k_bilu_factor<4><<<nblk(cnt, 128), 128, 0, c->stream>>>(c->lvl_f, s, cnt, c->rp, c->ci, c->diag, c->LU, c->flag), note_launch());
+            (k_bilu_factor<4><<<nblk(cnt, 128), 128, 0, c->stream>>>(c->lvl_f, s, cnt, c->ilu_rp, c->ilu_ci, c->ilu_diag,
+                                                                      c->LU, c->flag), note_launch());
     }
     CPTR_CUDA_TRY(c, cudaGetLastError());
     int32_t sing = 0;
     CPTR_CUDA_TRY(c, cudaMemcpyAsync(&sing, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
     CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (sing) return c->fail(CPTR_ESINGULAR, "ILU(0): singular pivot block");
-    return sf_build(c, rows_f, rows_b);
+    return sf_build(c, rows_f, rows_b, prp, pci, pdg, rowmap);
 }
 
 void ilu_free(Ctx *c) {
+    if (c->ilu_owns_pattern) { dfree(c->ilu_rp); dfree(c->ilu_ci); dfree(c->ilu_diag); }
+    c->ilu_owns_pattern = false;
+    c->ilu_rp = c->ilu_ci = c->ilu_diag = nullptr;
     dfree(c->lvl_f); dfree(c->lvl_b); dfree(c->LU); dfree(c->ybuf); dfree(c->zbuf);
     c->lvl_f = c->lvl_b = nullptr;
     c->LU = c->ybuf = c->zbuf = nullptr;
@@ -542,26 +641,42 @@ void ilu_free(Ctx *c) {
 }
 
 // z = (LU)^{-1} r + x1, where x1 carries dp in slot ps and dT in slot ts (either may be null):
-// sentinel fill, forward sweep, backward sweep (three launches)
-void ilu_apply(const Ctx *c, const double *r, double *z, const double *dp, const double *dT) {
+// sentinel fill, forward sweep, backward sweep (three launches).  T: factor storage and sweep
+// arithmetic; RT: type of r; XT: type of dp, dT.
+template <int B, typename T, typename RT, typename XT>
+static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT *dT) {
     cudaStream_t s = c->stream;
     const int32_t n = c->n;
     const unsigned grid = std::min<unsigned>(nblk(n, kSfThreads), 4 * 152);
-    (k_sf_fill<<<4 * 152, 256, 0, s>>>((int64_t)n * c->b, c->sf_y, c->sf_z, c->sf_ticket), note_launch());
-    if (c->inject_wait) (k_sf_fill<<<1, 32, 0, s>>>(1, c->never, c->never, c->sf_ticket + 2), note_launch());
-    if (c->b == 3) {
-        (k_ilu_fwd_sf<3><<<grid, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_f, c->sf_off_f, c->sf_col_f, c->sf_val_f,
-                                                      r, c->sf_y, c->ks, c->inject_wait ? c->never : nullptr), note_launch());
-        (k_ilu_bwd_sf<3><<<grid, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_b, c->sf_bmap, c->sf_off_b, c->sf_col_b,
-                                                      c->sf_val_b, c->sf_dinv, c->sf_y, c->sf_z, z, c->ps, c->ts, dp,
-                                                      dT, c->ks), note_launch());
+    T *y = (T *)c->sf_y, *zz = (T *)c->sf_z;
+    (k_sf_fill<T><<<4 * 152, 256, 0, s>>>((int64_t)n * B, y, zz, c->sf_ticket), note_launch());
+    if (c->inject_wait) (k_sf_fill<double><<<1, 32, 0, s>>>(1, c->never, c->never, c->sf_ticket + 2), note_launch());
+    int pf = prof_begin(c, PF_ILU_FWD);
+    (k_ilu_fwd_sf<B, T, RT><<<grid, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_f, c->sf_off_f, c->sf_col_f,
+                                                         (const T *)c->sf_val_f, r, y, c->ks,
+                                                         c->inject_wait ? c->never : nullptr), note_launch());
+    prof_end(c, pf);
+    pf = prof_begin(c, PF_ILU_BWD);
+    (k_ilu_bwd_sf<B, T, XT><<<grid, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_b, c->sf_bmap, c->sf_off_b,
+                                                         c->sf_col_b, (const T *)c->sf_val_b, (const T *)c->sf_dinv, y,
+                                                         zz, z, c->ps, c->ts, dp, dT, c->ks), note_launch());
+    prof_end(c, pf);
+}
+
+void ilu_apply(const Ctx *c, const double *r, double *z, const double *dp, const double *dT) {
+    if (c->o.precision == CPTR_PREC_MIXED) {
+        if (c->b == 3) sweeps<3, float, double, double>(c, r, z, dp, dT);
+        else sweeps<4, float, double, double>(c, r, z, dp, dT);
     } else {
-        (k_ilu_fwd_sf<4><<<grid, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_f, c->sf_off_f, c->sf_col_f, c->sf_val_f,
-                                                      r, c->sf_y, c->ks, c->inject_wait ? c->never : nullptr), note_launch());
-        (k_ilu_bwd_sf<4><<<grid, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_b, c->sf_bmap, c->sf_off_b, c->sf_col_b,
-                                                      c->sf_val_b, c->sf_dinv, c->sf_y, c->sf_z, z, c->ps, c->ts, dp,
-                                                      dT, c->ks), note_launch());
+        if (c->b == 3) sweeps<3, double, double, double>(c, r, z, dp, dT);
+        else sweeps<4, double, double, double>(c, r, z, dp, dT);
     }
+}
+
+// mixed-precision form: r, dp, dT in FP32, factors FP32, z FP64
+void ilu_apply32(const Ctx *c, const float *r, double *z, const float *dp, const float *dT) {
+    if (c->b == 3) sweeps<3, float, float, float>(c, r, z, dp, dT);
+    else sweeps<4, float, float, float>(c, r, z, dp, dT);
 }
 
 // z = (LU)^{-1} r with caller-supplied intermediate vectors ybuf, zbuf (n*b doubles each);

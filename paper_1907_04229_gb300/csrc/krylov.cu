@@ -196,16 +196,16 @@ __global__ void __launch_bounds__(256) k_update_x(int64_t nb, const double *__re
     }
 }
 
-__global__ void k_add_x1(int32_t n, int b, int ps, int ts, const double *dp, const double *dT, const double *b1,
-                         double *z) {
+template <typename XT>
+__global__ void k_add_x1(int32_t n, int b, int ps, int ts, const XT *dp, const XT *dT, const XT *b1, double *z) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int q = 0; q < b; ++q) {
         int64_t o = (int64_t)i * b + q;
         double add = 0.0;
-        if (dp && q == ps) add = dp[i];
-        if (dT && q == ts) add = dT[i];
-        z[o] = b1[o] + add;
+        if (dp && q == ps) add = (double)dp[i];
+        if (dT && q == ts) add = (double)dT[i];
+        z[o] = (double)b1[o] + add;
     }
 }
 
@@ -218,7 +218,7 @@ void apply_stage1(const Ctx *c, const double *v, const double **pdp, const doubl
     *pdT = nullptr;
     int mode = c->o.stage1;
     if (mode == CPTR_STAGE1_NONE) return;
-    launch_gather_pt(c, v, c->bp, c->bT);
+    launch_gather_pt<double>(c, v, c->bp, c->bT);
     switch (mode) {
     case CPTR_STAGE1_FULL:
         amg_vcycle(c, c->hp, c->bp, c->xp);                     // 1. A_pp x_p = b_p
@@ -250,8 +250,79 @@ void apply_stage1(const Ctx *c, const double *v, const double **pdp, const doubl
     *pdT = c->dT;
 }
 
+// stage 1 of the mixed-precision form: the same steps in FP32 vectors with the FP32/BF16 hierarchy
+void apply_stage1_32(const Ctx *c, const double *v, const float **pdp, const float **pdT) {
+    cudaStream_t s = c->stream;
+    const int32_t n = c->n, nnz = c->nnzb;
+    auto Tp = [&](const float *x, float *y, const float *c0) {   // y = c0 - A_Tp x
+        launch_csr_spmv_t<float, float>(s, n, nnz, c->rp, c->ci, c->ATp32, x, y, 1, c0);
+    };
+    auto pT = [&](const float *x, float *y, const float *c0) {   // y = c0 - A_pT x
+        launch_csr_spmv_t<float, float>(s, n, nnz, c->rp, c->ci, c->ApT32, x, y, 1, c0);
+    };
+    *pdp = nullptr;
+    *pdT = nullptr;
+    int mode = c->o.stage1;
+    if (mode == CPTR_STAGE1_NONE) return;
+    launch_gather_pt<float>(c, v, c->bp32, c->bT32);
+    switch (mode) {
+    case CPTR_STAGE1_FULL:
+        amg_vcycle32(c, c->hp, c->bp32, c->xp32);
+        Tp(c->xp32, c->t132, c->bT32);
+        amg_vcycle32(c, c->hT, c->t132, c->dT32);
+        pT(c->dT32, c->t132, c->bp32);
+        amg_vcycle32(c, c->hp, c->t132, c->dp32);
+        break;
+    case CPTR_STAGE1_LOWER:
+        amg_vcycle32(c, c->hp, c->bp32, c->dp32);
+        Tp(c->dp32, c->t132, c->bT32);
+        amg_vcycle32(c, c->hT, c->t132, c->dT32);
+        break;
+    case CPTR_STAGE1_UPPER:
+        amg_vcycle32(c, c->hT, c->bT32, c->dT32);
+        pT(c->dT32, c->t132, c->bp32);
+        amg_vcycle32(c, c->hp, c->t132, c->dp32);
+        break;
+    case CPTR_STAGE1_BD:
+        amg_vcycle32(c, c->hp, c->bp32, c->dp32);
+        amg_vcycle32(c, c->hT, c->bT32, c->dT32);
+        break;
+    case CPTR_STAGE1_CPR:
+        amg_vcycle32(c, c->hp, c->bp32, c->dp32);
+        *pdp = c->dp32;
+        return;
+    }
+    *pdp = c->dp32;
+    *pdT = c->dT32;
+}
+
+static void apply_precond32(const Ctx *c, const double *v, double *z) {
+    const float *dp, *dT;
+    int pf = prof_begin(c, PF_STAGE1);
+    apply_stage1_32(c, v, &dp, &dT);
+    prof_end(c, pf);
+    if (!dp) {   // no first stage: second stage on v itself
+        pf = prof_begin(c, PF_ILU);
+        if (c->o.stage2 == CPTR_STAGE2_ILU0) ilu_apply(c, v, z, (const double *)nullptr, (const double *)nullptr);
+        else cudaMemcpyAsync(z, v, sizeof(double) * (size_t)c->n * c->b, cudaMemcpyDeviceToDevice, c->stream);
+        prof_end(c, pf);
+        return;
+    }
+    pf = prof_begin(c, PF_RESID);
+    launch_resid_pt32(c, dp, dT, v, c->b132);
+    prof_end(c, pf);
+    pf = prof_begin(c, PF_ILU);
+    if (c->o.stage2 == CPTR_STAGE2_ILU0) ilu_apply32(c, c->b132, z, dp, dT);
+    else (k_add_x1<float><<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->ps, c->ts, dp, dT, c->b132, z), note_launch());
+    prof_end(c, pf);
+}
+
 // z = M2^{-1}(v - A' x1) + x1, x1 = M1^{-1} v  (Sec. 3, two-stage preconditioners)
 void apply_precond(const Ctx *c, const double *v, double *z) {
+    if (c->o.precision == CPTR_PREC_MIXED) {
+        apply_precond32(c, v, z);
+        return;
+    }
     const double *dp, *dT;
     int pf = prof_begin(c, PF_STAGE1);
     apply_stage1(c, v, &dp, &dT);
@@ -268,7 +339,7 @@ void apply_precond(const Ctx *c, const double *v, double *z) {
         ilu_apply(c, b1, z, dp, dT);
         prof_end(c, pf);
     } else {
-        (k_add_x1<<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->ps, c->ts, dp, dT, b1, z), note_launch());
+        (k_add_x1<double><<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->ps, c->ts, dp, dT, b1, z), note_launch());
     }
 }
 

@@ -54,6 +54,8 @@ extern "C" cptr_status cptr_apply_ilu_static(cptr_ctx *ctx, const double *r, dou
     c->err.clear();
     if (!c->ready) return c->fail(CPTR_ESTATE, "no successful cptr_setup on this context");
     if (c->o.stage2 != CPTR_STAGE2_ILU0) return c->fail(CPTR_ESTATE, "ILU(0) was not set up");
+    if (c->o.ilu_order != CPTR_ILU_NATURAL)
+        return c->fail(CPTR_EINVAL, "cptr_apply_ilu_static supports the natural ILU ordering only");
     if (!r || !z) return c->fail(CPTR_EINVAL, "r and z are required");
     const int64_t nb = (int64_t)c->n * c->b;
     if (nb > kStaticIluMax)

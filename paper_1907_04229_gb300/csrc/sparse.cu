@@ -306,6 +306,7 @@ cptr_status sell_build(Ctx *c) {
     CPTR_CUDA_TRY(c, cudaGetLastError());
     CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     c->sell_bytes = slots * (4 + 8 * B * B) + (nch + 1) * 8;
+    c->sell_nvals = slots * B * B;
     return CPTR_OK;
 }
 
@@ -391,20 +392,27 @@ void launch_bsr_resid_pt(const Ctx *c, const double *dp, const double *dT, const
 }
 
 // ------------------------------------------------------------------------------------------------
-// scalar CSR SpMV with G lanes per row: y = alpha * A x, or y = c0 - A x when c0 != nullptr
-// (alpha ignored), or y += A x when alpha == 2 (prolongation-add)
-template <int G>
+// scalar CSR SpMV with G lanes per row, values VT (double, float or bf16), vectors and sums XT:
+// mode 0 y = A x, mode 1 y = c0 - A x, mode 2 y += A x
+__device__ __forceinline__ double val_ld(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float val_ld(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float val_ld(const bf16 *p) {
+    return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p))));
+}
+
+template <int G, typename VT, typename XT>
 __global__ void __launch_bounds__(256) k_csr_spmv(int32_t n, const int32_t *__restrict__ rp,
-                                                   const int32_t *__restrict__ ci, const double *__restrict__ v,
-                                                   const double *__restrict__ x, double *__restrict__ y, int mode,
-                                                   const double *__restrict__ c0) {
+                                                   const int32_t *__restrict__ ci, const VT *__restrict__ v,
+                                                   const XT *__restrict__ x, XT *__restrict__ y, int mode,
+                                                   const XT *__restrict__ c0) {
     int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int32_t row = (int32_t)(gid / G);
     int lane = threadIdx.x % G;
-    double acc = 0.0;
+    XT acc = 0;
     if (row < n) {
         int32_t k1 = __ldg(rp + row + 1);
-        for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G) acc = fma(__ldg(v + k), __ldg(x + __ldg(ci + k)), acc);
+        for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G)
+            acc = fma((XT)val_ld(v + k), __ldg(x + __ldg(ci + k)), acc);
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
@@ -415,38 +423,136 @@ __global__ void __launch_bounds__(256) k_csr_spmv(int32_t n, const int32_t *__re
     }
 }
 
+template <typename VT, typename XT>
+void launch_csr_spmv_t(cudaStream_t s, int32_t n, int32_t nnz, const int32_t *rp, const int32_t *ci, const VT *v,
+                       const XT *x, XT *y, int mode, const XT *c0) {
+    int G = lanes_for(n, nnz);
+    unsigned grid = nblk((int64_t)n * G, 256);
+    switch (G) {
+    case 4: (k_csr_spmv<4, VT, XT><<<grid, 256, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
+    case 8: (k_csr_spmv<8, VT, XT><<<grid, 256, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
+    case 16: (k_csr_spmv<16, VT, XT><<<grid, 256, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
+    default: (k_csr_spmv<32, VT, XT><<<grid, 256, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
+    }
+}
+template void launch_csr_spmv_t<double, double>(cudaStream_t, int32_t, int32_t, const int32_t *, const int32_t *,
+                                                const double *, const double *, double *, int, const double *);
+template void launch_csr_spmv_t<float, float>(cudaStream_t, int32_t, int32_t, const int32_t *, const int32_t *,
+                                              const float *, const float *, float *, int, const float *);
+template void launch_csr_spmv_t<bf16, float>(cudaStream_t, int32_t, int32_t, const int32_t *, const int32_t *,
+                                             const bf16 *, const float *, float *, int, const float *);
+
 void launch_csr_spmv(cudaStream_t s, const Csr &A, const double *x, double *y, double alpha, const double *c0) {
     int mode = c0 ? 1 : (alpha == 2.0 ? 2 : 0);
-    int G = lanes_for(A.n, A.nnz);
-    unsigned grid = nblk((int64_t)A.n * G, 256);
-    switch (G) {
-    case 4: (k_csr_spmv<4><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, x, y, mode, c0), note_launch()); break;
-    case 8: (k_csr_spmv<8><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, x, y, mode, c0), note_launch()); break;
-    case 16: (k_csr_spmv<16><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, x, y, mode, c0), note_launch()); break;
-    default: (k_csr_spmv<32><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, x, y, mode, c0), note_launch()); break;
+    launch_csr_spmv_t<double, double>(s, A.n, A.nnz, A.rp, A.ci, A.v, x, y, mode, c0);
+}
+
+// FP64 -> FP32 (round to nearest) or FP64 -> FP32 -> BF16 (round to nearest even): the storage
+// rounding of the mixed-precision form
+__global__ void k_to_lower(const double *src, int64_t n, int st, void *dst) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < n; i += stride) {
+        float f = __double2float_rn(src[i]);
+        if (st == ST_BF16) static_cast<bf16 *>(dst)[i] = __float2bfloat16_rn(f);
+        else static_cast<float *>(dst)[i] = f;
     }
+}
+__global__ void k_d2f_vec(const double *a, float *b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+__global__ void k_f2d_vec(const float *a, double *b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+void launch_d2f(const Ctx *c, const double *a, float *b, int64_t n) {
+    (k_d2f_vec<<<nblk(n, 256), 256, 0, c->stream>>>(a, b, n), note_launch());
+}
+void launch_f2d(const Ctx *c, const float *a, double *b, int64_t n) {
+    (k_f2d_vec<<<nblk(n, 256), 256, 0, c->stream>>>(a, b, n), note_launch());
+}
+
+cptr_status to_lower(Ctx *c, const double *src, int64_t n, int st, void **dst) {
+    size_t bytes = (size_t)(n > 0 ? n : 1) * (st == ST_BF16 ? 2 : 4);
+    CPTR_TRY(dalloc(c, dst, bytes));
+    if (n > 0) (k_to_lower<<<4 * 152, 256, 0, c->stream>>>(src, n, st, *dst), note_launch());
+    return CPTR_OK;
 }
 
 // ------------------------------------------------------------------------------------------------
 // restriction to / prolongation from the p-T unknowns (Sec. 3.2)
-__global__ void k_gather_pt(int32_t n, int b, int ps, int ts, const double *v, double *bp, double *bT) {
+template <typename XT>
+__global__ void k_gather_pt(int32_t n, int b, int ps, int ts, const double *v, XT *bp, XT *bT) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        bp[i] = v[(int64_t)i * b + ps];
-        bT[i] = v[(int64_t)i * b + ts];
+        bp[i] = (XT)v[(int64_t)i * b + ps];
+        bT[i] = (XT)v[(int64_t)i * b + ts];
     }
 }
-void launch_gather_pt(const Ctx *c, const double *v, double *bp, double *bT) {
-    (k_gather_pt<<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->ps, c->ts, v, bp, bT), note_launch());
+template <typename XT>
+void launch_gather_pt(const Ctx *c, const double *v, XT *bp, XT *bT) {
+    (k_gather_pt<XT><<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->ps, c->ts, v, bp, bT), note_launch());
 }
-__global__ void k_scatter_pt(int32_t n, int b, int ps, int ts, const double *dp, const double *dT, double *x1) {
+template void launch_gather_pt<double>(const Ctx *, const double *, double *, double *);
+template void launch_gather_pt<float>(const Ctx *, const double *, float *, float *);
+
+template <typename XT>
+__global__ void k_scatter_pt(int32_t n, int b, int ps, int ts, const XT *dp, const XT *dT, double *x1) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n)
-        for (int q = 0; q < b; ++q) x1[(int64_t)i * b + q] = q == ps ? dp[i] : (q == ts && dT ? dT[i] : 0.0);
+        for (int q = 0; q < b; ++q) x1[(int64_t)i * b + q] = q == ps ? (double)dp[i] : (q == ts && dT ? (double)dT[i] : 0.0);
 }
-void launch_scatter_pt(const Ctx *c, const double *dp, const double *dT, double *x1) {
-    (k_scatter_pt<<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->ps, c->ts, dp, dT, x1), note_launch());
+template <typename XT>
+void launch_scatter_pt(const Ctx *c, const XT *dp, const XT *dT, double *x1) {
+    (k_scatter_pt<XT><<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->ps, c->ts, dp, dT, x1), note_launch());
 }
+template void launch_scatter_pt<double>(const Ctx *, const double *, const double *, double *);
+template void launch_scatter_pt<float>(const Ctx *, const float *, const float *, double *);
+
+// mixed-precision stage-1 residual b1 = v - A' R_0^T [dp; dT] with FP32 values of A' (SELL-32)
+template <int B>
+__global__ void __launch_bounds__(256) k_sell_resid_pt32(int32_t n, const int64_t *__restrict__ off,
+                                                          const int32_t *__restrict__ col,
+                                                          const float *__restrict__ val, const double *__restrict__ v,
+                                                          float *__restrict__ b1, int ps, int ts,
+                                                          const float *__restrict__ dp, const float *__restrict__ dT) {
+    int32_t row = blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t ch = row >> 5, lane = row & 31;
+    if (row >= ((n + 31) & ~31)) return;
+    const int64_t o0 = __ldg(off + ch), o1 = __ldg(off + ch + 1);
+    float acc[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) acc[r] = 0.f;
+    for (int64_t sl = o0; sl < o1; ++sl) {
+        const int32_t cidx = __ldg(col + sl * 32 + lane);
+        const float *a = val + sl * B * B * 32 + lane;
+        const float xp = __ldg(dp + cidx);
+        const float xt = dT ? __ldg(dT + cidx) : 0.f;
+#pragma unroll
+        for (int r = 0; r < B; ++r) {
+            acc[r] = fmaf(__ldg(a + (r * B + ps) * 32), xp, acc[r]);
+            if (dT) acc[r] = fmaf(__ldg(a + (r * B + ts) * 32), xt, acc[r]);
+        }
+    }
+    if (row < n) {
+#pragma unroll
+        for (int r = 0; r < B; ++r) {
+            int64_t oo = (int64_t)row * B + r;
+            b1[oo] = (float)v[oo] - acc[r];
+        }
+    }
+}
+void launch_resid_pt32(const Ctx *c, const float *dp, const float *dT, const double *v, float *b1) {
+    unsigned grid = nblk((int64_t)c->sell_nch * 32, 256);
+    if (c->b == 3)
+        (k_sell_resid_pt32<3><<<grid, 256, 0, c->stream>>>(c->n, c->sell_off, c->sell_col, c->sell_val32, v, b1, c->ps,
+                                                            c->ts, dp, dT), note_launch());
+    else
+        (k_sell_resid_pt32<4><<<grid, 256, 0, c->stream>>>(c->n, c->sell_off, c->sell_col, c->sell_val32, v, b1, c->ps,
+                                                            c->ts, dp, dT), note_launch());
+}
+
 __global__ void k_sub(int32_t n, const double *a, const double *b, double *out) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = a[i] - b[i];

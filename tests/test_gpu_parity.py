@@ -266,12 +266,71 @@ def test_graph_and_direct_launches_agree(use_graph):
 @pytest.mark.parametrize("use_graph", [0, 1])
 def test_profiling_counts_match_iterations(use_graph):
     s, o, g = pair("parity", use_graph=use_graph)
-    cp.cptr_set_profiling(g.ctx, 0b11111)
+    cp.cptr_set_profiling(g.ctx, 0b1111111)
     x, info = g.solve(dev(s["rhs"].reshape(-1)), 1e-8)
     prof = cp.cptr_profile(g.ctx)
-    for fam in ("spmv", "stage1", "stage1_resid", "ilu", "arnoldi"):
+    for fam in ("spmv", "stage1", "stage1_resid", "ilu", "arnoldi", "ilu_fwd", "ilu_bwd"):
         ms, n = prof[fam]
         assert n == info["iters"] and ms > 0.0, (fam, prof[fam])
     l0 = cp.cptr_launch_count()
     g.solve(dev(s["rhs"].reshape(-1)), 1e-8)
     assert cp.cptr_launch_count() - l0 > 20 * info["iters"]
+
+
+@pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "medium"])
+def test_multicolour_ilu_and_solve(name):
+    s, o, g = pair(name, ilu_order=1)
+    nf, nbk = cp.cptr_ilu_levels(g.ctx)
+    assert nf == 2 and nbk == 2        # red-black on a 7-point grid
+    nb = s["n"] * s["b"]
+    r = synth.normal(5, nb)
+    z = torch.empty(nb, dtype=torch.float64, device="cuda")
+    cp.cptr_apply_ilu(g.ctx, dev(r), z)
+    assert relerr(host(z), o.ilu_apply(r)) <= 1e-10
+    check_solve(s, o, g, 1e-8)
+
+
+# ------------------------------------------------------------------------------------------------
+# mixed-precision form: FP32 AMG (BF16 on levels >= 2) and FP32 ILU(0), FP64 Krylov.
+# The oracle with precision=1 stores the same rounded values and keeps FP64 arithmetic, so a
+# V-cycle differs only by FP32 arithmetic (unit roundoff 6e-8, a few dozen dependent operations
+# per entry, amplified by the coarsest solve): 1e-5 relative.  The preconditioner also differs by
+# the FP32 ILU factors (the oracle's ILU stays FP64): 1e-4 relative.  Solves must reach the FP64
+# true residual; their distance from the FP64 oracle's solution is reported and bounded by
+# 1e-4 per unknown kind.
+@pytest.mark.parametrize("name", ["parity", "ragged", "medium"])
+def test_mixed_vcycle_matches_rounded_oracle(name):
+    s, o, g = pair(name, precision=1)
+    for which in (0, 1):
+        b = synth.normal(21 + which, s["n"])
+        x = torch.empty(s["n"], dtype=torch.float64, device="cuda")
+        cp.cptr_apply_vcycle(g.ctx, which, dev(b), x)
+        assert relerr(host(x), o.vcycle(which, b)) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "medium"])
+def test_mixed_preconditioner(name):
+    s, o, g = pair(name, precision=1)
+    nb = s["n"] * s["b"]
+    v = synth.normal(9, nb)
+    z = torch.empty(nb, dtype=torch.float64, device="cuda")
+    cp.cptr_apply_precond(g.ctx, dev(v), z)
+    assert relerr(host(z), o.precond(v)) <= 1e-4
+
+
+@pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "medium"])
+def test_mixed_solve_reaches_fp64_residual(name):
+    s, o, g = pair(name, precision=1)
+    x_g, info = g.solve(dev(s["rhs"].reshape(-1)), 1e-8)
+    assert info["status"] == "CPTR_OK" and info["true_rel_res"] <= 1.05e-8
+    xg = host(x_g)
+    # independent residual check with the oracle's FP64 matrix on the host
+    bw = o.weight_rhs(s["rhs"].reshape(-1))
+    assert np.linalg.norm(bw - o.spmv(xg)) <= 1.05e-8 * np.linalg.norm(bw)
+    x_o, io = o.solve(s["rhs"], 1e-8)
+    assert abs(info["iters"] - io["iters"]) <= 2, (info["iters"], io["iters"])
+    o64 = oracle.Oracle.from_system(s, **OPTS[name])
+    x64, i64 = o64.solve(s["rhs"], 1e-8)
+    b = s["b"]
+    for u in range(b):
+        assert relerr(xg[u::b], x64[u::b]) <= 1e-4, (u, relerr(xg[u::b], x64[u::b]))

@@ -498,3 +498,96 @@ def test_cptr_needs_fewer_iterations_than_cpr_when_conduction_dominates():
         assert info["converged"]
         its[mode] = info["iters"]
     assert its[oracle.CPTR_FULL] < its[oracle.CPR], its
+
+
+# ------------------------------------------------------------------------------------------------
+# multicolour ordering of ILU(0) (a reading: the paper does not state the ILU ordering)
+def test_multicolour_order_is_red_black_on_a_grid():
+    r = tiny(5, 4, 3)
+    o = oracle.Oracle.from_system(r.system(), max_levels=1, ilu_order=1)
+    order = o.ilu_order()
+    idx = np.arange(r.n)
+    x, y, z = idx % r.nx, (idx // r.nx) % r.ny, idx // (r.nx * r.ny)
+    parity = (x + y + z) % 2
+    assert np.array_equal(order, np.concatenate([idx[parity == 0], idx[parity == 1]]))
+
+
+def _block_ilu_solve(s, order, rvec):
+    """Textbook block ILU(0) of the cell-permuted system, then the solve, in original order."""
+    n, b = s["n"], s["b"]
+    rp, ci, W = s["row_ptr"], s["col_idx"], s["weights"]
+    inv = np.empty(n, int)
+    inv[order] = np.arange(n)
+    blocks, rows = {}, []
+    for I in range(n):
+        i = order[I]
+        cols = []
+        for k in range(rp[i], rp[i + 1]):
+            J = int(inv[ci[k]])
+            blocks[(I, J)] = W[i] @ s["vals"][k]
+            cols.append(J)
+        rows.append(sorted(cols))
+    for I in range(n):
+        for K in [c for c in rows[I] if c < I]:
+            blocks[(I, K)] = blocks[(I, K)] @ np.linalg.inv(blocks[(K, K)])
+            for J in [c for c in rows[I] if c > K]:
+                if (K, J) in blocks:
+                    blocks[(I, J)] = blocks[(I, J)] - blocks[(I, K)] @ blocks[(K, J)]
+    rr = rvec.reshape(n, b)[order]
+    yv = np.zeros((n, b))
+    for I in range(n):
+        yv[I] = rr[I] - sum(blocks[(I, K)] @ yv[K] for K in rows[I] if K < I)
+    zv = np.zeros((n, b))
+    for I in reversed(range(n)):
+        t = yv[I] - sum(blocks[(I, K)] @ zv[K] for K in rows[I] if K > I)
+        zv[I] = np.linalg.solve(blocks[(I, I)], t)
+    out = np.zeros((n, b))
+    out[order] = zv
+    return out.reshape(-1)
+
+
+def test_multicolour_ilu0_equals_block_ilu0_of_permuted_system():
+    s = tiny(4, 3, 2).system()
+    o = oracle.Oracle.from_system(s, max_levels=1, dense_max=4096, ilu_order=1)
+    r = synth.normal(8, s["n"] * s["b"])
+    ref = _block_ilu_solve(s, o.ilu_order(), r)
+    assert np.linalg.norm(o.ilu_apply(r) - ref) <= 1e-10 * np.linalg.norm(ref)
+    # and it is a different operator from the natural-order ILU(0)
+    o0 = oracle.Oracle.from_system(s, max_levels=1, dense_max=4096)
+    assert np.linalg.norm(o0.ilu_apply(r) - ref) > 1e-6 * np.linalg.norm(ref)
+
+
+def test_multicolour_cptr_converges():
+    s = synth.recipe("parity").system()
+    x, info = oracle.Oracle.from_system(s, max_levels=2, ilu_order=1).solve(s["rhs"], 1e-8)
+    assert info["converged"] and info["true_rel_res"] <= 1e-8
+
+
+# ------------------------------------------------------------------------------------------------
+# storage rounding of the mixed-precision form
+def test_bf16_rounding_closed_forms():
+    # bf16 keeps 8 significant bits: spacing 2^-7 in [1, 2); round to nearest, ties to even
+    assert oracle.round_bf16(1.0) == 1.0
+    assert oracle.round_bf16(1.0 + 2.0 ** -8) == 1.0                    # tie -> even (1.0)
+    assert oracle.round_bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2 * 2.0 ** -7  # tie -> even (odd neighbour up)
+    assert oracle.round_bf16(1.0 + 2.0 ** -8 + 2.0 ** -20) == 1.0 + 2.0 ** -7
+    assert oracle.round_bf16(-3.0) == -3.0
+    assert oracle.round_bf16(2.0 ** -130) > 0.0                          # subnormal range survives
+    for x in synth.normal(3, 1000) * 1e3:
+        y = oracle.round_bf16(float(x))
+        assert abs(y - x) <= 2.0 ** -8 * abs(x)   # unit roundoff of 8 significant bits
+
+
+def test_mixed_precision_oracle_rounds_the_hierarchy():
+    s = synth.recipe("parity").system()
+    o64 = oracle.Oracle.from_system(s, n_coarse=8)
+    o16 = oracle.Oracle.from_system(s, n_coarse=8, precision=1)
+    l64, l16 = o64.levels(0), o16.levels(0)
+    assert len(l64) == len(l16) >= 3
+    for l, (a, b) in enumerate(zip(l64, l16)):
+        assert np.array_equal(a["ci"], b["ci"])          # same hierarchy, rounded values
+        rounded = np.array([oracle.round_bf16(v) for v in a["v"]]) if l >= 2 else a["v"].astype(np.float32).astype(np.float64)
+        assert np.array_equal(b["v"], rounded)
+    x, info = o16.solve(s["rhs"], 1e-8)
+    x64, i64 = o64.solve(s["rhs"], 1e-8)
+    assert info["converged"] and abs(info["iters"] - i64["iters"]) <= 2
