@@ -211,9 +211,7 @@ def ours(args, rank, world, local_rank):
     clk = clocks.stop()
     cp.cptr_set_profiling(S.ctx, 0)
     total_ms = sum(a.elapsed_time(bb) for a, bb in events)
-    total_ms = allreduce_max(total_ms, world, dev)
-    ms_per_step = total_ms / args.steps
-    value = world * dofs * args.steps / (total_ms / 1e3)
+    value, ms_per_step = aggregate(total_ms, world, dofs, args.steps, dev)
     setup_ms = statistics.mean(i["setup_ms"] for i in infos)
     solve_ms = statistics.mean(i["solve_ms"] for i in infos)
     iters = infos[-1]["iters"]
@@ -357,6 +355,13 @@ def barrier(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def aggregate(total_ms_local, world, dofs_per_rank, steps, dev):
+    """Whole-job throughput of independent replicas: every rank solved `steps` systems of
+    `dofs_per_rank` unknowns; the job took the slowest rank's time.  Returns (dofs/s, ms/step)."""
+    total_ms = allreduce_max(total_ms_local, world, dev)
+    return world * dofs_per_rank * steps / (total_ms / 1e3), total_ms / steps
 
 
 def allreduce_max(v, world, dev):

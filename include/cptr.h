@@ -213,9 +213,11 @@ int64_t cptr_launch_count(void);
 cptr_status cptr_set_profiling(cptr_ctx *ctx, uint32_t mask);
 
 /* Event time (ms) and number of timed regions per family during the last cptr_solve (host
- * arrays of 16 entries; either may be NULL): entries 0-7 the families above; entries 8, 9, 10
- * the host-clock time of the last cptr_setup's phases (inputs + decoupling + extraction, both
- * AMG hierarchies, ILU(0) + SELL layout), with count 1. */
+ * arrays of 16 entries; either may be NULL): entries 0-7 the families above; entries 8-15 the
+ * host-clock time of the last cptr_setup's phases, with count 1: 8 inputs + decoupling +
+ * extraction, 9 AMG coarsening (strength, PMIS, interpolation), 10 AMG Galerkin products,
+ * 11 AMG coarsest inverses, 12 ILU host work (ordering, level sets, sweep tables), 13 ILU
+ * factorisation, 14 SELL layout and mixed-precision copies, 15 other. */
 cptr_status cptr_profile(cptr_ctx *ctx, double *ms, int64_t *count);
 
 #ifdef __cplusplus

@@ -76,7 +76,8 @@ _SIGS = {
     "cptr_profile": (_I, [_P, _P, _P]),
 }
 PROFILE_FAMILIES = ("spmv", "stage1", "stage1_resid", "ilu", "arnoldi", "ilu_fwd", "ilu_bwd", "_7")
-SETUP_PHASES = {8: "setup_inputs", 9: "setup_amg", 10: "setup_ilu"}
+SETUP_PHASES = {8: "setup_inputs", 9: "setup_amg_coarsen", 10: "setup_amg_rap", 11: "setup_amg_coarsest",
+                12: "setup_ilu_host", 13: "setup_ilu_factor", 14: "setup_layout", 15: "setup_other"}
 
 
 def load():

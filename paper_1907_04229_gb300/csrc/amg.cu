@@ -212,6 +212,65 @@ __global__ void k_interp_fill(int32_t n, const int32_t *rp, const int32_t *ci, c
 // separately rounded multiply and add; output columns ascending.  NUM = false counts entries.
 constexpr int kMergeMax = 256;
 constexpr int kMergeThreads = 32;
+constexpr int kWarpMergeMax = 64;
+
+// The same product with one warp per output row for rows that merge at most 64 rows of B: lane
+// l holds the heads of the B rows selected by entries l and l + 32 of A's row; each step finds
+// the smallest head column with a warp min-reduction, and lane 0 adds the matching products in
+// ascending entry order (separately rounded multiply and add, as in the per-thread kernel).
+template <bool NUM>
+__global__ void __launch_bounds__(256) k_spgemm_warp(int32_t n, const int32_t *__restrict__ Arp,
+                                                      const int32_t *__restrict__ Aci, const double *__restrict__ Av,
+                                                      const int32_t *__restrict__ Brp, const int32_t *__restrict__ Bci,
+                                                      const double *__restrict__ Bv, const int32_t *__restrict__ Crp,
+                                                      int32_t *Cci_or_cnt, double *Cv) {
+    const int32_t row = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;                      // whole warp
+    const int32_t a0 = Arp[row], m = Arp[row + 1] - a0;
+    if (m > kWarpMergeMax) return;             // done by k_spgemm_merge
+    int32_t p0 = 0, e0 = 0, p1 = 0, e1 = 0;
+    double x0 = 0.0, x1 = 0.0;
+    if (lane < m) {
+        int32_t l = Aci[a0 + lane];
+        p0 = Brp[l]; e0 = Brp[l + 1]; x0 = Av[a0 + lane];
+    }
+    if (lane + 32 < m) {
+        int32_t l = Aci[a0 + lane + 32];
+        p1 = Brp[l]; e1 = Brp[l + 1]; x1 = Av[a0 + lane + 32];
+    }
+    int32_t out = NUM ? Crp[row] : 0;
+    int32_t cnt = 0;
+    for (;;) {
+        const int32_t h0 = p0 < e0 ? Bci[p0] : INT32_MAX;
+        const int32_t h1 = p1 < e1 ? Bci[p1] : INT32_MAX;
+        const int32_t jmin = __reduce_min_sync(0xffffffffu, min(h0, h1));
+        if (jmin == INT32_MAX) break;
+        const bool m0 = h0 == jmin, m1 = h1 == jmin;
+        if (NUM) {
+            const double q0 = m0 ? __dmul_rn(x0, Bv[p0]) : 0.0;
+            const double q1 = m1 ? __dmul_rn(x1, Bv[p1]) : 0.0;
+            unsigned b0 = __ballot_sync(0xffffffffu, m0), b1 = __ballot_sync(0xffffffffu, m1);
+            double acc = 0.0;
+            while (b0) {
+                const int l = __ffs(b0) - 1;
+                acc = __dadd_rn(acc, __shfl_sync(0xffffffffu, q0, l));
+                b0 &= b0 - 1;
+            }
+            while (b1) {
+                const int l = __ffs(b1) - 1;
+                acc = __dadd_rn(acc, __shfl_sync(0xffffffffu, q1, l));
+                b1 &= b1 - 1;
+            }
+            if (lane == 0) { Cci_or_cnt[out] = jmin; Cv[out] = acc; }
+            ++out;
+        }
+        if (m0) ++p0;
+        if (m1) ++p1;
+        ++cnt;
+    }
+    if (!NUM && lane == 0) Cci_or_cnt[row] = cnt;
+}
 
 template <bool NUM>
 __global__ void __launch_bounds__(kMergeThreads) k_spgemm_merge(int32_t n, const int32_t *Arp, const int32_t *Aci,
@@ -223,6 +282,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_spgemm_merge(int32_t n, const
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t a0 = Arp[i], m = Arp[i + 1] - a0;
+    if (m <= kWarpMergeMax) return;            // done by k_spgemm_warp
     if (m > kMergeMax) { atomicExch(err, 1); return; }
     int32_t *pos = sm, *end = sm + kMergeMax * kMergeThreads;
     const int t = threadIdx.x, T = kMergeThreads;
@@ -353,16 +413,20 @@ static cptr_status spgemm(Ctx *c, const Csr &A, const Csr &B, int32_t ncb, Csr &
     size_t smem = sizeof(int32_t) * 2 * kMergeMax * kMergeThreads;
     CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_spgemm_merge<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_spgemm_merge<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    (k_spgemm_warp<false><<<nblk((int64_t)A.n * 32, 256), 256, 0, c->stream>>>(
+        A.n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, nullptr, cnt, nullptr), note_launch());
     (k_spgemm_merge<false><<<nblk(A.n, kMergeThreads), kMergeThreads, smem, c->stream>>>(
         A.n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, nullptr, cnt, nullptr, c->flag), note_launch());
     int32_t total = 0;
     CPTR_TRY(scan_exclusive(c, cnt, C.rp, A.n, &total));
     int32_t bad = 0;
-    CPTR_CUDA_TRY(c, cudaMemcpy(&bad, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CPTR_TRY(copy_to_host(c, &bad, c->flag, sizeof(int32_t)));
     if (bad) return c->fail(CPTR_EINVAL, "AMG: a row of the Galerkin product merges more than 256 rows");
     C.nnz = total;
     CPTR_TRY(dalloc_t(c, &C.ci, (size_t)total));
     CPTR_TRY(dalloc_t(c, &C.v, (size_t)total));
+    (k_spgemm_warp<true><<<nblk((int64_t)A.n * 32, 256), 256, 0, c->stream>>>(
+        A.n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp, C.ci, C.v), note_launch());
     (k_spgemm_merge<true><<<nblk(A.n, kMergeThreads), kMergeThreads, smem, c->stream>>>(
         A.n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp, C.ci, C.v, c->flag), note_launch());
     CPTR_CUDA_TRY(c, cudaGetLastError());
@@ -414,16 +478,20 @@ static cptr_status coarsen(Ctx *c, Level &L, int lev, int32_t *nc_out) {
     CPTR_TRY(dalloc_t(c, &newc, (size_t)n));
     CPTR_TRY(dalloc_t(c, &und, 1));
     (k_pmis_init<<<nblk(n, 256), 256, 0, s>>>(n, Srp, Trp, (uint64_t)(int64_t)c->o.seed + (uint64_t)lev, key, state), note_launch());
+    // rounds are launched three at a time between host checks of the undecided count (a round
+    // after the last undecided point is decided changes nothing)
     int rounds = 0;
     for (;;) {
-        (k_pmis_select<<<nblk(n, 256), 256, 0, s>>>(n, Srp, Sci, Trp, Tci, key, state, newc), note_launch());
-        CPTR_CUDA_TRY(c, cudaMemsetAsync(und, 0, sizeof(int32_t), s));
-        (k_pmis_update<<<nblk(n, 256), 256, 0, s>>>(n, Srp, Sci, state, newc, und), note_launch());
+        for (int k = 0; k < 3; ++k) {
+            (k_pmis_select<<<nblk(n, 256), 256, 0, s>>>(n, Srp, Sci, Trp, Tci, key, state, newc), note_launch());
+            CPTR_CUDA_TRY(c, cudaMemsetAsync(und, 0, sizeof(int32_t), s));
+            (k_pmis_update<<<nblk(n, 256), 256, 0, s>>>(n, Srp, Sci, state, newc, und), note_launch());
+        }
         int32_t h_und = 0;
         CPTR_CUDA_TRY(c, cudaMemcpyAsync(&h_und, und, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         CPTR_CUDA_TRY(c, cudaStreamSynchronize(s));
         if (h_und == 0) break;
-        if (++rounds > 100000) return c->fail(CPTR_EINVAL, "AMG: PMIS did not terminate");
+        if ((rounds += 3) > 100000) return c->fail(CPTR_EINVAL, "AMG: PMIS did not terminate");
     }
     // coarse numbering
     CPTR_TRY(dalloc_t(c, &cidx, (size_t)n + 1));
@@ -455,7 +523,7 @@ static cptr_status coarsen(Ctx *c, Level &L, int lev, int32_t *nc_out) {
 cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, const double *v, int32_t n) {
     amg_free(h);
     int32_t nnz = 0;
-    CPTR_CUDA_TRY(c, cudaMemcpy(&nnz, rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CPTR_TRY(copy_to_host(c, &nnz, rp + n, sizeof(int32_t)));
     Csr &A0 = h.L[0].A;
     A0.n = n;
     A0.nnz = nnz;
@@ -474,7 +542,9 @@ cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, con
         nnz_sum += L.A.nnz;
         if (l + 1 >= maxl || L.A.n <= c->o.n_coarse) break;
         int32_t nc = 0;
+        double t0 = host_ms();
         CPTR_TRY(coarsen(c, L, l, &nc));
+        setup_tick(c, SETUP_COARSEN, &t0);
         if (nc == 0 || nc >= L.A.n) {   // no coarsening possible: this level is the coarsest
             csr_free(L.P);
             dfree(L.cf);
@@ -487,6 +557,7 @@ cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, con
         CPTR_TRY(spgemm(c, L.A, L.P, nc, AP));
         CPTR_TRY(spgemm(c, L.PT, AP, nc, h.L[l + 1].A));
         csr_free(AP);
+        setup_tick(c, SETUP_RAP, &t0);
         ++l;
     }
     h.nlev = l + 1;
@@ -494,6 +565,7 @@ cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, con
     Level &C = h.L[l];
     int32_t cn = C.A.n;
     h.dense = 0;
+    double tc = host_ms();
     if (cn <= c->o.dense_max) {
         double *D = nullptr;
         CPTR_TRY(dalloc_t(c, &D, (size_t)cn * cn));
@@ -507,11 +579,12 @@ cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, con
         (k_gauss_jordan<<<1, 1024, smem, c->stream>>>(cn, D, h.cinv, c->flag), note_launch());
         CPTR_CUDA_TRY(c, cudaGetLastError());
         int32_t sing = 0;
-        CPTR_CUDA_TRY(c, cudaMemcpy(&sing, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        CPTR_TRY(copy_to_host(c, &sing, c->flag, sizeof(int32_t)));
         dfree(D);
         if (sing) return c->fail(CPTR_ESINGULAR, "AMG: singular coarsest-level matrix");
         h.dense = 1;
     }
+    setup_tick(c, SETUP_COARSEST, &tc);
     CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return CPTR_OK;
 }

@@ -69,7 +69,7 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     if (b != 3 && b != 4) return c->fail(CPTR_EINVAL, "b must be 3 or 4");
     if (!row_ptr || !col_idx || !vals || !kind) return c->fail(CPTR_EINVAL, "row_ptr, col_idx, vals, unknown_kind are required");
     int32_t hk[4];
-    if (on_device) CPTR_CUDA_TRY(c, cudaMemcpy(hk, kind, sizeof(int32_t) * b, cudaMemcpyDeviceToHost));
+    if (on_device) CPTR_TRY(copy_to_host(c, hk, kind, sizeof(int32_t) * b));
     else memcpy(hk, kind, sizeof(int32_t) * b);
     int ps = -1, ts = -1;
     for (int q = 0; q < b; ++q) {
@@ -79,15 +79,16 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     }
     if (ps < 0 || ts < 0) return c->fail(CPTR_EINVAL, "unknown_kind needs one P and one T slot");
     release_setup(c);
+    for (double &v : c->prof.setup_ms) v = 0.0;
     auto t0 = std::chrono::steady_clock::now();
     // pattern to the host for validation and level scheduling
     c->h_rp.assign((size_t)n + 1, 0);
-    if (on_device) CPTR_CUDA_TRY(c, cudaMemcpy(c->h_rp.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost));
+    if (on_device) CPTR_TRY(copy_to_host(c, c->h_rp.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1)));
     else memcpy(c->h_rp.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1));
     int32_t nnzb = c->h_rp[n];
     if (nnzb <= 0 || c->h_rp[0] != 0) return c->fail(CPTR_EINVAL, "row_ptr must start at 0 and end at nnzb > 0");
     c->h_ci.assign((size_t)nnzb, 0);
-    if (on_device) CPTR_CUDA_TRY(c, cudaMemcpy(c->h_ci.data(), col_idx, sizeof(int32_t) * nnzb, cudaMemcpyDeviceToHost));
+    if (on_device) CPTR_TRY(copy_to_host(c, c->h_ci.data(), col_idx, sizeof(int32_t) * nnzb));
     else memcpy(c->h_ci.data(), col_idx, sizeof(int32_t) * nnzb);
     CPTR_TRY(validate_pattern(c, n));
     c->n = n; c->b = b; c->ps = ps; c->ts = ts; c->nnzb = nnzb;
@@ -135,17 +136,13 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     if (!(st && c->o.schur == CPTR_SCHUR_GIVEN)) launch_extract(c, ts, ts, c->St);
     CPTR_CUDA_TRY(c, cudaGetLastError());
     CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    auto ms_since = [](std::chrono::steady_clock::time_point a) {
-        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
-    };
-    c->prof.setup_ms[0] = ms_since(t0);
-    auto t1 = std::chrono::steady_clock::now();
+    c->prof.setup_ms[SETUP_INPUTS] +=
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     int s1 = c->o.stage1;
     if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_setup(c, c->hp, c->rp, c->ci, c->App, n));
     if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) CPTR_TRY(amg_setup(c, c->hT, c->rp, c->ci, c->St, n));
-    c->prof.setup_ms[1] = ms_since(t1);
-    auto t2 = std::chrono::steady_clock::now();
     if (c->o.stage2 == CPTR_STAGE2_ILU0) CPTR_TRY(ilu_setup(c));
+    double t2 = host_ms();
     // A' for the solve in the SELL-32 layout; the BSR copy is not needed after set-up
     CPTR_TRY(sell_build(c));
     if (c->o.precision == CPTR_PREC_MIXED) {
@@ -160,7 +157,7 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     }
     dfree(c->A);
     c->A = nullptr;
-    c->prof.setup_ms[2] = ms_since(t2);
+    setup_tick(c, SETUP_LAYOUT, &t2);
     // work vectors
     const size_t nb = (size_t)n * b;
     const int m = c->o.restart;
@@ -178,6 +175,7 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
 template <typename F>
 cptr_status guarded(cptr_ctx *ctx, F &&f) {
     if (!ctx) return CPTR_EINVAL;
+    CtxScope scope(&ctx->c);
     try {
         ctx->c.err.clear();
         return f(&ctx->c);
@@ -207,8 +205,7 @@ cptr_status clear_wait_flag(Ctx *c) {
 }
 cptr_status check_wait_flag(Ctx *c) {
     int32_t w = 0;
-    CPTR_CUDA_TRY(c, cudaMemcpy(&w, reinterpret_cast<char *>(c->ks) + offsetof(KState, wait_err), sizeof(int32_t),
-                                cudaMemcpyDeviceToHost));
+    CPTR_TRY(copy_to_host(c, &w, reinterpret_cast<char *>(c->ks) + offsetof(KState, wait_err), sizeof(int32_t)));
     if (w) return c->fail(CPTR_ETIMEOUT, "ILU(0) sweep: a bounded wait gave up");
     return CPTR_OK;
 }
@@ -256,6 +253,23 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
     Ctx *c = &ctx->c;
     c->o = o;
     c->stream = (cudaStream_t)o.stream;
+    CtxScope scope(c);
+    {
+        // a stream-ordered pool for this context; freed blocks stay reserved for the next set-up
+        int dev = 0;
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        if (cudaGetDevice(&dev) == cudaSuccess) {
+            props.location.id = dev;
+            if (cudaMemPoolCreate(&c->pool, &props) == cudaSuccess) {
+                uint64_t keep = UINT64_MAX;
+                cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            } else {
+                c->pool = nullptr;   // fall back to cudaMalloc
+            }
+        }
+    }
     cptr_status s = CPTR_OK;
     if ((s = dalloc_t(c, &c->ks, 1)) != CPTR_OK || (s = dalloc_t(c, &c->flag, 4)) != CPTR_OK ||
         (s = dalloc_t(c, &c->never, 1)) != CPTR_OK ||
@@ -275,9 +289,14 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
 void cptr_destroy(cptr_ctx *ctx) {
     if (!ctx) return;
     Ctx *c = &ctx->c;
-    cudaStreamSynchronize(c->stream);
-    release_setup(c);
-    dfree(c->ks); dfree(c->flag); dfree(c->partial); dfree(c->scan_tmp); dfree(c->never);
+    {
+        CtxScope scope(c);
+        cudaStreamSynchronize(c->stream);
+        release_setup(c);
+        dfree(c->ks); dfree(c->flag); dfree(c->partial); dfree(c->scan_tmp); dfree(c->never); dfree(c->ilu_flags);
+        cudaStreamSynchronize(c->stream);
+    }
+    if (c->pool) cudaMemPoolDestroy(c->pool);
     if (c->ks_host) cudaFreeHost(c->ks_host);
     for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -436,7 +455,7 @@ cptr_status cptr_hierarchy_level(cptr_ctx *ctx, int32_t which, int32_t l, int32_
         if (which < 0 || which > 1 || l < 0 || l >= h.nlev) return c->fail(CPTR_EINVAL, "no such level");
         const Level &L = h.L[l];
         auto cp = [&](void *dst, const void *src, size_t bytes) -> cptr_status {
-            if (dst && src && bytes) CPTR_CUDA_TRY(c, cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+            if (dst && src && bytes) CPTR_TRY(copy_to_host(c, dst, src, bytes));
             return CPTR_OK;
         };
         CPTR_TRY(cp(rp, L.A.rp, sizeof(int32_t) * ((size_t)L.A.n + 1)));
@@ -475,7 +494,7 @@ cptr_status cptr_profile(cptr_ctx *ctx, double *ms, int64_t *count) {
             double m = 0.0;
             int64_t n = 0;
             if (f < PF_N) { m = c->prof.ms[f]; n = c->prof.cnt[f]; }
-            else if (f < PF_N + 3) { m = c->prof.setup_ms[f - PF_N]; n = 1; }
+            else { m = c->prof.setup_ms[f - PF_N]; n = 1; }
             if (ms) ms[f] = m;
             if (count) count[f] = n;
         }

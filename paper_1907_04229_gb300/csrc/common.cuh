@@ -103,8 +103,16 @@ struct Prof {
     std::vector<size_t> gslots;    // slots recorded inside the captured iteration graph
     double ms[PF_N] = {0};
     int64_t cnt[PF_N] = {0};
-    double setup_ms[3] = {0};      // set-up phases: inputs+decoupling, AMG, ILU
+    double setup_ms[8] = {0};      // set-up phases (host clock, after a stream sync): see SETUP_*
 };
+// set-up phases: inputs + decoupling + extraction; AMG coarsening (strength + PMIS + interp);
+// AMG Galerkin products (transpose + two SpGEMMs); AMG coarsest inverse; ILU host work (ordering,
+// level sets, sweep tables); ILU factorisation; SELL layout + mixed-precision copies; other
+enum { SETUP_INPUTS = 0, SETUP_COARSEN = 1, SETUP_RAP = 2, SETUP_COARSEST = 3, SETUP_ILU_HOST = 4,
+       SETUP_ILU_FACTOR = 5, SETUP_LAYOUT = 6, SETUP_OTHER = 7 };
+// adds the host time since *t0 (after syncing the context's stream) to set-up phase `phase`
+void setup_tick(Ctx *c, int phase, double *t0);
+double host_ms();
 int prof_begin(const Ctx *c, int fam);
 void prof_end(const Ctx *c, int slot);
 void prof_reset(Ctx *c);
@@ -115,7 +123,16 @@ void prof_end_capture(Ctx *c);
 cptr_status build_iteration_graph(Ctx *c);
 
 // ---- memory helpers ----------------------------------------------------------------------------
+// Device memory comes from a stream-ordered pool owned by the context (freed memory stays in
+// the pool for the next set-up).  dfree releases on the stream of the context whose API call is
+// running on this thread (CtxScope), or synchronously when none is.
 cptr_status dalloc(Ctx *c, void **p, size_t bytes);
+cptr_status copy_to_host(Ctx *c, void *dst, const void *src, size_t bytes);
+struct CtxScope {
+    explicit CtxScope(Ctx *c);
+    ~CtxScope();
+    Ctx *prev;
+};
 template <typename T>
 inline cptr_status dalloc_t(Ctx *c, T **p, size_t count) {
     return dalloc(c, reinterpret_cast<void **>(p), count * sizeof(T));
@@ -171,6 +188,7 @@ void apply_precond(const Ctx *c, const double *v, double *z);
 struct Ctx {
     cptr_options o{};
     cudaStream_t stream = nullptr;
+    cudaMemPool_t pool = nullptr;
     std::string err;
     bool ready = false;
     int32_t n = 0, b = 0, ps = 0, ts = 1, nnzb = 0;
@@ -191,6 +209,9 @@ struct Ctx {
     double *LU = nullptr;
     int32_t *ilu_rp = nullptr, *ilu_ci = nullptr, *ilu_diag = nullptr;
     bool ilu_owns_pattern = false;   // false: the ILU pattern aliases rp/ci/diag
+    int32_t *ilu_rowmap = nullptr;     // multicolour: row of the factorised matrix -> original row
+    int32_t *ilu_flags = nullptr;      // per-row "factored" flags of the one-launch factorisation
+    int32_t ilu_flags_n = 0, ilu_epoch = 0;
     int32_t nlev_f = 0, nlev_b = 0;
     int32_t *lvl_f = nullptr, *lvl_b = nullptr;       // rows sorted by level (device)
     std::vector<int32_t> h_lptr_f, h_lptr_b;           // level pointers (host)

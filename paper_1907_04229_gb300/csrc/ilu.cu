@@ -1,10 +1,12 @@
 // Second stage of CPR/CPTR: block ILU(0) of the decoupled Jacobian A' on its own BSR pattern
-// (Sec. 3.1, Sec. 4: "ILU(0) is our default").  Factorisation and triangular solves are level
-// scheduled: level(i) = 1 + max level(j) over the rows j that row i depends on, so rows of one
+// (Sec. 3.1, Sec. 4: "ILU(0) is our default").  Factorisation and triangular solves follow the
+// level sets: level(i) = 1 + max level(j) over the rows j that row i depends on, so rows of one
 // level are independent.  Pivot blocks are stored inverted in the diagonal slots.  With dense
 // b x b blocks this is the same operator as scalar ILU(0) of the interleaved matrix.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <stddef.h>
 
 #include <algorithm>
 #include <type_traits>
@@ -52,58 +54,6 @@ __device__ __forceinline__ bool block_inverse(double *m) {
 #pragma unroll
         for (int q = 0; q < B; ++q) m[r * B + q] = a[r][B + q];
     return true;
-}
-
-template <int B>
-__global__ void k_bilu_factor(const int32_t *rows, int32_t start, int32_t count, const int32_t *rp,
-                              const int32_t *ci, const int32_t *diag, double *LU, int32_t *singular) {
-    int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= count) return;
-    int32_t i = rows[start + t];
-    int32_t e = rp[i + 1];
-    for (int32_t k = rp[i]; k < diag[i]; ++k) {
-        int32_t c = ci[k];
-        const double *dinv = LU + (int64_t)diag[c] * B * B;
-        double a[B * B], l[B * B];
-#pragma unroll
-        for (int q = 0; q < B * B; ++q) a[q] = LU[(int64_t)k * B * B + q];
-#pragma unroll
-        for (int r = 0; r < B; ++r)
-#pragma unroll
-            for (int q = 0; q < B; ++q) {
-                double s = 0.0;
-#pragma unroll
-                for (int u = 0; u < B; ++u) s = fma(a[r * B + u], dinv[u * B + q], s);
-                l[r * B + q] = s;
-            }
-#pragma unroll
-        for (int q = 0; q < B * B; ++q) LU[(int64_t)k * B * B + q] = l[q];
-        int32_t p = k + 1;
-        for (int32_t qq = diag[c] + 1; qq < rp[c + 1]; ++qq) {
-            int32_t j = ci[qq];
-            while (p < e && ci[p] < j) ++p;
-            if (p < e && ci[p] == j) {
-                const double *u = LU + (int64_t)qq * B * B;
-                double *dst = LU + (int64_t)p * B * B;
-#pragma unroll
-                for (int r = 0; r < B; ++r)
-#pragma unroll
-                    for (int q = 0; q < B; ++q) {
-                        double s = dst[r * B + q];
-#pragma unroll
-                        for (int w = 0; w < B; ++w) s = fma(-l[r * B + w], u[w * B + q], s);
-                        dst[r * B + q] = s;
-                    }
-            }
-        }
-    }
-    double d[B * B];
-    double *dd = LU + (int64_t)diag[i] * B * B;
-#pragma unroll
-    for (int q = 0; q < B * B; ++q) d[q] = dd[q];
-    if (!block_inverse<B>(d)) { atomicOr(singular, 1); return; }
-#pragma unroll
-    for (int q = 0; q < B * B; ++q) dd[q] = d[q];
 }
 
 // forward: y_i = r_i - sum_{k < i} L_ik y_k
@@ -412,104 +362,214 @@ __global__ void k_sf_pack(int64_t nslots32, int BB, const int32_t *kidx, const d
     for (int e = 0; e < BB; ++e) val[(sl * BB + e) * 32 + lane] = (T)(k >= 0 ? LU[(int64_t)k * BB + e] : 0.0);
 }
 
-static void level_sets(int32_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci, bool forward,
-                       std::vector<int32_t> &lptr, std::vector<int32_t> &rows) {
-    std::vector<int32_t> lev(n, 0);
-    int32_t nl = 0;
-    for (int32_t s = 0; s < n; ++s) {
-        int32_t i = forward ? s : n - 1 - s;
-        int32_t l = 0;
-        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
-            int32_t j = ci[k];
-            if (forward ? (j < i) : (j > i)) l = std::max(l, lev[j] + 1);
-        }
-        lev[i] = l;
-        nl = std::max(nl, l + 1);
+// ------------------------------------------------------------------------------------------------
+// Set-up of the sweeps on the device.  Level sets by monotone relaxation: every row takes 1 + the
+// largest level among the rows it depends on (lower columns forward, upper columns backward);
+// repeated in place until nothing changes (as many passes as levels, checked every 16).  Rows
+// are then ordered by level (counting sort; the order inside a level does not change any result,
+// since rows of one level are independent) and the SELL-32 dependency tables are filled.
+__global__ void k_lev_relax(int32_t n, const int32_t *rp, const int32_t *ci, int32_t *lev, int forward,
+                            int32_t *changed) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t l = 0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+        int32_t j = ci[k];
+        if (forward ? (j < i) : (j > i)) l = max(l, *(volatile int32_t *)(lev + j) + 1);
     }
-    lptr.assign(nl + 1, 0);
-    for (int32_t i = 0; i < n; ++i) lptr[lev[i] + 1]++;
-    for (int32_t l = 0; l < nl; ++l) lptr[l + 1] += lptr[l];
-    std::vector<int32_t> cur(lptr.begin(), lptr.end() - 1);
-    rows.assign(n, 0);
-    for (int32_t i = 0; i < n; ++i) rows[cur[lev[i]]++] = i;  // ascending within a level
+    if (l != lev[i]) {
+        lev[i] = l;
+        *changed = 1;
+    }
+}
+__global__ void k_compose(int32_t n, const int32_t *a, const int32_t *b, int32_t *out) {  // out[t] = a[b[t]]
+    int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = a[b[t]];
+}
+// dependency count of the row at each position -> per-chunk width (warp max)
+__global__ void k_chunk_width(int32_t n, const int32_t *pos, const int32_t *rp, const int32_t *dg, int lower,
+                              int32_t *w) {
+    int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t cnt = 0;
+    if (t < n) {
+        int32_t row = pos[t];
+        cnt = lower ? dg[row] - rp[row] : rp[row + 1] - dg[row] - 1;
+    }
+    cnt = __reduce_max_sync(0xffffffffu, cnt);
+    if ((t & 31) == 0 && (t >> 5) < (n + 31) / 32) w[t >> 5] = cnt;
+}
+__global__ void k_widen(int32_t m, const int32_t *a, int64_t *b) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= m) b[i] = a[i];
+}
+__global__ void k_fill_tables(int32_t n, const int32_t *pos, const int32_t *rp, const int32_t *ci, const int32_t *dg,
+                              const int32_t *inv, int lower, const int32_t *off, int32_t *col, int32_t *kidx) {
+    int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int32_t row = pos[t], ch = t >> 5, lane = t & 31;
+    int32_t k0 = lower ? rp[row] : dg[row] + 1, k1 = lower ? dg[row] : rp[row + 1];
+    for (int32_t k = k0; k < k1; ++k) {
+        int64_t u = ((int64_t)off[ch] + (k - k0)) * 32 + lane;
+        col[u] = inv[ci[k]];
+        kidx[u] = k;
+    }
+}
+__global__ void k_dinv_index(int32_t n, const int32_t *pos_b, const int32_t *dg, int32_t *kidx) {
+    int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) kidx[t] = dg[pos_b[t]];
 }
 
-// Level-ordered SELL-32 copies of the factors for the one-launch sweeps (see k_ilu_fwd_sf).
-// rp, ci, dg: the pattern of the factorised matrix (cells possibly permuted); rowmap: its row ->
-// original cell (the sweeps read r and write z in the caller's order).
-static cptr_status sf_build(Ctx *c, const std::vector<int32_t> &pos_f, const std::vector<int32_t> &pos_b,
-                            const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
-                            const std::vector<int32_t> &dg, const std::vector<int32_t> &rowmap) {
-    const int32_t n = c->n, BB = c->b * c->b, nch = (n + 31) / 32;
-    std::vector<int32_t> inv_f(n), inv_b(n), bmap(n);
-    for (int32_t t = 0; t < n; ++t) { inv_f[pos_f[t]] = t; inv_b[pos_b[t]] = t; }
-    for (int32_t t = 0; t < n; ++t) bmap[t] = inv_f[pos_b[t]];
-    auto build = [&](const std::vector<int32_t> &pos, const std::vector<int32_t> &inv, bool lower,
-                     std::vector<int64_t> &off, std::vector<int32_t> &col, std::vector<int32_t> &kidx) {
-        off.assign(nch + 1, 0);
-        for (int32_t ch = 0; ch < nch; ++ch) {
-            int32_t w = 0;
-            for (int32_t t = ch * 32; t < std::min(n, ch * 32 + 32); ++t) {
-                int32_t row = pos[t];
-                w = std::max(w, lower ? dg[row] - rp[row] : rp[row + 1] - dg[row] - 1);
+// Block ILU(0) factorisation in one launch: rows in forward level order, taken in ticket order;
+// a row waits (bounded) until every row it depends on has published its factored blocks
+// (release store of its flag), then computes its own blocks as in the level-by-level form.
+template <int B>
+__global__ void __launch_bounds__(64) k_bilu_factor_sf(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
+                                                       const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                                       const int32_t *__restrict__ diag, double *LU, int32_t *flag,
+                                                       int32_t epoch, int32_t *singular, KState *ks) {
+    __shared__ unsigned blk;
+    const unsigned nchunks = (unsigned)((n + 63) / 64);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) blk = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const unsigned b = blk;
+        if (b >= nchunks) return;
+        const int32_t t = (int32_t)(b * 64 + threadIdx.x);
+        if (t >= n) continue;
+        const int32_t i = pos[t];
+        const int32_t e = rp[i + 1];
+        // wait until every row this row depends on has published its blocks: poll all flags
+        // together, then re-poll only the ones not yet set
+        {
+            const int32_t k0 = rp[i], k1 = diag[i];
+            unsigned long long t0 = 0;
+            bool pending = true;
+            for (int round = 0; pending; ++round) {
+                pending = false;
+                for (int32_t k = k0; k < k1; ++k) {
+                    int32_t f;
+                    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flag + ci[k]) : "memory");
+                    pending |= f != epoch;
+                }
+                if (!pending) break;
+                if (round == 0) t0 = gtimer();
+                else if (gtimer() - t0 > kWaitNs) { atomicExch(&ks->wait_err, 1); break; }
+                __nanosleep(20);
             }
-            off[ch + 1] = off[ch] + w;
         }
-        col.assign((size_t)off[nch] * 32, -1);
-        kidx.assign((size_t)off[nch] * 32, -1);
-        for (int32_t t = 0; t < n; ++t) {
-            int32_t row = pos[t], ch = t >> 5, lane = t & 31;
-            int32_t k0 = lower ? rp[row] : dg[row] + 1, k1 = lower ? dg[row] : rp[row + 1];
-            for (int32_t k = k0; k < k1; ++k) {
-                int64_t u = (off[ch] + (k - k0)) * 32 + lane;
-                col[u] = inv[ci[k]];
-                kidx[u] = k;
+        for (int32_t k = rp[i]; k < diag[i]; ++k) {
+            const int32_t c = ci[k];
+            const double *dinv = LU + (int64_t)diag[c] * B * B;
+            double a[B * B], l[B * B];
+#pragma unroll
+            for (int q = 0; q < B * B; ++q) a[q] = LU[(int64_t)k * B * B + q];
+#pragma unroll
+            for (int r = 0; r < B; ++r)
+#pragma unroll
+                for (int q = 0; q < B; ++q) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int u = 0; u < B; ++u) s = fma(a[r * B + u], dinv[u * B + q], s);
+                    l[r * B + q] = s;
+                }
+#pragma unroll
+            for (int q = 0; q < B * B; ++q) LU[(int64_t)k * B * B + q] = l[q];
+            int32_t p = k + 1;
+            for (int32_t qq = diag[c] + 1; qq < rp[c + 1]; ++qq) {
+                const int32_t j = ci[qq];
+                while (p < e && ci[p] < j) ++p;
+                if (p < e && ci[p] == j) {
+                    const double *u = LU + (int64_t)qq * B * B;
+                    double *dst = LU + (int64_t)p * B * B;
+#pragma unroll
+                    for (int r = 0; r < B; ++r)
+#pragma unroll
+                        for (int q = 0; q < B; ++q) {
+                            double s = dst[r * B + q];
+#pragma unroll
+                            for (int w = 0; w < B; ++w) s = fma(-l[r * B + w], u[w * B + q], s);
+                            dst[r * B + q] = s;
+                        }
+                }
             }
         }
-    };
-    std::vector<int64_t> off_f, off_b;
-    std::vector<int32_t> col_f, col_b, kidx_f, kidx_b, kidx_d((size_t)nch * 32, -1);
-    build(pos_f, inv_f, true, off_f, col_f, kidx_f);
-    build(pos_b, inv_b, false, off_b, col_b, kidx_b);
-    for (int32_t t = 0; t < n; ++t) kidx_d[t] = dg[pos_b[t]];
-    auto up = [&](auto **dst, const auto &v) -> cptr_status {
-        using T = typename std::remove_reference<decltype(v)>::type::value_type;
-        CPTR_TRY(dalloc_t(c, reinterpret_cast<T **>(dst), v.size() > 0 ? v.size() : 1));
-        if (!v.empty())
-            CPTR_CUDA_TRY(c, cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, c->stream));
-        return CPTR_OK;
-    };
-    std::vector<int32_t> orig_f(n), orig_b(n);
-    for (int32_t t = 0; t < n; ++t) { orig_f[t] = rowmap[pos_f[t]]; orig_b[t] = rowmap[pos_b[t]]; }
-    CPTR_TRY(up(&c->sf_pos_f, orig_f));
-    CPTR_TRY(up(&c->sf_pos_b, orig_b));
-    CPTR_TRY(up(&c->sf_bmap, bmap));
-    CPTR_TRY(up(&c->sf_off_f, off_f));
-    CPTR_TRY(up(&c->sf_off_b, off_b));
-    CPTR_TRY(up(&c->sf_col_f, col_f));
-    CPTR_TRY(up(&c->sf_col_b, col_b));
-    int32_t *dk = nullptr;
-    const bool lo = c->o.precision == CPTR_PREC_MIXED;   // factors stored in FP32
-    auto pack = [&](const std::vector<int32_t> &kidx, void **dst) -> cptr_status {
-        int64_t ns = (int64_t)kidx.size();
-        CPTR_TRY(dalloc(c, dst, (size_t)(ns > 0 ? ns : 1) * BB * (lo ? 4 : 8)));
-        if (ns == 0) return CPTR_OK;
-        CPTR_TRY(dalloc_t(c, &dk, (size_t)ns));
-        CPTR_CUDA_TRY(c, cudaMemcpyAsync(dk, kidx.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, c->stream));
-        if (lo) (k_sf_pack<float><<<nblk(ns, 256), 256, 0, c->stream>>>(ns, BB, dk, c->LU, (float *)*dst), note_launch());
-        else (k_sf_pack<double><<<nblk(ns, 256), 256, 0, c->stream>>>(ns, BB, dk, c->LU, (double *)*dst), note_launch());
-        CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-        dfree(dk);
-        dk = nullptr;
-        return CPTR_OK;
-    };
-    CPTR_TRY(pack(kidx_f, &c->sf_val_f));
-    CPTR_TRY(pack(kidx_b, &c->sf_val_b));
-    CPTR_TRY(pack(kidx_d, &c->sf_dinv));
-    CPTR_TRY(dalloc_t(c, &c->sf_ticket, 4));
-    CPTR_TRY(dalloc(c, &c->sf_y, (size_t)n * c->b * (lo ? 4 : 8)));
-    CPTR_TRY(dalloc(c, &c->sf_z, (size_t)n * c->b * (lo ? 4 : 8)));
+        double d[B * B];
+        double *dd = LU + (int64_t)diag[i] * B * B;
+#pragma unroll
+        for (int q = 0; q < B * B; ++q) d[q] = dd[q];
+        if (!block_inverse<B>(d)) atomicOr(singular, 1);
+#pragma unroll
+        for (int q = 0; q < B * B; ++q) dd[q] = d[q];
+        asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(flag + i), "r"(epoch) : "memory");
+    }
+}
+
+// level sets of one direction: pos (position -> row), inv, and the level pointers (host)
+static cptr_status device_levels(Ctx *c, const int32_t *rp, const int32_t *ci, bool forward, int32_t *pos,
+                                 int32_t *inv, std::vector<int32_t> &h_lptr) {
+    const int32_t n = c->n;
+    cudaStream_t s = c->stream;
+    int32_t *lev = nullptr, *chg = nullptr, *cnt = nullptr, *lptr = nullptr;
+    CPTR_TRY(dalloc_t(c, &lev, (size_t)n));
+    CPTR_TRY(dalloc_t(c, &chg, 2));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(lev, 0, sizeof(int32_t) * n, s));
+    for (int pass = 0;; ++pass) {
+        CPTR_CUDA_TRY(c, cudaMemsetAsync(chg, 0, sizeof(int32_t), s));
+        for (int k = 0; k < 16; ++k)
+            (k_lev_relax<<<nblk(n, 256), 256, 0, s>>>(n, rp, ci, lev, forward ? 1 : 0, chg), note_launch());
+        int32_t h = 0;
+        CPTR_TRY(copy_to_host(c, &h, chg, sizeof(int32_t)));
+        if (!h) break;   // the last 16 passes changed nothing
+        if (pass > n) return c->fail(CPTR_EINVAL, "ILU(0): level sets did not converge");
+    }
+    // stable counting sort by level on the host (rows of a level in ascending order keep the
+    // sweeps' accesses local): one sequential pass over the levels
+    std::vector<int32_t> hl(n), hp(n), hi(n);
+    CPTR_TRY(copy_to_host(c, hl.data(), lev, sizeof(int32_t) * n));
+    int32_t nl = 0;
+    for (int32_t i = 0; i < n; ++i) nl = std::max(nl, hl[i] + 1);
+    h_lptr.assign(nl + 1, 0);
+    for (int32_t i = 0; i < n; ++i) h_lptr[hl[i] + 1]++;
+    for (int32_t l = 0; l < nl; ++l) h_lptr[l + 1] += h_lptr[l];
+    std::vector<int32_t> cur(h_lptr.begin(), h_lptr.end() - 1);
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t t = cur[hl[i]]++;
+        hp[t] = i;
+        hi[i] = t;
+    }
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(pos, hp.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(inv, hi.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(s));
+    dfree(lev); dfree(chg);
+    (void)cnt; (void)lptr;
+    return CPTR_OK;
+}
+
+// SELL-32 dependency table of one sweep: chunk offsets (int64), dependency positions and the
+// block index of every slot (-1 = padding)
+static cptr_status device_table(Ctx *c, const int32_t *pos, const int32_t *inv, const int32_t *rp, const int32_t *ci,
+                                const int32_t *dg, bool lower, int64_t **off64, int32_t **col, int32_t **kidx,
+                                int64_t *nslots) {
+    const int32_t n = c->n, nch = (n + 31) / 32;
+    cudaStream_t s = c->stream;
+    int32_t *w = nullptr, *off = nullptr;
+    CPTR_TRY(dalloc_t(c, &w, (size_t)nch + 1));
+    CPTR_TRY(dalloc_t(c, &off, (size_t)nch + 1));
+    (k_chunk_width<<<nblk((int64_t)nch * 32, 256), 256, 0, s>>>(n, pos, rp, dg, lower ? 1 : 0, w), note_launch());
+    int32_t total = 0;
+    CPTR_TRY(scan_exclusive(c, w, off, nch, &total));
+    CPTR_TRY(dalloc_t(c, off64, (size_t)nch + 1));
+    (k_widen<<<nblk(nch + 1, 256), 256, 0, s>>>(nch, off, *off64), note_launch());
+    const int64_t ns = (int64_t)total * 32;
+    CPTR_TRY(dalloc_t(c, col, (size_t)(ns > 0 ? ns : 1)));
+    CPTR_TRY(dalloc_t(c, kidx, (size_t)(ns > 0 ? ns : 1)));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(*col, 0xFF, sizeof(int32_t) * (ns > 0 ? ns : 1), s));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(*kidx, 0xFF, sizeof(int32_t) * (ns > 0 ? ns : 1), s));
+    (k_fill_tables<<<nblk(n, 256), 256, 0, s>>>(n, pos, rp, ci, dg, inv, lower ? 1 : 0, off, *col, *kidx), note_launch());
     CPTR_CUDA_TRY(c, cudaGetLastError());
+    dfree(w); dfree(off);
+    *nslots = ns;
     return CPTR_OK;
 }
 
@@ -546,18 +606,17 @@ __global__ void k_gather_blocks(int32_t nnzb, int BB, const int32_t *kmap, const
 
 cptr_status ilu_setup(Ctx *c) {
     ilu_free(c);
+    double t0 = host_ms();
     const int32_t n = c->n, BB = c->b * c->b;
+    cudaStream_t st = c->stream;
     CPTR_TRY(dalloc_t(c, &c->LU, (size_t)c->nnzb * BB));
     // the pattern the factorisation works on: the caller's order, or cells permuted by colour
-    std::vector<int32_t> prp, pci, pdg, rowmap(n);
+    std::vector<int32_t> rowmap;
     const bool mc = c->o.ilu_order == CPTR_ILU_MULTICOLOR;
     if (mc) {
         rowmap = multicolour_order(n, c->h_rp, c->h_ci);
-        std::vector<int32_t> inv(n), kmap(c->nnzb);
+        std::vector<int32_t> inv(n), kmap(c->nnzb), prp(n + 1, 0), pci(c->nnzb), pdg(n, -1);
         for (int32_t I = 0; I < n; ++I) inv[rowmap[I]] = I;
-        prp.assign(n + 1, 0);
-        pci.resize(c->nnzb);
-        pdg.assign(n, -1);
         std::vector<std::pair<int32_t, int32_t>> row;
         for (int32_t I = 0; I < n; ++I) {
             int32_t i = rowmap[I];
@@ -577,57 +636,110 @@ cptr_status ilu_setup(Ctx *c) {
         CPTR_TRY(dalloc_t(c, &c->ilu_rp, (size_t)n + 1));
         CPTR_TRY(dalloc_t(c, &c->ilu_ci, (size_t)c->nnzb));
         CPTR_TRY(dalloc_t(c, &c->ilu_diag, (size_t)n));
+        CPTR_TRY(dalloc_t(c, &c->ilu_rowmap, (size_t)n));
         int32_t *dk = nullptr;
         CPTR_TRY(dalloc_t(c, &dk, (size_t)c->nnzb));
-        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ilu_rp, prp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, c->stream));
-        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ilu_ci, pci.data(), sizeof(int32_t) * c->nnzb, cudaMemcpyHostToDevice, c->stream));
-        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ilu_diag, pdg.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
-        CPTR_CUDA_TRY(c, cudaMemcpyAsync(dk, kmap.data(), sizeof(int32_t) * c->nnzb, cudaMemcpyHostToDevice, c->stream));
-        (k_gather_blocks<<<nblk((int64_t)c->nnzb * BB, 256), 256, 0, c->stream>>>(c->nnzb, BB, dk, c->A, c->LU), note_launch());
-        CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ilu_rp, prp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, st));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ilu_ci, pci.data(), sizeof(int32_t) * c->nnzb, cudaMemcpyHostToDevice, st));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ilu_diag, pdg.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ilu_rowmap, rowmap.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(dk, kmap.data(), sizeof(int32_t) * c->nnzb, cudaMemcpyHostToDevice, st));
+        (k_gather_blocks<<<nblk((int64_t)c->nnzb * BB, 256), 256, 0, st>>>(c->nnzb, BB, dk, c->A, c->LU), note_launch());
+        CPTR_CUDA_TRY(c, cudaStreamSynchronize(st));
         dfree(dk);
     } else {
-        prp = c->h_rp;
-        pci = c->h_ci;
-        pdg = c->h_diag;
-        for (int32_t i = 0; i < n; ++i) rowmap[i] = i;
         c->ilu_rp = c->rp;
         c->ilu_ci = c->ci;
         c->ilu_diag = c->diag;
-        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->LU, c->A, sizeof(double) * (size_t)c->nnzb * BB, cudaMemcpyDeviceToDevice,
-                                         c->stream));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->LU, c->A, sizeof(double) * (size_t)c->nnzb * BB, cudaMemcpyDeviceToDevice, st));
     }
-    std::vector<int32_t> rows_f, rows_b;
-    level_sets(n, prp, pci, true, c->h_lptr_f, rows_f);
-    level_sets(n, prp, pci, false, c->h_lptr_b, rows_b);
-    c->nlev_f = (int32_t)c->h_lptr_f.size() - 1;
-    c->nlev_b = (int32_t)c->h_lptr_b.size() - 1;
+    // level sets of both sweeps (positions -> rows of the factorised matrix)
+    int32_t *inv_f = nullptr, *inv_b = nullptr;
     CPTR_TRY(dalloc_t(c, &c->lvl_f, (size_t)n));
     CPTR_TRY(dalloc_t(c, &c->lvl_b, (size_t)n));
+    CPTR_TRY(dalloc_t(c, &inv_f, (size_t)n));
+    CPTR_TRY(dalloc_t(c, &inv_b, (size_t)n));
+    CPTR_TRY(device_levels(c, c->ilu_rp, c->ilu_ci, true, c->lvl_f, inv_f, c->h_lptr_f));
+    CPTR_TRY(device_levels(c, c->ilu_rp, c->ilu_ci, false, c->lvl_b, inv_b, c->h_lptr_b));
+    c->nlev_f = (int32_t)c->h_lptr_f.size() - 1;
+    c->nlev_b = (int32_t)c->h_lptr_b.size() - 1;
     CPTR_TRY(dalloc_t(c, &c->ybuf, (size_t)n * c->b));
     CPTR_TRY(dalloc_t(c, &c->zbuf, (size_t)n * c->b));
-    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->lvl_f, rows_f.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
-    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->lvl_b, rows_b.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
-    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
-    for (int32_t l = 0; l < c->nlev_f; ++l) {
-        int32_t s = c->h_lptr_f[l], cnt = c->h_lptr_f[l + 1] - s;
-        if (c->b == 3)
-            (k_bilu_factor<3><<<nblk(cnt, 128), 128, 0, c->stream>>>(c->lvl_f, s, cnt, c->ilu_rp, c->ilu_ci, c->ilu_diag,
-                                                                      c->LU, c->flag), note_launch());
-        else
-            (k_bilu_factor<4><<<nblk(cnt, 128), 128, 0, c->stream>>>(c->lvl_f, s, cnt, c->ilu_rp, c->ilu_ci, c->ilu_diag,
-                                                                      c->LU, c->flag), note_launch());
+    setup_tick(c, SETUP_ILU_HOST, &t0);
+    // factorisation, one launch
+    CPTR_TRY(dalloc_t(c, &c->sf_ticket, 4));
+    if (c->ilu_flags && c->ilu_flags_n != n) {
+        dfree(c->ilu_flags);
+        c->ilu_flags = nullptr;
     }
+    if (!c->ilu_flags) {
+        CPTR_TRY(dalloc_t(c, &c->ilu_flags, (size_t)n));
+        CPTR_CUDA_TRY(c, cudaMemsetAsync(c->ilu_flags, 0, sizeof(int32_t) * n, st));
+        c->ilu_flags_n = n;
+        c->ilu_epoch = 0;
+    }
+    ++c->ilu_epoch;
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), st));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->sf_ticket, 0, 4 * sizeof(unsigned), st));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(reinterpret_cast<char *>(c->ks) + offsetof(KState, wait_err), 0, sizeof(int32_t), st));
+    const unsigned fgrid = std::min<unsigned>(nblk(n, 64), 8 * 152);
+    if (c->b == 3)
+        (k_bilu_factor_sf<3><<<fgrid, 64, 0, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, c->LU,
+                                                    c->ilu_flags, c->ilu_epoch, c->flag, c->ks), note_launch());
+    else
+        (k_bilu_factor_sf<4><<<fgrid, 64, 0, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, c->LU,
+                                                    c->ilu_flags, c->ilu_epoch, c->flag, c->ks), note_launch());
     CPTR_CUDA_TRY(c, cudaGetLastError());
-    int32_t sing = 0;
-    CPTR_CUDA_TRY(c, cudaMemcpyAsync(&sing, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
-    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    int32_t sing = 0, werr = 0;
+    CPTR_TRY(copy_to_host(c, &sing, c->flag, sizeof(int32_t)));
+    CPTR_TRY(copy_to_host(c, &werr, reinterpret_cast<char *>(c->ks) + offsetof(KState, wait_err), sizeof(int32_t)));
+    if (werr) return c->fail(CPTR_ETIMEOUT, "ILU(0) factorisation: a bounded wait gave up");
     if (sing) return c->fail(CPTR_ESINGULAR, "ILU(0): singular pivot block");
-    return sf_build(c, rows_f, rows_b, prp, pci, pdg, rowmap);
+    setup_tick(c, SETUP_ILU_FACTOR, &t0);
+    // sweep tables: positions of the sweeps in the caller's row order, dependency tables, factors
+    const int32_t nch = (n + 31) / 32;
+    CPTR_TRY(dalloc_t(c, &c->sf_pos_f, (size_t)n));
+    CPTR_TRY(dalloc_t(c, &c->sf_pos_b, (size_t)n));
+    CPTR_TRY(dalloc_t(c, &c->sf_bmap, (size_t)n));
+    if (mc) {
+        (k_compose<<<nblk(n, 256), 256, 0, st>>>(n, c->ilu_rowmap, c->lvl_f, c->sf_pos_f), note_launch());
+        (k_compose<<<nblk(n, 256), 256, 0, st>>>(n, c->ilu_rowmap, c->lvl_b, c->sf_pos_b), note_launch());
+    } else {
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->sf_pos_f, c->lvl_f, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->sf_pos_b, c->lvl_b, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
+    }
+    (k_compose<<<nblk(n, 256), 256, 0, st>>>(n, inv_f, c->lvl_b, c->sf_bmap), note_launch());
+    int32_t *kidx_f = nullptr, *kidx_b = nullptr, *kidx_d = nullptr;
+    int64_t ns_f = 0, ns_b = 0;
+    CPTR_TRY(device_table(c, c->lvl_f, inv_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, true, &c->sf_off_f, &c->sf_col_f,
+                          &kidx_f, &ns_f));
+    CPTR_TRY(device_table(c, c->lvl_b, inv_b, c->ilu_rp, c->ilu_ci, c->ilu_diag, false, &c->sf_off_b, &c->sf_col_b,
+                          &kidx_b, &ns_b));
+    CPTR_TRY(dalloc_t(c, &kidx_d, (size_t)nch * 32));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(kidx_d, 0xFF, sizeof(int32_t) * nch * 32, st));
+    (k_dinv_index<<<nblk(n, 256), 256, 0, st>>>(n, c->lvl_b, c->ilu_diag, kidx_d), note_launch());
+    const bool lo = c->o.precision == CPTR_PREC_MIXED;   // factors stored in FP32
+    auto pack = [&](const int32_t *kidx, int64_t ns, void **dst) -> cptr_status {
+        CPTR_TRY(dalloc(c, dst, (size_t)(ns > 0 ? ns : 1) * BB * (lo ? 4 : 8)));
+        if (ns == 0) return CPTR_OK;
+        if (lo) (k_sf_pack<float><<<nblk(ns, 256), 256, 0, st>>>(ns, BB, kidx, c->LU, (float *)*dst), note_launch());
+        else (k_sf_pack<double><<<nblk(ns, 256), 256, 0, st>>>(ns, BB, kidx, c->LU, (double *)*dst), note_launch());
+        return CPTR_OK;
+    };
+    CPTR_TRY(pack(kidx_f, ns_f, &c->sf_val_f));
+    CPTR_TRY(pack(kidx_b, ns_b, &c->sf_val_b));
+    CPTR_TRY(pack(kidx_d, (int64_t)nch * 32, &c->sf_dinv));
+    CPTR_TRY(dalloc(c, &c->sf_y, (size_t)n * c->b * (lo ? 4 : 8)));
+    CPTR_TRY(dalloc(c, &c->sf_z, (size_t)n * c->b * (lo ? 4 : 8)));
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    dfree(kidx_f); dfree(kidx_b); dfree(kidx_d); dfree(inv_f); dfree(inv_b);
+    setup_tick(c, SETUP_ILU_HOST, &t0);
+    return CPTR_OK;
 }
 
 void ilu_free(Ctx *c) {
-    if (c->ilu_owns_pattern) { dfree(c->ilu_rp); dfree(c->ilu_ci); dfree(c->ilu_diag); }
+    if (c->ilu_owns_pattern) { dfree(c->ilu_rp); dfree(c->ilu_ci); dfree(c->ilu_diag); dfree(c->ilu_rowmap); }
+    c->ilu_rowmap = nullptr;
     c->ilu_owns_pattern = false;
     c->ilu_rp = c->ilu_ci = c->ilu_diag = nullptr;
     dfree(c->lvl_f); dfree(c->lvl_b); dfree(c->LU); dfree(c->ybuf); dfree(c->zbuf);

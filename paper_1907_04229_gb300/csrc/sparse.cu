@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <vector>
 
 #include "common.cuh"
@@ -24,6 +25,16 @@ void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxe
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 void begin_capture_count() { t_capturing = true; t_captured = 0; }
 int64_t end_capture_count() { t_capturing = false; return t_captured; }
+
+double host_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+void setup_tick(Ctx *c, int phase, double *t0) {
+    cudaStreamSynchronize(c->stream);
+    double t = host_ms();
+    c->prof.setup_ms[phase] += t - *t0;
+    *t0 = t;
+}
 
 int prof_begin(const Ctx *c, int fam) {
     Prof &p = c->prof;
@@ -88,18 +99,30 @@ cptr_status prof_collect(Ctx *c) {
     return CPTR_OK;
 }
 
+static thread_local Ctx *t_scope = nullptr;
+CtxScope::CtxScope(Ctx *c) : prev(t_scope) { t_scope = c; }
+CtxScope::~CtxScope() { t_scope = prev; }
+
 cptr_status dalloc(Ctx *c, void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = c->pool ? cudaMallocFromPoolAsync(p, bytes, c->pool, c->stream) : cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
-        return c->fail(CPTR_ENOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        return c->fail(CPTR_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) + " bytes: " +
+                                        cudaGetErrorString(e));
     }
     return CPTR_OK;
 }
 void dfree(void *p) {
-    if (p) cudaFree(p);
+    if (!p) return;
+    if (t_scope && t_scope->pool) cudaFreeAsync(p, t_scope->stream);
+    else cudaFree(p);
+}
+cptr_status copy_to_host(Ctx *c, void *dst, const void *src, size_t bytes) {
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return CPTR_OK;
 }
 void csr_free(Csr &a) {
     dfree(a.rp); dfree(a.ci); dfree(a.v);
