@@ -99,6 +99,21 @@ def _load():
         lib.or_round_bf16.argtypes = [ctypes.c_double]
         lib.or_splitmix64.restype = ctypes.c_uint64
         lib.or_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        lib.or_schur_features.restype = None
+        lib.or_schur_features.argtypes = [P, P]
+        lib.or_att.restype = None
+        lib.or_att.argtypes = [P, P]
+        lib.or_mlp_nparam.restype = ctypes.c_int
+        lib.or_mlp_nparam.argtypes = []
+        lib.or_mlp_forward.restype = None
+        lib.or_mlp_forward.argtypes = [P, P, ctypes.c_int32, P]
+        lib.or_mlp_loss_grad.restype = ctypes.c_double
+        lib.or_mlp_loss_grad.argtypes = [P, P, P, ctypes.c_int32, P]
+        lib.or_adam_step.restype = None
+        lib.or_adam_step.argtypes = [P, P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double]
+        lib.or_mlp_infer_bf16.restype = None
+        lib.or_mlp_infer_bf16.argtypes = [P, P, ctypes.c_int32, P]
         _lib = lib
     return _lib
 
@@ -235,6 +250,18 @@ class Oracle:
         lib.or_field(self._c, f, _p(v))
         return v
 
+    def schur_features(self):
+        """The 16 local features of every cell for the learned Schur scaling, [n, 16] FP64."""
+        f = np.zeros((self.n, 16))
+        _load().or_schur_features(self._c, _p(f))
+        return f
+
+    def att(self, nnz):
+        """A_TT of A' on the cell pattern."""
+        v = np.zeros(nnz)
+        _load().or_att(self._c, _p(v))
+        return v
+
     def levels(self, which):
         """AMG hierarchy of A_pp (which=0) or S~_T (which=1): list of dicts per level."""
         lib = _load()
@@ -302,3 +329,102 @@ def round_bf16(x: float) -> float:
 
 def splitmix64(seed: int, i: int) -> int:
     return int(_load().or_splitmix64(seed, i))
+
+
+# ---------------------------------------------------------------------------------------------
+# learned diagonal scaling of the Schur approximation (network 16-64-64-1, tanh)
+
+N_FEATURES, N_HIDDEN = 16, 64
+
+
+def mlp_nparam() -> int:
+    return int(_load().or_mlp_nparam())
+
+
+def mlp_forward(params, X):
+    P = np.ascontiguousarray(params, np.float64)
+    X = np.ascontiguousarray(X, np.float64)
+    y = np.zeros(X.shape[0])
+    _load().or_mlp_forward(_p(P), _p(X), X.shape[0], _p(y))
+    return y
+
+
+def mlp_loss_grad(params, X, t):
+    """(loss, gradient) of the mean squared error of the FP64 network."""
+    P = np.ascontiguousarray(params, np.float64)
+    X = np.ascontiguousarray(X, np.float64)
+    t = np.ascontiguousarray(t, np.float64)
+    g = np.zeros(mlp_nparam())
+    loss = _load().or_mlp_loss_grad(_p(P), _p(X), _p(t), X.shape[0], _p(g))
+    return float(loss), g
+
+
+def adam_step(params, m, v, g, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step in place on FP64 arrays (step number t >= 1)."""
+    for a in (params, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = np.ascontiguousarray(g, np.float64)
+    _load().or_adam_step(_p(params), _p(m), _p(v), _p(g), len(params), t, lr, beta1, beta2, eps)
+
+
+def mlp_train(params, X, t, steps, lr=1e-3):
+    """Full-batch Adam from zero moments; returns (trained params, loss before each step)."""
+    P = np.array(params, np.float64)
+    m, v = np.zeros_like(P), np.zeros_like(P)
+    losses = []
+    for k in range(1, steps + 1):
+        loss, g = mlp_loss_grad(P, X, t)
+        losses.append(loss)
+        adam_step(P, m, v, g, k, lr)
+    return P, np.array(losses)
+
+
+def mlp_infer_bf16(params32, X):
+    """Network output as the BF16 inference form computes it (FP32 result)."""
+    P = np.ascontiguousarray(params32, np.float32)
+    X = np.ascontiguousarray(X, np.float64)
+    y = np.zeros(X.shape[0], np.float32)
+    _load().or_mlp_infer_bf16(_p(P), _p(X), X.shape[0], _p(y))
+    return y
+
+
+def exact_schur_diag(o: "Oracle", sys: dict, chunk: int = 512):
+    """Diagonal of the exact S_T = A_TT - A_Tp A_pp^{-1} A_pT of A' (Sec. 3.2 eq. A00 and the Schur
+    complement of Sec. 3.3), with A_pp^{-1} applied by a sparse LU factorisation (library step), in
+    column chunks: (A_Tp X)_ii with X = A_pp^{-1} A_pT[:, chunk]."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    n, rp, ci = sys["n"], sys["row_ptr"], sys["col_idx"]
+    nnz = int(rp[-1])
+    mk = lambda v: sp.csr_matrix((v, ci, rp), shape=(n, n))
+    App, ApT, ATp = (mk(o.field(f, nnz)) for f in range(3))
+    ATT = mk(o.att(nnz))
+    lu = spl.splu(App.tocsc())
+    ApTc = ApT.tocsc()
+    d = np.zeros(n)
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        X = lu.solve(ApTc[:, c0:c1].toarray())
+        d[c0:c1] = np.einsum("ij,ji->i", ATp[c0:c1, :].toarray(), X)
+    return ATT.diagonal() - d
+
+
+def schur_ratio_target(sys: dict):
+    """Training target of the learned scaling: asinh((S_T)_ii / (A_TT)_ii), and the features."""
+    o = Oracle.from_system(sys, use_st=False, max_levels=1, dense_max=1, stage2=NONE2)
+    nnz = int(sys["row_ptr"][-1])
+    rp, ci = sys["row_ptr"], sys["col_idx"]
+    att = o.att(nnz)
+    diag = np.array([att[rp[i] + np.searchsorted(ci[rp[i]:rp[i + 1]], i)] for i in range(sys["n"])])
+    return np.arcsinh(exact_schur_diag(o, sys) / diag), o.schur_features()
+
+
+def learned_st(sys: dict, params32):
+    """S~_T = diag(s) A_TT with s = sinh(y) of the BF16 network over the oracle's features;
+    returns (st values on the cell pattern, s, y)."""
+    o = Oracle.from_system(sys, use_st=False, max_levels=1, dense_max=1, stage2=NONE2)
+    nnz = int(sys["row_ptr"][-1])
+    y = mlp_infer_bf16(params32, o.schur_features())
+    s = np.sinh(y.astype(np.float64))
+    rows = np.repeat(np.arange(sys["n"]), np.diff(sys["row_ptr"]))
+    return o.att(nnz) * s[rows], s, y

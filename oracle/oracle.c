@@ -958,3 +958,217 @@ amg *or_amg_create(int32_t n, const int32_t *rp, const int32_t *ci, const double
 void or_amg_destroy(amg *h) { if (h) { amg_free(h); free(h); } }
 void or_amg_vcycle(amg *h, const double *b, double *x) { vcycle(h, 0, b, x); }
 int or_amg_nlevels(amg *h) { return h->nlev; }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Learned diagonal scaling of the temperature Schur approximation.                             */
+/*                                                                                              */
+/* The paper approximates S_T = A_TT - A_Tp A_pp^{-1} A_pT either by the discrete S_e or by the */
+/* algebraic A_TT (Sec. 3.3.1).  The learned form keeps the Jacobian-only approximation A_TT    */
+/* and scales its rows: S~_T = diag(s) A_TT, s_i = sinh(y_i), where y_i is the output of a      */
+/* 16-64-64-1 tanh network over local features of cell i.  The network is trained to regress    */
+/* asinh of the exact ratio (S_T)_ii / (A_TT)_ii.  The paper has no learned part; every choice  */
+/* below (features, target, network, optimiser) is this project's.                              */
+
+#define OR_NF 16
+#define OR_NH 64
+/* parameter layout: W1[NH][NF] | b1[NH] | W2[NH][NH] | b2[NH] | w3[NH] | b3 */
+#define OR_OFF_W1 0
+#define OR_OFF_B1 (OR_OFF_W1 + OR_NH * OR_NF)
+#define OR_OFF_W2 (OR_OFF_B1 + OR_NH)
+#define OR_OFF_B2 (OR_OFF_W2 + OR_NH * OR_NH)
+#define OR_OFF_W3 (OR_OFF_B2 + OR_NH)
+#define OR_OFF_B3 (OR_OFF_W3 + OR_NH)
+#define OR_NPARAM (OR_OFF_B3 + 1)
+
+int or_mlp_nparam(void) { return OR_NPARAM; }
+
+static double q_div(double x, double y) { return y == 0.0 ? 0.0 : x / y; }
+static double sgn(double x) { return x > 0.0 ? 1.0 : x < 0.0 ? -1.0 : 0.0; }
+
+/* value of the cell-pattern field F at (row, col), 0 if the pattern has no such entry */
+static double field_at(const csr *F, int32_t row, int32_t col) {
+    for (int32_t k = F->rp[row]; k < F->rp[row + 1]; ++k)
+        if (F->ci[k] == col) return F->v[k];
+    return 0.0;
+}
+
+/* entry (r, c) of the diagonal b x b block of cell i of A' (interleaved scalar CSR) */
+static double diag_block(const or_ctx *c, int32_t i, int r, int col) {
+    const csr *P = &c->App;
+    for (int32_t k = P->rp[i]; k < P->rp[i + 1]; ++k)
+        if (P->ci[k] == i) return c->A.v[c->A.rp[i * c->b + r] + (k - P->rp[i]) * c->b + col];
+    return 0.0;
+}
+
+/* The 16 features of every cell (row-major [n][16]); every sum runs over the pattern of row i
+ * in ascending position.  With B = A_TT and q(x, y) = x / y (0 when y = 0):
+ *   0  q(sum_j A_Tp,ij q(A_pT,ji, A_pp,jj), B_ii)     diagonal of A_Tp D_pp^-1 A_pT, relative
+ *   1  q(A_Tp,ii q(A_pT,ii, A_pp,ii), B_ii)           its j = i term
+ *   2  q(sum_{j!=i} |A_pp,ij|, |A_pp,ii|)             3  q(sum_{j!=i} |B_ij|, |B_ii|)
+ *   4  q(sum_{j!=i} A_pp,ij, |A_pp,ii|)               5  q(sum_{j!=i} B_ij, |B_ii|)
+ *   6  q(sum_j |A_Tp,ij q(A_pT,ji, A_pp,jj)|, |B_ii|)
+ *   7  q(sum_s a_Ts q(a_sT, a_ss), B_ii)              8  q(sum_s a_ps q(a_sp, a_ss), A_pp,ii)
+ *      (a = diagonal block of A', s over the saturation slots)
+ *   9  sign(A_pp,ii)                                  10 sign(B_ii)
+ *   11 q(A_pT,ii, sqrt|A_pp,ii B_ii|)                  12 q(A_Tp,ii, sqrt|A_pp,ii B_ii|)
+ *   13 (entries in row i) / 7
+ *   14 q(sum_{j!=i} |A_pT,ij| |A_Tp,ii|, |A_pp,ii B_ii|)
+ *   15 q(sum_{j!=i} |A_Tp,ij| |A_pT,ii|, |A_pp,ii B_ii|)
+ * and each value v is replaced by asinh(v). */
+void or_schur_features(or_ctx *c, double *feat) {
+    int32_t n = c->n, b = c->b;
+    csr ATT;
+    extract_field(c, c->App.rp, c->App.ci, c->ts, c->ts, &ATT);
+    const int32_t *rp = c->App.rp, *ci = c->App.ci;
+    for (int32_t i = 0; i < n; ++i) {
+        double app = field_at(&c->App, i, i), bii = field_at(&ATT, i, i);
+        double apt = field_at(&c->ApT, i, i), atp = field_at(&c->ATp, i, i);
+        double s0 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0, s6 = 0, s14 = 0, s15 = 0;
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+            int32_t j = ci[k];
+            double t = c->ATp.v[k] * q_div(field_at(&c->ApT, j, i), field_at(&c->App, j, j));
+            s0 += t;
+            s6 += fabs(t);
+            if (j != i) {
+                s2 += fabs(c->App.v[k]);
+                s3 += fabs(ATT.v[k]);
+                s4 += c->App.v[k];
+                s5 += ATT.v[k];
+                s14 += fabs(c->ApT.v[k]);
+                s15 += fabs(c->ATp.v[k]);
+            }
+        }
+        double s7 = 0, s8 = 0;
+        for (int s = 0; s < b; ++s) {
+            if (s == c->ps || s == c->ts) continue;
+            double ass = diag_block(c, i, s, s);
+            s7 += diag_block(c, i, c->ts, s) * q_div(diag_block(c, i, s, c->ts), ass);
+            s8 += diag_block(c, i, c->ps, s) * q_div(diag_block(c, i, s, c->ps), ass);
+        }
+        double r = sqrt(fabs(app * bii)), pb = fabs(app * bii);
+        double f[OR_NF];
+        f[0] = q_div(s0, bii);
+        f[1] = q_div(atp * q_div(apt, app), bii);
+        f[2] = q_div(s2, fabs(app));
+        f[3] = q_div(s3, fabs(bii));
+        f[4] = q_div(s4, fabs(app));
+        f[5] = q_div(s5, fabs(bii));
+        f[6] = q_div(s6, fabs(bii));
+        f[7] = q_div(s7, bii);
+        f[8] = q_div(s8, app);
+        f[9] = sgn(app);
+        f[10] = sgn(bii);
+        f[11] = q_div(apt, r);
+        f[12] = q_div(atp, r);
+        f[13] = (double)(rp[i + 1] - rp[i]) / 7.0;
+        f[14] = q_div(s14 * fabs(atp), pb);
+        f[15] = q_div(s15 * fabs(apt), pb);
+        for (int k = 0; k < OR_NF; ++k) feat[(int64_t)i * OR_NF + k] = asinh(f[k]);
+    }
+    csr_free(&ATT);
+}
+
+/* A_TT values on the cell pattern (the base of the learned scaling) */
+void or_att(or_ctx *c, double *v) {
+    csr ATT;
+    extract_field(c, c->App.rp, c->App.ci, c->ts, c->ts, &ATT);
+    memcpy(v, ATT.v, sizeof(double) * (size_t)ATT.nnz);
+    csr_free(&ATT);
+}
+
+/* Forward pass in FP64 for n samples x[n][16]: z1 = W1 x + b1, h1 = tanh z1, z2 = W2 h1 + b2,
+ * h2 = tanh z2, y = w3 . h2 + b3. */
+static double mlp_forward1(const double *P, const double *x, double *h1, double *h2) {
+    for (int j = 0; j < OR_NH; ++j) {
+        double z = P[OR_OFF_B1 + j];
+        for (int k = 0; k < OR_NF; ++k) z += P[OR_OFF_W1 + j * OR_NF + k] * x[k];
+        h1[j] = tanh(z);
+    }
+    for (int j = 0; j < OR_NH; ++j) {
+        double z = P[OR_OFF_B2 + j];
+        for (int k = 0; k < OR_NH; ++k) z += P[OR_OFF_W2 + j * OR_NH + k] * h1[k];
+        h2[j] = tanh(z);
+    }
+    double y = P[OR_OFF_B3];
+    for (int j = 0; j < OR_NH; ++j) y += P[OR_OFF_W3 + j] * h2[j];
+    return y;
+}
+
+void or_mlp_forward(const double *P, const double *x, int32_t n, double *y) {
+    double h1[OR_NH], h2[OR_NH];
+    for (int32_t i = 0; i < n; ++i) y[i] = mlp_forward1(P, x + (int64_t)i * OR_NF, h1, h2);
+}
+
+/* Mean squared error L = (1/n) sum_i (y_i - t_i)^2 and its gradient dL/dP by backpropagation
+ * (chain rule through the layers above; tanh' = 1 - tanh^2). */
+double or_mlp_loss_grad(const double *P, const double *x, const double *t, int32_t n, double *g) {
+    double h1[OR_NH], h2[OR_NH], d2[OR_NH], d1[OR_NH];
+    memset(g, 0, sizeof(double) * OR_NPARAM);
+    double loss = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        const double *xi = x + (int64_t)i * OR_NF;
+        double y = mlp_forward1(P, xi, h1, h2);
+        double e = y - t[i];
+        loss += e * e;
+        double dy = 2.0 * e / n;
+        g[OR_OFF_B3] += dy;
+        for (int j = 0; j < OR_NH; ++j) {
+            g[OR_OFF_W3 + j] += dy * h2[j];
+            d2[j] = dy * P[OR_OFF_W3 + j] * (1.0 - h2[j] * h2[j]);
+        }
+        for (int j = 0; j < OR_NH; ++j) {
+            g[OR_OFF_B2 + j] += d2[j];
+            for (int k = 0; k < OR_NH; ++k) g[OR_OFF_W2 + j * OR_NH + k] += d2[j] * h1[k];
+        }
+        for (int k = 0; k < OR_NH; ++k) {
+            double s = 0.0;
+            for (int j = 0; j < OR_NH; ++j) s += P[OR_OFF_W2 + j * OR_NH + k] * d2[j];
+            d1[k] = s * (1.0 - h1[k] * h1[k]);
+        }
+        for (int j = 0; j < OR_NH; ++j) {
+            g[OR_OFF_B1 + j] += d1[j];
+            for (int k = 0; k < OR_NF; ++k) g[OR_OFF_W1 + j * OR_NF + k] += d1[j] * xi[k];
+        }
+    }
+    return loss / n;
+}
+
+/* Adam (Kingma and Ba, 2015): step number t >= 1, moments m, v updated in place. */
+void or_adam_step(double *P, double *m, double *v, const double *g, int32_t np, int32_t t, double lr,
+                  double beta1, double beta2, double eps) {
+    double c1 = 1.0 - pow(beta1, t), c2 = 1.0 - pow(beta2, t);
+    for (int32_t p = 0; p < np; ++p) {
+        m[p] = beta1 * m[p] + (1.0 - beta1) * g[p];
+        v[p] = beta2 * v[p] + (1.0 - beta2) * g[p] * g[p];
+        double mh = m[p] / c1, vh = v[p] / c2;
+        P[p] -= lr * mh / (sqrt(vh) + eps);
+    }
+}
+
+/* Inference as the BF16 form computes it: weights (FP32 given) and every layer input rounded to
+ * BF16 (features: FP64 -> FP32 -> BF16), biases FP32, each layer's sum accumulated in FP32 from the
+ * bias in ascending input order (the BF16 x BF16 products are exact in FP32), tanh in FP32. */
+static float f32_tanh(float z) { return tanhf(z); }
+void or_mlp_infer_bf16(const float *P, const double *x, int32_t n, float *y) {
+    float w1[OR_NH * OR_NF], w2[OR_NH * OR_NH], w3[OR_NH];
+    for (int k = 0; k < OR_NH * OR_NF; ++k) w1[k] = (float)round_bf16(P[OR_OFF_W1 + k]);
+    for (int k = 0; k < OR_NH * OR_NH; ++k) w2[k] = (float)round_bf16(P[OR_OFF_W2 + k]);
+    for (int k = 0; k < OR_NH; ++k) w3[k] = (float)round_bf16(P[OR_OFF_W3 + k]);
+    for (int32_t i = 0; i < n; ++i) {
+        float xb[OR_NF], h1[OR_NH];
+        for (int k = 0; k < OR_NF; ++k) xb[k] = (float)round_bf16(x[(int64_t)i * OR_NF + k]);
+        for (int j = 0; j < OR_NH; ++j) {
+            float acc = P[OR_OFF_B1 + j];
+            for (int k = 0; k < OR_NF; ++k) acc = acc + w1[j * OR_NF + k] * xb[k];
+            h1[j] = (float)round_bf16(f32_tanh(acc));
+        }
+        float out = P[OR_OFF_B3];
+        for (int j = 0; j < OR_NH; ++j) {
+            float acc = P[OR_OFF_B2 + j];
+            for (int k = 0; k < OR_NH; ++k) acc = acc + w2[j * OR_NH + k] * h1[k];
+            float h2 = (float)round_bf16(f32_tanh(acc));
+            out = out + w3[j] * h2;
+        }
+        y[i] = out;
+    }
+}

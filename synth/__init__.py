@@ -357,6 +357,7 @@ def recipe(name: str) -> Reservoir:
     cptr200k : 100x100x20 (200k cells, 600k dofs, b=3), layered lognormal k (sigma 2, kv/kh 0.1),
              k_T = 2 W/m/K, 500 K injector, 0.5 x 0.5 x 0.25 m cells.
     three_phase2m : 200x200x50 (2M cells, b=4), lognormal k (sigma 2.5), 4 injectors, 4 producers.
+    three_phase_coupled : 24x24x8 three-phase model with c_o = 1e-7 1/Pa, beta_o = 5e-2 1/K.
     """
     if name == "parity":
         return make_box(16, 16, 4, 3.125, seed=1, sigma=1.0)
@@ -366,4 +367,23 @@ def recipe(name: str) -> Reservoir:
     if name == "three_phase2m":
         return make_box(200, 200, 50, 1.0, 1.0, 0.5, seed=21, sigma=2.5, nphase=3, wells="four",
                         T_inj=500.0, q_inj=4e-6)
+    if name == "three_phase_coupled":
+        # the three-phase model with a compressible, strongly expanding oil (strong p-T coupling)
+        return make_box(24, 24, 8, 1.0, 1.0, 0.5, seed=41, sigma=2.5, nphase=3, wells="four",
+                        T_inj=500.0, q_inj=4e-6, c_o=1e-7, beta_o=5e-2)
     raise KeyError(name)
+
+
+LEARNED_TRAIN_GRIDS = 16
+
+
+def learned_training_grid(k: int, nx: int = 32, ny: int = 32, nz: int = 8) -> Reservoir:
+    """Training grid k of the learned Schur scaling: the three-phase model (sigma 2.5, four
+    injectors, four producers, 1 x 1 x 0.5 m cells), permeability seed 101 + k, and the oil's
+    compressibility c_o and thermal expansion beta_o drawn log-uniformly per grid from
+    [1e-9, 1e-7] 1/Pa and [5e-4, 5e-2] 1/K (uniforms k of stream 900 and of stream 901), so that the
+    set spans weak to strong p-T coupling."""
+    u1 = float(uniform(900, k + 1)[k])
+    u2 = float(uniform(901, k + 1)[k])
+    return make_box(nx, ny, nz, 1.0, 1.0, 0.5, seed=101 + k, sigma=2.5, nphase=3, wells="four",
+                    T_inj=500.0, q_inj=4e-6, c_o=1e-9 * 100.0 ** u1, beta_o=5e-4 * 100.0 ** u2)
