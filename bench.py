@@ -33,6 +33,7 @@ RTOL = 1e-6
 WORKLOAD = "cptr200k"
 L2_BYTES = 129 * 2 ** 20
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+LEARNED_STEPS, LEARNED_LR = 2000, 2e-3
 
 
 def parse():
@@ -44,6 +45,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--no-three-phase", action="store_true")
     return p.parse_args()
 
 
@@ -301,6 +303,13 @@ def ours(args, rank, world, local_rank):
                               "status": infs[-1]["status"]}
             Sv.close()
 
+    tp = None
+    if not args.no_three_phase:
+        del flush
+        torch.cuda.empty_cache()
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+        tp = three_phase(args, dev, stream, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         secs, oinfo = oracle_step(s)
@@ -321,9 +330,111 @@ def ours(args, rank, world, local_rank):
                "solve_dofs_per_s": round(dofs / (solve_ms / 1e3), 1),
                "true_rel_res": infos[-1]["true_rel_res"], "levels": [infos[-1]["levels_p"], infos[-1]["levels_T"]],
                "families": families, "roofline": roofline, "rooflines": lines, "variants": variants,
+               "three_phase": tp,
                "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clk}
         print(json.dumps(out), flush=True)
+
+
+def train_learned(dev, stream, base):
+    """Train the Schur-scaling network on the GPU: features of the 16 three-phase training grids
+    (32x32x8) computed by the library against the base approximation ("se": the discrete S_e,
+    "att": A_TT), targets asinh((S_T)_ii / B_ii) stored with the package (written by the oracle).
+    Returns (params, train ms, first and last loss, samples)."""
+    import torch
+
+    import synth
+    import paper_1907_04229_gb300 as cp
+
+    data = np.load(os.path.join(ROOT, "paper_1907_04229_gb300", "data", "schur_targets.npz"))
+    targets, shape = data["targets_" + base], tuple(int(v) for v in data["shape"])
+    feats = []
+    S = cp.Solver(stream=stream, stage1="none", stage2="none")
+    for k in range(targets.shape[0]):
+        g = synth.learned_training_grid(k, *shape).system()
+        S.setup(g["n"], g["b"], g["row_ptr"], g["col_idx"], g["vals"].reshape(-1), g["unknown_kind"],
+                g["weights"].reshape(-1), g["st"] if base == "se" else None)
+        f = torch.empty((g["n"], cp.MLP_FEATURES), dtype=torch.float64, device=dev)
+        cp.cptr_schur_features(S.ctx, f)
+        feats.append(f)
+    X = torch.cat(feats)
+    T = torch.as_tensor(targets.reshape(-1).astype(np.float64), device=dev)
+    P = torch.as_tensor(synth.mlp_init(10), device=dev)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hist = cp.cptr_mlp_train(S.ctx, X, T, P, LEARNED_STEPS, lr=LEARNED_LR)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    S.close()
+    return P, e0.elapsed_time(e1), float(hist[0]), float(hist[-1]), int(T.numel())
+
+
+def three_phase(args, dev, stream, flush):
+    """The three-phase 200x200x50 workload (2M cells, 4 unknowns/cell, 8M dofs): FP64 CPTR with
+    the paper's S_e, with the learned scaling diag(s) S_e, with A_TT and with diag(s) A_TT (the
+    networks trained on the GPU first), and the learned S_e form with the mixed-precision
+    preconditioner."""
+    import torch
+
+    import synth
+    import paper_1907_04229_gb300 as cp
+
+    nets, training = {}, {}
+    for base in ("se", "att"):
+        P, train_ms, loss0, loss1, nsamp = train_learned(dev, stream, base)
+        nets[base] = P
+        training[base] = {"samples": nsamp, "steps": LEARNED_STEPS, "lr": LEARNED_LR, "train_ms": round(train_ms, 2),
+                          "loss_first": loss0, "loss_last": loss1}
+    s = synth.recipe("three_phase2m").system()
+    n, b = s["n"], s["b"]
+    dofs = n * b
+    d = {k: torch.as_tensor(np.ascontiguousarray(v), device=dev) for k, v in
+         {"rp": s["row_ptr"], "ci": s["col_idx"], "vals": s["vals"].reshape(-1), "kind": s["unknown_kind"],
+          "W": s["weights"].reshape(-1), "st": s["st"], "rhs": s["rhs"].reshape(-1)}.items()}
+    del s
+    x = torch.empty(dofs, dtype=torch.float64, device=dev)
+    out = {"workload": "three_phase2m: 200x200x50 cells, 4 unknowns/cell (8M dofs), lognormal permeability "
+                       "sigma 2.5, 4 injectors + 4 producers; CPTR + ILU(0), FGMRES(30), rtol 1e-6",
+           "training": dict(training, data="16 three-phase 32x32x8 grids (coupling drawn per grid), exact Schur "
+                                           "diagonal ratios from the oracle")}
+    # (name, options, network base, timed runs); the A_TT forms stall on this workload, so they run
+    # once with a 200-step limit
+    runs = (("fp64_se", dict(), "se", None, 2), ("fp64_learned_se", dict(schur="learned"), "se", "se", 2),
+            ("mixed_learned_se", dict(schur="learned", precision="mixed"), "se", "se", 2),
+            ("fp64_att", dict(schur="att", max_it=200), None, None, 1),
+            ("fp64_learned_att", dict(schur="learned", max_it=200), None, "att", 1))
+    for name, opts, st_base, net, nrun in runs:
+        Sv = cp.Solver(stream=stream, **opts)
+        if net:
+            cp.cptr_set_mlp(Sv.ctx, nets[net])
+
+        def step_v():
+            Sv.setup(n, b, d["rp"], d["ci"], d["vals"], d["kind"], d["W"], d["st"] if st_base == "se" else None)
+            return Sv.solve(d["rhs"], RTOL, x=x)[1]
+
+        if nrun > 1:
+            step_v()
+        evs, infs = [], []
+        for _ in range(nrun):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infs.append(step_v())
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(bb) for a, bb in evs) / len(evs)
+        prof = cp.cptr_profile(Sv.ctx)
+        solve_ms = statistics.mean(i["solve_ms"] for i in infs)
+        out[name] = {"ms_per_step": round(ms, 3), "dofs_per_s": round(dofs / (ms / 1e3), 1),
+                     "setup_ms": round(statistics.mean(i["setup_ms"] for i in infs), 3),
+                     "solve_ms": round(solve_ms, 3), "solve_dofs_per_s": round(dofs / (solve_ms / 1e3), 1),
+                     "iters": infs[-1]["iters"], "true_rel_res": infs[-1]["true_rel_res"],
+                     "status": infs[-1]["status"], "schur_used": infs[-1]["schur_used"],
+                     "learned_setup_ms": round(prof["setup_other"][0], 3), "timed_runs": nrun}
+        Sv.close()
+    return out
 
 
 def reference(args, rank, world):

@@ -52,8 +52,10 @@ enum { CPTR_STAGE1_FULL = 0, CPTR_STAGE1_UPPER = 1, CPTR_STAGE1_LOWER = 2, CPTR_
        CPTR_STAGE1_CPR = 4, CPTR_STAGE1_NONE = 5 };
 /* second stage M2: ILU(0) on the full system (Sec. 4) or none */
 enum { CPTR_STAGE2_ILU0 = 0, CPTR_STAGE2_NONE = 1 };
-/* Schur approximation: the caller's S~_T (eq. Se) or A_TT (Sec. 3.3.1) */
-enum { CPTR_SCHUR_GIVEN = 0, CPTR_SCHUR_ATT = 1 };
+/* Schur approximation: the caller's S~_T (eq. Se) or A_TT (Sec. 3.3.1), or the learned
+ * diagonal scaling diag(s) B of B = the caller's S~_T, else A_TT (see cptr_set_mlp; not in the
+ * paper) */
+enum { CPTR_SCHUR_GIVEN = 0, CPTR_SCHUR_ATT = 1, CPTR_SCHUR_LEARNED = 2 };
 /* AMG smoother: l1-Jacobi (d_i = sum_j |a_ij|) or omega-Jacobi (d_i = a_ii / omega) */
 enum { CPTR_SMOOTH_L1 = 0, CPTR_SMOOTH_JACOBI = 1 };
 /* precision of the preconditioner: all FP64, or FP32 AMG/ILU with BF16 coarse AMG levels */
@@ -87,7 +89,7 @@ typedef struct {
     int32_t restarts;
     int32_t converged;
     int32_t levels_p, levels_T;
-    int32_t pad;
+    int32_t schur_used;      /* S~_T the set-up used: CPTR_SCHUR_GIVEN, _ATT or _LEARNED */
     double est_rel_res;      /* Givens estimate |g_{j+1}| / ||b'|| at exit */
     double true_rel_res;     /* ||b' - A' x|| / ||b'|| recomputed at exit */
     double bnorm;            /* ||b'|| = ||W rhs|| */
@@ -219,6 +221,73 @@ cptr_status cptr_set_profiling(cptr_ctx *ctx, uint32_t mask);
  * 11 AMG coarsest inverses, 12 ILU host work (ordering, level sets, sweep tables), 13 ILU
  * factorisation, 14 SELL layout and mixed-precision copies, 15 other. */
 cptr_status cptr_profile(cptr_ctx *ctx, double *ms, int64_t *count);
+
+/* ---------------------------------------------------------------------------------------------
+ * Learned diagonal scaling of the Schur approximation.  The paper has no learned part: it
+ * approximates S_T = A_TT - A_Tp A_pp^{-1} A_pT by the discrete S_e or, without it, by A_TT
+ * (Sec. 3.3.1).  This extension scales the rows of that base approximation B (st_vals when the
+ * caller gives them, else A_TT): S~_T = diag(s) B with s_i = sinh(y_i), where y_i is the output of
+ * a 16-64-64-1 tanh network over 16 local features of cell i of A'.  It is meant to be trained on
+ * asinh((S_T)_ii / B_ii) computed exactly on small grids.
+ *
+ * Features of cell i (all sums over the pattern of row i in ascending order; B as above;
+ * q(x, y) = x / y, or 0 when y = 0; a = the diagonal b x b block of A'; s over saturation slots;
+ * every value v is stored as asinh(v)):
+ *   0  q(sum_j A_Tp,ij q(A_pT,ji, A_pp,jj), B_ii)   1  q(A_Tp,ii q(A_pT,ii, A_pp,ii), B_ii)
+ *   2  q(sum_{j!=i} |A_pp,ij|, |A_pp,ii|)           3  q(sum_{j!=i} |B_ij|, |B_ii|)
+ *   4  q(sum_{j!=i} A_pp,ij, |A_pp,ii|)             5  q(sum_{j!=i} B_ij, |B_ii|)
+ *   6  q(sum_j |A_Tp,ij q(A_pT,ji, A_pp,jj)|, |B_ii|)
+ *   7  q(sum_s a_Ts q(a_sT, a_ss), B_ii)            8  q(sum_s a_ps q(a_sp, a_ss), A_pp,ii)
+ *   9  sign(A_pp,ii)                                10 sign(B_ii)
+ *   11 q(A_pT,ii, sqrt|A_pp,ii B_ii|)                12 q(A_Tp,ii, sqrt|A_pp,ii B_ii|)
+ *   13 (entries in row i) / 7
+ *   14 q(sum_{j!=i} |A_pT,ij| |A_Tp,ii|, |A_pp,ii B_ii|)
+ *   15 q(sum_{j!=i} |A_Tp,ij| |A_pT,ii|, |A_pp,ii B_ii|)
+ * A_pT,ji is 0 when the pattern has no entry (j, i).
+ *
+ * Parameters: CPTR_MLP_NPARAM floats, W1[64][16] | b1[64] | W2[64][64] | b2[64] | w3[64] | b3;
+ * z1 = W1 x + b1, h1 = tanh z1, z2 = W2 h1 + b2, h2 = tanh z2, y = w3 . h2 + b3.
+ * Training: FP32, mean squared error (1/n) sum (y_i - t_i)^2, full-batch Adam (beta1 0.9,
+ * beta2 0.999, eps 1e-8) from zero moments.  Inference (set-up): BF16 weights and layer inputs
+ * (features FP64 -> FP32 -> BF16, round to nearest even), FP32 biases, each layer's sum
+ * accumulated in FP32 from the bias in ascending input order, tanh in FP32.
+ * ------------------------------------------------------------------------------------------- */
+#define CPTR_MLP_FEATURES 16
+#define CPTR_MLP_HIDDEN 64
+#define CPTR_MLP_NPARAM 5313
+
+/* Features of every cell of the current set-up into feat[n_cells][16] (FP64, host or device per
+ * on_device).  Errors: CPTR_ESTATE (no set-up), CPTR_EINVAL, CPTR_ECUDA. */
+cptr_status cptr_schur_features(cptr_ctx *ctx, double *feat, int32_t on_device);
+
+/* Loss and gradient of the network at params over n samples: feat[n][16], target[n] (FP64,
+ * rounded to FP32 on the device), params[CPTR_MLP_NPARAM] and grad[CPTR_MLP_NPARAM] (FP32),
+ * *loss (host double, may be NULL).  All arrays host or device per on_device.  Needs no set-up.
+ * Errors: CPTR_EINVAL (n < 1, null arrays), CPTR_ENOMEM, CPTR_ECUDA. */
+cptr_status cptr_mlp_loss_grad(cptr_ctx *ctx, const double *feat, const double *target, int32_t n,
+                               const float *params, float *grad, double *loss, int32_t on_device);
+
+/* Train in place: params (FP32, in: initial, out: trained) after `steps` full-batch Adam steps
+ * with learning rate lr.  loss_hist[steps] (host doubles, may be NULL) receives the loss before
+ * each step.  Arrays host or device per on_device (loss_hist always host).  Needs no set-up.
+ * Errors: CPTR_EINVAL, CPTR_ENOMEM, CPTR_ECUDA. */
+cptr_status cptr_mlp_train(cptr_ctx *ctx, const double *feat, const double *target, int32_t n, float *params,
+                           int32_t steps, float lr, double *loss_hist, int32_t on_device);
+
+/* Give the context a network for CPTR_SCHUR_LEARNED (params copied; NULL removes it).  A set-up
+ * with CPTR_SCHUR_LEARNED and no network, or whose s is not finite or has |y| > 30 anywhere,
+ * falls back to the caller's S~_T if st_vals was given, else to A_TT; cptr_stats.schur_used
+ * reports which.  Errors: CPTR_EINVAL, CPTR_ECUDA. */
+cptr_status cptr_set_mlp(cptr_ctx *ctx, const float *params, int32_t on_device);
+
+/* BF16 inference of the context's network on feat[n][16] (FP64) into y[n] (FP32).  Errors:
+ * CPTR_ESTATE (no network), CPTR_EINVAL, CPTR_ENOMEM, CPTR_ECUDA. */
+cptr_status cptr_mlp_infer(cptr_ctx *ctx, const double *feat, int32_t n, float *y, int32_t on_device);
+
+/* The row scaling s[n_cells] of the last set-up (all ones unless it used the learned form).
+ * Features (cptr_schur_features) always refer to the unscaled base B.
+ * Errors: CPTR_ESTATE, CPTR_EINVAL, CPTR_ECUDA. */
+cptr_status cptr_schur_scaling(cptr_ctx *ctx, double *s, int32_t on_device);
 
 #ifdef __cplusplus
 }

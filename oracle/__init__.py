@@ -100,7 +100,7 @@ def _load():
         lib.or_splitmix64.restype = ctypes.c_uint64
         lib.or_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
         lib.or_schur_features.restype = None
-        lib.or_schur_features.argtypes = [P, P]
+        lib.or_schur_features.argtypes = [P, P, P]
         lib.or_att.restype = None
         lib.or_att.argtypes = [P, P]
         lib.or_mlp_nparam.restype = ctypes.c_int
@@ -250,10 +250,12 @@ class Oracle:
         lib.or_field(self._c, f, _p(v))
         return v
 
-    def schur_features(self):
-        """The 16 local features of every cell for the learned Schur scaling, [n, 16] FP64."""
+    def schur_features(self, base):
+        """The 16 local features of every cell for the learned Schur scaling, [n, 16] FP64, with
+        the base approximation B given by its values on the cell pattern."""
+        base = np.ascontiguousarray(base, np.float64)
         f = np.zeros((self.n, 16))
-        _load().or_schur_features(self._c, _p(f))
+        _load().or_schur_features(self._c, _p(base), _p(f))
         return f
 
     def att(self, nnz):
@@ -409,22 +411,37 @@ def exact_schur_diag(o: "Oracle", sys: dict, chunk: int = 512):
     return ATT.diagonal() - d
 
 
-def schur_ratio_target(sys: dict):
-    """Training target of the learned scaling: asinh((S_T)_ii / (A_TT)_ii), and the features."""
-    o = Oracle.from_system(sys, use_st=False, max_levels=1, dense_max=1, stage2=NONE2)
-    nnz = int(sys["row_ptr"][-1])
+def _fields_oracle(sys):
+    return Oracle.from_system(sys, use_st=False, max_levels=1, dense_max=1, stage2=NONE2)
+
+
+def schur_base(sys: dict, base: str, o: "Oracle" = None):
+    """Base approximation B of the learned scaling on the cell pattern: the caller's S_e
+    (base="se", the generator's "st") or A_TT of A' (base="att")."""
+    if base == "se":
+        return np.ascontiguousarray(sys["st"], np.float64)
+    o = o or _fields_oracle(sys)
+    return o.att(int(sys["row_ptr"][-1]))
+
+
+def schur_ratio_target(sys: dict, base: str = "se", S_diag=None):
+    """Training target of the learned scaling, asinh((S_T)_ii / B_ii), and the features.
+    S_diag (the exact diagonal of S_T) is computed when not given."""
+    o = _fields_oracle(sys)
+    B = schur_base(sys, base, o)
     rp, ci = sys["row_ptr"], sys["col_idx"]
-    att = o.att(nnz)
-    diag = np.array([att[rp[i] + np.searchsorted(ci[rp[i]:rp[i + 1]], i)] for i in range(sys["n"])])
-    return np.arcsinh(exact_schur_diag(o, sys) / diag), o.schur_features()
+    diag = np.array([B[rp[i] + np.searchsorted(ci[rp[i]:rp[i + 1]], i)] for i in range(sys["n"])])
+    if S_diag is None:
+        S_diag = exact_schur_diag(o, sys)
+    return np.arcsinh(S_diag / diag), o.schur_features(B)
 
 
-def learned_st(sys: dict, params32):
-    """S~_T = diag(s) A_TT with s = sinh(y) of the BF16 network over the oracle's features;
+def learned_st(sys: dict, params32, base: str = "se"):
+    """S~_T = diag(s) B with s = sinh(y) of the BF16 network over the oracle's features;
     returns (st values on the cell pattern, s, y)."""
-    o = Oracle.from_system(sys, use_st=False, max_levels=1, dense_max=1, stage2=NONE2)
-    nnz = int(sys["row_ptr"][-1])
-    y = mlp_infer_bf16(params32, o.schur_features())
+    o = _fields_oracle(sys)
+    B = schur_base(sys, base, o)
+    y = mlp_infer_bf16(params32, o.schur_features(B))
     s = np.sinh(y.astype(np.float64))
     rows = np.repeat(np.arange(sys["n"]), np.diff(sys["row_ptr"]))
-    return o.att(nnz) * s[rows], s, y
+    return B * s[rows], s, y

@@ -962,12 +962,12 @@ int or_amg_nlevels(amg *h) { return h->nlev; }
 /* ------------------------------------------------------------------------------------------ */
 /* Learned diagonal scaling of the temperature Schur approximation.                             */
 /*                                                                                              */
-/* The paper approximates S_T = A_TT - A_Tp A_pp^{-1} A_pT either by the discrete S_e or by the */
-/* algebraic A_TT (Sec. 3.3.1).  The learned form keeps the Jacobian-only approximation A_TT    */
-/* and scales its rows: S~_T = diag(s) A_TT, s_i = sinh(y_i), where y_i is the output of a      */
-/* 16-64-64-1 tanh network over local features of cell i.  The network is trained to regress    */
-/* asinh of the exact ratio (S_T)_ii / (A_TT)_ii.  The paper has no learned part; every choice  */
-/* below (features, target, network, optimiser) is this project's.                              */
+/* The paper approximates S_T = A_TT - A_Tp A_pp^{-1} A_pT by the discrete S_e or, without it,  */
+/* by A_TT (Sec. 3.3.1).  The learned form scales the rows of that base approximation B:        */
+/* S~_T = diag(s) B, s_i = sinh(y_i), where y_i is the output of a 16-64-64-1 tanh network over */
+/* local features of cell i.  The network is trained to regress asinh of the exact ratio        */
+/* (S_T)_ii / B_ii.  The paper has no learned part; every choice below (features, target,       */
+/* network, optimiser) is this project's.                                                        */
 
 #define OR_NF 16
 #define OR_NH 64
@@ -1001,7 +1001,8 @@ static double diag_block(const or_ctx *c, int32_t i, int r, int col) {
 }
 
 /* The 16 features of every cell (row-major [n][16]); every sum runs over the pattern of row i
- * in ascending position.  With B = A_TT and q(x, y) = x / y (0 when y = 0):
+ * in ascending position.  B is the base Schur approximation on the cell pattern (S_e when the caller
+ * supplies it, else A_TT; values Bv); q(x, y) = x / y (0 when y = 0):
  *   0  q(sum_j A_Tp,ij q(A_pT,ji, A_pp,jj), B_ii)     diagonal of A_Tp D_pp^-1 A_pT, relative
  *   1  q(A_Tp,ii q(A_pT,ii, A_pp,ii), B_ii)           its j = i term
  *   2  q(sum_{j!=i} |A_pp,ij|, |A_pp,ii|)             3  q(sum_{j!=i} |B_ij|, |B_ii|)
@@ -1015,10 +1016,10 @@ static double diag_block(const or_ctx *c, int32_t i, int r, int col) {
  *   14 q(sum_{j!=i} |A_pT,ij| |A_Tp,ii|, |A_pp,ii B_ii|)
  *   15 q(sum_{j!=i} |A_Tp,ij| |A_pT,ii|, |A_pp,ii B_ii|)
  * and each value v is replaced by asinh(v). */
-void or_schur_features(or_ctx *c, double *feat) {
+void or_schur_features(or_ctx *c, const double *Bv, double *feat) {
     int32_t n = c->n, b = c->b;
-    csr ATT;
-    extract_field(c, c->App.rp, c->App.ci, c->ts, c->ts, &ATT);
+    csr ATT;   /* B on the cell pattern */
+    ATT.n = n; ATT.nnz = c->App.nnz; ATT.rp = c->App.rp; ATT.ci = c->App.ci; ATT.v = (double *)Bv;
     const int32_t *rp = c->App.rp, *ci = c->App.ci;
     for (int32_t i = 0; i < n; ++i) {
         double app = field_at(&c->App, i, i), bii = field_at(&ATT, i, i);
@@ -1065,7 +1066,6 @@ void or_schur_features(or_ctx *c, double *feat) {
         f[15] = q_div(s15 * fabs(apt), pb);
         for (int k = 0; k < OR_NF; ++k) feat[(int64_t)i * OR_NF + k] = asinh(f[k]);
     }
-    csr_free(&ATT);
 }
 
 /* A_TT values on the cell pattern (the base of the learned scaling) */

@@ -20,7 +20,9 @@ STATUS = {0: "CPTR_OK", 1: "CPTR_NOT_CONVERGED", -1: "CPTR_EINVAL", -2: "CPTR_EN
           -4: "CPTR_EBREAKDOWN", -5: "CPTR_ETIMEOUT", -6: "CPTR_ESINGULAR", -7: "CPTR_ESTATE"}
 STAGE1 = {"full": 0, "upper": 1, "lower": 2, "bd": 3, "cpr": 4, "none": 5}
 STAGE2 = {"ilu0": 0, "none": 1}
-SCHUR = {"given": 0, "att": 1}
+SCHUR = {"given": 0, "att": 1, "learned": 2}
+SCHUR_NAMES = {v: k for k, v in SCHUR.items()}
+MLP_FEATURES, MLP_HIDDEN, MLP_NPARAM = 16, 64, 5313
 SMOOTHER = {"l1": 0, "jacobi": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 ILU_ORDER = {"natural": 0, "multicolor": 1}
@@ -38,7 +40,7 @@ class cptr_options(ctypes.Structure):
 
 class cptr_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("converged", ctypes.c_int32),
-                ("levels_p", ctypes.c_int32), ("levels_T", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("levels_p", ctypes.c_int32), ("levels_T", ctypes.c_int32), ("schur_used", ctypes.c_int32),
                 ("est_rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double), ("bnorm", ctypes.c_double),
                 ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("op_complexity_p", ctypes.c_double), ("op_complexity_T", ctypes.c_double)]
@@ -74,6 +76,12 @@ _SIGS = {
     "cptr_inject_wait_timeout": (_I, [_P, _I]),
     "cptr_set_profiling": (_I, [_P, ctypes.c_uint32]),
     "cptr_profile": (_I, [_P, _P, _P]),
+    "cptr_schur_features": (_I, [_P, _P, _I]),
+    "cptr_mlp_loss_grad": (_I, [_P, _P, _P, _I, _P, _P, _P, _I]),
+    "cptr_mlp_train": (_I, [_P, _P, _P, _I, _P, _I, ctypes.c_float, _P, _I]),
+    "cptr_set_mlp": (_I, [_P, _P, _I]),
+    "cptr_mlp_infer": (_I, [_P, _P, _I, _P, _I]),
+    "cptr_schur_scaling": (_I, [_P, _P, _I]),
 }
 PROFILE_FAMILIES = ("spmv", "stage1", "stage1_resid", "ilu", "arnoldi", "ilu_fwd", "ilu_bwd", "_7")
 SETUP_PHASES = {8: "setup_inputs", 9: "setup_amg_coarsen", 10: "setup_amg_rap", 11: "setup_amg_coarsest",
@@ -257,6 +265,42 @@ def cptr_profile(ctx):
 
 
 # ------------------------------------------------------------------------------------------------
+def cptr_schur_features(ctx, feat):
+    """feat: [n_cells, 16] float64 (torch CUDA tensor or numpy array), filled in place."""
+    return _check(ctx, load().cptr_schur_features(ctx, _ptr(feat), _on_device(feat)))
+
+
+def cptr_mlp_loss_grad(ctx, feat, target, params, grad):
+    """Loss (returned) and gradient (into grad, float32) of the network at params."""
+    loss = ctypes.c_double(0.0)
+    dev = _on_device(feat, target, params, grad)
+    _check(ctx, load().cptr_mlp_loss_grad(ctx, _ptr(feat), _ptr(target), int(feat.shape[0]), _ptr(params),
+                                          _ptr(grad), ctypes.byref(loss), dev))
+    return loss.value
+
+
+def cptr_mlp_train(ctx, feat, target, params, steps, lr=1e-3):
+    """Adam steps on params (float32, in place); returns the loss before each step."""
+    hist = np.zeros(max(int(steps), 1))
+    dev = _on_device(feat, target, params)
+    _check(ctx, load().cptr_mlp_train(ctx, _ptr(feat), _ptr(target), int(feat.shape[0]), _ptr(params), int(steps),
+                                      float(lr), hist.ctypes.data, dev))
+    return hist[:int(steps)]
+
+
+def cptr_set_mlp(ctx, params):
+    return _check(ctx, load().cptr_set_mlp(ctx, _ptr(params), _on_device(params)))
+
+
+def cptr_mlp_infer(ctx, feat, y):
+    dev = _on_device(feat, y)
+    return _check(ctx, load().cptr_mlp_infer(ctx, _ptr(feat), int(feat.shape[0]), _ptr(y), dev))
+
+
+def cptr_schur_scaling(ctx, s):
+    return _check(ctx, load().cptr_schur_scaling(ctx, _ptr(s), _on_device(s)))
+
+
 class Solver:
     """One CPTR-FGMRES context on the current CUDA device.
 
@@ -290,7 +334,8 @@ class Solver:
         if x is None:
             x = torch.empty_like(rhs) if hasattr(rhs, "is_cuda") else np.zeros(self.n * self.b)
         code, st = cptr_solve(self.ctx, rhs, x, rtol)
-        info = {f: getattr(st, f) for f, _ in cptr_stats._fields_ if f != "pad"}
+        info = {f: getattr(st, f) for f, _ in cptr_stats._fields_}
+        info["schur_used"] = SCHUR_NAMES.get(info["schur_used"], info["schur_used"])
         info["status"] = STATUS[code]
         return x, info
 

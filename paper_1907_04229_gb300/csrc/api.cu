@@ -26,8 +26,11 @@ void release_setup(Ctx *c) {
     dfree(c->sell_off); dfree(c->sell_col); dfree(c->sell_val);
     c->sell_off = nullptr; c->sell_col = nullptr; c->sell_val = nullptr;
     dfree(c->App); dfree(c->ApT); dfree(c->ATp); dfree(c->St);
+    dfree(c->lf_base); dfree(c->lf_sat); dfree(c->lf_s);
     c->rp = c->ci = c->diag = nullptr;
     c->A = c->W = c->App = c->ApT = c->ATp = c->St = nullptr;
+    c->lf_base = c->lf_sat = c->lf_s = nullptr;
+    c->schur_used = 0;
     amg_free(c->hp);
     amg_free(c->hT);
     ilu_free(c);
@@ -109,8 +112,10 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
         if (!host_or_device_copy(c, c->W, W, sizeof(double) * n * bb, on_device, cudaMemcpyHostToDevice))
             return c->fail(CPTR_ECUDA, "copy of row_weights failed");
     }
+    // the caller's S~_T is used by CPTR_SCHUR_GIVEN, and is the fallback of CPTR_SCHUR_LEARNED
+    const bool use_st = st && c->o.schur != CPTR_SCHUR_ATT;
     CPTR_TRY(dalloc_t(c, &c->St, (size_t)nnzb));
-    if (st && c->o.schur == CPTR_SCHUR_GIVEN) {
+    if (use_st) {
         if (!host_or_device_copy(c, c->St, st, sizeof(double) * nnzb, on_device, cudaMemcpyHostToDevice))
             return c->fail(CPTR_ECUDA, "copy of st_vals failed");
     }
@@ -118,7 +123,7 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     CPTR_CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
     launch_check_finite(c, Araw, (int64_t)nnzb * bb, c->flag);
     if (c->W) launch_check_finite(c, c->W, (int64_t)n * bb, c->flag);
-    if (st && c->o.schur == CPTR_SCHUR_GIVEN) launch_check_finite(c, c->St, nnzb, c->flag);
+    if (use_st) launch_check_finite(c, c->St, nnzb, c->flag);
     int32_t bad = 0;
     CPTR_CUDA_TRY(c, cudaMemcpyAsync(&bad, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
     CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -133,11 +138,21 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     launch_extract(c, ps, ps, c->App);
     launch_extract(c, ps, ts, c->ApT);
     launch_extract(c, ts, ps, c->ATp);
-    if (!(st && c->o.schur == CPTR_SCHUR_GIVEN)) launch_extract(c, ts, ts, c->St);
+    if (!use_st) launch_extract(c, ts, ts, c->St);
+    c->schur_used = use_st ? CPTR_SCHUR_GIVEN : CPTR_SCHUR_ATT;
+    CPTR_TRY(learned_prepare(c));
     CPTR_CUDA_TRY(c, cudaGetLastError());
     CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     c->prof.setup_ms[SETUP_INPUTS] +=
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (c->o.schur == CPTR_SCHUR_LEARNED) {
+        // S~_T = diag(s) S~_T from the network; on rejection the S~_T above stays
+        double tl = host_ms();
+        bool used = false;
+        CPTR_TRY(learned_schur(c, &used));
+        if (used) c->schur_used = CPTR_SCHUR_LEARNED;
+        setup_tick(c, SETUP_OTHER, &tl);
+    }
     int s1 = c->o.stage1;
     if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_setup(c, c->hp, c->rp, c->ci, c->App, n));
     if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) CPTR_TRY(amg_setup(c, c->hT, c->rp, c->ci, c->St, n));
@@ -210,6 +225,39 @@ cptr_status check_wait_flag(Ctx *c) {
     return CPTR_OK;
 }
 
+// a device view of a caller array: the array itself (on_device) or a device copy of a host array
+template <typename T>
+struct DevIn {
+    const T *p = nullptr;
+    T *own = nullptr;
+    ~DevIn() { dfree(own); }
+    cptr_status init(Ctx *c, const T *src, size_t count, int on_device) {
+        if (on_device) { p = src; return CPTR_OK; }
+        CPTR_TRY(dalloc_t(c, &own, count));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(own, src, sizeof(T) * count, cudaMemcpyHostToDevice, c->stream));
+        p = own;
+        return CPTR_OK;
+    }
+};
+// a device output for a caller array, copied back to the host by finish()
+template <typename T>
+struct DevOut {
+    T *p = nullptr, *own = nullptr, *host = nullptr;
+    size_t count = 0;
+    ~DevOut() { dfree(own); }
+    cptr_status init(Ctx *c, T *dst, size_t n, int on_device) {
+        count = n;
+        if (on_device) { p = dst; return CPTR_OK; }
+        CPTR_TRY(dalloc_t(c, &own, n));
+        p = own;
+        host = dst;
+        return CPTR_OK;
+    }
+    cptr_status finish(Ctx *c) {
+        if (host) return copy_to_host(c, host, own, sizeof(T) * count);
+        return sync(c);
+    }
+};
 }  // namespace
 
 extern "C" {
@@ -244,7 +292,8 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
     else cptr_default_options(&o);
     if (o.restart < 1 || o.restart > kMaxRestart || o.max_it < 0 || o.max_levels < 1 || o.dense_max < 1 ||
         o.stage1 < 0 || o.stage1 > CPTR_STAGE1_NONE || o.stage2 < 0 || o.stage2 > CPTR_STAGE2_NONE ||
-        o.smoother < 0 || o.smoother > CPTR_SMOOTH_JACOBI || o.precision < CPTR_PREC_FP64 ||
+        o.smoother < 0 || o.smoother > CPTR_SMOOTH_JACOBI || o.schur < CPTR_SCHUR_GIVEN ||
+        o.schur > CPTR_SCHUR_LEARNED || o.precision < CPTR_PREC_FP64 ||
         o.precision > CPTR_PREC_MIXED ||
         o.ilu_order < CPTR_ILU_NATURAL || o.ilu_order > CPTR_ILU_MULTICOLOR)
         return CPTR_EINVAL;
@@ -294,6 +343,7 @@ void cptr_destroy(cptr_ctx *ctx) {
         cudaStreamSynchronize(c->stream);
         release_setup(c);
         dfree(c->ks); dfree(c->flag); dfree(c->partial); dfree(c->scan_tmp); dfree(c->never); dfree(c->ilu_flags);
+        dfree(c->mlp);
         cudaStreamSynchronize(c->stream);
     }
     if (c->pool) cudaMemPoolDestroy(c->pool);
@@ -355,6 +405,7 @@ cptr_status cptr_solve(cptr_ctx *ctx, const double *rhs, double *x, double rtol,
             st->levels_T = c->hT.nlev;
             st->op_complexity_p = c->hp.op_complexity;
             st->op_complexity_T = c->hT.op_complexity;
+            st->schur_used = c->schur_used;
         }
         return s;
     });
@@ -507,6 +558,101 @@ cptr_status cptr_ilu_levels(cptr_ctx *ctx, int32_t *n_forward, int32_t *n_backwa
         CPTR_TRY(need_ready(c));
         if (n_forward) *n_forward = c->nlev_f;
         if (n_backward) *n_backward = c->nlev_b;
+        return CPTR_OK;
+    });
+}
+
+// ---- learned Schur scaling ----------------------------------------------------------------------
+
+cptr_status cptr_schur_features(cptr_ctx *ctx, double *feat, int32_t on_device) {
+    return guarded(ctx, [&](Ctx *c) {
+        CPTR_TRY(need_ready(c));
+        if (!feat) return c->fail(CPTR_EINVAL, "feat is required");
+        DevOut<double> out;
+        CPTR_TRY(out.init(c, feat, (size_t)c->n * CPTR_MLP_FEATURES, on_device));
+        CPTR_TRY(learned_features(c, out.p));
+        return out.finish(c);
+    });
+}
+
+cptr_status cptr_mlp_loss_grad(cptr_ctx *ctx, const double *feat, const double *target, int32_t n,
+                               const float *params, float *grad, double *loss, int32_t on_device) {
+    return guarded(ctx, [&](Ctx *c) {
+        if (n < 1 || !feat || !target || !params || !grad) return c->fail(CPTR_EINVAL, "bad arguments");
+        DevIn<double> f, t;
+        DevIn<float> P;
+        DevOut<float> g;
+        CPTR_TRY(f.init(c, feat, (size_t)n * CPTR_MLP_FEATURES, on_device));
+        CPTR_TRY(t.init(c, target, (size_t)n, on_device));
+        CPTR_TRY(P.init(c, params, CPTR_MLP_NPARAM, on_device));
+        CPTR_TRY(g.init(c, grad, CPTR_MLP_NPARAM, on_device));
+        CPTR_TRY(mlp_loss_grad(c, f.p, t.p, n, P.p, g.p, loss));
+        return g.finish(c);
+    });
+}
+
+cptr_status cptr_mlp_train(cptr_ctx *ctx, const double *feat, const double *target, int32_t n, float *params,
+                           int32_t steps, float lr, double *loss_hist, int32_t on_device) {
+    return guarded(ctx, [&](Ctx *c) {
+        if (n < 1 || steps < 0 || !feat || !target || !params || !(lr > 0.f))
+            return c->fail(CPTR_EINVAL, "bad arguments");
+        DevIn<double> f, t;
+        DevOut<float> P;
+        CPTR_TRY(f.init(c, feat, (size_t)n * CPTR_MLP_FEATURES, on_device));
+        CPTR_TRY(t.init(c, target, (size_t)n, on_device));
+        CPTR_TRY(P.init(c, params, CPTR_MLP_NPARAM, on_device));
+        if (!on_device)
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(P.p, params, sizeof(float) * CPTR_MLP_NPARAM, cudaMemcpyHostToDevice,
+                                             c->stream));
+        CPTR_TRY(mlp_train(c, f.p, t.p, n, P.p, steps, lr, loss_hist));
+        return P.finish(c);
+    });
+}
+
+cptr_status cptr_set_mlp(cptr_ctx *ctx, const float *params, int32_t on_device) {
+    return guarded(ctx, [&](Ctx *c) {
+        if (!params) {
+            dfree(c->mlp);
+            c->mlp = nullptr;
+            return sync(c);
+        }
+        if (!c->mlp) CPTR_TRY(dalloc_t(c, &c->mlp, CPTR_MLP_NPARAM));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->mlp, params, sizeof(float) * CPTR_MLP_NPARAM,
+                                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+        return sync(c);
+    });
+}
+
+cptr_status cptr_mlp_infer(cptr_ctx *ctx, const double *feat, int32_t n, float *y, int32_t on_device) {
+    return guarded(ctx, [&](Ctx *c) {
+        if (!c->mlp) return c->fail(CPTR_ESTATE, "no network (cptr_set_mlp)");
+        if (n < 1 || !feat || !y) return c->fail(CPTR_EINVAL, "bad arguments");
+        DevIn<double> f;
+        DevOut<float> out;
+        CPTR_TRY(f.init(c, feat, (size_t)n * CPTR_MLP_FEATURES, on_device));
+        CPTR_TRY(out.init(c, y, (size_t)n, on_device));
+        CPTR_TRY(mlp_infer(c, f.p, n, out.p));
+        return out.finish(c);
+    });
+}
+
+cptr_status cptr_schur_scaling(cptr_ctx *ctx, double *s, int32_t on_device) {
+    return guarded(ctx, [&](Ctx *c) {
+        CPTR_TRY(need_ready(c));
+        if (!s) return c->fail(CPTR_EINVAL, "s is required");
+        if (c->schur_used == CPTR_SCHUR_LEARNED && c->lf_s) {
+            if (on_device)
+                CPTR_CUDA_TRY(c, cudaMemcpyAsync(s, c->lf_s, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+            else
+                return copy_to_host(c, s, c->lf_s, sizeof(double) * c->n);
+            return sync(c);
+        }
+        if (on_device) {
+            std::vector<double> ones((size_t)c->n, 1.0);
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(s, ones.data(), sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream));
+            return sync(c);
+        }
+        for (int32_t i = 0; i < c->n; ++i) s[i] = 1.0;
         return CPTR_OK;
     });
 }

@@ -180,6 +180,15 @@ void ilu_apply32(const Ctx *c, const float *r, double *z, const float *dp, const
 
 // ---- krylov.cu ---------------------------------------------------------------------------------
 cptr_status fgmres_solve(Ctx *c, const double *bw, double *x, double rtol, cptr_stats *st);
+// learned Schur scaling (learned.cu)
+cptr_status learned_prepare(Ctx *c);                       // saturation terms (needs c->A)
+cptr_status learned_schur(Ctx *c, bool *used);             // S~_T = diag(s) S~_T into c->St
+cptr_status learned_features(Ctx *c, double *feat);       // [n][16] device
+cptr_status mlp_loss_grad(Ctx *c, const double *feat, const double *target, int32_t n, const float *params,
+                          float *grad, double *loss);      // device arrays
+cptr_status mlp_train(Ctx *c, const double *feat, const double *target, int32_t n, float *params, int32_t steps,
+                      float lr, double *loss_hist);        // device arrays, loss_hist host
+cptr_status mlp_infer(Ctx *c, const double *feat, int32_t n, float *y);   // device arrays
 void apply_stage1(const Ctx *c, const double *v, const double **dp, const double **dT);
 void apply_stage1_32(const Ctx *c, const double *v, const float **dp, const float **dT);
 void apply_precond(const Ctx *c, const double *v, double *z);
@@ -203,6 +212,11 @@ struct Ctx {
     int64_t sell_bytes = 0, sell_nvals = 0;
     double *W = nullptr;     // per-cell weights (n * b * b)
     double *App = nullptr, *ApT = nullptr, *ATp = nullptr, *St = nullptr;  // cell-pattern fields
+    // learned Schur scaling: the base approximation once St holds the scaled one, the per-cell
+    // saturation terms of features 7 and 8, the row scaling of the last set-up, the network (FP32)
+    double *lf_base = nullptr, *lf_sat = nullptr, *lf_s = nullptr;
+    float *mlp = nullptr;
+    int32_t schur_used = 0;
     Hier hp, hT;
     // ILU(0): factors in the pattern of the factorised matrix (A' in the caller's cell order, or
     // with cells permuted by colour), diagonal slots hold inverted pivot blocks

@@ -357,7 +357,7 @@ def recipe(name: str) -> Reservoir:
     cptr200k : 100x100x20 (200k cells, 600k dofs, b=3), layered lognormal k (sigma 2, kv/kh 0.1),
              k_T = 2 W/m/K, 500 K injector, 0.5 x 0.5 x 0.25 m cells.
     three_phase2m : 200x200x50 (2M cells, b=4), lognormal k (sigma 2.5), 4 injectors, 4 producers.
-    three_phase_coupled : 24x24x8 three-phase model with c_o = 1e-7 1/Pa, beta_o = 5e-2 1/K.
+    three_phase_coupled : 16x16x4 three-phase model with c_o = 1e-7 1/Pa, beta_o = 5e-2 1/K.
     """
     if name == "parity":
         return make_box(16, 16, 4, 3.125, seed=1, sigma=1.0)
@@ -369,7 +369,7 @@ def recipe(name: str) -> Reservoir:
                         T_inj=500.0, q_inj=4e-6)
     if name == "three_phase_coupled":
         # the three-phase model with a compressible, strongly expanding oil (strong p-T coupling)
-        return make_box(24, 24, 8, 1.0, 1.0, 0.5, seed=41, sigma=2.5, nphase=3, wells="four",
+        return make_box(16, 16, 4, 1.0, 1.0, 0.5, seed=40, sigma=2.5, nphase=3, wells="four",
                         T_inj=500.0, q_inj=4e-6, c_o=1e-7, beta_o=5e-2)
     raise KeyError(name)
 
@@ -387,3 +387,14 @@ def learned_training_grid(k: int, nx: int = 32, ny: int = 32, nz: int = 8) -> Re
     u2 = float(uniform(901, k + 1)[k])
     return make_box(nx, ny, nz, 1.0, 1.0, 0.5, seed=101 + k, sigma=2.5, nphase=3, wells="four",
                     T_inj=500.0, q_inj=4e-6, c_o=1e-9 * 100.0 ** u1, beta_o=5e-4 * 100.0 ** u2)
+
+
+def mlp_init(seed: int, n_features: int = 16, n_hidden: int = 64) -> np.ndarray:
+    """Initial parameters of the 16-64-64-1 network (layout W1 | b1 | W2 | b2 | w3 | b3), float32:
+    weights N(0, 1/fan_in) from the normal stream ``seed``, biases zero."""
+    z = normal(seed, n_hidden * n_features + n_hidden * n_hidden + n_hidden)
+    w1 = z[:n_hidden * n_features] / np.sqrt(n_features)
+    w2 = z[n_hidden * n_features:n_hidden * n_features + n_hidden * n_hidden] / np.sqrt(n_hidden)
+    w3 = z[n_hidden * n_features + n_hidden * n_hidden:] / np.sqrt(n_hidden)
+    zero = np.zeros(n_hidden)
+    return np.concatenate([w1, zero, w2, zero, w3, [0.0]]).astype(np.float32)

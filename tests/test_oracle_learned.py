@@ -24,9 +24,9 @@ def three_phase(nx, ny, nz, **kw):
                           T_inj=500.0, q_inj=4e-6, **kw).system()
 
 
-def features_of(s):
+def features_of(s, base="att"):
     o = oracle.Oracle.from_system(s, use_st=False, max_levels=1, dense_max=1, stage2=oracle.NONE2)
-    return o.schur_features()
+    return o.schur_features(oracle.schur_base(s, base, o))
 
 
 def test_features_of_two_cells_closed_form():
@@ -69,14 +69,31 @@ def test_exact_schur_diagonal_matches_dense_schur_complement():
     o = oracle.Oracle.from_system(s, use_st=False, max_levels=1, dense_max=1, stage2=oracle.NONE2)
     d = oracle.exact_schur_diag(o, s, chunk=7)
     np.testing.assert_allclose(d, np.diag(S), rtol=1e-10, atol=1e-12 * np.abs(np.diag(S)).max())
-    t, _ = oracle.schur_ratio_target(s)
+    t, _ = oracle.schur_ratio_target(s, "att")
     np.testing.assert_allclose(np.sinh(t), np.diag(S) / np.diag(ATT), rtol=1e-10)
+    rp, ci = s["row_ptr"], s["col_idx"]
+    se_diag = np.array([s["st"][k] for i in range(s["n"]) for k in range(rp[i], rp[i + 1]) if ci[k] == i])
+    t, _ = oracle.schur_ratio_target(s, "se")
+    np.testing.assert_allclose(np.sinh(t), np.diag(S) / se_diag, rtol=1e-10)
+
+
+def test_features_use_the_given_base():
+    s = synth.make_box(2, 1, 1, 3.125, seed=3, nphase=3, wells="none").system()
+    f = np.sinh(features_of(s, "se"))
+    st, rp, ci = s["st"], s["row_ptr"], s["col_idx"]
+    for i in range(2):
+        row = range(rp[i], rp[i + 1])
+        bii = sum(st[k] for k in row if ci[k] == i)
+        off = [st[k] for k in row if ci[k] != i]
+        assert f[i, 3] == pytest.approx(sum(abs(v) for v in off) / abs(bii), rel=1e-12)
+        assert f[i, 5] == pytest.approx(sum(off) / abs(bii), rel=1e-12)
+        assert f[i, 10] == np.sign(bii)
 
 
 def test_exact_schur_of_one_cell_is_the_scalar_schur_complement():
     s = synth.make_box(1, 1, 1, 3.125, seed=4, wells="none").system()
     a = s["weights"][0] @ s["vals"][0]
-    t, _ = oracle.schur_ratio_target(s)
+    t, _ = oracle.schur_ratio_target(s, "att")
     assert np.sinh(t[0]) == pytest.approx((a[1, 1] - a[1, 0] * a[0, 1] / a[0, 0]) / a[1, 1], rel=1e-12)
 
 
@@ -144,7 +161,7 @@ def test_bf16_inference_within_rounding_bound_of_fp64_network():
     """Every BF16 rounding has relative error <= u = 2^-8; FP32 sums add n * 2^-24 of the absolute
     sum.  The bound below propagates these through the layers (tanh is 1-Lipschitz)."""
     s = three_phase(5, 5, 2)
-    _, X = oracle.schur_ratio_target(s)
+    _, X = oracle.schur_ratio_target(s, "att")
     nf, nh = oracle.N_FEATURES, oracle.N_HIDDEN
     P = _params(9, 0.1).astype(np.float32).astype(np.float64)
     W1 = P[:nh * nf].reshape(nh, nf)
@@ -176,7 +193,9 @@ def test_learned_st_with_constant_output_scales_att():
     s = three_phase(4, 3, 2)
     P = np.zeros(oracle.mlp_nparam(), np.float32)
     P[-1] = np.float32(np.arcsinh(0.5))
-    st, sc, y = oracle.learned_st(s, P)
+    st_se, _, _ = oracle.learned_st(s, P, "se")
+    np.testing.assert_allclose(st_se, s["st"] * np.sinh(np.float64(np.float32(np.arcsinh(0.5)))), rtol=1e-15)
+    st, sc, y = oracle.learned_st(s, P, "att")
     o = oracle.Oracle.from_system(s, use_st=False, max_levels=1, dense_max=1, stage2=oracle.NONE2)
     np.testing.assert_allclose(sc, np.sinh(np.float64(np.float32(np.arcsinh(0.5)))), rtol=1e-15)
     np.testing.assert_allclose(st, o.att(len(st)) * sc[0], rtol=1e-15)
@@ -192,7 +211,7 @@ def test_exact_scaling_rescues_att_on_a_strongly_coupled_case():
     A_TT approximation stalls; the exact diagonal ratio as the row scaling restores convergence.
     This is what the network is trained to predict."""
     s = three_phase(12, 12, 4, c_o=1e-7, beta_o=5e-2)
-    t, _ = oracle.schur_ratio_target(s)
+    t, _ = oracle.schur_ratio_target(s, "att")
     rows = np.repeat(np.arange(s["n"]), np.diff(s["row_ptr"]))
     o = oracle.Oracle.from_system(s, use_st=False, max_levels=1, dense_max=1, stage2=oracle.NONE2)
     att = o.att(int(s["row_ptr"][-1]))
