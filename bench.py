@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-three-phase", action="store_true")
+    p.add_argument("--no-ensemble", action="store_true")
     return p.parse_args()
 
 
@@ -309,6 +310,9 @@ def ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
         tp = three_phase(args, dev, stream, flush)
+    ens = None
+    if not args.no_ensemble:
+        ens = ensemble(args, dev, stream, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -330,7 +334,7 @@ def ours(args, rank, world, local_rank):
                "solve_dofs_per_s": round(dofs / (solve_ms / 1e3), 1),
                "true_rel_res": infos[-1]["true_rel_res"], "levels": [infos[-1]["levels_p"], infos[-1]["levels_T"]],
                "families": families, "roofline": roofline, "rooflines": lines, "variants": variants,
-               "three_phase": tp,
+               "three_phase": tp, "ensemble": ens,
                "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clk}
         print(json.dumps(out), flush=True)
@@ -434,6 +438,90 @@ def three_phase(args, dev, stream, flush):
                      "status": infs[-1]["status"], "schur_used": infs[-1]["schur_used"],
                      "learned_setup_ms": round(prof["setup_other"][0], 3), "timed_runs": nrun}
         Sv.close()
+    return out
+
+
+def ensemble(args, dev, stream, flush):
+    """The ensemble workload: 64 two-phase instances with sizes from 20k to 430k cells (4M cells,
+    12M dofs in total), mixed-precision CPTR, rtol 1e-6 per instance, set up and solved as one
+    batch (one captured graph per Arnoldi step for all instances) with autotuned launch shapes;
+    and, for comparison, the same instances set up and solved one after another with the
+    single-system calls."""
+    import torch
+
+    import synth
+    import paper_1907_04229_gb300 as cp
+
+    shapes = synth.ensemble_sizes()
+    systems = [synth.ensemble_member(k, sh).system() for k, sh in enumerate(shapes)]
+    b = systems[0]["b"]
+    kind = torch.as_tensor(systems[0]["unknown_kind"], device=dev)
+    inst, rhs = [], []
+    for s in systems:
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+        inst.append(dict(n_cells=s["n"], row_ptr=t(s["row_ptr"]), col_idx=t(s["col_idx"]), vals=t(s["vals"].reshape(-1)),
+                         row_weights=t(s["weights"].reshape(-1)), st_vals=t(s["st"])))
+        rhs.append(t(s["rhs"].reshape(-1)))
+    cells = [s["n"] for s in systems]
+    dofs = sum(cells) * b
+    del systems
+    xs = [torch.empty_like(r) for r in rhs]
+    opts = dict(precision="mixed", autotune=1)
+    S = cp.Solver(stream=stream, **opts)
+
+    def step():
+        S.setup_batch(b, inst, kind)
+        return S.solve_batch(rhs, RTOL, x=xs)
+
+    step()
+    evs, res = [], []
+    for _ in range(2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res.append(step())
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(bb) for a, bb in evs) / len(evs)
+    _, status, infos = res[-1]
+    its = [i["iters"] for i in infos]
+    out = {"workload": f"{len(cells)} two-phase instances (3 unknowns/cell), {min(cells)}..{max(cells)} cells, "
+                       f"{sum(cells)} cells / {dofs} dofs in total, mixed-precision CPTR + ILU(0), FGMRES(30), "
+                       "rtol 1e-6 per instance",
+           "batched": {"ms_per_step": round(ms, 3), "dofs_per_s": round(dofs / (ms / 1e3), 1),
+                       "setup_ms": round(infos[0]["setup_ms"], 3), "solve_ms": round(infos[0]["solve_ms"], 3),
+                       "status": status, "iters_min": min(its), "iters_median": int(np.median(its)),
+                       "iters_max": max(its), "max_true_rel_res": max(i["true_rel_res"] for i in infos),
+                       "levels": [infos[0]["levels_p"], infos[0]["levels_T"]],
+                       "autotuned_shapes": [list(r) for r in cp.cptr_tuning(S.ctx)]}}
+    S.close()
+    # the same instances one after another through the single-system calls
+    Sq = cp.Solver(stream=stream, **opts)
+
+    def seq():
+        inf = []
+        for I, r, x in zip(inst, rhs, xs):
+            Sq.setup(I["n_cells"], b, I["row_ptr"], I["col_idx"], I["vals"], kind, I["row_weights"], I["st_vals"])
+            inf.append(Sq.solve(r, RTOL, x=x)[1])
+        return inf
+
+    seq()
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    inf = seq()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_seq = e0.elapsed_time(e1)
+    its_s = [i["iters"] for i in inf]
+    out["sequential"] = {"ms_per_step": round(ms_seq, 3), "dofs_per_s": round(dofs / (ms_seq / 1e3), 1),
+                         "setup_ms": round(sum(i["setup_ms"] for i in inf), 3),
+                         "solve_ms": round(sum(i["solve_ms"] for i in inf), 3),
+                         "iters_min": min(its_s), "iters_median": int(np.median(its_s)), "iters_max": max(its_s),
+                         "all_converged": all(i["status"] == "CPTR_OK" for i in inf)}
+    out["speedup_batched_vs_sequential"] = round(ms_seq / ms, 3)
+    Sq.close()
     return out
 
 

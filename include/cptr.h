@@ -81,6 +81,8 @@ typedef struct {
     int32_t check_every; /* host reads the convergence flag every k Arnoldi steps (default 1) */
     int32_t use_graph;   /* 1: replay each Arnoldi step as one captured CUDA graph (default 1) */
     int32_t ilu_order;   /* CPTR_ILU_NATURAL (default) or CPTR_ILU_MULTICOLOR */
+    int32_t autotune;    /* 1: time the launch shapes of the V-cycle and SpMV kernels at set-up
+                            and keep the fastest (see cptr_tuning); 0 (default): fixed shapes */
     void *stream;        /* cudaStream_t for all work; NULL = the legacy default stream */
 } cptr_options;
 
@@ -194,6 +196,16 @@ cptr_status cptr_hierarchy_level(cptr_ctx *ctx, int32_t which, int32_t l, int32_
  * ILU(0)), CPTR_EINVAL, CPTR_ECUDA. */
 cptr_status cptr_apply_ilu_static(cptr_ctx *ctx, const double *r, double *z);
 
+/* Launch shapes in use (an engineering addition; the paper has none).  Writes up to cap rows of 5
+ * int32 into rows (host): {hierarchy (0 A_pp, 1 S~_T, 2 A'), level, kernel (0 smoother + residual,
+ * 1 restriction P^T, 2 prolongation P, 3 SELL SpMV of A'), lanes per row (0 = chosen from the
+ * average row length), threads per block}; *n_rows receives the number of rows available.  With
+ * autotune set, cptr_setup times for every operator G in {2, 4, 8, 16, 32} lanes x T in {128, 256,
+ * 512} threads (the SELL kernels: T in {64, 128, 256, 512}), 5 launches each after a warm-up, and
+ * keeps the fastest; results are cached in the context by operator size.  Shapes change only the
+ * order of the partial sums within a row.  Errors: CPTR_ESTATE, CPTR_EINVAL. */
+cptr_status cptr_tuning(cptr_ctx *ctx, int32_t *rows, int32_t cap, int32_t *n_rows);
+
 /* Number of ILU level sets of the forward and backward sweeps (host ints). */
 cptr_status cptr_ilu_levels(cptr_ctx *ctx, int32_t *n_forward, int32_t *n_backward);
 
@@ -221,6 +233,43 @@ cptr_status cptr_set_profiling(cptr_ctx *ctx, uint32_t mask);
  * 11 AMG coarsest inverses, 12 ILU host work (ordering, level sets, sweep tables), 13 ILU
  * factorisation, 14 SELL layout and mixed-precision copies, 15 other. */
 cptr_status cptr_profile(cptr_ctx *ctx, double *ms, int64_t *count);
+
+/* ---------------------------------------------------------------------------------------------
+ * Ensemble: many independent Jacobians (realisations of a model, of uneven sizes) set up and
+ * solved together.  The paper solves one system at a time; this extension follows its method per
+ * instance.  The instances are set up as ONE block-diagonal system (instance k = a consecutive
+ * range of cells), so the AMG hierarchies, ILU(0) factors and SpMVs are built and applied on the
+ * union with one launch per kernel, and every block of them acts on its own instance only (the
+ * strength graph, interpolation, Galerkin products, ILU(0) pattern and coarsest inverse of a
+ * block-diagonal matrix are block diagonal).  PMIS weights use the union's cell index, so an
+ * instance's coarse grids are not those of a separate set-up; coarsening continues while the union
+ * has more than n_coarse points.  FGMRES runs per instance: its own Krylov basis, Givens rotations
+ * and stopping test |g_{j+1}| <= rtol ||W_k rhs_k||.  All instances take Arnoldi steps in lockstep
+ * (one captured CUDA graph per step for the whole ensemble); an instance that has converged is
+ * skipped by the Gram-Schmidt kernels, keeps its solution, and its step count stops.
+ * --------------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t n_cells;
+    const int32_t *row_ptr, *col_idx;  /* BSR pattern of the instance, 0-based within it */
+    const double *vals;                /* [nnzb][b][b] */
+    const double *row_weights;         /* [n_cells][b][b] or NULL (NULL for all or for none) */
+    const double *st_vals;             /* S~_T on the instance's pattern or NULL (all or none) */
+} cptr_instance;
+
+/* Set up n_inst instances with the same b and unknown_kind (all arrays host or device per
+ * on_device; unknown_kind likewise).  Replaces any previous set-up of ctx.  Errors as cptr_setup,
+ * and CPTR_EINVAL when only some instances give row_weights or st_vals. */
+cptr_status cptr_setup_batch(cptr_ctx *ctx, int32_t n_inst, int32_t b, const cptr_instance *inst,
+                             const int32_t *unknown_kind, int32_t on_device);
+
+/* Solve every instance to its own relative residual rtol: rhs[k] and x[k] (host arrays of n_inst
+ * pointers to n_cells_k * b doubles each, host or device memory per on_device); x[k] is
+ * overwritten.  st: host array of n_inst stats (iters and restarts per instance; setup_ms and
+ * solve_ms are the whole ensemble's), may be NULL.  Returns CPTR_OK when all converged,
+ * CPTR_NOT_CONVERGED when some reached max_it total Arnoldi steps; other errors as cptr_solve.
+ * Errors: CPTR_ESTATE when the last set-up was not cptr_setup_batch. */
+cptr_status cptr_solve_batch(cptr_ctx *ctx, const double *const *rhs, double *const *x, double rtol,
+                             cptr_stats *st, int32_t on_device);
 
 /* ---------------------------------------------------------------------------------------------
  * Learned diagonal scaling of the Schur approximation.  The paper has no learned part: it

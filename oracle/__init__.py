@@ -64,6 +64,8 @@ def _load():
         lib.or_destroy.argtypes = [P]
         lib.or_solve.restype = ctypes.c_int
         lib.or_solve.argtypes = [P, P, P, ctypes.c_double, P]
+        lib.or_solve_block.restype = ctypes.c_int
+        lib.or_solve_block.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_double, P]
         for name in ("or_precond", "or_stage1", "or_ilu_apply", "or_spmv", "or_weight_rhs"):
             getattr(lib, name).restype = None
             getattr(lib, name).argtypes = [P, P, P]
@@ -182,6 +184,19 @@ class Oracle:
         x = np.zeros(self.nb)
         st = Stats()
         rc = lib.or_solve(self._c, _p(rhs), _p(x), rtol, ctypes.byref(st))
+        return x, dict(rc=rc, iters=st.iters, restarts=st.restarts, converged=bool(st.converged),
+                       est_rel_res=st.est_rel_res, true_rel_res=st.true_rel_res, bnorm=st.bnorm)
+
+    def solve_block(self, cell0, ncell, rhs, rtol=1e-8):
+        """FGMRES on the diagonal block of cells [cell0, cell0 + ncell) of a block-diagonal set-up
+        (one instance of an ensemble), with the whole preconditioner restricted to the block."""
+        lib = _load()
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64).reshape(-1)
+        x = np.zeros(ncell * self.b)
+        st = Stats()
+        rc = lib.or_solve_block(self._c, cell0, ncell, _p(rhs), _p(x), rtol, ctypes.byref(st))
+        if rc == -1:
+            raise ValueError("the block couples to cells outside it")
         return x, dict(rc=rc, iters=st.iters, restarts=st.restarts, converged=bool(st.converged),
                        est_rel_res=st.est_rel_res, true_rel_res=st.true_rel_res, bnorm=st.bnorm)
 

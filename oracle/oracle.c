@@ -799,10 +799,40 @@ void or_weight_rhs(const or_ctx *c, const double *rhs, double *bw) {
         }
 }
 
-/* Right-preconditioned flexible GMRES(m) from x = 0 on A' x = W rhs. Returns 0 if converged,
- * 1 if not, -4 on a non-finite value. */
-int or_solve(or_ctx *c, const double *rhs, double *x, double rtol, or_stats *st) {
-    int32_t nb = c->n * c->b, m = c->o.restart;
+/* Rows [r0, r1) of A' applied to x (indexed from r0): the rows of one diagonal block. */
+static void spmv_rows(const csr *A, int32_t r0, int32_t r1, const double *x, double *y) {
+    for (int32_t i = r0; i < r1; ++i) {
+        double s = 0.0;
+        for (int32_t k = A->rp[i]; k < A->rp[i + 1]; ++k) s += A->v[k] * x[A->ci[k] - r0];
+        y[i - r0] = s;
+    }
+}
+
+/* The preconditioner restricted to rows [r0, r1): v is embedded in a zero vector of the whole
+ * system, preconditioned, and the same rows are taken back (for a block-diagonal system this is
+ * the preconditioner of the block's own system). */
+static void precond_rows(or_ctx *c, int32_t r0, int32_t r1, const double *v, double *z, double *full_in,
+                         double *full_out) {
+    int32_t nb = c->n * c->b;
+    if (r0 == 0 && r1 == nb) { or_precond(c, v, z); return; }
+    memset(full_in, 0, sizeof(double) * (size_t)nb);
+    memcpy(full_in + r0, v, sizeof(double) * (size_t)(r1 - r0));
+    or_precond(c, full_in, full_out);
+    memcpy(z, full_out + r0, sizeof(double) * (size_t)(r1 - r0));
+}
+
+/* Right-preconditioned flexible GMRES(m) from x = 0 on the diagonal block of cells
+ * [cell0, cell0 + ncell) of A' x = W rhs (rhs and x indexed from the block's first row). Returns
+ * 0 if converged, 1 if not, -4 on a non-finite value, -1 if the block couples to other cells. */
+static int fgmres_block(or_ctx *c, int32_t cell0, int32_t ncell, const double *rhs, double *x, double rtol,
+                        or_stats *st) {
+    int32_t b = c->b, r0 = cell0 * b, r1 = (cell0 + ncell) * b, nb = r1 - r0, m = c->o.restart;
+    for (int32_t i = r0; i < r1; ++i)
+        for (int32_t k = c->A.rp[i]; k < c->A.rp[i + 1]; ++k)
+            if (c->A.ci[k] < r0 || c->A.ci[k] >= r1) return -1;
+    int whole = r0 == 0 && r1 == c->n * b;
+    double *full_in = whole ? NULL : (double *)malloc(sizeof(double) * (size_t)c->n * b);
+    double *full_out = whole ? NULL : (double *)malloc(sizeof(double) * (size_t)c->n * b);
     double *bw = (double *)malloc(sizeof(double) * (size_t)nb);
     double *V = (double *)malloc(sizeof(double) * (size_t)nb * (m + 1));
     double *Z = (double *)malloc(sizeof(double) * (size_t)nb * m);
@@ -812,7 +842,13 @@ int or_solve(or_ctx *c, const double *rhs, double *x, double rtol, or_stats *st)
     double *h2 = (double *)malloc(sizeof(double) * (size_t)(m + 1));
     double *cs = (double *)malloc(sizeof(double) * (size_t)m), *sn = (double *)malloc(sizeof(double) * (size_t)m);
     double *g = (double *)malloc(sizeof(double) * (size_t)(m + 1)), *y = (double *)malloc(sizeof(double) * (size_t)m);
-    or_weight_rhs(c, rhs, bw);
+    for (int32_t i = cell0; i < cell0 + ncell; ++i) /* b' = W b on the block */
+        for (int32_t r = 0; r < b; ++r) {
+            double s = 0.0;
+            for (int32_t t = 0; t < b; ++t)
+                s += c->W[(int64_t)i * b * b + r * b + t] * rhs[(int64_t)(i - cell0) * b + t];
+            bw[(int64_t)(i - cell0) * b + r] = s;
+        }
     memset(x, 0, sizeof(double) * (size_t)nb);
     double bnorm = sqrt(dot(nb, bw, bw));
     int it = 0, restarts = 0, conv = 0, rc = 1;
@@ -821,7 +857,7 @@ int or_solve(or_ctx *c, const double *rhs, double *x, double rtol, or_stats *st)
     if (bnorm == 0.0) { conv = 1; rc = 0; goto done; }
     for (;;) {
         /* r = b' - A' x */
-        spmv(&c->A, x, w);
+        spmv_rows(&c->A, r0, r1, x, w);
         for (int32_t i = 0; i < nb; ++i) w[i] = bw[i] - w[i];
         double beta = sqrt(dot(nb, w, w));
         est = beta / bnorm;
@@ -833,8 +869,8 @@ int or_solve(or_ctx *c, const double *rhs, double *x, double rtol, or_stats *st)
         int j, k = 0;
         for (j = 0; j < m && it < c->o.max_it; ++j) {
             double *vj = V + (size_t)j * nb, *zj = Z + (size_t)j * nb;
-            or_precond(c, vj, zj);
-            spmv(&c->A, zj, w);
+            precond_rows(c, r0, r1, vj, zj, full_in, full_out);
+            spmv_rows(&c->A, r0, r1, zj, w);
             /* CGS2: two passes of classical Gram-Schmidt against v_0..v_j */
             for (int32_t q = 0; q <= j; ++q) h[q] = dot(nb, V + (size_t)q * nb, w);
             for (int32_t q = 0; q <= j; ++q) {
@@ -886,7 +922,7 @@ int or_solve(or_ctx *c, const double *rhs, double *x, double rtol, or_stats *st)
         ++restarts;
     }
 done:
-    spmv(&c->A, x, w);
+    spmv_rows(&c->A, r0, r1, x, w);
     for (int32_t i = 0; i < nb; ++i) w[i] = bw[i] - w[i];
     st->iters = it;
     st->restarts = restarts;
@@ -894,7 +930,19 @@ done:
     st->est_rel_res = est;
     st->true_rel_res = bnorm > 0.0 ? sqrt(dot(nb, w, w)) / bnorm : 0.0;
     free(bw); free(V); free(Z); free(w); free(H); free(h); free(h2); free(cs); free(sn); free(g); free(y);
+    free(full_in); free(full_out);
     return rc;
+}
+
+int or_solve(or_ctx *c, const double *rhs, double *x, double rtol, or_stats *st) {
+    return fgmres_block(c, 0, c->n, rhs, x, rtol, st);
+}
+
+/* FGMRES on one instance of an ensemble set up as a block-diagonal system (cells [cell0,
+ * cell0 + ncell)), with the whole system's preconditioner restricted to the block. */
+int or_solve_block(or_ctx *c, int32_t cell0, int32_t ncell, const double *rhs, double *x, double rtol,
+                   or_stats *st) {
+    return fgmres_block(c, cell0, ncell, rhs, x, rtol, st);
 }
 
 /* ------------------------------------------------------------------------------------------ */

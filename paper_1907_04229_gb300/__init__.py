@@ -35,7 +35,7 @@ class cptr_options(ctypes.Structure):
                 ("n_coarse", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_it", ctypes.c_int32), ("dense_max", ctypes.c_int32), ("seed", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("check_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("ilu_order", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("ilu_order", ctypes.c_int32), ("autotune", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class cptr_stats(ctypes.Structure):
@@ -44,6 +44,11 @@ class cptr_stats(ctypes.Structure):
                 ("est_rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double), ("bnorm", ctypes.c_double),
                 ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("op_complexity_p", ctypes.c_double), ("op_complexity_T", ctypes.c_double)]
+
+
+class cptr_instance(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int32), ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
+                ("vals", ctypes.c_void_p), ("row_weights", ctypes.c_void_p), ("st_vals", ctypes.c_void_p)]
 
 
 class CptrError(RuntimeError):
@@ -76,6 +81,9 @@ _SIGS = {
     "cptr_inject_wait_timeout": (_I, [_P, _I]),
     "cptr_set_profiling": (_I, [_P, ctypes.c_uint32]),
     "cptr_profile": (_I, [_P, _P, _P]),
+    "cptr_setup_batch": (_I, [_P, _I, _I, _P, _P, _I]),
+    "cptr_tuning": (_I, [_P, _P, _I, _P]),
+    "cptr_solve_batch": (_I, [_P, _P, _P, ctypes.c_double, _P, _I]),
     "cptr_schur_features": (_I, [_P, _P, _I]),
     "cptr_mlp_loss_grad": (_I, [_P, _P, _P, _I, _P, _P, _P, _I]),
     "cptr_mlp_train": (_I, [_P, _P, _P, _I, _P, _I, ctypes.c_float, _P, _I]),
@@ -265,6 +273,40 @@ def cptr_profile(ctx):
 
 
 # ------------------------------------------------------------------------------------------------
+def cptr_tuning(ctx):
+    """Launch shapes in use: list of (hierarchy, level, kernel, lanes per row, threads per block)."""
+    n = ctypes.c_int32(0)
+    _check(ctx, load().cptr_tuning(ctx, None, 0, ctypes.byref(n)))
+    rows = np.zeros((max(n.value, 1), 5), np.int32)
+    _check(ctx, load().cptr_tuning(ctx, rows.ctypes.data, n.value, ctypes.byref(n)))
+    return [tuple(int(v) for v in r) for r in rows[:n.value]]
+
+
+def cptr_setup_batch(ctx, b, instances, unknown_kind):
+    """instances: list of dicts with n_cells, row_ptr, col_idx, vals and optional row_weights,
+    st_vals (all torch CUDA tensors or all numpy arrays)."""
+    arr = (cptr_instance * len(instances))()
+    arrays = [unknown_kind]
+    for k, I in enumerate(instances):
+        arr[k].n_cells = int(I["n_cells"])
+        for f in ("row_ptr", "col_idx", "vals", "row_weights", "st_vals"):
+            setattr(arr[k], f, _ptr(I.get(f)))
+            arrays.append(I.get(f))
+    dev = _on_device(*arrays)
+    return _check(ctx, load().cptr_setup_batch(ctx, len(instances), b, arr, _ptr(unknown_kind), dev))
+
+
+def cptr_solve_batch(ctx, rhs, x, rtol):
+    """rhs, x: lists of per-instance arrays.  Returns (status code, list of cptr_stats)."""
+    n = len(rhs)
+    pr = (ctypes.c_void_p * n)(*[_ptr(r) for r in rhs])
+    px = (ctypes.c_void_p * n)(*[_ptr(v) for v in x])
+    st = (cptr_stats * n)()
+    dev = _on_device(*rhs, *x)
+    code = _check(ctx, load().cptr_solve_batch(ctx, pr, px, rtol, st, dev), ok=(CPTR_OK, CPTR_NOT_CONVERGED))
+    return code, list(st)
+
+
 def cptr_schur_features(ctx, feat):
     """feat: [n_cells, 16] float64 (torch CUDA tensor or numpy array), filled in place."""
     return _check(ctx, load().cptr_schur_features(ctx, _ptr(feat), _on_device(feat)))
@@ -338,6 +380,24 @@ class Solver:
         info["schur_used"] = SCHUR_NAMES.get(info["schur_used"], info["schur_used"])
         info["status"] = STATUS[code]
         return x, info
+
+    def setup_batch(self, b, instances, unknown_kind):
+        self.b = int(b)
+        self.n_inst = [int(I["n_cells"]) for I in instances]
+        cptr_setup_batch(self.ctx, self.b, instances, unknown_kind)
+        return self
+
+    def solve_batch(self, rhs, rtol=1e-6, x=None):
+        import torch
+        if x is None:
+            x = [torch.empty_like(r) if hasattr(r, "is_cuda") else np.zeros(len(r)) for r in rhs]
+        code, sts = cptr_solve_batch(self.ctx, rhs, x, rtol)
+        infos = []
+        for st in sts:
+            info = {f: getattr(st, f) for f, _ in cptr_stats._fields_}
+            info["schur_used"] = SCHUR_NAMES.get(info["schur_used"], info["schur_used"])
+            infos.append(info)
+        return x, STATUS[code], infos
 
     def hierarchy(self, which):
         levels = cptr_hierarchy_info(self.ctx, which)

@@ -614,7 +614,7 @@ __device__ __forceinline__ float vld(const bf16 *p) {
 
 // pre-smoothing from zero fused with the residual: t = D^{-1} b, r = b - A t
 template <int G, typename VT, typename XT>
-__global__ void __launch_bounds__(256) k_vc_down(int32_t n, const int32_t *__restrict__ rp,
+__global__ void __launch_bounds__(512) k_vc_down(int32_t n, const int32_t *__restrict__ rp,
                                                   const int32_t *__restrict__ ci, const VT *__restrict__ v,
                                                   const XT *__restrict__ dinv, const XT *__restrict__ b,
                                                   XT *__restrict__ t, XT *__restrict__ r) {
@@ -639,7 +639,7 @@ __global__ void __launch_bounds__(256) k_vc_down(int32_t n, const int32_t *__res
 }
 // post-smoothing: x = t + D^{-1} (b - A t)
 template <int G, typename VT, typename XT>
-__global__ void __launch_bounds__(256) k_vc_post(int32_t n, const int32_t *__restrict__ rp,
+__global__ void __launch_bounds__(512) k_vc_post(int32_t n, const int32_t *__restrict__ rp,
                                                   const int32_t *__restrict__ ci, const VT *__restrict__ v,
                                                   const XT *__restrict__ dinv, const XT *__restrict__ b,
                                                   const XT *__restrict__ t, XT *__restrict__ x) {
@@ -675,26 +675,28 @@ __global__ void k_diag_scale(int32_t n, const XT *d, const XT *b, XT *x) {
 
 template <typename VT, typename XT>
 static void launch_down(cudaStream_t s, const Level &L, const VT *v, const XT *dinv, const XT *b, XT *t, XT *r) {
-    int G = lanes_for(L.A.n, L.A.nnz);
-    unsigned grid = nblk((int64_t)L.A.n * G, 256);
+    const int G = L.sh_A.G ? L.sh_A.G : lanes_for(L.A.n, L.A.nnz), T = L.sh_A.T;
+    unsigned grid = nblk((int64_t)L.A.n * G, T);
     const Csr &A = L.A;
     switch (G) {
-    case 4: (k_vc_down<4, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
-    case 8: (k_vc_down<8, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
-    case 16: (k_vc_down<16, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
-    default: (k_vc_down<32, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
+    case 2: (k_vc_down<2, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
+    case 4: (k_vc_down<4, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
+    case 8: (k_vc_down<8, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
+    case 16: (k_vc_down<16, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
+    default: (k_vc_down<32, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
     }
 }
 template <typename VT, typename XT>
 static void launch_post(cudaStream_t s, const Level &L, const VT *v, const XT *dinv, const XT *b, const XT *t, XT *x) {
-    int G = lanes_for(L.A.n, L.A.nnz);
-    unsigned grid = nblk((int64_t)L.A.n * G, 256);
+    const int G = L.sh_A.G ? L.sh_A.G : lanes_for(L.A.n, L.A.nnz), T = L.sh_A.T;
+    unsigned grid = nblk((int64_t)L.A.n * G, T);
     const Csr &A = L.A;
     switch (G) {
-    case 4: (k_vc_post<4, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
-    case 8: (k_vc_post<8, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
-    case 16: (k_vc_post<16, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
-    default: (k_vc_post<32, VT, XT><<<grid, 256, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
+    case 2: (k_vc_post<2, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
+    case 4: (k_vc_post<4, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
+    case 8: (k_vc_post<8, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
+    case 16: (k_vc_post<16, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
+    default: (k_vc_post<32, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
     }
 }
 
@@ -720,12 +722,14 @@ template <typename VT, typename XT>
 static void level_down(cudaStream_t s, const Level &L, const Level &C, const VT *Av, const VT *PTv, const XT *b) {
     using LV = LevelVecs<XT>;
     launch_down<VT, XT>(s, L, Av, LV::dinv(L), b, LV::t(L), LV::r(L));             // t = D^-1 b, r = b - A t
-    launch_csr_spmv_t<VT, XT>(s, L.PT.n, L.PT.nnz, L.PT.rp, L.PT.ci, PTv, LV::r(L), LV::b(C), 0, nullptr);  // b_c = P^T r
+    launch_csr_spmv_t<VT, XT>(s, L.PT.n, L.PT.nnz, L.PT.rp, L.PT.ci, PTv, LV::r(L), LV::b(C), 0, nullptr,
+                              L.sh_PT);                                                        // b_c = P^T r
 }
 template <typename VT, typename XT>
 static void level_up(cudaStream_t s, const Level &L, const Level &C, const VT *Av, const VT *Pv, const XT *b, XT *x) {
     using LV = LevelVecs<XT>;
-    launch_csr_spmv_t<VT, XT>(s, L.P.n, L.P.nnz, L.P.rp, L.P.ci, Pv, LV::x(C), LV::t(L), 2, nullptr);  // t += P x_c
+    launch_csr_spmv_t<VT, XT>(s, L.P.n, L.P.nnz, L.P.rp, L.P.ci, Pv, LV::x(C), LV::t(L), 2, nullptr,
+                              L.sh_P);                                                         // t += P x_c
     launch_post<VT, XT>(s, L, Av, LV::dinv(L), b, LV::t(L), x);                     // x = t + D^-1 (b - A t)
 }
 
@@ -786,6 +790,82 @@ cptr_status amg_lower_precision(Ctx *c, Hier &h) {
         for (float **p : {&L.dinv32, &L.b32, &L.x32, &L.t32, &L.r32}) CPTR_TRY(dalloc_t(c, p, n));
         (k_d2f<<<nblk(L.A.n, 256), 256, 0, c->stream>>>(L.dinv, L.A.n, L.dinv32), note_launch());
     }
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    return CPTR_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Autotuner of the V-cycle kernels.  For every non-coarsest level and each of its three kernels
+// (smoother + residual on A, restriction P^T, prolongation P), every launch shape G in
+// {2, 4, 8, 16, 32} lanes per row x T in {128, 256, 512} threads per block is timed with CUDA
+// events over 5 launches after one warm-up launch, on the level's own work vectors and in the
+// precision the cycle uses; the fastest is kept.  Shapes are cached by (kernel, rows, entries,
+// storage), so repeated set-ups of one workload tune once.  The shapes change only the order of
+// the partial sums inside a row (lanes), never which entries are summed.
+namespace {
+template <typename F>
+Shape pick_shape(Ctx *c, uint64_t key, F &&launch) {
+    auto it = c->tune_cache.find(key);
+    if (it != c->tune_cache.end()) return it->second;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    Shape best;
+    float best_ms = 1e30f;
+    for (int G : {2, 4, 8, 16, 32})
+        for (int T : {128, 256, 512}) {
+            Shape sh;
+            sh.G = (int16_t)G;
+            sh.T = (int16_t)T;
+            launch(sh);
+            cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < 5; ++r) launch(sh);
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) { best_ms = ms; best = sh; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tune_cache[key] = best;
+    return best;
+}
+
+uint64_t tune_key(int kind, const Csr &A, int st) {
+    return (uint64_t)kind << 60 | (uint64_t)st << 56 | ((uint64_t)A.n & 0xFFFFFFull) << 32 | (uint64_t)(uint32_t)A.nnz;
+}
+
+template <typename VT, typename XT>
+void tune_level(Ctx *c, Level &L, Level &C, const VT *Av, const VT *PTv, const VT *Pv) {
+    using LV = LevelVecs<XT>;
+    cudaStream_t s = c->stream;
+    for (XT *p : {LV::b(L), LV::t(L), LV::r(L), LV::x(L)}) cudaMemsetAsync(p, 0, sizeof(XT) * L.A.n, s);
+    for (XT *p : {LV::b(C), LV::x(C)}) cudaMemsetAsync(p, 0, sizeof(XT) * C.A.n, s);
+    L.sh_A = pick_shape(c, tune_key(1, L.A, L.st), [&](Shape sh) {
+        Level tmp = L;
+        tmp.sh_A = sh;
+        launch_down<VT, XT>(s, tmp, Av, LV::dinv(L), LV::b(L), LV::t(L), LV::r(L));
+    });
+    L.sh_PT = pick_shape(c, tune_key(2, L.PT, L.st), [&](Shape sh) {
+        launch_csr_spmv_t<VT, XT>(s, L.PT.n, L.PT.nnz, L.PT.rp, L.PT.ci, PTv, LV::r(L), LV::b(C), 0, nullptr, sh);
+    });
+    L.sh_P = pick_shape(c, tune_key(3, L.P, L.st), [&](Shape sh) {
+        launch_csr_spmv_t<VT, XT>(s, L.P.n, L.P.nnz, L.P.rp, L.P.ci, Pv, LV::x(C), LV::t(L), 2, nullptr, sh);
+    });
+}
+}  // namespace
+
+cptr_status amg_autotune(Ctx *c, Hier &h) {
+    const bool lo = c->o.precision == CPTR_PREC_MIXED;
+    for (int l = 0; l + 1 < h.nlev; ++l) {
+        Level &L = h.L[l], &C = h.L[l + 1];
+        if (!lo) tune_level<double, double>(c, L, C, L.A.v, L.PT.v, L.P.v);
+        else if (L.st == ST_BF16)
+            tune_level<bf16, float>(c, L, C, (const bf16 *)L.Av_lo, (const bf16 *)L.PTv_lo, (const bf16 *)L.Pv_lo);
+        else tune_level<float, float>(c, L, C, (const float *)L.Av_lo, (const float *)L.PTv_lo, (const float *)L.Pv_lo);
+    }
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     CPTR_CUDA_TRY(c, cudaGetLastError());
     return CPTR_OK;
 }

@@ -5,6 +5,7 @@
 
 #include <stddef.h>
 
+#include <algorithm>
 #include <chrono>
 #include <new>
 
@@ -44,6 +45,8 @@ void release_setup(Ctx *c) {
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;
     }
+    free_batch(c);
+    c->sell_shape = Shape();
     c->ready = false;
 }
 
@@ -67,12 +70,12 @@ cptr_status validate_pattern(Ctx *c, int32_t n) {
 }
 
 cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const int32_t *col_idx, const double *vals,
-                     const int32_t *kind, const double *W, const double *st, int on_device) {
+                     const int32_t *kind, const double *W, const double *st, int on_device, int kind_on_device) {
     if (n <= 0) return c->fail(CPTR_EINVAL, "n_cells must be positive");
     if (b != 3 && b != 4) return c->fail(CPTR_EINVAL, "b must be 3 or 4");
     if (!row_ptr || !col_idx || !vals || !kind) return c->fail(CPTR_EINVAL, "row_ptr, col_idx, vals, unknown_kind are required");
     int32_t hk[4];
-    if (on_device) CPTR_TRY(copy_to_host(c, hk, kind, sizeof(int32_t) * b));
+    if (kind_on_device) CPTR_TRY(copy_to_host(c, hk, kind, sizeof(int32_t) * b));
     else memcpy(hk, kind, sizeof(int32_t) * b);
     int ps = -1, ts = -1;
     for (int q = 0; q < b; ++q) {
@@ -180,6 +183,13 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     for (double **p : {&c->b1, &c->w, &c->bw, &c->xw, &c->vcur, &c->zcur}) CPTR_TRY(dalloc_t(c, p, nb));
     CPTR_TRY(dalloc_t(c, &c->V, nb * (m + 1)));
     CPTR_TRY(dalloc_t(c, &c->Z, nb * m));
+    if (c->o.autotune) {
+        double ta = host_ms();
+        if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_autotune(c, c->hp));
+        if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) CPTR_TRY(amg_autotune(c, c->hT));
+        CPTR_TRY(sell_autotune(c));
+        setup_tick(c, SETUP_OTHER, &ta);
+    }
     CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     CPTR_CUDA_TRY(c, cudaGetLastError());
     c->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -359,7 +369,8 @@ cptr_status cptr_setup(cptr_ctx *ctx, int32_t n_cells, int32_t b, const int32_t 
                        const double *vals, const int32_t *unknown_kind, const double *row_weights,
                        const double *st_vals, int32_t on_device) {
     return guarded(ctx, [&](Ctx *c) {
-        cptr_status s = do_setup(c, n_cells, b, row_ptr, col_idx, vals, unknown_kind, row_weights, st_vals, on_device);
+        cptr_status s = do_setup(c, n_cells, b, row_ptr, col_idx, vals, unknown_kind, row_weights, st_vals, on_device,
+                                 on_device);
         if (s != CPTR_OK) {
             std::string keep = c->err;
             cudaStreamSynchronize(c->stream);
@@ -553,6 +564,29 @@ cptr_status cptr_profile(cptr_ctx *ctx, double *ms, int64_t *count) {
     });
 }
 
+cptr_status cptr_tuning(cptr_ctx *ctx, int32_t *rows, int32_t cap, int32_t *n_rows) {
+    return guarded(ctx, [&](Ctx *c) {
+        CPTR_TRY(need_ready(c));
+        if (!n_rows || (cap > 0 && !rows)) return c->fail(CPTR_EINVAL, "bad arguments");
+        std::vector<int32_t> out;
+        auto add = [&](int h, int l, int k, const Shape &sh) {
+            for (int32_t v : {h, l, k, (int32_t)sh.G, (int32_t)sh.T}) out.push_back(v);
+        };
+        for (int h = 0; h < 2; ++h) {
+            const Hier &H = h == 0 ? c->hp : c->hT;
+            for (int l = 0; l + 1 < H.nlev; ++l) {
+                add(h, l, 0, H.L[l].sh_A);
+                add(h, l, 1, H.L[l].sh_PT);
+                add(h, l, 2, H.L[l].sh_P);
+            }
+        }
+        add(2, 0, 3, c->sell_shape);
+        *n_rows = (int32_t)(out.size() / 5);
+        for (int32_t i = 0; i < std::min<int32_t>(cap, *n_rows) * 5; ++i) rows[i] = out[i];
+        return CPTR_OK;
+    });
+}
+
 cptr_status cptr_ilu_levels(cptr_ctx *ctx, int32_t *n_forward, int32_t *n_backward) {
     return guarded(ctx, [&](Ctx *c) {
         CPTR_TRY(need_ready(c));
@@ -561,6 +595,191 @@ cptr_status cptr_ilu_levels(cptr_ctx *ctx, int32_t *n_forward, int32_t *n_backwa
         return CPTR_OK;
     });
 }
+
+}  // extern "C"
+
+// ---- ensemble --------------------------------------------------------------------------------
+namespace {
+__global__ void k_copy_add(int32_t *dst, const int32_t *src, int64_t count, int32_t add) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) dst[i] = src[i] + add;
+}
+
+constexpr int64_t kTile = 8192;   // union-vector elements per Krylov tile
+
+cptr_status batch_setup(Ctx *c, int32_t ni, int32_t b, const cptr_instance *inst, const int32_t *kind,
+                        int on_device) {
+    if (ni < 1 || !inst || !kind) return c->fail(CPTR_EINVAL, "n_inst >= 1, inst and unknown_kind are required");
+    if (b != 3 && b != 4) return c->fail(CPTR_EINVAL, "b must be 3 or 4");
+    const bool hasW = inst[0].row_weights != nullptr, hasS = inst[0].st_vals != nullptr;
+    std::vector<int32_t> cell0(ni + 1, 0), nnz0(ni + 1, 0);
+    for (int k = 0; k < ni; ++k) {
+        const cptr_instance &I = inst[k];
+        if (I.n_cells <= 0 || !I.row_ptr || !I.col_idx || !I.vals)
+            return c->fail(CPTR_EINVAL, "instance " + std::to_string(k) + ": n_cells > 0 and the BSR arrays are required");
+        if ((I.row_weights != nullptr) != hasW || (I.st_vals != nullptr) != hasS)
+            return c->fail(CPTR_EINVAL, "row_weights and st_vals must be given for all instances or for none");
+        int32_t nz = 0;
+        if (on_device) CPTR_TRY(copy_to_host(c, &nz, I.row_ptr + I.n_cells, sizeof(int32_t)));
+        else nz = I.row_ptr[I.n_cells];
+        if (nz <= 0) return c->fail(CPTR_EINVAL, "instance " + std::to_string(k) + ": empty pattern");
+        if ((int64_t)cell0[k] + I.n_cells > INT32_MAX || (int64_t)nnz0[k] + nz > INT32_MAX)
+            return c->fail(CPTR_EINVAL, "the ensemble exceeds 2^31 cells or blocks");
+        cell0[k + 1] = cell0[k] + I.n_cells;
+        nnz0[k + 1] = nnz0[k] + nz;
+    }
+    const int32_t N = cell0[ni], NZ = nnz0[ni];
+    const size_t bb = (size_t)b * b;
+    int32_t *rp = nullptr, *ci = nullptr;
+    double *vals = nullptr, *W = nullptr, *st = nullptr;
+    struct Tmp {
+        std::vector<void *> p;
+        ~Tmp() { for (void *q : p) dfree(q); }
+    } tmp;
+    CPTR_TRY(dalloc_t(c, &rp, (size_t)N + 1)); tmp.p.push_back(rp);
+    CPTR_TRY(dalloc_t(c, &ci, (size_t)NZ)); tmp.p.push_back(ci);
+    CPTR_TRY(dalloc_t(c, &vals, (size_t)NZ * bb)); tmp.p.push_back(vals);
+    if (hasW) { CPTR_TRY(dalloc_t(c, &W, (size_t)N * bb)); tmp.p.push_back(W); }
+    if (hasS) { CPTR_TRY(dalloc_t(c, &st, (size_t)NZ)); tmp.p.push_back(st); }
+    const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    int32_t *stage = nullptr;   // host pattern arrays are staged on the device before the offset
+    int64_t stage_len = 0;
+    for (int k = 0; k < ni; ++k) {
+        const cptr_instance &I = inst[k];
+        const int64_t nk = I.n_cells, zk = nnz0[k + 1] - nnz0[k];
+        const int32_t *src_rp = I.row_ptr, *src_ci = I.col_idx;
+        if (!on_device) {
+            if (stage_len < nk + zk) {
+                dfree(stage);
+                stage = nullptr;
+                CPTR_TRY(dalloc_t(c, &stage, (size_t)(nk + zk)));
+                stage_len = nk + zk;
+            }
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(stage, I.row_ptr, sizeof(int32_t) * nk, cudaMemcpyHostToDevice, c->stream));
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(stage + nk, I.col_idx, sizeof(int32_t) * zk, cudaMemcpyHostToDevice,
+                                             c->stream));
+            src_rp = stage;
+            src_ci = stage + nk;
+        }
+        (k_copy_add<<<(unsigned)((nk + 255) / 256), 256, 0, c->stream>>>(rp + cell0[k], src_rp, nk, nnz0[k]),
+         note_launch());
+        (k_copy_add<<<(unsigned)((zk + 255) / 256), 256, 0, c->stream>>>(ci + nnz0[k], src_ci, zk, cell0[k]),
+         note_launch());
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(vals + (size_t)nnz0[k] * bb, I.vals, sizeof(double) * zk * bb, kin, c->stream));
+        if (hasW)
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(W + (size_t)cell0[k] * bb, I.row_weights, sizeof(double) * nk * bb, kin,
+                                             c->stream));
+        if (hasS)
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(st + nnz0[k], I.st_vals, sizeof(double) * zk, kin, c->stream));
+        if (!on_device) CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // stage is reused
+    }
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(rp + N, &NZ, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    int32_t hk[4];
+    if (on_device) CPTR_TRY(copy_to_host(c, hk, kind, sizeof(int32_t) * b));
+    else memcpy(hk, kind, sizeof(int32_t) * b);
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    dfree(stage);
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    CPTR_TRY(do_setup(c, N, b, rp, ci, vals, hk, W, st, 1, 0));
+    // tiles of the union vector, none straddling two instances
+    std::vector<int32_t> t_inst, i_t0(ni + 1, 0);
+    std::vector<int64_t> t_beg;
+    for (int k = 0; k < ni; ++k) {
+        i_t0[k] = (int32_t)t_inst.size();
+        const int64_t beg = (int64_t)cell0[k] * b, end = (int64_t)cell0[k + 1] * b;
+        for (int64_t p = beg; p < end; p += kTile) {
+            t_inst.push_back(k);
+            t_beg.push_back(p);
+        }
+    }
+    i_t0[ni] = (int32_t)t_inst.size();
+    t_beg.push_back((int64_t)N * b);
+    c->n_tiles = (int32_t)t_inst.size();
+    CPTR_TRY(dalloc_t(c, &c->tile_inst, t_inst.size()));
+    CPTR_TRY(dalloc_t(c, &c->tile_beg, t_beg.size()));
+    CPTR_TRY(dalloc_t(c, &c->inst_tile0, i_t0.size()));
+    CPTR_TRY(dalloc_t(c, &c->ksb, (size_t)ni));
+    CPTR_TRY(dalloc_t(c, &c->hdr, (size_t)ni + 1));
+    CPTR_TRY(dalloc_t(c, &c->partial_b, (size_t)c->n_tiles * (kMaxRestart + 1)));
+    CPTR_CUDA_TRY(c, cudaMallocHost((void **)&c->hdr_host, sizeof(KHdr) * (ni + 1)));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->tile_inst, t_inst.data(), sizeof(int32_t) * t_inst.size(), cudaMemcpyHostToDevice, c->stream));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->tile_beg, t_beg.data(), sizeof(int64_t) * t_beg.size(), cudaMemcpyHostToDevice, c->stream));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->inst_tile0, i_t0.data(), sizeof(int32_t) * i_t0.size(), cudaMemcpyHostToDevice, c->stream));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->ksb, 0, sizeof(KState) * ni, c->stream));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->vcur, 0, sizeof(double) * N * b, c->stream));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->zcur, 0, sizeof(double) * N * b, c->stream));
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->n_inst = ni;
+    c->inst_cell0 = cell0;
+    return CPTR_OK;
+}
+}  // namespace
+
+extern "C" {
+cptr_status cptr_setup_batch(cptr_ctx *ctx, int32_t n_inst, int32_t b, const cptr_instance *inst,
+                             const int32_t *unknown_kind, int32_t on_device) {
+    return guarded(ctx, [&](Ctx *c) {
+        cptr_status s = batch_setup(c, n_inst, b, inst, unknown_kind, on_device);
+        if (s != CPTR_OK) {
+            std::string keep = c->err;
+            cudaStreamSynchronize(c->stream);
+            release_setup(c);
+            c->err = keep;
+        }
+        return s;
+    });
+}
+
+cptr_status cptr_solve_batch(cptr_ctx *ctx, const double *const *rhs, double *const *x, double rtol, cptr_stats *st,
+                             int32_t on_device) {
+    return guarded(ctx, [&](Ctx *c) {
+        CPTR_TRY(need_ready(c));
+        if (c->n_inst < 1) return c->fail(CPTR_ESTATE, "the last set-up was not cptr_setup_batch");
+        if (!rhs || !x) return c->fail(CPTR_EINVAL, "rhs and x are required");
+        if (!(rtol >= 0.0)) return c->fail(CPTR_EINVAL, "rtol must be >= 0");
+        const int ni = c->n_inst, b = c->b;
+        for (int k = 0; k < ni; ++k)
+            if (!rhs[k] || !x[k]) return c->fail(CPTR_EINVAL, "rhs[k] and x[k] are required for every instance");
+        cudaEvent_t e0, e1;
+        CPTR_CUDA_TRY(c, cudaEventCreate(&e0));
+        CPTR_CUDA_TRY(c, cudaEventCreate(&e1));
+        CPTR_CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+        const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        for (int k = 0; k < ni; ++k) {
+            const size_t off = (size_t)c->inst_cell0[k] * b, len = (size_t)(c->inst_cell0[k + 1] - c->inst_cell0[k]) * b;
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->xw + off, rhs[k], sizeof(double) * len, kin, c->stream));
+        }
+        launch_weight_vec(c, c->W, c->xw, c->bw);
+        prof_reset(c);
+        cptr_status s = fgmres_solve_batch(c, c->bw, c->xw, rtol, st);
+        if (s == CPTR_OK || s == CPTR_NOT_CONVERGED)
+            for (int k = 0; k < ni; ++k) {
+                const size_t off = (size_t)c->inst_cell0[k] * b, len = (size_t)(c->inst_cell0[k + 1] - c->inst_cell0[k]) * b;
+                CPTR_CUDA_TRY(c, cudaMemcpyAsync(x[k], c->xw + off, sizeof(double) * len, kout, c->stream));
+            }
+        CPTR_CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+        CPTR_CUDA_TRY(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st)
+            for (int k = 0; k < ni; ++k) {
+                st[k].solve_ms = ms;
+                st[k].setup_ms = c->setup_ms;
+                st[k].levels_p = c->hp.nlev;
+                st[k].levels_T = c->hT.nlev;
+                st[k].op_complexity_p = c->hp.op_complexity;
+                st[k].op_complexity_T = c->hT.op_complexity;
+                st[k].schur_used = c->schur_used;
+            }
+        return s;
+    });
+}
+}  // extern "C"
+
+extern "C" {
 
 // ---- learned Schur scaling ----------------------------------------------------------------------
 

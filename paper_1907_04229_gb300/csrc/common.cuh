@@ -4,8 +4,10 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -46,6 +48,13 @@ struct Csr {
 };
 
 typedef __nv_bfloat16 bf16;
+
+// launch shape of a row-parallel sparse kernel: G lanes per row (0: chosen from the average row
+// length), T threads per block; picked per operator by the autotuner (amg_autotune, sell_autotune)
+struct Shape {
+    int16_t G = 0;
+    int16_t T = 256;
+};
 enum { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2 };   // storage of matrix values
 
 struct Level {
@@ -58,6 +67,7 @@ struct Level {
     // mixed-precision form: values of A, P, P^T stored in FP32 (levels 0, 1) or BF16 (levels
     // >= 2), D^{-1} and the work vectors in FP32
     int st = ST_F64;
+    Shape sh_A, sh_PT, sh_P;   // launch shapes of the smoother/residual, restriction, prolongation
     void *Av_lo = nullptr, *Pv_lo = nullptr, *PTv_lo = nullptr;
     float *dinv32 = nullptr;
     float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr, *r32 = nullptr;
@@ -76,13 +86,24 @@ struct KState {
     int32_t k, done, breakdown, wait_err;  // columns completed in this cycle, flags; a bounded
                                            // device-side wait gave up (ILU sweeps)
     uint32_t ticket;                  // last-block ticket of the reductions
-    int32_t pad2;
+    int32_t active;                   // ensemble: this instance iterates in the current cycle
+    int32_t its;                      // ensemble: Arnoldi steps this instance has taken
+    int32_t pad3;
     double bnorm, beta, tol_abs, hnorm, est, true_res;
     double h[kMaxRestart + 1];       // first-pass CGS coefficients
     double h2[kMaxRestart + 1];      // second-pass CGS coefficients
     double g[kMaxRestart + 1], cs[kMaxRestart], sn[kMaxRestart], y[kMaxRestart];
     double H[(kMaxRestart + 1) * kMaxRestart];  // column-major, H[col * (m+1) + row]
 };
+
+// the leading fields of a KState (the part the host polls)
+struct KHdr {
+    int32_t k, done, breakdown, wait_err;
+    uint32_t ticket;
+    int32_t active, its, pad3;
+    double bnorm, beta, tol_abs, hnorm, est, true_res;
+};
+static_assert(sizeof(KHdr) == offsetof(KState, h), "KHdr mirrors the head of KState");
 
 struct Ctx;
 
@@ -155,7 +176,7 @@ void launch_csr_spmv(cudaStream_t s, const Csr &A, const double *x, double *y, d
 // y = A x (mode 0), y = c0 - A x (mode 1), y += A x (mode 2); values VT, vectors and sums XT
 template <typename VT, typename XT>
 void launch_csr_spmv_t(cudaStream_t s, int32_t n, int32_t nnz, const int32_t *rp, const int32_t *ci, const VT *v,
-                       const XT *x, XT *y, int mode, const XT *c0);
+                       const XT *x, XT *y, int mode, const XT *c0, Shape sh = Shape());
 cptr_status to_lower(Ctx *c, const double *src, int64_t n, int st, void **dst);
 void launch_d2f(const Ctx *c, const double *a, float *b, int64_t n);
 void launch_f2d(const Ctx *c, const float *a, double *b, int64_t n);
@@ -165,6 +186,8 @@ void launch_resid_pt32(const Ctx *c, const float *dp, const float *dT, const dou
 void launch_sub(cudaStream_t s, int32_t n, const double *a, const double *b, double *out);
 
 // ---- amg.cu ------------------------------------------------------------------------------------
+cptr_status amg_autotune(Ctx *c, Hier &h);    // launch shapes of every level's kernels
+cptr_status sell_autotune(Ctx *c);           // threads per block of the SELL SpMV
 cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, const double *v, int32_t n);
 void amg_free(Hier &h);
 void amg_vcycle(const Ctx *c, const Hier &h, const double *b, double *x);
@@ -180,6 +203,9 @@ void ilu_apply32(const Ctx *c, const float *r, double *z, const float *dp, const
 
 // ---- krylov.cu ---------------------------------------------------------------------------------
 cptr_status fgmres_solve(Ctx *c, const double *bw, double *x, double rtol, cptr_stats *st);
+// ensemble (one block-diagonal set-up, FGMRES per instance): x and bw are union vectors
+cptr_status fgmres_solve_batch(Ctx *c, const double *bw, double *x, double rtol, cptr_stats *st);
+void free_batch(Ctx *c);
 // learned Schur scaling (learned.cu)
 cptr_status learned_prepare(Ctx *c);                       // saturation terms (needs c->A)
 cptr_status learned_schur(Ctx *c, bool *used);             // S~_T = diag(s) S~_T into c->St
@@ -210,6 +236,8 @@ struct Ctx {
     int32_t *sell_col = nullptr;
     double *sell_val = nullptr;
     int64_t sell_bytes = 0, sell_nvals = 0;
+    Shape sell_shape;        // threads per block of the SELL kernels (G unused)
+    std::map<uint64_t, Shape> tune_cache;   // autotuned shapes by (kernel, size, storage)
     double *W = nullptr;     // per-cell weights (n * b * b)
     double *App = nullptr, *ApT = nullptr, *ATp = nullptr, *St = nullptr;  // cell-pattern fields
     // learned Schur scaling: the base approximation once St holds the scaled one, the per-cell
@@ -258,6 +286,18 @@ struct Ctx {
     int32_t graph_inject = 0;
     KState *ks = nullptr;    // device
     KState *ks_host = nullptr;  // pinned mirror
+    // ensemble: instances are consecutive cell ranges of the set-up system (block diagonal)
+    int32_t n_inst = 0;
+    std::vector<int32_t> inst_cell0;       // first cell of each instance, and n at the end
+    int32_t n_tiles = 0;                   // union vector tiles, none straddles two instances
+    int32_t *tile_inst = nullptr;          // tile -> instance
+    int64_t *tile_beg = nullptr;           // tile -> [beg, end) in the union vector
+    int32_t *inst_tile0 = nullptr;         // instance -> first tile (n_inst + 1 entries)
+    KState *ksb = nullptr;                 // per-instance Krylov state (device)
+    KHdr *hdr = nullptr, *hdr_host = nullptr;     // per-instance headers (+ the ILU wait flag)
+    double *partial_b = nullptr;           // per-tile reduction partials
+    cudaGraphExec_t bgraph_exec = nullptr;
+    int64_t bgraph_launches = 0;
     int32_t *flag = nullptr;    // device scratch flag
     int32_t *scan_tmp = nullptr; int64_t scan_tmp_len = 0;
     double setup_ms = 0.0;

@@ -20,6 +20,55 @@ enum { FIN_H = 0, FIN_H2 = 1, FIN_GIVENS = 2, FIN_BNORM = 3, FIN_RESTART = 4, FI
 constexpr int kMaxC = kMaxRestart;   // columns per pass
 constexpr int kPStride = kMaxC + 1;  // partial row stride
 
+// the work of the last block of a reduction: res[] holds the reduced sums of the pass
+__device__ void cgs_finish(KState *ks, const double *res, int fin, int j, int m, double rtol, int nc) {
+    if (fin == FIN_H) {
+        for (int q = 0; q < nc; ++q) ks->h[q] = res[q];
+    } else if (fin == FIN_H2) {
+        for (int q = 0; q < nc; ++q) ks->h2[q] = res[q];
+    } else if (fin == FIN_GIVENS) {
+        double hn = sqrt(res[0]);
+        double *col = ks->H + (int64_t)j * (m + 1);
+        for (int q = 0; q <= j; ++q) col[q] = ks->h[q] + ks->h2[q];
+        col[j + 1] = hn;
+        for (int q = 0; q < j; ++q) {
+            double a = col[q], b = col[q + 1];
+            col[q] = ks->cs[q] * a + ks->sn[q] * b;
+            col[q + 1] = -ks->sn[q] * a + ks->cs[q] * b;
+        }
+        double a = col[j], b = col[j + 1];
+        double den = sqrt(a * a + b * b);
+        ks->cs[j] = a / den;
+        ks->sn[j] = b / den;
+        col[j] = den;
+        col[j + 1] = 0.0;
+        ks->g[j + 1] = -ks->sn[j] * ks->g[j];
+        ks->g[j] = ks->cs[j] * ks->g[j];
+        ks->hnorm = hn;
+        ks->k = j + 1;
+        ks->its += 1;
+        ks->est = fabs(ks->g[j + 1]) / ks->bnorm;
+        if (!isfinite(hn) || !isfinite(den) || !isfinite(ks->g[j])) { ks->breakdown = 1; ks->done = 1; }
+        else if (fabs(ks->g[j + 1]) <= ks->tol_abs || hn == 0.0) ks->done = 1;
+    } else if (fin == FIN_BNORM || fin == FIN_RESTART) {
+        double beta = sqrt(res[0]);
+        if (fin == FIN_BNORM) {
+            ks->bnorm = beta;
+            ks->tol_abs = rtol * beta;
+        }
+        ks->beta = beta;
+        for (int q = 0; q <= m; ++q) ks->g[q] = 0.0;
+        ks->g[0] = beta;
+        ks->k = 0;
+        ks->est = ks->bnorm > 0.0 ? beta / ks->bnorm : 0.0;
+        if (!isfinite(beta)) { ks->breakdown = 1; ks->done = 1; }
+        else ks->done = (beta <= ks->tol_abs) ? 1 : 0;
+        ks->active = !ks->done;
+    } else {  // FIN_TRUE
+        ks->true_res = sqrt(res[0]);
+    }
+}
+
 // One Gram-Schmidt pass over v_0..v_{nc-1} (columns of V, stride nb):
 //   PASS_DOT       partial[q] = v_q . w
 //   PASS_UPD_DOT   w -= sum_q coef_q v_q; partial[q] = v_q . w
@@ -98,49 +147,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cgs(int64_t nb, const double *_
     __syncthreads();
     if (threadIdx.x != 0) return;
     ks->ticket = 0;
-    if (fin == FIN_H) {
-        for (int q = 0; q < nc; ++q) ks->h[q] = res[q];
-    } else if (fin == FIN_H2) {
-        for (int q = 0; q < nc; ++q) ks->h2[q] = res[q];
-    } else if (fin == FIN_GIVENS) {
-        double hn = sqrt(res[0]);
-        double *col = ks->H + (int64_t)j * (m + 1);
-        for (int q = 0; q <= j; ++q) col[q] = ks->h[q] + ks->h2[q];
-        col[j + 1] = hn;
-        for (int q = 0; q < j; ++q) {
-            double a = col[q], b = col[q + 1];
-            col[q] = ks->cs[q] * a + ks->sn[q] * b;
-            col[q + 1] = -ks->sn[q] * a + ks->cs[q] * b;
-        }
-        double a = col[j], b = col[j + 1];
-        double den = sqrt(a * a + b * b);
-        ks->cs[j] = a / den;
-        ks->sn[j] = b / den;
-        col[j] = den;
-        col[j + 1] = 0.0;
-        ks->g[j + 1] = -ks->sn[j] * ks->g[j];
-        ks->g[j] = ks->cs[j] * ks->g[j];
-        ks->hnorm = hn;
-        ks->k = j + 1;
-        ks->est = fabs(ks->g[j + 1]) / ks->bnorm;
-        if (!isfinite(hn) || !isfinite(den) || !isfinite(ks->g[j])) { ks->breakdown = 1; ks->done = 1; }
-        else if (fabs(ks->g[j + 1]) <= ks->tol_abs || hn == 0.0) ks->done = 1;
-    } else if (fin == FIN_BNORM || fin == FIN_RESTART) {
-        double beta = sqrt(res[0]);
-        if (fin == FIN_BNORM) {
-            ks->bnorm = beta;
-            ks->tol_abs = rtol * beta;
-        }
-        ks->beta = beta;
-        for (int q = 0; q <= m; ++q) ks->g[q] = 0.0;
-        ks->g[0] = beta;
-        ks->k = 0;
-        ks->est = ks->bnorm > 0.0 ? beta / ks->bnorm : 0.0;
-        if (!isfinite(beta)) { ks->breakdown = 1; ks->done = 1; }
-        else ks->done = (beta <= ks->tol_abs) ? 1 : 0;
-    } else {  // FIN_TRUE
-        ks->true_res = sqrt(res[0]);
-    }
+    cgs_finish(ks, res, fin, j, m, rtol, nc);
 }
 
 // dst = src / scale, scale = ks->hnorm (which = 0) or ks->beta (which = 1); skipped if 0 or done.
@@ -496,6 +503,334 @@ cptr_status fgmres_solve(Ctx *c, const double *bw, double *x, double rtol, cptr_
     }
     if (h.breakdown) return c->fail(CPTR_EBREAKDOWN, "FGMRES: non-finite value in the Arnoldi process");
     return (h.done) ? CPTR_OK : CPTR_NOT_CONVERGED;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Ensemble: independent instances set up as one block-diagonal system.  The preconditioner and
+// the outer SpMV act on the union (they are block diagonal, so each instance's block sees only its
+// own values); FGMRES runs per instance.  The union vector is cut into tiles that never straddle
+// two instances; one block per tile.  Every instance has its own KState: its own column index,
+// Givens rotations, convergence test and step count, and a per-instance last-block reduction
+// over its own tiles (in tile order: deterministic).  Instances advance in lockstep; one that has
+// converged is skipped by the Gram-Schmidt kernels until the others finish.
+
+// One Gram-Schmidt pass per instance (same passes as k_cgs), column index from the instance state
+template <int PASS>
+__global__ void __launch_bounds__(kRedThreads) k_bcgs(int64_t nb, const double *__restrict__ V, double *__restrict__ w,
+                                                     int coef_off, double *__restrict__ partial, KState *ksb,
+                                                     const int32_t *__restrict__ tile_inst,
+                                                     const int64_t *__restrict__ tile_beg,
+                                                     const int32_t *__restrict__ inst_tile0, int fin, int m,
+                                                     double rtol) {
+    __shared__ double scoef[kMaxC];
+    __shared__ double red[kRedThreads / 32][kMaxC];
+    __shared__ bool last;
+    const int inst = tile_inst[blockIdx.x];
+    KState *ks = ksb + inst;
+    // converged instances skip the Arnoldi passes and the restart; FIN_BNORM / FIN_TRUE run for all
+    if (ks->done && (fin <= FIN_GIVENS || fin == FIN_RESTART)) return;
+    const int j = ks->k, nc = j + 1;
+    constexpr bool UPD = PASS == PASS_UPD_DOT || PASS == PASS_UPD_NORM;
+    constexpr bool NORM = PASS == PASS_UPD_NORM || PASS == PASS_NORM;
+    constexpr int NA = NORM ? 1 : kMaxC;
+    if (UPD && threadIdx.x < kMaxC) {
+        const double *coef = reinterpret_cast<const double *>(reinterpret_cast<const char *>(ks) + coef_off);
+        scoef[threadIdx.x] = threadIdx.x < nc ? coef[threadIdx.x] : 0.0;
+    }
+    __syncthreads();
+    double acc[NA];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) acc[q] = 0.0;
+    const int64_t beg = tile_beg[blockIdx.x], end = tile_beg[blockIdx.x + 1];
+    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        double wi = w[i];
+        if (UPD) {
+#pragma unroll
+            for (int q = 0; q < kMaxC; ++q)
+                if (q < nc) wi = fma(-scoef[q], __ldg(V + (int64_t)q * nb + i), wi);
+            w[i] = wi;
+        }
+        if (NORM) {
+            acc[0] = fma(wi, wi, acc[0]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kMaxC; ++q)
+                if (q < nc) acc[q] = fma(__ldg(V + (int64_t)q * nb + i), wi, acc[q]);
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int na = NORM ? 1 : nc;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+        if (q >= na) break;
+        double v = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[wid][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < na) {
+        double sum = 0.0;
+        for (int w8 = 0; w8 < kRedThreads / 32; ++w8) sum += red[w8][threadIdx.x];
+        partial[(int64_t)blockIdx.x * kPStride + threadIdx.x] = sum;
+    }
+    __threadfence();
+    __syncthreads();
+    const int t0 = inst_tile0[inst], t1 = inst_tile0[inst + 1];
+    if (threadIdx.x == 0) last = atomicAdd(&ks->ticket, 1u) == (unsigned)(t1 - t0 - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    __shared__ double res[kMaxC];
+    for (int q = wid; q < na; q += kRedThreads / 32) {
+        double sum = 0.0;
+        for (int bb = t0 + lane; bb < t1; bb += 32) sum += __ldcg(partial + (int64_t)bb * kPStride + q);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+        if (lane == 0) res[q] = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    ks->ticket = 0;
+    cgs_finish(ks, res, fin, j, m, rtol, nc);
+}
+
+// dst = src / scale per instance (scale = hnorm (which 0) or beta (which 1)); jdev: dst is the
+// instance's column k
+__global__ void k_bscale(int64_t nb, const double *__restrict__ src, double *__restrict__ dst, const KState *ksb,
+                         const int32_t *__restrict__ tile_inst, const int64_t *__restrict__ tile_beg, int which,
+                         int jdev) {
+    const KState *ks = ksb + tile_inst[blockIdx.x];
+    if (ks->done) return;
+    if (jdev) dst += (int64_t)ks->k * nb;
+    const double sc = which == 0 ? ks->hnorm : ks->beta;
+    if (!(sc > 0.0)) return;
+    const double inv = 1.0 / sc;
+    const int64_t beg = tile_beg[blockIdx.x], end = tile_beg[blockIdx.x + 1];
+    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) dst[i] = src[i] * inv;
+}
+
+// vec <-> column k of each instance (dir 0: vec = base[k]; dir 1: base[k] = vec)
+__global__ void k_bcopy_col(int64_t nb, double *__restrict__ base, double *__restrict__ vec, const KState *ksb,
+                            const int32_t *__restrict__ tile_inst, const int64_t *__restrict__ tile_beg, int dir) {
+    const KState *ks = ksb + tile_inst[blockIdx.x];
+    const double *colr = base + (int64_t)ks->k * nb;
+    double *colw = base + (int64_t)ks->k * nb;
+    const int64_t beg = tile_beg[blockIdx.x], end = tile_beg[blockIdx.x + 1];
+    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        if (dir == 0) vec[i] = colr[i];
+        else colw[i] = vec[i];
+    }
+}
+
+// y = H^{-1} g for every instance that iterated in this cycle (one thread per instance)
+__global__ void k_btrisolve(KState *ksb, int n_inst, int m) {
+    const int inst = blockIdx.x * blockDim.x + threadIdx.x;
+    if (inst >= n_inst) return;
+    KState *ks = ksb + inst;
+    if (!ks->active) return;
+    const int k = ks->k;
+    for (int i = k - 1; i >= 0; --i) {
+        double sum = ks->g[i];
+        for (int q = i + 1; q < k; ++q) sum -= ks->H[(int64_t)q * (m + 1) + i] * ks->y[q];
+        ks->y[i] = sum / ks->H[(int64_t)i * (m + 1) + i];
+    }
+}
+
+// x += sum_{q < k} y_q z_q on the tiles of the instances that iterated in this cycle
+__global__ void __launch_bounds__(256) k_bupdate_x(int64_t nb, const double *__restrict__ Z, const KState *ksb,
+                                                   const int32_t *__restrict__ tile_inst,
+                                                   const int64_t *__restrict__ tile_beg, double *__restrict__ x) {
+    __shared__ double sy[kMaxC];
+    const KState *ks = ksb + tile_inst[blockIdx.x];
+    if (!ks->active) return;
+    const int k = ks->k;
+    if (threadIdx.x < kMaxC) sy[threadIdx.x] = threadIdx.x < k ? ks->y[threadIdx.x] : 0.0;
+    __syncthreads();
+    const int64_t beg = tile_beg[blockIdx.x], end = tile_beg[blockIdx.x + 1];
+    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        double sum = x[i];
+#pragma unroll
+        for (int q = 0; q < kMaxC; ++q)
+            if (q < k) sum = fma(sy[q], __ldg(Z + (int64_t)q * nb + i), sum);
+        x[i] = sum;
+    }
+}
+
+// end of a cycle: no instance is active until its restart
+__global__ void k_bend_cycle(KState *ksb, int n_inst) {
+    const int inst = blockIdx.x * blockDim.x + threadIdx.x;
+    if (inst < n_inst) ksb[inst].active = 0;
+}
+
+// compact copy of the instance headers (and, last, the ILU wait flag of the shared state)
+__global__ void k_bheaders(const KState *ksb, int n_inst, const KState *ks, KHdr *hdr) {
+    const int inst = blockIdx.x * blockDim.x + threadIdx.x;
+    if (inst < n_inst) memcpy(hdr + inst, ksb + inst, sizeof(KHdr));
+    if (inst == 0) {
+        memset(hdr + n_inst, 0, sizeof(KHdr));
+        hdr[n_inst].wait_err = ks->wait_err;
+    }
+}
+
+namespace {
+
+template <int PASS>
+void bcgs(const Ctx *c, const double *V, double *w, size_t coef_off, int fin, double rtol = 0.0) {
+    const int64_t nb = (int64_t)c->n * c->b;
+    (k_bcgs<PASS><<<c->n_tiles, kRedThreads, 0, c->stream>>>(nb, V, w, (int)coef_off, c->partial_b, c->ksb,
+                                                             c->tile_inst, c->tile_beg, c->inst_tile0, fin,
+                                                             c->o.restart, rtol), note_launch());
+}
+
+void bheaders(const Ctx *c) {
+    (k_bheaders<<<nblk(c->n_inst, 64), 64, 0, c->stream>>>(c->ksb, c->n_inst, c->ks, c->hdr), note_launch());
+}
+
+// one Arnoldi step of every instance (captured once per set-up, replayed every iteration)
+void arnoldi_step_batch(const Ctx *c) {
+    const int64_t nb = (int64_t)c->n * c->b;
+    cudaStream_t s = c->stream;
+    const unsigned T = c->n_tiles;
+    (k_bcopy_col<<<T, 256, 0, s>>>(nb, c->V, c->vcur, c->ksb, c->tile_inst, c->tile_beg, 0), note_launch());
+    apply_precond(c, c->vcur, c->zcur);
+    (k_bcopy_col<<<T, 256, 0, s>>>(nb, c->Z, c->zcur, c->ksb, c->tile_inst, c->tile_beg, 1), note_launch());
+    launch_bsr_spmv(c, c->zcur, c->w);
+    bcgs<PASS_DOT>(c, c->V, c->w, 0, FIN_H);
+    bcgs<PASS_UPD_DOT>(c, c->V, c->w, offsetof(KState, h), FIN_H2);
+    bcgs<PASS_UPD_NORM>(c, c->V, c->w, offsetof(KState, h2), FIN_GIVENS);
+    (k_bscale<<<T, 256, 0, s>>>(nb, c->w, c->V, c->ksb, c->tile_inst, c->tile_beg, 0, 1), note_launch());
+    bheaders(c);
+}
+
+cptr_status build_batch_graph(Ctx *c) {
+    if (c->bgraph_exec) {
+        cudaGraphExecDestroy(c->bgraph_exec);
+        c->bgraph_exec = nullptr;
+    }
+    if (!c->cap_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t orig = c->stream;
+    c->stream = c->cap_stream;
+    const uint32_t mask = c->prof.mask;
+    c->prof.mask = 0;   // no event timing inside the ensemble graph
+    begin_capture_count();
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        arnoldi_step_batch(c);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(c->cap_stream, &g);
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(&c->bgraph_exec, g, 0);
+            cudaGraphDestroy(g);
+        }
+    }
+    c->bgraph_launches = end_capture_count();
+    c->prof.mask = mask;
+    c->stream = orig;
+    if (e != cudaSuccess) {
+        c->bgraph_exec = nullptr;
+        return c->fail(CPTR_ECUDA, std::string("capture of the ensemble Arnoldi step: ") + cudaGetErrorString(e));
+    }
+    return CPTR_OK;
+}
+
+cptr_status read_headers(Ctx *c) {
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->hdr_host, c->hdr, sizeof(KHdr) * (c->n_inst + 1), cudaMemcpyDeviceToHost,
+                                     c->stream));
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return CPTR_OK;
+}
+
+}  // namespace
+
+void free_batch(Ctx *c) {
+    dfree(c->tile_inst); dfree(c->tile_beg); dfree(c->inst_tile0); dfree(c->ksb); dfree(c->hdr);
+    dfree(c->partial_b);
+    c->tile_inst = nullptr; c->tile_beg = nullptr; c->inst_tile0 = nullptr; c->ksb = nullptr; c->hdr = nullptr;
+    c->partial_b = nullptr;
+    if (c->hdr_host) cudaFreeHost(c->hdr_host);
+    c->hdr_host = nullptr;
+    if (c->bgraph_exec) cudaGraphExecDestroy(c->bgraph_exec);
+    c->bgraph_exec = nullptr;
+    c->n_inst = 0;
+    c->n_tiles = 0;
+    c->inst_cell0.clear();
+}
+
+cptr_status fgmres_solve_batch(Ctx *c, const double *bw, double *x, double rtol, cptr_stats *st) {
+    const int m = c->o.restart, ni = c->n_inst;
+    const int64_t nb = (int64_t)c->n * c->b;
+    cudaStream_t s = c->stream;
+    const unsigned T = c->n_tiles;
+    if (!c->bgraph_exec) CPTR_TRY(build_batch_graph(c));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->ksb, 0, sizeof(KState) * ni, s));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->ks, 0, sizeof(KState), s));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(x, 0, sizeof(double) * nb, s));
+    bcgs<PASS_NORM>(c, nullptr, const_cast<double *>(bw), 0, FIN_BNORM, rtol);
+    (k_bscale<<<T, 256, 0, s>>>(nb, bw, c->V, c->ksb, c->tile_inst, c->tile_beg, 1, 0), note_launch());
+    bheaders(c);
+    CPTR_TRY(read_headers(c));
+    std::vector<int32_t> restarts(ni, 0);
+    auto all_done = [&]() {
+        for (int i = 0; i < ni; ++i)
+            if (!c->hdr_host[i].done) return false;
+        return true;
+    };
+    auto none_active = [&]() {
+        for (int i = 0; i < ni; ++i)
+            if (c->hdr_host[i].active && !c->hdr_host[i].done) return false;
+        return true;
+    };
+    int it = 0;
+    bool stop = all_done();
+    while (!stop) {
+        for (int j = 0; j < m && it < c->o.max_it; ++j) {
+            CPTR_CUDA_TRY(c, cudaGraphLaunch(c->bgraph_exec, s));
+            note_launches(c->bgraph_launches);
+            ++it;
+            CPTR_TRY(read_headers(c));
+            if (c->hdr_host[ni].wait_err) return c->fail(CPTR_ETIMEOUT, "ILU(0) sweep: a bounded wait gave up");
+            if (none_active()) break;
+        }
+        (k_btrisolve<<<nblk(ni, 64), 64, 0, s>>>(c->ksb, ni, m), note_launch());
+        (k_bupdate_x<<<T, 256, 0, s>>>(nb, c->Z, c->ksb, c->tile_inst, c->tile_beg, x), note_launch());
+        (k_bend_cycle<<<nblk(ni, 64), 64, 0, s>>>(c->ksb, ni), note_launch());
+        bheaders(c);
+        CPTR_TRY(read_headers(c));
+        if (all_done() || it >= c->o.max_it) break;
+        // restart the instances that have not converged: r = b' - A' x, beta, v_0 = r / beta
+        for (int i = 0; i < ni; ++i)
+            if (!c->hdr_host[i].done) ++restarts[i];
+        launch_bsr_resid(c, x, bw, c->w);
+        bcgs<PASS_NORM>(c, nullptr, c->w, 0, FIN_RESTART);
+        (k_bscale<<<T, 256, 0, s>>>(nb, c->w, c->V, c->ksb, c->tile_inst, c->tile_beg, 1, 0), note_launch());
+        bheaders(c);
+        CPTR_TRY(read_headers(c));
+        stop = all_done();
+    }
+    // true residual of every instance
+    launch_bsr_resid(c, x, bw, c->w);
+    bcgs<PASS_NORM>(c, nullptr, c->w, 0, FIN_TRUE);
+    bheaders(c);
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    CPTR_TRY(read_headers(c));
+    if (c->hdr_host[ni].wait_err) return c->fail(CPTR_ETIMEOUT, "ILU(0) sweep: a bounded wait gave up");
+    bool conv = true, brk = false;
+    for (int i = 0; i < ni; ++i) {
+        const KHdr &h = c->hdr_host[i];
+        if (st) {
+            st[i].iters = h.its;
+            st[i].restarts = restarts[i];
+            st[i].converged = h.done && !h.breakdown;
+            st[i].est_rel_res = h.est;
+            st[i].bnorm = h.bnorm;
+            st[i].true_rel_res = h.bnorm > 0.0 ? h.true_res / h.bnorm : 0.0;
+        }
+        conv = conv && h.done && !h.breakdown;
+        brk = brk || h.breakdown;
+    }
+    if (brk) return c->fail(CPTR_EBREAKDOWN, "FGMRES: non-finite value in the Arnoldi process of an instance");
+    return conv ? CPTR_OK : CPTR_NOT_CONVERGED;
 }
 
 }  // namespace cptr

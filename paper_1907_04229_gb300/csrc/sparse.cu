@@ -353,7 +353,7 @@ void launch_bsr_to_sell(const Ctx *c) {
 // MODE 0: y = A' x;  MODE 1: y = v - A' x;  MODE 2: y = v - A' R_0^T [dp; dT] (only the p and T
 // columns of each block are read; dT may be null for CPR)
 template <int B, int MODE>
-__global__ void __launch_bounds__(256) k_sell_spmv(int32_t n, const int64_t *__restrict__ off,
+__global__ void __launch_bounds__(512) k_sell_spmv(int32_t n, const int64_t *__restrict__ off,
                                                     const int32_t *__restrict__ col, const double *__restrict__ val,
                                                     const double *__restrict__ x, const double *__restrict__ v,
                                                     double *__restrict__ y, int ps, int ts,
@@ -398,13 +398,14 @@ __global__ void __launch_bounds__(256) k_sell_spmv(int32_t n, const int64_t *__r
 template <int MODE>
 static void sell_dispatch(const Ctx *c, const double *x, const double *v, double *y, const double *dp,
                           const double *dT) {
-    unsigned grid = nblk((int64_t)c->sell_nch * 32, 256);
+    const int T = c->sell_shape.T;
+    unsigned grid = nblk((int64_t)c->sell_nch * 32, T);
     if (c->b == 3)
-        (k_sell_spmv<3, MODE><<<grid, 256, 0, c->stream>>>(c->n, c->sell_off, c->sell_col, c->sell_val, x, v, y, c->ps,
-                                                           c->ts, dp, dT), note_launch());
+        (k_sell_spmv<3, MODE><<<grid, T, 0, c->stream>>>(c->n, c->sell_off, c->sell_col, c->sell_val, x, v, y, c->ps,
+                                                         c->ts, dp, dT), note_launch());
     else
-        (k_sell_spmv<4, MODE><<<grid, 256, 0, c->stream>>>(c->n, c->sell_off, c->sell_col, c->sell_val, x, v, y, c->ps,
-                                                           c->ts, dp, dT), note_launch());
+        (k_sell_spmv<4, MODE><<<grid, T, 0, c->stream>>>(c->n, c->sell_off, c->sell_col, c->sell_val, x, v, y, c->ps,
+                                                         c->ts, dp, dT), note_launch());
 }
 void launch_bsr_spmv(const Ctx *c, const double *x, double *y) { sell_dispatch<0>(c, x, nullptr, y, nullptr, nullptr); }
 void launch_bsr_resid(const Ctx *c, const double *x, const double *v, double *y) {
@@ -424,7 +425,7 @@ __device__ __forceinline__ float val_ld(const bf16 *p) {
 }
 
 template <int G, typename VT, typename XT>
-__global__ void __launch_bounds__(256) k_csr_spmv(int32_t n, const int32_t *__restrict__ rp,
+__global__ void __launch_bounds__(512) k_csr_spmv(int32_t n, const int32_t *__restrict__ rp,
                                                    const int32_t *__restrict__ ci, const VT *__restrict__ v,
                                                    const XT *__restrict__ x, XT *__restrict__ y, int mode,
                                                    const XT *__restrict__ c0) {
@@ -448,22 +449,23 @@ __global__ void __launch_bounds__(256) k_csr_spmv(int32_t n, const int32_t *__re
 
 template <typename VT, typename XT>
 void launch_csr_spmv_t(cudaStream_t s, int32_t n, int32_t nnz, const int32_t *rp, const int32_t *ci, const VT *v,
-                       const XT *x, XT *y, int mode, const XT *c0) {
-    int G = lanes_for(n, nnz);
-    unsigned grid = nblk((int64_t)n * G, 256);
+                       const XT *x, XT *y, int mode, const XT *c0, Shape sh) {
+    const int G = sh.G ? sh.G : lanes_for(n, nnz), T = sh.T;
+    unsigned grid = nblk((int64_t)n * G, T);
     switch (G) {
-    case 4: (k_csr_spmv<4, VT, XT><<<grid, 256, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
-    case 8: (k_csr_spmv<8, VT, XT><<<grid, 256, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
-    case 16: (k_csr_spmv<16, VT, XT><<<grid, 256, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
-    default: (k_csr_spmv<32, VT, XT><<<grid, 256, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
+    case 2: (k_csr_spmv<2, VT, XT><<<grid, T, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
+    case 4: (k_csr_spmv<4, VT, XT><<<grid, T, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
+    case 8: (k_csr_spmv<8, VT, XT><<<grid, T, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
+    case 16: (k_csr_spmv<16, VT, XT><<<grid, T, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
+    default: (k_csr_spmv<32, VT, XT><<<grid, T, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
     }
 }
 template void launch_csr_spmv_t<double, double>(cudaStream_t, int32_t, int32_t, const int32_t *, const int32_t *,
-                                                const double *, const double *, double *, int, const double *);
+                                                const double *, const double *, double *, int, const double *, Shape);
 template void launch_csr_spmv_t<float, float>(cudaStream_t, int32_t, int32_t, const int32_t *, const int32_t *,
-                                              const float *, const float *, float *, int, const float *);
+                                              const float *, const float *, float *, int, const float *, Shape);
 template void launch_csr_spmv_t<bf16, float>(cudaStream_t, int32_t, int32_t, const int32_t *, const int32_t *,
-                                             const bf16 *, const float *, float *, int, const float *);
+                                             const bf16 *, const float *, float *, int, const float *, Shape);
 
 void launch_csr_spmv(cudaStream_t s, const Csr &A, const double *x, double *y, double alpha, const double *c0) {
     int mode = c0 ? 1 : (alpha == 2.0 ? 2 : 0);
@@ -535,7 +537,7 @@ template void launch_scatter_pt<float>(const Ctx *, const float *, const float *
 
 // mixed-precision stage-1 residual b1 = v - A' R_0^T [dp; dT] with FP32 values of A' (SELL-32)
 template <int B>
-__global__ void __launch_bounds__(256) k_sell_resid_pt32(int32_t n, const int64_t *__restrict__ off,
+__global__ void __launch_bounds__(512) k_sell_resid_pt32(int32_t n, const int64_t *__restrict__ off,
                                                           const int32_t *__restrict__ col,
                                                           const float *__restrict__ val, const double *__restrict__ v,
                                                           float *__restrict__ b1, int ps, int ts,
@@ -567,13 +569,14 @@ __global__ void __launch_bounds__(256) k_sell_resid_pt32(int32_t n, const int64_
     }
 }
 void launch_resid_pt32(const Ctx *c, const float *dp, const float *dT, const double *v, float *b1) {
-    unsigned grid = nblk((int64_t)c->sell_nch * 32, 256);
+    const int T = c->sell_shape.T;
+    unsigned grid = nblk((int64_t)c->sell_nch * 32, T);
     if (c->b == 3)
-        (k_sell_resid_pt32<3><<<grid, 256, 0, c->stream>>>(c->n, c->sell_off, c->sell_col, c->sell_val32, v, b1, c->ps,
-                                                            c->ts, dp, dT), note_launch());
+        (k_sell_resid_pt32<3><<<grid, T, 0, c->stream>>>(c->n, c->sell_off, c->sell_col, c->sell_val32, v, b1, c->ps,
+                                                          c->ts, dp, dT), note_launch());
     else
-        (k_sell_resid_pt32<4><<<grid, 256, 0, c->stream>>>(c->n, c->sell_off, c->sell_col, c->sell_val32, v, b1, c->ps,
-                                                            c->ts, dp, dT), note_launch());
+        (k_sell_resid_pt32<4><<<grid, T, 0, c->stream>>>(c->n, c->sell_off, c->sell_col, c->sell_val32, v, b1, c->ps,
+                                                          c->ts, dp, dT), note_launch());
 }
 
 __global__ void k_sub(int32_t n, const double *a, const double *b, double *out) {
@@ -582,6 +585,42 @@ __global__ void k_sub(int32_t n, const double *a, const double *b, double *out) 
 }
 void launch_sub(cudaStream_t s, int32_t n, const double *a, const double *b, double *out) {
     (k_sub<<<nblk(n, 256), 256, 0, s>>>(n, a, b, out), note_launch());
+}
+
+// ------------------------------------------------------------------------------------------------
+// Autotuner of the SELL kernels: threads per block in {64, 128, 256, 512}, each timed with CUDA
+// events over 5 launches of y = A' x after one warm-up launch; the fastest is kept (cached by the
+// matrix size, so repeated set-ups of one workload tune once).
+cptr_status sell_autotune(Ctx *c) {
+    const uint64_t key = (uint64_t)7 << 60 | (uint64_t)c->b << 56 | (uint64_t)(c->sell_nvals & ((1ull << 56) - 1));
+    auto it = c->tune_cache.find(key);
+    if (it != c->tune_cache.end()) {
+        c->sell_shape = it->second;
+        return CPTR_OK;
+    }
+    cudaEvent_t e0, e1;
+    CPTR_CUDA_TRY(c, cudaEventCreate(&e0));
+    CPTR_CUDA_TRY(c, cudaEventCreate(&e1));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->zcur, 0, sizeof(double) * (size_t)c->n * c->b, c->stream));
+    Shape best;
+    float best_ms = 1e30f;
+    for (int T : {64, 128, 256, 512}) {
+        c->sell_shape.T = (int16_t)T;
+        launch_bsr_spmv(c, c->zcur, c->w);
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 5; ++r) launch_bsr_spmv(c, c->zcur, c->w);
+        cudaEventRecord(e1, c->stream);
+        CPTR_CUDA_TRY(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = c->sell_shape; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->sell_shape = best;
+    c->tune_cache[key] = best;
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    return CPTR_OK;
 }
 
 }  // namespace cptr

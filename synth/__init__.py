@@ -398,3 +398,55 @@ def mlp_init(seed: int, n_features: int = 16, n_hidden: int = 64) -> np.ndarray:
     w3 = z[n_hidden * n_features + n_hidden * n_hidden:] / np.sqrt(n_hidden)
     zero = np.zeros(n_hidden)
     return np.concatenate([w1, zero, w2, zero, w3, [0.0]]).astype(np.float32)
+
+
+def concat(systems) -> dict:
+    """The block-diagonal union of several systems (same b): cells of system k follow those of
+    system k - 1.  Returns the union in the layout of ``Reservoir.system()`` plus ``cell0``, the
+    first cell of every system and the total at the end."""
+    b = systems[0]["b"]
+    cell0 = np.zeros(len(systems) + 1, np.int64)
+    for k, s in enumerate(systems):
+        assert s["b"] == b
+        cell0[k + 1] = cell0[k] + s["n"]
+    rp, ci, nz = [np.zeros(1, np.int32)], [], 0
+    for k, s in enumerate(systems):
+        rp.append((s["row_ptr"][1:] + nz).astype(np.int32))
+        ci.append((s["col_idx"] + cell0[k]).astype(np.int32))
+        nz += int(s["row_ptr"][-1])
+    out = {"n": int(cell0[-1]), "b": b, "row_ptr": np.concatenate(rp), "col_idx": np.concatenate(ci),
+           "vals": np.concatenate([s["vals"] for s in systems]),
+           "weights": np.concatenate([s["weights"] for s in systems]),
+           "st": np.concatenate([s["st"] for s in systems]),
+           "rhs": np.concatenate([s["rhs"] for s in systems]),
+           "unknown_kind": systems[0]["unknown_kind"], "cell0": cell0}
+    return out
+
+
+def ensemble_sizes(count: int = 64, lo: float = 20e3, hi: float = 500e3, total: float = 4e6, nz: int = 10,
+                   seed: int = 31):
+    """Cell counts of an ensemble of ``count`` boxes with sizes in [lo, hi] summing to about
+    ``total``: N_k = lo (hi / lo)^(u_k^g) with u_k the uniforms of stream ``seed`` and the exponent
+    g >= 1 found by bisection so that sum N_k = total (g = 1 is log-uniform; a larger g skews the
+    sizes toward lo while keeping the range).  Each instance is an nx x nx x nz box with
+    nx = round(sqrt(N_k / nz)).  Returns a list of (nx, ny, nz)."""
+    u = uniform(seed, count)
+    sizes = lambda g: lo * (hi / lo) ** (u ** g)
+    a, b = 1.0, 64.0
+    if sizes(a).sum() > total:
+        for _ in range(100):
+            g = 0.5 * (a + b)
+            if sizes(g).sum() > total:
+                a = g
+            else:
+                b = g
+    n = sizes(0.5 * (a + b))
+    return [(int(round(np.sqrt(v / nz))),) * 2 + (nz,) for v in n]
+
+
+def ensemble_member(k: int, shape) -> Reservoir:
+    """Instance k of the ensemble: the two-phase model of the parity workload (3.125 m cells,
+    lognormal permeability sigma 1, corner injector and producer, dt = 1 day) on an
+    nx x ny x nz box, permeability seed 100 + k."""
+    nx, ny, nz = shape
+    return make_box(nx, ny, nz, 3.125, seed=100 + k, sigma=1.0)

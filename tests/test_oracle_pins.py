@@ -591,3 +591,42 @@ def test_mixed_precision_oracle_rounds_the_hierarchy():
     x, info = o16.solve(s["rhs"], 1e-8)
     x64, i64 = o64.solve(s["rhs"], 1e-8)
     assert info["converged"] and abs(info["iters"] - i64["iters"]) <= 2
+
+
+# ------------------------------------------------------------------------------------------------
+# ensemble: FGMRES on one diagonal block of a block-diagonal union
+def test_block_solve_of_the_whole_system_is_the_solve():
+    s = tiny().system()
+    o = oracle.Oracle.from_system(s, n_coarse=16)
+    x1, i1 = o.solve(s["rhs"], 1e-10)
+    x2, i2 = o.solve_block(0, s["n"], s["rhs"], 1e-10)
+    assert i1["iters"] == i2["iters"] and np.array_equal(x1, x2)
+
+
+def test_block_solve_without_preconditioner_is_the_instance_gmres():
+    """With no first and no second stage the preconditioner is the identity, so FGMRES on a block
+    of the union is GMRES on the instance alone: the same iterates up to rounding."""
+    a = synth.make_box(5, 4, 2, 3.125, seed=3).system()
+    c = synth.make_box(3, 6, 2, 3.125, seed=5).system()
+    U = synth.concat([a, c])
+    opts = dict(stage1=oracle.NONE1, stage2=oracle.NONE2, restart=8)
+    ou = oracle.Oracle.from_system(U, **opts)
+    for k, s in enumerate((a, c)):
+        x_b, i_b = ou.solve_block(int(U["cell0"][k]), s["n"], s["rhs"], 1e-9)
+        x_s, i_s = oracle.Oracle.from_system(s, **opts).solve(s["rhs"], 1e-9)
+        assert i_b["iters"] == i_s["iters"]
+        np.testing.assert_allclose(x_b, x_s, rtol=1e-12, atol=1e-12 * np.abs(x_s).max())
+
+
+def test_union_preconditioner_is_block_diagonal():
+    a = synth.make_box(5, 4, 2, 3.125, seed=3).system()
+    c = synth.make_box(3, 6, 2, 3.125, seed=5).system()
+    U = synth.concat([a, c])
+    ou = oracle.Oracle.from_system(U, n_coarse=8)
+    nb0 = a["n"] * a["b"]
+    v = np.zeros(U["n"] * U["b"])
+    v[:nb0] = np.random.default_rng(1).normal(size=nb0)
+    z = ou.precond(v)
+    assert np.all(z[nb0:] == 0.0)
+    with pytest.raises(ValueError):
+        ou.solve_block(1, a["n"], a["rhs"], 1e-8)     # a range that cuts through the coupling
