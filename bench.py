@@ -34,6 +34,9 @@ WORKLOAD = "cptr200k"
 L2_BYTES = 129 * 2 ** 20
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 LEARNED_STEPS, LEARNED_LR = 2000, 2e-3
+# DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/ (the
+# current kernels; None where no capture of the current code exists)
+PROFILED_TRAFFIC = {"spmv": None, "stage1_resid": None, "ilu_fwd": 55.788544e6, "ilu_bwd": 75.43936e6}
 
 
 def parse():
@@ -47,6 +50,10 @@ def parse():
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-three-phase", action="store_true")
     p.add_argument("--no-ensemble", action="store_true")
+    p.add_argument("--three-phase-grid", type=int, nargs=3, default=None,
+                   help="run the three-phase section on an NX NY NZ box instead of 200x200x50 (profiling)")
+    p.add_argument("--ensemble-total", type=float, default=4e6,
+                   help="total cells of the ensemble (profiling runs use a smaller one)")
     return p.parse_args()
 
 
@@ -56,6 +63,8 @@ VARIANTS = {
     "cptr_fp64_multicolor_ilu": dict(ilu_order="multicolor"),
     "cptr_mixed": dict(precision="mixed"),
     "cptr_mixed_multicolor_ilu": dict(precision="mixed", ilu_order="multicolor"),
+    "cptr_fp64_autotuned": dict(autotune=1),
+    "cptr_mixed_autotuned": dict(precision="mixed", autotune=1),
 }
 
 
@@ -231,7 +240,8 @@ def ours(args, rank, world, local_rank):
         avg_ms = ms_tot / max(cnt, 1)
         achieved = alg[fam] / (avg_ms / 1e3) / 1e9
         lines[fam] = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                      "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                      "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                      "traffic": PROFILED_TRAFFIC.get(fam),
                       "algorithmic_bytes_per_launch": alg[fam], "avg_launch_us": round(avg_ms * 1e3, 2),
                       "launches_per_step": cnt / args.steps, "ms_per_step": round(ms_tot / args.steps, 3)}
     # FP64 ALU view of the SpMV: 9 FMA per 3x3 block (2 flop each) against 1.258 TFLOP/s
@@ -390,7 +400,12 @@ def three_phase(args, dev, stream, flush):
         nets[base] = P
         training[base] = {"samples": nsamp, "steps": LEARNED_STEPS, "lr": LEARNED_LR, "train_ms": round(train_ms, 2),
                           "loss_first": loss0, "loss_last": loss1}
-    s = synth.recipe("three_phase2m").system()
+    if args.three_phase_grid:
+        nx, ny, nz = args.three_phase_grid
+        s = synth.make_box(nx, ny, nz, 1.0, 1.0, 0.5, seed=21, sigma=2.5, nphase=3, wells="four", T_inj=500.0,
+                           q_inj=4e-6).system()
+    else:
+        s = synth.recipe("three_phase2m").system()
     n, b = s["n"], s["b"]
     dofs = n * b
     d = {k: torch.as_tensor(np.ascontiguousarray(v), device=dev) for k, v in
@@ -398,8 +413,10 @@ def three_phase(args, dev, stream, flush):
           "W": s["weights"].reshape(-1), "st": s["st"], "rhs": s["rhs"].reshape(-1)}.items()}
     del s
     x = torch.empty(dofs, dtype=torch.float64, device=dev)
-    out = {"workload": "three_phase2m: 200x200x50 cells, 4 unknowns/cell (8M dofs), lognormal permeability "
-                       "sigma 2.5, 4 injectors + 4 producers; CPTR + ILU(0), FGMRES(30), rtol 1e-6",
+    out = {"workload": (f"three-phase {n} cells, 4 unknowns/cell ({dofs} dofs)" if args.three_phase_grid else
+                        "three_phase2m: 200x200x50 cells, 4 unknowns/cell (8M dofs)") +
+                       ", lognormal permeability sigma 2.5, 4 injectors + 4 producers; CPTR + ILU(0), FGMRES(30), "
+                       "rtol 1e-6",
            "training": dict(training, data="16 three-phase 32x32x8 grids (coupling drawn per grid), exact Schur "
                                            "diagonal ratios from the oracle")}
     # (name, options, network base, timed runs); the A_TT forms stall on this workload, so they run
@@ -452,7 +469,7 @@ def ensemble(args, dev, stream, flush):
     import synth
     import paper_1907_04229_gb300 as cp
 
-    shapes = synth.ensemble_sizes()
+    shapes = synth.ensemble_sizes(total=args.ensemble_total, lo=min(20e3, args.ensemble_total / 64))
     systems = [synth.ensemble_member(k, sh).system() for k, sh in enumerate(shapes)]
     b = systems[0]["b"]
     kind = torch.as_tensor(systems[0]["unknown_kind"], device=dev)

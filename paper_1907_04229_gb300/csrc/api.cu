@@ -47,6 +47,8 @@ void release_setup(Ctx *c) {
     }
     free_batch(c);
     c->sell_shape = Shape();
+    c->sf_grid = 4 * 152;
+    c->sf_sleep = 20;
     c->ready = false;
 }
 
@@ -68,6 +70,9 @@ cptr_status validate_pattern(Ctx *c, int32_t n) {
     }
     return CPTR_OK;
 }
+
+cptr_status clear_wait_flag(Ctx *c);
+cptr_status check_wait_flag(Ctx *c);
 
 cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const int32_t *col_idx, const double *vals,
                      const int32_t *kind, const double *W, const double *st, int on_device, int kind_on_device) {
@@ -188,6 +193,11 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
         if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_autotune(c, c->hp));
         if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) CPTR_TRY(amg_autotune(c, c->hT));
         CPTR_TRY(sell_autotune(c));
+        if (c->o.stage2 == CPTR_STAGE2_ILU0) {
+            CPTR_TRY(clear_wait_flag(c));
+            CPTR_TRY(ilu_autotune(c));
+            CPTR_TRY(check_wait_flag(c));
+        }
         setup_tick(c, SETUP_OTHER, &ta);
     }
     CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -581,6 +591,10 @@ cptr_status cptr_tuning(cptr_ctx *ctx, int32_t *rows, int32_t cap, int32_t *n_ro
             }
         }
         add(2, 0, 3, c->sell_shape);
+        Shape isw;
+        isw.G = (int16_t)c->sf_sleep;
+        isw.T = (int16_t)c->sf_grid;
+        add(3, 0, 4, isw);
         *n_rows = (int32_t)(out.size() / 5);
         for (int32_t i = 0; i < std::min<int32_t>(cap, *n_rows) * 5; ++i) rows[i] = out[i];
         return CPTR_OK;

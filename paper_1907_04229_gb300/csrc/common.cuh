@@ -188,6 +188,7 @@ void launch_sub(cudaStream_t s, int32_t n, const double *a, const double *b, dou
 // ---- amg.cu ------------------------------------------------------------------------------------
 cptr_status amg_autotune(Ctx *c, Hier &h);    // launch shapes of every level's kernels
 cptr_status sell_autotune(Ctx *c);           // threads per block of the SELL SpMV
+cptr_status ilu_autotune(Ctx *c);            // grid and poll back-off of the ILU(0) sweeps
 cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, const double *v, int32_t n);
 void amg_free(Hier &h);
 void amg_vcycle(const Ctx *c, const Hier &h, const double *b, double *x);
@@ -267,6 +268,8 @@ struct Ctx {
     void *sf_dinv = nullptr;                           // inverted pivot blocks, backward order
     unsigned *sf_ticket = nullptr;                     // block tickets of the two sweeps
     void *sf_y = nullptr, *sf_z = nullptr;             // level-ordered y and z (sentinel-filled)
+    int32_t sf_grid = 4 * 152;                         // persistent grid of the sweeps (autotuned)
+    int32_t sf_sleep = 20;                             // back-off between polls, ns (autotuned)
     int32_t inject_wait = 0;                           // failure injection (see cptr_inject_wait_timeout)
     double *never = nullptr;                           // a word no thread writes
     // preconditioner work

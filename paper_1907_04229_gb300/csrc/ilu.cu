@@ -201,7 +201,7 @@ __device__ __forceinline__ double wait_value(const double *p, KState *ks) {
 constexpr int kDepGroup = 4;
 
 template <int B, typename T>
-__device__ __forceinline__ void load_group(const T *base, const int32_t *c, T (*v)[B], KState *ks) {
+__device__ __forceinline__ void load_group(const T *base, const int32_t *c, T (*v)[B], KState *ks, int sleep_ns) {
     bool pending = false;
 #pragma unroll
     for (int g = 0; g < kDepGroup; ++g)
@@ -214,7 +214,7 @@ __device__ __forceinline__ void load_group(const T *base, const int32_t *c, T (*
     if (!pending) return;
     const unsigned long long t0 = gtimer();
     while (pending) {
-        __nanosleep(20);
+        __nanosleep(sleep_ns);
         pending = false;
 #pragma unroll
         for (int g = 0; g < kDepGroup; ++g)
@@ -240,7 +240,7 @@ __device__ __forceinline__ void load_group(const T *base, const int32_t *c, T (*
 // s -= sum over the dependency slots [o0, o1) of block(slot) * value(dep(slot))
 template <int B, typename T>
 __device__ __forceinline__ void subtract_deps(T *s, int64_t o0, int64_t o1, int lane, const int32_t *__restrict__ col,
-                                              const T *__restrict__ val, const T *vec, KState *ks) {
+                                              const T *__restrict__ val, const T *vec, KState *ks, int sleep_ns) {
     for (int64_t sl0 = o0; sl0 < o1; sl0 += kDepGroup) {
         int32_t c[kDepGroup];
 #pragma unroll
@@ -252,7 +252,7 @@ __device__ __forceinline__ void subtract_deps(T *s, int64_t o0, int64_t o1, int 
 #pragma unroll
                 for (int e = 0; e < B * B; ++e) a[g][e] = __ldg(val + ((sl0 + g) * B * B + e) * 32 + lane);
         T v[kDepGroup][B];
-        load_group<B, T>(vec, c, v, ks);
+        load_group<B, T>(vec, c, v, ks, sleep_ns);
 #pragma unroll
         for (int g = 0; g < kDepGroup; ++g)
             if (c[g] >= 0)
@@ -281,7 +281,7 @@ template <int B, typename T, typename RT>
 __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_sf(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
                                                           const int64_t *__restrict__ off, const int32_t *__restrict__ col,
                                                           const T *__restrict__ val, const RT *__restrict__ r, T *y,
-                                                          KState *ks, const double *never) {
+                                                          KState *ks, const double *never, int sleep_ns) {
     __shared__ unsigned blk;
     const unsigned nchunks = (unsigned)((n + kSfThreads - 1) / kSfThreads);
     for (;;) {
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_sf(int32_t n, unsigned *
         T s[B];
 #pragma unroll
         for (int q = 0; q < B; ++q) s[q] = (T)__ldg(r + (int64_t)row * B + q);
-        subtract_deps<B, T>(s, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, y, ks);
+        subtract_deps<B, T>(s, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, y, ks, sleep_ns);
 #pragma unroll
         for (int q = 0; q < B; ++q) store_relaxed(y + (int64_t)t * B + q, s[q]);
     }
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_sf(int32_t n, unsigned *
                                                           const T *__restrict__ val, const T *__restrict__ dinv,
                                                           const T *__restrict__ y, T *z, double *__restrict__ out,
                                                           int ps, int ts, const XT *__restrict__ dp,
-                                                          const XT *__restrict__ dT, KState *ks) {
+                                                          const XT *__restrict__ dT, KState *ks, int sleep_ns) {
     __shared__ unsigned blk;
     const unsigned nchunks = (unsigned)((n + kSfThreads - 1) / kSfThreads);
     for (;;) {
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_sf(int32_t n, unsigned *
         T s[B];
 #pragma unroll
         for (int q = 0; q < B; ++q) s[q] = __ldcg(y + (int64_t)tf * B + q);
-        subtract_deps<B, T>(s, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, z, ks);
+        subtract_deps<B, T>(s, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, z, ks, sleep_ns);
         T zi[B];
 #pragma unroll
         for (int rr = 0; rr < B; ++rr) {
@@ -759,19 +759,19 @@ template <int B, typename T, typename RT, typename XT>
 static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT *dT) {
     cudaStream_t s = c->stream;
     const int32_t n = c->n;
-    const unsigned grid = std::min<unsigned>(nblk(n, kSfThreads), 4 * 152);
+    const unsigned grid = std::min<unsigned>(nblk(n, kSfThreads), (unsigned)c->sf_grid);
     T *y = (T *)c->sf_y, *zz = (T *)c->sf_z;
     (k_sf_fill<T><<<4 * 152, 256, 0, s>>>((int64_t)n * B, y, zz, c->sf_ticket), note_launch());
     if (c->inject_wait) (k_sf_fill<double><<<1, 32, 0, s>>>(1, c->never, c->never, c->sf_ticket + 2), note_launch());
     int pf = prof_begin(c, PF_ILU_FWD);
     (k_ilu_fwd_sf<B, T, RT><<<grid, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_f, c->sf_off_f, c->sf_col_f,
                                                          (const T *)c->sf_val_f, r, y, c->ks,
-                                                         c->inject_wait ? c->never : nullptr), note_launch());
+                                                         c->inject_wait ? c->never : nullptr, c->sf_sleep), note_launch());
     prof_end(c, pf);
     pf = prof_begin(c, PF_ILU_BWD);
     (k_ilu_bwd_sf<B, T, XT><<<grid, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_b, c->sf_bmap, c->sf_off_b,
                                                          c->sf_col_b, (const T *)c->sf_val_b, (const T *)c->sf_dinv, y,
-                                                         zz, z, c->ps, c->ts, dp, dT, c->ks), note_launch());
+                                                         zz, z, c->ps, c->ts, dp, dT, c->ks, c->sf_sleep), note_launch());
     prof_end(c, pf);
 }
 
@@ -809,6 +809,58 @@ void ilu_apply_into(const Ctx *c, const double *r, double *z, double *ybuf, doub
             (k_ilu_bwd<4><<<nblk(cnt, 128), 128, 0, s>>>(c->lvl_b, st, cnt, c->rp, c->ci, c->diag, c->LU, ybuf, zbuf, z,
                                                          c->ps, c->ts, nullptr, nullptr), note_launch());
     }
+}
+
+// Autotuner of the one-launch ILU(0) sweeps: the persistent grid (blocks in {152, 304, 608, 1216},
+// at most one per chunk) and the back-off between polls of a dependency not yet written
+// (__nanosleep of {8, 32, 128, 512} ns) set how many rows run ahead of the wavefront and how hard
+// they poll.  Each pair is timed with CUDA events over 3 applications (forward + backward) after
+// a warm-up, on a zero right-hand side; the fastest is kept and cached by the factor size.  The
+// sweeps compute the same values whatever the pair.
+cptr_status ilu_autotune(Ctx *c) {
+    if (!c->LU) return CPTR_OK;
+    const uint64_t key = (uint64_t)8 << 60 | (uint64_t)(c->o.precision & 1) << 56 |
+                         ((uint64_t)c->n & 0xFFFFFFull) << 32 | (uint64_t)(uint32_t)c->nnzb;
+    auto it = c->tune_cache.find(key);
+    if (it != c->tune_cache.end()) {
+        c->sf_grid = it->second.T;
+        c->sf_sleep = it->second.G;
+        return CPTR_OK;
+    }
+    double *r = c->xw, *z = c->w;   // scratch vectors of n*b doubles
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(r, 0, sizeof(double) * (size_t)c->n * c->b, c->stream));
+    cudaEvent_t e0, e1;
+    CPTR_CUDA_TRY(c, cudaEventCreate(&e0));
+    CPTR_CUDA_TRY(c, cudaEventCreate(&e1));
+    const int g0 = c->sf_grid, s0 = c->sf_sleep;
+    int best_g = g0, best_s = s0;
+    float best_ms = 1e30f;
+    const unsigned maxg = nblk(c->n, kSfThreads);
+    for (int g : {152, 304, 608, 1216}) {
+        if (g > (int)maxg && g != 152) continue;
+        for (int sl : {8, 32, 128, 512}) {
+            c->sf_grid = g;
+            c->sf_sleep = sl;
+            ilu_apply(c, r, z, nullptr, nullptr);
+            cudaEventRecord(e0, c->stream);
+            for (int rep = 0; rep < 3; ++rep) ilu_apply(c, r, z, nullptr, nullptr);
+            cudaEventRecord(e1, c->stream);
+            CPTR_CUDA_TRY(c, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) { best_ms = ms; best_g = g; best_s = sl; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->sf_grid = best_g;
+    c->sf_sleep = best_s;
+    Shape sh;
+    sh.T = (int16_t)best_g;
+    sh.G = (int16_t)best_s;
+    c->tune_cache[key] = sh;
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    return CPTR_OK;
 }
 
 }  // namespace cptr

@@ -610,10 +610,13 @@ __global__ void k_bscale(int64_t nb, const double *__restrict__ src, double *__r
     for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) dst[i] = src[i] * inv;
 }
 
-// vec <-> column k of each instance (dir 0: vec = base[k]; dir 1: base[k] = vec)
+// vec <-> column k of each instance (dir 0: vec = base[k]; dir 1: base[k] = vec).  Converged
+// instances are skipped: their k may equal m (converged on the last step of a cycle), and Z has
+// only m columns; their tiles of vec keep the last (finite) values
 __global__ void k_bcopy_col(int64_t nb, double *__restrict__ base, double *__restrict__ vec, const KState *ksb,
                             const int32_t *__restrict__ tile_inst, const int64_t *__restrict__ tile_beg, int dir) {
     const KState *ks = ksb + tile_inst[blockIdx.x];
+    if (ks->done) return;
     const double *colr = base + (int64_t)ks->k * nb;
     double *colw = base + (int64_t)ks->k * nb;
     const int64_t beg = tile_beg[blockIdx.x], end = tile_beg[blockIdx.x + 1];
