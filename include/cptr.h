@@ -83,6 +83,11 @@ typedef struct {
     int32_t ilu_order;   /* CPTR_ILU_NATURAL (default) or CPTR_ILU_MULTICOLOR */
     int32_t autotune;    /* 1: time the launch shapes of the V-cycle and SpMV kernels at set-up
                             and keep the fastest (see cptr_tuning); 0 (default): fixed shapes */
+    int32_t ilu_sweep;   /* schedule of the ILU(0) triangular sweeps (same values either way):
+                            0 (default) level sets, or, with autotune, the faster of level sets
+                            and the chunked wavefront where the pattern allows it (natural order,
+                            at most 4 dependencies per row, levels no wider than 256 rows inside a
+                            chunk); 1 level sets; 2 chunked wavefront where allowed */
     void *stream;        /* cudaStream_t for all work; NULL = the legacy default stream */
 } cptr_options;
 

@@ -26,6 +26,7 @@ MLP_FEATURES, MLP_HIDDEN, MLP_NPARAM = 16, 64, 5313
 SMOOTHER = {"l1": 0, "jacobi": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 ILU_ORDER = {"natural": 0, "multicolor": 1}
+ILU_SWEEP = {"auto": 0, "levels": 1, "chunked": 2}
 U_P, U_T, U_SAT = 0, 1, 2
 
 
@@ -35,7 +36,8 @@ class cptr_options(ctypes.Structure):
                 ("n_coarse", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_it", ctypes.c_int32), ("dense_max", ctypes.c_int32), ("seed", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("check_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("ilu_order", ctypes.c_int32), ("autotune", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("ilu_order", ctypes.c_int32), ("autotune", ctypes.c_int32), ("ilu_sweep", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
 
 
 class cptr_stats(ctypes.Structure):
@@ -156,6 +158,8 @@ def cptr_default_options(**kw) -> cptr_options:
             v = PRECISION[v]
         elif k == "ilu_order" and isinstance(v, str):
             v = ILU_ORDER[v]
+        elif k == "ilu_sweep" and isinstance(v, str):
+            v = ILU_SWEEP[v]
         setattr(o, k, v)
     return o
 

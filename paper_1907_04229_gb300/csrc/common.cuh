@@ -220,6 +220,13 @@ void apply_stage1(const Ctx *c, const double *v, const double **dp, const double
 void apply_stage1_32(const Ctx *c, const double *v, const float **dp, const float **dT);
 void apply_precond(const Ctx *c, const double *v, double *z);
 
+// tables of one chunked ILU(0) sweep (see ilu.cu)
+struct CwTables {
+    int32_t nchunks = 0, D = 0, W = 1, maxw = 0, threads = 0, smem = 0, ns = 2, maxlev = 0;
+    int32_t *clev = nullptr, *lptr = nullptr, *prow = nullptr, *code = nullptr;
+    void *val = nullptr;   // factor blocks (and inverted pivot blocks), FP64 or FP32
+};
+
 // ---- the context -------------------------------------------------------------------------------
 struct Ctx {
     cptr_options o{};
@@ -268,6 +275,8 @@ struct Ctx {
     void *sf_dinv = nullptr;                           // inverted pivot blocks, backward order
     unsigned *sf_ticket = nullptr;                     // block tickets of the two sweeps
     void *sf_y = nullptr, *sf_z = nullptr;             // level-ordered y and z (sentinel-filled)
+    CwTables cw_f, cw_b;                               // chunked wavefront sweeps (natural order)
+    bool cw_ok = false, cw_use = false;                // built / chosen (autotuner may switch)
     int32_t sf_grid = 4 * 152;                         // persistent grid of the sweeps (autotuned)
     int32_t sf_sleep = 20;                             // back-off between polls, ns (autotuned)
     int32_t inject_wait = 0;                           // failure injection (see cptr_inject_wait_timeout)

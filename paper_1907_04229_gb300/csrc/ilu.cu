@@ -351,6 +351,248 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_sf(int32_t n, unsigned *
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Chunked wavefront sweeps.  The rows of the factor order are cut into chunks of K consecutive
+// rows (K = the matrix's bandwidth, so that every dependency outside a chunk lies in an earlier
+// chunk of the sweep).  One block solves one chunk: it walks the chunk's own level sets (levels
+// counted over dependencies inside the chunk) with a __syncthreads between levels, keeping the
+// values of the last W levels in a shared-memory ring; dependencies on other chunks (and on
+// in-chunk rows more than W-1 levels back) are read from the global vector, whose unsolved
+// entries hold the sentinel, with bounded polls.  Chunks are handed out in sweep order by a
+// ticket, so a chunk only waits on chunks held by running blocks (no deadlock), and consecutive
+// chunks pipeline: on a natural-order grid a chunk is a plane and trails the previous plane by a
+// few levels.  The factor blocks of the next level are staged in shared memory by cp.async while
+// the current level computes, and the next level's outside dependencies are loaded early.
+// Each value is computed exactly as in the level-set sweeps above (same operations, same order).
+constexpr int kCwMaxD = 4;
+constexpr int kCwMaxThreads = 256;   // the widest level a chunk may have
+constexpr int32_t kCwNone = INT32_MIN;
+
+__device__ __forceinline__ void cp_async_elem(double *dst, const double *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(float *dst, const float *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+template <int NS>
+__device__ __forceinline__ void cp_async_wait_ns() {   // all but the NS - 1 most recent groups
+    asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1) : "memory");
+}
+
+// Software pipeline of one chunk.  Level l is computed at iteration l; at that iteration the
+// block also loads the rows and dependency codes of level l + 2 (position-indexed), the
+// right-hand sides and outside-dependency values of level l + 1 (indexed by the rows and codes
+// loaded one iteration earlier), and stages by cp.async the factor blocks of level l + NS - 1
+// into shared-memory slot (l + NS - 1) % NS.  Every global load therefore has one level of work
+// to arrive, and no load waits on another inside a level.  The chunk's level pointers are copied
+// to shared memory when the chunk starts.
+template <int B, typename T>
+struct CwA {          // position-indexed part of a level's row
+    bool act;
+    int32_t row;
+    int32_t cd[kCwMaxD];
+};
+template <int B, typename T>
+struct CwB {          // row-indexed part
+    T rhs[B];
+    T gv[kCwMaxD][B];
+};
+
+template <int B, typename T>
+__device__ __forceinline__ void cw_loadA(CwA<B, T> &a, int lp, int tid, int32_t n, int D, const int32_t *lv,
+                                         const int32_t *prow, const int32_t *code) {
+    const int32_t p = lv[lp] + tid;
+    a.act = p < lv[lp + 1];
+    if (!a.act) return;
+    a.row = __ldg(prow + p);
+#pragma unroll
+    for (int d = 0; d < kCwMaxD; ++d) a.cd[d] = d < D ? __ldg(code + (int64_t)d * n + p) : kCwNone;
+}
+
+template <int B, typename T, typename ST>
+__device__ __forceinline__ void cw_loadB(CwB<B, T> &b, const CwA<B, T> &a, const ST *src, const T *vec) {
+    if (!a.act) return;
+#pragma unroll
+    for (int q = 0; q < B; ++q) b.rhs[q] = (T)src[(int64_t)a.row * B + q];
+#pragma unroll
+    for (int d = 0; d < kCwMaxD; ++d)
+        if (a.cd[d] != kCwNone && a.cd[d] < 0) {
+            const int64_t j = -(int64_t)a.cd[d] - 1;
+#pragma unroll
+            for (int q = 0; q < B; ++q) b.gv[d][q] = load_relaxed(vec + j * B + q);
+        }
+}
+
+// stage the SW factor values of position p (planes e * n + p) into dst
+template <typename T>
+__device__ __forceinline__ void cw_stage(T *dst, int32_t p, int32_t n, int nvals, const T *val) {
+    for (int e = 0; e < nvals; ++e) cp_async_elem(dst + e, val + (int64_t)e * n + p);
+}
+
+// the value of dependency d: from the ring, or the early load (polled until written)
+template <int B, typename T>
+__device__ __forceinline__ void cw_dep(int32_t cd, const T *gv0, const T *ring, const T *vec, T *v, KState *ks,
+                                       int sleep_ns) {
+    if (cd >= 0) {
+#pragma unroll
+        for (int q = 0; q < B; ++q) v[q] = ring[(int64_t)cd * B + q];
+        return;
+    }
+    const int64_t j = -(int64_t)cd - 1;
+    bool pending = false;
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        v[q] = gv0[q];
+        pending |= is_sentinel(v[q]);
+    }
+    if (!pending) return;
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+        pending = false;
+#pragma unroll
+        for (int q = 0; q < B; ++q)
+            if (is_sentinel(v[q])) {
+                v[q] = load_relaxed(vec + j * B + q);
+                pending |= is_sentinel(v[q]);
+            }
+        if (!pending) return;
+        if (gtimer() - t0 > kWaitNs) {
+            atomicExch(&ks->wait_err, 1);
+#pragma unroll
+            for (int q = 0; q < B; ++q)
+                if (is_sentinel(v[q])) v[q] = (T)0;
+            return;
+        }
+        __nanosleep(sleep_ns);
+    }
+}
+
+// One kernel for both sweeps.  Forward (FWD): y(row) = r(row) - sum_d L(row, d) y(dep d).
+// Backward: z(row) = D(row)^{-1} (y(row) - sum_d U(row, d) z(dep d)), out(row) = z(row) + x1(row).
+// src: r (forward, type ST) or y (backward); vec: the vector being solved (y or z).
+template <int B, typename T, typename ST, typename XT, bool FWD, int NS>
+__global__ void __launch_bounds__(256) k_ilu_cw(int32_t nchunks, int32_t n, int D, int W, int maxw, int maxlev,
+                                                unsigned *ticket, const int32_t *__restrict__ clev,
+                                                const int32_t *__restrict__ lptr, const int32_t *__restrict__ prow,
+                                                const int32_t *__restrict__ code, const T *__restrict__ val,
+                                                const ST *__restrict__ src, T *vec, double *__restrict__ out, int ps,
+                                                int ts, const XT *__restrict__ dp, const XT *__restrict__ dT,
+                                                KState *ks, const double *never, int sleep_ns) {
+    constexpr int BB = B * B;
+    const int SW = FWD ? D * BB : D * BB + BB;
+    extern __shared__ __align__(16) unsigned char cw_smem[];
+    T *ring = reinterpret_cast<T *>(cw_smem);
+    T *stage = ring + (int64_t)W * maxw * B;
+    int32_t *lv = reinterpret_cast<int32_t *>(stage + (int64_t)NS * blockDim.x * SW);
+    __shared__ unsigned chunk_s;
+    const int tid = threadIdx.x;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) chunk_s = atomicAdd(ticket + (FWD ? 0 : 1), 1u);
+        __syncthreads();
+        const unsigned ch = chunk_s;
+        if (ch >= (unsigned)nchunks) return;
+        const int L0 = __ldg(clev + ch), nl = __ldg(clev + ch + 1) - L0;
+        for (int q = tid; q <= nl; q += blockDim.x) lv[q] = __ldg(lptr + L0 + q);
+        __syncthreads();
+        if (FWD && never && ch == 0 && tid == 0) (void)wait_value(never, ks);   // failure injection
+        // prologue: rows/codes of levels 0 and 1, values of level 0, blocks of levels 0 .. NS-2
+        CwA<B, T> a0, a1, a2;
+        CwB<B, T> b0, b1;
+        a0.act = a1.act = a2.act = false;
+        cw_loadA<B, T>(a0, 0, tid, n, D, lv, prow, code);
+        if (nl > 1) cw_loadA<B, T>(a1, 1, tid, n, D, lv, prow, code);
+        cw_loadB<B, T, ST>(b0, a0, src, vec);
+        for (int k = 0; k < NS - 1; ++k) {
+            if (k < nl) {
+                const int32_t p = lv[k] + tid;
+                if (p < lv[k + 1]) cw_stage(stage + ((int64_t)(k % NS) * blockDim.x + tid) * SW, p, n, SW, val);
+            }
+            cp_async_commit();
+        }
+        for (int l = 0; l < nl; ++l) {
+            // loads for later levels
+            a2.act = false;
+            if (l + 2 < nl) cw_loadA<B, T>(a2, l + 2, tid, n, D, lv, prow, code);
+            {
+                const int k = l + NS - 1;
+                if (k < nl) {
+                    const int32_t p = lv[k] + tid;
+                    if (p < lv[k + 1]) cw_stage(stage + ((int64_t)(k % NS) * blockDim.x + tid) * SW, p, n, SW, val);
+                }
+                cp_async_commit();
+            }
+            if (l + 1 < nl) cw_loadB<B, T, ST>(b1, a1, src, vec);
+            cp_async_wait_ns<NS>();   // the blocks of level l have arrived
+            if (a0.act) {
+                const T *a = stage + ((int64_t)(l % NS) * blockDim.x + tid) * SW;
+                T s[B];
+#pragma unroll
+                for (int q = 0; q < B; ++q) s[q] = b0.rhs[q];
+#pragma unroll
+                for (int d = 0; d < kCwMaxD; ++d) {
+                    if (a0.cd[d] == kCwNone) continue;
+                    T v[B];
+                    cw_dep<B, T>(a0.cd[d], b0.gv[d], ring, vec, v, ks, sleep_ns);
+                    const T *m = a + d * BB;
+#pragma unroll
+                    for (int rr = 0; rr < B; ++rr)
+#pragma unroll
+                        for (int q = 0; q < B; ++q) s[rr] = fma(-m[rr * B + q], v[q], s[rr]);
+                }
+                T res[B];
+                if (FWD) {
+#pragma unroll
+                    for (int q = 0; q < B; ++q) res[q] = s[q];
+                } else {
+                    const T *dinv = a + D * BB;
+#pragma unroll
+                    for (int rr = 0; rr < B; ++rr) {
+                        T acc = 0;
+#pragma unroll
+                        for (int q = 0; q < B; ++q) acc = fma(dinv[rr * B + q], s[q], acc);
+                        res[rr] = acc;
+                    }
+                }
+                T *slot = ring + ((int64_t)(l % W) * maxw + tid) * B;
+#pragma unroll
+                for (int q = 0; q < B; ++q) {
+                    slot[q] = res[q];
+                    store_relaxed(vec + (int64_t)a0.row * B + q, res[q]);
+                    if (!FWD) {
+                        double add = 0.0;
+                        if (dp && q == ps) add = (double)dp[a0.row];
+                        if (dT && q == ts) add = (double)dT[a0.row];
+                        out[(int64_t)a0.row * B + q] = (double)res[q] + add;
+                    }
+                }
+            }
+            __syncthreads();
+            a0 = a1;
+            a1 = a2;
+            b0 = b1;
+        }
+        cp_async_wait_0();
+    }
+}
+
+// gather factor blocks into the chunked tables: value e of slot d of position p (plane
+// (d * BB + e), entry p) comes from block kidx[d * n + p] (zero where there is none)
+template <typename T>
+__global__ void k_cw_pack(int32_t n, int nslots, int BB, const int32_t *kidx, const double *LU, T *val) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= (int64_t)nslots * n) return;
+    const int d = (int)(u / n);
+    const int32_t p = (int32_t)(u % n);
+    const int32_t k = kidx[u];
+    for (int e = 0; e < BB; ++e) val[((int64_t)d * BB + e) * n + p] = k >= 0 ? (T)LU[(int64_t)k * BB + e] : (T)0;
+}
+
 // pack factor blocks into the SELL-32 layout: slot u (slot * 32 + lane) takes block kidx[u]
 template <typename T>
 __global__ void k_sf_pack(int64_t nslots32, int BB, const int32_t *kidx, const double *LU, T *val) {
@@ -505,6 +747,124 @@ __global__ void __launch_bounds__(64) k_bilu_factor_sf(int32_t n, unsigned *tick
     }
 }
 
+// The same factorisation with the memory traffic of a row batched: the row's own blocks and
+// column indices are copied to shared memory while its dependency flags are polled; once all are
+// set, the inverted pivot blocks and upper blocks of every dependency are loaded in one batch;
+// then the row is factored in shared memory, in exactly the order of k_bilu_factor_sf (same
+// operations, same rounding), and written back.  A row thus costs about three memory round trips
+// instead of one per block update.  Per-thread shared memory: maxrow blocks + column indices, and
+// per dependency the pivot inverse plus maxu upper blocks (sizes from the pattern).
+template <int B>
+__global__ void __launch_bounds__(64) k_bilu_factor_st(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
+                                                       const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                                       const int32_t *__restrict__ diag, double *LU, int32_t *flag,
+                                                       int32_t epoch, int32_t *singular, KState *ks, int maxrow,
+                                                       int maxdep, int maxu) {
+    constexpr int BB = B * B;
+    extern __shared__ __align__(16) unsigned char fs_smem[];
+    const int per = (maxrow + maxdep * (1 + maxu)) * BB;       // doubles per thread
+    double *rowb = reinterpret_cast<double *>(fs_smem) + (int64_t)threadIdx.x * per;
+    double *depb = rowb + (int64_t)maxrow * BB;
+    int32_t *cols = reinterpret_cast<int32_t *>(reinterpret_cast<double *>(fs_smem) + (int64_t)blockDim.x * per) +
+                    threadIdx.x * maxrow;
+    __shared__ unsigned blk;
+    const unsigned nchunks = (unsigned)((n + 63) / 64);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) blk = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const unsigned b = blk;
+        if (b >= nchunks) return;
+        const int32_t t = (int32_t)(b * 64 + threadIdx.x);
+        if (t >= n) continue;
+        const int32_t i = pos[t];
+        const int32_t k0 = rp[i], e = rp[i + 1], kd = diag[i], len = e - k0;
+        // the row's own blocks and columns (nobody else writes them)
+        for (int32_t k = 0; k < len; ++k) {
+            cols[k] = ci[k0 + k];
+#pragma unroll
+            for (int q = 0; q < BB; ++q) rowb[k * BB + q] = LU[(int64_t)(k0 + k) * BB + q];
+        }
+        // wait until every row this row depends on has published its blocks
+        {
+            unsigned long long t0 = 0;
+            bool pending = true;
+            for (int round = 0; pending; ++round) {
+                pending = false;
+                for (int32_t k = k0; k < kd; ++k) {
+                    int32_t f;
+                    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flag + cols[k - k0]) : "memory");
+                    pending |= f != epoch;
+                }
+                if (!pending) break;
+                if (round == 0) t0 = gtimer();
+                else if (gtimer() - t0 > kWaitNs) { atomicExch(&ks->wait_err, 1); break; }
+                __nanosleep(20);
+            }
+        }
+        // every dependency's inverted pivot block and upper blocks, in one batch
+        for (int32_t k = k0; k < kd; ++k) {
+            const int32_t c = cols[k - k0];
+            double *dst = depb + (int64_t)(k - k0) * (1 + maxu) * BB;
+            const int32_t dc = diag[c], ec = rp[c + 1];
+#pragma unroll
+            for (int q = 0; q < BB; ++q) dst[q] = __ldcg(LU + (int64_t)dc * BB + q);
+            for (int32_t qq = dc + 1; qq < ec; ++qq)
+#pragma unroll
+                for (int q = 0; q < BB; ++q) dst[(1 + qq - dc - 1) * BB + q] = __ldcg(LU + (int64_t)qq * BB + q);
+        }
+        // factor the row in shared memory (the order of k_bilu_factor_sf)
+        for (int32_t k = k0; k < kd; ++k) {
+            const int32_t c = cols[k - k0];
+            const double *dep = depb + (int64_t)(k - k0) * (1 + maxu) * BB;
+            const double *dinv = dep;
+            double a[BB], l[BB];
+#pragma unroll
+            for (int q = 0; q < BB; ++q) a[q] = rowb[(k - k0) * BB + q];
+#pragma unroll
+            for (int r = 0; r < B; ++r)
+#pragma unroll
+                for (int q = 0; q < B; ++q) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int u = 0; u < B; ++u) s = fma(a[r * B + u], dinv[u * B + q], s);
+                    l[r * B + q] = s;
+                }
+#pragma unroll
+            for (int q = 0; q < BB; ++q) rowb[(k - k0) * BB + q] = l[q];
+            const int32_t dc = diag[c], ec = rp[c + 1];
+            int32_t p = k + 1;
+            for (int32_t qq = dc + 1; qq < ec; ++qq) {
+                const int32_t j = ci[qq];
+                while (p < e && cols[p - k0] < j) ++p;
+                if (p < e && cols[p - k0] == j) {
+                    const double *u = dep + (1 + qq - dc - 1) * BB;
+                    double *d = rowb + (p - k0) * BB;
+#pragma unroll
+                    for (int r = 0; r < B; ++r)
+#pragma unroll
+                        for (int q = 0; q < B; ++q) {
+                            double s = d[r * B + q];
+#pragma unroll
+                            for (int w = 0; w < B; ++w) s = fma(-l[r * B + w], u[w * B + q], s);
+                            d[r * B + q] = s;
+                        }
+                }
+            }
+        }
+        double dd[BB];
+#pragma unroll
+        for (int q = 0; q < BB; ++q) dd[q] = rowb[(kd - k0) * BB + q];
+        if (!block_inverse<B>(dd)) atomicOr(singular, 1);
+#pragma unroll
+        for (int q = 0; q < BB; ++q) rowb[(kd - k0) * BB + q] = dd[q];
+        for (int32_t k = 0; k < len; ++k)
+#pragma unroll
+            for (int q = 0; q < BB; ++q) LU[(int64_t)(k0 + k) * BB + q] = rowb[k * BB + q];
+        asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(flag + i), "r"(epoch) : "memory");
+    }
+}
+
 // level sets of one direction: pos (position -> row), inv, and the level pointers (host)
 static cptr_status device_levels(Ctx *c, const int32_t *rp, const int32_t *ci, bool forward, int32_t *pos,
                                  int32_t *inv, std::vector<int32_t> &h_lptr) {
@@ -604,6 +964,174 @@ __global__ void k_gather_blocks(int32_t nnzb, int BB, const int32_t *kmap, const
     dst[u] = src[(int64_t)kmap[k] * BB + e];
 }
 
+// Host tables of the chunked sweeps for one direction (forward: dependencies j < i, chunks in
+// increasing order; backward: j > i, chunks in decreasing order).  Positions enumerate the rows
+// chunk by chunk in processing order and, inside a chunk, by local level (rows in dependency
+// order within a level).  code[d * n + p]: >= 0 a ring slot (local level mod W) * maxw + index in
+// level; < 0 (but not kCwNone) the global row -(code + 1); kCwNone no dependency.  kidx gives the
+// factor block of each slot (and, backward, the diagonal block in slot D).
+struct CwHost {
+    int32_t nchunks = 0, D = 0, W = 1, maxw = 0, nlev_total = 0, max_chunk_levels = 0;
+    std::vector<int32_t> clev, lptr, prow, code, kidx;
+};
+
+static CwHost cw_build(int32_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
+                       const std::vector<int32_t> &dg, int32_t K, bool forward) {
+    CwHost h;
+    const int32_t nch = (n + K - 1) / K;
+    h.nchunks = nch;
+    std::vector<int32_t> lev(n, 0), idx(n, 0);
+    auto is_dep = [&](int32_t i, int32_t j) { return forward ? j < i : j > i; };
+    int32_t maxdist = 0, D = 0;
+    for (int32_t t = 0; t < nch; ++t) {
+        const int32_t c = forward ? t : nch - 1 - t;
+        const int32_t r0 = c * K, r1 = std::min<int32_t>(n, r0 + K);
+        for (int32_t u = 0; u < r1 - r0; ++u) {
+            const int32_t i = forward ? r0 + u : r1 - 1 - u;
+            int32_t l = 0, nd = 0;
+            for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+                const int32_t j = ci[k];
+                if (!is_dep(i, j)) continue;
+                ++nd;
+                if (j >= r0 && j < r1) l = std::max(l, lev[j] + 1);
+            }
+            lev[i] = l;
+            D = std::max(D, nd);
+        }
+        for (int32_t i = r0; i < r1; ++i)
+            for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+                const int32_t j = ci[k];
+                if (is_dep(i, j) && j >= r0 && j < r1) maxdist = std::max(maxdist, lev[i] - lev[j]);
+            }
+    }
+    h.D = D;
+    h.W = std::min(maxdist, 3) + 1;
+    // positions: per chunk, a stable counting sort by local level (dependency order inside a level)
+    h.prow.resize(n);
+    h.clev.assign(nch + 1, 0);
+    std::vector<int32_t> cnt;
+    int32_t pos = 0;
+    for (int32_t t = 0; t < nch; ++t) {
+        const int32_t c = forward ? t : nch - 1 - t;
+        const int32_t r0 = c * K, r1 = std::min<int32_t>(n, r0 + K);
+        int32_t nl = 0;
+        for (int32_t i = r0; i < r1; ++i) nl = std::max(nl, lev[i] + 1);
+        cnt.assign(nl + 1, 0);
+        for (int32_t i = r0; i < r1; ++i) ++cnt[lev[i] + 1];
+        for (int32_t l = 0; l < nl; ++l) cnt[l + 1] += cnt[l];
+        h.clev[t] = (int32_t)h.lptr.size();
+        for (int32_t l = 0; l < nl; ++l) {
+            h.lptr.push_back(pos + cnt[l]);
+            h.maxw = std::max(h.maxw, cnt[l + 1] - cnt[l]);
+        }
+        h.max_chunk_levels = std::max(h.max_chunk_levels, nl);
+        std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+        for (int32_t u = 0; u < r1 - r0; ++u) {
+            const int32_t i = forward ? r0 + u : r1 - 1 - u;
+            const int32_t q = fill[lev[i]]++;
+            h.prow[pos + q] = i;
+            idx[i] = q - cnt[lev[i]];
+        }
+        pos += r1 - r0;
+    }
+    h.clev[nch] = (int32_t)h.lptr.size();
+    h.nlev_total = (int32_t)h.lptr.size();
+    h.lptr.push_back(n);
+    // dependency codes and factor block indices
+    const int nslots = h.D + (forward ? 0 : 1);
+    h.code.assign((size_t)std::max(h.D, 1) * n, kCwNone);
+    h.kidx.assign((size_t)std::max(nslots, 1) * n, -1);
+    for (int32_t p = 0; p < n; ++p) {
+        const int32_t i = h.prow[p];
+        const int32_t c = i / K, r0 = c * K, r1 = std::min<int32_t>(n, r0 + K);
+        int d = 0;
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+            const int32_t j = ci[k];
+            if (!is_dep(i, j)) continue;
+            const bool ring = j >= r0 && j < r1 && lev[i] - lev[j] <= h.W - 1;
+            h.code[(size_t)d * n + p] = ring ? (lev[j] % h.W) * h.maxw + idx[j] : -(j + 1);
+            h.kidx[(size_t)d * n + p] = k;
+            ++d;
+        }
+        if (!forward) h.kidx[(size_t)h.D * n + p] = dg[i];
+    }
+    return h;
+}
+
+// chunked tables of both sweeps (natural order only); c->cw_ok tells whether they fit
+static cptr_status cw_setup(Ctx *c) {
+    c->cw_ok = false;
+    const int32_t n = c->n, B = c->b, BB = B * B;
+    const std::vector<int32_t> &rp = c->h_rp, &ci = c->h_ci;
+    int32_t K = 1;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) K = std::max(K, std::abs(i - ci[k]));
+    K = std::max<int32_t>(K, std::min<int32_t>(n, 4096));
+    CwHost hf = cw_build(n, rp, ci, c->h_diag, K, true);
+    CwHost hb = cw_build(n, rp, ci, c->h_diag, K, false);
+    const bool lo = c->o.precision == CPTR_PREC_MIXED;
+    const size_t tsz = lo ? 4 : 8;
+    const int maxw = std::max(hf.maxw, hb.maxw);
+    const int threads = std::max(32, (maxw + 31) / 32 * 32);
+    auto smem = [&](const CwHost &h, int extra, int ns) {
+        return (size_t)h.W * h.maxw * B * tsz + (size_t)ns * threads * (h.D * BB + extra) * tsz +
+               (size_t)(h.max_chunk_levels + 1) * 4;
+    };
+    const size_t kLimit = 200 * 1024;
+    auto pick_ns = [&](const CwHost &h, int extra) { return smem(h, extra, 3) <= kLimit ? 3 : 2; };
+    const int ns_f = pick_ns(hf, 0), ns_b = pick_ns(hb, BB);
+    if (hf.D > kCwMaxD || hb.D > kCwMaxD || threads > kCwMaxThreads || smem(hf, 0, ns_f) > kLimit ||
+        smem(hb, BB, ns_b) > kLimit)
+        return CPTR_OK;
+    cudaStream_t st = c->stream;
+    auto up = [&](const std::vector<int32_t> &v, int32_t **dst) -> cptr_status {
+        CPTR_TRY(dalloc_t(c, dst, std::max<size_t>(v.size(), 1)));
+        if (!v.empty())
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(*dst, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice, st));
+        return CPTR_OK;
+    };
+    CwTables *T2[2] = {&c->cw_f, &c->cw_b};
+    const CwHost *H2[2] = {&hf, &hb};
+    for (int dir = 0; dir < 2; ++dir) {
+        CwTables &t = *T2[dir];
+        const CwHost &h = *H2[dir];
+        t.nchunks = h.nchunks;
+        t.D = h.D;
+        t.W = h.W;
+        t.maxw = h.maxw;
+        t.threads = threads;
+        t.ns = dir ? ns_b : ns_f;
+        t.maxlev = h.max_chunk_levels;
+        t.smem = (int32_t)smem(h, dir ? BB : 0, t.ns);
+        CPTR_TRY(up(h.clev, &t.clev));
+        CPTR_TRY(up(h.lptr, &t.lptr));
+        CPTR_TRY(up(h.prow, &t.prow));
+        CPTR_TRY(up(h.code, &t.code));
+        int32_t *kidx = nullptr;
+        CPTR_TRY(up(h.kidx, &kidx));
+        const int nslots = h.D + dir;
+        CPTR_TRY(dalloc(c, &t.val, (size_t)std::max(nslots, 1) * BB * n * tsz));
+        if (nslots > 0) {
+            if (lo) (k_cw_pack<float><<<nblk((int64_t)nslots * n, 256), 256, 0, st>>>(n, nslots, BB, kidx, c->LU, (float *)t.val), note_launch());
+            else (k_cw_pack<double><<<nblk((int64_t)nslots * n, 256), 256, 0, st>>>(n, nslots, BB, kidx, c->LU, (double *)t.val), note_launch());
+        }
+        CPTR_CUDA_TRY(c, cudaStreamSynchronize(st));
+        dfree(kidx);
+    }
+    c->cw_ok = true;
+    c->cw_use = c->o.ilu_sweep == 2;   // with autotune, the timing decides
+    return CPTR_OK;
+}
+
+static void cw_free(Ctx *c) {
+    for (CwTables *t : {&c->cw_f, &c->cw_b}) {
+        dfree(t->clev); dfree(t->lptr); dfree(t->prow); dfree(t->code); dfree(t->val);
+        *t = CwTables();
+    }
+    c->cw_ok = false;
+    c->cw_use = false;
+}
+
 cptr_status ilu_setup(Ctx *c) {
     ilu_free(c);
     double t0 = host_ms();
@@ -682,8 +1210,48 @@ cptr_status ilu_setup(Ctx *c) {
     CPTR_CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), st));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(c->sf_ticket, 0, 4 * sizeof(unsigned), st));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(reinterpret_cast<char *>(c->ks) + offsetof(KState, wait_err), 0, sizeof(int32_t), st));
+    // per-row sizes of the pattern: the staged kernel holds a row, and the pivot inverse and upper
+    // blocks of each dependency, in shared memory when that fits
+    int maxrow = 0, maxdep = 0, maxu = 0;
+    {
+        const std::vector<int32_t> *prp = &c->h_rp, *pci = &c->h_ci;
+        std::vector<int32_t> mrp, mci;
+        if (mc) {   // the permuted pattern
+            mrp.resize(n + 1);
+            mci.resize(c->nnzb);
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(mrp.data(), c->ilu_rp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, st));
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(mci.data(), c->ilu_ci, sizeof(int32_t) * c->nnzb, cudaMemcpyDeviceToHost, st));
+            CPTR_CUDA_TRY(c, cudaStreamSynchronize(st));
+            prp = &mrp;
+            pci = &mci;
+        }
+        for (int32_t i = 0; i < n; ++i) {
+            int lower = 0, upper = 0;
+            for (int32_t k = (*prp)[i]; k < (*prp)[i + 1]; ++k) {
+                if ((*pci)[k] < i) ++lower;
+                if ((*pci)[k] > i) ++upper;
+            }
+            maxrow = std::max(maxrow, (*prp)[i + 1] - (*prp)[i]);
+            maxdep = std::max(maxdep, lower);
+            maxu = std::max(maxu, upper);
+        }
+    }
+    const size_t fs_bytes = (size_t)64 * ((size_t)(maxrow + maxdep * (1 + maxu)) * BB * 8 + (size_t)maxrow * 4);
     const unsigned fgrid = std::min<unsigned>(nblk(n, 64), 8 * 152);
-    if (c->b == 3)
+    if (fs_bytes <= 100 * 1024) {
+        const unsigned sgrid = std::min<unsigned>(nblk(n, 64), 2 * 152);
+        if (c->b == 3) {
+            cudaFuncSetAttribute(k_bilu_factor_st<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs_bytes);
+            (k_bilu_factor_st<3><<<sgrid, 64, fs_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
+                                                              c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch, c->flag,
+                                                              c->ks, maxrow, maxdep, maxu), note_launch());
+        } else {
+            cudaFuncSetAttribute(k_bilu_factor_st<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs_bytes);
+            (k_bilu_factor_st<4><<<sgrid, 64, fs_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
+                                                              c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch, c->flag,
+                                                              c->ks, maxrow, maxdep, maxu), note_launch());
+        }
+    } else if (c->b == 3)
         (k_bilu_factor_sf<3><<<fgrid, 64, 0, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, c->LU,
                                                     c->ilu_flags, c->ilu_epoch, c->flag, c->ks), note_launch());
     else
@@ -733,11 +1301,13 @@ cptr_status ilu_setup(Ctx *c) {
     CPTR_TRY(dalloc(c, &c->sf_z, (size_t)n * c->b * (lo ? 4 : 8)));
     CPTR_CUDA_TRY(c, cudaGetLastError());
     dfree(kidx_f); dfree(kidx_b); dfree(kidx_d); dfree(inv_f); dfree(inv_b);
+    if (!mc && (c->o.ilu_sweep == 2 || (c->o.ilu_sweep == 0 && c->o.autotune))) CPTR_TRY(cw_setup(c));
     setup_tick(c, SETUP_ILU_HOST, &t0);
     return CPTR_OK;
 }
 
 void ilu_free(Ctx *c) {
+    cw_free(c);
     if (c->ilu_owns_pattern) { dfree(c->ilu_rp); dfree(c->ilu_ci); dfree(c->ilu_diag); dfree(c->ilu_rowmap); }
     c->ilu_rowmap = nullptr;
     c->ilu_owns_pattern = false;
@@ -752,6 +1322,22 @@ void ilu_free(Ctx *c) {
     for (void **p : sf) { dfree(*p); *p = nullptr; }
 }
 
+// launch one chunked sweep with its tables (NS = stage slots chosen at set-up)
+template <int B, typename T, typename ST, typename XT, bool FWD>
+static void cw_launch(const Ctx *c, const CwTables &t, const ST *src, T *vec, double *out, const XT *dp, const XT *dT,
+                      const double *never) {
+    const unsigned grid = (unsigned)std::min(t.nchunks, 152);
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, t.smem);
+        (kern<<<grid, t.threads, t.smem, c->stream>>>(t.nchunks, c->n, t.D, t.W, t.maxw, t.maxlev, c->sf_ticket, t.clev,
+                                                     t.lptr, t.prow, t.code, (const T *)t.val, src, vec, out, c->ps,
+                                                     c->ts, dp, dT, c->ks, never, c->sf_sleep),
+         note_launch());
+    };
+    if (t.ns == 3) go(k_ilu_cw<B, T, ST, XT, FWD, 3>);
+    else go(k_ilu_cw<B, T, ST, XT, FWD, 2>);
+}
+
 // z = (LU)^{-1} r + x1, where x1 carries dp in slot ps and dT in slot ts (either may be null):
 // sentinel fill, forward sweep, backward sweep (three launches).  T: factor storage and sweep
 // arithmetic; RT: type of r; XT: type of dp, dT.
@@ -763,6 +1349,16 @@ static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT 
     T *y = (T *)c->sf_y, *zz = (T *)c->sf_z;
     (k_sf_fill<T><<<4 * 152, 256, 0, s>>>((int64_t)n * B, y, zz, c->sf_ticket), note_launch());
     if (c->inject_wait) (k_sf_fill<double><<<1, 32, 0, s>>>(1, c->never, c->never, c->sf_ticket + 2), note_launch());
+    if (c->cw_use) {
+        const CwTables &F = c->cw_f, &Bk = c->cw_b;
+        int pf = prof_begin(c, PF_ILU_FWD);
+        cw_launch<B, T, RT, XT, true>(c, F, r, y, nullptr, nullptr, nullptr, c->inject_wait ? c->never : nullptr);
+        prof_end(c, pf);
+        pf = prof_begin(c, PF_ILU_BWD);
+        cw_launch<B, T, T, XT, false>(c, Bk, y, zz, z, dp, dT, nullptr);
+        prof_end(c, pf);
+        return;
+    }
     int pf = prof_begin(c, PF_ILU_FWD);
     (k_ilu_fwd_sf<B, T, RT><<<grid, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_f, c->sf_off_f, c->sf_col_f,
                                                          (const T *)c->sf_val_f, r, y, c->ks,
@@ -811,23 +1407,27 @@ void ilu_apply_into(const Ctx *c, const double *r, double *z, double *ybuf, doub
     }
 }
 
-// Autotuner of the one-launch ILU(0) sweeps: the persistent grid (blocks in {152, 304, 608, 1216},
-// at most one per chunk) and the back-off between polls of a dependency not yet written
-// (__nanosleep of {8, 32, 128, 512} ns) set how many rows run ahead of the wavefront and how hard
-// they poll.  Each pair is timed with CUDA events over 3 applications (forward + backward) after
-// a warm-up, on a zero right-hand side; the fastest is kept and cached by the factor size.  The
-// sweeps compute the same values whatever the pair.
+// Autotuner of the one-launch ILU(0) sweeps: for the level-set schedule, the persistent grid
+// (blocks in {152, 304, 608, 1216}) and the back-off between polls of a dependency not yet
+// written (__nanosleep of {8, 32, 128, 512} ns), which set how many rows run ahead of the wavefront
+// and how hard they poll; then, where the chunked schedule exists, its back-off, and the faster
+// schedule is kept.  Each candidate is timed with CUDA events over 3 applications (forward +
+// backward) after a warm-up, on a zero right-hand side; the result is cached by the factor size.
+// The sweeps compute the same values whatever the choice.
 cptr_status ilu_autotune(Ctx *c) {
     if (!c->LU) return CPTR_OK;
     const uint64_t key = (uint64_t)8 << 60 | (uint64_t)(c->o.precision & 1) << 56 |
                          ((uint64_t)c->n & 0xFFFFFFull) << 32 | (uint64_t)(uint32_t)c->nnzb;
     auto it = c->tune_cache.find(key);
     if (it != c->tune_cache.end()) {
-        c->sf_grid = it->second.T;
+        c->sf_grid = std::abs((int)it->second.T);
         c->sf_sleep = it->second.G;
+        if (c->cw_ok && c->o.ilu_sweep == 0) c->cw_use = it->second.T < 0;
         return CPTR_OK;
     }
     double *r = c->xw, *z = c->w;   // scratch vectors of n*b doubles
+    const bool cw_was = c->cw_use;
+    c->cw_use = false;              // time the level-set sweeps first
     CPTR_CUDA_TRY(c, cudaMemsetAsync(r, 0, sizeof(double) * (size_t)c->n * c->b, c->stream));
     cudaEvent_t e0, e1;
     CPTR_CUDA_TRY(c, cudaEventCreate(&e0));
@@ -851,13 +1451,35 @@ cptr_status ilu_autotune(Ctx *c) {
             if (ms < best_ms) { best_ms = ms; best_g = g; best_s = sl; }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     c->sf_grid = best_g;
     c->sf_sleep = best_s;
     Shape sh;
     sh.T = (int16_t)best_g;
     sh.G = (int16_t)best_s;
+    if (c->cw_ok && c->o.ilu_sweep == 0) {   // the chunked sweeps at their best back-off
+        c->cw_use = true;
+        int cw_s = best_s;
+        float cw_ms = 1e30f;
+        for (int sl : {8, 32, 128, 512}) {
+            c->sf_sleep = sl;
+            ilu_apply(c, r, z, nullptr, nullptr);
+            cudaEventRecord(e0, c->stream);
+            for (int rep = 0; rep < 3; ++rep) ilu_apply(c, r, z, nullptr, nullptr);
+            cudaEventRecord(e1, c->stream);
+            CPTR_CUDA_TRY(c, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < cw_ms) { cw_ms = ms; cw_s = sl; }
+        }
+        c->cw_use = cw_ms < best_ms;
+        c->sf_sleep = c->cw_use ? cw_s : best_s;
+        sh.G = (int16_t)c->sf_sleep;
+        sh.T = (int16_t)(c->cw_use ? -best_g : best_g);   // negative: the chunked sweeps won
+    } else {
+        c->cw_use = cw_was;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     c->tune_cache[key] = sh;
     CPTR_CUDA_TRY(c, cudaGetLastError());
     return CPTR_OK;

@@ -69,6 +69,49 @@ __device__ void cgs_finish(KState *ks, const double *res, int fin, int j, int m,
     }
 }
 
+// The element loop of a Gram-Schmidt pass with NQ columns compiled in (NQ = nc rounded up to a
+// multiple of 8, so at most 7 columns are carried as predicated-off work): each element reads w
+// once, updates it (UPD) and adds its products to the per-column partial sums.
+template <int PASS, int NQ>
+__device__ __forceinline__ void cgs_elements(int64_t i0, int64_t i1, int64_t step, int64_t nb,
+                                             const double *__restrict__ V, int nc, double *__restrict__ w,
+                                             const double *scoef, double *acc) {
+    constexpr bool UPD = PASS == PASS_UPD_DOT || PASS == PASS_UPD_NORM;
+    constexpr bool NORM = PASS == PASS_UPD_NORM || PASS == PASS_NORM;
+    for (int64_t i = i0; i < i1; i += step) {
+        double wi = w[i];
+        if (UPD) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (q < nc) wi = fma(-scoef[q], __ldg(V + (int64_t)q * nb + i), wi);
+            w[i] = wi;
+        }
+        if (NORM) {
+            acc[0] = fma(wi, wi, acc[0]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (q < nc) acc[q] = fma(__ldg(V + (int64_t)q * nb + i), wi, acc[q]);
+        }
+    }
+}
+
+template <int PASS>
+__device__ __forceinline__ void cgs_dispatch(int64_t i0, int64_t i1, int64_t step, int64_t nb, const double *V, int nc,
+                                             double *w, const double *scoef, double *acc) {
+    constexpr bool NORM = PASS == PASS_UPD_NORM || PASS == PASS_NORM;
+    constexpr bool UPD = PASS == PASS_UPD_DOT || PASS == PASS_UPD_NORM;
+    if (NORM && !UPD) {
+        cgs_elements<PASS, 1>(i0, i1, step, nb, V, nc, w, scoef, acc);
+        return;
+    }
+    const int ng = (nc + 7) >> 3;
+    if (ng <= 1) cgs_elements<PASS, 8>(i0, i1, step, nb, V, nc, w, scoef, acc);
+    else if (ng == 2) cgs_elements<PASS, 16>(i0, i1, step, nb, V, nc, w, scoef, acc);
+    else if (ng == 3) cgs_elements<PASS, 24>(i0, i1, step, nb, V, nc, w, scoef, acc);
+    else cgs_elements<PASS, 32>(i0, i1, step, nb, V, nc, w, scoef, acc);
+}
+
 // One Gram-Schmidt pass over v_0..v_{nc-1} (columns of V, stride nb):
 //   PASS_DOT       partial[q] = v_q . w
 //   PASS_UPD_DOT   w -= sum_q coef_q v_q; partial[q] = v_q . w
@@ -96,22 +139,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cgs(int64_t nb, const double *_
 #pragma unroll
     for (int q = 0; q < NA; ++q) acc[q] = 0.0;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride) {
-        double wi = w[i];
-        if (UPD) {
-#pragma unroll
-            for (int q = 0; q < kMaxC; ++q)
-                if (q < nc) wi = fma(-scoef[q], __ldg(V + (int64_t)q * nb + i), wi);
-            w[i] = wi;
-        }
-        if (NORM) {
-            acc[0] = fma(wi, wi, acc[0]);
-        } else {
-#pragma unroll
-            for (int q = 0; q < kMaxC; ++q)
-                if (q < nc) acc[q] = fma(__ldg(V + (int64_t)q * nb + i), wi, acc[q]);
-        }
-    }
+    cgs_dispatch<PASS>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, nb, stride, nb, V, nc, w, scoef, acc);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int na = NORM ? 1 : nc;
 #pragma unroll
@@ -542,22 +570,7 @@ __global__ void __launch_bounds__(kRedThreads) k_bcgs(int64_t nb, const double *
 #pragma unroll
     for (int q = 0; q < NA; ++q) acc[q] = 0.0;
     const int64_t beg = tile_beg[blockIdx.x], end = tile_beg[blockIdx.x + 1];
-    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
-        double wi = w[i];
-        if (UPD) {
-#pragma unroll
-            for (int q = 0; q < kMaxC; ++q)
-                if (q < nc) wi = fma(-scoef[q], __ldg(V + (int64_t)q * nb + i), wi);
-            w[i] = wi;
-        }
-        if (NORM) {
-            acc[0] = fma(wi, wi, acc[0]);
-        } else {
-#pragma unroll
-            for (int q = 0; q < kMaxC; ++q)
-                if (q < nc) acc[q] = fma(__ldg(V + (int64_t)q * nb + i), wi, acc[q]);
-        }
-    }
+    cgs_dispatch<PASS>(beg + threadIdx.x, end, blockDim.x, nb, V, nc, w, scoef, acc);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int na = NORM ? 1 : nc;
 #pragma unroll

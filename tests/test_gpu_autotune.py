@@ -36,17 +36,19 @@ def test_tuned_solve_matches_untuned(precision):
     assert err <= (1e-10 if precision == "fp64" else 1e-6), float(err)
     rows = cp.cptr_tuning(b.ctx)
     levels = ia["levels_p"] - 1 + ia["levels_T"] - 1
-    assert len(rows) == 3 * levels + 2
+    assert len(rows) == 3 * levels + 3
     for h, l, k, G, T in rows:
         if k == 3:
             assert h == 2 and T in (64, 128, 256, 512)
-        elif k == 4:       # ILU sweeps: poll back-off (ns), persistent grid
+        elif k == 4:       # ILU sweeps: poll back-off (ns), persistent grid of the level-set schedule
             assert h == 3 and G in (8, 32, 128, 512) and T in (152, 304, 608, 1216)
+        elif k == 5:       # ILU sweeps: chunked wavefront chosen (1) or level sets (0)
+            assert h == 3 and G in (0, 1)
         else:
             assert G in (2, 4, 8, 16, 32) and T in (128, 256, 512)
-    # untuned: heuristic lanes, 256 threads; sweeps on 608 blocks, 20 ns back-off
+    # untuned: heuristic lanes, 256 threads; level-set sweeps on 608 blocks, 20 ns back-off
     for h, l, k, G, T in cp.cptr_tuning(a.ctx):
-        assert (G, T) == ((20, 608) if k == 4 else (0, 256))
+        assert (G, T) == {4: (20, 608), 5: (0, 0)}.get(k, (0, 256))
     # a second set-up of the same operators reuses the cached shapes
     b.setup(s["n"], s["b"], dev(s["row_ptr"]), dev(s["col_idx"]), dev(s["vals"].reshape(-1)),
             dev(s["unknown_kind"]), dev(s["weights"].reshape(-1)), dev(s["st"]))
