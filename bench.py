@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--no-ensemble", action="store_true")
     p.add_argument("--three-phase-grid", type=int, nargs=3, default=None,
                    help="run the three-phase section on an NX NY NZ box instead of 200x200x50 (profiling)")
+    p.add_argument("--autotune", action="store_true", help="autotune launch shapes in the headline solver")
+    p.add_argument("--ilu-sweep", choices=["auto", "levels", "chunked"], default="auto",
+                   help="schedule of the headline solver's ILU(0) sweeps")
     p.add_argument("--ensemble-total", type=float, default=4e6,
                    help="total cells of the ensemble (profiling runs use a smaller one)")
     return p.parse_args()
@@ -187,7 +190,8 @@ def ours(args, rank, world, local_rank):
     d = {k: torch.as_tensor(np.ascontiguousarray(v), device=dev) for k, v in host.items()}
     x = torch.empty(dofs, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    S = cp.Solver(stream=stream)
+    head_opts = dict(autotune=int(args.autotune), ilu_sweep=args.ilu_sweep)
+    S = cp.Solver(stream=stream, **head_opts)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
@@ -263,7 +267,7 @@ def ours(args, rank, world, local_rank):
     if not args.no_e2e:
         hp = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
         xh = torch.empty(dofs, dtype=torch.float64).pin_memory()
-        Sh = cp.Solver(stream=stream)
+        Sh = cp.Solver(stream=stream, **head_opts)
 
         def step_host():
             Sh.setup(n, b, hp["rp"].numpy(), hp["ci"].numpy(), hp["vals"].numpy(), hp["kind"].numpy(),

@@ -9,6 +9,8 @@
 #include <stddef.h>
 
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <type_traits>
 #include <utility>
 #include <vector>
@@ -475,7 +477,10 @@ __device__ __forceinline__ void cw_dep(int32_t cd, const T *gv0, const T *ring, 
 // One kernel for both sweeps.  Forward (FWD): y(row) = r(row) - sum_d L(row, d) y(dep d).
 // Backward: z(row) = D(row)^{-1} (y(row) - sum_d U(row, d) z(dep d)), out(row) = z(row) + x1(row).
 // src: r (forward, type ST) or y (backward); vec: the vector being solved (y or z).
-template <int B, typename T, typename ST, typename XT, bool FWD, int NS>
+// Pipeline with slack S: at iteration l the block loads rows/codes of level l + 2S, values of
+// level l + S (from the rows/codes loaded S iterations earlier) and stages the factor blocks of
+// level l + S into shared-memory slot (l + S) % (S + 1); every load has S levels of work to arrive.
+template <int B, typename T, typename ST, typename XT, bool FWD, int S>
 __global__ void __launch_bounds__(256) k_ilu_cw(int32_t nchunks, int32_t n, int D, int W, int maxw, int maxlev,
                                                 unsigned *ticket, const int32_t *__restrict__ clev,
                                                 const int32_t *__restrict__ lptr, const int32_t *__restrict__ prow,
@@ -483,7 +488,7 @@ __global__ void __launch_bounds__(256) k_ilu_cw(int32_t nchunks, int32_t n, int 
                                                 const ST *__restrict__ src, T *vec, double *__restrict__ out, int ps,
                                                 int ts, const XT *__restrict__ dp, const XT *__restrict__ dT,
                                                 KState *ks, const double *never, int sleep_ns) {
-    constexpr int BB = B * B;
+    constexpr int BB = B * B, NS = S + 1, QA = 2 * S + 1, QB = S + 1;
     const int SW = FWD ? D * BB : D * BB + BB;
     extern __shared__ __align__(16) unsigned char cw_smem[];
     T *ring = reinterpret_cast<T *>(cw_smem);
@@ -501,34 +506,38 @@ __global__ void __launch_bounds__(256) k_ilu_cw(int32_t nchunks, int32_t n, int 
         for (int q = tid; q <= nl; q += blockDim.x) lv[q] = __ldg(lptr + L0 + q);
         __syncthreads();
         if (FWD && never && ch == 0 && tid == 0) (void)wait_value(never, ks);   // failure injection
-        // prologue: rows/codes of levels 0 and 1, values of level 0, blocks of levels 0 .. NS-2
-        CwA<B, T> a0, a1, a2;
-        CwB<B, T> b0, b1;
-        a0.act = a1.act = a2.act = false;
-        cw_loadA<B, T>(a0, 0, tid, n, D, lv, prow, code);
-        if (nl > 1) cw_loadA<B, T>(a1, 1, tid, n, D, lv, prow, code);
-        cw_loadB<B, T, ST>(b0, a0, src, vec);
-        for (int k = 0; k < NS - 1; ++k) {
+        CwA<B, T> aq[QA];
+        CwB<B, T> bq[QB];
+#pragma unroll
+        for (int k = 0; k < QA; ++k) aq[k].act = false;
+        // prologue: rows/codes of levels 0 .. 2S-1, values and blocks of levels 0 .. S-1
+#pragma unroll
+        for (int k = 0; k < 2 * S; ++k)
+            if (k < nl) cw_loadA<B, T>(aq[k], k, tid, n, D, lv, prow, code);
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
             if (k < nl) {
+                cw_loadB<B, T, ST>(bq[k], aq[k], src, vec);
                 const int32_t p = lv[k] + tid;
                 if (p < lv[k + 1]) cw_stage(stage + ((int64_t)(k % NS) * blockDim.x + tid) * SW, p, n, SW, val);
             }
             cp_async_commit();
         }
         for (int l = 0; l < nl; ++l) {
-            // loads for later levels
-            a2.act = false;
-            if (l + 2 < nl) cw_loadA<B, T>(a2, l + 2, tid, n, D, lv, prow, code);
+            aq[2 * S].act = false;
+            if (l + 2 * S < nl) cw_loadA<B, T>(aq[2 * S], l + 2 * S, tid, n, D, lv, prow, code);
             {
-                const int k = l + NS - 1;
+                const int k = l + S;
                 if (k < nl) {
                     const int32_t p = lv[k] + tid;
                     if (p < lv[k + 1]) cw_stage(stage + ((int64_t)(k % NS) * blockDim.x + tid) * SW, p, n, SW, val);
+                    cw_loadB<B, T, ST>(bq[S], aq[S], src, vec);
                 }
                 cp_async_commit();
             }
-            if (l + 1 < nl) cw_loadB<B, T, ST>(b1, a1, src, vec);
             cp_async_wait_ns<NS>();   // the blocks of level l have arrived
+            const CwA<B, T> &a0 = aq[0];
+            const CwB<B, T> &b0 = bq[0];
             if (a0.act) {
                 const T *a = stage + ((int64_t)(l % NS) * blockDim.x + tid) * SW;
                 T s[B];
@@ -573,9 +582,10 @@ __global__ void __launch_bounds__(256) k_ilu_cw(int32_t nchunks, int32_t n, int 
                 }
             }
             __syncthreads();
-            a0 = a1;
-            a1 = a2;
-            b0 = b1;
+#pragma unroll
+            for (int k = 0; k < QA - 1; ++k) aq[k] = aq[k + 1];
+#pragma unroll
+            for (int k = 0; k < QB - 1; ++k) bq[k] = bq[k + 1];
         }
         cp_async_wait_0();
     }
@@ -975,17 +985,38 @@ struct CwHost {
     std::vector<int32_t> clev, lptr, prow, code, kidx;
 };
 
+// run f(c) for c in [0, count) on up to 16 host threads
+template <typename F>
+static void parallel_chunks(int32_t count, F &&f) {
+    const int nt = (int)std::max(1u, std::min<unsigned>(16u, std::min<unsigned>(std::thread::hardware_concurrency(),
+                                                                                (unsigned)count)));
+    if (nt <= 1) {
+        for (int32_t c = 0; c < count; ++c) f(c);
+        return;
+    }
+    std::atomic<int32_t> next(0);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t)
+        pool.emplace_back([&]() {
+            for (int32_t c = next++; c < count; c = next++) f(c);
+        });
+    for (auto &th : pool) th.join();
+}
+
 static CwHost cw_build(int32_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
                        const std::vector<int32_t> &dg, int32_t K, bool forward) {
     CwHost h;
     const int32_t nch = (n + K - 1) / K;
     h.nchunks = nch;
     std::vector<int32_t> lev(n, 0), idx(n, 0);
-    auto is_dep = [&](int32_t i, int32_t j) { return forward ? j < i : j > i; };
-    int32_t maxdist = 0, D = 0;
-    for (int32_t t = 0; t < nch; ++t) {
-        const int32_t c = forward ? t : nch - 1 - t;
+    auto is_dep = [forward](int32_t i, int32_t j) { return forward ? j < i : j > i; };
+    auto chunk_of_t = [&](int32_t t) { return forward ? t : nch - 1 - t; };   // t: processing order
+    std::vector<int32_t> nl(nch, 0), md(nch, 0), dd(nch, 0), mw(nch, 0);
+    // 1. local levels (dependencies inside the chunk), largest in-chunk distance, dependency count
+    parallel_chunks(nch, [&](int32_t t) {
+        const int32_t c = chunk_of_t(t);
         const int32_t r0 = c * K, r1 = std::min<int32_t>(n, r0 + K);
+        int32_t maxl = 0, D = 0;
         for (int32_t u = 0; u < r1 - r0; ++u) {
             const int32_t i = forward ? r0 + u : r1 - 1 - u;
             int32_t l = 0, nd = 0;
@@ -996,65 +1027,79 @@ static CwHost cw_build(int32_t n, const std::vector<int32_t> &rp, const std::vec
                 if (j >= r0 && j < r1) l = std::max(l, lev[j] + 1);
             }
             lev[i] = l;
+            maxl = std::max(maxl, l);
             D = std::max(D, nd);
         }
+        int32_t maxdist = 0;
         for (int32_t i = r0; i < r1; ++i)
             for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
                 const int32_t j = ci[k];
                 if (is_dep(i, j) && j >= r0 && j < r1) maxdist = std::max(maxdist, lev[i] - lev[j]);
             }
-    }
-    h.D = D;
-    h.W = std::min(maxdist, 3) + 1;
-    // positions: per chunk, a stable counting sort by local level (dependency order inside a level)
-    h.prow.resize(n);
-    h.clev.assign(nch + 1, 0);
-    std::vector<int32_t> cnt;
-    int32_t pos = 0;
+        nl[t] = maxl + 1;
+        md[t] = maxdist;
+        dd[t] = D;
+    });
+    int32_t maxdist = 0;
     for (int32_t t = 0; t < nch; ++t) {
-        const int32_t c = forward ? t : nch - 1 - t;
+        maxdist = std::max(maxdist, md[t]);
+        h.D = std::max(h.D, dd[t]);
+        h.max_chunk_levels = std::max(h.max_chunk_levels, nl[t]);
+    }
+    h.W = std::min(maxdist, 3) + 1;
+    // 2. offsets of every chunk's positions and levels (processing order)
+    std::vector<int32_t> pos0(nch + 1, 0);
+    h.clev.assign(nch + 1, 0);
+    for (int32_t t = 0; t < nch; ++t) {
+        const int32_t c = chunk_of_t(t);
+        pos0[t + 1] = pos0[t] + (std::min<int32_t>(n, (c + 1) * K) - c * K);
+        h.clev[t + 1] = h.clev[t] + nl[t];
+    }
+    h.nlev_total = h.clev[nch];
+    h.lptr.assign((size_t)h.nlev_total + 1, n);
+    h.prow.resize(n);
+    // 3. per chunk, a stable counting sort by local level (dependency order inside a level)
+    parallel_chunks(nch, [&](int32_t t) {
+        const int32_t c = chunk_of_t(t);
         const int32_t r0 = c * K, r1 = std::min<int32_t>(n, r0 + K);
-        int32_t nl = 0;
-        for (int32_t i = r0; i < r1; ++i) nl = std::max(nl, lev[i] + 1);
-        cnt.assign(nl + 1, 0);
+        std::vector<int32_t> cnt(nl[t] + 1, 0);
         for (int32_t i = r0; i < r1; ++i) ++cnt[lev[i] + 1];
-        for (int32_t l = 0; l < nl; ++l) cnt[l + 1] += cnt[l];
-        h.clev[t] = (int32_t)h.lptr.size();
-        for (int32_t l = 0; l < nl; ++l) {
-            h.lptr.push_back(pos + cnt[l]);
-            h.maxw = std::max(h.maxw, cnt[l + 1] - cnt[l]);
+        for (int32_t l = 0; l < nl[t]; ++l) cnt[l + 1] += cnt[l];
+        int32_t w = 0;
+        for (int32_t l = 0; l < nl[t]; ++l) {
+            h.lptr[h.clev[t] + l] = pos0[t] + cnt[l];
+            w = std::max(w, cnt[l + 1] - cnt[l]);
         }
-        h.max_chunk_levels = std::max(h.max_chunk_levels, nl);
+        mw[t] = w;
         std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
         for (int32_t u = 0; u < r1 - r0; ++u) {
             const int32_t i = forward ? r0 + u : r1 - 1 - u;
             const int32_t q = fill[lev[i]]++;
-            h.prow[pos + q] = i;
+            h.prow[pos0[t] + q] = i;
             idx[i] = q - cnt[lev[i]];
         }
-        pos += r1 - r0;
-    }
-    h.clev[nch] = (int32_t)h.lptr.size();
-    h.nlev_total = (int32_t)h.lptr.size();
-    h.lptr.push_back(n);
-    // dependency codes and factor block indices
+    });
+    for (int32_t t = 0; t < nch; ++t) h.maxw = std::max(h.maxw, mw[t]);
+    // 4. dependency codes and factor block indices
     const int nslots = h.D + (forward ? 0 : 1);
     h.code.assign((size_t)std::max(h.D, 1) * n, kCwNone);
     h.kidx.assign((size_t)std::max(nslots, 1) * n, -1);
-    for (int32_t p = 0; p < n; ++p) {
-        const int32_t i = h.prow[p];
-        const int32_t c = i / K, r0 = c * K, r1 = std::min<int32_t>(n, r0 + K);
-        int d = 0;
-        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
-            const int32_t j = ci[k];
-            if (!is_dep(i, j)) continue;
-            const bool ring = j >= r0 && j < r1 && lev[i] - lev[j] <= h.W - 1;
-            h.code[(size_t)d * n + p] = ring ? (lev[j] % h.W) * h.maxw + idx[j] : -(j + 1);
-            h.kidx[(size_t)d * n + p] = k;
-            ++d;
+    parallel_chunks(nch, [&](int32_t t) {
+        for (int32_t p = pos0[t]; p < pos0[t + 1]; ++p) {
+            const int32_t i = h.prow[p];
+            const int32_t c = i / K, r0 = c * K, r1 = std::min<int32_t>(n, r0 + K);
+            int d = 0;
+            for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+                const int32_t j = ci[k];
+                if (!is_dep(i, j)) continue;
+                const bool ring = j >= r0 && j < r1 && lev[i] - lev[j] <= h.W - 1;
+                h.code[(size_t)d * n + p] = ring ? (lev[j] % h.W) * h.maxw + idx[j] : -(j + 1);
+                h.kidx[(size_t)d * n + p] = k;
+                ++d;
+            }
+            if (!forward) h.kidx[(size_t)h.D * n + p] = dg[i];
         }
-        if (!forward) h.kidx[(size_t)h.D * n + p] = dg[i];
-    }
+    });
     return h;
 }
 
@@ -1078,7 +1123,8 @@ static cptr_status cw_setup(Ctx *c) {
                (size_t)(h.max_chunk_levels + 1) * 4;
     };
     const size_t kLimit = 200 * 1024;
-    auto pick_ns = [&](const CwHost &h, int extra) { return smem(h, extra, 3) <= kLimit ? 3 : 2; };
+    // stage slots: 4 (slack of three levels) when they fit, else 2 (slack of one level)
+    auto pick_ns = [&](const CwHost &h, int extra) { return smem(h, extra, 4) <= kLimit ? 4 : 2; };
     const int ns_f = pick_ns(hf, 0), ns_b = pick_ns(hb, BB);
     if (hf.D > kCwMaxD || hb.D > kCwMaxD || threads > kCwMaxThreads || smem(hf, 0, ns_f) > kLimit ||
         smem(hb, BB, ns_b) > kLimit)
@@ -1334,8 +1380,8 @@ static void cw_launch(const Ctx *c, const CwTables &t, const ST *src, T *vec, do
                                                      c->ts, dp, dT, c->ks, never, c->sf_sleep),
          note_launch());
     };
-    if (t.ns == 3) go(k_ilu_cw<B, T, ST, XT, FWD, 3>);
-    else go(k_ilu_cw<B, T, ST, XT, FWD, 2>);
+    if (t.ns == 4) go(k_ilu_cw<B, T, ST, XT, FWD, 3>);
+    else go(k_ilu_cw<B, T, ST, XT, FWD, 1>);
 }
 
 // z = (LU)^{-1} r + x1, where x1 carries dp in slot ps and dT in slot ts (either may be null):
