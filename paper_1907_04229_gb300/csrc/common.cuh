@@ -224,6 +224,7 @@ void apply_precond(const Ctx *c, const double *v, double *z);
 struct CwTables {
     int32_t nchunks = 0, D = 0, W = 1, maxw = 0, threads = 0, smem = 0, ns = 2, maxlev = 0;
     int32_t *clev = nullptr, *lptr = nullptr, *prow = nullptr, *code = nullptr;
+    int32_t *started = nullptr;   // per chunk: it has finished its first levels (reset per sweep)
     void *val = nullptr;   // factor blocks (and inverted pivot blocks), FP64 or FP32
 };
 

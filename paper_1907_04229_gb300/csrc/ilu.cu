@@ -368,6 +368,7 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_sf(int32_t n, unsigned *
 // Each value is computed exactly as in the level-set sweeps above (same operations, same order).
 constexpr int kCwMaxD = 4;
 constexpr int kCwMaxThreads = 256;   // the widest level a chunk may have
+constexpr int kCwLead = 4;           // levels a chunk runs ahead of the next before that one starts
 constexpr int32_t kCwNone = INT32_MIN;
 
 __device__ __forceinline__ void cp_async_elem(double *dst, const double *src) {
@@ -386,59 +387,31 @@ __device__ __forceinline__ void cp_async_wait_ns() {   // all but the NS - 1 mos
     asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1) : "memory");
 }
 
-// Software pipeline of one chunk.  Level l is computed at iteration l; at that iteration the
-// block also loads the rows and dependency codes of level l + 2 (position-indexed), the
-// right-hand sides and outside-dependency values of level l + 1 (indexed by the rows and codes
-// loaded one iteration earlier), and stages by cp.async the factor blocks of level l + NS - 1
-// into shared-memory slot (l + NS - 1) % NS.  Every global load therefore has one level of work
-// to arrive, and no load waits on another inside a level.  The chunk's level pointers are copied
-// to shared memory when the chunk starts.
-template <int B, typename T>
-struct CwA {          // position-indexed part of a level's row
-    bool act;
-    int32_t row;
-    int32_t cd[kCwMaxD];
-};
-template <int B, typename T>
-struct CwB {          // row-indexed part
-    T rhs[B];
-    T gv[kCwMaxD][B];
-};
-
-template <int B, typename T>
-__device__ __forceinline__ void cw_loadA(CwA<B, T> &a, int lp, int tid, int32_t n, int D, const int32_t *lv,
-                                         const int32_t *prow, const int32_t *code) {
-    const int32_t p = lv[lp] + tid;
-    a.act = p < lv[lp + 1];
-    if (!a.act) return;
-    a.row = __ldg(prow + p);
-#pragma unroll
-    for (int d = 0; d < kCwMaxD; ++d) a.cd[d] = d < D ? __ldg(code + (int64_t)d * n + p) : kCwNone;
+// Software pipeline of one chunk, all through shared memory (no register copies of loads in
+// flight).  Group g_l, committed at iteration l, copies by cp.async: the row index and dependency
+// codes of level l + 2S (position-indexed), the factor blocks of level l + S (position-indexed),
+// and the right-hand side and outside-dependency values of level l + S (addresses from the row
+// and codes of level l + S, which arrived with g_{l-S}).  Iteration l first waits for g_{l-S}
+// (at most S - 1 newer groups pending), so every copy has S levels of work to arrive.  Values of
+// outside dependencies that were still unwritten when copied hold the sentinel and are polled
+// from global memory when used.
+// 16 bytes through L2 only (values another block may have just written must not come from L1)
+__device__ __forceinline__ void cp_async_cg16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_i32(int32_t *dst, const int32_t *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+template <int S>
+__device__ __forceinline__ void cp_async_wait_slack() {   // all but the S - 1 most recent groups
+    asm volatile("cp.async.wait_group %0;" ::"n"(S - 1) : "memory");
 }
 
-template <int B, typename T, typename ST>
-__device__ __forceinline__ void cw_loadB(CwB<B, T> &b, const CwA<B, T> &a, const ST *src, const T *vec) {
-    if (!a.act) return;
-#pragma unroll
-    for (int q = 0; q < B; ++q) b.rhs[q] = (T)src[(int64_t)a.row * B + q];
-#pragma unroll
-    for (int d = 0; d < kCwMaxD; ++d)
-        if (a.cd[d] != kCwNone && a.cd[d] < 0) {
-            const int64_t j = -(int64_t)a.cd[d] - 1;
-#pragma unroll
-            for (int q = 0; q < B; ++q) b.gv[d][q] = load_relaxed(vec + j * B + q);
-        }
-}
-
-// stage the SW factor values of position p (planes e * n + p) into dst
-template <typename T>
-__device__ __forceinline__ void cw_stage(T *dst, int32_t p, int32_t n, int nvals, const T *val) {
-    for (int e = 0; e < nvals; ++e) cp_async_elem(dst + e, val + (int64_t)e * n + p);
-}
-
-// the value of dependency d: from the ring, or the early load (polled until written)
+// the value of dependency d: from the ring, or the staged copy (polled until written)
 template <int B, typename T>
-__device__ __forceinline__ void cw_dep(int32_t cd, const T *gv0, const T *ring, const T *vec, T *v, KState *ks,
+__device__ __forceinline__ void cw_dep(int32_t cd, const T *staged, const T *ring, const T *vec, T *v, KState *ks,
                                        int sleep_ns) {
     if (cd >= 0) {
 #pragma unroll
@@ -449,7 +422,7 @@ __device__ __forceinline__ void cw_dep(int32_t cd, const T *gv0, const T *ring, 
     bool pending = false;
 #pragma unroll
     for (int q = 0; q < B; ++q) {
-        v[q] = gv0[q];
+        v[q] = staged[q];
         pending |= is_sentinel(v[q]);
     }
     if (!pending) return;
@@ -474,12 +447,37 @@ __device__ __forceinline__ void cw_dep(int32_t cd, const T *gv0, const T *ring, 
     }
 }
 
+// shared-memory layout of the pipeline (per block), in this order: ring [W][maxw][B] (T);
+// blocks [S+1][threads][SW] (T); values [S+1][threads][D][B] (T); rhs [S+1][threads][B] (ST);
+// rows [2S+1][threads] and codes [2S+1][D][threads] (int32); level pointers [maxlev+1] (int32)
+// every region starts on a 16-byte boundary (the host computes the same sizes: cw_smem_bytes)
+__host__ __device__ inline size_t cw_align16(size_t x) { return (x + 15) & ~(size_t)15; }
+template <int B, typename T, typename ST>
+struct CwSmem {
+    T *ring, *blk, *gv;
+    ST *rhs;
+    int32_t *row, *cd, *lv;
+    __device__ CwSmem(unsigned char *base, int W, int maxw, int S, int nthr, int SW, int D) {
+        size_t o = 0;
+        ring = reinterpret_cast<T *>(base + o);
+        o += cw_align16(sizeof(T) * (size_t)W * maxw * B);
+        blk = reinterpret_cast<T *>(base + o);
+        o += cw_align16(sizeof(T) * (size_t)(S + 1) * nthr * SW);
+        gv = reinterpret_cast<T *>(base + o);
+        o += cw_align16((size_t)32 * (S + 1) * nthr * D);
+        rhs = reinterpret_cast<ST *>(base + o);
+        o += cw_align16(sizeof(ST) * (size_t)(S + 1) * nthr * B);
+        row = reinterpret_cast<int32_t *>(base + o);
+        o += cw_align16(4 * (size_t)(2 * S + 1) * nthr);
+        cd = reinterpret_cast<int32_t *>(base + o);
+        o += cw_align16(4 * (size_t)(2 * S + 1) * D * nthr);
+        lv = reinterpret_cast<int32_t *>(base + o);
+    }
+};
+
 // One kernel for both sweeps.  Forward (FWD): y(row) = r(row) - sum_d L(row, d) y(dep d).
 // Backward: z(row) = D(row)^{-1} (y(row) - sum_d U(row, d) z(dep d)), out(row) = z(row) + x1(row).
 // src: r (forward, type ST) or y (backward); vec: the vector being solved (y or z).
-// Pipeline with slack S: at iteration l the block loads rows/codes of level l + 2S, values of
-// level l + S (from the rows/codes loaded S iterations earlier) and stages the factor blocks of
-// level l + S into shared-memory slot (l + S) % (S + 1); every load has S levels of work to arrive.
 template <int B, typename T, typename ST, typename XT, bool FWD, int S>
 __global__ void __launch_bounds__(256) k_ilu_cw(int32_t nchunks, int32_t n, int D, int W, int maxw, int maxlev,
                                                 unsigned *ticket, const int32_t *__restrict__ clev,
@@ -487,15 +485,14 @@ __global__ void __launch_bounds__(256) k_ilu_cw(int32_t nchunks, int32_t n, int 
                                                 const int32_t *__restrict__ code, const T *__restrict__ val,
                                                 const ST *__restrict__ src, T *vec, double *__restrict__ out, int ps,
                                                 int ts, const XT *__restrict__ dp, const XT *__restrict__ dT,
-                                                KState *ks, const double *never, int sleep_ns) {
-    constexpr int BB = B * B, NS = S + 1, QA = 2 * S + 1, QB = S + 1;
+                                                KState *ks, const double *never, int sleep_ns, int32_t *started,
+                                                int lead) {
+    constexpr int BB = B * B, NA = 2 * S + 1, NB = S + 1;
     const int SW = FWD ? D * BB : D * BB + BB;
+    const int nthr = blockDim.x, tid = threadIdx.x;
     extern __shared__ __align__(16) unsigned char cw_smem[];
-    T *ring = reinterpret_cast<T *>(cw_smem);
-    T *stage = ring + (int64_t)W * maxw * B;
-    int32_t *lv = reinterpret_cast<int32_t *>(stage + (int64_t)NS * blockDim.x * SW);
+    CwSmem<B, T, ST> sm(cw_smem, W, maxw, S, nthr, SW, D);
     __shared__ unsigned chunk_s;
-    const int tid = threadIdx.x;
     for (;;) {
         __syncthreads();
         if (tid == 0) chunk_s = atomicAdd(ticket + (FWD ? 0 : 1), 1u);
@@ -503,51 +500,82 @@ __global__ void __launch_bounds__(256) k_ilu_cw(int32_t nchunks, int32_t n, int 
         const unsigned ch = chunk_s;
         if (ch >= (unsigned)nchunks) return;
         const int L0 = __ldg(clev + ch), nl = __ldg(clev + ch + 1) - L0;
-        for (int q = tid; q <= nl; q += blockDim.x) lv[q] = __ldg(lptr + L0 + q);
-        __syncthreads();
+        for (int q = tid; q <= nl; q += nthr) sm.lv[q] = __ldg(lptr + L0 + q);
         if (FWD && never && ch == 0 && tid == 0) (void)wait_value(never, ks);   // failure injection
-        CwA<B, T> aq[QA];
-        CwB<B, T> bq[QB];
-#pragma unroll
-        for (int k = 0; k < QA; ++k) aq[k].act = false;
-        // prologue: rows/codes of levels 0 .. 2S-1, values and blocks of levels 0 .. S-1
-#pragma unroll
-        for (int k = 0; k < 2 * S; ++k)
-            if (k < nl) cw_loadA<B, T>(aq[k], k, tid, n, D, lv, prow, code);
-#pragma unroll
-        for (int k = 0; k < S; ++k) {
-            if (k < nl) {
-                cw_loadB<B, T, ST>(bq[k], aq[k], src, vec);
-                const int32_t p = lv[k] + tid;
-                if (p < lv[k + 1]) cw_stage(stage + ((int64_t)(k % NS) * blockDim.x + tid) * SW, p, n, SW, val);
+        if (ch > 0 && tid == 0) {   // the previous chunk has finished its first `lead` levels
+            const unsigned long long t0 = gtimer();
+            for (;;) {
+                int32_t f;
+                asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(started + ch - 1) : "memory");
+                if (f) break;
+                if (gtimer() - t0 > kWaitNs) { atomicExch(&ks->wait_err, 1); break; }
+                __nanosleep(sleep_ns);
             }
+        }
+        __syncthreads();
+        const int lead_level = min(lead, nl) - 1;
+        // copies of level m into its slots: A part (row, codes), blocks, B part (rhs, values)
+        auto copyA = [&](int m) {
+            const int32_t p = sm.lv[m] + tid;
+            if (p >= sm.lv[m + 1]) return;
+            const int sa = m % NA;
+            cp_async_i32(sm.row + sa * nthr + tid, prow + p);
+            for (int d = 0; d < D; ++d) cp_async_i32(sm.cd + ((int64_t)sa * D + d) * nthr + tid, code + (int64_t)d * n + p);
+        };
+        auto copyB = [&](int m) {   // needs the A part of level m in shared memory
+            const int32_t p = sm.lv[m] + tid;
+            if (p >= sm.lv[m + 1]) return;
+            const int sa = m % NA, sb = m % NB;
+            const int32_t row = sm.row[sa * nthr + tid];
+            for (int e = 0; e < SW; ++e)
+                cp_async_elem(sm.blk + ((int64_t)sb * nthr + tid) * SW + e, val + (int64_t)e * n + p);
+            for (int q = 0; q < B; ++q)
+                cp_async_elem(sm.rhs + ((int64_t)sb * nthr + tid) * B + q, src + (int64_t)row * B + q);
+            for (int d = 0; d < D; ++d) {
+                const int32_t cd = sm.cd[((int64_t)sa * D + d) * nthr + tid];
+                if (cd != kCwNone && cd < 0) {
+                    const int64_t j = -(int64_t)cd - 1;
+                    const uintptr_t at = reinterpret_cast<uintptr_t>(vec + j * B) & ~(uintptr_t)15;
+                    unsigned char *dst = reinterpret_cast<unsigned char *>(sm.gv) + (((int64_t)sb * nthr + tid) * D + d) * 32;
+                    cp_async_cg16(dst, reinterpret_cast<const void *>(at));
+                    cp_async_cg16(dst + 16, reinterpret_cast<const void *>(at + 16));
+                }
+            }
+        };
+        // prologue: A of levels 0 .. 2S-1 (S groups of two levels), then B of levels 0 .. S-1
+        for (int k = 0; k < S; ++k) {
+            if (2 * k < nl) copyA(2 * k);
+            if (2 * k + 1 < nl) copyA(2 * k + 1);
+            cp_async_commit();
+        }
+        cp_async_wait_0();
+        for (int k = 0; k < S; ++k) {
+            if (k < nl) copyB(k);
             cp_async_commit();
         }
         for (int l = 0; l < nl; ++l) {
-            aq[2 * S].act = false;
-            if (l + 2 * S < nl) cw_loadA<B, T>(aq[2 * S], l + 2 * S, tid, n, D, lv, prow, code);
-            {
-                const int k = l + S;
-                if (k < nl) {
-                    const int32_t p = lv[k] + tid;
-                    if (p < lv[k + 1]) cw_stage(stage + ((int64_t)(k % NS) * blockDim.x + tid) * SW, p, n, SW, val);
-                    cw_loadB<B, T, ST>(bq[S], aq[S], src, vec);
-                }
-                cp_async_commit();
-            }
-            cp_async_wait_ns<NS>();   // the blocks of level l have arrived
-            const CwA<B, T> &a0 = aq[0];
-            const CwB<B, T> &b0 = bq[0];
-            if (a0.act) {
-                const T *a = stage + ((int64_t)(l % NS) * blockDim.x + tid) * SW;
+            cp_async_wait_slack<S>();            // g_{l-S} (or the prologue group of level l) is complete
+            if (l + 2 * S < nl) copyA(l + 2 * S);
+            if (l + S < nl) copyB(l + S);        // its A part arrived S iterations ago
+            cp_async_commit();
+            const int32_t p = sm.lv[l] + tid;
+            if (p < sm.lv[l + 1]) {
+                const int sa = l % NA, sb = l % NB;
+                const int32_t row = sm.row[sa * nthr + tid];
+                const T *a = sm.blk + ((int64_t)sb * nthr + tid) * SW;
+                const ST *rh = sm.rhs + ((int64_t)sb * nthr + tid) * B;
                 T s[B];
 #pragma unroll
-                for (int q = 0; q < B; ++q) s[q] = b0.rhs[q];
-#pragma unroll
-                for (int d = 0; d < kCwMaxD; ++d) {
-                    if (a0.cd[d] == kCwNone) continue;
+                for (int q = 0; q < B; ++q) s[q] = (T)rh[q];
+                for (int d = 0; d < D; ++d) {
+                    const int32_t cd = sm.cd[((int64_t)sa * D + d) * nthr + tid];
+                    if (cd == kCwNone) continue;
                     T v[B];
-                    cw_dep<B, T>(a0.cd[d], b0.gv[d], ring, vec, v, ks, sleep_ns);
+                    const T *win = reinterpret_cast<const T *>(reinterpret_cast<const unsigned char *>(sm.gv) +
+                                                               (((int64_t)sb * nthr + tid) * D + d) * 32);
+                    const int64_t jj = cd < 0 && cd != kCwNone ? -(int64_t)cd - 1 : 0;
+                    const int skew = (int)((reinterpret_cast<uintptr_t>(vec + jj * B) & 15) / sizeof(T));
+                    cw_dep<B, T>(cd, win + skew, sm.ring, vec, v, ks, sleep_ns);
                     const T *m = a + d * BB;
 #pragma unroll
                     for (int rr = 0; rr < B; ++rr)
@@ -568,24 +596,22 @@ __global__ void __launch_bounds__(256) k_ilu_cw(int32_t nchunks, int32_t n, int 
                         res[rr] = acc;
                     }
                 }
-                T *slot = ring + ((int64_t)(l % W) * maxw + tid) * B;
+                T *slot = sm.ring + ((int64_t)(l % W) * maxw + tid) * B;
 #pragma unroll
                 for (int q = 0; q < B; ++q) {
                     slot[q] = res[q];
-                    store_relaxed(vec + (int64_t)a0.row * B + q, res[q]);
+                    store_relaxed(vec + (int64_t)row * B + q, res[q]);
                     if (!FWD) {
                         double add = 0.0;
-                        if (dp && q == ps) add = (double)dp[a0.row];
-                        if (dT && q == ts) add = (double)dT[a0.row];
-                        out[(int64_t)a0.row * B + q] = (double)res[q] + add;
+                        if (dp && q == ps) add = (double)dp[row];
+                        if (dT && q == ts) add = (double)dT[row];
+                        out[(int64_t)row * B + q] = (double)res[q] + add;
                     }
                 }
             }
             __syncthreads();
-#pragma unroll
-            for (int k = 0; k < QA - 1; ++k) aq[k] = aq[k + 1];
-#pragma unroll
-            for (int k = 0; k < QB - 1; ++k) bq[k] = bq[k + 1];
+            if (l == lead_level && tid == 0)
+                asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(started + ch), "r"(1) : "memory");
         }
         cp_async_wait_0();
     }
@@ -988,8 +1014,8 @@ struct CwHost {
 // run f(c) for c in [0, count) on up to 16 host threads
 template <typename F>
 static void parallel_chunks(int32_t count, F &&f) {
-    const int nt = (int)std::max(1u, std::min<unsigned>(16u, std::min<unsigned>(std::thread::hardware_concurrency(),
-                                                                                (unsigned)count)));
+    const int nt = (int)std::max(1u, std::min<unsigned>(8u, std::min<unsigned>(std::thread::hardware_concurrency(),
+                                                                               (unsigned)count)));
     if (nt <= 1) {
         for (int32_t c = 0; c < count; ++c) f(c);
         return;
@@ -1012,11 +1038,13 @@ static CwHost cw_build(int32_t n, const std::vector<int32_t> &rp, const std::vec
     auto is_dep = [forward](int32_t i, int32_t j) { return forward ? j < i : j > i; };
     auto chunk_of_t = [&](int32_t t) { return forward ? t : nch - 1 - t; };   // t: processing order
     std::vector<int32_t> nl(nch, 0), md(nch, 0), dd(nch, 0), mw(nch, 0);
-    // 1. local levels (dependencies inside the chunk), largest in-chunk distance, dependency count
+    std::vector<std::vector<int32_t>> cnts(nch);
+    // 1. local levels (dependencies inside the chunk), level sizes, largest in-chunk distance,
+    //    dependency count
     parallel_chunks(nch, [&](int32_t t) {
         const int32_t c = chunk_of_t(t);
         const int32_t r0 = c * K, r1 = std::min<int32_t>(n, r0 + K);
-        int32_t maxl = 0, D = 0;
+        int32_t maxl = 0, D = 0, maxdist = 0;
         for (int32_t u = 0; u < r1 - r0; ++u) {
             const int32_t i = forward ? r0 + u : r1 - 1 - u;
             int32_t l = 0, nd = 0;
@@ -1030,21 +1058,29 @@ static CwHost cw_build(int32_t n, const std::vector<int32_t> &rp, const std::vec
             maxl = std::max(maxl, l);
             D = std::max(D, nd);
         }
-        int32_t maxdist = 0;
-        for (int32_t i = r0; i < r1; ++i)
+        std::vector<int32_t> &cnt = cnts[t];
+        cnt.assign(maxl + 2, 0);
+        for (int32_t i = r0; i < r1; ++i) {
+            ++cnt[lev[i] + 1];
             for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
                 const int32_t j = ci[k];
                 if (is_dep(i, j) && j >= r0 && j < r1) maxdist = std::max(maxdist, lev[i] - lev[j]);
             }
+        }
+        int32_t w = 0;
+        for (int32_t l = 0; l <= maxl; ++l) w = std::max(w, cnt[l + 1]);
+        for (int32_t l = 0; l <= maxl; ++l) cnt[l + 1] += cnt[l];
         nl[t] = maxl + 1;
         md[t] = maxdist;
         dd[t] = D;
+        mw[t] = w;
     });
     int32_t maxdist = 0;
     for (int32_t t = 0; t < nch; ++t) {
         maxdist = std::max(maxdist, md[t]);
         h.D = std::max(h.D, dd[t]);
         h.max_chunk_levels = std::max(h.max_chunk_levels, nl[t]);
+        h.maxw = std::max(h.maxw, mw[t]);
     }
     h.W = std::min(maxdist, 3) + 1;
     // 2. offsets of every chunk's positions and levels (processing order)
@@ -1058,19 +1094,15 @@ static CwHost cw_build(int32_t n, const std::vector<int32_t> &rp, const std::vec
     h.nlev_total = h.clev[nch];
     h.lptr.assign((size_t)h.nlev_total + 1, n);
     h.prow.resize(n);
-    // 3. per chunk, a stable counting sort by local level (dependency order inside a level)
+    const int nslots = h.D + (forward ? 0 : 1);
+    h.code.assign((size_t)std::max(h.D, 1) * n, kCwNone);
+    h.kidx.assign((size_t)std::max(nslots, 1) * n, -1);
+    // 3. per chunk: stable counting sort by local level, then dependency codes and block indices
     parallel_chunks(nch, [&](int32_t t) {
         const int32_t c = chunk_of_t(t);
         const int32_t r0 = c * K, r1 = std::min<int32_t>(n, r0 + K);
-        std::vector<int32_t> cnt(nl[t] + 1, 0);
-        for (int32_t i = r0; i < r1; ++i) ++cnt[lev[i] + 1];
-        for (int32_t l = 0; l < nl[t]; ++l) cnt[l + 1] += cnt[l];
-        int32_t w = 0;
-        for (int32_t l = 0; l < nl[t]; ++l) {
-            h.lptr[h.clev[t] + l] = pos0[t] + cnt[l];
-            w = std::max(w, cnt[l + 1] - cnt[l]);
-        }
-        mw[t] = w;
+        const std::vector<int32_t> &cnt = cnts[t];
+        for (int32_t l = 0; l < nl[t]; ++l) h.lptr[h.clev[t] + l] = pos0[t] + cnt[l];
         std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
         for (int32_t u = 0; u < r1 - r0; ++u) {
             const int32_t i = forward ? r0 + u : r1 - 1 - u;
@@ -1078,16 +1110,8 @@ static CwHost cw_build(int32_t n, const std::vector<int32_t> &rp, const std::vec
             h.prow[pos0[t] + q] = i;
             idx[i] = q - cnt[lev[i]];
         }
-    });
-    for (int32_t t = 0; t < nch; ++t) h.maxw = std::max(h.maxw, mw[t]);
-    // 4. dependency codes and factor block indices
-    const int nslots = h.D + (forward ? 0 : 1);
-    h.code.assign((size_t)std::max(h.D, 1) * n, kCwNone);
-    h.kidx.assign((size_t)std::max(nslots, 1) * n, -1);
-    parallel_chunks(nch, [&](int32_t t) {
         for (int32_t p = pos0[t]; p < pos0[t + 1]; ++p) {
             const int32_t i = h.prow[p];
-            const int32_t c = i / K, r0 = c * K, r1 = std::min<int32_t>(n, r0 + K);
             int d = 0;
             for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
                 const int32_t j = ci[k];
@@ -1118,17 +1142,23 @@ static cptr_status cw_setup(Ctx *c) {
     const size_t tsz = lo ? 4 : 8;
     const int maxw = std::max(hf.maxw, hb.maxw);
     const int threads = std::max(32, (maxw + 31) / 32 * 32);
-    auto smem = [&](const CwHost &h, int extra, int ns) {
-        return (size_t)h.W * h.maxw * B * tsz + (size_t)ns * threads * (h.D * BB + extra) * tsz +
+    const size_t rsz = 8;   // right-hand sides: FP64, or FP32 when the FP32 sweeps get FP32 input
+    auto smem = [&](const CwHost &h, int extra, int S) {
+        const size_t SW = (size_t)h.D * BB + extra;
+        return cw_align16(tsz * h.W * h.maxw * B) + cw_align16(tsz * (S + 1) * threads * SW) +
+               cw_align16((size_t)32 * (S + 1) * threads * h.D) + cw_align16(rsz * (S + 1) * threads * B) +
+               cw_align16(4 * (size_t)(2 * S + 1) * threads) + cw_align16(4 * (size_t)(2 * S + 1) * h.D * threads) +
                (size_t)(h.max_chunk_levels + 1) * 4;
     };
-    const size_t kLimit = 200 * 1024;
-    // stage slots: 4 (slack of three levels) when they fit, else 2 (slack of one level)
-    auto pick_ns = [&](const CwHost &h, int extra) { return smem(h, extra, 4) <= kLimit ? 4 : 2; };
-    const int ns_f = pick_ns(hf, 0), ns_b = pick_ns(hb, BB);
-    if (hf.D > kCwMaxD || hb.D > kCwMaxD || threads > kCwMaxThreads || smem(hf, 0, ns_f) > kLimit ||
-        smem(hb, BB, ns_b) > kLimit)
-        return CPTR_OK;
+    const size_t kLimit = 220 * 1024;
+    // pipeline slack: 3 levels when it fits, else 2, else 1
+    auto pick_s = [&](const CwHost &h, int extra) {
+        for (int S : {3, 2, 1})
+            if (smem(h, extra, S) <= kLimit) return S;
+        return 0;
+    };
+    const int s_f = pick_s(hf, 0), s_b = pick_s(hb, BB);
+    if (hf.D > kCwMaxD || hb.D > kCwMaxD || threads > kCwMaxThreads || s_f == 0 || s_b == 0) return CPTR_OK;
     cudaStream_t st = c->stream;
     auto up = [&](const std::vector<int32_t> &v, int32_t **dst) -> cptr_status {
         CPTR_TRY(dalloc_t(c, dst, std::max<size_t>(v.size(), 1)));
@@ -1146,13 +1176,14 @@ static cptr_status cw_setup(Ctx *c) {
         t.W = h.W;
         t.maxw = h.maxw;
         t.threads = threads;
-        t.ns = dir ? ns_b : ns_f;
+        t.ns = dir ? s_b : s_f;   // pipeline slack S
         t.maxlev = h.max_chunk_levels;
         t.smem = (int32_t)smem(h, dir ? BB : 0, t.ns);
         CPTR_TRY(up(h.clev, &t.clev));
         CPTR_TRY(up(h.lptr, &t.lptr));
         CPTR_TRY(up(h.prow, &t.prow));
         CPTR_TRY(up(h.code, &t.code));
+        CPTR_TRY(dalloc_t(c, &t.started, (size_t)std::max(h.nchunks, 1)));
         int32_t *kidx = nullptr;
         CPTR_TRY(up(h.kidx, &kidx));
         const int nslots = h.D + dir;
@@ -1171,7 +1202,7 @@ static cptr_status cw_setup(Ctx *c) {
 
 static void cw_free(Ctx *c) {
     for (CwTables *t : {&c->cw_f, &c->cw_b}) {
-        dfree(t->clev); dfree(t->lptr); dfree(t->prow); dfree(t->code); dfree(t->val);
+        dfree(t->clev); dfree(t->lptr); dfree(t->prow); dfree(t->code); dfree(t->val); dfree(t->started);
         *t = CwTables();
     }
     c->cw_ok = false;
@@ -1343,8 +1374,9 @@ cptr_status ilu_setup(Ctx *c) {
     CPTR_TRY(pack(kidx_f, ns_f, &c->sf_val_f));
     CPTR_TRY(pack(kidx_b, ns_b, &c->sf_val_b));
     CPTR_TRY(pack(kidx_d, (int64_t)nch * 32, &c->sf_dinv));
-    CPTR_TRY(dalloc(c, &c->sf_y, (size_t)n * c->b * (lo ? 4 : 8)));
-    CPTR_TRY(dalloc(c, &c->sf_z, (size_t)n * c->b * (lo ? 4 : 8)));
+    // (+64 bytes: the chunked sweeps read 32-byte windows around a row's values)
+    CPTR_TRY(dalloc(c, &c->sf_y, (size_t)n * c->b * (lo ? 4 : 8) + 64));
+    CPTR_TRY(dalloc(c, &c->sf_z, (size_t)n * c->b * (lo ? 4 : 8) + 64));
     CPTR_CUDA_TRY(c, cudaGetLastError());
     dfree(kidx_f); dfree(kidx_b); dfree(kidx_d); dfree(inv_f); dfree(inv_b);
     if (!mc && (c->o.ilu_sweep == 2 || (c->o.ilu_sweep == 0 && c->o.autotune))) CPTR_TRY(cw_setup(c));
@@ -1375,12 +1407,14 @@ static void cw_launch(const Ctx *c, const CwTables &t, const ST *src, T *vec, do
     const unsigned grid = (unsigned)std::min(t.nchunks, 152);
     auto go = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, t.smem);
+        cudaMemsetAsync(t.started, 0, sizeof(int32_t) * t.nchunks, c->stream);
         (kern<<<grid, t.threads, t.smem, c->stream>>>(t.nchunks, c->n, t.D, t.W, t.maxw, t.maxlev, c->sf_ticket, t.clev,
                                                      t.lptr, t.prow, t.code, (const T *)t.val, src, vec, out, c->ps,
-                                                     c->ts, dp, dT, c->ks, never, c->sf_sleep),
+                                                     c->ts, dp, dT, c->ks, never, c->sf_sleep, t.started, kCwLead),
          note_launch());
     };
-    if (t.ns == 4) go(k_ilu_cw<B, T, ST, XT, FWD, 3>);
+    if (t.ns == 3) go(k_ilu_cw<B, T, ST, XT, FWD, 3>);
+    else if (t.ns == 2) go(k_ilu_cw<B, T, ST, XT, FWD, 2>);
     else go(k_ilu_cw<B, T, ST, XT, FWD, 1>);
 }
 
