@@ -68,7 +68,6 @@ VARIANTS = {
     "cptr_mixed_multicolor_ilu": dict(precision="mixed", ilu_order="multicolor"),
     "cptr_fp64_autotuned": dict(autotune=1),
     "cptr_mixed_autotuned": dict(precision="mixed", autotune=1),
-    "cptr_mixed_chunked_ilu": dict(precision="mixed", ilu_sweep="chunked"),
 }
 
 

@@ -599,7 +599,11 @@ void amg_free(Hier &h) {
         L = Level{};
     }
     dfree(h.cinv);
+    dfree(h.ldev64);
+    dfree(h.ldev32);
     h.cinv = nullptr;
+    h.ldev64 = h.ldev32 = nullptr;
+    h.fuse_l0 = -1;
     h.nlev = 0;
     h.dense = 0;
 }
@@ -733,6 +737,117 @@ static void level_up(cudaStream_t s, const Level &L, const Level &C, const VT *A
     launch_post<VT, XT>(s, L, Av, LV::dinv(L), b, LV::t(L), x);                     // x = t + D^-1 (b - A t)
 }
 
+// ------------------------------------------------------------------------------------------------
+// Fused coarse levels.  Below a few thousand rows a level's kernels are too small to fill the GPU
+// and cost mostly their launch; one block of 1024 threads runs all of them instead, level after
+// level, with __syncthreads between the steps: the down path (pre-smoothing from zero fused with
+// the residual, restriction) of levels l0 .. lc-1 in one kernel, the coarsest solve as before,
+// then the up path (prolongation, post-smoothing) in a second kernel.  Same operations as the
+// level kernels (sums in row order).
+constexpr int kFuseRows = 300;
+constexpr int kFuseThreads = 1024;
+
+template <typename XT>
+__device__ __forceinline__ XT ldval(const void *v, int st, int64_t k) {
+    if (st == ST_F64) return (XT) static_cast<const double *>(v)[k];
+    if (st == ST_F32) return (XT) static_cast<const float *>(v)[k];
+    return (XT)__bfloat162float(static_cast<const bf16 *>(v)[k]);
+}
+
+template <typename XT>
+__global__ void __launch_bounds__(kFuseThreads) k_vc_fused_down(const LevelDev *__restrict__ L, int l0, int lc,
+                                                                const XT *b0) {
+    for (int l = l0; l < lc; ++l) {
+        const LevelDev &A = L[l];
+        const XT *b = l == l0 ? b0 : static_cast<const XT *>(A.b);
+        const XT *dinv = static_cast<const XT *>(A.dinv);
+        XT *t = static_cast<XT *>(A.t), *r = static_cast<XT *>(A.r);
+        for (int32_t i = threadIdx.x; i < A.n; i += blockDim.x) {   // t = D^-1 b, r = b - A t
+            XT acc = 0;
+            for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+                const int32_t j = A.ci[k];
+                acc = fma(ldval<XT>(A.v, A.st, k), dinv[j] * b[j], acc);
+            }
+            const XT bi = b[i];
+            t[i] = dinv[i] * bi;
+            r[i] = bi - acc;
+        }
+        __syncthreads();
+        const LevelDev &C = L[l + 1];
+        XT *bc = static_cast<XT *>(C.b);
+        for (int32_t i = threadIdx.x; i < C.n; i += blockDim.x) {   // b_c = P^T r
+            XT acc = 0;
+            for (int32_t k = A.PTrp[i]; k < A.PTrp[i + 1]; ++k) acc = fma(ldval<XT>(A.PTv, A.st, k), r[A.PTci[k]], acc);
+            bc[i] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename XT>
+__global__ void __launch_bounds__(kFuseThreads) k_vc_fused_up(const LevelDev *__restrict__ L, int l0, int lc,
+                                                              const XT *b0, XT *x0) {
+    for (int l = lc - 1; l >= l0; --l) {
+        const LevelDev &A = L[l];
+        const LevelDev &C = L[l + 1];
+        const XT *b = l == l0 ? b0 : static_cast<const XT *>(A.b);
+        XT *x = l == l0 ? x0 : static_cast<XT *>(A.x);
+        const XT *dinv = static_cast<const XT *>(A.dinv);
+        const XT *xc = static_cast<const XT *>(C.x);
+        XT *t = static_cast<XT *>(A.t);
+        for (int32_t i = threadIdx.x; i < A.n; i += blockDim.x) {   // t += P x_c
+            XT acc = 0;
+            for (int32_t k = A.Prp[i]; k < A.Prp[i + 1]; ++k) acc = fma(ldval<XT>(A.Pv, A.st, k), xc[A.Pci[k]], acc);
+            t[i] += acc;
+        }
+        __syncthreads();
+        for (int32_t i = threadIdx.x; i < A.n; i += blockDim.x) {   // x = t + D^-1 (b - A t)
+            XT acc = 0;
+            for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) acc = fma(ldval<XT>(A.v, A.st, k), t[A.ci[k]], acc);
+            x[i] = t[i] + dinv[i] * (b[i] - acc);
+        }
+        __syncthreads();
+    }
+}
+
+cptr_status amg_fuse_setup(Ctx *c, Hier &h) {
+    h.fuse_l0 = -1;
+    dfree(h.ldev64);
+    dfree(h.ldev32);
+    h.ldev64 = h.ldev32 = nullptr;
+    const int lc = h.nlev - 1;
+    int l0 = lc;
+    while (l0 > 0 && h.L[l0 - 1].A.n <= kFuseRows) --l0;
+    if (l0 >= lc || lc < 1) return CPTR_OK;   // nothing to fuse
+    const bool lo = c->o.precision == CPTR_PREC_MIXED;
+    std::vector<LevelDev> d64(h.nlev), d32(h.nlev);
+    for (int l = 0; l < h.nlev; ++l) {
+        const Level &L = h.L[l];
+        LevelDev a{};
+        a.n = L.A.n;
+        a.rp = L.A.rp; a.ci = L.A.ci;
+        a.Prp = L.P.rp; a.Pci = L.P.ci; a.PTrp = L.PT.rp; a.PTci = L.PT.ci;
+        LevelDev f = a;
+        a.st = ST_F64; a.v = L.A.v; a.Pv = L.P.v; a.PTv = L.PT.v; a.dinv = L.dinv;
+        a.b = L.b; a.x = L.x; a.t = L.t; a.r = L.r;
+        d64[l] = a;
+        if (lo) {
+            f.st = L.st; f.v = L.Av_lo; f.Pv = L.Pv_lo; f.PTv = L.PTv_lo; f.dinv = L.dinv32;
+            f.b = L.b32; f.x = L.x32; f.t = L.t32; f.r = L.r32;
+            d32[l] = f;
+        }
+    }
+    CPTR_TRY(dalloc_t(c, &h.ldev64, (size_t)h.nlev));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(h.ldev64, d64.data(), sizeof(LevelDev) * h.nlev, cudaMemcpyHostToDevice, c->stream));
+    if (lo) {
+        CPTR_TRY(dalloc_t(c, &h.ldev32, (size_t)h.nlev));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(h.ldev32, d32.data(), sizeof(LevelDev) * h.nlev, cudaMemcpyHostToDevice, c->stream));
+    }
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    h.fuse_l0 = l0;
+    return CPTR_OK;
+}
+
 template <typename XT>
 static void vcycle_level(const Ctx *c, const Hier &h, int l, const XT *b, XT *x) {
     using LV = LevelVecs<XT>;
@@ -749,6 +864,14 @@ static void vcycle_level(const Ctx *c, const Hier &h, int l, const XT *b, XT *x)
             else if (L.st == ST_BF16) launch_post<bf16, float>(s, L, (const bf16 *)L.Av_lo, L.dinv32, (const float *)b, L.t32, (float *)x);
             else launch_post<float, float>(s, L, (const float *)L.Av_lo, L.dinv32, (const float *)b, L.t32, (float *)x);
         }
+        return;
+    }
+    if (l == h.fuse_l0 && (lo ? h.ldev32 : h.ldev64)) {   // levels l .. nlev-2 fused
+        const LevelDev *ld = lo ? h.ldev32 : h.ldev64;
+        const int lc = h.nlev - 1;
+        (k_vc_fused_down<XT><<<1, kFuseThreads, 0, s>>>(ld, l, lc, b), note_launch());
+        vcycle_level<XT>(c, h, lc, LV::b(h.L[lc]), LV::x(h.L[lc]));
+        (k_vc_fused_up<XT><<<1, kFuseThreads, 0, s>>>(ld, l, lc, b, x), note_launch());
         return;
     }
     const Level &C = h.L[l + 1];

@@ -178,6 +178,8 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
         for (float **p : {&c->bp32, &c->bT32, &c->xp32, &c->dp32, &c->dT32, &c->t132}) CPTR_TRY(dalloc_t(c, p, (size_t)n));
         CPTR_TRY(dalloc_t(c, &c->b132, (size_t)n * b));
     }
+    if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_fuse_setup(c, c->hp));
+    if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) CPTR_TRY(amg_fuse_setup(c, c->hT));
     dfree(c->A);
     c->A = nullptr;
     setup_tick(c, SETUP_LAYOUT, &t2);

@@ -73,12 +73,23 @@ struct Level {
     float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr, *r32 = nullptr;
 };
 
+// a level as the fused coarse-level kernels see it (device array, one per hierarchy and cycle
+// precision): operators with their value storage, smoother diagonal and work vectors
+struct LevelDev {
+    int32_t n, st;
+    const int32_t *rp, *ci, *Prp, *Pci, *PTrp, *PTci;
+    const void *v, *Pv, *PTv, *dinv;
+    void *b, *x, *t, *r;
+};
+
 struct Hier {
     int nlev = 0;
     Level L[kMaxLevels];
     double *cinv = nullptr;  // coarsest level: dense inverse (row-major), if dense
     int dense = 0;
     double op_complexity = 0.0;
+    int fuse_l0 = -1;                 // levels fuse_l0 .. nlev-2 run in the fused coarse kernels
+    LevelDev *ldev64 = nullptr, *ldev32 = nullptr;   // device descriptors (FP64 / mixed cycle)
 };
 
 // Arnoldi/Givens state kept on the device (one per context)
@@ -187,6 +198,7 @@ void launch_sub(cudaStream_t s, int32_t n, const double *a, const double *b, dou
 
 // ---- amg.cu ------------------------------------------------------------------------------------
 cptr_status amg_autotune(Ctx *c, Hier &h);    // launch shapes of every level's kernels
+cptr_status amg_fuse_setup(Ctx *c, Hier &h);  // descriptors of the fused coarse levels
 cptr_status sell_autotune(Ctx *c);           // threads per block of the SELL SpMV
 cptr_status ilu_autotune(Ctx *c);            // grid and poll back-off of the ILU(0) sweeps
 cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, const double *v, int32_t n);
