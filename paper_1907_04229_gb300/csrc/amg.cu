@@ -383,6 +383,87 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(int32_t n, double *a, dou
     }
 }
 
+// The same inverse for matrices that fit in shared memory (n <= kGjSmemMax): in-place
+// Gauss-Jordan with partial pivoting by rows (the largest |a_ik|, i >= k, lowest index on ties),
+// the whole matrix held in shared memory; the row exchanges are undone at the end as column
+// exchanges in reverse order, so that the result is A^{-1}.
+constexpr int kGjSmemMax = 160;
+__global__ void __launch_bounds__(1024) k_gauss_jordan_smem(int32_t n, const double *a_in, double *inv,
+                                                            int32_t *singular) {
+    extern __shared__ double gj[];
+    double *a = gj;                       // n x n
+    double *fac = gj + (int64_t)n * n;    // n
+    int32_t *perm = reinterpret_cast<int32_t *>(fac + n);
+    __shared__ double red_v[32];
+    __shared__ int32_t red_i[32];
+    __shared__ int32_t piv_s;
+    __shared__ double dk_s;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int32_t nn = n * n;
+    for (int32_t e = tid; e < nn; e += nt) a[e] = a_in[e];
+    __syncthreads();
+    for (int32_t k = 0; k < n; ++k) {
+        double best = -1.0;
+        int32_t bi = k;
+        for (int32_t i = k + tid; i < n; i += nt) {
+            const double t = fabs(a[i * n + k]);
+            if (t > best) { best = t; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_down_sync(0xffffffffu, best, o);
+            const int32_t oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            double bb = -1.0;
+            int32_t ii = k;
+            for (int w = 0; w < (nt + 31) / 32; ++w)
+                if (red_v[w] > bb || (red_v[w] == bb && red_i[w] < ii)) { bb = red_v[w]; ii = red_i[w]; }
+            piv_s = (bb > 0.0) ? ii : -1;
+            if (bb <= 0.0) *singular = 1;
+            perm[k] = ii;
+        }
+        __syncthreads();
+        const int32_t p = piv_s;
+        if (p < 0) return;
+        if (p != k)
+            for (int32_t j = tid; j < n; j += nt) {
+                const double t = a[k * n + j];
+                a[k * n + j] = a[p * n + j];
+                a[p * n + j] = t;
+            }
+        __syncthreads();
+        if (tid == 0) dk_s = 1.0 / a[k * n + k];
+        __syncthreads();
+        const double dk = dk_s;
+        // row k: a_kk <- 1, then the row times 1 / pivot (so a_kk ends as 1 / pivot)
+        for (int32_t j = tid; j < n; j += nt) a[k * n + j] = (j == k ? 1.0 : a[k * n + j]) * dk;
+        for (int32_t i = tid; i < n; i += nt) fac[i] = (i == k) ? 0.0 : a[i * n + k];
+        __syncthreads();
+        // other rows: a_ik <- 0, then row_i -= f_i row_k
+        for (int32_t e = tid; e < nn; e += nt) {
+            const int32_t i = e / n, j = e - i * n;
+            const double f = fac[i];
+            if (f != 0.0) a[e] = (j == k ? 0.0 : a[e]) - f * a[k * n + j];
+        }
+        __syncthreads();
+    }
+    // undo the row exchanges as column exchanges, last first
+    for (int32_t k = n - 1; k >= 0; --k) {
+        const int32_t p = perm[k];
+        if (p != k)
+            for (int32_t i = tid; i < n; i += nt) {
+                const double t = a[i * n + k];
+                a[i * n + k] = a[i * n + p];
+                a[i * n + p] = t;
+            }
+        __syncthreads();
+    }
+    for (int32_t e = tid; e < nn; e += nt) inv[e] = a[e];
+}
+
 // ------------------------------------------------------------------------------------------------
 // host: one hierarchy
 static cptr_status transpose(Ctx *c, const Csr &A, int32_t ncols, Csr &T) {
@@ -573,10 +654,17 @@ cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, con
         CPTR_CUDA_TRY(c, cudaMemsetAsync(D, 0, sizeof(double) * (size_t)cn * cn, c->stream));
         (k_densify<<<nblk(cn, 128), 128, 0, c->stream>>>(cn, C.A.rp, C.A.ci, C.A.v, D), note_launch());
         CPTR_CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
-        size_t smem = sizeof(double) * (size_t)(cn > 0 ? cn : 1);
-        if (smem > 48 * 1024)
-            CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        (k_gauss_jordan<<<1, 1024, smem, c->stream>>>(cn, D, h.cinv, c->flag), note_launch());
+        if (cn <= kGjSmemMax) {
+            const size_t smem = sizeof(double) * ((size_t)cn * cn + cn) + sizeof(int32_t) * cn;
+            CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_gauss_jordan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)smem));
+            (k_gauss_jordan_smem<<<1, 1024, smem, c->stream>>>(cn, D, h.cinv, c->flag), note_launch());
+        } else {
+            const size_t smem = sizeof(double) * (size_t)(cn > 0 ? cn : 1);
+            if (smem > 48 * 1024)
+                CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            (k_gauss_jordan<<<1, 1024, smem, c->stream>>>(cn, D, h.cinv, c->flag), note_launch());
+        }
         CPTR_CUDA_TRY(c, cudaGetLastError());
         int32_t sing = 0;
         CPTR_TRY(copy_to_host(c, &sing, c->flag, sizeof(int32_t)));

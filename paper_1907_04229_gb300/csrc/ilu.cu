@@ -815,13 +815,17 @@ __global__ void __launch_bounds__(64) k_bilu_factor_st(int32_t n, unsigned *tick
         if (t >= n) continue;
         const int32_t i = pos[t];
         const int32_t k0 = rp[i], e = rp[i + 1], kd = diag[i], len = e - k0;
-        // the row's own blocks and columns (nobody else writes them)
+        // the row's own blocks and columns (nobody else writes them) arrive by cp.async while the
+        // dependency flags are polled
         for (int32_t k = 0; k < len; ++k) {
-            cols[k] = ci[k0 + k];
+            cp_async_i32(cols + k, ci + k0 + k);
 #pragma unroll
-            for (int q = 0; q < BB; ++q) rowb[k * BB + q] = LU[(int64_t)(k0 + k) * BB + q];
+            for (int q = 0; q < BB; ++q) cp_async_elem(rowb + k * BB + q, LU + (int64_t)(k0 + k) * BB + q);
         }
-        // wait until every row this row depends on has published its blocks
+        cp_async_commit();
+        // wait until every row this row depends on has published its blocks: all flags are read
+        // together with relaxed loads, re-read until set, then one acquire fence orders the reads
+        // of their blocks after the flags
         {
             unsigned long long t0 = 0;
             bool pending = true;
@@ -829,7 +833,7 @@ __global__ void __launch_bounds__(64) k_bilu_factor_st(int32_t n, unsigned *tick
                 pending = false;
                 for (int32_t k = k0; k < kd; ++k) {
                     int32_t f;
-                    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flag + cols[k - k0]) : "memory");
+                    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flag + __ldg(ci + k)) : "memory");
                     pending |= f != epoch;
                 }
                 if (!pending) break;
@@ -837,7 +841,9 @@ __global__ void __launch_bounds__(64) k_bilu_factor_st(int32_t n, unsigned *tick
                 else if (gtimer() - t0 > kWaitNs) { atomicExch(&ks->wait_err, 1); break; }
                 __nanosleep(20);
             }
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
         }
+        cp_async_wait_0();
         // every dependency's inverted pivot block and upper blocks, in one batch
         for (int32_t k = k0; k < kd; ++k) {
             const int32_t c = cols[k - k0];
