@@ -332,13 +332,17 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_sf(int32_t n, unsigned *
         T s[B];
 #pragma unroll
         for (int q = 0; q < B; ++q) s[q] = __ldcg(y + (int64_t)tf * B + q);
+        // the inverted pivot block does not depend on other rows: load it before the waits
+        T dv[B * B];
+#pragma unroll
+        for (int e = 0; e < B * B; ++e) dv[e] = __ldg(dinv + ((int64_t)ch * B * B + e) * 32 + lane);
         subtract_deps<B, T>(s, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, z, ks, sleep_ns);
         T zi[B];
 #pragma unroll
         for (int rr = 0; rr < B; ++rr) {
             T a = 0;
 #pragma unroll
-            for (int q = 0; q < B; ++q) a = fma(__ldg(dinv + ((int64_t)ch * B * B + rr * B + q) * 32 + lane), s[q], a);
+            for (int q = 0; q < B; ++q) a = fma(dv[rr * B + q], s[q], a);
             zi[rr] = a;
         }
 #pragma unroll
