@@ -52,7 +52,8 @@ def parse():
     p.add_argument("--no-ensemble", action="store_true")
     p.add_argument("--three-phase-grid", type=int, nargs=3, default=None,
                    help="run the three-phase section on an NX NY NZ box instead of 200x200x50 (profiling)")
-    p.add_argument("--autotune", action="store_true", help="autotune launch shapes in the headline solver")
+    p.add_argument("--no-autotune", dest="autotune", action="store_false",
+                   help="fixed launch shapes in the headline solver (default: autotuned at the first set-up, cached)")
     p.add_argument("--ilu-sweep", choices=["auto", "levels", "chunked"], default="auto",
                    help="schedule of the headline solver's ILU(0) sweeps")
     p.add_argument("--ensemble-total", type=float, default=4e6,
@@ -348,7 +349,10 @@ def ours(args, rank, world, local_rank):
                                       "rtol 1e-6, FP64",
                           "step": "cptr_setup + cptr_solve", "parallelism": f"replicas x{world}",
                           "solver": {"autotune": bool(args.autotune), "ilu_sweep": args.ilu_sweep,
-                                     "ilu_schedule_used": "chunked wavefront" if chunked else "level sets"},
+                                     "ilu_schedule_used": "chunked wavefront" if chunked else "level sets",
+                                     "ilu_sweep_tuning": [t for t in cp.cptr_tuning(S.ctx) if t[2] in (4, 5)],
+                                     "tuning_note": "launch shapes timed at the first (warm-up) set-up and cached "
+                                                    "by operator size; timed steps reuse them"},
                           "l2": "flushed before every step (256 MB write); working set > 1 GB"},
                "iters": iters, "setup_ms": round(setup_ms, 3), "solve_ms": round(solve_ms, 3),
                "solve_dofs_per_s": round(dofs / (solve_ms / 1e3), 1),

@@ -1219,6 +1219,17 @@ static void cw_free(Ctx *c) {
     c->cw_use = false;
 }
 
+// key of the sweeps' tuning in the context's cache, and whether a cached tuning chose the
+// level-set schedule (then a set-up with autotune needs no chunked tables)
+static uint64_t ilu_tune_key(const Ctx *c) {
+    return (uint64_t)8 << 60 | (uint64_t)(c->o.precision & 1) << 56 | ((uint64_t)c->n & 0xFFFFFFull) << 32 |
+           (uint64_t)(uint32_t)c->nnzb;
+}
+static bool ilu_tuned_levels(const Ctx *c) {
+    auto it = c->tune_cache.find(ilu_tune_key(c));
+    return it != c->tune_cache.end() && it->second.T > 0;
+}
+
 cptr_status ilu_setup(Ctx *c) {
     ilu_free(c);
     double t0 = host_ms();
@@ -1389,7 +1400,8 @@ cptr_status ilu_setup(Ctx *c) {
     CPTR_TRY(dalloc(c, &c->sf_z, (size_t)n * c->b * (lo ? 4 : 8) + 64));
     CPTR_CUDA_TRY(c, cudaGetLastError());
     dfree(kidx_f); dfree(kidx_b); dfree(kidx_d); dfree(inv_f); dfree(inv_b);
-    if (!mc && (c->o.ilu_sweep == 2 || (c->o.ilu_sweep == 0 && c->o.autotune))) CPTR_TRY(cw_setup(c));
+    if (!mc && (c->o.ilu_sweep == 2 || (c->o.ilu_sweep == 0 && c->o.autotune && !ilu_tuned_levels(c))))
+        CPTR_TRY(cw_setup(c));
     setup_tick(c, SETUP_ILU_HOST, &t0);
     return CPTR_OK;
 }
@@ -1506,8 +1518,7 @@ void ilu_apply_into(const Ctx *c, const double *r, double *z, double *ybuf, doub
 // The sweeps compute the same values whatever the choice.
 cptr_status ilu_autotune(Ctx *c) {
     if (!c->LU) return CPTR_OK;
-    const uint64_t key = (uint64_t)8 << 60 | (uint64_t)(c->o.precision & 1) << 56 |
-                         ((uint64_t)c->n & 0xFFFFFFull) << 32 | (uint64_t)(uint32_t)c->nnzb;
+    const uint64_t key = ilu_tune_key(c);
     auto it = c->tune_cache.find(key);
     if (it != c->tune_cache.end()) {
         c->sf_grid = std::abs((int)it->second.T);
