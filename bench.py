@@ -36,7 +36,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 LEARNED_STEPS, LEARNED_LR = 2000, 2e-3
 # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/ (the
 # current kernels; None where no capture of the current code exists)
-PROFILED_TRAFFIC = {"spmv": None, "stage1_resid": None, "ilu_fwd": 55.788544e6, "ilu_bwd": 75.43936e6}
+PROFILED_TRAFFIC = {"spmv": 113_717_248, "stage1_resid": None, "ilu_fwd": 55_712_512, "ilu_bwd": 75_466_496}
 
 
 def parse():
@@ -360,7 +360,7 @@ def ours(args, rank, world, local_rank):
                "families": families, "roofline": roofline, "rooflines": lines, "variants": variants,
                "three_phase": tp, "ensemble": ens,
                "cpu_baseline": cpu, "e2e": e2e,
-               "gpu_launches": launches, "clocks": clk}
+               "gpu_launches": launches, "launches_before_timed": launches0, "clocks": clk}
         print(json.dumps(out), flush=True)
 
 
