@@ -648,28 +648,40 @@ cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, con
     h.dense = 0;
     double tc = host_ms();
     if (cn <= c->o.dense_max) {
+        // densified on the main stream; inverted on the side stream (one block on one SM), which
+        // overlaps the rest of the set-up; amg_coarsest_wait joins it before the inverse is used
+        if (!c->side_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+        if (!c->side_fork) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&c->side_fork, cudaEventDisableTiming));
+        if (!h.gj_done) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&h.gj_done, cudaEventDisableTiming));
+        if (!h.gj_flag) CPTR_TRY(dalloc_t(c, &h.gj_flag, 1));
         double *D = nullptr;
         CPTR_TRY(dalloc_t(c, &D, (size_t)cn * cn));
         CPTR_TRY(dalloc_t(c, &h.cinv, (size_t)cn * cn));
         CPTR_CUDA_TRY(c, cudaMemsetAsync(D, 0, sizeof(double) * (size_t)cn * cn, c->stream));
         (k_densify<<<nblk(cn, 128), 128, 0, c->stream>>>(cn, C.A.rp, C.A.ci, C.A.v, D), note_launch());
-        CPTR_CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
+        CPTR_CUDA_TRY(c, cudaMemsetAsync(h.gj_flag, 0, sizeof(int32_t), c->stream));
+        CPTR_CUDA_TRY(c, cudaEventRecord(c->side_fork, c->stream));
+        CPTR_CUDA_TRY(c, cudaStreamWaitEvent(c->side_stream, c->side_fork, 0));
+        cudaStream_t ss = c->side_stream;
         if (cn <= kGjSmemMax) {
             const size_t smem = sizeof(double) * ((size_t)cn * cn + cn) + sizeof(int32_t) * cn;
             CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_gauss_jordan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   (int)smem));
-            (k_gauss_jordan_smem<<<1, 1024, smem, c->stream>>>(cn, D, h.cinv, c->flag), note_launch());
+            (k_gauss_jordan_smem<<<1, 1024, smem, ss>>>(cn, D, h.cinv, h.gj_flag), note_launch());
         } else {
             const size_t smem = sizeof(double) * (size_t)(cn > 0 ? cn : 1);
             if (smem > 48 * 1024)
                 CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            (k_gauss_jordan<<<1, 1024, smem, c->stream>>>(cn, D, h.cinv, c->flag), note_launch());
+            (k_gauss_jordan<<<1, 1024, smem, ss>>>(cn, D, h.cinv, h.gj_flag), note_launch());
         }
         CPTR_CUDA_TRY(c, cudaGetLastError());
-        int32_t sing = 0;
-        CPTR_TRY(copy_to_host(c, &sing, c->flag, sizeof(int32_t)));
-        dfree(D);
-        if (sing) return c->fail(CPTR_ESINGULAR, "AMG: singular coarsest-level matrix");
+        if (c->pool) CPTR_CUDA_TRY(c, cudaFreeAsync(D, ss));
+        else {
+            CPTR_CUDA_TRY(c, cudaStreamSynchronize(ss));
+            dfree(D);
+        }
+        CPTR_CUDA_TRY(c, cudaEventRecord(h.gj_done, ss));
+        h.gj_pending = true;
         h.dense = 1;
     }
     setup_tick(c, SETUP_COARSEST, &tc);
@@ -677,7 +689,23 @@ cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, con
     return CPTR_OK;
 }
 
+cptr_status amg_coarsest_wait(Ctx *c, Hier &h) {
+    if (!h.gj_pending) return CPTR_OK;
+    double t0 = host_ms();
+    h.gj_pending = false;
+    CPTR_CUDA_TRY(c, cudaStreamWaitEvent(c->stream, h.gj_done, 0));
+    int32_t sing = 0;
+    CPTR_TRY(copy_to_host(c, &sing, h.gj_flag, sizeof(int32_t)));
+    setup_tick(c, SETUP_COARSEST, &t0);
+    if (sing) return c->fail(CPTR_ESINGULAR, "AMG: singular coarsest-level matrix");
+    return CPTR_OK;
+}
+
 void amg_free(Hier &h) {
+    if (h.gj_pending) {   // the side stream may still use the coarsest matrices
+        cudaEventSynchronize(h.gj_done);
+        h.gj_pending = false;
+    }
     for (int l = 0; l < kMaxLevels; ++l) {
         Level &L = h.L[l];
         csr_free(L.A); csr_free(L.P); csr_free(L.PT);
@@ -687,6 +715,8 @@ void amg_free(Hier &h) {
         L = Level{};
     }
     dfree(h.cinv);
+    dfree(h.gj_flag);
+    h.gj_flag = nullptr;
     dfree(h.ldev64);
     dfree(h.ldev32);
     h.cinv = nullptr;

@@ -52,24 +52,60 @@ void release_setup(Ctx *c) {
     c->ready = false;
 }
 
-cptr_status validate_pattern(Ctx *c, int32_t n) {
-    const std::vector<int32_t> &rp = c->h_rp, &ci = c->h_ci;
-    if (rp[0] != 0) return c->fail(CPTR_EINVAL, "row_ptr[0] must be 0");
-    for (int32_t i = 0; i < n; ++i)
-        if (rp[i + 1] < rp[i]) return c->fail(CPTR_EINVAL, "row_ptr must be non-decreasing (row " + std::to_string(i) + ")");
-    c->h_diag.assign(n, -1);
-    for (int32_t i = 0; i < n; ++i) {
-        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
-            int32_t j = ci[k];
-            if (j < 0 || j >= n) return c->fail(CPTR_EINVAL, "col_idx out of range in row " + std::to_string(i));
-            if (k > rp[i] && ci[k - 1] >= j)
-                return c->fail(CPTR_EINVAL, "col_idx not strictly ascending in row " + std::to_string(i));
-            if (j == i) c->h_diag[i] = k;
-        }
-        if (c->h_diag[i] < 0) return c->fail(CPTR_EINVAL, "missing diagonal block in row " + std::to_string(i));
+// The pattern is checked on the device: per row, column indices in [0, n), strictly ascending,
+// and a diagonal block.  The first failing row (and its first failing entry) is kept as
+// row * 4 + kind (0 out of range, 1 not ascending, 2 no diagonal) by an atomic minimum.
+__global__ void k_validate_rows(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                int32_t *diag, unsigned long long *err) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t d = -1;
+    int kind = -1;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+        const int32_t j = ci[k];
+        if (j < 0 || j >= n) { kind = 0; break; }
+        if (k > rp[i] && ci[k - 1] >= j) { kind = 1; break; }
+        if (j == i) d = k;
     }
-    return CPTR_OK;
+    if (kind < 0 && d < 0) kind = 2;
+    diag[i] = d;
+    if (kind >= 0) atomicMin(err, ((unsigned long long)i << 2) | (unsigned long long)kind);
 }
+
+// row_ptr on the host (already checked to start at 0 and end at nnzb), col_idx on the device
+cptr_status validate_pattern(Ctx *c, int32_t n) {
+    const std::vector<int32_t> &rp = c->h_rp;
+    for (int32_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) return c->fail(CPTR_EINVAL, "row_ptr decreases at row " + std::to_string(i));
+    unsigned long long *err = nullptr, h_err = ~0ULL;
+    CPTR_TRY(dalloc_t(c, &err, 1));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(err, 0xFF, sizeof(unsigned long long), c->stream));
+    (k_validate_rows<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, c->rp, c->ci, c->diag, err), note_launch());
+    const cptr_status cs = copy_to_host(c, &h_err, err, sizeof(h_err));
+    dfree(err);
+    CPTR_TRY(cs);
+    if (h_err == ~0ULL) return CPTR_OK;
+    const std::string row = std::to_string((long long)(h_err >> 2));
+    switch ((int)(h_err & 3)) {
+        case 0: return c->fail(CPTR_EINVAL, "col_idx out of range in row " + row);
+        case 1: return c->fail(CPTR_EINVAL, "col_idx not strictly ascending in row " + row);
+        default: return c->fail(CPTR_EINVAL, "missing diagonal block in row " + row);
+    }
+}
+
+}  // namespace
+
+// column indices and pivot positions on the host, copied from the device once per set-up (the
+// multicolour ordering and the chunked sweep tables are built on the host)
+cptr_status cptr::host_pattern(Ctx *c) {
+    if (c->h_ci.size() == (size_t)c->nnzb && c->h_diag.size() == (size_t)c->n) return CPTR_OK;
+    c->h_ci.assign((size_t)c->nnzb, 0);
+    c->h_diag.assign((size_t)c->n, 0);
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->h_diag.data(), c->diag, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->stream));
+    return copy_to_host(c, c->h_ci.data(), c->ci, sizeof(int32_t) * c->nnzb);
+}
+
+namespace {
 
 cptr_status clear_wait_flag(Ctx *c);
 cptr_status check_wait_flag(Ctx *c);
@@ -98,18 +134,17 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     else memcpy(c->h_rp.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1));
     int32_t nnzb = c->h_rp[n];
     if (nnzb <= 0 || c->h_rp[0] != 0) return c->fail(CPTR_EINVAL, "row_ptr must start at 0 and end at nnzb > 0");
-    c->h_ci.assign((size_t)nnzb, 0);
-    if (on_device) CPTR_TRY(copy_to_host(c, c->h_ci.data(), col_idx, sizeof(int32_t) * nnzb));
-    else memcpy(c->h_ci.data(), col_idx, sizeof(int32_t) * nnzb);
-    CPTR_TRY(validate_pattern(c, n));
+    c->h_ci.clear();
+    c->h_diag.clear();
     c->n = n; c->b = b; c->ps = ps; c->ts = ts; c->nnzb = nnzb;
     const size_t bb = (size_t)b * b;
     CPTR_TRY(dalloc_t(c, &c->rp, (size_t)n + 1));
     CPTR_TRY(dalloc_t(c, &c->ci, (size_t)nnzb));
     CPTR_TRY(dalloc_t(c, &c->diag, (size_t)n));
     CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->rp, c->h_rp.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, c->stream));
-    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ci, c->h_ci.data(), sizeof(int32_t) * nnzb, cudaMemcpyHostToDevice, c->stream));
-    CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->diag, c->h_diag.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
+    if (!host_or_device_copy(c, c->ci, col_idx, sizeof(int32_t) * nnzb, on_device, cudaMemcpyHostToDevice))
+        return c->fail(CPTR_ECUDA, "copy of col_idx failed");
+    CPTR_TRY(validate_pattern(c, n));
     double *Araw = nullptr;
     CPTR_TRY(dalloc_t(c, &Araw, nnzb * bb));
     CPTR_TRY(dalloc_t(c, &c->A, nnzb * bb));
@@ -165,6 +200,9 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_setup(c, c->hp, c->rp, c->ci, c->App, n));
     if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) CPTR_TRY(amg_setup(c, c->hT, c->rp, c->ci, c->St, n));
     if (c->o.stage2 == CPTR_STAGE2_ILU0) CPTR_TRY(ilu_setup(c));
+    // the coarsest inverses ran on the side stream meanwhile
+    CPTR_TRY(amg_coarsest_wait(c, c->hp));
+    CPTR_TRY(amg_coarsest_wait(c, c->hT));
     double t2 = host_ms();
     // A' for the solve in the SELL-32 layout; the BSR copy is not needed after set-up
     CPTR_TRY(sell_build(c));
@@ -363,6 +401,7 @@ void cptr_destroy(cptr_ctx *ctx) {
     {
         CtxScope scope(c);
         cudaStreamSynchronize(c->stream);
+        if (c->side_stream) cudaStreamSynchronize(c->side_stream);
         release_setup(c);
         dfree(c->ks); dfree(c->flag); dfree(c->partial); dfree(c->scan_tmp); dfree(c->never); dfree(c->ilu_flags);
         dfree(c->mlp);
@@ -372,6 +411,10 @@ void cptr_destroy(cptr_ctx *ctx) {
     if (c->ks_host) cudaFreeHost(c->ks_host);
     for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side_stream) cudaStreamDestroy(c->side_stream);
+    if (c->side_fork) cudaEventDestroy(c->side_fork);
+    for (Hier *h : {&c->hp, &c->hT})
+        if (h->gj_done) cudaEventDestroy(h->gj_done);
     delete ctx;
 }
 

@@ -90,6 +90,10 @@ struct Hier {
     double op_complexity = 0.0;
     int fuse_l0 = -1;                 // levels fuse_l0 .. nlev-2 run in the fused coarse kernels
     LevelDev *ldev64 = nullptr, *ldev32 = nullptr;   // device descriptors (FP64 / mixed cycle)
+    // the coarsest inverse runs on the context's side stream while the set-up goes on
+    int32_t *gj_flag = nullptr;       // singular coarsest matrix
+    cudaEvent_t gj_done = nullptr;    // recorded on the side stream after the inverse
+    bool gj_pending = false;
 };
 
 // Arnoldi/Givens state kept on the device (one per context)
@@ -160,6 +164,7 @@ cptr_status build_iteration_graph(Ctx *c);
 // running on this thread (CtxScope), or synchronously when none is.
 cptr_status dalloc(Ctx *c, void **p, size_t bytes);
 cptr_status copy_to_host(Ctx *c, void *dst, const void *src, size_t bytes);
+cptr_status host_pattern(Ctx *c);   // h_ci and h_diag from the device pattern, once per set-up
 struct CtxScope {
     explicit CtxScope(Ctx *c);
     ~CtxScope();
@@ -203,6 +208,7 @@ cptr_status sell_autotune(Ctx *c);           // threads per block of the SELL Sp
 cptr_status ilu_autotune(Ctx *c);            // grid and poll back-off of the ILU(0) sweeps
 cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, const double *v, int32_t n);
 void amg_free(Hier &h);
+cptr_status amg_coarsest_wait(Ctx *c, Hier &h);   // join the side stream's coarsest inverse; its status
 void amg_vcycle(const Ctx *c, const Hier &h, const double *b, double *x);
 void amg_vcycle32(const Ctx *c, const Hier &h, const float *b, float *x);
 cptr_status amg_lower_precision(Ctx *c, Hier &h);
@@ -305,6 +311,8 @@ struct Ctx {
     double *V = nullptr, *Z = nullptr, *w = nullptr, *bw = nullptr, *xw = nullptr, *partial = nullptr;
     double *vcur = nullptr, *zcur = nullptr;           // fixed in/out vectors of the captured step
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t side_stream = nullptr;   // set-up work that overlaps the main stream
+    cudaEvent_t side_fork = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int64_t graph_launches = 0;
     uint32_t graph_mask = 0;

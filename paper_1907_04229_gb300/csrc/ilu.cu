@@ -357,6 +357,106 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_sf(int32_t n, unsigned *
     }
 }
 
+// The same sweeps with a row spread over four lanes, lane q of the group computing component q
+// (B <= 4): on GB300 a warp-wide FP64 instruction occupies a sub-partition's FP64 pipe for 64
+// cycles, and a level's latency includes the pipe time of its warps' FMAs, so a lane that does one
+// component's B FMAs per dependency (instead of a row's B*B) shortens every level.  Each component
+// is computed with exactly the operations and order of the per-row kernels above.
+constexpr int kSfGroup = 4;                          // lanes per row
+constexpr int kSfRowsG = kSfThreads / kSfGroup;      // rows per block chunk
+
+// s -= sum over the dependency slots [o0, o1) of row q of block(slot) * value(dep(slot))
+template <int B, typename T>
+__device__ __forceinline__ T subtract_deps_row(T s, int q4, int64_t o0, int64_t o1, int lane,
+                                               const int32_t *__restrict__ col, const T *__restrict__ val,
+                                               const T *vec, KState *ks, int sleep_ns) {
+    for (int64_t sl0 = o0; sl0 < o1; sl0 += kDepGroup) {
+        int32_t c[kDepGroup];
+#pragma unroll
+        for (int g = 0; g < kDepGroup; ++g) c[g] = (sl0 + g < o1) ? __ldg(col + (sl0 + g) * 32 + lane) : -1;
+        T a[kDepGroup][B];
+#pragma unroll
+        for (int g = 0; g < kDepGroup; ++g)
+            if (c[g] >= 0)
+#pragma unroll
+                for (int q = 0; q < B; ++q) a[g][q] = __ldg(val + ((sl0 + g) * B * B + q4 * B + q) * 32 + lane);
+        T v[kDepGroup][B];
+        load_group<B, T>(vec, c, v, ks, sleep_ns);
+#pragma unroll
+        for (int g = 0; g < kDepGroup; ++g)
+            if (c[g] >= 0)
+#pragma unroll
+                for (int q = 0; q < B; ++q) s = fma(-a[g][q], v[g][q], s);
+    }
+    return s;
+}
+
+template <int B, typename T, typename RT>
+__global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_g(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
+                                                         const int64_t *__restrict__ off, const int32_t *__restrict__ col,
+                                                         const T *__restrict__ val, const RT *__restrict__ r, T *y,
+                                                         KState *ks, const double *never, int sleep_ns) {
+    __shared__ unsigned blk;
+    const unsigned nchunks = (unsigned)((n + kSfRowsG - 1) / kSfRowsG);
+    const int q4 = threadIdx.x & (kSfGroup - 1);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) blk = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const unsigned b = blk;
+        if (b >= nchunks) return;
+        const int32_t t = (int32_t)(b * kSfRowsG + threadIdx.x / kSfGroup);
+        if (t >= n || q4 >= B) continue;
+        if (never && t == 0 && q4 == 0) (void)wait_value(never, ks);  // failure injection
+        const int32_t ch = t >> 5, lane = t & 31;
+        const int32_t row = __ldg(pos + t);
+        T s = (T)__ldg(r + (int64_t)row * B + q4);
+        s = subtract_deps_row<B, T>(s, q4, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, y, ks, sleep_ns);
+        store_relaxed(y + (int64_t)t * B + q4, s);
+    }
+}
+
+template <int B, typename T, typename XT>
+__global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_g(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
+                                                         const int32_t *__restrict__ bmap,
+                                                         const int64_t *__restrict__ off, const int32_t *__restrict__ col,
+                                                         const T *__restrict__ val, const T *__restrict__ dinv,
+                                                         const T *__restrict__ y, T *z, double *__restrict__ out,
+                                                         int ps, int ts, const XT *__restrict__ dp,
+                                                         const XT *__restrict__ dT, KState *ks, int sleep_ns) {
+    __shared__ unsigned blk;
+    const unsigned nchunks = (unsigned)((n + kSfRowsG - 1) / kSfRowsG);
+    const int q4 = threadIdx.x & (kSfGroup - 1);
+    const unsigned gmask = ((1u << B) - 1u) << ((threadIdx.x & 31) & ~(kSfGroup - 1));
+    const int g0 = (threadIdx.x & 31) & ~(kSfGroup - 1);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) blk = atomicAdd(ticket + 1, 1u);
+        __syncthreads();
+        const unsigned b = blk;
+        if (b >= nchunks) return;
+        const int32_t t = (int32_t)(b * kSfRowsG + threadIdx.x / kSfGroup);
+        if (t >= n || q4 >= B) continue;
+        const int32_t ch = t >> 5, lane = t & 31;
+        const int32_t row = __ldg(pos + t);
+        const int32_t tf = __ldg(bmap + t);
+        T s = __ldcg(y + (int64_t)tf * B + q4);
+        // row q4 of the inverted pivot block does not depend on other rows: load it first
+        T dv[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) dv[q] = __ldg(dinv + ((int64_t)ch * B * B + q4 * B + q) * 32 + lane);
+        s = subtract_deps_row<B, T>(s, q4, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, z, ks, sleep_ns);
+        T a = 0;
+#pragma unroll
+        for (int q = 0; q < B; ++q) a = fma(dv[q], __shfl_sync(gmask, s, g0 + q), a);
+        store_relaxed(z + (int64_t)t * B + q4, a);
+        double add = 0.0;
+        if (dp && q4 == ps) add = (double)dp[row];
+        if (dT && q4 == ts) add = (double)dT[row];
+        out[(int64_t)row * B + q4] = (double)a + add;
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // Chunked wavefront sweeps.  The rows of the factor order are cut into chunks of K consecutive
 // rows (K = the matrix's bandwidth, so that every dependency outside a chunk lies in an earlier
@@ -645,23 +745,50 @@ __global__ void k_sf_pack(int64_t nslots32, int BB, const int32_t *kidx, const d
 }
 
 // ------------------------------------------------------------------------------------------------
-// Set-up of the sweeps on the device.  Level sets by monotone relaxation: every row takes 1 + the
-// largest level among the rows it depends on (lower columns forward, upper columns backward);
-// repeated in place until nothing changes (as many passes as levels, checked every 16).  Rows
-// are then ordered by level (counting sort; the order inside a level does not change any result,
-// since rows of one level are independent) and the SELL-32 dependency tables are filled.
-__global__ void k_lev_relax(int32_t n, const int32_t *rp, const int32_t *ci, int32_t *lev, int forward,
-                            int32_t *changed) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int32_t l = 0;
-    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
-        int32_t j = ci[k];
-        if (forward ? (j < i) : (j > i)) l = max(l, *(volatile int32_t *)(lev + j) + 1);
-    }
-    if (l != lev[i]) {
-        lev[i] = l;
-        *changed = 1;
+// Set-up of the sweeps on the device.  Level sets in one launch: every row's level is 1 + the
+// largest level among the rows it depends on (lower columns forward, upper columns backward), 0
+// without dependencies.  Rows are taken by a ticket counter in a topological order (ascending
+// forward, descending backward), so a row waits only on rows of earlier tickets, held by blocks
+// that already run; it polls the levels of its dependencies (sentinel -1, bounded wait) and
+// publishes its own.  Rows are then ordered by level (counting sort; the order inside a level does
+// not change any result, since rows of one level are independent) and the SELL-32 dependency
+// tables are filled.
+__global__ void __launch_bounds__(128) k_levels_sf(int32_t n, unsigned *ticket, const int32_t *__restrict__ rp,
+                                                   const int32_t *__restrict__ ci, int32_t *lev, int forward,
+                                                   int32_t *err) {
+    __shared__ unsigned blk;
+    const unsigned nchunks = (unsigned)((n + 127) / 128);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) blk = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const unsigned b = blk;
+        if (b >= nchunks) return;
+        const int32_t t = (int32_t)(b * 128 + threadIdx.x);
+        if (t >= n) continue;
+        const int32_t i = forward ? t : n - 1 - t;
+        const int32_t k0 = rp[i], k1 = rp[i + 1];
+        int32_t l = 0;
+        unsigned long long t0 = 0;
+        for (int round = 0;; ++round) {
+            bool pending = false;
+            l = 0;
+#pragma unroll 4
+            for (int32_t k = k0; k < k1; ++k) {
+                const int32_t j = ci[k];
+                if (forward ? (j < i) : (j > i)) {
+                    int32_t v;
+                    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(lev + j) : "memory");
+                    pending |= v < 0;
+                    l = max(l, v + 1);
+                }
+            }
+            if (!pending) break;
+            if (round == 0) t0 = gtimer();
+            else if (gtimer() - t0 > kWaitNs) { atomicExch(err, 1); break; }
+            __nanosleep(20);
+        }
+        asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(lev + i), "r"(l) : "memory");
     }
 }
 __global__ void k_compose(int32_t n, const int32_t *a, const int32_t *b, int32_t *out) {  // out[t] = a[b[t]]
@@ -699,6 +826,27 @@ __global__ void k_fill_tables(int32_t n, const int32_t *pos, const int32_t *rp, 
 __global__ void k_dinv_index(int32_t n, const int32_t *pos_b, const int32_t *dg, int32_t *kidx) {
     int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) kidx[t] = dg[pos_b[t]];
+}
+
+// largest row length, lower count and upper count of a pattern (atomic maxima per warp)
+__global__ void k_row_extents(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t *ext) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t len = 0, lower = 0, upper = 0;
+    if (i < n) {
+        len = rp[i + 1] - rp[i];
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+            lower += ci[k] < i;
+            upper += ci[k] > i;
+        }
+    }
+    len = __reduce_max_sync(0xffffffffu, len);
+    lower = __reduce_max_sync(0xffffffffu, lower);
+    upper = __reduce_max_sync(0xffffffffu, upper);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(ext, len);
+        atomicMax(ext + 1, lower);
+        atomicMax(ext + 2, upper);
+    }
 }
 
 // Block ILU(0) factorisation in one launch: rows in forward level order, taken in ticket order;
@@ -787,13 +935,19 @@ __global__ void __launch_bounds__(64) k_bilu_factor_sf(int32_t n, unsigned *tick
     }
 }
 
-// The same factorisation with the memory traffic of a row batched: the row's own blocks and
-// column indices are copied to shared memory while its dependency flags are polled; once all are
-// set, the inverted pivot blocks and upper blocks of every dependency are loaded in one batch;
-// then the row is factored in shared memory, in exactly the order of k_bilu_factor_sf (same
-// operations, same rounding), and written back.  A row thus costs about three memory round trips
-// instead of one per block update.  Per-thread shared memory: maxrow blocks + column indices, and
-// per dependency the pivot inverse plus maxu upper blocks (sizes from the pattern).
+// The same factorisation with the memory traffic of a row batched so that, once its last
+// dependency is published, a row costs one memory round trip before it computes.  Before the
+// flags are set (off the critical path, since tickets run many levels ahead): the row's own
+// blocks and columns, then the pivot and row-end positions of its dependencies, then the column
+// indices of their upper parts, all by cp.async into shared memory (none of these are written
+// during the launch).  Once every flag is set and an acquire fence orders what follows: the pivot
+// inverse and upper blocks of every dependency (one contiguous run of blocks each) by 16-byte
+// cp.async through L2 only, into a window rounded out to 16-byte boundaries.  The row is then
+// factored in shared memory in exactly the order of k_bilu_factor_sf (same operations, same
+// rounding); its pivot and upper blocks are written and the flag released before its lower
+// blocks are written (no row of the launch reads those).  Shared memory per thread: rowsz
+// doubles for the row (maxrow blocks, even), maxdep windows of W doubles, and maxrow + 2 maxdep +
+// maxdep maxu integers.
 template <int B>
 __global__ void __launch_bounds__(64) k_bilu_factor_st(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
                                                        const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
@@ -802,11 +956,15 @@ __global__ void __launch_bounds__(64) k_bilu_factor_st(int32_t n, unsigned *tick
                                                        int maxdep, int maxu) {
     constexpr int BB = B * B;
     extern __shared__ __align__(16) unsigned char fs_smem[];
-    const int per = (maxrow + maxdep * (1 + maxu)) * BB;       // doubles per thread
+    const int rowsz = (maxrow * BB + 1) & ~1;
+    const int W = ((1 + maxu) * BB + 2 + 1) & ~1;
+    const int per = rowsz + maxdep * W;                       // doubles per thread (even)
     double *rowb = reinterpret_cast<double *>(fs_smem) + (int64_t)threadIdx.x * per;
-    double *depb = rowb + (int64_t)maxrow * BB;
+    double *depw = rowb + rowsz;
+    const int iper = maxrow + maxdep * (2 + maxu);
     int32_t *cols = reinterpret_cast<int32_t *>(reinterpret_cast<double *>(fs_smem) + (int64_t)blockDim.x * per) +
-                    threadIdx.x * maxrow;
+                    threadIdx.x * iper;
+    int32_t *dcs = cols + maxrow, *ecs = dcs + maxdep, *ucol = ecs + maxdep;
     __shared__ unsigned blk;
     const unsigned nchunks = (unsigned)((n + 63) / 64);
     for (;;) {
@@ -818,26 +976,37 @@ __global__ void __launch_bounds__(64) k_bilu_factor_st(int32_t n, unsigned *tick
         const int32_t t = (int32_t)(b * 64 + threadIdx.x);
         if (t >= n) continue;
         const int32_t i = pos[t];
-        const int32_t k0 = rp[i], e = rp[i + 1], kd = diag[i], len = e - k0;
-        // the row's own blocks and columns (nobody else writes them) arrive by cp.async while the
-        // dependency flags are polled
-        for (int32_t k = 0; k < len; ++k) {
-            cp_async_i32(cols + k, ci + k0 + k);
+        const int32_t k0 = rp[i], e = rp[i + 1], kd = diag[i], len = e - k0, nd = kd - k0;
+        // the row's columns (group 1) and blocks (group 2); nobody else writes them
+        for (int32_t k = 0; k < len; ++k) cp_async_i32(cols + k, ci + k0 + k);
+        cp_async_commit();
+        for (int32_t k = 0; k < len; ++k)
 #pragma unroll
             for (int q = 0; q < BB; ++q) cp_async_elem(rowb + k * BB + q, LU + (int64_t)(k0 + k) * BB + q);
+        cp_async_commit();
+        cp_async_wait_1();
+        // pivot position and row end of each dependency, then the columns of its upper part
+        for (int32_t k = 0; k < nd; ++k) {
+            const int32_t c = cols[k];
+            cp_async_i32(dcs + k, diag + c);
+            cp_async_i32(ecs + k, rp + c + 1);
         }
         cp_async_commit();
-        // wait until every row this row depends on has published its blocks: all flags are read
-        // together with relaxed loads, re-read until set, then one acquire fence orders the reads
-        // of their blocks after the flags
+        cp_async_wait_0();
+        for (int32_t k = 0; k < nd; ++k)
+            for (int32_t qq = dcs[k] + 1; qq < ecs[k]; ++qq) cp_async_i32(ucol + k * maxu + (qq - dcs[k] - 1), ci + qq);
+        cp_async_commit();
+        // wait until every dependency has published its blocks: all flags are read together
+        // with relaxed loads, re-read until set; one acquire fence then orders the copies of
+        // their blocks after the flags
         {
             unsigned long long t0 = 0;
             bool pending = true;
             for (int round = 0; pending; ++round) {
                 pending = false;
-                for (int32_t k = k0; k < kd; ++k) {
+                for (int32_t k = 0; k < nd; ++k) {
                     int32_t f;
-                    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flag + __ldg(ci + k)) : "memory");
+                    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flag + cols[k]) : "memory");
                     pending |= f != epoch;
                 }
                 if (!pending) break;
@@ -847,23 +1016,21 @@ __global__ void __launch_bounds__(64) k_bilu_factor_st(int32_t n, unsigned *tick
             }
             asm volatile("fence.acq_rel.gpu;" ::: "memory");
         }
-        cp_async_wait_0();
-        // every dependency's inverted pivot block and upper blocks, in one batch
-        for (int32_t k = k0; k < kd; ++k) {
-            const int32_t c = cols[k - k0];
-            double *dst = depb + (int64_t)(k - k0) * (1 + maxu) * BB;
-            const int32_t dc = diag[c], ec = rp[c + 1];
-#pragma unroll
-            for (int q = 0; q < BB; ++q) dst[q] = __ldcg(LU + (int64_t)dc * BB + q);
-            for (int32_t qq = dc + 1; qq < ec; ++qq)
-#pragma unroll
-                for (int q = 0; q < BB; ++q) dst[(1 + qq - dc - 1) * BB + q] = __ldcg(LU + (int64_t)qq * BB + q);
+        // every dependency's pivot inverse and upper blocks: the run of blocks [dc, ec) of LU,
+        // copied in 16-byte pieces from the 16-byte boundary at or below its start
+        for (int32_t k = 0; k < nd; ++k) {
+            const int64_t lo = (int64_t)dcs[k] * BB, hi = (int64_t)ecs[k] * BB;   // in doubles
+            const int64_t a0 = lo & ~(int64_t)1;
+            double *w = depw + (int64_t)k * W;
+            for (int64_t u = a0; u < hi; u += 2) cp_async_cg16(w + (u - a0), LU + u);
         }
+        cp_async_commit();
+        cp_async_wait_0();
         // factor the row in shared memory (the order of k_bilu_factor_sf)
         for (int32_t k = k0; k < kd; ++k) {
-            const int32_t c = cols[k - k0];
-            const double *dep = depb + (int64_t)(k - k0) * (1 + maxu) * BB;
-            const double *dinv = dep;
+            const int32_t dc = dcs[k - k0], ec = ecs[k - k0];
+            const double *dinv = depw + (int64_t)(k - k0) * W + (int)(((int64_t)dc * BB) & 1);
+            const int32_t *uc = ucol + (k - k0) * maxu;
             double a[BB], l[BB];
 #pragma unroll
             for (int q = 0; q < BB; ++q) a[q] = rowb[(k - k0) * BB + q];
@@ -878,13 +1045,12 @@ __global__ void __launch_bounds__(64) k_bilu_factor_st(int32_t n, unsigned *tick
                 }
 #pragma unroll
             for (int q = 0; q < BB; ++q) rowb[(k - k0) * BB + q] = l[q];
-            const int32_t dc = diag[c], ec = rp[c + 1];
             int32_t p = k + 1;
             for (int32_t qq = dc + 1; qq < ec; ++qq) {
-                const int32_t j = ci[qq];
+                const int32_t j = uc[qq - dc - 1];
                 while (p < e && cols[p - k0] < j) ++p;
                 if (p < e && cols[p - k0] == j) {
-                    const double *u = dep + (1 + qq - dc - 1) * BB;
+                    const double *u = dinv + (qq - dc) * BB;
                     double *d = rowb + (p - k0) * BB;
 #pragma unroll
                     for (int r = 0; r < B; ++r)
@@ -900,14 +1066,17 @@ __global__ void __launch_bounds__(64) k_bilu_factor_st(int32_t n, unsigned *tick
         }
         double dd[BB];
 #pragma unroll
-        for (int q = 0; q < BB; ++q) dd[q] = rowb[(kd - k0) * BB + q];
+        for (int q = 0; q < BB; ++q) dd[q] = rowb[nd * BB + q];
         if (!block_inverse<B>(dd)) atomicOr(singular, 1);
 #pragma unroll
-        for (int q = 0; q < BB; ++q) rowb[(kd - k0) * BB + q] = dd[q];
-        for (int32_t k = 0; k < len; ++k)
+        for (int q = 0; q < BB; ++q) rowb[nd * BB + q] = dd[q];
+        for (int32_t k = nd; k < len; ++k)
 #pragma unroll
             for (int q = 0; q < BB; ++q) LU[(int64_t)(k0 + k) * BB + q] = rowb[k * BB + q];
         asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(flag + i), "r"(epoch) : "memory");
+        for (int32_t k = 0; k < nd; ++k)
+#pragma unroll
+            for (int q = 0; q < BB; ++q) LU[(int64_t)(k0 + k) * BB + q] = rowb[k * BB + q];
     }
 }
 
@@ -916,23 +1085,25 @@ static cptr_status device_levels(Ctx *c, const int32_t *rp, const int32_t *ci, b
                                  int32_t *inv, std::vector<int32_t> &h_lptr) {
     const int32_t n = c->n;
     cudaStream_t s = c->stream;
-    int32_t *lev = nullptr, *chg = nullptr, *cnt = nullptr, *lptr = nullptr;
+    int32_t *lev = nullptr, *tk = nullptr;
     CPTR_TRY(dalloc_t(c, &lev, (size_t)n));
-    CPTR_TRY(dalloc_t(c, &chg, 2));
-    CPTR_CUDA_TRY(c, cudaMemsetAsync(lev, 0, sizeof(int32_t) * n, s));
-    for (int pass = 0;; ++pass) {
-        CPTR_CUDA_TRY(c, cudaMemsetAsync(chg, 0, sizeof(int32_t), s));
-        for (int k = 0; k < 16; ++k)
-            (k_lev_relax<<<nblk(n, 256), 256, 0, s>>>(n, rp, ci, lev, forward ? 1 : 0, chg), note_launch());
-        int32_t h = 0;
-        CPTR_TRY(copy_to_host(c, &h, chg, sizeof(int32_t)));
-        if (!h) break;   // the last 16 passes changed nothing
-        if (pass > n) return c->fail(CPTR_EINVAL, "ILU(0): level sets did not converge");
-    }
+    CPTR_TRY(dalloc_t(c, &tk, 2));   // ticket, wait error
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(lev, 0xFF, sizeof(int32_t) * n, s));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(tk, 0, 2 * sizeof(int32_t), s));
+    (k_levels_sf<<<std::min<unsigned>(nblk(n, 128), 8 * 152), 128, 0, s>>>(n, reinterpret_cast<unsigned *>(tk), rp, ci, lev,
+                                                                          forward ? 1 : 0, tk + 1), note_launch());
+    CPTR_CUDA_TRY(c, cudaGetLastError());
     // stable counting sort by level on the host (rows of a level in ascending order keep the
     // sweeps' accesses local): one sequential pass over the levels
     std::vector<int32_t> hl(n), hp(n), hi(n);
-    CPTR_TRY(copy_to_host(c, hl.data(), lev, sizeof(int32_t) * n));
+    int32_t werr = 0;
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(&werr, tk + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    const cptr_status cs = copy_to_host(c, hl.data(), lev, sizeof(int32_t) * n);
+    dfree(tk);
+    if (cs != CPTR_OK || werr) {
+        dfree(lev);
+        return cs != CPTR_OK ? cs : c->fail(CPTR_ETIMEOUT, "ILU(0) level sets: a bounded wait gave up");
+    }
     int32_t nl = 0;
     for (int32_t i = 0; i < n; ++i) nl = std::max(nl, hl[i] + 1);
     h_lptr.assign(nl + 1, 0);
@@ -947,8 +1118,7 @@ static cptr_status device_levels(Ctx *c, const int32_t *rp, const int32_t *ci, b
     CPTR_CUDA_TRY(c, cudaMemcpyAsync(pos, hp.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     CPTR_CUDA_TRY(c, cudaMemcpyAsync(inv, hi.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     CPTR_CUDA_TRY(c, cudaStreamSynchronize(s));
-    dfree(lev); dfree(chg);
-    (void)cnt; (void)lptr;
+    dfree(lev);
     return CPTR_OK;
 }
 
@@ -1141,6 +1311,7 @@ static CwHost cw_build(int32_t n, const std::vector<int32_t> &rp, const std::vec
 static cptr_status cw_setup(Ctx *c) {
     c->cw_ok = false;
     const int32_t n = c->n, B = c->b, BB = B * B;
+    CPTR_TRY(host_pattern(c));
     const std::vector<int32_t> &rp = c->h_rp, &ci = c->h_ci;
     int32_t K = 1;
     for (int32_t i = 0; i < n; ++i)
@@ -1235,11 +1406,13 @@ cptr_status ilu_setup(Ctx *c) {
     double t0 = host_ms();
     const int32_t n = c->n, BB = c->b * c->b;
     cudaStream_t st = c->stream;
-    CPTR_TRY(dalloc_t(c, &c->LU, (size_t)c->nnzb * BB));
+    // two spare doubles: the factorisation copies runs of blocks in 16-byte pieces rounded outwards
+    CPTR_TRY(dalloc_t(c, &c->LU, (size_t)c->nnzb * BB + 2));
     // the pattern the factorisation works on: the caller's order, or cells permuted by colour
     std::vector<int32_t> rowmap;
     const bool mc = c->o.ilu_order == CPTR_ILU_MULTICOLOR;
     if (mc) {
+        CPTR_TRY(host_pattern(c));
         rowmap = multicolour_order(n, c->h_rp, c->h_ci);
         std::vector<int32_t> inv(n), kmap(c->nnzb), prp(n + 1, 0), pci(c->nnzb), pdg(n, -1);
         for (int32_t I = 0; I < n; ++I) inv[rowmap[I]] = I;
@@ -1312,29 +1485,19 @@ cptr_status ilu_setup(Ctx *c) {
     // blocks of each dependency, in shared memory when that fits
     int maxrow = 0, maxdep = 0, maxu = 0;
     {
-        const std::vector<int32_t> *prp = &c->h_rp, *pci = &c->h_ci;
-        std::vector<int32_t> mrp, mci;
-        if (mc) {   // the permuted pattern
-            mrp.resize(n + 1);
-            mci.resize(c->nnzb);
-            CPTR_CUDA_TRY(c, cudaMemcpyAsync(mrp.data(), c->ilu_rp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, st));
-            CPTR_CUDA_TRY(c, cudaMemcpyAsync(mci.data(), c->ilu_ci, sizeof(int32_t) * c->nnzb, cudaMemcpyDeviceToHost, st));
-            CPTR_CUDA_TRY(c, cudaStreamSynchronize(st));
-            prp = &mrp;
-            pci = &mci;
-        }
-        for (int32_t i = 0; i < n; ++i) {
-            int lower = 0, upper = 0;
-            for (int32_t k = (*prp)[i]; k < (*prp)[i + 1]; ++k) {
-                if ((*pci)[k] < i) ++lower;
-                if ((*pci)[k] > i) ++upper;
-            }
-            maxrow = std::max(maxrow, (*prp)[i + 1] - (*prp)[i]);
-            maxdep = std::max(maxdep, lower);
-            maxu = std::max(maxu, upper);
-        }
+        int32_t *ext = nullptr, h_ext[3] = {0, 0, 0};
+        CPTR_TRY(dalloc_t(c, &ext, 3));
+        CPTR_CUDA_TRY(c, cudaMemsetAsync(ext, 0, 3 * sizeof(int32_t), st));
+        (k_row_extents<<<nblk(n, 256), 256, 0, st>>>(n, c->ilu_rp, c->ilu_ci, ext), note_launch());
+        const cptr_status cs = copy_to_host(c, h_ext, ext, sizeof(h_ext));
+        dfree(ext);
+        CPTR_TRY(cs);
+        maxrow = h_ext[0];
+        maxdep = h_ext[1];
+        maxu = h_ext[2];
     }
-    const size_t fs_bytes = (size_t)64 * ((size_t)(maxrow + maxdep * (1 + maxu)) * BB * 8 + (size_t)maxrow * 4);
+    const size_t fs_rowsz = (size_t)((maxrow * BB + 1) & ~1), fs_w = (size_t)(((1 + maxu) * BB + 3) & ~1);
+    const size_t fs_bytes = (size_t)64 * ((fs_rowsz + (size_t)maxdep * fs_w) * 8 + (size_t)(maxrow + maxdep * (2 + maxu)) * 4);
     const unsigned fgrid = std::min<unsigned>(nblk(n, 64), 8 * 152);
     if (fs_bytes <= 100 * 1024) {
         const unsigned sgrid = std::min<unsigned>(nblk(n, 64), 2 * 152);
@@ -1458,6 +1621,21 @@ static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT 
         prof_end(c, pf);
         pf = prof_begin(c, PF_ILU_BWD);
         cw_launch<B, T, T, XT, false>(c, Bk, y, zz, z, dp, dT, nullptr);
+        prof_end(c, pf);
+        return;
+    }
+    if constexpr (std::is_same<T, double>::value) {   // FP64: a row over four lanes
+        const unsigned gridg = std::min<unsigned>(nblk(n, kSfRowsG), (unsigned)c->sf_grid);
+        int pf = prof_begin(c, PF_ILU_FWD);
+        (k_ilu_fwd_g<B, T, RT><<<gridg, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_f, c->sf_off_f, c->sf_col_f,
+                                                             (const T *)c->sf_val_f, r, y, c->ks,
+                                                             c->inject_wait ? c->never : nullptr, c->sf_sleep), note_launch());
+        prof_end(c, pf);
+        pf = prof_begin(c, PF_ILU_BWD);
+        (k_ilu_bwd_g<B, T, XT><<<gridg, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_b, c->sf_bmap, c->sf_off_b,
+                                                             c->sf_col_b, (const T *)c->sf_val_b, (const T *)c->sf_dinv,
+                                                             y, zz, z, c->ps, c->ts, dp, dT, c->ks, c->sf_sleep),
+         note_launch());
         prof_end(c, pf);
         return;
     }

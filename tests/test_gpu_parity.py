@@ -239,6 +239,34 @@ def test_invalid_inputs_are_rejected():
     assert info["status"] == "CPTR_OK"
 
 
+def test_pattern_errors_name_the_first_bad_row():
+    # the pattern is checked on the device; the message names the first failing row and what fails
+    kind = system("ragged")["unknown_kind"]
+    S = cp.Solver()
+
+    def setup(rp, ci):
+        rp, ci = np.asarray(rp, np.int32), np.asarray(ci, np.int32)
+        v = np.tile(np.eye(3).reshape(-1), len(ci))
+        with pytest.raises(cp.CptrError) as e:
+            S.setup(len(rp) - 1, 3, rp, ci, v, kind)
+        assert e.value.code == -1
+        return str(e.value)
+
+    rp = [0, 2, 5, 7, 9]
+    assert "out of range in row 1" in setup(rp, [0, 1, 0, 1, 4, 2, 3, 2, 3])
+    assert "not strictly ascending in row 2" in setup(rp, [0, 1, 0, 1, 2, 3, 2, 2, 3])
+    assert "missing diagonal block in row 2" in setup(rp, [0, 1, 0, 1, 2, 1, 3, 2, 3])
+    # two bad rows: the first one is reported
+    assert "not strictly ascending in row 1" in setup(rp, [0, 1, 1, 0, 2, 1, 3, 2, 3])
+    assert "row_ptr decreases at row 1" in setup([0, 3, 2, 7, 9], [0, 1, 2, 0, 1, 2, 3, 2, 3])
+    # a valid pattern afterwards
+    s = system("ragged")
+    S.setup(s["n"], s["b"], s["row_ptr"], s["col_idx"], s["vals"].reshape(-1), s["unknown_kind"],
+            s["weights"].reshape(-1), s["st"])
+    x, info = S.solve(np.ascontiguousarray(s["rhs"].reshape(-1)), 1e-8)
+    assert info["status"] == "CPTR_OK"
+
+
 def test_bounded_wait_reports_timeout_and_context_recovers():
     # failure injection without a GPU fault: a row of the ILU sweep waits on a value nobody writes;
     # the wait gives up after ~0.5 s and the call reports CPTR_ETIMEOUT
