@@ -210,108 +210,103 @@ __global__ void k_interp_fill(int32_t n, const int32_t *rp, const int32_t *ci, c
 // C = A B by a per-row merge of the B rows selected by A's row.  Every output entry is the sum,
 // in ascending position of A's row, of the products a_il * b_lj, accumulated from 0.0 with
 // separately rounded multiply and add; output columns ascending.  NUM = false counts entries.
-constexpr int kMergeMax = 256;
-constexpr int kMergeThreads = 32;
-constexpr int kWarpMergeMax = 64;
+//
+// A group of S lanes merges one output row whose A row has m entries, mlo < m <= mhi: lane l of the
+// group holds, in slot j, the head of the B row selected by entry j*S + l (K = ceil(m / S) slots).
+// Each step finds the smallest head column by a group min-reduction; the products of the
+// matching heads are added in ascending entry order (slot by slot, lanes ascending) and lane 0
+// of the group writes the entry.  Short rows use groups of 4 or 8 lanes (eight or four rows per
+// warp), so that a warp-wide FP64 instruction serves several rows; long rows use the whole warp
+// and up to 8 slots.
+constexpr int kGemmTinyS = 4, kGemmTinyK = 2;       // m <= 8
+constexpr int kGemmSmallS = 8, kGemmSmallK = 4;     // 8 < m <= 32
+constexpr int kGemmLargeK = 8;                      // 32 < m <= 256
+constexpr int kGemmMaxM = 32 * kGemmLargeK;
 
-// The same product with one warp per output row for rows that merge at most 64 rows of B: lane
-// l holds the heads of the B rows selected by entries l and l + 32 of A's row; each step finds
-// the smallest head column with a warp min-reduction, and lane 0 adds the matching products in
-// ascending entry order (separately rounded multiply and add, as in the per-thread kernel).
-template <bool NUM>
-__global__ void __launch_bounds__(256) k_spgemm_warp(int32_t n, const int32_t *__restrict__ Arp,
-                                                      const int32_t *__restrict__ Aci, const double *__restrict__ Av,
-                                                      const int32_t *__restrict__ Brp, const int32_t *__restrict__ Bci,
-                                                      const double *__restrict__ Bv, const int32_t *__restrict__ Crp,
-                                                      int32_t *Cci_or_cnt, double *Cv) {
-    const int32_t row = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (row >= n) return;                      // whole warp
+template <bool NUM, int S, int KMAX>
+__global__ void __launch_bounds__(256) k_spgemm_grp(int32_t n, int32_t mlo, int32_t mhi, const int32_t *__restrict__ Arp,
+                                                     const int32_t *__restrict__ Aci, const double *__restrict__ Av,
+                                                     const int32_t *__restrict__ Brp, const int32_t *__restrict__ Bci,
+                                                     const double *__restrict__ Bv, const int32_t *__restrict__ Crp,
+                                                     int32_t *Cci_or_cnt, double *Cv, int32_t *err) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t row = (int32_t)(gt / S);
+    const int lane = threadIdx.x & 31, l = lane & (S - 1), gbase = lane & ~(S - 1);
+    const unsigned gmask = (S == 32) ? 0xffffffffu : (((1u << S) - 1u) << gbase);
+    if (row >= n) return;                      // the whole group
     const int32_t a0 = Arp[row], m = Arp[row + 1] - a0;
-    if (m > kWarpMergeMax) return;             // done by k_spgemm_merge
-    int32_t p0 = 0, e0 = 0, p1 = 0, e1 = 0;
-    double x0 = 0.0, x1 = 0.0;
-    if (lane < m) {
-        int32_t l = Aci[a0 + lane];
-        p0 = Brp[l]; e0 = Brp[l + 1]; x0 = Av[a0 + lane];
+    if (m <= mlo) return;
+    if (m > mhi) {
+        if (mhi >= kGemmMaxM && l == 0) atomicExch(err, 1);
+        return;
     }
-    if (lane + 32 < m) {
-        int32_t l = Aci[a0 + lane + 32];
-        p1 = Brp[l]; e1 = Brp[l + 1]; x1 = Av[a0 + lane + 32];
+    const int K = (m + S - 1) / S;             // slots in use, the same for the whole group
+    int32_t p[KMAX], e[KMAX];
+    double x[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+        p[j] = 0;
+        e[j] = 0;
+        x[j] = 0.0;
+        const int q = j * S + l;
+        if (j < K && q < m) {
+            const int32_t lj = Aci[a0 + q];
+            p[j] = Brp[lj];
+            e[j] = Brp[lj + 1];
+            x[j] = Av[a0 + q];
+        }
     }
     int32_t out = NUM ? Crp[row] : 0;
     int32_t cnt = 0;
     for (;;) {
-        const int32_t h0 = p0 < e0 ? Bci[p0] : INT32_MAX;
-        const int32_t h1 = p1 < e1 ? Bci[p1] : INT32_MAX;
-        const int32_t jmin = __reduce_min_sync(0xffffffffu, min(h0, h1));
-        if (jmin == INT32_MAX) break;
-        const bool m0 = h0 == jmin, m1 = h1 == jmin;
+        int32_t h[KMAX];
+        int32_t mn = INT32_MAX;
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) {
+            h[j] = (j < K && p[j] < e[j]) ? Bci[p[j]] : INT32_MAX;
+            mn = min(mn, h[j]);
+        }
+        if (S == 32) mn = __reduce_min_sync(0xffffffffu, mn);
+        else
+#pragma unroll
+            for (int o = S / 2; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(gmask, mn, o));
+        if (mn == INT32_MAX) break;
         if (NUM) {
-            const double q0 = m0 ? __dmul_rn(x0, Bv[p0]) : 0.0;
-            const double q1 = m1 ? __dmul_rn(x1, Bv[p1]) : 0.0;
-            unsigned b0 = __ballot_sync(0xffffffffu, m0), b1 = __ballot_sync(0xffffffffu, m1);
             double acc = 0.0;
-            while (b0) {
-                const int l = __ffs(b0) - 1;
-                acc = __dadd_rn(acc, __shfl_sync(0xffffffffu, q0, l));
-                b0 &= b0 - 1;
-            }
-            while (b1) {
-                const int l = __ffs(b1) - 1;
-                acc = __dadd_rn(acc, __shfl_sync(0xffffffffu, q1, l));
-                b1 &= b1 - 1;
-            }
-            if (lane == 0) { Cci_or_cnt[out] = jmin; Cv[out] = acc; }
+#pragma unroll
+            for (int j = 0; j < KMAX; ++j)
+                if (j < K) {
+                    const bool mt = h[j] == mn;
+                    const double q = mt ? __dmul_rn(x[j], Bv[p[j]]) : 0.0;
+                    unsigned bm = __ballot_sync(gmask, mt) & gmask;
+                    while (bm) {
+                        const int src = __ffs(bm) - 1;
+                        acc = __dadd_rn(acc, __shfl_sync(gmask, q, src));
+                        bm &= bm - 1;
+                    }
+                }
+            if (l == 0) { Cci_or_cnt[out] = mn; Cv[out] = acc; }
             ++out;
         }
-        if (m0) ++p0;
-        if (m1) ++p1;
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j)
+            if (j < K && h[j] == mn) ++p[j];
         ++cnt;
     }
-    if (!NUM && lane == 0) Cci_or_cnt[row] = cnt;
+    if (!NUM && l == 0) Cci_or_cnt[row] = cnt;
 }
 
 template <bool NUM>
-__global__ void __launch_bounds__(kMergeThreads) k_spgemm_merge(int32_t n, const int32_t *Arp, const int32_t *Aci,
-                                                                const double *Av, const int32_t *Brp,
-                                                                const int32_t *Bci, const double *Bv,
-                                                                const int32_t *Crp, int32_t *Cci_or_cnt, double *Cv,
-                                                                int32_t *err) {
-    extern __shared__ int32_t sm[];
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int32_t a0 = Arp[i], m = Arp[i + 1] - a0;
-    if (m <= kWarpMergeMax) return;            // done by k_spgemm_warp
-    if (m > kMergeMax) { atomicExch(err, 1); return; }
-    int32_t *pos = sm, *end = sm + kMergeMax * kMergeThreads;
-    const int t = threadIdx.x, T = kMergeThreads;
-    for (int q = 0; q < m; ++q) {
-        int32_t l = Aci[a0 + q];
-        pos[q * T + t] = Brp[l];
-        end[q * T + t] = Brp[l + 1];
-    }
-    int32_t out = NUM ? Crp[i] : 0;
-    int32_t cnt = 0;
-    for (;;) {
-        int32_t jmin = INT32_MAX;
-        for (int q = 0; q < m; ++q) {
-            int32_t p = pos[q * T + t];
-            if (p < end[q * T + t]) jmin = min(jmin, Bci[p]);
-        }
-        if (jmin == INT32_MAX) break;
-        double acc = 0.0;
-        for (int q = 0; q < m; ++q) {
-            int32_t p = pos[q * T + t];
-            if (p < end[q * T + t] && Bci[p] == jmin) {
-                if (NUM) acc = __dadd_rn(acc, __dmul_rn(Av[a0 + q], Bv[p]));
-                pos[q * T + t] = p + 1;
-            }
-        }
-        if (NUM) { Cci_or_cnt[out] = jmin; Cv[out] = acc; ++out; }
-        ++cnt;
-    }
-    if (!NUM) Cci_or_cnt[i] = cnt;
+static void launch_spgemm(Ctx *c, const Csr &A, const Csr &B, const int32_t *Crp, int32_t *Cci_or_cnt, double *Cv) {
+    (k_spgemm_grp<NUM, kGemmTinyS, kGemmTinyK><<<nblk((int64_t)A.n * kGemmTinyS, 256), 256, 0, c->stream>>>(
+         A.n, 0, kGemmTinyS * kGemmTinyK, A.rp, A.ci, A.v, B.rp, B.ci, B.v, Crp, Cci_or_cnt, Cv, c->flag),
+     note_launch());
+    (k_spgemm_grp<NUM, kGemmSmallS, kGemmSmallK><<<nblk((int64_t)A.n * kGemmSmallS, 256), 256, 0, c->stream>>>(
+         A.n, kGemmTinyS * kGemmTinyK, kGemmSmallS * kGemmSmallK, A.rp, A.ci, A.v, B.rp, B.ci, B.v, Crp, Cci_or_cnt, Cv, c->flag),
+     note_launch());
+    (k_spgemm_grp<NUM, 32, kGemmLargeK><<<nblk((int64_t)A.n * 32, 256), 256, 0, c->stream>>>(
+         A.n, kGemmSmallS * kGemmSmallK, kGemmMaxM, A.rp, A.ci, A.v, B.rp, B.ci, B.v, Crp, Cci_or_cnt, Cv, c->flag),
+     note_launch());
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -491,25 +486,19 @@ static cptr_status spgemm(Ctx *c, const Csr &A, const Csr &B, int32_t ncb, Csr &
     int32_t *cnt = nullptr;
     CPTR_TRY(dalloc_t(c, &cnt, (size_t)A.n + 1));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
-    size_t smem = sizeof(int32_t) * 2 * kMergeMax * kMergeThreads;
-    CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_spgemm_merge<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_spgemm_merge<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    (k_spgemm_warp<false><<<nblk((int64_t)A.n * 32, 256), 256, 0, c->stream>>>(
-        A.n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, nullptr, cnt, nullptr), note_launch());
-    (k_spgemm_merge<false><<<nblk(A.n, kMergeThreads), kMergeThreads, smem, c->stream>>>(
-        A.n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, nullptr, cnt, nullptr, c->flag), note_launch());
+    launch_spgemm<false>(c, A, B, nullptr, cnt, nullptr);
     int32_t total = 0;
     CPTR_TRY(scan_exclusive(c, cnt, C.rp, A.n, &total));
     int32_t bad = 0;
     CPTR_TRY(copy_to_host(c, &bad, c->flag, sizeof(int32_t)));
-    if (bad) return c->fail(CPTR_EINVAL, "AMG: a row of the Galerkin product merges more than 256 rows");
+    if (bad) {
+        dfree(cnt);
+        return c->fail(CPTR_EINVAL, "AMG: a row of the Galerkin product merges more than 256 rows");
+    }
     C.nnz = total;
     CPTR_TRY(dalloc_t(c, &C.ci, (size_t)total));
     CPTR_TRY(dalloc_t(c, &C.v, (size_t)total));
-    (k_spgemm_warp<true><<<nblk((int64_t)A.n * 32, 256), 256, 0, c->stream>>>(
-        A.n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp, C.ci, C.v), note_launch());
-    (k_spgemm_merge<true><<<nblk(A.n, kMergeThreads), kMergeThreads, smem, c->stream>>>(
-        A.n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp, C.ci, C.v, c->flag), note_launch());
+    launch_spgemm<true>(c, A, B, C.rp, C.ci, C.v);
     CPTR_CUDA_TRY(c, cudaGetLastError());
     dfree(cnt);
     (void)ncb;
@@ -648,9 +637,9 @@ cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, con
     h.dense = 0;
     double tc = host_ms();
     if (cn <= c->o.dense_max) {
-        // densified on the main stream; inverted on the side stream (one block on one SM), which
+        // densified on the main stream; inverted on the coarse stream (one block on one SM), which
         // overlaps the rest of the set-up; amg_coarsest_wait joins it before the inverse is used
-        if (!c->side_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+        if (!c->coarse_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->coarse_stream, cudaStreamNonBlocking));
         if (!c->side_fork) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&c->side_fork, cudaEventDisableTiming));
         if (!h.gj_done) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&h.gj_done, cudaEventDisableTiming));
         if (!h.gj_flag) CPTR_TRY(dalloc_t(c, &h.gj_flag, 1));
@@ -661,8 +650,8 @@ cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, con
         (k_densify<<<nblk(cn, 128), 128, 0, c->stream>>>(cn, C.A.rp, C.A.ci, C.A.v, D), note_launch());
         CPTR_CUDA_TRY(c, cudaMemsetAsync(h.gj_flag, 0, sizeof(int32_t), c->stream));
         CPTR_CUDA_TRY(c, cudaEventRecord(c->side_fork, c->stream));
-        CPTR_CUDA_TRY(c, cudaStreamWaitEvent(c->side_stream, c->side_fork, 0));
-        cudaStream_t ss = c->side_stream;
+        CPTR_CUDA_TRY(c, cudaStreamWaitEvent(c->coarse_stream, c->side_fork, 0));
+        cudaStream_t ss = c->coarse_stream;
         if (cn <= kGjSmemMax) {
             const size_t smem = sizeof(double) * ((size_t)cn * cn + cn) + sizeof(int32_t) * cn;
             CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_gauss_jordan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,

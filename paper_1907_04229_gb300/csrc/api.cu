@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <chrono>
 #include <new>
+#include <thread>
 
 #include "common.cuh"
 
@@ -197,10 +198,41 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
         setup_tick(c, SETUP_OTHER, &tl);
     }
     int s1 = c->o.stage1;
-    if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_setup(c, c->hp, c->rp, c->ci, c->App, n));
-    if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) CPTR_TRY(amg_setup(c, c->hT, c->rp, c->ci, c->St, n));
-    if (c->o.stage2 == CPTR_STAGE2_ILU0) CPTR_TRY(ilu_setup(c));
-    // the coarsest inverses ran on the side stream meanwhile
+    if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) {
+        // The two hierarchies are independent: the temperature one is built by a second host
+        // thread on its own stream (a context view with its own stream, scratch flag and scan
+        // buffer) while this thread builds the pressure one and then the ILU(0) factors.
+        if (!c->amg_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->amg_stream, cudaStreamNonBlocking));
+        if (!c->coarse_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->coarse_stream, cudaStreamNonBlocking));
+        if (!c->amg_fork) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&c->amg_fork, cudaEventDisableTiming));
+        Ctx w;
+        w.o = c->o;
+        w.stream = c->amg_stream;
+        w.pool = c->pool;
+        w.coarse_stream = c->coarse_stream;
+        w.side_fork = c->amg_fork;
+        CPTR_TRY(dalloc_t(c, &w.flag, 4));
+        CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // inputs and allocations are ready
+        cptr_status st_T = CPTR_OK;
+        std::thread worker([&] {
+            CtxScope ws(&w);
+            st_T = amg_setup(&w, c->hT, c->rp, c->ci, c->St, n);
+            dfree(w.scan_tmp);
+            w.scan_tmp = nullptr;
+            cudaStreamSynchronize(w.stream);
+        });
+        cptr_status st_p = amg_setup(c, c->hp, c->rp, c->ci, c->App, n);
+        if (st_p == CPTR_OK && c->o.stage2 == CPTR_STAGE2_ILU0) st_p = ilu_setup(c);
+        worker.join();
+        for (int q = 0; q < kSetupPhases; ++q) c->prof.setup_ms[q] += w.prof.setup_ms[q];
+        dfree(w.flag);
+        if (st_p != CPTR_OK) return st_p;
+        if (st_T != CPTR_OK) return c->fail(st_T, w.err);
+    } else {
+        if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_setup(c, c->hp, c->rp, c->ci, c->App, n));
+        if (c->o.stage2 == CPTR_STAGE2_ILU0) CPTR_TRY(ilu_setup(c));
+    }
+    // the coarsest inverses ran on the coarse stream meanwhile
     CPTR_TRY(amg_coarsest_wait(c, c->hp));
     CPTR_TRY(amg_coarsest_wait(c, c->hT));
     double t2 = host_ms();
@@ -402,6 +434,8 @@ void cptr_destroy(cptr_ctx *ctx) {
         CtxScope scope(c);
         cudaStreamSynchronize(c->stream);
         if (c->side_stream) cudaStreamSynchronize(c->side_stream);
+        if (c->coarse_stream) cudaStreamSynchronize(c->coarse_stream);
+        if (c->amg_stream) cudaStreamSynchronize(c->amg_stream);
         release_setup(c);
         dfree(c->ks); dfree(c->flag); dfree(c->partial); dfree(c->scan_tmp); dfree(c->never); dfree(c->ilu_flags);
         dfree(c->mlp);
@@ -412,7 +446,11 @@ void cptr_destroy(cptr_ctx *ctx) {
     for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->side_stream) cudaStreamDestroy(c->side_stream);
+    if (c->coarse_stream) cudaStreamDestroy(c->coarse_stream);
+    if (c->amg_stream) cudaStreamDestroy(c->amg_stream);
+    if (c->amg_fork) cudaEventDestroy(c->amg_fork);
     if (c->side_fork) cudaEventDestroy(c->side_fork);
+    if (c->side_join) cudaEventDestroy(c->side_join);
     for (Hier *h : {&c->hp, &c->hT})
         if (h->gj_done) cudaEventDestroy(h->gj_done);
     delete ctx;

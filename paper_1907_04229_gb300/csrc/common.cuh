@@ -90,9 +90,9 @@ struct Hier {
     double op_complexity = 0.0;
     int fuse_l0 = -1;                 // levels fuse_l0 .. nlev-2 run in the fused coarse kernels
     LevelDev *ldev64 = nullptr, *ldev32 = nullptr;   // device descriptors (FP64 / mixed cycle)
-    // the coarsest inverse runs on the context's side stream while the set-up goes on
+    // the coarsest inverse runs on the context's coarse stream while the set-up goes on
     int32_t *gj_flag = nullptr;       // singular coarsest matrix
-    cudaEvent_t gj_done = nullptr;    // recorded on the side stream after the inverse
+    cudaEvent_t gj_done = nullptr;    // recorded on the coarse stream after the inverse
     bool gj_pending = false;
 };
 
@@ -130,6 +130,7 @@ void begin_capture_count();  // launches noted on this thread while capturing ar
 int64_t end_capture_count(); // ...but returned here (the graph's kernel node count)
 enum { PF_SPMV = 0, PF_STAGE1 = 1, PF_RESID = 2, PF_ILU = 3, PF_ARNOLDI = 4, PF_ILU_FWD = 5, PF_ILU_BWD = 6,
        PF_N = 8 };
+constexpr int kSetupPhases = 8;
 struct Prof {
     uint32_t mask = 0;
     std::vector<cudaEvent_t> ev;   // pairs (begin, end)
@@ -139,7 +140,7 @@ struct Prof {
     std::vector<size_t> gslots;    // slots recorded inside the captured iteration graph
     double ms[PF_N] = {0};
     int64_t cnt[PF_N] = {0};
-    double setup_ms[8] = {0};      // set-up phases (host clock, after a stream sync): see SETUP_*
+    double setup_ms[kSetupPhases] = {0};   // set-up phases (host clock, after a stream sync): see SETUP_*
 };
 // set-up phases: inputs + decoupling + extraction; AMG coarsening (strength + PMIS + interp);
 // AMG Galerkin products (transpose + two SpGEMMs); AMG coarsest inverse; ILU host work (ordering,
@@ -208,7 +209,7 @@ cptr_status sell_autotune(Ctx *c);           // threads per block of the SELL Sp
 cptr_status ilu_autotune(Ctx *c);            // grid and poll back-off of the ILU(0) sweeps
 cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, const double *v, int32_t n);
 void amg_free(Hier &h);
-cptr_status amg_coarsest_wait(Ctx *c, Hier &h);   // join the side stream's coarsest inverse; its status
+cptr_status amg_coarsest_wait(Ctx *c, Hier &h);   // join the coarse stream's inverse; its status
 void amg_vcycle(const Ctx *c, const Hier &h, const double *b, double *x);
 void amg_vcycle32(const Ctx *c, const Hier &h, const float *b, float *x);
 cptr_status amg_lower_precision(Ctx *c, Hier &h);
@@ -312,7 +313,10 @@ struct Ctx {
     double *vcur = nullptr, *zcur = nullptr;           // fixed in/out vectors of the captured step
     cudaStream_t cap_stream = nullptr;
     cudaStream_t side_stream = nullptr;   // set-up work that overlaps the main stream
-    cudaEvent_t side_fork = nullptr;
+    cudaStream_t coarse_stream = nullptr; // the coarsest AMG inverses, overlapping the rest of the set-up
+    cudaStream_t amg_stream = nullptr;    // the second hierarchy, built by a second host thread
+    cudaEvent_t amg_fork = nullptr;
+    cudaEvent_t side_fork = nullptr, side_join = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int64_t graph_launches = 0;
     uint32_t graph_mask = 0;

@@ -1080,45 +1080,249 @@ __global__ void __launch_bounds__(64) k_bilu_factor_st(int32_t n, unsigned *tick
     }
 }
 
-// level sets of one direction: pos (position -> row), inv, and the level pointers (host)
-static cptr_status device_levels(Ctx *c, const int32_t *rp, const int32_t *ci, bool forward, int32_t *pos,
-                                 int32_t *inv, std::vector<int32_t> &h_lptr) {
-    const int32_t n = c->n;
-    cudaStream_t s = c->stream;
-    int32_t *lev = nullptr, *tk = nullptr;
-    CPTR_TRY(dalloc_t(c, &lev, (size_t)n));
-    CPTR_TRY(dalloc_t(c, &tk, 2));   // ticket, wait error
-    CPTR_CUDA_TRY(c, cudaMemsetAsync(lev, 0xFF, sizeof(int32_t) * n, s));
-    CPTR_CUDA_TRY(c, cudaMemsetAsync(tk, 0, 2 * sizeof(int32_t), s));
-    (k_levels_sf<<<std::min<unsigned>(nblk(n, 128), 8 * 152), 128, 0, s>>>(n, reinterpret_cast<unsigned *>(tk), rp, ci, lev,
-                                                                          forward ? 1 : 0, tk + 1), note_launch());
-    CPTR_CUDA_TRY(c, cudaGetLastError());
-    // stable counting sort by level on the host (rows of a level in ascending order keep the
-    // sweeps' accesses local): one sequential pass over the levels
-    std::vector<int32_t> hl(n), hp(n), hi(n);
-    int32_t werr = 0;
-    CPTR_CUDA_TRY(c, cudaMemcpyAsync(&werr, tk + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    const cptr_status cs = copy_to_host(c, hl.data(), lev, sizeof(int32_t) * n);
-    dfree(tk);
-    if (cs != CPTR_OK || werr) {
-        dfree(lev);
-        return cs != CPTR_OK ? cs : c->fail(CPTR_ETIMEOUT, "ILU(0) level sets: a bounded wait gave up");
+// In-place inverse of the pivot block by the four lanes of a row's group, lane r holding row r of
+// [D | I] (lanes r >= B only take part in the shuffles): Gauss-Jordan with partial pivoting, the
+// same operations and order as block_inverse (largest |d_rk| among the remaining rows, lowest row
+// on ties; the pivot row times 1 / pivot; every other row minus its multiple of the pivot row).
+// The rows are not moved: each lane keeps the index of the row it holds.  Returns false if
+// singular (the block is then left as it was).
+template <int B>
+__device__ __forceinline__ bool group_inverse(double *blk, int r, unsigned gmask, int g0) {
+    double a[2 * B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) a[q] = r < B ? blk[r * B + q] : 0.0;
+#pragma unroll
+    for (int q = 0; q < B; ++q) a[B + q] = (q == r) ? 1.0 : 0.0;
+    int ri = r;
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+        const bool cand = r < B && ri >= k;
+        double v = cand ? fabs(a[k]) : -1.0;
+        int idx = cand ? ri : 0x7fffffff;
+#pragma unroll
+        for (int o = 1; o < kSfGroup; o <<= 1) {
+            const double ov = __shfl_xor_sync(gmask, v, o);
+            const int oi = __shfl_xor_sync(gmask, idx, o);
+            if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+        }
+        if (!(v > 0.0)) return false;
+        const int p = idx;
+        if (r < B) {
+            if (ri == k) ri = p;
+            else if (ri == p) ri = k;
+        }
+        const unsigned pl = __ballot_sync(gmask, r < B && ri == k);
+        const int src = __ffs(pl) - 1;
+        if (r < B && ri == k) {
+            const double d = 1.0 / a[k];
+#pragma unroll
+            for (int q = 0; q < 2 * B; ++q) a[q] *= d;
+        }
+        double pr[2 * B];
+#pragma unroll
+        for (int q = 0; q < 2 * B; ++q) pr[q] = __shfl_sync(gmask, a[q], src);
+        if (r < B && ri != k) {
+            const double f = a[k];
+#pragma unroll
+            for (int q = 0; q < 2 * B; ++q) a[q] = fma(-f, pr[q], a[q]);
+        }
     }
+    __syncwarp(gmask);
+    if (r < B)
+#pragma unroll
+        for (int q = 0; q < B; ++q) blk[ri * B + q] = a[B + q];
+    (void)g0;
+    return true;
+}
+
+// The staged factorisation with a row over four lanes (B <= 4): lane r computes row r of every
+// block of the row (its B FMAs per entry of L_ik = A_ik D_k^{-1} and of each update A_ij -= L_ik
+// U_kj), so that a level's FP64 pipe time is a quarter of the one-thread-per-row form, and the
+// pivot block is inverted by the group together (group_inverse).  The copies of the staged
+// kernel are shared out over the lanes.  Same values as k_bilu_factor_sf.  Shared memory per row
+// as in k_bilu_factor_st; kSfRowsG rows per block.
+template <int B>
+__global__ void __launch_bounds__(kSfThreads) k_bilu_factor_g(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
+                                                             const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                                             const int32_t *__restrict__ diag, double *LU, int32_t *flag,
+                                                             int32_t epoch, int32_t *singular, KState *ks, int maxrow,
+                                                             int maxdep, int maxu) {
+    constexpr int BB = B * B, G = kSfGroup;
+    extern __shared__ __align__(16) unsigned char fs_smem[];
+    const int rowsz = (maxrow * BB + 1) & ~1;
+    const int W = ((1 + maxu) * BB + 2 + 1) & ~1;
+    const int per = rowsz + maxdep * W;
+    const int j = threadIdx.x / G, r = threadIdx.x & (G - 1);
+    const int g0 = (threadIdx.x & 31) & ~(G - 1);
+    const unsigned gmask = 0xFu << g0;
+    double *rowb = reinterpret_cast<double *>(fs_smem) + (int64_t)j * per;
+    double *depw = rowb + rowsz;
+    const int iper = maxrow + maxdep * (2 + maxu);
+    int32_t *cols = reinterpret_cast<int32_t *>(reinterpret_cast<double *>(fs_smem) + (int64_t)kSfRowsG * per) + j * iper;
+    int32_t *dcs = cols + maxrow, *ecs = dcs + maxdep, *ucol = ecs + maxdep;
+    __shared__ unsigned blk;
+    const unsigned nchunks = (unsigned)((n + kSfRowsG - 1) / kSfRowsG);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) blk = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const unsigned b = blk;
+        if (b >= nchunks) return;
+        const int32_t t = (int32_t)(b * kSfRowsG + j);
+        if (t >= n) continue;                       // the whole group
+        const int32_t i = pos[t];
+        const int32_t k0 = rp[i], e = rp[i + 1], kd = diag[i], len = e - k0, nd = kd - k0;
+        for (int32_t k = r; k < len; k += G) cp_async_i32(cols + k, ci + k0 + k);
+        cp_async_commit();
+        for (int32_t u = r; u < len * BB; u += G) cp_async_elem(rowb + u, LU + (int64_t)k0 * BB + u);
+        cp_async_commit();
+        cp_async_wait_1();
+        __syncwarp(gmask);
+        for (int32_t k = r; k < nd; k += G) {
+            const int32_t c = cols[k];
+            cp_async_i32(dcs + k, diag + c);
+            cp_async_i32(ecs + k, rp + c + 1);
+        }
+        cp_async_commit();
+        cp_async_wait_0();
+        __syncwarp(gmask);
+        for (int32_t k = 0; k < nd; ++k)
+            for (int32_t qq = dcs[k] + 1 + r; qq < ecs[k]; qq += G)
+                cp_async_i32(ucol + k * maxu + (qq - dcs[k] - 1), ci + qq);
+        cp_async_commit();
+        {
+            unsigned long long t0 = 0;
+            bool pending = true;
+            for (int round = 0; pending; ++round) {
+                pending = false;
+                for (int32_t k = 0; k < nd; ++k) {
+                    int32_t f;
+                    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flag + cols[k]) : "memory");
+                    pending |= f != epoch;
+                }
+                if (!pending) break;
+                if (round == 0) t0 = gtimer();
+                else if (gtimer() - t0 > kWaitNs) { atomicExch(&ks->wait_err, 1); break; }
+                __nanosleep(20);
+            }
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        }
+        for (int32_t k = 0; k < nd; ++k) {
+            const int64_t lo = (int64_t)dcs[k] * BB, hi = (int64_t)ecs[k] * BB;
+            const int64_t a0 = lo & ~(int64_t)1;
+            double *w = depw + (int64_t)k * W;
+            for (int64_t u = a0 + 2 * r; u < hi; u += 2 * G) cp_async_cg16(w + (u - a0), LU + u);
+        }
+        cp_async_commit();
+        cp_async_wait_0();
+        __syncwarp(gmask);
+        if (r < B) {
+            for (int32_t k = k0; k < kd; ++k) {
+                const int32_t dc = dcs[k - k0], ec = ecs[k - k0];
+                const double *dinv = depw + (int64_t)(k - k0) * W + (int)(((int64_t)dc * BB) & 1);
+                const int32_t *uc = ucol + (k - k0) * maxu;
+                double a[B], l[B];
+#pragma unroll
+                for (int q = 0; q < B; ++q) a[q] = rowb[(k - k0) * BB + r * B + q];
+#pragma unroll
+                for (int q = 0; q < B; ++q) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int u = 0; u < B; ++u) s = fma(a[u], dinv[u * B + q], s);
+                    l[q] = s;
+                }
+#pragma unroll
+                for (int q = 0; q < B; ++q) rowb[(k - k0) * BB + r * B + q] = l[q];
+                int32_t p = k + 1;
+                for (int32_t qq = dc + 1; qq < ec; ++qq) {
+                    const int32_t jj = uc[qq - dc - 1];
+                    while (p < e && cols[p - k0] < jj) ++p;
+                    if (p < e && cols[p - k0] == jj) {
+                        const double *u = dinv + (qq - dc) * BB;
+                        double *d = rowb + (p - k0) * BB + r * B;
+#pragma unroll
+                        for (int q = 0; q < B; ++q) {
+                            double s = d[q];
+#pragma unroll
+                            for (int w = 0; w < B; ++w) s = fma(-l[w], u[w * B + q], s);
+                            d[q] = s;
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp(gmask);
+        if (!group_inverse<B>(rowb + nd * BB, r, gmask, g0) && r == 0) atomicOr(singular, 1);
+        __syncwarp(gmask);
+        for (int32_t u = nd * BB + r; u < len * BB; u += G) LU[(int64_t)k0 * BB + u] = rowb[u];
+        __threadfence();
+        __syncwarp(gmask);
+        if (r == 0) asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(flag + i), "r"(epoch) : "memory");
+        for (int32_t u = r; u < nd * BB; u += G) LU[(int64_t)k0 * BB + u] = rowb[u];
+    }
+}
+
+// level sets of one direction: pos (position -> row), inv, and the level pointers (host)
+// stable counting sort of the rows by level on the host (rows of a level in ascending order keep
+// the sweeps' accesses local): positions -> rows, rows -> positions, level pointers
+static void sort_by_level(int32_t n, const std::vector<int32_t> &hl, std::vector<int32_t> &hp, std::vector<int32_t> &hi,
+                          std::vector<int32_t> &h_lptr) {
     int32_t nl = 0;
     for (int32_t i = 0; i < n; ++i) nl = std::max(nl, hl[i] + 1);
     h_lptr.assign(nl + 1, 0);
     for (int32_t i = 0; i < n; ++i) h_lptr[hl[i] + 1]++;
     for (int32_t l = 0; l < nl; ++l) h_lptr[l + 1] += h_lptr[l];
     std::vector<int32_t> cur(h_lptr.begin(), h_lptr.end() - 1);
+    hp.resize(n);
+    hi.resize(n);
     for (int32_t i = 0; i < n; ++i) {
         int32_t t = cur[hl[i]]++;
         hp[t] = i;
         hi[i] = t;
     }
-    CPTR_CUDA_TRY(c, cudaMemcpyAsync(pos, hp.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
-    CPTR_CUDA_TRY(c, cudaMemcpyAsync(inv, hi.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
-    CPTR_CUDA_TRY(c, cudaStreamSynchronize(s));
+}
+
+// level sets of both sweeps: the forward levels on the main stream and the backward ones on the
+// side stream at the same time (both launches are latency bound), then the two sorts
+static cptr_status device_levels(Ctx *c, const int32_t *rp, const int32_t *ci, int32_t *pos_f, int32_t *inv_f,
+                                 std::vector<int32_t> &lptr_f, int32_t *pos_b, int32_t *inv_b,
+                                 std::vector<int32_t> &lptr_b) {
+    const int32_t n = c->n;
+    cudaStream_t s = c->stream;
+    if (!c->side_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+    if (!c->side_fork) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&c->side_fork, cudaEventDisableTiming));
+    if (!c->side_join) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&c->side_join, cudaEventDisableTiming));
+    int32_t *lev = nullptr, *tk = nullptr;
+    CPTR_TRY(dalloc_t(c, &lev, 2 * (size_t)n));
+    CPTR_TRY(dalloc_t(c, &tk, 4));   // ticket and wait error of each direction
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(lev, 0xFF, sizeof(int32_t) * 2 * (size_t)n, s));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(tk, 0, 4 * sizeof(int32_t), s));
+    CPTR_CUDA_TRY(c, cudaEventRecord(c->side_fork, s));
+    CPTR_CUDA_TRY(c, cudaStreamWaitEvent(c->side_stream, c->side_fork, 0));
+    const unsigned grid = std::min<unsigned>(nblk(n, 128), 8 * 152);
+    (k_levels_sf<<<grid, 128, 0, s>>>(n, reinterpret_cast<unsigned *>(tk), rp, ci, lev, 1, tk + 1), note_launch());
+    (k_levels_sf<<<grid, 128, 0, c->side_stream>>>(n, reinterpret_cast<unsigned *>(tk + 2), rp, ci, lev + n, 0, tk + 3),
+     note_launch());
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    CPTR_CUDA_TRY(c, cudaEventRecord(c->side_join, c->side_stream));
+    CPTR_CUDA_TRY(c, cudaStreamWaitEvent(s, c->side_join, 0));
+    std::vector<int32_t> hl(2 * (size_t)n), hp, hi;
+    int32_t werr[4] = {0, 0, 0, 0};
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(werr, tk, sizeof(werr), cudaMemcpyDeviceToHost, s));
+    const cptr_status cs = copy_to_host(c, hl.data(), lev, sizeof(int32_t) * 2 * (size_t)n);
+    dfree(tk);
     dfree(lev);
+    CPTR_TRY(cs);
+    if (werr[1] || werr[3]) return c->fail(CPTR_ETIMEOUT, "ILU(0) level sets: a bounded wait gave up");
+    std::vector<int32_t> hlf(hl.begin(), hl.begin() + n), hlb(hl.begin() + n, hl.end());
+    sort_by_level(n, hlf, hp, hi, lptr_f);
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(pos_f, hp.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(inv_f, hi.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(s));
+    sort_by_level(n, hlb, hp, hi, lptr_b);
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(pos_b, hp.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(inv_b, hi.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(s));
     return CPTR_OK;
 }
 
@@ -1458,8 +1662,7 @@ cptr_status ilu_setup(Ctx *c) {
     CPTR_TRY(dalloc_t(c, &c->lvl_b, (size_t)n));
     CPTR_TRY(dalloc_t(c, &inv_f, (size_t)n));
     CPTR_TRY(dalloc_t(c, &inv_b, (size_t)n));
-    CPTR_TRY(device_levels(c, c->ilu_rp, c->ilu_ci, true, c->lvl_f, inv_f, c->h_lptr_f));
-    CPTR_TRY(device_levels(c, c->ilu_rp, c->ilu_ci, false, c->lvl_b, inv_b, c->h_lptr_b));
+    CPTR_TRY(device_levels(c, c->ilu_rp, c->ilu_ci, c->lvl_f, inv_f, c->h_lptr_f, c->lvl_b, inv_b, c->h_lptr_b));
     c->nlev_f = (int32_t)c->h_lptr_f.size() - 1;
     c->nlev_b = (int32_t)c->h_lptr_b.size() - 1;
     CPTR_TRY(dalloc_t(c, &c->ybuf, (size_t)n * c->b));
@@ -1499,7 +1702,21 @@ cptr_status ilu_setup(Ctx *c) {
     const size_t fs_rowsz = (size_t)((maxrow * BB + 1) & ~1), fs_w = (size_t)(((1 + maxu) * BB + 3) & ~1);
     const size_t fs_bytes = (size_t)64 * ((fs_rowsz + (size_t)maxdep * fs_w) * 8 + (size_t)(maxrow + maxdep * (2 + maxu)) * 4);
     const unsigned fgrid = std::min<unsigned>(nblk(n, 64), 8 * 152);
-    if (fs_bytes <= 100 * 1024) {
+    const size_t fg_bytes = fs_bytes / 64 * kSfRowsG;   // the same per row, kSfRowsG rows per block
+    if (fg_bytes <= 100 * 1024) {
+        const unsigned ggrid = std::min<unsigned>(nblk(n, kSfRowsG), (unsigned)std::min<size_t>(8, 200 * 1024 / fg_bytes) * 152);
+        if (c->b == 3) {
+            cudaFuncSetAttribute(k_bilu_factor_g<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fg_bytes);
+            (k_bilu_factor_g<3><<<ggrid, kSfThreads, fg_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
+                                                                      c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch,
+                                                                      c->flag, c->ks, maxrow, maxdep, maxu), note_launch());
+        } else {
+            cudaFuncSetAttribute(k_bilu_factor_g<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fg_bytes);
+            (k_bilu_factor_g<4><<<ggrid, kSfThreads, fg_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
+                                                                      c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch,
+                                                                      c->flag, c->ks, maxrow, maxdep, maxu), note_launch());
+        }
+    } else if (fs_bytes <= 100 * 1024) {
         const unsigned sgrid = std::min<unsigned>(nblk(n, 64), 2 * 152);
         if (c->b == 3) {
             cudaFuncSetAttribute(k_bilu_factor_st<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs_bytes);
