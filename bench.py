@@ -351,6 +351,8 @@ def ours(args, rank, world, local_rank):
                           "solver": {"autotune": bool(args.autotune), "ilu_sweep": args.ilu_sweep,
                                      "ilu_schedule_used": "chunked wavefront" if chunked else "level sets",
                                      "ilu_sweep_tuning": [t for t in cp.cptr_tuning(S.ctx) if t[2] in (4, 5)],
+                                     "amg_shapes_hier_level_kernel_G_T": [t for t in cp.cptr_tuning(S.ctx)
+                                                                          if t[2] in (0, 1, 2)],
                                      "tuning_note": "launch shapes timed at the first (warm-up) set-up and cached "
                                                     "by operator size; timed steps reuse them"},
                           "l2": "flushed before every step (256 MB write); working set > 1 GB"},

@@ -202,13 +202,15 @@ cptr_status cptr_hierarchy_level(cptr_ctx *ctx, int32_t which, int32_t l, int32_
 cptr_status cptr_apply_ilu_static(cptr_ctx *ctx, const double *r, double *z);
 
 /* Launch shapes in use (an engineering addition; the paper has none).  Writes up to cap rows of 5
- * int32 into rows (host): {hierarchy (0 A_pp, 1 S~_T, 2 A'), level, kernel (0 smoother + residual,
- * 1 restriction P^T, 2 prolongation P, 3 SELL SpMV of A'), lanes per row (0 = chosen from the
- * average row length), threads per block}; *n_rows receives the number of rows available.  With
- * autotune set, cptr_setup times for every operator G in {2, 4, 8, 16, 32} lanes x T in {128, 256,
- * 512} threads (the SELL kernels: T in {64, 128, 256, 512}), 5 launches each after a warm-up, and
- * keeps the fastest; results are cached in the context by operator size.  Shapes change only the
- * order of the partial sums within a row.  Errors: CPTR_ESTATE, CPTR_EINVAL. */
+ * int32 into rows (host): {hierarchy (0 A_pp, 1 S~_T, 2 A', 3 ILU(0)), level, kernel (0 smoother +
+ * residual, 1 restriction P^T, 2 prolongation P, 3 SELL SpMV of A', 4 ILU(0) sweeps, 5 ILU(0)
+ * schedule), lanes per row (0 = chosen from the average row length; kernel 4: back-off between
+ * polls in ns; kernel 5: 1 chunked wavefront, 0 level sets), threads per block (kernel 4: blocks of
+ * the persistent grid)}; *n_rows receives the number of rows available.  With autotune set,
+ * cptr_setup times for every operator G in {1, 2, 4, 8, 16, 32} lanes x T in {128, 256, 512}
+ * threads (the SELL kernels: T in {64, 128, 256, 512}), 5 launches each after a warm-up, and keeps
+ * the fastest; results are cached in the context by operator size.  Shapes change only the order
+ * of the partial sums within a row.  Errors: CPTR_ESTATE, CPTR_EINVAL. */
 cptr_status cptr_tuning(cptr_ctx *ctx, int32_t *rows, int32_t cap, int32_t *n_rows);
 
 /* Number of ILU level sets of the forward and backward sweeps (host ints). */

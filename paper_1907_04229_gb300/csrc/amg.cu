@@ -790,6 +790,7 @@ static void launch_down(cudaStream_t s, const Level &L, const VT *v, const XT *d
     unsigned grid = nblk((int64_t)L.A.n * G, T);
     const Csr &A = L.A;
     switch (G) {
+    case 1: (k_vc_down<1, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
     case 2: (k_vc_down<2, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
     case 4: (k_vc_down<4, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
     case 8: (k_vc_down<8, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
@@ -803,6 +804,7 @@ static void launch_post(cudaStream_t s, const Level &L, const VT *v, const XT *d
     unsigned grid = nblk((int64_t)L.A.n * G, T);
     const Csr &A = L.A;
     switch (G) {
+    case 1: (k_vc_post<1, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
     case 2: (k_vc_post<2, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
     case 4: (k_vc_post<4, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
     case 8: (k_vc_post<8, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
@@ -1027,11 +1029,13 @@ cptr_status amg_lower_precision(Ctx *c, Hier &h) {
 // ------------------------------------------------------------------------------------------------
 // Autotuner of the V-cycle kernels.  For every non-coarsest level and each of its three kernels
 // (smoother + residual on A, restriction P^T, prolongation P), every launch shape G in
-// {2, 4, 8, 16, 32} lanes per row x T in {128, 256, 512} threads per block is timed with CUDA
+// {1, 2, 4, 8, 16, 32} lanes per row x T in {128, 256, 512} threads per block is timed with CUDA
 // events over 5 launches after one warm-up launch, on the level's own work vectors and in the
 // precision the cycle uses; the fastest is kept.  Shapes are cached by (kernel, rows, entries,
 // storage), so repeated set-ups of one workload tune once.  The shapes change only the order of
-// the partial sums inside a row (lanes), never which entries are summed.
+// the partial sums inside a row (lanes), never which entries are summed.  In FP64 one lane per row
+// often wins on GB300: every step of a cross-lane reduction is a warp-wide FP64 addition, and a
+// warp-wide FP64 instruction occupies a sub-partition's FP64 pipe for 64 cycles.
 namespace {
 template <typename F>
 Shape pick_shape(Ctx *c, uint64_t key, F &&launch) {
@@ -1042,7 +1046,7 @@ Shape pick_shape(Ctx *c, uint64_t key, F &&launch) {
     cudaEventCreate(&e1);
     Shape best;
     float best_ms = 1e30f;
-    for (int G : {2, 4, 8, 16, 32})
+    for (int G : {1, 2, 4, 8, 16, 32})
         for (int T : {128, 256, 512}) {
             Shape sh;
             sh.G = (int16_t)G;

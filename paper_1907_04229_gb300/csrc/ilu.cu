@@ -1299,7 +1299,7 @@ static cptr_status device_levels(Ctx *c, const int32_t *rp, const int32_t *ci, i
     CPTR_CUDA_TRY(c, cudaMemsetAsync(tk, 0, 4 * sizeof(int32_t), s));
     CPTR_CUDA_TRY(c, cudaEventRecord(c->side_fork, s));
     CPTR_CUDA_TRY(c, cudaStreamWaitEvent(c->side_stream, c->side_fork, 0));
-    const unsigned grid = std::min<unsigned>(nblk(n, 128), 8 * 152);
+    const unsigned grid = std::min<unsigned>(nblk(n, 128), 2 * 152);
     (k_levels_sf<<<grid, 128, 0, s>>>(n, reinterpret_cast<unsigned *>(tk), rp, ci, lev, 1, tk + 1), note_launch());
     (k_levels_sf<<<grid, 128, 0, c->side_stream>>>(n, reinterpret_cast<unsigned *>(tk + 2), rp, ci, lev + n, 0, tk + 3),
      note_launch());

@@ -453,6 +453,7 @@ void launch_csr_spmv_t(cudaStream_t s, int32_t n, int32_t nnz, const int32_t *rp
     const int G = sh.G ? sh.G : lanes_for(n, nnz), T = sh.T;
     unsigned grid = nblk((int64_t)n * G, T);
     switch (G) {
+    case 1: (k_csr_spmv<1, VT, XT><<<grid, T, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
     case 2: (k_csr_spmv<2, VT, XT><<<grid, T, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
     case 4: (k_csr_spmv<4, VT, XT><<<grid, T, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
     case 8: (k_csr_spmv<8, VT, XT><<<grid, T, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;

@@ -45,7 +45,7 @@ def test_tuned_solve_matches_untuned(precision):
         elif k == 5:       # ILU sweeps: chunked wavefront chosen (1) or level sets (0)
             assert h == 3 and G in (0, 1)
         else:
-            assert G in (2, 4, 8, 16, 32) and T in (128, 256, 512)
+            assert G in (1, 2, 4, 8, 16, 32) and T in (128, 256, 512)
     # untuned: heuristic lanes, 256 threads; level-set sweeps on 608 blocks, 20 ns back-off
     for h, l, k, G, T in cp.cptr_tuning(a.ctx):
         assert (G, T) == {4: (20, 608), 5: (0, 0)}.get(k, (0, 256))
