@@ -75,7 +75,7 @@ typedef struct {
     int32_t max_levels;  /* AMG levels including the coarsest (default 25) */
     int32_t restart;     /* FGMRES restart length m (default 30, at most 32) */
     int32_t max_it;      /* total Arnoldi steps (default 1000) */
-    int32_t dense_max;   /* coarsest level solved densely if n <= dense_max (default 1024) */
+    int32_t dense_max;   /* coarsest level solved densely if n <= dense_max (default 1024, at most 25600) */
     int32_t seed;        /* PMIS weights: SplitMix64 stream seed + level */
     int32_t precision;   /* CPTR_PREC_* */
     int32_t check_every; /* host reads the convergence flag every k Arnoldi steps (default 1) */

@@ -383,6 +383,8 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(int32_t n, double *a, dou
 // the whole matrix held in shared memory; the row exchanges are undone at the end as column
 // exchanges in reverse order, so that the result is A^{-1}.
 constexpr int kGjSmemMax = 160;
+constexpr int kGjSmemBytes = (kGjSmemMax * kGjSmemMax + kGjSmemMax) * 8 + kGjSmemMax * 4;
+constexpr int kGjFacBytes = 200 * 1024;     // the pivot-column buffer of k_gauss_jordan: n <= 25600 (dense_max)
 __global__ void __launch_bounds__(1024) k_gauss_jordan_smem(int32_t n, const double *a_in, double *inv,
                                                             int32_t *singular) {
     extern __shared__ double gj[];
@@ -652,15 +654,17 @@ cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, con
         CPTR_CUDA_TRY(c, cudaEventRecord(c->side_fork, c->stream));
         CPTR_CUDA_TRY(c, cudaStreamWaitEvent(c->coarse_stream, c->side_fork, 0));
         cudaStream_t ss = c->coarse_stream;
+        // the shared-memory limits are set to the largest size any call uses, so that the two
+        // host threads of the set-up, which may run this at the same time, set the same values
         if (cn <= kGjSmemMax) {
             const size_t smem = sizeof(double) * ((size_t)cn * cn + cn) + sizeof(int32_t) * cn;
             CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_gauss_jordan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)smem));
+                                                  kGjSmemBytes));
             (k_gauss_jordan_smem<<<1, 1024, smem, ss>>>(cn, D, h.cinv, h.gj_flag), note_launch());
         } else {
             const size_t smem = sizeof(double) * (size_t)(cn > 0 ? cn : 1);
-            if (smem > 48 * 1024)
-                CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  kGjFacBytes));
             (k_gauss_jordan<<<1, 1024, smem, ss>>>(cn, D, h.cinv, h.gj_flag), note_launch());
         }
         CPTR_CUDA_TRY(c, cudaGetLastError());

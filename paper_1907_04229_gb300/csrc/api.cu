@@ -382,7 +382,7 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
     cptr_options o;
     if (opt) o = *opt;
     else cptr_default_options(&o);
-    if (o.restart < 1 || o.restart > kMaxRestart || o.max_it < 0 || o.max_levels < 1 || o.dense_max < 1 ||
+    if (o.restart < 1 || o.restart > kMaxRestart || o.max_it < 0 || o.max_levels < 1 || o.dense_max < 1 || o.dense_max > 25600 ||
         o.stage1 < 0 || o.stage1 > CPTR_STAGE1_NONE || o.stage2 < 0 || o.stage2 > CPTR_STAGE2_NONE ||
         o.smoother < 0 || o.smoother > CPTR_SMOOTH_JACOBI || o.schur < CPTR_SCHUR_GIVEN ||
         o.schur > CPTR_SCHUR_LEARNED || o.precision < CPTR_PREC_FP64 ||

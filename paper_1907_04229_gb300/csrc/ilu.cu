@@ -365,30 +365,92 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_sf(int32_t n, unsigned *
 constexpr int kSfGroup = 4;                          // lanes per row
 constexpr int kSfRowsG = kSfThreads / kSfGroup;      // rows per block chunk
 
-// s -= sum over the dependency slots [o0, o1) of row q of block(slot) * value(dep(slot))
+// The rows of a warp advance in lockstep rounds: in each round every unfinished group checks the
+// dependency values loaded in the previous round (one L2 round trip), reloads those still holding
+// the sentinel, and the groups whose values are all present do their FMAs together, so that a
+// warp issues each FP64 instruction once per round rather than once per row that happens to have
+// diverged from the others.  No group ever waits for another one (a group that is ready computes
+// in the same round), so rows of one warp may depend on each other.  State of a lane: its
+// component s of the row, and the dependency slots [sl0, sl0 + kDepGroup) in flight.
 template <int B, typename T>
-__device__ __forceinline__ T subtract_deps_row(T s, int q4, int64_t o0, int64_t o1, int lane,
-                                               const int32_t *__restrict__ col, const T *__restrict__ val,
-                                               const T *vec, KState *ks, int sleep_ns) {
-    for (int64_t sl0 = o0; sl0 < o1; sl0 += kDepGroup) {
-        int32_t c[kDepGroup];
+struct SweepLane {
+    int64_t sl0, o1;
+    int32_t c[kDepGroup];
+    T a[kDepGroup][B];
+    T v[kDepGroup][B];
+    T s;
+    unsigned long long t0;
+    bool waiting;
+};
+
+// columns, row q4 of the blocks, and the first loads of the values of slots [sl0, sl0 + kDepGroup)
+template <int B, typename T>
+__device__ __forceinline__ void sweep_stage(SweepLane<B, T> &L, int q4, int lane, const int32_t *__restrict__ col,
+                                            const T *__restrict__ val, const T *vec) {
 #pragma unroll
-        for (int g = 0; g < kDepGroup; ++g) c[g] = (sl0 + g < o1) ? __ldg(col + (sl0 + g) * 32 + lane) : -1;
-        T a[kDepGroup][B];
+    for (int g = 0; g < kDepGroup; ++g) L.c[g] = (L.sl0 + g < L.o1) ? __ldg(col + (L.sl0 + g) * 32 + lane) : -1;
 #pragma unroll
-        for (int g = 0; g < kDepGroup; ++g)
-            if (c[g] >= 0)
+    for (int g = 0; g < kDepGroup; ++g)
+        if (L.c[g] >= 0)
 #pragma unroll
-                for (int q = 0; q < B; ++q) a[g][q] = __ldg(val + ((sl0 + g) * B * B + q4 * B + q) * 32 + lane);
-        T v[kDepGroup][B];
-        load_group<B, T>(vec, c, v, ks, sleep_ns);
+            for (int q = 0; q < B; ++q) {
+                L.a[g][q] = __ldg(val + ((L.sl0 + g) * B * B + q4 * B + q) * 32 + lane);
+                L.v[g][q] = load_relaxed(vec + (int64_t)L.c[g] * B + q);
+            }
+}
+
+// One round of a group that is not finished: returns true once all its slots are subtracted.
+// *pend tells whether the group still waits on a value after this round.
+template <int B, typename T>
+__device__ __forceinline__ bool sweep_round(SweepLane<B, T> &L, int q4, int lane, unsigned gmask,
+                                            const int32_t *__restrict__ col, const T *__restrict__ val,
+                                            const T *vec, KState *ks, bool *pend) {
+    bool p = false;
 #pragma unroll
-        for (int g = 0; g < kDepGroup; ++g)
-            if (c[g] >= 0)
+    for (int g = 0; g < kDepGroup; ++g)
+        if (L.c[g] >= 0)
 #pragma unroll
-                for (int q = 0; q < B; ++q) s = fma(-a[g][q], v[g][q], s);
+            for (int q = 0; q < B; ++q) p |= is_sentinel(L.v[g][q]);
+    p = __any_sync(gmask, p);
+    if (p) {
+        bool late = false;
+        if (!L.waiting) {
+            L.t0 = gtimer();
+            L.waiting = true;
+        } else {
+            late = gtimer() - L.t0 > kWaitNs;
+        }
+        if (__any_sync(gmask, late)) {   // the bounded wait gives up: missing values count as 0
+            atomicExch(&ks->wait_err, 1);
+#pragma unroll
+            for (int g = 0; g < kDepGroup; ++g)
+#pragma unroll
+                for (int q = 0; q < B; ++q)
+                    if (is_sentinel(L.v[g][q])) L.v[g][q] = (T)0;
+        } else {
+#pragma unroll
+            for (int g = 0; g < kDepGroup; ++g)
+                if (L.c[g] >= 0)
+#pragma unroll
+                    for (int q = 0; q < B; ++q)
+                        if (is_sentinel(L.v[g][q])) L.v[g][q] = load_relaxed(vec + (int64_t)L.c[g] * B + q);
+            *pend = true;
+            return false;
+        }
     }
-    return s;
+    L.waiting = false;
+#pragma unroll
+    for (int g = 0; g < kDepGroup; ++g)
+        if (L.c[g] >= 0)
+#pragma unroll
+            for (int q = 0; q < B; ++q) L.s = fma(-L.a[g][q], L.v[g][q], L.s);
+    L.sl0 += kDepGroup;
+    if (L.sl0 < L.o1) {
+        sweep_stage<B, T>(L, q4, lane, col, val, vec);
+        *pend = true;
+        return false;
+    }
+    return true;
 }
 
 template <int B, typename T, typename RT>
@@ -399,6 +461,8 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_g(int32_t n, unsigned *t
     __shared__ unsigned blk;
     const unsigned nchunks = (unsigned)((n + kSfRowsG - 1) / kSfRowsG);
     const int q4 = threadIdx.x & (kSfGroup - 1);
+    const int g0 = (threadIdx.x & 31) & ~(kSfGroup - 1);
+    const unsigned gmask = ((1u << B) - 1u) << g0;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) blk = atomicAdd(ticket, 1u);
@@ -406,13 +470,30 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_g(int32_t n, unsigned *t
         const unsigned b = blk;
         if (b >= nchunks) return;
         const int32_t t = (int32_t)(b * kSfRowsG + threadIdx.x / kSfGroup);
-        if (t >= n || q4 >= B) continue;
+        bool done = t >= n || q4 >= B;
         if (never && t == 0 && q4 == 0) (void)wait_value(never, ks);  // failure injection
-        const int32_t ch = t >> 5, lane = t & 31;
-        const int32_t row = __ldg(pos + t);
-        T s = (T)__ldg(r + (int64_t)row * B + q4);
-        s = subtract_deps_row<B, T>(s, q4, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, y, ks, sleep_ns);
-        store_relaxed(y + (int64_t)t * B + q4, s);
+        SweepLane<B, T> L;
+        const int32_t lane = t & 31;
+        if (!done) {
+            const int32_t ch = t >> 5;
+            L.s = (T)__ldg(r + (int64_t)__ldg(pos + t) * B + q4);
+            L.sl0 = __ldg(off + ch);
+            L.o1 = __ldg(off + ch + 1);
+            L.waiting = false;
+            if (L.sl0 < L.o1) sweep_stage<B, T>(L, q4, lane, col, val, y);
+            else {
+                store_relaxed(y + (int64_t)t * B + q4, L.s);
+                done = true;
+            }
+        }
+        while (__any_sync(0xffffffffu, !done)) {
+            bool pend = false;
+            if (!done && sweep_round<B, T>(L, q4, lane, gmask, col, val, y, ks, &pend)) {
+                store_relaxed(y + (int64_t)t * B + q4, L.s);
+                done = true;
+            }
+            if (__any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
+        }
     }
 }
 
@@ -427,8 +508,8 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_g(int32_t n, unsigned *t
     __shared__ unsigned blk;
     const unsigned nchunks = (unsigned)((n + kSfRowsG - 1) / kSfRowsG);
     const int q4 = threadIdx.x & (kSfGroup - 1);
-    const unsigned gmask = ((1u << B) - 1u) << ((threadIdx.x & 31) & ~(kSfGroup - 1));
     const int g0 = (threadIdx.x & 31) & ~(kSfGroup - 1);
+    const unsigned gmask = ((1u << B) - 1u) << g0;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) blk = atomicAdd(ticket + 1, 1u);
@@ -436,24 +517,41 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_g(int32_t n, unsigned *t
         const unsigned b = blk;
         if (b >= nchunks) return;
         const int32_t t = (int32_t)(b * kSfRowsG + threadIdx.x / kSfGroup);
-        if (t >= n || q4 >= B) continue;
-        const int32_t ch = t >> 5, lane = t & 31;
-        const int32_t row = __ldg(pos + t);
-        const int32_t tf = __ldg(bmap + t);
-        T s = __ldcg(y + (int64_t)tf * B + q4);
-        // row q4 of the inverted pivot block does not depend on other rows: load it first
+        bool done = t >= n || q4 >= B;
+        SweepLane<B, T> L;
+        const int32_t lane = t & 31;
         T dv[B];
-#pragma unroll
-        for (int q = 0; q < B; ++q) dv[q] = __ldg(dinv + ((int64_t)ch * B * B + q4 * B + q) * 32 + lane);
-        s = subtract_deps_row<B, T>(s, q4, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, z, ks, sleep_ns);
-        T a = 0;
-#pragma unroll
-        for (int q = 0; q < B; ++q) a = fma(dv[q], __shfl_sync(gmask, s, g0 + q), a);
-        store_relaxed(z + (int64_t)t * B + q4, a);
+        bool fin = false;
+        int32_t row = 0;
         double add = 0.0;
-        if (dp && q4 == ps) add = (double)dp[row];
-        if (dT && q4 == ts) add = (double)dT[row];
-        out[(int64_t)row * B + q4] = (double)a + add;
+        if (!done) {
+            const int32_t ch = t >> 5;
+            // inputs that do not depend on other rows are loaded before the rounds
+            row = __ldg(pos + t);
+            if (dp && q4 == ps) add = (double)dp[row];
+            if (dT && q4 == ts) add = (double)dT[row];
+            L.s = __ldcg(y + (int64_t)__ldg(bmap + t) * B + q4);
+            // row q4 of the inverted pivot block does not depend on other rows: load it first
+#pragma unroll
+            for (int q = 0; q < B; ++q) dv[q] = __ldg(dinv + ((int64_t)ch * B * B + q4 * B + q) * 32 + lane);
+            L.sl0 = __ldg(off + ch);
+            L.o1 = __ldg(off + ch + 1);
+            L.waiting = false;
+            if (L.sl0 < L.o1) sweep_stage<B, T>(L, q4, lane, col, val, z);
+            else fin = true;
+        }
+        while (__any_sync(0xffffffffu, !done)) {
+            bool pend = false;
+            if (!done && (fin || sweep_round<B, T>(L, q4, lane, gmask, col, val, z, ks, &pend))) {
+                T a = 0;
+#pragma unroll
+                for (int q = 0; q < B; ++q) a = fma(dv[q], __shfl_sync(gmask, L.s, g0 + q), a);
+                store_relaxed(z + (int64_t)t * B + q4, a);
+                out[(int64_t)row * B + q4] = (double)a + add;
+                done = true;
+            }
+            if (__any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
+        }
     }
 }
 
@@ -1169,96 +1267,124 @@ __global__ void __launch_bounds__(kSfThreads) k_bilu_factor_g(int32_t n, unsigne
         const unsigned b = blk;
         if (b >= nchunks) return;
         const int32_t t = (int32_t)(b * kSfRowsG + j);
-        if (t >= n) continue;                       // the whole group
-        const int32_t i = pos[t];
-        const int32_t k0 = rp[i], e = rp[i + 1], kd = diag[i], len = e - k0, nd = kd - k0;
-        for (int32_t k = r; k < len; k += G) cp_async_i32(cols + k, ci + k0 + k);
-        cp_async_commit();
-        for (int32_t u = r; u < len * BB; u += G) cp_async_elem(rowb + u, LU + (int64_t)k0 * BB + u);
-        cp_async_commit();
-        cp_async_wait_1();
-        __syncwarp(gmask);
-        for (int32_t k = r; k < nd; k += G) {
-            const int32_t c = cols[k];
-            cp_async_i32(dcs + k, diag + c);
-            cp_async_i32(ecs + k, rp + c + 1);
+        bool done = t >= n;                         // the whole group
+        int32_t i = 0, k0 = 0, e = 0, kd = 0, len = 0, nd = 0;
+        if (!done) {
+            i = pos[t];
+            k0 = rp[i];
+            e = rp[i + 1];
+            kd = diag[i];
+            len = e - k0;
+            nd = kd - k0;
+            for (int32_t k = r; k < len; k += G) cp_async_i32(cols + k, ci + k0 + k);
+            cp_async_commit();
+            for (int32_t u = r; u < len * BB; u += G) cp_async_elem(rowb + u, LU + (int64_t)k0 * BB + u);
+            cp_async_commit();
+            cp_async_wait_1();
+            __syncwarp(gmask);
+            for (int32_t k = r; k < nd; k += G) {
+                const int32_t c = cols[k];
+                cp_async_i32(dcs + k, diag + c);
+                cp_async_i32(ecs + k, rp + c + 1);
+            }
+            cp_async_commit();
+            cp_async_wait_0();
+            __syncwarp(gmask);
+            for (int32_t k = 0; k < nd; ++k)
+                for (int32_t qq = dcs[k] + 1 + r; qq < ecs[k]; qq += G)
+                    cp_async_i32(ucol + k * maxu + (qq - dcs[k] - 1), ci + qq);
+            cp_async_commit();
         }
-        cp_async_commit();
-        cp_async_wait_0();
-        __syncwarp(gmask);
-        for (int32_t k = 0; k < nd; ++k)
-            for (int32_t qq = dcs[k] + 1 + r; qq < ecs[k]; qq += G)
-                cp_async_i32(ucol + k * maxu + (qq - dcs[k] - 1), ci + qq);
-        cp_async_commit();
-        {
-            unsigned long long t0 = 0;
-            bool pending = true;
-            for (int round = 0; pending; ++round) {
-                pending = false;
+        // Lockstep rounds over the warp (as in the sweeps): every unfinished group reads its
+        // dependency flags once per round; the groups whose flags are all set factor their rows
+        // in that round, together.  No group waits for another one.
+        unsigned long long t0 = 0;
+        bool waiting = false;
+        while (__any_sync(0xffffffffu, !done)) {
+            bool pend = false;
+            if (!done) {
+                bool p = false;
                 for (int32_t k = 0; k < nd; ++k) {
                     int32_t f;
                     asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flag + cols[k]) : "memory");
-                    pending |= f != epoch;
+                    p |= f != epoch;
                 }
-                if (!pending) break;
-                if (round == 0) t0 = gtimer();
-                else if (gtimer() - t0 > kWaitNs) { atomicExch(&ks->wait_err, 1); break; }
-                __nanosleep(20);
-            }
-            asm volatile("fence.acq_rel.gpu;" ::: "memory");
-        }
-        for (int32_t k = 0; k < nd; ++k) {
-            const int64_t lo = (int64_t)dcs[k] * BB, hi = (int64_t)ecs[k] * BB;
-            const int64_t a0 = lo & ~(int64_t)1;
-            double *w = depw + (int64_t)k * W;
-            for (int64_t u = a0 + 2 * r; u < hi; u += 2 * G) cp_async_cg16(w + (u - a0), LU + u);
-        }
-        cp_async_commit();
-        cp_async_wait_0();
-        __syncwarp(gmask);
-        if (r < B) {
-            for (int32_t k = k0; k < kd; ++k) {
-                const int32_t dc = dcs[k - k0], ec = ecs[k - k0];
-                const double *dinv = depw + (int64_t)(k - k0) * W + (int)(((int64_t)dc * BB) & 1);
-                const int32_t *uc = ucol + (k - k0) * maxu;
-                double a[B], l[B];
-#pragma unroll
-                for (int q = 0; q < B; ++q) a[q] = rowb[(k - k0) * BB + r * B + q];
-#pragma unroll
-                for (int q = 0; q < B; ++q) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int u = 0; u < B; ++u) s = fma(a[u], dinv[u * B + q], s);
-                    l[q] = s;
-                }
-#pragma unroll
-                for (int q = 0; q < B; ++q) rowb[(k - k0) * BB + r * B + q] = l[q];
-                int32_t p = k + 1;
-                for (int32_t qq = dc + 1; qq < ec; ++qq) {
-                    const int32_t jj = uc[qq - dc - 1];
-                    while (p < e && cols[p - k0] < jj) ++p;
-                    if (p < e && cols[p - k0] == jj) {
-                        const double *u = dinv + (qq - dc) * BB;
-                        double *d = rowb + (p - k0) * BB + r * B;
-#pragma unroll
-                        for (int q = 0; q < B; ++q) {
-                            double s = d[q];
-#pragma unroll
-                            for (int w = 0; w < B; ++w) s = fma(-l[w], u[w * B + q], s);
-                            d[q] = s;
-                        }
+                p = __any_sync(gmask, p);
+                if (p) {
+                    bool late = false;
+                    if (!waiting) {
+                        t0 = gtimer();
+                        waiting = true;
+                    } else {
+                        late = gtimer() - t0 > kWaitNs;
+                    }
+                    if (__any_sync(gmask, late)) {
+                        if (r == 0) atomicExch(&ks->wait_err, 1);
+                        p = false;
+                    } else {
+                        pend = true;
                     }
                 }
+                if (!p) {
+                    // one acquire fence orders the copies of the dependencies' blocks after the flags
+                    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                    for (int32_t k = 0; k < nd; ++k) {
+                        const int64_t lo = (int64_t)dcs[k] * BB, hi = (int64_t)ecs[k] * BB;
+                        const int64_t a0 = lo & ~(int64_t)1;
+                        double *w = depw + (int64_t)k * W;
+                        for (int64_t u = a0 + 2 * r; u < hi; u += 2 * G) cp_async_cg16(w + (u - a0), LU + u);
+                    }
+                    cp_async_commit();
+                    cp_async_wait_0();
+                    __syncwarp(gmask);
+                    if (r < B) {
+                        for (int32_t k = k0; k < kd; ++k) {
+                            const int32_t dc = dcs[k - k0], ec = ecs[k - k0];
+                            const double *dinv = depw + (int64_t)(k - k0) * W + (int)(((int64_t)dc * BB) & 1);
+                            const int32_t *uc = ucol + (k - k0) * maxu;
+                            double a[B], l[B];
+#pragma unroll
+                            for (int q = 0; q < B; ++q) a[q] = rowb[(k - k0) * BB + r * B + q];
+#pragma unroll
+                            for (int q = 0; q < B; ++q) {
+                                double sacc = 0.0;
+#pragma unroll
+                                for (int u = 0; u < B; ++u) sacc = fma(a[u], dinv[u * B + q], sacc);
+                                l[q] = sacc;
+                            }
+#pragma unroll
+                            for (int q = 0; q < B; ++q) rowb[(k - k0) * BB + r * B + q] = l[q];
+                            int32_t p2 = k + 1;
+                            for (int32_t qq = dc + 1; qq < ec; ++qq) {
+                                const int32_t jj = uc[qq - dc - 1];
+                                while (p2 < e && cols[p2 - k0] < jj) ++p2;
+                                if (p2 < e && cols[p2 - k0] == jj) {
+                                    const double *u = dinv + (qq - dc) * BB;
+                                    double *d = rowb + (p2 - k0) * BB + r * B;
+#pragma unroll
+                                    for (int q = 0; q < B; ++q) {
+                                        double sacc = d[q];
+#pragma unroll
+                                        for (int w2 = 0; w2 < B; ++w2) sacc = fma(-l[w2], u[w2 * B + q], sacc);
+                                        d[q] = sacc;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    __syncwarp(gmask);
+                    if (!group_inverse<B>(rowb + nd * BB, r, gmask, g0) && r == 0) atomicOr(singular, 1);
+                    __syncwarp(gmask);
+                    for (int32_t u = nd * BB + r; u < len * BB; u += G) LU[(int64_t)k0 * BB + u] = rowb[u];
+                    __threadfence();
+                    __syncwarp(gmask);
+                    if (r == 0) asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(flag + i), "r"(epoch) : "memory");
+                    for (int32_t u = r; u < nd * BB; u += G) LU[(int64_t)k0 * BB + u] = rowb[u];
+                    done = true;
+                }
             }
+            if (__any_sync(0xffffffffu, pend)) __nanosleep(20);
         }
-        __syncwarp(gmask);
-        if (!group_inverse<B>(rowb + nd * BB, r, gmask, g0) && r == 0) atomicOr(singular, 1);
-        __syncwarp(gmask);
-        for (int32_t u = nd * BB + r; u < len * BB; u += G) LU[(int64_t)k0 * BB + u] = rowb[u];
-        __threadfence();
-        __syncwarp(gmask);
-        if (r == 0) asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(flag + i), "r"(epoch) : "memory");
-        for (int32_t u = r; u < nd * BB; u += G) LU[(int64_t)k0 * BB + u] = rowb[u];
     }
 }
 
@@ -1299,7 +1425,7 @@ static cptr_status device_levels(Ctx *c, const int32_t *rp, const int32_t *ci, i
     CPTR_CUDA_TRY(c, cudaMemsetAsync(tk, 0, 4 * sizeof(int32_t), s));
     CPTR_CUDA_TRY(c, cudaEventRecord(c->side_fork, s));
     CPTR_CUDA_TRY(c, cudaStreamWaitEvent(c->side_stream, c->side_fork, 0));
-    const unsigned grid = std::min<unsigned>(nblk(n, 128), 2 * 152);
+    const unsigned grid = std::min<unsigned>(nblk(n, 128), 8 * 152);
     (k_levels_sf<<<grid, 128, 0, s>>>(n, reinterpret_cast<unsigned *>(tk), rp, ci, lev, 1, tk + 1), note_launch());
     (k_levels_sf<<<grid, 128, 0, c->side_stream>>>(n, reinterpret_cast<unsigned *>(tk + 2), rp, ci, lev + n, 0, tk + 3),
      note_launch());
@@ -1706,12 +1832,12 @@ cptr_status ilu_setup(Ctx *c) {
     if (fg_bytes <= 100 * 1024) {
         const unsigned ggrid = std::min<unsigned>(nblk(n, kSfRowsG), (unsigned)std::min<size_t>(8, 200 * 1024 / fg_bytes) * 152);
         if (c->b == 3) {
-            cudaFuncSetAttribute(k_bilu_factor_g<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fg_bytes);
+            cudaFuncSetAttribute(k_bilu_factor_g<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
             (k_bilu_factor_g<3><<<ggrid, kSfThreads, fg_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
                                                                       c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch,
                                                                       c->flag, c->ks, maxrow, maxdep, maxu), note_launch());
         } else {
-            cudaFuncSetAttribute(k_bilu_factor_g<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fg_bytes);
+            cudaFuncSetAttribute(k_bilu_factor_g<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
             (k_bilu_factor_g<4><<<ggrid, kSfThreads, fg_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
                                                                       c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch,
                                                                       c->flag, c->ks, maxrow, maxdep, maxu), note_launch());
@@ -1719,12 +1845,12 @@ cptr_status ilu_setup(Ctx *c) {
     } else if (fs_bytes <= 100 * 1024) {
         const unsigned sgrid = std::min<unsigned>(nblk(n, 64), 2 * 152);
         if (c->b == 3) {
-            cudaFuncSetAttribute(k_bilu_factor_st<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs_bytes);
+            cudaFuncSetAttribute(k_bilu_factor_st<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
             (k_bilu_factor_st<3><<<sgrid, 64, fs_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
                                                               c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch, c->flag,
                                                               c->ks, maxrow, maxdep, maxu), note_launch());
         } else {
-            cudaFuncSetAttribute(k_bilu_factor_st<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs_bytes);
+            cudaFuncSetAttribute(k_bilu_factor_st<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
             (k_bilu_factor_st<4><<<sgrid, 64, fs_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
                                                               c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch, c->flag,
                                                               c->ks, maxrow, maxdep, maxu), note_launch());
