@@ -54,7 +54,7 @@ def parse():
                    help="run the three-phase section on an NX NY NZ box instead of 200x200x50 (profiling)")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="fixed launch shapes in the headline solver (default: autotuned at the first set-up, cached)")
-    p.add_argument("--ilu-sweep", choices=["auto", "levels", "chunked"], default="auto",
+    p.add_argument("--ilu-sweep", choices=["auto", "levels", "chunked", "paired"], default="auto",
                    help="schedule of the headline solver's ILU(0) sweeps")
     p.add_argument("--ensemble-total", type=float, default=4e6,
                    help="total cells of the ensemble (profiling runs use a smaller one)")
@@ -237,12 +237,15 @@ def ours(args, rank, world, local_rank):
     # (largest total time) is reported as "roofline"
     peak, peak_kind = peaks()
     alg = algorithmic_bytes(s)
-    chunked = [t for t in cp.cptr_tuning(S.ctx) if t[2] == 5][0][3] == 1
+    schedule = [t for t in cp.cptr_tuning(S.ctx) if t[2] == 5][0][3]
+    chunked, paired = schedule == 1, schedule == 2
     kernels = {"spmv": "k_sell_spmv<3,0> (outer w = A' z_j)", "stage1_resid": "k_sell_spmv<3,2> (stage-1 residual)",
                "ilu_fwd": ("k_ilu_cw<3,...,FWD> (forward ILU(0) sweep, chunked wavefront)" if chunked else
-                           "k_ilu_fwd_g<3> (forward ILU(0) sweep, level sets, a row over 4 lanes)"),
+                           "k_ilu_fwd_g<3> (forward ILU(0) sweep, %s, a row over 4 lanes)"
+                           % ("paired levels" if paired else "level sets")),
                "ilu_bwd": ("k_ilu_cw<3,...,BWD> (backward ILU(0) sweep, chunked wavefront)" if chunked else
-                           "k_ilu_bwd_g<3> (backward ILU(0) sweep, level sets, a row over 4 lanes)")}
+                           "k_ilu_bwd_g<3> (backward ILU(0) sweep, %s, a row over 4 lanes)"
+                           % ("paired levels" if paired else "level sets"))}
     lines = {}
     for fam, kname in kernels.items():
         ms_tot, cnt = prof_sum[fam]
@@ -262,7 +265,9 @@ def ours(args, rank, world, local_rank):
     dominant = max(("ilu_fwd", "ilu_bwd", "spmv", "stage1_resid"), key=lambda f: prof_sum[f][0])
     roofline = dict(lines[dominant])
     if dominant.startswith("ilu"):
-        roofline["note"] = (f"latency bound: a dependency chain of {ilu_levels} level sets per sweep"
+        roofline["note"] = ((f"latency bound: a dependency chain of {ilu_levels} level sets per sweep, "
+                             f"run as {(ilu_levels + 1) // 2} steps of paired levels" if paired else
+                             f"latency bound: a dependency chain of {ilu_levels} level sets per sweep")
                             + ("; DRAM traffic equals the algorithmic bytes" if roofline["traffic"] else ""))
     families = {k: {"ms_per_step": round(v[0] / args.steps, 3), "regions_per_step": v[1] / args.steps}
                 for k, v in prof_sum.items()}
@@ -349,7 +354,8 @@ def ours(args, rank, world, local_rank):
                                       "rtol 1e-6, FP64",
                           "step": "cptr_setup + cptr_solve", "parallelism": f"replicas x{world}",
                           "solver": {"autotune": bool(args.autotune), "ilu_sweep": args.ilu_sweep,
-                                     "ilu_schedule_used": "chunked wavefront" if chunked else "level sets",
+                                     "ilu_schedule_used": ("chunked wavefront" if chunked else
+                                                           "paired levels" if paired else "level sets"),
                                      "ilu_sweep_tuning": [t for t in cp.cptr_tuning(S.ctx) if t[2] in (4, 5)],
                                      "amg_shapes_hier_level_kernel_G_T": [t for t in cp.cptr_tuning(S.ctx)
                                                                           if t[2] in (0, 1, 2)],

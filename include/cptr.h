@@ -83,11 +83,14 @@ typedef struct {
     int32_t ilu_order;   /* CPTR_ILU_NATURAL (default) or CPTR_ILU_MULTICOLOR */
     int32_t autotune;    /* 1: time the launch shapes of the V-cycle and SpMV kernels at set-up
                             and keep the fastest (see cptr_tuning); 0 (default): fixed shapes */
-    int32_t ilu_sweep;   /* schedule of the ILU(0) triangular sweeps (same values either way):
-                            0 (default) level sets, or, with autotune, the faster of level sets
-                            and the chunked wavefront where the pattern allows it (natural order,
-                            at most 4 dependencies per row, levels no wider than 256 rows inside a
-                            chunk); 1 level sets; 2 chunked wavefront where allowed */
+    int32_t ilu_sweep;   /* schedule of the ILU(0) triangular sweeps: 0 (default) level sets, or,
+                            with autotune, the fastest of level sets, paired levels and the chunked
+                            wavefront where the pattern allows them; 1 level sets; 2 chunked
+                            wavefront (natural order, at most 4 dependencies per row, levels no
+                            wider than 256 rows inside a chunk; same values as level sets);
+                            3 paired levels (FP64 only, at most 32 dependencies per paired row: a
+                            row of odd level substitutes its dependencies of the level before, so
+                            two levels run as one; values differ from level sets by rounding) */
     void *stream;        /* cudaStream_t for all work; NULL = the legacy default stream */
 } cptr_options;
 
@@ -205,7 +208,7 @@ cptr_status cptr_apply_ilu_static(cptr_ctx *ctx, const double *r, double *z);
  * int32 into rows (host): {hierarchy (0 A_pp, 1 S~_T, 2 A', 3 ILU(0)), level, kernel (0 smoother +
  * residual, 1 restriction P^T, 2 prolongation P, 3 SELL SpMV of A', 4 ILU(0) sweeps, 5 ILU(0)
  * schedule), lanes per row (0 = chosen from the average row length; kernel 4: back-off between
- * polls in ns; kernel 5: 1 chunked wavefront, 0 level sets), threads per block (kernel 4: blocks of
+ * polls in ns; kernel 5: 0 level sets, 1 chunked wavefront, 2 paired levels), threads per block (kernel 4: blocks of
  * the persistent grid)}; *n_rows receives the number of rows available.  With autotune set,
  * cptr_setup times for every operator G in {1, 2, 4, 8, 16, 32} lanes x T in {128, 256, 512}
  * threads (the SELL kernels: T in {64, 128, 256, 512}), 5 launches each after a warm-up, and keeps

@@ -26,7 +26,7 @@ MLP_FEATURES, MLP_HIDDEN, MLP_NPARAM = 16, 64, 5313
 SMOOTHER = {"l1": 0, "jacobi": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 ILU_ORDER = {"natural": 0, "multicolor": 1}
-ILU_SWEEP = {"auto": 0, "levels": 1, "chunked": 2}
+ILU_SWEEP = {"auto": 0, "levels": 1, "chunked": 2, "paired": 3}
 U_P, U_T, U_SAT = 0, 1, 2
 
 

@@ -387,7 +387,7 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
         o.smoother < 0 || o.smoother > CPTR_SMOOTH_JACOBI || o.schur < CPTR_SCHUR_GIVEN ||
         o.schur > CPTR_SCHUR_LEARNED || o.precision < CPTR_PREC_FP64 ||
         o.precision > CPTR_PREC_MIXED ||
-        o.ilu_order < CPTR_ILU_NATURAL || o.ilu_order > CPTR_ILU_MULTICOLOR || o.ilu_sweep < 0 || o.ilu_sweep > 2)
+        o.ilu_order < CPTR_ILU_NATURAL || o.ilu_order > CPTR_ILU_MULTICOLOR || o.ilu_sweep < 0 || o.ilu_sweep > 3)
         return CPTR_EINVAL;
     cptr_ctx *ctx = new (std::nothrow) cptr_ctx();
     if (!ctx) return CPTR_ENOMEM;
@@ -679,7 +679,7 @@ cptr_status cptr_tuning(cptr_ctx *ctx, int32_t *rows, int32_t cap, int32_t *n_ro
         isw.T = (int16_t)c->sf_grid;
         add(3, 0, 4, isw);
         Shape chosen;
-        chosen.G = c->cw_use ? 1 : 0;
+        chosen.G = c->cw_use ? 1 : (c->sp_use ? 2 : 0);
         chosen.T = 0;
         add(3, 0, 5, chosen);
         *n_rows = (int32_t)(out.size() / 5);

@@ -371,46 +371,46 @@ constexpr int kSfRowsG = kSfThreads / kSfGroup;      // rows per block chunk
 // warp issues each FP64 instruction once per round rather than once per row that happens to have
 // diverged from the others.  No group ever waits for another one (a group that is ready computes
 // in the same round), so rows of one warp may depend on each other.  State of a lane: its
-// component s of the row, and the dependency slots [sl0, sl0 + kDepGroup) in flight.
-template <int B, typename T>
+// component s of the row, and the dependency slots [sl0, sl0 + DG) in flight (DG = 4 for the
+// level-set tables, 8 for the paired-level ones, whose rows have up to 6 dependencies on a 3-D grid).
+template <int B, typename T, int DG>
 struct SweepLane {
     int64_t sl0, o1;
-    int32_t c[kDepGroup];
-    T a[kDepGroup][B];
-    T v[kDepGroup][B];
+    int32_t c[DG];
+    T a[DG][B];
+    T pv[DG];      // component q4 of each dependency's value: each lane of a row polls its own
     T s;
     unsigned long long t0;
     bool waiting;
 };
 
-// columns, row q4 of the blocks, and the first loads of the values of slots [sl0, sl0 + kDepGroup)
-template <int B, typename T>
-__device__ __forceinline__ void sweep_stage(SweepLane<B, T> &L, int q4, int lane, const int32_t *__restrict__ col,
+// columns, row q4 of the blocks, and the first loads of component q4 of the values of slots
+// [sl0, sl0 + DG)
+template <int B, typename T, int DG>
+__device__ __forceinline__ void sweep_stage(SweepLane<B, T, DG> &L, int q4, int lane, const int32_t *__restrict__ col,
                                             const T *__restrict__ val, const T *vec) {
 #pragma unroll
-    for (int g = 0; g < kDepGroup; ++g) L.c[g] = (L.sl0 + g < L.o1) ? __ldg(col + (L.sl0 + g) * 32 + lane) : -1;
+    for (int g = 0; g < DG; ++g) L.c[g] = (L.sl0 + g < L.o1) ? __ldg(col + (L.sl0 + g) * 32 + lane) : -1;
 #pragma unroll
-    for (int g = 0; g < kDepGroup; ++g)
-        if (L.c[g] >= 0)
+    for (int g = 0; g < DG; ++g)
+        if (L.c[g] >= 0) {
 #pragma unroll
-            for (int q = 0; q < B; ++q) {
-                L.a[g][q] = __ldg(val + ((L.sl0 + g) * B * B + q4 * B + q) * 32 + lane);
-                L.v[g][q] = load_relaxed(vec + (int64_t)L.c[g] * B + q);
-            }
+            for (int q = 0; q < B; ++q) L.a[g][q] = __ldg(val + ((L.sl0 + g) * B * B + q4 * B + q) * 32 + lane);
+            L.pv[g] = load_relaxed(vec + (int64_t)L.c[g] * B + q4);
+        }
 }
 
 // One round of a group that is not finished: returns true once all its slots are subtracted.
-// *pend tells whether the group still waits on a value after this round.
-template <int B, typename T>
-__device__ __forceinline__ bool sweep_round(SweepLane<B, T> &L, int q4, int lane, unsigned gmask,
+// *pend tells whether the group still waits on a value after this round.  The lanes of a row
+// poll one component each; once all are present, each lane takes the others' by shuffles.
+template <int B, typename T, int DG>
+__device__ __forceinline__ bool sweep_round(SweepLane<B, T, DG> &L, int q4, int lane, unsigned gmask, int g0,
                                             const int32_t *__restrict__ col, const T *__restrict__ val,
                                             const T *vec, KState *ks, bool *pend) {
     bool p = false;
 #pragma unroll
-    for (int g = 0; g < kDepGroup; ++g)
-        if (L.c[g] >= 0)
-#pragma unroll
-            for (int q = 0; q < B; ++q) p |= is_sentinel(L.v[g][q]);
+    for (int g = 0; g < DG; ++g)
+        if (L.c[g] >= 0) p |= is_sentinel(L.pv[g]);
     p = __any_sync(gmask, p);
     if (p) {
         bool late = false;
@@ -423,41 +423,55 @@ __device__ __forceinline__ bool sweep_round(SweepLane<B, T> &L, int q4, int lane
         if (__any_sync(gmask, late)) {   // the bounded wait gives up: missing values count as 0
             atomicExch(&ks->wait_err, 1);
 #pragma unroll
-            for (int g = 0; g < kDepGroup; ++g)
-#pragma unroll
-                for (int q = 0; q < B; ++q)
-                    if (is_sentinel(L.v[g][q])) L.v[g][q] = (T)0;
+            for (int g = 0; g < DG; ++g)
+                if (is_sentinel(L.pv[g])) L.pv[g] = (T)0;
         } else {
 #pragma unroll
-            for (int g = 0; g < kDepGroup; ++g)
-                if (L.c[g] >= 0)
-#pragma unroll
-                    for (int q = 0; q < B; ++q)
-                        if (is_sentinel(L.v[g][q])) L.v[g][q] = load_relaxed(vec + (int64_t)L.c[g] * B + q);
+            for (int g = 0; g < DG; ++g)
+                if (L.c[g] >= 0 && is_sentinel(L.pv[g])) L.pv[g] = load_relaxed(vec + (int64_t)L.c[g] * B + q4);
             *pend = true;
             return false;
         }
     }
     L.waiting = false;
 #pragma unroll
-    for (int g = 0; g < kDepGroup; ++g)
+    for (int g = 0; g < DG; ++g)
         if (L.c[g] >= 0)
 #pragma unroll
-            for (int q = 0; q < B; ++q) L.s = fma(-L.a[g][q], L.v[g][q], L.s);
-    L.sl0 += kDepGroup;
+            for (int q = 0; q < B; ++q) L.s = fma(-L.a[g][q], __shfl_sync(gmask, L.pv[g], g0 + q), L.s);
+    L.sl0 += DG;
     if (L.sl0 < L.o1) {
-        sweep_stage<B, T>(L, q4, lane, col, val, vec);
+        sweep_stage<B, T, DG>(L, q4, lane, col, val, vec);
         *pend = true;
         return false;
     }
     return true;
 }
 
-template <int B, typename T, typename RT>
+// the part of a paired row's equation that needs no other row's result: s -= sum over the slots
+// [coff[ch], coff[ch+1]) of row q4 of block(slot) * src(source(slot)) (none for other rows)
+template <int B, typename T, typename ST>
+__device__ __forceinline__ T pair_terms(T s, int q4, int32_t ch, int lane, const int64_t *__restrict__ coff,
+                                        const int32_t *__restrict__ ccol, const T *__restrict__ cval,
+                                        const ST *__restrict__ src) {
+    if (!coff) return s;
+    const int64_t c1 = __ldg(coff + ch + 1);
+    for (int64_t sl = __ldg(coff + ch); sl < c1; ++sl) {
+        const int32_t k = __ldg(ccol + sl * 32 + lane);
+        if (k < 0) continue;
+#pragma unroll
+        for (int u = 0; u < B; ++u) s = fma(-__ldg(cval + (sl * B * B + q4 * B + u) * 32 + lane), (T)src[(int64_t)k * B + u], s);
+    }
+    return s;
+}
+
+template <int B, typename T, typename RT, int DG>
 __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_g(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
                                                          const int64_t *__restrict__ off, const int32_t *__restrict__ col,
                                                          const T *__restrict__ val, const RT *__restrict__ r, T *y,
-                                                         KState *ks, const double *never, int sleep_ns) {
+                                                         KState *ks, const double *never, int sleep_ns,
+                                                         const int64_t *__restrict__ coff,
+                                                         const int32_t *__restrict__ ccol, const T *__restrict__ cval) {
     __shared__ unsigned blk;
     const unsigned nchunks = (unsigned)((n + kSfRowsG - 1) / kSfRowsG);
     const int q4 = threadIdx.x & (kSfGroup - 1);
@@ -472,15 +486,16 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_g(int32_t n, unsigned *t
         const int32_t t = (int32_t)(b * kSfRowsG + threadIdx.x / kSfGroup);
         bool done = t >= n || q4 >= B;
         if (never && t == 0 && q4 == 0) (void)wait_value(never, ks);  // failure injection
-        SweepLane<B, T> L;
+        SweepLane<B, T, DG> L;
         const int32_t lane = t & 31;
         if (!done) {
             const int32_t ch = t >> 5;
             L.s = (T)__ldg(r + (int64_t)__ldg(pos + t) * B + q4);
+            L.s = pair_terms<B, T, RT>(L.s, q4, ch, lane, coff, ccol, cval, r);
             L.sl0 = __ldg(off + ch);
             L.o1 = __ldg(off + ch + 1);
             L.waiting = false;
-            if (L.sl0 < L.o1) sweep_stage<B, T>(L, q4, lane, col, val, y);
+            if (L.sl0 < L.o1) sweep_stage<B, T, DG>(L, q4, lane, col, val, y);
             else {
                 store_relaxed(y + (int64_t)t * B + q4, L.s);
                 done = true;
@@ -488,7 +503,7 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_g(int32_t n, unsigned *t
         }
         while (__any_sync(0xffffffffu, !done)) {
             bool pend = false;
-            if (!done && sweep_round<B, T>(L, q4, lane, gmask, col, val, y, ks, &pend)) {
+            if (!done && sweep_round<B, T, DG>(L, q4, lane, gmask, g0, col, val, y, ks, &pend)) {
                 store_relaxed(y + (int64_t)t * B + q4, L.s);
                 done = true;
             }
@@ -497,14 +512,16 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_g(int32_t n, unsigned *t
     }
 }
 
-template <int B, typename T, typename XT>
+template <int B, typename T, typename XT, int DG>
 __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_g(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
                                                          const int32_t *__restrict__ bmap,
                                                          const int64_t *__restrict__ off, const int32_t *__restrict__ col,
                                                          const T *__restrict__ val, const T *__restrict__ dinv,
                                                          const T *__restrict__ y, T *z, double *__restrict__ out,
                                                          int ps, int ts, const XT *__restrict__ dp,
-                                                         const XT *__restrict__ dT, KState *ks, int sleep_ns) {
+                                                         const XT *__restrict__ dT, KState *ks, int sleep_ns,
+                                                         const int64_t *__restrict__ coff,
+                                                         const int32_t *__restrict__ ccol, const T *__restrict__ cval) {
     __shared__ unsigned blk;
     const unsigned nchunks = (unsigned)((n + kSfRowsG - 1) / kSfRowsG);
     const int q4 = threadIdx.x & (kSfGroup - 1);
@@ -518,7 +535,7 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_g(int32_t n, unsigned *t
         if (b >= nchunks) return;
         const int32_t t = (int32_t)(b * kSfRowsG + threadIdx.x / kSfGroup);
         bool done = t >= n || q4 >= B;
-        SweepLane<B, T> L;
+        SweepLane<B, T, DG> L;
         const int32_t lane = t & 31;
         T dv[B];
         bool fin = false;
@@ -531,18 +548,19 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_g(int32_t n, unsigned *t
             if (dp && q4 == ps) add = (double)dp[row];
             if (dT && q4 == ts) add = (double)dT[row];
             L.s = __ldcg(y + (int64_t)__ldg(bmap + t) * B + q4);
+            L.s = pair_terms<B, T, T>(L.s, q4, ch, lane, coff, ccol, cval, y);
             // row q4 of the inverted pivot block does not depend on other rows: load it first
 #pragma unroll
             for (int q = 0; q < B; ++q) dv[q] = __ldg(dinv + ((int64_t)ch * B * B + q4 * B + q) * 32 + lane);
             L.sl0 = __ldg(off + ch);
             L.o1 = __ldg(off + ch + 1);
             L.waiting = false;
-            if (L.sl0 < L.o1) sweep_stage<B, T>(L, q4, lane, col, val, z);
+            if (L.sl0 < L.o1) sweep_stage<B, T, DG>(L, q4, lane, col, val, z);
             else fin = true;
         }
         while (__any_sync(0xffffffffu, !done)) {
             bool pend = false;
-            if (!done && (fin || sweep_round<B, T>(L, q4, lane, gmask, col, val, z, ks, &pend))) {
+            if (!done && (fin || sweep_round<B, T, DG>(L, q4, lane, gmask, g0, col, val, z, ks, &pend))) {
                 T a = 0;
 #pragma unroll
                 for (int q = 0; q < B; ++q) a = fma(dv[q], __shfl_sync(gmask, L.s, g0 + q), a);
@@ -1412,7 +1430,7 @@ static void sort_by_level(int32_t n, const std::vector<int32_t> &hl, std::vector
 // side stream at the same time (both launches are latency bound), then the two sorts
 static cptr_status device_levels(Ctx *c, const int32_t *rp, const int32_t *ci, int32_t *pos_f, int32_t *inv_f,
                                  std::vector<int32_t> &lptr_f, int32_t *pos_b, int32_t *inv_b,
-                                 std::vector<int32_t> &lptr_b) {
+                                 std::vector<int32_t> &lptr_b, int32_t *levr_f, int32_t *levr_b) {
     const int32_t n = c->n;
     cudaStream_t s = c->stream;
     if (!c->side_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
@@ -1441,6 +1459,9 @@ static cptr_status device_levels(Ctx *c, const int32_t *rp, const int32_t *ci, i
     CPTR_TRY(cs);
     if (werr[1] || werr[3]) return c->fail(CPTR_ETIMEOUT, "ILU(0) level sets: a bounded wait gave up");
     std::vector<int32_t> hlf(hl.begin(), hl.begin() + n), hlb(hl.begin() + n, hl.end());
+    // the level of every row, for the paired-level tables
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(levr_f, hlf.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(levr_b, hlb.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     sort_by_level(n, hlf, hp, hi, lptr_f);
     CPTR_CUDA_TRY(c, cudaMemcpyAsync(pos_f, hp.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     CPTR_CUDA_TRY(c, cudaMemcpyAsync(inv_f, hi.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
@@ -1720,15 +1741,243 @@ static void cw_free(Ctx *c) {
     c->cw_use = false;
 }
 
-// key of the sweeps' tuning in the context's cache, and whether a cached tuning chose the
-// level-set schedule (then a set-up with autotune needs no chunked tables)
+// ------------------------------------------------------------------------------------------------
+// Paired-level tables.  In each sweep a row i of odd level L (the sweep's own level numbering)
+// replaces every dependency k of level L - 1 by that row's own equation, so that it depends only
+// on rows of level <= L - 2 and is solved together with the rows of level L - 1: the chain of
+// dependent steps halves.  K1 denotes the dependencies of level L - 1, K0 the others.
+//   forward, y = L^{-1} r:   y_i = c_i - sum_j M_ij y_j,  c_i = r_i - sum_{k in K1} L_ik r_k,
+//                             M_ij = [j in K0] L_ij - sum_{k in K1} L_ik L_kj;
+//   backward, z = U^{-1} y:   z_i = D_i^{-1} (c_i - sum_j M_ij z_j),  c_i = y_i - sum_{k in K1} P_ik y_k,
+//                             P_ik = U_ik D_k^{-1},  M_ij = [j in K0] U_ij - sum_{k in K1} P_ik U_kj
+// (D_k^{-1} is the stored inverted pivot block).  Mathematically these are the same solves; the
+// sums are grouped differently, so values differ from the level-set sweeps by rounding only.
+// Rows of even level keep their own entries.  The entries of a paired row are ordered by
+// dependency position; each M_ij starts from the K0 block (or zero) and subtracts the products in
+// the row's pattern order; the c_i terms follow the row's pattern order.
+constexpr int kPairMax = 32;   // dependencies of a paired row; more and the tables are not built
+
+template <int B>
+__device__ __forceinline__ void pair_factor(const double *__restrict__ LU, int32_t k, int32_t dk, int lower,
+                                            double *pk) {   // L_ik, or U_ik D_k^{-1}
+    constexpr int BB = B * B;
+    if (lower) {
+        for (int e = 0; e < BB; ++e) pk[e] = LU[(int64_t)k * BB + e];
+        return;
+    }
+    for (int r = 0; r < B; ++r)
+        for (int q = 0; q < B; ++q) {
+            double a = 0.0;
+            for (int u = 0; u < B; ++u) a = fma(LU[(int64_t)k * BB + r * B + u], LU[(int64_t)dk * BB + u * B + q], a);
+            pk[r * B + q] = a;
+        }
+}
+
+// FILL = 0: entry counts per position (main and c terms), flagging rows with more than kPairMax
+// dependencies; FILL = 1: the entries (dependency position or source index, and the block)
+template <int B, int FILL>
+__global__ void k_pair_rows(int32_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ inv,
+                            const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const int32_t *__restrict__ dg, const int32_t *__restrict__ levr, int lower,
+                            const double *__restrict__ LU, const int32_t *__restrict__ src_of_row, int32_t *mcnt,
+                            int32_t *ccnt, const int32_t *__restrict__ moff, const int32_t *__restrict__ coff,
+                            int32_t *mdep, double *mblk, int32_t *cdep, double *cblk, int32_t *err) {
+    constexpr int BB = B * B;
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int32_t i = pos[t];
+    const int32_t L = levr[i];
+    const int32_t k0 = lower ? rp[i] : dg[i] + 1, k1 = lower ? dg[i] : rp[i + 1];
+    if (!(L & 1)) {
+        if (!FILL) {
+            mcnt[t] = k1 - k0;
+            ccnt[t] = 0;
+            return;
+        }
+        int32_t o = moff[t];
+        for (int32_t k = k0; k < k1; ++k, ++o) {
+            mdep[o] = inv[ci[k]];
+            for (int e = 0; e < BB; ++e) mblk[(int64_t)o * BB + e] = LU[(int64_t)k * BB + e];
+        }
+        return;
+    }
+    int32_t J[kPairMax];
+    int nj = 0, nk1 = 0;
+    bool over = false;
+    for (int32_t k = k0; k < k1; ++k) {
+        const int32_t cc = ci[k];
+        const bool k1dep = levr[cc] == L - 1;
+        nk1 += k1dep;
+        const int32_t kk0 = k1dep ? (lower ? rp[cc] : dg[cc] + 1) : 0, kk1 = k1dep ? (lower ? dg[cc] : rp[cc + 1]) : 1;
+        for (int32_t kk = kk0; kk < kk1; ++kk) {
+            const int32_t p = inv[k1dep ? ci[kk] : cc];
+            bool seen = false;
+            for (int q = 0; q < nj; ++q) seen |= J[q] == p;
+            if (seen) continue;
+            if (nj == kPairMax) { over = true; continue; }
+            J[nj++] = p;
+        }
+    }
+    if (!FILL) {
+        mcnt[t] = nj;
+        ccnt[t] = nk1;
+        if (over) atomicExch(err, 1);
+        return;
+    }
+    for (int a = 1; a < nj; ++a) {   // ascending dependency positions
+        const int32_t v = J[a];
+        int b = a - 1;
+        while (b >= 0 && J[b] > v) { J[b + 1] = J[b]; --b; }
+        J[b + 1] = v;
+    }
+    const int32_t mo = moff[t];
+    for (int q = 0; q < nj; ++q) {
+        const int32_t j = J[q];
+        double m[BB];
+        for (int e = 0; e < BB; ++e) m[e] = 0.0;
+        for (int32_t k = k0; k < k1; ++k)
+            if (levr[ci[k]] != L - 1 && inv[ci[k]] == j)
+                for (int e = 0; e < BB; ++e) m[e] = LU[(int64_t)k * BB + e];
+        for (int32_t k = k0; k < k1; ++k) {
+            const int32_t cc = ci[k];
+            if (levr[cc] != L - 1) continue;
+            const int32_t kk0 = lower ? rp[cc] : dg[cc] + 1, kk1 = lower ? dg[cc] : rp[cc + 1];
+            for (int32_t kk = kk0; kk < kk1; ++kk) {
+                if (inv[ci[kk]] != j) continue;
+                double pk[BB];
+                pair_factor<B>(LU, k, dg[cc], lower, pk);
+                for (int r = 0; r < B; ++r)
+                    for (int qq = 0; qq < B; ++qq) {
+                        double a = m[r * B + qq];
+                        for (int u = 0; u < B; ++u) a = fma(-pk[r * B + u], LU[(int64_t)kk * BB + u * B + qq], a);
+                        m[r * B + qq] = a;
+                    }
+            }
+        }
+        mdep[mo + q] = j;
+        for (int e = 0; e < BB; ++e) mblk[(int64_t)(mo + q) * BB + e] = m[e];
+    }
+    int32_t co = coff[t];
+    for (int32_t k = k0; k < k1; ++k) {
+        const int32_t cc = ci[k];
+        if (levr[cc] != L - 1) continue;
+        double pk[BB];
+        pair_factor<B>(LU, k, dg[cc], lower, pk);
+        cdep[co] = src_of_row ? src_of_row[cc] : cc;
+        for (int e = 0; e < BB; ++e) cblk[(int64_t)co * BB + e] = pk[e];
+        ++co;
+    }
+}
+
+// SELL-32 tables from per-position entry lists (counts, CSR offsets, dependencies, blocks)
+__global__ void k_chunk_width_cnt(int32_t n, const int32_t *cnt, int32_t *w) {
+    int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t v = t < n ? cnt[t] : 0;
+    v = __reduce_max_sync(0xffffffffu, v);
+    if ((t & 31) == 0 && (t >> 5) < (n + 31) / 32) w[t >> 5] = v;
+}
+__global__ void k_fill_sell_csr(int32_t n, const int32_t *cnt, const int32_t *csr_off, const int32_t *dep,
+                                const int32_t *off, int32_t *col, int32_t *kidx) {
+    int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int32_t ch = t >> 5, lane = t & 31;
+    for (int32_t e = 0; e < cnt[t]; ++e) {
+        const int64_t u = ((int64_t)off[ch] + e) * 32 + lane;
+        col[u] = dep[csr_off[t] + e];
+        kidx[u] = csr_off[t] + e;
+    }
+}
+static cptr_status csr_to_sell(Ctx *c, const int32_t *cnt, const int32_t *csr_off, const int32_t *dep,
+                               const double *blk, int64_t **off64, int32_t **col, double **val) {
+    const int32_t n = c->n, nch = (n + 31) / 32, BB = c->b * c->b;
+    cudaStream_t s = c->stream;
+    int32_t *w = nullptr, *off = nullptr, *kidx = nullptr;
+    CPTR_TRY(dalloc_t(c, &w, (size_t)nch + 1));
+    CPTR_TRY(dalloc_t(c, &off, (size_t)nch + 1));
+    (k_chunk_width_cnt<<<nblk((int64_t)nch * 32, 256), 256, 0, s>>>(n, cnt, w), note_launch());
+    int32_t total = 0;
+    CPTR_TRY(scan_exclusive(c, w, off, nch, &total));
+    CPTR_TRY(dalloc_t(c, off64, (size_t)nch + 1));
+    (k_widen<<<nblk(nch + 1, 256), 256, 0, s>>>(nch, off, *off64), note_launch());
+    const int64_t ns = (int64_t)total * 32;
+    CPTR_TRY(dalloc_t(c, col, (size_t)(ns > 0 ? ns : 1)));
+    CPTR_TRY(dalloc_t(c, &kidx, (size_t)(ns > 0 ? ns : 1)));
+    CPTR_TRY(dalloc_t(c, val, (size_t)(ns > 0 ? ns : 1) * BB));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(*col, 0xFF, sizeof(int32_t) * (ns > 0 ? ns : 1), s));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(kidx, 0xFF, sizeof(int32_t) * (ns > 0 ? ns : 1), s));
+    (k_fill_sell_csr<<<nblk(n, 256), 256, 0, s>>>(n, cnt, csr_off, dep, off, *col, kidx), note_launch());
+    if (ns > 0) (k_sf_pack<double><<<nblk(ns, 256), 256, 0, s>>>(ns, BB, kidx, blk, *val), note_launch());
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    dfree(w); dfree(off); dfree(kidx);
+    return CPTR_OK;
+}
+
+// the paired-level tables of one sweep; *ok = false when a paired row has too many dependencies
+static cptr_status pair_table(Ctx *c, bool lower, const int32_t *pos, const int32_t *inv, const int32_t *levr,
+                              const int32_t *src_of_row, int64_t **off, int32_t **col, double **val, int64_t **coff,
+                              int32_t **ccol, double **cval, bool *ok) {
+    const int32_t n = c->n, BB = c->b * c->b;
+    cudaStream_t s = c->stream;
+    int32_t *mcnt = nullptr, *ccnt = nullptr, *moff = nullptr, *coffc = nullptr, *err = nullptr;
+    CPTR_TRY(dalloc_t(c, &mcnt, (size_t)n + 1));
+    CPTR_TRY(dalloc_t(c, &ccnt, (size_t)n + 1));
+    CPTR_TRY(dalloc_t(c, &moff, (size_t)n + 1));
+    CPTR_TRY(dalloc_t(c, &coffc, (size_t)n + 1));
+    CPTR_TRY(dalloc_t(c, &err, 1));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+    auto rows = [&](auto kern, int32_t *mdep, double *mblk, int32_t *cdep, double *cblk) {
+        (kern<<<nblk(n, 128), 128, 0, s>>>(n, pos, inv, c->ilu_rp, c->ilu_ci, c->ilu_diag, levr, lower ? 1 : 0, c->LU,
+                                           src_of_row, mcnt, ccnt, moff, coffc, mdep, mblk, cdep, cblk, err),
+         note_launch());
+    };
+    if (c->b == 3) rows(k_pair_rows<3, 0>, nullptr, nullptr, nullptr, nullptr);
+    else rows(k_pair_rows<4, 0>, nullptr, nullptr, nullptr, nullptr);
+    int32_t mtot = 0, ctot = 0, h_err = 0;
+    CPTR_TRY(scan_exclusive(c, mcnt, moff, n, &mtot));
+    CPTR_TRY(scan_exclusive(c, ccnt, coffc, n, &ctot));
+    CPTR_TRY(copy_to_host(c, &h_err, err, sizeof(int32_t)));
+    *ok = !h_err;
+    if (*ok) {
+        int32_t *mdep = nullptr, *cdep = nullptr;
+        double *mblk = nullptr, *cblk = nullptr;
+        CPTR_TRY(dalloc_t(c, &mdep, (size_t)(mtot > 0 ? mtot : 1)));
+        CPTR_TRY(dalloc_t(c, &cdep, (size_t)(ctot > 0 ? ctot : 1)));
+        CPTR_TRY(dalloc_t(c, &mblk, (size_t)(mtot > 0 ? mtot : 1) * BB));
+        CPTR_TRY(dalloc_t(c, &cblk, (size_t)(ctot > 0 ? ctot : 1) * BB));
+        if (c->b == 3) rows(k_pair_rows<3, 1>, mdep, mblk, cdep, cblk);
+        else rows(k_pair_rows<4, 1>, mdep, mblk, cdep, cblk);
+        CPTR_TRY(csr_to_sell(c, mcnt, moff, mdep, mblk, off, col, val));
+        CPTR_TRY(csr_to_sell(c, ccnt, coffc, cdep, cblk, coff, ccol, cval));
+        CPTR_CUDA_TRY(c, cudaStreamSynchronize(s));
+        dfree(mdep); dfree(cdep); dfree(mblk); dfree(cblk);
+    }
+    dfree(mcnt); dfree(ccnt); dfree(moff); dfree(coffc); dfree(err);
+    return CPTR_OK;
+}
+
+// both sweeps' paired-level tables (FP64 sweeps only); c->sp_ok tells whether they were built
+static cptr_status pair_setup(Ctx *c, const int32_t *inv_f, const int32_t *inv_b, const int32_t *levr_f,
+                              const int32_t *levr_b) {
+    c->sp_ok = false;
+    bool okf = false, okb = false;
+    CPTR_TRY(pair_table(c, true, c->lvl_f, inv_f, levr_f, c->ilu_rowmap, &c->sp_off_f, &c->sp_col_f, &c->sp_val_f,
+                        &c->sp_coff_f, &c->sp_ccol_f, &c->sp_cval_f, &okf));
+    if (okf)
+        CPTR_TRY(pair_table(c, false, c->lvl_b, inv_b, levr_b, inv_f, &c->sp_off_b, &c->sp_col_b, &c->sp_val_b,
+                            &c->sp_coff_b, &c->sp_ccol_b, &c->sp_cval_b, &okb));
+    c->sp_ok = okf && okb;
+    return CPTR_OK;
+}
+
+// key of the sweeps' tuning in the context's cache (grid and back-off; the schedule at key + 1)
 static uint64_t ilu_tune_key(const Ctx *c) {
     return (uint64_t)8 << 60 | (uint64_t)(c->o.precision & 1) << 56 | ((uint64_t)c->n & 0xFFFFFFull) << 32 |
            (uint64_t)(uint32_t)c->nnzb;
 }
-static bool ilu_tuned_levels(const Ctx *c) {
-    auto it = c->tune_cache.find(ilu_tune_key(c));
-    return it != c->tune_cache.end() && it->second.T > 0;
+// the schedule a cached tuning chose (0 level sets, 1 chunked, 2 paired levels), -1 if none
+static int ilu_tuned_schedule(const Ctx *c) {
+    auto it = c->tune_cache.find(ilu_tune_key(c) + 1);
+    return it == c->tune_cache.end() ? -1 : it->second.G;
 }
 
 cptr_status ilu_setup(Ctx *c) {
@@ -1788,7 +2037,11 @@ cptr_status ilu_setup(Ctx *c) {
     CPTR_TRY(dalloc_t(c, &c->lvl_b, (size_t)n));
     CPTR_TRY(dalloc_t(c, &inv_f, (size_t)n));
     CPTR_TRY(dalloc_t(c, &inv_b, (size_t)n));
-    CPTR_TRY(device_levels(c, c->ilu_rp, c->ilu_ci, c->lvl_f, inv_f, c->h_lptr_f, c->lvl_b, inv_b, c->h_lptr_b));
+    int32_t *levr_f = nullptr, *levr_b = nullptr;
+    CPTR_TRY(dalloc_t(c, &levr_f, (size_t)n));
+    CPTR_TRY(dalloc_t(c, &levr_b, (size_t)n));
+    CPTR_TRY(device_levels(c, c->ilu_rp, c->ilu_ci, c->lvl_f, inv_f, c->h_lptr_f, c->lvl_b, inv_b, c->h_lptr_b,
+                           levr_f, levr_b));
     c->nlev_f = (int32_t)c->h_lptr_f.size() - 1;
     c->nlev_b = (int32_t)c->h_lptr_b.size() - 1;
     CPTR_TRY(dalloc_t(c, &c->ybuf, (size_t)n * c->b));
@@ -1905,8 +2158,18 @@ cptr_status ilu_setup(Ctx *c) {
     CPTR_TRY(dalloc(c, &c->sf_y, (size_t)n * c->b * (lo ? 4 : 8) + 64));
     CPTR_TRY(dalloc(c, &c->sf_z, (size_t)n * c->b * (lo ? 4 : 8) + 64));
     CPTR_CUDA_TRY(c, cudaGetLastError());
-    dfree(kidx_f); dfree(kidx_b); dfree(kidx_d); dfree(inv_f); dfree(inv_b);
-    if (!mc && (c->o.ilu_sweep == 2 || (c->o.ilu_sweep == 0 && c->o.autotune && !ilu_tuned_levels(c))))
+    dfree(kidx_f); dfree(kidx_b); dfree(kidx_d);
+    const int sched = ilu_tuned_schedule(c);
+    if (!lo && (c->o.ilu_sweep == 3 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 2)))) {
+        const cptr_status ps = pair_setup(c, inv_f, inv_b, levr_f, levr_b);
+        if (ps != CPTR_OK) {
+            dfree(inv_f); dfree(inv_b); dfree(levr_f); dfree(levr_b);
+            return ps;
+        }
+        c->sp_use = c->sp_ok && (c->o.ilu_sweep == 3 || sched == 2);
+    }
+    dfree(inv_f); dfree(inv_b); dfree(levr_f); dfree(levr_b);
+    if (!mc && (c->o.ilu_sweep == 2 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 1))))
         CPTR_TRY(cw_setup(c));
     setup_tick(c, SETUP_ILU_HOST, &t0);
     return CPTR_OK;
@@ -1924,8 +2187,12 @@ void ilu_free(Ctx *c) {
     void **sf[] = {(void **)&c->sf_pos_f, (void **)&c->sf_pos_b, (void **)&c->sf_bmap, (void **)&c->sf_off_f,
                    (void **)&c->sf_off_b, (void **)&c->sf_col_f, (void **)&c->sf_col_b, (void **)&c->sf_val_f,
                    (void **)&c->sf_val_b, (void **)&c->sf_dinv, (void **)&c->sf_ticket, (void **)&c->sf_y,
-                   (void **)&c->sf_z};
+                   (void **)&c->sf_z, (void **)&c->sp_off_f, (void **)&c->sp_off_b, (void **)&c->sp_coff_f,
+                   (void **)&c->sp_coff_b, (void **)&c->sp_col_f, (void **)&c->sp_col_b, (void **)&c->sp_ccol_f,
+                   (void **)&c->sp_ccol_b, (void **)&c->sp_val_f, (void **)&c->sp_val_b, (void **)&c->sp_cval_f,
+                   (void **)&c->sp_cval_b};
     for (void **p : sf) { dfree(*p); *p = nullptr; }
+    c->sp_ok = c->sp_use = false;
 }
 
 // launch one chunked sweep with its tables (NS = stage slots chosen at set-up)
@@ -1969,16 +2236,31 @@ static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT 
     }
     if constexpr (std::is_same<T, double>::value) {   // FP64: a row over four lanes
         const unsigned gridg = std::min<unsigned>(nblk(n, kSfRowsG), (unsigned)c->sf_grid);
+        // the level-set tables, or the paired-level ones (their c-term tables non-null)
+        const bool pr = c->sp_use;
         int pf = prof_begin(c, PF_ILU_FWD);
-        (k_ilu_fwd_g<B, T, RT><<<gridg, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_f, c->sf_off_f, c->sf_col_f,
-                                                             (const T *)c->sf_val_f, r, y, c->ks,
-                                                             c->inject_wait ? c->never : nullptr, c->sf_sleep), note_launch());
+        auto fwd = [&](auto kern) {
+            (kern<<<gridg, kSfThreads, 0, s>>>(
+                 n, c->sf_ticket, c->sf_pos_f, pr ? c->sp_off_f : c->sf_off_f, pr ? c->sp_col_f : c->sf_col_f,
+                 pr ? (const T *)c->sp_val_f : (const T *)c->sf_val_f, r, y, c->ks,
+                 c->inject_wait ? c->never : nullptr, c->sf_sleep, pr ? c->sp_coff_f : nullptr, c->sp_ccol_f,
+                 (const T *)c->sp_cval_f),
+             note_launch());
+        };
+        if (pr) fwd(k_ilu_fwd_g<B, T, RT, 8>);
+        else fwd(k_ilu_fwd_g<B, T, RT, kDepGroup>);
         prof_end(c, pf);
         pf = prof_begin(c, PF_ILU_BWD);
-        (k_ilu_bwd_g<B, T, XT><<<gridg, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_b, c->sf_bmap, c->sf_off_b,
-                                                             c->sf_col_b, (const T *)c->sf_val_b, (const T *)c->sf_dinv,
-                                                             y, zz, z, c->ps, c->ts, dp, dT, c->ks, c->sf_sleep),
-         note_launch());
+        auto bwd = [&](auto kern) {
+            (kern<<<gridg, kSfThreads, 0, s>>>(
+                 n, c->sf_ticket, c->sf_pos_b, c->sf_bmap, pr ? c->sp_off_b : c->sf_off_b,
+                 pr ? c->sp_col_b : c->sf_col_b, pr ? (const T *)c->sp_val_b : (const T *)c->sf_val_b,
+                 (const T *)c->sf_dinv, y, zz, z, c->ps, c->ts, dp, dT, c->ks, c->sf_sleep,
+                 pr ? c->sp_coff_b : nullptr, c->sp_ccol_b, (const T *)c->sp_cval_b),
+             note_launch());
+        };
+        if (pr) bwd(k_ilu_bwd_g<B, T, XT, 8>);
+        else bwd(k_ilu_bwd_g<B, T, XT, kDepGroup>);
         prof_end(c, pf);
         return;
     }
@@ -2030,32 +2312,47 @@ void ilu_apply_into(const Ctx *c, const double *r, double *z, double *ybuf, doub
     }
 }
 
-// Autotuner of the one-launch ILU(0) sweeps: for the level-set schedule, the persistent grid
-// (blocks in {152, 304, 608, 1216}) and the back-off between polls of a dependency not yet
-// written (__nanosleep of {8, 32, 128, 512} ns), which set how many rows run ahead of the wavefront
-// and how hard they poll; then, where the chunked schedule exists, its back-off, and the faster
-// schedule is kept.  Each candidate is timed with CUDA events over 3 applications (forward +
-// backward) after a warm-up, on a zero right-hand side; the result is cached by the factor size.
-// The sweeps compute the same values whatever the choice.
+// Autotuner of the one-launch ILU(0) sweeps: the persistent grid (blocks in {152, 304, 608,
+// 1216}) and the back-off between polls of a dependency not yet written (__nanosleep of {8, 32,
+// 128, 512} ns), which set how many rows run ahead of the wavefront and how hard they poll; then,
+// where they were built, the paired-level and the chunked schedules at that grid, each at its best
+// back-off, and the fastest schedule is kept.  Each candidate is timed with CUDA events over 3
+// applications (forward + backward) after a warm-up, on a zero right-hand side; the result is
+// cached by the factor size.
 cptr_status ilu_autotune(Ctx *c) {
     if (!c->LU) return CPTR_OK;
     const uint64_t key = ilu_tune_key(c);
+    const bool auto_sched = c->o.ilu_sweep == 0;
     auto it = c->tune_cache.find(key);
     if (it != c->tune_cache.end()) {
-        c->sf_grid = std::abs((int)it->second.T);
+        c->sf_grid = it->second.T;
         c->sf_sleep = it->second.G;
-        if (c->cw_ok && c->o.ilu_sweep == 0) c->cw_use = it->second.T < 0;
+        if (auto_sched) {
+            const int sched = ilu_tuned_schedule(c);
+            c->cw_use = c->cw_ok && sched == 1;
+            c->sp_use = c->sp_ok && sched == 2;
+        }
         return CPTR_OK;
     }
     double *r = c->xw, *z = c->w;   // scratch vectors of n*b doubles
-    const bool cw_was = c->cw_use;
-    c->cw_use = false;              // time the level-set sweeps first
+    const bool cw_was = c->cw_use, sp_was = c->sp_use;
+    c->cw_use = false;              // time the level-set sweeps first (or the paired ones if forced)
+    c->sp_use = c->sp_ok && c->o.ilu_sweep == 3;
     CPTR_CUDA_TRY(c, cudaMemsetAsync(r, 0, sizeof(double) * (size_t)c->n * c->b, c->stream));
     cudaEvent_t e0, e1;
     CPTR_CUDA_TRY(c, cudaEventCreate(&e0));
     CPTR_CUDA_TRY(c, cudaEventCreate(&e1));
-    const int g0 = c->sf_grid, s0 = c->sf_sleep;
-    int best_g = g0, best_s = s0;
+    auto time3 = [&]() -> float {   // one warm-up, then 3 applications
+        ilu_apply(c, r, z, nullptr, nullptr);
+        cudaEventRecord(e0, c->stream);
+        for (int rep = 0; rep < 3; ++rep) ilu_apply(c, r, z, nullptr, nullptr);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    int best_g = c->sf_grid, best_s = c->sf_sleep;
     float best_ms = 1e30f;
     const unsigned maxg = nblk(c->n, kSfThreads);
     for (int g : {152, 304, 608, 1216}) {
@@ -2063,46 +2360,53 @@ cptr_status ilu_autotune(Ctx *c) {
         for (int sl : {8, 32, 128, 512}) {
             c->sf_grid = g;
             c->sf_sleep = sl;
-            ilu_apply(c, r, z, nullptr, nullptr);
-            cudaEventRecord(e0, c->stream);
-            for (int rep = 0; rep < 3; ++rep) ilu_apply(c, r, z, nullptr, nullptr);
-            cudaEventRecord(e1, c->stream);
-            CPTR_CUDA_TRY(c, cudaEventSynchronize(e1));
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            const float ms = time3();
             if (ms < best_ms) { best_ms = ms; best_g = g; best_s = sl; }
         }
     }
     c->sf_grid = best_g;
-    c->sf_sleep = best_s;
-    Shape sh;
-    sh.T = (int16_t)best_g;
-    sh.G = (int16_t)best_s;
-    if (c->cw_ok && c->o.ilu_sweep == 0) {   // the chunked sweeps at their best back-off
-        c->cw_use = true;
-        int cw_s = best_s;
-        float cw_ms = 1e30f;
+    int sched = c->sp_use ? 2 : 0;
+    // the other schedules at the best grid, each at its best back-off; the fastest is kept
+    auto sleeps = [&](int *bs) -> float {
+        float bm = 1e30f;
         for (int sl : {8, 32, 128, 512}) {
             c->sf_sleep = sl;
-            ilu_apply(c, r, z, nullptr, nullptr);
-            cudaEventRecord(e0, c->stream);
-            for (int rep = 0; rep < 3; ++rep) ilu_apply(c, r, z, nullptr, nullptr);
-            cudaEventRecord(e1, c->stream);
-            CPTR_CUDA_TRY(c, cudaEventSynchronize(e1));
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < cw_ms) { cw_ms = ms; cw_s = sl; }
+            const float ms = time3();
+            if (ms < bm) { bm = ms; *bs = sl; }
         }
-        c->cw_use = cw_ms < best_ms;
-        c->sf_sleep = c->cw_use ? cw_s : best_s;
-        sh.G = (int16_t)c->sf_sleep;
-        sh.T = (int16_t)(c->cw_use ? -best_g : best_g);   // negative: the chunked sweeps won
+        return bm;
+    };
+    if (auto_sched && c->sp_ok) {
+        c->sp_use = true;
+        int sl = best_s;
+        const float ms = sleeps(&sl);
+        c->sp_use = false;
+        if (ms < best_ms) { best_ms = ms; best_s = sl; sched = 2; }
+    }
+    if (auto_sched && c->cw_ok) {
+        c->cw_use = true;
+        int sl = best_s;
+        const float ms = sleeps(&sl);
+        c->cw_use = false;
+        if (ms < best_ms) { best_ms = ms; best_s = sl; sched = 1; }
+    }
+    if (auto_sched) {
+        c->cw_use = sched == 1;
+        c->sp_use = sched == 2;
     } else {
         c->cw_use = cw_was;
+        c->sp_use = sp_was;
     }
+    c->sf_sleep = best_s;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    Shape sh, sc;
+    sh.T = (int16_t)best_g;
+    sh.G = (int16_t)best_s;
+    sc.G = (int16_t)sched;
+    sc.T = 0;
     c->tune_cache[key] = sh;
+    c->tune_cache[key + 1] = sc;
     CPTR_CUDA_TRY(c, cudaGetLastError());
     return CPTR_OK;
 }

@@ -42,8 +42,8 @@ def test_tuned_solve_matches_untuned(precision):
             assert h == 2 and T in (64, 128, 256, 512)
         elif k == 4:       # ILU sweeps: poll back-off (ns), persistent grid of the level-set schedule
             assert h == 3 and G in (8, 32, 128, 512) and T in (152, 304, 608, 1216)
-        elif k == 5:       # ILU sweeps: chunked wavefront chosen (1) or level sets (0)
-            assert h == 3 and G in (0, 1)
+        elif k == 5:       # ILU sweeps: level sets (0), chunked wavefront (1) or paired levels (2)
+            assert h == 3 and G in (0, 1, 2)
         else:
             assert G in (1, 2, 4, 8, 16, 32) and T in (128, 256, 512)
     # untuned: heuristic lanes, 256 threads; level-set sweeps on 608 blocks, 20 ns back-off
