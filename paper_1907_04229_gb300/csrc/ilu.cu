@@ -1321,8 +1321,8 @@ __global__ void __launch_bounds__(kSfThreads) k_bilu_factor_g(int32_t n, unsigne
         while (__any_sync(0xffffffffu, !done)) {
             bool pend = false;
             if (!done) {
-                bool p = false;
-                for (int32_t k = 0; k < nd; ++k) {
+                bool p = false;   // the four lanes of the row poll a quarter of the flags each
+                for (int32_t k = r; k < nd; k += G) {
                     int32_t f;
                     asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flag + cols[k]) : "memory");
                     p |= f != epoch;
@@ -1344,8 +1344,10 @@ __global__ void __launch_bounds__(kSfThreads) k_bilu_factor_g(int32_t n, unsigne
                     }
                 }
                 if (!p) {
-                    // one acquire fence orders the copies of the dependencies' blocks after the flags
+                    // each lane's acquire fence orders what follows after the flags it read; the
+                    // warp barrier then orders every lane's copies after all four lanes' fences
                     asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                    __syncwarp(gmask);
                     for (int32_t k = 0; k < nd; ++k) {
                         const int64_t lo = (int64_t)dcs[k] * BB, hi = (int64_t)ecs[k] * BB;
                         const int64_t a0 = lo & ~(int64_t)1;
@@ -2083,7 +2085,9 @@ cptr_status ilu_setup(Ctx *c) {
     const unsigned fgrid = std::min<unsigned>(nblk(n, 64), 8 * 152);
     const size_t fg_bytes = fs_bytes / 64 * kSfRowsG;   // the same per row, kSfRowsG rows per block
     if (fg_bytes <= 100 * 1024) {
-        const unsigned ggrid = std::min<unsigned>(nblk(n, kSfRowsG), (unsigned)std::min<size_t>(8, 200 * 1024 / fg_bytes) * 152);
+        // one block per SM (32 rows each, a few levels ahead of the wavefront): more rows in flight
+        // only poll, and measured slower
+        const unsigned ggrid = std::min<unsigned>(nblk(n, kSfRowsG), 152u);
         if (c->b == 3) {
             cudaFuncSetAttribute(k_bilu_factor_g<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
             (k_bilu_factor_g<3><<<ggrid, kSfThreads, fg_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
