@@ -36,7 +36,9 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 LEARNED_STEPS, LEARNED_LR = 2000, 2e-3
 # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/ (the
 # current kernels; None where no capture of the current code exists)
-PROFILED_TRAFFIC = {"spmv": 113_717_248, "stage1_resid": None, "ilu_fwd": 55_712_512, "ilu_bwd": 75_466_496}
+PROFILED_TRAFFIC = {"spmv": 113_717_248, "stage1_resid": None, "ilu_fwd": 102_265_344, "ilu_bwd": 118_584_832}
+# the ILU figures are those of the paired-level sweeps (their tables hold the substituted blocks)
+PROFILED_ILU_SCHEDULE = "paired"
 
 
 def parse():
@@ -253,7 +255,8 @@ def ours(args, rank, world, local_rank):
         achieved = alg[fam] / (avg_ms / 1e3) / 1e9
         lines[fam] = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                       "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                      "traffic": None if fam.startswith("ilu") else PROFILED_TRAFFIC.get(fam),
+                      "traffic": (PROFILED_TRAFFIC.get(fam) if not fam.startswith("ilu") or
+                                  (paired and PROFILED_ILU_SCHEDULE == "paired") else None),
                       "algorithmic_bytes_per_launch": alg[fam], "avg_launch_us": round(avg_ms * 1e3, 2),
                       "launches_per_step": cnt / args.steps, "ms_per_step": round(ms_tot / args.steps, 3)}
     # FP64 ALU view of the SpMV: 9 FMA per 3x3 block (2 flop each) against 1.258 TFLOP/s
