@@ -201,7 +201,8 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) {
         // The two hierarchies are independent: the temperature one is built by a second host
         // thread on its own stream (a context view with its own stream, scratch flag and scan
-        // buffer) while this thread builds the pressure one and then the ILU(0) factors.
+        // buffer) while this thread builds the ILU(0) factors and, while their factorisation
+        // kernel runs, the pressure hierarchy.
         if (!c->amg_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->amg_stream, cudaStreamNonBlocking));
         if (!c->coarse_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->coarse_stream, cudaStreamNonBlocking));
         if (!c->amg_fork) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&c->amg_fork, cudaEventDisableTiming));
@@ -221,16 +222,20 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
             w.scan_tmp = nullptr;
             cudaStreamSynchronize(w.stream);
         });
-        cptr_status st_p = amg_setup(c, c->hp, c->rp, c->ci, c->App, n);
-        if (st_p == CPTR_OK && c->o.stage2 == CPTR_STAGE2_ILU0) st_p = ilu_setup(c);
+        // the pressure hierarchy is built while the ILU(0) factorisation kernel runs
+        auto hp_setup = [&] { return amg_setup(c, c->hp, c->rp, c->ci, c->App, n); };
+        cptr_status st_p = c->o.stage2 == CPTR_STAGE2_ILU0 ? ilu_setup(c, hp_setup) : hp_setup();
         worker.join();
         for (int q = 0; q < kSetupPhases; ++q) c->prof.setup_ms[q] += w.prof.setup_ms[q];
         dfree(w.flag);
         if (st_p != CPTR_OK) return st_p;
         if (st_T != CPTR_OK) return c->fail(st_T, w.err);
     } else {
-        if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_setup(c, c->hp, c->rp, c->ci, c->App, n));
-        if (c->o.stage2 == CPTR_STAGE2_ILU0) CPTR_TRY(ilu_setup(c));
+        auto hp_setup = [&] {
+            return s1 != CPTR_STAGE1_NONE ? amg_setup(c, c->hp, c->rp, c->ci, c->App, n) : CPTR_OK;
+        };
+        if (c->o.stage2 == CPTR_STAGE2_ILU0) CPTR_TRY(ilu_setup(c, hp_setup));
+        else CPTR_TRY(hp_setup());
     }
     // the coarsest inverses ran on the coarse stream meanwhile
     CPTR_TRY(amg_coarsest_wait(c, c->hp));
@@ -436,6 +441,7 @@ void cptr_destroy(cptr_ctx *ctx) {
         if (c->side_stream) cudaStreamSynchronize(c->side_stream);
         if (c->coarse_stream) cudaStreamSynchronize(c->coarse_stream);
         if (c->amg_stream) cudaStreamSynchronize(c->amg_stream);
+        if (c->ilu_stream) cudaStreamSynchronize(c->ilu_stream);
         release_setup(c);
         dfree(c->ks); dfree(c->flag); dfree(c->partial); dfree(c->scan_tmp); dfree(c->never); dfree(c->ilu_flags);
         dfree(c->mlp);
@@ -449,6 +455,9 @@ void cptr_destroy(cptr_ctx *ctx) {
     if (c->coarse_stream) cudaStreamDestroy(c->coarse_stream);
     if (c->amg_stream) cudaStreamDestroy(c->amg_stream);
     if (c->amg_fork) cudaEventDestroy(c->amg_fork);
+    if (c->ilu_stream) cudaStreamDestroy(c->ilu_stream);
+    if (c->ilu_fork) cudaEventDestroy(c->ilu_fork);
+    if (c->ilu_done) cudaEventDestroy(c->ilu_done);
     if (c->side_fork) cudaEventDestroy(c->side_fork);
     if (c->side_join) cudaEventDestroy(c->side_join);
     for (Hier *h : {&c->hp, &c->hT})

@@ -1982,7 +1982,7 @@ static int ilu_tuned_schedule(const Ctx *c) {
     return it == c->tune_cache.end() ? -1 : it->second.G;
 }
 
-cptr_status ilu_setup(Ctx *c) {
+cptr_status ilu_setup(Ctx *c, const std::function<cptr_status()> &overlap) {
     ilu_free(c);
     double t0 = host_ms();
     const int32_t n = c->n, BB = c->b * c->b;
@@ -2062,7 +2062,8 @@ cptr_status ilu_setup(Ctx *c) {
         c->ilu_epoch = 0;
     }
     ++c->ilu_epoch;
-    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), st));
+    int32_t *fsing = c->flag + 3;   // the factorisation's singular flag (flag[0] serves the overlapped work)
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(fsing, 0, sizeof(int32_t), st));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(c->sf_ticket, 0, 4 * sizeof(unsigned), st));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(reinterpret_cast<char *>(c->ks) + offsetof(KState, wait_err), 0, sizeof(int32_t), st));
     // per-row sizes of the pattern: the staged kernel holds a row, and the pivot inverse and upper
@@ -2080,47 +2081,65 @@ cptr_status ilu_setup(Ctx *c) {
         maxdep = h_ext[1];
         maxu = h_ext[2];
     }
+    // the factorisation runs on its own stream; the caller's overlapped work goes on meanwhile
+    if (!c->ilu_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->ilu_stream, cudaStreamNonBlocking));
+    if (!c->ilu_fork) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&c->ilu_fork, cudaEventDisableTiming));
+    if (!c->ilu_done) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&c->ilu_done, cudaEventDisableTiming));
+    cudaStream_t fst = c->ilu_stream;
+    CPTR_CUDA_TRY(c, cudaEventRecord(c->ilu_fork, st));
+    CPTR_CUDA_TRY(c, cudaStreamWaitEvent(fst, c->ilu_fork, 0));
     const size_t fs_rowsz = (size_t)((maxrow * BB + 1) & ~1), fs_w = (size_t)(((1 + maxu) * BB + 3) & ~1);
     const size_t fs_bytes = (size_t)64 * ((fs_rowsz + (size_t)maxdep * fs_w) * 8 + (size_t)(maxrow + maxdep * (2 + maxu)) * 4);
     const unsigned fgrid = std::min<unsigned>(nblk(n, 64), 8 * 152);
     const size_t fg_bytes = fs_bytes / 64 * kSfRowsG;   // the same per row, kSfRowsG rows per block
     if (fg_bytes <= 100 * 1024) {
         // one block per SM (32 rows each, a few levels ahead of the wavefront): more rows in flight
-        // only poll, and measured slower
-        const unsigned ggrid = std::min<unsigned>(nblk(n, kSfRowsG), 152u);
+        // only poll, and measured slower.  Two SMs are left to the coarsest AMG inverses, whose
+        // single blocks need most of an SM's shared memory and run at the same time.
+        const unsigned ggrid = std::min<unsigned>(nblk(n, kSfRowsG), 150u);
         if (c->b == 3) {
             cudaFuncSetAttribute(k_bilu_factor_g<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-            (k_bilu_factor_g<3><<<ggrid, kSfThreads, fg_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
+            (k_bilu_factor_g<3><<<ggrid, kSfThreads, fg_bytes, fst>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
                                                                       c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch,
-                                                                      c->flag, c->ks, maxrow, maxdep, maxu), note_launch());
+                                                                      fsing, c->ks, maxrow, maxdep, maxu), note_launch());
         } else {
             cudaFuncSetAttribute(k_bilu_factor_g<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-            (k_bilu_factor_g<4><<<ggrid, kSfThreads, fg_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
+            (k_bilu_factor_g<4><<<ggrid, kSfThreads, fg_bytes, fst>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
                                                                       c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch,
-                                                                      c->flag, c->ks, maxrow, maxdep, maxu), note_launch());
+                                                                      fsing, c->ks, maxrow, maxdep, maxu), note_launch());
         }
     } else if (fs_bytes <= 100 * 1024) {
         const unsigned sgrid = std::min<unsigned>(nblk(n, 64), 2 * 152);
         if (c->b == 3) {
             cudaFuncSetAttribute(k_bilu_factor_st<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-            (k_bilu_factor_st<3><<<sgrid, 64, fs_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
-                                                              c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch, c->flag,
+            (k_bilu_factor_st<3><<<sgrid, 64, fs_bytes, fst>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
+                                                              c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch, fsing,
                                                               c->ks, maxrow, maxdep, maxu), note_launch());
         } else {
             cudaFuncSetAttribute(k_bilu_factor_st<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-            (k_bilu_factor_st<4><<<sgrid, 64, fs_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
-                                                              c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch, c->flag,
+            (k_bilu_factor_st<4><<<sgrid, 64, fs_bytes, fst>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
+                                                              c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch, fsing,
                                                               c->ks, maxrow, maxdep, maxu), note_launch());
         }
     } else if (c->b == 3)
-        (k_bilu_factor_sf<3><<<fgrid, 64, 0, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, c->LU,
-                                                    c->ilu_flags, c->ilu_epoch, c->flag, c->ks), note_launch());
+        (k_bilu_factor_sf<3><<<fgrid, 64, 0, fst>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, c->LU,
+                                                    c->ilu_flags, c->ilu_epoch, fsing, c->ks), note_launch());
     else
-        (k_bilu_factor_sf<4><<<fgrid, 64, 0, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, c->LU,
-                                                    c->ilu_flags, c->ilu_epoch, c->flag, c->ks), note_launch());
+        (k_bilu_factor_sf<4><<<fgrid, 64, 0, fst>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, c->LU,
+                                                    c->ilu_flags, c->ilu_epoch, fsing, c->ks), note_launch());
     CPTR_CUDA_TRY(c, cudaGetLastError());
+    CPTR_CUDA_TRY(c, cudaEventRecord(c->ilu_done, fst));
+    if (overlap) {
+        const cptr_status ov = overlap();
+        if (ov != CPTR_OK) {
+            cudaEventSynchronize(c->ilu_done);   // the factors are freed with the failed set-up
+            return ov;
+        }
+        t0 = host_ms();
+    }
+    CPTR_CUDA_TRY(c, cudaStreamWaitEvent(st, c->ilu_done, 0));
     int32_t sing = 0, werr = 0;
-    CPTR_TRY(copy_to_host(c, &sing, c->flag, sizeof(int32_t)));
+    CPTR_TRY(copy_to_host(c, &sing, fsing, sizeof(int32_t)));
     CPTR_TRY(copy_to_host(c, &werr, reinterpret_cast<char *>(c->ks) + offsetof(KState, wait_err), sizeof(int32_t)));
     if (werr) return c->fail(CPTR_ETIMEOUT, "ILU(0) factorisation: a bounded wait gave up");
     if (sing) return c->fail(CPTR_ESINGULAR, "ILU(0): singular pivot block");
