@@ -300,12 +300,12 @@ struct Ctx {
     void *sf_y = nullptr, *sf_z = nullptr;             // level-ordered y and z (sentinel-filled)
     CwTables cw_f, cw_b;                               // chunked wavefront sweeps (natural order)
     bool cw_ok = false, cw_use = false;                // built / chosen (autotuner may switch)
-    // paired-level sweeps (FP64): a row of odd level substitutes its dependencies of the level
+    // paired-level sweeps: a row of odd level substitutes its dependencies of the level
     // before, so that two levels run as one; main tables (off/col/val) and the tables of the part
     // that needs no other row's result (coff/ccol/cval)
     int64_t *sp_off_f = nullptr, *sp_off_b = nullptr, *sp_coff_f = nullptr, *sp_coff_b = nullptr;
     int32_t *sp_col_f = nullptr, *sp_col_b = nullptr, *sp_ccol_f = nullptr, *sp_ccol_b = nullptr;
-    double *sp_val_f = nullptr, *sp_val_b = nullptr, *sp_cval_f = nullptr, *sp_cval_b = nullptr;
+    void *sp_val_f = nullptr, *sp_val_b = nullptr, *sp_cval_f = nullptr, *sp_cval_b = nullptr;   // FP64, or FP32 when mixed
     bool sp_ok = false, sp_use = false;                // built / chosen
     int32_t sf_grid = 4 * 152;                         // persistent grid of the sweeps (autotuned)
     int32_t sf_sleep = 20;                             // back-off between polls, ns (autotuned)

@@ -133,13 +133,13 @@ __global__ void k_ilu_bwd(const int32_t *__restrict__ rows, int32_t start, int32
 
 // ------------------------------------------------------------------------------------------------
 // Triangular solves in one launch per sweep.  Positions t = 0..n-1 enumerate the rows level by
-// level; a ticket counter hands out chunks of kSfThreads consecutive positions to a persistent
-// grid, and a block finishes its chunk before it takes another.  Each thread solves one row.  The
-// values of an unsolved row hold a sentinel NaN payload; the producer overwrites them (the last
-// one with release semantics) and a dependent row polls that last value with acquire loads, so the
-// value doubles as its ready flag.  A row depends only on earlier positions, which belong to
-// chunks held by blocks that already run: no deadlock.  Every wait is bounded by kWaitNs of GPU
-// time; a wait that gives up sets ks->wait_err and the call reports CPTR_ETIMEOUT.
+// level; a ticket counter hands out chunks of consecutive positions (32 rows of four lanes each,
+// below) to a persistent grid, and a block finishes its chunk before it takes another.  The
+// values of an unsolved row hold a sentinel NaN payload; the producer overwrites them with relaxed
+// stores and a dependent row polls each value with relaxed loads, so every value doubles as its
+// own ready flag.  A row depends only on earlier positions, which belong to chunks held by blocks
+// that already run: no deadlock.  Every wait is bounded by kWaitNs of GPU time; a wait that gives
+// up sets ks->wait_err and the call reports CPTR_ETIMEOUT.
 constexpr unsigned long long kSentinel = 0x7FF4C0DEDEADBEEFULL;  // never produced by arithmetic
 constexpr unsigned kSentinel32 = 0x7FA6C0DEu;                      // the same for FP32 vectors
 constexpr unsigned long long kWaitNs = 500ULL * 1000ULL * 1000ULL;
@@ -196,11 +196,27 @@ __device__ __forceinline__ double wait_value(const double *p, KState *ks) {
     }
 }
 
-// Rows depended on are read in groups of up to kDepGroup: all their values are loaded at once
+// Dependency slots are handled kDepGroup at a time (8 for the paired-level tables).
+constexpr int kDepGroup = 4;
+
+template <typename T>
+__global__ void k_sf_fill(int64_t nvals, T *y, T *z, unsigned *ticket) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const T sent = sentinel_value<T>();
+    for (; i < nvals; i += stride) {
+        y[i] = sent;
+        z[i] = sent;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 2) ticket[threadIdx.x] = 0u;
+}
+
+// FP32 level-set sweeps, one thread per row (FP32 arithmetic is not limited by the FP64 pipe, and
+// this form measured faster than four lanes per row there).  Rows depended on are read in groups
+// of up to kDepGroup: all their values are loaded at once
 // (relaxed, independent loads), then only the entries still holding the sentinel are polled
 // again, with a short sleep between rounds, until the bounded wait gives up.  Every value is
 // checked on its own, so producers publish with plain relaxed stores and no fence.
-constexpr int kDepGroup = 4;
 
 template <int B, typename T>
 __device__ __forceinline__ void load_group(const T *base, const int32_t *c, T (*v)[B], KState *ks, int sleep_ns) {
@@ -265,17 +281,6 @@ __device__ __forceinline__ void subtract_deps(T *s, int64_t o0, int64_t o1, int 
     }
 }
 
-template <typename T>
-__global__ void k_sf_fill(int64_t nvals, T *y, T *z, unsigned *ticket) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const T sent = sentinel_value<T>();
-    for (; i < nvals; i += stride) {
-        y[i] = sent;
-        z[i] = sent;
-    }
-    if (blockIdx.x == 0 && threadIdx.x < 2) ticket[threadIdx.x] = 0u;
-}
 
 // y(t) = r(pos[t]) - sum_s L(t, s) y(dep(t, s)).  A persistent grid: each block takes chunks of
 // kSfThreads positions in ticket order until none is left.  Factors and y in T, r in RT.
@@ -356,6 +361,7 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_sf(int32_t n, unsigned *
         }
     }
 }
+
 
 // The same sweeps with a row spread over four lanes, lane q of the group computing component q
 // (B <= 4): on GB300 a warp-wide FP64 instruction occupies a sub-partition's FP64 pipe for 64
@@ -1890,7 +1896,8 @@ __global__ void k_fill_sell_csr(int32_t n, const int32_t *cnt, const int32_t *cs
     }
 }
 static cptr_status csr_to_sell(Ctx *c, const int32_t *cnt, const int32_t *csr_off, const int32_t *dep,
-                               const double *blk, int64_t **off64, int32_t **col, double **val) {
+                               const double *blk, int64_t **off64, int32_t **col, void **val) {
+    const bool lo = c->o.precision == CPTR_PREC_MIXED;   // blocks stored in FP32
     const int32_t n = c->n, nch = (n + 31) / 32, BB = c->b * c->b;
     cudaStream_t s = c->stream;
     int32_t *w = nullptr, *off = nullptr, *kidx = nullptr;
@@ -1904,11 +1911,12 @@ static cptr_status csr_to_sell(Ctx *c, const int32_t *cnt, const int32_t *csr_of
     const int64_t ns = (int64_t)total * 32;
     CPTR_TRY(dalloc_t(c, col, (size_t)(ns > 0 ? ns : 1)));
     CPTR_TRY(dalloc_t(c, &kidx, (size_t)(ns > 0 ? ns : 1)));
-    CPTR_TRY(dalloc_t(c, val, (size_t)(ns > 0 ? ns : 1) * BB));
+    CPTR_TRY(dalloc(c, val, (size_t)(ns > 0 ? ns : 1) * BB * (lo ? 4 : 8)));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(*col, 0xFF, sizeof(int32_t) * (ns > 0 ? ns : 1), s));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(kidx, 0xFF, sizeof(int32_t) * (ns > 0 ? ns : 1), s));
     (k_fill_sell_csr<<<nblk(n, 256), 256, 0, s>>>(n, cnt, csr_off, dep, off, *col, kidx), note_launch());
-    if (ns > 0) (k_sf_pack<double><<<nblk(ns, 256), 256, 0, s>>>(ns, BB, kidx, blk, *val), note_launch());
+    if (ns > 0 && lo) (k_sf_pack<float><<<nblk(ns, 256), 256, 0, s>>>(ns, BB, kidx, blk, (float *)*val), note_launch());
+    else if (ns > 0) (k_sf_pack<double><<<nblk(ns, 256), 256, 0, s>>>(ns, BB, kidx, blk, (double *)*val), note_launch());
     CPTR_CUDA_TRY(c, cudaGetLastError());
     dfree(w); dfree(off); dfree(kidx);
     return CPTR_OK;
@@ -1916,8 +1924,8 @@ static cptr_status csr_to_sell(Ctx *c, const int32_t *cnt, const int32_t *csr_of
 
 // the paired-level tables of one sweep; *ok = false when a paired row has too many dependencies
 static cptr_status pair_table(Ctx *c, bool lower, const int32_t *pos, const int32_t *inv, const int32_t *levr,
-                              const int32_t *src_of_row, int64_t **off, int32_t **col, double **val, int64_t **coff,
-                              int32_t **ccol, double **cval, bool *ok) {
+                              const int32_t *src_of_row, int64_t **off, int32_t **col, void **val, int64_t **coff,
+                              int32_t **ccol, void **cval, bool *ok) {
     const int32_t n = c->n, BB = c->b * c->b;
     cudaStream_t s = c->stream;
     int32_t *mcnt = nullptr, *ccnt = nullptr, *moff = nullptr, *coffc = nullptr, *err = nullptr;
@@ -1957,7 +1965,7 @@ static cptr_status pair_table(Ctx *c, bool lower, const int32_t *pos, const int3
     return CPTR_OK;
 }
 
-// both sweeps' paired-level tables (FP64 sweeps only); c->sp_ok tells whether they were built
+// both sweeps' paired-level tables (blocks in the sweeps' precision); c->sp_ok tells whether they were built
 static cptr_status pair_setup(Ctx *c, const int32_t *inv_f, const int32_t *inv_b, const int32_t *levr_f,
                               const int32_t *levr_b) {
     c->sp_ok = false;
@@ -2183,7 +2191,7 @@ cptr_status ilu_setup(Ctx *c, const std::function<cptr_status()> &overlap) {
     CPTR_CUDA_TRY(c, cudaGetLastError());
     dfree(kidx_f); dfree(kidx_b); dfree(kidx_d);
     const int sched = ilu_tuned_schedule(c);
-    if (!lo && (c->o.ilu_sweep == 3 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 2)))) {
+    if (c->o.ilu_sweep == 3 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 2))) {
         const cptr_status ps = pair_setup(c, inv_f, inv_b, levr_f, levr_b);
         if (ps != CPTR_OK) {
             dfree(inv_f); dfree(inv_b); dfree(levr_f); dfree(levr_b);
@@ -2243,7 +2251,6 @@ template <int B, typename T, typename RT, typename XT>
 static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT *dT) {
     cudaStream_t s = c->stream;
     const int32_t n = c->n;
-    const unsigned grid = std::min<unsigned>(nblk(n, kSfThreads), (unsigned)c->sf_grid);
     T *y = (T *)c->sf_y, *zz = (T *)c->sf_z;
     (k_sf_fill<T><<<4 * 152, 256, 0, s>>>((int64_t)n * B, y, zz, c->sf_ticket), note_launch());
     if (c->inject_wait) (k_sf_fill<double><<<1, 32, 0, s>>>(1, c->never, c->never, c->sf_ticket + 2), note_launch());
@@ -2257,7 +2264,7 @@ static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT 
         prof_end(c, pf);
         return;
     }
-    if constexpr (std::is_same<T, double>::value) {   // FP64: a row over four lanes
+    if (std::is_same<T, double>::value || c->sp_use) {   // a row over four lanes, lockstep rounds
         const unsigned gridg = std::min<unsigned>(nblk(n, kSfRowsG), (unsigned)c->sf_grid);
         // the level-set tables, or the paired-level ones (their c-term tables non-null)
         const bool pr = c->sp_use;
@@ -2287,6 +2294,7 @@ static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT 
         prof_end(c, pf);
         return;
     }
+    const unsigned grid = std::min<unsigned>(nblk(n, kSfThreads), (unsigned)c->sf_grid);
     int pf = prof_begin(c, PF_ILU_FWD);
     (k_ilu_fwd_sf<B, T, RT><<<grid, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_f, c->sf_off_f, c->sf_col_f,
                                                          (const T *)c->sf_val_f, r, y, c->ks,

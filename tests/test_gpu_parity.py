@@ -403,3 +403,27 @@ def test_paired_level_sweeps(name):
     o = oracle.Oracle.from_system(s, **OPTS[name])
     assert relerr(host(zb), o.ilu_apply(r)) <= 1e-10
     check_solve(s, o, b, 1e-8)
+
+
+@pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "medium", "line"])
+def test_paired_level_sweeps_mixed(name):
+    """The paired-level tables in FP32 (mixed form): against the FP64 ILU(0), the FP32 paired
+    sweeps are as accurate as the FP32 level-set sweeps (both carry FP32 rounding through every
+    level), and solves converge like them."""
+    s = system(name)
+    o = {**OPTS[name], "precision": cp.PRECISION["mixed"]}
+    a = gpu_solver(s, ilu_sweep=cp.ILU_SWEEP["levels"], **o)
+    b = gpu_solver(s, ilu_sweep=cp.ILU_SWEEP["paired"], **o)
+    f = gpu_solver(s, ilu_sweep=cp.ILU_SWEEP["levels"], **OPTS[name])
+    assert [r for r in cp.cptr_tuning(b.ctx) if r[2] == 5][0][3] == 2
+    r = dev(np.random.default_rng(5).normal(size=s["n"] * s["b"]))
+    za, zb, z64 = torch.empty_like(r), torch.empty_like(r), torch.empty_like(r)
+    cp.cptr_apply_ilu(a.ctx, r, za)
+    cp.cptr_apply_ilu(b.ctx, r, zb)
+    cp.cptr_apply_ilu(f.ctx, r, z64)
+    ea, eb = relerr(host(za), host(z64)), relerr(host(zb), host(z64))
+    assert ea <= 1e-3 and eb <= 2 * ea + 1e-6, (ea, eb)
+    xa, ia = a.solve(dev(s["rhs"].reshape(-1)), 1e-8)
+    xb, ib = b.solve(dev(s["rhs"].reshape(-1)), 1e-8)
+    assert ib["status"] == "CPTR_OK" and ib["true_rel_res"] <= 1e-8 * 1.05
+    assert abs(ia["iters"] - ib["iters"]) <= 1
