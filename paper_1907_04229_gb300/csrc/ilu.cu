@@ -2165,31 +2165,9 @@ cptr_status ilu_setup(Ctx *c, const std::function<cptr_status()> &overlap) {
         CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->sf_pos_b, c->lvl_b, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
     }
     (k_compose<<<nblk(n, 256), 256, 0, st>>>(n, inv_f, c->lvl_b, c->sf_bmap), note_launch());
-    int32_t *kidx_f = nullptr, *kidx_b = nullptr, *kidx_d = nullptr;
-    int64_t ns_f = 0, ns_b = 0;
-    CPTR_TRY(device_table(c, c->lvl_f, inv_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, true, &c->sf_off_f, &c->sf_col_f,
-                          &kidx_f, &ns_f));
-    CPTR_TRY(device_table(c, c->lvl_b, inv_b, c->ilu_rp, c->ilu_ci, c->ilu_diag, false, &c->sf_off_b, &c->sf_col_b,
-                          &kidx_b, &ns_b));
-    CPTR_TRY(dalloc_t(c, &kidx_d, (size_t)nch * 32));
-    CPTR_CUDA_TRY(c, cudaMemsetAsync(kidx_d, 0xFF, sizeof(int32_t) * nch * 32, st));
-    (k_dinv_index<<<nblk(n, 256), 256, 0, st>>>(n, c->lvl_b, c->ilu_diag, kidx_d), note_launch());
     const bool lo = c->o.precision == CPTR_PREC_MIXED;   // factors stored in FP32
-    auto pack = [&](const int32_t *kidx, int64_t ns, void **dst) -> cptr_status {
-        CPTR_TRY(dalloc(c, dst, (size_t)(ns > 0 ? ns : 1) * BB * (lo ? 4 : 8)));
-        if (ns == 0) return CPTR_OK;
-        if (lo) (k_sf_pack<float><<<nblk(ns, 256), 256, 0, st>>>(ns, BB, kidx, c->LU, (float *)*dst), note_launch());
-        else (k_sf_pack<double><<<nblk(ns, 256), 256, 0, st>>>(ns, BB, kidx, c->LU, (double *)*dst), note_launch());
-        return CPTR_OK;
-    };
-    CPTR_TRY(pack(kidx_f, ns_f, &c->sf_val_f));
-    CPTR_TRY(pack(kidx_b, ns_b, &c->sf_val_b));
-    CPTR_TRY(pack(kidx_d, (int64_t)nch * 32, &c->sf_dinv));
-    // (+64 bytes: the chunked sweeps read 32-byte windows around a row's values)
-    CPTR_TRY(dalloc(c, &c->sf_y, (size_t)n * c->b * (lo ? 4 : 8) + 64));
-    CPTR_TRY(dalloc(c, &c->sf_z, (size_t)n * c->b * (lo ? 4 : 8) + 64));
-    CPTR_CUDA_TRY(c, cudaGetLastError());
-    dfree(kidx_f); dfree(kidx_b); dfree(kidx_d);
+    // paired-level tables first: when they are the schedule in use (forced, or chosen by a cached
+    // tuning), the level-set tables of L and U are not needed
     const int sched = ilu_tuned_schedule(c);
     if (c->o.ilu_sweep == 3 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 2))) {
         const cptr_status ps = pair_setup(c, inv_f, inv_b, levr_f, levr_b);
@@ -2199,6 +2177,32 @@ cptr_status ilu_setup(Ctx *c, const std::function<cptr_status()> &overlap) {
         }
         c->sp_use = c->sp_ok && (c->o.ilu_sweep == 3 || sched == 2);
     }
+    int32_t *kidx_f = nullptr, *kidx_b = nullptr, *kidx_d = nullptr;
+    int64_t ns_f = 0, ns_b = 0;
+    auto pack = [&](const int32_t *kidx, int64_t ns, void **dst) -> cptr_status {
+        CPTR_TRY(dalloc(c, dst, (size_t)(ns > 0 ? ns : 1) * BB * (lo ? 4 : 8)));
+        if (ns == 0) return CPTR_OK;
+        if (lo) (k_sf_pack<float><<<nblk(ns, 256), 256, 0, st>>>(ns, BB, kidx, c->LU, (float *)*dst), note_launch());
+        else (k_sf_pack<double><<<nblk(ns, 256), 256, 0, st>>>(ns, BB, kidx, c->LU, (double *)*dst), note_launch());
+        return CPTR_OK;
+    };
+    if (!c->sp_use) {
+        CPTR_TRY(device_table(c, c->lvl_f, inv_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, true, &c->sf_off_f, &c->sf_col_f,
+                              &kidx_f, &ns_f));
+        CPTR_TRY(device_table(c, c->lvl_b, inv_b, c->ilu_rp, c->ilu_ci, c->ilu_diag, false, &c->sf_off_b,
+                              &c->sf_col_b, &kidx_b, &ns_b));
+        CPTR_TRY(pack(kidx_f, ns_f, &c->sf_val_f));
+        CPTR_TRY(pack(kidx_b, ns_b, &c->sf_val_b));
+    }
+    CPTR_TRY(dalloc_t(c, &kidx_d, (size_t)nch * 32));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(kidx_d, 0xFF, sizeof(int32_t) * nch * 32, st));
+    (k_dinv_index<<<nblk(n, 256), 256, 0, st>>>(n, c->lvl_b, c->ilu_diag, kidx_d), note_launch());
+    CPTR_TRY(pack(kidx_d, (int64_t)nch * 32, &c->sf_dinv));
+    // (+64 bytes: the chunked sweeps read 32-byte windows around a row's values)
+    CPTR_TRY(dalloc(c, &c->sf_y, (size_t)n * c->b * (lo ? 4 : 8) + 64));
+    CPTR_TRY(dalloc(c, &c->sf_z, (size_t)n * c->b * (lo ? 4 : 8) + 64));
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    dfree(kidx_f); dfree(kidx_b); dfree(kidx_d);
     dfree(inv_f); dfree(inv_b); dfree(levr_f); dfree(levr_b);
     if (!mc && (c->o.ilu_sweep == 2 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 1))))
         CPTR_TRY(cw_setup(c));
