@@ -201,8 +201,7 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) {
         // The two hierarchies are independent: the temperature one is built by a second host
         // thread on its own stream (a context view with its own stream, scratch flag and scan
-        // buffer) while this thread builds the ILU(0) factors and, while their factorisation
-        // kernel runs, the pressure hierarchy.
+        // buffer) while this thread builds the pressure one and then the ILU(0) factors.
         if (!c->amg_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->amg_stream, cudaStreamNonBlocking));
         if (!c->coarse_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->coarse_stream, cudaStreamNonBlocking));
         if (!c->amg_fork) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&c->amg_fork, cudaEventDisableTiming));
@@ -222,20 +221,19 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
             w.scan_tmp = nullptr;
             cudaStreamSynchronize(w.stream);
         });
-        // the pressure hierarchy is built while the ILU(0) factorisation kernel runs
-        auto hp_setup = [&] { return amg_setup(c, c->hp, c->rp, c->ci, c->App, n); };
-        cptr_status st_p = c->o.stage2 == CPTR_STAGE2_ILU0 ? ilu_setup(c, hp_setup) : hp_setup();
+        // This thread builds the pressure hierarchy, then the ILU(0) factors.  (Running the
+        // factorisation kernel on a stream of its own during the pressure hierarchy saved ~2 ms on
+        // cptr200k, but on 2M-cell systems some set-ups then stalled for ~0.3 s; not used.)
+        cptr_status st_p = amg_setup(c, c->hp, c->rp, c->ci, c->App, n);
+        if (st_p == CPTR_OK && c->o.stage2 == CPTR_STAGE2_ILU0) st_p = ilu_setup(c);
         worker.join();
         for (int q = 0; q < kSetupPhases; ++q) c->prof.setup_ms[q] += w.prof.setup_ms[q];
         dfree(w.flag);
         if (st_p != CPTR_OK) return st_p;
         if (st_T != CPTR_OK) return c->fail(st_T, w.err);
     } else {
-        auto hp_setup = [&] {
-            return s1 != CPTR_STAGE1_NONE ? amg_setup(c, c->hp, c->rp, c->ci, c->App, n) : CPTR_OK;
-        };
-        if (c->o.stage2 == CPTR_STAGE2_ILU0) CPTR_TRY(ilu_setup(c, hp_setup));
-        else CPTR_TRY(hp_setup());
+        if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_setup(c, c->hp, c->rp, c->ci, c->App, n));
+        if (c->o.stage2 == CPTR_STAGE2_ILU0) CPTR_TRY(ilu_setup(c));
     }
     // the coarsest inverses ran on the coarse stream meanwhile
     CPTR_TRY(amg_coarsest_wait(c, c->hp));
@@ -411,6 +409,12 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
             if (cudaMemPoolCreate(&c->pool, &props) == cudaSuccess) {
                 uint64_t keep = UINT64_MAX;
                 cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+                // the set-up allocates from several streams (two host threads, the factorisation
+                // and the coarsest inverses on streams of their own): memory freed on one stream is
+                // reused on another only once the free has completed, never by making the
+                // allocating stream wait on the other one's pending work
+                int no = 0;
+                cudaMemPoolSetAttribute(c->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
             } else {
                 c->pool = nullptr;   // fall back to cudaMalloc
             }
@@ -441,7 +445,6 @@ void cptr_destroy(cptr_ctx *ctx) {
         if (c->side_stream) cudaStreamSynchronize(c->side_stream);
         if (c->coarse_stream) cudaStreamSynchronize(c->coarse_stream);
         if (c->amg_stream) cudaStreamSynchronize(c->amg_stream);
-        if (c->ilu_stream) cudaStreamSynchronize(c->ilu_stream);
         release_setup(c);
         dfree(c->ks); dfree(c->flag); dfree(c->partial); dfree(c->scan_tmp); dfree(c->never); dfree(c->ilu_flags);
         dfree(c->mlp);
@@ -455,9 +458,6 @@ void cptr_destroy(cptr_ctx *ctx) {
     if (c->coarse_stream) cudaStreamDestroy(c->coarse_stream);
     if (c->amg_stream) cudaStreamDestroy(c->amg_stream);
     if (c->amg_fork) cudaEventDestroy(c->amg_fork);
-    if (c->ilu_stream) cudaStreamDestroy(c->ilu_stream);
-    if (c->ilu_fork) cudaEventDestroy(c->ilu_fork);
-    if (c->ilu_done) cudaEventDestroy(c->ilu_done);
     if (c->side_fork) cudaEventDestroy(c->side_fork);
     if (c->side_join) cudaEventDestroy(c->side_join);
     for (Hier *h : {&c->hp, &c->hT})

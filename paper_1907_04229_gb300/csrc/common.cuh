@@ -7,7 +7,6 @@
 #include <stddef.h>
 #include <stdint.h>
 
-#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -216,9 +215,7 @@ void amg_vcycle32(const Ctx *c, const Hier &h, const float *b, float *x);
 cptr_status amg_lower_precision(Ctx *c, Hier &h);
 
 // ---- ilu.cu ------------------------------------------------------------------------------------
-// ILU(0) set-up; overlap (if given) runs on this thread while the factorisation kernel runs on
-// its own stream, and its status is returned if not CPTR_OK
-cptr_status ilu_setup(Ctx *c, const std::function<cptr_status()> &overlap = {});
+cptr_status ilu_setup(Ctx *c);
 void ilu_free(Ctx *c);
 void ilu_apply(const Ctx *c, const double *r, double *z, const double *dp, const double *dT);
 void ilu_apply_into(const Ctx *c, const double *r, double *z, double *ybuf, double *zbuf);
@@ -324,8 +321,6 @@ struct Ctx {
     cudaStream_t cap_stream = nullptr;
     cudaStream_t side_stream = nullptr;   // set-up work that overlaps the main stream
     cudaStream_t coarse_stream = nullptr; // the coarsest AMG inverses, overlapping the rest of the set-up
-    cudaStream_t ilu_stream = nullptr;    // the ILU(0) factorisation, overlapping the pressure hierarchy
-    cudaEvent_t ilu_fork = nullptr, ilu_done = nullptr;
     cudaStream_t amg_stream = nullptr;    // the second hierarchy, built by a second host thread
     cudaEvent_t amg_fork = nullptr;
     cudaEvent_t side_fork = nullptr, side_join = nullptr;

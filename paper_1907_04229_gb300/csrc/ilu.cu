@@ -1990,7 +1990,7 @@ static int ilu_tuned_schedule(const Ctx *c) {
     return it == c->tune_cache.end() ? -1 : it->second.G;
 }
 
-cptr_status ilu_setup(Ctx *c, const std::function<cptr_status()> &overlap) {
+cptr_status ilu_setup(Ctx *c) {
     ilu_free(c);
     double t0 = host_ms();
     const int32_t n = c->n, BB = c->b * c->b;
@@ -2070,7 +2070,7 @@ cptr_status ilu_setup(Ctx *c, const std::function<cptr_status()> &overlap) {
         c->ilu_epoch = 0;
     }
     ++c->ilu_epoch;
-    int32_t *fsing = c->flag + 3;   // the factorisation's singular flag (flag[0] serves the overlapped work)
+    int32_t *fsing = c->flag + 3;   // the factorisation's singular flag
     CPTR_CUDA_TRY(c, cudaMemsetAsync(fsing, 0, sizeof(int32_t), st));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(c->sf_ticket, 0, 4 * sizeof(unsigned), st));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(reinterpret_cast<char *>(c->ks) + offsetof(KState, wait_err), 0, sizeof(int32_t), st));
@@ -2089,13 +2089,7 @@ cptr_status ilu_setup(Ctx *c, const std::function<cptr_status()> &overlap) {
         maxdep = h_ext[1];
         maxu = h_ext[2];
     }
-    // the factorisation runs on its own stream; the caller's overlapped work goes on meanwhile
-    if (!c->ilu_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->ilu_stream, cudaStreamNonBlocking));
-    if (!c->ilu_fork) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&c->ilu_fork, cudaEventDisableTiming));
-    if (!c->ilu_done) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&c->ilu_done, cudaEventDisableTiming));
-    cudaStream_t fst = c->ilu_stream;
-    CPTR_CUDA_TRY(c, cudaEventRecord(c->ilu_fork, st));
-    CPTR_CUDA_TRY(c, cudaStreamWaitEvent(fst, c->ilu_fork, 0));
+    cudaStream_t fst = st;
     const size_t fs_rowsz = (size_t)((maxrow * BB + 1) & ~1), fs_w = (size_t)(((1 + maxu) * BB + 3) & ~1);
     const size_t fs_bytes = (size_t)64 * ((fs_rowsz + (size_t)maxdep * fs_w) * 8 + (size_t)(maxrow + maxdep * (2 + maxu)) * 4);
     const unsigned fgrid = std::min<unsigned>(nblk(n, 64), 8 * 152);
@@ -2136,16 +2130,6 @@ cptr_status ilu_setup(Ctx *c, const std::function<cptr_status()> &overlap) {
         (k_bilu_factor_sf<4><<<fgrid, 64, 0, fst>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, c->LU,
                                                     c->ilu_flags, c->ilu_epoch, fsing, c->ks), note_launch());
     CPTR_CUDA_TRY(c, cudaGetLastError());
-    CPTR_CUDA_TRY(c, cudaEventRecord(c->ilu_done, fst));
-    if (overlap) {
-        const cptr_status ov = overlap();
-        if (ov != CPTR_OK) {
-            cudaEventSynchronize(c->ilu_done);   // the factors are freed with the failed set-up
-            return ov;
-        }
-        t0 = host_ms();
-    }
-    CPTR_CUDA_TRY(c, cudaStreamWaitEvent(st, c->ilu_done, 0));
     int32_t sing = 0, werr = 0;
     CPTR_TRY(copy_to_host(c, &sing, fsing, sizeof(int32_t)));
     CPTR_TRY(copy_to_host(c, &werr, reinterpret_cast<char *>(c->ks) + offsetof(KState, wait_err), sizeof(int32_t)));
