@@ -1057,150 +1057,6 @@ __global__ void __launch_bounds__(64) k_bilu_factor_sf(int32_t n, unsigned *tick
     }
 }
 
-// The same factorisation with the memory traffic of a row batched so that, once its last
-// dependency is published, a row costs one memory round trip before it computes.  Before the
-// flags are set (off the critical path, since tickets run many levels ahead): the row's own
-// blocks and columns, then the pivot and row-end positions of its dependencies, then the column
-// indices of their upper parts, all by cp.async into shared memory (none of these are written
-// during the launch).  Once every flag is set and an acquire fence orders what follows: the pivot
-// inverse and upper blocks of every dependency (one contiguous run of blocks each) by 16-byte
-// cp.async through L2 only, into a window rounded out to 16-byte boundaries.  The row is then
-// factored in shared memory in exactly the order of k_bilu_factor_sf (same operations, same
-// rounding); its pivot and upper blocks are written and the flag released before its lower
-// blocks are written (no row of the launch reads those).  Shared memory per thread: rowsz
-// doubles for the row (maxrow blocks, even), maxdep windows of W doubles, and maxrow + 2 maxdep +
-// maxdep maxu integers.
-template <int B>
-__global__ void __launch_bounds__(64) k_bilu_factor_st(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
-                                                       const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                                       const int32_t *__restrict__ diag, double *LU, int32_t *flag,
-                                                       int32_t epoch, int32_t *singular, KState *ks, int maxrow,
-                                                       int maxdep, int maxu) {
-    constexpr int BB = B * B;
-    extern __shared__ __align__(16) unsigned char fs_smem[];
-    const int rowsz = (maxrow * BB + 1) & ~1;
-    const int W = ((1 + maxu) * BB + 2 + 1) & ~1;
-    const int per = rowsz + maxdep * W;                       // doubles per thread (even)
-    double *rowb = reinterpret_cast<double *>(fs_smem) + (int64_t)threadIdx.x * per;
-    double *depw = rowb + rowsz;
-    const int iper = maxrow + maxdep * (2 + maxu);
-    int32_t *cols = reinterpret_cast<int32_t *>(reinterpret_cast<double *>(fs_smem) + (int64_t)blockDim.x * per) +
-                    threadIdx.x * iper;
-    int32_t *dcs = cols + maxrow, *ecs = dcs + maxdep, *ucol = ecs + maxdep;
-    __shared__ unsigned blk;
-    const unsigned nchunks = (unsigned)((n + 63) / 64);
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) blk = atomicAdd(ticket, 1u);
-        __syncthreads();
-        const unsigned b = blk;
-        if (b >= nchunks) return;
-        const int32_t t = (int32_t)(b * 64 + threadIdx.x);
-        if (t >= n) continue;
-        const int32_t i = pos[t];
-        const int32_t k0 = rp[i], e = rp[i + 1], kd = diag[i], len = e - k0, nd = kd - k0;
-        // the row's columns (group 1) and blocks (group 2); nobody else writes them
-        for (int32_t k = 0; k < len; ++k) cp_async_i32(cols + k, ci + k0 + k);
-        cp_async_commit();
-        for (int32_t k = 0; k < len; ++k)
-#pragma unroll
-            for (int q = 0; q < BB; ++q) cp_async_elem(rowb + k * BB + q, LU + (int64_t)(k0 + k) * BB + q);
-        cp_async_commit();
-        cp_async_wait_1();
-        // pivot position and row end of each dependency, then the columns of its upper part
-        for (int32_t k = 0; k < nd; ++k) {
-            const int32_t c = cols[k];
-            cp_async_i32(dcs + k, diag + c);
-            cp_async_i32(ecs + k, rp + c + 1);
-        }
-        cp_async_commit();
-        cp_async_wait_0();
-        for (int32_t k = 0; k < nd; ++k)
-            for (int32_t qq = dcs[k] + 1; qq < ecs[k]; ++qq) cp_async_i32(ucol + k * maxu + (qq - dcs[k] - 1), ci + qq);
-        cp_async_commit();
-        // wait until every dependency has published its blocks: all flags are read together
-        // with relaxed loads, re-read until set; one acquire fence then orders the copies of
-        // their blocks after the flags
-        {
-            unsigned long long t0 = 0;
-            bool pending = true;
-            for (int round = 0; pending; ++round) {
-                pending = false;
-                for (int32_t k = 0; k < nd; ++k) {
-                    int32_t f;
-                    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flag + cols[k]) : "memory");
-                    pending |= f != epoch;
-                }
-                if (!pending) break;
-                if (round == 0) t0 = gtimer();
-                else if (gtimer() - t0 > kWaitNs) { atomicExch(&ks->wait_err, 1); break; }
-                __nanosleep(20);
-            }
-            asm volatile("fence.acq_rel.gpu;" ::: "memory");
-        }
-        // every dependency's pivot inverse and upper blocks: the run of blocks [dc, ec) of LU,
-        // copied in 16-byte pieces from the 16-byte boundary at or below its start
-        for (int32_t k = 0; k < nd; ++k) {
-            const int64_t lo = (int64_t)dcs[k] * BB, hi = (int64_t)ecs[k] * BB;   // in doubles
-            const int64_t a0 = lo & ~(int64_t)1;
-            double *w = depw + (int64_t)k * W;
-            for (int64_t u = a0; u < hi; u += 2) cp_async_cg16(w + (u - a0), LU + u);
-        }
-        cp_async_commit();
-        cp_async_wait_0();
-        // factor the row in shared memory (the order of k_bilu_factor_sf)
-        for (int32_t k = k0; k < kd; ++k) {
-            const int32_t dc = dcs[k - k0], ec = ecs[k - k0];
-            const double *dinv = depw + (int64_t)(k - k0) * W + (int)(((int64_t)dc * BB) & 1);
-            const int32_t *uc = ucol + (k - k0) * maxu;
-            double a[BB], l[BB];
-#pragma unroll
-            for (int q = 0; q < BB; ++q) a[q] = rowb[(k - k0) * BB + q];
-#pragma unroll
-            for (int r = 0; r < B; ++r)
-#pragma unroll
-                for (int q = 0; q < B; ++q) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int u = 0; u < B; ++u) s = fma(a[r * B + u], dinv[u * B + q], s);
-                    l[r * B + q] = s;
-                }
-#pragma unroll
-            for (int q = 0; q < BB; ++q) rowb[(k - k0) * BB + q] = l[q];
-            int32_t p = k + 1;
-            for (int32_t qq = dc + 1; qq < ec; ++qq) {
-                const int32_t j = uc[qq - dc - 1];
-                while (p < e && cols[p - k0] < j) ++p;
-                if (p < e && cols[p - k0] == j) {
-                    const double *u = dinv + (qq - dc) * BB;
-                    double *d = rowb + (p - k0) * BB;
-#pragma unroll
-                    for (int r = 0; r < B; ++r)
-#pragma unroll
-                        for (int q = 0; q < B; ++q) {
-                            double s = d[r * B + q];
-#pragma unroll
-                            for (int w = 0; w < B; ++w) s = fma(-l[r * B + w], u[w * B + q], s);
-                            d[r * B + q] = s;
-                        }
-                }
-            }
-        }
-        double dd[BB];
-#pragma unroll
-        for (int q = 0; q < BB; ++q) dd[q] = rowb[nd * BB + q];
-        if (!block_inverse<B>(dd)) atomicOr(singular, 1);
-#pragma unroll
-        for (int q = 0; q < BB; ++q) rowb[nd * BB + q] = dd[q];
-        for (int32_t k = nd; k < len; ++k)
-#pragma unroll
-            for (int q = 0; q < BB; ++q) LU[(int64_t)(k0 + k) * BB + q] = rowb[k * BB + q];
-        asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(flag + i), "r"(epoch) : "memory");
-        for (int32_t k = 0; k < nd; ++k)
-#pragma unroll
-            for (int q = 0; q < BB; ++q) LU[(int64_t)(k0 + k) * BB + q] = rowb[k * BB + q];
-    }
-}
 
 // In-place inverse of the pivot block by the four lanes of a row's group, lane r holding row r of
 // [D | I] (lanes r >= B only take part in the shuffles): Gauss-Jordan with partial pivoting, the
@@ -1257,12 +1113,21 @@ __device__ __forceinline__ bool group_inverse(double *blk, int r, unsigned gmask
     return true;
 }
 
-// The staged factorisation with a row over four lanes (B <= 4): lane r computes row r of every
-// block of the row (its B FMAs per entry of L_ik = A_ik D_k^{-1} and of each update A_ij -= L_ik
-// U_kj), so that a level's FP64 pipe time is a quarter of the one-thread-per-row form, and the
-// pivot block is inverted by the group together (group_inverse).  The copies of the staged
-// kernel are shared out over the lanes.  Same values as k_bilu_factor_sf.  Shared memory per row
-// as in k_bilu_factor_st; kSfRowsG rows per block.
+// The factorisation with a row over four lanes (B <= 4) and its memory traffic batched, so that
+// once its last dependency is published a row costs one memory round trip before it computes.
+// Before the flags are set (off the critical path, since tickets run levels ahead): the row's
+// own blocks and columns, then the pivot and row-end positions of its dependencies, then the
+// column indices of their upper parts, all by cp.async into shared memory (none of these are
+// written during the launch).  Once every flag is set and acquire fences order what follows:
+// each dependency's pivot inverse and upper blocks (one contiguous run of blocks) by 16-byte
+// cp.async through L2 only, into a window rounded out to 16-byte boundaries (LU has two spare
+// doubles for that).  Lane r then computes row r of every block of the row (its B FMAs per entry
+// of L_ik = A_ik D_k^{-1} and of each update A_ij -= L_ik U_kj, in the order of
+// k_bilu_factor_sf), and the four lanes invert the pivot block together (group_inverse).  The
+// pivot and upper blocks are written and the flag released before the lower blocks are written
+// (no row of the launch reads those).  Shared memory per row: rowsz doubles for the row's blocks
+// (even), maxdep windows of W doubles, and maxrow + 2 maxdep + maxdep maxu integers; kSfRowsG
+// rows per block.  Patterns too wide for that run k_bilu_factor_sf.
 template <int B>
 __global__ void __launch_bounds__(kSfThreads) k_bilu_factor_g(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
                                                              const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
@@ -2074,7 +1939,7 @@ cptr_status ilu_setup(Ctx *c) {
     CPTR_CUDA_TRY(c, cudaMemsetAsync(fsing, 0, sizeof(int32_t), st));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(c->sf_ticket, 0, 4 * sizeof(unsigned), st));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(reinterpret_cast<char *>(c->ks) + offsetof(KState, wait_err), 0, sizeof(int32_t), st));
-    // per-row sizes of the pattern: the staged kernel holds a row, and the pivot inverse and upper
+    // per-row sizes of the pattern: the factorisation kernel holds a row, and the pivot inverse and upper
     // blocks of each dependency, in shared memory when that fits
     int maxrow = 0, maxdep = 0, maxu = 0;
     {
@@ -2109,19 +1974,6 @@ cptr_status ilu_setup(Ctx *c) {
             (k_bilu_factor_g<4><<<ggrid, kSfThreads, fg_bytes, fst>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
                                                                       c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch,
                                                                       fsing, c->ks, maxrow, maxdep, maxu), note_launch());
-        }
-    } else if (fs_bytes <= 100 * 1024) {
-        const unsigned sgrid = std::min<unsigned>(nblk(n, 64), 2 * 152);
-        if (c->b == 3) {
-            cudaFuncSetAttribute(k_bilu_factor_st<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-            (k_bilu_factor_st<3><<<sgrid, 64, fs_bytes, fst>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
-                                                              c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch, fsing,
-                                                              c->ks, maxrow, maxdep, maxu), note_launch());
-        } else {
-            cudaFuncSetAttribute(k_bilu_factor_st<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-            (k_bilu_factor_st<4><<<sgrid, 64, fs_bytes, fst>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
-                                                              c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch, fsing,
-                                                              c->ks, maxrow, maxdep, maxu), note_launch());
         }
     } else if (c->b == 3)
         (k_bilu_factor_sf<3><<<fgrid, 64, 0, fst>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, c->LU,
