@@ -2184,10 +2184,10 @@ void ilu_apply_into(const Ctx *c, const double *r, double *z, double *ybuf, doub
 }
 
 // Autotuner of the one-launch ILU(0) sweeps: the persistent grid (blocks in {152, 304, 608,
-// 1216}) and the back-off between polls of a dependency not yet written (__nanosleep of {8, 32,
-// 128, 512} ns), which set how many rows run ahead of the wavefront and how hard they poll; then,
-// where they were built, the paired-level and the chunked schedules at that grid, each at its best
-// back-off, and the fastest schedule is kept.  Each candidate is timed with CUDA events over 3
+// 1216}) and the back-off between polls of a dependency not yet written (__nanosleep of {0, 8, 32,
+// 128, 512} ns), which set how many rows run ahead of the wavefront and how hard they poll, for
+// the level-set schedule and, where they were built, the paired-level one; the back-off of the
+// chunked schedule; the fastest schedule is kept.  Each candidate is timed with CUDA events over 3
 // applications (forward + backward) after a warm-up, on a zero right-hand side; the result is
 // cached by the factor size.
 cptr_status ilu_autotune(Ctx *c) {
@@ -2223,44 +2223,45 @@ cptr_status ilu_autotune(Ctx *c) {
         cudaEventElapsedTime(&ms, e0, e1);
         return ms;
     };
-    int best_g = c->sf_grid, best_s = c->sf_sleep;
-    float best_ms = 1e30f;
     const unsigned maxg = nblk(c->n, kSfThreads);
-    for (int g : {152, 304, 608, 1216}) {
-        if (g > (int)maxg && g != 152) continue;
-        for (int sl : {8, 32, 128, 512}) {
-            c->sf_grid = g;
-            c->sf_sleep = sl;
-            const float ms = time3();
-            if (ms < best_ms) { best_ms = ms; best_g = g; best_s = sl; }
-        }
-    }
-    c->sf_grid = best_g;
-    int sched = c->sp_use ? 2 : 0;
-    // the other schedules at the best grid, each at its best back-off; the fastest is kept
-    auto sleeps = [&](int *bs) -> float {
+    // grid x back-off of the schedule now set; the fastest pair and its time
+    auto search = [&](int *bg, int *bs) -> float {
         float bm = 1e30f;
-        for (int sl : {8, 32, 128, 512}) {
-            c->sf_sleep = sl;
-            const float ms = time3();
-            if (ms < bm) { bm = ms; *bs = sl; }
+        for (int g : {152, 304, 608, 1216}) {
+            if (g > (int)maxg && g != 152) continue;
+            for (int sl : {0, 8, 32, 128, 512}) {
+                c->sf_grid = g;
+                c->sf_sleep = sl;
+                const float ms = time3();
+                if (ms < bm) { bm = ms; *bg = g; *bs = sl; }
+            }
         }
         return bm;
     };
+    int best_g = c->sf_grid, best_s = c->sf_sleep;
+    float best_ms = search(&best_g, &best_s);
+    int sched = c->sp_use ? 2 : 0;
+    // the other schedules, each at its own best grid and back-off; the fastest is kept
     if (auto_sched && c->sp_ok) {
         c->sp_use = true;
-        int sl = best_s;
-        const float ms = sleeps(&sl);
+        int g = best_g, sl = best_s;
+        const float ms = search(&g, &sl);
         c->sp_use = false;
-        if (ms < best_ms) { best_ms = ms; best_s = sl; sched = 2; }
+        if (ms < best_ms) { best_ms = ms; best_g = g; best_s = sl; sched = 2; }
     }
-    if (auto_sched && c->cw_ok) {
+    if (auto_sched && c->cw_ok) {   // one block per chunk: only the back-off matters
         c->cw_use = true;
+        float bm = 1e30f;
         int sl = best_s;
-        const float ms = sleeps(&sl);
+        for (int v : {0, 8, 32, 128, 512}) {
+            c->sf_sleep = v;
+            const float ms = time3();
+            if (ms < bm) { bm = ms; sl = v; }
+        }
         c->cw_use = false;
-        if (ms < best_ms) { best_ms = ms; best_s = sl; sched = 1; }
+        if (bm < best_ms) { best_ms = bm; best_s = sl; sched = 1; }
     }
+    c->sf_grid = best_g;
     if (auto_sched) {
         c->cw_use = sched == 1;
         c->sp_use = sched == 2;
