@@ -1954,7 +1954,6 @@ cptr_status ilu_setup(Ctx *c) {
         maxdep = h_ext[1];
         maxu = h_ext[2];
     }
-    cudaStream_t fst = st;
     const size_t fs_rowsz = (size_t)((maxrow * BB + 1) & ~1), fs_w = (size_t)(((1 + maxu) * BB + 3) & ~1);
     const size_t fs_bytes = (size_t)64 * ((fs_rowsz + (size_t)maxdep * fs_w) * 8 + (size_t)(maxrow + maxdep * (2 + maxu)) * 4);
     const unsigned fgrid = std::min<unsigned>(nblk(n, 64), 8 * 152);
@@ -1966,20 +1965,20 @@ cptr_status ilu_setup(Ctx *c) {
         const unsigned ggrid = std::min<unsigned>(nblk(n, kSfRowsG), 150u);
         if (c->b == 3) {
             cudaFuncSetAttribute(k_bilu_factor_g<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-            (k_bilu_factor_g<3><<<ggrid, kSfThreads, fg_bytes, fst>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
+            (k_bilu_factor_g<3><<<ggrid, kSfThreads, fg_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
                                                                       c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch,
                                                                       fsing, c->ks, maxrow, maxdep, maxu), note_launch());
         } else {
             cudaFuncSetAttribute(k_bilu_factor_g<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-            (k_bilu_factor_g<4><<<ggrid, kSfThreads, fg_bytes, fst>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
+            (k_bilu_factor_g<4><<<ggrid, kSfThreads, fg_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
                                                                       c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch,
                                                                       fsing, c->ks, maxrow, maxdep, maxu), note_launch());
         }
     } else if (c->b == 3)
-        (k_bilu_factor_sf<3><<<fgrid, 64, 0, fst>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, c->LU,
+        (k_bilu_factor_sf<3><<<fgrid, 64, 0, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, c->LU,
                                                     c->ilu_flags, c->ilu_epoch, fsing, c->ks), note_launch());
     else
-        (k_bilu_factor_sf<4><<<fgrid, 64, 0, fst>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, c->LU,
+        (k_bilu_factor_sf<4><<<fgrid, 64, 0, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci, c->ilu_diag, c->LU,
                                                     c->ilu_flags, c->ilu_epoch, fsing, c->ks), note_launch());
     CPTR_CUDA_TRY(c, cudaGetLastError());
     int32_t sing = 0, werr = 0;
