@@ -630,3 +630,121 @@ def test_union_preconditioner_is_block_diagonal():
     assert np.all(z[nb0:] == 0.0)
     with pytest.raises(ValueError):
         ou.solve_block(1, a["n"], a["rhs"], 1e-8)     # a range that cuts through the coupling
+
+
+# ------------------------------------------------------------------------------------------------
+# Paired levels (the evaluation order of the GPU's ILU(0) sweeps, not a separate method): a row
+# of odd level substitutes its dependencies of the level before.  Written here from the algebra
+# of the two triangular solves, on textbook block ILU(0) factors, and checked against the plain
+# substitution on a random block pattern (dependencies one and several levels back) and on the
+# oracle's own ILU solve.
+def _block_ilu_factors(n, b, pattern, blocks):
+    """Textbook block ILU(0): L_ik = A_ik D_k^-1 (i > k), U_ij (i < j), D_i, in place."""
+    F = {key: val.copy() for key, val in blocks.items()}
+    for i in range(n):
+        row = sorted(pattern[i])
+        for k in [c for c in row if c < i]:
+            F[(i, k)] = F[(i, k)] @ np.linalg.inv(F[(k, k)])
+            for j in [c for c in row if c > k]:
+                if (k, j) in F:
+                    F[(i, j)] = F[(i, j)] - F[(i, k)] @ F[(k, j)]
+    return F
+
+
+def _levels(n, deps):
+    lev = np.zeros(n, int)
+    order = range(n) if all(k < i for i in range(n) for k in deps[i]) else reversed(range(n))
+    for i in order:
+        lev[i] = 1 + max((lev[k] for k in deps[i]), default=-1)
+    return lev
+
+
+def _paired_solves(n, b, pattern, F, r):
+    lower = [[k for k in sorted(pattern[i]) if k < i] for i in range(n)]
+    upper = [[k for k in sorted(pattern[i]) if k > i] for i in range(n)]
+    lf, lb = _levels(n, lower), _levels(n, upper)
+    Dinv = {i: np.linalg.inv(F[(i, i)]) for i in range(n)}
+    y, ready = np.full((n, b), np.nan), np.full(n, -1)
+    for L in range(lf.max() + 1):
+        for i in np.flatnonzero(lf == L):
+            if L % 2 == 0:
+                y[i] = r[i] - sum(F[(i, k)] @ y[k] for k in lower[i])
+            else:
+                K1 = [k for k in lower[i] if lf[k] == L - 1]
+                K0 = [k for k in lower[i] if lf[k] != L - 1]
+                c = r[i] - sum((F[(i, k)] @ r[k] for k in K1), np.zeros(b))
+                js = sorted(set(K0) | {j for k in K1 for j in lower[k]})
+                for j in js:
+                    assert lf[j] <= L - 2          # only rows of earlier steps are needed
+                    M = F[(i, j)].copy() if j in K0 else np.zeros((b, b))
+                    M -= sum((F[(i, k)] @ F[(k, j)] for k in K1 if j in lower[k]), np.zeros((b, b)))
+                    c = c - M @ y[j]
+                y[i] = c
+            ready[i] = L
+    z = np.full((n, b), np.nan)
+    for L in range(lb.max() + 1):
+        for i in np.flatnonzero(lb == L):
+            if L % 2 == 0:
+                z[i] = Dinv[i] @ (y[i] - sum((F[(i, k)] @ z[k] for k in upper[i]), np.zeros(b)))
+            else:
+                K1 = [k for k in upper[i] if lb[k] == L - 1]
+                K0 = [k for k in upper[i] if lb[k] != L - 1]
+                P = {k: F[(i, k)] @ Dinv[k] for k in K1}
+                c = y[i] - sum((P[k] @ y[k] for k in K1), np.zeros(b))
+                for j in sorted(set(K0) | {j for k in K1 for j in upper[k]}):
+                    assert lb[j] <= L - 2
+                    M = F[(i, j)].copy() if j in K0 else np.zeros((b, b))
+                    M -= sum((P[k] @ F[(k, j)] for k in K1 if j in upper[k]), np.zeros((b, b)))
+                    c = c - M @ z[j]
+                z[i] = Dinv[i] @ c
+    return y, z
+
+
+def _plain_solves(n, b, pattern, F, r):
+    y = np.zeros((n, b))
+    for i in range(n):
+        y[i] = r[i] - sum((F[(i, k)] @ y[k] for k in pattern[i] if k < i), np.zeros(b))
+    z = np.zeros((n, b))
+    for i in reversed(range(n)):
+        z[i] = np.linalg.solve(F[(i, i)], y[i] - sum((F[(i, k)] @ z[k] for k in pattern[i] if k > i), np.zeros(b)))
+    return y, z
+
+
+def test_paired_levels_equal_plain_substitution_random_pattern():
+    rng = np.random.default_rng(7)
+    n, b = 60, 3
+    pattern = [{i} for i in range(n)]
+    for i in range(n):
+        for j in rng.choice(n, size=3, replace=False):
+            if j != i and abs(int(j) - i) <= 12:
+                pattern[i].add(int(j))
+                pattern[int(j)].add(i)
+    blocks = {}
+    for i in range(n):
+        for j in pattern[i]:
+            blocks[(i, j)] = rng.normal(size=(b, b)) * (0.3 if j != i else 1.0)
+        blocks[(i, i)] += 4.0 * b * np.eye(b)
+    F = _block_ilu_factors(n, b, pattern, blocks)
+    lower = [[k for k in pattern[i] if k < i] for i in range(n)]
+    lf = _levels(n, lower)
+    # the pattern has dependencies more than one level back (K0 non-empty somewhere)
+    assert any(lf[k] < lf[i] - 1 for i in range(n) for k in lower[i])
+    r = rng.normal(size=(n, b))
+    y0, z0 = _plain_solves(n, b, pattern, F, r)
+    y1, z1 = _paired_solves(n, b, pattern, F, r)
+    assert np.linalg.norm(y1 - y0) <= 1e-12 * np.linalg.norm(y0)
+    assert np.linalg.norm(z1 - z0) <= 1e-12 * np.linalg.norm(z0)
+
+
+def test_paired_levels_equal_oracle_ilu_on_a_grid():
+    s = tiny(4, 3, 2).system()
+    o = oracle.Oracle.from_system(s, max_levels=1, dense_max=4096)
+    n, b = s["n"], s["b"]
+    rp, ci, W = s["row_ptr"], s["col_idx"], s["weights"]
+    pattern = [set(int(c) for c in ci[rp[i]:rp[i + 1]]) for i in range(n)]
+    blocks = {(i, int(ci[k])): W[i] @ s["vals"][k] for i in range(n) for k in range(rp[i], rp[i + 1])}
+    F = _block_ilu_factors(n, b, pattern, blocks)
+    r = synth.normal(9, n * b).reshape(n, b)
+    _, z = _paired_solves(n, b, pattern, F, r)
+    zo = o.ilu_apply(r.reshape(-1))
+    assert np.linalg.norm(zo - z.reshape(-1)) <= 1e-10 * np.linalg.norm(zo)
