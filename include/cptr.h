@@ -88,9 +88,10 @@ typedef struct {
                             wavefront where the pattern allows them; 1 level sets; 2 chunked
                             wavefront (natural order, at most 4 dependencies per row, levels no
                             wider than 256 rows inside a chunk; same values as level sets);
-                            3 paired levels (FP64 only, at most 32 dependencies per paired row: a
-                            row of odd level substitutes its dependencies of the level before, so
-                            two levels run as one; values differ from level sets by rounding) */
+                            3 paired levels where no paired row has more than 32 dependencies,
+                            else level sets (a row of odd level substitutes its dependencies of
+                            the level before, so two levels run as one; values differ from level
+                            sets by rounding) */
     void *stream;        /* cudaStream_t for all work; NULL = the legacy default stream */
 } cptr_options;
 
