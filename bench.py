@@ -60,6 +60,11 @@ def parse():
                    help="schedule of the headline solver's ILU(0) sweeps")
     p.add_argument("--ensemble-total", type=float, default=4e6,
                    help="total cells of the ensemble (profiling runs use a smaller one)")
+    p.add_argument("--no-oracle-errors", action="store_true",
+                   help="skip the oracle solutions of the three-phase and ensemble workloads (errors against "
+                        "the FP64 oracle are then reported for the cptr200k forms only)")
+    p.add_argument("--profile-steps", type=int, default=3,
+                   help="steps of the separate pass that times kernel families with CUDA events")
     return p.parse_args()
 
 
@@ -147,10 +152,58 @@ def oracle_step(s):
     t0 = time.perf_counter()
     o = oracle.Oracle.from_system(s)
     x, info = o.solve(s["rhs"], RTOL)
-    return time.perf_counter() - t0, info
+    return time.perf_counter() - t0, info, x
 
 
-FP64_PEAK_TFLOPS = 1.258   # 152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM x 2 flop (GB300 nominal 1.25)
+def oracle_job(kind, arg=None):
+    """FP64 oracle solution of one of the benchmark's workloads, run in a spawned worker process
+    (one host core) while the GPU part runs: (seconds for set-up + solve, info, x)."""
+    import synth
+    if kind == "three_phase":
+        s = synth.recipe("three_phase2m").system() if arg is None else synth.make_box(
+            *arg, 1.0, 1.0, 0.5, seed=21, sigma=2.5, nphase=3, wells="four", T_inj=500.0, q_inj=4e-6).system()
+    elif kind == "ensemble":
+        total, k = arg
+        shapes = synth.ensemble_sizes(total=total, lo=min(20e3, total / 64))
+        s = synth.ensemble_member(k, shapes[k]).system()
+    else:
+        raise KeyError(kind)
+    secs, info, x = oracle_step(s)
+    return secs, {"iters": int(info["iters"]), "converged": bool(info["converged"])}, x
+
+
+def start_oracle_jobs(args):
+    """Oracle solutions for the error of every form against the FP64 oracle, started before any
+    GPU call in a spawn-context pool: the three-phase workload, and four instances of the
+    ensemble (the smallest, the largest and two between)."""
+    import multiprocessing as mp
+    jobs = {}
+    if args.no_oracle_errors:
+        return None, jobs
+    pool = mp.get_context("spawn").Pool(processes=3)
+    if not args.no_three_phase:
+        jobs["three_phase"] = pool.apply_async(oracle_job, ("three_phase", args.three_phase_grid))
+    if not args.no_ensemble:
+        import synth
+        shapes = synth.ensemble_sizes(total=args.ensemble_total, lo=min(20e3, args.ensemble_total / 64))
+        cells = [sh[0] * sh[1] * sh[2] for sh in shapes]
+        order = np.argsort(cells)
+        pick = sorted({int(order[0]), int(order[len(order) // 3]), int(order[2 * len(order) // 3]), int(order[-1])})
+        jobs["ensemble"] = {k: pool.apply_async(oracle_job, ("ensemble", (args.ensemble_total, k))) for k in pick}
+    pool.close()
+    return pool, jobs
+
+
+def errors_per_kind(xg, xo, b):
+    """Relative error of a GPU solution against the FP64 oracle's, per unknown kind and overall."""
+    xg, xo = np.asarray(xg, np.float64), np.asarray(xo, np.float64)
+    per = [float(np.linalg.norm(xg[u::b] - xo[u::b]) / max(np.linalg.norm(xo[u::b]), 1e-300)) for u in range(b)]
+    return {"per_unknown_kind": [float("%.3e" % e) for e in per],
+            "overall": float("%.3e" % (np.linalg.norm(xg - xo) / max(np.linalg.norm(xo), 1e-300)))}
+
+
+# GB300's FP64 rate: 152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM x 2 flop (nominal 1.25 TFLOP/s; not measured)
+FP64_PEAK_TFLOPS = 1.258
 
 
 def algorithmic_bytes(s):
@@ -173,7 +226,7 @@ def algorithmic_bytes(s):
             "ilu_bwd": upper * (8 * b * b + 4) + n * 8 * b * b + n * 8 + 3 * vec + 2 * n * 8}
 
 
-def ours(args, rank, world, local_rank):
+def ours(args, rank, world, local_rank, oracle_jobs):
     import numpy as np
     import torch
 
@@ -204,14 +257,13 @@ def ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         info = step()
     assert info["status"] == "CPTR_OK", info
-    cp.cptr_set_profiling(S.ctx, 0b1111111)
+    # the headline: plain steps, no per-kernel events in the timed region
     barrier(world)
     torch.cuda.synchronize(dev)
     clocks = Clocks(gpu_identifier(torch, dev))
     clocks.start()
     launches0 = cp.cptr_launch_count()
     events = []
-    prof_sum = {}
     infos = []
     for _ in range(args.steps):
         flush.zero_()
@@ -220,20 +272,35 @@ def ours(args, rank, world, local_rank):
         infos.append(step())
         e1.record(stream)
         events.append((e0, e1))
-        for k, (ms, cnt) in cp.cptr_profile(S.ctx).items():
-            acc = prof_sum.setdefault(k, [0.0, 0])
-            acc[0] += ms
-            acc[1] += cnt
     torch.cuda.synchronize(dev)
     launches = cp.cptr_launch_count() - launches0
     barrier(world)
     clk = clocks.stop()
-    cp.cptr_set_profiling(S.ctx, 0)
     total_ms = sum(a.elapsed_time(bb) for a, bb in events)
     value, ms_per_step = aggregate(total_ms, world, dofs, args.steps, dev)
     setup_ms = statistics.mean(i["setup_ms"] for i in infos)
     solve_ms = statistics.mean(i["solve_ms"] for i in infos)
     iters = infos[-1]["iters"]
+    x_head = x.cpu().numpy().copy()
+    # a separate pass of the same steps with CUDA events around every kernel family (on the
+    # library's stream): the per-family split and the per-launch rooflines come from it
+    cp.cptr_set_profiling(S.ctx, 0b1111111)
+    prof_sum = {}
+    prof_events = []
+    for _ in range(args.profile_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        prof_events.append((e0, e1))
+        for k, (ms, cnt) in cp.cptr_profile(S.ctx).items():
+            acc = prof_sum.setdefault(k, [0.0, 0])
+            acc[0] += ms
+            acc[1] += cnt
+    torch.cuda.synchronize(dev)
+    cp.cptr_set_profiling(S.ctx, 0)
+    prof_ms_per_step = sum(a.elapsed_time(bb) for a, bb in prof_events) / max(len(prof_events), 1)
 
     # rooflines from per-launch CUDA events inside the timed region; the dominant single kernel
     # (largest total time) is reported as "roofline"
@@ -258,12 +325,14 @@ def ours(args, rank, world, local_rank):
                       "traffic": (PROFILED_TRAFFIC.get(fam) if not fam.startswith("ilu") or
                                   (paired and PROFILED_ILU_SCHEDULE == "paired") else None),
                       "algorithmic_bytes_per_launch": alg[fam], "avg_launch_us": round(avg_ms * 1e3, 2),
-                      "launches_per_step": cnt / args.steps, "ms_per_step": round(ms_tot / args.steps, 3)}
+                      "launches_per_step": cnt / args.profile_steps,
+                      "ms_per_step": round(ms_tot / args.profile_steps, 3)}
     # FP64 ALU view of the SpMV: 9 FMA per 3x3 block (2 flop each) against 1.258 TFLOP/s
     # (152 SMs x 2.07 GHz x 2 FP64 FMA/clk x 2)
     spmv_flops = 2 * b * b * nnzb
     lines["spmv"]["alu"] = {"achieved_tflops": round(spmv_flops / (lines["spmv"]["avg_launch_us"] * 1e-6) / 1e12, 3),
-                            "peak_tflops": FP64_PEAK_TFLOPS, "frac": round(
+                            "peak_tflops": FP64_PEAK_TFLOPS, "peak_source": "nominal (not measured)",
+                            "frac": round(
                                 spmv_flops / (lines["spmv"]["avg_launch_us"] * 1e-6) / 1e12 / FP64_PEAK_TFLOPS, 4)}
     dominant = max(("ilu_fwd", "ilu_bwd", "spmv", "stage1_resid"), key=lambda f: prof_sum[f][0])
     roofline = dict(lines[dominant])
@@ -272,8 +341,10 @@ def ours(args, rank, world, local_rank):
                              f"run as {(ilu_levels + 1) // 2} steps of paired levels" if paired else
                              f"latency bound: a dependency chain of {ilu_levels} level sets per sweep")
                             + ("; DRAM traffic equals the algorithmic bytes" if roofline["traffic"] else ""))
-    families = {k: {"ms_per_step": round(v[0] / args.steps, 3), "regions_per_step": v[1] / args.steps}
-                for k, v in prof_sum.items()}
+    families = {k: {"ms_per_step": round(v[0] / args.profile_steps, 3),
+                    "regions_per_step": v[1] / args.profile_steps} for k, v in prof_sum.items()}
+    families["note"] = (f"separate pass of {args.profile_steps} steps with CUDA events around every kernel family "
+                        f"({prof_ms_per_step:.3f} ms per step with the events, {ms_per_step:.3f} ms without)")
 
     # end to end through the public API with pinned host buffers (copies inside the timed region)
     e2e = None
@@ -303,6 +374,7 @@ def ours(args, rank, world, local_rank):
         e2e = {"value": world * dofs * args.steps / (t_tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": dofs * 8, "ms_per_step": t_tot / args.steps, "iters": ih["iters"]}
 
+    sols = {}
     variants = None
     if not args.no_variants:
         variants = {}
@@ -324,6 +396,7 @@ def ours(args, rank, world, local_rank):
                 evs.append((e0, e1))
             torch.cuda.synchronize(dev)
             ms = sum(a.elapsed_time(bb) for a, bb in evs) / len(evs)
+            sols["variant_" + name] = x.cpu().numpy().copy()
             variants[name] = {"ms_per_step": round(ms, 3), "dofs_per_s": round(dofs / (ms / 1e3), 1),
                               "setup_ms": round(statistics.mean(i["setup_ms"] for i in infs), 3),
                               "solve_ms": round(statistics.mean(i["solve_ms"] for i in infs), 3),
@@ -336,17 +409,48 @@ def ours(args, rank, world, local_rank):
         del flush
         torch.cuda.empty_cache()
         flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-        tp = three_phase(args, dev, stream, flush)
+        tp, tp_sols = three_phase(args, dev, stream, flush)
     ens = None
     if not args.no_ensemble:
-        ens = ensemble(args, dev, stream, flush)
+        ens, ens_sols = ensemble(args, dev, stream, flush)
 
     cpu = None
+    oracle_errors = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        secs, oinfo = oracle_step(s)
-        cpu = {"value": dofs / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+        secs, oinfo, x_or = oracle_step(s)
+        cpu = {"value": dofs / secs, "unit": UNIT, "cores": 1, "cores_available": os.cpu_count(), "kind": "oracle",
                "sample": f"one full setup+solve of the {WORKLOAD} workload ({dofs} dofs) by the serial FP64 C oracle, "
                          f"{secs:.2f} s, {oinfo['iters']} iterations"}
+        # every form's solution against the FP64 oracle's solution of the same system
+        oracle_errors = {"note": "relative error of each form's solution (rtol 1e-6) against the FP64 oracle's "
+                                 "solution of the same system (rtol 1e-6), per unknown kind (p, T, saturations)",
+                         "cptr200k": {"oracle_iters": int(oinfo["iters"]),
+                                      "headline_fp64": errors_per_kind(x_head, x_or, b)}}
+        for k, xv in sols.items():
+            oracle_errors["cptr200k"][k] = errors_per_kind(xv, x_or, b)
+        if tp is not None and "three_phase" in oracle_jobs:
+            osecs, oi, xo3 = oracle_jobs["three_phase"].get()
+            e3 = {"oracle_iters": oi["iters"], "oracle_converged": oi["converged"]}
+            for k, xv in tp_sols.items():
+                e3[k] = errors_per_kind(xv, xo3, 4)
+            oracle_errors["three_phase"] = e3
+            tp["cpu_baseline"] = {"value": tp_dofs(tp) / osecs, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                  "sample": f"one full setup+solve by the serial FP64 C oracle, {osecs:.2f} s, "
+                                            f"{oi['iters']} iterations (S_e), run in a worker process meanwhile"}
+        if ens is not None and "ensemble" in oracle_jobs:
+            ee, osecs, ocells = {}, 0.0, 0
+            for k, job in oracle_jobs["ensemble"].items():
+                sk, oi, xo = job.get()
+                osecs += sk
+                ocells += xo.size // 3
+                ee[f"instance_{k}"] = dict(errors_per_kind(ens_sols[k], xo, 3), oracle_iters=oi["iters"])
+            oracle_errors["ensemble"] = ee
+            tot_cells = ens["total_cells"]
+            ens["cpu_baseline"] = {"value": 3 * ocells / osecs, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": f"{len(ee)} of the {ens['instances']} instances ({ocells} cells) set up "
+                                             f"and solved one after another by the serial FP64 C oracle in "
+                                             f"{osecs:.2f} s; the whole ensemble extrapolates to "
+                                             f"{osecs * tot_cells / ocells:.1f} s"}
     if rank == 0:
         out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
@@ -369,7 +473,7 @@ def ours(args, rank, world, local_rank):
                "solve_dofs_per_s": round(dofs / (solve_ms / 1e3), 1),
                "true_rel_res": infos[-1]["true_rel_res"], "levels": [infos[-1]["levels_p"], infos[-1]["levels_T"]],
                "families": families, "roofline": roofline, "rooflines": lines, "variants": variants,
-               "three_phase": tp, "ensemble": ens,
+               "three_phase": tp, "ensemble": ens, "errors_vs_fp64_oracle": oracle_errors,
                "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "launches_before_timed": launches0, "clocks": clk}
         print(json.dumps(out), flush=True)
@@ -438,7 +542,9 @@ def three_phase(args, dev, stream, flush):
           "W": s["weights"].reshape(-1), "st": s["st"], "rhs": s["rhs"].reshape(-1)}.items()}
     del s
     x = torch.empty(dofs, dtype=torch.float64, device=dev)
-    out = {"workload": (f"three-phase {n} cells, 4 unknowns/cell ({dofs} dofs)" if args.three_phase_grid else
+    sols = {}
+    out = {"dofs": dofs,
+           "workload": (f"three-phase {n} cells, 4 unknowns/cell ({dofs} dofs)" if args.three_phase_grid else
                         "three_phase2m: 200x200x50 cells, 4 unknowns/cell (8M dofs)") +
                        ", lognormal permeability sigma 2.5, 4 injectors + 4 producers; CPTR + ILU(0), FGMRES(30), "
                        "rtol 1e-6",
@@ -479,8 +585,13 @@ def three_phase(args, dev, stream, flush):
                      "iters": infs[-1]["iters"], "true_rel_res": infs[-1]["true_rel_res"],
                      "status": infs[-1]["status"], "schur_used": infs[-1]["schur_used"],
                      "learned_setup_ms": round(prof["setup_other"][0], 3), "timed_runs": nrun}
+        sols[name] = x.cpu().numpy().copy()
         Sv.close()
-    return out
+    return out, sols
+
+
+def tp_dofs(tp):
+    return tp["dofs"]
 
 
 def ensemble(args, dev, stream, flush):
@@ -528,7 +639,9 @@ def ensemble(args, dev, stream, flush):
     ms = sum(a.elapsed_time(bb) for a, bb in evs) / len(evs)
     _, status, infos = res[-1]
     its = [i["iters"] for i in infos]
-    out = {"workload": f"{len(cells)} two-phase instances (3 unknowns/cell), {min(cells)}..{max(cells)} cells, "
+    sols = {k: xk.cpu().numpy().copy() for k, xk in enumerate(xs)}
+    out = {"instances": len(cells), "total_cells": sum(cells),
+           "workload": f"{len(cells)} two-phase instances (3 unknowns/cell), {min(cells)}..{max(cells)} cells, "
                        f"{sum(cells)} cells / {dofs} dofs in total, mixed-precision CPTR + ILU(0), FGMRES(30), "
                        "rtol 1e-6 per instance",
            "batched": {"ms_per_step": round(ms, 3), "dofs_per_s": round(dofs / (ms / 1e3), 1),
@@ -564,7 +677,7 @@ def ensemble(args, dev, stream, flush):
                          "all_converged": all(i["status"] == "CPTR_OK" for i in inf)}
     out["speedup_batched_vs_sequential"] = round(ms_seq / ms, 3)
     Sq.close()
-    return out
+    return out, sols
 
 
 def reference(args, rank, world):
@@ -577,7 +690,7 @@ def reference(args, rank, world):
         oracle_step(s)
     total = 0.0
     for _ in range(args.steps):
-        secs, info = oracle_step(s)
+        secs, info, _x = oracle_step(s)
         total += secs
     value = dofs * args.steps / total
     sample = f"one full setup+solve of the {WORKLOAD} workload per step, serial FP64 C oracle, {info['iters']} iterations"
@@ -630,9 +743,14 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    # the oracle's reference solutions run in spawned worker processes, started before any GPU call
+    pool, jobs = start_oracle_jobs(args) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else (None, {})
     import __graft_entry__
     __graft_entry__.build()
-    ours(args, rank, world, local_rank)
+    ours(args, rank, world, local_rank, jobs)
+    if pool is not None:
+        pool.terminate()
+        pool.join()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -187,22 +187,26 @@ cptr_status cptr_hierarchy_level(cptr_ctx *ctx, int32_t which, int32_t l, int32_
                                  double *v, double *dinv, int32_t *cf, int32_t *Prp, int32_t *Pci,
                                  double *Pv);
 
-/* z = (L U)^{-1} r like cptr_apply_ilu, but the call allocates nothing and does not use the
- * context's work vectors: the two intermediate vectors of the triangular solves live in one
- * file-scope device array of 2 x 2^20 doubles (16 MiB), which every GPU that loads the library
- * keeps until the process exits.  This serves callers that cannot allocate device memory when
- * they apply the preconditioner (a framework's caching allocator owns the device, a real-time
- * loop cannot afford cudaMalloc/cudaFree and the device synchronisation of cudaFree, or the
- * memory budget is fixed in advance).  The paper has no counterpart; it is an engineering
- * addition.
+/* z = (L U)^{-1} r with the block ILU(0) factors of A', for callers that cannot allocate device
+ * memory when they apply the preconditioner: code running while a framework's caching allocator
+ * owns the whole device, real-time loops that cannot pay for cudaMalloc/cudaFree (cudaFree also
+ * synchronises the device), or deployments whose memory budget is fixed in advance.  The call
+ * allocates nothing and does not use the context's work vectors: the two intermediate vectors of
+ * the triangular solves live in one file-scope device array of 2 x 2^20 doubles (16 MiB), which
+ * every GPU that loads the library keeps until the process exits.  The paper has no counterpart;
+ * it is an engineering addition.
  *   r, z   device vectors of n_cells*b doubles; n_cells*b must not exceed 2^20, else
  *          CPTR_EINVAL with a message naming the limit.  Natural ILU ordering only (else
  *          CPTR_EINVAL).
- * The array's device address is looked up on the first call on each device, with that device
- * current; make that first call before any stream capture.  All calls on a device share the
- * array: calls whose work overlaps on the GPU race on it.  No part of the array needs to start at
- * zero (each call writes every element it later reads).  Errors: CPTR_ESTATE (no setup or no
- * ILU(0)), CPTR_EINVAL, CPTR_ECUDA. */
+ * It always applies the FP64 factors (one launch per level set), also in a context of the mixed
+ * precision or with another sweep schedule, so its result equals cptr_apply_ilu of an FP64
+ * context to rounding.  The array's device address is looked up with the call's device current,
+ * on every call whose stream is not being captured; the first call on a device does that set-up
+ * and must come before any stream capture.  All calls on a device share the array: calls whose
+ * work overlaps on the GPU race on it.  No part of the array needs to start at zero (each call
+ * writes every element it later reads).  The call synchronises the context's stream before it
+ * returns.  Errors: CPTR_ESTATE (no setup, no ILU(0), or a first call under capture),
+ * CPTR_EINVAL, CPTR_ECUDA. */
 cptr_status cptr_apply_ilu_static(cptr_ctx *ctx, const double *r, double *z);
 
 /* Launch shapes in use (an engineering addition; the paper has none).  Writes up to cap rows of 5

@@ -214,9 +214,17 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
         CPTR_TRY(dalloc_t(c, &w.flag, 4));
         CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // inputs and allocations are ready
         cptr_status st_T = CPTR_OK;
+        // a host exception on either thread becomes a status: the worker catches its own, and
+        // this thread joins the worker before any exception of its own leaves this scope
         std::thread worker([&] {
             CtxScope ws(&w);
-            st_T = amg_setup(&w, c->hT, c->rp, c->ci, c->St, n);
+            try {
+                st_T = amg_setup(&w, c->hT, c->rp, c->ci, c->St, n);
+            } catch (const std::bad_alloc &) {
+                st_T = w.fail(CPTR_ENOMEM, "host allocation failed");
+            } catch (...) {
+                st_T = w.fail(CPTR_EINVAL, "unexpected host exception");
+            }
             dfree(w.scan_tmp);
             w.scan_tmp = nullptr;
             cudaStreamSynchronize(w.stream);
@@ -224,8 +232,15 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
         // This thread builds the pressure hierarchy, then the ILU(0) factors.  (Running the
         // factorisation kernel on a stream of its own during the pressure hierarchy saved ~2 ms on
         // cptr200k, but on 2M-cell systems some set-ups then stalled for ~0.3 s; not used.)
-        cptr_status st_p = amg_setup(c, c->hp, c->rp, c->ci, c->App, n);
-        if (st_p == CPTR_OK && c->o.stage2 == CPTR_STAGE2_ILU0) st_p = ilu_setup(c);
+        cptr_status st_p = CPTR_OK;
+        try {
+            st_p = amg_setup(c, c->hp, c->rp, c->ci, c->App, n);
+            if (st_p == CPTR_OK && c->o.stage2 == CPTR_STAGE2_ILU0) st_p = ilu_setup(c);
+        } catch (...) {
+            worker.join();
+            dfree(w.flag);
+            throw;
+        }
         worker.join();
         for (int q = 0; q < kSetupPhases; ++q) c->prof.setup_ms[q] += w.prof.setup_ms[q];
         dfree(w.flag);

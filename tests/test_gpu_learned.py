@@ -197,12 +197,20 @@ def test_learned_setup_and_solve_match_oracle(base):
     assert info_g["schur_used"] == "learned"
     assert info_g["status"] == "CPTR_OK" and info_o["converged"]
     assert abs(info_g["iters"] - info_o["iters"]) <= 1
-    if ok.all():
-        x_g = host(x_g)
-        b = s["b"]
-        for u in range(b):
-            err = np.linalg.norm(x_g[u::b] - x_o[u::b]) / np.linalg.norm(x_o[u::b])
-            assert err <= 1e-8, (u, err)
+    if not ok.all():
+        # s_i of a few cells differs from the oracle's by a BF16 rounding flip (a hidden unit's
+        # FP32 tanh against the FP64 one), so the two preconditioners differ slightly and the
+        # iterates at 1e-8 need not agree to 1e-8.  Both solves are then converged to 1e-12, where
+        # each solution lies within kappa * 1e-12 of the exact one, and compared there.
+        print(f"learned s: {np.count_nonzero(~ok)} of {ok.size} cells differ by more than 1e-5")
+        x_o, info_o = o.solve(s["rhs"], 1e-12)
+        x_g, info_g = g.solve(dev(s["rhs"].reshape(-1)), 1e-12)
+        assert info_g["status"] == "CPTR_OK" and info_o["converged"]
+    x_g = host(x_g)
+    b = s["b"]
+    for u in range(b):
+        err = np.linalg.norm(x_g[u::b] - x_o[u::b]) / np.linalg.norm(x_o[u::b])
+        assert err <= 1e-8, (u, err)
 
 
 def _iters(s, mode, P=None, base=None, max_it=300):
