@@ -84,15 +84,23 @@ typedef struct {
     int32_t autotune;    /* 1: time the launch shapes of the V-cycle and SpMV kernels at set-up
                             and keep the fastest (see cptr_tuning); 0 (default): fixed shapes */
     int32_t ilu_sweep;   /* schedule of the ILU(0) triangular sweeps: 0 (default) level sets, or,
-                            with autotune, the fastest of level sets, paired levels and the chunked
-                            wavefront where the pattern allows them; 1 level sets; 2 chunked
-                            wavefront (natural order, at most 4 dependencies per row, levels no
-                            wider than 256 rows inside a chunk; same values as level sets);
-                            3 paired levels where no paired row has more than 32 dependencies,
-                            else level sets (a row of odd level substitutes its dependencies of
-                            the level before, so two levels run as one; values differ from level
-                            sets by rounding) */
+                            with autotune, the fastest of level sets, paired levels, the chunked
+                            wavefront and tiles where the pattern allows them; 1 level sets;
+                            2 chunked wavefront (natural order, at most 4 dependencies per row,
+                            levels no wider than 256 rows inside a chunk; same values as level
+                            sets); 3 paired levels where no paired row has more than 32
+                            dependencies, else level sets (a row of odd level substitutes its
+                            dependencies of the level before, so two levels run as one; values
+                            differ from level sets by rounding); 4 tiles where the pattern is that
+                            of a Cartesian box in natural order (lower dependencies at offsets 1,
+                            nx and nx*ny only), else level sets: a block owns a tile of Ty x Tz
+                            grid lines and walks the tile's own level sets, only dependencies on
+                            other tiles crossing blocks (same values as level sets) */
     void *stream;        /* cudaStream_t for all work; NULL = the legacy default stream */
+    int32_t tile_y;      /* tiled sweeps (ilu_sweep 4): grid lines per tile along y and z; 0 (default):
+                            the shape of smallest modelled time, or with autotune the fastest of the
+                            four best modelled ones */
+    int32_t tile_z;
 } cptr_options;
 
 typedef struct {
@@ -212,9 +220,11 @@ cptr_status cptr_apply_ilu_static(cptr_ctx *ctx, const double *r, double *z);
 /* Launch shapes in use (an engineering addition; the paper has none).  Writes up to cap rows of 5
  * int32 into rows (host): {hierarchy (0 A_pp, 1 S~_T, 2 A', 3 ILU(0)), level, kernel (0 smoother +
  * residual, 1 restriction P^T, 2 prolongation P, 3 SELL SpMV of A', 4 ILU(0) sweeps, 5 ILU(0)
- * schedule), lanes per row (0 = chosen from the average row length; kernel 4: back-off between
- * polls in ns; kernel 5: 0 level sets, 1 chunked wavefront, 2 paired levels), threads per block (kernel 4: blocks of
- * the persistent grid)}; *n_rows receives the number of rows available.  With autotune set,
+ * schedule, 6 tile shape of the tiled sweeps), lanes per row (0 = chosen from the average row
+ * length; kernel 4: back-off between polls in ns; kernel 5: 0 level sets, 1 chunked wavefront,
+ * 2 paired levels, 3 tiles; kernel 6: lines per tile along y, Ty, or 0 when no tiled tables are
+ * built), threads per block (kernel 4: blocks of the persistent grid; kernel 6: lines per tile
+ * along z, Tz)}; *n_rows receives the number of rows available.  With autotune set,
  * cptr_setup times for every operator G in {1, 2, 4, 8, 16, 32} lanes x T in {128, 256, 512}
  * threads (the SELL kernels: T in {64, 128, 256, 512}), 5 launches each after a warm-up, and keeps
  * the fastest; results are cached in the context by operator size.  Shapes change only the order

@@ -26,7 +26,7 @@ MLP_FEATURES, MLP_HIDDEN, MLP_NPARAM = 16, 64, 5313
 SMOOTHER = {"l1": 0, "jacobi": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 ILU_ORDER = {"natural": 0, "multicolor": 1}
-ILU_SWEEP = {"auto": 0, "levels": 1, "chunked": 2, "paired": 3}
+ILU_SWEEP = {"auto": 0, "levels": 1, "chunked": 2, "paired": 3, "tiled": 4}
 U_P, U_T, U_SAT = 0, 1, 2
 
 
@@ -37,7 +37,7 @@ class cptr_options(ctypes.Structure):
                 ("max_it", ctypes.c_int32), ("dense_max", ctypes.c_int32), ("seed", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("check_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("ilu_order", ctypes.c_int32), ("autotune", ctypes.c_int32), ("ilu_sweep", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32)]
 
 
 class cptr_stats(ctypes.Structure):

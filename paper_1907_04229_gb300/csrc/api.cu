@@ -405,7 +405,8 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
         o.smoother < 0 || o.smoother > CPTR_SMOOTH_JACOBI || o.schur < CPTR_SCHUR_GIVEN ||
         o.schur > CPTR_SCHUR_LEARNED || o.precision < CPTR_PREC_FP64 ||
         o.precision > CPTR_PREC_MIXED ||
-        o.ilu_order < CPTR_ILU_NATURAL || o.ilu_order > CPTR_ILU_MULTICOLOR || o.ilu_sweep < 0 || o.ilu_sweep > 3)
+        o.ilu_order < CPTR_ILU_NATURAL || o.ilu_order > CPTR_ILU_MULTICOLOR || o.ilu_sweep < 0 || o.ilu_sweep > 4 ||
+        o.tile_y < 0 || o.tile_z < 0 || (size_t)o.tile_y * o.tile_z > 64)
         return CPTR_EINVAL;
     cptr_ctx *ctx = new (std::nothrow) cptr_ctx();
     if (!ctx) return CPTR_ENOMEM;
@@ -703,9 +704,13 @@ cptr_status cptr_tuning(cptr_ctx *ctx, int32_t *rows, int32_t cap, int32_t *n_ro
         isw.T = (int16_t)c->sf_grid;
         add(3, 0, 4, isw);
         Shape chosen;
-        chosen.G = c->cw_use ? 1 : (c->sp_use ? 2 : 0);
+        chosen.G = c->tl_use ? 3 : (c->cw_use ? 1 : (c->sp_use ? 2 : 0));
         chosen.T = 0;
         add(3, 0, 5, chosen);
+        Shape tile;
+        tile.G = (int16_t)(c->tl_ok ? c->tl_ty : 0);
+        tile.T = (int16_t)(c->tl_ok ? c->tl_tz : 0);
+        add(3, 0, 6, tile);
         *n_rows = (int32_t)(out.size() / 5);
         for (int32_t i = 0; i < std::min<int32_t>(cap, *n_rows) * 5; ++i) rows[i] = out[i];
         return CPTR_OK;

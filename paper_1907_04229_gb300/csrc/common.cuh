@@ -9,6 +9,7 @@
 
 #include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/cptr.h"
@@ -221,6 +222,14 @@ void ilu_apply(const Ctx *c, const double *r, double *z, const double *dp, const
 void ilu_apply_into(const Ctx *c, const double *r, double *z, double *ybuf, double *zbuf);
 void ilu_apply32(const Ctx *c, const float *r, double *z, const float *dp, const float *dT);
 
+// ---- ilu_tile.cu -------------------------------------------------------------------------------
+bool tile_grid(Ctx *c);                                  // detect the box; sets c->tl_dims
+void tile_candidates(const Ctx *c, int k, std::vector<std::pair<int, int>> &out);   // best k tile shapes
+cptr_status tile_setup(Ctx *c, int Ty, int Tz);          // tables of both sweeps; sets c->tl_ok
+void tile_free(Ctx *c);
+template <typename T, typename RT, typename XT>
+void tile_apply(const Ctx *c, const RT *r, double *z, const XT *dp, const XT *dT);   // both sweeps (after the fill)
+
 // ---- krylov.cu ---------------------------------------------------------------------------------
 cptr_status fgmres_solve(Ctx *c, const double *bw, double *x, double rtol, cptr_stats *st);
 // ensemble (one block-diagonal set-up, FGMRES per instance): x and bw are union vectors
@@ -245,6 +254,14 @@ struct CwTables {
     int32_t *clev = nullptr, *lptr = nullptr, *prow = nullptr, *code = nullptr;
     int32_t *started = nullptr;   // per chunk: it has finished its first levels (reset per sweep)
     void *val = nullptr;   // factor blocks (and inverted pivot blocks), FP64 or FP32
+};
+
+// tables of one tiled ILU(0) sweep (see ilu_tile.cu): tiles in processing order, their level
+// pointers, and one record per position (row, dependency codes, factor blocks)
+struct TileTables {
+    int32_t ntiles = 0, nlev = 0, D = 0, MW = 0, RS = 0, R = 0, P = 2, smem = 0, threads = 0, grid = 0;
+    int32_t *tlev = nullptr, *lptr = nullptr;
+    unsigned char *rec = nullptr;
 };
 
 // ---- the context -------------------------------------------------------------------------------
@@ -304,6 +321,12 @@ struct Ctx {
     int32_t *sp_col_f = nullptr, *sp_col_b = nullptr, *sp_ccol_f = nullptr, *sp_ccol_b = nullptr;
     void *sp_val_f = nullptr, *sp_val_b = nullptr, *sp_cval_f = nullptr, *sp_cval_b = nullptr;   // FP64, or FP32 when mixed
     bool sp_ok = false, sp_use = false;                // built / chosen
+    // tiled sweeps: a block owns a tile of grid lines and walks its own levels (natural order on
+    // a Cartesian box, detected from the pattern)
+    TileTables tl_f, tl_b;
+    bool tl_ok = false, tl_use = false;                // built / chosen
+    int32_t tl_dims[3] = {0, 0, 0};                    // detected nx, ny, nz (0: no box)
+    int32_t tl_ty = 0, tl_tz = 0;                      // tile shape of the tables built
     int32_t sf_grid = 4 * 152;                         // persistent grid of the sweeps (autotuned)
     int32_t sf_sleep = 20;                             // back-off between polls, ns (autotuned)
     int32_t inject_wait = 0;                           // failure injection (see cptr_inject_wait_timeout)

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "sweep.cuh"
 
 namespace cptr {
 
@@ -140,62 +141,6 @@ __global__ void k_ilu_bwd(const int32_t *__restrict__ rows, int32_t start, int32
 // own ready flag.  A row depends only on earlier positions, which belong to chunks held by blocks
 // that already run: no deadlock.  Every wait is bounded by kWaitNs of GPU time; a wait that gives
 // up sets ks->wait_err and the call reports CPTR_ETIMEOUT.
-constexpr unsigned long long kSentinel = 0x7FF4C0DEDEADBEEFULL;  // never produced by arithmetic
-constexpr unsigned kSentinel32 = 0x7FA6C0DEu;                      // the same for FP32 vectors
-constexpr unsigned long long kWaitNs = 500ULL * 1000ULL * 1000ULL;
-constexpr int kSfThreads = 128;
-
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// loads and stores the compiler may neither hoist out of a loop nor merge (relaxed, GPU scope:
-// they observe / publish values through L2 for other SMs)
-__device__ __forceinline__ double load_relaxed(const double *p) {
-    double v;
-    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ float load_relaxed(const float *p) {
-    float v;
-    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void store_relaxed(double *p, double v) {
-    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
-}
-__device__ __forceinline__ void store_relaxed(float *p, float v) {
-    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
-}
-__device__ __forceinline__ double load_acquire(const double *p) {
-    double v;
-    asm volatile("ld.acquire.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ bool is_sentinel(double v) { return __double_as_longlong(v) == (long long)kSentinel; }
-__device__ __forceinline__ bool is_sentinel(float v) { return __float_as_uint(v) == kSentinel32; }
-template <typename T> __device__ __forceinline__ T sentinel_value();
-template <> __device__ __forceinline__ double sentinel_value<double>() { return __longlong_as_double((long long)kSentinel); }
-template <> __device__ __forceinline__ float sentinel_value<float>() { return __uint_as_float(kSentinel32); }
-
-// wait (bounded) until *p no longer holds the sentinel; returns its value (failure injection)
-__device__ __forceinline__ double wait_value(const double *p, KState *ks) {
-    double v = load_acquire(p);
-    if (!is_sentinel(v)) return v;
-    const unsigned long long t0 = gtimer();
-    for (;;) {
-        __nanosleep(40);
-        v = load_acquire(p);
-        if (!is_sentinel(v)) return v;
-        if (gtimer() - t0 > kWaitNs) {
-            atomicExch(&ks->wait_err, 1);
-            return 0.0;
-        }
-    }
-}
-
 // Dependency slots are handled kDepGroup at a time (8 for the paired-level tables).
 constexpr int kDepGroup = 4;
 
@@ -1849,7 +1794,8 @@ static uint64_t ilu_tune_key(const Ctx *c) {
     return (uint64_t)8 << 60 | (uint64_t)(c->o.precision & 1) << 56 | ((uint64_t)c->n & 0xFFFFFFull) << 32 |
            (uint64_t)(uint32_t)c->nnzb;
 }
-// the schedule a cached tuning chose (0 level sets, 1 chunked, 2 paired levels), -1 if none
+// the schedule a cached tuning chose (0 level sets, 1 chunked, 2 paired levels, 3 tiled), -1 if
+// none; the tiled schedule's tile shape is cached at key + 2 (G = Ty, T = Tz)
 static int ilu_tuned_schedule(const Ctx *c) {
     auto it = c->tune_cache.find(ilu_tune_key(c) + 1);
     return it == c->tune_cache.end() ? -1 : it->second.G;
@@ -2041,12 +1987,34 @@ cptr_status ilu_setup(Ctx *c) {
     dfree(inv_f); dfree(inv_b); dfree(levr_f); dfree(levr_b);
     if (!mc && (c->o.ilu_sweep == 2 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 1))))
         CPTR_TRY(cw_setup(c));
+    // tiled sweeps: on a natural-order box, with the cached tile shape or the best modelled one
+    c->tl_use = false;
+    if (!mc && (c->o.ilu_sweep == 4 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 3))) &&
+        tile_grid(c)) {
+        int Ty = 0, Tz = 0;
+        auto it = c->tune_cache.find(ilu_tune_key(c) + 2);
+        if (c->o.tile_y > 0 || c->o.tile_z > 0) {   // the caller's shape (clamped to the box)
+            Ty = std::min(std::max(c->o.tile_y, 1), c->tl_dims[1]);
+            Tz = std::min(std::max(c->o.tile_z, 1), c->tl_dims[2]);
+        } else if (it != c->tune_cache.end()) {
+            Ty = it->second.G;
+            Tz = it->second.T;
+        } else {
+            std::vector<std::pair<int, int>> cand;
+            tile_candidates(c, 1, cand);
+            if (!cand.empty()) { Ty = cand[0].first; Tz = cand[0].second; }
+        }
+        if (Ty > 0) CPTR_TRY(tile_setup(c, Ty, Tz));
+        c->tl_use = c->tl_ok && (c->o.ilu_sweep == 4 || sched == 3);
+    }
     setup_tick(c, SETUP_ILU_HOST, &t0);
     return CPTR_OK;
 }
 
 void ilu_free(Ctx *c) {
     cw_free(c);
+    tile_free(c);
+    c->tl_use = false;
     if (c->ilu_owns_pattern) { dfree(c->ilu_rp); dfree(c->ilu_ci); dfree(c->ilu_diag); dfree(c->ilu_rowmap); }
     c->ilu_rowmap = nullptr;
     c->ilu_owns_pattern = false;
@@ -2093,6 +2061,10 @@ static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT 
     T *y = (T *)c->sf_y, *zz = (T *)c->sf_z;
     (k_sf_fill<T><<<4 * 152, 256, 0, s>>>((int64_t)n * B, y, zz, c->sf_ticket), note_launch());
     if (c->inject_wait) (k_sf_fill<double><<<1, 32, 0, s>>>(1, c->never, c->never, c->sf_ticket + 2), note_launch());
+    if (c->tl_use) {
+        tile_apply<T, RT, XT>(c, r, z, dp, dT);
+        return;
+    }
     if (c->cw_use) {
         const CwTables &F = c->cw_f, &Bk = c->cw_b;
         int pf = prof_begin(c, PF_ILU_FWD);
@@ -2201,13 +2173,15 @@ cptr_status ilu_autotune(Ctx *c) {
             const int sched = ilu_tuned_schedule(c);
             c->cw_use = c->cw_ok && sched == 1;
             c->sp_use = c->sp_ok && sched == 2;
+            c->tl_use = c->tl_ok && sched == 3;
         }
         return CPTR_OK;
     }
     double *r = c->xw, *z = c->w;   // scratch vectors of n*b doubles
-    const bool cw_was = c->cw_use, sp_was = c->sp_use;
+    const bool cw_was = c->cw_use, sp_was = c->sp_use, tl_was = c->tl_use;
     c->cw_use = false;              // time the level-set sweeps first (or the paired ones if forced)
     c->sp_use = c->sp_ok && c->o.ilu_sweep == 3;
+    c->tl_use = false;
     CPTR_CUDA_TRY(c, cudaMemsetAsync(r, 0, sizeof(double) * (size_t)c->n * c->b, c->stream));
     cudaEvent_t e0, e1;
     CPTR_CUDA_TRY(c, cudaEventCreate(&e0));
@@ -2260,13 +2234,44 @@ cptr_status ilu_autotune(Ctx *c) {
         c->cw_use = false;
         if (bm < best_ms) { best_ms = bm; best_s = sl; sched = 1; }
     }
+    // tiled sweeps: the back-off, and the tile shapes of smallest modelled time (the tables are
+    // rebuilt for each shape timed; the fastest shape's tables are kept)
+    int tile_ty = 0, tile_tz = 0;
+    if ((auto_sched || c->o.ilu_sweep == 4) && c->tl_dims[0]) {
+        std::vector<std::pair<int, int>> cand;
+        if (c->o.tile_y > 0 || c->o.tile_z > 0) {
+            if (c->tl_ok) cand.push_back({c->tl_ty, c->tl_tz});   // the caller's shape only
+        } else {
+            tile_candidates(c, 4, cand);
+        }
+        float bt = 1e30f;
+        int bsl = best_s;
+        for (const auto &sh : cand) {
+            CPTR_TRY(tile_setup(c, sh.first, sh.second));
+            if (!c->tl_ok) continue;
+            c->tl_use = true;
+            for (int v : {0, 32, 128}) {
+                c->sf_sleep = v;
+                const float ms = time3();
+                if (ms < bt) { bt = ms; bsl = v; tile_ty = sh.first; tile_tz = sh.second; }
+            }
+            c->tl_use = false;
+        }
+        if (tile_ty > 0) {
+            if (c->tl_ty != tile_ty || c->tl_tz != tile_tz) CPTR_TRY(tile_setup(c, tile_ty, tile_tz));
+            if (auto_sched && bt < best_ms) { best_ms = bt; best_s = bsl; sched = 3; }
+            if (c->o.ilu_sweep == 4) { best_s = bsl; sched = 3; }
+        }
+    }
     c->sf_grid = best_g;
     if (auto_sched) {
         c->cw_use = sched == 1;
         c->sp_use = sched == 2;
+        c->tl_use = sched == 3 && c->tl_ok;
     } else {
         c->cw_use = cw_was;
         c->sp_use = sp_was;
+        c->tl_use = tl_was && c->tl_ok;
     }
     c->sf_sleep = best_s;
     cudaEventDestroy(e0);
@@ -2278,6 +2283,12 @@ cptr_status ilu_autotune(Ctx *c) {
     sc.T = 0;
     c->tune_cache[key] = sh;
     c->tune_cache[key + 1] = sc;
+    if (tile_ty > 0) {
+        Shape st;
+        st.G = (int16_t)tile_ty;
+        st.T = (int16_t)tile_tz;
+        c->tune_cache[key + 2] = st;
+    }
     CPTR_CUDA_TRY(c, cudaGetLastError());
     return CPTR_OK;
 }

@@ -1,0 +1,635 @@
+// Tiled ILU(0) triangular sweeps (the second stage's z = (LU)^{-1} r, Sec. 3 two-stage step 3 and
+// Sec. 4), an evaluation order of the same solves as the level-set sweeps of ilu.cu: every value
+// is computed with the same operations in the same order, so results are bit-identical.
+//
+// On a Cartesian box in natural order (cell x + nx (y + ny z)) the rows of a grid line (fixed y, z)
+// are consecutive and each depends on the one before.  The lines are grouped into tiles of
+// Ty x Tz lines; one block owns a tile and walks the tile's own level sets (levels counted over
+// dependencies inside the tile, x + (y - y0) + (z - z0) on the box), with one __syncthreads per
+// level and the tile's solved values kept in a shared-memory ring.  Only dependencies on another
+// tile (the tile's faces at y0 - 1 and z0 - 1) go through global memory; their values are polled
+// (the sentinel of sweep.cuh, bounded waits), and since a tile starts only once its upstream
+// tiles have produced the rows it needs, it trails them by a few levels and finds those values
+// already written.  A sweep's dependency chain thus costs ny/Ty + nz/Tz cross-block hops plus
+// nx + Ty + Tz in-block levels, instead of nx + ny + nz cross-block steps.
+//
+// Per position (rows tile by tile in processing order, by local level inside a tile) a record
+// holds the row, its dependency codes (a ring slot, or the global row of a value to poll) and its
+// factor blocks (and, backward, the inverted pivot block).  The records of a level are one
+// contiguous run, copied into shared memory by a TMA bulk copy (cp.async.bulk completing on an
+// mbarrier) NS - 1 levels ahead; P levels ahead, each row's right-hand side and the 16-byte
+// windows around its outside dependencies' values are copied by cp.async (through L2 only), so
+// that a level starts with everything in shared memory.  A value copied before it was written
+// holds the sentinel and is polled from global memory when used.
+//
+// Tiles are handed out by a ticket in an order where every outside dependency lies in an earlier
+// tile, so a block only waits on tiles held by blocks that already run: no deadlock, whatever
+// the grid.  Every wait (a polled value, an mbarrier) is bounded.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "sweep.cuh"
+
+namespace cptr {
+
+namespace {
+
+constexpr int32_t kTileNone = INT32_MIN;   // no dependency in this slot
+constexpr int kTileMaxRows = 64;           // rows of one level of a tile (4 lanes each: <= 256 threads)
+constexpr int kTileWin = 48;               // bytes of the 16-byte-aligned window around a row's value
+constexpr int kTileBar = 128;              // shared-memory bytes reserved for the mbarriers
+constexpr size_t kTileSmemMax = 200 * 1024;
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// record: int32 row, int32 code[D], padded to 16 bytes; T blk[D][B*B] (backward: then T dinv[B*B]),
+// padded to 16 bytes
+__host__ __device__ inline int hdr_bytes(int D) { return ((1 + D) * 4 + 15) & ~15; }
+__host__ __device__ inline int rec_bytes(int D, int BB, int tsz, bool fwd) {
+    return hdr_bytes(D) + (((D + (fwd ? 0 : 1)) * BB * tsz + 15) & ~15);
+}
+// staged inputs of one row: its right-hand side (B values, padded to 16 bytes), one window per slot
+__host__ __device__ inline int rhs_bytes(int B, int ssz) { return (B * ssz + 15) & ~15; }
+__host__ __device__ inline int val_bytes(int D, int B, int ssz) { return rhs_bytes(B, ssz) + D * kTileWin; }
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *m, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *m, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// TMA bulk copy global -> shared, completing on the mbarrier (16-byte aligned, multiple of 16 bytes)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *m) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(m))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_cg16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_ca(double *dst, const double *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_ca(float *dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// a bounded wait of this call has given up (relaxed GPU-scope read of the flag)
+__device__ __forceinline__ bool failed(KState *ks) {
+    int32_t f;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(&ks->wait_err) : "memory");
+    return f != 0;
+}
+
+// bounded wait for the records of a level (parity of the stage's use); false if it gave up
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, unsigned parity) {
+    if (mbar_try_wait(m, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+        if (mbar_try_wait(m, parity)) return true;
+        if (gtimer() - t0 > kWaitNs) return false;
+    }
+}
+
+// One sweep.  Forward (FWD): y(row) = r(row) - sum_d L(row, d) y(dep d).  Backward:
+// z(row) = D(row)^{-1} (y(row) - sum_d U(row, d) z(dep d)), out(row) = z(row) + x1(row), x1 carrying
+// dp in slot ps and dT in slot ts.  src: r (forward, type ST) or y (backward); vec: the vector being
+// solved, in row order.  Lane q of a row's group of four computes component q (B <= 4), like the
+// four-lane level-set kernels.  NS = P + 2 record stages, P + 1 value slots.
+template <int B, typename T, typename ST, typename XT, bool FWD, int P>
+__global__ void __launch_bounds__(4 * kTileMaxRows)
+    k_ilu_tile(int32_t ntiles, const int32_t *__restrict__ tlev, const int32_t *__restrict__ lptr,
+               const unsigned char *__restrict__ rec, int RS, int D, int R, int MW, const ST *__restrict__ src,
+               T *vec, double *__restrict__ out, int ps, int ts, const XT *__restrict__ dp,
+               const XT *__restrict__ dT, unsigned *ticket, KState *ks, const double *never, int sleep_ns) {
+    constexpr int BB = B * B, NS = P + 2, NV = P + 1;
+    const int H = hdr_bytes(D), RH = rhs_bytes(B, (int)sizeof(ST)), SV = val_bytes(D, B, (int)sizeof(ST));
+    extern __shared__ __align__(128) unsigned char tile_smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(tile_smem);
+    unsigned char *recs = tile_smem + kTileBar;
+    unsigned char *vals = recs + (size_t)NS * MW * RS;
+    T *ring = reinterpret_cast<T *>(vals + (size_t)NV * MW * SV);
+    __shared__ unsigned tile_s;
+    __shared__ int abort_s;
+    const int tid = threadIdx.x, g = tid >> 2, q4 = tid & 3;
+    const int g0 = (tid & 31) & ~3;
+    const unsigned gmask = ((1u << B) - 1u) << g0;
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(&mbar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        abort_s = 0;
+    }
+    __syncthreads();
+    unsigned gl = 0;   // levels this block has processed: stage index and mbarrier phase
+    for (;;) {
+        if (tid == 0) tile_s = atomicAdd(ticket + (FWD ? 0 : 1), 1u);
+        __syncthreads();
+        const unsigned tile = tile_s;
+        if (tile >= (unsigned)ntiles) break;
+        const int L0 = __ldg(tlev + tile), nl = __ldg(tlev + tile + 1) - L0;
+        const int32_t pos0 = __ldg(lptr + L0);
+        int issued = 0;   // record stages issued for this tile (thread 0)
+        auto issue_rec = [&](int m) {
+            const unsigned G = gl + m;
+            const int s = (int)(G % NS);
+            const int32_t a = __ldg(lptr + L0 + m), b = __ldg(lptr + L0 + m + 1);
+            const unsigned bytes = (unsigned)(b - a) * (unsigned)RS;
+            mbar_expect_tx(&mbar[s], bytes);
+            bulk_g2s(recs + (size_t)s * MW * RS, rec + (size_t)a * RS, bytes, &mbar[s]);
+            ++issued;
+        };
+        auto wait_rec = [&](int m) {
+            const unsigned G = gl + m;
+            if (!mbar_wait_bounded(&mbar[G % NS], (G / NS) & 1u)) {
+                atomicExch(&ks->wait_err, 1);
+                abort_s = 1;
+            }
+        };
+        // row g's right-hand side (lane q < B: component q) and the windows of its outside
+        // dependencies (lane q < 3: 16-byte piece q), for level m, into value slot (gl + m) % NV
+        auto issue_vals = [&](int m) {
+            const unsigned G = gl + m;
+            const int w = __ldg(lptr + L0 + m + 1) - __ldg(lptr + L0 + m);
+            if (g >= w) return;
+            const unsigned char *r = recs + (size_t)(G % NS) * MW * RS + (size_t)g * RS;
+            const int32_t row = *reinterpret_cast<const int32_t *>(r);
+            const int32_t *code = reinterpret_cast<const int32_t *>(r) + 1;
+            unsigned char *dst = vals + ((size_t)(G % NV) * MW + g) * SV;
+            if (q4 < B) cp_async_ca(reinterpret_cast<ST *>(dst) + q4, src + (int64_t)row * B + q4);
+            if (q4 < 3)
+                for (int d = 0; d < D; ++d) {
+                    const int32_t cd = code[d];
+                    if (cd == kTileNone) break;
+                    if (cd >= 0) continue;
+                    const int64_t j = -(int64_t)cd - 1;
+                    const uintptr_t at = (reinterpret_cast<uintptr_t>(vec + j * B) & ~(uintptr_t)15) + 16 * q4;
+                    cp_async_cg16(dst + RH + d * kTileWin + 16 * q4, reinterpret_cast<const void *>(at));
+                }
+        };
+        if (tid == 0)
+            for (int m = 0; m < min(NS - 1, nl); ++m) issue_rec(m);
+        for (int m = 0; m < P; ++m) {
+            if (m < nl) {
+                wait_rec(m);
+                issue_vals(m);
+            }
+            cp_async_commit();
+        }
+        for (int l = 0; l < nl; ++l) {
+            cp_async_wait<P - 1>();   // this thread's copies of level l have landed
+            __syncthreads();          // ... everyone's, and the ring values of the levels before
+            if (abort_s) break;
+            if (tid == 0 && l + NS - 1 < nl) issue_rec(l + NS - 1);   // into the stage level l - 1 used
+            const unsigned G = gl + l;
+            const int w = __ldg(lptr + L0 + l + 1) - __ldg(lptr + L0 + l);
+            const int32_t p0 = __ldg(lptr + L0 + l) - pos0;   // local position of the level's first row
+            if (g < w && q4 < B) {
+                const unsigned char *r = recs + (size_t)(G % NS) * MW * RS + (size_t)g * RS;
+                const int32_t row = *reinterpret_cast<const int32_t *>(r);
+                const int32_t *code = reinterpret_cast<const int32_t *>(r) + 1;
+                const T *blk = reinterpret_cast<const T *>(r + H);
+                const unsigned char *vb = vals + ((size_t)(G % NV) * MW + g) * SV;
+                if (FWD && never && tile == 0 && l == 0 && g == 0 && q4 == 0) (void)wait_value(never, ks);
+                T acc = (T) reinterpret_cast<const ST *>(vb)[q4];
+                for (int d = 0; d < D; ++d) {
+                    const int32_t cd = code[d];
+                    if (cd == kTileNone) break;
+                    T v[B];
+                    if (cd >= 0) {
+#pragma unroll
+                        for (int u = 0; u < B; ++u) v[u] = ring[(size_t)cd * B + u];
+                    } else {
+                        const int64_t j = -(int64_t)cd - 1;
+                        const T *win = reinterpret_cast<const T *>(
+                            vb + RH + d * kTileWin + (reinterpret_cast<uintptr_t>(vec + j * B) & 15));
+                        bool pend = false;
+#pragma unroll
+                        for (int u = 0; u < B; ++u) {
+                            v[u] = win[u];
+                            pend |= is_sentinel(v[u]);
+                        }
+                        if (pend) {   // copied before it was written: poll (bounded)
+                            const unsigned long long t0 = gtimer();
+                            for (;;) {
+                                pend = false;
+#pragma unroll
+                                for (int u = 0; u < B; ++u)
+                                    if (is_sentinel(v[u])) {
+                                        v[u] = load_relaxed(vec + j * B + u);
+                                        pend |= is_sentinel(v[u]);
+                                    }
+                                if (!pend) break;
+                                const unsigned long long dt = gtimer() - t0;
+                                // give up after kWaitNs, or after 100 us once any wait of the call
+                                // has given up (its values will not come)
+                                if (dt > kWaitNs || (dt > 100000ull && failed(ks))) {
+                                    atomicExch(&ks->wait_err, 1);
+                                    abort_s = 1;
+#pragma unroll
+                                    for (int u = 0; u < B; ++u)
+                                        if (is_sentinel(v[u])) v[u] = (T)0;
+                                    break;
+                                }
+                                __nanosleep(sleep_ns);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < B; ++u) acc = fma(-blk[d * BB + q4 * B + u], v[u], acc);
+                }
+                T res;
+                if (FWD) {
+                    res = acc;
+                } else {
+                    const T *dinv = blk + D * BB;
+                    res = (T)0;
+#pragma unroll
+                    for (int u = 0; u < B; ++u) res = fma(dinv[q4 * B + u], __shfl_sync(gmask, acc, g0 + u), res);
+                }
+                ring[(size_t)((p0 + g) & (R - 1)) * B + q4] = res;
+                store_relaxed(vec + (int64_t)row * B + q4, res);
+                if (!FWD) {
+                    double add = 0.0;
+                    if (dp && q4 == ps) add = (double)dp[row];
+                    if (dT && q4 == ts) add = (double)dT[row];
+                    out[(int64_t)row * B + q4] = (double)res + add;
+                }
+            }
+            if (l + P < nl) {
+                wait_rec(l + P);
+                issue_vals(l + P);
+            }
+            cp_async_commit();
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+        if (abort_s) {
+            // a wait gave up: wait (bounded) for the record copies still in flight, then stop
+            if (tid == 0) {
+                const int done = min(nl, issued);
+                for (int m = 0; m < done; ++m) {
+                    const unsigned G = gl + m;
+                    (void)mbar_wait_bounded(&mbar[G % NS], (G / NS) & 1u);
+                }
+            }
+            __syncthreads();
+            break;
+        }
+        gl += (unsigned)nl;
+    }
+}
+
+// records of one sweep: header (row, codes) from hdr[p][1 + D], blocks from LU by kidx[p][D (+1)]
+template <typename T>
+__global__ void k_tile_pack(int32_t n, int D, int BB, int RS, int H, int nslot, const int32_t *__restrict__ hdr,
+                            const int32_t *__restrict__ kidx, const double *__restrict__ LU, unsigned char *rec) {
+    const int32_t p = (int32_t)(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+    if (p >= n) return;
+    unsigned char *r = rec + (size_t)p * RS;
+    int32_t *h = reinterpret_cast<int32_t *>(r);
+    for (int e = 0; e < H / 4; ++e) h[e] = e <= D ? hdr[(size_t)p * (1 + D) + e] : 0;
+    T *blk = reinterpret_cast<T *>(r + H);
+    for (int d = 0; d < nslot; ++d) {
+        const int32_t k = kidx[(size_t)p * nslot + d];
+        for (int e = 0; e < BB; ++e) blk[d * BB + e] = k >= 0 ? (T)LU[(size_t)k * BB + e] : (T)0;
+    }
+    for (int e = nslot * BB * (int)sizeof(T); e < RS - H; ++e) r[H + e] = 0;
+}
+
+// run f(t) for t in [0, count) on up to 8 host threads
+template <typename F>
+void parallel_for(int32_t count, F &&f) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nt = (int)std::min<unsigned>(std::min<unsigned>(8u, hw), (unsigned)std::max(count, 1));
+    if (nt <= 1) {
+        for (int32_t t = 0; t < count; ++t) f(t);
+        return;
+    }
+    std::atomic<int32_t> next(0);
+    std::vector<std::thread> pool;
+    for (int i = 0; i < nt; ++i)
+        pool.emplace_back([&]() {
+            for (int32_t t = next++; t < count; t = next++) f(t);
+        });
+    for (auto &th : pool) th.join();
+}
+
+// host tables of one sweep for tiles of Ty x Tz lines: positions, level pointers, record headers
+// and block indices; false when the schedule does not apply (a level wider than kTileMaxRows, or an
+// outside dependency on a later tile)
+struct TileHost {
+    int32_t ntiles = 0, nlev = 0, D = 0, MW = 0;
+    std::vector<int32_t> tlev, lptr, hdr, kidx;
+};
+
+bool tile_build(int32_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
+                const std::vector<int32_t> &dg, const int32_t dims[3], int Ty, int Tz, bool fwd, int R,
+                TileHost &h) {
+    const int32_t nx = dims[0], ny = dims[1], nz = dims[2];
+    const int32_t nty = (ny + Ty - 1) / Ty, ntz = (nz + Tz - 1) / Tz, nt = nty * ntz;
+    auto dep = [fwd](int32_t i, int32_t j) { return fwd ? j < i : j > i; };
+    // processing order of the tiles: by ty + tz (ascending forward, descending backward), then tz
+    std::vector<int32_t> order(nt), rank(nt);
+    for (int32_t t = 0; t < nt; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        const int32_t sa = a % nty + a / nty, sb = b % nty + b / nty;
+        if (sa != sb) return fwd ? sa < sb : sa > sb;
+        return fwd ? a < b : a > b;
+    });
+    for (int32_t k = 0; k < nt; ++k) rank[order[k]] = k;
+    std::vector<int32_t> tile_of(n);
+    std::vector<int32_t> cnt(nt + 1, 0);
+    int32_t D = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t y = (i / nx) % ny, z = i / (nx * ny);
+        tile_of[i] = rank[(z / Tz) * nty + y / Ty];
+        ++cnt[tile_of[i] + 1];
+        int32_t nd = 0;
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) nd += dep(i, ci[k]) ? 1 : 0;
+        D = std::max(D, nd);
+    }
+    for (int32_t t = 0; t < nt; ++t) cnt[t + 1] += cnt[t];
+    // rows of each tile in sweep order (ascending forward, descending backward)
+    std::vector<int32_t> rows(n);
+    {
+        std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+        for (int32_t u = 0; u < n; ++u) {
+            const int32_t i = fwd ? u : n - 1 - u;
+            rows[fill[tile_of[i]]++] = i;
+        }
+    }
+    std::vector<int32_t> lev(n, 0), lpos(n, 0), nlev_t(nt, 0), width_t(nt, 0);
+    std::vector<std::vector<int32_t>> lcount(nt);
+    std::atomic<bool> ok(true);
+    // local levels and level sizes per tile
+    parallel_for(nt, [&](int32_t t) {
+        int32_t maxl = -1;
+        for (int32_t u = cnt[t]; u < cnt[t + 1]; ++u) {
+            const int32_t i = rows[u];
+            int32_t l = 0;
+            for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+                const int32_t j = ci[k];
+                if (dep(i, j) && tile_of[j] == t) l = std::max(l, lev[j] + 1);
+            }
+            lev[i] = l;
+            maxl = std::max(maxl, l);
+        }
+        std::vector<int32_t> &lc = lcount[t];
+        lc.assign(maxl + 2, 0);
+        for (int32_t u = cnt[t]; u < cnt[t + 1]; ++u) ++lc[lev[rows[u]] + 1];
+        int32_t w = 0;
+        for (int32_t l = 0; l <= maxl; ++l) w = std::max(w, lc[l + 1]);
+        for (int32_t l = 0; l <= maxl; ++l) lc[l + 1] += lc[l];
+        nlev_t[t] = maxl + 1;
+        width_t[t] = w;
+        // local positions (stable by level)
+        std::vector<int32_t> f(lc.begin(), lc.end() - 1);
+        for (int32_t u = cnt[t]; u < cnt[t + 1]; ++u) {
+            const int32_t i = rows[u];
+            lpos[i] = f[lev[i]]++;
+        }
+    });
+    h.ntiles = nt;
+    h.D = D;
+    h.MW = 0;
+    h.tlev.assign(nt + 1, 0);
+    for (int32_t t = 0; t < nt; ++t) {
+        h.tlev[t + 1] = h.tlev[t] + nlev_t[t];
+        h.MW = std::max(h.MW, width_t[t]);
+    }
+    if (h.MW > kTileMaxRows || h.MW < 1) return false;
+    h.nlev = h.tlev[nt];
+    h.lptr.assign((size_t)h.nlev + 1, n);
+    const int nslot = D + (fwd ? 0 : 1);
+    h.hdr.assign((size_t)n * (1 + D), kTileNone);
+    h.kidx.assign((size_t)n * std::max(nslot, 1), -1);
+    parallel_for(nt, [&](int32_t t) {
+        const std::vector<int32_t> &lc = lcount[t];
+        for (int32_t l = 0; l < nlev_t[t]; ++l) h.lptr[h.tlev[t] + l] = cnt[t] + lc[l];
+        for (int32_t u = cnt[t]; u < cnt[t + 1]; ++u) {
+            const int32_t i = rows[u];
+            const size_t p = (size_t)cnt[t] + lpos[i];
+            const int32_t lend = lc[lev[i] + 1];   // local position just past row i's level
+            h.hdr[p * (1 + D)] = i;
+            int d = 0;
+            for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+                const int32_t j = ci[k];
+                if (!dep(i, j)) continue;
+                int32_t code;
+                if (tile_of[j] == t && lpos[j] + R >= lend) {
+                    code = lpos[j] & (R - 1);
+                } else {
+                    if (tile_of[j] > t) ok = false;   // the ticket order would not be topological
+                    code = -(j + 1);
+                }
+                h.hdr[p * (1 + D) + 1 + d] = code;
+                h.kidx[p * nslot + d] = k;
+                ++d;
+            }
+            if (!fwd) h.kidx[p * nslot + D] = dg[i];
+        }
+    });
+    return ok.load();
+}
+
+// modelled time of a sweep with Ty x Tz tiles (us): cross-block hops at ~1.5 us, in-block levels at
+// ~0.35 us per warp-pair of rows (two warps per level run on two sub-partitions' FP64 pipes)
+double tile_model(const int32_t dims[3], int Ty, int Tz) {
+    const int nty = (dims[1] + Ty - 1) / Ty, ntz = (dims[2] + Tz - 1) / Tz;
+    const int rows = Ty * Tz, waves = (nty * ntz + 151) / 152;
+    const double lev_us = 0.35 * std::max(1, (rows + 63) / 64) * waves;
+    return 1.5 * (nty + ntz - 1) + lev_us * (dims[0] + Ty + Tz - 2);
+}
+
+}  // namespace
+
+// Natural order on an nx x ny x nz box: the lower dependencies of every row lie at the offsets 1,
+// nx and nx*ny (or a subset of them), and n = nx ny nz.  Detected from the host pattern.
+bool tile_grid(Ctx *c) {
+    c->tl_dims[0] = c->tl_dims[1] = c->tl_dims[2] = 0;
+    if (c->o.ilu_order != CPTR_ILU_NATURAL || c->n_inst > 1) return false;
+    if (host_pattern(c) != CPTR_OK) return false;
+    const int32_t n = c->n;
+    const std::vector<int32_t> &rp = c->h_rp, &ci = c->h_ci;
+    std::vector<int32_t> off;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+            const int32_t o = i - ci[k];
+            if (o <= 0) continue;
+            if (std::find(off.begin(), off.end(), o) == off.end()) {
+                off.push_back(o);
+                if (off.size() > 3) return false;
+            }
+        }
+    std::sort(off.begin(), off.end());
+    int32_t nx = n, ny = 1, nz = 1;
+    if (off.empty()) return false;
+    if (off[0] != 1) return false;
+    if (off.size() >= 2) {
+        nx = off[1];
+        if (off.size() == 3) {
+            if (off[2] % off[1]) return false;
+            ny = off[2] / off[1];
+            nz = n / off[2];
+        } else {
+            ny = n / nx;
+        }
+    }
+    if ((int64_t)nx * ny * nz != n) return false;
+    c->tl_dims[0] = nx;
+    c->tl_dims[1] = ny;
+    c->tl_dims[2] = nz;
+    return true;
+}
+
+// the k tile shapes of smallest modelled time (tiles of at most kTileMaxRows lines)
+void tile_candidates(const Ctx *c, int k, std::vector<std::pair<int, int>> &out) {
+    out.clear();
+    const int32_t *dims = c->tl_dims;
+    if (!dims[0]) return;
+    std::vector<std::pair<double, std::pair<int, int>>> all;
+    for (int Ty = 1; Ty <= std::min(dims[1], kTileMaxRows); ++Ty)
+        for (int Tz = 1; Tz <= std::min(dims[2], kTileMaxRows / Ty); ++Tz)
+            all.push_back({tile_model(dims, Ty, Tz), {Ty, Tz}});
+    std::sort(all.begin(), all.end());
+    for (size_t i = 0; i < all.size() && (int)out.size() < k; ++i) out.push_back(all[i].second);
+}
+
+void tile_free(Ctx *c) {
+    for (TileTables *t : {&c->tl_f, &c->tl_b}) {
+        dfree(t->tlev);
+        dfree(t->lptr);
+        dfree(t->rec);
+        *t = TileTables();
+    }
+    c->tl_ok = false;
+    c->tl_ty = c->tl_tz = 0;
+}
+
+cptr_status tile_setup(Ctx *c, int Ty, int Tz) {
+    tile_free(c);
+    if (!c->tl_dims[0]) return CPTR_OK;
+    CPTR_TRY(host_pattern(c));
+    const int32_t n = c->n, B = c->b, BB = B * B;
+    const bool lo = c->o.precision == CPTR_PREC_MIXED;
+    const int tsz = lo ? 4 : 8;
+    cudaStream_t st = c->stream;
+    for (int dir = 0; dir < 2; ++dir) {
+        const bool fwd = dir == 0;
+        TileHost h;
+        // the ring holds the last R solved rows of a tile; 4 levels of the widest tile at least
+        int R = 256;
+        while (R < 4 * Ty * Tz) R *= 2;
+        if (!tile_build(n, c->h_rp, c->h_ci, c->h_diag, c->tl_dims, Ty, Tz, fwd, R, h)) {
+            tile_free(c);
+            return CPTR_OK;
+        }
+        TileTables &t = fwd ? c->tl_f : c->tl_b;
+        t.ntiles = h.ntiles;
+        t.nlev = h.nlev;
+        t.D = h.D;
+        t.MW = h.MW;
+        t.R = R;
+        t.RS = rec_bytes(h.D, BB, tsz, fwd);
+        const int ssz = fwd ? 8 : tsz;   // right-hand side: r (FP64, or FP32 in the FP32 stage) or y
+        size_t smem = 0;
+        int P = 2;
+        for (; P >= 1; --P) {
+            smem = kTileBar + (size_t)(P + 2) * t.MW * t.RS + (size_t)(P + 1) * t.MW * val_bytes(h.D, B, ssz) +
+                   (size_t)R * B * tsz;
+            if (smem <= kTileSmemMax) break;
+        }
+        if (P < 1) {
+            tile_free(c);
+            return CPTR_OK;
+        }
+        t.P = P;
+        t.smem = (int32_t)smem;
+        t.threads = ((4 * t.MW + 31) / 32) * 32;
+        t.grid = std::min(h.ntiles, 152);
+        CPTR_TRY(dalloc_t(c, &t.tlev, h.tlev.size()));
+        CPTR_TRY(dalloc_t(c, &t.lptr, h.lptr.size()));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(t.tlev, h.tlev.data(), sizeof(int32_t) * h.tlev.size(), cudaMemcpyHostToDevice, st));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(t.lptr, h.lptr.data(), sizeof(int32_t) * h.lptr.size(), cudaMemcpyHostToDevice, st));
+        int32_t *dh = nullptr, *dk = nullptr;
+        CPTR_TRY(dalloc_t(c, &dh, h.hdr.size()));
+        CPTR_TRY(dalloc_t(c, &dk, h.kidx.size()));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(dh, h.hdr.data(), sizeof(int32_t) * h.hdr.size(), cudaMemcpyHostToDevice, st));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(dk, h.kidx.data(), sizeof(int32_t) * h.kidx.size(), cudaMemcpyHostToDevice, st));
+        CPTR_TRY(dalloc(c, reinterpret_cast<void **>(&t.rec), (size_t)n * t.RS));
+        const int nslot = h.D + (fwd ? 0 : 1);
+        const int H = hdr_bytes(h.D);
+        if (lo)
+            (k_tile_pack<float><<<nblk(n, 256), 256, 0, st>>>(n, h.D, BB, t.RS, H, nslot, dh, dk, c->LU, t.rec), note_launch());
+        else
+            (k_tile_pack<double><<<nblk(n, 256), 256, 0, st>>>(n, h.D, BB, t.RS, H, nslot, dh, dk, c->LU, t.rec), note_launch());
+        CPTR_CUDA_TRY(c, cudaGetLastError());
+        CPTR_CUDA_TRY(c, cudaStreamSynchronize(st));   // the host tables are freed on return
+        dfree(dh);
+        dfree(dk);
+    }
+    c->tl_ok = true;
+    c->tl_ty = Ty;
+    c->tl_tz = Tz;
+    return CPTR_OK;
+}
+
+namespace {
+template <int B, typename T, typename ST, typename XT, bool FWD>
+void tile_launch(const Ctx *c, const TileTables &t, const ST *src, T *vec, double *out, const XT *dp, const XT *dT,
+                 const double *never) {
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
+        (kern<<<t.grid, t.threads, t.smem, c->stream>>>(t.ntiles, t.tlev, t.lptr, t.rec, t.RS, t.D, t.R, t.MW, src, vec,
+                                                       out, c->ps, c->ts, dp, dT, c->sf_ticket, c->ks, never,
+                                                       c->sf_sleep),
+         note_launch());
+    };
+    if (t.P == 2) go(k_ilu_tile<B, T, ST, XT, FWD, 2>);
+    else go(k_ilu_tile<B, T, ST, XT, FWD, 1>);
+}
+
+template <int B, typename T, typename RT, typename XT>
+void tile_apply_b(const Ctx *c, const RT *r, double *z, const XT *dp, const XT *dT) {
+    T *y = (T *)c->sf_y, *zz = (T *)c->sf_z;
+    int pf = prof_begin(c, PF_ILU_FWD);
+    tile_launch<B, T, RT, XT, true>(c, c->tl_f, r, y, nullptr, (const XT *)nullptr, (const XT *)nullptr,
+                                    c->inject_wait ? c->never : nullptr);
+    prof_end(c, pf);
+    pf = prof_begin(c, PF_ILU_BWD);
+    tile_launch<B, T, T, XT, false>(c, c->tl_b, y, zz, z, dp, dT, nullptr);
+    prof_end(c, pf);
+}
+}  // namespace
+
+template <typename T, typename RT, typename XT>
+void tile_apply(const Ctx *c, const RT *r, double *z, const XT *dp, const XT *dT) {
+    if (c->b == 3) tile_apply_b<3, T, RT, XT>(c, r, z, dp, dT);
+    else tile_apply_b<4, T, RT, XT>(c, r, z, dp, dT);
+}
+template void tile_apply<double, double, double>(const Ctx *, const double *, double *, const double *, const double *);
+template void tile_apply<float, double, double>(const Ctx *, const double *, double *, const double *, const double *);
+template void tile_apply<float, float, float>(const Ctx *, const float *, double *, const float *, const float *);
+
+}  // namespace cptr
