@@ -259,7 +259,7 @@ struct CwTables {
 // tables of one tiled ILU(0) sweep (see ilu_tile.cu): tiles in processing order, their level
 // pointers, and one record per position (row, dependency codes, factor blocks)
 struct TileTables {
-    int32_t ntiles = 0, nlev = 0, D = 0, MW = 0, RS = 0, R = 0, P = 2, smem = 0, threads = 0, grid = 0;
+    int32_t ntiles = 0, nlev = 0, D = 0, MW = 0, RS = 0, R = 0, P = 2, smem = 0, threads = 0, grid = 0, maxnl = 0;
     int32_t *tlev = nullptr, *lptr = nullptr;
     unsigned char *rec = nullptr;
 };

@@ -17,7 +17,7 @@
 // holds the row, its dependency codes (a ring slot, or the global row of a value to poll) and its
 // factor blocks (and, backward, the inverted pivot block).  The records of a level are one
 // contiguous run, copied into shared memory by a TMA bulk copy (cp.async.bulk completing on an
-// mbarrier) NS - 1 levels ahead; P levels ahead, each row's right-hand side and the 16-byte
+// mbarrier) 2P levels ahead; P levels ahead, each row's right-hand side and the 16-byte
 // windows around its outside dependencies' values are copied by cp.async (through L2 only), so
 // that a level starts with everything in shared memory.  A value copied before it was written
 // holds the sentinel and is polled from global memory when used.
@@ -43,7 +43,7 @@ namespace {
 constexpr int32_t kTileNone = INT32_MIN;   // no dependency in this slot
 constexpr int kTileMaxRows = 64;           // rows of one level of a tile (4 lanes each: <= 256 threads)
 constexpr int kTileWin = 48;               // bytes of the 16-byte-aligned window around a row's value
-constexpr int kTileBar = 128;              // shared-memory bytes reserved for the mbarriers
+constexpr int kTileBar = 256;              // shared-memory bytes reserved for the mbarriers
 constexpr size_t kTileSmemMax = 200 * 1024;
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -54,9 +54,12 @@ __host__ __device__ inline int hdr_bytes(int D) { return ((1 + D) * 4 + 15) & ~1
 __host__ __device__ inline int rec_bytes(int D, int BB, int tsz, bool fwd) {
     return hdr_bytes(D) + (((D + (fwd ? 0 : 1)) * BB * tsz + 15) & ~15);
 }
-// staged inputs of one row: its right-hand side (B values, padded to 16 bytes), one window per slot
-__host__ __device__ inline int rhs_bytes(int B, int ssz) { return (B * ssz + 15) & ~15; }
+// staged inputs of one row: its right-hand side (B values, padded to 16 bytes), the backward
+// sweep's x1 terms (B doubles: lane ps holds dp, lane ts holds dT), one window per slot
+__host__ __device__ inline int rhs_bytes(int B, int ssz) { return ((B * ssz + 15) & ~15) + ((B * 8 + 15) & ~15); }
 __host__ __device__ inline int val_bytes(int D, int B, int ssz) { return rhs_bytes(B, ssz) + D * kTileWin; }
+// shared-memory bytes of a tile's level pointers
+__host__ __device__ inline int lv_bytes(int maxnl) { return ((maxnl + 1) * 4 + 15) & ~15; }
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t *m, unsigned count) {
@@ -90,6 +93,15 @@ __device__ __forceinline__ void cp_async_ca(double *dst, const double *src) {
 __device__ __forceinline__ void cp_async_ca(float *dst, const float *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
+// the x1 term of a row (dp or dT, FP64 or FP32) into a staged double slot; read back by x1_value
+__device__ __forceinline__ void cp_async_x1(double *dst, const double *src) { cp_async_ca(dst, src); }
+__device__ __forceinline__ void cp_async_x1(double *dst, const float *src) {
+    cp_async_ca(reinterpret_cast<float *>(dst), src);
+}
+__device__ __forceinline__ double x1_value(const double *slot, const double *) { return *slot; }
+__device__ __forceinline__ double x1_value(const double *slot, const float *) {
+    return (double)*reinterpret_cast<const float *>(slot);
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -114,188 +126,219 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, unsigned parity) 
 // One sweep.  Forward (FWD): y(row) = r(row) - sum_d L(row, d) y(dep d).  Backward:
 // z(row) = D(row)^{-1} (y(row) - sum_d U(row, d) z(dep d)), out(row) = z(row) + x1(row), x1 carrying
 // dp in slot ps and dT in slot ts.  src: r (forward, type ST) or y (backward); vec: the vector being
-// solved, in row order.  Lane q of a row's group of four computes component q (B <= 4), like the
-// four-lane level-set kernels.  NS = P + 2 record stages, P + 1 value slots.
+// solved, in row order.
+//
+// Warp-specialised: the last warp of the block is the producer, the others are consumers.  Lane q
+// of a consumer row group of four computes component q (B <= 4), like the four-lane level-set
+// kernels; the consumers only read shared memory and do the level's arithmetic, one named barrier
+// per level among themselves.  The producer runs P levels ahead: at its step m it copies the
+// records of level m + P (TMA bulk copy onto rec_full), waits for the records of level m, and
+// copies each row's right-hand side, x1 terms and outside-dependency windows (cp.async, completion
+// tracked by cp.async.mbarrier.arrive on val_full).  Consumers release a value slot (val_empty)
+// when they finish its level; that also frees the record stage the producer refills next, since
+// NS = 2P + 1 stages and NV = P + 1 value slots are in flight.
 template <int B, typename T, typename ST, typename XT, bool FWD, int P>
-__global__ void __launch_bounds__(4 * kTileMaxRows)
+__global__ void __launch_bounds__(4 * kTileMaxRows + 32)
     k_ilu_tile(int32_t ntiles, const int32_t *__restrict__ tlev, const int32_t *__restrict__ lptr,
-               const unsigned char *__restrict__ rec, int RS, int D, int R, int MW, const ST *__restrict__ src,
-               T *vec, double *__restrict__ out, int ps, int ts, const XT *__restrict__ dp,
-               const XT *__restrict__ dT, unsigned *ticket, KState *ks, const double *never, int sleep_ns) {
-    constexpr int BB = B * B, NS = P + 2, NV = P + 1;
+               const unsigned char *__restrict__ rec, int RS, int D, int R, int MW, int maxnl,
+               const ST *__restrict__ src, T *vec, double *__restrict__ out, int ps, int ts,
+               const XT *__restrict__ dp, const XT *__restrict__ dT, unsigned *ticket, KState *ks,
+               const double *never, int sleep_ns) {
+    constexpr int BB = B * B, NS = 2 * P + 1, NV = P + 1;
+    constexpr int WPIECES = (8 * B + 15 + 15) / 16;   // 16-byte pieces of a window (value + skew)
     const int H = hdr_bytes(D), RH = rhs_bytes(B, (int)sizeof(ST)), SV = val_bytes(D, B, (int)sizeof(ST));
+    const int XA = (B * (int)sizeof(ST) + 15) & ~15;   // offset of the x1 terms in a staged row
     extern __shared__ __align__(128) unsigned char tile_smem[];
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(tile_smem);
-    unsigned char *recs = tile_smem + kTileBar;
+    uint64_t *rec_full = reinterpret_cast<uint64_t *>(tile_smem);
+    uint64_t *val_full = rec_full + NS;
+    uint64_t *val_empty = val_full + NV;
+    int32_t *lv = reinterpret_cast<int32_t *>(tile_smem + kTileBar);   // the tile's level pointers
+    unsigned char *recs = tile_smem + kTileBar + lv_bytes(maxnl);
     unsigned char *vals = recs + (size_t)NS * MW * RS;
     T *ring = reinterpret_cast<T *>(vals + (size_t)NV * MW * SV);
     __shared__ unsigned tile_s;
-    __shared__ int abort_s;
-    const int tid = threadIdx.x, g = tid >> 2, q4 = tid & 3;
+    __shared__ volatile int abort_s;   // a bounded wait gave up: every wait returns at once
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ncons = (int)blockDim.x - 32;   // consumer threads; the producer is the last warp
+    const bool producer = tid >= ncons;
+    const int g = tid >> 2, q4 = tid & 3;
     const int g0 = (tid & 31) & ~3;
     const unsigned gmask = ((1u << B) - 1u) << g0;
+    (void)warp;
     if (tid == 0) {
-        for (int s = 0; s < NS; ++s) mbar_init(&mbar[s], 1);
+        for (int s = 0; s < NS; ++s) mbar_init(&rec_full[s], 1);
+        for (int s = 0; s < NV; ++s) {
+            mbar_init(&val_full[s], 32);
+            mbar_init(&val_empty[s], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         abort_s = 0;
     }
     __syncthreads();
-    unsigned gl = 0;   // levels this block has processed: stage index and mbarrier phase
+    // bounded wait on an mbarrier phase; gives up at once when this call has already failed
+    auto wait_bar = [&](uint64_t *m, unsigned parity) {
+        if (mbar_try_wait(m, parity)) return;
+        const unsigned long long t0 = gtimer();
+        for (;;) {
+            if (mbar_try_wait(m, parity)) return;
+            const unsigned long long dt = gtimer() - t0;
+            if (dt > kWaitNs || abort_s || (dt > 100000ull && failed(ks))) {
+                atomicExch(&ks->wait_err, 1);
+                abort_s = 1;
+                return;
+            }
+        }
+    };
+    unsigned gl = 0;   // levels this block has processed: stage indices and mbarrier phases
     for (;;) {
         if (tid == 0) tile_s = atomicAdd(ticket + (FWD ? 0 : 1), 1u);
         __syncthreads();
         const unsigned tile = tile_s;
-        if (tile >= (unsigned)ntiles) break;
+        if (tile >= (unsigned)ntiles || abort_s) break;
         const int L0 = __ldg(tlev + tile), nl = __ldg(tlev + tile + 1) - L0;
-        const int32_t pos0 = __ldg(lptr + L0);
-        int issued = 0;   // record stages issued for this tile (thread 0)
-        auto issue_rec = [&](int m) {
-            const unsigned G = gl + m;
-            const int s = (int)(G % NS);
-            const int32_t a = __ldg(lptr + L0 + m), b = __ldg(lptr + L0 + m + 1);
-            const unsigned bytes = (unsigned)(b - a) * (unsigned)RS;
-            mbar_expect_tx(&mbar[s], bytes);
-            bulk_g2s(recs + (size_t)s * MW * RS, rec + (size_t)a * RS, bytes, &mbar[s]);
-            ++issued;
-        };
-        auto wait_rec = [&](int m) {
-            const unsigned G = gl + m;
-            if (!mbar_wait_bounded(&mbar[G % NS], (G / NS) & 1u)) {
-                atomicExch(&ks->wait_err, 1);
-                abort_s = 1;
-            }
-        };
-        // row g's right-hand side (lane q < B: component q) and the windows of its outside
-        // dependencies (lane q < 3: 16-byte piece q), for level m, into value slot (gl + m) % NV
-        auto issue_vals = [&](int m) {
-            const unsigned G = gl + m;
-            const int w = __ldg(lptr + L0 + m + 1) - __ldg(lptr + L0 + m);
-            if (g >= w) return;
-            const unsigned char *r = recs + (size_t)(G % NS) * MW * RS + (size_t)g * RS;
-            const int32_t row = *reinterpret_cast<const int32_t *>(r);
-            const int32_t *code = reinterpret_cast<const int32_t *>(r) + 1;
-            unsigned char *dst = vals + ((size_t)(G % NV) * MW + g) * SV;
-            if (q4 < B) cp_async_ca(reinterpret_cast<ST *>(dst) + q4, src + (int64_t)row * B + q4);
-            if (q4 < 3)
-                for (int d = 0; d < D; ++d) {
-                    const int32_t cd = code[d];
-                    if (cd == kTileNone) break;
-                    if (cd >= 0) continue;
-                    const int64_t j = -(int64_t)cd - 1;
-                    const uintptr_t at = (reinterpret_cast<uintptr_t>(vec + j * B) & ~(uintptr_t)15) + 16 * q4;
-                    cp_async_cg16(dst + RH + d * kTileWin + 16 * q4, reinterpret_cast<const void *>(at));
-                }
-        };
-        if (tid == 0)
-            for (int m = 0; m < min(NS - 1, nl); ++m) issue_rec(m);
-        for (int m = 0; m < P; ++m) {
-            if (m < nl) {
-                wait_rec(m);
-                issue_vals(m);
-            }
-            cp_async_commit();
-        }
-        for (int l = 0; l < nl; ++l) {
-            cp_async_wait<P - 1>();   // this thread's copies of level l have landed
-            __syncthreads();          // ... everyone's, and the ring values of the levels before
-            if (abort_s) break;
-            if (tid == 0 && l + NS - 1 < nl) issue_rec(l + NS - 1);   // into the stage level l - 1 used
-            const unsigned G = gl + l;
-            const int w = __ldg(lptr + L0 + l + 1) - __ldg(lptr + L0 + l);
-            const int32_t p0 = __ldg(lptr + L0 + l) - pos0;   // local position of the level's first row
-            if (g < w && q4 < B) {
-                const unsigned char *r = recs + (size_t)(G % NS) * MW * RS + (size_t)g * RS;
-                const int32_t row = *reinterpret_cast<const int32_t *>(r);
-                const int32_t *code = reinterpret_cast<const int32_t *>(r) + 1;
-                const T *blk = reinterpret_cast<const T *>(r + H);
-                const unsigned char *vb = vals + ((size_t)(G % NV) * MW + g) * SV;
-                if (FWD && never && tile == 0 && l == 0 && g == 0 && q4 == 0) (void)wait_value(never, ks);
-                T acc = (T) reinterpret_cast<const ST *>(vb)[q4];
-                for (int d = 0; d < D; ++d) {
-                    const int32_t cd = code[d];
-                    if (cd == kTileNone) break;
-                    T v[B];
-                    if (cd >= 0) {
+        for (int q = tid; q <= nl; q += blockDim.x) lv[q] = __ldg(lptr + L0 + q);
+        __syncthreads();
+        const int32_t pos0 = lv[0];
+        if (producer) {
+            int issued = 0;   // record stages issued (lane 0)
+            auto issue_rec = [&](int m) {
+                const unsigned G = gl + m;
+                const unsigned bytes = (unsigned)(lv[m + 1] - lv[m]) * (unsigned)RS;
+                mbar_expect_tx(&rec_full[G % NS], bytes);
+                bulk_g2s(recs + (size_t)(G % NS) * MW * RS, rec + (size_t)lv[m] * RS, bytes, &rec_full[G % NS]);
+                ++issued;
+            };
+            if (lane == 0)
+                for (int m = 0; m < min(P, nl); ++m) issue_rec(m);
+            for (int m = 0; m < nl && !abort_s; ++m) {
+                const unsigned G = gl + m;
+                if (G >= (unsigned)NV) wait_bar(&val_empty[G % NV], (G / NV - 1) & 1u);   // level G - NV done
+                if (lane == 0 && m + P < nl) issue_rec(m + P);   // its stage's last level was G - NV
+                wait_bar(&rec_full[G % NS], (G / NS) & 1u);
+                const int w = lv[m + 1] - lv[m];
+                for (int r0 = lane; r0 < w; r0 += 32) {
+                    const unsigned char *r = recs + (size_t)(G % NS) * MW * RS + (size_t)r0 * RS;
+                    const int32_t row = *reinterpret_cast<const int32_t *>(r);
+                    const int32_t *code = reinterpret_cast<const int32_t *>(r) + 1;
+                    unsigned char *dst = vals + ((size_t)(G % NV) * MW + r0) * SV;
 #pragma unroll
-                        for (int u = 0; u < B; ++u) v[u] = ring[(size_t)cd * B + u];
-                    } else {
+                    for (int q = 0; q < B; ++q) cp_async_ca(reinterpret_cast<ST *>(dst) + q, src + (int64_t)row * B + q);
+                    if (!FWD) {
+                        double *xa = reinterpret_cast<double *>(dst + XA);
+                        if (dp) cp_async_x1(xa + ps, dp + row);
+                        if (dT) cp_async_x1(xa + ts, dT + row);
+                    }
+                    for (int d = 0; d < D; ++d) {
+                        const int32_t cd = code[d];
+                        if (cd == kTileNone) break;
+                        if (cd >= 0) continue;
                         const int64_t j = -(int64_t)cd - 1;
-                        const T *win = reinterpret_cast<const T *>(
-                            vb + RH + d * kTileWin + (reinterpret_cast<uintptr_t>(vec + j * B) & 15));
-                        bool pend = false;
+                        const uintptr_t at = reinterpret_cast<uintptr_t>(vec + j * B) & ~(uintptr_t)15;
 #pragma unroll
-                        for (int u = 0; u < B; ++u) {
-                            v[u] = win[u];
-                            pend |= is_sentinel(v[u]);
-                        }
-                        if (pend) {   // copied before it was written: poll (bounded)
-                            const unsigned long long t0 = gtimer();
-                            for (;;) {
-                                pend = false;
+                        for (int k = 0; k < WPIECES; ++k)
+                            cp_async_cg16(dst + RH + d * kTileWin + 16 * k, reinterpret_cast<const void *>(at + 16 * k));
+                    }
+                }
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&val_full[G % NV]))
+                             : "memory");
+            }
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            if (abort_s && lane == 0)   // record copies still in flight: wait (bounded) for them
+                for (int m = 0; m < issued; ++m) {
+                    const unsigned G = gl + m;
+                    (void)mbar_wait_bounded(&rec_full[G % NS], (G / NS) & 1u);
+                }
+        } else {
+            for (int l = 0; l < nl; ++l) {
+                const unsigned G = gl + l;
+                // after a failed wait the consumers still pass every level's barrier together
+                wait_bar(&val_full[G % NV], (G / NV) & 1u);
+                wait_bar(&rec_full[G % NS], (G / NS) & 1u);
+                const int w = abort_s ? 0 : lv[l + 1] - lv[l];
+                const int32_t p0 = lv[l] - pos0;   // local position of the level's first row
+                if (g < w && q4 < B) {
+                    const unsigned char *r = recs + (size_t)(G % NS) * MW * RS + (size_t)g * RS;
+                    const int32_t row = *reinterpret_cast<const int32_t *>(r);
+                    const int32_t *code = reinterpret_cast<const int32_t *>(r) + 1;
+                    const T *blk = reinterpret_cast<const T *>(r + H);
+                    const unsigned char *vb = vals + ((size_t)(G % NV) * MW + g) * SV;
+                    if (FWD && never && tile == 0 && l == 0 && g == 0 && q4 == 0) (void)wait_value(never, ks);
+                    T acc = (T) reinterpret_cast<const ST *>(vb)[q4];
+                    for (int d = 0; d < D; ++d) {
+                        const int32_t cd = code[d];
+                        if (cd == kTileNone) break;
+                        T v[B];
+                        if (cd >= 0) {
 #pragma unroll
-                                for (int u = 0; u < B; ++u)
-                                    if (is_sentinel(v[u])) {
-                                        v[u] = load_relaxed(vec + j * B + u);
-                                        pend |= is_sentinel(v[u]);
-                                    }
-                                if (!pend) break;
-                                const unsigned long long dt = gtimer() - t0;
-                                // give up after kWaitNs, or after 100 us once any wait of the call
-                                // has given up (its values will not come)
-                                if (dt > kWaitNs || (dt > 100000ull && failed(ks))) {
-                                    atomicExch(&ks->wait_err, 1);
-                                    abort_s = 1;
+                            for (int u = 0; u < B; ++u) v[u] = ring[cd * B + u];
+                        } else {
+                            const uint32_t j32 = (uint32_t)(-(cd + 1));
+                            const T *win = reinterpret_cast<const T *>(vb + RH + d * kTileWin +
+                                                                       ((j32 * (uint32_t)(B * sizeof(T))) & 15u));
+                            bool pend = false;
+#pragma unroll
+                            for (int u = 0; u < B; ++u) {
+                                v[u] = win[u];
+                                pend |= is_sentinel(v[u]);
+                            }
+                            if (pend) {   // copied before it was written: poll (bounded)
+                                const int64_t j = (int64_t)j32;
+                                const unsigned long long t0 = gtimer();
+                                for (;;) {
+                                    pend = false;
 #pragma unroll
                                     for (int u = 0; u < B; ++u)
-                                        if (is_sentinel(v[u])) v[u] = (T)0;
-                                    break;
+                                        if (is_sentinel(v[u])) {
+                                            v[u] = load_relaxed(vec + j * B + u);
+                                            pend |= is_sentinel(v[u]);
+                                        }
+                                    if (!pend) break;
+                                    const unsigned long long dt = gtimer() - t0;
+                                    // give up after kWaitNs, or after 100 us once any wait of the
+                                    // call has given up (its values will not come)
+                                    if (dt > kWaitNs || (dt > 100000ull && failed(ks))) {
+                                        atomicExch(&ks->wait_err, 1);
+                                        abort_s = 1;
+#pragma unroll
+                                        for (int u = 0; u < B; ++u)
+                                            if (is_sentinel(v[u])) v[u] = (T)0;
+                                        break;
+                                    }
+                                    __nanosleep(sleep_ns);
                                 }
-                                __nanosleep(sleep_ns);
                             }
                         }
+#pragma unroll
+                        for (int u = 0; u < B; ++u) acc = fma(-blk[d * BB + q4 * B + u], v[u], acc);
                     }
+                    T res;
+                    if (FWD) {
+                        res = acc;
+                    } else {
+                        const T *dinv = blk + D * BB;
+                        res = (T)0;
 #pragma unroll
-                    for (int u = 0; u < B; ++u) acc = fma(-blk[d * BB + q4 * B + u], v[u], acc);
+                        for (int u = 0; u < B; ++u) res = fma(dinv[q4 * B + u], __shfl_sync(gmask, acc, g0 + u), res);
+                    }
+                    ring[((p0 + g) & (R - 1)) * B + q4] = res;
+                    store_relaxed(vec + (int64_t)row * B + q4, res);
+                    if (!FWD) {
+                        const double *xa = reinterpret_cast<const double *>(vb + XA);
+                        double add = 0.0;
+                        if (dp && q4 == ps) add = x1_value(xa + q4, dp);
+                        if (dT && q4 == ts) add = x1_value(xa + q4, dT);
+                        out[(int64_t)row * B + q4] = (double)res + add;
+                    }
                 }
-                T res;
-                if (FWD) {
-                    res = acc;
-                } else {
-                    const T *dinv = blk + D * BB;
-                    res = (T)0;
-#pragma unroll
-                    for (int u = 0; u < B; ++u) res = fma(dinv[q4 * B + u], __shfl_sync(gmask, acc, g0 + u), res);
-                }
-                ring[(size_t)((p0 + g) & (R - 1)) * B + q4] = res;
-                store_relaxed(vec + (int64_t)row * B + q4, res);
-                if (!FWD) {
-                    double add = 0.0;
-                    if (dp && q4 == ps) add = (double)dp[row];
-                    if (dT && q4 == ts) add = (double)dT[row];
-                    out[(int64_t)row * B + q4] = (double)res + add;
-                }
+                // the level's ring values are visible to every consumer, and its slots are free
+                asm volatile("bar.sync 1, %0;" ::"r"(ncons) : "memory");
+                if (tid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&val_empty[G % NV]))
+                                           : "memory");
             }
-            if (l + P < nl) {
-                wait_rec(l + P);
-                issue_vals(l + P);
-            }
-            cp_async_commit();
         }
-        cp_async_wait<0>();
         __syncthreads();
-        if (abort_s) {
-            // a wait gave up: wait (bounded) for the record copies still in flight, then stop
-            if (tid == 0) {
-                const int done = min(nl, issued);
-                for (int m = 0; m < done; ++m) {
-                    const unsigned G = gl + m;
-                    (void)mbar_wait_bounded(&mbar[G % NS], (G / NS) & 1u);
-                }
-            }
-            __syncthreads();
-            break;
-        }
+        if (abort_s) break;
         gl += (unsigned)nl;
     }
 }
@@ -339,7 +382,7 @@ void parallel_for(int32_t count, F &&f) {
 // and block indices; false when the schedule does not apply (a level wider than kTileMaxRows, or an
 // outside dependency on a later tile)
 struct TileHost {
-    int32_t ntiles = 0, nlev = 0, D = 0, MW = 0;
+    int32_t ntiles = 0, nlev = 0, D = 0, MW = 0, maxnl = 0;
     std::vector<int32_t> tlev, lptr, hdr, kidx;
 };
 
@@ -417,6 +460,7 @@ bool tile_build(int32_t n, const std::vector<int32_t> &rp, const std::vector<int
     for (int32_t t = 0; t < nt; ++t) {
         h.tlev[t + 1] = h.tlev[t] + nlev_t[t];
         h.MW = std::max(h.MW, width_t[t]);
+        h.maxnl = std::max(h.maxnl, nlev_t[t]);
     }
     if (h.MW > kTileMaxRows || h.MW < 1) return false;
     h.nlev = h.tlev[nt];
@@ -453,13 +497,15 @@ bool tile_build(int32_t n, const std::vector<int32_t> &rp, const std::vector<int
     return ok.load();
 }
 
-// modelled time of a sweep with Ty x Tz tiles (us): cross-block hops at ~1.5 us, in-block levels at
-// ~0.35 us per warp-pair of rows (two warps per level run on two sub-partitions' FP64 pipes)
+// modelled time of a sweep with Ty x Tz tiles (us).  The wavefront crosses nx + ny + nz levels in
+// all, each at the in-block level time (~0.4 us while a level's rows fit one warp per
+// sub-partition, i.e. 32 rows; a tile's blocks beyond 152 run in a second wave), plus ~1.5 us for
+// each of the ny/Ty + nz/Tz - 1 hops between blocks.
 double tile_model(const int32_t dims[3], int Ty, int Tz) {
     const int nty = (dims[1] + Ty - 1) / Ty, ntz = (dims[2] + Tz - 1) / Tz;
     const int rows = Ty * Tz, waves = (nty * ntz + 151) / 152;
-    const double lev_us = 0.35 * std::max(1, (rows + 63) / 64) * waves;
-    return 1.5 * (nty + ntz - 1) + lev_us * (dims[0] + Ty + Tz - 2);
+    const double lev_us = 0.4 * std::max(1, (rows + 31) / 32) * waves;
+    return 1.5 * (nty + ntz - 1) + lev_us * (dims[0] + dims[1] + dims[2]);
 }
 
 }  // namespace
@@ -551,14 +597,19 @@ cptr_status tile_setup(Ctx *c, int Ty, int Tz) {
         t.D = h.D;
         t.MW = h.MW;
         t.R = R;
+        t.maxnl = h.maxnl;
         t.RS = rec_bytes(h.D, BB, tsz, fwd);
         const int ssz = fwd ? 8 : tsz;   // right-hand side: r (FP64, or FP32 in the FP32 stage) or y
         size_t smem = 0;
-        int P = 2;
-        for (; P >= 1; --P) {
-            smem = kTileBar + (size_t)(P + 2) * t.MW * t.RS + (size_t)(P + 1) * t.MW * val_bytes(h.D, B, ssz) +
+        // the deepest pipeline that fits (P levels of lookahead for the values, 2P for the records)
+        int P = 0;
+        for (int p : {4, 2, 1}) {
+            smem = kTileBar + lv_bytes(h.maxnl) + (size_t)(2 * p + 1) * t.MW * t.RS + (size_t)(p + 1) * t.MW * val_bytes(h.D, B, ssz) +
                    (size_t)R * B * tsz;
-            if (smem <= kTileSmemMax) break;
+            if (smem <= kTileSmemMax) {
+                P = p;
+                break;
+            }
         }
         if (P < 1) {
             tile_free(c);
@@ -566,7 +617,7 @@ cptr_status tile_setup(Ctx *c, int Ty, int Tz) {
         }
         t.P = P;
         t.smem = (int32_t)smem;
-        t.threads = ((4 * t.MW + 31) / 32) * 32;
+        t.threads = ((4 * t.MW + 31) / 32) * 32 + 32;   // consumer warps and one producer warp
         t.grid = std::min(h.ntiles, 152);
         CPTR_TRY(dalloc_t(c, &t.tlev, h.tlev.size()));
         CPTR_TRY(dalloc_t(c, &t.lptr, h.lptr.size()));
@@ -601,12 +652,13 @@ void tile_launch(const Ctx *c, const TileTables &t, const ST *src, T *vec, doubl
                  const double *never) {
     auto go = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
-        (kern<<<t.grid, t.threads, t.smem, c->stream>>>(t.ntiles, t.tlev, t.lptr, t.rec, t.RS, t.D, t.R, t.MW, src, vec,
+        (kern<<<t.grid, t.threads, t.smem, c->stream>>>(t.ntiles, t.tlev, t.lptr, t.rec, t.RS, t.D, t.R, t.MW, t.maxnl, src, vec,
                                                        out, c->ps, c->ts, dp, dT, c->sf_ticket, c->ks, never,
                                                        c->sf_sleep),
          note_launch());
     };
-    if (t.P == 2) go(k_ilu_tile<B, T, ST, XT, FWD, 2>);
+    if (t.P == 4) go(k_ilu_tile<B, T, ST, XT, FWD, 4>);
+    else if (t.P == 2) go(k_ilu_tile<B, T, ST, XT, FWD, 2>);
     else go(k_ilu_tile<B, T, ST, XT, FWD, 1>);
 }
 
