@@ -20,9 +20,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
-CPTR_FULL, CPTR_UPPER, CPTR_LOWER, BD, CPR, NONE1 = range(6)
+CPTR_FULL, CPTR_UPPER, CPTR_LOWER, BD, CPR, NONE1, UAMG = range(7)
 ILU0, NONE2 = 0, 1
-SCHUR_GIVEN, SCHUR_ATT = 0, 1
+SCHUR_GIVEN, SCHUR_ATT, SCHUR_DIAG = 0, 1, 3
 L1, JACOBI = 0, 1
 
 
@@ -30,7 +30,7 @@ def build(force: bool = False) -> str:
     src = os.path.join(_HERE, "oracle.c")
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
         tmp = _LIB_PATH + ".tmp"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+        subprocess.check_call(["gcc", "-O3", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -81,6 +81,8 @@ def _load():
         lib.or_hierarchy.argtypes = [P, ctypes.c_int]
         lib.or_amg_create.restype = P
         lib.or_amg_create.argtypes = [ctypes.c_int32, P, P, P, P, P]
+        lib.or_uamg_create.restype = P
+        lib.or_uamg_create.argtypes = [ctypes.c_int32, P, P, P, ctypes.c_int32, P, P]
         lib.or_amg_destroy.restype = None
         lib.or_amg_destroy.argtypes = [P]
         lib.or_amg_vcycle.restype = None
@@ -156,7 +158,7 @@ class Oracle:
         else:
             st_rp, st_ci = rp, ci
         self.opts = default_opts(**opts)
-        if st_v is None:
+        if st_v is None and self.opts.schur == SCHUR_GIVEN:
             self.opts.schur = SCHUR_ATT
         self._c = lib.or_create(self.n, self.b, _p(rp), _p(ci), _p(v), _p(W), ps, ts, _p(st_rp), _p(st_ci),
                                 _p(st_v), ctypes.byref(self.opts))
@@ -280,7 +282,8 @@ class Oracle:
         return v
 
     def levels(self, which):
-        """AMG hierarchy of A_pp (which=0) or S~_T (which=1): list of dicts per level."""
+        """AMG hierarchy of A_pp (which=0), S~_T (which=1) or, with the uAMG first stage, of A_00 in
+        unknown-wise order (which=2): list of dicts per level."""
         lib = _load()
         return _levels(lib.or_hierarchy(self._c, which), lib.or_nlevels(self._c, which))
 
@@ -311,16 +314,23 @@ def _levels(h, nlev):
 
 class AMG:
     """Standalone oracle AMG hierarchy on a scalar CSR matrix (strength, PMIS, direct
-    interpolation, Galerkin RAP, smoother diagonal, dense coarsest solve)."""
+    interpolation, Galerkin RAP, smoother diagonal, dense coarsest solve).  With ``np`` given, the
+    unknown-based AMG of Sec. 3.4 on a matrix in unknown-wise order whose first ``np`` rows are the
+    first unknown."""
 
-    def __init__(self, rp, ci, v, **opts):
+    def __init__(self, rp, ci, v, np_first=None, **opts):
         lib = _load()
         self._keep = [np.ascontiguousarray(rp, np.int32), np.ascontiguousarray(ci, np.int32),
                       np.ascontiguousarray(v, np.float64)]
         self.n = len(rp) - 1
         self.opts = default_opts(**opts)
         st = ctypes.c_int(0)
-        self._h = lib.or_amg_create(self.n, *(_p(a) for a in self._keep), ctypes.byref(self.opts), ctypes.byref(st))
+        if np_first is None:
+            self._h = lib.or_amg_create(self.n, *(_p(a) for a in self._keep), ctypes.byref(self.opts),
+                                        ctypes.byref(st))
+        else:
+            self._h = lib.or_uamg_create(self.n, *(_p(a) for a in self._keep), int(np_first),
+                                         ctypes.byref(self.opts), ctypes.byref(st))
         if st.value != 0:
             raise RuntimeError(f"oracle AMG setup failed with status {st.value}")
 

@@ -16,6 +16,10 @@
  *   block preconditioner  5 steps for A_00^{-1}          Sec. 3.3 eq. (Aschur) and its step list
  *   Schur approximation   S~_T given (eq. Se) or A_TT    Sec. 3.3.1
  *   CPR first stage       A_pp^{-1} on b_p               Sec. 3.1
+ *   uAMG first stage      unknown-based AMG V-cycle on A_00 (coarsening and interpolation of each
+ *                         diagonal block on its own, Galerkin product and smoothing on the coupled
+ *                         A_00)                           Sec. 3.4
+ *   S~_diag               A_TT - A_Tp diag(A_pp)^{-1} A_pT   Sec. 3.3.1
  *   two-stage combination x1 = M1^-1 v, b1 = v - A x1,
  *                         z = M2^-1 b1 + x1              Sec. 3 "Two-stage preconditioners"
  *   second stage          ILU(0)                         Sec. 4 (ILU(0) default)
@@ -33,9 +37,9 @@
 
 /* ------------------------------------------------------------------------------------------ */
 /* options and stats (layout mirrored by oracle/__init__.py)                                   */
-enum { OR_CPTR_FULL = 0, OR_CPTR_UPPER = 1, OR_CPTR_LOWER = 2, OR_BD = 3, OR_CPR = 4, OR_NONE1 = 5 };
+enum { OR_CPTR_FULL = 0, OR_CPTR_UPPER = 1, OR_CPTR_LOWER = 2, OR_BD = 3, OR_CPR = 4, OR_NONE1 = 5, OR_UAMG = 6 };
 enum { OR_ILU0 = 0, OR_NONE2 = 1 };
-enum { OR_SCHUR_GIVEN = 0, OR_SCHUR_ATT = 1 };
+enum { OR_SCHUR_GIVEN = 0, OR_SCHUR_ATT = 1, OR_SCHUR_DIAG = 3 };
 enum { OR_L1 = 0, OR_JACOBI = 1 };
 
 typedef struct {
@@ -417,6 +421,98 @@ static void amg_free(amg *h) {
     memset(h, 0, sizeof(*h));
 }
 
+/* The diagonal block of rows and columns [r0, r1) of A, re-indexed from 0. */
+static void extract_block(const csr *A, int32_t r0, int32_t r1, csr *B) {
+    int32_t nnz = 0;
+    for (int32_t i = r0; i < r1; ++i)
+        for (int32_t k = A->rp[i]; k < A->rp[i + 1]; ++k) nnz += (A->ci[k] >= r0 && A->ci[k] < r1);
+    csr_alloc(B, r1 - r0, nnz);
+    int32_t o = 0;
+    for (int32_t i = r0; i < r1; ++i) {
+        for (int32_t k = A->rp[i]; k < A->rp[i + 1]; ++k)
+            if (A->ci[k] >= r0 && A->ci[k] < r1) { B->ci[o] = A->ci[k] - r0; B->v[o] = A->v[k]; ++o; }
+        B->rp[i - r0 + 1] = o;
+    }
+}
+
+/* Unknown-based AMG (Sec. 3.4) on A_00 in unknown-wise order: rows [0, np) are the pressure
+ * unknowns, rows [np, n) the temperature unknowns.  On every level, classical coarsening (strength,
+ * PMIS) and direct interpolation are applied to each diagonal block on its own (the pressure block
+ * and the temperature block, with PMIS weights indexed within the block), P = blockdiag(P_p, P_T)
+ * with the coarse pressure points first, and the coarse operator is the Galerkin product of the
+ * whole coupled level matrix, A_c = P^T (A P), so the coupling blocks stay in the coarse-grid
+ * correction.  The smoother and the coarsest solve act on the whole level matrix.  Coarsening stops
+ * as in amg_setup (n <= n_coarse, max_levels, or no coarsening possible in either block). */
+static int uamg_setup(amg *h, const csr *A0, int32_t np0, const or_opts *o) {
+    memset(h, 0, sizeof(*h));
+    csr_copy(A0, &h->L[0].A);
+    int l = 0;
+    int32_t np = np0;
+    int maxl = o->max_levels < 1 ? 1 : (o->max_levels > 32 ? 32 : o->max_levels);
+    for (;;) {
+        amg_level *L = &h->L[l];
+        int32_t n = L->A.n;
+        L->dinv = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        smoother_diag(&L->A, o->smoother, o->omega, L->dinv);
+        L->r = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+        L->x = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+        L->b = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+        if (l + 1 >= maxl || n <= o->n_coarse) break;
+        /* each unknown's diagonal block: strength, PMIS, direct interpolation */
+        csr blk[2], Pb[2];
+        int32_t nc[2], r0[2] = {0, np}, r1[2] = {np, n};
+        int32_t *cfb[2];
+        for (int u = 0; u < 2; ++u) {
+            extract_block(&L->A, r0[u], r1[u], &blk[u]);
+            int32_t *Srp, *Sci;
+            strength(&blk[u], o->theta, &Srp, &Sci);
+            cfb[u] = (int32_t *)malloc(sizeof(int32_t) * (size_t)(blk[u].n > 0 ? blk[u].n : 1));
+            pmis(blk[u].n, Srp, Sci, (uint64_t)o->seed + (uint64_t)l, cfb[u]);
+            direct_interp(&blk[u], Srp, Sci, cfb[u], &Pb[u], &nc[u]);
+            free(Srp); free(Sci);
+        }
+        int32_t ncs = nc[0] + nc[1];
+        if (ncs == 0 || ncs >= n) { /* no coarsening possible: this level is the coarsest */
+            for (int u = 0; u < 2; ++u) { csr_free(&blk[u]); csr_free(&Pb[u]); free(cfb[u]); }
+            break;
+        }
+        /* P = blockdiag(P_p, P_T): temperature columns after the nc[0] pressure columns */
+        csr_alloc(&L->P, n, Pb[0].nnz + Pb[1].nnz);
+        L->cf = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+        int32_t o2 = 0;
+        for (int u = 0; u < 2; ++u)
+            for (int32_t i = 0; i < Pb[u].n; ++i) {
+                L->cf[r0[u] + i] = cfb[u][i];
+                for (int32_t k = Pb[u].rp[i]; k < Pb[u].rp[i + 1]; ++k) {
+                    L->P.ci[o2] = Pb[u].ci[k] + (u ? nc[0] : 0);
+                    L->P.v[o2] = Pb[u].v[k];
+                    ++o2;
+                }
+                L->P.rp[r0[u] + i + 1] = o2;
+            }
+        for (int u = 0; u < 2; ++u) { csr_free(&blk[u]); csr_free(&Pb[u]); free(cfb[u]); }
+        csr_transpose(&L->P, ncs, &L->PT);
+        csr AP;
+        spgemm(&L->A, &L->P, ncs, &AP);
+        spgemm(&L->PT, &AP, ncs, &h->L[l + 1].A);
+        csr_free(&AP);
+        np = nc[0];
+        ++l;
+    }
+    h->nlev = l + 1;
+    amg_level *C = &h->L[l];
+    int32_t n = C->A.n;
+    if (n <= o->dense_max) {
+        h->dense = 1;
+        h->lu = (double *)calloc((size_t)n * n + 1, sizeof(double));
+        h->piv = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t k = C->A.rp[i]; k < C->A.rp[i + 1]; ++k) h->lu[(size_t)i * n + C->A.ci[k]] += C->A.v[k];
+        if (dense_lu(n, h->lu, h->piv) != 0) return -6;
+    }
+    return 0;
+}
+
 /* One V(1,1)-cycle with zero initial guess: x ~= A_l^{-1} b. */
 static void vcycle(amg *h, int l, const double *b, double *x) {
     amg_level *L = &h->L[l];
@@ -511,6 +607,9 @@ typedef struct {
     double *W;         /* [n, b, b] row weights (identity if none was given) */
     csr App, ApT, ATp, St;
     amg hp, hT;
+    csr A00;           /* uAMG: A_00 in unknown-wise order [p; T] */
+    amg hU;
+    double *b00, *x00;
     ilu0 ilu;
     int32_t *cperm;    /* multicolour ILU: new cell index -> original cell (NULL: natural) */
     csr Aperm;         /* A' with cells permuted (multicolour ILU only) */
@@ -657,6 +756,61 @@ static void permute_cells(const csr *A, int32_t b, const int32_t *order, csr *P)
 }
 
 /* z = (LU)^{-1} r for the factors of the (possibly cell-permuted) matrix */
+/* A_00 = [A_pp A_pT; A_Tp A_TT] in unknown-wise order (Sec. 3.2 eq. A00): row i < n holds A_pp row
+ * i (columns j) then A_pT row i (columns n + j); row n + i holds A_Tp row i then A_TT row i. */
+static void assemble_a00(const csr *App, const csr *ApT, const csr *ATp, const csr *ATT, csr *A) {
+    int32_t n = App->n;
+    csr_alloc(A, 2 * n, App->nnz + ApT->nnz + ATp->nnz + ATT->nnz);
+    int32_t o = 0;
+    const csr *row_blocks[2][2] = {{App, ApT}, {ATp, ATT}};
+    for (int u = 0; u < 2; ++u)
+        for (int32_t i = 0; i < n; ++i) {
+            for (int w = 0; w < 2; ++w) {
+                const csr *F = row_blocks[u][w];
+                for (int32_t k = F->rp[i]; k < F->rp[i + 1]; ++k) {
+                    A->ci[o] = F->ci[k] + (w ? n : 0);
+                    A->v[o] = F->v[k];
+                    ++o;
+                }
+            }
+            A->rp[u * n + i + 1] = o;
+        }
+}
+
+/* S~_diag = A_TT - A_Tp diag(A_pp)^{-1} A_pT (Sec. 3.3.1): the product column-scales A_Tp by
+ * 1 / (A_pp)_kk, then multiplies by A_pT (each entry summed over k ascending); the difference is
+ * taken on the union pattern, columns ascending. */
+static void schur_diag(const or_ctx *c, const int32_t *rp, const int32_t *ci, csr *S) {
+    int32_t n = c->n;
+    csr ATT, B, C;
+    extract_field(c, rp, ci, c->ts, c->ts, &ATT);
+    csr_copy(&c->ATp, &B);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = B.rp[i]; k < B.rp[i + 1]; ++k) {
+            int32_t j = B.ci[k];
+            double d = 0.0;
+            for (int32_t q = c->App.rp[j]; q < c->App.rp[j + 1]; ++q)
+                if (c->App.ci[q] == j) d = c->App.v[q];
+            B.v[k] = B.v[k] * (1.0 / d);
+        }
+    spgemm(&B, &c->ApT, n, &C);
+    csr_alloc(S, n, ATT.nnz + C.nnz);
+    int32_t o = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t a = ATT.rp[i], ae = ATT.rp[i + 1], b = C.rp[i], be = C.rp[i + 1];
+        while (a < ae || b < be) {
+            int32_t ja = a < ae ? ATT.ci[a] : INT32_MAX, jb = b < be ? C.ci[b] : INT32_MAX;
+            if (ja == jb) { S->ci[o] = ja; S->v[o] = ATT.v[a] - C.v[b]; ++a; ++b; }
+            else if (ja < jb) { S->ci[o] = ja; S->v[o] = ATT.v[a]; ++a; }
+            else { S->ci[o] = jb; S->v[o] = -C.v[b]; ++b; }
+            ++o;
+        }
+        S->rp[i + 1] = o;
+    }
+    S->nnz = o;
+    csr_free(&ATT); csr_free(&B); csr_free(&C);
+}
+
 static void ilu_apply_ordered(or_ctx *c, const double *r, double *z) {
     if (!c->cperm) { ilu0_solve(&c->ilu, r, z); return; }
     int32_t b = c->b;
@@ -687,12 +841,22 @@ or_ctx *or_create(int32_t n, int32_t b, const int32_t *rp, const int32_t *ci, co
         memcpy(c->St.rp, st_rp, sizeof(int32_t) * ((size_t)n + 1));
         memcpy(c->St.ci, st_ci, sizeof(int32_t) * (size_t)st_rp[n]);
         memcpy(c->St.v, st_v, sizeof(double) * (size_t)st_rp[n]);
+    } else if (o->schur == OR_SCHUR_DIAG) {
+        schur_diag(c, rp, ci, &c->St);             /* S~_diag (Sec. 3.3.1) */
     } else {
         extract_field(c, rp, ci, ts, ts, &c->St); /* S~_{A_TT} = A_TT (Sec. 3.3.1) */
     }
     int rc = 0;
-    if (o->stage1 != OR_NONE1) rc = amg_setup(&c->hp, &c->App, o);
-    if (!rc && o->stage1 != OR_NONE1 && o->stage1 != OR_CPR) rc = amg_setup(&c->hT, &c->St, o);
+    if (o->stage1 == OR_UAMG) {
+        csr ATT;
+        extract_field(c, rp, ci, ts, ts, &ATT);
+        assemble_a00(&c->App, &c->ApT, &c->ATp, &ATT, &c->A00);
+        csr_free(&ATT);
+        rc = uamg_setup(&c->hU, &c->A00, n, o);
+    } else {
+        if (o->stage1 != OR_NONE1) rc = amg_setup(&c->hp, &c->App, o);
+        if (!rc && o->stage1 != OR_NONE1 && o->stage1 != OR_CPR) rc = amg_setup(&c->hT, &c->St, o);
+    }
     if (!rc && o->stage2 == OR_ILU0) {
         if (o->ilu_order == 1) {
             c->cperm = multicolour_order(n, rp, ci);
@@ -707,6 +871,7 @@ or_ctx *or_create(int32_t n, int32_t b, const int32_t *rp, const int32_t *ci, co
     if (!rc && o->precision == 1) {
         round_hierarchy(&c->hp);
         round_hierarchy(&c->hT);
+        round_hierarchy(&c->hU);
         round_array(c->ApT.v, c->ApT.nnz, 0);
         round_array(c->ATp.v, c->ATp.nnz, 0);
         csr_copy(&c->A, &c->Alow);            /* A' for the stage-1 residual, FP32 values */
@@ -718,6 +883,7 @@ or_ctx *or_create(int32_t n, int32_t b, const int32_t *rp, const int32_t *ci, co
     c->xp = calloc(n, sizeof(double)); c->dT = calloc(n, sizeof(double));
     c->dp = calloc(n, sizeof(double)); c->t1 = calloc(n, sizeof(double));
     c->x1 = calloc(nb, sizeof(double)); c->b1 = calloc(nb, sizeof(double));
+    c->b00 = calloc(2 * (size_t)n, sizeof(double)); c->x00 = calloc(2 * (size_t)n, sizeof(double));
     return c;
 }
 
@@ -726,7 +892,7 @@ int or_status(const or_ctx *c) { return c->status; }
 void or_destroy(or_ctx *c) {
     if (!c) return;
     csr_free(&c->A); csr_free(&c->App); csr_free(&c->ApT); csr_free(&c->ATp); csr_free(&c->St);
-    amg_free(&c->hp); amg_free(&c->hT);
+    amg_free(&c->hp); amg_free(&c->hT); amg_free(&c->hU); csr_free(&c->A00); free(c->b00); free(c->x00);
     csr_free(&c->ilu.LU); free(c->ilu.diag);
     free(c->cperm); csr_free(&c->Aperm); free(c->rp_tmp); free(c->zp_tmp); csr_free(&c->Alow);
     free(c->W); free(c->bp); free(c->bT); free(c->xp); free(c->dT); free(c->dp); free(c->t1);
@@ -769,6 +935,13 @@ static void stage1(or_ctx *c, const double *v, double *x1) {
     case OR_CPR: /* Sec. 3.1: pressure only */
         vcycle(&c->hp, 0, c->bp, c->dp);
         memset(c->dT, 0, sizeof(double) * (size_t)n);
+        break;
+    case OR_UAMG: /* Sec. 3.4: one unknown-based V-cycle on A_00 [d_p; d_T] = [b_p; b_T] */
+        memcpy(c->b00, c->bp, sizeof(double) * (size_t)n);
+        memcpy(c->b00 + n, c->bT, sizeof(double) * (size_t)n);
+        vcycle(&c->hU, 0, c->b00, c->x00);
+        memcpy(c->dp, c->x00, sizeof(double) * (size_t)n);
+        memcpy(c->dT, c->x00 + n, sizeof(double) * (size_t)n);
         break;
     }
     for (int32_t i = 0; i < n; ++i) {
@@ -947,7 +1120,7 @@ int or_solve_block(or_ctx *c, int32_t cell0, int32_t ncell, const double *rhs, d
 
 /* ------------------------------------------------------------------------------------------ */
 /* accessors for tests                                                                          */
-static amg *pick(or_ctx *c, int which) { return which == 0 ? &c->hp : &c->hT; }
+static amg *pick(or_ctx *c, int which) { return which == 0 ? &c->hp : which == 1 ? &c->hT : &c->hU; }
 int or_nlevels(or_ctx *c, int which) { return pick(c, which)->nlev; }
 /* info = {n, nnz, nnzP, nc, dense} */
 void or_hier_level_info(amg *h, int l, int32_t *info) {
@@ -1001,6 +1174,17 @@ amg *or_amg_create(int32_t n, const int32_t *rp, const int32_t *ci, const double
     A.n = n; A.nnz = rp[n];
     A.rp = (int32_t *)rp; A.ci = (int32_t *)ci; A.v = (double *)v;
     *status = amg_setup(h, &A, o);
+    return h;
+}
+/* Standalone unknown-based AMG on a scalar CSR matrix in unknown-wise order (first np rows: the
+ * first unknown). */
+amg *or_uamg_create(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, int32_t np, const or_opts *o,
+                    int *status) {
+    amg *h = (amg *)calloc(1, sizeof(amg));
+    csr A;
+    A.n = n; A.nnz = rp[n];
+    A.rp = (int32_t *)rp; A.ci = (int32_t *)ci; A.v = (double *)v;
+    *status = uamg_setup(h, &A, np, o);
     return h;
 }
 void or_amg_destroy(amg *h) { if (h) { amg_free(h); free(h); } }

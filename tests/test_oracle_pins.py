@@ -748,3 +748,128 @@ def test_paired_levels_equal_oracle_ilu_on_a_grid():
     _, z = _paired_solves(n, b, pattern, F, r)
     zo = o.ilu_apply(r.reshape(-1))
     assert np.linalg.norm(zo - z.reshape(-1)) <= 1e-10 * np.linalg.norm(zo)
+
+
+# ------------------------------------------------------------------------------------------------
+# unknown-based AMG for A_00 (Sec. 3.4) and S~_diag (Sec. 3.3.1)
+def _csr_from_dense(M):
+    rp, ci, v = [0], [], []
+    for i in range(M.shape[0]):
+        nz = np.nonzero(M[i])[0]
+        ci.extend(nz.tolist())
+        v.extend(M[i, nz].tolist())
+        rp.append(len(ci))
+    return np.array(rp, np.int32), np.array(ci, np.int32), np.array(v)
+
+
+def _random_mmatrix(nx, ny, nz, seed):
+    """A 7-point M-matrix with seeded face weights and a small positive shift (not symmetric)."""
+    rp, ci, v = poisson3d(nx, ny, nz)
+    n = nx * ny * nz
+    A = dense_csr(rp, ci, v, n)
+    w = 0.5 + synth.uniform(seed, n * n).reshape(n, n)
+    off = (A < 0) * w * A
+    return off + np.diag(-off.sum(axis=1) + 0.05 + 0.1 * synth.uniform(seed + 1, n))
+
+
+def test_uamg_of_a_decoupled_system_is_two_scalar_amgs():
+    """With no coupling between the unknowns, unknown-based AMG is classical AMG on each diagonal
+    block: hierarchy, V-cycle and all, exactly (Sec. 3.4)."""
+    A1, A2 = _random_mmatrix(7, 6, 4, 31), _random_mmatrix(6, 5, 5, 32)
+    n1, n2 = A1.shape[0], A2.shape[0]
+    A = np.zeros((n1 + n2, n1 + n2))
+    A[:n1, :n1], A[n1:, n1:] = A1, A2
+    opts = dict(n_coarse=1, max_levels=3)
+    hu = oracle.AMG(*_csr_from_dense(A), np_first=n1, **opts)
+    h1, h2 = oracle.AMG(*_csr_from_dense(A1), **opts), oracle.AMG(*_csr_from_dense(A2), **opts)
+    lu, l1, l2 = hu.levels(), h1.levels(), h2.levels()
+    assert len(lu) == len(l1) == len(l2) == 3
+    for a, p, t in zip(lu, l1, l2):
+        Ad = dense_csr(a["rp"], a["ci"], a["v"], a["n"])
+        np1 = p["n"]
+        assert np.array_equal(Ad[:np1, :np1], dense_csr(p["rp"], p["ci"], p["v"], p["n"]))
+        assert np.array_equal(Ad[np1:, np1:], dense_csr(t["rp"], t["ci"], t["v"], t["n"]))
+        assert not Ad[:np1, np1:].any() and not Ad[np1:, :np1].any()
+    b = synth.normal(33, n1 + n2)
+    x = hu.vcycle(b)
+    assert np.array_equal(x[:n1], h1.vcycle(b[:n1])) and np.array_equal(x[n1:], h2.vcycle(b[n1:]))
+
+
+def test_uamg_hierarchy_of_a_coupled_a00():
+    """On the coupled A_00 of a thermal Jacobian: P is block diagonal (no interpolation across
+    unknowns), each block is classical direct interpolation of that unknown's diagonal block, the
+    coarse pressure points come first, and the coarse operator is the whole Galerkin product
+    P^T A_00 P (the coupling blocks stay in the coarse-grid correction)."""
+    s = synth.make_box(8, 7, 3, 3.125, seed=21).system()
+    o = oracle.Oracle.from_system(s, stage1=oracle.UAMG, n_coarse=20)
+    levels = o.levels(2)
+    assert len(levels) >= 3
+    n = s["n"]
+    App, ApT, ATp, ATT = pt_blocks(o.dense(), s["b"])
+    A00 = np.block([[App, ApT], [ATp, ATT]])
+    lev0 = levels[0]
+    assert np.array_equal(dense_csr(lev0["rp"], lev0["ci"], lev0["v"], 2 * n), A00)
+    np_l = n
+    for l in range(len(levels) - 1):
+        f, c = levels[l], levels[l + 1]
+        A = dense_csr(f["rp"], f["ci"], f["v"], f["n"])
+        P = dense_csr(f["Prp"], f["Pci"], f["Pv"], f["n"], f["nc"])
+        ncp = int((f["cf"][:np_l] == 1).sum())
+        assert not P[:np_l, ncp:].any() and not P[np_l:, :ncp].any()
+        for blk, (r0, r1, c0, c1) in enumerate(((0, np_l, 0, ncp), (np_l, f["n"], ncp, f["nc"]))):
+            sub = oracle.AMG(*_csr_from_dense(A[r0:r1, r0:r1]), n_coarse=1, max_levels=2, seed=l).levels()[0]
+            assert np.array_equal(f["cf"][r0:r1], sub["cf"])
+            assert np.array_equal(P[r0:r1, c0:c1], dense_csr(sub["Prp"], sub["Pci"], sub["Pv"], r1 - r0, c1 - c0))
+        Ac = dense_csr(c["rp"], c["ci"], c["v"], c["n"])
+        ref = P.T @ A @ P
+        assert np.abs(Ac - ref).max() <= 1e-13 * np.abs(ref).max()
+        assert np.abs(Ac[:ncp, ncp:]).max() > 0.0       # coupling kept on the coarse level
+        np_l = ncp
+
+
+def test_uamg_single_level_is_exact_a00_inverse():
+    s = tiny().system()
+    o = oracle.Oracle.from_system(s, stage1=oracle.UAMG, max_levels=1, dense_max=4096)
+    n, b = s["n"], s["b"]
+    App, ApT, ATp, ATT = pt_blocks(o.dense(), b)
+    A00 = np.block([[App, ApT], [ATp, ATT]])
+    v = synth.normal(34, n * b)
+    x1 = o.stage1(v).reshape(n, b)
+    vv = v.reshape(n, b)
+    want = np.linalg.solve(A00, np.concatenate([vv[:, 0], vv[:, 1]]))
+    assert np.linalg.norm(np.concatenate([x1[:, 0], x1[:, 1]]) - want) <= 1e-10 * np.linalg.norm(want)
+    assert not x1[:, 2:].any()
+
+
+def test_cptr_uamg_solve_matches_dense_solve():
+    s = synth.make_box(8, 7, 3, 3.125, seed=21).system()
+    o = oracle.Oracle.from_system(s, stage1=oracle.UAMG, n_coarse=20)
+    x, info = o.solve(s["rhs"], 1e-10)
+    assert info["converged"]
+    Ad = bsr_dense(s)
+    ref = np.linalg.solve(Ad, s["rhs"].reshape(-1))
+    assert np.linalg.norm(x - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_schur_diag_is_the_schur_complement_with_a_diagonal_pressure_block():
+    """S~_diag = A_TT - A_Tp diag(A_pp)^{-1} A_pT (Sec. 3.3.1) is the Schur complement of
+    [[diag(A_pp), A_pT], [A_Tp, A_TT]]: its inverse is the T-T block of that matrix's inverse."""
+    s = tiny().system()
+    o = oracle.Oracle.from_system(s, schur=oracle.SCHUR_DIAG, max_levels=1, dense_max=4096)
+    n = s["n"]
+    App, ApT, ATp, ATT = pt_blocks(o.dense(), s["b"])
+    M = np.block([[np.diag(np.diag(App)), ApT], [ATp, ATT]])
+    want = np.linalg.inv(np.linalg.inv(M)[n:, n:])
+    lev = o.levels(1)[0]
+    got = dense_csr(lev["rp"], lev["ci"], lev["v"], n)
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+    # its pattern is that of A_TT joined with the pressure couplings two cells away
+    assert lev["rp"][-1] > s["row_ptr"][-1]
+
+
+def test_schur_diag_is_exact_for_one_cell():
+    s = synth.make_box(1, 1, 1, 3.125, seed=5, wells="none").system()
+    o = oracle.Oracle.from_system(s, schur=oracle.SCHUR_DIAG, max_levels=1)
+    App, ApT, ATp, ATT = pt_blocks(o.dense(), s["b"])
+    lev = o.levels(1)[0]
+    assert abs(lev["v"][0] - (ATT - ATp @ np.linalg.solve(App, ApT))[0, 0]) <= 1e-14 * abs(lev["v"][0])
