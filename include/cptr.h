@@ -46,16 +46,22 @@ typedef enum {
     CPTR_ESTATE = -7        /* call out of order (e.g. solve before setup) */
 } cptr_status;
 
-/* first stage M1 (Sec. 3.1, 3.3): full block factorisation, its block-triangular variants
- * (one factor of eq. (Aschur) dropped), block diagonal, CPR pressure-only, or none */
+/* first stage M1 (Sec. 3.1, 3.3, 3.4): full block factorisation, its block-triangular variants
+ * (one factor of eq. (Aschur) dropped), block diagonal, CPR pressure-only, none, or one V-cycle of
+ * unknown-based AMG on A_00 (Sec. 3.4: classical coarsening and direct interpolation of the A_pp
+ * and A_TT diagonal blocks on their own, with PMIS weights indexed within each block; the Galerkin
+ * product and the smoother on the whole coupled A_00 in unknown-wise order [p; T], so the coupling
+ * blocks stay in the coarse-grid correction; the Schur approximation is not used) */
 enum { CPTR_STAGE1_FULL = 0, CPTR_STAGE1_UPPER = 1, CPTR_STAGE1_LOWER = 2, CPTR_STAGE1_BD = 3,
-       CPTR_STAGE1_CPR = 4, CPTR_STAGE1_NONE = 5 };
+       CPTR_STAGE1_CPR = 4, CPTR_STAGE1_NONE = 5, CPTR_STAGE1_UAMG = 6 };
 /* second stage M2: ILU(0) on the full system (Sec. 4) or none */
 enum { CPTR_STAGE2_ILU0 = 0, CPTR_STAGE2_NONE = 1 };
-/* Schur approximation: the caller's S~_T (eq. Se) or A_TT (Sec. 3.3.1), or the learned
- * diagonal scaling diag(s) B of B = the caller's S~_T, else A_TT (see cptr_set_mlp; not in the
- * paper) */
-enum { CPTR_SCHUR_GIVEN = 0, CPTR_SCHUR_ATT = 1, CPTR_SCHUR_LEARNED = 2 };
+/* Schur approximation: the caller's S~_T (eq. Se) or A_TT (Sec. 3.3.1), the learned diagonal
+ * scaling diag(s) B of B = the caller's S~_T, else A_TT (see cptr_set_mlp; not in the paper), or
+ * S~_diag = A_TT - A_Tp diag(A_pp)^{-1} A_pT (Sec. 3.3.1), formed on the device on its own pattern
+ * (A_TT's joined with that of the product): the product column-scales A_Tp by 1 / (A_pp)_kk and
+ * sums every entry over k ascending with separately rounded products and sums */
+enum { CPTR_SCHUR_GIVEN = 0, CPTR_SCHUR_ATT = 1, CPTR_SCHUR_LEARNED = 2, CPTR_SCHUR_DIAG = 3 };
 /* AMG smoother: l1-Jacobi (d_i = sum_j |a_ij|) or omega-Jacobi (d_i = a_ii / omega) */
 enum { CPTR_SMOOTH_L1 = 0, CPTR_SMOOTH_JACOBI = 1 };
 /* precision of the preconditioner: all FP64, or FP32 AMG/ILU with BF16 coarse AMG levels */
@@ -180,7 +186,9 @@ cptr_status cptr_apply_ilu(cptr_ctx *ctx, const double *r, double *z);
 /* z = M^{-1} v, the full two-stage preconditioner. */
 cptr_status cptr_apply_precond(cptr_ctx *ctx, const double *v, double *z);
 
-/* x = one V(1,1)-cycle from zero on hierarchy `which` (0: A_pp, 1: S~_T); b, x of length n_cells. */
+/* x = one V(1,1)-cycle from zero on hierarchy `which` (0: A_pp, 1: S~_T); b, x of length n_cells.
+ * With CPTR_STAGE1_UAMG, hierarchy 0 is the unknown-based one of A_00 and b, x have length 2 n_cells
+ * ([p; T], unknown-wise). */
 cptr_status cptr_apply_vcycle(cptr_ctx *ctx, int32_t which, const double *b, double *x);
 
 /* Hierarchy shape: *nlev levels; for level l, info[l*4 + {0,1,2,3}] = {n, nnz, nnzP, dense}

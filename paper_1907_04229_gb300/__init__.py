@@ -18,9 +18,9 @@ LIB_PATH = _build.LIB
 CPTR_OK, CPTR_NOT_CONVERGED = 0, 1
 STATUS = {0: "CPTR_OK", 1: "CPTR_NOT_CONVERGED", -1: "CPTR_EINVAL", -2: "CPTR_ENOMEM", -3: "CPTR_ECUDA",
           -4: "CPTR_EBREAKDOWN", -5: "CPTR_ETIMEOUT", -6: "CPTR_ESINGULAR", -7: "CPTR_ESTATE"}
-STAGE1 = {"full": 0, "upper": 1, "lower": 2, "bd": 3, "cpr": 4, "none": 5}
+STAGE1 = {"full": 0, "upper": 1, "lower": 2, "bd": 3, "cpr": 4, "none": 5, "uamg": 6}
 STAGE2 = {"ilu0": 0, "none": 1}
-SCHUR = {"given": 0, "att": 1, "learned": 2}
+SCHUR = {"given": 0, "att": 1, "learned": 2, "diag": 3}
 SCHUR_NAMES = {v: k for k, v in SCHUR.items()}
 MLP_FEATURES, MLP_HIDDEN, MLP_NPARAM = 16, 64, 5313
 SMOOTHER = {"l1": 0, "jacobi": 1}

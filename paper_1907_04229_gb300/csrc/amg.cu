@@ -33,13 +33,16 @@ __global__ void k_dinv(int32_t n, const int32_t *rp, const int32_t *ci, const do
 }
 
 // ------------------------------------------------------------------------------------------------
-// strength: j != i strong iff -a_ij >= theta * max_{k != i}(-a_ik) > 0
+// strength: j != i strong iff -a_ij >= theta * max_{k != i}(-a_ik) > 0.  With an unknown id per
+// row (fn, unknown-based AMG of Sec. 3.4), only entries between rows of the same unknown count: the
+// classical definitions applied to each diagonal block of a matrix in unknown-wise order.
+__device__ __forceinline__ bool same_unknown(const int32_t *fn, int32_t i, int32_t j) { return !fn || fn[i] == fn[j]; }
 __device__ __forceinline__ bool row_threshold(const int32_t *rp, const int32_t *ci, const double *v, int32_t i,
-                                              double theta, double *thr) {
+                                              double theta, double *thr, const int32_t *fn) {
     double m = 0.0;
     bool have = false;
     for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
-        if (ci[k] == i) continue;
+        if (ci[k] == i || !same_unknown(fn, i, ci[k])) continue;
         double t = -v[k];
         if (!have || t > m) { m = t; have = true; }
     }
@@ -48,25 +51,25 @@ __device__ __forceinline__ bool row_threshold(const int32_t *rp, const int32_t *
 }
 
 __global__ void k_strength_count(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, double theta,
-                                 int32_t *cnt) {
+                                 int32_t *cnt, const int32_t *fn) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double thr;
     int32_t c = 0;
-    if (row_threshold(rp, ci, v, i, theta, &thr))
-        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) c += (ci[k] != i && -v[k] >= thr);
+    if (row_threshold(rp, ci, v, i, theta, &thr, fn))
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) c += (ci[k] != i && same_unknown(fn, i, ci[k]) && -v[k] >= thr);
     cnt[i] = c;
 }
 
 __global__ void k_strength_fill(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, double theta,
-                                const int32_t *Srp, int32_t *Sci, int32_t *Spos) {
+                                const int32_t *Srp, int32_t *Sci, int32_t *Spos, const int32_t *fn) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double thr;
     int32_t o = Srp[i];
-    if (row_threshold(rp, ci, v, i, theta, &thr))
+    if (row_threshold(rp, ci, v, i, theta, &thr, fn))
         for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
-            if (ci[k] != i && -v[k] >= thr) { Sci[o] = ci[k]; Spos[o] = k; ++o; }
+            if (ci[k] != i && same_unknown(fn, i, ci[k]) && -v[k] >= thr) { Sci[o] = ci[k]; Spos[o] = k; ++o; }
 }
 
 // pattern transpose helpers
@@ -116,12 +119,15 @@ __device__ __forceinline__ bool beats(uint64_t ki, int32_t i, uint64_t kj, int32
     return ki > kj || (ki == kj && i > j);
 }
 
+// PMIS weights are drawn by the row's index within its unknown (rows [np, n) of the second unknown
+// start again at 0), so that each diagonal block is coarsened as it would be on its own
 __global__ void k_pmis_init(int32_t n, const int32_t *Srp, const int32_t *Trp, uint64_t seed, uint64_t *key,
-                            int32_t *state) {
+                            int32_t *state, const int32_t *fn, int32_t np) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint64_t deg = (uint64_t)(Trp[i + 1] - Trp[i]);
-    key[i] = (deg << 32) | (splitmix64_at(seed, (uint64_t)i) >> 32);
+    const int32_t li = (fn && fn[i]) ? i - np : i;
+    key[i] = (deg << 32) | (splitmix64_at(seed, (uint64_t)li) >> 32);
     bool isolated = (Srp[i + 1] == Srp[i]) && (Trp[i + 1] == Trp[i]);
     state[i] = isolated ? 2 : 0;
 }
@@ -179,7 +185,7 @@ __global__ void k_interp_count(int32_t n, const int32_t *Srp, const int32_t *Sci
 
 __global__ void k_interp_fill(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, const int32_t *Srp,
                               const int32_t *Sci, const int32_t *Spos, const int32_t *state, const int32_t *cidx,
-                              const int32_t *Prp, int32_t *Pci, double *Pv) {
+                              const int32_t *Prp, int32_t *Pci, double *Pv, const int32_t *fn) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t o = Prp[i];
@@ -188,6 +194,7 @@ __global__ void k_interp_fill(int32_t n, const int32_t *rp, const int32_t *ci, c
     double aii = 0.0, sneg = 0.0, spos = 0.0, sc = 0.0;
     for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
         int32_t j = ci[k];
+        if (!same_unknown(fn, i, j)) continue;
         double a = v[k];
         if (j == i) aii = __dadd_rn(aii, a);
         else if (a < 0.0) sneg = __dadd_rn(sneg, a);
@@ -519,8 +526,15 @@ static cptr_status alloc_level_vectors(Ctx *c, Level &L) {
     return CPTR_OK;
 }
 
+__global__ void k_coarse_fn(int32_t n, const int32_t *state, const int32_t *cidx, const int32_t *fn, int32_t *fn_c) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && state[i] == 1) fn_c[cidx[i]] = fn[i];
+}
+
 // Coarsen level L into P (n x nc) with PMIS + direct interpolation.  *nc_out = 0 if no C points.
-static cptr_status coarsen(Ctx *c, Level &L, int lev, int32_t *nc_out) {
+// With unknown ids (L.fn), each unknown's diagonal block is coarsened on its own; *fn_c and *np_c
+// receive the coarse level's unknown ids and its number of first-unknown rows.
+static cptr_status coarsen(Ctx *c, Level &L, int lev, int32_t *nc_out, int32_t **fn_c, int32_t *np_c) {
     const Csr &A = L.A;
     int32_t n = A.n;
     cudaStream_t s = c->stream;
@@ -530,12 +544,12 @@ static cptr_status coarsen(Ctx *c, Level &L, int lev, int32_t *nc_out) {
     uint8_t *newc = nullptr;
     CPTR_TRY(dalloc_t(c, &cnt, (size_t)n + 1));
     CPTR_TRY(dalloc_t(c, &Srp, (size_t)n + 1));
-    (k_strength_count<<<nblk(n, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, c->o.theta, cnt), note_launch());
+    (k_strength_count<<<nblk(n, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, c->o.theta, cnt, L.fn), note_launch());
     int32_t nnzS = 0;
     CPTR_TRY(scan_exclusive(c, cnt, Srp, n, &nnzS));
     CPTR_TRY(dalloc_t(c, &Sci, (size_t)nnzS));
     CPTR_TRY(dalloc_t(c, &Spos, (size_t)nnzS));
-    (k_strength_fill<<<nblk(n, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, c->o.theta, Srp, Sci, Spos), note_launch());
+    (k_strength_fill<<<nblk(n, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, c->o.theta, Srp, Sci, Spos, L.fn), note_launch());
     // S^T pattern (neighbour sets; order irrelevant)
     CPTR_TRY(dalloc_t(c, &Trp, (size_t)n + 1));
     CPTR_TRY(dalloc_t(c, &Tci, (size_t)nnzS));
@@ -549,7 +563,8 @@ static cptr_status coarsen(Ctx *c, Level &L, int lev, int32_t *nc_out) {
     CPTR_TRY(dalloc_t(c, &state, (size_t)n));
     CPTR_TRY(dalloc_t(c, &newc, (size_t)n));
     CPTR_TRY(dalloc_t(c, &und, 1));
-    (k_pmis_init<<<nblk(n, 256), 256, 0, s>>>(n, Srp, Trp, (uint64_t)(int64_t)c->o.seed + (uint64_t)lev, key, state), note_launch());
+    (k_pmis_init<<<nblk(n, 256), 256, 0, s>>>(n, Srp, Trp, (uint64_t)(int64_t)c->o.seed + (uint64_t)lev, key, state,
+                                              L.fn, L.np), note_launch());
     // rounds are launched three at a time between host checks of the undecided count (a round
     // after the last undecided point is decided changes nothing)
     int rounds = 0;
@@ -584,15 +599,22 @@ static cptr_status coarsen(Ctx *c, Level &L, int lev, int32_t *nc_out) {
         CPTR_TRY(dalloc_t(c, &L.P.ci, (size_t)nnzP));
         CPTR_TRY(dalloc_t(c, &L.P.v, (size_t)nnzP));
         (k_interp_fill<<<nblk(n, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, Srp, Sci, Spos, L.cf, cidx, L.P.rp, L.P.ci,
-                                                   L.P.v), note_launch());
+                                                   L.P.v, L.fn), note_launch());
         CPTR_CUDA_TRY(c, cudaGetLastError());
+        if (L.fn) {   // unknown ids of the coarse points (C points keep their order: pressure first)
+            CPTR_TRY(dalloc_t(c, fn_c, (size_t)nc));
+            (k_coarse_fn<<<nblk(n, 256), 256, 0, s>>>(n, L.cf, cidx, L.fn, *fn_c), note_launch());
+            *np_c = nc;
+            if (L.np < n) CPTR_TRY(copy_to_host(c, np_c, cidx + L.np, sizeof(int32_t)));
+        }
     }
     dfree(cnt); dfree(Srp); dfree(Sci); dfree(Spos); dfree(Trp); dfree(Tci);
     dfree(key); dfree(newc); dfree(und); dfree(cidx);
     return CPTR_OK;
 }
 
-cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, const double *v, int32_t n) {
+cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, const double *v, int32_t n,
+                      const int32_t *fn0, int32_t np0) {
     amg_free(h);
     int32_t nnz = 0;
     CPTR_TRY(copy_to_host(c, &nnz, rp + n, sizeof(int32_t)));
@@ -605,6 +627,11 @@ cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, con
     CPTR_CUDA_TRY(c, cudaMemcpyAsync(A0.rp, rp, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, c->stream));
     CPTR_CUDA_TRY(c, cudaMemcpyAsync(A0.ci, ci, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToDevice, c->stream));
     CPTR_CUDA_TRY(c, cudaMemcpyAsync(A0.v, v, sizeof(double) * (size_t)nnz, cudaMemcpyDeviceToDevice, c->stream));
+    if (fn0) {   // unknown-based AMG: the unknown of every row, first-unknown rows first
+        CPTR_TRY(dalloc_t(c, &h.L[0].fn, (size_t)n));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(h.L[0].fn, fn0, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
+        h.L[0].np = np0;
+    }
     int maxl = c->o.max_levels < 1 ? 1 : (c->o.max_levels > kMaxLevels ? kMaxLevels : c->o.max_levels);
     int l = 0;
     double nnz_sum = 0.0;
@@ -613,16 +640,20 @@ cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, con
         CPTR_TRY(alloc_level_vectors(c, L));
         nnz_sum += L.A.nnz;
         if (l + 1 >= maxl || L.A.n <= c->o.n_coarse) break;
-        int32_t nc = 0;
+        int32_t nc = 0, np_c = 0;
+        int32_t *fn_c = nullptr;
         double t0 = host_ms();
-        CPTR_TRY(coarsen(c, L, l, &nc));
+        CPTR_TRY(coarsen(c, L, l, &nc, &fn_c, &np_c));
         setup_tick(c, SETUP_COARSEN, &t0);
         if (nc == 0 || nc >= L.A.n) {   // no coarsening possible: this level is the coarsest
             csr_free(L.P);
             dfree(L.cf);
+            dfree(fn_c);
             L.cf = nullptr;
             break;
         }
+        h.L[l + 1].fn = fn_c;
+        h.L[l + 1].np = np_c;
         L.nc = nc;
         CPTR_TRY(transpose(c, L.P, nc, L.PT));
         Csr AP;
@@ -682,6 +713,111 @@ cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, con
     return CPTR_OK;
 }
 
+// ------------------------------------------------------------------------------------------------
+// A_00 = [A_pp A_pT; A_Tp A_TT] in unknown-wise order (Sec. 3.2 eq. A00) from the cell-pattern
+// fields: row i < n holds A_pp row i (columns j) then A_pT row i (columns n + j); row n + i holds
+// A_Tp row i then A_TT row i.  fn: 0 on the first n rows, 1 on the others.
+__global__ void k_build_a00(int32_t n, int32_t nnzb, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const double *__restrict__ App, const double *__restrict__ ApT,
+                            const double *__restrict__ ATp, const double *__restrict__ ATT, int32_t *rp0,
+                            int32_t *ci0, double *v0, int32_t *fn) {
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= 2 * n) return;
+    const int u = r >= n, i = u ? r - n : r;
+    const int32_t a = rp[i], len = rp[i + 1] - a;
+    const int32_t o = 2 * (u ? nnzb + a : a);
+    rp0[r] = o;
+    if (r == 2 * n - 1) rp0[2 * n] = 4 * nnzb;
+    fn[r] = u;
+    const double *L = u ? ATp : App, *R = u ? ATT : ApT;
+    for (int32_t k = 0; k < len; ++k) {
+        ci0[o + k] = ci[a + k];
+        v0[o + k] = L[a + k];
+        ci0[o + len + k] = n + ci[a + k];
+        v0[o + len + k] = R[a + k];
+    }
+}
+
+cptr_status build_a00(Ctx *c, Csr &A, int32_t **fn) {
+    const int32_t n = c->n, nnzb = c->nnzb;
+    double *ATT = nullptr;
+    CPTR_TRY(dalloc_t(c, &ATT, (size_t)nnzb));
+    launch_extract(c, c->ts, c->ts, ATT);
+    A.n = 2 * n;
+    A.nnz = 4 * nnzb;
+    CPTR_TRY(dalloc_t(c, &A.rp, 2 * (size_t)n + 1));
+    CPTR_TRY(dalloc_t(c, &A.ci, (size_t)A.nnz));
+    CPTR_TRY(dalloc_t(c, &A.v, (size_t)A.nnz));
+    CPTR_TRY(dalloc_t(c, fn, 2 * (size_t)n));
+    (k_build_a00<<<nblk(2 * (int64_t)n, 256), 256, 0, c->stream>>>(n, nnzb, c->rp, c->ci, c->App, c->ApT, c->ATp, ATT,
+                                                                   A.rp, A.ci, A.v, *fn), note_launch());
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    dfree(ATT);
+    return CPTR_OK;
+}
+
+// S~_diag = A_TT - A_Tp diag(A_pp)^{-1} A_pT (Sec. 3.3.1).  B = A_Tp with column k scaled by
+// 1 / (A_pp)_kk (the product a * (1 / d), each rounded), C = B A_pT by the Galerkin SpGEMM (every
+// entry summed over k ascending from 0, products and sums separately rounded), then A_TT - C on
+// the union of the two patterns, columns ascending.
+__global__ void k_scale_cols_by_diag_recip(int32_t n, const int32_t *rp, const int32_t *ci, const double *v,
+                                           const int32_t *diag, const double *App, double *out) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+        out[k] = __dmul_rn(v[k], __ddiv_rn(1.0, App[diag[ci[k]]]));
+}
+template <bool FILL>
+__global__ void k_union_sub(int32_t n, const int32_t *arp, const int32_t *aci, const double *av, const int32_t *brp,
+                            const int32_t *bci, const double *bv, int32_t *cnt_or_rp, int32_t *sci, double *sv) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t a = arp[i], ae = arp[i + 1], b = brp[i], be = brp[i + 1], o = FILL ? cnt_or_rp[i] : 0;
+    while (a < ae || b < be) {
+        const int32_t ja = a < ae ? aci[a] : INT32_MAX, jb = b < be ? bci[b] : INT32_MAX;
+        if (FILL) {
+            if (ja == jb) { sci[o] = ja; sv[o] = __dsub_rn(av[a], bv[b]); }
+            else if (ja < jb) { sci[o] = ja; sv[o] = av[a]; }
+            else { sci[o] = jb; sv[o] = -bv[b]; }
+        }
+        if (ja <= jb) ++a;
+        if (jb <= ja) ++b;
+        ++o;
+    }
+    if (!FILL) cnt_or_rp[i] = o;
+}
+
+cptr_status schur_diag(Ctx *c, Csr &S) {
+    const int32_t n = c->n, nnzb = c->nnzb;
+    cudaStream_t s = c->stream;
+    double *ATT = nullptr, *Bv = nullptr;
+    CPTR_TRY(dalloc_t(c, &ATT, (size_t)nnzb));
+    CPTR_TRY(dalloc_t(c, &Bv, (size_t)nnzb));
+    launch_extract(c, c->ts, c->ts, ATT);
+    (k_scale_cols_by_diag_recip<<<nblk(n, 256), 256, 0, s>>>(n, c->rp, c->ci, c->ATp, c->diag, c->App, Bv), note_launch());
+    Csr B{n, nnzb, c->rp, c->ci, Bv}, PT{n, nnzb, c->rp, c->ci, c->ApT}, C;
+    CPTR_TRY(spgemm(c, B, PT, n, C));
+    int32_t *cnt = nullptr;
+    CPTR_TRY(dalloc_t(c, &cnt, (size_t)n + 1));
+    (k_union_sub<false><<<nblk(n, 256), 256, 0, s>>>(n, c->rp, c->ci, ATT, C.rp, C.ci, C.v, cnt, nullptr, nullptr),
+     note_launch());
+    S.n = n;
+    CPTR_TRY(dalloc_t(c, &S.rp, (size_t)n + 1));
+    int32_t nnz = 0;
+    CPTR_TRY(scan_exclusive(c, cnt, S.rp, n, &nnz));
+    S.nnz = nnz;
+    CPTR_TRY(dalloc_t(c, &S.ci, (size_t)nnz));
+    CPTR_TRY(dalloc_t(c, &S.v, (size_t)nnz));
+    (k_union_sub<true><<<nblk(n, 256), 256, 0, s>>>(n, c->rp, c->ci, ATT, C.rp, C.ci, C.v, S.rp, S.ci, S.v),
+     note_launch());
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(s));
+    csr_free(C);
+    dfree(cnt); dfree(ATT); dfree(Bv);
+    return CPTR_OK;
+}
+
 cptr_status amg_coarsest_wait(Ctx *c, Hier &h) {
     if (!h.gj_pending) return CPTR_OK;
     double t0 = host_ms();
@@ -705,6 +841,7 @@ void amg_free(Hier &h) {
         dfree(L.dinv); dfree(L.cf); dfree(L.b); dfree(L.x); dfree(L.t); dfree(L.r);
         dfree(L.Av_lo); dfree(L.Pv_lo); dfree(L.PTv_lo);
         dfree(L.dinv32); dfree(L.b32); dfree(L.x32); dfree(L.t32); dfree(L.r32);
+        dfree(L.fn);
         L = Level{};
     }
     dfree(h.cinv);

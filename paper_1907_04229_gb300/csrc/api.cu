@@ -37,10 +37,10 @@ void release_setup(Ctx *c) {
     amg_free(c->hT);
     ilu_free(c);
     double **vecs[] = {&c->bp, &c->bT, &c->xp, &c->dp, &c->dT, &c->t1, &c->b1, &c->V, &c->Z, &c->w, &c->bw, &c->xw,
-                       &c->vcur, &c->zcur};
+                       &c->vcur, &c->zcur, &c->b00, &c->x00};
     for (double **p : vecs) { dfree(*p); *p = nullptr; }
     float **vecs32[] = {&c->ApT32, &c->ATp32, &c->sell_val32, &c->bp32, &c->bT32, &c->xp32, &c->dp32, &c->dT32,
-                        &c->t132, &c->b132};
+                        &c->t132, &c->b132, &c->b0032, &c->x0032};
     for (float **p : vecs32) { dfree(*p); *p = nullptr; }
     if (c->graph_exec) {
         cudaGraphExecDestroy(c->graph_exec);
@@ -198,7 +198,23 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
         setup_tick(c, SETUP_OTHER, &tl);
     }
     int s1 = c->o.stage1;
-    if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) {
+    // S~_diag = A_TT - A_Tp diag(A_pp)^{-1} A_pT (Sec. 3.3.1), on its own (wider) pattern
+    Csr Sd;
+    if (c->o.schur == CPTR_SCHUR_DIAG && s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR && s1 != CPTR_STAGE1_UAMG) {
+        CPTR_TRY(schur_diag(c, Sd));
+        c->schur_used = CPTR_SCHUR_DIAG;
+    }
+    if (s1 == CPTR_STAGE1_UAMG) {
+        // unknown-based AMG (Sec. 3.4) on A_00 in unknown-wise order, kept in the pressure slot
+        Csr A00;
+        int32_t *fn = nullptr;
+        CPTR_TRY(build_a00(c, A00, &fn));
+        const cptr_status su = amg_setup(c, c->hp, A00.rp, A00.ci, A00.v, 2 * n, fn, n);
+        csr_free(A00);
+        dfree(fn);
+        CPTR_TRY(su);
+        if (c->o.stage2 == CPTR_STAGE2_ILU0) CPTR_TRY(ilu_setup(c));
+    } else if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) {
         // The two hierarchies are independent: the temperature one is built by a second host
         // thread on its own stream (a context view with its own stream, scratch flag and scan
         // buffer) while this thread builds the pressure one and then the ILU(0) factors.
@@ -219,7 +235,7 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
         std::thread worker([&] {
             CtxScope ws(&w);
             try {
-                st_T = amg_setup(&w, c->hT, c->rp, c->ci, c->St, n);
+                st_T = Sd.v ? amg_setup(&w, c->hT, Sd.rp, Sd.ci, Sd.v, n) : amg_setup(&w, c->hT, c->rp, c->ci, c->St, n);
             } catch (const std::bad_alloc &) {
                 st_T = w.fail(CPTR_ENOMEM, "host allocation failed");
             } catch (...) {
@@ -239,9 +255,11 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
         } catch (...) {
             worker.join();
             dfree(w.flag);
+            csr_free(Sd);
             throw;
         }
         worker.join();
+        csr_free(Sd);
         for (int q = 0; q < kSetupPhases; ++q) c->prof.setup_ms[q] += w.prof.setup_ms[q];
         dfree(w.flag);
         if (st_p != CPTR_OK) return st_p;
@@ -259,7 +277,7 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     if (c->o.precision == CPTR_PREC_MIXED) {
         // FP32/BF16 copies of the preconditioner's operators (the FP64 set-up is rounded once)
         if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_lower_precision(c, c->hp));
-        if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) CPTR_TRY(amg_lower_precision(c, c->hT));
+        if (uses_T(s1)) CPTR_TRY(amg_lower_precision(c, c->hT));
         CPTR_TRY(to_lower(c, c->ApT, nnzb, ST_F32, (void **)&c->ApT32));
         CPTR_TRY(to_lower(c, c->ATp, nnzb, ST_F32, (void **)&c->ATp32));
         CPTR_TRY(to_lower(c, c->sell_val, c->sell_nvals, ST_F32, (void **)&c->sell_val32));
@@ -267,7 +285,7 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
         CPTR_TRY(dalloc_t(c, &c->b132, (size_t)n * b));
     }
     if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_fuse_setup(c, c->hp));
-    if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) CPTR_TRY(amg_fuse_setup(c, c->hT));
+    if (uses_T(s1)) CPTR_TRY(amg_fuse_setup(c, c->hT));
     dfree(c->A);
     c->A = nullptr;
     setup_tick(c, SETUP_LAYOUT, &t2);
@@ -275,13 +293,21 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     const size_t nb = (size_t)n * b;
     const int m = c->o.restart;
     for (double **p : {&c->bp, &c->bT, &c->xp, &c->dp, &c->dT, &c->t1}) CPTR_TRY(dalloc_t(c, p, (size_t)n));
+    if (s1 == CPTR_STAGE1_UAMG) {   // [b_p; b_T] and [d_p; d_T] of the unknown-based V-cycle
+        CPTR_TRY(dalloc_t(c, &c->b00, 2 * (size_t)n));
+        CPTR_TRY(dalloc_t(c, &c->x00, 2 * (size_t)n));
+        if (c->o.precision == CPTR_PREC_MIXED) {
+            CPTR_TRY(dalloc_t(c, &c->b0032, 2 * (size_t)n));
+            CPTR_TRY(dalloc_t(c, &c->x0032, 2 * (size_t)n));
+        }
+    }
     for (double **p : {&c->b1, &c->w, &c->bw, &c->xw, &c->vcur, &c->zcur}) CPTR_TRY(dalloc_t(c, p, nb));
     CPTR_TRY(dalloc_t(c, &c->V, nb * (m + 1)));
     CPTR_TRY(dalloc_t(c, &c->Z, nb * m));
     if (c->o.autotune) {
         double ta = host_ms();
         if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_autotune(c, c->hp));
-        if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) CPTR_TRY(amg_autotune(c, c->hT));
+        if (uses_T(s1)) CPTR_TRY(amg_autotune(c, c->hT));
         CPTR_TRY(sell_autotune(c));
         if (c->o.stage2 == CPTR_STAGE2_ILU0) {
             CPTR_TRY(clear_wait_flag(c));
@@ -401,9 +427,9 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
     if (opt) o = *opt;
     else cptr_default_options(&o);
     if (o.restart < 1 || o.restart > kMaxRestart || o.max_it < 0 || o.max_levels < 1 || o.dense_max < 1 || o.dense_max > 25600 ||
-        o.stage1 < 0 || o.stage1 > CPTR_STAGE1_NONE || o.stage2 < 0 || o.stage2 > CPTR_STAGE2_NONE ||
+        o.stage1 < 0 || o.stage1 > CPTR_STAGE1_UAMG || o.stage2 < 0 || o.stage2 > CPTR_STAGE2_NONE ||
         o.smoother < 0 || o.smoother > CPTR_SMOOTH_JACOBI || o.schur < CPTR_SCHUR_GIVEN ||
-        o.schur > CPTR_SCHUR_LEARNED || o.precision < CPTR_PREC_FP64 ||
+        o.schur > CPTR_SCHUR_DIAG || o.precision < CPTR_PREC_FP64 ||
         o.precision > CPTR_PREC_MIXED ||
         o.ilu_order < CPTR_ILU_NATURAL || o.ilu_order > CPTR_ILU_MULTICOLOR || o.ilu_sweep < 0 || o.ilu_sweep > 4 ||
         o.tile_y < 0 || o.tile_z < 0 || (size_t)o.tile_y * o.tile_z > 64)
@@ -598,12 +624,15 @@ cptr_status cptr_apply_precond(cptr_ctx *ctx, const double *v, double *z) {
 cptr_status cptr_apply_vcycle(cptr_ctx *ctx, int32_t which, const double *b, double *x) {
     return guarded(ctx, [&](Ctx *c) {
         CPTR_TRY(need_ready(c));
+        if (which < 0 || which > 1) return c->fail(CPTR_EINVAL, "no such AMG hierarchy");
         const Hier &h = which == 0 ? c->hp : c->hT;
-        if (which < 0 || which > 1 || h.nlev == 0) return c->fail(CPTR_EINVAL, "no such AMG hierarchy");
+        if (h.nlev == 0) return c->fail(CPTR_EINVAL, "no such AMG hierarchy");
         if (c->o.precision == CPTR_PREC_MIXED) {   // FP64 in and out, FP32 cycle
-            launch_d2f(c, b, c->bp32, c->n);
-            amg_vcycle32(c, h, c->bp32, c->dp32);
-            launch_f2d(c, c->dp32, x, c->n);
+            const int32_t len = h.L[0].A.n;      // n, or 2n for the unknown-based A_00 hierarchy
+            float *b32 = len > c->n ? c->b0032 : c->bp32, *x32 = len > c->n ? c->x0032 : c->dp32;
+            launch_d2f(c, b, b32, len);
+            amg_vcycle32(c, h, b32, x32);
+            launch_f2d(c, x32, x, len);
         } else {
             amg_vcycle(c, h, b, x);
         }

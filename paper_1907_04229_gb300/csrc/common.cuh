@@ -72,6 +72,10 @@ struct Level {
     void *Av_lo = nullptr, *Pv_lo = nullptr, *PTv_lo = nullptr;
     float *dinv32 = nullptr;
     float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr, *r32 = nullptr;
+    // unknown-based AMG (Sec. 3.4): the unknown of every row (0 pressure, 1 temperature; null for
+    // classical AMG) and the number of pressure rows, which come first
+    int32_t *fn = nullptr;
+    int32_t np = 0;
 };
 
 // a level as the fused coarse-level kernels see it (device array, one per hierarchy and cycle
@@ -203,12 +207,19 @@ template <typename XT> void launch_scatter_pt(const Ctx *c, const XT *dp, const 
 void launch_resid_pt32(const Ctx *c, const float *dp, const float *dT, const double *v, float *b1);
 void launch_sub(cudaStream_t s, int32_t n, const double *a, const double *b, double *out);
 
+// the stage-1 kinds that build the S~_T hierarchy (the unknown-based AMG keeps its A_00 hierarchy
+// in the pressure slot)
+inline bool uses_T(int s1) { return s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR && s1 != CPTR_STAGE1_UAMG; }
+
 // ---- amg.cu ------------------------------------------------------------------------------------
+cptr_status build_a00(Ctx *c, Csr &A00, int32_t **fn);   // A_00 in unknown-wise order, unknown ids
+cptr_status schur_diag(Ctx *c, Csr &S);                  // S~_diag = A_TT - A_Tp diag(A_pp)^{-1} A_pT
 cptr_status amg_autotune(Ctx *c, Hier &h);    // launch shapes of every level's kernels
 cptr_status amg_fuse_setup(Ctx *c, Hier &h);  // descriptors of the fused coarse levels
 cptr_status sell_autotune(Ctx *c);           // threads per block of the SELL SpMV
 cptr_status ilu_autotune(Ctx *c);            // grid and poll back-off of the ILU(0) sweeps
-cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, const double *v, int32_t n);
+cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, const double *v, int32_t n,
+                      const int32_t *fn0 = nullptr, int32_t np0 = 0);
 void amg_free(Hier &h);
 cptr_status amg_coarsest_wait(Ctx *c, Hier &h);   // join the coarse stream's inverse; its status
 void amg_vcycle(const Ctx *c, const Hier &h, const double *b, double *x);
@@ -333,6 +344,8 @@ struct Ctx {
     double *never = nullptr;                           // a word no thread writes
     // preconditioner work
     double *bp = nullptr, *bT = nullptr, *xp = nullptr, *dp = nullptr, *dT = nullptr, *t1 = nullptr;
+    double *b00 = nullptr, *x00 = nullptr;             // unknown-based AMG: [b_p; b_T], [d_p; d_T]
+    float *b0032 = nullptr, *x0032 = nullptr;
     double *b1 = nullptr;
     // mixed-precision form: FP32 copies of the stage-1 operators and the stage-1 vectors
     float *ApT32 = nullptr, *ATp32 = nullptr, *sell_val32 = nullptr;

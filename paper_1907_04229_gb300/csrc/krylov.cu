@@ -253,6 +253,13 @@ void apply_stage1(const Ctx *c, const double *v, const double **pdp, const doubl
     *pdT = nullptr;
     int mode = c->o.stage1;
     if (mode == CPTR_STAGE1_NONE) return;
+    if (mode == CPTR_STAGE1_UAMG) {   // Sec. 3.4: one unknown-based V-cycle on A_00 [d_p; d_T] = [b_p; b_T]
+        launch_gather_pt<double>(c, v, c->b00, c->b00 + c->n);
+        amg_vcycle(c, c->hp, c->b00, c->x00);
+        *pdp = c->x00;
+        *pdT = c->x00 + c->n;
+        return;
+    }
     launch_gather_pt<double>(c, v, c->bp, c->bT);
     switch (mode) {
     case CPTR_STAGE1_FULL:
@@ -299,6 +306,13 @@ void apply_stage1_32(const Ctx *c, const double *v, const float **pdp, const flo
     *pdT = nullptr;
     int mode = c->o.stage1;
     if (mode == CPTR_STAGE1_NONE) return;
+    if (mode == CPTR_STAGE1_UAMG) {
+        launch_gather_pt<float>(c, v, c->b0032, c->b0032 + n);
+        amg_vcycle32(c, c->hp, c->b0032, c->x0032);
+        *pdp = c->x0032;
+        *pdT = c->x0032 + n;
+        return;
+    }
     launch_gather_pt<float>(c, v, c->bp32, c->bT32);
     switch (mode) {
     case CPTR_STAGE1_FULL:

@@ -303,3 +303,76 @@ def test_tiled_sweeps_timeout_reported_and_context_recovers():
     assert e.value.code == -5
     cp.cptr_inject_wait_timeout(g.ctx, False)
     check_solve(s, o, g, 1e-8)
+
+
+# ------------------------------------------------------------------------------------------------
+# unknown-based AMG first stage on A_00 (Sec. 3.4) and the S~_diag Schur approximation (Sec. 3.3.1)
+def _bitwise_levels(lo, lg):
+    assert len(lo) == len(lg) >= 2
+    for a, b in zip(lo, lg):
+        assert a["n"] == b["n"]
+        for key in ("rp", "ci", "v", "dinv"):
+            assert np.array_equal(a[key], b[key]), key
+        if "cf" in a:
+            for key in ("cf", "Prp", "Pci", "Pv"):
+                assert np.array_equal(a[key], b[key]), key
+
+
+@pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "medium"])
+def test_uamg_hierarchy_bitwise(name):
+    """The device's unknown-based hierarchy of A_00 (per-block strength, PMIS and direct
+    interpolation, Galerkin product of the coupled matrix) equals the oracle's bit for bit."""
+    s, o, g = pair(name, stage1=cp.STAGE1["uamg"])
+    _bitwise_levels(o.levels(2), g.hierarchy(0))
+
+
+@pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "medium"])
+def test_uamg_vcycle_stage1_precond_and_solve(name):
+    s, o, g = pair(name, stage1=cp.STAGE1["uamg"])
+    n, nb = s["n"], s["n"] * s["b"]
+    b = synth.normal(41, 2 * n)
+    x = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+    cp.cptr_apply_vcycle(g.ctx, 0, dev(b), x)
+    assert relerr(host(x), o.vcycle(2, b)) <= 1e-10
+    v = synth.normal(42, nb)
+    x1 = torch.empty(nb, dtype=torch.float64, device="cuda")
+    cp.cptr_apply_stage1(g.ctx, dev(v), x1)
+    assert relerr(host(x1), o.stage1(v)) <= 1e-10
+    z = torch.empty(nb, dtype=torch.float64, device="cuda")
+    cp.cptr_apply_precond(g.ctx, dev(v), z)
+    assert relerr(host(z), o.precond(v)) <= 1e-10
+    check_solve(s, o, g, 1e-8)
+
+
+def test_uamg_full_size_workload():
+    """CPTR-uAMG on the benchmark's 600k-unknown workload against the oracle run in full."""
+    s = system("cptr200k")
+    o = oracle.Oracle.from_system(s, stage1=oracle.UAMG, **OPTS["cptr200k"])
+    g = gpu_solver(s, stage1=cp.STAGE1["uamg"], **OPTS["cptr200k"])
+    info_o, info_g = check_solve(s, o, g, 1e-6)
+    print(f"CPTR-uAMG full size: {info_g['iters']} iterations (oracle {info_o['iters']}), "
+          f"{info_g['levels_p']} levels")
+
+
+@pytest.mark.parametrize("name", ["parity", "medium"])
+def test_uamg_mixed_precision(name):
+    """Mixed form of CPTR-uAMG: the V-cycle matches the oracle's rounded hierarchy, and the solve
+    reaches the FP64 residual."""
+    s, o, g = pair(name, stage1=cp.STAGE1["uamg"], precision=1)
+    n = s["n"]
+    b = synth.normal(43, 2 * n)
+    x = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+    cp.cptr_apply_vcycle(g.ctx, 0, dev(b), x)
+    assert relerr(host(x), o.vcycle(2, b)) <= 1e-5
+    xg, info = g.solve(dev(s["rhs"].reshape(-1)), 1e-8)
+    assert info["status"] == "CPTR_OK" and info["true_rel_res"] <= 1.05e-8
+
+
+@pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "medium"])
+def test_schur_diag_hierarchy_and_solve(name):
+    """S~_diag formed on the device (column scaling, SpGEMM, union difference) and its hierarchy
+    equal the oracle's bit for bit; the solve matches the oracle."""
+    s, o, g = pair(name, schur=cp.SCHUR["diag"])
+    _bitwise_levels(o.levels(1), g.hierarchy(1))
+    info_o, info_g = check_solve(s, o, g, 1e-8)
+    assert info_g["schur_used"] == "diag"
