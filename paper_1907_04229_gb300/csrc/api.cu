@@ -48,6 +48,7 @@ void release_setup(Ctx *c) {
     }
     free_batch(c);
     c->sell_shape = Shape();
+    c->tl_best_ty = c->tl_best_tz = 0;
     c->sf_grid = 4 * 152;
     c->sf_sleep = 20;
     c->ready = false;
@@ -737,8 +738,8 @@ cptr_status cptr_tuning(cptr_ctx *ctx, int32_t *rows, int32_t cap, int32_t *n_ro
         chosen.T = 0;
         add(3, 0, 5, chosen);
         Shape tile;
-        tile.G = (int16_t)(c->tl_ok ? c->tl_ty : 0);
-        tile.T = (int16_t)(c->tl_ok ? c->tl_tz : 0);
+        tile.G = (int16_t)c->tl_best_ty;
+        tile.T = (int16_t)c->tl_best_tz;
         add(3, 0, 6, tile);
         *n_rows = (int32_t)(out.size() / 5);
         for (int32_t i = 0; i < std::min<int32_t>(cap, *n_rows) * 5; ++i) rows[i] = out[i];

@@ -338,6 +338,7 @@ struct Ctx {
     bool tl_ok = false, tl_use = false;                // built / chosen
     int32_t tl_dims[3] = {0, 0, 0};                    // detected nx, ny, nz (0: no box)
     int32_t tl_ty = 0, tl_tz = 0;                      // tile shape of the tables built
+    int32_t tl_best_ty = 0, tl_best_tz = 0;            // tile shape the set-up chose (tuned or given)
     int32_t sf_grid = 4 * 152;                         // persistent grid of the sweeps (autotuned)
     int32_t sf_sleep = 20;                             // back-off between polls, ns (autotuned)
     int32_t inject_wait = 0;                           // failure injection (see cptr_inject_wait_timeout)

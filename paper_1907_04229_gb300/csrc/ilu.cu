@@ -2006,6 +2006,7 @@ cptr_status ilu_setup(Ctx *c) {
         }
         if (Ty > 0) CPTR_TRY(tile_setup(c, Ty, Tz));
         c->tl_use = c->tl_ok && (c->o.ilu_sweep == 4 || sched == 3);
+        if (c->tl_ok) { c->tl_best_ty = c->tl_ty; c->tl_best_tz = c->tl_tz; }
     }
     setup_tick(c, SETUP_ILU_HOST, &t0);
     return CPTR_OK;
@@ -2175,6 +2176,8 @@ cptr_status ilu_autotune(Ctx *c) {
             c->sp_use = c->sp_ok && sched == 2;
             c->tl_use = c->tl_ok && sched == 3;
         }
+        auto ts = c->tune_cache.find(key + 2);
+        if (ts != c->tune_cache.end()) { c->tl_best_ty = ts->second.G; c->tl_best_tz = ts->second.T; }
         return CPTR_OK;
     }
     double *r = c->xw, *z = c->w;   // scratch vectors of n*b doubles
@@ -2284,6 +2287,8 @@ cptr_status ilu_autotune(Ctx *c) {
     c->tune_cache[key] = sh;
     c->tune_cache[key + 1] = sc;
     if (tile_ty > 0) {
+        c->tl_best_ty = tile_ty;
+        c->tl_best_tz = tile_tz;
         Shape st;
         st.G = (int16_t)tile_ty;
         st.T = (int16_t)tile_tz;
