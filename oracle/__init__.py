@@ -23,6 +23,7 @@ _lib = None
 CPTR_FULL, CPTR_UPPER, CPTR_LOWER, BD, CPR, NONE1, UAMG = range(7)
 ILU0, NONE2 = 0, 1
 SCHUR_GIVEN, SCHUR_ATT, SCHUR_DIAG = 0, 1, 3
+DECOUPLE_NONE, DECOUPLE_QI, DECOUPLE_TI = 0, 1, 2
 L1, JACOBI = 0, 1
 
 
@@ -40,7 +41,7 @@ class Opts(ctypes.Structure):
                 ("smoother", ctypes.c_int32), ("omega", ctypes.c_double), ("theta", ctypes.c_double),
                 ("n_coarse", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_it", ctypes.c_int32), ("dense_max", ctypes.c_int32), ("seed", ctypes.c_int32),
-                ("ilu_order", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("ilu_order", ctypes.c_int32), ("precision", ctypes.c_int32), ("decouple", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -128,7 +129,8 @@ def _p(a):
 
 def default_opts(**kw) -> Opts:
     o = Opts(stage1=CPTR_FULL, stage2=ILU0, schur=SCHUR_GIVEN, smoother=L1, omega=2.0 / 3.0, theta=0.25,
-             n_coarse=256, max_levels=25, restart=30, max_it=1000, dense_max=1024, seed=0, ilu_order=0, precision=0)
+             n_coarse=256, max_levels=25, restart=30, max_it=1000, dense_max=1024, seed=0, ilu_order=0, precision=0,
+             decouple=0)
     for k, v in kw.items():
         setattr(o, k, v)
     return o

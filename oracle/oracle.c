@@ -20,6 +20,9 @@
  *                         diagonal block on its own, Galerkin product and smoothing on the coupled
  *                         A_00)                           Sec. 3.4
  *   S~_diag               A_TT - A_Tp diag(A_pp)^{-1} A_pT   Sec. 3.3.1
+ *   QI / TI decoupling    stage 1 solves with S = A_00 - D A_s0 (CPR: A_pp - D A_sp) on the
+ *                         decoupled right-hand side R G v, G = [I -D; 0 I], D_QI = diag(A_0s)
+ *                         diag(A_ss)^{-1}, D_TI = colsum(A_0s) colsum(A_ss)^{-1}   Sec. 3.1, 3.2
  *   two-stage combination x1 = M1^-1 v, b1 = v - A x1,
  *                         z = M2^-1 b1 + x1              Sec. 3 "Two-stage preconditioners"
  *   second stage          ILU(0)                         Sec. 4 (ILU(0) default)
@@ -50,6 +53,7 @@ typedef struct {
     int32_t ilu_order;       /* 0: natural cell order; 1: multicolour (greedy colouring) */
     int32_t precision;       /* 0: FP64 everywhere; 1: stored preconditioner values rounded as the
                                 mixed-precision GPU form stores them (FP64 arithmetic) */
+    int32_t decouple;        /* 0: none; 1: Quasi-IMPES; 2: True-IMPES (CPR and uAMG first stages) */
 } or_opts;
 
 typedef struct {
@@ -608,6 +612,8 @@ typedef struct {
     csr App, ApT, ATp, St;
     amg hp, hT;
     csr A00;           /* uAMG: A_00 in unknown-wise order [p; T] */
+    double *Ddec;      /* decoupling: D_i of every cell, [n][2][b] (rows p, T; columns by slot, zero
+                          outside the secondary slots) */
     amg hU;
     double *b00, *x00;
     ilu0 ilu;
@@ -756,6 +762,112 @@ static void permute_cells(const csr *A, int32_t b, const int32_t *order, csr *P)
 }
 
 /* z = (LU)^{-1} r for the factors of the (possibly cell-permuted) matrix */
+/* entry (r, c) of block k (block row i) of the interleaved scalar CSR A' */
+static double blk_at(const or_ctx *c, const int32_t *rp, int32_t i, int32_t k, int r, int col) {
+    int32_t b = c->b;
+    return c->A.v[c->A.rp[i * b + r] + (k - rp[i]) * b + col];
+}
+
+/* the primary slots of the decoupled first stage: {p} for CPR, {p, T} for the p-T first stages */
+static int primary_slots(const or_ctx *c, int *prim) {
+    prim[0] = c->ps;
+    if (c->o.stage1 == OR_CPR) return 1;
+    prim[1] = c->ts;
+    return 2;
+}
+
+/* in-place inverse of an m x m row-major matrix by Gauss-Jordan elimination with partial pivoting
+ * (largest |y_rk| among the remaining rows, lowest row on ties; the pivot row times 1 / pivot;
+ * every other row minus its multiple of the pivot row); returns -1 if singular */
+static int small_inverse(int m, double *y) {
+    double a[3][6];
+    for (int r = 0; r < m; ++r)
+        for (int q = 0; q < 2 * m; ++q) a[r][q] = q < m ? y[r * m + q] : (q - m == r ? 1.0 : 0.0);
+    for (int k = 0; k < m; ++k) {
+        int p = k;
+        for (int r = k + 1; r < m; ++r)
+            if (fabs(a[r][k]) > fabs(a[p][k])) p = r;
+        if (a[p][k] == 0.0) return -1;
+        if (p != k)
+            for (int q = 0; q < 2 * m; ++q) { double t = a[k][q]; a[k][q] = a[p][q]; a[p][q] = t; }
+        double inv = 1.0 / a[k][k];
+        for (int q = 0; q < 2 * m; ++q) a[k][q] = a[k][q] * inv;
+        for (int r = 0; r < m; ++r) {
+            if (r == k) continue;
+            double f = a[r][k];
+            for (int q = 0; q < 2 * m; ++q) a[r][q] = a[r][q] - f * a[k][q];
+        }
+    }
+    for (int r = 0; r < m; ++r)
+        for (int q = 0; q < m; ++q) y[r * m + q] = a[r][m + q];
+    return 0;
+}
+
+/* Decoupling operator G = [I -D; 0 I] (Sec. 3.1 for CPR, extended to the p-T system in Sec. 3.2):
+ * D_i = X_i Y_i^{-1} per cell, with X_i from the primary rows and secondary columns and Y_i from
+ * the secondary rows and columns of A'.  Quasi-IMPES: the cell's diagonal block (diag);
+ * True-IMPES: the sum of the blocks in the cell's block column (colsum), over the block rows j
+ * ascending.  D_i[r][t] = sum over u ascending of X_i[r][u] Yinv_i[u][t]. */
+static int compute_decoupling(or_ctx *c, const int32_t *rp, const int32_t *ci) {
+    int32_t n = c->n, b = c->b;
+    int prim[2], sec[4], np_ = primary_slots(c, prim), ns = 0;
+    for (int q = 0; q < b; ++q) {
+        int is_p = 0;
+        for (int t = 0; t < np_; ++t) is_p |= (prim[t] == q);
+        if (!is_p) sec[ns++] = q;
+    }
+    c->Ddec = (double *)calloc((size_t)n * 2 * b, sizeof(double));
+    for (int32_t i = 0; i < n; ++i) {
+        double X[2][3] = {{0}}, Y[9] = {0};
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+            int32_t j = ci[k];
+            if (c->o.decouple == 1) {          /* QI: the diagonal block of row i */
+                if (j != i) continue;
+                for (int r = 0; r < np_; ++r)
+                    for (int t = 0; t < ns; ++t) X[r][t] = blk_at(c, rp, i, k, prim[r], sec[t]);
+                for (int r = 0; r < ns; ++r)
+                    for (int t = 0; t < ns; ++t) Y[r * ns + t] = blk_at(c, rp, i, k, sec[r], sec[t]);
+            } else {                           /* TI: block (j, i) of every row j with one */
+                int32_t kk = -1;
+                for (int32_t q = rp[j]; q < rp[j + 1]; ++q)
+                    if (ci[q] == i) { kk = q; break; }
+                if (kk < 0) return -1;         /* the pattern must be structurally symmetric */
+                for (int r = 0; r < np_; ++r)
+                    for (int t = 0; t < ns; ++t) X[r][t] = X[r][t] + blk_at(c, rp, j, kk, prim[r], sec[t]);
+                for (int r = 0; r < ns; ++r)
+                    for (int t = 0; t < ns; ++t) Y[r * ns + t] = Y[r * ns + t] + blk_at(c, rp, j, kk, sec[r], sec[t]);
+            }
+        }
+        if (small_inverse(ns, Y) != 0) return -6;
+        for (int r = 0; r < np_; ++r)
+            for (int t = 0; t < ns; ++t) {
+                double d = 0.0;
+                for (int u = 0; u < ns; ++u) d = d + X[r][u] * Y[u * ns + t];
+                c->Ddec[((size_t)i * 2 + r) * b + sec[t]] = d;
+            }
+    }
+    return 0;
+}
+
+/* Field (u, w) of G A' on the cell pattern: entry a(i,u; j,w) - sum_s D_i[u][s] a(i,s; j,w) over the
+ * secondary slots s ascending (u a primary slot). */
+static void extract_field_g(const or_ctx *c, const int32_t *rp, const int32_t *ci, int u, int w, csr *F) {
+    int32_t n = c->n, b = c->b;
+    int ru = (u == c->ps) ? 0 : 1;
+    csr_alloc(F, n, rp[n]);
+    memcpy(F->rp, rp, sizeof(int32_t) * ((size_t)n + 1));
+    memcpy(F->ci, ci, sizeof(int32_t) * (size_t)rp[n]);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+            double v = blk_at(c, rp, i, k, u, w);
+            for (int s = 0; s < b; ++s) {
+                double d = c->Ddec[((size_t)i * 2 + ru) * b + s];
+                if (d != 0.0) v = v - d * blk_at(c, rp, i, k, s, w);
+            }
+            F->v[k] = v;
+        }
+}
+
 /* A_00 = [A_pp A_pT; A_Tp A_TT] in unknown-wise order (Sec. 3.2 eq. A00): row i < n holds A_pp row
  * i (columns j) then A_pT row i (columns n + j); row n + i holds A_Tp row i then A_TT row i. */
 static void assemble_a00(const csr *App, const csr *ApT, const csr *ATp, const csr *ATT, csr *A) {
@@ -833,9 +945,18 @@ or_ctx *or_create(int32_t n, int32_t b, const int32_t *rp, const int32_t *ci, co
             for (int32_t t = 0; t < b; ++t)
                 c->W[(int64_t)i * b * b + r * b + t] = W ? W[(int64_t)i * b * b + r * b + t] : (r == t ? 1.0 : 0.0);
     bsr_to_csr_weighted(n, b, rp, ci, vals, W, &c->A);
-    extract_field(c, rp, ci, ps, ps, &c->App);
-    extract_field(c, rp, ci, ps, ts, &c->ApT);
-    extract_field(c, rp, ci, ts, ps, &c->ATp);
+    int rc = 0;
+    if (o->decouple) rc = compute_decoupling(c, rp, ci);
+    if (c->Ddec) {   /* the first stage's fields of G A' (Sec. 3.1, 3.2) */
+        extract_field_g(c, rp, ci, ps, ps, &c->App);
+        extract_field_g(c, rp, ci, ps, ts, &c->ApT);
+        if (o->stage1 == OR_CPR) extract_field(c, rp, ci, ts, ps, &c->ATp);
+        else extract_field_g(c, rp, ci, ts, ps, &c->ATp);
+    } else {
+        extract_field(c, rp, ci, ps, ps, &c->App);
+        extract_field(c, rp, ci, ps, ts, &c->ApT);
+        extract_field(c, rp, ci, ts, ps, &c->ATp);
+    }
     if (st_v && o->schur == OR_SCHUR_GIVEN) {
         csr_alloc(&c->St, n, st_rp[n]);
         memcpy(c->St.rp, st_rp, sizeof(int32_t) * ((size_t)n + 1));
@@ -846,10 +967,11 @@ or_ctx *or_create(int32_t n, int32_t b, const int32_t *rp, const int32_t *ci, co
     } else {
         extract_field(c, rp, ci, ts, ts, &c->St); /* S~_{A_TT} = A_TT (Sec. 3.3.1) */
     }
-    int rc = 0;
+    if (rc) { c->status = rc; return c; }
     if (o->stage1 == OR_UAMG) {
         csr ATT;
-        extract_field(c, rp, ci, ts, ts, &ATT);
+        if (c->Ddec) extract_field_g(c, rp, ci, ts, ts, &ATT);
+        else extract_field(c, rp, ci, ts, ts, &ATT);
         assemble_a00(&c->App, &c->ApT, &c->ATp, &ATT, &c->A00);
         csr_free(&ATT);
         rc = uamg_setup(&c->hU, &c->A00, n, o);
@@ -893,6 +1015,7 @@ void or_destroy(or_ctx *c) {
     if (!c) return;
     csr_free(&c->A); csr_free(&c->App); csr_free(&c->ApT); csr_free(&c->ATp); csr_free(&c->St);
     amg_free(&c->hp); amg_free(&c->hT); amg_free(&c->hU); csr_free(&c->A00); free(c->b00); free(c->x00);
+    free(c->Ddec);
     csr_free(&c->ilu.LU); free(c->ilu.diag);
     free(c->cperm); csr_free(&c->Aperm); free(c->rp_tmp); free(c->zp_tmp); csr_free(&c->Alow);
     free(c->W); free(c->bp); free(c->bT); free(c->xp); free(c->dT); free(c->dp); free(c->t1);
@@ -906,6 +1029,13 @@ static void stage1(or_ctx *c, const double *v, double *x1) {
     memset(x1, 0, sizeof(double) * (size_t)n * b);
     if (c->o.stage1 == OR_NONE1) return;
     for (int32_t i = 0; i < n; ++i) { c->bp[i] = v[i * b + c->ps]; c->bT[i] = v[i * b + c->ts]; }
+    if (c->Ddec)   /* the decoupled right-hand side R G v */
+        for (int32_t i = 0; i < n; ++i)
+            for (int s = 0; s < b; ++s) {
+                double dp = c->Ddec[((size_t)i * 2 + 0) * b + s], dT = c->Ddec[((size_t)i * 2 + 1) * b + s];
+                if (dp != 0.0) c->bp[i] = c->bp[i] - dp * v[i * b + s];
+                if (dT != 0.0) c->bT[i] = c->bT[i] - dT * v[i * b + s];
+            }
     switch (c->o.stage1) {
     case OR_CPTR_FULL: /* Sec. 3.3: the five steps */
         vcycle(&c->hp, 0, c->bp, c->xp);                                         /* 1. A_pp x_p = b_p */

@@ -873,3 +873,84 @@ def test_schur_diag_is_exact_for_one_cell():
     App, ApT, ATp, ATT = pt_blocks(o.dense(), s["b"])
     lev = o.levels(1)[0]
     assert abs(lev["v"][0] - (ATT - ATp @ np.linalg.solve(App, ApT))[0, 0]) <= 1e-14 * abs(lev["v"][0])
+
+
+# ------------------------------------------------------------------------------------------------
+# QI / TI decoupling operators (Sec. 3.1 for CPR, extended to the p-T system in Sec. 3.2)
+def _dense_decoupling(Ad, n, b, prim, kind):
+    """D_i = X_i Y_i^{-1} from the dense A' by numpy: QI from the diagonal block, TI from the sum of
+    the blocks of block column i; and G A' with G_i = [I -D_i; 0 I] on the primary rows of cell i."""
+    sec = [q for q in range(b) if q not in prim]
+    GA = Ad.copy()
+    D = np.zeros((n, len(prim), len(sec)))
+    for i in range(n):
+        cols = [i * b + s for s in sec]
+        if kind == "qi":
+            X = Ad[np.ix_([i * b + p for p in prim], cols)]
+            Y = Ad[np.ix_([i * b + s for s in sec], cols)]
+        else:
+            X = sum(Ad[np.ix_([j * b + p for p in prim], cols)] for j in range(n))
+            Y = sum(Ad[np.ix_([j * b + s for s in sec], cols)] for j in range(n))
+        D[i] = np.linalg.solve(Y.T, X.T).T
+        for r, p in enumerate(prim):
+            GA[i * b + p] = Ad[i * b + p] - sum(D[i, r, t] * Ad[i * b + s] for t, s in enumerate(sec))
+    return D, GA, sec
+
+
+@pytest.mark.parametrize("kind", ["qi", "ti"])
+@pytest.mark.parametrize("stage1", ["cpr", "uamg"])
+def test_decoupled_first_stage_fields(kind, stage1):
+    """The first stage's fields are those of G A': A_pp - D A_sp for CPR (Sec. 3.1), A_00 - D A_s0
+    for the p-T first stage (Sec. 3.2), with D_QI / D_TI computed from the dense A' by numpy."""
+    s = tiny().system()
+    n, b = s["n"], s["b"]
+    st1 = oracle.CPR if stage1 == "cpr" else oracle.UAMG
+    dec = oracle.DECOUPLE_QI if kind == "qi" else oracle.DECOUPLE_TI
+    o = oracle.Oracle.from_system(s, stage1=st1, decouple=dec, max_levels=1, dense_max=4096)
+    Ad = oracle.Oracle.from_system(s, max_levels=1, dense_max=4096).dense()
+    prim = [0] if stage1 == "cpr" else [0, 1]
+    D, GA, sec = _dense_decoupling(Ad, n, b, prim, kind)
+    nnzb = int(s["row_ptr"][-1])
+    App = dense_csr(s["row_ptr"], s["col_idx"], o.field(0, nnzb), n)
+    ApT = dense_csr(s["row_ptr"], s["col_idx"], o.field(1, nnzb), n)
+    assert np.abs(App - GA[0::b, 0::b]).max() <= 1e-12 * np.abs(GA[0::b, 0::b]).max()
+    assert np.abs(ApT - GA[0::b, 1::b]).max() <= 1e-12 * np.abs(GA[0::b, 1::b]).max()
+    if kind == "qi":   # the defining property: no secondary unknown of its own cell in a primary row
+        for i in range(n):
+            blk = GA[np.ix_([i * b + p for p in prim], [i * b + q for q in sec])]
+            assert np.abs(blk).max() <= 1e-12 * np.abs(Ad[i * b:(i + 1) * b, i * b:(i + 1) * b]).max()
+
+
+@pytest.mark.parametrize("kind", ["qi", "ti"])
+def test_decoupled_cpr_stage1_with_exact_inner_solve(kind):
+    """With an exact inner solve, the decoupled CPR first stage is x_p = (A_pp - D A_sp)^{-1} (G v)_p
+    (Sec. 3.1: M1^{-1} = R_p^T (R_p G A R_p^T)^{-1} R_p G)."""
+    s = tiny().system()
+    n, b = s["n"], s["b"]
+    dec = oracle.DECOUPLE_QI if kind == "qi" else oracle.DECOUPLE_TI
+    o = oracle.Oracle.from_system(s, stage1=oracle.CPR, decouple=dec, max_levels=1, dense_max=4096)
+    Ad = oracle.Oracle.from_system(s, max_levels=1, dense_max=4096).dense()
+    D, GA, sec = _dense_decoupling(Ad, n, b, [0], kind)
+    v = synth.normal(51, n * b)
+    Gv = v.copy().reshape(n, b)
+    for i in range(n):
+        Gv[i, 0] = v[i * b] - sum(D[i, 0, t] * v[i * b + q] for t, q in enumerate(sec))
+    want = np.linalg.solve(GA[0::b, 0::b], Gv[:, 0])
+    x1 = o.stage1(v).reshape(n, b)
+    assert np.linalg.norm(x1[:, 0] - want) <= 1e-10 * np.linalg.norm(want)
+    assert not x1[:, 1:].any()
+
+
+def test_decoupling_trend_ti_better_than_qi():
+    """Sec. 3.1: TI is superior to QI, which can increase the number of GMRES iterations; TI also
+    helps the unknown-based first stage (Tables meshW-anisomeshW, CPTR-uAMG(TI))."""
+    s = synth.make_box(40, 40, 10, 0.5, 0.5, 0.25, seed=11, sigma=2.0, layered=True, kv_ratio=0.1,
+                       kT_const=2.0, T_inj=500.0, q_inj=1e-6, dt=86400.0).system()
+    its = {}
+    for st1 in (oracle.CPR, oracle.UAMG):
+        for dec in (0, 1, 2):
+            x, info = oracle.Oracle.from_system(s, stage1=st1, decouple=dec, max_it=300).solve(s["rhs"], 1e-8)
+            assert info["converged"]
+            its[st1, dec] = info["iters"]
+    assert its[oracle.CPR, 2] <= its[oracle.CPR, 1] and its[oracle.UAMG, 2] <= its[oracle.UAMG, 1]
+    assert its[oracle.UAMG, 2] < its[oracle.UAMG, 0]
