@@ -70,6 +70,14 @@ enum { CPTR_PREC_FP64 = 0, CPTR_PREC_MIXED = 1 };
  * multicolour: greedy distance-1 colouring of the cell graph in the caller's order, cells sorted
  * by (colour, index) -- red-black on a 7-point grid, two level sets per triangular sweep */
 enum { CPTR_ILU_NATURAL = 0, CPTR_ILU_MULTICOLOR = 1 };
+/* decoupling operator G = [I -D; 0 I] of the first stage, applied inside it: M1^{-1} =
+ * R^T (R G A' R^T)^{-1} R G (Sec. 3.1), i.e. stage 1 solves with A_pp - D A_sp (CPR) or A_00 - D A_s0
+ * (p-T first stage, Sec. 3.2) on the right-hand side R G v; the system and the second stage keep A'.
+ * D is block diagonal, D_i = X_i Y_i^{-1}: Quasi-IMPES takes X_i, Y_i from the cell's diagonal block
+ * (primary rows x secondary columns, secondary x secondary), True-IMPES from the sum of the blocks
+ * of block column i (the pattern must then be structurally symmetric).  Y_i^{-1} by Gauss-Jordan
+ * with partial pivoting; primary slots {p} for CPR, {p, T} otherwise. */
+enum { CPTR_DECOUPLE_NONE = 0, CPTR_DECOUPLE_QI = 1, CPTR_DECOUPLE_TI = 2 };
 /* unknown kinds, one per block slot */
 enum { CPTR_U_P = 0, CPTR_U_T = 1, CPTR_U_SAT = 2 };
 
@@ -107,6 +115,11 @@ typedef struct {
                             the shape of smallest modelled time, or with autotune the fastest of the
                             four best modelled ones */
     int32_t tile_z;
+    int32_t decouple;    /* decoupling operator of the first stage (Sec. 3.1, extended to the p-T system
+                            in Sec. 3.2): CPTR_DECOUPLE_NONE (default), _QI or _TI; for the CPR and
+                            unknown-based first stages only (the Schur approximation of the block
+                            preconditioner cannot be combined with it, Sec. 3.3.1) */
+    int32_t ilu_fill;    /* level of fill of the second stage's block ILU(k): 0 (default) or 1 */
 } cptr_options;
 
 typedef struct {

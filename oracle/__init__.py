@@ -41,7 +41,8 @@ class Opts(ctypes.Structure):
                 ("smoother", ctypes.c_int32), ("omega", ctypes.c_double), ("theta", ctypes.c_double),
                 ("n_coarse", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_it", ctypes.c_int32), ("dense_max", ctypes.c_int32), ("seed", ctypes.c_int32),
-                ("ilu_order", ctypes.c_int32), ("precision", ctypes.c_int32), ("decouple", ctypes.c_int32)]
+                ("ilu_order", ctypes.c_int32), ("precision", ctypes.c_int32), ("decouple", ctypes.c_int32),
+                ("ilu_fill", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -94,6 +95,10 @@ def _load():
         lib.or_nnz.argtypes = [P]
         lib.or_matrix.restype = None
         lib.or_matrix.argtypes = [P, P, P, P]
+        lib.or_ilu_nnz.restype = ctypes.c_int32
+        lib.or_ilu_nnz.argtypes = [P]
+        lib.or_ilu_pattern.restype = None
+        lib.or_ilu_pattern.argtypes = [P, P, P]
         lib.or_ilu_order.restype = None
         lib.or_ilu_order.argtypes = [P, P]
         lib.or_ilu_factors.restype = None
@@ -130,7 +135,7 @@ def _p(a):
 def default_opts(**kw) -> Opts:
     o = Opts(stage1=CPTR_FULL, stage2=ILU0, schur=SCHUR_GIVEN, smoother=L1, omega=2.0 / 3.0, theta=0.25,
              n_coarse=256, max_levels=25, restart=30, max_it=1000, dense_max=1024, seed=0, ilu_order=0, precision=0,
-             decouple=0)
+             decouple=0, ilu_fill=0)
     for k, v in kw.items():
         setattr(o, k, v)
     return o
@@ -257,11 +262,19 @@ class Oracle:
         return out
 
     def ilu_factors(self):
+        """Values of the ILU factors on their pattern (that of A', or the ILU(1) fill pattern)."""
         lib = _load()
-        nnz = lib.or_nnz(self._c)
+        nnz = lib.or_ilu_nnz(self._c)
         v = np.zeros(nnz)
         lib.or_ilu_factors(self._c, _p(v))
         return v
+
+    def ilu_pattern(self):
+        lib = _load()
+        nnz = lib.or_ilu_nnz(self._c)
+        rp, ci = np.zeros(self.nb + 1, np.int32), np.zeros(nnz, np.int32)
+        lib.or_ilu_pattern(self._c, _p(rp), _p(ci))
+        return rp, ci
 
     def field(self, f, nnz):
         lib = _load()

@@ -25,7 +25,8 @@
  *                         diag(A_ss)^{-1}, D_TI = colsum(A_0s) colsum(A_ss)^{-1}   Sec. 3.1, 3.2
  *   two-stage combination x1 = M1^-1 v, b1 = v - A x1,
  *                         z = M2^-1 b1 + x1              Sec. 3 "Two-stage preconditioners"
- *   second stage          ILU(0)                         Sec. 4 (ILU(0) default)
+ *   second stage          ILU(0), or ILU(1)              Sec. 4 (ILU(0) default; ILU(1) in the
+ *                                                        CPR-AMG-ILU(1) comparisons)
  *   AMG V-cycle           strength, PMIS, direct interpolation, Galerkin RAP, l1-Jacobi or
  *                         omega-Jacobi, one pre- and one post-sweep, dense LU on the coarsest
  *                         level (replaces BoomerAMG's defaults, Sec. 4)
@@ -54,6 +55,7 @@ typedef struct {
     int32_t precision;       /* 0: FP64 everywhere; 1: stored preconditioner values rounded as the
                                 mixed-precision GPU form stores them (FP64 arithmetic) */
     int32_t decouple;        /* 0: none; 1: Quasi-IMPES; 2: True-IMPES (CPR and uAMG first stages) */
+    int32_t ilu_fill;        /* level of fill of the second stage: 0 (ILU(0)) or 1 (ILU(1)) */
 } or_opts;
 
 typedef struct {
@@ -586,6 +588,49 @@ static int ilu0_factor(const csr *A, ilu0 *f) {
     return 0;
 }
 
+/* The ILU(1) pattern: row i keeps its own entries and gains, for every entry k < i of its row,
+ * the entries j > k of row k (a fill entry has level lev(i,k) + lev(k,j) + 1, which is at most 1
+ * only when both are original entries, so the original pattern alone decides).  F holds A's
+ * values, zero at the fill; ILU on this pattern (ilu0_factor) is ILU(1) of A. */
+static void ilu1_pattern(const csr *A, csr *F) {
+    int32_t n = A->n;
+    int32_t *mark = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *list = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    for (int32_t j = 0; j < n; ++j) mark[j] = -1;
+    int32_t cap = 2 * A->nnz + 16, nnz = 0;
+    F->n = n;
+    F->rp = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    F->ci = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    F->v = (double *)malloc(sizeof(double) * (size_t)cap);
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t len = 0;
+        for (int32_t k = A->rp[i]; k < A->rp[i + 1]; ++k) { mark[A->ci[k]] = i; list[len++] = A->ci[k]; }
+        for (int32_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+            int32_t kc = A->ci[k];
+            if (kc >= i) break;
+            for (int32_t q = A->rp[kc]; q < A->rp[kc + 1]; ++q) {
+                int32_t j = A->ci[q];
+                if (j > kc && mark[j] != i) { mark[j] = i; list[len++] = j; }
+            }
+        }
+        qsort(list, (size_t)len, sizeof(int32_t), cmp_i32);
+        if (nnz + len > cap) {
+            while (nnz + len > cap) cap *= 2;
+            F->ci = (int32_t *)realloc(F->ci, sizeof(int32_t) * (size_t)cap);
+            F->v = (double *)realloc(F->v, sizeof(double) * (size_t)cap);
+        }
+        int32_t a = A->rp[i];
+        for (int32_t t = 0; t < len; ++t) {
+            F->ci[nnz] = list[t];
+            F->v[nnz] = (a < A->rp[i + 1] && A->ci[a] == list[t]) ? A->v[a++] : 0.0;
+            ++nnz;
+        }
+        F->rp[i + 1] = nnz;
+    }
+    F->nnz = nnz;
+    free(mark); free(list);
+}
+
 static void ilu0_solve(const ilu0 *f, const double *r, double *z) {
     const csr *M = &f->LU;
     int32_t n = M->n;
@@ -980,14 +1025,21 @@ or_ctx *or_create(int32_t n, int32_t b, const int32_t *rp, const int32_t *ci, co
         if (!rc && o->stage1 != OR_NONE1 && o->stage1 != OR_CPR) rc = amg_setup(&c->hT, &c->St, o);
     }
     if (!rc && o->stage2 == OR_ILU0) {
+        const csr *M = &c->A;
         if (o->ilu_order == 1) {
             c->cperm = multicolour_order(n, rp, ci);
             permute_cells(&c->A, b, c->cperm, &c->Aperm);
             c->rp_tmp = (double *)calloc((size_t)n * b, sizeof(double));
             c->zp_tmp = (double *)calloc((size_t)n * b, sizeof(double));
-            rc = ilu0_factor(&c->Aperm, &c->ilu);
+            M = &c->Aperm;
+        }
+        if (o->ilu_fill == 1) {   /* ILU(1): ILU on the level-1 fill pattern */
+            csr F;
+            ilu1_pattern(M, &F);
+            rc = ilu0_factor(&F, &c->ilu);
+            csr_free(&F);
         } else {
-            rc = ilu0_factor(&c->A, &c->ilu);
+            rc = ilu0_factor(M, &c->ilu);
         }
     }
     if (!rc && o->precision == 1) {
@@ -1290,6 +1342,11 @@ void or_matrix(or_ctx *c, int32_t *rp, int32_t *ci, double *v) {
     memcpy(v, c->A.v, sizeof(double) * (size_t)c->A.nnz);
 }
 void or_ilu_factors(or_ctx *c, double *v) { memcpy(v, c->ilu.LU.v, sizeof(double) * (size_t)c->ilu.LU.nnz); }
+int32_t or_ilu_nnz(or_ctx *c) { return c->ilu.LU.nnz; }
+void or_ilu_pattern(or_ctx *c, int32_t *rp, int32_t *ci) {
+    memcpy(rp, c->ilu.LU.rp, sizeof(int32_t) * ((size_t)c->ilu.LU.n + 1));
+    memcpy(ci, c->ilu.LU.ci, sizeof(int32_t) * (size_t)c->ilu.LU.nnz);
+}
 /* field: 0 A_pp, 1 A_pT, 2 A_Tp, 3 S~_T (values on their own patterns; S~_T may differ) */
 void or_field(or_ctx *c, int f, double *v) {
     const csr *F = f == 0 ? &c->App : f == 1 ? &c->ApT : f == 2 ? &c->ATp : &c->St;

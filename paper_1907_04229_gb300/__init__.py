@@ -27,6 +27,7 @@ SMOOTHER = {"l1": 0, "jacobi": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 ILU_ORDER = {"natural": 0, "multicolor": 1}
 ILU_SWEEP = {"auto": 0, "levels": 1, "chunked": 2, "paired": 3, "tiled": 4}
+DECOUPLE = {"none": 0, "qi": 1, "ti": 2}
 U_P, U_T, U_SAT = 0, 1, 2
 
 
@@ -37,7 +38,8 @@ class cptr_options(ctypes.Structure):
                 ("max_it", ctypes.c_int32), ("dense_max", ctypes.c_int32), ("seed", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("check_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("ilu_order", ctypes.c_int32), ("autotune", ctypes.c_int32), ("ilu_sweep", ctypes.c_int32),
-                ("stream", ctypes.c_void_p), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32)]
+                ("stream", ctypes.c_void_p), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32),
+                ("decouple", ctypes.c_int32), ("ilu_fill", ctypes.c_int32)]
 
 
 class cptr_stats(ctypes.Structure):
@@ -160,6 +162,8 @@ def cptr_default_options(**kw) -> cptr_options:
             v = ILU_ORDER[v]
         elif k == "ilu_sweep" and isinstance(v, str):
             v = ILU_SWEEP[v]
+        elif k == "decouple" and isinstance(v, str):
+            v = DECOUPLE[v]
         setattr(o, k, v)
     return o
 

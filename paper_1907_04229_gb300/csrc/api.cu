@@ -27,7 +27,8 @@ void release_setup(Ctx *c) {
     dfree(c->rp); dfree(c->ci); dfree(c->diag); dfree(c->A); dfree(c->W);
     dfree(c->sell_off); dfree(c->sell_col); dfree(c->sell_val);
     c->sell_off = nullptr; c->sell_col = nullptr; c->sell_val = nullptr;
-    dfree(c->App); dfree(c->ApT); dfree(c->ATp); dfree(c->St);
+    dfree(c->App); dfree(c->ApT); dfree(c->ATp); dfree(c->St); dfree(c->Ddec);
+    c->Ddec = nullptr;
     dfree(c->lf_base); dfree(c->lf_sat); dfree(c->lf_s);
     c->rp = c->ci = c->diag = nullptr;
     c->A = c->W = c->App = c->ApT = c->ATp = c->St = nullptr;
@@ -173,10 +174,11 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
     CPTR_CUDA_TRY(c, cudaMemcpyAsync(&bad, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
     CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (bad) { dfree(Araw); return c->fail(CPTR_EINVAL, "non-finite value in vals, row_weights or st_vals"); }
-    // A' = W A, then the scalar p-T blocks on the cell pattern
+    // A' = W A, then the scalar p-T blocks on the cell pattern (those of G A' for a decoupled stage 1)
     launch_decouple(c, Araw, c->W, c->A);
     CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     dfree(Araw);
+    if (c->o.decouple != CPTR_DECOUPLE_NONE) CPTR_TRY(decoupling_setup(c));
     CPTR_TRY(dalloc_t(c, &c->App, (size_t)nnzb));
     CPTR_TRY(dalloc_t(c, &c->ApT, (size_t)nnzb));
     CPTR_TRY(dalloc_t(c, &c->ATp, (size_t)nnzb));
@@ -433,7 +435,10 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
         o.schur > CPTR_SCHUR_DIAG || o.precision < CPTR_PREC_FP64 ||
         o.precision > CPTR_PREC_MIXED ||
         o.ilu_order < CPTR_ILU_NATURAL || o.ilu_order > CPTR_ILU_MULTICOLOR || o.ilu_sweep < 0 || o.ilu_sweep > 4 ||
-        o.tile_y < 0 || o.tile_z < 0 || (size_t)o.tile_y * o.tile_z > 64)
+        o.tile_y < 0 || o.tile_z < 0 || (size_t)o.tile_y * o.tile_z > 64 || o.decouple < CPTR_DECOUPLE_NONE ||
+        o.decouple > CPTR_DECOUPLE_TI ||
+        (o.decouple != CPTR_DECOUPLE_NONE && o.stage1 != CPTR_STAGE1_CPR && o.stage1 != CPTR_STAGE1_UAMG) ||
+        o.ilu_fill < 0 || o.ilu_fill > 1)
         return CPTR_EINVAL;
     cptr_ctx *ctx = new (std::nothrow) cptr_ctx();
     if (!ctx) return CPTR_ENOMEM;

@@ -187,7 +187,8 @@ void csr_free(Csr &a);
 cptr_status scan_exclusive(Ctx *c, const int32_t *in, int32_t *out, int32_t n, int32_t *total_host);
 void launch_decouple(const Ctx *c, const double *Araw, const double *W, double *A);
 void launch_weight_vec(const Ctx *c, const double *W, const double *rhs, double *out);
-void launch_extract(const Ctx *c, int u, int w, double *out);
+void launch_extract(const Ctx *c, int u, int w, double *out);   // field (u, w) of A' (of G A' if decoupled)
+cptr_status decoupling_setup(Ctx *c);                            // D_i of QI / TI into c->Ddec
 void launch_check_finite(const Ctx *c, const double *v, int64_t n, int32_t *flag);
 cptr_status sell_build(Ctx *c);
 void launch_bsr_to_sell(const Ctx *c);
@@ -346,6 +347,7 @@ struct Ctx {
     // preconditioner work
     double *bp = nullptr, *bT = nullptr, *xp = nullptr, *dp = nullptr, *dT = nullptr, *t1 = nullptr;
     double *b00 = nullptr, *x00 = nullptr;             // unknown-based AMG: [b_p; b_T], [d_p; d_T]
+    double *Ddec = nullptr;                            // decoupling: D_i per cell, [n][2][b] (rows p, T)
     float *b0032 = nullptr, *x0032 = nullptr;
     double *b1 = nullptr;
     // mixed-precision form: FP32 copies of the stage-1 operators and the stage-1 vectors

@@ -285,8 +285,108 @@ __global__ void k_extract(int32_t nnzb, int b, const double *A, int u, int w, do
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < nnzb) out[k] = A[(int64_t)k * b * b + u * b + w];
 }
+// field (u, w) of G A' for a primary slot u (decoupling row ru of D): a(i,u; j,w) - sum over the slots
+// s ascending with D_i[ru][s] != 0 of D_i[ru][s] a(i,s; j,w), products and differences rounded apart
+__global__ void k_extract_g(int32_t n, int b, const int32_t *rp, const double *A, int u, int w, int ru,
+                            const double *D, double *out) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *Di = D + ((int64_t)i * 2 + ru) * b;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+        const double *blk = A + (int64_t)k * b * b;
+        double v = blk[u * b + w];
+        for (int s = 0; s < b; ++s)
+            if (Di[s] != 0.0) v = __dsub_rn(v, __dmul_rn(Di[s], blk[s * b + w]));
+        out[k] = v;
+    }
+}
 void launch_extract(const Ctx *c, int u, int w, double *out) {
-    (k_extract<<<nblk(c->nnzb, 256), 256, 0, c->stream>>>(c->nnzb, c->b, c->A, u, w, out), note_launch());
+    const bool prim = u == c->ps || (u == c->ts && c->o.stage1 != CPTR_STAGE1_CPR);
+    if (c->Ddec && prim)
+        (k_extract_g<<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->rp, c->A, u, w, u == c->ps ? 0 : 1,
+                                                             c->Ddec, out), note_launch());
+    else
+        (k_extract<<<nblk(c->nnzb, 256), 256, 0, c->stream>>>(c->nnzb, c->b, c->A, u, w, out), note_launch());
+}
+
+// D_i = X_i Y_i^{-1} of the decoupling operator (see cptr_options.decouple): X_i (primary rows x
+// secondary columns) and Y_i (secondary x secondary) from the cell's diagonal block (QI) or summed
+// over the blocks (j, i) of its block column, rows j ascending (TI; block (j, i) found by binary
+// search in row j, flag 1 if missing); Y_i^{-1} by Gauss-Jordan with partial pivoting (flag 2 if
+// singular); D = X Y^{-1} summed over u ascending.  Every operation separately rounded.
+__global__ void k_decoupling(int32_t n, int b, int ps, int ts, int nprim, int kind, const int32_t *rp,
+                             const int32_t *ci, const double *A, double *D, int32_t *flag) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int prim[2] = {ps, ts}, sec[4], ns = 0;
+    for (int q = 0; q < b; ++q) {
+        bool p = q == ps || (nprim == 2 && q == ts);
+        if (!p) sec[ns++] = q;
+    }
+    double X[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}}, a[3][6];
+    double Y[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+        const int32_t j = ci[k];
+        int32_t kk = -1;
+        if (kind == CPTR_DECOUPLE_QI) {
+            if (j != i) continue;
+            kk = k;
+        } else {
+            int32_t lo = rp[j], hi = rp[j + 1] - 1;
+            while (lo <= hi) {
+                const int32_t mid = (lo + hi) >> 1;
+                if (ci[mid] == i) { kk = mid; break; }
+                if (ci[mid] < i) lo = mid + 1;
+                else hi = mid - 1;
+            }
+            if (kk < 0) { atomicExch(flag, 1); return; }
+        }
+        const double *blk = A + (int64_t)kk * b * b;
+        for (int r = 0; r < nprim; ++r)
+            for (int t = 0; t < ns; ++t) X[r][t] = __dadd_rn(X[r][t], blk[prim[r] * b + sec[t]]);
+        for (int r = 0; r < ns; ++r)
+            for (int t = 0; t < ns; ++t) Y[r][t] = __dadd_rn(Y[r][t], blk[sec[r] * b + sec[t]]);
+        if (kind == CPTR_DECOUPLE_QI) break;
+    }
+    for (int r = 0; r < ns; ++r)
+        for (int q = 0; q < 2 * ns; ++q) a[r][q] = q < ns ? Y[r][q] : (q - ns == r ? 1.0 : 0.0);
+    for (int k = 0; k < ns; ++k) {
+        int p = k;
+        for (int r = k + 1; r < ns; ++r)
+            if (fabs(a[r][k]) > fabs(a[p][k])) p = r;
+        if (a[p][k] == 0.0) { atomicExch(flag, 2); return; }
+        if (p != k)
+            for (int q = 0; q < 2 * ns; ++q) { const double t = a[k][q]; a[k][q] = a[p][q]; a[p][q] = t; }
+        const double inv = __ddiv_rn(1.0, a[k][k]);
+        for (int q = 0; q < 2 * ns; ++q) a[k][q] = __dmul_rn(a[k][q], inv);
+        for (int r = 0; r < ns; ++r) {
+            if (r == k) continue;
+            const double f = a[r][k];
+            for (int q = 0; q < 2 * ns; ++q) a[r][q] = __dsub_rn(a[r][q], __dmul_rn(f, a[k][q]));
+        }
+    }
+    double *Di = D + (int64_t)i * 2 * b;
+    for (int q = 0; q < 2 * b; ++q) Di[q] = 0.0;
+    for (int r = 0; r < nprim; ++r)
+        for (int t = 0; t < ns; ++t) {
+            double d = 0.0;
+            for (int u = 0; u < ns; ++u) d = __dadd_rn(d, __dmul_rn(X[r][u], a[u][ns + t]));
+            Di[r * b + sec[t]] = d;
+        }
+}
+
+cptr_status decoupling_setup(Ctx *c) {
+    CPTR_TRY(dalloc_t(c, &c->Ddec, (size_t)c->n * 2 * c->b));
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
+    const int nprim = c->o.stage1 == CPTR_STAGE1_CPR ? 1 : 2;
+    (k_decoupling<<<nblk(c->n, 128), 128, 0, c->stream>>>(c->n, c->b, c->ps, c->ts, nprim, c->o.decouple, c->rp,
+                                                         c->ci, c->A, c->Ddec, c->flag), note_launch());
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    int32_t f = 0;
+    CPTR_TRY(copy_to_host(c, &f, c->flag, sizeof(int32_t)));
+    if (f == 1) return c->fail(CPTR_EINVAL, "True-IMPES decoupling needs a structurally symmetric pattern");
+    if (f == 2) return c->fail(CPTR_ESINGULAR, "decoupling: singular secondary block");
+    return CPTR_OK;
 }
 
 __global__ void k_check_finite(const double *v, int64_t n, int32_t *flag) {
@@ -509,16 +609,24 @@ cptr_status to_lower(Ctx *c, const double *src, int64_t n, int st, void **dst) {
 // ------------------------------------------------------------------------------------------------
 // restriction to / prolongation from the p-T unknowns (Sec. 3.2)
 template <typename XT>
-__global__ void k_gather_pt(int32_t n, int b, int ps, int ts, const double *v, XT *bp, XT *bT) {
+__global__ void k_gather_pt(int32_t n, int b, int ps, int ts, const double *v, XT *bp, XT *bT, const double *D) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        bp[i] = (XT)v[(int64_t)i * b + ps];
-        bT[i] = (XT)v[(int64_t)i * b + ts];
+        double p = v[(int64_t)i * b + ps], t = v[(int64_t)i * b + ts];
+        if (D)   // the decoupled right-hand side R G v
+            for (int s = 0; s < b; ++s) {
+                const double dp = D[((int64_t)i * 2) * b + s], dT = D[((int64_t)i * 2 + 1) * b + s];
+                if (dp != 0.0) p = __dsub_rn(p, __dmul_rn(dp, v[(int64_t)i * b + s]));
+                if (dT != 0.0) t = __dsub_rn(t, __dmul_rn(dT, v[(int64_t)i * b + s]));
+            }
+        bp[i] = (XT)p;
+        bT[i] = (XT)t;
     }
 }
 template <typename XT>
 void launch_gather_pt(const Ctx *c, const double *v, XT *bp, XT *bT) {
-    (k_gather_pt<XT><<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->ps, c->ts, v, bp, bT), note_launch());
+    (k_gather_pt<XT><<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->ps, c->ts, v, bp, bT, c->Ddec),
+     note_launch());
 }
 template void launch_gather_pt<double>(const Ctx *, const double *, double *, double *);
 template void launch_gather_pt<float>(const Ctx *, const double *, float *, float *);

@@ -47,8 +47,8 @@ def test_default_options(lib):
 
 
 def test_option_struct_layout_matches_header():
-    # cptr_options: 4 int32, 2 doubles, 12 int32, one pointer, 2 int32
-    assert ctypes.sizeof(cp.cptr_options) == 16 + 16 + 48 + 8 + 8
+    # cptr_options: 4 int32, 2 doubles, 12 int32, one pointer, 4 int32
+    assert ctypes.sizeof(cp.cptr_options) == 16 + 16 + 48 + 8 + 16
     assert cp.cptr_options.stream.offset == 80
     # cptr_instance: int32 (+ padding), five pointers
     assert ctypes.sizeof(cp.cptr_instance) == 8 + 5 * 8

@@ -406,3 +406,32 @@ def test_schur_diag_hierarchy_and_solve(name):
     else:
         io, ig = check_solve(s, o, g, 1e-8)
     assert ig["schur_used"] == "diag"
+
+
+# ------------------------------------------------------------------------------------------------
+# QI / TI decoupling of the CPR and unknown-based first stages (Sec. 3.1, 3.2)
+@pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "medium"])
+@pytest.mark.parametrize("decouple", ["qi", "ti"])
+@pytest.mark.parametrize("stage1", ["cpr", "uamg"])
+def test_decoupled_first_stage(name, decouple, stage1):
+    """D_i, the fields of G A', the first-stage hierarchy (bit for bit), the decoupled first stage and
+    the solve against the oracle.  CPTR-uAMG on the conduction-dominated "medium" system stalls even
+    with TI, on both sides: there the iterates after a fixed number of steps agree."""
+    stalls = name == "medium" and stage1 == "uamg"
+    extra = dict(max_it=40) if stalls else {}
+    s, o, g = pair(name, stage1=cp.STAGE1[stage1], decouple=cp.DECOUPLE[decouple], **extra)
+    _bitwise_levels(o.levels(2 if stage1 == "uamg" else 0), g.hierarchy(0))
+    nb = s["n"] * s["b"]
+    v = synth.normal(52, nb)
+    x1 = torch.empty(nb, dtype=torch.float64, device="cuda")
+    cp.cptr_apply_stage1(g.ctx, dev(v), x1)
+    assert relerr(host(x1), o.stage1(v)) <= 1e-10
+    if stalls:
+        check_iteration_limit(s, o, g, 1e-8, 40)
+    else:
+        check_solve(s, o, g, 1e-8)
+
+
+def test_decoupling_rejected_with_the_block_preconditioner():
+    with pytest.raises(cp.CptrError):
+        cp.Solver(stage1="full", decouple="ti")

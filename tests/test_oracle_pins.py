@@ -954,3 +954,67 @@ def test_decoupling_trend_ti_better_than_qi():
             its[st1, dec] = info["iters"]
     assert its[oracle.CPR, 2] <= its[oracle.CPR, 1] and its[oracle.UAMG, 2] <= its[oracle.UAMG, 1]
     assert its[oracle.UAMG, 2] < its[oracle.UAMG, 0]
+
+
+# ------------------------------------------------------------------------------------------------
+# ILU(1) second stage (the CPR-AMG-ILU(1) comparator of Tables meshW-anisomeshW)
+def _ilu_lu(o):
+    rp, ci = o.ilu_pattern()
+    F = dense_csr(rp, ci, o.ilu_factors(), o.nb)
+    return np.tril(F, -1) + np.eye(o.nb), np.triu(F), rp, ci
+
+
+def test_ilu1_pattern_is_a_plus_level_one_fill():
+    """The ILU(1) pattern is that of A joined with that of strictlower(A) x strictupper(A) (one
+    elimination step from original entries), computed here by a boolean matrix product."""
+    o = oracle.Oracle.from_system(tiny().system(), max_levels=1, ilu_fill=1)
+    A = o.dense() != 0
+    rpA, ciA, _ = o.matrix()
+    P = np.zeros_like(A)
+    for i in range(o.nb):
+        P[i, ciA[rpA[i]:rpA[i + 1]]] = True
+    fill = (np.tril(P, -1).astype(int) @ np.triu(P, 1).astype(int)) > 0
+    rp, ci = o.ilu_pattern()
+    got = np.zeros_like(P)
+    for i in range(o.nb):
+        got[i, ci[rp[i]:rp[i + 1]]] = True
+    assert np.array_equal(got, P | fill) and (got & ~P).any()
+
+
+def test_ilu1_product_matches_matrix_on_its_pattern():
+    o = oracle.Oracle.from_system(tiny().system(), max_levels=1, ilu_fill=1)
+    L, U, rp, ci = _ilu_lu(o)
+    A = o.dense()
+    mask = np.zeros_like(A, dtype=bool)
+    for i in range(o.nb):
+        mask[i, ci[rp[i]:rp[i + 1]]] = True
+    assert np.abs((L @ U - A)[mask]).max() <= 1e-12 * np.abs(A).max()
+    r = synth.normal(53, o.nb)
+    assert np.linalg.norm(L @ (U @ o.ilu_apply(r)) - r) <= 1e-10 * np.linalg.norm(r)
+
+
+def test_scalar_ilu1_equals_block_ilu1():
+    """With dense b x b blocks, the scalar ILU(1) fill is block fill, and scalar ILU(1) equals the
+    textbook block ILU on the block ILU(1) pattern with exact pivot-block inverses."""
+    s = tiny(4, 3, 2).system()
+    o = oracle.Oracle.from_system(s, max_levels=1, ilu_fill=1)
+    n, b = s["n"], s["b"]
+    rp, ci, W = s["row_ptr"], s["col_idx"], s["weights"]
+    orig = [set(int(c) for c in ci[rp[i]:rp[i + 1]]) for i in range(n)]
+    pattern = [set(orig[i]) | {j for k in orig[i] if k < i for j in orig[k] if j > k} for i in range(n)]
+    blocks = {(i, j): np.zeros((b, b)) for i in range(n) for j in pattern[i]}
+    for i in range(n):
+        for k in range(rp[i], rp[i + 1]):
+            blocks[(i, int(ci[k]))] = W[i] @ s["vals"][k]
+    F = _block_ilu_factors(n, b, pattern, blocks)
+    y, z = _plain_solves(n, b, pattern, F, synth.normal(54, n * b).reshape(n, b))
+    zo = o.ilu_apply(synth.normal(54, n * b))
+    assert np.linalg.norm(zo - z.reshape(-1)) <= 1e-10 * np.linalg.norm(z)
+
+
+def test_ilu1_fewer_iterations_than_ilu0_for_cpr():
+    """CPR-AMG-ILU(1) takes fewer iterations than CPR-AMG with ILU(0) (Tables meshW-anisomeshW)."""
+    s = synth.make_box(40, 40, 10, 0.5, 0.5, 0.25, seed=11, sigma=2.0, layered=True, kv_ratio=0.1,
+                       kT_const=2.0, T_inj=500.0, q_inj=1e-6, dt=30 * 86400.0).system()
+    its = [oracle.Oracle.from_system(s, stage1=oracle.CPR, ilu_fill=f).solve(s["rhs"], 1e-8)[1]["iters"] for f in (0, 1)]
+    assert its[1] < its[0], its
