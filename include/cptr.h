@@ -119,7 +119,9 @@ typedef struct {
                             in Sec. 3.2): CPTR_DECOUPLE_NONE (default), _QI or _TI; for the CPR and
                             unknown-based first stages only (the Schur approximation of the block
                             preconditioner cannot be combined with it, Sec. 3.3.1) */
-    int32_t ilu_fill;    /* level of fill of the second stage's block ILU(k): 0 (default) or 1 */
+    int32_t ilu_fill;    /* level of fill of the second stage's block ILU(k): 0 (default) or 1 (block row
+                            i gains, for every block k < i of its row, the blocks j > k of row k;
+                            natural ILU order only; the sweeps then use level sets or paired levels) */
 } cptr_options;
 
 typedef struct {
@@ -225,8 +227,8 @@ cptr_status cptr_hierarchy_level(cptr_ctx *ctx, int32_t which, int32_t l, int32_
  * every GPU that loads the library keeps until the process exits.  The paper has no counterpart;
  * it is an engineering addition.
  *   r, z   device vectors of n_cells*b doubles; n_cells*b must not exceed 2^20, else
- *          CPTR_EINVAL with a message naming the limit.  Natural ILU ordering only (else
- *          CPTR_EINVAL).
+ *          CPTR_EINVAL with a message naming the limit.  Natural ILU ordering and ILU(0) only
+ *          (else CPTR_EINVAL).
  * It always applies the FP64 factors (one launch per level set), also in a context of the mixed
  * precision or with another sweep schedule, so its result equals cptr_apply_ilu of an FP64
  * context to rounding.  The array's device address is looked up with the call's device current,

@@ -438,7 +438,7 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
         o.tile_y < 0 || o.tile_z < 0 || (size_t)o.tile_y * o.tile_z > 64 || o.decouple < CPTR_DECOUPLE_NONE ||
         o.decouple > CPTR_DECOUPLE_TI ||
         (o.decouple != CPTR_DECOUPLE_NONE && o.stage1 != CPTR_STAGE1_CPR && o.stage1 != CPTR_STAGE1_UAMG) ||
-        o.ilu_fill < 0 || o.ilu_fill > 1)
+        o.ilu_fill < 0 || o.ilu_fill > 1 || (o.ilu_fill == 1 && o.ilu_order == CPTR_ILU_MULTICOLOR))
         return CPTR_EINVAL;
     cptr_ctx *ctx = new (std::nothrow) cptr_ctx();
     if (!ctx) return CPTR_ENOMEM;

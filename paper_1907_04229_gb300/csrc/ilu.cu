@@ -1791,7 +1791,8 @@ static cptr_status pair_setup(Ctx *c, const int32_t *inv_f, const int32_t *inv_b
 
 // key of the sweeps' tuning in the context's cache (grid and back-off; the schedule at key + 1)
 static uint64_t ilu_tune_key(const Ctx *c) {
-    return (uint64_t)8 << 60 | (uint64_t)(c->o.precision & 1) << 56 | ((uint64_t)c->n & 0xFFFFFFull) << 32 |
+    return (uint64_t)8 << 60 | (uint64_t)(c->o.ilu_fill & 1) << 57 | (uint64_t)(c->o.precision & 1) << 56 |
+           ((uint64_t)c->n & 0xFFFFFFull) << 32 |
            (uint64_t)(uint32_t)c->nnzb;
 }
 // the schedule a cached tuning chose (0 level sets, 1 chunked, 2 paired levels, 3 tiled), -1 if
@@ -1801,17 +1802,93 @@ static int ilu_tuned_schedule(const Ctx *c) {
     return it == c->tune_cache.end() ? -1 : it->second.G;
 }
 
+// Block ILU(1) pattern (Sec. 4; the CPR-AMG-ILU(1) comparator): block row i keeps its own blocks and
+// gains, for every block k < i of its row, the blocks j > k of row k -- a fill block has level
+// lev(i,k) + lev(k,j) + 1, at most 1 only when both are original blocks.  kmap: the original block of
+// every position of the new pattern, -1 at fill.  Rows are built on up to 8 host threads.
+static void ilu1_pattern(int32_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
+                         std::vector<int32_t> &prp, std::vector<int32_t> &pci, std::vector<int32_t> &pdg,
+                         std::vector<int32_t> &kmap) {
+    std::vector<std::vector<int32_t>> rows(n);
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nt = (int)std::min<unsigned>(8u, hw);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t)
+        pool.emplace_back([&, t]() {
+            std::vector<int32_t> cols;
+            for (int32_t i = t; i < n; i += nt) {
+                cols.assign(ci.begin() + rp[i], ci.begin() + rp[i + 1]);
+                for (int32_t k = rp[i]; k < rp[i + 1] && ci[k] < i; ++k) {
+                    const int32_t kc = ci[k];
+                    for (int32_t q = rp[kc]; q < rp[kc + 1]; ++q)
+                        if (ci[q] > kc) cols.push_back(ci[q]);
+                }
+                std::sort(cols.begin(), cols.end());
+                cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+                rows[i] = cols;
+            }
+        });
+    for (auto &th : pool) th.join();
+    prp.assign((size_t)n + 1, 0);
+    for (int32_t i = 0; i < n; ++i) prp[i + 1] = prp[i] + (int32_t)rows[i].size();
+    pci.resize(prp[n]);
+    kmap.assign(prp[n], -1);
+    pdg.assign(n, -1);
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t a = rp[i];
+        for (size_t t = 0; t < rows[i].size(); ++t) {
+            const int32_t o = prp[i] + (int32_t)t, j = rows[i][t];
+            pci[o] = j;
+            if (a < rp[i + 1] && ci[a] == j) kmap[o] = a++;
+            if (j == i) pdg[i] = o;
+        }
+    }
+}
+
+__global__ void k_scatter_blocks(int64_t nnz, int BB, const int32_t *kmap, const double *src, double *dst) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nnz * BB) return;
+    const int32_t k = kmap[u / BB];
+    dst[u] = k >= 0 ? src[(int64_t)k * BB + u % BB] : 0.0;
+}
+
 cptr_status ilu_setup(Ctx *c) {
     ilu_free(c);
     double t0 = host_ms();
     const int32_t n = c->n, BB = c->b * c->b;
     cudaStream_t st = c->stream;
-    // two spare doubles: the factorisation copies runs of blocks in 16-byte pieces rounded outwards
-    CPTR_TRY(dalloc_t(c, &c->LU, (size_t)c->nnzb * BB + 2));
-    // the pattern the factorisation works on: the caller's order, or cells permuted by colour
+    // the pattern the factorisation works on: the caller's order, cells permuted by colour, or the
+    // ILU(1) fill pattern
     std::vector<int32_t> rowmap;
     const bool mc = c->o.ilu_order == CPTR_ILU_MULTICOLOR;
-    if (mc) {
+    const bool fill = c->o.ilu_fill == 1;
+    int64_t nnz_ilu = c->nnzb;
+    if (fill) {
+        CPTR_TRY(host_pattern(c));
+        std::vector<int32_t> prp, pci, pdg, kmap;
+        ilu1_pattern(n, c->h_rp, c->h_ci, prp, pci, pdg, kmap);
+        nnz_ilu = prp[n];
+        c->ilu_owns_pattern = true;
+        CPTR_TRY(dalloc_t(c, &c->ilu_rp, (size_t)n + 1));
+        CPTR_TRY(dalloc_t(c, &c->ilu_ci, (size_t)nnz_ilu));
+        CPTR_TRY(dalloc_t(c, &c->ilu_diag, (size_t)n));
+        // two spare doubles: the factorisation copies runs of blocks in 16-byte pieces rounded outwards
+        CPTR_TRY(dalloc_t(c, &c->LU, (size_t)nnz_ilu * BB + 2));
+        int32_t *dk = nullptr;
+        CPTR_TRY(dalloc_t(c, &dk, (size_t)nnz_ilu));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ilu_rp, prp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, st));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ilu_ci, pci.data(), sizeof(int32_t) * nnz_ilu, cudaMemcpyHostToDevice, st));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->ilu_diag, pdg.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(dk, kmap.data(), sizeof(int32_t) * nnz_ilu, cudaMemcpyHostToDevice, st));
+        (k_scatter_blocks<<<nblk(nnz_ilu * BB, 256), 256, 0, st>>>(nnz_ilu, BB, dk, c->A, c->LU), note_launch());
+        CPTR_CUDA_TRY(c, cudaStreamSynchronize(st));
+        dfree(dk);
+    } else {
+        // two spare doubles: the factorisation copies runs of blocks in 16-byte pieces rounded outwards
+        CPTR_TRY(dalloc_t(c, &c->LU, (size_t)c->nnzb * BB + 2));
+    }
+    if (fill) {
+    } else if (mc) {
         CPTR_TRY(host_pattern(c));
         rowmap = multicolour_order(n, c->h_rp, c->h_ci);
         std::vector<int32_t> inv(n), kmap(c->nnzb), prp(n + 1, 0), pci(c->nnzb), pdg(n, -1);
@@ -1985,11 +2062,12 @@ cptr_status ilu_setup(Ctx *c) {
     CPTR_CUDA_TRY(c, cudaGetLastError());
     dfree(kidx_f); dfree(kidx_b); dfree(kidx_d);
     dfree(inv_f); dfree(inv_b); dfree(levr_f); dfree(levr_b);
-    if (!mc && (c->o.ilu_sweep == 2 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 1))))
+    // the chunked and tiled schedules read the caller's pattern: natural order without fill only
+    if (!mc && !fill && (c->o.ilu_sweep == 2 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 1))))
         CPTR_TRY(cw_setup(c));
     // tiled sweeps: on a natural-order box, with the cached tile shape or the best modelled one
     c->tl_use = false;
-    if (!mc && (c->o.ilu_sweep == 4 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 3))) &&
+    if (!mc && !fill && (c->o.ilu_sweep == 4 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 3))) &&
         tile_grid(c)) {
         int Ty = 0, Tz = 0;
         auto it = c->tune_cache.find(ilu_tune_key(c) + 2);

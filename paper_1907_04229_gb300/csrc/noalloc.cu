@@ -63,6 +63,7 @@ cptr_status apply_static(Ctx *c, const double *r, double *z) {
     if (c->o.stage2 != CPTR_STAGE2_ILU0) return c->fail(CPTR_ESTATE, "ILU(0) was not set up");
     if (c->o.ilu_order != CPTR_ILU_NATURAL)
         return c->fail(CPTR_EINVAL, "cptr_apply_ilu_static supports the natural ILU ordering only");
+    if (c->o.ilu_fill != 0) return c->fail(CPTR_EINVAL, "cptr_apply_ilu_static supports ILU(0) only");
     if (!r || !z) return c->fail(CPTR_EINVAL, "r and z are required");
     const int64_t nb = (int64_t)c->n * c->b;
     if (nb > kStaticIluMax)

@@ -435,3 +435,39 @@ def test_decoupled_first_stage(name, decouple, stage1):
 def test_decoupling_rejected_with_the_block_preconditioner():
     with pytest.raises(cp.CptrError):
         cp.Solver(stage1="full", decouple="ti")
+
+
+# ------------------------------------------------------------------------------------------------
+# ILU(1) second stage
+@pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "medium", "line"])
+@pytest.mark.parametrize("sweep", ["levels", "paired"])
+def test_ilu1_apply_and_solve(name, sweep):
+    """Block ILU(1) (fill pattern and factors on the device path, the one-launch factorisation and
+    sweeps on the filled pattern) against the oracle's scalar ILU(1): applications to 1e-10, solves
+    iterations +-1 and 1e-8; CPR-AMG-ILU(1) as in the paper's comparisons."""
+    s, o, g = pair(name, ilu_fill=1, ilu_sweep=cp.ILU_SWEEP[sweep])
+    nb = s["n"] * s["b"]
+    r = synth.normal(55, nb)
+    z = torch.empty(nb, dtype=torch.float64, device="cuda")
+    cp.cptr_apply_ilu(g.ctx, dev(r), z)
+    assert relerr(host(z), o.ilu_apply(r)) <= 1e-10
+    check_solve(s, o, g, 1e-8)
+    s, o, g = pair(name, ilu_fill=1, ilu_sweep=cp.ILU_SWEEP[sweep], stage1=cp.STAGE1["cpr"])
+    check_solve(s, o, g, 1e-8)
+
+
+def test_ilu1_mixed_precision_solve():
+    s, o, g = pair("medium", ilu_fill=1, precision=1)
+    x, info = g.solve(dev(s["rhs"].reshape(-1)), 1e-8)
+    assert info["status"] == "CPTR_OK" and info["true_rel_res"] <= 1.05e-8
+
+
+def test_ilu1_rejected_where_unsupported():
+    with pytest.raises(cp.CptrError):
+        cp.Solver(ilu_fill=1, ilu_order="multicolor")
+    s, o, g = pair("ragged", ilu_fill=1)
+    nb = s["n"] * s["b"]
+    z = torch.empty(nb, dtype=torch.float64, device="cuda")
+    with pytest.raises(cp.CptrError) as e:
+        cp.cptr_apply_ilu_static(g.ctx, dev(synth.normal(5, nb)), z)
+    assert e.value.code == -1
