@@ -63,6 +63,9 @@ def parse():
     p.add_argument("--no-oracle-errors", action="store_true",
                    help="skip the oracle solutions of the three-phase and ensemble workloads (errors against "
                         "the FP64 oracle are then reported for the cptr200k forms only)")
+    p.add_argument("--no-mesh-study", action="store_true",
+                   help="skip the 2-D mesh-refinement study (Tables meshW, meshH, anisomeshW analogues)")
+    p.add_argument("--mesh-study-max-n", type=int, default=640)
     p.add_argument("--profile-steps", type=int, default=3,
                    help="steps of the separate pass that times kernel families with CUDA events")
     return p.parse_args()
@@ -414,6 +417,10 @@ def ours(args, rank, world, local_rank, oracle_jobs):
     if not args.no_ensemble:
         ens, ens_sols = ensemble(args, dev, stream, flush)
 
+    mesh = None
+    if not args.no_mesh_study:
+        mesh = mesh_study(args, dev, stream)
+
     cpu = None
     oracle_errors = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -473,7 +480,7 @@ def ours(args, rank, world, local_rank, oracle_jobs):
                "solve_dofs_per_s": round(dofs / (solve_ms / 1e3), 1),
                "true_rel_res": infos[-1]["true_rel_res"], "levels": [infos[-1]["levels_p"], infos[-1]["levels_T"]],
                "families": families, "roofline": roofline, "rooflines": lines, "variants": variants,
-               "three_phase": tp, "ensemble": ens, "errors_vs_fp64_oracle": oracle_errors,
+               "three_phase": tp, "ensemble": ens, "mesh_refinement": mesh, "errors_vs_fp64_oracle": oracle_errors,
                "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "launches_before_timed": launches0, "clocks": clk}
         print(json.dumps(out), flush=True)
@@ -588,6 +595,52 @@ def three_phase(args, dev, stream, flush):
         sols[name] = x.cpu().numpy().copy()
         Sv.close()
     return out, sols
+
+
+MESH_METHODS = (("CPR-AMG", dict(stage1="cpr")), ("CPR-AMG(TI)", dict(stage1="cpr", decouple="ti")),
+                ("CPR-AMG-ILU(1)", dict(stage1="cpr", ilu_fill=1)), ("CPTR-Block(AMG)", dict(stage1="full")),
+                ("CPTR-uAMG", dict(stage1="uamg")), ("CPTR-uAMG(TI)", dict(stage1="uamg", decouple="ti")))
+
+
+def mesh_study(args, dev, stream):
+    """The 2-D mesh-refinement study of Sec. 4.1.1 (Tables meshW, meshH, anisomeshW) on its synthetic
+    analogues (synth.mesh_refinement_case): for N = 20 .. 640 and the paper's six methods, one
+    Jacobian per case (the first Newton iterate of the first 10-day step), GMRES tolerance 1e-8 as in
+    Sec. 4, FP64; iterations and GPU set-up and solve times (CUDA events, one untimed run first)."""
+    import torch
+
+    import synth
+    import paper_1907_04229_gb300 as cp
+
+    out = {"tolerance": 1e-8, "note": "one Jacobian per case (first Newton iterate of the first 10-day step), "
+                                      "not the paper's average over Newton iterations of two steps"}
+    Ns = [n for n in (20, 40, 80, 160, 320, 640) if n <= args.mesh_study_max_n]
+    for kind in ("wells", "heaters", "aniso"):
+        res = {m: {} for m, _ in MESH_METHODS}
+        for N in Ns:
+            s = synth.mesh_refinement_case(kind, N).system()
+            d = {k: torch.as_tensor(np.ascontiguousarray(v), device=dev) for k, v in
+                 {"rp": s["row_ptr"], "ci": s["col_idx"], "vals": s["vals"].reshape(-1), "kind": s["unknown_kind"],
+                  "W": s["weights"].reshape(-1), "st": s["st"], "rhs": s["rhs"].reshape(-1)}.items()}
+            x = torch.empty(s["n"] * s["b"], dtype=torch.float64, device=dev)
+            for name, opts in MESH_METHODS:
+                S = cp.Solver(stream=stream, max_it=500, **opts)
+
+                def run():
+                    S.setup(s["n"], s["b"], d["rp"], d["ci"], d["vals"], d["kind"], d["W"], d["st"])
+                    return S.solve(d["rhs"], 1e-8, x=x)[1]
+
+                run()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = run()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                res[name][N] = {"iters": info["iters"], "status": info["status"], "setup_ms": round(info["setup_ms"], 2),
+                                "solve_ms": round(info["solve_ms"], 2), "step_ms": round(e0.elapsed_time(e1), 2)}
+                S.close()
+        out[kind] = res
+    return out
 
 
 def tp_dofs(tp):

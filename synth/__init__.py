@@ -423,6 +423,35 @@ def concat(systems) -> dict:
     return out
 
 
+def mesh_refinement_case(kind: str, N: int) -> Reservoir:
+    """The 2-D mesh-refinement workloads (Sec. 4.1.1, Tables meshW, meshH, anisomeshW) on synthetic
+    analogues: a 50 m x 50 m square on an N x N grid, represented as an x-z slice one metre thick
+    (nx = nz = N, ny = 1) with gravity off, so that the second direction's permeability can differ
+    (kind "aniso": 3e-13 m^2 along x, 3e-10 m^2 along the other direction; otherwise 3e-13 m^2
+    isotropic), porosity 0.2, initial S_w = 0.1 (S_o = 0.9) with the seeded perturbation, uniform
+    initial pressure (1 Pa of seeded noise keeps upwind directions generic), T = 300 K, dt = 10 days.  Six point sources, three on each of two opposite sides (rows N/4, N/2, 3N/4 of
+    columns 0 and N-1): kind "heaters" heats all six at 373.15 K (U = 100 W/K each); the well kinds
+    inject water at 3e-7 m^3/s and 373.15 K on one side and produce on the other (stated reading:
+    producers at a bottom-hole pressure 1 bar below the initial pressure, as the well model here has
+    no rate-controlled producer)."""
+    d = 50.0 / N
+    k_md = 3e-13 / MD_TO_M2
+    r = make_box(N, 1, N, d, 1.0, d, seed=61, sigma=0.0, mean_log=math.log(k_md), wells="none", gravity=False,
+                 kv_ratio=1000.0 if kind == "aniso" else 1.0, dt=10 * 86400.0, p_sigma=1.0)
+    r.x0[:, 0] = P0 + normal(64, N * N)          # uniform initial pressure (no gravity), 1 Pa noise
+    r.x0[:, 2] -= 0.1
+    rows = [N // 4, N // 2, (3 * N) // 4]
+    if kind == "heaters":
+        r.heaters = [(r.cell(x, 0, z), 100.0, 373.15) for x in (0, N - 1) for z in rows]
+    else:
+        wl = [(r.cell(0, 0, z), 0, 3e-7, 373.15) for z in rows]
+        for z in rows:
+            c = r.cell(N - 1, 0, z)
+            wl.append((c, 1, float(_wi(r.kh_md[c:c + 1], 1.0)[0]), float(r.x0[c, 0] - 1e5)))
+        r.wells = wl
+    return r
+
+
 def ensemble_sizes(count: int = 64, lo: float = 20e3, hi: float = 500e3, total: float = 4e6, nz: int = 10,
                    seed: int = 31):
     """Cell counts of an ensemble of ``count`` boxes with sizes in [lo, hi] summing to about

@@ -471,3 +471,21 @@ def test_ilu1_rejected_where_unsupported():
     with pytest.raises(cp.CptrError) as e:
         cp.cptr_apply_ilu_static(g.ctx, dev(synth.normal(5, nb)), z)
     assert e.value.code == -1
+
+
+# ------------------------------------------------------------------------------------------------
+# the 2-D mesh-refinement workloads (Sec. 4.1.1) with the paper's six methods
+MESH_METHODS = (dict(stage1="cpr"), dict(stage1="cpr", decouple="ti"), dict(stage1="cpr", ilu_fill=1),
+                dict(stage1="full"), dict(stage1="uamg"), dict(stage1="uamg", decouple="ti"))
+
+
+@pytest.mark.parametrize("kind", ["wells", "heaters", "aniso"])
+@pytest.mark.parametrize("N", [20, 40])
+def test_mesh_refinement_methods_match_oracle(kind, N):
+    s = synth.mesh_refinement_case(kind, N).system()
+    for opts in MESH_METHODS:
+        g = gpu_solver(s, **{k: (cp.STAGE1[v] if k == "stage1" else cp.DECOUPLE[v] if k == "decouple" else v)
+                             for k, v in opts.items()})
+        o = oracle.Oracle.from_system(s, **{k: (cp.STAGE1[v] if k == "stage1" else cp.DECOUPLE[v] if k == "decouple"
+                                                else v) for k, v in opts.items()})
+        check_solve(s, o, g, 1e-8)
