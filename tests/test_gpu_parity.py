@@ -489,3 +489,34 @@ def test_mesh_refinement_methods_match_oracle(kind, N):
         o = oracle.Oracle.from_system(s, **{k: (cp.STAGE1[v] if k == "stage1" else cp.DECOUPLE[v] if k == "decouple"
                                                 else v) for k, v in opts.items()})
         check_solve(s, o, g, 1e-8)
+
+
+# ------------------------------------------------------------------------------------------------
+# failure paths reached from the host, no GPU fault involved
+def test_singular_pivot_block_reports_esingular_and_context_recovers():
+    """A zero diagonal block in the first cell's row: ILU(0) meets a singular pivot block at set-up
+    (CPTR_ESINGULAR); the context then sets up and solves a valid system."""
+    s = system("ragged")
+    vals = s["vals"].copy()
+    rp, ci = s["row_ptr"], s["col_idx"]
+    k0 = [k for k in range(rp[0], rp[1]) if ci[k] == 0][0]
+    vals[k0] = 0.0
+    S = cp.Solver(stage1="none")
+    with pytest.raises(cp.CptrError) as e:
+        S.setup(s["n"], s["b"], rp, ci, vals.reshape(-1), s["unknown_kind"])
+    assert e.value.code == -6, e.value
+    S.setup(s["n"], s["b"], rp, ci, s["vals"].reshape(-1), s["unknown_kind"], s["weights"].reshape(-1), s["st"])
+    x, info = S.solve(np.ascontiguousarray(s["rhs"].reshape(-1)), 1e-8)
+    assert info["status"] == "CPTR_OK"
+
+
+def test_non_finite_rhs_reports_ebreakdown_and_context_recovers():
+    """A NaN in the right-hand side makes the Arnoldi process non-finite: CPTR_EBREAKDOWN; the next
+    solve of the same set-up converges."""
+    s, o, g = pair("ragged")
+    rhs = s["rhs"].reshape(-1).copy()
+    rhs[7] = np.nan
+    with pytest.raises(cp.CptrError) as e:
+        g.solve(dev(rhs), 1e-8)
+    assert e.value.code == -4, e.value
+    check_solve(s, o, g, 1e-8)
