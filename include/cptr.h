@@ -386,6 +386,69 @@ cptr_status cptr_mlp_infer(cptr_ctx *ctx, const double *feat, int32_t n, float *
  * Errors: CPTR_ESTATE, CPTR_EINVAL, CPTR_ECUDA. */
 cptr_status cptr_schur_scaling(cptr_ctx *ctx, double *s, int32_t on_device);
 
+/* ---------------------------------------------------------------------------------------------
+ * Newton's method around the solve (Sec. 3 eq. (AXR): every Newton iteration solves J dx = -R with
+ * the context's CPTR-FGMRES; Sec. 4: Newton with line search, tolerance 1e-8 on the relative
+ * function norm and on the relative step norm), with the residual, Jacobian and S_e assembled on
+ * the device for the thermal multiphase finite-volume model of Sec. 2 on an nx x ny x nz Cartesian
+ * box in natural cell order (x fastest).  Unknowns per cell (p, T, S_w[, S_g]) in Pa, K and
+ * fractions; raw equation rows water mass, energy, oil mass[, gas mass] (kg/s, W).  TPFA with
+ * harmonic K and k_T, arithmetic face density, phase upwinding on the potential difference (ties to
+ * the lower-index cell), implicit Euler; water density and viscosity by the correlations of
+ * Appendix A; oil density rho_o_ref exp(c_o (p - p0) - beta_o (T - T0)), oil viscosity
+ * mu_o_ref exp(-beta_mu (T - T0)), ideal gas of molar mass gas_M and viscosity mu_g; Corey k_r =
+ * max(S, 0)^corey_n; k_T = kT_const if > 0, else (1 - phi) kT_rock + phi sum_alpha S_alpha kT_alpha.
+ * Wells: kind 0 injects water at rate a (m^3/s) and temperature c (K); kind 1 produces each phase at
+ * q_alpha = a lam_alpha (p - c)^+ (a = WI in m^3, c = bottom-hole pressure).  Heaters add
+ * U (T_heater - T) to the energy equation.  S_e (eq. Se): the energy equation with every
+ * coefficient frozen at the iterate, differentiated in the explicit temperature factors only.
+ * --------------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t nx, ny, nz, nphase;   /* nphase 2 (b = 3) or 3 (b = 4) */
+    double dx, dy, dz;            /* cell sizes, m; depth grows with z */
+    double dt, phi, grav;         /* time step (s), porosity, gravity (m/s^2) */
+    const double *kh, *kv;        /* [n] permeability, m^2: x and y faces use kh, z faces kv */
+    double kT_const, kT_rock, kT_w, kT_o, kT_g;         /* W/m/K */
+    double cv_w, cv_o, cv_g, c_rock, rho_rock;          /* J/kg/K, kg/m^3 */
+    double mu_o_ref, beta_mu, T0, rho_o_ref, c_o, beta_o, p0;
+    double gas_M, mu_g, corey_n;
+    int32_t n_wells, n_heaters;
+    const int32_t *well_cell, *well_kind;   /* [n_wells] */
+    const double *well_a, *well_c;          /* [n_wells] */
+    const int32_t *heater_cell;             /* [n_heaters] */
+    const double *heater_U, *heater_T;      /* [n_heaters] W/K, K */
+    const double *weights;                  /* [n][b][b] equation weights W of the solve (NULL: identity) */
+} cptr_model;
+
+typedef struct {
+    int32_t newton_its, linear_its, line_search_cuts, converged;
+    double res0, res;             /* ||W R|| at the start and at the end */
+    double setup_ms, solve_ms;    /* summed over the Newton iterations */
+} cptr_newton_stats;
+
+/* Give the context a model (copied; its arrays host or device per on_device).  Errors: CPTR_EINVAL,
+ * CPTR_ENOMEM, CPTR_ECUDA. */
+cptr_status cptr_model_set(cptr_ctx *ctx, const cptr_model *model, int32_t on_device);
+
+/* Residual R(x) ([n][b] raw rows) of the implicit Euler step from xn to x, and if J / Se are not NULL
+ * the analytic Jacobian dR/dx ([nnzb][b][b], row-major blocks) and S_e ([nnzb]) on the 7-point
+ * pattern (rows in natural order, columns ascending).  One thread per cell gathers its rows: its
+ * accumulation terms, its wells and heaters in the caller's order, then its faces (i - nx ny, i),
+ * (i - nx, i), (i - 1, i), (i, i + 1), (i, i + nx), (i, i + nx ny), every product and sum rounded on
+ * its own.  Arrays host or device per on_device.  Errors: CPTR_ESTATE (no model), CPTR_EINVAL. */
+cptr_status cptr_assemble(cptr_ctx *ctx, const double *x, const double *xn, double *R, double *J, double *Se,
+                          int32_t on_device);
+
+/* One implicit Euler step from state xn by Newton's method, x in: the initial iterate, out: the
+ * solution ([n][b], host or device per on_device).  F(x) = ||W R(x)||_2.  Each iteration assembles
+ * J and S_e at x on the device, sets up the context's preconditioner on them (cptr_setup with the
+ * model's weights) and solves J dx = -R to rtol_lin (cptr_solve); then a backtracking line search:
+ * a = 1, 1/2, ... (at most 10 halvings) until F(x + a dx) <= (1 - 1e-4 a) F(x).  Converged when
+ * F <= 1e-8 F(x^0), or when ||a dx|| <= 1e-8 ||x|| with F not above F(x^0).  Returns CPTR_OK,
+ * CPTR_NOT_CONVERGED after max_newton iterations, or the errors of cptr_setup / cptr_solve. */
+cptr_status cptr_newton(cptr_ctx *ctx, double *x, const double *xn, double rtol_lin, int32_t max_newton,
+                        cptr_newton_stats *st, int32_t on_device);
+
 #ifdef __cplusplus
 }
 #endif

@@ -485,3 +485,54 @@ def learned_st(sys: dict, params32, base: str = "se"):
     s = np.sinh(y.astype(np.float64))
     rows = np.repeat(np.arange(sys["n"]), np.diff(sys["row_ptr"]))
     return B * s[rows], s, y
+
+
+def newton_step(reservoir, x, xn, rtol_lin=1e-8, max_newton=20, **opts):
+    """One implicit Euler step from state xn by Newton's method with a backtracking line search (Sec. 3
+    eq. (AXR), Sec. 4), the oracle's restatement of the library's cptr_newton: F(x) = ||W R(x)||_2
+    with the generator's residual (pinned by finite differences); each iteration solves
+    J dx = -R with the oracle's CPTR-FGMRES (Jacobian, S_e and weights of the generator) to
+    rtol_lin; a = 1, 1/2, ... (at most 10 halvings) until F(x + a dx) <= (1 - 1e-4 a) F(x);
+    converged when F <= 1e-8 F(x^0), or when ||a dx|| <= 1e-8 ||x|| with F <= F(x^0).
+    Returns (x, dict(newton_its, linear_its, line_search_cuts, converged, res0, res, per_iteration))."""
+    W = reservoir.weights()
+    n, b = reservoir.n, reservoir.b
+    x = np.array(x, dtype=np.float64).reshape(n, b)
+    xn = np.asarray(xn, dtype=np.float64).reshape(n, b)
+
+    def F(R):
+        return float(np.sqrt(np.sum(np.einsum("nij,nj->ni", W, R) ** 2)))
+
+    F0 = F(reservoir.evaluate(x, jacobian=False, schur=False, xn=xn)["R"])
+    Fx, tol = F0, 1e-8
+    out = dict(newton_its=0, linear_its=0, line_search_cuts=0, converged=False, res0=F0, per_iteration=[])
+    for it in range(max_newton):
+        if not Fx > tol * F0:
+            out["converged"] = True
+            break
+        ev = reservoir.evaluate(x, jacobian=True, schur=True, xn=xn)
+        o = Oracle(n, b, ev["row_ptr"], ev["col_idx"], ev["J"], W, st=ev["Se"], **opts)
+        dx, info = o.solve(-ev["R"].reshape(-1), rtol_lin)
+        dx = dx.reshape(n, b)
+        out["linear_its"] += info["iters"]
+        a, cut = 1.0, 0
+        while True:
+            xt = x + a * dx
+            Ft = F(reservoir.evaluate(xt, jacobian=False, schur=False, xn=xn)["R"])
+            if Ft <= (1.0 - 1e-4 * a) * Fx or cut >= 10:
+                break
+            a *= 0.5
+            cut += 1
+        out["line_search_cuts"] += cut
+        out["per_iteration"].append(dict(linear_its=info["iters"], alpha=a, res=Ft))
+        step, xnorm = a * np.linalg.norm(dx), np.linalg.norm(x)
+        x, Fx = xt, Ft
+        out["newton_its"] = it + 1
+        if step <= tol * xnorm:
+            out["converged"] = Fx <= F0
+            break
+    if not out["converged"] and not Fx > tol * F0:
+        out["converged"] = True
+    out["res"] = Fx
+    return x, out
+

@@ -55,6 +55,27 @@ class cptr_instance(ctypes.Structure):
                 ("vals", ctypes.c_void_p), ("row_weights", ctypes.c_void_p), ("st_vals", ctypes.c_void_p)]
 
 
+class cptr_model(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("nphase", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("dt", ctypes.c_double), ("phi", ctypes.c_double), ("grav", ctypes.c_double),
+                ("kh", ctypes.c_void_p), ("kv", ctypes.c_void_p)] + \
+        [(k, ctypes.c_double) for k in ("kT_const", "kT_rock", "kT_w", "kT_o", "kT_g", "cv_w", "cv_o", "cv_g",
+                                        "c_rock", "rho_rock", "mu_o_ref", "beta_mu", "T0", "rho_o_ref", "c_o",
+                                        "beta_o", "p0", "gas_M", "mu_g", "corey_n")] + \
+        [("n_wells", ctypes.c_int32), ("n_heaters", ctypes.c_int32), ("well_cell", ctypes.c_void_p),
+         ("well_kind", ctypes.c_void_p), ("well_a", ctypes.c_void_p), ("well_c", ctypes.c_void_p),
+         ("heater_cell", ctypes.c_void_p), ("heater_U", ctypes.c_void_p), ("heater_T", ctypes.c_void_p),
+         ("weights", ctypes.c_void_p)]
+
+
+class cptr_newton_stats(ctypes.Structure):
+    _fields_ = [("newton_its", ctypes.c_int32), ("linear_its", ctypes.c_int32),
+                ("line_search_cuts", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("res0", ctypes.c_double), ("res", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double)]
+
+
 class CptrError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
@@ -94,6 +115,9 @@ _SIGS = {
     "cptr_set_mlp": (_I, [_P, _P, _I]),
     "cptr_mlp_infer": (_I, [_P, _P, _I, _P, _I]),
     "cptr_schur_scaling": (_I, [_P, _P, _I]),
+    "cptr_model_set": (_I, [_P, _P, _I]),
+    "cptr_assemble": (_I, [_P, _P, _P, _P, _P, _P, _I]),
+    "cptr_newton": (_I, [_P, _P, _P, ctypes.c_double, _I, _P, _I]),
 }
 PROFILE_FAMILIES = ("spmv", "stage1", "stage1_resid", "ilu", "arnoldi", "ilu_fwd", "ilu_bwd", "_7")
 SETUP_PHASES = {8: "setup_inputs", 9: "setup_amg_coarsen", 10: "setup_amg_rap", 11: "setup_amg_coarsest",
@@ -349,6 +373,50 @@ def cptr_mlp_infer(ctx, feat, y):
 
 def cptr_schur_scaling(ctx, s):
     return _check(ctx, load().cptr_schur_scaling(ctx, _ptr(s), _on_device(s)))
+
+
+_MODEL_ARRAYS = {"kh": np.float64, "kv": np.float64, "well_cell": np.int32, "well_kind": np.int32,
+                 "well_a": np.float64, "well_c": np.float64, "heater_cell": np.int32, "heater_U": np.float64,
+                 "heater_T": np.float64, "weights": np.float64}
+
+
+def cptr_model_set(ctx, fields: dict):
+    """Marshal a model description (scalars and arrays; arrays all host numpy or all torch CUDA)
+    into cptr_model and hand it to the context."""
+    m = cptr_model()
+    keep = []
+    arrays = [fields.get(k) for k in _MODEL_ARRAYS]
+    on_dev = _on_device(*arrays)
+    for k, dt in _MODEL_ARRAYS.items():
+        a = fields.get(k)
+        if a is None:
+            continue
+        if not on_dev:
+            a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        count = a.numel() if hasattr(a, "numel") else a.size
+        setattr(m, k, _ptr(a) if count else None)
+    for k, t in cptr_model._fields_:
+        if k in _MODEL_ARRAYS or k in ("n_wells", "n_heaters"):
+            continue
+        setattr(m, k, fields[k])
+    m.n_wells = len(fields.get("well_cell", []))
+    m.n_heaters = len(fields.get("heater_cell", []))
+    return _check(ctx, load().cptr_model_set(ctx, ctypes.byref(m), on_dev))
+
+
+def cptr_assemble(ctx, x, xn, R, J=None, Se=None):
+    return _check(ctx, load().cptr_assemble(ctx, _ptr(x), _ptr(xn), _ptr(R), _ptr(J), _ptr(Se),
+                                            _on_device(x, xn, R, J, Se)))
+
+
+def cptr_newton(ctx, x, xn, rtol_lin, max_newton):
+    st = cptr_newton_stats()
+    code = _check(ctx, load().cptr_newton(ctx, _ptr(x), _ptr(xn), rtol_lin, max_newton, ctypes.byref(st),
+                                          _on_device(x, xn)), ok=(CPTR_OK, CPTR_NOT_CONVERGED))
+    return dict(status=STATUS.get(code, code), newton_its=st.newton_its, linear_its=st.linear_its,
+                line_search_cuts=st.line_search_cuts, converged=bool(st.converged), res0=st.res0, res=st.res,
+                setup_ms=st.setup_ms, solve_ms=st.solve_ms)
 
 
 class Solver:

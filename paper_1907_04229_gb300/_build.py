@@ -32,7 +32,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(pair):
         s, o = pair
-        cmd = [NVCC, *ARCH, *FLAGS, "-c", s, "-o", o]
+        # the model assembly rounds every product and sum on its own (no fused multiply-add)
+        extra = ["-fmad=false"] if os.path.basename(s) == "model.cu" else []
+        cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", s, "-o", o]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(s)}:\n{r.stderr}")

@@ -496,6 +496,7 @@ void cptr_destroy(cptr_ctx *ctx) {
         release_setup(c);
         dfree(c->ks); dfree(c->flag); dfree(c->partial); dfree(c->scan_tmp); dfree(c->never); dfree(c->ilu_flags);
         dfree(c->mlp);
+        model_free(c);
         cudaStreamSynchronize(c->stream);
     }
     if (c->pool) cudaMemPoolDestroy(c->pool);

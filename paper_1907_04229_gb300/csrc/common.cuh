@@ -242,6 +242,9 @@ void tile_free(Ctx *c);
 template <typename T, typename RT, typename XT>
 void tile_apply(const Ctx *c, const RT *r, double *z, const XT *dp, const XT *dT);   // both sweeps (after the fill)
 
+// ---- model.cu ----------------------------------------------------------------------------------
+void model_free(Ctx *c);
+
 // ---- krylov.cu ---------------------------------------------------------------------------------
 cptr_status fgmres_solve(Ctx *c, const double *bw, double *x, double rtol, cptr_stats *st);
 // ensemble (one block-diagonal set-up, FGMRES per instance): x and bw are union vectors
@@ -348,6 +351,7 @@ struct Ctx {
     double *bp = nullptr, *bT = nullptr, *xp = nullptr, *dp = nullptr, *dT = nullptr, *t1 = nullptr;
     double *b00 = nullptr, *x00 = nullptr;             // unknown-based AMG: [b_p; b_T], [d_p; d_T]
     double *Ddec = nullptr;                            // decoupling: D_i per cell, [n][2][b] (rows p, T)
+    void *model = nullptr;                             // the finite-volume model of the Newton loop (model.cu)
     float *b0032 = nullptr, *x0032 = nullptr;
     double *b1 = nullptr;
     // mixed-precision form: FP32 copies of the stage-1 operators and the stage-1 vectors

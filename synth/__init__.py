@@ -218,14 +218,15 @@ class Reservoir:
         lib.synth_pattern(ctypes.byref(P), _ptr(rp), _ptr(ci))
         return rp, ci
 
-    def evaluate(self, x: np.ndarray, jacobian: bool = True, schur: bool = True):
-        """Residual R(x) (raw rows), and optionally the Jacobian dR/dx (BSR) and S_e at x."""
+    def evaluate(self, x: np.ndarray, jacobian: bool = True, schur: bool = True, xn: np.ndarray = None):
+        """Residual R(x) (raw rows) of the step from xn (default: x0), and optionally the Jacobian
+        dR/dx (BSR) and S_e at x."""
         lib = _load()
         P, keep = self._struct()
         rp, ci = self.pattern()
         b = self.b
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(self.n, b)
-        xn = np.ascontiguousarray(self.x0, dtype=np.float64).reshape(self.n, b)
+        xn = np.ascontiguousarray(self.x0 if xn is None else xn, dtype=np.float64).reshape(self.n, b)
         R = np.zeros((self.n, b))
         J = np.zeros((ci.size, b, b)) if jacobian else None
         Se = np.zeros(ci.size) if schur else None
@@ -234,6 +235,26 @@ class Reservoir:
         if rc != 0:
             raise RuntimeError("synth_assemble: inconsistent pattern")
         return dict(R=R, J=J, Se=Se, row_ptr=rp, col_idx=ci)
+
+    def model_fields(self) -> dict:
+        """The model as the solver library's cptr_model describes it (SI units, permeabilities in
+        m^2, wells and heaters as arrays)."""
+        if self.thermal_props_off:
+            raise ValueError("the library's model has no property freeze")
+        w, h = self.wells, self.heaters
+        out = dict(nx=self.nx, ny=self.ny, nz=self.nz, nphase=self.nphase, dx=self.dx, dy=self.dy, dz=self.dz,
+                   dt=self.dt, phi=self.phi, grav=self.grav, kh=self.kh_md * MD_TO_M2, kv=self.kv_md * MD_TO_M2,
+                   well_cell=np.array([c for c, _, _, _ in w], np.int32),
+                   well_kind=np.array([k for _, k, _, _ in w], np.int32),
+                   well_a=np.array([a for _, _, a, _ in w], np.float64),
+                   well_c=np.array([cc for _, _, _, cc in w], np.float64),
+                   heater_cell=np.array([c for c, _, _ in h], np.int32),
+                   heater_U=np.array([u for _, u, _ in h], np.float64),
+                   heater_T=np.array([t for _, _, t in h], np.float64), weights=self.weights())
+        for name in ("kT_const", "kT_rock", "kT_w", "kT_o", "kT_g", "cv_w", "cv_o", "cv_g", "c_rock", "rho_rock",
+                     "mu_o_ref", "beta_mu", "T0", "rho_o_ref", "c_o", "beta_o", "p0", "gas_M", "mu_g", "corey_n"):
+            out[name] = float(getattr(self, name))
+        return out
 
     def weights(self) -> np.ndarray:
         """Per-cell equation weights W (b x b): decoupled row = W @ raw rows.

@@ -1018,3 +1018,22 @@ def test_ilu1_fewer_iterations_than_ilu0_for_cpr():
                        kT_const=2.0, T_inj=500.0, q_inj=1e-6, dt=30 * 86400.0).system()
     its = [oracle.Oracle.from_system(s, stage1=oracle.CPR, ilu_fill=f).solve(s["rhs"], 1e-8)[1]["iters"] for f in (0, 1)]
     assert its[1] < its[0], its
+
+
+# ------------------------------------------------------------------------------------------------
+# Newton's method around the solve (Sec. 3 eq. AXR, Sec. 4)
+def test_newton_oracle_solves_the_step_with_quadratic_convergence():
+    """The oracle's Newton step drives ||W R|| below 1e-8 of its start (the generator's residual,
+    pinned by finite differences, evaluated independently at the result), with full steps near the
+    solution and the error ratio of a quadratically convergent method."""
+    r = synth.make_box(8, 6, 3, 3.125, seed=17, heaters=[(11, 80.0, 420.0)])
+    x, info = oracle.newton_step(r, r.x0.copy(), r.x0, rtol_lin=1e-12)
+    assert info["converged"] and info["newton_its"] >= 3
+    W = r.weights()
+    R = r.evaluate(x, jacobian=False, schur=False)["R"]
+    assert np.linalg.norm(np.einsum("nij,nj->ni", W, R)) <= 1e-8 * info["res0"]
+    res = [info["res0"]] + [p["res"] for p in info["per_iteration"]]
+    assert all(p["alpha"] == 1.0 for p in info["per_iteration"][1:])
+    # quadratic: r_{k+1} / r_k^2 stays bounded while r_k falls by orders of magnitude
+    rat = [res[k + 1] / res[k] ** 2 for k in range(1, len(res) - 1)]
+    assert res[-2] / res[1] < 1e-3 and max(rat[1:]) <= 10 * rat[0] + 1e-30, (res, rat)
