@@ -63,6 +63,7 @@ def parse():
     p.add_argument("--no-oracle-errors", action="store_true",
                    help="skip the oracle solutions of the three-phase and ensemble workloads (errors against "
                         "the FP64 oracle are then reported for the cptr200k forms only)")
+    p.add_argument("--no-newton", action="store_true", help="skip the Newton time-stepping section")
     p.add_argument("--no-mesh-study", action="store_true",
                    help="skip the 2-D mesh-refinement study (Tables meshW, meshH, anisomeshW analogues)")
     p.add_argument("--mesh-study-max-n", type=int, default=640)
@@ -165,6 +166,13 @@ def oracle_job(kind, arg=None):
     if kind == "three_phase":
         s = synth.recipe("three_phase2m").system() if arg is None else synth.make_box(
             *arg, 1.0, 1.0, 0.5, seed=21, sigma=2.5, nphase=3, wells="four", T_inj=500.0, q_inj=4e-6).system()
+    elif kind == "newton":   # the first implicit Euler step of the Newton section, by the oracle's driver
+        import oracle
+        r = newton_reservoir()
+        t0 = time.perf_counter()
+        x, info = oracle.newton_step(r, r.x0.copy(), r.x0, NEWTON_RTOL)
+        secs = time.perf_counter() - t0
+        return secs, {k: v for k, v in info.items() if k != "per_iteration"}, x.reshape(-1)
     elif kind == "ensemble":
         total, k = arg
         shapes = synth.ensemble_sizes(total=total, lo=min(20e3, total / 64))
@@ -186,6 +194,8 @@ def start_oracle_jobs(args):
     pool = mp.get_context("spawn").Pool(processes=3)
     if not args.no_three_phase:
         jobs["three_phase"] = pool.apply_async(oracle_job, ("three_phase", args.three_phase_grid))
+    if not args.no_newton:
+        jobs["newton"] = pool.apply_async(oracle_job, ("newton",))
     if not args.no_ensemble:
         import synth
         shapes = synth.ensemble_sizes(total=args.ensemble_total, lo=min(20e3, args.ensemble_total / 64))
@@ -417,6 +427,10 @@ def ours(args, rank, world, local_rank, oracle_jobs):
     if not args.no_ensemble:
         ens, ens_sols = ensemble(args, dev, stream, flush)
 
+    newton = None
+    if not args.no_newton:
+        newton, newton_x = newton_section(args, dev, stream)
+
     mesh = None
     if not args.no_mesh_study:
         mesh = mesh_study(args, dev, stream)
@@ -444,6 +458,14 @@ def ours(args, rank, world, local_rank, oracle_jobs):
             tp["cpu_baseline"] = {"value": tp_dofs(tp) / osecs, "unit": UNIT, "cores": 1, "kind": "oracle",
                                   "sample": f"one full setup+solve by the serial FP64 C oracle, {osecs:.2f} s, "
                                             f"{oi['iters']} iterations (S_e), run in a worker process meanwhile"}
+        if newton is not None and "newton" in oracle_jobs:
+            osecs, oi, xo = oracle_jobs["newton"].get()
+            oracle_errors["newton_first_step"] = dict(errors_per_kind(newton_x, xo, b), oracle_newton_its=oi["newton_its"],
+                                                      oracle_linear_its=oi["linear_its"])
+            newton["cpu_baseline"] = {"value": round(osecs * 1e3, 1), "unit": "ms per time step", "cores": 1,
+                                      "kind": "oracle", "sample": f"the first time step by the oracle's Newton driver "
+                                      f"({oi['newton_its']} Newton, {oi['linear_its']} linear iterations), run in a "
+                                      "worker process meanwhile"}
         if ens is not None and "ensemble" in oracle_jobs:
             ee, osecs, ocells = {}, 0.0, 0
             for k, job in oracle_jobs["ensemble"].items():
@@ -480,7 +502,8 @@ def ours(args, rank, world, local_rank, oracle_jobs):
                "solve_dofs_per_s": round(dofs / (solve_ms / 1e3), 1),
                "true_rel_res": infos[-1]["true_rel_res"], "levels": [infos[-1]["levels_p"], infos[-1]["levels_T"]],
                "families": families, "roofline": roofline, "rooflines": lines, "variants": variants,
-               "three_phase": tp, "ensemble": ens, "mesh_refinement": mesh, "errors_vs_fp64_oracle": oracle_errors,
+               "three_phase": tp, "ensemble": ens, "newton": newton, "mesh_refinement": mesh,
+               "errors_vs_fp64_oracle": oracle_errors,
                "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "launches_before_timed": launches0, "clocks": clk}
         print(json.dumps(out), flush=True)
@@ -595,6 +618,57 @@ def three_phase(args, dev, stream, flush):
         sols[name] = x.cpu().numpy().copy()
         Sv.close()
     return out, sols
+
+
+NEWTON_RTOL, NEWTON_STEPS = 1e-8, 3
+
+
+def newton_reservoir():
+    """The Newton section's model: the cptr200k reservoir (100x100x20, layered permeability, 2 W/m/K,
+    500 K injector) with 30-day implicit Euler steps."""
+    import synth
+    r = synth.recipe("cptr200k")
+    r.dt = 30 * 86400.0
+    return r
+
+
+def newton_section(args, dev, stream):
+    """Three implicit Euler steps on the device (cptr_newton: assembly, CPTR-FGMRES with the headline
+    solver's options, line search), linear tolerance 1e-8 as in Sec. 4; per step the Newton and linear
+    iterations and the GPU time (CUDA events)."""
+    import torch
+
+    import paper_1907_04229_gb300 as cp
+
+    r = newton_reservoir()
+    S = cp.Solver(stream=stream, autotune=1)
+    cp.cptr_model_set(S.ctx, {k: (torch.as_tensor(np.ascontiguousarray(v), device=dev) if isinstance(v, np.ndarray)
+                                  else v) for k, v in r.model_fields().items()})
+    x = torch.as_tensor(np.ascontiguousarray(r.x0.reshape(-1)), device=dev)
+    warm = x.clone()
+    cp.cptr_newton(S.ctx, warm, x.clone(), NEWTON_RTOL, 20)   # tunes the launch shapes (cached)
+    steps = []
+    first_x = None
+    for k in range(NEWTON_STEPS):
+        xn = x.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = cp.cptr_newton(S.ctx, x, xn, NEWTON_RTOL, 20)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if k == 0:
+            first_x = x.cpu().numpy().copy()
+        steps.append({"step_ms": round(e0.elapsed_time(e1), 2), "newton_its": info["newton_its"],
+                      "linear_its": info["linear_its"], "line_search_cuts": info["line_search_cuts"],
+                      "status": info["status"], "res0": info["res0"], "res": info["res"],
+                      "setup_ms": round(info["setup_ms"], 2), "solve_ms": round(info["solve_ms"], 2)})
+    S.close()
+    total_ms = sum(t["step_ms"] for t in steps)
+    return {"workload": "cptr200k model (100x100x20, 600k dofs) with 30-day implicit Euler steps; Newton with "
+                        "backtracking line search, tolerance 1e-8 (function and step norms), CPTR-FGMRES to 1e-8",
+            "steps": steps, "ms_per_time_step": round(total_ms / NEWTON_STEPS, 2),
+            "newton_its_per_step": sum(t["newton_its"] for t in steps) / NEWTON_STEPS,
+            "linear_its_per_newton": sum(t["linear_its"] for t in steps) / max(1, sum(t["newton_its"] for t in steps))}, first_x
 
 
 MESH_METHODS = (("CPR-AMG", dict(stage1="cpr")), ("CPR-AMG(TI)", dict(stage1="cpr", decouple="ti")),
