@@ -1207,8 +1207,13 @@ Shape pick_shape(Ctx *c, uint64_t key, F &&launch) {
     return best;
 }
 
+// operators of about the same size and row length share a tuning (rows in steps of ~9%, average
+// row length in steps of ~19%), so that the set-ups of a Newton loop, whose coarse levels change size
+// slightly from one Jacobian to the next, reuse the first set-up's shapes
 uint64_t tune_key(int kind, const Csr &A, int st) {
-    return (uint64_t)kind << 60 | (uint64_t)st << 56 | ((uint64_t)A.n & 0xFFFFFFull) << 32 | (uint64_t)(uint32_t)A.nnz;
+    const double n = A.n > 0 ? (double)A.n : 1.0, avg = A.nnz > 0 ? (double)A.nnz / n : 1.0;
+    const uint64_t nb = (uint64_t)llround(8.0 * log2(n)), ab = (uint64_t)llround(4.0 * log2(avg) + 64.0);
+    return (uint64_t)kind << 60 | (uint64_t)st << 56 | (nb & 0xFFFFull) << 16 | (ab & 0xFFFFull);
 }
 
 template <typename VT, typename XT>
