@@ -81,6 +81,8 @@ VARIANTS = {
     "cptr_fp64_autotuned": dict(autotune=1),
     "cptr_mixed_autotuned": dict(precision="mixed", autotune=1),
 }
+# the variant whose kernels get roofline lines of their own ("..._mixed")
+MIXED_PROFILED = "cptr_mixed_autotuned"
 
 
 def peaks():
@@ -219,12 +221,14 @@ def errors_per_kind(xg, xo, b):
 FP64_PEAK_TFLOPS = 1.258
 
 
-def algorithmic_bytes(s):
-    """Bytes each kernel must move once per launch (FP64 values, int32 indices):
-    spmv: blocks (b*b values + column) + chunk offsets + z read + w written;
-    stage1_resid: the p and T columns of every block (2b values + column) + v read + b1 written
-    + dp, dT read; ilu_fwd: L blocks + columns + positions + r read + y written; ilu_bwd: U blocks +
-    columns + inverted pivot blocks + positions (2) + y read + z and out written + dp, dT read."""
+def algorithmic_bytes(s, mixed=False):
+    """Bytes each kernel must move once per launch (int32 indices; FP64 values and vectors, or in
+    the mixed form FP32 values of the preconditioner and FP32 vectors inside it):
+    spmv: blocks (b*b values + column) + chunk offsets + z read + w written (FP64 in both forms);
+    stage1_resid: the p and T columns of every block (2b values + column) + chunk offsets + v read
+    (FP64) + b1 written + dp, dT read; ilu_fwd: L blocks + columns + positions + r read + y
+    written; ilu_bwd: U blocks + columns + inverted pivot blocks + positions (2) + y read + the
+    intermediate written + z written (FP64) + dp, dT read."""
     n, b = s["n"], s["b"]
     rp, ci = s["row_ptr"], s["col_idx"]
     nnzb = int(rp[-1])
@@ -232,11 +236,102 @@ def algorithmic_bytes(s):
     lower = int((ci < rows).sum())
     upper = nnzb - n - lower
     chunks = (n + 31) // 32
-    vec = n * b * 8
-    return {"spmv": nnzb * (8 * b * b + 4) + (chunks + 1) * 8 + 2 * vec,
-            "stage1_resid": nnzb * (8 * 2 * b + 4) + (chunks + 1) * 8 + 2 * vec + 2 * n * 8,
-            "ilu_fwd": lower * (8 * b * b + 4) + n * 4 + 2 * vec,
-            "ilu_bwd": upper * (8 * b * b + 4) + n * 8 * b * b + n * 8 + 3 * vec + 2 * n * 8}
+    nb = n * b
+    f = 4 if mixed else 8   # preconditioner values and inner vectors
+    return {"spmv": nnzb * (8 * b * b + 4) + (chunks + 1) * 8 + 2 * nb * 8,
+            "stage1_resid": nnzb * (f * 2 * b + 4) + (chunks + 1) * 8 + nb * 8 + nb * f + 2 * n * f,
+            "ilu_fwd": lower * (f * b * b + 4) + n * 4 + 2 * nb * f,
+            "ilu_bwd": upper * (f * b * b + 4) + n * f * b * b + n * 8 + 2 * nb * f + nb * 8 + 2 * n * f}
+
+
+VC_STEPS = {"down": "k_vc_down (pre-smoothing from zero + residual, t = D^-1 b, r = b - A t)",
+            "restrict": "k_csr_spmv (restriction b_c = P^T r)",
+            "prolong": "k_csr_spmv (prolongation t += P x_c)",
+            "post": "k_vc_post (post-smoothing x = t + D^-1 (b - A t))"}
+
+
+def vcycle_bytes(info, f):
+    """Algorithmic bytes of the finest level's four V-cycle kernels from the level sizes (n rows,
+    nnz of A, nnz of P, nc coarse rows), f = bytes per value and per vector entry (8 in FP64; 4 in
+    the mixed form, whose finest level is FP32): down reads A (values + columns + row pointers),
+    D^-1 and b, writes t and r; restrict reads P^T and r, writes b_c; prolong reads P and x_c,
+    reads and writes t; post reads A, D^-1, b and t, writes x."""
+    n, nnz, nnzp = info[0]["n"], info[0]["nnz"], info[0]["nnzP"]
+    nc = info[1]["n"]
+    return {"down": nnz * (4 + f) + 4 * (n + 1) + 4 * f * n,
+            "restrict": nnzp * (4 + f) + 4 * (nc + 1) + f * n + f * nc,
+            "prolong": nnzp * (4 + f) + 4 * (n + 1) + f * nc + 2 * f * n,
+            "post": nnz * (4 + f) + 4 * (n + 1) + 4 * f * n}
+
+
+def roofline_line(kernel, alg, ms_tot, cnt, steps, peak, peak_kind, traffic=None):
+    avg_ms = ms_tot / max(cnt, 1)
+    achieved = alg / (avg_ms / 1e3) / 1e9
+    return {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+            "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "algorithmic_bytes_per_launch": int(alg), "avg_launch_us": round(avg_ms * 1e3, 2),
+            "launches_per_step": cnt / steps, "ms_per_step": round(ms_tot / steps, 3)}
+
+
+def family_kernels(cp, S, b, mixed):
+    """Kernel names of the profiled families of solver S (from its ILU schedule)."""
+    sched = [t for t in cp.cptr_tuning(S.ctx) if t[2] == 5][0][3]
+    t = "float" if mixed else "double"
+    sweep = {0: "level sets", 1: "chunked wavefront", 2: "paired levels", 3: "tiled"}[sched]
+    four = sched == 2 or (sched == 0 and not mixed)
+    how = sweep + (", a row over 4 lanes" if four else "")
+    if sched == 1:
+        fwd, bwd = f"k_ilu_cw<{b},{t},...,FWD>", f"k_ilu_cw<{b},{t},...,BWD>"
+    elif sched == 3:
+        fwd, bwd = f"k_ilu_tile<{b},{t},...,FWD>", f"k_ilu_tile<{b},{t},...,BWD>"
+    elif four:
+        fwd, bwd = f"k_ilu_fwd_g<{b},{t},...>", f"k_ilu_bwd_g<{b},{t},...>"
+    else:
+        fwd, bwd = f"k_ilu_fwd_sf<{b},{t},...>", f"k_ilu_bwd_sf<{b},{t},...>"
+    return {"spmv": f"k_sell_spmv<{b},0> (outer w = A' z_j, FP64)",
+            "stage1_resid": (f"k_sell_resid_pt32<{b}> (stage-1 residual, FP32 values)" if mixed else
+                             f"k_sell_spmv<{b},2> (stage-1 residual)"),
+            "ilu_fwd": f"{fwd} (forward ILU(0) sweep, {how})",
+            "ilu_bwd": f"{bwd} (backward ILU(0) sweep, {how})"}, sched
+
+
+def vcycle_lines(cp, S, vc_sum, steps, peak, peak_kind, mixed, suffix, traffic=None):
+    """Roofline lines of the finest level's V-cycle kernels of both hierarchies."""
+    lines = {}
+    f = 4 if mixed else 8
+    vt = "float" if mixed else "double"
+    for h, which in (("p", 0), ("T", 1)):
+        if vc_sum.get(f"{h}_down", (0.0, 0))[1] == 0:
+            continue
+        info = cp.cptr_hierarchy_info(S.ctx, which)
+        if len(info) < 2:
+            continue
+        alg = vcycle_bytes(info, f)
+        for k, desc in VC_STEPS.items():
+            ms_tot, cnt = vc_sum[f"{h}_{k}"]
+            name = f"vcycle_{h}_{k}{suffix}"
+            lines[name] = roofline_line(f"{desc.split(' ', 1)[0]}<..., {vt}> {desc.split(' ', 1)[1]}, finest level of "
+                                        f"the {'pressure' if h == 'p' else 'temperature'} hierarchy "
+                                        f"({info[0]['n']} rows, {info[0]['nnz']} entries)",
+                                        alg[k], ms_tot, cnt, steps, peak, peak_kind,
+                                        (traffic or {}).get(name))
+    return lines
+
+
+def profiled_pass(cp, S, step, flush, steps, mask):
+    """Steps with CUDA events around the families and kernels that `mask` selects; summed times."""
+    cp.cptr_set_profiling(S.ctx, mask)
+    fam, vc = {}, {}
+    for _ in range(steps):
+        flush.zero_()
+        step()
+        for src, dst in ((cp.cptr_profile(S.ctx), fam), (cp.cptr_profile_vcycle(S.ctx), vc)):
+            for k, (ms, cnt) in src.items():
+                acc = dst.setdefault(k, [0.0, 0])
+                acc[0] += ms
+                acc[1] += cnt
+    cp.cptr_set_profiling(S.ctx, 0)
+    return fam, vc
 
 
 def ours(args, rank, world, local_rank, oracle_jobs):
@@ -319,27 +414,17 @@ def ours(args, rank, world, local_rank, oracle_jobs):
     # (largest total time) is reported as "roofline"
     peak, peak_kind = peaks()
     alg = algorithmic_bytes(s)
-    schedule = [t for t in cp.cptr_tuning(S.ctx) if t[2] == 5][0][3]
+    kernels, schedule = family_kernels(cp, S, b, False)
     chunked, paired = schedule == 1, schedule == 2
-    kernels = {"spmv": "k_sell_spmv<3,0> (outer w = A' z_j)", "stage1_resid": "k_sell_spmv<3,2> (stage-1 residual)",
-               "ilu_fwd": ("k_ilu_cw<3,...,FWD> (forward ILU(0) sweep, chunked wavefront)" if chunked else
-                           "k_ilu_fwd_g<3> (forward ILU(0) sweep, %s, a row over 4 lanes)"
-                           % ("paired levels" if paired else "level sets")),
-               "ilu_bwd": ("k_ilu_cw<3,...,BWD> (backward ILU(0) sweep, chunked wavefront)" if chunked else
-                           "k_ilu_bwd_g<3> (backward ILU(0) sweep, %s, a row over 4 lanes)"
-                           % ("paired levels" if paired else "level sets"))}
     lines = {}
     for fam, kname in kernels.items():
         ms_tot, cnt = prof_sum[fam]
-        avg_ms = ms_tot / max(cnt, 1)
-        achieved = alg[fam] / (avg_ms / 1e3) / 1e9
-        lines[fam] = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                      "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                      "traffic": (PROFILED_TRAFFIC.get(fam) if not fam.startswith("ilu") or
-                                  (paired and PROFILED_ILU_SCHEDULE == "paired") else None),
-                      "algorithmic_bytes_per_launch": alg[fam], "avg_launch_us": round(avg_ms * 1e3, 2),
-                      "launches_per_step": cnt / args.profile_steps,
-                      "ms_per_step": round(ms_tot / args.profile_steps, 3)}
+        lines[fam] = roofline_line(kname, alg[fam], ms_tot, cnt, args.profile_steps, peak, peak_kind,
+                                   PROFILED_TRAFFIC.get(fam) if not fam.startswith("ilu") or
+                                   (paired and PROFILED_ILU_SCHEDULE == "paired") else None)
+    # the finest level's V-cycle kernels, timed one by one in a pass of their own
+    _, vc_sum = profiled_pass(cp, S, step, flush, args.profile_steps, cp.PROFILE_MASK_VCYCLE)
+    lines.update(vcycle_lines(cp, S, vc_sum, args.profile_steps, peak, peak_kind, False, "", PROFILED_TRAFFIC))
     # FP64 ALU view of the SpMV: 9 FMA per 3x3 block (2 flop each) against 1.258 TFLOP/s
     # (152 SMs x 2.07 GHz x 2 FP64 FMA/clk x 2)
     spmv_flops = 2 * b * b * nnzb
@@ -353,7 +438,9 @@ def ours(args, rank, world, local_rank, oracle_jobs):
         roofline["note"] = ((f"latency bound: a dependency chain of {ilu_levels} level sets per sweep, "
                              f"run as {(ilu_levels + 1) // 2} steps of paired levels" if paired else
                              f"latency bound: a dependency chain of {ilu_levels} level sets per sweep")
-                            + ("; DRAM traffic equals the algorithmic bytes" if roofline["traffic"] else ""))
+                            + (f"; DRAM traffic {roofline['traffic'] / roofline['algorithmic_bytes_per_launch']:.2f}x "
+                               "the algorithmic ILU(0) bytes (the paired tables hold the substituted blocks)"
+                               if roofline["traffic"] and paired else ""))
     families = {k: {"ms_per_step": round(v[0] / args.profile_steps, 3),
                     "regions_per_step": v[1] / args.profile_steps} for k, v in prof_sum.items()}
     families["note"] = (f"separate pass of {args.profile_steps} steps with CUDA events around every kernel family "
@@ -415,6 +502,16 @@ def ours(args, rank, world, local_rank, oracle_jobs):
                               "solve_ms": round(statistics.mean(i["solve_ms"] for i in infs), 3),
                               "iters": infs[-1]["iters"], "true_rel_res": infs[-1]["true_rel_res"],
                               "status": infs[-1]["status"]}
+            if name == MIXED_PROFILED:
+                # the mixed form's kernels: families and the finest V-cycle level, one profiled pass
+                fam, vc = profiled_pass(cp, Sv, step_v, flush, args.profile_steps, 0xFF)
+                kern, _ = family_kernels(cp, Sv, b, True)
+                alg_m = algorithmic_bytes(s, mixed=True)
+                for f in ("stage1_resid", "ilu_fwd", "ilu_bwd"):
+                    lines[f + "_mixed"] = roofline_line(kern[f], alg_m[f], *fam[f], args.profile_steps, peak,
+                                                        peak_kind, PROFILED_TRAFFIC.get(f + "_mixed"))
+                lines.update(vcycle_lines(cp, Sv, vc, args.profile_steps, peak, peak_kind, True, "_mixed",
+                                          PROFILED_TRAFFIC))
             Sv.close()
 
     tp = None
@@ -422,7 +519,8 @@ def ours(args, rank, world, local_rank, oracle_jobs):
         del flush
         torch.cuda.empty_cache()
         flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-        tp, tp_sols = three_phase(args, dev, stream, flush)
+        tp, tp_sols, tp_lines = three_phase(args, dev, stream, flush)
+        lines.update(tp_lines)
     ens = None
     if not args.no_ensemble:
         ens, ens_sols = ensemble(args, dev, stream, flush)
@@ -567,10 +665,13 @@ def three_phase(args, dev, stream, flush):
         s = synth.recipe("three_phase2m").system()
     n, b = s["n"], s["b"]
     dofs = n * b
+    alg = algorithmic_bytes(s)
     d = {k: torch.as_tensor(np.ascontiguousarray(v), device=dev) for k, v in
          {"rp": s["row_ptr"], "ci": s["col_idx"], "vals": s["vals"].reshape(-1), "kind": s["unknown_kind"],
           "W": s["weights"].reshape(-1), "st": s["st"], "rhs": s["rhs"].reshape(-1)}.items()}
     del s
+    peak, peak_kind = peaks()
+    lines = {}
     x = torch.empty(dofs, dtype=torch.float64, device=dev)
     sols = {}
     out = {"dofs": dofs,
@@ -616,8 +717,18 @@ def three_phase(args, dev, stream, flush):
                      "status": infs[-1]["status"], "schur_used": infs[-1]["schur_used"],
                      "learned_setup_ms": round(prof["setup_other"][0], 3), "timed_runs": nrun}
         sols[name] = x.cpu().numpy().copy()
+        if name == "fp64_se":
+            # b = 4 kernels on a working set far above L2: families and the finest V-cycle level
+            fam, vc = profiled_pass(cp, Sv, step_v, flush, 1, 0xFF)
+            kern, _ = family_kernels(cp, Sv, b, False)
+            for f in ("spmv", "stage1_resid", "ilu_fwd", "ilu_bwd"):
+                lines[f + "_b4"] = roofline_line(kern[f], alg[f], *fam[f], 1, peak, peak_kind,
+                                                 PROFILED_TRAFFIC.get(f + "_b4"))
+            lines.update(vcycle_lines(cp, Sv, vc, 1, peak, peak_kind, False, "_b4", PROFILED_TRAFFIC))
         Sv.close()
-    return out, sols
+    out["rooflines_note"] = ("the b = 4 lines of the top-level rooflines come from the fp64_se solve of this "
+                             "workload (one profiled step)")
+    return out, sols, lines
 
 
 NEWTON_RTOL, NEWTON_STEPS = 1e-8, 3

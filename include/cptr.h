@@ -271,7 +271,8 @@ int64_t cptr_launch_count(void);
  * of mask enables family f: 0 the outer SpMV w = A' z_j (one kernel per region), 1 stage 1,
  * 2 the stage-1 residual v - A' x1 (one kernel), 3 the ILU(0) solve (three kernels), 4 Arnoldi
  * (three Gram-Schmidt passes, Givens, normalisation), 5 the forward ILU sweep (one kernel),
- * 6 the backward ILU sweep (one kernel).  0 disables (the default). */
+ * 6 the backward ILU sweep (one kernel); bit 7 times each kernel of the finest level of the
+ * V-cycles one by one (read by cptr_profile_vcycle).  0 disables (the default). */
 cptr_status cptr_set_profiling(cptr_ctx *ctx, uint32_t mask);
 
 /* Event time (ms) and number of timed regions per family during the last cptr_solve (host
@@ -281,6 +282,16 @@ cptr_status cptr_set_profiling(cptr_ctx *ctx, uint32_t mask);
  * 11 AMG coarsest inverses, 12 ILU host work (ordering, level sets, sweep tables), 13 ILU
  * factorisation, 14 SELL layout and mixed-precision copies, 15 other. */
 cptr_status cptr_profile(cptr_ctx *ctx, double *ms, int64_t *count);
+
+/* Event time (ms) and number of launches of the finest AMG level's V(1,1)-cycle kernels during the
+ * last cptr_solve with bit 7 of the profiling mask set (host arrays of 8 entries; either may be
+ * NULL).  Entry 4*h + k: hierarchy h (0 the pressure hierarchy, or the p-T one of the
+ * unknown-based first stage; 1 the temperature hierarchy of S~_T), kernel k: 0 pre-smoothing from
+ * zero fused with the residual (t = D^-1 b, r = b - A t), 1 restriction b_c = P^T r,
+ * 2 prolongation t += P x_c, 3 post-smoothing x = t + D^-1 (b - A t) (Sec. 3.3: the V-cycles of
+ * the first stage).  A fine level whose kernels are fused with the coarse ones (at most a few
+ * hundred rows) is not timed. */
+cptr_status cptr_profile_vcycle(cptr_ctx *ctx, double *ms, int64_t *count);
 
 /* ---------------------------------------------------------------------------------------------
  * Ensemble: many independent Jacobians (realisations of a model, of uneven sizes) set up and

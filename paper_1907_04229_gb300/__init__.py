@@ -106,6 +106,7 @@ _SIGS = {
     "cptr_inject_wait_timeout": (_I, [_P, _I]),
     "cptr_set_profiling": (_I, [_P, ctypes.c_uint32]),
     "cptr_profile": (_I, [_P, _P, _P]),
+    "cptr_profile_vcycle": (_I, [_P, _P, _P]),
     "cptr_setup_batch": (_I, [_P, _I, _I, _P, _P, _I]),
     "cptr_tuning": (_I, [_P, _P, _I, _P]),
     "cptr_solve_batch": (_I, [_P, _P, _P, ctypes.c_double, _P, _I]),
@@ -120,6 +121,8 @@ _SIGS = {
     "cptr_newton": (_I, [_P, _P, _P, ctypes.c_double, _I, _P, _I]),
 }
 PROFILE_FAMILIES = ("spmv", "stage1", "stage1_resid", "ilu", "arnoldi", "ilu_fwd", "ilu_bwd", "_7")
+PROFILE_VCYCLE = tuple(f"{h}_{k}" for h in ("p", "T") for k in ("down", "restrict", "prolong", "post"))
+PROFILE_MASK_VCYCLE = 1 << 7
 SETUP_PHASES = {8: "setup_inputs", 9: "setup_amg_coarsen", 10: "setup_amg_rap", 11: "setup_amg_coarsest",
                 12: "setup_ilu_host", 13: "setup_ilu_factor", 14: "setup_layout", 15: "setup_other"}
 
@@ -302,6 +305,14 @@ def cptr_profile(ctx):
     for i, name in SETUP_PHASES.items():
         out[name] = (float(ms[i]), int(cnt[i]))
     return out
+
+
+def cptr_profile_vcycle(ctx):
+    """{"p_down": (ms, launches), ...}: the finest level's V-cycle kernels of the last solve."""
+    ms = np.zeros(8)
+    cnt = np.zeros(8, np.int64)
+    _check(ctx, load().cptr_profile_vcycle(ctx, ms.ctypes.data, cnt.ctypes.data))
+    return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(PROFILE_VCYCLE)}
 
 
 # ------------------------------------------------------------------------------------------------

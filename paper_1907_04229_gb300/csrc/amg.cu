@@ -971,20 +971,33 @@ template <> struct LevelVecs<float> {
     static float *r(const Level &L) { return L.r32; }
 };
 
-// one smoothing/residual/transfer step of level L with its matrix values in storage VT
+// one smoothing/residual/transfer step of level L with its matrix values in storage VT; pf >= 0
+// times each kernel as profiling family pf + step (the fine level only)
 template <typename VT, typename XT>
-static void level_down(cudaStream_t s, const Level &L, const Level &C, const VT *Av, const VT *PTv, const XT *b) {
+static void level_down(const Ctx *c, int pf, const Level &L, const Level &C, const VT *Av, const VT *PTv,
+                       const XT *b) {
     using LV = LevelVecs<XT>;
+    cudaStream_t s = c->stream;
+    int ev = pf < 0 ? -1 : prof_begin(c, pf);
     launch_down<VT, XT>(s, L, Av, LV::dinv(L), b, LV::t(L), LV::r(L));             // t = D^-1 b, r = b - A t
+    prof_end(c, ev);
+    ev = pf < 0 ? -1 : prof_begin(c, pf + 1);
     launch_csr_spmv_t<VT, XT>(s, L.PT.n, L.PT.nnz, L.PT.rp, L.PT.ci, PTv, LV::r(L), LV::b(C), 0, nullptr,
                               L.sh_PT);                                                        // b_c = P^T r
+    prof_end(c, ev);
 }
 template <typename VT, typename XT>
-static void level_up(cudaStream_t s, const Level &L, const Level &C, const VT *Av, const VT *Pv, const XT *b, XT *x) {
+static void level_up(const Ctx *c, int pf, const Level &L, const Level &C, const VT *Av, const VT *Pv, const XT *b,
+                     XT *x) {
     using LV = LevelVecs<XT>;
+    cudaStream_t s = c->stream;
+    int ev = pf < 0 ? -1 : prof_begin(c, pf + 2);
     launch_csr_spmv_t<VT, XT>(s, L.P.n, L.P.nnz, L.P.rp, L.P.ci, Pv, LV::x(C), LV::t(L), 2, nullptr,
                               L.sh_P);                                                         // t += P x_c
+    prof_end(c, ev);
+    ev = pf < 0 ? -1 : prof_begin(c, pf + 3);
     launch_post<VT, XT>(s, L, Av, LV::dinv(L), b, LV::t(L), x);                     // x = t + D^-1 (b - A t)
+    prof_end(c, ev);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1125,18 +1138,19 @@ static void vcycle_level(const Ctx *c, const Hier &h, int l, const XT *b, XT *x)
         return;
     }
     const Level &C = h.L[l + 1];
+    const int pf = l == 0 ? PF_VC + 4 * (&h == &c->hT) : -1;
     if (!lo) {
-        level_down<double, double>(s, L, C, L.A.v, L.PT.v, (const double *)b);
+        level_down<double, double>(c, pf, L, C, L.A.v, L.PT.v, (const double *)b);
         vcycle_level<XT>(c, h, l + 1, LV::b(C), LV::x(C));
-        level_up<double, double>(s, L, C, L.A.v, L.P.v, (const double *)b, (double *)x);
+        level_up<double, double>(c, pf, L, C, L.A.v, L.P.v, (const double *)b, (double *)x);
     } else if (L.st == ST_BF16) {
-        level_down<bf16, float>(s, L, C, (const bf16 *)L.Av_lo, (const bf16 *)L.PTv_lo, (const float *)b);
+        level_down<bf16, float>(c, pf, L, C, (const bf16 *)L.Av_lo, (const bf16 *)L.PTv_lo, (const float *)b);
         vcycle_level<XT>(c, h, l + 1, LV::b(C), LV::x(C));
-        level_up<bf16, float>(s, L, C, (const bf16 *)L.Av_lo, (const bf16 *)L.Pv_lo, (const float *)b, (float *)x);
+        level_up<bf16, float>(c, pf, L, C, (const bf16 *)L.Av_lo, (const bf16 *)L.Pv_lo, (const float *)b, (float *)x);
     } else {
-        level_down<float, float>(s, L, C, (const float *)L.Av_lo, (const float *)L.PTv_lo, (const float *)b);
+        level_down<float, float>(c, pf, L, C, (const float *)L.Av_lo, (const float *)L.PTv_lo, (const float *)b);
         vcycle_level<XT>(c, h, l + 1, LV::b(C), LV::x(C));
-        level_up<float, float>(s, L, C, (const float *)L.Av_lo, (const float *)L.Pv_lo, (const float *)b, (float *)x);
+        level_up<float, float>(c, pf, L, C, (const float *)L.Av_lo, (const float *)L.Pv_lo, (const float *)b, (float *)x);
     }
 }
 

@@ -709,10 +709,20 @@ cptr_status cptr_profile(cptr_ctx *ctx, double *ms, int64_t *count) {
         for (int f = 0; f < 16; ++f) {
             double m = 0.0;
             int64_t n = 0;
-            if (f < PF_N) { m = c->prof.ms[f]; n = c->prof.cnt[f]; }
-            else { m = c->prof.setup_ms[f - PF_N]; n = 1; }
+            if (f < PF_FAMILIES) { m = c->prof.ms[f]; n = c->prof.cnt[f]; }
+            else { m = c->prof.setup_ms[f - PF_FAMILIES]; n = 1; }
             if (ms) ms[f] = m;
             if (count) count[f] = n;
+        }
+        return CPTR_OK;
+    });
+}
+
+cptr_status cptr_profile_vcycle(cptr_ctx *ctx, double *ms, int64_t *count) {
+    return guarded(ctx, [&](Ctx *c) {
+        for (int k = 0; k < 8; ++k) {
+            if (ms) ms[k] = c->prof.ms[PF_VC + k];
+            if (count) count[k] = c->prof.cnt[PF_VC + k];
         }
         return CPTR_OK;
     });

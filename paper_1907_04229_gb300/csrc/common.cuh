@@ -133,8 +133,11 @@ void note_launches(int64_t n);  // a graph replay of n kernel nodes
 int64_t launch_count();
 void begin_capture_count();  // launches noted on this thread while capturing are not counted...
 int64_t end_capture_count(); // ...but returned here (the graph's kernel node count)
+// families 0-6 are switched on by bits 0-6 of the profiling mask; bit 7 switches on the eight
+// fine-level V-cycle kernels PF_VC + 4 * hierarchy (0 pressure or p-T, 1 temperature) + step
+// (0 pre-smoothing + residual, 1 restriction, 2 prolongation, 3 post-smoothing)
 enum { PF_SPMV = 0, PF_STAGE1 = 1, PF_RESID = 2, PF_ILU = 3, PF_ARNOLDI = 4, PF_ILU_FWD = 5, PF_ILU_BWD = 6,
-       PF_N = 8 };
+       PF_FAMILIES = 8, PF_VC = 8, PF_N = 16 };
 constexpr int kSetupPhases = 8;
 struct Prof {
     uint32_t mask = 0;

@@ -38,7 +38,7 @@ void setup_tick(Ctx *c, int phase, double *t0) {
 
 int prof_begin(const Ctx *c, int fam) {
     Prof &p = c->prof;
-    if (!(p.mask & (1u << fam))) return -1;
+    if (!(p.mask & (1u << (fam < PF_FAMILIES ? fam : 7)))) return -1;
     if (2 * (p.used + 1) > p.ev.size()) {
         for (int k = 0; k < 64; ++k) {
             cudaEvent_t e;
