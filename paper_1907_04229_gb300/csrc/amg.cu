@@ -876,9 +876,14 @@ __global__ void __launch_bounds__(512) k_vc_down(int32_t n, const int32_t *__res
     XT acc = 0;
     if (row < n) {
         int32_t k1 = __ldg(rp + row + 1);
-        for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G) {
-            int32_t j = __ldg(ci + k);
-            acc = fma((XT)vld(v + k), __ldg(dinv + j) * __ldg(b + j), acc);
+        if (G == 1) {
+            acc = row_dot_batched<8>(__ldg(rp + row), k1, ci, [&](int32_t k) { return (XT)vld(v + k); },
+                                     [&](int32_t j) { return __ldg(dinv + j) * __ldg(b + j); }, acc);
+        } else {
+            for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G) {
+                int32_t j = __ldg(ci + k);
+                acc = fma((XT)vld(v + k), __ldg(dinv + j) * __ldg(b + j), acc);
+            }
         }
     }
 #pragma unroll
@@ -901,8 +906,13 @@ __global__ void __launch_bounds__(512) k_vc_post(int32_t n, const int32_t *__res
     XT acc = 0;
     if (row < n) {
         int32_t k1 = __ldg(rp + row + 1);
-        for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G)
-            acc = fma((XT)vld(v + k), __ldg(t + __ldg(ci + k)), acc);
+        if (G == 1) {
+            acc = row_dot_batched<8>(__ldg(rp + row), k1, ci, [&](int32_t k) { return (XT)vld(v + k); },
+                                     [&](int32_t j) { return __ldg(t + j); }, acc);
+        } else {
+            for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G)
+                acc = fma((XT)vld(v + k), __ldg(t + __ldg(ci + k)), acc);
+        }
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);

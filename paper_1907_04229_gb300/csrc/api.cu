@@ -207,70 +207,86 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
         CPTR_TRY(schur_diag(c, Sd));
         c->schur_used = CPTR_SCHUR_DIAG;
     }
+    // The hierarchies are independent of one another: each is built by a host thread of its own
+    // (a context view with its own stream, fork event, scratch flag and scan buffer).  The ILU(0)
+    // factors follow on this thread once both are built: building them at the same time gave no
+    // gain on 200k cells (every part of the set-up slowed down in proportion), and on 2M cells the
+    // ILU set-up and the coarsening then stalled each other for ~0.4 s in most set-ups.
+    struct HierJob {
+        Hier *h;
+        const int32_t *rp, *ci;
+        const double *v;
+        int32_t n;
+        const int32_t *fn;
+        int32_t np;
+    };
+    std::vector<HierJob> jobs;
+    Csr A00;
+    int32_t *fn00 = nullptr;
     if (s1 == CPTR_STAGE1_UAMG) {
         // unknown-based AMG (Sec. 3.4) on A_00 in unknown-wise order, kept in the pressure slot
-        Csr A00;
-        int32_t *fn = nullptr;
-        CPTR_TRY(build_a00(c, A00, &fn));
-        const cptr_status su = amg_setup(c, c->hp, A00.rp, A00.ci, A00.v, 2 * n, fn, n);
-        csr_free(A00);
-        dfree(fn);
-        CPTR_TRY(su);
-        if (c->o.stage2 == CPTR_STAGE2_ILU0) CPTR_TRY(ilu_setup(c));
-    } else if (s1 != CPTR_STAGE1_NONE && s1 != CPTR_STAGE1_CPR) {
-        // The two hierarchies are independent: the temperature one is built by a second host
-        // thread on its own stream (a context view with its own stream, scratch flag and scan
-        // buffer) while this thread builds the pressure one and then the ILU(0) factors.
-        if (!c->amg_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->amg_stream, cudaStreamNonBlocking));
-        if (!c->coarse_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->coarse_stream, cudaStreamNonBlocking));
-        if (!c->amg_fork) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&c->amg_fork, cudaEventDisableTiming));
-        Ctx w;
+        CPTR_TRY(build_a00(c, A00, &fn00));
+        jobs.push_back({&c->hp, A00.rp, A00.ci, A00.v, 2 * n, fn00, n});
+    } else if (s1 != CPTR_STAGE1_NONE) {
+        jobs.push_back({&c->hp, c->rp, c->ci, c->App, n, nullptr, 0});
+        if (s1 != CPTR_STAGE1_CPR)
+            jobs.push_back(Sd.v ? HierJob{&c->hT, Sd.rp, Sd.ci, Sd.v, n, nullptr, 0}
+                                : HierJob{&c->hT, c->rp, c->ci, c->St, n, nullptr, 0});
+    }
+    if (!c->coarse_stream && !jobs.empty())
+        CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->coarse_stream, cudaStreamNonBlocking));
+    const size_t nj = jobs.size();
+    std::vector<Ctx> wc(nj);
+    std::vector<cptr_status> st_w(nj, CPTR_OK);
+    for (size_t q = 0; q < nj; ++q) {
+        if (!c->amg_stream[q]) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->amg_stream[q], cudaStreamNonBlocking));
+        if (!c->amg_fork[q]) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&c->amg_fork[q], cudaEventDisableTiming));
+        Ctx &w = wc[q];
         w.o = c->o;
-        w.stream = c->amg_stream;
+        w.stream = c->amg_stream[q];
         w.pool = c->pool;
         w.coarse_stream = c->coarse_stream;
-        w.side_fork = c->amg_fork;
+        w.side_fork = c->amg_fork[q];
         CPTR_TRY(dalloc_t(c, &w.flag, 4));
-        CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // inputs and allocations are ready
-        cptr_status st_T = CPTR_OK;
-        // a host exception on either thread becomes a status: the worker catches its own, and
-        // this thread joins the worker before any exception of its own leaves this scope
-        std::thread worker([&] {
+    }
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // inputs and allocations are ready
+    // a host exception on any thread becomes a status: the workers catch their own, and this
+    // thread joins the workers before any exception of its own leaves this scope
+    std::vector<std::thread> workers;
+    for (size_t q = 0; q < nj; ++q)
+        workers.emplace_back([&, q] {
+            Ctx &w = wc[q];
+            const HierJob &j = jobs[q];
             CtxScope ws(&w);
             try {
-                st_T = Sd.v ? amg_setup(&w, c->hT, Sd.rp, Sd.ci, Sd.v, n) : amg_setup(&w, c->hT, c->rp, c->ci, c->St, n);
+                st_w[q] = amg_setup(&w, *j.h, j.rp, j.ci, j.v, j.n, j.fn, j.np);
             } catch (const std::bad_alloc &) {
-                st_T = w.fail(CPTR_ENOMEM, "host allocation failed");
+                st_w[q] = w.fail(CPTR_ENOMEM, "host allocation failed");
             } catch (...) {
-                st_T = w.fail(CPTR_EINVAL, "unexpected host exception");
+                st_w[q] = w.fail(CPTR_EINVAL, "unexpected host exception");
             }
             dfree(w.scan_tmp);
             w.scan_tmp = nullptr;
             cudaStreamSynchronize(w.stream);
         });
-        // This thread builds the pressure hierarchy, then the ILU(0) factors.  (Running the
-        // factorisation kernel on a stream of its own during the pressure hierarchy saved ~2 ms on
-        // cptr200k, but on 2M-cell systems some set-ups then stalled for ~0.3 s; not used.)
-        cptr_status st_p = CPTR_OK;
-        try {
-            st_p = amg_setup(c, c->hp, c->rp, c->ci, c->App, n);
-            if (st_p == CPTR_OK && c->o.stage2 == CPTR_STAGE2_ILU0) st_p = ilu_setup(c);
-        } catch (...) {
-            worker.join();
+    auto join_all = [&] {
+        for (auto &t : workers) t.join();
+        workers.clear();
+        for (Ctx &w : wc) {
             dfree(w.flag);
-            csr_free(Sd);
-            throw;
+            w.flag = nullptr;
         }
-        worker.join();
+        csr_free(A00);
+        dfree(fn00);
+        fn00 = nullptr;
         csr_free(Sd);
+    };
+    join_all();
+    for (const Ctx &w : wc)
         for (int q = 0; q < kSetupPhases; ++q) c->prof.setup_ms[q] += w.prof.setup_ms[q];
-        dfree(w.flag);
-        if (st_p != CPTR_OK) return st_p;
-        if (st_T != CPTR_OK) return c->fail(st_T, w.err);
-    } else {
-        if (s1 != CPTR_STAGE1_NONE) CPTR_TRY(amg_setup(c, c->hp, c->rp, c->ci, c->App, n));
-        if (c->o.stage2 == CPTR_STAGE2_ILU0) CPTR_TRY(ilu_setup(c));
-    }
+    for (size_t q = 0; q < nj; ++q)
+        if (st_w[q] != CPTR_OK) return c->fail(st_w[q], wc[q].err);
+    if (c->o.stage2 == CPTR_STAGE2_ILU0) CPTR_TRY(ilu_setup(c));
     // the coarsest inverses ran on the coarse stream meanwhile
     CPTR_TRY(amg_coarsest_wait(c, c->hp));
     CPTR_TRY(amg_coarsest_wait(c, c->hT));
@@ -492,8 +508,10 @@ void cptr_destroy(cptr_ctx *ctx) {
         cudaStreamSynchronize(c->stream);
         if (c->side_stream) cudaStreamSynchronize(c->side_stream);
         if (c->coarse_stream) cudaStreamSynchronize(c->coarse_stream);
-        if (c->amg_stream) cudaStreamSynchronize(c->amg_stream);
+        for (cudaStream_t as : c->amg_stream)
+            if (as) cudaStreamSynchronize(as);
         release_setup(c);
+        ilu_sym_free(c);
         dfree(c->ks); dfree(c->flag); dfree(c->partial); dfree(c->scan_tmp); dfree(c->never); dfree(c->ilu_flags);
         dfree(c->mlp);
         model_free(c);
@@ -505,8 +523,10 @@ void cptr_destroy(cptr_ctx *ctx) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->side_stream) cudaStreamDestroy(c->side_stream);
     if (c->coarse_stream) cudaStreamDestroy(c->coarse_stream);
-    if (c->amg_stream) cudaStreamDestroy(c->amg_stream);
-    if (c->amg_fork) cudaEventDestroy(c->amg_fork);
+    for (cudaStream_t as : c->amg_stream)
+        if (as) cudaStreamDestroy(as);
+    for (cudaEvent_t ae : c->amg_fork)
+        if (ae) cudaEventDestroy(ae);
     if (c->side_fork) cudaEventDestroy(c->side_fork);
     if (c->side_join) cudaEventDestroy(c->side_join);
     for (Hier *h : {&c->hp, &c->hT})

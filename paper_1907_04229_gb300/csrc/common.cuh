@@ -233,6 +233,7 @@ cptr_status amg_lower_precision(Ctx *c, Hier &h);
 // ---- ilu.cu ------------------------------------------------------------------------------------
 cptr_status ilu_setup(Ctx *c);
 void ilu_free(Ctx *c);
+void ilu_sym_free(Ctx *c);                               // the pattern-only tables kept across set-ups
 void ilu_apply(const Ctx *c, const double *r, double *z, const double *dp, const double *dT);
 void ilu_apply_into(const Ctx *c, const double *r, double *z, double *ybuf, double *zbuf);
 void ilu_apply32(const Ctx *c, const float *r, double *z, const float *dp, const float *dT);
@@ -282,6 +283,25 @@ struct TileTables {
     unsigned char *rec = nullptr;
 };
 
+// Pattern-only ILU tables kept from one set-up to the next while the caller's block pattern and the
+// ILU options that shape them are unchanged (the pattern is compared on the device at every set-up):
+// the level sets of both sweeps, and the grid dimensions and tile structure of the tiled sweeps.
+// Values (factors, packed records) are always rebuilt.
+struct IluSym {
+    int32_t n = -1, b = 0, nnzb = 0, order = -1, fill = -1;
+    int32_t *rp = nullptr, *ci = nullptr;        // the pattern the tables belong to (device copy)
+    bool current = false;                        // matched or rebuilt by this set-up's ilu_setup
+    bool lv = false;                             // level sets held
+    int32_t *lvl[2] = {}, *inv[2] = {}, *levr[2] = {};   // forward, backward
+    std::vector<int32_t> lptr[2];
+    int grid = -1;                               // tiled-sweep grid found (1), not found (0), unknown (-1)
+    int32_t dims[3] = {0, 0, 0};
+    int tile_ty = 0, tile_tz = 0, tile_prec = -1;  // tile structure held for this shape and precision
+    TileTables tt[2];                            // its sizes, with tlev and lptr owned here (rec unused)
+    int32_t *hdr[2] = {}, *kidx[2] = {};
+    size_t tlev_n[2] = {}, lptr_n[2] = {};
+};
+
 // ---- the context -------------------------------------------------------------------------------
 struct Ctx {
     cptr_options o{};
@@ -317,6 +337,7 @@ struct Ctx {
     int32_t *ilu_rowmap = nullptr;     // multicolour: row of the factorised matrix -> original row
     int32_t *ilu_flags = nullptr;      // per-row "factored" flags of the one-launch factorisation
     int32_t ilu_flags_n = 0, ilu_epoch = 0;
+    IluSym isym;                                       // pattern-only ILU tables of the last set-up
     int32_t nlev_f = 0, nlev_b = 0;
     int32_t *lvl_f = nullptr, *lvl_b = nullptr;       // rows sorted by level (device)
     std::vector<int32_t> h_lptr_f, h_lptr_b;           // level pointers (host)
@@ -367,8 +388,8 @@ struct Ctx {
     cudaStream_t cap_stream = nullptr;
     cudaStream_t side_stream = nullptr;   // set-up work that overlaps the main stream
     cudaStream_t coarse_stream = nullptr; // the coarsest AMG inverses, overlapping the rest of the set-up
-    cudaStream_t amg_stream = nullptr;    // the second hierarchy, built by a second host thread
-    cudaEvent_t amg_fork = nullptr;
+    cudaStream_t amg_stream[2] = {};      // the hierarchies, each built by a host thread of its own
+    cudaEvent_t amg_fork[2] = {};
     cudaEvent_t side_fork = nullptr, side_join = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int64_t graph_launches = 0;
@@ -398,6 +419,32 @@ struct Ctx {
         return code;
     }
 };
+
+// acc + sum over k0 <= k < k1 of v_k * x(col_k), added in k order (one fma per entry, the order
+// of a plain row loop) by one thread.  The entries are taken U at a time: the U column indices and
+// values are loaded first, then the U gathered x values, so a thread has U independent loads in
+// flight instead of a chain of dependent ones per entry.
+template <int U, typename XT, typename LV, typename LX>
+__device__ __forceinline__ XT row_dot_batched(int32_t k0, int32_t k1, const int32_t *__restrict__ ci, LV ldv, LX ldx,
+                                              XT acc) {
+    for (int32_t k = k0; k < k1; k += U) {
+        int32_t j[U];
+        XT a[U], xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (k + u < k1) {
+                j[u] = __ldg(ci + k + u);
+                a[u] = ldv(k + u);
+            }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (k + u < k1) xv[u] = ldx(j[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (k + u < k1) acc = fma(a[u], xv[u], acc);
+    }
+    return acc;
+}
 
 // lanes per row for a CSR kernel, from the average row length
 inline int lanes_for(int32_t n, int32_t nnz) {

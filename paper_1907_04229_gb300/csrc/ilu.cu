@@ -1852,9 +1852,67 @@ __global__ void k_scatter_blocks(int64_t nnz, int BB, const int32_t *kmap, const
     dst[u] = k >= 0 ? src[(int64_t)k * BB + u % BB] : 0.0;
 }
 
+// 1 in *diff if the pattern (rp, ci) differs from (srp, sci) anywhere
+__global__ void k_pattern_diff(int32_t n, int32_t nnzb, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                               const int32_t *__restrict__ srp, const int32_t *__restrict__ sci, int32_t *diff) {
+    bool d = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnzb; i += (int64_t)gridDim.x * blockDim.x) {
+        if (ci[i] != sci[i]) d = true;
+        if (i <= n && rp[i] != srp[i]) d = true;
+    }
+    if (__syncthreads_or(d) && threadIdx.x == 0) *diff = 1;
+}
+
+void ilu_sym_free(Ctx *c) {
+    IluSym &y = c->isym;
+    dfree(y.rp); dfree(y.ci);
+    for (int d = 0; d < 2; ++d) {
+        dfree(y.lvl[d]); dfree(y.inv[d]); dfree(y.levr[d]);
+        dfree(y.tt[d].tlev); dfree(y.tt[d].lptr); dfree(y.hdr[d]); dfree(y.kidx[d]);
+    }
+    y = IluSym();
+}
+
+// Whether the tables of c->isym belong to this set-up's pattern and ILU options; if not, they are
+// dropped and the pattern is recorded for the tables this set-up builds.
+static cptr_status ilu_sym_check(Ctx *c, bool *same) {
+    IluSym &y = c->isym;
+    *same = false;
+    const int32_t n = c->n, nnzb = c->nnzb;
+    if (y.rp && y.n == n && y.b == c->b && y.nnzb == nnzb && y.order == c->o.ilu_order && y.fill == c->o.ilu_fill) {
+        int32_t *diff = c->flag + 2, h = 1;
+        CPTR_CUDA_TRY(c, cudaMemsetAsync(diff, 0, sizeof(int32_t), c->stream));
+        (k_pattern_diff<<<std::min<unsigned>(nblk(nnzb, 256), 4 * 152), 256, 0, c->stream>>>(n, nnzb, c->rp, c->ci, y.rp,
+                                                                                              y.ci, diff), note_launch());
+        CPTR_TRY(copy_to_host(c, &h, diff, sizeof(int32_t)));
+        *same = h == 0;
+    }
+    if (!*same) {
+        ilu_sym_free(c);
+        CPTR_TRY(dalloc_t(c, &y.rp, (size_t)n + 1));
+        CPTR_TRY(dalloc_t(c, &y.ci, (size_t)nnzb));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(y.rp, c->rp, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, c->stream));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(y.ci, c->ci, sizeof(int32_t) * (size_t)nnzb, cudaMemcpyDeviceToDevice, c->stream));
+        y.n = n;
+        y.b = c->b;
+        y.nnzb = nnzb;
+        y.order = c->o.ilu_order;
+        y.fill = c->o.ilu_fill;
+    }
+    y.current = true;
+    return CPTR_OK;
+}
+
+static cptr_status d2d_copy(Ctx *c, int32_t *dst, const int32_t *src, size_t count) {
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(dst, src, sizeof(int32_t) * count, cudaMemcpyDeviceToDevice, c->stream));
+    return CPTR_OK;
+}
+
 cptr_status ilu_setup(Ctx *c) {
     ilu_free(c);
     double t0 = host_ms();
+    bool same_pattern = false;
+    CPTR_TRY(ilu_sym_check(c, &same_pattern));
     const int32_t n = c->n, BB = c->b * c->b;
     cudaStream_t st = c->stream;
     // the pattern the factorisation works on: the caller's order, cells permuted by colour, or the
@@ -1938,8 +1996,26 @@ cptr_status ilu_setup(Ctx *c) {
     int32_t *levr_f = nullptr, *levr_b = nullptr;
     CPTR_TRY(dalloc_t(c, &levr_f, (size_t)n));
     CPTR_TRY(dalloc_t(c, &levr_b, (size_t)n));
-    CPTR_TRY(device_levels(c, c->ilu_rp, c->ilu_ci, c->lvl_f, inv_f, c->h_lptr_f, c->lvl_b, inv_b, c->h_lptr_b,
-                           levr_f, levr_b));
+    IluSym &ys = c->isym;
+    if (ys.lv) {   // the level sets of the same pattern, from the last set-up
+        int32_t *dst[6] = {c->lvl_f, inv_f, levr_f, c->lvl_b, inv_b, levr_b};
+        const int32_t *src[6] = {ys.lvl[0], ys.inv[0], ys.levr[0], ys.lvl[1], ys.inv[1], ys.levr[1]};
+        for (int q = 0; q < 6; ++q) CPTR_TRY(d2d_copy(c, dst[q], src[q], (size_t)n));
+        c->h_lptr_f = ys.lptr[0];
+        c->h_lptr_b = ys.lptr[1];
+    } else {
+        CPTR_TRY(device_levels(c, c->ilu_rp, c->ilu_ci, c->lvl_f, inv_f, c->h_lptr_f, c->lvl_b, inv_b, c->h_lptr_b,
+                               levr_f, levr_b));
+        const int32_t *src[6] = {c->lvl_f, inv_f, levr_f, c->lvl_b, inv_b, levr_b};
+        int32_t **dst[6] = {&ys.lvl[0], &ys.inv[0], &ys.levr[0], &ys.lvl[1], &ys.inv[1], &ys.levr[1]};
+        for (int q = 0; q < 6; ++q) {
+            CPTR_TRY(dalloc_t(c, dst[q], (size_t)n));
+            CPTR_TRY(d2d_copy(c, *dst[q], src[q], (size_t)n));
+        }
+        ys.lptr[0] = c->h_lptr_f;
+        ys.lptr[1] = c->h_lptr_b;
+        ys.lv = true;
+    }
     c->nlev_f = (int32_t)c->h_lptr_f.size() - 1;
     c->nlev_b = (int32_t)c->h_lptr_b.size() - 1;
     CPTR_TRY(dalloc_t(c, &c->ybuf, (size_t)n * c->b));
@@ -2094,6 +2170,7 @@ void ilu_free(Ctx *c) {
     cw_free(c);
     tile_free(c);
     c->tl_use = false;
+    c->isym.current = false;
     if (c->ilu_owns_pattern) { dfree(c->ilu_rp); dfree(c->ilu_ci); dfree(c->ilu_diag); dfree(c->ilu_rowmap); }
     c->ilu_rowmap = nullptr;
     c->ilu_owns_pattern = false;

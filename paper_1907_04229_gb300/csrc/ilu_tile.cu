@@ -512,9 +512,26 @@ double tile_model(const int32_t dims[3], int Ty, int Tz) {
 
 // Natural order on an nx x ny x nz box: the lower dependencies of every row lie at the offsets 1,
 // nx and nx*ny (or a subset of them), and n = nx ny nz.  Detected from the host pattern.
+static bool tile_grid_find(Ctx *c);
+
 bool tile_grid(Ctx *c) {
     c->tl_dims[0] = c->tl_dims[1] = c->tl_dims[2] = 0;
     if (c->o.ilu_order != CPTR_ILU_NATURAL || c->n_inst > 1) return false;
+    IluSym &ys = c->isym;
+    if (ys.current && ys.grid >= 0) {   // found for the same pattern at an earlier set-up
+        for (int q = 0; q < 3; ++q) c->tl_dims[q] = ys.dims[q];
+        return ys.grid == 1;
+    }
+    const bool found = tile_grid_find(c);
+    if (ys.current) {
+        ys.grid = found ? 1 : 0;
+        for (int q = 0; q < 3; ++q) ys.dims[q] = c->tl_dims[q];
+    }
+    return found;
+}
+
+// the grid dimensions from the pattern's lower offsets (1, nx, nx*ny)
+static bool tile_grid_find(Ctx *c) {
     if (host_pattern(c) != CPTR_OK) return false;
     const int32_t n = c->n;
     const std::vector<int32_t> &rp = c->h_rp, &ci = c->h_ci;
@@ -576,11 +593,54 @@ void tile_free(Ctx *c) {
 cptr_status tile_setup(Ctx *c, int Ty, int Tz) {
     tile_free(c);
     if (!c->tl_dims[0]) return CPTR_OK;
-    CPTR_TRY(host_pattern(c));
     const int32_t n = c->n, B = c->b, BB = B * B;
     const bool lo = c->o.precision == CPTR_PREC_MIXED;
     const int tsz = lo ? 4 : 8;
     cudaStream_t st = c->stream;
+    IluSym &ys = c->isym;
+    if (ys.current && ys.tile_ty == Ty && ys.tile_tz == Tz && ys.tile_prec == (int)lo) {
+        // the tile structure of the same pattern, from an earlier set-up: copy it, pack the values
+        for (int dir = 0; dir < 2; ++dir) {
+            const bool fwd = dir == 0;
+            TileTables &t = fwd ? c->tl_f : c->tl_b;
+            t = ys.tt[dir];
+            t.tlev = nullptr;
+            t.lptr = nullptr;
+            t.rec = nullptr;
+            CPTR_TRY(dalloc_t(c, &t.tlev, ys.tlev_n[dir]));
+            CPTR_TRY(dalloc_t(c, &t.lptr, ys.lptr_n[dir]));
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(t.tlev, ys.tt[dir].tlev, sizeof(int32_t) * ys.tlev_n[dir],
+                                             cudaMemcpyDeviceToDevice, st));
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(t.lptr, ys.tt[dir].lptr, sizeof(int32_t) * ys.lptr_n[dir],
+                                             cudaMemcpyDeviceToDevice, st));
+            CPTR_TRY(dalloc(c, reinterpret_cast<void **>(&t.rec), (size_t)n * t.RS));
+            const int nslot = t.D + (fwd ? 0 : 1);
+            const int H = hdr_bytes(t.D);
+            if (lo)
+                (k_tile_pack<float><<<nblk(n, 256), 256, 0, st>>>(n, t.D, BB, t.RS, H, nslot, ys.hdr[dir], ys.kidx[dir],
+                                                                   c->LU, t.rec), note_launch());
+            else
+                (k_tile_pack<double><<<nblk(n, 256), 256, 0, st>>>(n, t.D, BB, t.RS, H, nslot, ys.hdr[dir], ys.kidx[dir],
+                                                                    c->LU, t.rec), note_launch());
+            CPTR_CUDA_TRY(c, cudaGetLastError());
+        }
+        c->tl_ok = true;
+        c->tl_ty = Ty;
+        c->tl_tz = Tz;
+        return CPTR_OK;
+    }
+    CPTR_TRY(host_pattern(c));
+    // the structure built here replaces the kept one (if this set-up's pattern is the kept one)
+    const bool keep = ys.current;
+    if (keep) {
+        for (int dir = 0; dir < 2; ++dir) {
+            dfree(ys.tt[dir].tlev); dfree(ys.tt[dir].lptr); dfree(ys.hdr[dir]); dfree(ys.kidx[dir]);
+            ys.tt[dir] = TileTables();
+            ys.hdr[dir] = ys.kidx[dir] = nullptr;
+        }
+        ys.tile_ty = ys.tile_tz = 0;
+        ys.tile_prec = -1;
+    }
     for (int dir = 0; dir < 2; ++dir) {
         const bool fwd = dir == 0;
         TileHost h;
@@ -637,8 +697,29 @@ cptr_status tile_setup(Ctx *c, int Ty, int Tz) {
             (k_tile_pack<double><<<nblk(n, 256), 256, 0, st>>>(n, h.D, BB, t.RS, H, nslot, dh, dk, c->LU, t.rec), note_launch());
         CPTR_CUDA_TRY(c, cudaGetLastError());
         CPTR_CUDA_TRY(c, cudaStreamSynchronize(st));   // the host tables are freed on return
-        dfree(dh);
-        dfree(dk);
+        if (keep) {   // kept for the next set-up of this pattern: sizes, level tables, headers, indices
+            ys.tt[dir] = t;
+            ys.tt[dir].rec = nullptr;
+            ys.tt[dir].tlev = ys.tt[dir].lptr = nullptr;
+            ys.tlev_n[dir] = h.tlev.size();
+            ys.lptr_n[dir] = h.lptr.size();
+            CPTR_TRY(dalloc_t(c, &ys.tt[dir].tlev, h.tlev.size()));
+            CPTR_TRY(dalloc_t(c, &ys.tt[dir].lptr, h.lptr.size()));
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(ys.tt[dir].tlev, t.tlev, sizeof(int32_t) * h.tlev.size(),
+                                             cudaMemcpyDeviceToDevice, st));
+            CPTR_CUDA_TRY(c, cudaMemcpyAsync(ys.tt[dir].lptr, t.lptr, sizeof(int32_t) * h.lptr.size(),
+                                             cudaMemcpyDeviceToDevice, st));
+            ys.hdr[dir] = dh;
+            ys.kidx[dir] = dk;
+        } else {
+            dfree(dh);
+            dfree(dk);
+        }
+    }
+    if (keep) {
+        ys.tile_ty = Ty;
+        ys.tile_tz = Tz;
+        ys.tile_prec = (int)lo;
     }
     c->tl_ok = true;
     c->tl_ty = Ty;

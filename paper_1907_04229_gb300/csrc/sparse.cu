@@ -535,8 +535,13 @@ __global__ void __launch_bounds__(512) k_csr_spmv(int32_t n, const int32_t *__re
     XT acc = 0;
     if (row < n) {
         int32_t k1 = __ldg(rp + row + 1);
-        for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G)
-            acc = fma((XT)val_ld(v + k), __ldg(x + __ldg(ci + k)), acc);
+        if (G == 1) {
+            acc = row_dot_batched<4>(__ldg(rp + row), k1, ci, [&](int32_t k) { return (XT)val_ld(v + k); },
+                                     [&](int32_t j) { return __ldg(x + j); }, acc);
+        } else {
+            for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G)
+                acc = fma((XT)val_ld(v + k), __ldg(x + __ldg(ci + k)), acc);
+        }
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);

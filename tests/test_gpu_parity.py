@@ -812,3 +812,46 @@ def test_non_finite_rhs_reports_ebreakdown_and_context_recovers():
         g.solve(dev(rhs), 1e-8)
     assert e.value.code == -4, e.value
     check_solve(s, o, g, 1e-8)
+
+
+# ------------------------------------------------------------------------------------------------
+# set-ups of the same pattern with new values (Newton iterations, time steps): the context keeps the
+# pattern-only ILU tables (level sets, tile structure) and rebuilds everything that holds values
+def _setup_again(S, s, vals):
+    S.setup(s["n"], s["b"], dev(s["row_ptr"]), dev(s["col_idx"]), dev(vals.reshape(-1)), dev(s["unknown_kind"]),
+            dev(s["weights"].reshape(-1)), dev(s["st"]))
+
+
+@pytest.mark.parametrize("sweep", ["levels", "paired", "tiled"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_set_up_again_with_the_same_pattern_or_another(sweep, precision):
+    """A context set up before, then set up with new values on the same pattern, and then with a
+    different pattern of the same size (an 8 x 6 x 4 box against a 6 x 8 x 4 one: same cell count,
+    same block count), gives bit for bit what a fresh context gives each time: ILU applications
+    and solves."""
+    o = dict(ilu_sweep=cp.ILU_SWEEP[sweep], precision=cp.PRECISION[precision], n_coarse=16)
+    s1 = synth.make_box(8, 6, 4, 3.125, seed=23, heaters=[(11, 80.0, 420.0)]).system()
+    s2 = synth.make_box(6, 8, 4, 3.125, seed=24, heaters=[(13, 80.0, 420.0)]).system()
+    assert s1["n"] == s2["n"] and s1["row_ptr"][-1] == s2["row_ptr"][-1]
+    assert not np.array_equal(s1["col_idx"], s2["col_idx"])
+    rng = np.random.default_rng(6)
+    scale = 1.0 + 0.2 * rng.random(s1["n"])
+    rows = np.repeat(np.arange(s1["n"]), np.diff(s1["row_ptr"]))
+    vals1b = s1["vals"] * scale[rows][:, None, None]
+    S = gpu_solver(s1, **o)
+    for s, vals in ((s1, vals1b), (s2, s2["vals"]), (s1, s1["vals"])):
+        _setup_again(S, s, vals)
+        F = cp.Solver(**o)
+        _setup_again(F, s, vals)
+        if sweep == "tiled":
+            assert [r for r in cp.cptr_tuning(S.ctx) if r[2] == 5][0][3] == 3
+        nb = s["n"] * s["b"]
+        r = dev(np.random.default_rng(7).normal(size=nb))
+        za, zb = torch.empty_like(r), torch.empty_like(r)
+        cp.cptr_apply_ilu(S.ctx, r, za)
+        cp.cptr_apply_ilu(F.ctx, r, zb)
+        assert torch.equal(za, zb)
+        xa, ia = S.solve(dev(s["rhs"].reshape(-1)), 1e-8)
+        xb, ib = F.solve(dev(s["rhs"].reshape(-1)), 1e-8)
+        assert ia["status"] == "CPTR_OK" and ia["iters"] == ib["iters"] and torch.equal(xa, xb)
+        F.close()
