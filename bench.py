@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-three-phase", action="store_true")
+    p.add_argument("--no-small", action="store_true", help="skip the 16x16x4 two-level configuration")
     p.add_argument("--no-ensemble", action="store_true")
     p.add_argument("--three-phase-grid", type=int, nargs=3, default=None,
                    help="run the three-phase section on an NX NY NZ box instead of 200x200x50 (profiling)")
@@ -514,6 +515,10 @@ def ours(args, rank, world, local_rank, oracle_jobs):
                                           PROFILED_TRAFFIC))
             Sv.close()
 
+    small = None
+    if not args.no_small:
+        small = small_section(args, dev, stream, flush)
+
     tp = None
     if not args.no_three_phase:
         del flush
@@ -600,7 +605,7 @@ def ours(args, rank, world, local_rank, oracle_jobs):
                "solve_dofs_per_s": round(dofs / (solve_ms / 1e3), 1),
                "true_rel_res": infos[-1]["true_rel_res"], "levels": [infos[-1]["levels_p"], infos[-1]["levels_T"]],
                "families": families, "roofline": roofline, "rooflines": lines, "variants": variants,
-               "three_phase": tp, "ensemble": ens, "newton": newton, "mesh_refinement": mesh,
+               "small_1024": small, "three_phase": tp, "ensemble": ens, "newton": newton, "mesh_refinement": mesh,
                "errors_vs_fp64_oracle": oracle_errors,
                "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "launches_before_timed": launches0, "clocks": clk}
@@ -828,6 +833,58 @@ def mesh_study(args, dev, stream):
                 S.close()
         out[kind] = res
     return out
+
+
+def small_section(args, dev, stream, flush):
+    """The small plain-CPTR configuration: 16x16x4 cells (3072 dofs), FP64, two-level AMG (its
+    coarsest level a dense inverse of a few hundred rows) + ILU(0), FGMRES(30) to 1e-8; set-up and
+    solve timed like the headline step, the oracle's set-up + solve of the same system beside it,
+    and the error against the oracle per unknown kind."""
+    import torch
+
+    import oracle
+    import synth
+    import paper_1907_04229_gb300 as cp
+    s = synth.recipe("parity").system()
+    n, b = s["n"], s["b"]
+    d = {k: torch.as_tensor(np.ascontiguousarray(v), device=dev) for k, v in
+         {"rp": s["row_ptr"], "ci": s["col_idx"], "vals": s["vals"].reshape(-1), "kind": s["unknown_kind"],
+          "W": s["weights"].reshape(-1), "st": s["st"], "rhs": s["rhs"].reshape(-1)}.items()}
+    x = torch.empty(n * b, dtype=torch.float64, device=dev)
+    S = cp.Solver(stream=stream, max_levels=2)
+
+    def step():
+        S.setup(n, b, d["rp"], d["ci"], d["vals"], d["kind"], d["W"], d["st"])
+        return S.solve(d["rhs"], 1e-8, x=x)[1]
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    evs, infs = [], []
+    for _ in range(10):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infs.append(step())
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(bb) for a, bb in evs) / len(evs)
+    lev = [L["n"] for L in S.hierarchy(0)]
+    xg = x.cpu().numpy().copy()
+    S.close()
+    t0 = time.perf_counter()
+    o = oracle.Oracle.from_system(s, max_levels=2)
+    xo, io = o.solve(s["rhs"], 1e-8)
+    osecs = time.perf_counter() - t0
+    return {"workload": "16x16x4 cells (3072 dofs), two-phase thermal, FP64 CPTR, two-level AMG (dense coarsest "
+                        "inverse) + ILU(0), FGMRES(30), rtol 1e-8",
+            "ms_per_step": round(ms, 3), "dofs_per_s": round(n * b / (ms / 1e3), 1),
+            "setup_ms": round(statistics.mean(i["setup_ms"] for i in infs), 3),
+            "solve_ms": round(statistics.mean(i["solve_ms"] for i in infs), 3), "iters": infs[-1]["iters"],
+            "levels_p": lev, "status": infs[-1]["status"],
+            "error_vs_fp64_oracle": errors_per_kind(xg, xo, b), "oracle_iters": int(io["iters"]),
+            "cpu_baseline": {"value": round(n * b / osecs, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one set-up + solve by the serial FP64 C oracle, {osecs * 1e3:.1f} ms"}}
 
 
 def tp_dofs(tp):

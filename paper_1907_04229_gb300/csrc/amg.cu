@@ -468,6 +468,138 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan_smem(int32_t n, const dou
     for (int32_t e = tid; e < nn; e += nt) inv[e] = a[e];
 }
 
+// The same inverse for larger matrices, spread over many blocks: the matrix in global memory (row i
+// updated by block i mod gridDim.x), block 0 choosing each pivot and staging the pivot row and row k,
+// two grid barriers per pivot.  Launched cooperatively (all blocks resident); every barrier wait is
+// bounded (flags[3] records a wait that gave up, and every block then returns).
+// flags: [0] singular, [1] barrier arrivals, [2] barrier generation, [3] barrier timeout.
+constexpr int kGjThreads = 256;
+constexpr unsigned long long kGjWaitNs = 500ULL * 1000ULL * 1000ULL;
+
+__device__ __forceinline__ unsigned gj_load_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void gj_store_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// all blocks of the grid arrive before any leaves; false (in every thread of the block) if the
+// wait gave up or another block's wait had given up
+__device__ bool gj_grid_barrier(int32_t *flags) {
+    __shared__ int ok_s;
+    unsigned *count = reinterpret_cast<unsigned *>(flags + 1), *gen = reinterpret_cast<unsigned *>(flags + 2);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = gj_load_acquire(gen);
+        __threadfence();
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            atomicExch(count, 0u);
+            gj_store_release(gen, g + 1);
+        } else {
+            unsigned long long t0;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+            while (gj_load_acquire(gen) == g) {
+                if (atomicAdd(reinterpret_cast<unsigned *>(flags + 3), 0u)) { ok = 0; break; }
+                unsigned long long t;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                if (t - t0 > kGjWaitNs) {
+                    atomicExch(flags + 3, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+__global__ void __launch_bounds__(kGjThreads) k_gauss_jordan_grid(int32_t n, const double *__restrict__ a_in,
+                                                                  double *a, double *prow, double *krow,
+                                                                  int32_t *perm, int32_t *flags) {
+    __shared__ double red_v[kGjThreads / 32];
+    __shared__ int32_t red_i[kGjThreads / 32];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int32_t G = gridDim.x, bid = blockIdx.x;
+    for (int32_t i = bid; i < n; i += G)
+        for (int32_t j = tid; j < n; j += nt) a[(int64_t)i * n + j] = a_in[(int64_t)i * n + j];
+    if (!gj_grid_barrier(flags)) return;
+    for (int32_t k = 0; k < n; ++k) {
+        if (bid == 0) {
+            // pivot: max |a_ik|, i >= k, lowest index on ties
+            double best = -1.0;
+            int32_t bi = k;
+            for (int32_t i = k + tid; i < n; i += nt) {
+                const double t = fabs(__ldcg(a + (int64_t)i * n + k));
+                if (t > best) { best = t; bi = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_down_sync(0xffffffffu, best, o);
+                const int32_t oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
+            __syncthreads();
+            if (tid == 0) {
+                double bb = -1.0;
+                int32_t ii = k;
+                for (int w = 0; w < nt / 32; ++w)
+                    if (red_v[w] > bb || (red_v[w] == bb && red_i[w] < ii)) { bb = red_v[w]; ii = red_i[w]; }
+                red_i[0] = bb > 0.0 ? ii : -1;
+                perm[k] = red_i[0];
+                if (bb <= 0.0) flags[0] = 1;
+            }
+            __syncthreads();
+            const int32_t p = red_i[0];
+            if (p >= 0)
+                for (int32_t j = tid; j < n; j += nt) {
+                    prow[j] = __ldcg(a + (int64_t)p * n + j);
+                    krow[j] = __ldcg(a + (int64_t)k * n + j);
+                }
+        }
+        if (!gj_grid_barrier(flags)) return;
+        const int32_t p = __ldcg(perm + k);
+        if (p < 0) return;   // singular: every block leaves at the same step
+        const double dk = 1.0 / __ldcg(prow + k);
+        for (int32_t i = bid; i < n; i += G) {
+            double *row = a + (int64_t)i * n;
+            if (i == k) {   // the new row k: the pivot row with a_kk <- 1, times 1 / pivot
+                for (int32_t j = tid; j < n; j += nt) row[j] = (j == k ? 1.0 : __ldcg(prow + j)) * dk;
+                continue;
+            }
+            const double *src = i == p ? krow : row;   // row p now holds the old row k
+            const double f = __ldcg(src + k);
+            __syncthreads();   // every thread has f before the thread of column k overwrites it
+            if (f != 0.0) {   // a_ik <- 0, then row_i -= f_i (new row k)
+                for (int32_t j = tid; j < n; j += nt) {
+                    const double nk = (j == k ? 1.0 : __ldcg(prow + j)) * dk;
+                    row[j] = (j == k ? 0.0 : __ldcg(src + j)) - f * nk;
+                }
+            } else if (i == p) {
+                for (int32_t j = tid; j < n; j += nt) row[j] = __ldcg(krow + j);
+            }
+        }
+        if (!gj_grid_barrier(flags)) return;
+    }
+    // undo the row exchanges as column exchanges, last first (one thread per row)
+    for (int32_t i = bid + G * tid; i < n; i += G * nt) {
+        double *row = a + (int64_t)i * n;
+        for (int32_t k = n - 1; k >= 0; --k) {
+            const int32_t p = __ldcg(perm + k);
+            if (p != k) {
+                const double t = row[k];
+                row[k] = row[p];
+                row[p] = t;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // host: one hierarchy
 static cptr_status transpose(Ctx *c, const Csr &A, int32_t ncols, Csr &T) {
@@ -675,13 +807,13 @@ cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, con
         if (!c->coarse_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->coarse_stream, cudaStreamNonBlocking));
         if (!c->side_fork) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&c->side_fork, cudaEventDisableTiming));
         if (!h.gj_done) CPTR_CUDA_TRY(c, cudaEventCreateWithFlags(&h.gj_done, cudaEventDisableTiming));
-        if (!h.gj_flag) CPTR_TRY(dalloc_t(c, &h.gj_flag, 1));
-        double *D = nullptr;
-        CPTR_TRY(dalloc_t(c, &D, (size_t)cn * cn));
+        if (!h.gj_flag) CPTR_TRY(dalloc_t(c, &h.gj_flag, 4));
+        double *D = nullptr;   // the dense matrix, then (multi-block inverse) pivot row, row k, pivots
+        CPTR_TRY(dalloc_t(c, &D, (size_t)cn * cn + 3 * (size_t)cn));
         CPTR_TRY(dalloc_t(c, &h.cinv, (size_t)cn * cn));
         CPTR_CUDA_TRY(c, cudaMemsetAsync(D, 0, sizeof(double) * (size_t)cn * cn, c->stream));
         (k_densify<<<nblk(cn, 128), 128, 0, c->stream>>>(cn, C.A.rp, C.A.ci, C.A.v, D), note_launch());
-        CPTR_CUDA_TRY(c, cudaMemsetAsync(h.gj_flag, 0, sizeof(int32_t), c->stream));
+        CPTR_CUDA_TRY(c, cudaMemsetAsync(h.gj_flag, 0, 4 * sizeof(int32_t), c->stream));
         CPTR_CUDA_TRY(c, cudaEventRecord(c->side_fork, c->stream));
         CPTR_CUDA_TRY(c, cudaStreamWaitEvent(c->coarse_stream, c->side_fork, 0));
         cudaStream_t ss = c->coarse_stream;
@@ -693,10 +825,31 @@ cptr_status amg_setup(Ctx *c, Hier &h, const int32_t *rp, const int32_t *ci, con
                                                   kGjSmemBytes));
             (k_gauss_jordan_smem<<<1, 1024, smem, ss>>>(cn, D, h.cinv, h.gj_flag), note_launch());
         } else {
-            const size_t smem = sizeof(double) * (size_t)(cn > 0 ? cn : 1);
-            CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  kGjFacBytes));
-            (k_gauss_jordan<<<1, 1024, smem, ss>>>(cn, D, h.cinv, h.gj_flag), note_launch());
+            // many blocks, all resident (cooperative launch); one block where that is not available
+            int dev = 0, sms = 0, coop = 0, per_sm = 0;
+            CPTR_CUDA_TRY(c, cudaGetDevice(&dev));
+            CPTR_CUDA_TRY(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            CPTR_CUDA_TRY(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+            CPTR_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gauss_jordan_grid, kGjThreads, 0));
+            const int G = std::min<int>(sms, cn);
+            bool launched = false;
+            if (coop && per_sm >= 1 && G >= 2) {
+                int32_t n_arg = cn;
+                const double *a_in = D;
+                double *a_out = h.cinv, *prow = D + (size_t)cn * cn, *krow = prow + cn;
+                int32_t *perm = reinterpret_cast<int32_t *>(krow + cn), *flags = h.gj_flag;
+                void *args[] = {&n_arg, &a_in, &a_out, &prow, &krow, &perm, &flags};
+                launched = cudaLaunchCooperativeKernel((const void *)k_gauss_jordan_grid, dim3(G), dim3(kGjThreads), args,
+                                                       0, ss) == cudaSuccess;
+                if (launched) note_launch();
+                else cudaGetLastError();   // clear the refusal; the one-block kernel follows
+            }
+            if (!launched) {
+                const size_t smem = sizeof(double) * (size_t)(cn > 0 ? cn : 1);
+                CPTR_CUDA_TRY(c, cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      kGjFacBytes));
+                (k_gauss_jordan<<<1, 1024, smem, ss>>>(cn, D, h.cinv, h.gj_flag), note_launch());
+            }
         }
         CPTR_CUDA_TRY(c, cudaGetLastError());
         if (c->pool) CPTR_CUDA_TRY(c, cudaFreeAsync(D, ss));
@@ -823,10 +976,11 @@ cptr_status amg_coarsest_wait(Ctx *c, Hier &h) {
     double t0 = host_ms();
     h.gj_pending = false;
     CPTR_CUDA_TRY(c, cudaStreamWaitEvent(c->stream, h.gj_done, 0));
-    int32_t sing = 0;
-    CPTR_TRY(copy_to_host(c, &sing, h.gj_flag, sizeof(int32_t)));
+    int32_t fl[4] = {0, 0, 0, 0};
+    CPTR_TRY(copy_to_host(c, fl, h.gj_flag, sizeof(fl)));
     setup_tick(c, SETUP_COARSEST, &t0);
-    if (sing) return c->fail(CPTR_ESINGULAR, "AMG: singular coarsest-level matrix");
+    if (fl[3]) return c->fail(CPTR_ETIMEOUT, "AMG coarsest inverse: a bounded wait gave up");
+    if (fl[0]) return c->fail(CPTR_ESINGULAR, "AMG: singular coarsest-level matrix");
     return CPTR_OK;
 }
 

@@ -117,6 +117,28 @@ def test_vcycle(name, smoother):
         assert relerr(host(x), o.vcycle(which, b)) <= 1e-10
 
 
+@pytest.mark.parametrize("n_levels", [1, 2])
+def test_coarsest_inverse_of_many_rows(n_levels):
+    """Coarsest matrices larger than one block's shared memory are inverted by the multi-block
+    Gauss-Jordan kernel (one grid of resident blocks, two grid barriers per pivot): with one level
+    the V-cycle is A^{-1} b on the 1024-cell system, with two levels the coarsest level has a few
+    hundred rows; against the oracle's dense LU solve, and A x = b checked on the host."""
+    s, o, g = pair("parity", max_levels=n_levels, dense_max=4096)
+    for which in (0, 1):
+        lev = g.hierarchy(which)
+        assert lev[-1]["dense"] and lev[-1]["n"] > 160, [L["n"] for L in lev]
+        b = synth.normal(31 + which, s["n"])
+        x = torch.empty(s["n"], dtype=torch.float64, device="cuda")
+        cp.cptr_apply_vcycle(g.ctx, which, dev(b), x)
+        assert relerr(host(x), o.vcycle(which, b)) <= 1e-10
+        if n_levels == 1:
+            L = lev[0]
+            A = np.zeros((L["n"], L["n"]))
+            for i in range(L["n"]):
+                A[i, L["ci"][L["rp"][i]:L["rp"][i + 1]]] = L["v"][L["rp"][i]:L["rp"][i + 1]]
+            assert np.linalg.norm(A @ host(x) - b) <= 1e-10 * np.linalg.norm(b)
+
+
 @pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "line"])
 def test_ilu(name):
     s, o, g = pair(name)
