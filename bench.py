@@ -68,6 +68,13 @@ def parse():
     p.add_argument("--no-mesh-study", action="store_true",
                    help="skip the 2-D mesh-refinement study (Tables meshW, meshH, anisomeshW analogues)")
     p.add_argument("--mesh-study-max-n", type=int, default=640)
+    p.add_argument("--ncu-range", choices=["headline", "vcycle", "vcycle_mixed", "spmv_b4"], default=None,
+                   help="after the warm-up, run one untimed piece of work between cudaProfilerStart and "
+                        "cudaProfilerStop (for ncu --profile-from-start off): a headline step; one V-cycle of "
+                        "the headline's pressure hierarchy; the same in the mixed form; one outer SpMV and one "
+                        "preconditioner application of the three-phase FP64 S_e solver")
+    p.add_argument("--three-phase-forms", default=None,
+                   help="comma-separated subset of the three-phase forms to run (default: all)")
     p.add_argument("--profile-steps", type=int, default=3,
                    help="steps of the separate pass that times kernel families with CUDA events")
     return p.parse_args()
@@ -335,6 +342,27 @@ def profiled_pass(cp, S, step, flush, steps, mask):
     return fam, vc
 
 
+def profiled_range(args, section, work):
+    """work() once, untimed, inside a profiler range when --ncu-range names this section."""
+    if args.ncu_range != section:
+        return
+    import torch
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    work()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+
+
+def vcycle_once(cp, S, n, dev):
+    """One V-cycle of the pressure hierarchy on a seeded right-hand side (cptr_apply_vcycle)."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(5)
+    b = torch.randn(n, generator=g, dtype=torch.float64).to(dev)
+    x = torch.empty_like(b)
+    return lambda: cp.cptr_apply_vcycle(S.ctx, 0, b, x)
+
+
 def ours(args, rank, world, local_rank, oracle_jobs):
     import numpy as np
     import torch
@@ -366,6 +394,8 @@ def ours(args, rank, world, local_rank, oracle_jobs):
     for _ in range(args.warmup):
         info = step()
     assert info["status"] == "CPTR_OK", info
+    profiled_range(args, "headline", step)
+    profiled_range(args, "vcycle", vcycle_once(cp, S, n, dev))
     # the headline: plain steps, no per-kernel events in the timed region
     barrier(world)
     torch.cuda.synchronize(dev)
@@ -487,6 +517,8 @@ def ours(args, rank, world, local_rank, oracle_jobs):
                 return Sv.solve(d["rhs"], RTOL, x=x)[1]
 
             step_v()
+            if name == "cptr_mixed":
+                profiled_range(args, "vcycle_mixed", vcycle_once(cp, Sv, n, dev))
             evs, infs = [], []
             for _ in range(3):
                 flush.zero_()
@@ -656,8 +688,11 @@ def three_phase(args, dev, stream, flush):
     import synth
     import paper_1907_04229_gb300 as cp
 
+    forms = None if args.three_phase_forms is None else set(args.three_phase_forms.split(","))
     nets, training = {}, {}
     for base in ("se", "att"):
+        if forms is not None and not any(f"learned_{base}" in f for f in forms):
+            continue
         P, train_ms, loss0, loss1, nsamp = train_learned(dev, stream, base)
         nets[base] = P
         training[base] = {"samples": nsamp, "steps": LEARNED_STEPS, "lr": LEARNED_LR, "train_ms": round(train_ms, 2),
@@ -695,6 +730,8 @@ def three_phase(args, dev, stream, flush):
             ("fp64_att", dict(schur="att", max_it=200), None, None, 1),
             ("fp64_learned_att", dict(schur="learned", max_it=200), None, "att", 1))
     for name, opts, st_base, net, nrun in runs:
+        if forms is not None and name not in forms:
+            continue
         Sv = cp.Solver(stream=stream, **opts)
         if net:
             cp.cptr_set_mlp(Sv.ctx, nets[net])
@@ -705,6 +742,13 @@ def three_phase(args, dev, stream, flush):
 
         if nrun > 1:
             step_v()
+        if name == "fp64_se":
+            zt, wt = torch.zeros_like(x).normal_(), torch.empty_like(x)
+
+            def spmv_and_precond():
+                cp.cptr_apply_matrix(Sv.ctx, zt, wt)
+                cp.cptr_apply_precond(Sv.ctx, zt, wt)
+            profiled_range(args, "spmv_b4", spmv_and_precond)
         evs, infs = [], []
         for _ in range(nrun):
             flush.zero_()

@@ -1024,6 +1024,7 @@ __global__ void __launch_bounds__(512) k_vc_down(int32_t n, const int32_t *__res
                                                   const int32_t *__restrict__ ci, const VT *__restrict__ v,
                                                   const XT *__restrict__ dinv, const XT *__restrict__ b,
                                                   XT *__restrict__ t, XT *__restrict__ r) {
+    pdl_wait();
     int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int32_t row = (int32_t)(gid / G);
     int lane = threadIdx.x % G;
@@ -1054,6 +1055,7 @@ __global__ void __launch_bounds__(512) k_vc_post(int32_t n, const int32_t *__res
                                                   const int32_t *__restrict__ ci, const VT *__restrict__ v,
                                                   const XT *__restrict__ dinv, const XT *__restrict__ b,
                                                   const XT *__restrict__ t, XT *__restrict__ x) {
+    pdl_wait();
     int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int32_t row = (int32_t)(gid / G);
     int lane = threadIdx.x % G;
@@ -1075,6 +1077,7 @@ __global__ void __launch_bounds__(512) k_vc_post(int32_t n, const int32_t *__res
 // coarsest dense solve x = A_c^{-1} b in FP64 (one warp per row), whatever the vector type
 template <typename XT>
 __global__ void k_dense_mv(int32_t n, const double *__restrict__ M, const XT *__restrict__ b, XT *__restrict__ x) {
+    pdl_wait();
     int32_t row = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (row >= n) return;
@@ -1085,6 +1088,7 @@ __global__ void k_dense_mv(int32_t n, const double *__restrict__ M, const XT *__
 }
 template <typename XT>
 __global__ void k_diag_scale(int32_t n, const XT *d, const XT *b, XT *x) {
+    pdl_wait();
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = d[i] * b[i];
 }
@@ -1095,12 +1099,12 @@ static void launch_down(cudaStream_t s, const Level &L, const VT *v, const XT *d
     unsigned grid = nblk((int64_t)L.A.n * G, T);
     const Csr &A = L.A;
     switch (G) {
-    case 1: (k_vc_down<1, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
-    case 2: (k_vc_down<2, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
-    case 4: (k_vc_down<4, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
-    case 8: (k_vc_down<8, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
-    case 16: (k_vc_down<16, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
-    default: (k_vc_down<32, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, r), note_launch()); break;
+    case 1: launch_pdl(k_vc_down<1, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
+    case 2: launch_pdl(k_vc_down<2, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
+    case 4: launch_pdl(k_vc_down<4, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
+    case 8: launch_pdl(k_vc_down<8, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
+    case 16: launch_pdl(k_vc_down<16, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
+    default: launch_pdl(k_vc_down<32, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
     }
 }
 template <typename VT, typename XT>
@@ -1109,12 +1113,12 @@ static void launch_post(cudaStream_t s, const Level &L, const VT *v, const XT *d
     unsigned grid = nblk((int64_t)L.A.n * G, T);
     const Csr &A = L.A;
     switch (G) {
-    case 1: (k_vc_post<1, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
-    case 2: (k_vc_post<2, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
-    case 4: (k_vc_post<4, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
-    case 8: (k_vc_post<8, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
-    case 16: (k_vc_post<16, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
-    default: (k_vc_post<32, VT, XT><<<grid, T, 0, s>>>(A.n, A.rp, A.ci, v, dinv, b, t, x), note_launch()); break;
+    case 1: launch_pdl(k_vc_post<1, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, x); break;
+    case 2: launch_pdl(k_vc_post<2, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, x); break;
+    case 4: launch_pdl(k_vc_post<4, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, x); break;
+    case 8: launch_pdl(k_vc_post<8, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, x); break;
+    case 16: launch_pdl(k_vc_post<16, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, x); break;
+    default: launch_pdl(k_vc_post<32, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, x); break;
     }
 }
 
@@ -1184,6 +1188,7 @@ __device__ __forceinline__ XT ldval(const void *v, int st, int64_t k) {
 template <typename XT>
 __global__ void __launch_bounds__(kFuseThreads) k_vc_fused_down(const LevelDev *__restrict__ L, int l0, int lc,
                                                                 const XT *b0) {
+    pdl_wait();
     for (int l = l0; l < lc; ++l) {
         const LevelDev &A = L[l];
         const XT *b = l == l0 ? b0 : static_cast<const XT *>(A.b);
@@ -1214,6 +1219,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_vc_fused_down(const LevelDev *
 template <typename XT>
 __global__ void __launch_bounds__(kFuseThreads) k_vc_fused_up(const LevelDev *__restrict__ L, int l0, int lc,
                                                               const XT *b0, XT *x0) {
+    pdl_wait();
     for (int l = lc - 1; l >= l0; --l) {
         const LevelDev &A = L[l];
         const LevelDev &C = L[l + 1];
@@ -1284,9 +1290,9 @@ static void vcycle_level(const Ctx *c, const Hier &h, int l, const XT *b, XT *x)
     const bool lo = sizeof(XT) == 4;
     if (l == h.nlev - 1) {
         if (h.dense) {
-            (k_dense_mv<XT><<<nblk((int64_t)n * 32, 256), 256, 0, s>>>(n, h.cinv, b, x), note_launch());
+            launch_pdl(k_dense_mv<XT>, nblk((int64_t)n * 32, 256), 256, 0, s, n, (const double *)h.cinv, b, x);
         } else {  // two smoothing sweeps from zero
-            (k_diag_scale<XT><<<nblk(n, 256), 256, 0, s>>>(n, LV::dinv(L), b, LV::t(L)), note_launch());
+            launch_pdl(k_diag_scale<XT>, nblk(n, 256), 256, 0, s, n, LV::dinv(L), b, LV::t(L));
             if (!lo) launch_post<double, double>(s, L, L.A.v, L.dinv, (const double *)b, L.t, (double *)x);
             else if (L.st == ST_BF16) launch_post<bf16, float>(s, L, (const bf16 *)L.Av_lo, L.dinv32, (const float *)b, L.t32, (float *)x);
             else launch_post<float, float>(s, L, (const float *)L.Av_lo, L.dinv32, (const float *)b, L.t32, (float *)x);
@@ -1296,9 +1302,9 @@ static void vcycle_level(const Ctx *c, const Hier &h, int l, const XT *b, XT *x)
     if (l == h.fuse_l0 && (lo ? h.ldev32 : h.ldev64)) {   // levels l .. nlev-2 fused
         const LevelDev *ld = lo ? h.ldev32 : h.ldev64;
         const int lc = h.nlev - 1;
-        (k_vc_fused_down<XT><<<1, kFuseThreads, 0, s>>>(ld, l, lc, b), note_launch());
+        launch_pdl(k_vc_fused_down<XT>, 1, kFuseThreads, 0, s, ld, l, lc, b);
         vcycle_level<XT>(c, h, lc, LV::b(h.L[lc]), LV::x(h.L[lc]));
-        (k_vc_fused_up<XT><<<1, kFuseThreads, 0, s>>>(ld, l, lc, b, x), note_launch());
+        launch_pdl(k_vc_fused_up<XT>, 1, kFuseThreads, 0, s, ld, l, lc, b, x);
         return;
     }
     const Level &C = h.L[l + 1];

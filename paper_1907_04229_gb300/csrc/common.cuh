@@ -446,9 +446,38 @@ __device__ __forceinline__ XT row_dot_batched(int32_t k0, int32_t k1, const int3
     return acc;
 }
 
-// lanes per row for a CSR kernel, from the average row length
+// Programmatic dependent launch: a kernel launched by launch_pdl may be scheduled while the kernel
+// before it on the stream is still running, which hides the launch latency of short kernels in a
+// chain (the V-cycle's).  Such a kernel calls pdl_wait() before its first global memory access:
+// that waits until the previous kernel has completed and its writes are visible, then lets the
+// next kernel on the stream be scheduled.  In a kernel launched without the attribute both
+// instructions do nothing.
+__device__ __forceinline__ void pdl_wait() {
+    asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory");
+}
+void note_launch();
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+    note_launch();
+}
+
+// lanes per row for a CSR kernel without a tuned shape: one lane per row on large operators with
+// short rows (what the autotuner picks there on GB300: a cross-lane sum costs a warp-wide FP64
+// instruction per step), otherwise from the average row length
 inline int lanes_for(int32_t n, int32_t nnz) {
     double avg = n > 0 ? double(nnz) / n : 1.0;
+    if (n >= 16384 && avg <= 24.0) return 1;
     if (avg <= 4.5) return 4;
     if (avg <= 9.0) return 8;
     if (avg <= 24.0) return 16;

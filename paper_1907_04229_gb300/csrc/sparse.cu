@@ -529,6 +529,7 @@ __global__ void __launch_bounds__(512) k_csr_spmv(int32_t n, const int32_t *__re
                                                    const int32_t *__restrict__ ci, const VT *__restrict__ v,
                                                    const XT *__restrict__ x, XT *__restrict__ y, int mode,
                                                    const XT *__restrict__ c0) {
+    pdl_wait();
     int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int32_t row = (int32_t)(gid / G);
     int lane = threadIdx.x % G;
@@ -558,12 +559,12 @@ void launch_csr_spmv_t(cudaStream_t s, int32_t n, int32_t nnz, const int32_t *rp
     const int G = sh.G ? sh.G : lanes_for(n, nnz), T = sh.T;
     unsigned grid = nblk((int64_t)n * G, T);
     switch (G) {
-    case 1: (k_csr_spmv<1, VT, XT><<<grid, T, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
-    case 2: (k_csr_spmv<2, VT, XT><<<grid, T, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
-    case 4: (k_csr_spmv<4, VT, XT><<<grid, T, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
-    case 8: (k_csr_spmv<8, VT, XT><<<grid, T, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
-    case 16: (k_csr_spmv<16, VT, XT><<<grid, T, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
-    default: (k_csr_spmv<32, VT, XT><<<grid, T, 0, s>>>(n, rp, ci, v, x, y, mode, c0), note_launch()); break;
+    case 1: launch_pdl(k_csr_spmv<1, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0); break;
+    case 2: launch_pdl(k_csr_spmv<2, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0); break;
+    case 4: launch_pdl(k_csr_spmv<4, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0); break;
+    case 8: launch_pdl(k_csr_spmv<8, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0); break;
+    case 16: launch_pdl(k_csr_spmv<16, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0); break;
+    default: launch_pdl(k_csr_spmv<32, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0); break;
     }
 }
 template void launch_csr_spmv_t<double, double>(cudaStream_t, int32_t, int32_t, const int32_t *, const int32_t *,
