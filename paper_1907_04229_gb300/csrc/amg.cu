@@ -600,6 +600,13 @@ __global__ void __launch_bounds__(kGjThreads) k_gauss_jordan_grid(int32_t n, con
     }
 }
 
+void amg_preload() {
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_gauss_jordan_grid);
+    cudaFuncGetAttributes(&fa, k_gauss_jordan_smem);
+    cudaFuncGetAttributes(&fa, k_gauss_jordan);
+}
+
 // ------------------------------------------------------------------------------------------------
 // host: one hierarchy
 static cptr_status transpose(Ctx *c, const Csr &A, int32_t ncols, Csr &T) {

@@ -496,6 +496,7 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
         cptr_destroy(ctx);
         return CPTR_ENOMEM;
     }
+    amg_preload();
     *out = ctx;
     return CPTR_OK;
 }

@@ -1224,6 +1224,147 @@ __global__ void __launch_bounds__(kSfThreads) k_bilu_factor_g(int32_t n, unsigne
     }
 }
 
+// The factorisation with a row per warp.  On GB300 a warp-wide FP64 instruction occupies a
+// sub-partition's FP64 pipe for 64 cycles, so a level's time is bounded by the FP64 instructions
+// the warp holding a row issues: here every block product is spread over the lanes (one lane per
+// entry of L_ik = A_ik D_k^{-1}, one per entry of each updated block A_ij -= L_ik U_kj), about 40
+// FP64 instructions per row of a 7-point 3 x 3 pattern instead of ~150 with a row over four lanes.
+// Each entry is summed in the order of k_bilu_factor_sf (the same values), and four lanes invert
+// the pivot block together (group_inverse).  Warps take rows by ticket in level order, so every
+// dependency belongs to a warp that is already running.  Before the flags are set: the row's own
+// blocks and columns, the pivot and row-end positions of its dependencies and the column indices
+// of their upper parts (none written during the launch).  Once every flag is set and an acquire
+// fence orders what follows: each dependency's pivot inverse and upper blocks, read through L2.
+// The pivot and upper blocks are written and the flag released before the lower blocks (no row of
+// the launch reads those).  Shared memory per warp: the row's blocks, the dependencies' windows,
+// L_ik, and the integer tables (kFwWarps warps per block).
+constexpr int kFwWarps = 4;
+__host__ __device__ inline int fw_row_doubles(int B, int maxrow) { return (maxrow * B * B + 1) & ~1; }
+__host__ __device__ inline int fw_win_doubles(int B, int maxu) { return ((1 + maxu) * B * B + 1) & ~1; }
+__host__ __device__ inline int fw_warp_doubles(int B, int maxrow, int maxdep, int maxu) {
+    return fw_row_doubles(B, maxrow) + maxdep * fw_win_doubles(B, maxu) + ((B * B + 1) & ~1);
+}
+__host__ __device__ inline int fw_warp_ints(int maxrow, int maxdep, int maxu) {
+    return maxrow + maxdep * (2 + maxu) + maxu;
+}
+
+template <int B>
+__global__ void __launch_bounds__(32 * kFwWarps) k_bilu_factor_w(int32_t n, unsigned *ticket,
+                                                                 const int32_t *__restrict__ pos,
+                                                                 const int32_t *__restrict__ rp,
+                                                                 const int32_t *__restrict__ ci,
+                                                                 const int32_t *__restrict__ diag, double *LU,
+                                                                 int32_t *flag, int32_t epoch, int32_t *singular,
+                                                                 KState *ks, int maxrow, int maxdep, int maxu) {
+    constexpr int BB = B * B;
+    constexpr unsigned kAll = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char fw_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int per = fw_warp_doubles(B, maxrow, maxdep, maxu), W = fw_win_doubles(B, maxu);
+    double *rowb = reinterpret_cast<double *>(fw_smem) + (int64_t)warp * per;
+    double *depw = rowb + fw_row_doubles(B, maxrow);
+    double *lbuf = depw + (int64_t)maxdep * W;
+    int32_t *cols = reinterpret_cast<int32_t *>(reinterpret_cast<double *>(fw_smem) + (int64_t)kFwWarps * per) +
+                    warp * fw_warp_ints(maxrow, maxdep, maxu);
+    int32_t *dcs = cols + maxrow, *ecs = dcs + maxdep, *ucol = ecs + maxdep, *upos = ucol + maxdep * maxu;
+    for (;;) {
+        unsigned tk = 0;
+        if (lane == 0) tk = atomicAdd(ticket, 1u);
+        const int32_t t = (int32_t)__shfl_sync(kAll, tk, 0);
+        if (t >= n) return;
+        const int32_t i = pos[t], k0 = rp[i], e = rp[i + 1], kd = diag[i];
+        const int32_t len = e - k0, nd = kd - k0;
+        for (int32_t k = lane; k < len; k += 32) cols[k] = ci[k0 + k];
+        for (int32_t u = lane; u < len * BB; u += 32) rowb[u] = LU[(int64_t)k0 * BB + u];
+        __syncwarp();
+        for (int32_t k = lane; k < nd; k += 32) {
+            const int32_t c = cols[k];
+            dcs[k] = diag[c];
+            ecs[k] = rp[c + 1];
+        }
+        __syncwarp();
+        for (int32_t k = 0; k < nd; ++k)
+            for (int32_t qq = dcs[k] + 1 + lane; qq < ecs[k]; qq += 32) ucol[k * maxu + (qq - dcs[k] - 1)] = ci[qq];
+        // the dependencies' flags (each lane polls some), bounded
+        unsigned long long tw = 0;
+        bool waiting = false;
+        for (;;) {
+            bool p = false;
+            for (int32_t k = lane; k < nd; k += 32) {
+                int32_t f;
+                asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flag + cols[k]) : "memory");
+                p |= f != epoch;
+            }
+            if (!__any_sync(kAll, p)) break;
+            bool late = false;
+            if (!waiting) {
+                tw = gtimer();
+                waiting = true;
+            } else {
+                late = gtimer() - tw > kWaitNs;
+            }
+            if (__any_sync(kAll, late)) {
+                if (lane == 0) atomicExch(&ks->wait_err, 1);
+                break;
+            }
+            __nanosleep(20);
+        }
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        __syncwarp();
+        for (int32_t k = 0; k < nd; ++k) {
+            const int64_t lo = (int64_t)dcs[k] * BB, hi = (int64_t)ecs[k] * BB;
+            for (int64_t u = lo + lane; u < hi; u += 32) depw[(int64_t)k * W + (u - lo)] = __ldcg(LU + u);
+        }
+        __syncwarp();
+        for (int32_t k = 0; k < nd; ++k) {
+            const double *dinv = depw + (int64_t)k * W;   // the pivot inverse, then the upper blocks
+            const int32_t m = ecs[k] - dcs[k] - 1;
+            for (int32_t q2 = lane; q2 < m; q2 += 32) {   // where each upper block of row k sits in row i
+                const int32_t jj = ucol[k * maxu + q2];
+                int32_t p = -1;
+                for (int32_t c = k + 1; c < len; ++c)
+                    if (cols[c] == jj) {
+                        p = c;
+                        break;
+                    }
+                upos[q2] = p;
+            }
+            if (lane < BB) {   // L_ik = A_ik D_k^{-1}
+                const int rr = lane / B, q = lane - rr * B;
+                double sacc = 0.0;
+#pragma unroll
+                for (int u = 0; u < B; ++u) sacc = fma(rowb[k * BB + rr * B + u], dinv[u * B + q], sacc);
+                lbuf[lane] = sacc;
+            }
+            __syncwarp();
+            if (lane < BB) rowb[k * BB + lane] = lbuf[lane];
+            for (int32_t x = lane; x < m * BB; x += 32) {   // A_ij -= L_ik U_kj
+                const int32_t q2 = x / BB, ee = x - q2 * BB;
+                const int32_t p = upos[q2];
+                if (p >= 0) {
+                    const int rr = ee / B, q = ee - rr * B;
+                    const double *u = dinv + (q2 + 1) * BB;
+                    double sacc = rowb[p * BB + ee];
+#pragma unroll
+                    for (int w2 = 0; w2 < B; ++w2) sacc = fma(-lbuf[rr * B + w2], u[w2 * B + q], sacc);
+                    rowb[p * BB + ee] = sacc;
+                }
+            }
+            __syncwarp();
+        }
+        if (lane < 4) {
+            if (!group_inverse<B>(rowb + nd * BB, lane, 0xFu, 0) && lane == 0) atomicOr(singular, 1);
+        }
+        __syncwarp();
+        for (int32_t u = nd * BB + lane; u < len * BB; u += 32) LU[(int64_t)k0 * BB + u] = rowb[u];
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(flag + i), "r"(epoch) : "memory");
+        for (int32_t u = lane; u < nd * BB; u += 32) LU[(int64_t)k0 * BB + u] = rowb[u];
+        __syncwarp();
+    }
+}
+
 // level sets of one direction: pos (position -> row), inv, and the level pointers (host)
 // stable counting sort of the rows by level on the host (rows of a level in ascending order keep
 // the sweeps' accesses local): positions -> rows, rows -> positions, level pointers
@@ -2053,14 +2194,37 @@ cptr_status ilu_setup(Ctx *c) {
         maxdep = h_ext[1];
         maxu = h_ext[2];
     }
-    const size_t fs_rowsz = (size_t)((maxrow * BB + 1) & ~1), fs_w = (size_t)(((1 + maxu) * BB + 3) & ~1);
-    const size_t fs_bytes = (size_t)64 * ((fs_rowsz + (size_t)maxdep * fs_w) * 8 + (size_t)(maxrow + maxdep * (2 + maxu)) * 4);
     const unsigned fgrid = std::min<unsigned>(nblk(n, 64), 8 * 152);
-    const size_t fg_bytes = fs_bytes / 64 * kSfRowsG;   // the same per row, kSfRowsG rows per block
-    if (fg_bytes <= 100 * 1024) {
+    // a row per warp (k_bilu_factor_w) while its tables fit; one row per thread otherwise
+    const size_t fw_bytes = (size_t)kFwWarps * ((size_t)fw_warp_doubles(c->b, maxrow, maxdep, maxu) * 8 +
+                                                 (size_t)fw_warp_ints(maxrow, maxdep, maxu) * 4);
+    const size_t fs_rowsz = (size_t)((maxrow * BB + 1) & ~1), fs_w = (size_t)(((1 + maxu) * BB + 3) & ~1);
+    const size_t fg_bytes = (size_t)kSfRowsG * ((fs_rowsz + (size_t)maxdep * fs_w) * 8 +
+                                                (size_t)(maxrow + maxdep * (2 + maxu)) * 4);
+    // Narrow levels (up to ~2000 rows on average) are latency bound: a row per warp issues the
+    // fewest FP64 instructions per row's chain.  Wide levels are bound by the FP64 pipe's
+    // throughput, where a row over four lanes issues ~2.5x fewer FP64 instructions per row.
+    const bool narrow = (double)n <= 2000.0 * std::max<int32_t>(c->nlev_f, 1);
+    if (narrow && fw_bytes <= 100 * 1024) {
+        // two blocks per SM: rows a few levels ahead of the wavefront are taken and wait on their
+        // flags, so a level's rows start as soon as the last of their dependencies is published
+        const unsigned wgrid = std::min<unsigned>(nblk(n, kFwWarps), 2 * 152);
+        if (c->b == 3) {
+            cudaFuncSetAttribute(k_bilu_factor_w<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+            (k_bilu_factor_w<3><<<wgrid, 32 * kFwWarps, fw_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
+                                                                         c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch,
+                                                                         fsing, c->ks, maxrow, maxdep, maxu),
+             note_launch());
+        } else {
+            cudaFuncSetAttribute(k_bilu_factor_w<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+            (k_bilu_factor_w<4><<<wgrid, 32 * kFwWarps, fw_bytes, st>>>(n, c->sf_ticket, c->lvl_f, c->ilu_rp, c->ilu_ci,
+                                                                         c->ilu_diag, c->LU, c->ilu_flags, c->ilu_epoch,
+                                                                         fsing, c->ks, maxrow, maxdep, maxu),
+             note_launch());
+        }
+    } else if (fg_bytes <= 100 * 1024) {
         // one block per SM (32 rows each, a few levels ahead of the wavefront): more rows in flight
-        // only poll, and measured slower.  Two SMs are left to the coarsest AMG inverses, whose
-        // single blocks need most of an SM's shared memory and run at the same time.
+        // only poll, and measured slower.  Two SMs are left to the coarsest AMG inverses.
         const unsigned ggrid = std::min<unsigned>(nblk(n, kSfRowsG), 150u);
         if (c->b == 3) {
             cudaFuncSetAttribute(k_bilu_factor_g<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
