@@ -47,6 +47,10 @@ void release_setup(Ctx *c) {
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;
     }
+    if (c->cycle_exec) {
+        cudaGraphExecDestroy(c->cycle_exec);
+        c->cycle_exec = nullptr;
+    }
     free_batch(c);
     c->sell_shape = Shape();
     c->tl_best_ty = c->tl_best_tz = 0;

@@ -396,6 +396,9 @@ struct Ctx {
     cudaEvent_t amg_fork[2] = {};
     cudaEvent_t side_fork = nullptr, side_join = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    cudaGraphExec_t cycle_exec = nullptr;   // a whole restart cycle: WHILE node over the Arnoldi step
+    int64_t cycle_step_launches = 0;        // kernels per step of the cycle graph
+    bool cycle_failed = false;              // not available here: per-step graphs are used
     int64_t graph_launches = 0;
     uint32_t graph_mask = 0;
     int32_t graph_inject = 0;
