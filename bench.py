@@ -36,7 +36,12 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 LEARNED_STEPS, LEARNED_LR = 2000, 2e-3
 # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/ (the
 # current kernels; None where no capture of the current code exists)
-PROFILED_TRAFFIC = {"spmv": 113_717_248, "stage1_resid": None, "ilu_fwd": 102_265_344, "ilu_bwd": 118_584_832}
+PROFILED_TRAFFIC = {"spmv": 113_717_248, "stage1_resid": None, "ilu_fwd": 102_265_344, "ilu_bwd": 118_584_832,
+                    # the finest V-cycle level of the pressure hierarchy (cold-L2 captures, one launch each)
+                    "vcycle_p_down": 20_470_528, "vcycle_p_restrict": 6_354_944, "vcycle_p_prolong": 7_413_760,
+                    "vcycle_p_post": 22_069_504, "vcycle_p_down_mixed": 13_381_120,
+                    "vcycle_p_restrict_mixed": 4_057_344, "vcycle_p_prolong_mixed": 4_857_600,
+                    "vcycle_p_post_mixed": 14_180_608}
 # the ILU figures are those of the paired-level sweeps (their tables hold the substituted blocks)
 PROFILED_ILU_SCHEDULE = "paired"
 
@@ -57,6 +62,9 @@ def parse():
                    help="run the three-phase section on an NX NY NZ box instead of 200x200x50 (profiling)")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="fixed launch shapes in the headline solver (default: autotuned at the first set-up, cached)")
+    p.add_argument("--graph", choices=["cycle", "step"], default="cycle",
+                   help="headline solver: each restart cycle as one graph launch (device-side loop), or one "
+                        "graph launch per Arnoldi step (what per-kernel profilers see kernel by kernel)")
     p.add_argument("--ilu-sweep", choices=["auto", "levels", "chunked", "paired"], default="auto",
                    help="schedule of the headline solver's ILU(0) sweeps")
     p.add_argument("--ensemble-total", type=float, default=4e6,
@@ -383,7 +391,7 @@ def ours(args, rank, world, local_rank, oracle_jobs):
     d = {k: torch.as_tensor(np.ascontiguousarray(v), device=dev) for k, v in host.items()}
     x = torch.empty(dofs, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    head_opts = dict(autotune=int(args.autotune), ilu_sweep=args.ilu_sweep)
+    head_opts = dict(autotune=int(args.autotune), ilu_sweep=args.ilu_sweep, use_graph=1 if args.graph == "cycle" else 2)
     S = cp.Solver(stream=stream, **head_opts)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 

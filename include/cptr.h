@@ -93,7 +93,12 @@ typedef struct {
     int32_t seed;        /* PMIS weights: SplitMix64 stream seed + level */
     int32_t precision;   /* CPTR_PREC_* */
     int32_t check_every; /* host reads the convergence flag every k Arnoldi steps (default 1) */
-    int32_t use_graph;   /* 1: replay each Arnoldi step as one captured CUDA graph (default 1) */
+    int32_t use_graph;   /* 1 (default): each FGMRES restart cycle is one captured CUDA graph whose
+                          * conditional WHILE node repeats the Arnoldi step on the device until the
+                          * cycle ends (the host waits once per cycle); 2: one captured graph launch
+                          * per Arnoldi step (the host checks convergence after each); 0: direct
+                          * kernel launches.  Solves with per-family profiling or wait injection on
+                          * use per-step graphs. */
     int32_t ilu_order;   /* CPTR_ILU_NATURAL (default) or CPTR_ILU_MULTICOLOR */
     int32_t autotune;    /* 1: time the launch shapes of the V-cycle and SpMV kernels at set-up
                             and keep the fastest (see cptr_tuning); 0 (default): fixed shapes */

@@ -454,7 +454,7 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
         o.smoother < 0 || o.smoother > CPTR_SMOOTH_JACOBI || o.schur < CPTR_SCHUR_GIVEN ||
         o.schur > CPTR_SCHUR_DIAG || o.precision < CPTR_PREC_FP64 ||
         o.precision > CPTR_PREC_MIXED ||
-        o.ilu_order < CPTR_ILU_NATURAL || o.ilu_order > CPTR_ILU_MULTICOLOR || o.ilu_sweep < 0 || o.ilu_sweep > 4 ||
+        o.ilu_order < CPTR_ILU_NATURAL || o.ilu_order > CPTR_ILU_MULTICOLOR || o.ilu_sweep < 0 || o.ilu_sweep > 4 || o.use_graph < 0 || o.use_graph > 2 ||
         o.tile_y < 0 || o.tile_z < 0 || (size_t)o.tile_y * o.tile_z > 64 || o.decouple < CPTR_DECOUPLE_NONE ||
         o.decouple > CPTR_DECOUPLE_TI ||
         (o.decouple != CPTR_DECOUPLE_NONE && o.stage1 != CPTR_STAGE1_CPR && o.stage1 != CPTR_STAGE1_UAMG) ||

@@ -416,6 +416,9 @@ struct Ctx {
     double *partial_b = nullptr;           // per-tile reduction partials
     cudaGraphExec_t bgraph_exec = nullptr;
     int64_t bgraph_launches = 0;
+    cudaGraphExec_t bcycle_exec = nullptr;   // the ensemble's restart cycle as one graph launch
+    int64_t bcycle_step_launches = 0;
+    bool bcycle_failed = false;
     int32_t *flag = nullptr;    // device scratch flag
     int32_t *scan_tmp = nullptr; int64_t scan_tmp_len = 0;
     double setup_ms = 0.0;

@@ -527,7 +527,7 @@ cptr_status fgmres_solve(Ctx *c, const double *bw, double *x, double rtol, cptr_
     const unsigned vgrid = 4 * 152;
     // a whole cycle per launch when nothing is timed per kernel family (event nodes may not sit in
     // a conditional body) and no wait failure is injected; otherwise one graph per step
-    const bool cycle = c->o.use_graph && c->prof.mask == 0 && !c->inject_wait && !c->cycle_failed;
+    const bool cycle = c->o.use_graph == 1 && c->prof.mask == 0 && !c->inject_wait && !c->cycle_failed;
     if (cycle && !c->cycle_exec) CPTR_TRY(build_cycle_graph(c));
     if (c->o.use_graph && !(cycle && c->cycle_exec) &&
         (!c->graph_exec || c->graph_mask != c->prof.mask || c->graph_inject != c->inject_wait))
@@ -832,6 +832,79 @@ cptr_status build_batch_graph(Ctx *c) {
     return CPTR_OK;
 }
 
+// The condition of the ensemble cycle's WHILE node, after every lockstep step: count the step
+// (ks->k steps in this cycle, ks->its in the solve, mirrored into the shared header) and go on
+// while an instance still iterates in this cycle, the cycle and the solve have steps left and no
+// bounded wait gave up.
+__global__ void k_bcycle_cond(const KState *ksb, int n_inst, KState *ks, KHdr *hdr, int m, int max_it,
+                              cudaGraphConditionalHandle h) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    bool a = false;
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) a |= ksb[i].active && !ksb[i].done;
+    if (a) atomicOr(&any, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ks->k += 1;
+        ks->its += 1;
+        hdr[n_inst].k = ks->k;
+        hdr[n_inst].its = ks->its;
+        const bool more = any && !ks->wait_err && ks->k < m && ks->its < max_it;
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
+}
+
+// The ensemble's restart cycle as one graph launch (a conditional WHILE node over the lockstep
+// Arnoldi step of every instance); the per-step graph where conditional nodes are not available.
+cptr_status build_batch_cycle_graph(Ctx *c) {
+    if (c->bcycle_exec) {
+        cudaGraphExecDestroy(c->bcycle_exec);
+        c->bcycle_exec = nullptr;
+    }
+    if (!c->cap_stream) CPTR_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    CPTR_CUDA_TRY(c, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraph_t body = nullptr;
+    if (e == cudaSuccess) {
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
+        if (e == cudaSuccess) body = p.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess) {
+        cudaStream_t orig = c->stream;
+        c->stream = c->cap_stream;
+        const uint32_t mask = c->prof.mask;
+        c->prof.mask = 0;
+        begin_capture_count();
+        e = cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            arnoldi_step_batch(c);
+            (k_bcycle_cond<<<1, 256, 0, c->cap_stream>>>(c->ksb, c->n_inst, c->ks, c->hdr, c->o.restart, c->o.max_it, h),
+             note_launch());
+            e = cudaStreamEndCapture(c->cap_stream, &body);
+        }
+        c->bcycle_step_launches = end_capture_count();
+        c->prof.mask = mask;
+        c->stream = orig;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->bcycle_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->bcycle_exec = nullptr;
+        c->bcycle_failed = true;
+    }
+    return CPTR_OK;
+}
+
 cptr_status read_headers(Ctx *c) {
     CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->hdr_host, c->hdr, sizeof(KHdr) * (c->n_inst + 1), cudaMemcpyDeviceToHost,
                                      c->stream));
@@ -850,6 +923,8 @@ void free_batch(Ctx *c) {
     c->hdr_host = nullptr;
     if (c->bgraph_exec) cudaGraphExecDestroy(c->bgraph_exec);
     c->bgraph_exec = nullptr;
+    if (c->bcycle_exec) cudaGraphExecDestroy(c->bcycle_exec);
+    c->bcycle_exec = nullptr;
     c->n_inst = 0;
     c->n_tiles = 0;
     c->inst_cell0.clear();
@@ -860,7 +935,9 @@ cptr_status fgmres_solve_batch(Ctx *c, const double *bw, double *x, double rtol,
     const int64_t nb = (int64_t)c->n * c->b;
     cudaStream_t s = c->stream;
     const unsigned T = c->n_tiles;
-    if (!c->bgraph_exec) CPTR_TRY(build_batch_graph(c));
+    const bool cycle = c->o.use_graph == 1 && !c->inject_wait && !c->bcycle_failed;
+    if (cycle && !c->bcycle_exec) CPTR_TRY(build_batch_cycle_graph(c));
+    if (!(cycle && c->bcycle_exec) && !c->bgraph_exec) CPTR_TRY(build_batch_graph(c));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(c->ksb, 0, sizeof(KState) * ni, s));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(c->ks, 0, sizeof(KState), s));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(x, 0, sizeof(double) * nb, s));
@@ -882,7 +959,15 @@ cptr_status fgmres_solve_batch(Ctx *c, const double *bw, double *x, double rtol,
     int it = 0;
     bool stop = all_done();
     while (!stop) {
-        for (int j = 0; j < m && it < c->o.max_it; ++j) {
+        if (cycle && c->bcycle_exec && it < c->o.max_it) {   // the whole cycle, one launch
+            CPTR_CUDA_TRY(c, cudaMemsetAsync(&c->ks->k, 0, sizeof(int32_t), s));
+            CPTR_CUDA_TRY(c, cudaGraphLaunch(c->bcycle_exec, s));
+            CPTR_TRY(read_headers(c));
+            note_launches((int64_t)c->hdr_host[ni].k * c->bcycle_step_launches);
+            it = c->hdr_host[ni].its;
+            if (c->hdr_host[ni].wait_err) return c->fail(CPTR_ETIMEOUT, "ILU(0) sweep: a bounded wait gave up");
+        }
+        for (int j = 0; j < m && it < c->o.max_it && !(cycle && c->bcycle_exec); ++j) {
             CPTR_CUDA_TRY(c, cudaGraphLaunch(c->bgraph_exec, s));
             note_launches(c->bgraph_launches);
             ++it;

@@ -391,13 +391,13 @@ def test_bounded_wait_reports_timeout_and_context_recovers():
     check_solve(s, o, g, 1e-8)
 
 
-@pytest.mark.parametrize("use_graph", [0, 1])
+@pytest.mark.parametrize("use_graph", [0, 1, 2])
 def test_graph_and_direct_launches_agree(use_graph):
     s, o, g = pair("medium", use_graph=use_graph)
     info_o, info_g = check_solve(s, o, g, 1e-8)
 
 
-@pytest.mark.parametrize("use_graph", [0, 1])
+@pytest.mark.parametrize("use_graph", [0, 1, 2])
 def test_profiling_counts_match_iterations(use_graph):
     s, o, g = pair("parity", use_graph=use_graph)
     cp.cptr_set_profiling(g.ctx, 0b1111111)
