@@ -65,7 +65,7 @@ def parse():
     p.add_argument("--graph", choices=["cycle", "step"], default="cycle",
                    help="headline solver: each restart cycle as one graph launch (device-side loop), or one "
                         "graph launch per Arnoldi step (what per-kernel profilers see kernel by kernel)")
-    p.add_argument("--ilu-sweep", choices=["auto", "levels", "chunked", "paired"], default="auto",
+    p.add_argument("--ilu-sweep", choices=["auto", "levels", "chunked", "paired", "tiled"], default="auto",
                    help="schedule of the headline solver's ILU(0) sweeps")
     p.add_argument("--ensemble-total", type=float, default=4e6,
                    help="total cells of the ensemble (profiling runs use a smaller one)")
