@@ -43,7 +43,10 @@ typedef enum {
     CPTR_EBREAKDOWN = -4,   /* non-finite value in the Krylov iteration */
     CPTR_ETIMEOUT = -5,     /* a bounded device-side wait gave up */
     CPTR_ESINGULAR = -6,    /* zero pivot in ILU(0) or singular coarsest AMG matrix */
-    CPTR_ESTATE = -7        /* call out of order (e.g. solve before setup) */
+    CPTR_ESTATE = -7,       /* call out of order (e.g. solve before setup) */
+    CPTR_ECHECK = -8        /* bounds-checking build (libcptr_check.so) only: an index read from a
+                             * table on the device fell outside its array; the access was skipped,
+                             * and the message names the kernel site, the index and the bound */
 } cptr_status;
 
 /* first stage M1 (Sec. 3.1, 3.3, 3.4): full block factorisation, its block-triangular variants

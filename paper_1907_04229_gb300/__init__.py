@@ -17,7 +17,7 @@ LIB_PATH = _build.LIB
 
 CPTR_OK, CPTR_NOT_CONVERGED = 0, 1
 STATUS = {0: "CPTR_OK", 1: "CPTR_NOT_CONVERGED", -1: "CPTR_EINVAL", -2: "CPTR_ENOMEM", -3: "CPTR_ECUDA",
-          -4: "CPTR_EBREAKDOWN", -5: "CPTR_ETIMEOUT", -6: "CPTR_ESINGULAR", -7: "CPTR_ESTATE"}
+          -4: "CPTR_EBREAKDOWN", -5: "CPTR_ETIMEOUT", -6: "CPTR_ESINGULAR", -7: "CPTR_ESTATE", -8: "CPTR_ECHECK"}
 STAGE1 = {"full": 0, "upper": 1, "lower": 2, "bd": 3, "cpr": 4, "none": 5, "uamg": 6}
 STAGE2 = {"ilu0": 0, "none": 1}
 SCHUR = {"given": 0, "att": 1, "learned": 2, "diag": 3}
@@ -127,12 +127,23 @@ SETUP_PHASES = {8: "setup_inputs", 9: "setup_amg_coarsen", 10: "setup_amg_rap", 
                 12: "setup_ilu_host", 13: "setup_ilu_factor", 14: "setup_layout", 15: "setup_other"}
 
 
+def select_library(variant: str = "") -> None:
+    """Choose the library this process loads, before its first use: "" (libcptr.so) or "check"
+    (libcptr_check.so, the bounds-checking build: every failed index check makes the call return
+    CPTR_ECHECK)."""
+    global LIB_PATH
+    if _lib is not None:
+        raise RuntimeError("the library is already loaded in this process")
+    LIB_PATH = _build.VARIANTS[variant][0]
+
+
 def load():
     """Load libcptr.so (built by ``build()``); raises if it is missing."""
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError(f"libcptr.so not found at {LIB_PATH}: run __graft_entry__.build() (no CPU fallback)")
+            raise ImportError(f"{os.path.basename(LIB_PATH)} not found at {LIB_PATH}: run __graft_entry__.build() "
+                              "(no CPU fallback)")
         lib = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in _SIGS.items():
             f = getattr(lib, name)

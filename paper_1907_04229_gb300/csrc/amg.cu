@@ -1040,10 +1040,14 @@ __global__ void __launch_bounds__(512) k_vc_down(int32_t n, const int32_t *__res
         int32_t k1 = __ldg(rp + row + 1);
         if (G == 1) {
             acc = row_dot_batched<8>(__ldg(rp + row), k1, ci, [&](int32_t k) { return (XT)vld(v + k); },
-                                     [&](int32_t j) { return __ldg(dinv + j) * __ldg(b + j); }, acc);
+                                     [&](int32_t j) {
+                                         j = (int32_t)chk(j, n, CHK_VC_COL);
+                                         return __ldg(dinv + j) * __ldg(b + j);
+                                     },
+                                     acc);
         } else {
             for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G) {
-                int32_t j = __ldg(ci + k);
+                int32_t j = (int32_t)chk(__ldg(ci + k), n, CHK_VC_COL);
                 acc = fma((XT)vld(v + k), __ldg(dinv + j) * __ldg(b + j), acc);
             }
         }
@@ -1071,10 +1075,10 @@ __global__ void __launch_bounds__(512) k_vc_post(int32_t n, const int32_t *__res
         int32_t k1 = __ldg(rp + row + 1);
         if (G == 1) {
             acc = row_dot_batched<8>(__ldg(rp + row), k1, ci, [&](int32_t k) { return (XT)vld(v + k); },
-                                     [&](int32_t j) { return __ldg(t + j); }, acc);
+                                     [&](int32_t j) { return __ldg(t + chk(j, n, CHK_VC_COL)); }, acc);
         } else {
             for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G)
-                acc = fma((XT)vld(v + k), __ldg(t + __ldg(ci + k)), acc);
+                acc = fma((XT)vld(v + k), __ldg(t + chk(__ldg(ci + k), n, CHK_VC_COL)), acc);
         }
     }
 #pragma unroll
@@ -1158,7 +1162,7 @@ static void level_down(const Ctx *c, int pf, const Level &L, const Level &C, con
     prof_end(c, ev);
     ev = pf < 0 ? -1 : prof_begin(c, pf + 1);
     launch_csr_spmv_t<VT, XT>(s, L.PT.n, L.PT.nnz, L.PT.rp, L.PT.ci, PTv, LV::r(L), LV::b(C), 0, nullptr,
-                              L.sh_PT);                                                        // b_c = P^T r
+                              L.sh_PT, L.A.n);                                                 // b_c = P^T r
     prof_end(c, ev);
 }
 template <typename VT, typename XT>
@@ -1168,7 +1172,7 @@ static void level_up(const Ctx *c, int pf, const Level &L, const Level &C, const
     cudaStream_t s = c->stream;
     int ev = pf < 0 ? -1 : prof_begin(c, pf + 2);
     launch_csr_spmv_t<VT, XT>(s, L.P.n, L.P.nnz, L.P.rp, L.P.ci, Pv, LV::x(C), LV::t(L), 2, nullptr,
-                              L.sh_P);                                                         // t += P x_c
+                              L.sh_P, C.A.n);                                                  // t += P x_c
     prof_end(c, ev);
     ev = pf < 0 ? -1 : prof_begin(c, pf + 3);
     launch_post<VT, XT>(s, L, Av, LV::dinv(L), b, LV::t(L), x);                     // x = t + D^-1 (b - A t)
@@ -1419,10 +1423,12 @@ void tune_level(Ctx *c, Level &L, Level &C, const VT *Av, const VT *PTv, const V
         launch_down<VT, XT>(s, tmp, Av, LV::dinv(L), LV::b(L), LV::t(L), LV::r(L));
     });
     L.sh_PT = pick_shape(c, tune_key(2, L.PT, L.st), [&](Shape sh) {
-        launch_csr_spmv_t<VT, XT>(s, L.PT.n, L.PT.nnz, L.PT.rp, L.PT.ci, PTv, LV::r(L), LV::b(C), 0, nullptr, sh);
+        launch_csr_spmv_t<VT, XT>(s, L.PT.n, L.PT.nnz, L.PT.rp, L.PT.ci, PTv, LV::r(L), LV::b(C), 0, nullptr, sh,
+                                  L.A.n);
     });
     L.sh_P = pick_shape(c, tune_key(3, L.P, L.st), [&](Shape sh) {
-        launch_csr_spmv_t<VT, XT>(s, L.P.n, L.P.nnz, L.P.rp, L.P.ci, Pv, LV::x(C), LV::t(L), 2, nullptr, sh);
+        launch_csr_spmv_t<VT, XT>(s, L.P.n, L.P.nnz, L.P.rp, L.P.ci, Pv, LV::x(C), LV::t(L), 2, nullptr, sh,
+                                  C.A.n);
     });
 }
 }  // namespace

@@ -352,7 +352,9 @@ cptr_status guarded(cptr_ctx *ctx, F &&f) {
     CtxScope scope(&ctx->c);
     try {
         ctx->c.err.clear();
-        return f(&ctx->c);
+        const cptr_status st = f(&ctx->c);
+        const cptr_status ck = check_report(&ctx->c);   // the bounds-checking build only
+        return ck != CPTR_OK ? ck : st;
     } catch (const std::bad_alloc &) {
         return ctx->c.fail(CPTR_ENOMEM, "host allocation failed");
     } catch (...) {

@@ -202,7 +202,7 @@ void launch_csr_spmv(cudaStream_t s, const Csr &A, const double *x, double *y, d
 // y = A x (mode 0), y = c0 - A x (mode 1), y += A x (mode 2); values VT, vectors and sums XT
 template <typename VT, typename XT>
 void launch_csr_spmv_t(cudaStream_t s, int32_t n, int32_t nnz, const int32_t *rp, const int32_t *ci, const VT *v,
-                       const XT *x, XT *y, int mode, const XT *c0, Shape sh = Shape());
+                       const XT *x, XT *y, int mode, const XT *c0, Shape sh = Shape(), int32_t ncol = INT32_MAX);
 cptr_status to_lower(Ctx *c, const double *src, int64_t n, int st, void **dst);
 void launch_d2f(const Ctx *c, const double *a, float *b, int64_t n);
 void launch_f2d(const Ctx *c, const float *a, double *b, int64_t n);
@@ -455,6 +455,51 @@ __device__ __forceinline__ XT row_dot_batched(int32_t k0, int32_t k1, const int3
     }
     return acc;
 }
+
+// Index checks of the bounds-checking build (compiled with -DCPTR_CHECK into libcptr_check.so).
+// chk(i, n, site) returns i when 0 <= i < n.  Otherwise it records the first failure of the
+// translation unit (site, index, bound) and returns 0, so that the access stays inside the array and
+// the kernel completes; every entry point then reports CPTR_ECHECK.  No trap and no device assert:
+// the context stays usable.  In the normal build chk() is the identity.  Each translation unit
+// keeps its own record (device symbols are per unit without relocatable device code) and registers
+// host functions that read and clear it.
+struct CheckRec {
+    int32_t count, site;
+    int64_t index, bound;
+};
+#ifdef CPTR_CHECK
+void check_register(cudaError_t (*fetch)(CheckRec *), cudaError_t (*clear)());
+struct CheckRegistration {
+    CheckRegistration(cudaError_t (*fetch)(CheckRec *), cudaError_t (*clear)()) { check_register(fetch, clear); }
+};
+static __device__ CheckRec g_check_tu;
+static cudaError_t check_fetch_tu(CheckRec *out) { return cudaMemcpyFromSymbol(out, g_check_tu, sizeof(CheckRec)); }
+static cudaError_t check_clear_tu() {
+    const CheckRec z{};
+    return cudaMemcpyToSymbol(g_check_tu, &z, sizeof(CheckRec));
+}
+static CheckRegistration check_registration_tu(check_fetch_tu, check_clear_tu);
+__device__ __forceinline__ int64_t chk(int64_t i, int64_t n, int site) {
+    if (i >= 0 && i < n) return i;
+    if (atomicAdd(&g_check_tu.count, 1) == 0) {
+        g_check_tu.site = site;
+        g_check_tu.index = i;
+        g_check_tu.bound = n;
+    }
+    return 0;
+}
+#else
+__device__ __forceinline__ int64_t chk(int64_t i, int64_t, int) { return i; }
+#endif
+// the sites of chk() (reported by number)
+enum { CHK_SELL_COL = 1, CHK_CSR_COL = 2, CHK_VC_COL = 3, CHK_ILU_DEP = 4, CHK_ILU_PAIR = 5, CHK_FACTOR_COL = 6,
+       CHK_FACTOR_DEP = 7, CHK_GATHER = 8 };
+// a dependency position of the sweep tables: -1 marks an empty slot, anything else is checked
+__device__ __forceinline__ int32_t chk_dep(int32_t c, int32_t n) {
+    return c < 0 ? -1 : (int32_t)chk(c, n, CHK_ILU_DEP);
+}
+// true (and the context's error set) if a check of this process failed since the last call
+cptr_status check_report(Ctx *c);
 
 // Programmatic dependent launch: a kernel launched by launch_pdl may be scheduled while the kernel
 // before it on the stream is still running, which hides the launch latency of short kernels in a

@@ -203,11 +203,13 @@ __device__ __forceinline__ void load_group(const T *base, const int32_t *c, T (*
 // s -= sum over the dependency slots [o0, o1) of block(slot) * value(dep(slot))
 template <int B, typename T>
 __device__ __forceinline__ void subtract_deps(T *s, int64_t o0, int64_t o1, int lane, const int32_t *__restrict__ col,
-                                              const T *__restrict__ val, const T *vec, KState *ks, int sleep_ns) {
+                                              const T *__restrict__ val, const T *vec, KState *ks, int sleep_ns,
+                                              int32_t n) {
     for (int64_t sl0 = o0; sl0 < o1; sl0 += kDepGroup) {
         int32_t c[kDepGroup];
 #pragma unroll
-        for (int g = 0; g < kDepGroup; ++g) c[g] = (sl0 + g < o1) ? __ldg(col + (sl0 + g) * 32 + lane) : -1;
+        for (int g = 0; g < kDepGroup; ++g)
+            c[g] = (sl0 + g < o1) ? chk_dep(__ldg(col + (sl0 + g) * 32 + lane), n) : -1;
         T a[kDepGroup][B * B];
 #pragma unroll
         for (int g = 0; g < kDepGroup; ++g)
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_sf(int32_t n, unsigned *
         T s[B];
 #pragma unroll
         for (int q = 0; q < B; ++q) s[q] = (T)__ldg(r + (int64_t)row * B + q);
-        subtract_deps<B, T>(s, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, y, ks, sleep_ns);
+        subtract_deps<B, T>(s, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, y, ks, sleep_ns, n);
 #pragma unroll
         for (int q = 0; q < B; ++q) store_relaxed(y + (int64_t)t * B + q, s[q]);
     }
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_sf(int32_t n, unsigned *
         T dv[B * B];
 #pragma unroll
         for (int e = 0; e < B * B; ++e) dv[e] = __ldg(dinv + ((int64_t)ch * B * B + e) * 32 + lane);
-        subtract_deps<B, T>(s, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, z, ks, sleep_ns);
+        subtract_deps<B, T>(s, __ldg(off + ch), __ldg(off + ch + 1), lane, col, val, z, ks, sleep_ns, n);
         T zi[B];
 #pragma unroll
         for (int rr = 0; rr < B; ++rr) {
@@ -333,6 +335,7 @@ struct SweepLane {
     T s;
     unsigned long long t0;
     bool waiting;
+    int32_t nrows;   // bound of the dependency positions (index checks)
 };
 
 // columns, row q4 of the blocks, and the first loads of component q4 of the values of slots
@@ -341,7 +344,8 @@ template <int B, typename T, int DG>
 __device__ __forceinline__ void sweep_stage(SweepLane<B, T, DG> &L, int q4, int lane, const int32_t *__restrict__ col,
                                             const T *__restrict__ val, const T *vec) {
 #pragma unroll
-    for (int g = 0; g < DG; ++g) L.c[g] = (L.sl0 + g < L.o1) ? __ldg(col + (L.sl0 + g) * 32 + lane) : -1;
+    for (int g = 0; g < DG; ++g)
+        L.c[g] = (L.sl0 + g < L.o1) ? chk_dep(__ldg(col + (L.sl0 + g) * 32 + lane), L.nrows) : -1;
 #pragma unroll
     for (int g = 0; g < DG; ++g)
         if (L.c[g] >= 0) {
@@ -404,12 +408,13 @@ __device__ __forceinline__ bool sweep_round(SweepLane<B, T, DG> &L, int q4, int 
 template <int B, typename T, typename ST>
 __device__ __forceinline__ T pair_terms(T s, int q4, int32_t ch, int lane, const int64_t *__restrict__ coff,
                                         const int32_t *__restrict__ ccol, const T *__restrict__ cval,
-                                        const ST *__restrict__ src) {
+                                        const ST *__restrict__ src, int32_t n) {
     if (!coff) return s;
     const int64_t c1 = __ldg(coff + ch + 1);
     for (int64_t sl = __ldg(coff + ch); sl < c1; ++sl) {
-        const int32_t k = __ldg(ccol + sl * 32 + lane);
+        int32_t k = __ldg(ccol + sl * 32 + lane);
         if (k < 0) continue;
+        k = (int32_t)chk(k, n, CHK_ILU_PAIR);
 #pragma unroll
         for (int u = 0; u < B; ++u) s = fma(-__ldg(cval + (sl * B * B + q4 * B + u) * 32 + lane), (T)src[(int64_t)k * B + u], s);
     }
@@ -442,7 +447,8 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_g(int32_t n, unsigned *t
         if (!done) {
             const int32_t ch = t >> 5;
             L.s = (T)__ldg(r + (int64_t)__ldg(pos + t) * B + q4);
-            L.s = pair_terms<B, T, RT>(L.s, q4, ch, lane, coff, ccol, cval, r);
+            L.s = pair_terms<B, T, RT>(L.s, q4, ch, lane, coff, ccol, cval, r, n);
+            L.nrows = n;
             L.sl0 = __ldg(off + ch);
             L.o1 = __ldg(off + ch + 1);
             L.waiting = false;
@@ -499,7 +505,8 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_g(int32_t n, unsigned *t
             if (dp && q4 == ps) add = (double)dp[row];
             if (dT && q4 == ts) add = (double)dT[row];
             L.s = __ldcg(y + (int64_t)__ldg(bmap + t) * B + q4);
-            L.s = pair_terms<B, T, T>(L.s, q4, ch, lane, coff, ccol, cval, y);
+            L.s = pair_terms<B, T, T>(L.s, q4, ch, lane, coff, ccol, cval, y, n);
+            L.nrows = n;
             // row q4 of the inverted pivot block does not depend on other rows: load it first
 #pragma unroll
             for (int q = 0; q < B; ++q) dv[q] = __ldg(dinv + ((int64_t)ch * B * B + q4 * B + q) * 32 + lane);
@@ -1274,17 +1281,18 @@ __global__ void __launch_bounds__(32 * kFwWarps) k_bilu_factor_w(int32_t n, unsi
         if (t >= n) return;
         const int32_t i = pos[t], k0 = rp[i], e = rp[i + 1], kd = diag[i];
         const int32_t len = e - k0, nd = kd - k0;
-        for (int32_t k = lane; k < len; k += 32) cols[k] = ci[k0 + k];
+        for (int32_t k = lane; k < len; k += 32) cols[k] = (int32_t)chk(ci[k0 + k], n, CHK_FACTOR_COL);
         for (int32_t u = lane; u < len * BB; u += 32) rowb[u] = LU[(int64_t)k0 * BB + u];
         __syncwarp();
         for (int32_t k = lane; k < nd; k += 32) {
             const int32_t c = cols[k];
-            dcs[k] = diag[c];
+            dcs[k] = (int32_t)chk(diag[c], rp[n], CHK_FACTOR_DEP);
             ecs[k] = rp[c + 1];
         }
         __syncwarp();
         for (int32_t k = 0; k < nd; ++k)
-            for (int32_t qq = dcs[k] + 1 + lane; qq < ecs[k]; qq += 32) ucol[k * maxu + (qq - dcs[k] - 1)] = ci[qq];
+            for (int32_t qq = dcs[k] + 1 + lane; qq < ecs[k]; qq += 32)
+                ucol[k * maxu + (qq - dcs[k] - 1)] = (int32_t)chk(ci[qq], n, CHK_FACTOR_COL);
         // the dependencies' flags (each lane polls some), bounded
         unsigned long long tw = 0;
         bool waiting = false;

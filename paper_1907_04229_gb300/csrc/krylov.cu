@@ -297,10 +297,10 @@ void apply_stage1_32(const Ctx *c, const double *v, const float **pdp, const flo
     cudaStream_t s = c->stream;
     const int32_t n = c->n, nnz = c->nnzb;
     auto Tp = [&](const float *x, float *y, const float *c0) {   // y = c0 - A_Tp x
-        launch_csr_spmv_t<float, float>(s, n, nnz, c->rp, c->ci, c->ATp32, x, y, 1, c0);
+        launch_csr_spmv_t<float, float>(s, n, nnz, c->rp, c->ci, c->ATp32, x, y, 1, c0, Shape(), n);
     };
     auto pT = [&](const float *x, float *y, const float *c0) {   // y = c0 - A_pT x
-        launch_csr_spmv_t<float, float>(s, n, nnz, c->rp, c->ci, c->ApT32, x, y, 1, c0);
+        launch_csr_spmv_t<float, float>(s, n, nnz, c->rp, c->ci, c->ApT32, x, y, 1, c0, Shape(), n);
     };
     *pdp = nullptr;
     *pdT = nullptr;

@@ -85,7 +85,9 @@ extern "C" cptr_status cptr_apply_ilu_static(cptr_ctx *ctx, const double *r, dou
     CtxScope scope(c);
     try {
         c->err.clear();
-        return apply_static(c, r, z);
+        const cptr_status st = apply_static(c, r, z);
+        const cptr_status ck = check_report(c);   // the bounds-checking build only
+        return ck != CPTR_OK ? ck : st;
     } catch (const std::bad_alloc &) {
         return c->fail(CPTR_ENOMEM, "host allocation failed");
     } catch (...) {

@@ -10,6 +10,8 @@
 #include <chrono>
 #include <vector>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace cptr {
@@ -98,6 +100,57 @@ cptr_status prof_collect(Ctx *c) {
     p.used = first;
     return CPTR_OK;
 }
+
+#ifdef CPTR_CHECK
+namespace {
+struct CheckFns {
+    cudaError_t (*fetch)(CheckRec *);
+    cudaError_t (*clear)();
+};
+std::vector<CheckFns> &check_list() {
+    static std::vector<CheckFns> v;   // filled by static initialisers at load time
+    return v;
+}
+std::mutex g_check_mu;
+const char *check_site(int s) {
+    switch (s) {
+    case CHK_SELL_COL: return "SELL SpMV column";
+    case CHK_CSR_COL: return "CSR SpMV column";
+    case CHK_VC_COL: return "V-cycle column";
+    case CHK_ILU_DEP: return "ILU sweep dependency";
+    case CHK_ILU_PAIR: return "paired-level term";
+    case CHK_FACTOR_COL: return "ILU factorisation column";
+    case CHK_FACTOR_DEP: return "ILU factorisation pivot position";
+    default: return "index";
+    }
+}
+}  // namespace
+void check_register(cudaError_t (*fetch)(CheckRec *), cudaError_t (*clear)()) {
+    std::lock_guard<std::mutex> lock(g_check_mu);
+    check_list().push_back({fetch, clear});
+}
+cptr_status check_report(Ctx *c) {
+    std::lock_guard<std::mutex> lock(g_check_mu);
+    CPTR_CUDA_TRY(c, cudaDeviceSynchronize());
+    CheckRec first{};
+    int64_t total = 0;
+    for (const CheckFns &f : check_list()) {
+        CheckRec r{};
+        CPTR_CUDA_TRY(c, f.fetch(&r));
+        if (r.count > 0) {
+            if (total == 0) first = r;
+            total += r.count;
+            CPTR_CUDA_TRY(c, f.clear());
+        }
+    }
+    if (total == 0) return CPTR_OK;
+    return c->fail(CPTR_ECHECK, std::string("index check failed: ") + check_site(first.site) + " " +
+                                    std::to_string(first.index) + " outside [0, " + std::to_string(first.bound) +
+                                    ") (" + std::to_string(total) + " failed accesses skipped)");
+}
+#else
+cptr_status check_report(Ctx *) { return CPTR_OK; }
+#endif
 
 static thread_local Ctx *t_scope = nullptr;
 CtxScope::CtxScope(Ctx *c) : prev(t_scope) { t_scope = c; }
@@ -466,7 +519,7 @@ __global__ void __launch_bounds__(512) k_sell_spmv(int32_t n, const int64_t *__r
 #pragma unroll
     for (int r = 0; r < B; ++r) acc[r] = 0.0;
     for (int64_t sl = o0; sl < o1; ++sl) {
-        const int32_t cidx = __ldg(col + sl * 32 + lane);
+        const int32_t cidx = (int32_t)chk(__ldg(col + sl * 32 + lane), n, CHK_SELL_COL);
         const double *a = val + sl * B * B * 32 + lane;
         if (MODE == 2) {
             const double xp = __ldg(dp + cidx);
@@ -528,7 +581,7 @@ template <int G, typename VT, typename XT>
 __global__ void __launch_bounds__(512) k_csr_spmv(int32_t n, const int32_t *__restrict__ rp,
                                                    const int32_t *__restrict__ ci, const VT *__restrict__ v,
                                                    const XT *__restrict__ x, XT *__restrict__ y, int mode,
-                                                   const XT *__restrict__ c0) {
+                                                   const XT *__restrict__ c0, int32_t ncol) {
     pdl_wait();
     int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int32_t row = (int32_t)(gid / G);
@@ -538,10 +591,10 @@ __global__ void __launch_bounds__(512) k_csr_spmv(int32_t n, const int32_t *__re
         int32_t k1 = __ldg(rp + row + 1);
         if (G == 1) {
             acc = row_dot_batched<4>(__ldg(rp + row), k1, ci, [&](int32_t k) { return (XT)val_ld(v + k); },
-                                     [&](int32_t j) { return __ldg(x + j); }, acc);
+                                     [&](int32_t j) { return __ldg(x + chk(j, ncol, CHK_CSR_COL)); }, acc);
         } else {
             for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G)
-                acc = fma((XT)val_ld(v + k), __ldg(x + __ldg(ci + k)), acc);
+                acc = fma((XT)val_ld(v + k), __ldg(x + chk(__ldg(ci + k), ncol, CHK_CSR_COL)), acc);
         }
     }
 #pragma unroll
@@ -555,28 +608,28 @@ __global__ void __launch_bounds__(512) k_csr_spmv(int32_t n, const int32_t *__re
 
 template <typename VT, typename XT>
 void launch_csr_spmv_t(cudaStream_t s, int32_t n, int32_t nnz, const int32_t *rp, const int32_t *ci, const VT *v,
-                       const XT *x, XT *y, int mode, const XT *c0, Shape sh) {
+                       const XT *x, XT *y, int mode, const XT *c0, Shape sh, int32_t ncol) {
     const int G = sh.G ? sh.G : lanes_for(n, nnz), T = sh.T;
     unsigned grid = nblk((int64_t)n * G, T);
     switch (G) {
-    case 1: launch_pdl(k_csr_spmv<1, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0); break;
-    case 2: launch_pdl(k_csr_spmv<2, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0); break;
-    case 4: launch_pdl(k_csr_spmv<4, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0); break;
-    case 8: launch_pdl(k_csr_spmv<8, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0); break;
-    case 16: launch_pdl(k_csr_spmv<16, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0); break;
-    default: launch_pdl(k_csr_spmv<32, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0); break;
+    case 1: launch_pdl(k_csr_spmv<1, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol); break;
+    case 2: launch_pdl(k_csr_spmv<2, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol); break;
+    case 4: launch_pdl(k_csr_spmv<4, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol); break;
+    case 8: launch_pdl(k_csr_spmv<8, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol); break;
+    case 16: launch_pdl(k_csr_spmv<16, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol); break;
+    default: launch_pdl(k_csr_spmv<32, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol); break;
     }
 }
 template void launch_csr_spmv_t<double, double>(cudaStream_t, int32_t, int32_t, const int32_t *, const int32_t *,
-                                                const double *, const double *, double *, int, const double *, Shape);
+                                                const double *, const double *, double *, int, const double *, Shape, int32_t);
 template void launch_csr_spmv_t<float, float>(cudaStream_t, int32_t, int32_t, const int32_t *, const int32_t *,
-                                              const float *, const float *, float *, int, const float *, Shape);
+                                              const float *, const float *, float *, int, const float *, Shape, int32_t);
 template void launch_csr_spmv_t<bf16, float>(cudaStream_t, int32_t, int32_t, const int32_t *, const int32_t *,
-                                             const bf16 *, const float *, float *, int, const float *, Shape);
+                                             const bf16 *, const float *, float *, int, const float *, Shape, int32_t);
 
 void launch_csr_spmv(cudaStream_t s, const Csr &A, const double *x, double *y, double alpha, const double *c0) {
     int mode = c0 ? 1 : (alpha == 2.0 ? 2 : 0);
-    launch_csr_spmv_t<double, double>(s, A.n, A.nnz, A.rp, A.ci, A.v, x, y, mode, c0);
+    launch_csr_spmv_t<double, double>(s, A.n, A.nnz, A.rp, A.ci, A.v, x, y, mode, c0, Shape(), A.n);   // square
 }
 
 // FP64 -> FP32 (round to nearest) or FP64 -> FP32 -> BF16 (round to nearest even): the storage

@@ -31,6 +31,16 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(names) == set(cp._SIGS), set(names) ^ set(cp._SIGS)
 
 
+def test_bounds_checking_build_exports_the_same_symbols():
+    """libcptr_check.so (-DCPTR_CHECK) is the same library with index checks: every declared
+    entry point is exported (loaded by path here; the package's own library stays the default)."""
+    from paper_1907_04229_gb300 import _build
+    path = _build.build(variant="check")
+    chk = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(chk, name), name
+
+
 def test_library_targets_sm103a():
     # the fat binary embeds sm_103a code only; cuobjdump is not needed: nvcc's -gencode list is fixed
     from paper_1907_04229_gb300 import _build
