@@ -96,7 +96,18 @@ VARIANTS = {
     "cptr_mixed_multicolor_ilu": dict(precision="mixed", ilu_order="multicolor"),
     "cptr_fp64_autotuned": dict(autotune=1),
     "cptr_mixed_autotuned": dict(precision="mixed", autotune=1),
+    # the paper's parallel second stage (Sec. 4): ILU(0) on each of 16 parts of the domain (4 x 4
+    # columns of 25 x 25 x 20 cells), as 16 processes would apply it
+    "cptr_fp64_block_jacobi16": dict(autotune=1, part=(4, 4)),
+    "cptr_mixed_block_jacobi16": dict(precision="mixed", autotune=1, part=(4, 4)),
 }
+
+
+def grid_parts(nx, ny, nz, px, py):
+    """Part id per cell of a natural-order nx x ny x nz grid cut into px x py columns."""
+    i = np.arange(nx * ny * nz)
+    x, y = i % nx, (i // nx) % ny
+    return ((x * px) // nx + px * ((y * py) // ny)).astype(np.int32)
 # the variant whose kernels get roofline lines of their own ("..._mixed")
 MIXED_PROFILED = "cptr_mixed_autotuned"
 
@@ -518,7 +529,11 @@ def ours(args, rank, world, local_rank, oracle_jobs):
     if not args.no_variants:
         variants = {}
         for name, opts in VARIANTS.items():
+            opts = dict(opts)
+            parts = opts.pop("part", None)
             Sv = cp.Solver(stream=stream, **opts)
+            if parts:
+                cp.cptr_set_partition(Sv.ctx, torch.as_tensor(grid_parts(nx, ny, nz, *parts), device=dev))
 
             def step_v():
                 Sv.setup(n, b, d["rp"], d["ci"], d["vals"], d["kind"], d["W"], d["st"])

@@ -189,6 +189,20 @@ cptr_status cptr_setup(cptr_ctx *ctx, int32_t n_cells, int32_t b, const int32_t 
 cptr_status cptr_solve(cptr_ctx *ctx, const double *rhs, double *x, double rtol, cptr_stats *st,
                        int32_t on_device);
 
+/*
+ * Block-Jacobi second stage (Sec. 4: in parallel the paper applies ILU(k) to each block of the
+ * domain's partition across processes, "block Jacobi"): with a partition set, the ILU(0) factors
+ * drop every coupling between cells of different parts, so each part is factored and solved on
+ * its own.  This is the paper's second stage for that many processes, in one solve.
+ *   part  [n_cells] part id of every cell (any int32 values; cells with equal ids form a part);
+ *         NULL removes the partition (global ILU(0), the default)
+ * Copied into context memory (host or device pointer, on_device as in cptr_setup); takes effect at
+ * the next cptr_setup, whose n_cells must equal n_cells here.  Natural order and ILU(0) only:
+ * that set-up returns CPTR_EINVAL with the multicolour order or ILU(1); the chunked and tiled sweep
+ * schedules are not used with a partition.  Errors: CPTR_EINVAL, CPTR_ENOMEM, CPTR_ECUDA.
+ */
+cptr_status cptr_set_partition(cptr_ctx *ctx, int32_t n_cells, const int32_t *part, int32_t on_device);
+
 /* ------------------------------------------------------------------------------------------
  * Component entry points.  They apply one piece of the set-up operator, for parity tests and
  * profiling.  All vectors are device memory of length n_cells*b (cell-major) unless stated.

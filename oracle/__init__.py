@@ -42,7 +42,7 @@ class Opts(ctypes.Structure):
                 ("n_coarse", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_it", ctypes.c_int32), ("dense_max", ctypes.c_int32), ("seed", ctypes.c_int32),
                 ("ilu_order", ctypes.c_int32), ("precision", ctypes.c_int32), ("decouple", ctypes.c_int32),
-                ("ilu_fill", ctypes.c_int32)]
+                ("ilu_fill", ctypes.c_int32), ("part", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -164,7 +164,9 @@ class Oracle:
             st_rp, st_ci = keep(st_pattern[0], np.int32), keep(st_pattern[1], np.int32)
         else:
             st_rp, st_ci = rp, ci
+        part = keep(opts.pop("part", None), np.int32)   # block-Jacobi ILU(0) over these parts
         self.opts = default_opts(**opts)
+        self.opts.part = _p(part)
         if st_v is None and self.opts.schur == SCHUR_GIVEN:
             self.opts.schur = SCHUR_ATT
         self._c = lib.or_create(self.n, self.b, _p(rp), _p(ci), _p(v), _p(W), ps, ts, _p(st_rp), _p(st_ci),

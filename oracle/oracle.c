@@ -56,6 +56,7 @@ typedef struct {
                                 mixed-precision GPU form stores them (FP64 arithmetic) */
     int32_t decouple;        /* 0: none; 1: Quasi-IMPES; 2: True-IMPES (CPR and uAMG first stages) */
     int32_t ilu_fill;        /* level of fill of the second stage: 0 (ILU(0)) or 1 (ILU(1)) */
+    const int32_t *part;     /* part id per cell: block-Jacobi ILU(0) over the parts (Sec. 4), or NULL */
 } or_opts;
 
 typedef struct {
@@ -631,6 +632,28 @@ static void ilu1_pattern(const csr *A, csr *F) {
     free(mark); free(list);
 }
 
+/* Block Jacobi (Sec. 4: in parallel, ILU(k) on each block of the domain's partition): the entries
+ * of A whose row and column cells (scalar index / b) lie in the same part.  ILU(0) on this pattern
+ * factors every part on its own. */
+static void partition_pattern(const csr *A, int32_t b, const int32_t *part, csr *F) {
+    int32_t n = A->n;
+    F->n = n;
+    F->rp = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    F->ci = (int32_t *)malloc(sizeof(int32_t) * (size_t)(A->nnz > 0 ? A->nnz : 1));
+    F->v = (double *)malloc(sizeof(double) * (size_t)(A->nnz > 0 ? A->nnz : 1));
+    int32_t nnz = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t k = A->rp[i]; k < A->rp[i + 1]; ++k)
+            if (part[A->ci[k] / b] == part[i / b]) {
+                F->ci[nnz] = A->ci[k];
+                F->v[nnz] = A->v[k];
+                ++nnz;
+            }
+        F->rp[i + 1] = nnz;
+    }
+    F->nnz = nnz;
+}
+
 static void ilu0_solve(const ilu0 *f, const double *r, double *z) {
     const csr *M = &f->LU;
     int32_t n = M->n;
@@ -1033,7 +1056,14 @@ or_ctx *or_create(int32_t n, int32_t b, const int32_t *rp, const int32_t *ci, co
             c->zp_tmp = (double *)calloc((size_t)n * b, sizeof(double));
             M = &c->Aperm;
         }
-        if (o->ilu_fill == 1) {   /* ILU(1): ILU on the level-1 fill pattern */
+        if (o->part && (o->ilu_order != 0 || o->ilu_fill != 0)) {
+            rc = 2;   /* block Jacobi: natural order and ILU(0) only */
+        } else if (o->part) {     /* block-Jacobi ILU(0) */
+            csr F;
+            partition_pattern(M, b, o->part, &F);
+            rc = ilu0_factor(&F, &c->ilu);
+            csr_free(&F);
+        } else if (o->ilu_fill == 1) {   /* ILU(1): ILU on the level-1 fill pattern */
             csr F;
             ilu1_pattern(M, &F);
             rc = ilu0_factor(&F, &c->ilu);

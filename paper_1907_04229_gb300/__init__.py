@@ -107,6 +107,7 @@ _SIGS = {
     "cptr_set_profiling": (_I, [_P, ctypes.c_uint32]),
     "cptr_profile": (_I, [_P, _P, _P]),
     "cptr_profile_vcycle": (_I, [_P, _P, _P]),
+    "cptr_set_partition": (_I, [_P, _I, _P, _I]),
     "cptr_setup_batch": (_I, [_P, _I, _I, _P, _P, _I]),
     "cptr_tuning": (_I, [_P, _P, _I, _P]),
     "cptr_solve_batch": (_I, [_P, _P, _P, ctypes.c_double, _P, _I]),
@@ -316,6 +317,16 @@ def cptr_profile(ctx):
     for i, name in SETUP_PHASES.items():
         out[name] = (float(ms[i]), int(cnt[i]))
     return out
+
+
+def cptr_set_partition(ctx, part):
+    """Part id per cell for the block-Jacobi ILU(0) (torch tensor or numpy array, int32); None removes it."""
+    if part is None:
+        return _check(ctx, load().cptr_set_partition(ctx, 0, None, 0))
+    on = _on_device(part)
+    if not on:
+        part = np.ascontiguousarray(part, dtype=np.int32)
+    return _check(ctx, load().cptr_set_partition(ctx, len(part), _ptr(part), int(on)))
 
 
 def cptr_profile_vcycle(ctx):

@@ -519,6 +519,8 @@ void cptr_destroy(cptr_ctx *ctx) {
             if (as) cudaStreamSynchronize(as);
         release_setup(c);
         ilu_sym_free(c);
+        dfree(c->part);
+        c->part = nullptr;
         dfree(c->ks); dfree(c->flag); dfree(c->partial); dfree(c->scan_tmp); dfree(c->never); dfree(c->ilu_flags);
         dfree(c->mlp);
         model_free(c);
@@ -751,6 +753,23 @@ cptr_status cptr_profile_vcycle(cptr_ctx *ctx, double *ms, int64_t *count) {
             if (ms) ms[k] = c->prof.ms[PF_VC + k];
             if (count) count[k] = c->prof.cnt[PF_VC + k];
         }
+        return CPTR_OK;
+    });
+}
+
+cptr_status cptr_set_partition(cptr_ctx *ctx, int32_t n_cells, const int32_t *part, int32_t on_device) {
+    return guarded(ctx, [&](Ctx *c) {
+        dfree(c->part);
+        c->part = nullptr;
+        c->n_part = 0;
+        ilu_sym_free(c);   // the ILU pattern changes with the partition
+        if (!part) return CPTR_OK;
+        if (n_cells <= 0) return c->fail(CPTR_EINVAL, "n_cells must be positive");
+        CPTR_TRY(dalloc_t(c, &c->part, (size_t)n_cells));
+        if (!host_or_device_copy(c, c->part, part, sizeof(int32_t) * (size_t)n_cells, on_device, cudaMemcpyHostToDevice))
+            return c->fail(CPTR_ECUDA, "copy of the partition failed");
+        CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        c->n_part = n_cells;
         return CPTR_OK;
     });
 }

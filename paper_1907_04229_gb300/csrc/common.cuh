@@ -342,6 +342,7 @@ struct Ctx {
     int32_t *ilu_flags = nullptr;      // per-row "factored" flags of the one-launch factorisation
     int32_t ilu_flags_n = 0, ilu_epoch = 0;
     IluSym isym;                                       // pattern-only ILU tables of the last set-up
+    int32_t *part = nullptr, n_part = 0;               // cell partition of a block-Jacobi ILU (device)
     int32_t nlev_f = 0, nlev_b = 0;
     int32_t *lvl_f = nullptr, *lvl_b = nullptr;       // rows sorted by level (device)
     std::vector<int32_t> h_lptr_f, h_lptr_b;           // level pointers (host)

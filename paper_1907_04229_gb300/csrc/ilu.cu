@@ -1940,7 +1940,8 @@ static cptr_status pair_setup(Ctx *c, const int32_t *inv_f, const int32_t *inv_b
 
 // key of the sweeps' tuning in the context's cache (grid and back-off; the schedule at key + 1)
 static uint64_t ilu_tune_key(const Ctx *c) {
-    return (uint64_t)8 << 60 | (uint64_t)(c->o.ilu_fill & 1) << 57 | (uint64_t)(c->o.precision & 1) << 56 |
+    return (uint64_t)8 << 60 | (uint64_t)(c->part != nullptr) << 58 | (uint64_t)(c->o.ilu_fill & 1) << 57 |
+           (uint64_t)(c->o.precision & 1) << 56 |
            ((uint64_t)c->n & 0xFFFFFFull) << 32 |
            (uint64_t)(uint32_t)c->nnzb;
 }
@@ -1999,6 +2000,35 @@ __global__ void k_scatter_blocks(int64_t nnz, int BB, const int32_t *kmap, const
     if (u >= nnz * BB) return;
     const int32_t k = kmap[u / BB];
     dst[u] = k >= 0 ? src[(int64_t)k * BB + u % BB] : 0.0;
+}
+
+// Block-Jacobi pattern (Sec. 4: in parallel, ILU(k) is applied to each block of the domain's
+// partition): row i keeps the blocks whose column lies in its own part.  kmap: the original block
+// of every kept position; pdg: the kept diagonal's position.
+__global__ void k_part_count(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                             const int32_t *__restrict__ part, int32_t *cnt) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t pi = part[i];
+    int32_t c = 0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) c += part[ci[k]] == pi;
+    cnt[i] = c;
+}
+__global__ void k_part_fill(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const int32_t *__restrict__ part, const int32_t *__restrict__ prp, int32_t *pci,
+                            int32_t *pdg, int32_t *kmap) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t pi = part[i];
+    int32_t o = prp[i];
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+        const int32_t j = ci[k];
+        if (part[j] != pi) continue;
+        if (j == i) pdg[i] = o;
+        pci[o] = j;
+        kmap[o] = k;
+        ++o;
+    }
 }
 
 // 1 in *diff if the pattern (rp, ci) differs from (srp, sci) anywhere
@@ -2064,13 +2094,37 @@ cptr_status ilu_setup(Ctx *c) {
     CPTR_TRY(ilu_sym_check(c, &same_pattern));
     const int32_t n = c->n, BB = c->b * c->b;
     cudaStream_t st = c->stream;
-    // the pattern the factorisation works on: the caller's order, cells permuted by colour, or the
-    // ILU(1) fill pattern
+    // the pattern the factorisation works on: the caller's order, cells permuted by colour, the
+    // ILU(1) fill pattern, or the caller's pattern without the couplings between parts (block Jacobi)
     std::vector<int32_t> rowmap;
     const bool mc = c->o.ilu_order == CPTR_ILU_MULTICOLOR;
     const bool fill = c->o.ilu_fill == 1;
+    const bool bj = c->part != nullptr;
+    if (bj && (c->n_part != n || mc || fill))
+        return c->fail(CPTR_EINVAL, c->n_part != n ? "the partition's cell count differs from the set-up's"
+                                                   : "the block-Jacobi ILU(0) needs the natural order and no fill");
     int64_t nnz_ilu = c->nnzb;
-    if (fill) {
+    if (bj) {
+        int32_t *cnt = nullptr, *dk = nullptr;
+        CPTR_TRY(dalloc_t(c, &cnt, (size_t)n + 1));
+        CPTR_TRY(dalloc_t(c, &c->ilu_rp, (size_t)n + 1));
+        c->ilu_owns_pattern = true;
+        (k_part_count<<<nblk(n, 256), 256, 0, st>>>(n, c->rp, c->ci, c->part, cnt), note_launch());
+        int32_t total = 0;
+        CPTR_TRY(scan_exclusive(c, cnt, c->ilu_rp, n, &total));
+        nnz_ilu = total;
+        CPTR_TRY(dalloc_t(c, &c->ilu_ci, (size_t)nnz_ilu));
+        CPTR_TRY(dalloc_t(c, &c->ilu_diag, (size_t)n));
+        CPTR_TRY(dalloc_t(c, &dk, (size_t)nnz_ilu));
+        (k_part_fill<<<nblk(n, 256), 256, 0, st>>>(n, c->rp, c->ci, c->part, c->ilu_rp, c->ilu_ci, c->ilu_diag, dk),
+         note_launch());
+        // two spare doubles: the factorisation copies runs of blocks in 16-byte pieces rounded outwards
+        CPTR_TRY(dalloc_t(c, &c->LU, (size_t)nnz_ilu * BB + 2));
+        (k_scatter_blocks<<<nblk(nnz_ilu * BB, 256), 256, 0, st>>>(nnz_ilu, BB, dk, c->A, c->LU), note_launch());
+        CPTR_CUDA_TRY(c, cudaStreamSynchronize(st));
+        dfree(cnt);
+        dfree(dk);
+    } else if (fill) {
         CPTR_TRY(host_pattern(c));
         std::vector<int32_t> prp, pci, pdg, kmap;
         ilu1_pattern(n, c->h_rp, c->h_ci, prp, pci, pdg, kmap);
@@ -2094,7 +2148,7 @@ cptr_status ilu_setup(Ctx *c) {
         // two spare doubles: the factorisation copies runs of blocks in 16-byte pieces rounded outwards
         CPTR_TRY(dalloc_t(c, &c->LU, (size_t)c->nnzb * BB + 2));
     }
-    if (fill) {
+    if (fill || bj) {
     } else if (mc) {
         CPTR_TRY(host_pattern(c));
         rowmap = multicolour_order(n, c->h_rp, c->h_ci);
@@ -2311,11 +2365,11 @@ cptr_status ilu_setup(Ctx *c) {
     dfree(kidx_f); dfree(kidx_b); dfree(kidx_d);
     dfree(inv_f); dfree(inv_b); dfree(levr_f); dfree(levr_b);
     // the chunked and tiled schedules read the caller's pattern: natural order without fill only
-    if (!mc && !fill && (c->o.ilu_sweep == 2 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 1))))
+    if (!mc && !fill && !bj && (c->o.ilu_sweep == 2 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 1))))
         CPTR_TRY(cw_setup(c));
     // tiled sweeps: on a natural-order box, with the cached tile shape or the best modelled one
     c->tl_use = false;
-    if (!mc && !fill && (c->o.ilu_sweep == 4 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 3))) &&
+    if (!mc && !fill && !bj && (c->o.ilu_sweep == 4 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 3))) &&
         tile_grid(c)) {
         int Ty = 0, Tz = 0;
         auto it = c->tune_cache.find(ilu_tune_key(c) + 2);

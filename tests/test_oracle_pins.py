@@ -1037,3 +1037,56 @@ def test_newton_oracle_solves_the_step_with_quadratic_convergence():
     # quadratic: r_{k+1} / r_k^2 stays bounded while r_k falls by orders of magnitude
     rat = [res[k + 1] / res[k] ** 2 for k in range(1, len(res) - 1)]
     assert res[-2] / res[1] < 1e-3 and max(rat[1:]) <= 10 * rat[0] + 1e-30, (res, rat)
+
+
+# ------------------------------------------------------------------------------------------------
+# Block-Jacobi ILU(0) (Sec. 4: the paper's parallel second stage, ILU(k) on each part of the domain)
+def _quadrants(nx, ny, nz, px=2, py=2):
+    i = np.arange(nx * ny * nz)
+    x, y = i % nx, (i // nx) % ny
+    return ((x * px) // nx + px * ((y * py) // ny)).astype(np.int32)
+
+
+def _drop_cross_part_blocks(s, part):
+    """The same system with every block between cells of different parts removed from the input."""
+    rp, ci, vals = s["row_ptr"], s["col_idx"], s["vals"]
+    keep = np.array([part[i] == part[ci[k]] for i in range(s["n"]) for k in range(rp[i], rp[i + 1])])
+    rows = np.repeat(np.arange(s["n"]), np.diff(rp))
+    out = dict(s)
+    out["col_idx"] = ci[keep].astype(np.int32)
+    out["vals"] = vals[keep]
+    out["row_ptr"] = np.concatenate([[0], np.cumsum(np.bincount(rows[keep], minlength=s["n"]))]).astype(np.int32)
+    out["st"] = s["st"][keep]
+    return out
+
+
+def test_block_jacobi_ilu_is_ilu_of_the_matrix_without_cross_part_couplings():
+    """ILU(0) over parts equals, bit for bit, ILU(0) of the system whose cross-part blocks were
+    removed before the set-up; one part gives the global ILU(0)."""
+    r = synth.make_box(8, 6, 3, 3.125, seed=21)
+    s = r.system()
+    part = _quadrants(8, 6, 3)
+    o_bj = oracle.Oracle.from_system(s, max_levels=1, part=part)
+    o_drop = oracle.Oracle.from_system(_drop_cross_part_blocks(s, part), max_levels=1)
+    assert np.array_equal(o_bj.ilu_factors(), o_drop.ilu_factors())
+    rp, ci = o_bj.ilu_pattern()
+    cells = np.repeat(np.arange(o_bj.nb), np.diff(rp)) // 3
+    assert np.all(part[cells] == part[ci // 3])
+    v = synth.normal(61, o_bj.nb)
+    assert np.array_equal(o_bj.ilu_apply(v), o_drop.ilu_apply(v))
+    o_one = oracle.Oracle.from_system(s, max_levels=1, part=np.zeros(s["n"], np.int32))
+    o_glob = oracle.Oracle.from_system(s, max_levels=1)
+    assert np.array_equal(o_one.ilu_factors(), o_glob.ilu_factors())
+
+
+def test_block_jacobi_ilu_trend():
+    """More parts, a weaker second stage: the solve still converges, in at least as many iterations."""
+    s = synth.make_box(40, 40, 10, 0.5, 0.5, 0.25, seed=11, sigma=2.0, layered=True, kv_ratio=0.1,
+                       kT_const=2.0, T_inj=500.0, q_inj=1e-6, dt=30 * 86400.0).system()
+    its = []
+    for px, py in ((1, 1), (2, 2), (4, 4)):
+        part = _quadrants(40, 40, 10, px, py)
+        x, info = oracle.Oracle.from_system(s, part=part).solve(s["rhs"], 1e-8)
+        assert info["converged"]
+        its.append(info["iters"])
+    assert its[0] <= its[1] <= its[2], its
