@@ -1026,7 +1026,9 @@ __device__ __forceinline__ float vld(const bf16 *p) {
 }
 
 // pre-smoothing from zero fused with the residual: t = D^{-1} b, r = b - A t
-template <int G, typename VT, typename XT>
+// (TR: t = D^{-1} b was written by the producer of b, so the row reads t instead of D^{-1} and b:
+// one multiply fewer per entry, the same values)
+template <int G, typename VT, typename XT, bool TR>
 __global__ void __launch_bounds__(512) k_vc_down(int32_t n, const int32_t *__restrict__ rp,
                                                   const int32_t *__restrict__ ci, const VT *__restrict__ v,
                                                   const XT *__restrict__ dinv, const XT *__restrict__ b,
@@ -1042,13 +1044,13 @@ __global__ void __launch_bounds__(512) k_vc_down(int32_t n, const int32_t *__res
             acc = row_dot_batched<8>(__ldg(rp + row), k1, ci, [&](int32_t k) { return (XT)vld(v + k); },
                                      [&](int32_t j) {
                                          j = (int32_t)chk(j, n, CHK_VC_COL);
-                                         return __ldg(dinv + j) * __ldg(b + j);
+                                         return TR ? __ldg(t + j) : __ldg(dinv + j) * __ldg(b + j);
                                      },
                                      acc);
         } else {
             for (int32_t k = __ldg(rp + row) + lane; k < k1; k += G) {
                 int32_t j = (int32_t)chk(__ldg(ci + k), n, CHK_VC_COL);
-                acc = fma((XT)vld(v + k), __ldg(dinv + j) * __ldg(b + j), acc);
+                acc = fma((XT)vld(v + k), TR ? __ldg(t + j) : __ldg(dinv + j) * __ldg(b + j), acc);
             }
         }
     }
@@ -1056,7 +1058,7 @@ __global__ void __launch_bounds__(512) k_vc_down(int32_t n, const int32_t *__res
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
     if (row < n && lane == 0) {
         XT bi = b[row];
-        t[row] = dinv[row] * bi;
+        if (!TR) t[row] = dinv[row] * bi;
         r[row] = bi - acc;
     }
 }
@@ -1104,19 +1106,25 @@ __global__ void k_diag_scale(int32_t n, const XT *d, const XT *b, XT *x) {
     if (i < n) x[i] = d[i] * b[i];
 }
 
-template <typename VT, typename XT>
-static void launch_down(cudaStream_t s, const Level &L, const VT *v, const XT *dinv, const XT *b, XT *t, XT *r) {
+template <typename VT, typename XT, bool TR>
+static void launch_down_t(cudaStream_t s, const Level &L, const VT *v, const XT *dinv, const XT *b, XT *t, XT *r) {
     const int G = L.sh_A.G ? L.sh_A.G : lanes_for(L.A.n, L.A.nnz), T = L.sh_A.T;
     unsigned grid = nblk((int64_t)L.A.n * G, T);
     const Csr &A = L.A;
     switch (G) {
-    case 1: launch_pdl(k_vc_down<1, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
-    case 2: launch_pdl(k_vc_down<2, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
-    case 4: launch_pdl(k_vc_down<4, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
-    case 8: launch_pdl(k_vc_down<8, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
-    case 16: launch_pdl(k_vc_down<16, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
-    default: launch_pdl(k_vc_down<32, VT, XT>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
+    case 1: launch_pdl(k_vc_down<1, VT, XT, TR>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
+    case 2: launch_pdl(k_vc_down<2, VT, XT, TR>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
+    case 4: launch_pdl(k_vc_down<4, VT, XT, TR>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
+    case 8: launch_pdl(k_vc_down<8, VT, XT, TR>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
+    case 16: launch_pdl(k_vc_down<16, VT, XT, TR>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
+    default: launch_pdl(k_vc_down<32, VT, XT, TR>, grid, T, 0, s, A.n, A.rp, A.ci, v, dinv, b, t, r); break;
     }
+}
+template <typename VT, typename XT>
+static void launch_down(cudaStream_t s, const Level &L, const VT *v, const XT *dinv, const XT *b, XT *t, XT *r,
+                        bool t_ready = false) {
+    if (t_ready) launch_down_t<VT, XT, true>(s, L, v, dinv, b, t, r);
+    else launch_down_t<VT, XT, false>(s, L, v, dinv, b, t, r);
 }
 template <typename VT, typename XT>
 static void launch_post(cudaStream_t s, const Level &L, const VT *v, const XT *dinv, const XT *b, const XT *t, XT *x) {
@@ -1152,17 +1160,19 @@ template <> struct LevelVecs<float> {
 
 // one smoothing/residual/transfer step of level L with its matrix values in storage VT; pf >= 0
 // times each kernel as profiling family pf + step (the fine level only)
+// (t_ready: this level's t = D^{-1} b was written by the producer of b; the restriction writes the
+// coarse level's t = D_c^{-1} b_c for the same reason)
 template <typename VT, typename XT>
 static void level_down(const Ctx *c, int pf, const Level &L, const Level &C, const VT *Av, const VT *PTv,
-                       const XT *b) {
+                       const XT *b, bool t_ready) {
     using LV = LevelVecs<XT>;
     cudaStream_t s = c->stream;
     int ev = pf < 0 ? -1 : prof_begin(c, pf);
-    launch_down<VT, XT>(s, L, Av, LV::dinv(L), b, LV::t(L), LV::r(L));             // t = D^-1 b, r = b - A t
+    launch_down<VT, XT>(s, L, Av, LV::dinv(L), b, LV::t(L), LV::r(L), t_ready);    // t = D^-1 b, r = b - A t
     prof_end(c, ev);
     ev = pf < 0 ? -1 : prof_begin(c, pf + 1);
     launch_csr_spmv_t<VT, XT>(s, L.PT.n, L.PT.nnz, L.PT.rp, L.PT.ci, PTv, LV::r(L), LV::b(C), 0, nullptr,
-                              L.sh_PT, L.A.n);                                                 // b_c = P^T r
+                              L.sh_PT, L.A.n, LV::dinv(C), LV::t(C));                          // b_c = P^T r
     prof_end(c, ev);
 }
 template <typename VT, typename XT>
@@ -1293,7 +1303,7 @@ cptr_status amg_fuse_setup(Ctx *c, Hier &h) {
 }
 
 template <typename XT>
-static void vcycle_level(const Ctx *c, const Hier &h, int l, const XT *b, XT *x) {
+static void vcycle_level(const Ctx *c, const Hier &h, int l, const XT *b, XT *x, bool t_ready) {
     using LV = LevelVecs<XT>;
     cudaStream_t s = c->stream;
     const Level &L = h.L[l];
@@ -1314,29 +1324,33 @@ static void vcycle_level(const Ctx *c, const Hier &h, int l, const XT *b, XT *x)
         const LevelDev *ld = lo ? h.ldev32 : h.ldev64;
         const int lc = h.nlev - 1;
         launch_pdl(k_vc_fused_down<XT>, 1, kFuseThreads, 0, s, ld, l, lc, b);
-        vcycle_level<XT>(c, h, lc, LV::b(h.L[lc]), LV::x(h.L[lc]));
+        vcycle_level<XT>(c, h, lc, LV::b(h.L[lc]), LV::x(h.L[lc]), false);
         launch_pdl(k_vc_fused_up<XT>, 1, kFuseThreads, 0, s, ld, l, lc, b, x);
         return;
     }
     const Level &C = h.L[l + 1];
     const int pf = l == 0 ? PF_VC + 4 * (&h == &c->hT) : -1;
     if (!lo) {
-        level_down<double, double>(c, pf, L, C, L.A.v, L.PT.v, (const double *)b);
-        vcycle_level<XT>(c, h, l + 1, LV::b(C), LV::x(C));
+        level_down<double, double>(c, pf, L, C, L.A.v, L.PT.v, (const double *)b, t_ready);
+        vcycle_level<XT>(c, h, l + 1, LV::b(C), LV::x(C), true);
         level_up<double, double>(c, pf, L, C, L.A.v, L.P.v, (const double *)b, (double *)x);
     } else if (L.st == ST_BF16) {
-        level_down<bf16, float>(c, pf, L, C, (const bf16 *)L.Av_lo, (const bf16 *)L.PTv_lo, (const float *)b);
-        vcycle_level<XT>(c, h, l + 1, LV::b(C), LV::x(C));
+        level_down<bf16, float>(c, pf, L, C, (const bf16 *)L.Av_lo, (const bf16 *)L.PTv_lo, (const float *)b, t_ready);
+        vcycle_level<XT>(c, h, l + 1, LV::b(C), LV::x(C), true);
         level_up<bf16, float>(c, pf, L, C, (const bf16 *)L.Av_lo, (const bf16 *)L.Pv_lo, (const float *)b, (float *)x);
     } else {
-        level_down<float, float>(c, pf, L, C, (const float *)L.Av_lo, (const float *)L.PTv_lo, (const float *)b);
-        vcycle_level<XT>(c, h, l + 1, LV::b(C), LV::x(C));
+        level_down<float, float>(c, pf, L, C, (const float *)L.Av_lo, (const float *)L.PTv_lo, (const float *)b, t_ready);
+        vcycle_level<XT>(c, h, l + 1, LV::b(C), LV::x(C), true);
         level_up<float, float>(c, pf, L, C, (const float *)L.Av_lo, (const float *)L.Pv_lo, (const float *)b, (float *)x);
     }
 }
 
-void amg_vcycle(const Ctx *c, const Hier &h, const double *b, double *x) { vcycle_level<double>(c, h, 0, b, x); }
-void amg_vcycle32(const Ctx *c, const Hier &h, const float *b, float *x) { vcycle_level<float>(c, h, 0, b, x); }
+void amg_vcycle(const Ctx *c, const Hier &h, const double *b, double *x, bool t_ready) {
+    vcycle_level<double>(c, h, 0, b, x, t_ready);
+}
+void amg_vcycle32(const Ctx *c, const Hier &h, const float *b, float *x, bool t_ready) {
+    vcycle_level<float>(c, h, 0, b, x, t_ready);
+}
 
 // the mixed-precision copies of a hierarchy: levels 0 and 1 in FP32, levels >= 2 in BF16
 // (matrix and transfer values); D^{-1} and work vectors in FP32; the coarsest dense inverse and

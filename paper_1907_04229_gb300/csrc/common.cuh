@@ -198,15 +198,22 @@ void launch_bsr_to_sell(const Ctx *c);
 void launch_bsr_spmv(const Ctx *c, const double *x, double *y);
 void launch_bsr_resid(const Ctx *c, const double *x, const double *v, double *y);
 void launch_bsr_resid_pt(const Ctx *c, const double *dp, const double *dT, const double *v, double *b1);
-void launch_csr_spmv(cudaStream_t s, const Csr &A, const double *x, double *y, double alpha, const double *c0);
+// ts, to (optional): also to = ts * y per row (the first smoothing step of a V-cycle on y)
+void launch_csr_spmv(cudaStream_t s, const Csr &A, const double *x, double *y, double alpha, const double *c0,
+                     const double *ts = nullptr, double *to = nullptr);
 // y = A x (mode 0), y = c0 - A x (mode 1), y += A x (mode 2); values VT, vectors and sums XT
 template <typename VT, typename XT>
 void launch_csr_spmv_t(cudaStream_t s, int32_t n, int32_t nnz, const int32_t *rp, const int32_t *ci, const VT *v,
-                       const XT *x, XT *y, int mode, const XT *c0, Shape sh = Shape(), int32_t ncol = INT32_MAX);
+                       const XT *x, XT *y, int mode, const XT *c0, Shape sh = Shape(), int32_t ncol = INT32_MAX,
+                       const XT *ts = nullptr, XT *to = nullptr);
 cptr_status to_lower(Ctx *c, const double *src, int64_t n, int st, void **dst);
 void launch_d2f(const Ctx *c, const double *a, float *b, int64_t n);
 void launch_f2d(const Ctx *c, const float *a, double *b, int64_t n);
-template <typename XT> void launch_gather_pt(const Ctx *c, const double *v, XT *bp, XT *bT);
+// bp, bT of stage 1 from v (decoupled when the context has D); sp/tp, sT/tT (optional): also
+// tp = sp * bp, tT = sT * bT (the first smoothing step of a V-cycle on bp or bT)
+template <typename XT>
+void launch_gather_pt(const Ctx *c, const double *v, XT *bp, XT *bT, const XT *sp = nullptr, XT *tp = nullptr,
+                      const XT *sT = nullptr, XT *tT = nullptr);
 template <typename XT> void launch_scatter_pt(const Ctx *c, const XT *dp, const XT *dT, double *x1);
 void launch_resid_pt32(const Ctx *c, const float *dp, const float *dT, const double *v, float *b1);
 void launch_sub(cudaStream_t s, int32_t n, const double *a, const double *b, double *out);
@@ -230,8 +237,9 @@ void amg_free(Hier &h);
 // its other thread for ~0.4 s on a 2M-cell system.
 void amg_preload();
 cptr_status amg_coarsest_wait(Ctx *c, Hier &h);   // join the coarse stream's inverse; its status
-void amg_vcycle(const Ctx *c, const Hier &h, const double *b, double *x);
-void amg_vcycle32(const Ctx *c, const Hier &h, const float *b, float *x);
+// x = one V(1,1)-cycle on b; t_ready: the finest level's t = D^{-1} b was written by b's producer
+void amg_vcycle(const Ctx *c, const Hier &h, const double *b, double *x, bool t_ready = false);
+void amg_vcycle32(const Ctx *c, const Hier &h, const float *b, float *x, bool t_ready = false);
 cptr_status amg_lower_precision(Ctx *c, Hier &h);
 
 // ---- ilu.cu ------------------------------------------------------------------------------------

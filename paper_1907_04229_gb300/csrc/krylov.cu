@@ -253,38 +253,43 @@ void apply_stage1(const Ctx *c, const double *v, const double **pdp, const doubl
     *pdT = nullptr;
     int mode = c->o.stage1;
     if (mode == CPTR_STAGE1_NONE) return;
+    // Every right-hand side of a V-cycle below is written together with its finest level's
+    // t = D^{-1} b (the first smoothing step), so the V-cycles start from it (t_ready).
+    const Level &P0 = c->hp.L[0], &T0 = c->hT.L[0];
     if (mode == CPTR_STAGE1_UAMG) {   // Sec. 3.4: one unknown-based V-cycle on A_00 [d_p; d_T] = [b_p; b_T]
-        launch_gather_pt<double>(c, v, c->b00, c->b00 + c->n);
-        amg_vcycle(c, c->hp, c->b00, c->x00);
+        launch_gather_pt<double>(c, v, c->b00, c->b00 + c->n, P0.dinv, P0.t, P0.dinv + c->n, P0.t + c->n);
+        amg_vcycle(c, c->hp, c->b00, c->x00, true);
         *pdp = c->x00;
         *pdT = c->x00 + c->n;
         return;
     }
-    launch_gather_pt<double>(c, v, c->bp, c->bT);
+    const bool t_direct = mode == CPTR_STAGE1_UPPER || mode == CPTR_STAGE1_BD;   // b_T itself goes to a V-cycle
+    launch_gather_pt<double>(c, v, c->bp, c->bT, P0.dinv, P0.t, t_direct ? T0.dinv : nullptr,
+                             t_direct ? T0.t : nullptr);
     switch (mode) {
     case CPTR_STAGE1_FULL:
-        amg_vcycle(c, c->hp, c->bp, c->xp);                     // 1. A_pp x_p = b_p
-        launch_csr_spmv(s, ATp, c->xp, c->t1, 1.0, c->bT);      // 2. b~_T = b_T - A_Tp x_p
-        amg_vcycle(c, c->hT, c->t1, c->dT);                     // 3. S~_T d_T = b~_T
-        launch_csr_spmv(s, ApT, c->dT, c->t1, 1.0, c->bp);      // 4. b~_p = b_p - A_pT d_T
-        amg_vcycle(c, c->hp, c->t1, c->dp);                     // 5. A_pp d_p = b~_p
+        amg_vcycle(c, c->hp, c->bp, c->xp, true);                               // 1. A_pp x_p = b_p
+        launch_csr_spmv(s, ATp, c->xp, c->t1, 1.0, c->bT, T0.dinv, T0.t);      // 2. b~_T = b_T - A_Tp x_p
+        amg_vcycle(c, c->hT, c->t1, c->dT, true);                               // 3. S~_T d_T = b~_T
+        launch_csr_spmv(s, ApT, c->dT, c->t1, 1.0, c->bp, P0.dinv, P0.t);      // 4. b~_p = b_p - A_pT d_T
+        amg_vcycle(c, c->hp, c->t1, c->dp, true);                               // 5. A_pp d_p = b~_p
         break;
     case CPTR_STAGE1_LOWER:
-        amg_vcycle(c, c->hp, c->bp, c->dp);
-        launch_csr_spmv(s, ATp, c->dp, c->t1, 1.0, c->bT);
-        amg_vcycle(c, c->hT, c->t1, c->dT);
+        amg_vcycle(c, c->hp, c->bp, c->dp, true);
+        launch_csr_spmv(s, ATp, c->dp, c->t1, 1.0, c->bT, T0.dinv, T0.t);
+        amg_vcycle(c, c->hT, c->t1, c->dT, true);
         break;
     case CPTR_STAGE1_UPPER:
-        amg_vcycle(c, c->hT, c->bT, c->dT);
-        launch_csr_spmv(s, ApT, c->dT, c->t1, 1.0, c->bp);
-        amg_vcycle(c, c->hp, c->t1, c->dp);
+        amg_vcycle(c, c->hT, c->bT, c->dT, true);
+        launch_csr_spmv(s, ApT, c->dT, c->t1, 1.0, c->bp, P0.dinv, P0.t);
+        amg_vcycle(c, c->hp, c->t1, c->dp, true);
         break;
     case CPTR_STAGE1_BD:
-        amg_vcycle(c, c->hp, c->bp, c->dp);
-        amg_vcycle(c, c->hT, c->bT, c->dT);
+        amg_vcycle(c, c->hp, c->bp, c->dp, true);
+        amg_vcycle(c, c->hT, c->bT, c->dT, true);
         break;
     case CPTR_STAGE1_CPR:
-        amg_vcycle(c, c->hp, c->bp, c->dp);
+        amg_vcycle(c, c->hp, c->bp, c->dp, true);
         *pdp = c->dp;
         return;
     }
@@ -296,48 +301,52 @@ void apply_stage1(const Ctx *c, const double *v, const double **pdp, const doubl
 void apply_stage1_32(const Ctx *c, const double *v, const float **pdp, const float **pdT) {
     cudaStream_t s = c->stream;
     const int32_t n = c->n, nnz = c->nnzb;
-    auto Tp = [&](const float *x, float *y, const float *c0) {   // y = c0 - A_Tp x
-        launch_csr_spmv_t<float, float>(s, n, nnz, c->rp, c->ci, c->ATp32, x, y, 1, c0, Shape(), n);
+    // as in apply_stage1: every V-cycle right-hand side comes with its finest level's t = D^{-1} b
+    const Level &P0 = c->hp.L[0], &T0 = c->hT.L[0];
+    auto Tp = [&](const float *x, float *y, const float *c0) {   // y = c0 - A_Tp x, for the T V-cycle
+        launch_csr_spmv_t<float, float>(s, n, nnz, c->rp, c->ci, c->ATp32, x, y, 1, c0, Shape(), n, T0.dinv32, T0.t32);
     };
-    auto pT = [&](const float *x, float *y, const float *c0) {   // y = c0 - A_pT x
-        launch_csr_spmv_t<float, float>(s, n, nnz, c->rp, c->ci, c->ApT32, x, y, 1, c0, Shape(), n);
+    auto pT = [&](const float *x, float *y, const float *c0) {   // y = c0 - A_pT x, for the p V-cycle
+        launch_csr_spmv_t<float, float>(s, n, nnz, c->rp, c->ci, c->ApT32, x, y, 1, c0, Shape(), n, P0.dinv32, P0.t32);
     };
     *pdp = nullptr;
     *pdT = nullptr;
     int mode = c->o.stage1;
     if (mode == CPTR_STAGE1_NONE) return;
     if (mode == CPTR_STAGE1_UAMG) {
-        launch_gather_pt<float>(c, v, c->b0032, c->b0032 + n);
-        amg_vcycle32(c, c->hp, c->b0032, c->x0032);
+        launch_gather_pt<float>(c, v, c->b0032, c->b0032 + n, P0.dinv32, P0.t32, P0.dinv32 + n, P0.t32 + n);
+        amg_vcycle32(c, c->hp, c->b0032, c->x0032, true);
         *pdp = c->x0032;
         *pdT = c->x0032 + n;
         return;
     }
-    launch_gather_pt<float>(c, v, c->bp32, c->bT32);
+    const bool t_direct = mode == CPTR_STAGE1_UPPER || mode == CPTR_STAGE1_BD;   // b_T itself goes to a V-cycle
+    launch_gather_pt<float>(c, v, c->bp32, c->bT32, P0.dinv32, P0.t32, t_direct ? T0.dinv32 : nullptr,
+                            t_direct ? T0.t32 : nullptr);
     switch (mode) {
     case CPTR_STAGE1_FULL:
-        amg_vcycle32(c, c->hp, c->bp32, c->xp32);
+        amg_vcycle32(c, c->hp, c->bp32, c->xp32, true);
         Tp(c->xp32, c->t132, c->bT32);
-        amg_vcycle32(c, c->hT, c->t132, c->dT32);
+        amg_vcycle32(c, c->hT, c->t132, c->dT32, true);
         pT(c->dT32, c->t132, c->bp32);
-        amg_vcycle32(c, c->hp, c->t132, c->dp32);
+        amg_vcycle32(c, c->hp, c->t132, c->dp32, true);
         break;
     case CPTR_STAGE1_LOWER:
-        amg_vcycle32(c, c->hp, c->bp32, c->dp32);
+        amg_vcycle32(c, c->hp, c->bp32, c->dp32, true);
         Tp(c->dp32, c->t132, c->bT32);
-        amg_vcycle32(c, c->hT, c->t132, c->dT32);
+        amg_vcycle32(c, c->hT, c->t132, c->dT32, true);
         break;
     case CPTR_STAGE1_UPPER:
-        amg_vcycle32(c, c->hT, c->bT32, c->dT32);
+        amg_vcycle32(c, c->hT, c->bT32, c->dT32, true);
         pT(c->dT32, c->t132, c->bp32);
-        amg_vcycle32(c, c->hp, c->t132, c->dp32);
+        amg_vcycle32(c, c->hp, c->t132, c->dp32, true);
         break;
     case CPTR_STAGE1_BD:
-        amg_vcycle32(c, c->hp, c->bp32, c->dp32);
-        amg_vcycle32(c, c->hT, c->bT32, c->dT32);
+        amg_vcycle32(c, c->hp, c->bp32, c->dp32, true);
+        amg_vcycle32(c, c->hT, c->bT32, c->dT32, true);
         break;
     case CPTR_STAGE1_CPR:
-        amg_vcycle32(c, c->hp, c->bp32, c->dp32);
+        amg_vcycle32(c, c->hp, c->bp32, c->dp32, true);
         *pdp = c->dp32;
         return;
     }

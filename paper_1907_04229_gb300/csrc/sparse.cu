@@ -581,7 +581,8 @@ template <int G, typename VT, typename XT>
 __global__ void __launch_bounds__(512) k_csr_spmv(int32_t n, const int32_t *__restrict__ rp,
                                                    const int32_t *__restrict__ ci, const VT *__restrict__ v,
                                                    const XT *__restrict__ x, XT *__restrict__ y, int mode,
-                                                   const XT *__restrict__ c0, int32_t ncol) {
+                                                   const XT *__restrict__ c0, int32_t ncol, const XT *__restrict__ ts,
+                                                   XT *__restrict__ to) {
     pdl_wait();
     int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int32_t row = (int32_t)(gid / G);
@@ -603,33 +604,39 @@ __global__ void __launch_bounds__(512) k_csr_spmv(int32_t n, const int32_t *__re
         if (mode == 0) y[row] = acc;
         else if (mode == 1) y[row] = c0[row] - acc;
         else y[row] += acc;
+        // the output feeds a V-cycle level: its first smoothing step t = D^{-1} y as well
+        if (to) to[row] = ts[row] * (mode == 0 ? acc : c0[row] - acc);
     }
 }
 
 template <typename VT, typename XT>
 void launch_csr_spmv_t(cudaStream_t s, int32_t n, int32_t nnz, const int32_t *rp, const int32_t *ci, const VT *v,
-                       const XT *x, XT *y, int mode, const XT *c0, Shape sh, int32_t ncol) {
+                       const XT *x, XT *y, int mode, const XT *c0, Shape sh, int32_t ncol, const XT *ts, XT *to) {
     const int G = sh.G ? sh.G : lanes_for(n, nnz), T = sh.T;
     unsigned grid = nblk((int64_t)n * G, T);
     switch (G) {
-    case 1: launch_pdl(k_csr_spmv<1, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol); break;
-    case 2: launch_pdl(k_csr_spmv<2, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol); break;
-    case 4: launch_pdl(k_csr_spmv<4, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol); break;
-    case 8: launch_pdl(k_csr_spmv<8, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol); break;
-    case 16: launch_pdl(k_csr_spmv<16, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol); break;
-    default: launch_pdl(k_csr_spmv<32, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol); break;
+    case 1: launch_pdl(k_csr_spmv<1, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol, ts, to); break;
+    case 2: launch_pdl(k_csr_spmv<2, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol, ts, to); break;
+    case 4: launch_pdl(k_csr_spmv<4, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol, ts, to); break;
+    case 8: launch_pdl(k_csr_spmv<8, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol, ts, to); break;
+    case 16: launch_pdl(k_csr_spmv<16, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol, ts, to); break;
+    default: launch_pdl(k_csr_spmv<32, VT, XT>, grid, T, 0, s, n, rp, ci, v, x, y, mode, c0, ncol, ts, to); break;
     }
 }
 template void launch_csr_spmv_t<double, double>(cudaStream_t, int32_t, int32_t, const int32_t *, const int32_t *,
-                                                const double *, const double *, double *, int, const double *, Shape, int32_t);
+                                                const double *, const double *, double *, int, const double *, Shape, int32_t,
+                                                const double *, double *);
 template void launch_csr_spmv_t<float, float>(cudaStream_t, int32_t, int32_t, const int32_t *, const int32_t *,
-                                              const float *, const float *, float *, int, const float *, Shape, int32_t);
+                                              const float *, const float *, float *, int, const float *, Shape, int32_t,
+                                              const float *, float *);
 template void launch_csr_spmv_t<bf16, float>(cudaStream_t, int32_t, int32_t, const int32_t *, const int32_t *,
-                                             const bf16 *, const float *, float *, int, const float *, Shape, int32_t);
+                                             const bf16 *, const float *, float *, int, const float *, Shape, int32_t,
+                                             const float *, float *);
 
-void launch_csr_spmv(cudaStream_t s, const Csr &A, const double *x, double *y, double alpha, const double *c0) {
+void launch_csr_spmv(cudaStream_t s, const Csr &A, const double *x, double *y, double alpha, const double *c0,
+                     const double *ts, double *to) {
     int mode = c0 ? 1 : (alpha == 2.0 ? 2 : 0);
-    launch_csr_spmv_t<double, double>(s, A.n, A.nnz, A.rp, A.ci, A.v, x, y, mode, c0, Shape(), A.n);   // square
+    launch_csr_spmv_t<double, double>(s, A.n, A.nnz, A.rp, A.ci, A.v, x, y, mode, c0, Shape(), A.n, ts, to);   // square
 }
 
 // FP64 -> FP32 (round to nearest) or FP64 -> FP32 -> BF16 (round to nearest even): the storage
@@ -668,7 +675,8 @@ cptr_status to_lower(Ctx *c, const double *src, int64_t n, int st, void **dst) {
 // ------------------------------------------------------------------------------------------------
 // restriction to / prolongation from the p-T unknowns (Sec. 3.2)
 template <typename XT>
-__global__ void k_gather_pt(int32_t n, int b, int ps, int ts, const double *v, XT *bp, XT *bT, const double *D) {
+__global__ void k_gather_pt(int32_t n, int b, int ps, int ts, const double *v, XT *bp, XT *bT, const double *D,
+                            const XT *sp, XT *tp, const XT *sT, XT *tT) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         double p = v[(int64_t)i * b + ps], t = v[(int64_t)i * b + ts];
@@ -680,15 +688,21 @@ __global__ void k_gather_pt(int32_t n, int b, int ps, int ts, const double *v, X
             }
         bp[i] = (XT)p;
         bT[i] = (XT)t;
+        // the first smoothing step of a V-cycle on bp or bT: t = D^{-1} b of its finest level
+        if (tp) tp[i] = sp[i] * (XT)p;
+        if (tT) tT[i] = sT[i] * (XT)t;
     }
 }
 template <typename XT>
-void launch_gather_pt(const Ctx *c, const double *v, XT *bp, XT *bT) {
-    (k_gather_pt<XT><<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->ps, c->ts, v, bp, bT, c->Ddec),
+void launch_gather_pt(const Ctx *c, const double *v, XT *bp, XT *bT, const XT *sp, XT *tp, const XT *sT, XT *tT) {
+    (k_gather_pt<XT><<<nblk(c->n, 256), 256, 0, c->stream>>>(c->n, c->b, c->ps, c->ts, v, bp, bT, c->Ddec, sp, tp, sT,
+                                                            tT),
      note_launch());
 }
-template void launch_gather_pt<double>(const Ctx *, const double *, double *, double *);
-template void launch_gather_pt<float>(const Ctx *, const double *, float *, float *);
+template void launch_gather_pt<double>(const Ctx *, const double *, double *, double *, const double *, double *,
+                                       const double *, double *);
+template void launch_gather_pt<float>(const Ctx *, const double *, float *, float *, const float *, float *,
+                                      const float *, float *);
 
 template <typename XT>
 __global__ void k_scatter_pt(int32_t n, int b, int ps, int ts, const XT *dp, const XT *dT, double *x1) {
