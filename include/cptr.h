@@ -130,6 +130,11 @@ typedef struct {
     int32_t ilu_fill;    /* level of fill of the second stage's block ILU(k): 0 (default) or 1 (block row
                             i gains, for every block k < i of its row, the blocks j > k of row k;
                             natural ILU order only; the sweeps then use level sets or paired levels) */
+    int32_t csr_lanes;   /* lanes per row of the V-cycle kernels (smoother + residual, restriction,
+                            prolongation) on every level when autotune is 0: 0 (default) chosen from
+                            each operator's size and average row length, else 1, 2, 4, 8, 16 or 32
+                            (other values: CPTR_EINVAL at cptr_create).  One lane adds a row's
+                            products in order; more lanes add lane-strided partial sums. */
 } cptr_options;
 
 typedef struct {

@@ -338,6 +338,12 @@ cptr_status do_setup(Ctx *c, int32_t n, int32_t b, const int32_t *row_ptr, const
             CPTR_TRY(check_wait_flag(c));
         }
         setup_tick(c, SETUP_OTHER, &ta);
+    } else if (c->o.csr_lanes) {
+        for (Hier *h : {&c->hp, &c->hT})
+            for (int l = 0; l < h->nlev; ++l) {
+                Level &L = h->L[l];
+                L.sh_A.G = L.sh_PT.G = L.sh_P.G = (int16_t)c->o.csr_lanes;
+            }
     }
     CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     CPTR_CUDA_TRY(c, cudaGetLastError());
@@ -460,7 +466,8 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
         o.tile_y < 0 || o.tile_z < 0 || (size_t)o.tile_y * o.tile_z > 64 || o.decouple < CPTR_DECOUPLE_NONE ||
         o.decouple > CPTR_DECOUPLE_TI ||
         (o.decouple != CPTR_DECOUPLE_NONE && o.stage1 != CPTR_STAGE1_CPR && o.stage1 != CPTR_STAGE1_UAMG) ||
-        o.ilu_fill < 0 || o.ilu_fill > 1 || (o.ilu_fill == 1 && o.ilu_order == CPTR_ILU_MULTICOLOR))
+        o.ilu_fill < 0 || o.ilu_fill > 1 || (o.ilu_fill == 1 && o.ilu_order == CPTR_ILU_MULTICOLOR) ||
+        o.csr_lanes < 0 || o.csr_lanes > 32 || (o.csr_lanes & (o.csr_lanes - 1)))
         return CPTR_EINVAL;
     cptr_ctx *ctx = new (std::nothrow) cptr_ctx();
     if (!ctx) return CPTR_ENOMEM;

@@ -57,12 +57,51 @@ def test_default_options(lib):
 
 
 def test_option_struct_layout_matches_header():
-    # cptr_options: 4 int32, 2 doubles, 12 int32, one pointer, 4 int32
-    assert ctypes.sizeof(cp.cptr_options) == 16 + 16 + 48 + 8 + 16
+    # cptr_options: 4 int32, 2 doubles, 12 int32, one pointer, 5 int32 (+ padding)
+    assert ctypes.sizeof(cp.cptr_options) == 16 + 16 + 48 + 8 + 24
     assert cp.cptr_options.stream.offset == 80
     # cptr_instance: int32 (+ padding), five pointers
     assert ctypes.sizeof(cp.cptr_instance) == 8 + 5 * 8
     assert ctypes.sizeof(cp.cptr_stats) == 24 + 7 * 8
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """The binding's ctypes structures against the C compiler's own layout of the header: the size
+    of each struct and the offset of every field."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"cptr_options": cp.cptr_options, "cptr_instance": cp.cptr_instance, "cptr_stats": cp.cptr_stats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "cptr.h"', "int main(void) {"]
+    for name, st in structs.items():
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f in st._fields_:
+            lines.append(f'printf("{name} {f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in filter(None, out):
+        name, field, value = line.split()
+        st = structs[name]
+        expect = ctypes.sizeof(st) if field == "sizeof" else getattr(st, field).offset
+        assert int(value) == expect, (name, field, value, expect)
+        seen += 1
+    assert seen == sum(len(st._fields_) + 1 for st in structs.values())
+
+
+def test_invalid_options_are_rejected_before_any_device_work(lib):
+    # cptr_create validates its options first and returns CPTR_EINVAL without touching a device
+    for kw in (dict(csr_lanes=-1), dict(csr_lanes=3), dict(csr_lanes=64), dict(use_graph=3), dict(restart=0)):
+        o = cp.cptr_default_options(**kw)
+        h = ctypes.c_void_p()
+        assert lib.cptr_create(ctypes.byref(h), ctypes.byref(o)) == -1, kw
+        assert not h.value
 
 
 def test_null_context_is_rejected(lib):

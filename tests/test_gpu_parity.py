@@ -43,6 +43,8 @@ def system(name):
         elif name == "medium":        # several AMG levels
             r = synth.make_box(40, 40, 10, 0.5, 0.5, 0.25, seed=11, sigma=2.0, layered=True, kv_ratio=0.1,
                                kT_const=2.0, T_inj=500.0, q_inj=1e-6, dt=365 * 86400.0)
+        elif name == "ragged_mid":    # 7,659 cells: several levels above the fused size, a partial last warp
+            r = synth.make_box(37, 23, 9, 3.125, seed=23, sigma=1.5)
         elif name == "line":
             r = synth.make_box(24, 1, 1, 3.125, seed=4)
         elif name == "cptr200k":
@@ -54,7 +56,7 @@ def system(name):
 
 
 OPTS = {"parity": dict(max_levels=2), "ragged": dict(max_levels=3, n_coarse=8), "three_phase": dict(n_coarse=16),
-        "medium": dict(), "line": dict(max_levels=2, n_coarse=4), "cptr200k": dict()}
+        "medium": dict(), "ragged_mid": dict(), "line": dict(max_levels=2, n_coarse=4), "cptr200k": dict()}
 
 
 def gpu_solver(s, **opts):
@@ -115,6 +117,33 @@ def test_vcycle(name, smoother):
         x = torch.empty(s["n"], dtype=torch.float64, device="cuda")
         cp.cptr_apply_vcycle(g.ctx, which, dev(b), x)
         assert relerr(host(x), o.vcycle(which, b)) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["parity", "ragged_mid", "medium"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_vcycle_launch_shapes(name, precision):
+    """Every lane count of the V-cycle kernels (smoother + residual, restriction, prolongation),
+    forced on all levels above the fused size (rows of 7 to ~30 entries; the 7,659-cell box ends in
+    a partial warp on every level): all match the oracle's cycle (FP64 1e-10; mixed, against the
+    oracle's cycle on the same rounded values, 1e-5: the FP32 bound of the mixed tests below), and
+    each agrees with the one-lane cycle to the same bound."""
+    s = system(name)
+    prec = cp.PRECISION[precision]
+    o = oracle.Oracle.from_system(s, precision=prec, **OPTS[name])   # mixed: the oracle's rounded values
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    for which in (0, 1):
+        b = synth.normal(21 + which, s["n"])
+        xo = o.vcycle(which, b)
+        out = {}
+        for lanes in (1, 2, 4, 8, 16, 32):
+            g = gpu_solver(s, csr_lanes=lanes, precision=prec, **OPTS[name])
+            assert all(r[3] == lanes for r in cp.cptr_tuning(g.ctx) if r[2] in (0, 1, 2) and r[0] == which)
+            x = torch.empty(s["n"], dtype=torch.float64, device="cuda")
+            cp.cptr_apply_vcycle(g.ctx, which, dev(b), x)
+            out[lanes] = host(x)
+            assert relerr(out[lanes], xo) <= tol, (lanes, relerr(out[lanes], xo))
+        for lanes in (2, 4, 8, 16, 32):
+            assert relerr(out[lanes], out[1]) <= tol, (lanes, relerr(out[lanes], out[1]))
 
 
 @pytest.mark.parametrize("n_levels", [1, 2])
