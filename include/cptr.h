@@ -106,14 +106,14 @@ typedef struct {
     int32_t autotune;    /* 1: time the launch shapes of the V-cycle and SpMV kernels at set-up
                             and keep the fastest (see cptr_tuning); 0 (default): fixed shapes */
     int32_t ilu_sweep;   /* schedule of the ILU(0) triangular sweeps: 0 (default) level sets, or,
-                            with autotune, the fastest of level sets, paired levels, the chunked
+                            with autotune, the fastest of level sets, grouped levels, the chunked
                             wavefront and tiles where the pattern allows them; 1 level sets;
                             2 chunked wavefront (natural order, at most 4 dependencies per row,
                             levels no wider than 256 rows inside a chunk; same values as level
-                            sets); 3 paired levels where no paired row has more than 32
-                            dependencies, else level sets (a row of odd level substitutes its
-                            dependencies of the level before, so two levels run as one; values
-                            differ from level sets by rounding); 4 tiles where the pattern is that
+                            sets); 3 grouped levels (ilu_group levels per group, two by default:
+                            paired levels), else level sets (a row substitutes its dependencies
+                            inside its group, so the group's levels run as one; values differ from
+                            level sets by rounding); 4 tiles where the pattern is that
                             of a Cartesian box in natural order (lower dependencies at offsets 1,
                             nx and nx*ny only), else level sets: a block owns a tile of Ty x Tz
                             grid lines and walks the tile's own level sets, only dependencies on
@@ -129,12 +129,20 @@ typedef struct {
                             preconditioner cannot be combined with it, Sec. 3.3.1) */
     int32_t ilu_fill;    /* level of fill of the second stage's block ILU(k): 0 (default) or 1 (block row
                             i gains, for every block k < i of its row, the blocks j > k of row k;
-                            natural ILU order only; the sweeps then use level sets or paired levels) */
+                            natural ILU order only; the sweeps then use level sets or grouped levels) */
     int32_t csr_lanes;   /* lanes per row of the V-cycle kernels (smoother + residual, restriction,
                             prolongation) on every level when autotune is 0: 0 (default) chosen from
                             each operator's size and average row length, else 1, 2, 4, 8, 16 or 32
                             (other values: CPTR_EINVAL at cptr_create).  One lane adds a row's
                             products in order; more lanes add lane-strided partial sums. */
+    int32_t ilu_group;   /* levels per group of the grouped-level sweeps (ilu_sweep 3, or the autotuner's
+                            grouped-level candidate): 0 (default) two, or 2, 3 or 4.  A row
+                            of a group substitutes the equations of its dependencies inside the group
+                            (chains of up to group - 1 links), so the sweep's dependent steps are the
+                            level count divided by the group size; values differ from level sets by
+                            rounding.  When a row's expansion has more than 32 dependencies (or 32
+                            right-hand-side terms) the tables are not built and level sets are used
+                            (other values: CPTR_EINVAL at cptr_create). */
 } cptr_options;
 
 typedef struct {
@@ -272,9 +280,9 @@ cptr_status cptr_apply_ilu_static(cptr_ctx *ctx, const double *r, double *z);
  * residual, 1 restriction P^T, 2 prolongation P, 3 SELL SpMV of A', 4 ILU(0) sweeps, 5 ILU(0)
  * schedule, 6 tile shape of the tiled sweeps), lanes per row (0 = chosen from the average row
  * length; kernel 4: back-off between polls in ns; kernel 5: 0 level sets, 1 chunked wavefront,
- * 2 paired levels, 3 tiles; kernel 6: lines per tile along y, Ty, or 0 when no tiled tables are
- * built), threads per block (kernel 4: blocks of the persistent grid; kernel 6: lines per tile
- * along z, Tz)}; *n_rows receives the number of rows available.  With autotune set,
+ * 2 grouped levels, 3 tiles; kernel 6: lines per tile along y, Ty, or 0 when no tiled tables are
+ * built), threads per block (kernel 4: blocks of the persistent grid; kernel 5: levels per group
+ * of the grouped levels, else 0; kernel 6: lines per tile along z, Tz)}; *n_rows receives the number of rows available.  With autotune set,
  * cptr_setup times for every operator G in {1, 2, 4, 8, 16, 32} lanes x T in {128, 256, 512}
  * threads (the SELL kernels: T in {64, 128, 256, 512}), 5 launches each after a warm-up, and keeps
  * the fastest; results are cached in the context by operator size.  Shapes change only the order

@@ -467,7 +467,8 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
         o.decouple > CPTR_DECOUPLE_TI ||
         (o.decouple != CPTR_DECOUPLE_NONE && o.stage1 != CPTR_STAGE1_CPR && o.stage1 != CPTR_STAGE1_UAMG) ||
         o.ilu_fill < 0 || o.ilu_fill > 1 || (o.ilu_fill == 1 && o.ilu_order == CPTR_ILU_MULTICOLOR) ||
-        o.csr_lanes < 0 || o.csr_lanes > 32 || (o.csr_lanes & (o.csr_lanes - 1)))
+        o.csr_lanes < 0 || o.csr_lanes > 32 || (o.csr_lanes & (o.csr_lanes - 1)) || o.ilu_group < 0 || o.ilu_group == 1 ||
+        o.ilu_group > 4)
         return CPTR_EINVAL;
     cptr_ctx *ctx = new (std::nothrow) cptr_ctx();
     if (!ctx) return CPTR_ENOMEM;
@@ -804,7 +805,7 @@ cptr_status cptr_tuning(cptr_ctx *ctx, int32_t *rows, int32_t cap, int32_t *n_ro
         add(3, 0, 4, isw);
         Shape chosen;
         chosen.G = c->tl_use ? 3 : (c->cw_use ? 1 : (c->sp_use ? 2 : 0));
-        chosen.T = 0;
+        chosen.T = (int16_t)(c->sp_use ? c->sp_group : 0);
         add(3, 0, 5, chosen);
         Shape tile;
         tile.G = (int16_t)c->tl_best_ty;

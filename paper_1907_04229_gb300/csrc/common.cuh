@@ -373,6 +373,9 @@ struct Ctx {
     int32_t *sp_col_f = nullptr, *sp_col_b = nullptr, *sp_ccol_f = nullptr, *sp_ccol_b = nullptr;
     void *sp_val_f = nullptr, *sp_val_b = nullptr, *sp_cval_f = nullptr, *sp_cval_b = nullptr;   // FP64, or FP32 when mixed
     bool sp_ok = false, sp_use = false;                // built / chosen
+    int sp_group = 0;                                  // levels per group of the tables built
+    int32_t *sp_inv_f = nullptr, *sp_inv_b = nullptr;  // position of each row in either sweep
+    int32_t *sp_levr_f = nullptr, *sp_levr_b = nullptr;   // level of each row in either sweep
     // tiled sweeps: a block owns a tile of grid lines and walks its own levels (natural order on
     // a Cartesian box, detected from the pattern)
     TileTables tl_f, tl_b;

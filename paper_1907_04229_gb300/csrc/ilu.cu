@@ -325,7 +325,8 @@ constexpr int kSfRowsG = kSfThreads / kSfGroup;      // rows per block chunk
 // diverged from the others.  No group ever waits for another one (a group that is ready computes
 // in the same round), so rows of one warp may depend on each other.  State of a lane: its
 // component s of the row, and the dependency slots [sl0, sl0 + DG) in flight (DG = 4 for the
-// level-set tables, 8 for the paired-level ones, whose rows have up to 6 dependencies on a 3-D grid).
+// level-set tables, 8 for the paired-level ones, whose rows have up to 6 dependencies on a 3-D grid,
+// and 12 for groups of three levels, up to 10 there).
 template <int B, typename T, int DG>
 struct SweepLane {
     int64_t sl0, o1;
@@ -1709,58 +1710,149 @@ static void cw_free(Ctx *c) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Paired-level tables.  In each sweep a row i of odd level L (the sweep's own level numbering)
-// replaces every dependency k of level L - 1 by that row's own equation, so that it depends only
-// on rows of level <= L - 2 and is solved together with the rows of level L - 1: the chain of
-// dependent steps halves.  K1 denotes the dependencies of level L - 1, K0 the others.
-//   forward, y = L^{-1} r:   y_i = c_i - sum_j M_ij y_j,  c_i = r_i - sum_{k in K1} L_ik r_k,
-//                             M_ij = [j in K0] L_ij - sum_{k in K1} L_ik L_kj;
-//   backward, z = U^{-1} y:   z_i = D_i^{-1} (c_i - sum_j M_ij z_j),  c_i = y_i - sum_{k in K1} P_ik y_k,
-//                             P_ik = U_ik D_k^{-1},  M_ij = [j in K0] U_ij - sum_{k in K1} P_ik U_kj
-// (D_k^{-1} is the stored inverted pivot block).  Mathematically these are the same solves; the
-// sums are grouped differently, so values differ from the level-set sweeps by rounding only.
-// Rows of even level keep their own entries.  The entries of a paired row are ordered by
-// dependency position; each M_ij starts from the K0 block (or zero) and subtracts the products in
-// the row's pattern order; the c_i terms follow the row's pattern order.
-constexpr int kPairMax = 32;   // dependencies of a paired row; more and the tables are not built
+// Grouped-level tables.  The levels of a sweep (its own level numbering) are taken in groups of G
+// consecutive levels, [G0, G0 + G), solved as one step: a row of the group substitutes, along every
+// chain of dependencies inside its group, the equations of those rows, so that it depends only on
+// rows of earlier groups and on right-hand-side values.  G = 2 is the paired-level schedule (a row
+// of odd level replaces its dependencies of the level before); G = 3 cuts the chain of dependent
+// steps to a third.  With F_ik the factor of a dependency k of row i (forward L_ik; backward
+// U_ik D_k^{-1} for k inside the group, U_ik for k outside, D_k^{-1} the stored inverted pivot):
+//   forward, y = L^{-1} r:   y_i = c_i - sum_j M_ij y_j,         c_i = r_i - sum_l W_il r_l
+//   backward, z = U^{-1} y:   z_i = D_i^{-1} (c_i - sum_j M_ij z_j), c_i = y_i - sum_l W_il y_l
+// with, over the dependencies k of row i,
+//   M_ij = [j outside the group] F_ij - sum_{k inside} F_ik M_kj,
+//   W_il = [l inside the group] F_il - sum_{k inside} F_ik W_kl,
+// M_kj and W_kl being row k's own expansion (a row at the group's first level keeps its own
+// entries and has no W terms).  Mathematically these are the same solves; the sums are grouped
+// differently, so values differ from the level-set sweeps by rounding only.  The tables are built
+// in G passes, one per position in the group, each reading the expansions of the earlier positions.
+// A row's M entries are ordered by dependency position, its W terms by first discovery in a
+// depth-first walk of its in-group chains (the row's pattern order at every node); each entry
+// starts from the row's own block (or zero) and subtracts the products in the row's pattern order.
+constexpr int kPairMax = 32;   // entries of an expanded row; more and the tables are not built
+constexpr int kGroupMax = 4;   // levels per group
 
+// the dependencies of row u on the sweep's side of the diagonal: [*k0, *k1)
+__device__ __forceinline__ void side_range(int lower, const int32_t *__restrict__ rp, const int32_t *__restrict__ dg,
+                                           int32_t u, int32_t *k0, int32_t *k1) {
+    *k0 = lower ? rp[u] : dg[u] + 1;
+    *k1 = lower ? dg[u] : rp[u + 1];
+}
+
+// the distinct outside dependencies (as positions, J) and in-group sources (C, as source indices)
+// reached from row i through chains inside its group; false if either exceeds kPairMax
+__device__ bool group_sets(int32_t i, int32_t G0, int lower, const int32_t *__restrict__ inv,
+                           const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const int32_t *__restrict__ dg, const int32_t *__restrict__ levr,
+                           const int32_t *__restrict__ src_of_row, int32_t *J, int *nj, int32_t *C, int *nc) {
+    int32_t node[kGroupMax], e[kGroupMax], e1[kGroupMax];
+    int sp = 0;
+    node[0] = i;
+    side_range(lower, rp, dg, i, &e[0], &e1[0]);
+    *nj = *nc = 0;
+    bool ok = true;
+    while (sp >= 0) {
+        if (e[sp] == e1[sp]) {
+            --sp;
+            continue;
+        }
+        const int32_t k = ci[e[sp]++];
+        if (levr[k] < G0) {
+            const int32_t p = inv[k];
+            bool seen = false;
+            for (int q = 0; q < *nj; ++q) seen |= J[q] == p;
+            if (!seen) {
+                if (*nj == kPairMax) ok = false;
+                else J[(*nj)++] = p;
+            }
+        } else {
+            const int32_t l = src_of_row ? src_of_row[k] : k;
+            bool seen = false;
+            for (int q = 0; q < *nc; ++q) seen |= C[q] == l;
+            if (!seen) {
+                if (*nc == kPairMax) ok = false;
+                else C[(*nc)++] = l;
+            }
+            if (sp + 1 < kGroupMax) {   // a chain inside the group is at most G - 1 links long
+                ++sp;
+                node[sp] = k;
+                side_range(lower, rp, dg, k, &e[sp], &e1[sp]);
+            } else {
+                ok = false;
+            }
+        }
+    }
+    return ok;
+}
+
+// entry counts per position (main and W terms); *err set when a row exceeds kPairMax
+__global__ void k_group_count(int32_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ inv,
+                              const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              const int32_t *__restrict__ dg, const int32_t *__restrict__ levr, int lower, int G,
+                              const int32_t *__restrict__ src_of_row, int32_t *mcnt, int32_t *ccnt, int32_t *err) {
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int32_t i = pos[t];
+    const int32_t L = levr[i], G0 = L - L % G;
+    if (L == G0) {   // the group's first level: the row's own entries
+        int32_t k0, k1;
+        side_range(lower, rp, dg, i, &k0, &k1);
+        mcnt[t] = k1 - k0;
+        ccnt[t] = 0;
+        return;
+    }
+    int32_t J[kPairMax], C[kPairMax];
+    int nj, nc;
+    if (!group_sets(i, G0, lower, inv, rp, ci, dg, levr, src_of_row, J, &nj, C, &nc)) atomicExch(err, 1);
+    mcnt[t] = nj;
+    ccnt[t] = nc;
+}
+
+// the factor of dependency k of row i (entry e of the pattern): L_ik, U_ik, or U_ik D_k^{-1}
 template <int B>
-__device__ __forceinline__ void pair_factor(const double *__restrict__ LU, int32_t k, int32_t dk, int lower,
-                                            double *pk) {   // L_ik, or U_ik D_k^{-1}
+__device__ __forceinline__ void group_factor(const double *__restrict__ LU, int32_t e, int32_t dk, bool times_dinv,
+                                             double *f) {
     constexpr int BB = B * B;
-    if (lower) {
-        for (int e = 0; e < BB; ++e) pk[e] = LU[(int64_t)k * BB + e];
+    if (!times_dinv) {
+        for (int q = 0; q < BB; ++q) f[q] = LU[(int64_t)e * BB + q];
         return;
     }
     for (int r = 0; r < B; ++r)
         for (int q = 0; q < B; ++q) {
             double a = 0.0;
-            for (int u = 0; u < B; ++u) a = fma(LU[(int64_t)k * BB + r * B + u], LU[(int64_t)dk * BB + u * B + q], a);
-            pk[r * B + q] = a;
+            for (int u = 0; u < B; ++u) a = fma(LU[(int64_t)e * BB + r * B + u], LU[(int64_t)dk * BB + u * B + q], a);
+            f[r * B + q] = a;
+        }
+}
+// m -= f * blk (B x B)
+template <int B>
+__device__ __forceinline__ void sub_product(double *m, const double *f, const double *__restrict__ blk) {
+    for (int r = 0; r < B; ++r)
+        for (int q = 0; q < B; ++q) {
+            double a = m[r * B + q];
+            for (int u = 0; u < B; ++u) a = fma(-f[r * B + u], blk[u * B + q], a);
+            m[r * B + q] = a;
         }
 }
 
-// FILL = 0: entry counts per position (main and c terms), flagging rows with more than kPairMax
-// dependencies; FILL = 1: the entries (dependency position or source index, and the block)
-template <int B, int FILL>
-__global__ void k_pair_rows(int32_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ inv,
-                            const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                            const int32_t *__restrict__ dg, const int32_t *__restrict__ levr, int lower,
-                            const double *__restrict__ LU, const int32_t *__restrict__ src_of_row, int32_t *mcnt,
-                            int32_t *ccnt, const int32_t *__restrict__ moff, const int32_t *__restrict__ coff,
-                            int32_t *mdep, double *mblk, int32_t *cdep, double *cblk, int32_t *err) {
+// the entries of the rows at position p of their group (pass p; earlier positions are filled)
+template <int B>
+__global__ void k_group_fill(int32_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ inv,
+                             const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                             const int32_t *__restrict__ dg, const int32_t *__restrict__ levr, int lower, int G, int p,
+                             const double *__restrict__ LU, const int32_t *__restrict__ src_of_row,
+                             const int32_t *__restrict__ mcnt, const int32_t *__restrict__ ccnt,
+                             const int32_t *__restrict__ moff, const int32_t *__restrict__ coff, int32_t *mdep,
+                             double *mblk, int32_t *cdep, double *cblk) {
     constexpr int BB = B * B;
     const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const int32_t i = pos[t];
-    const int32_t L = levr[i];
-    const int32_t k0 = lower ? rp[i] : dg[i] + 1, k1 = lower ? dg[i] : rp[i + 1];
-    if (!(L & 1)) {
-        if (!FILL) {
-            mcnt[t] = k1 - k0;
-            ccnt[t] = 0;
-            return;
-        }
+    const int32_t L = levr[i], G0 = L - L % G;
+    if (L - G0 != p) return;
+    int32_t k0, k1;
+    side_range(lower, rp, dg, i, &k0, &k1);
+    if (p == 0) {
         int32_t o = moff[t];
         for (int32_t k = k0; k < k1; ++k, ++o) {
             mdep[o] = inv[ci[k]];
@@ -1768,71 +1860,59 @@ __global__ void k_pair_rows(int32_t n, const int32_t *__restrict__ pos, const in
         }
         return;
     }
-    int32_t J[kPairMax];
-    int nj = 0, nk1 = 0;
-    bool over = false;
-    for (int32_t k = k0; k < k1; ++k) {
-        const int32_t cc = ci[k];
-        const bool k1dep = levr[cc] == L - 1;
-        nk1 += k1dep;
-        const int32_t kk0 = k1dep ? (lower ? rp[cc] : dg[cc] + 1) : 0, kk1 = k1dep ? (lower ? dg[cc] : rp[cc + 1]) : 1;
-        for (int32_t kk = kk0; kk < kk1; ++kk) {
-            const int32_t p = inv[k1dep ? ci[kk] : cc];
-            bool seen = false;
-            for (int q = 0; q < nj; ++q) seen |= J[q] == p;
-            if (seen) continue;
-            if (nj == kPairMax) { over = true; continue; }
-            J[nj++] = p;
-        }
-    }
-    if (!FILL) {
-        mcnt[t] = nj;
-        ccnt[t] = nk1;
-        if (over) atomicExch(err, 1);
-        return;
-    }
+    int32_t J[kPairMax], C[kPairMax];
+    int nj, nc;
+    group_sets(i, G0, lower, inv, rp, ci, dg, levr, src_of_row, J, &nj, C, &nc);
     for (int a = 1; a < nj; ++a) {   // ascending dependency positions
         const int32_t v = J[a];
-        int b = a - 1;
-        while (b >= 0 && J[b] > v) { J[b + 1] = J[b]; --b; }
-        J[b + 1] = v;
+        int q = a - 1;
+        while (q >= 0 && J[q] > v) { J[q + 1] = J[q]; --q; }
+        J[q + 1] = v;
     }
-    const int32_t mo = moff[t];
+    const int32_t mo = moff[t], co = coff[t];
     for (int q = 0; q < nj; ++q) {
         const int32_t j = J[q];
         double m[BB];
         for (int e = 0; e < BB; ++e) m[e] = 0.0;
-        for (int32_t k = k0; k < k1; ++k)
-            if (levr[ci[k]] != L - 1 && inv[ci[k]] == j)
+        for (int32_t k = k0; k < k1; ++k)   // the row's own block of an outside dependency
+            if (levr[ci[k]] < G0 && inv[ci[k]] == j)
                 for (int e = 0; e < BB; ++e) m[e] = LU[(int64_t)k * BB + e];
-        for (int32_t k = k0; k < k1; ++k) {
+        for (int32_t k = k0; k < k1; ++k) {   // minus F_ik M_kj over the dependencies inside the group
             const int32_t cc = ci[k];
-            if (levr[cc] != L - 1) continue;
-            const int32_t kk0 = lower ? rp[cc] : dg[cc] + 1, kk1 = lower ? dg[cc] : rp[cc + 1];
-            for (int32_t kk = kk0; kk < kk1; ++kk) {
-                if (inv[ci[kk]] != j) continue;
-                double pk[BB];
-                pair_factor<B>(LU, k, dg[cc], lower, pk);
-                for (int r = 0; r < B; ++r)
-                    for (int qq = 0; qq < B; ++qq) {
-                        double a = m[r * B + qq];
-                        for (int u = 0; u < B; ++u) a = fma(-pk[r * B + u], LU[(int64_t)kk * BB + u * B + qq], a);
-                        m[r * B + qq] = a;
-                    }
+            if (levr[cc] < G0) continue;
+            const int32_t tk = inv[cc], o1 = moff[tk] + mcnt[tk];
+            for (int32_t o = moff[tk]; o < o1; ++o) {
+                if (mdep[o] != j) continue;
+                double f[BB];
+                group_factor<B>(LU, k, dg[cc], !lower, f);
+                sub_product<B>(m, f, mblk + (int64_t)o * BB);
             }
         }
         mdep[mo + q] = j;
         for (int e = 0; e < BB; ++e) mblk[(int64_t)(mo + q) * BB + e] = m[e];
     }
-    int32_t co = coff[t];
-    for (int32_t k = k0; k < k1; ++k) {
-        const int32_t cc = ci[k];
-        if (levr[cc] != L - 1) continue;
-        double pk[BB];
-        pair_factor<B>(LU, k, dg[cc], lower, pk);
-        cdep[co] = src_of_row ? src_of_row[cc] : cc;
-        for (int e = 0; e < BB; ++e) cblk[(int64_t)co * BB + e] = pk[e];
-        ++co;
+    for (int q = 0; q < nc; ++q) {
+        const int32_t l = C[q];
+        double w[BB];
+        for (int e = 0; e < BB; ++e) w[e] = 0.0;
+        for (int32_t k = k0; k < k1; ++k) {   // F_il for a direct dependency inside the group
+            const int32_t cc = ci[k];
+            if (levr[cc] < G0 || (src_of_row ? src_of_row[cc] : cc) != l) continue;
+            group_factor<B>(LU, k, dg[cc], !lower, w);
+        }
+        for (int32_t k = k0; k < k1; ++k) {   // minus F_ik W_kl
+            const int32_t cc = ci[k];
+            if (levr[cc] < G0) continue;
+            const int32_t tk = inv[cc], o1 = coff[tk] + ccnt[tk];
+            for (int32_t o = coff[tk]; o < o1; ++o) {
+                if (cdep[o] != l) continue;
+                double f[BB];
+                group_factor<B>(LU, k, dg[cc], !lower, f);
+                sub_product<B>(w, f, cblk + (int64_t)o * BB);
+            }
+        }
+        cdep[co + q] = l;
+        for (int e = 0; e < BB; ++e) cblk[(int64_t)(co + q) * BB + e] = w[e];
     }
 }
 
@@ -1881,8 +1961,18 @@ static cptr_status csr_to_sell(Ctx *c, const int32_t *cnt, const int32_t *csr_of
     return CPTR_OK;
 }
 
-// the paired-level tables of one sweep; *ok = false when a paired row has too many dependencies
-static cptr_status pair_table(Ctx *c, bool lower, const int32_t *pos, const int32_t *inv, const int32_t *levr,
+static void pair_free(Ctx *c) {
+    void **sp[] = {(void **)&c->sp_off_f, (void **)&c->sp_off_b, (void **)&c->sp_coff_f, (void **)&c->sp_coff_b,
+                   (void **)&c->sp_col_f, (void **)&c->sp_col_b, (void **)&c->sp_ccol_f, (void **)&c->sp_ccol_b,
+                   (void **)&c->sp_val_f, (void **)&c->sp_val_b, (void **)&c->sp_cval_f, (void **)&c->sp_cval_b};
+    for (void **p : sp) { dfree(*p); *p = nullptr; }
+    c->sp_ok = false;
+    c->sp_group = 0;
+}
+
+// the grouped-level tables of one sweep (G levels per group); *ok = false when an expanded row has
+// too many entries
+static cptr_status pair_table(Ctx *c, bool lower, int G, const int32_t *pos, const int32_t *inv, const int32_t *levr,
                               const int32_t *src_of_row, int64_t **off, int32_t **col, void **val, int64_t **coff,
                               int32_t **ccol, void **cval, bool *ok) {
     const int32_t n = c->n, BB = c->b * c->b;
@@ -1894,13 +1984,9 @@ static cptr_status pair_table(Ctx *c, bool lower, const int32_t *pos, const int3
     CPTR_TRY(dalloc_t(c, &coffc, (size_t)n + 1));
     CPTR_TRY(dalloc_t(c, &err, 1));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(err, 0, sizeof(int32_t), s));
-    auto rows = [&](auto kern, int32_t *mdep, double *mblk, int32_t *cdep, double *cblk) {
-        (kern<<<nblk(n, 128), 128, 0, s>>>(n, pos, inv, c->ilu_rp, c->ilu_ci, c->ilu_diag, levr, lower ? 1 : 0, c->LU,
-                                           src_of_row, mcnt, ccnt, moff, coffc, mdep, mblk, cdep, cblk, err),
-         note_launch());
-    };
-    if (c->b == 3) rows(k_pair_rows<3, 0>, nullptr, nullptr, nullptr, nullptr);
-    else rows(k_pair_rows<4, 0>, nullptr, nullptr, nullptr, nullptr);
+    (k_group_count<<<nblk(n, 128), 128, 0, s>>>(n, pos, inv, c->ilu_rp, c->ilu_ci, c->ilu_diag, levr, lower ? 1 : 0, G,
+                                                src_of_row, mcnt, ccnt, err),
+     note_launch());
     int32_t mtot = 0, ctot = 0, h_err = 0;
     CPTR_TRY(scan_exclusive(c, mcnt, moff, n, &mtot));
     CPTR_TRY(scan_exclusive(c, ccnt, coffc, n, &ctot));
@@ -1913,8 +1999,16 @@ static cptr_status pair_table(Ctx *c, bool lower, const int32_t *pos, const int3
         CPTR_TRY(dalloc_t(c, &cdep, (size_t)(ctot > 0 ? ctot : 1)));
         CPTR_TRY(dalloc_t(c, &mblk, (size_t)(mtot > 0 ? mtot : 1) * BB));
         CPTR_TRY(dalloc_t(c, &cblk, (size_t)(ctot > 0 ? ctot : 1) * BB));
-        if (c->b == 3) rows(k_pair_rows<3, 1>, mdep, mblk, cdep, cblk);
-        else rows(k_pair_rows<4, 1>, mdep, mblk, cdep, cblk);
+        for (int p = 0; p < G; ++p) {   // one pass per position in the group: earlier positions first
+            auto fill = [&](auto kern) {
+                (kern<<<nblk(n, 128), 128, 0, s>>>(n, pos, inv, c->ilu_rp, c->ilu_ci, c->ilu_diag, levr, lower ? 1 : 0,
+                                                   G, p, c->LU, src_of_row, mcnt, ccnt, moff, coffc, mdep, mblk, cdep,
+                                                   cblk),
+                 note_launch());
+            };
+            if (c->b == 3) fill(k_group_fill<3>);
+            else fill(k_group_fill<4>);
+        }
         CPTR_TRY(csr_to_sell(c, mcnt, moff, mdep, mblk, off, col, val));
         CPTR_TRY(csr_to_sell(c, ccnt, coffc, cdep, cblk, coff, ccol, cval));
         CPTR_CUDA_TRY(c, cudaStreamSynchronize(s));
@@ -1924,17 +2018,20 @@ static cptr_status pair_table(Ctx *c, bool lower, const int32_t *pos, const int3
     return CPTR_OK;
 }
 
-// both sweeps' paired-level tables (blocks in the sweeps' precision); c->sp_ok tells whether they were built
-static cptr_status pair_setup(Ctx *c, const int32_t *inv_f, const int32_t *inv_b, const int32_t *levr_f,
-                              const int32_t *levr_b) {
-    c->sp_ok = false;
+// both sweeps' grouped-level tables with G levels per group (blocks in the sweeps' precision);
+// c->sp_ok tells whether they were built, c->sp_group their group size.  Tables built before are
+// dropped first.
+static cptr_status pair_setup(Ctx *c, int G) {
+    pair_free(c);
     bool okf = false, okb = false;
-    CPTR_TRY(pair_table(c, true, c->lvl_f, inv_f, levr_f, c->ilu_rowmap, &c->sp_off_f, &c->sp_col_f, &c->sp_val_f,
-                        &c->sp_coff_f, &c->sp_ccol_f, &c->sp_cval_f, &okf));
+    CPTR_TRY(pair_table(c, true, G, c->lvl_f, c->sp_inv_f, c->sp_levr_f, c->ilu_rowmap, &c->sp_off_f, &c->sp_col_f,
+                        &c->sp_val_f, &c->sp_coff_f, &c->sp_ccol_f, &c->sp_cval_f, &okf));
     if (okf)
-        CPTR_TRY(pair_table(c, false, c->lvl_b, inv_b, levr_b, inv_f, &c->sp_off_b, &c->sp_col_b, &c->sp_val_b,
-                            &c->sp_coff_b, &c->sp_ccol_b, &c->sp_cval_b, &okb));
+        CPTR_TRY(pair_table(c, false, G, c->lvl_b, c->sp_inv_b, c->sp_levr_b, c->sp_inv_f, &c->sp_off_b, &c->sp_col_b,
+                            &c->sp_val_b, &c->sp_coff_b, &c->sp_ccol_b, &c->sp_cval_b, &okb));
     c->sp_ok = okf && okb;
+    c->sp_group = c->sp_ok ? G : 0;
+    if (!c->sp_ok) pair_free(c);
     return CPTR_OK;
 }
 
@@ -1950,6 +2047,14 @@ static uint64_t ilu_tune_key(const Ctx *c) {
 static int ilu_tuned_schedule(const Ctx *c) {
     auto it = c->tune_cache.find(ilu_tune_key(c) + 1);
     return it == c->tune_cache.end() ? -1 : it->second.G;
+}
+// levels per group of the grouped-level tables: the caller's, else the one a cached tuning chose
+// (kept at key + 1 as T), else two
+static int ilu_group_size(const Ctx *c) {
+    if (c->o.ilu_group >= 2) return c->o.ilu_group;
+    auto it = c->tune_cache.find(ilu_tune_key(c) + 1);
+    if (it != c->tune_cache.end() && it->second.G == 2 && it->second.T >= 2) return it->second.T;
+    return 2;
 }
 
 // Block ILU(1) pattern (Sec. 4; the CPR-AMG-ILU(1) comparator): block row i keeps its own blocks and
@@ -2191,14 +2296,14 @@ cptr_status ilu_setup(Ctx *c) {
         CPTR_CUDA_TRY(c, cudaMemcpyAsync(c->LU, c->A, sizeof(double) * (size_t)c->nnzb * BB, cudaMemcpyDeviceToDevice, st));
     }
     // level sets of both sweeps (positions -> rows of the factorised matrix)
-    int32_t *inv_f = nullptr, *inv_b = nullptr;
+    // (positions and levels stay with the context: the autotuner rebuilds grouped-level tables)
     CPTR_TRY(dalloc_t(c, &c->lvl_f, (size_t)n));
     CPTR_TRY(dalloc_t(c, &c->lvl_b, (size_t)n));
-    CPTR_TRY(dalloc_t(c, &inv_f, (size_t)n));
-    CPTR_TRY(dalloc_t(c, &inv_b, (size_t)n));
-    int32_t *levr_f = nullptr, *levr_b = nullptr;
-    CPTR_TRY(dalloc_t(c, &levr_f, (size_t)n));
-    CPTR_TRY(dalloc_t(c, &levr_b, (size_t)n));
+    CPTR_TRY(dalloc_t(c, &c->sp_inv_f, (size_t)n));
+    CPTR_TRY(dalloc_t(c, &c->sp_inv_b, (size_t)n));
+    CPTR_TRY(dalloc_t(c, &c->sp_levr_f, (size_t)n));
+    CPTR_TRY(dalloc_t(c, &c->sp_levr_b, (size_t)n));
+    int32_t *inv_f = c->sp_inv_f, *inv_b = c->sp_inv_b, *levr_f = c->sp_levr_f, *levr_b = c->sp_levr_b;
     IluSym &ys = c->isym;
     if (ys.lv) {   // the level sets of the same pattern, from the last set-up
         int32_t *dst[6] = {c->lvl_f, inv_f, levr_f, c->lvl_b, inv_b, levr_b};
@@ -2330,11 +2435,7 @@ cptr_status ilu_setup(Ctx *c) {
     // tuning), the level-set tables of L and U are not needed
     const int sched = ilu_tuned_schedule(c);
     if (c->o.ilu_sweep == 3 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 2))) {
-        const cptr_status ps = pair_setup(c, inv_f, inv_b, levr_f, levr_b);
-        if (ps != CPTR_OK) {
-            dfree(inv_f); dfree(inv_b); dfree(levr_f); dfree(levr_b);
-            return ps;
-        }
+        CPTR_TRY(pair_setup(c, ilu_group_size(c)));
         c->sp_use = c->sp_ok && (c->o.ilu_sweep == 3 || sched == 2);
     }
     int32_t *kidx_f = nullptr, *kidx_b = nullptr, *kidx_d = nullptr;
@@ -2363,7 +2464,6 @@ cptr_status ilu_setup(Ctx *c) {
     CPTR_TRY(dalloc(c, &c->sf_z, (size_t)n * c->b * (lo ? 4 : 8) + 64));
     CPTR_CUDA_TRY(c, cudaGetLastError());
     dfree(kidx_f); dfree(kidx_b); dfree(kidx_d);
-    dfree(inv_f); dfree(inv_b); dfree(levr_f); dfree(levr_b);
     // the chunked and tiled schedules read the caller's pattern: natural order without fill only
     if (!mc && !fill && !bj && (c->o.ilu_sweep == 2 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 1))))
         CPTR_TRY(cw_setup(c));
@@ -2407,12 +2507,11 @@ void ilu_free(Ctx *c) {
     void **sf[] = {(void **)&c->sf_pos_f, (void **)&c->sf_pos_b, (void **)&c->sf_bmap, (void **)&c->sf_off_f,
                    (void **)&c->sf_off_b, (void **)&c->sf_col_f, (void **)&c->sf_col_b, (void **)&c->sf_val_f,
                    (void **)&c->sf_val_b, (void **)&c->sf_dinv, (void **)&c->sf_ticket, (void **)&c->sf_y,
-                   (void **)&c->sf_z, (void **)&c->sp_off_f, (void **)&c->sp_off_b, (void **)&c->sp_coff_f,
-                   (void **)&c->sp_coff_b, (void **)&c->sp_col_f, (void **)&c->sp_col_b, (void **)&c->sp_ccol_f,
-                   (void **)&c->sp_ccol_b, (void **)&c->sp_val_f, (void **)&c->sp_val_b, (void **)&c->sp_cval_f,
-                   (void **)&c->sp_cval_b};
+                   (void **)&c->sf_z, (void **)&c->sp_inv_f, (void **)&c->sp_inv_b, (void **)&c->sp_levr_f,
+                   (void **)&c->sp_levr_b};
     for (void **p : sf) { dfree(*p); *p = nullptr; }
-    c->sp_ok = c->sp_use = false;
+    pair_free(c);
+    c->sp_use = false;
 }
 
 // launch one chunked sweep with its tables (NS = stage slots chosen at set-up)
@@ -2470,7 +2569,8 @@ static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT 
                  (const T *)c->sp_cval_f),
              note_launch());
         };
-        if (pr) fwd(k_ilu_fwd_g<B, T, RT, 8>);
+        if (pr && c->sp_group >= 3) fwd(k_ilu_fwd_g<B, T, RT, 12>);
+        else if (pr) fwd(k_ilu_fwd_g<B, T, RT, 8>);
         else fwd(k_ilu_fwd_g<B, T, RT, kDepGroup>);
         prof_end(c, pf);
         pf = prof_begin(c, PF_ILU_BWD);
@@ -2482,7 +2582,8 @@ static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT 
                  pr ? c->sp_coff_b : nullptr, c->sp_ccol_b, (const T *)c->sp_cval_b),
              note_launch());
         };
-        if (pr) bwd(k_ilu_bwd_g<B, T, XT, 8>);
+        if (pr && c->sp_group >= 3) bwd(k_ilu_bwd_g<B, T, XT, 12>);
+        else if (pr) bwd(k_ilu_bwd_g<B, T, XT, 8>);
         else bwd(k_ilu_bwd_g<B, T, XT, kDepGroup>);
         prof_end(c, pf);
         return;
@@ -2598,13 +2699,16 @@ cptr_status ilu_autotune(Ctx *c) {
     int best_g = c->sf_grid, best_s = c->sf_sleep;
     float best_ms = search(&best_g, &best_s);
     int sched = c->sp_use ? 2 : 0;
+    int group = c->sp_use ? c->sp_group : 0;
     // the other schedules, each at its own best grid and back-off; the fastest is kept
+    // (grouped levels are timed with the group size built at set-up: groups of three were measured
+    // to cost more set-up time than their sweeps save, so they are used only when asked for)
     if (auto_sched && c->sp_ok) {
         c->sp_use = true;
         int g = best_g, sl = best_s;
         const float ms = search(&g, &sl);
         c->sp_use = false;
-        if (ms < best_ms) { best_ms = ms; best_g = g; best_s = sl; sched = 2; }
+        if (ms < best_ms) { best_ms = ms; best_g = g; best_s = sl; sched = 2; group = c->sp_group; }
     }
     if (auto_sched && c->cw_ok) {   // one block per chunk: only the back-off matters
         c->cw_use = true;
@@ -2664,7 +2768,7 @@ cptr_status ilu_autotune(Ctx *c) {
     sh.T = (int16_t)best_g;
     sh.G = (int16_t)best_s;
     sc.G = (int16_t)sched;
-    sc.T = 0;
+    sc.T = (int16_t)(sched == 2 ? group : 0);
     c->tune_cache[key] = sh;
     c->tune_cache[key + 1] = sc;
     if (tile_ty > 0) {

@@ -750,6 +750,116 @@ def test_paired_levels_equal_oracle_ilu_on_a_grid():
     assert np.linalg.norm(zo - z.reshape(-1)) <= 1e-10 * np.linalg.norm(zo)
 
 
+# Grouped levels, the generalisation of the pairs above: the levels of a sweep in groups of g, a
+# row substituting the equations of its dependencies inside its group (recursively, through chains
+# of up to g - 1 links), so that it depends only on rows of earlier groups.  Written from the
+# algebra: with F_ik = L_ik forward, and U_ik D_k^-1 backward for k inside the group (U_ik outside),
+#   M_ij = [j outside] F_ij - sum_{k inside} F_ik M_kj,   W_il = [l inside] F_il - sum_{k inside} F_ik W_kl,
+#   y_i = r_i - sum_l W_il r_l - sum_j M_ij y_j,   z_i = D_i^-1 (y_i - sum_l W_il y_l - sum_j M_ij z_j).
+def _grouped_solves(n, b, pattern, F, r, g, drop_second_order=False):
+    lower = [[k for k in sorted(pattern[i]) if k < i] for i in range(n)]
+    upper = [[k for k in sorted(pattern[i]) if k > i] for i in range(n)]
+    Dinv = {i: np.linalg.inv(F[(i, i)]) for i in range(n)}
+
+    def expansions(deps, lev, backward):
+        E = {}
+        for L in range(lev.max() + 1):
+            G0 = L - L % g
+            for i in np.flatnonzero(lev == L):
+                M, W = {}, {}
+                for k in deps[i]:
+                    if lev[k] < G0:
+                        M[k] = M.get(k, 0) + F[(i, k)]
+                        continue
+                    f = F[(i, k)] @ Dinv[k] if backward else F[(i, k)]
+                    W[k] = W.get(k, 0) + f
+                    Mk, Wk = E[k]
+                    for j, blk in Mk.items():
+                        M[j] = M.get(j, 0) - f @ blk
+                    if not drop_second_order:
+                        for l, blk in Wk.items():
+                            W[l] = W.get(l, 0) - f @ blk
+                assert all(lev[j] < G0 for j in M) and all(G0 <= lev[l] < L for l in W)
+                E[i] = (M, W)
+        return E
+
+    lf, lb = _levels(n, lower), _levels(n, upper)
+    Ef, Eb = expansions(lower, lf, False), expansions(upper, lb, True)
+    y = np.full((n, b), np.nan)
+    for G0 in range(0, lf.max() + 1, g):   # a group at a time; only earlier groups' y are read
+        grp = np.flatnonzero((lf >= G0) & (lf < G0 + g))
+        new = {i: r[i] - sum((w @ r[l] for l, w in Ef[i][1].items()), np.zeros(b))
+               - sum((m @ y[j] for j, m in Ef[i][0].items()), np.zeros(b)) for i in grp}
+        for i, v in new.items():
+            y[i] = v
+    z = np.full((n, b), np.nan)
+    for G0 in range(0, lb.max() + 1, g):
+        grp = np.flatnonzero((lb >= G0) & (lb < G0 + g))
+        new = {i: Dinv[i] @ (y[i] - sum((w @ y[l] for l, w in Eb[i][1].items()), np.zeros(b))
+                             - sum((m @ z[j] for j, m in Eb[i][0].items()), np.zeros(b))) for i in grp}
+        for i, v in new.items():
+            z[i] = v
+    return y, z
+
+
+def _random_factors(n, b, seed, reach=12):
+    rng = np.random.default_rng(seed)
+    pattern = [{i} for i in range(n)]
+    for i in range(n):
+        for j in rng.choice(n, size=3, replace=False):
+            if j != i and abs(int(j) - i) <= reach:
+                pattern[i].add(int(j))
+                pattern[int(j)].add(i)
+    blocks = {}
+    for i in range(n):
+        for j in pattern[i]:
+            blocks[(i, j)] = rng.normal(size=(b, b)) * (0.3 if j != i else 1.0)
+        blocks[(i, i)] += 4.0 * b * np.eye(b)
+    return pattern, _block_ilu_factors(n, b, pattern, blocks), rng.normal(size=(n, b))
+
+
+@pytest.mark.parametrize("g", [1, 2, 3, 4])
+def test_grouped_levels_equal_plain_substitution_random_pattern(g):
+    n, b = 60, 3
+    pattern, F, r = _random_factors(n, b, 7)
+    y0, z0 = _plain_solves(n, b, pattern, F, r)
+    y1, z1 = _grouped_solves(n, b, pattern, F, r, g)
+    assert np.linalg.norm(y1 - y0) <= 1e-12 * np.linalg.norm(y0)
+    assert np.linalg.norm(z1 - z0) <= 1e-12 * np.linalg.norm(z0)
+    if g == 2:   # two levels per group are the paired levels
+        y2, z2 = _paired_solves(n, b, pattern, F, r)
+        assert np.linalg.norm(y1 - y2) <= 1e-13 * np.linalg.norm(y2)
+        assert np.linalg.norm(z1 - z2) <= 1e-13 * np.linalg.norm(z2)
+
+
+def test_grouped_levels_need_the_second_order_terms():
+    """A planted mistake: dropping the W terms carried through a chain of two links (a row's
+    right-hand-side terms of rows two levels back) breaks groups of three, not groups of two."""
+    n, b = 60, 3
+    pattern, F, r = _random_factors(n, b, 7)
+    y0, z0 = _plain_solves(n, b, pattern, F, r)
+    y2, _ = _grouped_solves(n, b, pattern, F, r, 2, drop_second_order=True)
+    assert np.linalg.norm(y2 - y0) <= 1e-12 * np.linalg.norm(y0)
+    y3, z3 = _grouped_solves(n, b, pattern, F, r, 3, drop_second_order=True)
+    assert np.linalg.norm(y3 - y0) > 1e-6 * np.linalg.norm(y0)   # a million times the pass bound
+    assert np.linalg.norm(z3 - z0) > 1e-6 * np.linalg.norm(z0)
+
+
+@pytest.mark.parametrize("g", [3, 4])
+def test_grouped_levels_equal_oracle_ilu_on_a_grid(g):
+    s = tiny(4, 3, 2).system()
+    o = oracle.Oracle.from_system(s, max_levels=1, dense_max=4096)
+    n, b = s["n"], s["b"]
+    rp, ci, W = s["row_ptr"], s["col_idx"], s["weights"]
+    pattern = [set(int(c) for c in ci[rp[i]:rp[i + 1]]) for i in range(n)]
+    blocks = {(i, int(ci[k])): W[i] @ s["vals"][k] for i in range(n) for k in range(rp[i], rp[i + 1])}
+    F = _block_ilu_factors(n, b, pattern, blocks)
+    r = synth.normal(9, n * b).reshape(n, b)
+    _, z = _grouped_solves(n, b, pattern, F, r, g)
+    zo = o.ilu_apply(r.reshape(-1))
+    assert np.linalg.norm(zo - z.reshape(-1)) <= 1e-10 * np.linalg.norm(zo)
+
+
 # ------------------------------------------------------------------------------------------------
 # unknown-based AMG for A_00 (Sec. 3.4) and S~_diag (Sec. 3.3.1)
 def _csr_from_dense(M):
