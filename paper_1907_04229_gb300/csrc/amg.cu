@@ -635,10 +635,12 @@ static cptr_status spgemm(Ctx *c, const Csr &A, const Csr &B, int32_t ncb, Csr &
     CPTR_TRY(dalloc_t(c, &cnt, (size_t)A.n + 1));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
     launch_spgemm<false>(c, A, B, nullptr, cnt, nullptr);
-    int32_t total = 0;
-    CPTR_TRY(scan_exclusive(c, cnt, C.rp, A.n, &total));
-    int32_t bad = 0;
-    CPTR_TRY(copy_to_host(c, &bad, c->flag, sizeof(int32_t)));
+    CPTR_TRY(scan_exclusive(c, cnt, C.rp, A.n, nullptr));
+    int32_t rd[2] = {0, 0};   // the entry count and the overflow flag, one synchronisation
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(&rd[0], C.rp + A.n, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(&rd[1], c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int32_t total = rd[0], bad = rd[1];
     if (bad) {
         dfree(cnt);
         return c->fail(CPTR_EINVAL, "AMG: a row of the Galerkin product merges more than 256 rows");
@@ -719,21 +721,26 @@ static cptr_status coarsen(Ctx *c, Level &L, int lev, int32_t *nc_out, int32_t *
         if (h_und == 0) break;
         if ((rounds += 3) > 100000) return c->fail(CPTR_EINVAL, "AMG: PMIS did not terminate");
     }
-    // coarse numbering
+    // coarse numbering and the interpolation's row counts (both totals read with one synchronisation;
+    // the counts are not needed when no coarse level follows)
     CPTR_TRY(dalloc_t(c, &cidx, (size_t)n + 1));
     (k_is_c<<<nblk(n, 256), 256, 0, s>>>(n, state, cnt), note_launch());
-    int32_t nc = 0;
-    CPTR_TRY(scan_exclusive(c, cnt, cidx, n, &nc));
-    *nc_out = nc;
+    CPTR_TRY(scan_exclusive(c, cnt, cidx, n, nullptr));
     L.cf = state;
     state = nullptr;
+    L.P.n = n;
+    CPTR_TRY(dalloc_t(c, &L.P.rp, (size_t)n + 1));
+    (k_interp_count<<<nblk(n, 256), 256, 0, s>>>(n, Srp, Sci, L.cf, cnt), note_launch());
+    CPTR_TRY(scan_exclusive(c, cnt, L.P.rp, n, nullptr));
+    int32_t tot[2] = {0, 0};
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(&tot[0], cidx + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(&tot[1], L.P.rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(s));
+    const int32_t nc = tot[0];
+    *nc_out = nc;
     if (nc > 0 && nc < n) {
         // interpolation
-        L.P.n = n;
-        CPTR_TRY(dalloc_t(c, &L.P.rp, (size_t)n + 1));
-        (k_interp_count<<<nblk(n, 256), 256, 0, s>>>(n, Srp, Sci, L.cf, cnt), note_launch());
-        int32_t nnzP = 0;
-        CPTR_TRY(scan_exclusive(c, cnt, L.P.rp, n, &nnzP));
+        const int32_t nnzP = tot[1];
         L.P.nnz = nnzP;
         CPTR_TRY(dalloc_t(c, &L.P.ci, (size_t)nnzP));
         CPTR_TRY(dalloc_t(c, &L.P.v, (size_t)nnzP));
