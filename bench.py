@@ -302,12 +302,17 @@ def roofline_line(kernel, alg, ms_tot, cnt, steps, peak, peak_kind, traffic=None
 
 def family_kernels(cp, S, b, mixed):
     """Kernel names of the profiled families of solver S (from its ILU schedule)."""
-    sched = [t for t in cp.cptr_tuning(S.ctx) if t[2] == 5][0][3]
+    tun = cp.cptr_tuning(S.ctx)
+    sched, group = [t for t in tun if t[2] == 5][0][3:5]
+    lanes = [t for t in tun if t[2] == 7][0][3]
     t = "float" if mixed else "double"
-    sweep = {0: "level sets", 1: "chunked wavefront", 2: "paired levels", 3: "tiled"}[sched]
+    sweep = {0: "level sets", 1: "chunked wavefront", 2: "paired levels" if group == 2 else f"groups of {group} levels",
+             3: "tiled"}[sched]
     four = sched == 2 or (sched == 0 and not mixed)
-    how = sweep + (", a row over 4 lanes" if four else "")
-    if sched == 1:
+    how = sweep + (f", a row over {lanes if sched == 2 else 4} lanes" if four else "")
+    if sched == 2 and lanes == 8:
+        fwd, bwd = f"k_ilu_fwd_h<{b},{t},...>", f"k_ilu_bwd_h<{b},{t},...>"
+    elif sched == 1:
         fwd, bwd = f"k_ilu_cw<{b},{t},...,FWD>", f"k_ilu_cw<{b},{t},...,BWD>"
     elif sched == 3:
         fwd, bwd = f"k_ilu_tile<{b},{t},...,FWD>", f"k_ilu_tile<{b},{t},...,BWD>"

@@ -143,6 +143,12 @@ typedef struct {
                             rounding.  When a row's expansion has more than 32 dependencies (or 32
                             right-hand-side terms) the tables are not built and level sets are used
                             (other values: CPTR_EINVAL at cptr_create). */
+    int32_t ilu_lanes;   /* lanes per row of the grouped-level sweeps: 0 (default) four, or with
+                            autotune the faster of four and eight; 4 or 8 fixes it.  Four lanes: lane
+                            q computes component q over all of the row's dependency slots; eight: two
+                            halves of four each take every other slot, and their partial sums are
+                            added at the end (half 0's first), which halves each lane's chain of FP64
+                            instructions; values differ by rounding (other values: CPTR_EINVAL). */
 } cptr_options;
 
 typedef struct {
@@ -278,11 +284,13 @@ cptr_status cptr_apply_ilu_static(cptr_ctx *ctx, const double *r, double *z);
 /* Launch shapes in use (an engineering addition; the paper has none).  Writes up to cap rows of 5
  * int32 into rows (host): {hierarchy (0 A_pp, 1 S~_T, 2 A', 3 ILU(0)), level, kernel (0 smoother +
  * residual, 1 restriction P^T, 2 prolongation P, 3 SELL SpMV of A', 4 ILU(0) sweeps, 5 ILU(0)
- * schedule, 6 tile shape of the tiled sweeps), lanes per row (0 = chosen from the average row
- * length; kernel 4: back-off between polls in ns; kernel 5: 0 level sets, 1 chunked wavefront,
- * 2 grouped levels, 3 tiles; kernel 6: lines per tile along y, Ty, or 0 when no tiled tables are
- * built), threads per block (kernel 4: blocks of the persistent grid; kernel 5: levels per group
- * of the grouped levels, else 0; kernel 6: lines per tile along z, Tz)}; *n_rows receives the number of rows available.  With autotune set,
+ * schedule, 6 tile shape of the tiled sweeps, 7 lanes per row of the grouped-level sweeps), lanes
+ * per row (0 = chosen from the average row length; kernel 4: back-off between polls in ns;
+ * kernel 5: 0 level sets, 1 chunked wavefront, 2 grouped levels, 3 tiles; kernel 6: lines per tile
+ * along y, Ty, or 0 when no tiled tables are built; kernel 7: 4 or 8, or 0 when the grouped levels
+ * are not in use), threads per block (kernel 4: blocks of the persistent grid; kernel 5: levels
+ * per group of the grouped levels, else 0; kernel 6: lines per tile along z, Tz)}; *n_rows
+ * receives the number of rows available.  With autotune set,
  * cptr_setup times for every operator G in {1, 2, 4, 8, 16, 32} lanes x T in {128, 256, 512}
  * threads (the SELL kernels: T in {64, 128, 256, 512}), 5 launches each after a warm-up, and keeps
  * the fastest; results are cached in the context by operator size.  Shapes change only the order

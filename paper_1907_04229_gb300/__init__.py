@@ -40,7 +40,7 @@ class cptr_options(ctypes.Structure):
                 ("ilu_order", ctypes.c_int32), ("autotune", ctypes.c_int32), ("ilu_sweep", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32),
                 ("decouple", ctypes.c_int32), ("ilu_fill", ctypes.c_int32), ("csr_lanes", ctypes.c_int32),
-                ("ilu_group", ctypes.c_int32)]
+                ("ilu_group", ctypes.c_int32), ("ilu_lanes", ctypes.c_int32)]
 
 
 class cptr_stats(ctypes.Structure):

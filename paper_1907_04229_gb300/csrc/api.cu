@@ -468,7 +468,7 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
         (o.decouple != CPTR_DECOUPLE_NONE && o.stage1 != CPTR_STAGE1_CPR && o.stage1 != CPTR_STAGE1_UAMG) ||
         o.ilu_fill < 0 || o.ilu_fill > 1 || (o.ilu_fill == 1 && o.ilu_order == CPTR_ILU_MULTICOLOR) ||
         o.csr_lanes < 0 || o.csr_lanes > 32 || (o.csr_lanes & (o.csr_lanes - 1)) || o.ilu_group < 0 || o.ilu_group == 1 ||
-        o.ilu_group > 4)
+        o.ilu_group > 4 || (o.ilu_lanes != 0 && o.ilu_lanes != 4 && o.ilu_lanes != 8))
         return CPTR_EINVAL;
     cptr_ctx *ctx = new (std::nothrow) cptr_ctx();
     if (!ctx) return CPTR_ENOMEM;
@@ -811,6 +811,10 @@ cptr_status cptr_tuning(cptr_ctx *ctx, int32_t *rows, int32_t cap, int32_t *n_ro
         tile.G = (int16_t)c->tl_best_ty;
         tile.T = (int16_t)c->tl_best_tz;
         add(3, 0, 6, tile);
+        Shape lanes;
+        lanes.G = (int16_t)(c->sp_use ? 4 * c->sf_half : 0);
+        lanes.T = 0;
+        add(3, 0, 7, lanes);
         *n_rows = (int32_t)(out.size() / 5);
         for (int32_t i = 0; i < std::min<int32_t>(cap, *n_rows) * 5; ++i) rows[i] = out[i];
         return CPTR_OK;

@@ -340,18 +340,18 @@ struct SweepLane {
 };
 
 // columns, row q4 of the blocks, and the first loads of component q4 of the values of slots
-// [sl0, sl0 + DG)
-template <int B, typename T, int DG>
+// sl0, sl0 + H, ..., sl0 + (DG - 1) H (H = 2: a row's slots split between two lane halves)
+template <int B, typename T, int DG, int H = 1>
 __device__ __forceinline__ void sweep_stage(SweepLane<B, T, DG> &L, int q4, int lane, const int32_t *__restrict__ col,
                                             const T *__restrict__ val, const T *vec) {
 #pragma unroll
     for (int g = 0; g < DG; ++g)
-        L.c[g] = (L.sl0 + g < L.o1) ? chk_dep(__ldg(col + (L.sl0 + g) * 32 + lane), L.nrows) : -1;
+        L.c[g] = (L.sl0 + g * H < L.o1) ? chk_dep(__ldg(col + (L.sl0 + g * H) * 32 + lane), L.nrows) : -1;
 #pragma unroll
     for (int g = 0; g < DG; ++g)
         if (L.c[g] >= 0) {
 #pragma unroll
-            for (int q = 0; q < B; ++q) L.a[g][q] = __ldg(val + ((L.sl0 + g) * B * B + q4 * B + q) * 32 + lane);
+            for (int q = 0; q < B; ++q) L.a[g][q] = __ldg(val + ((L.sl0 + g * H) * B * B + q4 * B + q) * 32 + lane);
             L.pv[g] = load_relaxed(vec + (int64_t)L.c[g] * B + q4);
         }
 }
@@ -359,7 +359,7 @@ __device__ __forceinline__ void sweep_stage(SweepLane<B, T, DG> &L, int q4, int 
 // One round of a group that is not finished: returns true once all its slots are subtracted.
 // *pend tells whether the group still waits on a value after this round.  The lanes of a row
 // poll one component each; once all are present, each lane takes the others' by shuffles.
-template <int B, typename T, int DG>
+template <int B, typename T, int DG, int H = 1>
 __device__ __forceinline__ bool sweep_round(SweepLane<B, T, DG> &L, int q4, int lane, unsigned gmask, int g0,
                                             const int32_t *__restrict__ col, const T *__restrict__ val,
                                             const T *vec, KState *ks, bool *pend) {
@@ -395,9 +395,9 @@ __device__ __forceinline__ bool sweep_round(SweepLane<B, T, DG> &L, int q4, int 
         if (L.c[g] >= 0)
 #pragma unroll
             for (int q = 0; q < B; ++q) L.s = fma(-L.a[g][q], __shfl_sync(gmask, L.pv[g], g0 + q), L.s);
-    L.sl0 += DG;
+    L.sl0 += DG * H;
     if (L.sl0 < L.o1) {
-        sweep_stage<B, T, DG>(L, q4, lane, col, val, vec);
+        sweep_stage<B, T, DG, H>(L, q4, lane, col, val, vec);
         *pend = true;
         return false;
     }
@@ -405,14 +405,15 @@ __device__ __forceinline__ bool sweep_round(SweepLane<B, T, DG> &L, int q4, int 
 }
 
 // the part of a paired row's equation that needs no other row's result: s -= sum over the slots
-// [coff[ch], coff[ch+1]) of row q4 of block(slot) * src(source(slot)) (none for other rows)
-template <int B, typename T, typename ST>
+// [coff[ch], coff[ch+1]) of row q4 of block(slot) * src(source(slot)) (none for other rows); with
+// H = 2 lane half h takes the slots coff[ch] + h, + h + 2, ...
+template <int B, typename T, typename ST, int H = 1>
 __device__ __forceinline__ T pair_terms(T s, int q4, int32_t ch, int lane, const int64_t *__restrict__ coff,
                                         const int32_t *__restrict__ ccol, const T *__restrict__ cval,
-                                        const ST *__restrict__ src, int32_t n) {
+                                        const ST *__restrict__ src, int32_t n, int h = 0) {
     if (!coff) return s;
     const int64_t c1 = __ldg(coff + ch + 1);
-    for (int64_t sl = __ldg(coff + ch); sl < c1; ++sl) {
+    for (int64_t sl = __ldg(coff + ch) + h; sl < c1; sl += H) {
         int32_t k = __ldg(ccol + sl * 32 + lane);
         if (k < 0) continue;
         k = (int32_t)chk(k, n, CHK_ILU_PAIR);
@@ -527,6 +528,134 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_g(int32_t n, unsigned *t
                 out[(int64_t)row * B + q4] = (double)a + add;
                 done = true;
             }
+            if (__any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
+        }
+    }
+}
+
+// The same sweeps with a row over eight lanes, two halves of four: half h subtracts the row's
+// dependency slots h, h + 2, ... (and its share of the right-hand-side terms), lane q of a half
+// component q, so that each lane's chain of FP64 instructions is about half as long; when both
+// halves have subtracted their slots the halves' partial sums are added (half 0's first) and half 0
+// finishes the row.  The sums are grouped differently from the four-lane kernels above, so values
+// differ from them by rounding only.  Rows of a warp advance in the same lockstep rounds.
+constexpr int kSfGroup2 = 2 * kSfGroup;              // lanes per row
+constexpr int kSfRowsG2 = kSfThreads / kSfGroup2;    // rows per block chunk
+
+template <int B, typename T, typename RT, int DG>
+__global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_h(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
+                                                         const int64_t *__restrict__ off, const int32_t *__restrict__ col,
+                                                         const T *__restrict__ val, const RT *__restrict__ r, T *y,
+                                                         KState *ks, const double *never, int sleep_ns,
+                                                         const int64_t *__restrict__ coff,
+                                                         const int32_t *__restrict__ ccol, const T *__restrict__ cval) {
+    __shared__ unsigned blk;
+    const unsigned nchunks = (unsigned)((n + kSfRowsG2 - 1) / kSfRowsG2);
+    const int q4 = threadIdx.x & (kSfGroup - 1), h = (threadIdx.x / kSfGroup) & 1;
+    const int lw = threadIdx.x & 31, gr = lw & ~(kSfGroup2 - 1), g0 = gr + kSfGroup * h;
+    const unsigned gmask = ((1u << B) - 1u) << g0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) blk = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const unsigned b = blk;
+        if (b >= nchunks) return;
+        const int32_t t = (int32_t)(b * kSfRowsG2 + threadIdx.x / kSfGroup2);
+        const bool idle = t >= n || q4 >= B;   // lanes that compute nothing (they still vote)
+        bool done = t >= n, half = idle;       // row finished; this half's slots subtracted
+        if (never && t == 0 && q4 == 0 && h == 0) (void)wait_value(never, ks);  // failure injection
+        SweepLane<B, T, DG> L;
+        L.s = (T)0;
+        const int32_t lane = t & 31;
+        if (!idle) {
+            const int32_t ch = t >> 5;
+            if (h == 0) L.s = (T)__ldg(r + (int64_t)__ldg(pos + t) * B + q4);
+            L.s = pair_terms<B, T, RT, 2>(L.s, q4, ch, lane, coff, ccol, cval, r, n, h);
+            L.nrows = n;
+            L.sl0 = __ldg(off + ch) + h;
+            L.o1 = __ldg(off + ch + 1);
+            L.waiting = false;
+            if (L.sl0 < L.o1) sweep_stage<B, T, DG, 2>(L, q4, lane, col, val, y);
+            else half = true;
+        }
+        while (__any_sync(0xffffffffu, !done)) {
+            bool pend = false;
+            if (!half && sweep_round<B, T, DG, 2>(L, q4, lane, gmask, g0, col, val, y, ks, &pend)) half = true;
+            // a row is ready once all eight of its lanes have voted; half 0 adds half 1's sum
+            const unsigned hv = __ballot_sync(0xffffffffu, half);
+            const T other = __shfl_xor_sync(0xffffffffu, L.s, kSfGroup);
+            const bool ready = !done && ((hv >> gr) & 0xFFu) == 0xFFu;
+            if (ready && !idle && h == 0) store_relaxed(y + (int64_t)t * B + q4, L.s + other);
+            if (ready) done = true;
+            if (__any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
+        }
+    }
+}
+
+template <int B, typename T, typename XT, int DG>
+__global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_h(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
+                                                         const int32_t *__restrict__ bmap,
+                                                         const int64_t *__restrict__ off, const int32_t *__restrict__ col,
+                                                         const T *__restrict__ val, const T *__restrict__ dinv,
+                                                         const T *__restrict__ y, T *z, double *__restrict__ out,
+                                                         int ps, int ts, const XT *__restrict__ dp,
+                                                         const XT *__restrict__ dT, KState *ks, int sleep_ns,
+                                                         const int64_t *__restrict__ coff,
+                                                         const int32_t *__restrict__ ccol, const T *__restrict__ cval) {
+    __shared__ unsigned blk;
+    const unsigned nchunks = (unsigned)((n + kSfRowsG2 - 1) / kSfRowsG2);
+    const int q4 = threadIdx.x & (kSfGroup - 1), h = (threadIdx.x / kSfGroup) & 1;
+    const int lw = threadIdx.x & 31, gr = lw & ~(kSfGroup2 - 1), g0 = gr + kSfGroup * h;
+    const unsigned gmask = ((1u << B) - 1u) << g0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) blk = atomicAdd(ticket + 1, 1u);
+        __syncthreads();
+        const unsigned b = blk;
+        if (b >= nchunks) return;
+        const int32_t t = (int32_t)(b * kSfRowsG2 + threadIdx.x / kSfGroup2);
+        const bool idle = t >= n || q4 >= B;
+        bool done = t >= n, half = idle;
+        SweepLane<B, T, DG> L;
+        L.s = (T)0;
+        const int32_t lane = t & 31;
+        T dv[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) dv[q] = (T)0;
+        int32_t row = 0;
+        double add = 0.0;
+        if (!idle) {
+            const int32_t ch = t >> 5;
+            row = __ldg(pos + t);
+            if (h == 0) {
+                if (dp && q4 == ps) add = (double)dp[row];
+                if (dT && q4 == ts) add = (double)dT[row];
+                L.s = __ldcg(y + (int64_t)__ldg(bmap + t) * B + q4);
+            }
+            L.s = pair_terms<B, T, T, 2>(L.s, q4, ch, lane, coff, ccol, cval, y, n, h);
+            L.nrows = n;
+#pragma unroll
+            for (int q = 0; q < B; ++q) dv[q] = __ldg(dinv + ((int64_t)ch * B * B + q4 * B + q) * 32 + lane);
+            L.sl0 = __ldg(off + ch) + h;
+            L.o1 = __ldg(off + ch + 1);
+            L.waiting = false;
+            if (L.sl0 < L.o1) sweep_stage<B, T, DG, 2>(L, q4, lane, col, val, z);
+            else half = true;
+        }
+        while (__any_sync(0xffffffffu, !done)) {
+            bool pend = false;
+            if (!half && sweep_round<B, T, DG, 2>(L, q4, lane, gmask, g0, col, val, z, ks, &pend)) half = true;
+            const unsigned hv = __ballot_sync(0xffffffffu, half);
+            const T sum = L.s + __shfl_xor_sync(0xffffffffu, L.s, kSfGroup);   // half 0's first in both halves
+            const bool ready = !done && ((hv >> gr) & 0xFFu) == 0xFFu;
+            T a = 0;
+#pragma unroll
+            for (int q = 0; q < B; ++q) a = fma(dv[q], __shfl_sync(0xffffffffu, sum, gr + q), a);
+            if (ready && !idle && h == 0) {
+                store_relaxed(z + (int64_t)t * B + q4, a);
+                out[(int64_t)row * B + q4] = (double)a + add;
+            }
+            if (ready) done = true;
             if (__any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
         }
     }
@@ -2437,6 +2566,7 @@ cptr_status ilu_setup(Ctx *c) {
     if (c->o.ilu_sweep == 3 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 2))) {
         CPTR_TRY(pair_setup(c, ilu_group_size(c)));
         c->sp_use = c->sp_ok && (c->o.ilu_sweep == 3 || sched == 2);
+        c->sf_half = c->o.ilu_lanes == 8 ? 2 : 1;   // (a cached tuning's choice is restored by the autotuner)
     }
     int32_t *kidx_f = nullptr, *kidx_b = nullptr, *kidx_d = nullptr;
     int64_t ns_f = 0, ns_b = 0;
@@ -2556,6 +2686,31 @@ static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT 
         prof_end(c, pf);
         return;
     }
+    if (c->sp_use && c->sf_half == 2) {   // grouped levels, a row over eight lanes (two halves)
+        const unsigned gridh = std::min<unsigned>(nblk(n, kSfRowsG2), (unsigned)c->sf_grid);
+        int pf = prof_begin(c, PF_ILU_FWD);
+        auto fwd = [&](auto kern) {
+            (kern<<<gridh, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_f, c->sp_off_f, c->sp_col_f,
+                                               (const T *)c->sp_val_f, r, y, c->ks, c->inject_wait ? c->never : nullptr,
+                                               c->sf_sleep, c->sp_coff_f, c->sp_ccol_f, (const T *)c->sp_cval_f),
+             note_launch());
+        };
+        if (c->sp_group >= 3) fwd(k_ilu_fwd_h<B, T, RT, 6>);
+        else fwd(k_ilu_fwd_h<B, T, RT, 4>);
+        prof_end(c, pf);
+        pf = prof_begin(c, PF_ILU_BWD);
+        auto bwd = [&](auto kern) {
+            (kern<<<gridh, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_b, c->sf_bmap, c->sp_off_b, c->sp_col_b,
+                                               (const T *)c->sp_val_b, (const T *)c->sf_dinv, y, zz, z, c->ps, c->ts, dp,
+                                               dT, c->ks, c->sf_sleep, c->sp_coff_b, c->sp_ccol_b,
+                                               (const T *)c->sp_cval_b),
+             note_launch());
+        };
+        if (c->sp_group >= 3) bwd(k_ilu_bwd_h<B, T, XT, 6>);
+        else bwd(k_ilu_bwd_h<B, T, XT, 4>);
+        prof_end(c, pf);
+        return;
+    }
     if (std::is_same<T, double>::value || c->sp_use) {   // a row over four lanes, lockstep rounds
         const unsigned gridg = std::min<unsigned>(nblk(n, kSfRowsG), (unsigned)c->sf_grid);
         // the level-set tables, or the paired-level ones (their c-term tables non-null)
@@ -2652,6 +2807,8 @@ cptr_status ilu_autotune(Ctx *c) {
     if (it != c->tune_cache.end()) {
         c->sf_grid = it->second.T;
         c->sf_sleep = it->second.G;
+        auto hf = c->tune_cache.find(key + 3);
+        c->sf_half = c->o.ilu_lanes ? c->o.ilu_lanes / 4 : (hf != c->tune_cache.end() ? hf->second.G : 1);
         if (auto_sched) {
             const int sched = ilu_tuned_schedule(c);
             c->cw_use = c->cw_ok && sched == 1;
@@ -2697,7 +2854,17 @@ cptr_status ilu_autotune(Ctx *c) {
         return bm;
     };
     int best_g = c->sf_grid, best_s = c->sf_sleep;
+    const int fixed_half = c->o.ilu_lanes / 4;   // 0: both are timed
+    c->sf_half = fixed_half ? fixed_half : 1;
     float best_ms = search(&best_g, &best_s);
+    int best_half = c->sf_half;   // grouped levels: a row over four lanes, or over eight (two halves)
+    if (c->sp_use && !fixed_half) {
+        c->sf_half = 2;
+        int g = best_g, sl = best_s;
+        const float ms = search(&g, &sl);
+        if (ms < best_ms) { best_ms = ms; best_g = g; best_s = sl; best_half = 2; }
+        c->sf_half = 1;
+    }
     int sched = c->sp_use ? 2 : 0;
     int group = c->sp_use ? c->sp_group : 0;
     // the other schedules, each at its own best grid and back-off; the fastest is kept
@@ -2705,10 +2872,15 @@ cptr_status ilu_autotune(Ctx *c) {
     // to cost more set-up time than their sweeps save, so they are used only when asked for)
     if (auto_sched && c->sp_ok) {
         c->sp_use = true;
-        int g = best_g, sl = best_s;
-        const float ms = search(&g, &sl);
+        for (int hf : {1, 2}) {
+            if (fixed_half && hf != fixed_half) continue;
+            c->sf_half = hf;
+            int g = best_g, sl = best_s;
+            const float ms = search(&g, &sl);
+            if (ms < best_ms) { best_ms = ms; best_g = g; best_s = sl; sched = 2; group = c->sp_group; best_half = hf; }
+        }
+        c->sf_half = 1;
         c->sp_use = false;
-        if (ms < best_ms) { best_ms = ms; best_g = g; best_s = sl; sched = 2; group = c->sp_group; }
     }
     if (auto_sched && c->cw_ok) {   // one block per chunk: only the back-off matters
         c->cw_use = true;
@@ -2762,6 +2934,7 @@ cptr_status ilu_autotune(Ctx *c) {
         c->tl_use = tl_was && c->tl_ok;
     }
     c->sf_sleep = best_s;
+    c->sf_half = c->sp_use ? best_half : 1;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     Shape sh, sc;
@@ -2771,6 +2944,10 @@ cptr_status ilu_autotune(Ctx *c) {
     sc.T = (int16_t)(sched == 2 ? group : 0);
     c->tune_cache[key] = sh;
     c->tune_cache[key + 1] = sc;
+    Shape hs;
+    hs.G = (int16_t)c->sf_half;
+    hs.T = 0;
+    c->tune_cache[key + 3] = hs;
     if (tile_ty > 0) {
         c->tl_best_ty = tile_ty;
         c->tl_best_tz = tile_tz;

@@ -57,8 +57,8 @@ def test_default_options(lib):
 
 
 def test_option_struct_layout_matches_header():
-    # cptr_options: 4 int32, 2 doubles, 12 int32, one pointer, 6 int32
-    assert ctypes.sizeof(cp.cptr_options) == 16 + 16 + 48 + 8 + 24
+    # cptr_options: 4 int32, 2 doubles, 12 int32, one pointer, 7 int32 (+ padding)
+    assert ctypes.sizeof(cp.cptr_options) == 16 + 16 + 48 + 8 + 32
     assert cp.cptr_options.stream.offset == 80
     # cptr_instance: int32 (+ padding), five pointers
     assert ctypes.sizeof(cp.cptr_instance) == 8 + 5 * 8
@@ -98,7 +98,7 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
 def test_invalid_options_are_rejected_before_any_device_work(lib):
     # cptr_create validates its options first and returns CPTR_EINVAL without touching a device
     for kw in (dict(csr_lanes=-1), dict(csr_lanes=3), dict(csr_lanes=64), dict(use_graph=3), dict(restart=0),
-               dict(ilu_group=1), dict(ilu_group=5), dict(ilu_group=-1)):
+               dict(ilu_group=1), dict(ilu_group=5), dict(ilu_group=-1), dict(ilu_lanes=2), dict(ilu_lanes=16)):
         o = cp.cptr_default_options(**kw)
         h = ctypes.c_void_p()
         assert lib.cptr_create(ctypes.byref(h), ctypes.byref(o)) == -1, kw

@@ -36,7 +36,7 @@ def test_tuned_solve_matches_untuned(precision):
     assert err <= (1e-10 if precision == "fp64" else 1e-6), float(err)
     rows = cp.cptr_tuning(b.ctx)
     levels = ia["levels_p"] - 1 + ia["levels_T"] - 1
-    assert len(rows) == 3 * levels + 4
+    assert len(rows) == 3 * levels + 5
     for h, l, k, G, T in rows:
         if k == 3:
             assert h == 2 and T in (64, 128, 256, 512)
@@ -46,11 +46,13 @@ def test_tuned_solve_matches_untuned(precision):
             assert h == 3 and G in (0, 1, 2, 3)
         elif k == 6:       # tile shape the autotuner chose (lines per tile along y and z)
             assert h == 3 and 0 < G * T <= 64
+        elif k == 7:       # lanes per row of the grouped-level sweeps (0: not in use)
+            assert h == 3 and G in (0, 4, 8) and T == 0
         else:
             assert G in (1, 2, 4, 8, 16, 32) and T in (128, 256, 512)
     # untuned: heuristic lanes, 256 threads; level-set sweeps on 608 blocks, 20 ns back-off
     for h, l, k, G, T in cp.cptr_tuning(a.ctx):
-        assert (G, T) == {4: (20, 608), 5: (0, 0), 6: (0, 0)}.get(k, (0, 256))
+        assert (G, T) == {4: (20, 608), 5: (0, 0), 6: (0, 0), 7: (0, 0)}.get(k, (0, 256))
     # a second set-up of the same operators reuses the cached shapes
     b.setup(s["n"], s["b"], dev(s["row_ptr"]), dev(s["col_idx"]), dev(s["vals"].reshape(-1)),
             dev(s["unknown_kind"]), dev(s["weights"].reshape(-1)), dev(s["st"]))

@@ -549,15 +549,18 @@ def test_chunked_and_level_sweeps_agree(name, precision):
 
 @pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "medium", "line"])
 @pytest.mark.parametrize("group", [2, 3, 4])
-def test_paired_level_sweeps(name, group):
+@pytest.mark.parametrize("lanes", [4, 8])
+def test_paired_level_sweeps(name, group, lanes):
     """Grouped levels solve the same triangular systems with the sums grouped differently (a row
     substitutes its dependencies inside its group of two, three or four levels, through chains of
-    up to group - 1 links): ILU applications agree with the level-set sweeps to rounding and with
-    the oracle within the operator tolerance, and solves match the oracle."""
+    up to group - 1 links; with eight lanes a row's slots are split between two halves): ILU
+    applications agree with the level-set sweeps to rounding and with the oracle within the
+    operator tolerance, and solves match the oracle."""
     s = system(name)
     a = gpu_solver(s, ilu_sweep=cp.ILU_SWEEP["levels"], **OPTS[name])
-    b = gpu_solver(s, ilu_sweep=cp.ILU_SWEEP["paired"], ilu_group=group, **OPTS[name])
-    assert [r for r in cp.cptr_tuning(b.ctx) if r[2] == 5][0][3:5] == (2, group)
+    b = gpu_solver(s, ilu_sweep=cp.ILU_SWEEP["paired"], ilu_group=group, ilu_lanes=lanes, **OPTS[name])
+    tun = cp.cptr_tuning(b.ctx)
+    assert [r for r in tun if r[2] == 5][0][3:5] == (2, group) and [r for r in tun if r[2] == 7][0][3] == lanes
     r = np.random.default_rng(4).normal(size=s["n"] * s["b"])
     za, zb = torch.empty(r.size, dtype=torch.float64, device="cuda"), torch.empty(r.size, dtype=torch.float64, device="cuda")
     cp.cptr_apply_ilu(a.ctx, dev(r), za)
@@ -570,16 +573,18 @@ def test_paired_level_sweeps(name, group):
 
 @pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "medium", "line"])
 @pytest.mark.parametrize("group", [2, 3])
-def test_paired_level_sweeps_mixed(name, group):
+@pytest.mark.parametrize("lanes", [4, 8])
+def test_paired_level_sweeps_mixed(name, group, lanes):
     """The grouped-level tables in FP32 (mixed form): against the FP64 ILU(0), the FP32 grouped
     sweeps are about as accurate as the FP32 level-set sweeps (both carry FP32 rounding through
-    every level; pairs within twice the level sets' error, groups of three within ten times, since a
-    row then sums products of three factor blocks, larger than its result, each rounded to FP32),
-    and solves converge like them."""
+    every level; pairs over four lanes within twice the level sets' error; groups of three, or a
+    row's slots split over two halves of eight lanes, within ten times: the row then sums terms
+    larger than its result (products of three factor blocks, or two partial sums that cancel), each
+    rounded to FP32), and solves converge like them."""
     s = system(name)
     o = {**OPTS[name], "precision": cp.PRECISION["mixed"]}
     a = gpu_solver(s, ilu_sweep=cp.ILU_SWEEP["levels"], **o)
-    b = gpu_solver(s, ilu_sweep=cp.ILU_SWEEP["paired"], ilu_group=group, **o)
+    b = gpu_solver(s, ilu_sweep=cp.ILU_SWEEP["paired"], ilu_group=group, ilu_lanes=lanes, **o)
     f = gpu_solver(s, ilu_sweep=cp.ILU_SWEEP["levels"], **OPTS[name])
     assert [r for r in cp.cptr_tuning(b.ctx) if r[2] == 5][0][3:5] == (2, group)
     r = dev(np.random.default_rng(5).normal(size=s["n"] * s["b"]))
@@ -588,7 +593,7 @@ def test_paired_level_sweeps_mixed(name, group):
     cp.cptr_apply_ilu(b.ctx, r, zb)
     cp.cptr_apply_ilu(f.ctx, r, z64)
     ea, eb = relerr(host(za), host(z64)), relerr(host(zb), host(z64))
-    assert ea <= 1e-3 and eb <= (2 if group == 2 else 10) * ea + 1e-6, (ea, eb)
+    assert ea <= 1e-3 and eb <= (2 if group == 2 and lanes == 4 else 10) * ea + 1e-6, (ea, eb)
     xa, ia = a.solve(dev(s["rhs"].reshape(-1)), 1e-8)
     xb, ib = b.solve(dev(s["rhs"].reshape(-1)), 1e-8)
     assert ib["status"] == "CPTR_OK" and ib["true_rel_res"] <= 1e-8 * 1.05
@@ -640,6 +645,25 @@ def test_tiled_and_level_sweeps_agree(name, precision, shape):
     xa, ia = a.solve(dev(s["rhs"].reshape(-1)), 1e-8)
     xb, ib = b.solve(dev(s["rhs"].reshape(-1)), 1e-8)
     assert ia["iters"] == ib["iters"] and torch.equal(xa, xb)
+
+
+@pytest.mark.parametrize("lanes", [4, 8])
+def test_paired_sweeps_timeout_reported_and_context_recovers(lanes):
+    """The bounded waits of the grouped-level sweeps (four or eight lanes per row): the injected
+    wait on a value nobody writes gives up, the call reports CPTR_ETIMEOUT, and the context solves
+    normally afterwards."""
+    s = system("medium")
+    o = oracle.Oracle.from_system(s, **OPTS["medium"])
+    g = gpu_solver(s, ilu_sweep=cp.ILU_SWEEP["paired"], ilu_lanes=lanes, **OPTS["medium"])
+    assert [r for r in cp.cptr_tuning(g.ctx) if r[2] == 7][0][3] == lanes
+    nb = s["n"] * s["b"]
+    cp.cptr_inject_wait_timeout(g.ctx, True)
+    z = torch.empty(nb, dtype=torch.float64, device="cuda")
+    with pytest.raises(cp.CptrError) as e:
+        cp.cptr_apply_ilu(g.ctx, dev(synth.normal(5, nb)), z)
+    assert e.value.code == -5
+    cp.cptr_inject_wait_timeout(g.ctx, False)
+    check_solve(s, o, g, 1e-8)
 
 
 def test_tiled_sweeps_timeout_reported_and_context_recovers():
