@@ -310,7 +310,7 @@ def family_kernels(cp, S, b, mixed):
              3: "tiled"}[sched]
     four = sched == 2 or (sched == 0 and not mixed)
     how = sweep + (f", a row over {lanes if sched == 2 else 4} lanes" if four else "")
-    if sched == 2 and lanes == 8:
+    if sched == 2 and lanes in (8, 16):
         fwd, bwd = f"k_ilu_fwd_h<{b},{t},...>", f"k_ilu_bwd_h<{b},{t},...>"
     elif sched == 1:
         fwd, bwd = f"k_ilu_cw<{b},{t},...,FWD>", f"k_ilu_cw<{b},{t},...,BWD>"

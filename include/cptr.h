@@ -144,11 +144,12 @@ typedef struct {
                             right-hand-side terms) the tables are not built and level sets are used
                             (other values: CPTR_EINVAL at cptr_create). */
     int32_t ilu_lanes;   /* lanes per row of the grouped-level sweeps: 0 (default) four, or with
-                            autotune the faster of four and eight; 4 or 8 fixes it.  Four lanes: lane
-                            q computes component q over all of the row's dependency slots; eight: two
-                            halves of four each take every other slot, and their partial sums are
-                            added at the end (half 0's first), which halves each lane's chain of FP64
-                            instructions; values differ by rounding (other values: CPTR_EINVAL). */
+                            autotune the fastest of 4, 8 and 16; 4, 8 or 16 fixes it.  Four lanes:
+                            lane q computes component q over all of the row's dependency slots; 8 or
+                            16: H = 2 or 4 parts of four lanes each take every H-th slot, and their
+                            partial sums are added pairwise at the end, which shortens each lane's
+                            chain of FP64 instructions to about 1/H; values differ by rounding (other
+                            values: CPTR_EINVAL at cptr_create). */
 } cptr_options;
 
 typedef struct {
@@ -287,7 +288,7 @@ cptr_status cptr_apply_ilu_static(cptr_ctx *ctx, const double *r, double *z);
  * schedule, 6 tile shape of the tiled sweeps, 7 lanes per row of the grouped-level sweeps), lanes
  * per row (0 = chosen from the average row length; kernel 4: back-off between polls in ns;
  * kernel 5: 0 level sets, 1 chunked wavefront, 2 grouped levels, 3 tiles; kernel 6: lines per tile
- * along y, Ty, or 0 when no tiled tables are built; kernel 7: 4 or 8, or 0 when the grouped levels
+ * along y, Ty, or 0 when no tiled tables are built; kernel 7: 4, 8 or 16, or 0 when the grouped levels
  * are not in use), threads per block (kernel 4: blocks of the persistent grid; kernel 5: levels
  * per group of the grouped levels, else 0; kernel 6: lines per tile along z, Tz)}; *n_rows
  * receives the number of rows available.  With autotune set,

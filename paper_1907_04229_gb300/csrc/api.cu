@@ -468,7 +468,7 @@ cptr_status cptr_create(cptr_ctx **out, const cptr_options *opt) {
         (o.decouple != CPTR_DECOUPLE_NONE && o.stage1 != CPTR_STAGE1_CPR && o.stage1 != CPTR_STAGE1_UAMG) ||
         o.ilu_fill < 0 || o.ilu_fill > 1 || (o.ilu_fill == 1 && o.ilu_order == CPTR_ILU_MULTICOLOR) ||
         o.csr_lanes < 0 || o.csr_lanes > 32 || (o.csr_lanes & (o.csr_lanes - 1)) || o.ilu_group < 0 || o.ilu_group == 1 ||
-        o.ilu_group > 4 || (o.ilu_lanes != 0 && o.ilu_lanes != 4 && o.ilu_lanes != 8))
+        o.ilu_group > 4 || (o.ilu_lanes != 0 && o.ilu_lanes != 4 && o.ilu_lanes != 8 && o.ilu_lanes != 16))
         return CPTR_EINVAL;
     cptr_ctx *ctx = new (std::nothrow) cptr_ctx();
     if (!ctx) return CPTR_ENOMEM;

@@ -374,7 +374,7 @@ struct Ctx {
     void *sp_val_f = nullptr, *sp_val_b = nullptr, *sp_cval_f = nullptr, *sp_cval_b = nullptr;   // FP64, or FP32 when mixed
     bool sp_ok = false, sp_use = false;                // built / chosen
     int sp_group = 0;                                  // levels per group of the tables built
-    int sf_half = 1;                                   // grouped-level sweeps: lanes per row / 4 (1 or 2)
+    int sf_half = 1;                                   // grouped-level sweeps: lanes per row / 4 (1, 2 or 4)
     int32_t *sp_inv_f = nullptr, *sp_inv_b = nullptr;  // position of each row in either sweep
     int32_t *sp_levr_f = nullptr, *sp_levr_b = nullptr;   // level of each row in either sweep
     // tiled sweeps: a block owns a tile of grid lines and walks its own levels (natural order on

@@ -533,26 +533,26 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_g(int32_t n, unsigned *t
     }
 }
 
-// The same sweeps with a row over eight lanes, two halves of four: half h subtracts the row's
-// dependency slots h, h + 2, ... (and its share of the right-hand-side terms), lane q of a half
-// component q, so that each lane's chain of FP64 instructions is about half as long; when both
-// halves have subtracted their slots the halves' partial sums are added (half 0's first) and half 0
-// finishes the row.  The sums are grouped differently from the four-lane kernels above, so values
-// differ from them by rounding only.  Rows of a warp advance in the same lockstep rounds.
-constexpr int kSfGroup2 = 2 * kSfGroup;              // lanes per row
-constexpr int kSfRowsG2 = kSfThreads / kSfGroup2;    // rows per block chunk
-
-template <int B, typename T, typename RT, int DG>
+// The same sweeps with a row over 4H lanes, H parts of four (H = 2 or 4): part h subtracts the
+// row's dependency slots h, h + H, ... (and its share of the right-hand-side terms), lane q of a part
+// component q, so that each lane's chain of FP64 instructions is about 1/H as long; when every part
+// has subtracted its slots the parts' partial sums are added pairwise (a butterfly: parts 0 + 1, then
+// with 2 + 3, the same value in every part) and part 0 finishes the row.  The sums are grouped
+// differently from the four-lane kernels above, so values differ from them by rounding only.  Rows
+// of a warp advance in the same lockstep rounds.
+template <int B, typename T, typename RT, int DG, int H>
 __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_h(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
                                                          const int64_t *__restrict__ off, const int32_t *__restrict__ col,
                                                          const T *__restrict__ val, const RT *__restrict__ r, T *y,
                                                          KState *ks, const double *never, int sleep_ns,
                                                          const int64_t *__restrict__ coff,
                                                          const int32_t *__restrict__ ccol, const T *__restrict__ cval) {
+    constexpr int LPR = kSfGroup * H, RPB = kSfThreads / LPR;   // lanes per row, rows per block chunk
+    constexpr unsigned RMASK = (LPR == 32) ? 0xffffffffu : ((1u << LPR) - 1u);
     __shared__ unsigned blk;
-    const unsigned nchunks = (unsigned)((n + kSfRowsG2 - 1) / kSfRowsG2);
-    const int q4 = threadIdx.x & (kSfGroup - 1), h = (threadIdx.x / kSfGroup) & 1;
-    const int lw = threadIdx.x & 31, gr = lw & ~(kSfGroup2 - 1), g0 = gr + kSfGroup * h;
+    const unsigned nchunks = (unsigned)((n + RPB - 1) / RPB);
+    const int q4 = threadIdx.x & (kSfGroup - 1), h = (threadIdx.x / kSfGroup) & (H - 1);
+    const int lw = threadIdx.x & 31, gr = lw & ~(LPR - 1), g0 = gr + kSfGroup * h;
     const unsigned gmask = ((1u << B) - 1u) << g0;
     for (;;) {
         __syncthreads();
@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_h(int32_t n, unsigned *t
         __syncthreads();
         const unsigned b = blk;
         if (b >= nchunks) return;
-        const int32_t t = (int32_t)(b * kSfRowsG2 + threadIdx.x / kSfGroup2);
+        const int32_t t = (int32_t)(b * RPB + threadIdx.x / LPR);
         const bool idle = t >= n || q4 >= B;   // lanes that compute nothing (they still vote)
         bool done = t >= n, half = idle;       // row finished; this half's slots subtracted
         if (never && t == 0 && q4 == 0 && h == 0) (void)wait_value(never, ks);  // failure injection
@@ -570,29 +570,31 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_h(int32_t n, unsigned *t
         if (!idle) {
             const int32_t ch = t >> 5;
             if (h == 0) L.s = (T)__ldg(r + (int64_t)__ldg(pos + t) * B + q4);
-            L.s = pair_terms<B, T, RT, 2>(L.s, q4, ch, lane, coff, ccol, cval, r, n, h);
+            L.s = pair_terms<B, T, RT, H>(L.s, q4, ch, lane, coff, ccol, cval, r, n, h);
             L.nrows = n;
             L.sl0 = __ldg(off + ch) + h;
             L.o1 = __ldg(off + ch + 1);
             L.waiting = false;
-            if (L.sl0 < L.o1) sweep_stage<B, T, DG, 2>(L, q4, lane, col, val, y);
+            if (L.sl0 < L.o1) sweep_stage<B, T, DG, H>(L, q4, lane, col, val, y);
             else half = true;
         }
         while (__any_sync(0xffffffffu, !done)) {
             bool pend = false;
-            if (!half && sweep_round<B, T, DG, 2>(L, q4, lane, gmask, g0, col, val, y, ks, &pend)) half = true;
-            // a row is ready once all eight of its lanes have voted; half 0 adds half 1's sum
+            if (!half && sweep_round<B, T, DG, H>(L, q4, lane, gmask, g0, col, val, y, ks, &pend)) half = true;
+            // a row is ready once all of its lanes have voted; part 0 stores the parts' sum
             const unsigned hv = __ballot_sync(0xffffffffu, half);
-            const T other = __shfl_xor_sync(0xffffffffu, L.s, kSfGroup);
-            const bool ready = !done && ((hv >> gr) & 0xFFu) == 0xFFu;
-            if (ready && !idle && h == 0) store_relaxed(y + (int64_t)t * B + q4, L.s + other);
+            T sum = L.s;
+#pragma unroll
+            for (int o = kSfGroup; o < LPR; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            const bool ready = !done && ((hv >> gr) & RMASK) == RMASK;
+            if (ready && !idle && h == 0) store_relaxed(y + (int64_t)t * B + q4, sum);
             if (ready) done = true;
             if (__any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
         }
     }
 }
 
-template <int B, typename T, typename XT, int DG>
+template <int B, typename T, typename XT, int DG, int H>
 __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_h(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
                                                          const int32_t *__restrict__ bmap,
                                                          const int64_t *__restrict__ off, const int32_t *__restrict__ col,
@@ -602,10 +604,12 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_h(int32_t n, unsigned *t
                                                          const XT *__restrict__ dT, KState *ks, int sleep_ns,
                                                          const int64_t *__restrict__ coff,
                                                          const int32_t *__restrict__ ccol, const T *__restrict__ cval) {
+    constexpr int LPR = kSfGroup * H, RPB = kSfThreads / LPR;   // lanes per row, rows per block chunk
+    constexpr unsigned RMASK = (LPR == 32) ? 0xffffffffu : ((1u << LPR) - 1u);
     __shared__ unsigned blk;
-    const unsigned nchunks = (unsigned)((n + kSfRowsG2 - 1) / kSfRowsG2);
-    const int q4 = threadIdx.x & (kSfGroup - 1), h = (threadIdx.x / kSfGroup) & 1;
-    const int lw = threadIdx.x & 31, gr = lw & ~(kSfGroup2 - 1), g0 = gr + kSfGroup * h;
+    const unsigned nchunks = (unsigned)((n + RPB - 1) / RPB);
+    const int q4 = threadIdx.x & (kSfGroup - 1), h = (threadIdx.x / kSfGroup) & (H - 1);
+    const int lw = threadIdx.x & 31, gr = lw & ~(LPR - 1), g0 = gr + kSfGroup * h;
     const unsigned gmask = ((1u << B) - 1u) << g0;
     for (;;) {
         __syncthreads();
@@ -613,7 +617,7 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_h(int32_t n, unsigned *t
         __syncthreads();
         const unsigned b = blk;
         if (b >= nchunks) return;
-        const int32_t t = (int32_t)(b * kSfRowsG2 + threadIdx.x / kSfGroup2);
+        const int32_t t = (int32_t)(b * RPB + threadIdx.x / LPR);
         const bool idle = t >= n || q4 >= B;
         bool done = t >= n, half = idle;
         SweepLane<B, T, DG> L;
@@ -632,22 +636,24 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_h(int32_t n, unsigned *t
                 if (dT && q4 == ts) add = (double)dT[row];
                 L.s = __ldcg(y + (int64_t)__ldg(bmap + t) * B + q4);
             }
-            L.s = pair_terms<B, T, T, 2>(L.s, q4, ch, lane, coff, ccol, cval, y, n, h);
+            L.s = pair_terms<B, T, T, H>(L.s, q4, ch, lane, coff, ccol, cval, y, n, h);
             L.nrows = n;
 #pragma unroll
             for (int q = 0; q < B; ++q) dv[q] = __ldg(dinv + ((int64_t)ch * B * B + q4 * B + q) * 32 + lane);
             L.sl0 = __ldg(off + ch) + h;
             L.o1 = __ldg(off + ch + 1);
             L.waiting = false;
-            if (L.sl0 < L.o1) sweep_stage<B, T, DG, 2>(L, q4, lane, col, val, z);
+            if (L.sl0 < L.o1) sweep_stage<B, T, DG, H>(L, q4, lane, col, val, z);
             else half = true;
         }
         while (__any_sync(0xffffffffu, !done)) {
             bool pend = false;
-            if (!half && sweep_round<B, T, DG, 2>(L, q4, lane, gmask, g0, col, val, z, ks, &pend)) half = true;
+            if (!half && sweep_round<B, T, DG, H>(L, q4, lane, gmask, g0, col, val, z, ks, &pend)) half = true;
             const unsigned hv = __ballot_sync(0xffffffffu, half);
-            const T sum = L.s + __shfl_xor_sync(0xffffffffu, L.s, kSfGroup);   // half 0's first in both halves
-            const bool ready = !done && ((hv >> gr) & 0xFFu) == 0xFFu;
+            T sum = L.s;
+#pragma unroll
+            for (int o = kSfGroup; o < LPR; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            const bool ready = !done && ((hv >> gr) & RMASK) == RMASK;
             T a = 0;
 #pragma unroll
             for (int q = 0; q < B; ++q) a = fma(dv[q], __shfl_sync(0xffffffffu, sum, gr + q), a);
@@ -2566,7 +2572,7 @@ cptr_status ilu_setup(Ctx *c) {
     if (c->o.ilu_sweep == 3 || (c->o.ilu_sweep == 0 && c->o.autotune && (sched < 0 || sched == 2))) {
         CPTR_TRY(pair_setup(c, ilu_group_size(c)));
         c->sp_use = c->sp_ok && (c->o.ilu_sweep == 3 || sched == 2);
-        c->sf_half = c->o.ilu_lanes == 8 ? 2 : 1;   // (a cached tuning's choice is restored by the autotuner)
+        c->sf_half = c->o.ilu_lanes ? c->o.ilu_lanes / 4 : 1;   // (a cached tuning's choice is restored by the autotuner)
     }
     int32_t *kidx_f = nullptr, *kidx_b = nullptr, *kidx_d = nullptr;
     int64_t ns_f = 0, ns_b = 0;
@@ -2686,8 +2692,8 @@ static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT 
         prof_end(c, pf);
         return;
     }
-    if (c->sp_use && c->sf_half == 2) {   // grouped levels, a row over eight lanes (two halves)
-        const unsigned gridh = std::min<unsigned>(nblk(n, kSfRowsG2), (unsigned)c->sf_grid);
+    if (c->sp_use && c->sf_half >= 2) {   // grouped levels, a row over 8 or 16 lanes (2 or 4 parts)
+        const unsigned gridh = std::min<unsigned>(nblk(n, kSfThreads / (kSfGroup * c->sf_half)), (unsigned)c->sf_grid);
         int pf = prof_begin(c, PF_ILU_FWD);
         auto fwd = [&](auto kern) {
             (kern<<<gridh, kSfThreads, 0, s>>>(n, c->sf_ticket, c->sf_pos_f, c->sp_off_f, c->sp_col_f,
@@ -2695,8 +2701,9 @@ static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT 
                                                c->sf_sleep, c->sp_coff_f, c->sp_ccol_f, (const T *)c->sp_cval_f),
              note_launch());
         };
-        if (c->sp_group >= 3) fwd(k_ilu_fwd_h<B, T, RT, 6>);
-        else fwd(k_ilu_fwd_h<B, T, RT, 4>);
+        if (c->sf_half == 4) fwd(k_ilu_fwd_h<B, T, RT, 3, 4>);
+        else if (c->sp_group >= 3) fwd(k_ilu_fwd_h<B, T, RT, 6, 2>);
+        else fwd(k_ilu_fwd_h<B, T, RT, 4, 2>);
         prof_end(c, pf);
         pf = prof_begin(c, PF_ILU_BWD);
         auto bwd = [&](auto kern) {
@@ -2706,8 +2713,9 @@ static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT 
                                                (const T *)c->sp_cval_b),
              note_launch());
         };
-        if (c->sp_group >= 3) bwd(k_ilu_bwd_h<B, T, XT, 6>);
-        else bwd(k_ilu_bwd_h<B, T, XT, 4>);
+        if (c->sf_half == 4) bwd(k_ilu_bwd_h<B, T, XT, 3, 4>);
+        else if (c->sp_group >= 3) bwd(k_ilu_bwd_h<B, T, XT, 6, 2>);
+        else bwd(k_ilu_bwd_h<B, T, XT, 4, 2>);
         prof_end(c, pf);
         return;
     }
@@ -2859,10 +2867,12 @@ cptr_status ilu_autotune(Ctx *c) {
     float best_ms = search(&best_g, &best_s);
     int best_half = c->sf_half;   // grouped levels: a row over four lanes, or over eight (two halves)
     if (c->sp_use && !fixed_half) {
-        c->sf_half = 2;
-        int g = best_g, sl = best_s;
-        const float ms = search(&g, &sl);
-        if (ms < best_ms) { best_ms = ms; best_g = g; best_s = sl; best_half = 2; }
+        for (int hf : {2, 4}) {
+            c->sf_half = hf;
+            int g = best_g, sl = best_s;
+            const float ms = search(&g, &sl);
+            if (ms < best_ms) { best_ms = ms; best_g = g; best_s = sl; best_half = hf; }
+        }
         c->sf_half = 1;
     }
     int sched = c->sp_use ? 2 : 0;
@@ -2872,7 +2882,7 @@ cptr_status ilu_autotune(Ctx *c) {
     // to cost more set-up time than their sweeps save, so they are used only when asked for)
     if (auto_sched && c->sp_ok) {
         c->sp_use = true;
-        for (int hf : {1, 2}) {
+        for (int hf : {1, 2, 4}) {
             if (fixed_half && hf != fixed_half) continue;
             c->sf_half = hf;
             int g = best_g, sl = best_s;

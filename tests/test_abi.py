@@ -98,7 +98,7 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
 def test_invalid_options_are_rejected_before_any_device_work(lib):
     # cptr_create validates its options first and returns CPTR_EINVAL without touching a device
     for kw in (dict(csr_lanes=-1), dict(csr_lanes=3), dict(csr_lanes=64), dict(use_graph=3), dict(restart=0),
-               dict(ilu_group=1), dict(ilu_group=5), dict(ilu_group=-1), dict(ilu_lanes=2), dict(ilu_lanes=16)):
+               dict(ilu_group=1), dict(ilu_group=5), dict(ilu_group=-1), dict(ilu_lanes=2), dict(ilu_lanes=32)):
         o = cp.cptr_default_options(**kw)
         h = ctypes.c_void_p()
         assert lib.cptr_create(ctypes.byref(h), ctypes.byref(o)) == -1, kw

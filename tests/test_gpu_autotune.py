@@ -47,7 +47,7 @@ def test_tuned_solve_matches_untuned(precision):
         elif k == 6:       # tile shape the autotuner chose (lines per tile along y and z)
             assert h == 3 and 0 < G * T <= 64
         elif k == 7:       # lanes per row of the grouped-level sweeps (0: not in use)
-            assert h == 3 and G in (0, 4, 8) and T == 0
+            assert h == 3 and G in (0, 4, 8, 16) and T == 0
         else:
             assert G in (1, 2, 4, 8, 16, 32) and T in (128, 256, 512)
     # untuned: heuristic lanes, 256 threads; level-set sweeps on 608 blocks, 20 ns back-off

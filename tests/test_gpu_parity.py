@@ -549,11 +549,11 @@ def test_chunked_and_level_sweeps_agree(name, precision):
 
 @pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "medium", "line"])
 @pytest.mark.parametrize("group", [2, 3, 4])
-@pytest.mark.parametrize("lanes", [4, 8])
+@pytest.mark.parametrize("lanes", [4, 8, 16])
 def test_paired_level_sweeps(name, group, lanes):
     """Grouped levels solve the same triangular systems with the sums grouped differently (a row
     substitutes its dependencies inside its group of two, three or four levels, through chains of
-    up to group - 1 links; with eight lanes a row's slots are split between two halves): ILU
+    up to group - 1 links; with 8 or 16 lanes a row's slots are split between 2 or 4 parts): ILU
     applications agree with the level-set sweeps to rounding and with the oracle within the
     operator tolerance, and solves match the oracle."""
     s = system(name)
@@ -573,12 +573,12 @@ def test_paired_level_sweeps(name, group, lanes):
 
 @pytest.mark.parametrize("name", ["parity", "ragged", "three_phase", "medium", "line"])
 @pytest.mark.parametrize("group", [2, 3])
-@pytest.mark.parametrize("lanes", [4, 8])
+@pytest.mark.parametrize("lanes", [4, 8, 16])
 def test_paired_level_sweeps_mixed(name, group, lanes):
     """The grouped-level tables in FP32 (mixed form): against the FP64 ILU(0), the FP32 grouped
     sweeps are about as accurate as the FP32 level-set sweeps (both carry FP32 rounding through
     every level; pairs over four lanes within twice the level sets' error; groups of three, or a
-    row's slots split over two halves of eight lanes, within ten times: the row then sums terms
+    row's slots split over parts of four lanes, within ten times: the row then sums terms
     larger than its result (products of three factor blocks, or two partial sums that cancel), each
     rounded to FP32), and solves converge like them."""
     s = system(name)
@@ -647,7 +647,7 @@ def test_tiled_and_level_sweeps_agree(name, precision, shape):
     assert ia["iters"] == ib["iters"] and torch.equal(xa, xb)
 
 
-@pytest.mark.parametrize("lanes", [4, 8])
+@pytest.mark.parametrize("lanes", [4, 8, 16])
 def test_paired_sweeps_timeout_reported_and_context_recovers(lanes):
     """The bounded waits of the grouped-level sweeps (four or eight lanes per row): the injected
     wait on a value nobody writes gives up, the call reports CPTR_ETIMEOUT, and the context solves
