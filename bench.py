@@ -36,14 +36,15 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 LEARNED_STEPS, LEARNED_LR = 2000, 2e-3
 # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/ (the
 # current kernels; None where no capture of the current code exists)
-PROFILED_TRAFFIC = {"spmv": 113_717_248, "stage1_resid": None, "ilu_fwd": 102_265_344, "ilu_bwd": 118_584_832,
+PROFILED_TRAFFIC = {"spmv": 113_717_248, "stage1_resid": None, "ilu_fwd": 165_831_936, "ilu_bwd": 187_658_240,
                     # the finest V-cycle level of the pressure hierarchy (cold-L2 captures, one launch each)
                     "vcycle_p_down": 20_470_528, "vcycle_p_restrict": 6_354_944, "vcycle_p_prolong": 7_413_760,
                     "vcycle_p_post": 22_069_504, "vcycle_p_down_mixed": 13_381_120,
                     "vcycle_p_restrict_mixed": 4_057_344, "vcycle_p_prolong_mixed": 4_857_600,
                     "vcycle_p_post_mixed": 14_180_608}
-# the ILU figures are those of the paired-level sweeps (their tables hold the substituted blocks)
-PROFILED_ILU_SCHEDULE = "paired"
+# the ILU figures belong to one sweep configuration (schedule 2: grouped levels; levels per group;
+# lanes per row): they are attached only when the timed solver runs that configuration
+PROFILED_ILU_SCHEDULE = (2, 3, 8)
 
 
 def parse():
@@ -65,6 +66,10 @@ def parse():
     p.add_argument("--graph", choices=["cycle", "step"], default="cycle",
                    help="headline solver: each restart cycle as one graph launch (device-side loop), or one "
                         "graph launch per Arnoldi step (what per-kernel profilers see kernel by kernel)")
+    p.add_argument("--ilu-group", type=int, default=0,
+                   help="levels per group of the grouped-level (paired) sweeps; 0: the library's choice")
+    p.add_argument("--ilu-lanes", type=int, default=0,
+                   help="lanes per row of the grouped-level sweeps (4, 8, 16); 0: the library's choice")
     p.add_argument("--ilu-sweep", choices=["auto", "levels", "chunked", "paired", "tiled"], default="auto",
                    help="schedule of the headline solver's ILU(0) sweeps")
     p.add_argument("--ensemble-total", type=float, default=4e6,
@@ -407,7 +412,8 @@ def ours(args, rank, world, local_rank, oracle_jobs):
     d = {k: torch.as_tensor(np.ascontiguousarray(v), device=dev) for k, v in host.items()}
     x = torch.empty(dofs, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    head_opts = dict(autotune=int(args.autotune), ilu_sweep=args.ilu_sweep, use_graph=1 if args.graph == "cycle" else 2)
+    head_opts = dict(autotune=int(args.autotune), ilu_sweep=args.ilu_sweep, use_graph=1 if args.graph == "cycle" else 2,
+                     ilu_group=args.ilu_group, ilu_lanes=args.ilu_lanes)
     S = cp.Solver(stream=stream, **head_opts)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -471,12 +477,15 @@ def ours(args, rank, world, local_rank, oracle_jobs):
     alg = algorithmic_bytes(s)
     kernels, schedule = family_kernels(cp, S, b, False)
     chunked, paired = schedule == 1, schedule == 2
+    tun = cp.cptr_tuning(S.ctx)
+    group = [t for t in tun if t[2] == 5][0][4]
+    ilu_config = (schedule, group, [t for t in tun if t[2] == 7][0][3])
     lines = {}
     for fam, kname in kernels.items():
         ms_tot, cnt = prof_sum[fam]
         lines[fam] = roofline_line(kname, alg[fam], ms_tot, cnt, args.profile_steps, peak, peak_kind,
                                    PROFILED_TRAFFIC.get(fam) if not fam.startswith("ilu") or
-                                   (paired and PROFILED_ILU_SCHEDULE == "paired") else None)
+                                   ilu_config == PROFILED_ILU_SCHEDULE else None)
     # the finest level's V-cycle kernels, timed one by one in a pass of their own
     _, vc_sum = profiled_pass(cp, S, step, flush, args.profile_steps, cp.PROFILE_MASK_VCYCLE)
     lines.update(vcycle_lines(cp, S, vc_sum, args.profile_steps, peak, peak_kind, False, "", PROFILED_TRAFFIC))
@@ -491,10 +500,10 @@ def ours(args, rank, world, local_rank, oracle_jobs):
     roofline = dict(lines[dominant])
     if dominant.startswith("ilu"):
         roofline["note"] = ((f"latency bound: a dependency chain of {ilu_levels} level sets per sweep, "
-                             f"run as {(ilu_levels + 1) // 2} steps of paired levels" if paired else
+                             f"run as {(ilu_levels + group - 1) // group} steps of groups of {group} levels" if paired else
                              f"latency bound: a dependency chain of {ilu_levels} level sets per sweep")
                             + (f"; DRAM traffic {roofline['traffic'] / roofline['algorithmic_bytes_per_launch']:.2f}x "
-                               "the algorithmic ILU(0) bytes (the paired tables hold the substituted blocks)"
+                               "the algorithmic ILU(0) bytes (the grouped tables hold the substituted blocks)"
                                if roofline["traffic"] and paired else ""))
     families = {k: {"ms_per_step": round(v[0] / args.profile_steps, 3),
                     "regions_per_step": v[1] / args.profile_steps} for k, v in prof_sum.items()}

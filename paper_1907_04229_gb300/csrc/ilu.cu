@@ -1866,6 +1866,7 @@ static void cw_free(Ctx *c) {
 // starts from the row's own block (or zero) and subtracts the products in the row's pattern order.
 constexpr int kPairMax = 32;   // entries of an expanded row; more and the tables are not built
 constexpr int kGroupMax = 4;   // levels per group
+constexpr int kInMax = 8;      // dependencies of a row inside its group; more and the tables are not built
 
 // the dependencies of row u on the sweep's side of the diagonal: [*k0, *k1)
 __device__ __forceinline__ void side_range(int lower, const int32_t *__restrict__ rp, const int32_t *__restrict__ dg,
@@ -1939,6 +1940,10 @@ __global__ void k_group_count(int32_t n, const int32_t *__restrict__ pos, const 
     int32_t J[kPairMax], C[kPairMax];
     int nj, nc;
     if (!group_sets(i, G0, lower, inv, rp, ci, dg, levr, src_of_row, J, &nj, C, &nc)) atomicExch(err, 1);
+    int32_t k0, k1, nin = 0;
+    side_range(lower, rp, dg, i, &k0, &k1);
+    for (int32_t k = k0; k < k1; ++k) nin += levr[ci[k]] >= G0 ? 1 : 0;
+    if (nin > kInMax) atomicExch(err, 1);
     mcnt[t] = nj;
     ccnt[t] = nc;
 }
@@ -2004,6 +2009,19 @@ __global__ void k_group_fill(int32_t n, const int32_t *__restrict__ pos, const i
         while (q >= 0 && J[q] > v) { J[q + 1] = J[q]; --q; }
         J[q + 1] = v;
     }
+    // the factors F_ik of the dependencies inside the group, in pattern order (at most kInMax, which
+    // the counting pass checked), each formed once
+    int32_t tin[kInMax], sin[kInMax];
+    double fin[kInMax][BB];
+    int nin = 0;
+    for (int32_t k = k0; k < k1 && nin < kInMax; ++k) {
+        const int32_t cc = ci[k];
+        if (levr[cc] < G0) continue;
+        tin[nin] = inv[cc];
+        sin[nin] = src_of_row ? src_of_row[cc] : cc;
+        group_factor<B>(LU, k, dg[cc], !lower, fin[nin]);
+        ++nin;
+    }
     const int32_t mo = moff[t], co = coff[t];
     for (int q = 0; q < nj; ++q) {
         const int32_t j = J[q];
@@ -2012,16 +2030,10 @@ __global__ void k_group_fill(int32_t n, const int32_t *__restrict__ pos, const i
         for (int32_t k = k0; k < k1; ++k)   // the row's own block of an outside dependency
             if (levr[ci[k]] < G0 && inv[ci[k]] == j)
                 for (int e = 0; e < BB; ++e) m[e] = LU[(int64_t)k * BB + e];
-        for (int32_t k = k0; k < k1; ++k) {   // minus F_ik M_kj over the dependencies inside the group
-            const int32_t cc = ci[k];
-            if (levr[cc] < G0) continue;
-            const int32_t tk = inv[cc], o1 = moff[tk] + mcnt[tk];
-            for (int32_t o = moff[tk]; o < o1; ++o) {
-                if (mdep[o] != j) continue;
-                double f[BB];
-                group_factor<B>(LU, k, dg[cc], !lower, f);
-                sub_product<B>(m, f, mblk + (int64_t)o * BB);
-            }
+        for (int a = 0; a < nin; ++a) {   // minus F_ik M_kj over the dependencies inside the group
+            const int32_t tk = tin[a], o1 = moff[tk] + mcnt[tk];
+            for (int32_t o = moff[tk]; o < o1; ++o)
+                if (mdep[o] == j) sub_product<B>(m, fin[a], mblk + (int64_t)o * BB);
         }
         mdep[mo + q] = j;
         for (int e = 0; e < BB; ++e) mblk[(int64_t)(mo + q) * BB + e] = m[e];
@@ -2030,21 +2042,13 @@ __global__ void k_group_fill(int32_t n, const int32_t *__restrict__ pos, const i
         const int32_t l = C[q];
         double w[BB];
         for (int e = 0; e < BB; ++e) w[e] = 0.0;
-        for (int32_t k = k0; k < k1; ++k) {   // F_il for a direct dependency inside the group
-            const int32_t cc = ci[k];
-            if (levr[cc] < G0 || (src_of_row ? src_of_row[cc] : cc) != l) continue;
-            group_factor<B>(LU, k, dg[cc], !lower, w);
-        }
-        for (int32_t k = k0; k < k1; ++k) {   // minus F_ik W_kl
-            const int32_t cc = ci[k];
-            if (levr[cc] < G0) continue;
-            const int32_t tk = inv[cc], o1 = coff[tk] + ccnt[tk];
-            for (int32_t o = coff[tk]; o < o1; ++o) {
-                if (cdep[o] != l) continue;
-                double f[BB];
-                group_factor<B>(LU, k, dg[cc], !lower, f);
-                sub_product<B>(w, f, cblk + (int64_t)o * BB);
-            }
+        for (int a = 0; a < nin; ++a)   // F_il for a direct dependency inside the group
+            if (sin[a] == l)
+                for (int e = 0; e < BB; ++e) w[e] = fin[a][e];
+        for (int a = 0; a < nin; ++a) {   // minus F_ik W_kl
+            const int32_t tk = tin[a], o1 = coff[tk] + ccnt[tk];
+            for (int32_t o = coff[tk]; o < o1; ++o)
+                if (cdep[o] == l) sub_product<B>(w, fin[a], cblk + (int64_t)o * BB);
         }
         cdep[co + q] = l;
         for (int e = 0; e < BB; ++e) cblk[(int64_t)(co + q) * BB + e] = w[e];
@@ -2122,11 +2126,15 @@ static cptr_status pair_table(Ctx *c, bool lower, int G, const int32_t *pos, con
     (k_group_count<<<nblk(n, 128), 128, 0, s>>>(n, pos, inv, c->ilu_rp, c->ilu_ci, c->ilu_diag, levr, lower ? 1 : 0, G,
                                                 src_of_row, mcnt, ccnt, err),
      note_launch());
-    int32_t mtot = 0, ctot = 0, h_err = 0;
-    CPTR_TRY(scan_exclusive(c, mcnt, moff, n, &mtot));
-    CPTR_TRY(scan_exclusive(c, ccnt, coffc, n, &ctot));
-    CPTR_TRY(copy_to_host(c, &h_err, err, sizeof(int32_t)));
-    *ok = !h_err;
+    CPTR_TRY(scan_exclusive(c, mcnt, moff, n, nullptr));
+    CPTR_TRY(scan_exclusive(c, ccnt, coffc, n, nullptr));
+    int32_t rd[3] = {0, 0, 0};   // both totals and the overflow flag, one synchronisation
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(&rd[0], moff + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(&rd[1], coffc + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CPTR_CUDA_TRY(c, cudaMemcpyAsync(&rd[2], err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CPTR_CUDA_TRY(c, cudaStreamSynchronize(s));
+    const int32_t mtot = rd[0], ctot = rd[1];
+    *ok = !rd[2];
     if (*ok) {
         int32_t *mdep = nullptr, *cdep = nullptr;
         double *mblk = nullptr, *cblk = nullptr;
@@ -2146,8 +2154,7 @@ static cptr_status pair_table(Ctx *c, bool lower, int G, const int32_t *pos, con
         }
         CPTR_TRY(csr_to_sell(c, mcnt, moff, mdep, mblk, off, col, val));
         CPTR_TRY(csr_to_sell(c, ccnt, coffc, cdep, cblk, coff, ccol, cval));
-        CPTR_CUDA_TRY(c, cudaStreamSynchronize(s));
-        dfree(mdep); dfree(cdep); dfree(mblk); dfree(cblk);
+        dfree(mdep); dfree(cdep); dfree(mblk); dfree(cblk);   // (stream-ordered frees)
     }
     dfree(mcnt); dfree(ccnt); dfree(moff); dfree(coffc); dfree(err);
     return CPTR_OK;
@@ -2878,19 +2885,36 @@ cptr_status ilu_autotune(Ctx *c) {
     int sched = c->sp_use ? 2 : 0;
     int group = c->sp_use ? c->sp_group : 0;
     // the other schedules, each at its own best grid and back-off; the fastest is kept
-    // (grouped levels are timed with the group size built at set-up: groups of three were measured
-    // to cost more set-up time than their sweeps save, so they are used only when asked for)
+    // grouped levels: groups of two (the tables built at set-up) and, unless the caller fixed the
+    // group size, of three (tables rebuilt for the timing), each over 4, 8 and 16 lanes per row.
+    // Groups of three cost more set-up (their tables hold products of three factor blocks), so
+    // they are kept only when their sweeps are at least 5% faster than the best so far.
     if (auto_sched && c->sp_ok) {
-        c->sp_use = true;
-        for (int hf : {1, 2, 4}) {
-            if (fixed_half && hf != fixed_half) continue;
-            c->sf_half = hf;
-            int g = best_g, sl = best_s;
-            const float ms = search(&g, &sl);
-            if (ms < best_ms) { best_ms = ms; best_g = g; best_s = sl; sched = 2; group = c->sp_group; best_half = hf; }
+        const int g0 = c->sp_group;
+        const int ng = (c->o.ilu_group >= 2 || g0 == 3) ? 1 : 2;
+        int bgroup = 0;
+        for (int gi = 0; gi < ng; ++gi) {
+            const int G = gi == 0 ? g0 : 3;
+            if (gi > 0) {
+                CPTR_TRY(pair_setup(c, G));
+                if (!c->sp_ok) break;
+            }
+            const float need = G == g0 ? 1.0f : 0.95f;
+            c->sp_use = true;
+            for (int hf : {1, 2, 4}) {
+                if (fixed_half && hf != fixed_half) continue;
+                c->sf_half = hf;
+                int g = best_g, sl = best_s;
+                const float ms = search(&g, &sl);
+                if (ms < need * best_ms) {
+                    best_ms = ms; best_g = g; best_s = sl; sched = 2; group = G; best_half = hf; bgroup = G;
+                }
+            }
+            c->sf_half = 1;
+            c->sp_use = false;
         }
-        c->sf_half = 1;
-        c->sp_use = false;
+        const int keep = bgroup ? bgroup : g0;
+        if (c->sp_group != keep || !c->sp_ok) CPTR_TRY(pair_setup(c, keep));
     }
     if (auto_sched && c->cw_ok) {   // one block per chunk: only the back-off matters
         c->cw_use = true;
