@@ -1283,7 +1283,7 @@ __global__ void __launch_bounds__(kSfThreads) k_bilu_factor_g(int32_t n, unsigne
                 bool p = false;   // the four lanes of the row poll a quarter of the flags each
                 for (int32_t k = r; k < nd; k += G) {
                     int32_t f;
-                    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flag + cols[k]) : "memory");
+                    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flag + cols[k]) : "memory");
                     p |= f != epoch;
                 }
                 p = __any_sync(gmask, p);
@@ -1303,9 +1303,8 @@ __global__ void __launch_bounds__(kSfThreads) k_bilu_factor_g(int32_t n, unsigne
                     }
                 }
                 if (!p) {
-                    // each lane's acquire fence orders what follows after the flags it read; the
-                    // warp barrier then orders every lane's copies after all four lanes' fences
-                    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                    // each lane's acquire loads order what follows after the flags it read; the warp
+                    // barrier then orders every lane's copies after all four lanes' acquires
                     __syncwarp(gmask);
                     for (int32_t k = 0; k < nd; ++k) {
                         const int64_t lo = (int64_t)dcs[k] * BB, hi = (int64_t)ecs[k] * BB;
@@ -1355,7 +1354,8 @@ __global__ void __launch_bounds__(kSfThreads) k_bilu_factor_g(int32_t n, unsigne
                     if (!group_inverse<B>(rowb + nd * BB, r, gmask, g0) && r == 0) atomicOr(singular, 1);
                     __syncwarp(gmask);
                     for (int32_t u = nd * BB + r; u < len * BB; u += G) LU[(int64_t)k0 * BB + u] = rowb[u];
-                    __threadfence();
+                    // the warp barrier orders the four lanes' stores before lane 0's release store,
+                    // which publishes them all (release is cumulative)
                     __syncwarp(gmask);
                     if (r == 0) asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(flag + i), "r"(epoch) : "memory");
                     for (int32_t u = r; u < nd * BB; u += G) LU[(int64_t)k0 * BB + u] = rowb[u];
@@ -1436,7 +1436,7 @@ __global__ void __launch_bounds__(32 * kFwWarps) k_bilu_factor_w(int32_t n, unsi
             bool p = false;
             for (int32_t k = lane; k < nd; k += 32) {
                 int32_t f;
-                asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flag + cols[k]) : "memory");
+                asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flag + cols[k]) : "memory");
                 p |= f != epoch;
             }
             if (!__any_sync(kAll, p)) break;
@@ -1453,7 +1453,8 @@ __global__ void __launch_bounds__(32 * kFwWarps) k_bilu_factor_w(int32_t n, unsi
             }
             __nanosleep(20);
         }
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        // each lane's acquire loads order its later reads after the flags it saw; the warp barrier
+        // orders every lane's reads after all lanes' acquires
         __syncwarp();
         for (int32_t k = 0; k < nd; ++k) {
             const int64_t lo = (int64_t)dcs[k] * BB, hi = (int64_t)ecs[k] * BB;
@@ -1501,7 +1502,8 @@ __global__ void __launch_bounds__(32 * kFwWarps) k_bilu_factor_w(int32_t n, unsi
         }
         __syncwarp();
         for (int32_t u = nd * BB + lane; u < len * BB; u += 32) LU[(int64_t)k0 * BB + u] = rowb[u];
-        __threadfence();
+        // the warp barrier orders every lane's stores before lane 0's release store, which
+        // publishes them all (release is cumulative)
         __syncwarp();
         if (lane == 0) asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(flag + i), "r"(epoch) : "memory");
         for (int32_t u = lane; u < nd * BB; u += 32) LU[(int64_t)k0 * BB + u] = rowb[u];
