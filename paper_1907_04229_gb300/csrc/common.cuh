@@ -312,6 +312,18 @@ struct IluSym {
     TileTables tt[2];                            // its sizes, with tlev and lptr owned here (rec unused)
     int32_t *hdr[2] = {}, *kidx[2] = {};
     size_t tlev_n[2] = {}, lptr_n[2] = {};
+    // the structure of the grouped-level tables of both sweeps for one group size (grp): entry
+    // counts and offsets per position, dependency positions and right-hand-side sources, and the
+    // SELL layout (chunk offsets, slot columns, slot -> entry index) of the M and W tables
+    struct GroupDir {
+        int32_t *mcnt = nullptr, *ccnt = nullptr, *moff = nullptr, *coff = nullptr, *mdep = nullptr, *cdep = nullptr;
+        int32_t mtot = 0, ctot = 0;
+        int64_t *off[2] = {};
+        int32_t *col[2] = {}, *kidx[2] = {};
+        int64_t ns[2] = {};
+    };
+    int grp = 0;
+    GroupDir gd[2];
 };
 
 // ---- the context -------------------------------------------------------------------------------

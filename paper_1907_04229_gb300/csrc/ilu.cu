@@ -2075,12 +2075,13 @@ __global__ void k_fill_sell_csr(int32_t n, const int32_t *cnt, const int32_t *cs
         kidx[u] = csr_off[t] + e;
     }
 }
-static cptr_status csr_to_sell(Ctx *c, const int32_t *cnt, const int32_t *csr_off, const int32_t *dep,
-                               const double *blk, int64_t **off64, int32_t **col, void **val) {
-    const bool lo = c->o.precision == CPTR_PREC_MIXED;   // blocks stored in FP32
-    const int32_t n = c->n, nch = (n + 31) / 32, BB = c->b * c->b;
+// SELL-32 layout of per-position entry lists: chunk offsets, the column of every slot and its
+// entry index in the lists (-1 for padding); *ns_out slots in all
+static cptr_status sell_layout(Ctx *c, const int32_t *cnt, const int32_t *csr_off, const int32_t *dep,
+                               int64_t **off64, int32_t **col, int32_t **kidx, int64_t *ns_out) {
+    const int32_t n = c->n, nch = (n + 31) / 32;
     cudaStream_t s = c->stream;
-    int32_t *w = nullptr, *off = nullptr, *kidx = nullptr;
+    int32_t *w = nullptr, *off = nullptr;
     CPTR_TRY(dalloc_t(c, &w, (size_t)nch + 1));
     CPTR_TRY(dalloc_t(c, &off, (size_t)nch + 1));
     (k_chunk_width_cnt<<<nblk((int64_t)nch * 32, 256), 256, 0, s>>>(n, cnt, w), note_launch());
@@ -2090,15 +2091,30 @@ static cptr_status csr_to_sell(Ctx *c, const int32_t *cnt, const int32_t *csr_of
     (k_widen<<<nblk(nch + 1, 256), 256, 0, s>>>(nch, off, *off64), note_launch());
     const int64_t ns = (int64_t)total * 32;
     CPTR_TRY(dalloc_t(c, col, (size_t)(ns > 0 ? ns : 1)));
-    CPTR_TRY(dalloc_t(c, &kidx, (size_t)(ns > 0 ? ns : 1)));
-    CPTR_TRY(dalloc(c, val, (size_t)(ns > 0 ? ns : 1) * BB * (lo ? 4 : 8)));
+    CPTR_TRY(dalloc_t(c, kidx, (size_t)(ns > 0 ? ns : 1)));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(*col, 0xFF, sizeof(int32_t) * (ns > 0 ? ns : 1), s));
-    CPTR_CUDA_TRY(c, cudaMemsetAsync(kidx, 0xFF, sizeof(int32_t) * (ns > 0 ? ns : 1), s));
-    (k_fill_sell_csr<<<nblk(n, 256), 256, 0, s>>>(n, cnt, csr_off, dep, off, *col, kidx), note_launch());
+    CPTR_CUDA_TRY(c, cudaMemsetAsync(*kidx, 0xFF, sizeof(int32_t) * (ns > 0 ? ns : 1), s));
+    (k_fill_sell_csr<<<nblk(n, 256), 256, 0, s>>>(n, cnt, csr_off, dep, off, *col, *kidx), note_launch());
+    CPTR_CUDA_TRY(c, cudaGetLastError());
+    dfree(w); dfree(off);
+    *ns_out = ns;
+    return CPTR_OK;
+}
+// the slots' blocks, in the sweeps' precision
+static cptr_status sell_pack(Ctx *c, const int32_t *kidx, int64_t ns, const double *blk, void **val) {
+    const bool lo = c->o.precision == CPTR_PREC_MIXED;   // blocks stored in FP32
+    const int BB = c->b * c->b;
+    cudaStream_t s = c->stream;
+    CPTR_TRY(dalloc(c, val, (size_t)(ns > 0 ? ns : 1) * BB * (lo ? 4 : 8)));
     if (ns > 0 && lo) (k_sf_pack<float><<<nblk(ns, 256), 256, 0, s>>>(ns, BB, kidx, blk, (float *)*val), note_launch());
     else if (ns > 0) (k_sf_pack<double><<<nblk(ns, 256), 256, 0, s>>>(ns, BB, kidx, blk, (double *)*val), note_launch());
     CPTR_CUDA_TRY(c, cudaGetLastError());
-    dfree(w); dfree(off); dfree(kidx);
+    return CPTR_OK;
+}
+template <typename I>
+static cptr_status dcopy(Ctx *c, I **dst, const I *src, size_t count) {
+    CPTR_TRY(dalloc_t(c, dst, count > 0 ? count : 1));
+    if (count) CPTR_CUDA_TRY(c, cudaMemcpyAsync(*dst, src, sizeof(I) * count, cudaMemcpyDeviceToDevice, c->stream));
     return CPTR_OK;
 }
 
@@ -2116,32 +2132,48 @@ static void pair_free(Ctx *c) {
 static cptr_status pair_table(Ctx *c, bool lower, int G, const int32_t *pos, const int32_t *inv, const int32_t *levr,
                               const int32_t *src_of_row, int64_t **off, int32_t **col, void **val, int64_t **coff,
                               int32_t **ccol, void **cval, bool *ok) {
-    const int32_t n = c->n, BB = c->b * c->b;
+    const int32_t n = c->n, nch = (n + 31) / 32, BB = c->b * c->b;
     cudaStream_t s = c->stream;
-    int32_t *mcnt = nullptr, *ccnt = nullptr, *moff = nullptr, *coffc = nullptr, *err = nullptr;
-    CPTR_TRY(dalloc_t(c, &mcnt, (size_t)n + 1));
-    CPTR_TRY(dalloc_t(c, &ccnt, (size_t)n + 1));
-    CPTR_TRY(dalloc_t(c, &moff, (size_t)n + 1));
-    CPTR_TRY(dalloc_t(c, &coffc, (size_t)n + 1));
-    CPTR_TRY(dalloc_t(c, &err, 1));
-    CPTR_CUDA_TRY(c, cudaMemsetAsync(err, 0, sizeof(int32_t), s));
-    (k_group_count<<<nblk(n, 128), 128, 0, s>>>(n, pos, inv, c->ilu_rp, c->ilu_ci, c->ilu_diag, levr, lower ? 1 : 0, G,
-                                                src_of_row, mcnt, ccnt, err),
-     note_launch());
-    CPTR_TRY(scan_exclusive(c, mcnt, moff, n, nullptr));
-    CPTR_TRY(scan_exclusive(c, ccnt, coffc, n, nullptr));
-    int32_t rd[3] = {0, 0, 0};   // both totals and the overflow flag, one synchronisation
-    CPTR_CUDA_TRY(c, cudaMemcpyAsync(&rd[0], moff + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    CPTR_CUDA_TRY(c, cudaMemcpyAsync(&rd[1], coffc + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    CPTR_CUDA_TRY(c, cudaMemcpyAsync(&rd[2], err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    CPTR_CUDA_TRY(c, cudaStreamSynchronize(s));
-    const int32_t mtot = rd[0], ctot = rd[1];
-    *ok = !rd[2];
+    // the structure of a set-up of the same pattern with the same group size, if kept
+    IluSym &ys = c->isym;
+    IluSym::GroupDir *gd = ys.current ? &ys.gd[lower ? 0 : 1] : nullptr;
+    const bool cached = gd && ys.grp == G && gd->mcnt;
+    int32_t *mcnt = nullptr, *ccnt = nullptr, *moff = nullptr, *coffc = nullptr, *mdep = nullptr, *cdep = nullptr;
+    int32_t mtot = 0, ctot = 0;
+    if (cached) {
+        mcnt = gd->mcnt; ccnt = gd->ccnt; moff = gd->moff; coffc = gd->coff; mdep = gd->mdep; cdep = gd->cdep;
+        mtot = gd->mtot;
+        ctot = gd->ctot;
+        *ok = true;
+    } else {
+        int32_t *err = nullptr;
+        CPTR_TRY(dalloc_t(c, &mcnt, (size_t)n + 1));
+        CPTR_TRY(dalloc_t(c, &ccnt, (size_t)n + 1));
+        CPTR_TRY(dalloc_t(c, &moff, (size_t)n + 1));
+        CPTR_TRY(dalloc_t(c, &coffc, (size_t)n + 1));
+        CPTR_TRY(dalloc_t(c, &err, 1));
+        CPTR_CUDA_TRY(c, cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+        (k_group_count<<<nblk(n, 128), 128, 0, s>>>(n, pos, inv, c->ilu_rp, c->ilu_ci, c->ilu_diag, levr, lower ? 1 : 0,
+                                                    G, src_of_row, mcnt, ccnt, err),
+         note_launch());
+        CPTR_TRY(scan_exclusive(c, mcnt, moff, n, nullptr));
+        CPTR_TRY(scan_exclusive(c, ccnt, coffc, n, nullptr));
+        int32_t rd[3] = {0, 0, 0};   // both totals and the overflow flag, one synchronisation
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(&rd[0], moff + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(&rd[1], coffc + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CPTR_CUDA_TRY(c, cudaMemcpyAsync(&rd[2], err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CPTR_CUDA_TRY(c, cudaStreamSynchronize(s));
+        dfree(err);
+        mtot = rd[0];
+        ctot = rd[1];
+        *ok = !rd[2];
+        if (*ok) {
+            CPTR_TRY(dalloc_t(c, &mdep, (size_t)(mtot > 0 ? mtot : 1)));
+            CPTR_TRY(dalloc_t(c, &cdep, (size_t)(ctot > 0 ? ctot : 1)));
+        }
+    }
     if (*ok) {
-        int32_t *mdep = nullptr, *cdep = nullptr;
         double *mblk = nullptr, *cblk = nullptr;
-        CPTR_TRY(dalloc_t(c, &mdep, (size_t)(mtot > 0 ? mtot : 1)));
-        CPTR_TRY(dalloc_t(c, &cdep, (size_t)(ctot > 0 ? ctot : 1)));
         CPTR_TRY(dalloc_t(c, &mblk, (size_t)(mtot > 0 ? mtot : 1) * BB));
         CPTR_TRY(dalloc_t(c, &cblk, (size_t)(ctot > 0 ? ctot : 1) * BB));
         for (int p = 0; p < G; ++p) {   // one pass per position in the group: earlier positions first
@@ -2154,11 +2186,44 @@ static cptr_status pair_table(Ctx *c, bool lower, int G, const int32_t *pos, con
             if (c->b == 3) fill(k_group_fill<3>);
             else fill(k_group_fill<4>);
         }
-        CPTR_TRY(csr_to_sell(c, mcnt, moff, mdep, mblk, off, col, val));
-        CPTR_TRY(csr_to_sell(c, ccnt, coffc, cdep, cblk, coff, ccol, cval));
-        dfree(mdep); dfree(cdep); dfree(mblk); dfree(cblk);   // (stream-ordered frees)
+        if (cached) {   // the kept SELL layouts, values packed anew
+            CPTR_TRY(dcopy(c, off, gd->off[0], (size_t)nch + 1));
+            CPTR_TRY(dcopy(c, col, gd->col[0], (size_t)gd->ns[0]));
+            CPTR_TRY(dcopy(c, coff, gd->off[1], (size_t)nch + 1));
+            CPTR_TRY(dcopy(c, ccol, gd->col[1], (size_t)gd->ns[1]));
+            CPTR_TRY(sell_pack(c, gd->kidx[0], gd->ns[0], mblk, val));
+            CPTR_TRY(sell_pack(c, gd->kidx[1], gd->ns[1], cblk, cval));
+        } else {
+            int32_t *kidx[2] = {};
+            int64_t ns[2] = {};
+            CPTR_TRY(sell_layout(c, mcnt, moff, mdep, off, col, &kidx[0], &ns[0]));
+            CPTR_TRY(sell_layout(c, ccnt, coffc, cdep, coff, ccol, &kidx[1], &ns[1]));
+            CPTR_TRY(sell_pack(c, kidx[0], ns[0], mblk, val));
+            CPTR_TRY(sell_pack(c, kidx[1], ns[1], cblk, cval));
+            if (gd) {   // kept for the next set-up of this pattern (group size recorded by the caller)
+                IluSym::GroupDir &g = *gd;
+                dfree(g.mcnt); dfree(g.ccnt); dfree(g.moff); dfree(g.coff); dfree(g.mdep); dfree(g.cdep);
+                for (int t = 0; t < 2; ++t) { dfree(g.off[t]); dfree(g.col[t]); dfree(g.kidx[t]); }
+                g = IluSym::GroupDir();
+                g.mcnt = mcnt; g.ccnt = ccnt; g.moff = moff; g.coff = coffc; g.mdep = mdep; g.cdep = cdep;
+                g.mtot = mtot;
+                g.ctot = ctot;
+                CPTR_TRY(dcopy(c, &g.off[0], *off, (size_t)nch + 1));
+                CPTR_TRY(dcopy(c, &g.col[0], *col, (size_t)ns[0]));
+                CPTR_TRY(dcopy(c, &g.off[1], *coff, (size_t)nch + 1));
+                CPTR_TRY(dcopy(c, &g.col[1], *ccol, (size_t)ns[1]));
+                g.kidx[0] = kidx[0];
+                g.kidx[1] = kidx[1];
+                g.ns[0] = ns[0];
+                g.ns[1] = ns[1];
+                mcnt = ccnt = moff = coffc = mdep = cdep = nullptr;   // owned by the cache now
+            } else {
+                dfree(kidx[0]); dfree(kidx[1]);
+            }
+        }
+        dfree(mblk); dfree(cblk);   // (stream-ordered frees)
     }
-    dfree(mcnt); dfree(ccnt); dfree(moff); dfree(coffc); dfree(err);
+    if (!cached) { dfree(mcnt); dfree(ccnt); dfree(moff); dfree(coffc); dfree(mdep); dfree(cdep); }
     return CPTR_OK;
 }
 
@@ -2167,6 +2232,9 @@ static cptr_status pair_table(Ctx *c, bool lower, int G, const int32_t *pos, con
 // dropped first.
 static cptr_status pair_setup(Ctx *c, int G) {
     pair_free(c);
+    // a kept structure of another group size is replaced direction by direction below: until both
+    // are built it belongs to no group size
+    if (c->isym.grp != G) c->isym.grp = 0;
     bool okf = false, okb = false;
     CPTR_TRY(pair_table(c, true, G, c->lvl_f, c->sp_inv_f, c->sp_levr_f, c->ilu_rowmap, &c->sp_off_f, &c->sp_col_f,
                         &c->sp_val_f, &c->sp_coff_f, &c->sp_ccol_f, &c->sp_cval_f, &okf));
@@ -2175,6 +2243,7 @@ static cptr_status pair_setup(Ctx *c, int G) {
                             &c->sp_val_b, &c->sp_coff_b, &c->sp_ccol_b, &c->sp_cval_b, &okb));
     c->sp_ok = okf && okb;
     c->sp_group = c->sp_ok ? G : 0;
+    if (c->isym.current) c->isym.grp = c->sp_ok ? G : 0;   // the kept structure's group size (both sweeps)
     if (!c->sp_ok) pair_free(c);
     return CPTR_OK;
 }
@@ -2297,6 +2366,9 @@ void ilu_sym_free(Ctx *c) {
     for (int d = 0; d < 2; ++d) {
         dfree(y.lvl[d]); dfree(y.inv[d]); dfree(y.levr[d]);
         dfree(y.tt[d].tlev); dfree(y.tt[d].lptr); dfree(y.hdr[d]); dfree(y.kidx[d]);
+        IluSym::GroupDir &g = y.gd[d];
+        dfree(g.mcnt); dfree(g.ccnt); dfree(g.moff); dfree(g.coff); dfree(g.mdep); dfree(g.cdep);
+        for (int t = 0; t < 2; ++t) { dfree(g.off[t]); dfree(g.col[t]); dfree(g.kidx[t]); }
     }
     y = IluSym();
 }

@@ -900,20 +900,22 @@ def test_non_finite_rhs_reports_ebreakdown_and_context_recovers():
 
 # ------------------------------------------------------------------------------------------------
 # set-ups of the same pattern with new values (Newton iterations, time steps): the context keeps the
-# pattern-only ILU tables (level sets, tile structure) and rebuilds everything that holds values
+# pattern-only ILU tables (level sets, tile structure, the grouped-level tables' structure) and
+# rebuilds everything that holds values
 def _setup_again(S, s, vals):
     S.setup(s["n"], s["b"], dev(s["row_ptr"]), dev(s["col_idx"]), dev(vals.reshape(-1)), dev(s["unknown_kind"]),
             dev(s["weights"].reshape(-1)), dev(s["st"]))
 
 
-@pytest.mark.parametrize("sweep", ["levels", "paired", "tiled"])
+@pytest.mark.parametrize("sweep", ["levels", "paired", "grouped3", "tiled"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_set_up_again_with_the_same_pattern_or_another(sweep, precision):
     """A context set up before, then set up with new values on the same pattern, and then with a
     different pattern of the same size (an 8 x 6 x 4 box against a 6 x 8 x 4 one: same cell count,
     same block count), gives bit for bit what a fresh context gives each time: ILU applications
     and solves."""
-    o = dict(ilu_sweep=cp.ILU_SWEEP[sweep], precision=cp.PRECISION[precision], n_coarse=16)
+    o = dict(ilu_sweep=cp.ILU_SWEEP[sweep.replace("grouped3", "paired")], precision=cp.PRECISION[precision],
+             n_coarse=16, **(dict(ilu_group=3, ilu_lanes=8) if sweep == "grouped3" else {}))
     s1 = synth.make_box(8, 6, 4, 3.125, seed=23, heaters=[(11, 80.0, 420.0)]).system()
     s2 = synth.make_box(6, 8, 4, 3.125, seed=24, heaters=[(13, 80.0, 420.0)]).system()
     assert s1["n"] == s2["n"] and s1["row_ptr"][-1] == s2["row_ptr"][-1]
