@@ -1,7 +1,8 @@
 """The bounds-checking build (libcptr_check.so, compiled with -DCPTR_CHECK): every index that a
 hot-path kernel reads from a table is checked against its array. A failed check is recorded, the
 access is skipped, and the call returns CPTR_ECHECK. Here the check build runs the configurations
-of the parity tests: FP64 and mixed precision, level-set, paired and tiled sweeps, multicolour
+of the parity tests: FP64 and mixed precision, level-set, grouped-level (pairs and groups of three,
+four to sixteen lanes per row) and tiled sweeps, multicolour
 order, ILU(1), the unknown-based first stage, CPR, b = 4, and an ensemble. Every call must return
 without a failed check, and the solves must match the oracle as in the parity tests.
 
@@ -19,6 +20,8 @@ CASES = [
     ("ragged", dict(max_levels=3, n_coarse=8)),
     ("ragged", dict(max_levels=3, n_coarse=8, precision=1)),
     ("medium", dict(ilu_sweep=3)),
+    ("medium", dict(ilu_sweep=3, ilu_group=3, ilu_lanes=8)),
+    ("medium", dict(ilu_sweep=3, ilu_lanes=16)),
     ("medium", dict(ilu_sweep=4, tile_y=2, tile_z=2)),
     ("medium", dict(ilu_sweep=2)),
     ("medium", dict(ilu_order=1)),
@@ -27,6 +30,7 @@ CASES = [
     ("medium", dict(stage1=4)),
     ("three_phase", dict(n_coarse=16)),
     ("three_phase", dict(n_coarse=16, precision=1, ilu_sweep=3)),
+    ("three_phase", dict(n_coarse=16, precision=1, ilu_sweep=3, ilu_group=3, ilu_lanes=8)),
 ]
 
 
