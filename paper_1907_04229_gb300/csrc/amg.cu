@@ -73,9 +73,11 @@ __global__ void k_strength_fill(int32_t n, const int32_t *rp, const int32_t *ci,
 }
 
 // pattern transpose helpers
-__global__ void k_count_cols(int32_t nnz, const int32_t *ci, int32_t *cnt) {
+// cnt[j] += number of entries of column j among ci[0, nnz) (nnz_dev: the count in device memory
+// instead, for a launch sized by an upper bound)
+__global__ void k_count_cols(int32_t nnz, const int32_t *ci, int32_t *cnt, const int32_t *nnz_dev = nullptr) {
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < nnz) atomicAdd(cnt + ci[k], 1);
+    if (k < (nnz_dev ? *nnz_dev : nnz)) atomicAdd(cnt + ci[k], 1);
 }
 __global__ void k_fill_transpose(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, const int32_t *Trp,
                                  int32_t *cursor, int32_t *Tci, double *Tv) {
@@ -686,16 +688,18 @@ static cptr_status coarsen(Ctx *c, Level &L, int lev, int32_t *nc_out, int32_t *
     CPTR_TRY(dalloc_t(c, &cnt, (size_t)n + 1));
     CPTR_TRY(dalloc_t(c, &Srp, (size_t)n + 1));
     (k_strength_count<<<nblk(n, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, c->o.theta, cnt, L.fn), note_launch());
-    int32_t nnzS = 0;
-    CPTR_TRY(scan_exclusive(c, cnt, Srp, n, &nnzS));
-    CPTR_TRY(dalloc_t(c, &Sci, (size_t)nnzS));
-    CPTR_TRY(dalloc_t(c, &Spos, (size_t)nnzS));
+    // the strength matrix S has at most A's entries: its arrays are allocated by that bound and its
+    // entry count stays on the device (Srp[n]), so no host synchronisation is needed here
+    CPTR_TRY(scan_exclusive(c, cnt, Srp, n, nullptr));
+    const int32_t nnzS_max = A.nnz;
+    CPTR_TRY(dalloc_t(c, &Sci, (size_t)nnzS_max));
+    CPTR_TRY(dalloc_t(c, &Spos, (size_t)nnzS_max));
     (k_strength_fill<<<nblk(n, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, c->o.theta, Srp, Sci, Spos, L.fn), note_launch());
     // S^T pattern (neighbour sets; order irrelevant)
     CPTR_TRY(dalloc_t(c, &Trp, (size_t)n + 1));
-    CPTR_TRY(dalloc_t(c, &Tci, (size_t)nnzS));
+    CPTR_TRY(dalloc_t(c, &Tci, (size_t)nnzS_max));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)n + 1), s));
-    (k_count_cols<<<nblk(nnzS, 256), 256, 0, s>>>(nnzS, Sci, cnt), note_launch());
+    (k_count_cols<<<nblk(nnzS_max, 256), 256, 0, s>>>(nnzS_max, Sci, cnt, Srp + n), note_launch());
     CPTR_TRY(scan_exclusive(c, cnt, Trp, n, nullptr));
     CPTR_CUDA_TRY(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)n + 1), s));
     (k_fill_transpose<<<nblk(n, 256), 256, 0, s>>>(n, Srp, Sci, nullptr, Trp, cnt, Tci, nullptr), note_launch());
