@@ -471,7 +471,9 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_g(int32_t n, unsigned *t
     }
 }
 
-template <int B, typename T, typename XT, int DG>
+// FOLD: the tables' blocks carry the row's inverted pivot (grouped-level backward tables): the row
+// starts from D^{-1} y and its sum is the result; otherwise D^{-1} is applied to the sum at the end
+template <int B, typename T, typename XT, int DG, bool FOLD = false>
 __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_g(int32_t n, unsigned *ticket, const int32_t *__restrict__ pos,
                                                          const int32_t *__restrict__ bmap,
                                                          const int64_t *__restrict__ off, const int32_t *__restrict__ col,
@@ -506,12 +508,19 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_g(int32_t n, unsigned *t
             row = __ldg(pos + t);
             if (dp && q4 == ps) add = (double)dp[row];
             if (dT && q4 == ts) add = (double)dT[row];
-            L.s = __ldcg(y + (int64_t)__ldg(bmap + t) * B + q4);
-            L.s = pair_terms<B, T, T>(L.s, q4, ch, lane, coff, ccol, cval, y, n);
-            L.nrows = n;
             // row q4 of the inverted pivot block does not depend on other rows: load it first
 #pragma unroll
             for (int q = 0; q < B; ++q) dv[q] = __ldg(dinv + ((int64_t)ch * B * B + q4 * B + q) * 32 + lane);
+            const T *yr = y + (int64_t)__ldg(bmap + t) * B;
+            if (FOLD) {
+                L.s = (T)0;
+#pragma unroll
+                for (int q = 0; q < B; ++q) L.s = fma(dv[q], __ldcg(yr + q), L.s);
+            } else {
+                L.s = __ldcg(yr + q4);
+            }
+            L.s = pair_terms<B, T, T>(L.s, q4, ch, lane, coff, ccol, cval, y, n);
+            L.nrows = n;
             L.sl0 = __ldg(off + ch);
             L.o1 = __ldg(off + ch + 1);
             L.waiting = false;
@@ -521,9 +530,12 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_g(int32_t n, unsigned *t
         while (__any_sync(0xffffffffu, !done)) {
             bool pend = false;
             if (!done && (fin || sweep_round<B, T, DG>(L, q4, lane, gmask, g0, col, val, z, ks, &pend))) {
-                T a = 0;
+                T a = L.s;
+                if (!FOLD) {
+                    a = 0;
 #pragma unroll
-                for (int q = 0; q < B; ++q) a = fma(dv[q], __shfl_sync(gmask, L.s, g0 + q), a);
+                    for (int q = 0; q < B; ++q) a = fma(dv[q], __shfl_sync(gmask, L.s, g0 + q), a);
+                }
                 store_relaxed(z + (int64_t)t * B + q4, a);
                 out[(int64_t)row * B + q4] = (double)a + add;
                 done = true;
@@ -631,15 +643,17 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_h(int32_t n, unsigned *t
         if (!idle) {
             const int32_t ch = t >> 5;
             row = __ldg(pos + t);
-            if (h == 0) {
+            if (h == 0) {   // the tables carry the row's inverted pivot: start from D^{-1} y
                 if (dp && q4 == ps) add = (double)dp[row];
                 if (dT && q4 == ts) add = (double)dT[row];
-                L.s = __ldcg(y + (int64_t)__ldg(bmap + t) * B + q4);
+#pragma unroll
+                for (int q = 0; q < B; ++q) dv[q] = __ldg(dinv + ((int64_t)ch * B * B + q4 * B + q) * 32 + lane);
+                const T *yr = y + (int64_t)__ldg(bmap + t) * B;
+#pragma unroll
+                for (int q = 0; q < B; ++q) L.s = fma(dv[q], __ldcg(yr + q), L.s);
             }
             L.s = pair_terms<B, T, T, H>(L.s, q4, ch, lane, coff, ccol, cval, y, n, h);
             L.nrows = n;
-#pragma unroll
-            for (int q = 0; q < B; ++q) dv[q] = __ldg(dinv + ((int64_t)ch * B * B + q4 * B + q) * 32 + lane);
             L.sl0 = __ldg(off + ch) + h;
             L.o1 = __ldg(off + ch + 1);
             L.waiting = false;
@@ -654,12 +668,9 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_h(int32_t n, unsigned *t
 #pragma unroll
             for (int o = kSfGroup; o < LPR; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
             const bool ready = !done && ((hv >> gr) & RMASK) == RMASK;
-            T a = 0;
-#pragma unroll
-            for (int q = 0; q < B; ++q) a = fma(dv[q], __shfl_sync(0xffffffffu, sum, gr + q), a);
             if (ready && !idle && h == 0) {
-                store_relaxed(z + (int64_t)t * B + q4, a);
-                out[(int64_t)row * B + q4] = (double)a + add;
+                store_relaxed(z + (int64_t)t * B + q4, sum);
+                out[(int64_t)row * B + q4] = (double)sum + add;
             }
             if (ready) done = true;
             if (__any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
@@ -2057,6 +2068,34 @@ __global__ void k_group_fill(int32_t n, const int32_t *__restrict__ pos, const i
     }
 }
 
+// backward tables: every block of the expanded row i (M and W entries) left-multiplied by row i's
+// inverted pivot, z_i = D_i^{-1} y_i - sum_l (D_i^{-1} W_il) y_l - sum_j (D_i^{-1} M_ij) z_j, so that
+// the sweep starts from D_i^{-1} y_i (known before any wait) and needs no product after its waits
+template <int B>
+__global__ void k_group_fold(int32_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ dg,
+                             const double *__restrict__ LU, const int32_t *__restrict__ mcnt,
+                             const int32_t *__restrict__ ccnt, const int32_t *__restrict__ moff,
+                             const int32_t *__restrict__ coff, double *mblk, double *cblk) {
+    constexpr int BB = B * B;
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double *d = LU + (int64_t)dg[pos[t]] * BB;
+    for (int side = 0; side < 2; ++side) {
+        double *blk = side == 0 ? mblk + (int64_t)moff[t] * BB : cblk + (int64_t)coff[t] * BB;
+        const int32_t cnt = side == 0 ? mcnt[t] : ccnt[t];
+        for (int32_t e = 0; e < cnt; ++e, blk += BB) {
+            double m[BB];
+            for (int r = 0; r < B; ++r)
+                for (int q = 0; q < B; ++q) {
+                    double a = 0.0;
+                    for (int u = 0; u < B; ++u) a = fma(d[r * B + u], blk[u * B + q], a);
+                    m[r * B + q] = a;
+                }
+            for (int q = 0; q < BB; ++q) blk[q] = m[q];
+        }
+    }
+}
+
 // SELL-32 tables from per-position entry lists (counts, CSR offsets, dependencies, blocks)
 __global__ void k_chunk_width_cnt(int32_t n, const int32_t *cnt, int32_t *w) {
     int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2185,6 +2224,14 @@ static cptr_status pair_table(Ctx *c, bool lower, int G, const int32_t *pos, con
             };
             if (c->b == 3) fill(k_group_fill<3>);
             else fill(k_group_fill<4>);
+        }
+        if (!lower) {   // the backward blocks with the rows' inverted pivots folded in
+            if (c->b == 3)
+                (k_group_fold<3><<<nblk(n, 128), 128, 0, s>>>(n, pos, c->ilu_diag, c->LU, mcnt, ccnt, moff, coffc, mblk,
+                                                             cblk), note_launch());
+            else
+                (k_group_fold<4><<<nblk(n, 128), 128, 0, s>>>(n, pos, c->ilu_diag, c->LU, mcnt, ccnt, moff, coffc, mblk,
+                                                             cblk), note_launch());
         }
         if (cached) {   // the kept SELL layouts, values packed anew
             CPTR_TRY(dcopy(c, off, gd->off[0], (size_t)nch + 1));
@@ -2826,8 +2873,8 @@ static void sweeps(const Ctx *c, const RT *r, double *z, const XT *dp, const XT 
                  pr ? c->sp_coff_b : nullptr, c->sp_ccol_b, (const T *)c->sp_cval_b),
              note_launch());
         };
-        if (pr && c->sp_group >= 3) bwd(k_ilu_bwd_g<B, T, XT, 12>);
-        else if (pr) bwd(k_ilu_bwd_g<B, T, XT, 8>);
+        if (pr && c->sp_group >= 3) bwd(k_ilu_bwd_g<B, T, XT, 12, true>);
+        else if (pr) bwd(k_ilu_bwd_g<B, T, XT, 8, true>);
         else bwd(k_ilu_bwd_g<B, T, XT, kDepGroup>);
         prof_end(c, pf);
         return;
