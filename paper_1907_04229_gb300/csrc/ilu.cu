@@ -595,11 +595,15 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_h(int32_t n, unsigned *t
             if (!half && sweep_round<B, T, DG, H>(L, q4, lane, gmask, g0, col, val, y, ks, &pend)) half = true;
             // a row is ready once all of its lanes have voted; part 0 stores the parts' sum
             const unsigned hv = __ballot_sync(0xffffffffu, half);
-            T sum = L.s;
-#pragma unroll
-            for (int o = kSfGroup; o < LPR; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
             const bool ready = !done && ((hv >> gr) & RMASK) == RMASK;
-            if (ready && !idle && h == 0) store_relaxed(y + (int64_t)t * B + q4, sum);
+            // the parts' sum only in rounds where a row of the warp is ready: an FP64 add issued by
+            // every polling warp in every round would hold the FP64 pipe the ready rows need
+            if (__any_sync(0xffffffffu, ready)) {
+                T sum = L.s;
+#pragma unroll
+                for (int o = kSfGroup; o < LPR; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                if (ready && !idle && h == 0) store_relaxed(y + (int64_t)t * B + q4, sum);
+            }
             if (ready) done = true;
             if (__any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
         }
@@ -664,13 +668,15 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_h(int32_t n, unsigned *t
             bool pend = false;
             if (!half && sweep_round<B, T, DG, H>(L, q4, lane, gmask, g0, col, val, z, ks, &pend)) half = true;
             const unsigned hv = __ballot_sync(0xffffffffu, half);
-            T sum = L.s;
-#pragma unroll
-            for (int o = kSfGroup; o < LPR; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
             const bool ready = !done && ((hv >> gr) & RMASK) == RMASK;
-            if (ready && !idle && h == 0) {
-                store_relaxed(z + (int64_t)t * B + q4, sum);
-                out[(int64_t)row * B + q4] = (double)sum + add;
+            if (__any_sync(0xffffffffu, ready)) {   // (the parts' sum only when a row is ready)
+                T sum = L.s;
+#pragma unroll
+                for (int o = kSfGroup; o < LPR; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                if (ready && !idle && h == 0) {
+                    store_relaxed(z + (int64_t)t * B + q4, sum);
+                    out[(int64_t)row * B + q4] = (double)sum + add;
+                }
             }
             if (ready) done = true;
             if (__any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);

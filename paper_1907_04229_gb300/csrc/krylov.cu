@@ -70,7 +70,7 @@ __device__ void cgs_finish(KState *ks, const double *res, int fin, int j, int m,
 }
 
 // The element loop of a Gram-Schmidt pass with NQ columns compiled in (NQ = nc rounded up to a
-// multiple of 8, so at most 7 columns are carried as predicated-off work): each element reads w
+// multiple of 4, so at most 3 columns are carried as predicated-off work): each element reads w
 // once, updates it (UPD) and adds its products to the per-column partial sums.
 template <int PASS, int NQ>
 __device__ __forceinline__ void cgs_elements(int64_t i0, int64_t i1, int64_t step, int64_t nb,
@@ -96,20 +96,71 @@ __device__ __forceinline__ void cgs_elements(int64_t i0, int64_t i1, int64_t ste
     }
 }
 
+// Column sums over a warp: every lane holds P = 2^LP partial sums a[0..P); at each of LP halving
+// steps a lane keeps half of its columns and adds its partner's values of them (so a step costs
+// one FP64 add per kept column, not one per column), then the lanes sharing a column are added
+// by a butterfly.  Lane l ends with the warp's sum of column l >> (5 - LP).  On GB300 a warp-wide
+// FP64 add holds the FP64 pipe as long as an FMA, so this costs about P adds against 5 P for a
+// shuffle tree per column.
+template <int LP>
+__device__ __forceinline__ double warp_colsum(double *a, int lane) {
+    constexpr int P = 1 << LP;
+#pragma unroll
+    for (int st = 0; st < LP; ++st) {
+        const int o = 16 >> st;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int q = 0; q < (P >> (st + 1)); ++q) {
+            const int hf = P >> (st + 1);
+            const double send = up ? a[q] : a[q + hf];
+            const double keep = up ? a[q + hf] : a[q];
+            a[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    double v = a[0];
+#pragma unroll
+    for (int o = 16 >> LP; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// A pass's element loop and its warp sums with NQ columns compiled in; red[wid][c] receives the
+// warp's sum of column c (columns nc..P-1 carry zeros)
+template <int PASS, int NQ>
+__device__ __forceinline__ void cgs_pass(int64_t i0, int64_t i1, int64_t step, int64_t nb, const double *V, int nc,
+                                         double *w, const double *scoef, double (*red)[kMaxC], int lane, int wid) {
+    constexpr bool NORM = PASS == PASS_UPD_NORM || PASS == PASS_NORM;
+    constexpr int LP = NORM ? 0 : (NQ <= 4 ? 2 : NQ <= 8 ? 3 : NQ <= 16 ? 4 : 5);
+    constexpr int SH = 5 - LP;
+    double acc[1 << LP];
+#pragma unroll
+    for (int q = 0; q < (1 << LP); ++q) acc[q] = 0.0;
+    cgs_elements<PASS, NQ>(i0, i1, step, nb, V, nc, w, scoef, acc);
+    const double v = warp_colsum<LP>(acc, lane);
+    if ((lane & ((1 << SH) - 1)) == 0) red[wid][lane >> SH] = v;
+}
+
+// NQ = nc rounded up to a multiple of 4: the columns past nc are predicated off, and a
+// predicated-off FP64 instruction still takes its turn on the pipe
 template <int PASS>
 __device__ __forceinline__ void cgs_dispatch(int64_t i0, int64_t i1, int64_t step, int64_t nb, const double *V, int nc,
-                                             double *w, const double *scoef, double *acc) {
+                                             double *w, const double *scoef, double (*red)[kMaxC], int lane, int wid) {
     constexpr bool NORM = PASS == PASS_UPD_NORM || PASS == PASS_NORM;
     constexpr bool UPD = PASS == PASS_UPD_DOT || PASS == PASS_UPD_NORM;
     if (NORM && !UPD) {
-        cgs_elements<PASS, 1>(i0, i1, step, nb, V, nc, w, scoef, acc);
+        cgs_pass<PASS, 1>(i0, i1, step, nb, V, nc, w, scoef, red, lane, wid);
         return;
     }
-    const int ng = (nc + 7) >> 3;
-    if (ng <= 1) cgs_elements<PASS, 8>(i0, i1, step, nb, V, nc, w, scoef, acc);
-    else if (ng == 2) cgs_elements<PASS, 16>(i0, i1, step, nb, V, nc, w, scoef, acc);
-    else if (ng == 3) cgs_elements<PASS, 24>(i0, i1, step, nb, V, nc, w, scoef, acc);
-    else cgs_elements<PASS, 32>(i0, i1, step, nb, V, nc, w, scoef, acc);
+    switch ((nc + 3) >> 2) {
+    case 0:
+    case 1: cgs_pass<PASS, 4>(i0, i1, step, nb, V, nc, w, scoef, red, lane, wid); break;
+    case 2: cgs_pass<PASS, 8>(i0, i1, step, nb, V, nc, w, scoef, red, lane, wid); break;
+    case 3: cgs_pass<PASS, 12>(i0, i1, step, nb, V, nc, w, scoef, red, lane, wid); break;
+    case 4: cgs_pass<PASS, 16>(i0, i1, step, nb, V, nc, w, scoef, red, lane, wid); break;
+    case 5: cgs_pass<PASS, 20>(i0, i1, step, nb, V, nc, w, scoef, red, lane, wid); break;
+    case 6: cgs_pass<PASS, 24>(i0, i1, step, nb, V, nc, w, scoef, red, lane, wid); break;
+    case 7: cgs_pass<PASS, 28>(i0, i1, step, nb, V, nc, w, scoef, red, lane, wid); break;
+    default: cgs_pass<PASS, 32>(i0, i1, step, nb, V, nc, w, scoef, red, lane, wid); break;
+    }
 }
 
 // One Gram-Schmidt pass over v_0..v_{nc-1} (columns of V, stride nb):
@@ -132,24 +183,12 @@ __global__ void __launch_bounds__(kRedThreads) k_cgs(int64_t nb, const double *_
     }
     constexpr bool UPD = PASS == PASS_UPD_DOT || PASS == PASS_UPD_NORM;
     constexpr bool NORM = PASS == PASS_UPD_NORM || PASS == PASS_NORM;
-    constexpr int NA = NORM ? 1 : kMaxC;
     if (UPD && threadIdx.x < kMaxC) scoef[threadIdx.x] = threadIdx.x < nc ? coef[threadIdx.x] : 0.0;
     __syncthreads();
-    double acc[NA];
-#pragma unroll
-    for (int q = 0; q < NA; ++q) acc[q] = 0.0;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    cgs_dispatch<PASS>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, nb, stride, nb, V, nc, w, scoef, acc);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int na = NORM ? 1 : nc;
-#pragma unroll
-    for (int q = 0; q < NA; ++q) {
-        if (q >= na) break;
-        double v = acc[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[wid][q] = v;
-    }
+    cgs_dispatch<PASS>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, nb, stride, nb, V, nc, w, scoef, red, lane, wid);
     __syncthreads();
     if (threadIdx.x < na) {
         double s = 0.0;
@@ -162,12 +201,24 @@ __global__ void __launch_bounds__(kRedThreads) k_cgs(int64_t nb, const double *_
     __syncthreads();
     if (!last) return;
     // last block: one warp per column; lane l sums blocks l, l+32, ... and the lanes are combined
-    // by a fixed shuffle tree (the same order every run)
+    // by a fixed shuffle tree (the same order every run).  A lane loads its blocks' partials
+    // before adding them, so a column costs one L2 round trip rather than one per block it sums.
     __threadfence();
     __shared__ double res[kMaxC];
+    constexpr int kPU = (kRedBlocks + 31) / 32;   // partials per lane in one batch of loads
     for (int q = wid; q < na; q += kRedThreads / 32) {
         double s = 0.0;
-        for (unsigned bb = lane; bb < gridDim.x; bb += 32) s += __ldcg(partial + (int64_t)bb * kPStride + q);
+        for (unsigned b0 = lane; b0 < gridDim.x; b0 += 32 * kPU) {
+            double pv[kPU];
+#pragma unroll
+            for (int u = 0; u < kPU; ++u) {
+                const unsigned bb = b0 + 32u * u;
+                pv[u] = bb < gridDim.x ? __ldcg(partial + (int64_t)bb * kPStride + q) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kPU; ++u)
+                if (b0 + 32u * u < gridDim.x) s += pv[u];
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) res[q] = s;
@@ -651,27 +702,15 @@ __global__ void __launch_bounds__(kRedThreads) k_bcgs(int64_t nb, const double *
     const int j = ks->k, nc = j + 1;
     constexpr bool UPD = PASS == PASS_UPD_DOT || PASS == PASS_UPD_NORM;
     constexpr bool NORM = PASS == PASS_UPD_NORM || PASS == PASS_NORM;
-    constexpr int NA = NORM ? 1 : kMaxC;
     if (UPD && threadIdx.x < kMaxC) {
         const double *coef = reinterpret_cast<const double *>(reinterpret_cast<const char *>(ks) + coef_off);
         scoef[threadIdx.x] = threadIdx.x < nc ? coef[threadIdx.x] : 0.0;
     }
     __syncthreads();
-    double acc[NA];
-#pragma unroll
-    for (int q = 0; q < NA; ++q) acc[q] = 0.0;
     const int64_t beg = tile_beg[blockIdx.x], end = tile_beg[blockIdx.x + 1];
-    cgs_dispatch<PASS>(beg + threadIdx.x, end, blockDim.x, nb, V, nc, w, scoef, acc);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int na = NORM ? 1 : nc;
-#pragma unroll
-    for (int q = 0; q < NA; ++q) {
-        if (q >= na) break;
-        double v = acc[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[wid][q] = v;
-    }
+    cgs_dispatch<PASS>(beg + threadIdx.x, end, blockDim.x, nb, V, nc, w, scoef, red, lane, wid);
     __syncthreads();
     if (threadIdx.x < na) {
         double sum = 0.0;
@@ -686,9 +725,18 @@ __global__ void __launch_bounds__(kRedThreads) k_bcgs(int64_t nb, const double *
     if (!last) return;
     __threadfence();
     __shared__ double res[kMaxC];
+    constexpr int kPU = 8;   // partials per lane in one batch of loads (then added in block order)
     for (int q = wid; q < na; q += kRedThreads / 32) {
         double sum = 0.0;
-        for (int bb = t0 + lane; bb < t1; bb += 32) sum += __ldcg(partial + (int64_t)bb * kPStride + q);
+        for (int b0 = t0 + lane; b0 < t1; b0 += 32 * kPU) {
+            double pv[kPU];
+#pragma unroll
+            for (int u = 0; u < kPU; ++u)
+                pv[u] = b0 + 32 * u < t1 ? __ldcg(partial + (int64_t)(b0 + 32 * u) * kPStride + q) : 0.0;
+#pragma unroll
+            for (int u = 0; u < kPU; ++u)
+                if (b0 + 32 * u < t1) sum += pv[u];
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
         if (lane == 0) res[q] = sum;
