@@ -1167,8 +1167,11 @@ __global__ void __launch_bounds__(64) k_bilu_factor_sf(int32_t n, unsigned *tick
 // [D | I] (lanes r >= B only take part in the shuffles): Gauss-Jordan with partial pivoting, the
 // same operations and order as block_inverse (largest |d_rk| among the remaining rows, lowest row
 // on ties; the pivot row times 1 / pivot; every other row minus its multiple of the pivot row).
-// The rows are not moved: each lane keeps the index of the row it holds.  Returns false if
-// singular (the block is then left as it was).
+// The rows are not moved: each lane keeps the index of the row it holds.  The pivot search
+// compares the bit patterns of |d_rk| as integers (for non-negative doubles their order is the
+// numeric order), so it takes no turn on the FP64 pipe; a NaN candidate makes the block singular.
+// Returns false if singular (the block is then left as it was).
+constexpr long long kInfBits = 0x7ff0000000000000LL;   // bit pattern of +inf
 template <int B>
 __device__ __forceinline__ bool group_inverse(double *blk, int r, unsigned gmask, int g0) {
     double a[2 * B];
@@ -1180,15 +1183,15 @@ __device__ __forceinline__ bool group_inverse(double *blk, int r, unsigned gmask
 #pragma unroll
     for (int k = 0; k < B; ++k) {
         const bool cand = r < B && ri >= k;
-        double v = cand ? fabs(a[k]) : -1.0;
+        long long v = cand ? __double_as_longlong(fabs(a[k])) : -1LL;
         int idx = cand ? ri : 0x7fffffff;
 #pragma unroll
         for (int o = 1; o < kSfGroup; o <<= 1) {
-            const double ov = __shfl_xor_sync(gmask, v, o);
+            const long long ov = __shfl_xor_sync(gmask, v, o);
             const int oi = __shfl_xor_sync(gmask, idx, o);
             if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
         }
-        if (!(v > 0.0)) return false;
+        if (!(v > 0 && v <= kInfBits)) return false;
         const int p = idx;
         if (r < B) {
             if (ri == k) ri = p;
@@ -1215,6 +1218,59 @@ __device__ __forceinline__ bool group_inverse(double *blk, int r, unsigned gmask
 #pragma unroll
         for (int q = 0; q < B; ++q) blk[ri * B + q] = a[B + q];
     (void)g0;
+    return true;
+}
+
+// The same inverse by a whole warp, one lane per entry of [D | I]: lane s * 2B + q holds entry q of
+// the row that started in slot s (2 B^2 lanes; the others only take part in the shuffles), and
+// every lane keeps the positions of all B rows, updated alike.  Each entry gets the operations of
+// block_inverse in the same order (the pivot row times 1 / pivot, every other row minus f times the
+// scaled pivot row), so the inverse is the same bit for bit.  On GB300 a warp-wide FP64 instruction
+// holds the sub-partition's pipe for 64 cycles: a step issues the reciprocal, one multiply and one
+// FMA, against B and 2B of them with a row per lane.  Returns false if singular (the same in every
+// lane; the block is then left as it was).
+template <int B>
+__device__ __forceinline__ bool warp_inverse(double *blk, int lane) {
+    constexpr int W2 = 2 * B;
+    constexpr unsigned kAll = 0xffffffffu;
+    const bool act = lane < B * W2;
+    const int s = act ? lane / W2 : 0, q = act ? lane - s * W2 : 0;
+    double a = 0.0;
+    if (act) a = q < B ? blk[s * B + q] : (q - B == s ? 1.0 : 0.0);
+    int ri[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) ri[u] = u;
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+        // largest |d_rk| among the rows at positions >= k, lowest position on ties
+        const long long mine = __double_as_longlong(fabs(a));
+        long long best = -1LL;
+        int p = 0x7fffffff;
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const long long v = __shfl_sync(kAll, mine, u * W2 + k);
+            if (ri[u] >= k && (v > best || (v == best && ri[u] < p))) { best = v; p = ri[u]; }
+        }
+        if (!(best > 0 && best <= kInfBits)) return false;
+        int ps = 0;   // the slot whose row moves to position k
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            if (ri[u] == k) ri[u] = p;
+            else if (ri[u] == p) ri[u] = k;
+            if (ri[u] == k) ps = u;
+        }
+        const double d = 1.0 / __shfl_sync(kAll, a, ps * W2 + k);
+        const double f = __shfl_sync(kAll, a, s * W2 + k);
+        if (act && s == ps) a *= d;
+        const double pr = __shfl_sync(kAll, a, ps * W2 + q);
+        if (act && s != ps) a = fma(-f, pr, a);
+    }
+    int rs = 0;   // the final position of this lane's row (a select chain keeps ri in registers)
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+        if (u == s) rs = ri[u];
+    __syncwarp();
+    if (act && q >= B) blk[rs * B + (q - B)] = a;
     return true;
 }
 
@@ -1387,10 +1443,10 @@ __global__ void __launch_bounds__(kSfThreads) k_bilu_factor_g(int32_t n, unsigne
 // The factorisation with a row per warp.  On GB300 a warp-wide FP64 instruction occupies a
 // sub-partition's FP64 pipe for 64 cycles, so a level's time is bounded by the FP64 instructions
 // the warp holding a row issues: here every block product is spread over the lanes (one lane per
-// entry of L_ik = A_ik D_k^{-1}, one per entry of each updated block A_ij -= L_ik U_kj), about 40
-// FP64 instructions per row of a 7-point 3 x 3 pattern instead of ~150 with a row over four lanes.
-// Each entry is summed in the order of k_bilu_factor_sf (the same values), and four lanes invert
-// the pivot block together (group_inverse).  Warps take rows by ticket in level order, so every
+// entry of L_ik = A_ik D_k^{-1}, one per entry of each updated block A_ij -= L_ik U_kj: six FP64
+// instructions per dependency of a 3 x 3 row), and so is the pivot inverse (warp_inverse: per
+// pivot step a reciprocal, one multiply and one FMA).  Each entry is summed in the order of
+// k_bilu_factor_sf (the same values).  Warps take rows by ticket in level order, so every
 // dependency belongs to a warp that is already running.  Before the flags are set: the row's own
 // blocks and columns, the pivot and row-end positions of its dependencies and the column indices
 // of their upper parts (none written during the launch).  Once every flag is set and an acquire
@@ -1514,9 +1570,7 @@ __global__ void __launch_bounds__(32 * kFwWarps) k_bilu_factor_w(int32_t n, unsi
             }
             __syncwarp();
         }
-        if (lane < 4) {
-            if (!group_inverse<B>(rowb + nd * BB, lane, 0xFu, 0) && lane == 0) atomicOr(singular, 1);
-        }
+        if (!warp_inverse<B>(rowb + nd * BB, lane) && lane == 0) atomicOr(singular, 1);
         __syncwarp();
         for (int32_t u = nd * BB + lane; u < len * BB; u += 32) LU[(int64_t)k0 * BB + u] = rowb[u];
         // the warp barrier orders every lane's stores before lane 0's release store, which
