@@ -178,6 +178,50 @@ def test_ilu(name):
     assert relerr(host(z), o.ilu_apply(r)) <= 1e-10
 
 
+def _shuffled_blocks(n, b, seed):
+    """Well-conditioned b x b blocks ((b + 1) I + uniform(-1, 1)) with their rows shuffled per
+    cell, so that partial pivoting exchanges rows; every fourth block has an exact tie of
+    magnitudes (2 and -2) between the first two candidates of its first pivot step."""
+    rng = np.random.default_rng(seed)
+    D = np.empty((n, b, b))
+    for i in range(n):
+        while True:
+            m = rng.uniform(-1.0, 1.0, (b, b)) + (b + 1.0) * np.eye(b)
+            m = m[rng.permutation(b)]
+            if i % 4 == 0:
+                m[0, 0], m[1, 0] = 2.0, -2.0
+                m[2:, 0] = rng.uniform(-1.0, 1.0, b - 2)
+            if np.linalg.cond(m) < 1e2:
+                break
+        D[i] = m
+    return D
+
+
+@pytest.mark.parametrize("b", [3, 4])
+def test_pivot_inverses_with_row_exchanges(b):
+    """ILU(0) of a block-diagonal matrix is its pivot inverses, so an ILU application gives
+    D_i^{-1} r_i.  The blocks need row exchanges (and every fourth one breaks a tie by the lowest
+    position).  512 cells, one narrow level, take the row-per-warp factorisation and its warp-wide
+    inverse; 4096 cells take the four-lane factorisation.  Both match numpy's solve, and they
+    agree bit for bit on the cells they share: the same pivots, ties and operations."""
+    kind = system("parity" if b == 3 else "three_phase")["unknown_kind"]
+    Dall = _shuffled_blocks(4096, b, 41)
+    rall = synth.normal(43, 4096 * b)
+    out = {}
+    for n in (512, 4096):
+        D, r = Dall[:n], rall[:n * b]
+        S = cp.Solver(stage1=cp.STAGE1["none"])
+        S.setup(n, b, dev(np.arange(n + 1, dtype=np.int32)), dev(np.arange(n, dtype=np.int32)),
+                dev(D.reshape(-1)), dev(kind))
+        z = torch.empty(n * b, dtype=torch.float64, device="cuda")
+        cp.cptr_apply_ilu(S.ctx, dev(r), z)
+        ref = np.linalg.solve(D, r.reshape(n, b, 1))[..., 0].reshape(-1)
+        assert relerr(host(z), ref) <= 1e-13, (n, relerr(host(z), ref))
+        out[n] = host(z)
+        S.close()
+    assert np.array_equal(out[512], out[4096][:512 * b])
+
+
 @pytest.mark.parametrize("mode", ["full", "upper", "lower", "bd", "cpr", "none"])
 def test_stage1_and_precond(mode):
     s, o, g = pair("parity", stage1=cp.STAGE1[mode])
