@@ -36,7 +36,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 LEARNED_STEPS, LEARNED_LR = 2000, 2e-3
 # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/ (the
 # current kernels; None where no capture of the current code exists)
-PROFILED_TRAFFIC = {"spmv": 113_717_248, "stage1_resid": None, "ilu_fwd": 102_481_408, "ilu_bwd": 123_192_064,
+PROFILED_TRAFFIC = {"spmv": 113_717_248, "stage1_resid": None, "ilu_fwd": 102_685_952, "ilu_bwd": 122_592_512,
                     # the finest V-cycle level of the pressure hierarchy (cold-L2 captures, one launch each)
                     "vcycle_p_down": 20_470_528, "vcycle_p_restrict": 6_354_944, "vcycle_p_prolong": 7_413_760,
                     "vcycle_p_post": 22_069_504, "vcycle_p_down_mixed": 13_381_120,

@@ -336,6 +336,7 @@ struct SweepLane {
     T s;
     unsigned long long t0;
     bool waiting;
+    int32_t nw;      // rounds waited (the bounded wait reads the clock every eighth round)
     int32_t nrows;   // bound of the dependency positions (index checks)
 };
 
@@ -373,10 +374,12 @@ __device__ __forceinline__ bool sweep_round(SweepLane<B, T, DG> &L, int q4, int 
         if (!L.waiting) {
             L.t0 = gtimer();
             L.waiting = true;
-        } else {
+            L.nw = 0;
+        } else if ((++L.nw & 7) == 0) {
             late = gtimer() - L.t0 > kWaitNs;
         }
-        if (__any_sync(gmask, late)) {   // the bounded wait gives up: missing values count as 0
+        // (the lanes of a group count the same rounds, so they all take part in the vote or none)
+        if ((L.nw & 7) == 0 && __any_sync(gmask, late)) {   // the bounded wait gives up: missing values count as 0
             atomicExch(&ks->wait_err, 1);
 #pragma unroll
             for (int g = 0; g < DG; ++g)
@@ -466,7 +469,7 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_g(int32_t n, unsigned *t
                 store_relaxed(y + (int64_t)t * B + q4, L.s);
                 done = true;
             }
-            if (__any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
+            if (sleep_ns > 0 && __any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
         }
     }
 }
@@ -540,9 +543,21 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_g(int32_t n, unsigned *t
                 out[(int64_t)row * B + q4] = (double)a + add;
                 done = true;
             }
-            if (__any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
+            if (sleep_ns > 0 && __any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
         }
     }
+}
+
+// Whether a row of the warp is ready (every lane of its LPR-lane segment has voted in hv) and not
+// yet done (dm: the lanes whose row is done; a row's lanes are done together), from the two
+// ballots alone: after the shifts, bit g LPR of x is set iff segment g of hv is full.
+template <int LPR>
+__device__ __forceinline__ bool ready_rows(unsigned hv, unsigned dm) {
+    constexpr unsigned kFirst = LPR == 32 ? 1u : LPR == 16 ? 0x00010001u : LPR == 8 ? 0x01010101u : 0x11111111u;
+    unsigned x = hv;
+#pragma unroll
+    for (int o = 1; o < LPR; o <<= 1) x &= x >> o;
+    return (x & ~dm & kFirst) != 0u;
 }
 
 // The same sweeps with a row over 4H lanes, H parts of four (H = 2 or 4): part h subtracts the
@@ -590,7 +605,10 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_h(int32_t n, unsigned *t
             if (L.sl0 < L.o1) sweep_stage<B, T, DG, H>(L, q4, lane, col, val, y);
             else half = true;
         }
-        while (__any_sync(0xffffffffu, !done)) {
+        // votes per round: the parts' progress and the rows' completion (two ballots), from which
+        // every lane also derives whether a row of the warp is ready (ready_rows)
+        unsigned dm = __ballot_sync(0xffffffffu, done);
+        while (dm != 0xffffffffu) {
             bool pend = false;
             if (!half && sweep_round<B, T, DG, H>(L, q4, lane, gmask, g0, col, val, y, ks, &pend)) half = true;
             // a row is ready once all of its lanes have voted; part 0 stores the parts' sum
@@ -598,14 +616,15 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_fwd_h(int32_t n, unsigned *t
             const bool ready = !done && ((hv >> gr) & RMASK) == RMASK;
             // the parts' sum only in rounds where a row of the warp is ready: an FP64 add issued by
             // every polling warp in every round would hold the FP64 pipe the ready rows need
-            if (__any_sync(0xffffffffu, ready)) {
+            if (ready_rows<LPR>(hv, dm)) {
                 T sum = L.s;
 #pragma unroll
                 for (int o = kSfGroup; o < LPR; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
                 if (ready && !idle && h == 0) store_relaxed(y + (int64_t)t * B + q4, sum);
             }
             if (ready) done = true;
-            if (__any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
+            if (sleep_ns > 0 && __any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
+            dm = __ballot_sync(0xffffffffu, done);
         }
     }
 }
@@ -664,12 +683,13 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_h(int32_t n, unsigned *t
             if (L.sl0 < L.o1) sweep_stage<B, T, DG, H>(L, q4, lane, col, val, z);
             else half = true;
         }
-        while (__any_sync(0xffffffffu, !done)) {
+        unsigned dm = __ballot_sync(0xffffffffu, done);
+        while (dm != 0xffffffffu) {
             bool pend = false;
             if (!half && sweep_round<B, T, DG, H>(L, q4, lane, gmask, g0, col, val, z, ks, &pend)) half = true;
             const unsigned hv = __ballot_sync(0xffffffffu, half);
             const bool ready = !done && ((hv >> gr) & RMASK) == RMASK;
-            if (__any_sync(0xffffffffu, ready)) {   // (the parts' sum only when a row is ready)
+            if (ready_rows<LPR>(hv, dm)) {   // (the parts' sum only when a row is ready)
                 T sum = L.s;
 #pragma unroll
                 for (int o = kSfGroup; o < LPR; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -679,7 +699,8 @@ __global__ void __launch_bounds__(kSfThreads) k_ilu_bwd_h(int32_t n, unsigned *t
                 }
             }
             if (ready) done = true;
-            if (__any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
+            if (sleep_ns > 0 && __any_sync(0xffffffffu, pend)) __nanosleep(sleep_ns);
+            dm = __ballot_sync(0xffffffffu, done);
         }
     }
 }
