@@ -378,8 +378,9 @@ __device__ __forceinline__ bool sweep_round(SweepLane<B, T, DG> &L, int q4, int 
         } else if ((++L.nw & 7) == 0) {
             late = gtimer() - L.t0 > kWaitNs;
         }
-        // (the lanes of a group count the same rounds, so they all take part in the vote or none)
-        if ((L.nw & 7) == 0 && __any_sync(gmask, late)) {   // the bounded wait gives up: missing values count as 0
+        // the bounded wait gives up: missing values count as 0 (the lanes of a group count the same
+        // rounds, so they all take part in the vote or none)
+        if ((L.nw & 7) == 0 && __any_sync(gmask, late)) {
             atomicExch(&ks->wait_err, 1);
 #pragma unroll
             for (int g = 0; g < DG; ++g)
@@ -1248,7 +1249,7 @@ __device__ __forceinline__ bool group_inverse(double *blk, int r, unsigned gmask
 // block_inverse in the same order (the pivot row times 1 / pivot, every other row minus f times the
 // scaled pivot row), so the inverse is the same bit for bit.  On GB300 a warp-wide FP64 instruction
 // holds the sub-partition's pipe for 64 cycles: a step issues the reciprocal, one multiply and one
-// FMA, against B and 2B of them with a row per lane.  Returns false if singular (the same in every
+// FMA, against 2B multiplies and 2B FMAs with a row per lane.  Returns false if singular (the same in every
 // lane; the block is then left as it was).
 template <int B>
 __device__ __forceinline__ bool warp_inverse(double *blk, int lane) {
